@@ -1,0 +1,739 @@
+/*
+ * dcem_oracle.c -- plain, slow, brute-force FP64 CPU oracle of the dynamic
+ * coherence-based EM ray tracer (DCEM, arXiv 2112.07115).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library. It shares no code,
+ * header, table or constant with the CUDA path.
+ *
+ * What it computes, in the paper's order (Sec. III "Backward ray tracing",
+ * steps 1-4 and 6; Eq. 1-3 for the field):
+ *   or_transform   rigid transform of moving objects' vertices (per-frame
+ *                  update of the scene, Sec. III "Efficient BVH updating"),
+ *                  evaluated as fmaf(R0,x, fmaf(R1,y, fmaf(R2,z,t))) in FP32.
+ *   or_trace       step 1-2: shoot every ray of the sampled sphere, find the
+ *                  closest hit against ALL triangles (no acceleration
+ *                  structure), reflect specularly up to N times, and record
+ *                  every reception-sphere capture (ray, segment, receiver).
+ *   or_validate    steps 3-4 and 6: image-receiver chain through the planes
+ *                  of a triangle sequence, back-trace, point-in-triangle and
+ *                  occlusion tests, then length, delay, Fresnel TE/TM
+ *                  reflection with vector polarisation and complex amplitude
+ *                  (ray field of Eq. 1 with the free-space loss of Eq. 3).
+ *   or_exhaustive  every triangle sequence of length <= N validated by the
+ *                  image method (no sampling): the complete valid path set.
+ *   or_fresnel     Fresnel reflection coefficients.
+ *
+ * Everything after the FP32 inputs is FP64. Decisions that FP32 arithmetic
+ * could take differently (a ray passing within a margin of a triangle edge,
+ * two hits at almost equal distance, a receiver on the capture-sphere
+ * boundary, an occluder near a sub-segment end) are FLAGGED here so that
+ * callers can exclude them from bit-exact comparisons.
+ *
+ * Build: gcc -O2 -ffp-contract=off -shared -fPIC -pthread dcem_oracle.c -lm
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define OR_MAX_REFL 10
+
+/* ray / path flag bits */
+#define ORF_NEAR_EDGE 1u     /* a triangle's in/out decision is within the margin */
+#define ORF_TIE 2u           /* two hit candidates at nearly equal distance       */
+#define ORF_NEAR_TMIN 4u     /* a hit candidate near the self-hit offset t_min    */
+#define ORF_NEAR_SPHERE 8u   /* a receiver near its capture-sphere boundary       */
+#define ORF_VAL_EDGE 16u     /* a reflection point near its triangle's boundary   */
+#define ORF_VAL_PARAM 32u    /* back-trace parameter near 0 or 1                  */
+#define ORF_OCC_NEAR 64u     /* an occlusion decision within the margin           */
+#define ORF_POL_DEGEN 128u   /* polarisation reference parallel to a path end     */
+
+typedef struct { double x, y, z; } v3;
+
+static inline v3 mk(double x, double y, double z) { v3 r = {x, y, z}; return r; }
+static inline v3 add(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static inline v3 sub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static inline v3 scl(v3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static inline double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static inline v3 cross(v3 a, v3 b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static inline double norm(v3 a) { return sqrt(dot(a, a)); }
+static inline v3 unit(v3 a) { return scl(a, 1.0 / norm(a)); }
+static inline double maxabs(v3 a) { return fmax(fabs(a.x), fmax(fabs(a.y), fabs(a.z))); }
+
+/* ------------------------------------------------------------------------ */
+/* parameters (the oracle's own copy; the CUDA path has its own struct)      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double freq_hz;          /* carrier frequency                                */
+  double tx_power_w;       /* transmit power (Sec. III: 5 W outdoor)           */
+  double alpha;            /* angular ray spacing sqrt(4 pi / n_rays)          */
+  double rx_radius_scale;  /* capture radius = scale * alpha * (D + s) / sqrt 3 */
+  double t_min;            /* self-hit offset after a reflection [m]           */
+  double escape_len;       /* length of an escaping segment for capture [m]    */
+  double eps_occ;          /* occlusion tests ignore (0,eps) and (1-eps,1)     */
+  double edge_eps;         /* relative flag margin for FP32 decisions          */
+  double val_eps;          /* relative flag margin for FP64 validation         */
+  double pol[3];           /* antenna polarisation reference vector u          */
+  int32_t max_refl;        /* N reflections                                    */
+  int32_t nthreads;        /* 0 = all cores                                     */
+} or_params;
+
+/* ------------------------------------------------------------------------ */
+/* scene: FP32 world triangles widened to FP64                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  v3 v[3];
+  v3 n;       /* (v1-v0) x (v2-v0) */
+  v3 nh;      /* unit normal */
+  v3 e[3];    /* edges v0->v1, v1->v2, v2->v0 */
+  double elen[3];
+  int mat;
+} otri;
+
+typedef struct {
+  int ntri;
+  otri* t;
+  const float* mats;  /* nmat x 3: eps_r, sigma, pec */
+  int nmat;
+} oscene;
+
+static int scene_load(oscene* s, const float* tris, const int32_t* tri_mat, int ntri,
+                      const float* mats, int nmat) {
+  s->ntri = ntri;
+  s->mats = mats;
+  s->nmat = nmat;
+  s->t = (otri*)calloc((size_t)(ntri > 0 ? ntri : 1), sizeof(otri));
+  if (!s->t) return -1;
+  for (int i = 0; i < ntri; ++i) {
+    otri* T = &s->t[i];
+    for (int k = 0; k < 3; ++k)
+      T->v[k] = mk(tris[9 * i + 3 * k], tris[9 * i + 3 * k + 1], tris[9 * i + 3 * k + 2]);
+    T->e[0] = sub(T->v[1], T->v[0]);
+    T->e[1] = sub(T->v[2], T->v[1]);
+    T->e[2] = sub(T->v[0], T->v[2]);
+    for (int k = 0; k < 3; ++k) T->elen[k] = norm(T->e[k]);
+    T->n = cross(sub(T->v[1], T->v[0]), sub(T->v[2], T->v[0]));
+    double nn = norm(T->n);
+    T->nh = nn > 0 ? scl(T->n, 1.0 / nn) : mk(0, 0, 0);
+    T->mat = tri_mat ? tri_mat[i] : 0;
+  }
+  return 0;
+}
+
+static void scene_free(oscene* s) { free(s->t); }
+
+static int default_threads(int req) {
+  if (req > 0) return req;
+  long n = sysconf(_SC_NPROCESSORS_ONLN);
+  return n > 0 ? (int)n : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A1: rigid transform of the moving objects' vertices                      */
+/* ------------------------------------------------------------------------ */
+/* x' = R0.x*x + R0.y*y + R0.z*z + t0, evaluated innermost-first with
+ * correctly rounded fused multiply-adds (C99 fmaf) in FP32. */
+void or_transform(int32_t ntri, const float* tris_in, const int32_t* tri_obj,
+                  const float* xf, int32_t nobj, float* tris_out) {
+  for (int i = 0; i < ntri; ++i) {
+    int o = tri_obj ? tri_obj[i] : -1;
+    for (int k = 0; k < 3; ++k) {
+      const float* p = &tris_in[9 * i + 3 * k];
+      float* q = &tris_out[9 * i + 3 * k];
+      if (o < 0 || o >= nobj) {
+        q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        continue;
+      }
+      const float* m = &xf[12 * o];
+      for (int r = 0; r < 3; ++r)
+        q[r] = fmaf(m[4 * r + 0], p[0], fmaf(m[4 * r + 1], p[1], fmaf(m[4 * r + 2], p[2], m[4 * r + 3])));
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fresnel reflection (eps_c = eps_r - j sigma / (omega eps0), exp(+j w t))   */
+/* ------------------------------------------------------------------------ */
+static const double EPS0 = 8.8541878128e-12;
+static const double C0 = 299792458.0;
+
+/* Gamma_TE, Gamma_TM at incidence cos(theta) = cos_t for a half-space of
+ * relative permittivity eps_r and conductivity sigma; pec selects the perfect
+ * conductor limits (-1, +1). */
+static void fresnel64(double eps_r, double sigma, int pec, double freq, double cos_t,
+                      double complex* g_te, double complex* g_tm) {
+  if (pec) {
+    *g_te = -1.0;
+    *g_tm = 1.0;
+    return;
+  }
+  double complex ec = eps_r - I * (sigma / (2.0 * M_PI * freq * EPS0));
+  double sin2 = 1.0 - cos_t * cos_t;
+  double complex root = csqrt(ec - sin2);
+  *g_te = (cos_t - root) / (cos_t + root);
+  *g_tm = (ec * cos_t - root) / (ec * cos_t + root);
+}
+
+/* material row (eps_r, sigma, pec) as stored in FP32 */
+static void fresnel(const float* mat, double freq, double cos_t, double complex* g_te,
+                    double complex* g_tm) {
+  fresnel64((double)mat[0], (double)mat[1], mat[2] != 0.0f, freq, cos_t, g_te, g_tm);
+}
+
+void or_fresnel(double eps_r, double sigma, int32_t pec, double freq, double cos_t,
+                double* out4) {
+  float m[3] = {(float)eps_r, (float)sigma, (float)pec};
+  double complex te, tm;
+  fresnel(m, freq, cos_t, &te, &tm);
+  out4[0] = creal(te); out4[1] = cimag(te);
+  out4[2] = creal(tm); out4[3] = cimag(tm);
+}
+
+/* Same with eps_r, sigma taken at full double precision (closed-form pins). */
+void or_fresnel64(double eps_r, double sigma, int32_t pec, double freq, double cos_t,
+                  double* out4) {
+  double complex te, tm;
+  fresnel64(eps_r, sigma, pec != 0, freq, cos_t, &te, &tm);
+  out4[0] = creal(te); out4[1] = cimag(te);
+  out4[2] = creal(tm); out4[3] = cimag(tm);
+}
+
+/* ------------------------------------------------------------------------ */
+/* ray vs triangle, exact definition: the ray line passes through the        */
+/* triangle iff the three signed volumes d.((P-o)x(Q-o)) of its edges share  */
+/* a sign; the hit distance is the plane crossing. No back-face culling.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double t;       /* plane crossing parameter (NAN if parallel) */
+  int inside;     /* ray line passes through the closed triangle */
+  int flippable;  /* a perturbation of the ray by `delta` could change `inside` */
+  double cos_t;   /* |d . n^| */
+} xinfo;
+
+/* delta: ray-line displacement budget at the crossing. */
+static void ray_tri(const otri* T, v3 o, v3 d, double delta_base, double delta_slope, xinfo* x) {
+  double dn = dot(d, T->n);
+  x->cos_t = T->elen[0] > 0 ? fabs(dot(d, T->nh)) : 0.0;
+  if (dn == 0.0 || !(norm(T->n) > 0)) {
+    x->t = NAN; x->inside = 0; x->flippable = 0;
+    return;
+  }
+  x->t = dot(sub(T->v[0], o), T->n) / dn;
+  double delta = delta_base + delta_slope * fabs(x->t);
+  v3 a = sub(T->v[0], o), b = sub(T->v[1], o), c = sub(T->v[2], o);
+  double E[3];
+  E[0] = dot(d, cross(a, b));
+  E[1] = dot(d, cross(b, c));
+  E[2] = dot(d, cross(c, a));
+  int pos = (E[0] >= 0) && (E[1] >= 0) && (E[2] >= 0);
+  int neg = (E[0] <= 0) && (E[1] <= 0) && (E[2] <= 0);
+  x->inside = (pos || neg) && !(E[0] == 0 && E[1] == 0 && E[2] == 0);
+  /* line distance between the ray and edge k: |E_k| / |d x e_k| (d unit, so
+   * |d x e_k| <= |e_k|: when |E_k| >= delta |e_k| the edge is surely farther
+   * than delta and the exact distance is not needed). */
+  double dist[3];
+  for (int k = 0; k < 3; ++k) {
+    if (fabs(E[k]) >= delta * T->elen[k]) { dist[k] = INFINITY; continue; }
+    double den = norm(cross(d, T->e[k]));
+    dist[k] = den > 0 ? fabs(E[k]) / den : INFINITY;
+  }
+  if (x->inside) {
+    x->flippable = (dist[0] < delta) || (dist[1] < delta) || (dist[2] < delta);
+  } else {
+    int to_pos = 1, to_neg = 1;
+    for (int k = 0; k < 3; ++k) {
+      if (E[k] < 0 && !(dist[k] < delta)) to_pos = 0;
+      if (E[k] > 0 && !(dist[k] < delta)) to_neg = 0;
+    }
+    x->flippable = to_pos || to_neg;
+  }
+}
+
+/* Closest hit of the ray (o, d unit) over all triangles except `excl`, with
+ * t > t_min; ties in t go to the lowest triangle id. Sets flag bits. */
+static int closest_hit(const oscene* S, v3 o, v3 d, double D, int excl, const or_params* P,
+                       xinfo* xs, double* t_out, double* cos_out, uint32_t* flags) {
+  double base = P->edge_eps * (maxabs(o) + D);
+  double slope = P->edge_eps;
+  int best = -1;
+  double bt = INFINITY;
+  for (int j = 0; j < S->ntri; ++j) {
+    if (j == excl) { xs[j].t = NAN; xs[j].inside = 0; xs[j].flippable = 0; continue; }
+    ray_tri(&S->t[j], o, d, base, slope, &xs[j]);
+    if (xs[j].inside && xs[j].t > P->t_min) {
+      if (xs[j].t < bt) { bt = xs[j].t; best = j; }
+    }
+  }
+  /* flags */
+  double dtb = 0;
+  if (best >= 0) dtb = (base + slope * bt) / fmax(xs[best].cos_t, 1e-6);
+  for (int j = 0; j < S->ntri; ++j) {
+    if (j == excl || isnan(xs[j].t)) continue;
+    if (!(xs[j].inside || xs[j].flippable)) continue;
+    double dt = (base + slope * fabs(xs[j].t)) / fmax(xs[j].cos_t, 1e-6);
+    if (xs[j].t < P->t_min - dt) continue;
+    if (best >= 0 && xs[j].t > bt + dt + dtb) continue;
+    if (xs[j].flippable) *flags |= ORF_NEAR_EDGE;
+    if (fabs(xs[j].t - P->t_min) <= dt) *flags |= ORF_NEAR_TMIN;
+    if (best >= 0 && j != best && fabs(xs[j].t - bt) <= dt + dtb) *flags |= ORF_TIE;
+  }
+  *t_out = bt;
+  *cos_out = best >= 0 ? xs[best].cos_t : 0;
+  return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* or_trace: SBR shooting of all rays (steps 1-2)                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t ray, seg, rx;
+} ocand;
+
+typedef struct {
+  ocand* c;
+  long n, cap;
+} cvec;
+
+static int cpush(cvec* v, int ray, int seg, int rx) {
+  if (v->n == v->cap) {
+    long nc = v->cap ? 2 * v->cap : 1024;
+    ocand* p = (ocand*)realloc(v->c, (size_t)nc * sizeof(ocand));
+    if (!p) return -1;
+    v->c = p; v->cap = nc;
+  }
+  v->c[v->n].ray = ray; v->c[v->n].seg = seg; v->c[v->n].rx = rx;
+  v->n++;
+  return 0;
+}
+
+typedef struct {
+  const oscene* S;
+  const or_params* P;
+  v3 tx;
+  const float* rays;
+  int nrays;
+  const float* rx;
+  int nrx;
+  int32_t* hit_id;    /* nrays x (N+1) */
+  double* hit_t;      /* nrays x (N+1) */
+  int32_t* nseg;      /* nrays */
+  uint32_t* flags;    /* nrays */
+  double* seg_od;     /* optional nrays x (N+1) x 7: o, d, D */
+  atomic_long next;
+  cvec* cv;           /* per thread */
+  int err;
+} trace_job;
+
+typedef struct { trace_job* J; int tid; } targ;
+
+static void trace_one(trace_job* J, int i, xinfo* xs, cvec* cv) {
+  const or_params* P = J->P;
+  int N = P->max_refl, W = N + 1;
+  v3 o = J->tx;
+  v3 d = unit(mk(J->rays[3 * i], J->rays[3 * i + 1], J->rays[3 * i + 2]));
+  double D = 0;
+  int last = -1;
+  uint32_t fl = 0;
+  double ae = P->rx_radius_scale * P->alpha / sqrt(3.0);
+  for (int b = 0; b <= N; ++b) {
+    double t, ct;
+    int id = closest_hit(J->S, o, d, D, last, P, xs, &t, &ct, &fl);
+    double tend = id >= 0 ? t : P->escape_len;
+    double base = P->edge_eps * (maxabs(o) + D);
+    double dtb = id >= 0 ? (base + P->edge_eps * t) / fmax(ct, 1e-6) : 0.0;
+    if (J->seg_od) {
+      double* q = &J->seg_od[((size_t)i * W + b) * 7];
+      q[0] = o.x; q[1] = o.y; q[2] = o.z; q[3] = d.x; q[4] = d.y; q[5] = d.z; q[6] = D;
+    }
+    /* reception-sphere capture of this segment */
+    for (int r = 0; r < J->nrx; ++r) {
+      v3 R = mk(J->rx[3 * r], J->rx[3 * r + 1], J->rx[3 * r + 2]);
+      v3 w = sub(R, o);
+      double s = dot(w, d);
+      int clamped = 0;
+      if (s < 0) s = 0;
+      if (s > tend) { s = tend; clamped = 1; }
+      double dist = norm(sub(w, scl(d, s)));
+      double rho = ae * (D + s);
+      double m = (base + P->edge_eps * s) * (1.0 + ae) + (clamped ? dtb * (1.0 + ae) : 0.0);
+      if (fabs(dist - rho) <= m) fl |= ORF_NEAR_SPHERE;
+      if (dist <= rho) {
+        if (cpush(cv, i, b, r)) J->err = 1;
+      }
+    }
+    J->hit_id[(size_t)i * W + b] = id;
+    J->hit_t[(size_t)i * W + b] = id >= 0 ? t : INFINITY;
+    if (id < 0) { J->nseg[i] = b + 1; break; }
+    J->nseg[i] = b + 1;
+    /* specular reflection: d' = d - 2 (d.n^) n^ */
+    const otri* T = &J->S->t[id];
+    v3 p = add(o, scl(d, t));
+    d = unit(sub(d, scl(T->nh, 2.0 * dot(d, T->nh))));
+    o = p;
+    D += t;
+    last = id;
+  }
+  for (int b = J->nseg[i]; b <= N; ++b) {
+    J->hit_id[(size_t)i * W + b] = -2;
+    J->hit_t[(size_t)i * W + b] = NAN;
+  }
+  J->flags[i] = fl;
+}
+
+static void* trace_worker(void* p) {
+  targ* a = (targ*)p;
+  trace_job* J = a->J;
+  xinfo* xs = (xinfo*)malloc(sizeof(xinfo) * (size_t)(J->S->ntri > 0 ? J->S->ntri : 1));
+  if (!xs) { J->err = 1; return NULL; }
+  for (;;) {
+    long s = atomic_fetch_add(&J->next, 64);
+    if (s >= J->nrays) break;
+    long e = s + 64 < J->nrays ? s + 64 : J->nrays;
+    for (long i = s; i < e; ++i) trace_one(J, (int)i, xs, &J->cv[a->tid]);
+  }
+  free(xs);
+  return NULL;
+}
+
+static int cand_cmp(const void* a, const void* b) {
+  const ocand* x = (const ocand*)a;
+  const ocand* y = (const ocand*)b;
+  if (x->ray != y->ray) return x->ray < y->ray ? -1 : 1;
+  if (x->seg != y->seg) return x->seg < y->seg ? -1 : 1;
+  if (x->rx != y->rx) return x->rx < y->rx ? -1 : 1;
+  return 0;
+}
+
+/* Returns 0 on success. *cand_out is malloc'd (3 ints per capture, sorted by
+ * ray, segment, receiver); free it with or_free. */
+int or_trace(const float* tris, const int32_t* tri_mat, int32_t ntri, const float* mats,
+             int32_t nmat, const float* tx, const float* rays, int32_t nrays, const float* rx,
+             int32_t nrx, const or_params* P, int32_t* hit_id, double* hit_t, int32_t* nseg,
+             uint32_t* flags, double* seg_od, int32_t** cand_out, int64_t* ncand_out) {
+  if (P->max_refl < 0 || P->max_refl > OR_MAX_REFL) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  trace_job J;
+  memset(&J, 0, sizeof(J));
+  J.S = &S; J.P = P; J.tx = mk(tx[0], tx[1], tx[2]);
+  J.rays = rays; J.nrays = nrays; J.rx = rx; J.nrx = nrx;
+  J.hit_id = hit_id; J.hit_t = hit_t; J.nseg = nseg; J.flags = flags; J.seg_od = seg_od;
+  atomic_init(&J.next, 0);
+  int nt = default_threads(P->nthreads);
+  J.cv = (cvec*)calloc((size_t)nt, sizeof(cvec));
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+  targ* args = (targ*)malloc(sizeof(targ) * (size_t)nt);
+  for (int k = 0; k < nt; ++k) {
+    args[k].J = &J; args[k].tid = k;
+    pthread_create(&th[k], NULL, trace_worker, &args[k]);
+  }
+  for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+  long tot = 0;
+  for (int k = 0; k < nt; ++k) tot += J.cv[k].n;
+  ocand* all = (ocand*)malloc(sizeof(ocand) * (size_t)(tot > 0 ? tot : 1));
+  long pos = 0;
+  for (int k = 0; k < nt; ++k) {
+    if (J.cv[k].n) memcpy(all + pos, J.cv[k].c, sizeof(ocand) * (size_t)J.cv[k].n);
+    pos += J.cv[k].n;
+    free(J.cv[k].c);
+  }
+  qsort(all, (size_t)tot, sizeof(ocand), cand_cmp);
+  *cand_out = (int32_t*)all;
+  *ncand_out = tot;
+  free(J.cv); free(th); free(args);
+  scene_free(&S);
+  return J.err ? -3 : 0;
+}
+
+void or_free(void* p) { free(p); }
+
+/* ------------------------------------------------------------------------ */
+/* or_validate: image method + field (steps 3, 4, 6)                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t valid;
+  uint32_t flags;
+  double len_m;
+  double delay_s;
+  double amp_re, amp_im;
+  double pts[OR_MAX_REFL][3];
+} opath;
+
+/* distance from point p (in the triangle's plane) to the triangle boundary */
+static double edge_margin(const otri* T, v3 p) {
+  double m = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    v3 a = T->v[k], e = T->e[k];
+    double L2 = dot(e, e);
+    double u = L2 > 0 ? dot(sub(p, a), e) / L2 : 0;
+    if (u < 0) u = 0;
+    if (u > 1) u = 1;
+    double dd = norm(sub(p, add(a, scl(e, u))));
+    if (dd < m) m = dd;
+  }
+  return m;
+}
+
+/* p inside triangle T (p lies in its plane): same-side test of p against each
+ * edge, measured along the triangle normal. */
+static int point_in_tri(const otri* T, v3 p) {
+  double s0 = dot(cross(T->e[0], sub(p, T->v[0])), T->n);
+  double s1 = dot(cross(T->e[1], sub(p, T->v[1])), T->n);
+  double s2 = dot(cross(T->e[2], sub(p, T->v[2])), T->n);
+  return s0 >= 0 && s1 >= 0 && s2 >= 0;
+}
+
+/* Occlusion of the open sub-segment a->b by any triangle except ex0/ex1.
+ * Parameter range (eps_occ, 1-eps_occ). Returns 1 if occluded. */
+static int occluded(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_params* P,
+                    double scale, uint32_t* fl) {
+  v3 dv = sub(b, a);
+  double len = norm(dv);
+  if (!(len > 0)) return 0;
+  v3 d = scl(dv, 1.0 / len);  /* unit; parameter u = t / len */
+  double base = P->edge_eps * scale;
+  int occ = 0;
+  for (int j = 0; j < S->ntri; ++j) {
+    if (j == ex0 || j == ex1) continue;
+    xinfo x;
+    ray_tri(&S->t[j], a, d, base, P->edge_eps, &x);
+    if (isnan(x.t)) continue;
+    double u = x.t / len;
+    double du = (base + P->edge_eps * fabs(x.t)) / fmax(x.cos_t, 1e-6) / len;
+    double lo = P->eps_occ, hi = 1.0 - P->eps_occ;
+    if (x.inside && u > lo && u < hi) occ = 1;
+    if (x.inside || x.flippable) {
+      if (u > lo - du && u < hi + du) {
+        if (x.flippable) *fl |= ORF_OCC_NEAR;
+        if (fabs(u - lo) <= du || fabs(u - hi) <= du) *fl |= ORF_OCC_NEAR;
+      }
+    }
+  }
+  return occ;
+}
+
+typedef struct { double complex x, y, z; } c3;
+
+static inline double complex cdot(c3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+/* antenna polarisation for a path leaving/arriving along d: u - (u.d) d, unit */
+static v3 pol_dir(v3 u, v3 d, uint32_t* fl) {
+  v3 p = sub(u, scl(d, dot(u, d)));
+  double n = norm(p);
+  if (n < 1e-9) {  /* u parallel to d: fall back to a fixed perpendicular */
+    *fl |= ORF_POL_DEGEN;
+    v3 a = fabs(d.x) < 0.9 ? mk(1, 0, 0) : mk(0, 1, 0);
+    p = sub(a, scl(d, dot(a, d)));
+    n = norm(p);
+  }
+  return scl(p, 1.0 / n);
+}
+
+static void validate_one(const oscene* S, const or_params* P, v3 tx, v3 rx, int k,
+                         const int32_t* ids, opath* out) {
+  memset(out, 0, sizeof(*out));
+  uint32_t fl = 0;
+  for (int j = 0; j < k; ++j)
+    if (ids[j] < 0 || ids[j] >= S->ntri) { out->valid = 0; return; }
+  /* image sources I_1..I_k of the transmitter in the planes of tri_1..tri_k */
+  v3 img[OR_MAX_REFL + 1];
+  img[0] = tx;
+  for (int j = 1; j <= k; ++j) {
+    const otri* T = &S->t[ids[j - 1]];
+    double nn = dot(T->n, T->n);
+    if (!(nn > 0)) { out->valid = 0; return; }
+    double h = dot(sub(img[j - 1], T->v[0]), T->n) / nn;
+    img[j] = sub(img[j - 1], scl(T->n, 2.0 * h));
+  }
+  /* back-trace from the receiver: X_{k+1} = Rx, P_j on plane j toward I_j */
+  v3 X[OR_MAX_REFL + 2];
+  X[k + 1] = rx;
+  X[0] = tx;
+  double scale = fmax(maxabs(tx), maxabs(rx));
+  for (int j = k; j >= 1; --j) {
+    const otri* T = &S->t[ids[j - 1]];
+    v3 dir = sub(img[j], X[j + 1]);
+    double den = dot(dir, T->n);
+    if (den == 0) { out->valid = 0; out->flags = fl; return; }
+    double s = dot(sub(T->v[0], X[j + 1]), T->n) / den;
+    double ve = P->val_eps;
+    if (fabs(s) <= ve || fabs(s - 1.0) <= ve) fl |= ORF_VAL_PARAM;
+    if (!(s > 0 && s < 1)) { out->valid = 0; out->flags = fl; return; }
+    X[j] = add(X[j + 1], scl(dir, s));
+    scale = fmax(scale, maxabs(X[j]));
+  }
+  int ok = 1;
+  for (int j = 1; j <= k; ++j) {
+    const otri* T = &S->t[ids[j - 1]];
+    double m = edge_margin(T, X[j]);
+    if (m <= P->val_eps * (scale + 1.0)) fl |= ORF_VAL_EDGE;
+    if (!point_in_tri(T, X[j])) ok = 0;
+  }
+  if (!ok) { out->valid = 0; out->flags = fl; return; }
+  /* every sub-segment X_j -> X_{j+1} must be unoccluded */
+  double L = 0;
+  for (int j = 0; j <= k; ++j) L += norm(sub(X[j + 1], X[j]));
+  if (!(L > 0)) { out->valid = 0; out->flags = fl; return; }
+  for (int j = 0; j <= k; ++j) {
+    int ex0 = j >= 1 ? ids[j - 1] : -1;
+    int ex1 = j + 1 <= k ? ids[j] : -1;
+    if (occluded(S, X[j], X[j + 1], ex0, ex1, P, scale + L, &fl)) ok = 0;
+  }
+  out->flags = fl;
+  if (!ok) { out->valid = 0; return; }
+  /* geometry of the valid path */
+  out->valid = 1;
+  out->len_m = L;
+  out->delay_s = L / C0;
+  for (int j = 1; j <= k; ++j) {
+    out->pts[j - 1][0] = X[j].x; out->pts[j - 1][1] = X[j].y; out->pts[j - 1][2] = X[j].z;
+  }
+  /* field with vector polarisation */
+  v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  v3 d0 = unit(sub(X[1], X[0]));
+  v3 e0 = pol_dir(u, d0, &fl);
+  c3 E = {e0.x, e0.y, e0.z};
+  for (int j = 1; j <= k; ++j) {
+    const otri* T = &S->t[ids[j - 1]];
+    v3 din = unit(sub(X[j], X[j - 1]));
+    v3 dout = unit(sub(X[j + 1], X[j]));
+    v3 nh = T->nh;
+    double ct = fabs(dot(din, nh));
+    v3 sv = cross(din, nh);
+    double sn = norm(sv);
+    if (sn < 1e-12) {  /* normal incidence: any unit vector perpendicular to n */
+      v3 a = fabs(nh.x) < 0.9 ? mk(1, 0, 0) : mk(0, 1, 0);
+      sv = unit(cross(nh, a));
+    } else {
+      sv = scl(sv, 1.0 / sn);
+    }
+    v3 pin = cross(sv, din), pout = cross(sv, dout);
+    double complex gte, gtm;
+    int mi = T->mat;
+    if (mi < 0 || mi >= S->nmat) mi = 0;
+    fresnel(&S->mats[3 * mi], P->freq_hz, ct, &gte, &gtm);
+    double complex es = cdot(E, sv), ep = cdot(E, pin);
+    c3 En;
+    En.x = gte * es * sv.x + gtm * ep * pout.x;
+    En.y = gte * es * sv.y + gtm * ep * pout.y;
+    En.z = gte * es * sv.z + gtm * ep * pout.z;
+    E = En;
+  }
+  v3 drx = unit(sub(X[k + 1], X[k]));
+  v3 prx = pol_dir(u, scl(drx, -1.0), &fl);
+  double lam = C0 / P->freq_hz;
+  double kw = 2.0 * M_PI * P->freq_hz / C0;
+  double complex a = (lam / (4.0 * M_PI)) * cdot(E, prx) * cexp(-I * kw * L) / L;
+  out->amp_re = creal(a);
+  out->amp_im = cimag(a);
+  out->flags = fl;
+}
+
+typedef struct {
+  const oscene* S;
+  const or_params* P;
+  v3 tx;
+  const float* rx;
+  const int32_t* keys;  /* ncand x (2 + N): rx, depth, ids[N] */
+  int stride;
+  long ncand;
+  opath* out;
+  atomic_long next;
+} val_job;
+
+static void* val_worker(void* p) {
+  val_job* J = (val_job*)p;
+  for (;;) {
+    long s = atomic_fetch_add(&J->next, 16);
+    if (s >= J->ncand) break;
+    long e = s + 16 < J->ncand ? s + 16 : J->ncand;
+    for (long i = s; i < e; ++i) {
+      const int32_t* kk = &J->keys[(size_t)i * J->stride];
+      int r = kk[0], depth = kk[1];
+      v3 R = mk(J->rx[3 * r], J->rx[3 * r + 1], J->rx[3 * r + 2]);
+      validate_one(J->S, J->P, J->tx, R, depth, kk + 2, &J->out[i]);
+    }
+  }
+  return NULL;
+}
+
+/* keys: ncand rows of (2 + max_refl) int32: rx index, depth k, tri ids (k used). */
+int or_validate(const float* tris, const int32_t* tri_mat, int32_t ntri, const float* mats,
+                int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                const int32_t* keys, int64_t ncand, const or_params* P, opath* out) {
+  (void)nrx;
+  if (P->max_refl < 0 || P->max_refl > OR_MAX_REFL) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  val_job J;
+  J.S = &S; J.P = P; J.tx = mk(tx[0], tx[1], tx[2]); J.rx = rx; J.keys = keys;
+  J.stride = 2 + P->max_refl; J.ncand = ncand; J.out = out;
+  atomic_init(&J.next, 0);
+  int nt = default_threads(P->nthreads);
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+  for (int k = 0; k < nt; ++k) pthread_create(&th[k], NULL, val_worker, &J);
+  for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+  free(th);
+  scene_free(&S);
+  return 0;
+}
+
+int32_t or_path_size(void) { return (int32_t)sizeof(opath); }
+
+/* ------------------------------------------------------------------------ */
+/* or_exhaustive: image-method validation of EVERY sequence of length <= N   */
+/* ------------------------------------------------------------------------ */
+/* Writes up to `cap` valid keys (rows of 2 + max_refl ints) and their path
+ * records; returns the number of valid paths (may exceed cap). */
+int64_t or_exhaustive(const float* tris, const int32_t* tri_mat, int32_t ntri, const float* mats,
+                      int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                      const or_params* P, int32_t* keys_out, opath* paths_out, int64_t cap) {
+  if (P->max_refl < 0 || P->max_refl > OR_MAX_REFL) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  int N = P->max_refl, stride = 2 + N;
+  int64_t nvalid = 0;
+  int32_t ids[OR_MAX_REFL];
+  opath tmp;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (int k = 0; k <= N; ++k) {
+      if (k > 0 && ntri == 0) break;
+      for (int j = 0; j < k; ++j) ids[j] = 0;
+      for (;;) {
+        int okseq = 1;
+        for (int j = 1; j < k; ++j)
+          if (ids[j] == ids[j - 1]) { okseq = 0; break; }
+        if (okseq) {
+          validate_one(&S, P, mk(tx[0], tx[1], tx[2]), R, k, ids, &tmp);
+          if (tmp.valid) {
+            if (nvalid < cap) {
+              int32_t* kk = &keys_out[(size_t)nvalid * stride];
+              kk[0] = r; kk[1] = k;
+              for (int j = 0; j < N; ++j) kk[2 + j] = j < k ? ids[j] : -1;
+              paths_out[nvalid] = tmp;
+            }
+            nvalid++;
+          }
+        }
+        /* next sequence (odometer) */
+        int j = k - 1;
+        while (j >= 0) {
+          if (++ids[j] < ntri) break;
+          ids[j] = 0;
+          --j;
+        }
+        if (j < 0) break;
+      }
+    }
+  }
+  scene_free(&S);
+  return nvalid;
+}

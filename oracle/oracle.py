@@ -1,0 +1,297 @@
+"""Python driver of the FP64 CPU oracle (``dcem_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the test-suite, the smoke check and the
+benchmark's CPU-baseline leg, never by the product path. It shares no code
+with the CUDA library; both consume the FP32 arrays of the seeded input
+generators.
+
+Pipeline of one frame (arXiv 2112.07115, Sec. III):
+  transform   -> world-space vertices of moving objects (per-frame update)
+  trace       -> step 1-2: sampled-sphere shooting with up to N specular
+                 reflections, closest hit by brute force over all triangles,
+                 reception-sphere captures
+  dedupe      -> step 2: the set of distinct (receiver, depth, triangle
+                 sequence) keys ("hash table of visited propagation paths for
+                 each depth"), here simply sorted and made unique
+  validate    -> steps 3-4, 6: image receivers, back-trace, point-in-triangle,
+                 occlusion; length, delay, Fresnel TE/TM, complex amplitude
+  reduce      -> received power per receiver: coherent P_t |sum a|^2 and
+                 incoherent P_t sum |a|^2 in dBm, summed in sorted key order.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dcem_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libdcem_oracle.so")
+
+MAX_REFL = 10
+C0 = 299792458.0
+
+# flag bits (mirror the C definitions of this oracle)
+NEAR_EDGE, TIE, NEAR_TMIN, NEAR_SPHERE = 1, 2, 4, 8
+VAL_EDGE, VAL_PARAM, OCC_NEAR, POL_DEGEN = 16, 32, 64, 128
+RAY_FLAGS = NEAR_EDGE | TIE | NEAR_TMIN | NEAR_SPHERE
+PATH_FLAGS = VAL_EDGE | VAL_PARAM | OCC_NEAR
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, portable flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+                        "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(C.Structure):
+    _fields_ = [("freq_hz", C.c_double), ("tx_power_w", C.c_double), ("alpha", C.c_double),
+                ("rx_radius_scale", C.c_double), ("t_min", C.c_double),
+                ("escape_len", C.c_double), ("eps_occ", C.c_double), ("edge_eps", C.c_double),
+                ("val_eps", C.c_double), ("pol", C.c_double * 3), ("max_refl", C.c_int32),
+                ("nthreads", C.c_int32)]
+
+
+PATH_DTYPE = np.dtype([("valid", np.int32), ("flags", np.uint32), ("len_m", np.float64),
+                       ("delay_s", np.float64), ("amp_re", np.float64), ("amp_im", np.float64),
+                       ("pts", np.float64, (MAX_REFL, 3))])
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.POINTER
+        f32, i32, f64, u32 = P(C.c_float), P(C.c_int32), P(C.c_double), P(C.c_uint32)
+        _lib.or_transform.argtypes = [C.c_int32, f32, i32, f32, C.c_int32, f32]
+        _lib.or_transform.restype = None
+        _lib.or_trace.argtypes = [f32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32, f32,
+                                  C.c_int32, P(_Params), i32, f64, i32, u32, f64,
+                                  P(P(C.c_int32)), P(C.c_int64)]
+        _lib.or_trace.restype = C.c_int
+        _lib.or_validate.argtypes = [f32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                     i32, C.c_int64, P(_Params), C.c_void_p]
+        _lib.or_validate.restype = C.c_int
+        _lib.or_exhaustive.argtypes = [f32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                       P(_Params), i32, C.c_void_p, C.c_int64]
+        _lib.or_exhaustive.restype = C.c_int64
+        _lib.or_fresnel.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double, f64]
+        _lib.or_fresnel64.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double, f64]
+        _lib.or_free.argtypes = [C.c_void_p]
+        _lib.or_path_size.restype = C.c_int32
+        assert _lib.or_path_size() == PATH_DTYPE.itemsize, "path record layout mismatch"
+    return _lib
+
+
+@dataclass
+class OracleParams:
+    """Tracer parameters (defaults: Sec. III -- 5 W transmit power, isotropic
+    antennas; readings: vertical polarisation reference, capture radius
+    1.35 * alpha * (D+s)/sqrt(3), self-hit offset 1e-4 m)."""
+    freq_hz: float = 28e9
+    tx_power_w: float = 5.0
+    n_rays: int = 10_000
+    max_refl: int = 3
+    rx_radius_scale: float = 1.35
+    t_min: float = 1e-4
+    escape_len: float = 1e4
+    eps_occ: float = 1e-4
+    edge_eps: float = 1e-5
+    val_eps: float = 1e-9
+    pol: tuple = (0.0, 0.0, 1.0)
+    nthreads: int = 0
+
+    def c(self) -> _Params:
+        p = _Params()
+        p.freq_hz = self.freq_hz
+        p.tx_power_w = self.tx_power_w
+        p.alpha = float(np.sqrt(4.0 * np.pi / max(self.n_rays, 1)))
+        p.rx_radius_scale = self.rx_radius_scale
+        p.t_min = self.t_min
+        p.escape_len = self.escape_len
+        p.eps_occ = self.eps_occ
+        p.edge_eps = self.edge_eps
+        p.val_eps = self.val_eps
+        for i in range(3):
+            p.pol[i] = self.pol[i]
+        p.max_refl = self.max_refl
+        p.nthreads = self.nthreads
+        return p
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def transform(tris: np.ndarray, tri_obj: np.ndarray, xf: np.ndarray) -> np.ndarray:
+    """World-space vertices: static triangles copied, object triangles mapped by
+    their object's row-major 3x4 transform with fmaf(R0,x,fmaf(R1,y,fmaf(R2,z,t)))."""
+    tris = _f32(tris).reshape(-1, 9)
+    out = np.empty_like(tris)
+    xf = _f32(xf).reshape(-1)
+    nobj = xf.size // 12
+    lib().or_transform(tris.shape[0], _p(tris, C.c_float), _p(_i32(tri_obj), C.c_int32),
+                       _p(xf if xf.size else np.zeros(12, np.float32), C.c_float), nobj,
+                       _p(out, C.c_float))
+    return out.reshape(-1, 3, 3)
+
+
+def trace(world_tris, tri_mat, materials, tx, rays, rx, prm: OracleParams, seg_od=False):
+    """Step 1-2 over every ray. Returns a dict with per-ray hit ids per segment
+    (-1 escaped, -2 not reached), hit distances, segment counts, flag bits and
+    the captures (ray, segment, receiver), sorted."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rays = _f32(rays).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    n, W = rays.shape[0], prm.max_refl + 1
+    hit_id = np.empty((n, W), np.int32)
+    hit_t = np.empty((n, W), np.float64)
+    nseg = np.empty(n, np.int32)
+    flags = np.empty(n, np.uint32)
+    od = np.empty((n, W, 7), np.float64) if seg_od else None
+    cptr = C.POINTER(C.c_int32)()
+    ncand = C.c_int64(0)
+    prm_c = prm.c()
+    rc = lib().or_trace(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), wt.shape[0],
+                        _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                        _p(rays, C.c_float), n, _p(rx, C.c_float), rx.shape[0], C.byref(prm_c),
+                        _p(hit_id, C.c_int32), _p(hit_t, C.c_double), _p(nseg, C.c_int32),
+                        _p(flags, C.c_uint32), _p(od, C.c_double) if od is not None else None,
+                        C.byref(cptr), C.byref(ncand))
+    m = int(ncand.value)
+    cands = np.ctypeslib.as_array(cptr, shape=(max(m, 1) * 3,))[:m * 3].reshape(m, 3).copy()
+    lib().or_free(C.cast(cptr, C.c_void_p))
+    if rc != 0:
+        raise RuntimeError(f"or_trace failed: {rc}")
+    out = {"hit_id": hit_id, "hit_t": hit_t, "nseg": nseg, "flags": flags, "cands": cands}
+    if od is not None:
+        out["seg_od"] = od
+    return out
+
+
+def candidate_keys(cands: np.ndarray, hit_id: np.ndarray, max_refl: int) -> np.ndarray:
+    """Key rows (rx, depth, tri ids of bounces 1..depth, -1 padding) of each capture."""
+    m = cands.shape[0]
+    keys = np.full((m, 2 + max_refl), -1, np.int32)
+    keys[:, 0] = cands[:, 2]
+    keys[:, 1] = cands[:, 1]
+    for j in range(max_refl):
+        sel = cands[:, 1] > j
+        keys[sel, 2 + j] = hit_id[cands[sel, 0], j]
+    return keys
+
+
+def unique_keys(keys: np.ndarray) -> np.ndarray:
+    """Distinct key rows in lexicographic (rx, depth, ids...) order."""
+    if keys.shape[0] == 0:
+        return keys.copy()
+    return np.unique(keys, axis=0)
+
+
+def validate(world_tris, tri_mat, materials, tx, rx, keys, prm: OracleParams) -> np.ndarray:
+    """Steps 3-4, 6 for every key row; returns PATH_DTYPE records (valid or not)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    keys = _i32(keys).reshape(-1, 2 + prm.max_refl)
+    out = np.zeros(keys.shape[0], PATH_DTYPE)
+    prm_c = prm.c()
+    rc = lib().or_validate(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), wt.shape[0],
+                           _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                           _p(rx, C.c_float), rx.shape[0], _p(keys, C.c_int32), keys.shape[0],
+                           C.byref(prm_c), out.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        raise RuntimeError(f"or_validate failed: {rc}")
+    return out
+
+
+def exhaustive(world_tris, tri_mat, materials, tx, rx, prm: OracleParams, cap=1 << 20):
+    """All valid paths of depth <= N by enumerating every triangle sequence."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    stride = 2 + prm.max_refl
+    keys = np.zeros((cap, stride), np.int32)
+    paths = np.zeros(cap, PATH_DTYPE)
+    prm_c = prm.c()
+    n = lib().or_exhaustive(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), wt.shape[0],
+                            _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                            _p(rx, C.c_float), rx.shape[0], C.byref(prm_c),
+                            _p(keys, C.c_int32), paths.ctypes.data_as(C.c_void_p), cap)
+    if n < 0:
+        raise RuntimeError(f"or_exhaustive failed: {n}")
+    if n > cap:
+        raise RuntimeError(f"or_exhaustive: {n} paths exceed capacity {cap}")
+    return keys[:n].copy(), paths[:n].copy()
+
+
+def fresnel(eps_r, sigma, pec, freq_hz, cos_t, exact=False):
+    """(Gamma_TE, Gamma_TM) as complex numbers."""
+    out = np.zeros(4)
+    f = lib().or_fresnel64 if exact else lib().or_fresnel
+    f(eps_r, sigma, int(pec), freq_hz, cos_t, _p(out, C.c_double))
+    return complex(out[0], out[1]), complex(out[2], out[3])
+
+
+def dbm(p_w):
+    with np.errstate(divide="ignore"):
+        return 10.0 * np.log10(np.asarray(p_w, np.float64)) + 30.0
+
+
+def reduce(keys: np.ndarray, paths: np.ndarray, nrx: int, tx_power_w: float):
+    """Per receiver: complex field sum a (FP64, in the given key order -- callers
+    pass keys sorted lexicographically), P_coh = P_t|sum a|^2 and
+    P_inc = P_t sum|a|^2 in dBm."""
+    field = np.zeros(nrx, np.complex128)
+    inc = np.zeros(nrx, np.float64)
+    for i in range(keys.shape[0]):
+        if not paths["valid"][i]:
+            continue
+        r = int(keys[i, 0])
+        a = complex(paths["amp_re"][i], paths["amp_im"][i])
+        field[r] += a
+        inc[r] += abs(a) ** 2
+    return field, dbm(tx_power_w * np.abs(field) ** 2), dbm(tx_power_w * inc)
+
+
+@dataclass
+class FrameResult:
+    world_tris: np.ndarray
+    tr: dict
+    keys: np.ndarray          # unique candidate keys, sorted
+    paths: np.ndarray         # PATH_DTYPE per key
+    field: np.ndarray
+    p_coh_dbm: np.ndarray
+    p_inc_dbm: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+
+def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> FrameResult:
+    """The whole oracle pipeline for frame ``f`` of a ``scenes.Scene``."""
+    wt = transform(scene.tris, scene.tri_obj, scene.xf[f] if scene.nobj else np.zeros((0, 12)))
+    rx = scene.rx[f]
+    tr = trace(wt, scene.tri_mat, scene.materials, scene.tx, rays, rx, prm, seg_od=seg_od)
+    keys = unique_keys(candidate_keys(tr["cands"], tr["hit_id"], prm.max_refl))
+    paths = validate(wt, scene.tri_mat, scene.materials, scene.tx, rx, keys, prm)
+    fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)
+    return FrameResult(wt, tr, keys, paths, fld, pc, pi)

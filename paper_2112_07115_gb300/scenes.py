@@ -1,0 +1,391 @@
+"""Seeded synthetic workloads for the dynamic EM ray tracer.
+
+This module only *generates inputs*: triangle meshes, materials, per-frame
+rigid transforms (3x4, row major), transmitter and receiver positions, and the
+sampled sphere of ray directions. It contains none of the tracer's arithmetic
+(no transform application, intersection, reflection, capture, image method or
+field computation), so both the CUDA path and the CPU oracle consume exactly
+the same FP32 bits from here.
+
+Workloads:
+  * ``toy_street``  -- ground, two buildings, four moving PEC vehicles, 8 Rx,
+    28 GHz, 10k rays, 3 reflections, 10 frames at 10 Hz.
+  * ``highway``     -- 2 km six-lane road with concrete barriers, 200 vehicles
+    of three box classes with lane changes, one roadside Tx, one Rx per
+    vehicle roof, 1M rays, 4 reflections, 100 frames at 10 Hz.
+  * small closed-form scenes (ground plane, parallel plates, random triangles).
+
+The paper (Sec. III) uses an .obj town model and measurement campaigns that
+are not available; these seeded scenes stand in for its vehicular workloads.
+Material constants: concrete eps_r=5.31, sigma=0.0326 S/m; vehicles are
+perfect conductors ("metal").
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+MAT_CONCRETE = 0
+MAT_METAL = 1
+
+
+def default_materials() -> np.ndarray:
+    """Material table rows: (eps_r, sigma [S/m], pec flag)."""
+    return np.array([[5.31, 0.0326, 0.0],   # concrete: ground, buildings, barriers
+                     [1.0, 0.0, 1.0]],      # metal: vehicles (perfect conductor)
+                    dtype=np.float32)
+
+
+@dataclass
+class Scene:
+    """A dynamic scene plus the radio set-up for a sequence of frames.
+
+    tris     float32 (T,3,3)  vertex coordinates; world space when
+                              tri_obj == -1, object space otherwise
+    tri_obj  int32 (T,)       -1 for static geometry, else rigid-object id
+    tri_mat  int32 (T,)       row of ``materials``
+    materials float32 (M,3)   (eps_r, sigma, pec)
+    xf       float32 (F,nobj,12) per-frame row-major 3x4 [R | t]
+    tx       float32 (3,)     transmitter (static)
+    rx       float32 (F,nrx,3) receivers per frame
+    """
+    name: str
+    tris: np.ndarray
+    tri_obj: np.ndarray
+    tri_mat: np.ndarray
+    materials: np.ndarray
+    nobj: int
+    xf: np.ndarray
+    tx: np.ndarray
+    rx: np.ndarray
+    freq_hz: float = 28e9
+    n_rays: int = 10_000
+    max_refl: int = 3
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def ntri(self) -> int:
+        return int(self.tris.shape[0])
+
+    @property
+    def nframes(self) -> int:
+        return int(self.xf.shape[0])
+
+    @property
+    def nrx(self) -> int:
+        return int(self.rx.shape[1])
+
+
+# ----------------------------------------------------------------------------
+# ray directions
+# ----------------------------------------------------------------------------
+
+def fibonacci_sphere(n: int) -> np.ndarray:
+    """n unit directions on a Fibonacci lattice, computed in FP64, rounded once to FP32.
+
+    z_i = 1 - (2i+1)/n, phi_i = i*pi*(3 - sqrt 5). This is the "sphere of
+    sampled rays" that the tracer casts (Sec. III, backward ray tracing, step 1).
+    """
+    if n <= 0:
+        return np.zeros((0, 3), np.float32)
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * (np.pi * (3.0 - np.sqrt(5.0)))
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    return d.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# meshes
+# ----------------------------------------------------------------------------
+
+def _quad(a, b, c, d):
+    """Two triangles (a,b,c), (a,c,d) of the planar quad a-b-c-d."""
+    return [[a, b, c], [a, c, d]]
+
+
+def box_tris(lx, ly, lz, center=(0.0, 0.0, 0.0), faces=("top", "xm", "xp", "ym", "yp")):
+    """Triangles of an axis-aligned box [cx-lx/2,cx+lx/2] x [cy-ly/2,..] x [cz, cz+lz].
+
+    ``faces`` chooses which faces to emit (bottom is omitted by default: it
+    rests on the ground and no ray can reach it).
+    """
+    cx, cy, cz = center
+    x0, x1 = cx - lx / 2, cx + lx / 2
+    y0, y1 = cy - ly / 2, cy + ly / 2
+    z0, z1 = cz, cz + lz
+    out = []
+    if "top" in faces:
+        out += _quad((x0, y0, z1), (x1, y0, z1), (x1, y1, z1), (x0, y1, z1))
+    if "bottom" in faces:
+        out += _quad((x0, y0, z0), (x0, y1, z0), (x1, y1, z0), (x1, y0, z0))
+    if "xm" in faces:
+        out += _quad((x0, y0, z0), (x0, y0, z1), (x0, y1, z1), (x0, y1, z0))
+    if "xp" in faces:
+        out += _quad((x1, y0, z0), (x1, y1, z0), (x1, y1, z1), (x1, y0, z1))
+    if "ym" in faces:
+        out += _quad((x0, y0, z0), (x1, y0, z0), (x1, y0, z1), (x0, y0, z1))
+    if "yp" in faces:
+        out += _quad((x0, y1, z0), (x0, y1, z1), (x1, y1, z1), (x1, y1, z0))
+    return out
+
+
+def _xf_row(yaw: float, tx: float, ty: float, tz: float) -> np.ndarray:
+    """Row-major 3x4 [R|t] of a rotation about +z by ``yaw`` then a translation."""
+    c, s = np.cos(yaw), np.sin(yaw)
+    return np.array([c, -s, 0.0, tx,
+                     s, c, 0.0, ty,
+                     0.0, 0.0, 1.0, tz], dtype=np.float64)
+
+
+def _assemble(static_tris, static_mat, obj_meshes, obj_mat):
+    tris, tobj, tmat = [], [], []
+    for t, m in zip(static_tris, static_mat):
+        tris.append(t)
+        tobj.append(-1)
+        tmat.append(m)
+    for k, mesh in enumerate(obj_meshes):
+        for t in mesh:
+            tris.append(t)
+            tobj.append(k)
+            tmat.append(obj_mat[k])
+    return (np.asarray(tris, np.float32).reshape(-1, 3, 3),
+            np.asarray(tobj, np.int32), np.asarray(tmat, np.int32))
+
+
+# ----------------------------------------------------------------------------
+# toy street (58 triangles)
+# ----------------------------------------------------------------------------
+
+def toy_street(seed: int = 0, n_frames: int = 10, n_rays: int = 10_000,
+               max_refl: int = 3, freq_hz: float = 28e9) -> Scene:
+    """Toy street: 2 ground tris, two 20x20x15 m buildings (walls only, 8 tris each),
+    four 4.5x1.8x1.5 m PEC vehicles (10 tris each) at 15 m/s, Tx at (0,12,6),
+    8 Rx at 1.5 m along y = +-12. 58 triangles, 10 frames at 10 Hz.
+
+    The seed jitters the vehicles' start positions by up to +-1 m so that
+    different seeds give different geometry; seed 0 is the nominal layout.
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 1])))
+    static, smat = [], []
+    static += _quad((-100, -100, 0), (100, -100, 0), (100, 100, 0), (-100, 100, 0))
+    smat += [MAT_CONCRETE] * 2
+    for (bx, by) in [(-30.0, 25.0), (30.0, -25.0)]:
+        walls = box_tris(20, 20, 15, (bx, by, 0.0), faces=("xm", "xp", "ym", "yp"))
+        static += walls
+        smat += [MAT_CONCRETE] * len(walls)
+    veh = box_tris(4.5, 1.8, 1.5)
+    lanes = [-6.0, -2.0, 2.0, 6.0]
+    x0 = np.array([-40.0, -10.0, 10.0, 40.0])
+    if seed != 0:
+        x0 = x0 + rng.uniform(-1.0, 1.0, size=4)
+    vdir = np.array([-1.0, -1.0, 1.0, 1.0])  # y<0 lanes drive -x, y>0 lanes +x
+    tris, tobj, tmat = _assemble(static, smat, [veh] * 4, [MAT_METAL] * 4)
+    dt, v = 0.1, 15.0
+    xf = np.zeros((n_frames, 4, 12), np.float64)
+    for f in range(n_frames):
+        for k in range(4):
+            yaw = 0.0 if vdir[k] > 0 else np.pi
+            xf[f, k] = _xf_row(yaw, x0[k] + vdir[k] * v * dt * f, lanes[k], 0.0)
+    rx1 = np.array([[x, y, 1.5] for y in (-12.0, 12.0) for x in (-36.0, -12.0, 12.0, 36.0)])
+    rx = np.broadcast_to(rx1, (n_frames, 8, 3)).astype(np.float32).copy()
+    return Scene("toy_street", tris, tobj, tmat, default_materials(), 4,
+                 xf.astype(np.float32), np.array([0.0, 12.0, 6.0], np.float32), rx,
+                 freq_hz=freq_hz, n_rays=n_rays, max_refl=max_refl,
+                 meta={"seed": seed, "dt": dt})
+
+
+# ----------------------------------------------------------------------------
+# highway V2I (about 4.0k triangles)
+# ----------------------------------------------------------------------------
+
+HW_LENGTH = 2000.0
+HW_PIECE = 20.0
+HW_LANE_W = 3.75
+HW_LANES = [4.375 + HW_LANE_W * k for k in range(3)]        # carriageway y>0 (drives +x)
+HW_BARRIER_Y = [-14.75, 0.0, 14.75]
+VEH_CLASSES = {  # length, width, height
+    "car": (4.5, 1.8, 1.5),
+    "van": (6.0, 2.2, 2.5),
+    "truck": (12.0, 2.5, 4.0),
+}
+
+
+def highway(seed: int = 0, n_frames: int = 100, n_vehicles: int = 200,
+            n_rays: int = 1_000_000, max_refl: int = 4, freq_hz: float = 28e9,
+            length: float = HW_LENGTH) -> Scene:
+    """Highway V2I: straight 6-lane road (30 m wide, 20 m tessellation), three
+    2 m x 0.5 m concrete barriers (road edges and median), ``n_vehicles``
+    vehicles (70% car, 20% van, 10% truck, 10 tris each) at U[20,35] m/s with
+    Poisson(0.05/s) lane changes along a 3 s cosine profile, a 10 m gap rule,
+    and wrap-around at the road ends. Tx at (L/2, 20, 8); one Rx 0.1 m above
+    each vehicle roof. Frames at 10 Hz.
+    """
+    ss = np.random.SeedSequence([seed, 2])
+    r_layout, r_speed, r_lc = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
+    npieces = int(round(length / HW_PIECE))
+    static, smat = [], []
+    for p in range(npieces):
+        xa, xb = p * HW_PIECE, (p + 1) * HW_PIECE
+        static += _quad((xa, -15.0, 0.0), (xb, -15.0, 0.0), (xb, 15.0, 0.0), (xa, 15.0, 0.0))
+        smat += [MAT_CONCRETE] * 2
+    for by in HW_BARRIER_Y:
+        for p in range(npieces):
+            xa = p * HW_PIECE
+            b = box_tris(HW_PIECE, 0.5, 2.0, (xa + HW_PIECE / 2, by, 0.0), faces=("top", "ym", "yp"))
+            static += b
+            smat += [MAT_CONCRETE] * len(b)
+    # vehicles
+    u = r_layout.uniform(size=n_vehicles)
+    cls = np.where(u < 0.7, 0, np.where(u < 0.9, 1, 2))
+    names = ["car", "van", "truck"]
+    dims = np.array([VEH_CLASSES[names[c]] for c in cls])
+    lane_y = np.array(HW_LANES + [-y for y in HW_LANES])          # 6 lanes
+    lane = r_layout.integers(0, 6, size=n_vehicles)
+    # place vehicles per lane with at least (length + 10 m) spacing
+    x = np.zeros(n_vehicles)
+    for ln in range(6):
+        idx = np.nonzero(lane == ln)[0]
+        if len(idx) == 0:
+            continue
+        need = dims[idx, 0] + 10.0
+        free = length - need.sum()
+        if free < 0:
+            raise ValueError("too many vehicles for the road length")
+        gaps = r_layout.dirichlet(np.ones(len(idx) + 1)) * free
+        pos = r_layout.uniform(0, length)
+        order = r_layout.permutation(len(idx))
+        cur = pos
+        for j, k in enumerate(order):
+            cur += gaps[j]
+            x[idx[k]] = (cur + need[k] / 2) % length
+            cur += need[k]
+    speed0 = r_speed.uniform(20.0, 35.0, size=n_vehicles)
+    meshes = [box_tris(*dims[k]) for k in range(n_vehicles)]
+    tris, tobj, tmat = _assemble(static, smat, meshes, [MAT_METAL] * n_vehicles)
+
+    dt, t_lc = 0.1, 3.0
+    y = lane_y[lane].astype(np.float64).copy()
+    sgn = np.where(lane < 3, 1.0, -1.0)           # +x on y>0 carriageway
+    lc_from = y.copy()
+    lc_to = y.copy()
+    lc_t = np.full(n_vehicles, -1.0)               # time into current lane change (<0: none)
+    xf = np.zeros((n_frames, n_vehicles, 12), np.float64)
+    rx = np.zeros((n_frames, n_vehicles, 3), np.float64)
+    for f in range(n_frames):
+        vy = np.zeros(n_vehicles)
+        active = lc_t >= 0
+        if np.any(active):
+            ph = np.clip(lc_t[active] / t_lc, 0.0, 1.0)
+            y[active] = lc_from[active] + (lc_to[active] - lc_from[active]) * 0.5 * (1 - np.cos(np.pi * ph))
+            vy[active] = ((lc_to[active] - lc_from[active]) * 0.5 * np.pi / t_lc
+                          * np.sin(np.pi * ph))
+        vx = sgn * speed0
+        yaw = np.arctan2(vy, vx)
+        for k in range(n_vehicles):
+            xf[f, k] = _xf_row(yaw[k], x[k], y[k], 0.0)
+        rx[f, :, 0] = x
+        rx[f, :, 1] = y
+        rx[f, :, 2] = dims[:, 2] + 0.1
+        # --- advance dynamics to the next frame ---
+        eff = speed0.copy()
+        for ln_sign in (1.0, -1.0):                 # gap rule per carriageway & lane
+            sel = np.nonzero(sgn == ln_sign)[0]
+            for ly in lane_y[(lane_y > 0) if ln_sign > 0 else (lane_y < 0)]:
+                inl = sel[np.abs(y[sel] - ly) < HW_LANE_W / 2]
+                if len(inl) < 2:
+                    continue
+                order = inl[np.argsort(x[inl] * ln_sign)]
+                for a, b in zip(order[:-1], order[1:]):
+                    gap = (x[b] - x[a]) * ln_sign - (dims[a, 0] + dims[b, 0]) / 2
+                    if gap < 10.0:
+                        eff[a] = min(eff[a], eff[b])
+        x = (x + sgn * eff * dt) % length
+        lc_t[active] += dt
+        done = active & (lc_t > t_lc)
+        y[done] = lc_to[done]
+        lc_t[done] = -1.0
+        start = (lc_t < 0) & (r_lc.uniform(size=n_vehicles) < 1.0 - np.exp(-0.05 * dt))
+        for k in np.nonzero(start)[0]:
+            same = lane_y[(lane_y * sgn[k]) > 0]
+            cur = same[np.argmin(np.abs(same - y[k]))]
+            nb = same[np.abs(np.abs(same - cur) - HW_LANE_W) < 1e-6]
+            if len(nb) == 0:
+                continue
+            lc_from[k] = cur
+            lc_to[k] = nb[r_lc.integers(0, len(nb))]
+            lc_t[k] = 0.0
+    return Scene("highway", tris, tobj, tmat, default_materials(), n_vehicles,
+                 xf.astype(np.float32), np.array([length / 2, 20.0, 8.0], np.float32),
+                 rx.astype(np.float32), freq_hz=freq_hz, n_rays=n_rays, max_refl=max_refl,
+                 meta={"seed": seed, "dt": dt, "classes": cls.tolist()})
+
+
+# ----------------------------------------------------------------------------
+# small scenes with closed forms
+# ----------------------------------------------------------------------------
+
+def _static_scene(name, tris, mats, tx, rx, **kw) -> Scene:
+    tris = np.asarray(tris, np.float32).reshape(-1, 3, 3)
+    n = tris.shape[0]
+    rx = np.asarray(rx, np.float32).reshape(1, -1, 3)
+    return Scene(name, tris, np.full(n, -1, np.int32), np.asarray(mats, np.int32),
+                 kw.pop("materials", default_materials()), 0,
+                 np.zeros((1, 0, 12), np.float32), np.asarray(tx, np.float32), rx, **kw)
+
+
+def ground_plane(tx=(0.0, 0.0, 6.0), rx=((50.0, 0.0, 1.5),), half=2000.0,
+                 material=MAT_CONCRETE, **kw) -> Scene:
+    """One square ground at z = 0 made of two triangles (two-ray model)."""
+    t = _quad((-half, -half, 0.0), (half, -half, 0.0), (half, half, 0.0), (-half, half, 0.0))
+    return _static_scene("ground", t, [material] * 2, tx, rx, **kw)
+
+
+def parallel_plates(h: float = 10.0, half: float = 5000.0, tx=(0.0, 0.0, 3.0),
+                    rx=((40.0, 0.0, 7.0),), **kw) -> Scene:
+    """Two parallel PEC plates z = 0 and z = h (two triangles each)."""
+    t = _quad((-half, -half, 0.0), (half, -half, 0.0), (half, half, 0.0), (-half, half, 0.0))
+    t += _quad((-half, -half, h), (-half, half, h), (half, half, h), (half, -half, h))
+    return _static_scene("plates", t, [MAT_METAL] * 4, tx, rx, **kw)
+
+
+def free_space(tx=(0.0, 0.0, 0.0), rx=((100.0, 0.0, 0.0),), **kw) -> Scene:
+    """No geometry at all (Friis)."""
+    return _static_scene("free", np.zeros((0, 3, 3), np.float32), [], tx, rx, **kw)
+
+
+def random_tiny(seed: int, ntri: int = 8, nobj: int = 2, n_frames: int = 3,
+                nrx: int = 3, extent: float = 20.0, **kw) -> Scene:
+    """Random triangles in a box plus a large ground; a share of them belong to
+    ``nobj`` rigid objects that translate/rotate each frame."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 3])))
+    static = _quad((-200, -200, 0), (200, -200, 0), (200, 200, 0), (-200, 200, 0))
+    smat = [MAT_CONCRETE] * 2
+    meshes = [[] for _ in range(max(nobj, 0))]
+    for i in range(ntri):
+        c = rng.uniform([-extent, -extent, 1.0], [extent, extent, extent])
+        tri = (c + rng.normal(scale=extent / 4, size=(3, 3))).tolist()
+        if nobj > 0 and rng.uniform() < 0.5:
+            k = int(rng.integers(0, nobj))
+            meshes[k].append((np.asarray(tri) - c).tolist())
+        else:
+            static.append(tri)
+            smat.append(MAT_CONCRETE)
+    nonempty = [m for m in meshes if m]
+    tris, tobj, tmat = _assemble(static, smat, nonempty,
+                                 [MAT_METAL if k % 2 else MAT_CONCRETE for k in range(len(nonempty))])
+    no = len(nonempty)
+    base = rng.uniform([-extent, -extent, 2.0], [extent, extent, extent], size=(no, 3))
+    vel = rng.normal(scale=1.0, size=(no, 3)) * np.array([1, 1, 0.2])
+    w = rng.normal(scale=0.1, size=no)
+    xf = np.zeros((n_frames, no, 12))
+    for f in range(n_frames):
+        for k in range(no):
+            p = base[k] + vel[k] * f
+            xf[f, k] = _xf_row(w[k] * f, p[0], p[1], p[2])
+    tx = rng.uniform([-extent, -extent, 1.0], [extent, extent, extent])
+    rx = rng.uniform([-extent, -extent, 1.0], [extent, extent, extent], size=(nrx, 3))
+    rx = np.broadcast_to(rx, (n_frames, nrx, 3)).copy()
+    return Scene(f"tiny{seed}", tris, tobj, tmat, default_materials(), no,
+                 xf.astype(np.float32), tx.astype(np.float32), rx.astype(np.float32), **kw)

@@ -1,0 +1,391 @@
+"""Pins of the FP64 CPU oracle against closed forms, invariants and brute force.
+
+Each test checks the oracle against something other than itself:
+  * Friis free-space loss (Eq. 3 read with path-loss exponent 2, AT = 0),
+  * the two-ray ground-reflection model (scalar closed form),
+  * image-method path lengths off one plane and between two parallel plates
+    (image heights written in closed form, not by iterating mirrors),
+  * Fresnel coefficients against Snell-law textbook forms, Brewster's angle,
+    normal incidence and the perfect-conductor limit,
+  * Tx/Rx reciprocity of the valid path set and amplitudes,
+  * sampled-sphere discovery versus exhaustive enumeration of all sequences,
+  * the FP32 rigid transform against exact rational arithmetic.
+"""
+from fractions import Fraction
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2112_07115_gb300 import scenes
+
+C0 = 299792458.0
+EPS0 = 8.8541878128e-12
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def closed_fresnel_lossless(n, theta):
+    """Textbook Fresnel amplitudes via Snell's law (lossless, below critical):
+    Gamma_s = -sin(ti - tt)/sin(ti + tt), Gamma_p = tan(ti - tt)/tan(ti + tt)."""
+    tt = np.arcsin(np.sin(theta) / n)
+    if theta == 0.0:
+        r = (1 - n) / (1 + n)
+        return r, -r
+    return (-np.sin(theta - tt) / np.sin(theta + tt), np.tan(theta - tt) / np.tan(theta + tt))
+
+
+# ---------------------------------------------------------------- paper data
+
+def test_paper_parameters_fixture():
+    """Parameter values printed in the paper (Sec. III and Table II)."""
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as fh:
+        g = json.load(fh)
+    from oracle.oracle import OracleParams
+    p = OracleParams()
+    assert p.tx_power_w == g["tx_power_outdoor_w"]["value"]
+    assert g["max_reflections"]["value"] == 10
+    from oracle.oracle import MAX_REFL
+    assert MAX_REFL == g["max_reflections"]["value"]
+
+
+# ---------------------------------------------------------------- Friis
+
+@pytest.mark.parametrize("freq,d", [(28e9, 100.0), (5.9e9, 100.0), (30e9, 37.5), (28e9, 1000.0)])
+def test_friis_free_space(oracle_mod, freq, d):
+    O = oracle_mod
+    s = scenes.free_space(tx=(0.0, 0.0, 0.0), rx=((d, 0.0, 0.0),))
+    prm = O.OracleParams(freq_hz=freq, max_refl=2, n_rays=2000)
+    rays = scenes.fibonacci_sphere(2000)
+    res = O.frame(s, 0, rays, prm)
+    # Eq. 3 with n = 2, AT = 0: PL = FSPL(f, 1 m) + 20 log10(d)
+    fspl1 = 20 * np.log10(4 * np.pi * freq / C0)
+    want = 10 * np.log10(5.0) + 30 - (fspl1 + 20 * np.log10(f32(d)))
+    assert res.keys.shape[0] == 1 and res.paths["valid"][0] == 1
+    assert abs(res.p_coh_dbm[0] - want) < 1e-9
+    assert abs(res.p_inc_dbm[0] - want) < 1e-9
+    assert abs(res.paths["delay_s"][0] - f32(d) / C0) < 1e-18
+
+
+def test_fspl_at_one_metre_values():
+    """FSPL(f, 1 m) = 20 log10(4 pi f / c): 61.39 dB at 28 GHz, 61.99 dB at 30 GHz."""
+    assert abs(20 * np.log10(4 * np.pi * 28e9 / C0) - 61.3909) < 1e-4
+    assert abs(20 * np.log10(4 * np.pi * 30e9 / C0) - 61.9902) < 1e-4
+
+
+# ---------------------------------------------------------------- two-ray
+
+@pytest.mark.parametrize("freq", [28e9, 5.9e9])
+@pytest.mark.parametrize("x", [50.0, 200.0, 733.0])
+def test_two_ray_ground(oracle_mod, freq, x):
+    O = oracle_mod
+    ht, hr = 6.0, 1.5
+    s = scenes.ground_plane(tx=(0.0, 0.0, ht), rx=((x, 0.0, hr),), half=5000.0)
+    prm = O.OracleParams(freq_hz=freq, max_refl=2)
+    keys, paths = O.exhaustive(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    assert sorted(keys[:, 1].tolist()) == [0, 1]
+    _, pc, pi = O.reduce(keys, paths, 1, 5.0)
+    # scalar two-ray model; materials enter as their FP32 values
+    d1, d2 = np.hypot(x, ht - hr), np.hypot(x, ht + hr)
+    cos = (ht + hr) / d2
+    gte, gtm = O.fresnel(5.31, 0.0326, 0, freq, cos)
+    k, lam = 2 * np.pi * freq / C0, C0 / freq
+    e = lam / (4 * np.pi) * (np.exp(-1j * k * d1) / d1 + gtm * np.exp(-1j * k * d2) / d2)
+    inc = (lam / (4 * np.pi)) ** 2 * (1 / d1 ** 2 + abs(gtm) ** 2 / d2 ** 2)
+    assert abs(pc[0] - (10 * np.log10(5 * abs(e) ** 2) + 30)) < 1e-6
+    assert abs(pi[0] - (10 * np.log10(5 * inc) + 30)) < 1e-6
+    # image method off one infinite plane: L = sqrt(x^2 + (ht + hr)^2)
+    refl = keys[:, 1] == 1
+    assert abs(paths["len_m"][refl][0] - d2) < 1e-9
+    assert abs(paths["delay_s"][refl][0] - d2 / C0) < 1e-18
+    # the reflection point is where the image line crosses z = 0
+    assert abs(paths["pts"][refl][0][0][0] - x * ht / (ht + hr)) < 1e-9
+
+
+def test_vertical_pol_two_ray_far_field_cancels(oracle_mod):
+    """Grazing vertical-polarisation reflection tends to -1: at long range the
+    coherent power falls well below the incoherent power (d^-4 regime)."""
+    O = oracle_mod
+    s = scenes.ground_plane(tx=(0.0, 0.0, 6.0), rx=((20000.0, 0.0, 1.5),), half=40000.0)
+    prm = O.OracleParams(freq_hz=5.9e9, max_refl=1, escape_len=1e5)
+    keys, paths = O.exhaustive(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    _, pc, pi = O.reduce(keys, paths, 1, 5.0)
+    # k * (d2 - d1) ~ 0.11 rad and Gamma_TM ~ -0.998: |1 + Gamma e^{-jk dd}|^2 / 2 ~ -22 dB
+    assert pc[0] < pi[0] - 18
+
+
+# ---------------------------------------------------------------- Fresnel
+
+@pytest.mark.parametrize("freq", [28e9, 5.9e9])
+def test_fresnel_normal_incidence(oracle_mod, freq):
+    O = oracle_mod
+    ec = 5.31 - 1j * 0.0326 / (2 * np.pi * freq * EPS0)
+    r = (1 - np.sqrt(ec)) / (1 + np.sqrt(ec))
+    te, tm = O.fresnel(5.31, 0.0326, 0, freq, 1.0, exact=True)
+    assert abs(te - r) < 1e-13
+    assert abs(tm + r) < 1e-13   # Gamma_TM(0) = -Gamma_TE(0) in the p_in/p_out basis
+
+
+def test_fresnel_normal_incidence_value_28ghz(oracle_mod):
+    te, _ = oracle_mod.fresnel(5.31, 0.0326, 0, 28e9, 1.0, exact=True)
+    assert abs(te - (-0.394738 + 0.000832j)) < 2e-6
+    assert abs(20 * np.log10(abs(te)) - (-8.0738)) < 1e-3
+
+
+@pytest.mark.parametrize("theta_deg", [0.0, 10.0, 30.0, 45.0, 60.0, 75.0, 85.0, 89.0])
+def test_fresnel_lossless_snell(oracle_mod, theta_deg):
+    n2 = 5.31
+    th = np.radians(theta_deg)
+    te, tm = oracle_mod.fresnel(n2, 0.0, 0, 28e9, np.cos(th), exact=True)
+    s, p = closed_fresnel_lossless(np.sqrt(n2), th)
+    assert abs(te - s) < 1e-12 and abs(tm - p) < 1e-12
+
+
+def test_fresnel_brewster(oracle_mod):
+    er = 5.31
+    tb = np.arctan(np.sqrt(er))
+    assert abs(np.degrees(tb) - 66.5409) < 1e-4
+    te, tm = oracle_mod.fresnel(er, 0.0, 0, 28e9, np.cos(tb), exact=True)
+    assert abs(tm) < 1e-12
+    assert abs(te - (1 - er) / (1 + er)) < 1e-12
+
+
+def test_fresnel_pec_and_limits(oracle_mod):
+    O = oracle_mod
+    for c in [1.0, 0.5, 0.01]:
+        te, tm = O.fresnel(1.0, 0.0, 1, 28e9, c)
+        assert te == -1 and tm == 1
+    for c in [1.0, 0.5]:
+        # a very good conductor approaches the PEC values (away from grazing,
+        # where a finite conductor's TM coefficient still tends to -1)
+        te2, tm2 = O.fresnel(1.0, 1e9, 0, 28e9, c, exact=True)
+        assert abs(te2 + 1) < 1e-3 and abs(tm2 - 1) < 1e-3
+    # grazing incidence -> -1 for both
+    te, tm = O.fresnel(5.31, 0.0326, 0, 28e9, 1e-9, exact=True)
+    assert abs(te + 1) < 1e-6 and abs(tm + 1) < 1e-6
+
+
+def test_fresnel_passive(oracle_mod):
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        er = rng.uniform(1.0, 80.0)
+        sg = 10 ** rng.uniform(-4, 2)
+        c = rng.uniform(0, 1)
+        te, tm = oracle_mod.fresnel(er, sg, 0, 10 ** rng.uniform(9, 11), c, exact=True)
+        assert abs(te) <= 1 + 1e-12 and abs(tm) <= 1 + 1e-12
+
+
+# ---------------------------------------------------------------- plates
+
+def _plate_image_z(m, first, h, H):
+    """Closed-form image height of a source at height h after m alternating
+    reflections between z = 0 and z = H, starting on plate `first`."""
+    if first == "bottom":
+        return -(m - 1) * H - h if m % 2 else m * H + h
+    return (m + 1) * H - h if m % 2 else -m * H + h
+
+
+@pytest.mark.parametrize("freq", [28e9, 5.9e9])
+def test_parallel_pec_plates_multibounce(oracle_mod, freq):
+    O = oracle_mod
+    H, ht, hr, x = 10.0, 3.0, 7.0, 40.0
+    s = scenes.parallel_plates(h=H, tx=(0.0, 0.0, ht), rx=((x, 0.0, hr),))
+    N = 4
+    prm = O.OracleParams(freq_hz=freq, max_refl=N)
+    keys, paths = O.exhaustive(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    bottom = {0, 1}
+    lam, k = C0 / freq, 2 * np.pi * freq / C0
+    got = {}
+    for kk, p in zip(keys, paths):
+        m = int(kk[1])
+        first = "bottom" if (m and int(kk[2]) in bottom) else "top"
+        got.setdefault(m, []).append((first, p))
+    assert len(got[0]) == 1
+    for m in range(1, N + 1):
+        assert sorted(f for f, _ in got[m]) == ["bottom", "top"]
+        for first, p in got[m]:
+            L = np.hypot(x, _plate_image_z(m, first, ht, H) - hr)
+            assert abs(p["len_m"] - L) < 1e-9
+            # |Gamma| = 1 and the vertical polarisation maps onto itself
+            a = complex(p["amp_re"], p["amp_im"])
+            want = lam / (4 * np.pi) * np.exp(-1j * k * L) / L
+            # phase k*L carries the FP64 rounding of L (k ~ 590 rad/m at 28 GHz)
+            assert abs(a - want) < 1e-9 * abs(want)
+
+
+def test_plates_sbr_finds_all(oracle_mod):
+    """Sampled-sphere discovery recovers every exhaustive path between plates."""
+    O = oracle_mod
+    s = scenes.parallel_plates(h=10.0, tx=(0.0, 0.0, 3.0), rx=((40.0, 0.0, 7.0),))
+    prm = O.OracleParams(max_refl=4, n_rays=200_000)
+    res = O.frame(s, 0, scenes.fibonacci_sphere(200_000), prm)
+    ek, _ = O.exhaustive(res.world_tris, s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    sbr = {tuple(k) for k, p in zip(res.keys, res.paths) if p["valid"]}
+    assert sbr == {tuple(k) for k in ek}
+
+
+# ---------------------------------------------------------------- reciprocity
+
+@pytest.mark.parametrize("seed", range(6))
+def test_reciprocity(oracle_mod, seed):
+    O = oracle_mod
+    s = scenes.random_tiny(seed, ntri=10, nobj=0, nrx=1)
+    wt = s.tris.reshape(-1, 9)
+    prm = O.OracleParams(max_refl=3, pol=(0.3, -0.2, 0.9))
+    tx, rx = s.tx, s.rx[0][0]
+    k1, p1 = O.exhaustive(wt, s.tri_mat, s.materials, tx, rx[None], prm)
+    k2, p2 = O.exhaustive(wt, s.tri_mat, s.materials, rx, tx[None], prm)
+    fw = {}
+    for k, p in zip(k1, p1):
+        fw[tuple(k[2:2 + k[1]])] = p
+    bw = {}
+    for k, p in zip(k2, p2):
+        bw[tuple(k[2:2 + k[1]][::-1])] = p
+    assert set(fw) == set(bw) and len(fw) >= 2
+    for seq in fw:
+        a, b = fw[seq], bw[seq]
+        assert abs(a["len_m"] - b["len_m"]) < 1e-9
+        za, zb = complex(a["amp_re"], a["amp_im"]), complex(b["amp_re"], b["amp_im"])
+        assert abs(za - zb) <= 1e-9 * abs(za) + 1e-18
+
+
+# ---------------------------------------------------------------- discovery
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sbr_subset_of_exhaustive(oracle_mod, seed):
+    """Every path the sampled sphere finds is a valid exhaustive path; with
+    many rays the two sets coincide on small scenes."""
+    O = oracle_mod
+    s = scenes.random_tiny(seed, ntri=8, nobj=2, nrx=2)
+    for n_rays in (3000, 400_000):
+        prm = O.OracleParams(max_refl=2, n_rays=n_rays)
+        res = O.frame(s, 1, scenes.fibonacci_sphere(n_rays), prm)
+        ek, _ = O.exhaustive(res.world_tris, s.tri_mat, s.materials, s.tx, s.rx[1], prm)
+        ex = {tuple(k) for k in ek}
+        sbr = {tuple(k) for k, p in zip(res.keys, res.paths) if p["valid"]}
+        assert sbr <= ex
+        if n_rays > 100_000:
+            assert sbr == ex
+
+
+def test_toy_street_sbr_equals_exhaustive(oracle_mod):
+    O = oracle_mod
+    s = scenes.toy_street()
+    prm = O.OracleParams(max_refl=3, n_rays=10_000)
+    res = O.frame(s, 0, scenes.fibonacci_sphere(10_000), prm)
+    ek, ep = O.exhaustive(res.world_tris, s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    sbr = {tuple(k) for k, p in zip(res.keys, res.paths) if p["valid"]}
+    assert sbr == {tuple(k) for k in ek}
+    _, pc, pi = O.reduce(ek, ep, s.nrx, 5.0)
+    assert np.allclose(pc, res.p_coh_dbm, atol=1e-12) and np.allclose(pi, res.p_inc_dbm, atol=1e-12)
+
+
+# ---------------------------------------------------------------- flags
+
+def test_edge_flag(oracle_mod):
+    """A ray aimed at the shared diagonal of the two ground triangles is
+    flagged; a ray aimed at a triangle interior is not."""
+    O = oracle_mod
+    s = scenes.ground_plane(tx=(0.0, 0.0, 6.0), half=100.0)
+    d_edge = np.array([[10.0, 10.0, -6.0]]) / np.linalg.norm([10.0, 10.0, -6.0])
+    d_in = np.array([[10.0, -4.0, -6.0]]) / np.linalg.norm([10.0, -4.0, -6.0])
+    prm = O.OracleParams(max_refl=1)
+    for d, want in ((d_edge, True), (d_in, False)):
+        tr = O.trace(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, d.astype(np.float32),
+                     s.rx[0], prm)
+        assert bool(tr["flags"][0] & O.NEAR_EDGE) == want
+        assert tr["hit_id"][0, 0] in (0, 1)
+
+
+def test_reflection_law(oracle_mod):
+    """Two-segment ray off the ground: the second segment's direction is the
+    mirror image of the first (angle of incidence = angle of reflection)."""
+    O = oracle_mod
+    s = scenes.ground_plane(tx=(0.0, 0.0, 6.0), half=100.0)
+    d = np.array([[3.0, -4.0, -6.0]], np.float32)
+    d /= np.linalg.norm(d)
+    tr = O.trace(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, d, s.rx[0],
+                 O.OracleParams(max_refl=1), seg_od=True)
+    od = tr["seg_od"][0]
+    d0 = d[0].astype(np.float64) / np.linalg.norm(d[0].astype(np.float64))
+    assert np.allclose(od[1, 3:6], d0 * [1, 1, -1], atol=1e-15)
+    assert abs(tr["hit_t"][0, 0] - 6.0 / -d0[2]) < 1e-12
+    assert abs(od[1, 6] - tr["hit_t"][0, 0]) < 1e-12          # unfolded length D
+    assert tr["hit_id"][0, 1] == -1 and tr["nseg"][0] == 2
+
+
+# ---------------------------------------------------------------- transform
+
+def _fmaf_exact(a, b, c):
+    """Correctly rounded float32 of a*b + c using exact rationals."""
+    v = Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c))
+    f = np.float32(float(v))
+    cands = [f, np.nextafter(f, np.float32(np.inf)), np.nextafter(f, np.float32(-np.inf))]
+    best = None
+    for x in cands:
+        err = abs(Fraction(float(x)) - v)
+        if best is None or err < best[0] or (err == best[0] and
+                                             (np.float32(x).view(np.uint32) & 1) == 0):
+            best = (err, x)
+    return np.float32(best[1])
+
+
+def _random_xf(rng, n):
+    """General rigid transforms: random unit quaternion rotations + translations."""
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1)
+    t = rng.uniform(-1500, 1500, size=(n, 3))
+    xf = np.concatenate([R.reshape(n, 3, 3), t[:, :, None]], axis=2).reshape(n, 12)
+    return xf.astype(np.float32)
+
+
+def test_transform_fmaf_order(oracle_mod):
+    """x' = fmaf(R0, x, fmaf(R1, y, fmaf(R2, z, t))) with each fmaf correctly
+    rounded, checked bit for bit against exact rational arithmetic."""
+    O = oracle_mod
+    rng = np.random.default_rng(1)
+    nobj, ntri = 6, 60
+    xf = _random_xf(rng, nobj)
+    tris = rng.uniform(-7, 7, size=(ntri, 3, 3)).astype(np.float32)
+    tri_obj = rng.integers(-1, nobj, size=ntri).astype(np.int32)
+    wt = O.transform(tris, tri_obj, xf)
+    for i in range(ntri):
+        if tri_obj[i] < 0:
+            assert np.array_equal(wt[i].view(np.uint32), tris[i].view(np.uint32))
+            continue
+        m = xf[tri_obj[i]]
+        for k in range(3):
+            v = tris[i, k]
+            for r in range(3):
+                inner = _fmaf_exact(m[4 * r + 2], v[2], m[4 * r + 3])
+                mid = _fmaf_exact(m[4 * r + 1], v[1], inner)
+                want = _fmaf_exact(m[4 * r + 0], v[0], mid)
+                assert wt[i, k, r].view(np.uint32) == want.view(np.uint32)
+
+
+def test_transform_highway_static_untouched(oracle_mod):
+    O = oracle_mod
+    s = scenes.highway(n_frames=2, n_vehicles=10, length=400.0)
+    wt = O.transform(s.tris, s.tri_obj, s.xf[1])
+    st = np.nonzero(s.tri_obj < 0)[0]
+    assert np.array_equal(wt[st].view(np.uint32), s.tris[st].view(np.uint32))
+
+
+def test_transform_exact_cases(oracle_mod):
+    """Identity and quarter-turn rotations with integral translations are exact."""
+    O = oracle_mod
+    tris = np.array([[[1.5, -2.25, 0.5], [3.0, 4.0, 5.0], [-7.0, 0.125, 2.0]]], np.float32)
+    ident = np.array([[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]], np.float32)
+    assert np.array_equal(O.transform(tris, np.array([0]), ident), tris)
+    rot = np.array([[0, -1, 0, 10, 1, 0, 0, -20, 0, 0, 1, 3]], np.float32)
+    out = O.transform(tris, np.array([0]), rot)
+    want = np.stack([10 - tris[0, :, 1], -20 + tris[0, :, 0], 3 + tris[0, :, 2]], axis=1)
+    assert np.array_equal(out[0], want.astype(np.float32))
