@@ -1,0 +1,233 @@
+/*
+ * dcem.h -- C ABI of the GB300 dynamic coherence-based EM ray tracer.
+ *
+ * The library computes, per frame, the propagation paths between one
+ * transmitter (Tx) and a set of receivers (Rx) in a scene of static triangles
+ * plus rigid moving objects, and the power each Rx receives, following
+ * arXiv 2112.07115 (DCEM), Sec. III:
+ *   - per-frame update of the scene and of its bounding volume hierarchy
+ *     ("Efficient BVH updating": the hierarchy is refit every frame);
+ *   - shooting a sphere of sampled rays with up to N specular reflections
+ *     ("Backward ray tracing", steps 1-2; shot from the Tx, which gives the
+ *     same valid path set by reciprocity);
+ *   - a table of visited triangle sequences per reflection depth, image
+ *     receivers and path validation (steps 2-4);
+ *   - total distance, direction, attenuation and phase of every valid path
+ *     (step 6; ray field of Eq. 1, free-space loss of Eq. 3, reflection per
+ *     Fresnel TE/TM);
+ *   - reuse of the previous frame's work where objects did not move
+ *     ("Propagation path caching", frame-to-frame coherence).
+ *
+ * Conventions for every entry point:
+ *   - Return DCEM_OK (0) or a negative dcem_status; nothing aborts, traps or
+ *     throws across the ABI. dcem_status_string() names a status.
+ *   - Arguments are validated before any device work; an invalid argument
+ *     returns DCEM_ERR_ARG and leaves the scene unchanged.
+ *   - A scene is NOT thread-safe. All its device work is ordered on the CUDA
+ *     stream given at creation (or by dcem_scene_set_stream). Calls that
+ *     return results to the caller synchronise that stream before returning.
+ *   - Triangle ids are the caller's input indices (0..ntri-1) and stay fixed.
+ *   - Coordinates are metres, FP32, right-handed; a 3x4 transform is row
+ *     major [R | t]: x' = R x + t.
+ *   - Pointers marked "host" must be host memory; pointers whose kind is
+ *     selected by a DCEM_PTR_* argument may be host (pageable or pinned) or
+ *     device memory of the scene's GPU. The library never keeps caller
+ *     pointers beyond the call.
+ *   - The scene owns all the device memory it allocates and frees it in
+ *     dcem_scene_destroy.
+ */
+#ifndef DCEM_H
+#define DCEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest reflection order (Sec. III: the maximum number of reflections is
+ * limited to 10). */
+#define DCEM_MAX_REFL 10
+
+typedef enum {
+  DCEM_OK = 0,
+  DCEM_ERR_ARG = -1,       /* invalid argument (null, size, index out of range) */
+  DCEM_ERR_CUDA = -2,      /* a CUDA call failed (no device, launch error, ...)  */
+  DCEM_ERR_CAPACITY = -3,  /* an output or internal buffer is too small          */
+  DCEM_ERR_NONFINITE = -4, /* NaN or Inf in geometry, transforms, Tx or Rx       */
+  DCEM_ERR_STACK = -5,     /* BVH traversal stack overflow (counted, not trapped) */
+  DCEM_ERR_HASH = -6,      /* 64-bit path-key collision between distinct keys    */
+  DCEM_ERR_STATE = -7,     /* call out of order (e.g. trace before set_rays)     */
+  DCEM_ERR_NOMEM = -8      /* device allocation failed                           */
+} dcem_status;
+
+typedef enum { DCEM_MODE_FULL = 0, DCEM_MODE_COHERENT = 1 } dcem_mode;
+typedef enum { DCEM_PTR_HOST = 0, DCEM_PTR_DEVICE = 1 } dcem_ptr_kind;
+
+/* Path flag bits (dcem_path.flags). */
+#define DCEM_PATH_POL_DEGENERATE 1u /* polarisation reference parallel to a path end */
+
+typedef struct dcem_scene dcem_scene;
+
+/* Half-space material for Fresnel reflection: complex permittivity
+ * eps_c = eps_r - j sigma / (2 pi f eps0); pec != 0 selects a perfect
+ * conductor (Gamma_TE = -1, Gamma_TM = +1). */
+typedef struct {
+  float eps_r;
+  float sigma;   /* S/m */
+  int32_t pec;
+} dcem_material;
+
+typedef struct {
+  double freq_hz;         /* carrier frequency; default 28e9                     */
+  double tx_power_w;      /* transmit power; default 5 W (Sec. III, outdoor)     */
+  int32_t max_refl;       /* N: reflections per ray, 0..DCEM_MAX_REFL; default 3 */
+  int32_t mode;           /* DCEM_MODE_FULL or DCEM_MODE_COHERENT                */
+  float rx_radius_scale;  /* capture radius = scale * alpha * (D+s) / sqrt(3),
+                             alpha = sqrt(4 pi / n_rays); default 1.35           */
+  float t_min;            /* self-hit offset after a reflection [m]; 1e-4        */
+  float escape_len;       /* capture length of a ray that leaves the scene; 1e4 */
+  float eps_occ;          /* occlusion ignores the first/last eps of a sub-
+                             segment (relative); default 1e-4                    */
+  float pol[3];           /* antenna polarisation reference u; default (0,0,1)  */
+  int32_t timing;         /* 1: record per-stage device times in the stats       */
+} dcem_params;
+
+/* One valid propagation path (Sec. III step 6). */
+typedef struct {
+  int32_t rx;                       /* receiver index                           */
+  int32_t depth;                    /* number of reflections k                  */
+  int32_t tri[DCEM_MAX_REFL];       /* reflecting triangle ids, Tx side first   */
+  uint32_t flags;                   /* DCEM_PATH_* bits                         */
+  int32_t ray;                      /* a ray that discovered the path           */
+  uint64_t key;                     /* 64-bit hash of (rx, depth, tri[0..k))    */
+  double len_m;                     /* unfolded path length L                   */
+  double delay_s;                   /* L / c                                    */
+  double amp_re, amp_im;            /* complex amplitude a (received field per
+                                       unit transmit amplitude, isotropic)      */
+  float pts[DCEM_MAX_REFL][3];      /* reflection points, Tx side first         */
+} dcem_path;
+
+typedef struct {
+  int64_t n_rays;              /* rays in the sampled sphere                     */
+  int64_t segments_traced;     /* closest-hit traversals this frame              */
+  int64_t segments_reused;     /* logged segments reused without traversal       */
+  int64_t rays_retraced;       /* rays (partially) retraced in COHERENT mode     */
+  int64_t candidates;          /* reception-sphere captures (with duplicates)    */
+  int64_t candidates_reused;   /* captures carried over from the previous frame  */
+  int64_t unique_candidates;   /* distinct (rx, depth, sequence) keys            */
+  int64_t paths_valid;         /* validated paths                                */
+  int64_t objects_moved;       /* rigid objects whose transform changed          */
+  int64_t rx_moved;            /* receivers whose position changed               */
+  int32_t stack_overflow;      /* traversals that overflowed the stack           */
+  int32_t coherent;            /* 1 if the frame reused the cache                */
+  float ms_stage[8];           /* if params.timing: prep, mark, trace, dedupe,
+                                  validate, reduce, copy-out, total              */
+} dcem_stats;
+
+typedef struct {
+  int32_t ptr_kind;     /* DCEM_PTR_HOST / DCEM_PTR_DEVICE for the arrays below */
+  int32_t max_paths;    /* capacity of `paths`                                  */
+  double* field;        /* nrx x 2 (re, im) of sum a, or NULL                   */
+  double* p_coh_dbm;    /* nrx: P_t |sum a|^2 in dBm (-inf without paths)      */
+  double* p_inc_dbm;    /* nrx: P_t sum |a|^2 in dBm                           */
+  dcem_path* paths;     /* max_paths records ordered by (rx, key), or NULL     */
+  int32_t n_paths;      /* out: number of valid paths (may exceed max_paths:
+                           then DCEM_ERR_CAPACITY and the first max_paths are
+                           written)                                             */
+  dcem_stats stats;     /* out                                                  */
+} dcem_result;
+
+/* Fills `p` with the defaults listed in dcem_params. */
+void dcem_params_default(dcem_params* p);
+
+/* Creates a scene on the current CUDA device (Sec. III: BVH built once).
+ *   tris     host, ntri*9 floats: v0,v1,v2 of each triangle; world space if
+ *            tri_obj[i] < 0, else object space of rigid object tri_obj[i]
+ *   tri_mat  host, ntri material indices into mats (0..nmat-1)
+ *   mats     host, nmat materials
+ *   tri_obj  host, ntri object ids (-1 static, else 0..nobj-1); NULL = all static
+ *   nobj     number of rigid objects (>= 0)
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ *   out      receives the scene handle
+ * Objects start at the identity transform until dcem_scene_update_transforms.
+ * Errors: DCEM_ERR_ARG, DCEM_ERR_NONFINITE, DCEM_ERR_CUDA, DCEM_ERR_NOMEM. */
+int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat,
+                      const dcem_material* mats, int32_t nmat, const int32_t* tri_obj,
+                      int32_t nobj, void* stream, dcem_scene** out);
+
+/* Sets the sampled sphere of ray directions (Sec. III step 1): host, n*3
+ * floats of unit vectors, uploaded once and reused every frame. n may be 0.
+ * Invalidates the coherence cache. */
+int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays);
+
+/* Per-frame update (Sec. III "Efficient BVH updating"): xf holds nobj
+ * row-major 3x4 transforms (host or device per ptr_kind). World vertices are
+ * recomputed as fmaf(R0,x, fmaf(R1,y, fmaf(R2,z,t))) per row and the moving
+ * objects' hierarchy is refit bottom-up. Asynchronous on the scene stream.
+ * Errors: DCEM_ERR_ARG; DCEM_ERR_NONFINITE if a host transform holds NaN/Inf
+ * (device transforms are checked on the device and reported by the next
+ * dcem_trace_frame). */
+int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kind);
+
+/* Traces one frame (Sec. III steps 1-4 and 6; coherence reuse when
+ * params->mode == DCEM_MODE_COHERENT and the cache is valid):
+ *   tx       host, 3 floats
+ *   rx       nrx*3 floats (host or device per rx_ptr_kind)
+ *   params   host
+ *   out      host struct; its arrays are caller-owned (see dcem_result)
+ * COHERENT mode falls back to a full retrace (stats.coherent = 0) when the
+ * ray set, tx, nrx or the parameters changed since the cached frame. Results
+ * equal a full retrace bit for bit. Synchronises the scene stream.
+ * Errors: DCEM_ERR_ARG, DCEM_ERR_STATE (no rays set), DCEM_ERR_NONFINITE,
+ * DCEM_ERR_CAPACITY (out->n_paths holds the required count),
+ * DCEM_ERR_STACK, DCEM_ERR_HASH, DCEM_ERR_CUDA. */
+int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nrx,
+                     int32_t rx_ptr_kind, const dcem_params* params, dcem_result* out);
+
+/* Drops the coherence cache: the next COHERENT frame is a full retrace. */
+int dcem_scene_reset_cache(dcem_scene* s);
+
+/* Changes the stream used by the scene (after synchronising the old one). */
+int dcem_scene_set_stream(dcem_scene* s, void* stream);
+
+/* Frees every device and host resource of the scene. NULL is a no-op. */
+void dcem_scene_destroy(dcem_scene* s);
+
+/* Static string for a status code. */
+const char* dcem_status_string(int status);
+
+/* ---- introspection (tests and tools; synchronise the scene stream) ---- */
+
+/* Counts of the scene: ntri, nobj, n_rays, internal nodes of the static and
+ * dynamic trees. Any pointer may be NULL. */
+int dcem_scene_info(const dcem_scene* s, int32_t* ntri, int32_t* nobj, int32_t* n_rays,
+                    int32_t* static_nodes, int32_t* dynamic_nodes);
+
+/* Current world-space vertices in input triangle order: host, ntri*9 floats. */
+int dcem_scene_get_world_tris(dcem_scene* s, float* out);
+
+/* The hierarchy as flat host arrays, static tree first then dynamic tree:
+ *   child   (static_nodes+dynamic_nodes)*2 int32: >= 0 internal node index,
+ *           < 0 leaf holding triangle id (-c-1)
+ *   bounds  (static_nodes+dynamic_nodes)*12 floats: lo.xyz, hi.xyz of child 0
+ *           then child 1 (bit-exact min/max of the children's vertices)
+ *   roots   2 int32: root code of the static and dynamic tree (node index,
+ *           leaf code as in `child`, or INT32_MIN when the tree is empty) */
+int dcem_scene_get_bvh(dcem_scene* s, int32_t* child, float* bounds, int32_t* roots);
+
+/* Per-ray log of the last traced frame: hit_id n_rays*(max_refl+1) int32
+ * (triangle id, -1 escaped, -2 not reached), hit_t same shape (FP32 ray
+ * parameter; +inf when escaped), nseg n_rays. Any pointer may be NULL. */
+int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t* nseg);
+
+/* Reception-sphere captures of the last traced frame as (ray, segment, rx)
+ * int32 triples in unspecified order. *n receives the count; at most cap
+ * triples are written (DCEM_ERR_CAPACITY if cap < count). */
+int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCEM_H */

@@ -1,0 +1,886 @@
+// api.cu -- the C ABI (include/dcem.h): scene state, device buffers and the
+// per-frame orchestration of the kernels on the scene's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bvh.cuh"
+#include "paths.cuh"
+#include "trace.cuh"
+
+using namespace dcem;
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  return cudaMalloc((void**)p, (n > 0 ? n : 1) * sizeof(T));
+}
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int status_of(cudaError_t e) {
+  if (e == cudaSuccess) return DCEM_OK;
+  if (e == cudaErrorMemoryAllocation) return DCEM_ERR_NOMEM;
+  return DCEM_ERR_CUDA;
+}
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) {               \
+      cudaGetLastError();                  \
+      return status_of(e_);                \
+    }                                      \
+  } while (0)
+
+unsigned pow2_at_least(unsigned long long v) {
+  unsigned long long p = 1;
+  while (p < v) p <<= 1;
+  return (unsigned)p;
+}
+
+__global__ void k_objv_src(const float* __restrict__ v9, const int* __restrict__ sel,
+                           const int* __restrict__ tri_obj, int n, float4* objv_src) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int gid = sel[i];
+    const float* v = v9 + 9 * (size_t)gid;
+    objv_src[3 * (size_t)i] = make_float4(v[0], v[1], v[2], __int_as_float(tri_obj[gid]));
+    objv_src[3 * (size_t)i + 1] = make_float4(v[3], v[4], v[5], 0.0f);
+    objv_src[3 * (size_t)i + 2] = make_float4(v[6], v[7], v[8], 0.0f);
+  }
+}
+
+// world vertices of the moving triangles in primitive order (for a rebuild)
+__global__ void k_xform_prims(const float4* __restrict__ objv_src, const float* __restrict__ xf, int n,
+                              float* v9) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* m = xf + 12 * (size_t)__float_as_int(objv_src[3 * (size_t)i].w);
+    for (int k = 0; k < 3; ++k) {
+      float4 p = objv_src[3 * (size_t)i + k];
+      for (int r = 0; r < 3; ++r)
+        v9[9 * (size_t)i + 3 * k + r] =
+            __fmaf_rn(m[4 * r], p.x, __fmaf_rn(m[4 * r + 1], p.y, __fmaf_rn(m[4 * r + 2], p.z, m[4 * r + 3])));
+    }
+  }
+}
+
+__global__ void k_place_dyn(const float* __restrict__ v9, const float4* __restrict__ objv_src,
+                            const int* __restrict__ perm, const int* __restrict__ sel,
+                            const int* __restrict__ tri_mat, int n, int leaf_base, float4* tris, float4* objv,
+                            int* slot_of_id) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int i = perm[j];
+    int gid = sel[i];
+    const float* v = v9 + 9 * (size_t)i;
+    int slot = leaf_base + j;
+    tris[3 * (size_t)slot] = make_float4(v[0], v[1], v[2], __int_as_float(gid));
+    tris[3 * (size_t)slot + 1] = make_float4(v[3], v[4], v[5], __int_as_float(tri_mat[gid]));
+    tris[3 * (size_t)slot + 2] = make_float4(v[6], v[7], v[8], 0.0f);
+    for (int k = 0; k < 3; ++k) objv[3 * (size_t)j + k] = objv_src[3 * (size_t)i + k];
+    slot_of_id[gid] = slot;
+  }
+}
+
+}  // namespace
+
+struct dcem_scene {
+  int device = 0;
+  int sms = 1;
+  cudaStream_t st = nullptr;
+  int ntri = 0, nobj = 0, nmat = 0, ns = 0, nd = 0, nint_s = 0, nint_d = 0;
+  // geometry and hierarchy
+  float4* tris = nullptr;
+  int* slot_of_id = nullptr;
+  float4* objv = nullptr;       // moving triangles, leaf order, object space
+  float4* objv_src = nullptr;   // moving triangles, primitive order, object space
+  int* sel_d = nullptr;         // primitive -> triangle id (moving tree)
+  int* tri_mat_d = nullptr;
+  float* v9d = nullptr;         // world vertices of moving primitives (rebuilds)
+  float4* nodes = nullptr;
+  int* leaf_parent = nullptr;
+  int* arrive = nullptr;
+  int* roots = nullptr;
+  float* root_box = nullptr;
+  int* perm = nullptr;
+  float* prim = nullptr;
+  float4* mats = nullptr;
+  float* xf_cur = nullptr;
+  float* xf_traced = nullptr;
+  unsigned* obj_box_cur = nullptr;
+  unsigned* obj_box_traced = nullptr;
+  float* moved_boxes = nullptr;
+  BuildScratch scr;
+  int root_h[2] = {kEmpty, kEmpty};
+  bool dyn_on_world = false;
+  DevCounters* ctr = nullptr;
+  DevCounters* uctr = nullptr;  // errors raised by per-frame updates
+  DevCounters* ctr_h = nullptr; // pinned: [0] frame counters, [1] update counters
+  // rays and segment log
+  bool rays_set = false;
+  int R = 0;
+  float4* rays = nullptr;
+  int logW = 0;
+  float4* log_o = nullptr;
+  float4* log_d = nullptr;
+  int* log_id = nullptr;
+  int* nseg = nullptr;
+  int* restart = nullptr;
+  int* queue = nullptr;
+  // captures and distinct paths
+  Cand* cand[2] = {nullptr, nullptr};
+  unsigned cand_cap = 0;
+  int cur = 0;
+  unsigned* prev_ncand = nullptr;
+  unsigned long long* hkey = nullptr;
+  unsigned long long* hrep = nullptr;
+  unsigned hcap = 0;
+  int* cand_slot = nullptr;
+  int* uniq = nullptr;
+  unsigned ucap = 0;
+  PathRec* prec = nullptr;
+  dcem_path* pout = nullptr;
+  // receivers
+  int nrx_cap = 0;
+  float* rx3 = nullptr;
+  float4* rx_cur = nullptr;
+  float4* rx_traced = nullptr;
+  unsigned char* rx_moved = nullptr;
+  int* moved_list = nullptr;
+  int* bucket = nullptr;
+  unsigned* bucket_cnt = nullptr;
+  int bucket_cap = 1024;
+  double* rxout = nullptr;
+  // coherence cache
+  bool cache_valid = false;
+  dcem_params cparams;
+  float ctx[3] = {0, 0, 0};
+  int cnrx = -1;
+  unsigned last_ncand = 0;
+  cudaEvent_t ev[9] = {};
+  bool events = false;
+};
+
+namespace {
+
+void scene_free(dcem_scene* s) {
+  if (!s) return;
+  if (s->st || true) cudaStreamSynchronize(s->st);
+  dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
+  dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->leaf_parent); dfree(s->arrive);
+  dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
+  dfree(s->xf_cur); dfree(s->xf_traced); dfree(s->obj_box_cur); dfree(s->obj_box_traced);
+  dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
+  dfree(s->scr.v1); dfree(s->scr.hist); dfree(s->scr.keys); dfree(s->ctr); dfree(s->uctr);
+  if (s->ctr_h) cudaFreeHost(s->ctr_h);
+  dfree(s->rays); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->nseg); dfree(s->restart);
+  dfree(s->queue); dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->prev_ncand); dfree(s->hkey);
+  dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
+  dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list); dfree(s->bucket);
+  dfree(s->bucket_cnt); dfree(s->rxout);
+  for (auto& e : s->ev)
+    if (e) cudaEventDestroy(e);
+  delete s;
+}
+
+bool finite_arr(const float* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int grid_cap_of(const dcem_scene* s, int per_sm) { return s->sms * per_sm; }
+
+int root_code(int n, int node_base, int leaf_base) {
+  return n >= 2 ? node_base : (n == 1 ? ~leaf_base : kEmpty);
+}
+
+// (Re)builds the moving-object tree over the objects' current world positions.
+int rebuild_dynamic(dcem_scene* s) {
+  if (s->nd == 0) return DCEM_OK;
+  int bs = 256, g = (s->nd + bs - 1) / bs;
+  k_xform_prims<<<g, bs, 0, s->st>>>(s->objv_src, s->xf_cur, s->nd, s->v9d);
+  launch_tri_boxes(s->v9d, nullptr, s->nd, s->prim, s->st);
+  CK(build_tree(s->prim, s->nd, s->nint_s, s->ns, s->nodes, s->leaf_parent, s->perm, s->arrive, s->roots + 1,
+                s->root_box + 6, s->scr, s->st));
+  k_place_dyn<<<g, bs, 0, s->st>>>(s->v9d, s->objv_src, s->perm, s->sel_d, s->tri_mat_d, s->nd, s->ns, s->tris,
+                                   s->objv, s->slot_of_id);
+  CK(cudaGetLastError());
+  return DCEM_OK;
+}
+
+int alloc_build_scratch(dcem_scene* s, int n) {
+  if (n <= kSmallBuild) return DCEM_OK;
+  int nb = (n + 1023) / 1024;
+  CK(dalloc(&s->scr.bounds, 6));
+  CK(dalloc(&s->scr.k0, n)); CK(dalloc(&s->scr.v0, n)); CK(dalloc(&s->scr.k1, n)); CK(dalloc(&s->scr.v1, n));
+  CK(dalloc(&s->scr.hist, (size_t)256 * nb));
+  CK(dalloc(&s->scr.keys, n));
+  return DCEM_OK;
+}
+
+int ensure_log(dcem_scene* s, int W) {
+  if (s->logW >= W && s->log_o) return DCEM_OK;
+  dfree(s->log_o); dfree(s->log_d); dfree(s->log_id);
+  size_t n = (size_t)W * (size_t)(s->R > 0 ? s->R : 1);
+  CK(dalloc(&s->log_o, n));
+  CK(dalloc(&s->log_d, n));
+  CK(dalloc(&s->log_id, n));
+  s->logW = W;
+  s->cache_valid = false;
+  return DCEM_OK;
+}
+
+int ensure_paths(dcem_scene* s, unsigned cand_cap, unsigned ucap) {
+  if (cand_cap > s->cand_cap) {
+    dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->cand_slot); dfree(s->hkey); dfree(s->hrep);
+    CK(dalloc(&s->cand[0], cand_cap));
+    CK(dalloc(&s->cand[1], cand_cap));
+    CK(dalloc(&s->cand_slot, cand_cap));
+    unsigned hcap = pow2_at_least(2ull * cand_cap);
+    CK(dalloc(&s->hkey, hcap));
+    CK(dalloc(&s->hrep, hcap));
+    CK(cudaMemsetAsync(s->hkey, 0, sizeof(unsigned long long) * hcap, s->st));
+    CK(cudaMemsetAsync(s->hrep, 0xff, sizeof(unsigned long long) * hcap, s->st));
+    s->hcap = hcap;
+    s->cand_cap = cand_cap;
+    s->cache_valid = false;  // previous captures are gone
+  }
+  if (ucap > s->ucap) {
+    dfree(s->uniq); dfree(s->prec); dfree(s->pout);
+    CK(dalloc(&s->uniq, ucap));
+    CK(dalloc(&s->prec, ucap));
+    CK(dalloc(&s->pout, ucap));
+    s->ucap = ucap;
+  }
+  return DCEM_OK;
+}
+
+int ensure_rx(dcem_scene* s, int nrx, int bucket_cap) {
+  if (nrx <= s->nrx_cap && bucket_cap <= s->bucket_cap && s->rx3) return DCEM_OK;
+  int cap = nrx > s->nrx_cap ? nrx : s->nrx_cap;
+  if (cap < 1) cap = 1;
+  dfree(s->rx3); dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list);
+  dfree(s->bucket); dfree(s->bucket_cnt); dfree(s->rxout);
+  CK(dalloc(&s->rx3, 3 * (size_t)cap));
+  CK(dalloc(&s->rx_cur, cap));
+  CK(dalloc(&s->rx_traced, cap));
+  CK(dalloc(&s->rx_moved, cap));
+  CK(dalloc(&s->moved_list, cap));
+  if (bucket_cap > s->bucket_cap) s->bucket_cap = bucket_cap;
+  CK(dalloc(&s->bucket, (size_t)cap * s->bucket_cap));
+  CK(dalloc(&s->bucket_cnt, cap));
+  CK(dalloc(&s->rxout, 4 * (size_t)cap));
+  s->nrx_cap = cap;
+  s->cache_valid = false;
+  return DCEM_OK;
+}
+
+bool same_traversal(const dcem_params& a, const dcem_params& b) {
+  return a.max_refl == b.max_refl && a.rx_radius_scale == b.rx_radius_scale && a.t_min == b.t_min &&
+         a.escape_len == b.escape_len;
+}
+
+float alpha_eff_of(const dcem_scene* s, const dcem_params* p) {
+  double alpha = std::sqrt(4.0 * M_PI / (double)(s->R > 0 ? s->R : 1));
+  return (float)((double)p->rx_radius_scale * alpha / std::sqrt(3.0));
+}
+
+}  // namespace
+
+extern "C" {
+
+void dcem_params_default(dcem_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->freq_hz = 28e9;
+  p->tx_power_w = 5.0;
+  p->max_refl = 3;
+  p->mode = DCEM_MODE_FULL;
+  p->rx_radius_scale = 1.35f;
+  p->t_min = 1e-4f;
+  p->escape_len = 1e4f;
+  p->eps_occ = 1e-4f;
+  p->pol[0] = 0.0f;
+  p->pol[1] = 0.0f;
+  p->pol[2] = 1.0f;
+  p->timing = 0;
+}
+
+const char* dcem_status_string(int st) {
+  switch (st) {
+    case DCEM_OK: return "ok";
+    case DCEM_ERR_ARG: return "invalid argument";
+    case DCEM_ERR_CUDA: return "CUDA error";
+    case DCEM_ERR_CAPACITY: return "capacity exceeded";
+    case DCEM_ERR_NONFINITE: return "non-finite input";
+    case DCEM_ERR_STACK: return "traversal stack overflow";
+    case DCEM_ERR_HASH: return "path-key hash collision";
+    case DCEM_ERR_STATE: return "call out of order";
+    case DCEM_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, const dcem_material* mats,
+                      int32_t nmat, const int32_t* tri_obj, int32_t nobj, void* stream, dcem_scene** out) {
+  if (!out) return DCEM_ERR_ARG;
+  *out = nullptr;
+  if (ntri < 0 || nmat < 0 || nobj < 0) return DCEM_ERR_ARG;
+  if (ntri > 0 && (!tris || !tri_mat)) return DCEM_ERR_ARG;
+  if (nmat > 0 && !mats) return DCEM_ERR_ARG;
+  if (ntri > 0 && nmat == 0) return DCEM_ERR_ARG;
+  if (ntri > (1 << 26)) return DCEM_ERR_ARG;
+  for (int i = 0; i < ntri; ++i) {
+    if (tri_mat[i] < 0 || tri_mat[i] >= nmat) return DCEM_ERR_ARG;
+    if (tri_obj && (tri_obj[i] < -1 || tri_obj[i] >= nobj)) return DCEM_ERR_ARG;
+  }
+  for (int m = 0; m < nmat; ++m)
+    if (!std::isfinite(mats[m].eps_r) || !std::isfinite(mats[m].sigma) || mats[m].sigma < 0.0f)
+      return DCEM_ERR_ARG;
+  if (ntri > 0 && !finite_arr(tris, 9 * (size_t)ntri)) return DCEM_ERR_NONFINITE;
+
+  dcem_scene* s = new (std::nothrow) dcem_scene();
+  if (!s) return DCEM_ERR_NOMEM;
+  dcem_params_default(&s->cparams);
+  int rc = DCEM_OK;
+  auto fail = [&](int code) {
+    scene_free(s);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(status_of(e)); }
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (s->sms < 1) s->sms = 1;
+  s->st = (cudaStream_t)stream;
+  s->ntri = ntri;
+  s->nobj = nobj;
+  s->nmat = nmat;
+  std::vector<int> sel_s, sel_d;
+  for (int i = 0; i < ntri; ++i) ((tri_obj && tri_obj[i] >= 0) ? sel_d : sel_s).push_back(i);
+  s->ns = (int)sel_s.size();
+  s->nd = (int)sel_d.size();
+  s->nint_s = s->ns > 1 ? s->ns - 1 : 0;
+  s->nint_d = s->nd > 1 ? s->nd - 1 : 0;
+  int nmax = s->ns > s->nd ? s->ns : s->nd;
+
+  float* v9 = nullptr;
+  int *tri_obj_d = nullptr, *sel_s_d = nullptr;
+  auto fail2 = [&](int code) {
+    dfree(v9); dfree(tri_obj_d); dfree(sel_s_d);
+    return fail(code);
+  };
+#define CKF(x)                                  \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      cudaGetLastError();                       \
+      return fail2(status_of(e_));              \
+    }                                           \
+  } while (0)
+  CKF(dalloc(&s->tris, 3 * (size_t)ntri));
+  CKF(dalloc(&s->slot_of_id, ntri));
+  CKF(dalloc(&s->objv, 3 * (size_t)s->nd));
+  CKF(dalloc(&s->objv_src, 3 * (size_t)s->nd));
+  CKF(dalloc(&s->sel_d, s->nd));
+  CKF(dalloc(&s->tri_mat_d, ntri));
+  CKF(dalloc(&s->v9d, 9 * (size_t)s->nd));
+  CKF(dalloc(&s->nodes, 4 * (size_t)(s->nint_s + s->nint_d)));
+  CKF(dalloc(&s->leaf_parent, ntri));
+  CKF(dalloc(&s->arrive, nmax));
+  CKF(dalloc(&s->roots, 2));
+  CKF(dalloc(&s->root_box, 12));
+  CKF(dalloc(&s->perm, nmax));
+  CKF(dalloc(&s->prim, 6 * (size_t)nmax));
+  CKF(dalloc(&s->mats, nmat));
+  CKF(dalloc(&s->xf_cur, 12 * (size_t)nobj));
+  CKF(dalloc(&s->xf_traced, 12 * (size_t)nobj));
+  CKF(dalloc(&s->obj_box_cur, 6 * (size_t)nobj));
+  CKF(dalloc(&s->obj_box_traced, 6 * (size_t)nobj));
+  CKF(dalloc(&s->moved_boxes, 12 * (size_t)nobj));
+  CKF(dalloc(&s->ctr, 1));
+  CKF(dalloc(&s->uctr, 1));
+  CKF(dalloc(&s->prev_ncand, 1));
+  CKF(cudaMallocHost((void**)&s->ctr_h, 2 * sizeof(DevCounters)));
+  if ((rc = alloc_build_scratch(s, nmax)) != DCEM_OK) return fail2(rc);
+  CKF(dalloc(&v9, 9 * (size_t)ntri));
+  CKF(dalloc(&tri_obj_d, ntri));
+  CKF(dalloc(&sel_s_d, s->ns));
+  cudaStream_t st = s->st;
+  if (ntri > 0) {
+    CKF(cudaMemcpyAsync(v9, tris, sizeof(float) * 9 * (size_t)ntri, cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync(s->tri_mat_d, tri_mat, sizeof(int) * ntri, cudaMemcpyHostToDevice, st));
+    std::vector<int> to(ntri, -1);
+    if (tri_obj) std::memcpy(to.data(), tri_obj, sizeof(int) * ntri);
+    CKF(cudaMemcpyAsync(tri_obj_d, to.data(), sizeof(int) * ntri, cudaMemcpyHostToDevice, st));
+    CKF(cudaStreamSynchronize(st));  // `to` goes out of scope
+  }
+  if (s->ns) CKF(cudaMemcpyAsync(sel_s_d, sel_s.data(), sizeof(int) * s->ns, cudaMemcpyHostToDevice, st));
+  if (s->nd) CKF(cudaMemcpyAsync(s->sel_d, sel_d.data(), sizeof(int) * s->nd, cudaMemcpyHostToDevice, st));
+  std::vector<float4> mh(nmat > 0 ? nmat : 1);
+  for (int m = 0; m < nmat; ++m) mh[m] = make_float4(mats[m].eps_r, mats[m].sigma, mats[m].pec ? 1.0f : 0.0f, 0.0f);
+  if (nmat) CKF(cudaMemcpyAsync(s->mats, mh.data(), sizeof(float4) * nmat, cudaMemcpyHostToDevice, st));
+  // static tree (built once)
+  launch_tri_boxes(v9, sel_s_d, s->ns, s->prim, st);
+  CKF(build_tree(s->prim, s->ns, 0, 0, s->nodes, s->leaf_parent, s->perm, s->arrive, s->roots, s->root_box,
+                 s->scr, st));
+  launch_place_tris(v9, sel_s_d, s->perm, s->tri_mat_d, tri_obj_d, s->ns, 0, s->tris, nullptr, s->slot_of_id, st);
+  CKF(cudaGetLastError());
+  // moving objects: identity transforms until the first update
+  if (s->nd) {
+    int g = (s->nd + 255) / 256;
+    k_objv_src<<<g, 256, 0, st>>>(v9, s->sel_d, tri_obj_d, s->nd, s->objv_src);
+    CKF(cudaGetLastError());
+  }
+  if (nobj) {
+    std::vector<float> id(12 * (size_t)nobj, 0.0f);
+    for (int o = 0; o < nobj; ++o) id[12 * o] = id[12 * o + 5] = id[12 * o + 10] = 1.0f;
+    CKF(cudaMemcpyAsync(s->xf_cur, id.data(), sizeof(float) * id.size(), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync(s->xf_traced, id.data(), sizeof(float) * id.size(), cudaMemcpyHostToDevice, st));
+    CKF(cudaStreamSynchronize(st));
+  }
+  if ((rc = rebuild_dynamic(s)) != DCEM_OK) return fail2(rc);
+  CKF(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
+  CKF(cudaMemsetAsync(s->uctr, 0, sizeof(DevCounters), st));
+  CKF(cudaMemsetAsync(s->prev_ncand, 0, sizeof(unsigned), st));
+  if (nobj) {
+    CKF(cudaMemsetAsync(s->obj_box_cur, 0xff, sizeof(unsigned) * 3 * nobj, st));
+    CKF(cudaMemsetAsync(s->obj_box_cur + 3 * nobj, 0, sizeof(unsigned) * 3 * nobj, st));
+    if (s->nd) {
+      CKF(cudaMemsetAsync(s->arrive, 0, sizeof(int) * (s->nint_d > 0 ? s->nint_d : 1), st));
+      launch_transform_refit(s->objv, s->xf_cur, s->nd, nobj, s->nint_s, s->ns, s->tris, s->nodes, s->leaf_parent,
+                             s->arrive, s->root_box + 6, s->obj_box_cur, s->uctr, st);
+      CKF(cudaGetLastError());
+    }
+    CKF(cudaMemcpyAsync(s->obj_box_traced, s->obj_box_cur, sizeof(unsigned) * 6 * nobj, cudaMemcpyDeviceToDevice, st));
+  }
+  s->root_h[0] = root_code(s->ns, 0, 0);
+  s->root_h[1] = root_code(s->nd, s->nint_s, s->ns);
+  CKF(cudaStreamSynchronize(st));
+  for (auto& ev : s->ev) CKF(cudaEventCreate(&ev));
+  dfree(v9); dfree(tri_obj_d); dfree(sel_s_d);
+#undef CKF
+  *out = s;
+  return DCEM_OK;
+}
+
+int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays) {
+  if (!s || n_rays < 0 || (n_rays > 0 && !dirs)) return DCEM_ERR_ARG;
+  if (n_rays > 0 && !finite_arr(dirs, 3 * (size_t)n_rays)) return DCEM_ERR_NONFINITE;
+  for (int i = 0; i < n_rays; ++i) {
+    float x = dirs[3 * i], y = dirs[3 * i + 1], z = dirs[3 * i + 2];
+    if (!(x * x + y * y + z * z > 0.0f)) return DCEM_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(s->st));
+  dfree(s->rays); dfree(s->nseg); dfree(s->restart); dfree(s->queue);
+  dfree(s->log_o); dfree(s->log_d); dfree(s->log_id);
+  s->logW = 0;
+  s->R = n_rays;
+  CK(dalloc(&s->rays, n_rays));
+  CK(dalloc(&s->nseg, n_rays));
+  CK(dalloc(&s->restart, n_rays));
+  CK(dalloc(&s->queue, n_rays));
+  std::vector<float4> h(n_rays > 0 ? n_rays : 1);
+  for (int i = 0; i < n_rays; ++i) h[i] = make_float4(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], 0.0f);
+  if (n_rays) CK(cudaMemcpy(s->rays, h.data(), sizeof(float4) * n_rays, cudaMemcpyHostToDevice));
+  s->rays_set = true;
+  s->cache_valid = false;
+  return DCEM_OK;
+}
+
+int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kind) {
+  if (!s) return DCEM_ERR_ARG;
+  if (ptr_kind != DCEM_PTR_HOST && ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
+  if (s->nobj == 0) return DCEM_OK;
+  if (!xf) return DCEM_ERR_ARG;
+  if (ptr_kind == DCEM_PTR_HOST && !finite_arr(xf, 12 * (size_t)s->nobj)) return DCEM_ERR_NONFINITE;
+  cudaStream_t st = s->st;
+  CK(cudaMemcpyAsync(s->xf_cur, xf, sizeof(float) * 12 * s->nobj,
+                     ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  if (!s->dyn_on_world) {
+    int rc = rebuild_dynamic(s);
+    if (rc != DCEM_OK) return rc;
+    s->dyn_on_world = true;
+  }
+  CK(cudaMemsetAsync(s->obj_box_cur, 0xff, sizeof(unsigned) * 3 * s->nobj, st));
+  CK(cudaMemsetAsync(s->obj_box_cur + 3 * s->nobj, 0, sizeof(unsigned) * 3 * s->nobj, st));
+  if (s->nd) {
+    CK(cudaMemsetAsync(s->arrive, 0, sizeof(int) * (s->nint_d > 0 ? s->nint_d : 1), st));
+    launch_transform_refit(s->objv, s->xf_cur, s->nd, s->nobj, s->nint_s, s->ns, s->tris, s->nodes,
+                           s->leaf_parent, s->arrive, s->root_box + 6, s->obj_box_cur, s->uctr, st);
+    CK(cudaGetLastError());
+  }
+  return DCEM_OK;
+}
+
+int dcem_scene_reset_cache(dcem_scene* s) {
+  if (!s) return DCEM_ERR_ARG;
+  s->cache_valid = false;
+  return DCEM_OK;
+}
+
+int dcem_scene_set_stream(dcem_scene* s, void* stream) {
+  if (!s) return DCEM_ERR_ARG;
+  CK(cudaStreamSynchronize(s->st));
+  s->st = (cudaStream_t)stream;
+  return DCEM_OK;
+}
+
+void dcem_scene_destroy(dcem_scene* s) { scene_free(s); }
+
+static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent) {
+  cudaStream_t st = s->st;
+  int N = p->max_refl;
+  int nxt = s->cur ^ 1;
+  bool tm = p->timing != 0;
+  if (tm) CK(cudaEventRecord(s->ev[0], st));
+  CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
+  if (nrx) CK(cudaMemsetAsync(s->bucket_cnt, 0, sizeof(unsigned) * nrx, st));
+  CK(launch_rx_pack(s->rx3, nrx, s->rx_cur, s->rx_traced, coherent ? 1 : 0, s->rx_moved, s->moved_list, s->ctr, st));
+
+  TraceArgs a;
+  a.bvh.nodes = s->nodes;
+  a.bvh.tris = s->tris;
+  a.bvh.root0 = s->root_h[0];
+  a.bvh.root1 = s->root_h[1];
+  a.bvh.max_visits = 2 * (s->nint_s + s->nint_d + s->ntri) + 8;
+  a.rays = s->rays;
+  a.tx = make_float3(tx[0], tx[1], tx[2]);
+  a.R = s->R;
+  a.N = N;
+  a.tmin = p->t_min;
+  a.escape = p->escape_len;
+  a.alpha_eff = alpha_eff_of(s, p);
+  a.rx = s->rx_cur;
+  a.nrx = nrx;
+  a.log_o = s->log_o;
+  a.log_d = s->log_d;
+  a.log_id = s->log_id;
+  a.nseg = s->nseg;
+  a.queue = nullptr;
+  a.queue_w = s->queue;
+  a.restart = s->restart;
+  a.nq_dev = &s->ctr->n_retrace;
+  a.cand = s->cand[nxt];
+  a.cand_cap = s->cand_cap;
+  a.ctr = s->ctr;
+  if (coherent) {
+    CoherentArgs c;
+    c.nobj = s->nobj;
+    c.xf_cur = s->xf_cur;
+    c.xf_traced = s->xf_traced;
+    c.obj_box_cur = s->obj_box_cur;
+    c.obj_box_traced = s->obj_box_traced;
+    c.moved_boxes = s->moved_boxes;
+    c.moved_list = s->moved_list;
+    c.rx_moved = s->rx_moved;
+    c.restart = s->restart;
+    c.ctr = s->ctr;
+    c.prev_cand = s->cand[s->cur];
+    c.prev_ncand = s->prev_ncand;
+    c.prev_cap = s->cand_cap;
+    c.smem_boxes = 2 * s->nobj < kMovedSmem ? 2 * s->nobj : kMovedSmem;
+    c.smem_rx = nrx < kRxSmem ? nrx : kRxSmem;
+    CK(launch_coherent_prep(c, st));
+    if (tm) CK(cudaEventRecord(s->ev[1], st));
+    CK(launch_mark(a, c, grid_cap_of(s, 8), st));
+    CK(launch_carry(a, c, st));
+    if (tm) CK(cudaEventRecord(s->ev[2], st));
+    a.queue = s->queue;
+  } else {
+    if (tm) {
+      CK(cudaEventRecord(s->ev[1], st));
+      CK(cudaEventRecord(s->ev[2], st));
+    }
+  }
+  if (s->R > 0) CK(launch_trace(a, grid_cap_of(s, 16), st));
+  if (tm) CK(cudaEventRecord(s->ev[3], st));
+
+  PathArgs q;
+  q.R = s->R;
+  q.log_id = s->log_id;
+  q.cand = s->cand[nxt];
+  q.cand_cap = s->cand_cap;
+  q.hkey = s->hkey;
+  q.hrep = s->hrep;
+  q.hcap = s->hcap;
+  q.cand_slot = s->cand_slot;
+  q.uniq = s->uniq;
+  q.ucap = s->ucap;
+  q.prec = s->prec;
+  q.bucket = s->bucket;
+  q.bucket_cnt = s->bucket_cnt;
+  q.bucket_cap = s->bucket_cap;
+  q.pout = s->pout;
+  q.pout_cap = s->ucap;
+  q.rxout = s->rxout;
+  q.tris = s->tris;
+  q.slot_of_id = s->slot_of_id;
+  q.mats = s->mats;
+  q.bvh = a.bvh;
+  q.rx = s->rx_cur;
+  q.tx = a.tx;
+  q.pol = make_float3(p->pol[0], p->pol[1], p->pol[2]);
+  q.eps_occ = p->eps_occ;
+  q.freq = p->freq_hz;
+  q.tx_power = p->tx_power_w;
+  q.ctr = s->ctr;
+  CK(launch_dedupe(q, grid_cap_of(s, 4), st));
+  if (tm) CK(cudaEventRecord(s->ev[4], st));
+  CK(launch_validate(q, grid_cap_of(s, 4), st));
+  if (tm) CK(cudaEventRecord(s->ev[5], st));
+  CK(launch_reduce(q, nrx, st));
+  if (tm) CK(cudaEventRecord(s->ev[6], st));
+  // state the next frame compares against
+  CK(cudaMemcpyAsync(s->prev_ncand, &s->ctr->n_cand, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+  if (nrx) CK(cudaMemcpyAsync(s->rx_traced, s->rx_cur, sizeof(float4) * nrx, cudaMemcpyDeviceToDevice, st));
+  if (s->nobj) {
+    CK(cudaMemcpyAsync(s->xf_traced, s->xf_cur, sizeof(float) * 12 * s->nobj, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s->obj_box_traced, s->obj_box_cur, sizeof(unsigned) * 6 * s->nobj,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaMemcpyAsync(s->ctr_h, s->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(s->ctr_h + 1, s->uctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(s->uctr, 0, sizeof(DevCounters), st));
+  CK(cudaStreamSynchronize(st));
+  s->cur = nxt;
+  return DCEM_OK;
+}
+
+int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                     const dcem_params* p, dcem_result* out) {
+  if (!s || !tx || !p || !out) return DCEM_ERR_ARG;
+  if (nrx < 0 || (nrx > 0 && !rx)) return DCEM_ERR_ARG;
+  if (nrx >= (1 << 27)) return DCEM_ERR_ARG;
+  if (rx_ptr_kind != DCEM_PTR_HOST && rx_ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
+  if (out->ptr_kind != DCEM_PTR_HOST && out->ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
+  if (out->max_paths < 0 || (out->max_paths > 0 && !out->paths)) return DCEM_ERR_ARG;
+  if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
+  if (p->mode != DCEM_MODE_FULL && p->mode != DCEM_MODE_COHERENT) return DCEM_ERR_ARG;
+  if (!(p->freq_hz > 0) || !std::isfinite(p->freq_hz) || !(p->tx_power_w > 0) || !std::isfinite(p->tx_power_w))
+    return DCEM_ERR_ARG;
+  if (!(p->rx_radius_scale > 0) || !std::isfinite(p->rx_radius_scale) || !(p->t_min >= 0) ||
+      !std::isfinite(p->t_min) || !(p->escape_len > 0) || !std::isfinite(p->escape_len) ||
+      !(p->eps_occ >= 0) || !(p->eps_occ < 0.5f))
+    return DCEM_ERR_ARG;
+  if (!finite_arr(p->pol, 3) || !(p->pol[0] * p->pol[0] + p->pol[1] * p->pol[1] + p->pol[2] * p->pol[2] > 0))
+    return DCEM_ERR_ARG;
+  if (!finite_arr(tx, 3)) return DCEM_ERR_NONFINITE;
+  if (rx_ptr_kind == DCEM_PTR_HOST && nrx > 0 && !finite_arr(rx, 3 * (size_t)nrx)) return DCEM_ERR_NONFINITE;
+  if (!s->rays_set) return DCEM_ERR_STATE;
+  std::memset(&out->stats, 0, sizeof(out->stats));
+  out->n_paths = 0;
+
+  int rc;
+  if ((rc = ensure_log(s, p->max_refl + 1)) != DCEM_OK) return rc;
+  unsigned want_c = s->cand_cap ? s->cand_cap : (unsigned)std::max(65536, s->R / 8);
+  unsigned want_u = s->ucap ? s->ucap : std::min(want_c, 1u << 18);
+  if ((rc = ensure_paths(s, want_c, want_u)) != DCEM_OK) return rc;
+  if ((rc = ensure_rx(s, nrx, s->bucket_cap)) != DCEM_OK) return rc;
+  cudaStream_t st = s->st;
+  if (nrx)
+    CK(cudaMemcpyAsync(s->rx3, rx, sizeof(float) * 3 * nrx,
+                       rx_ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+
+  bool coherent = p->mode == DCEM_MODE_COHERENT && s->cache_valid && same_traversal(*p, s->cparams) &&
+                  nrx == s->cnrx && std::memcmp(tx, s->ctx, sizeof(s->ctx)) == 0 &&
+                  s->logW == p->max_refl + 1;
+  DevCounters* c = nullptr;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    rc = trace_once(s, tx, nrx, p, coherent);
+    if (rc != DCEM_OK) {
+      s->cache_valid = false;
+      return rc;
+    }
+    c = s->ctr_h;
+    unsigned err = c[0].err | c[1].err;
+    unsigned grow = err & (ERR_CAND_OVERFLOW | ERR_UNIQUE_OVERFLOW | ERR_HASH_FULL | ERR_BUCKET_OVERFLOW);
+    if (!grow) break;
+    // internal capacity exceeded: grow and retrace the frame from scratch
+    CK(cudaStreamSynchronize(st));
+    unsigned nc = std::max(s->cand_cap, (unsigned)std::min<unsigned long long>(
+                                            0x3fffffffull, (unsigned long long)c[0].n_cand * 3 / 2 + 1024));
+    unsigned nu = std::max(s->ucap, std::min(nc, c[0].n_unique * 3 / 2 + 1024));
+    if (err & (ERR_CAND_OVERFLOW | ERR_HASH_FULL)) nc = std::max(nc, 2 * s->cand_cap);
+    if ((rc = ensure_paths(s, nc, nu)) != DCEM_OK) return rc;
+    CK(cudaMemsetAsync(s->hkey, 0, sizeof(unsigned long long) * s->hcap, st));
+    CK(cudaMemsetAsync(s->hrep, 0xff, sizeof(unsigned long long) * s->hcap, st));
+    if (err & ERR_BUCKET_OVERFLOW) {
+      int nb = s->bucket_cap * 2;
+      if (nb > 8192) {
+        s->cache_valid = false;
+        return DCEM_ERR_CAPACITY;
+      }
+      if ((rc = ensure_rx(s, nrx, nb)) != DCEM_OK) return rc;
+      CK(cudaMemcpyAsync(s->rx3, rx, sizeof(float) * 3 * nrx,
+                         rx_ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    }
+    coherent = false;
+    s->cache_valid = false;
+    if (attempt == 3) return DCEM_ERR_CAPACITY;
+  }
+  unsigned err = c[0].err | c[1].err;
+  dcem_stats& S = out->stats;
+  S.n_rays = s->R;
+  S.segments_traced = (int64_t)c[0].segments_traced;
+  S.segments_reused = (int64_t)c[0].segments_reused;
+  S.rays_retraced = coherent ? (int64_t)c[0].n_retrace : (int64_t)s->R;
+  S.candidates = c[0].n_cand;
+  S.candidates_reused = c[0].n_cand_reused;
+  S.unique_candidates = c[0].n_unique;
+  S.paths_valid = c[0].n_valid;
+  S.objects_moved = coherent ? (int64_t)c[0].objects_moved : (int64_t)s->nobj;
+  S.rx_moved = c[0].rx_moved;
+  S.stack_overflow = (int32_t)c[0].stack_overflow;
+  S.coherent = coherent ? 1 : 0;
+  s->last_ncand = std::min(c[0].n_cand, s->cand_cap);
+  if (err & ERR_HASH_COLLISION) {
+    s->cache_valid = false;
+    CK(cudaMemsetAsync(s->hkey, 0, sizeof(unsigned long long) * s->hcap, st));
+    CK(cudaMemsetAsync(s->hrep, 0xff, sizeof(unsigned long long) * s->hcap, st));
+    return DCEM_ERR_HASH;
+  }
+  if (err & ERR_NONFINITE) {
+    s->cache_valid = false;
+    return DCEM_ERR_NONFINITE;
+  }
+  // copy out
+  bool tm = p->timing != 0;
+  cudaMemcpyKind k = out->ptr_kind == DCEM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (nrx) {
+    if (out->field) CK(cudaMemcpy2DAsync(out->field, 16, s->rxout, 32, 16, nrx, k, st));
+    if (out->p_coh_dbm) CK(cudaMemcpy2DAsync(out->p_coh_dbm, 8, s->rxout + 2, 32, 8, nrx, k, st));
+    if (out->p_inc_dbm) CK(cudaMemcpy2DAsync(out->p_inc_dbm, 8, s->rxout + 3, 32, 8, nrx, k, st));
+  }
+  int nvalid = (int)c[0].n_valid;
+  int ncopy = std::min(nvalid, out->max_paths);
+  if (ncopy > 0) CK(cudaMemcpyAsync(out->paths, s->pout, sizeof(dcem_path) * ncopy, k, st));
+  if (tm) CK(cudaEventRecord(s->ev[7], st));
+  CK(cudaStreamSynchronize(st));
+  if (tm) {
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&S.ms_stage[i], s->ev[i], s->ev[i + 1]);
+    cudaEventElapsedTime(&S.ms_stage[7], s->ev[0], s->ev[7]);
+  }
+  out->n_paths = nvalid;
+  s->cache_valid = true;
+  s->cparams = *p;
+  std::memcpy(s->ctx, tx, sizeof(s->ctx));
+  s->cnrx = nrx;
+  if (err & ERR_STACK) return DCEM_ERR_STACK;
+  if (nvalid > out->max_paths && out->paths) return DCEM_ERR_CAPACITY;
+  return DCEM_OK;
+}
+
+int dcem_scene_info(const dcem_scene* s, int32_t* ntri, int32_t* nobj, int32_t* n_rays, int32_t* static_nodes,
+                    int32_t* dynamic_nodes) {
+  if (!s) return DCEM_ERR_ARG;
+  if (ntri) *ntri = s->ntri;
+  if (nobj) *nobj = s->nobj;
+  if (n_rays) *n_rays = s->R;
+  if (static_nodes) *static_nodes = s->nint_s;
+  if (dynamic_nodes) *dynamic_nodes = s->nint_d;
+  return DCEM_OK;
+}
+
+int dcem_scene_get_world_tris(dcem_scene* s, float* out) {
+  if (!s || (!out && s->ntri > 0)) return DCEM_ERR_ARG;
+  if (s->ntri == 0) return DCEM_OK;
+  std::vector<float4> t(3 * (size_t)s->ntri);
+  CK(cudaStreamSynchronize(s->st));
+  CK(cudaMemcpy(t.data(), s->tris, sizeof(float4) * t.size(), cudaMemcpyDeviceToHost));
+  for (int slot = 0; slot < s->ntri; ++slot) {
+    int id;
+    std::memcpy(&id, &t[3 * (size_t)slot].w, 4);
+    if (id < 0 || id >= s->ntri) return DCEM_ERR_STATE;
+    for (int k = 0; k < 3; ++k) {
+      out[9 * (size_t)id + 3 * k] = t[3 * (size_t)slot + k].x;
+      out[9 * (size_t)id + 3 * k + 1] = t[3 * (size_t)slot + k].y;
+      out[9 * (size_t)id + 3 * k + 2] = t[3 * (size_t)slot + k].z;
+    }
+  }
+  return DCEM_OK;
+}
+
+int dcem_scene_get_bvh(dcem_scene* s, int32_t* child, float* bounds, int32_t* roots) {
+  if (!s) return DCEM_ERR_ARG;
+  int nn = s->nint_s + s->nint_d;
+  std::vector<float4> nodes(4 * (size_t)(nn > 0 ? nn : 1));
+  std::vector<float4> t(3 * (size_t)(s->ntri > 0 ? s->ntri : 1));
+  CK(cudaStreamSynchronize(s->st));
+  if (nn) CK(cudaMemcpy(nodes.data(), s->nodes, sizeof(float4) * 4 * nn, cudaMemcpyDeviceToHost));
+  if (s->ntri) CK(cudaMemcpy(t.data(), s->tris, sizeof(float4) * 3 * s->ntri, cudaMemcpyDeviceToHost));
+  auto conv = [&](int code) -> int {
+    if (code == kEmpty || code >= 0) return code;
+    int id;
+    std::memcpy(&id, &t[3 * (size_t)(~code)].w, 4);
+    return -id - 1;
+  };
+  for (int i = 0; i < nn; ++i) {
+    const float4* n = &nodes[4 * (size_t)i];
+    int c0, c1;
+    std::memcpy(&c0, &n[3].x, 4);
+    std::memcpy(&c1, &n[3].y, 4);
+    if (child) {
+      child[2 * i] = conv(c0);
+      child[2 * i + 1] = conv(c1);
+    }
+    if (bounds) {
+      float* b = bounds + 12 * (size_t)i;
+      b[0] = n[0].x; b[1] = n[0].z; b[2] = n[2].x; b[3] = n[0].y; b[4] = n[0].w; b[5] = n[2].y;
+      b[6] = n[1].x; b[7] = n[1].z; b[8] = n[2].z; b[9] = n[1].y; b[10] = n[1].w; b[11] = n[2].w;
+    }
+  }
+  if (roots) {
+    roots[0] = conv(s->root_h[0]);
+    roots[1] = conv(s->root_h[1]);
+  }
+  return DCEM_OK;
+}
+
+int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t* nseg) {
+  if (!s) return DCEM_ERR_ARG;
+  if (!s->rays_set || s->logW == 0) return DCEM_ERR_STATE;
+  int R = s->R, W = s->cparams.max_refl + 1;
+  CK(cudaStreamSynchronize(s->st));
+  std::vector<int> ns(R > 0 ? R : 1), ids((size_t)W * (R > 0 ? R : 1));
+  std::vector<float4> ld((size_t)W * (R > 0 ? R : 1));
+  if (R) {
+    CK(cudaMemcpy(ns.data(), s->nseg, sizeof(int) * R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ids.data(), s->log_id, sizeof(int) * (size_t)W * R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ld.data(), s->log_d, sizeof(float4) * (size_t)W * R, cudaMemcpyDeviceToHost));
+  }
+  for (int i = 0; i < R; ++i) {
+    if (nseg) nseg[i] = ns[i];
+    for (int b = 0; b < W; ++b) {
+      bool live = b < ns[i];
+      if (hit_id) hit_id[(size_t)i * W + b] = live ? ids[(size_t)b * R + i] : -2;
+      if (hit_t) hit_t[(size_t)i * W + b] = live ? ld[(size_t)b * R + i].w : NAN;
+    }
+  }
+  return DCEM_OK;
+}
+
+int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t* n) {
+  if (!s || !n || cap < 0 || (cap > 0 && !out)) return DCEM_ERR_ARG;
+  *n = s->last_ncand;
+  if (s->last_ncand == 0) return DCEM_OK;
+  std::vector<Cand> c(s->last_ncand);
+  CK(cudaStreamSynchronize(s->st));
+  CK(cudaMemcpy(c.data(), s->cand[s->cur], sizeof(Cand) * c.size(), cudaMemcpyDeviceToHost));
+  int64_t m = std::min<int64_t>(cap, (int64_t)c.size());
+  for (int64_t i = 0; i < m; ++i) {
+    out[3 * i] = c[i].ray;
+    out[3 * i + 1] = cand_seg(c[i]);
+    out[3 * i + 2] = cand_rx(c[i]);
+  }
+  return cap < (int64_t)c.size() ? DCEM_ERR_CAPACITY : DCEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,528 @@
+// bvh.cu -- LBVH construction (once per scene) and per-frame update.
+//
+// Sec. III "Efficient BVH updating": the hierarchy over the scene is built
+// once and updated (refit) every frame instead of rebuilt. Construction is a
+// linear BVH: 30-bit Morton codes of primitive centroids, a stable sort, and
+// the binary radix tree of Karras (HPG 2012) over the (code, index) keys. One
+// primitive per leaf. The refit walks bottom-up; the second child to arrive at
+// a node (atomic counter) unions the two child boxes and continues, so every
+// box is the exact min/max of its leaves' FP32 vertices.
+//
+// Per frame, the moving objects' vertices are transformed
+// (fmaf(R0,x, fmaf(R1,y, fmaf(R2,z,t))) per row) inside the refit kernel.
+#include "bvh.cuh"
+
+namespace dcem {
+
+// ---------------------------------------------------------------------------
+// Morton codes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned expand_bits10(unsigned v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__device__ __forceinline__ unsigned morton30(float cx, float cy, float cz, const float* lo,
+                                             const float* ext_inv) {
+  float q[3] = {(cx - lo[0]) * ext_inv[0], (cy - lo[1]) * ext_inv[1], (cz - lo[2]) * ext_inv[2]};
+  unsigned b[3];
+  for (int k = 0; k < 3; ++k) {
+    float f = fminf(fmaxf(q[k] * 1024.0f, 0.0f), 1023.0f);
+    b[k] = (unsigned)f;
+  }
+  return (expand_bits10(b[0]) << 2) | (expand_bits10(b[1]) << 1) | expand_bits10(b[2]);
+}
+
+__device__ __forceinline__ int delta64(const unsigned long long* k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  return __clzll(k[i] ^ k[j]);
+}
+
+// Karras' radix-tree node i over n sorted unique keys. Writes child codes
+// (internal: node_base + c, leaf: ~(leaf_base + c)) and parents.
+__device__ __forceinline__ void karras_node(const unsigned long long* k, int n, int i, int node_base,
+                                            int leaf_base, float4* nodes, int* leaf_parent) {
+  int d = (delta64(k, n, i, i + 1) - delta64(k, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta64(k, n, i, i - d);
+  int lmax = 2;
+  while (delta64(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta64(k, n, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = delta64(k, n, i, j);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta64(k, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int g = i + s * d + (d < 0 ? d : 0);
+  int lo = i < j ? i : j, hi = i < j ? j : i;
+  int c0 = (lo == g) ? ~(leaf_base + g) : node_base + g;
+  int c1 = (hi == g + 1) ? ~(leaf_base + g + 1) : node_base + g + 1;
+  float4* nd = nodes + 4 * (size_t)(node_base + i);
+  int4 n3 = make_int4(c0, c1, -1, 0);
+  // parent of node i is written by its parent; keep the slot's current parent
+  int* n3i = reinterpret_cast<int*>(&nd[3]);
+  n3i[0] = n3.x;
+  n3i[1] = n3.y;
+  if (c0 >= 0) reinterpret_cast<int*>(nodes + 4 * (size_t)c0 + 3)[2] = node_base + i;
+  else leaf_parent[~c0] = node_base + i;
+  if (c1 >= 0) reinterpret_cast<int*>(nodes + 4 * (size_t)c1 + 3)[2] = node_base + i;
+  else leaf_parent[~c1] = node_base + i;
+}
+
+// Store box b (lo.xyz, hi.xyz) into the child slot `side` of node p.
+__device__ __forceinline__ void put_child_box(float4* nodes, int p, int side, const float* b) {
+  float* n = reinterpret_cast<float*>(nodes + 4 * (size_t)p);
+  // n0 = c0 x/y, n1 = c1 x/y, n2 = (c0.z lo/hi, c1.z lo/hi)
+  float* xy = n + (side ? 4 : 0);
+  xy[0] = b[0]; xy[1] = b[3]; xy[2] = b[1]; xy[3] = b[4];
+  n[8 + 2 * side] = b[2];
+  n[8 + 2 * side + 1] = b[5];
+}
+
+__device__ __forceinline__ void get_union_cg(const float4* nodes, int p, float* u) {
+  const float4* n = nodes + 4 * (size_t)p;
+  float4 n0 = __ldcg(n), n1 = __ldcg(n + 1), n2 = __ldcg(n + 2);
+  u[0] = fminf(n0.x, n1.x); u[3] = fmaxf(n0.y, n1.y);
+  u[1] = fminf(n0.z, n1.z); u[4] = fmaxf(n0.w, n1.w);
+  u[2] = fminf(n2.x, n2.z); u[5] = fmaxf(n2.y, n2.w);
+}
+
+__device__ __forceinline__ int node_parent_cg(const float4* nodes, int p) {
+  return __float_as_int(__ldcg(reinterpret_cast<const float*>(nodes + 4 * (size_t)p + 3) + 2));
+}
+
+__device__ __forceinline__ int node_side(const float4* nodes, int p, int code) {
+  int c0 = __float_as_int(__ldcg(reinterpret_cast<const float*>(nodes + 4 * (size_t)p + 3)));
+  return c0 == code ? 0 : 1;
+}
+
+// Bottom-up propagation from a finished child (code, box) at parent p, with
+// atomic arrival counters: the second arrival at a node unions its two child
+// boxes and continues. Returns when it is the first arrival or after the root.
+__device__ __forceinline__ void refit_up(float4* nodes, int* arrive, int node_base, int p, int code,
+                                         const float* box, float* root_box) {
+  float b[6] = {box[0], box[1], box[2], box[3], box[4], box[5]};
+  if (p < 0) {
+    for (int k = 0; k < 6; ++k) root_box[k] = b[k];
+    return;
+  }
+  for (int depth = 0; depth < 128; ++depth) {  // LBVH depth <= 64
+    put_child_box(nodes, p, node_side(nodes, p, code), b);
+    __threadfence();
+    int old = atomicAdd(&arrive[p - node_base], 1);
+    if (old == 0) return;
+    __threadfence();
+    get_union_cg(nodes, p, b);
+    int pp = node_parent_cg(nodes, p);
+    if (pp < 0) {
+      for (int k = 0; k < 6; ++k) root_box[k] = b[k];
+      return;
+    }
+    code = p;
+    p = pp;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one-CTA builder: n <= kSmallBuild primitives given as boxes (lo.xyz, hi.xyz)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_build_small(const float* __restrict__ prim, int n,
+                                                      int node_base, int leaf_base, float4* nodes,
+                                                      int* leaf_parent, int* perm, int* arrive,
+                                                      int* root_out, float* root_box) {
+  extern __shared__ unsigned long long keys[];
+  __shared__ float red[6][32];
+  __shared__ float bnd[6];
+  int tid = threadIdx.x, nt = blockDim.x;
+  if (n <= 0) {
+    if (tid == 0) root_out[0] = kEmpty;
+    return;
+  }
+  // centroid bounds
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  for (int i = tid; i < n; i += nt) {
+    const float* b = prim + 6 * (size_t)i;
+    for (int k = 0; k < 3; ++k) {
+      float c = 0.5f * (b[k] + b[k + 3]);
+      lo[k] = fminf(lo[k], c);
+      hi[k] = fmaxf(hi[k], c);
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if ((tid & 31) == 0)
+    for (int k = 0; k < 3; ++k) { red[k][tid >> 5] = lo[k]; red[k + 3][tid >> 5] = hi[k]; }
+  __syncthreads();
+  if (tid < 3) {
+    float a = 3.4e38f, b = -3.4e38f;
+    for (int w = 0; w < (nt + 31) / 32; ++w) { a = fminf(a, red[tid][w]); b = fmaxf(b, red[tid + 3][w]); }
+    bnd[tid] = a;
+    bnd[tid + 3] = (b > a) ? 1.0f / (b - a) : 0.0f;
+  }
+  __syncthreads();
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int i = tid; i < np2; i += nt) {
+    if (i < n) {
+      const float* b = prim + 6 * (size_t)i;
+      unsigned code = morton30(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]), bnd,
+                               bnd + 3);
+      keys[i] = ((unsigned long long)code << 32) | (unsigned)i;
+    } else {
+      keys[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  // bitonic sort (keys unique: code, index)
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < np2; i += nt) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = keys[i], b = keys[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < n; i += nt) perm[i] = (int)(keys[i] & 0xffffffffu);
+  if (n == 1) {
+    if (tid == 0) {
+      root_out[0] = ~leaf_base;
+      leaf_parent[leaf_base] = -1;
+      for (int k = 0; k < 6; ++k) root_box[k] = prim[k];
+    }
+    return;
+  }
+  for (int i = tid; i < n - 1; i += nt) {
+    reinterpret_cast<int*>(nodes + 4 * (size_t)(node_base + i) + 3)[2] = -1;
+    arrive[i] = 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < n - 1; i += nt) karras_node(keys, n, i, node_base, leaf_base, nodes, leaf_parent);
+  __syncthreads();
+  if (tid == 0) root_out[0] = node_base;
+  // in-CTA refit
+  for (int j = tid; j < n; j += nt) {
+    const float* b = prim + 6 * (size_t)perm[j];
+    refit_up(nodes, arrive, node_base, leaf_parent[leaf_base + j], ~(leaf_base + j), b, root_box);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// multi-CTA builder for large trees: Morton codes, 4-pass stable LSD radix
+// sort of the 30-bit codes carrying the primitive index, Karras nodes.
+// ---------------------------------------------------------------------------
+__global__ void k_centroid_bounds(const float* __restrict__ prim, int n, unsigned* ob) {
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* b = prim + 6 * (size_t)i;
+    for (int k = 0; k < 3; ++k) {
+      float c = 0.5f * (b[k] + b[k + 3]);
+      lo[k] = fminf(lo[k], c);
+      hi[k] = fmaxf(hi[k], c);
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&ob[k], f2o(lo[k]));
+      atomicMax(&ob[k + 3], f2o(hi[k]));
+    }
+  }
+}
+
+__global__ void k_morton(const float* __restrict__ prim, int n, const unsigned* ob, unsigned* codes,
+                         unsigned* idx) {
+  float lo[3], inv[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = o2f(ob[k]);
+    float h = o2f(ob[k + 3]);
+    inv[k] = h > lo[k] ? 1.0f / (h - lo[k]) : 0.0f;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* b = prim + 6 * (size_t)i;
+    codes[i] = morton30(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]), lo, inv);
+    idx[i] = (unsigned)i;
+  }
+}
+
+constexpr int kRadixItems = 1024;  // per block: 4 rounds of 256
+
+__global__ void __launch_bounds__(256) k_radix_hist(const unsigned* __restrict__ keys, int n, int shift,
+                                                    unsigned* hist, int nblocks) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * kRadixItems;
+  for (int r = 0; r < 4; ++r) {
+    int i = base + r * 256 + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m counts in one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan_excl(unsigned* a, int m) {
+  __shared__ unsigned part[1024];
+  int per = (m + 1023) / 1024;
+  int s = threadIdx.x * per, e = min(s + per, m);
+  unsigned acc = 0;
+  for (int i = s; i < e; ++i) acc += a[i];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int i = s; i < e; ++i) {
+    unsigned v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_radix_scatter(const unsigned* __restrict__ kin,
+                                                       const unsigned* __restrict__ vin, int n, int shift,
+                                                       const unsigned* __restrict__ hist, int nblocks,
+                                                       unsigned* kout, unsigned* vout) {
+  __shared__ unsigned run[256];
+  __shared__ unsigned wcnt[8][256];
+  int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  run[tid] = hist[tid * nblocks + blockIdx.x];
+  int base = blockIdx.x * kRadixItems;
+  for (int r = 0; r < 4; ++r) {
+    for (int q = 0; q < 8; ++q) wcnt[q][tid] = 0;
+    __syncthreads();
+    int i = base + r * 256 + tid;
+    bool valid = i < n;
+    unsigned key = valid ? kin[i] : 0u, val = valid ? vin[i] : 0u;
+    unsigned dig = valid ? ((key >> shift) & 255u) : 256u + (unsigned)lane;  // invalid lanes unique
+    unsigned peers = __match_any_sync(0xffffffffu, dig);
+    unsigned rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[w][dig] = __popc(peers);
+    __syncthreads();
+    // per digit: exclusive prefix over warps (thread tid owns digit tid)
+    unsigned acc = 0;
+    for (int q = 0; q < 8; ++q) {
+      unsigned c = wcnt[q][tid];
+      wcnt[q][tid] = acc;
+      acc += c;
+    }
+    __syncthreads();
+    if (valid) {
+      unsigned pos = run[dig] + wcnt[w][dig] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    run[tid] += acc;
+    __syncthreads();
+  }
+}
+
+__global__ void k_make_keys(const unsigned* codes, const unsigned* idx, int n, unsigned long long* keys,
+                            int* perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    keys[i] = ((unsigned long long)codes[i] << 32) | idx[i];
+    perm[i] = (int)idx[i];
+  }
+}
+
+__global__ void k_karras(const unsigned long long* __restrict__ keys, int n, int node_base, int leaf_base,
+                         float4* nodes, int* leaf_parent) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x)
+    karras_node(keys, n, i, node_base, leaf_base, nodes, leaf_parent);
+}
+
+__global__ void k_init_parents(float4* nodes, int node_base, int nint, int* arrive) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nint; i += gridDim.x * blockDim.x) {
+    reinterpret_cast<int*>(nodes + 4 * (size_t)(node_base + i) + 3)[2] = -1;
+    arrive[i] = 0;
+  }
+}
+
+// refit from primitive boxes in leaf order (prim[perm[j]])
+__global__ void k_refit_prims(const float* __restrict__ prim, const int* __restrict__ perm, int n,
+                              int node_base, int leaf_base, float4* nodes, const int* leaf_parent,
+                              int* arrive, float* root_box) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const float* b = prim + 6 * (size_t)perm[j];
+    refit_up(nodes, arrive, node_base, leaf_parent[leaf_base + j], ~(leaf_base + j), b, root_box);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// triangles
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tri_box(float3 a, float3 b, float3 c, float* o) {
+  o[0] = fminf(a.x, fminf(b.x, c.x)); o[1] = fminf(a.y, fminf(b.y, c.y)); o[2] = fminf(a.z, fminf(b.z, c.z));
+  o[3] = fmaxf(a.x, fmaxf(b.x, c.x)); o[4] = fmaxf(a.y, fmaxf(b.y, c.y)); o[5] = fmaxf(a.z, fmaxf(b.z, c.z));
+}
+
+// boxes of triangles given as 9 floats each, indices sel[i] (or i when sel is null)
+__global__ void k_tri_boxes(const float* __restrict__ v9, const int* __restrict__ sel, int n, float* prim) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float* v = v9 + 9 * (size_t)(sel ? sel[i] : i);
+    tri_box(f3(v[0], v[1], v[2]), f3(v[3], v[4], v[5]), f3(v[6], v[7], v[8]), prim + 6 * (size_t)i);
+  }
+}
+
+// Scatter triangles into leaf order: leaf j of a tree holds input triangle
+// gid = sel[perm[j]]; v9 are its (world or object space) vertices.
+__global__ void k_place_tris(const float* __restrict__ v9, const int* __restrict__ sel,
+                             const int* __restrict__ perm, const int* __restrict__ tri_mat,
+                             const int* __restrict__ tri_obj, int n, int leaf_base, float4* tris,
+                             float4* objv, int* slot_of_id) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int gid = sel[perm[j]];
+    const float* v = v9 + 9 * (size_t)gid;
+    int slot = leaf_base + j;
+    float4* t = tris + 3 * (size_t)slot;
+    t[0] = make_float4(v[0], v[1], v[2], __int_as_float(gid));
+    t[1] = make_float4(v[3], v[4], v[5], __int_as_float(tri_mat[gid]));
+    t[2] = make_float4(v[6], v[7], v[8], 0.0f);
+    if (objv) {
+      float4* q = objv + 3 * (size_t)j;
+      int ob = tri_obj[gid];
+      q[0] = make_float4(v[0], v[1], v[2], __int_as_float(ob));
+      q[1] = make_float4(v[3], v[4], v[5], 0.0f);
+      q[2] = make_float4(v[6], v[7], v[8], 0.0f);
+    }
+    slot_of_id[gid] = slot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-frame: transform dynamic triangles + refit + per-object boxes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 xform(const float* m, float3 p) {
+  return f3(__fmaf_rn(m[0], p.x, __fmaf_rn(m[1], p.y, __fmaf_rn(m[2], p.z, m[3]))),
+            __fmaf_rn(m[4], p.x, __fmaf_rn(m[5], p.y, __fmaf_rn(m[6], p.z, m[7]))),
+            __fmaf_rn(m[8], p.x, __fmaf_rn(m[9], p.y, __fmaf_rn(m[10], p.z, m[11]))));
+}
+
+__global__ void k_transform_refit(const float4* __restrict__ objv, const float* __restrict__ xf, int n, int nobj,
+                                  int node_base, int leaf_base, float4* tris, float4* nodes,
+                                  const int* __restrict__ leaf_parent, int* arrive, float* root_box,
+                                  unsigned* obj_box, DevCounters* ctr) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    float4 a = objv[3 * (size_t)j], b = objv[3 * (size_t)j + 1], c = objv[3 * (size_t)j + 2];
+    int ob = __float_as_int(a.w);
+    const float* m = xf + 12 * (size_t)ob;
+    float3 w0 = xform(m, f3(a.x, a.y, a.z)), w1 = xform(m, f3(b.x, b.y, b.z)), w2 = xform(m, f3(c.x, c.y, c.z));
+    int slot = leaf_base + j;
+    float4* t = tris + 3 * (size_t)slot;
+    float4 t0 = t[0], t1 = t[1];
+    t[0] = make_float4(w0.x, w0.y, w0.z, t0.w);
+    t[1] = make_float4(w1.x, w1.y, w1.z, t1.w);
+    t[2] = make_float4(w2.x, w2.y, w2.z, 0.0f);
+    float box[6];
+    tri_box(w0, w1, w2, box);
+    bool fin = true;
+    for (int k = 0; k < 6; ++k) fin = fin && isfinite(box[k]);
+    if (!fin) atomicOr(&ctr->err, ERR_NONFINITE);
+    // per-object world box: lo in obj_box[0, 3 nobj), hi in obj_box[3 nobj, 6 nobj)
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&obj_box[3 * (size_t)ob + k], f2o(box[k]));
+      atomicMax(&obj_box[3 * (size_t)(nobj + ob) + k], f2o(box[k + 3]));
+    }
+    refit_up(nodes, arrive, node_base, leaf_parent[slot], ~slot, box, root_box);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline int nblk(long n, int bs, int cap = 4096) {
+  long b = (n + bs - 1) / bs;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+cudaError_t build_tree(const float* d_prim, int n, int node_base, int leaf_base, float4* d_nodes,
+                       int* d_leaf_parent, int* d_perm, int* d_arrive, int* d_root, float* d_root_box,
+                       BuildScratch& scr, cudaStream_t st) {
+  if (n <= 0) {
+    int e = kEmpty;
+    return cudaMemcpyAsync(d_root, &e, sizeof(int), cudaMemcpyHostToDevice, st);
+  }
+  if (n <= kSmallBuild) {
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    size_t smem = (size_t)np2 * sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(k_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kSmallBuild * sizeof(unsigned long long)));
+    if (e != cudaSuccess) return e;
+    k_build_small<<<1, 1024, smem, st>>>(d_prim, n, node_base, leaf_base, d_nodes, d_leaf_parent, d_perm,
+                                         d_arrive, d_root, d_root_box);
+    return cudaGetLastError();
+  }
+  // large path
+  cudaError_t e;
+  unsigned init[6];
+  for (int k = 0; k < 3; ++k) { init[k] = 0xffffffffu; init[k + 3] = 0u; }
+  if ((e = cudaMemcpyAsync(scr.bounds, init, sizeof(init), cudaMemcpyHostToDevice, st))) return e;
+  k_centroid_bounds<<<nblk(n, 256, 1024), 256, 0, st>>>(d_prim, n, scr.bounds);
+  k_morton<<<nblk(n, 256), 256, 0, st>>>(d_prim, n, scr.bounds, scr.k0, scr.v0);
+  int nb = (n + kRadixItems - 1) / kRadixItems;
+  unsigned *ki = scr.k0, *vi = scr.v0, *ko = scr.k1, *vo = scr.v1;
+  for (int pass = 0; pass < 4; ++pass) {
+    int shift = 8 * pass;
+    k_radix_hist<<<nb, 256, 0, st>>>(ki, n, shift, scr.hist, nb);
+    k_scan_excl<<<1, 1024, 0, st>>>(scr.hist, 256 * nb);
+    k_radix_scatter<<<nb, 256, 0, st>>>(ki, vi, n, shift, scr.hist, nb, ko, vo);
+    unsigned* t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  k_make_keys<<<nblk(n, 256), 256, 0, st>>>(ki, vi, n, scr.keys, d_perm);
+  k_init_parents<<<nblk(n, 256), 256, 0, st>>>(d_nodes, node_base, n - 1, d_arrive);
+  k_karras<<<nblk(n, 256), 256, 0, st>>>(scr.keys, n, node_base, leaf_base, d_nodes, d_leaf_parent);
+  int root = node_base;
+  if ((e = cudaMemcpyAsync(d_root, &root, sizeof(int), cudaMemcpyHostToDevice, st))) return e;
+  k_refit_prims<<<nblk(n, 256), 256, 0, st>>>(d_prim, d_perm, n, node_base, leaf_base, d_nodes,
+                                              d_leaf_parent, d_arrive, d_root_box);
+  return cudaGetLastError();
+}
+
+void launch_tri_boxes(const float* d_v9, const int* d_sel, int n, float* d_prim, cudaStream_t st) {
+  if (n > 0) k_tri_boxes<<<nblk(n, 256), 256, 0, st>>>(d_v9, d_sel, n, d_prim);
+}
+
+void launch_place_tris(const float* d_v9, const int* d_sel, const int* d_perm, const int* d_tri_mat,
+                       const int* d_tri_obj, int n, int leaf_base, float4* d_tris, float4* d_objv,
+                       int* d_slot_of_id, cudaStream_t st) {
+  if (n > 0)
+    k_place_tris<<<nblk(n, 256), 256, 0, st>>>(d_v9, d_sel, d_perm, d_tri_mat, d_tri_obj, n, leaf_base,
+                                               d_tris, d_objv, d_slot_of_id);
+}
+
+void launch_transform_refit(const float4* d_objv, const float* d_xf, int n, int nobj, int node_base, int leaf_base,
+                            float4* d_tris, float4* d_nodes, const int* d_leaf_parent, int* d_arrive,
+                            float* d_root_box, unsigned* d_obj_box, DevCounters* d_ctr, cudaStream_t st) {
+  if (n > 0)
+    k_transform_refit<<<nblk(n, 256), 256, 0, st>>>(d_objv, d_xf, n, nobj, node_base, leaf_base, d_tris, d_nodes,
+                                                    d_leaf_parent, d_arrive, d_root_box, d_obj_box, d_ctr);
+}
+
+}  // namespace dcem

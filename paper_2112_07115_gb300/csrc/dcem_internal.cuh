@@ -1,0 +1,336 @@
+// dcem_internal.cuh -- device data layout and inline device functions of the
+// GB300 tracer. Compiled with -fmad=false: every fused multiply-add below is
+// written explicitly, so a device function evaluates to the same bits in
+// every kernel that inlines it (this is what makes a coherent-reuse frame
+// equal to a full retrace bit for bit).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dcem.h"
+
+namespace dcem {
+
+constexpr int kMaxRefl = DCEM_MAX_REFL;
+constexpr int kStack = 72;              // traversal stack entries (LBVH depth <= 64 per tree)
+constexpr int kEmpty = (int)0x80000000; // empty tree / no node
+constexpr int kSmallBuild = 16384;      // largest tree built by the one-CTA builder
+constexpr int kRxSmem = 4096;           // receivers staged in shared memory per CTA
+constexpr int kMovedSmem = 4096;        // moved-object boxes staged in shared memory
+
+// device error bits (DevCounters::err)
+enum : unsigned {
+  ERR_CAND_OVERFLOW = 1u,
+  ERR_UNIQUE_OVERFLOW = 2u,
+  ERR_BUCKET_OVERFLOW = 4u,
+  ERR_HASH_COLLISION = 8u,
+  ERR_NONFINITE = 16u,
+  ERR_STACK = 32u,
+  ERR_HASH_FULL = 64u,
+  ERR_QUEUE_OVERFLOW = 128u,
+};
+
+struct DevCounters {
+  unsigned long long segments_traced;
+  unsigned long long segments_reused;
+  unsigned int n_cand;
+  unsigned int n_cand_reused;
+  unsigned int n_unique;
+  unsigned int n_valid;
+  unsigned int n_retrace;
+  unsigned int stack_overflow;
+  unsigned int err;
+  unsigned int objects_moved;
+  unsigned int rx_moved;
+  unsigned int n_moved_boxes;
+  unsigned int pad[4];
+};
+
+// Candidate = one reception-sphere capture: ray index and (rx << 4 | segment).
+struct Cand {
+  int ray;
+  int rxseg;
+};
+__host__ __device__ inline int cand_rx(Cand c) { return (int)((unsigned)c.rxseg >> 4); }
+__host__ __device__ inline int cand_seg(Cand c) { return c.rxseg & 15; }
+
+// Internal record of one distinct candidate after validation.
+struct PathRec {
+  unsigned long long key;
+  int rx;
+  int depth;
+  int ray;
+  unsigned int flags;
+  int valid;
+  int pad;
+  double len;
+  double amp_re, amp_im;
+  int tri[kMaxRefl];
+  float pts[kMaxRefl][3];
+};
+
+// ---------------------------------------------------------------------------
+// FP32 vector helpers with a fixed evaluation order
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
+  return f3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+            __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// ---------------------------------------------------------------------------
+// Triangles: three float4 per leaf slot: (v0, id bits), (v1, material), (v2, 0)
+// Nodes: four float4 per internal node:
+//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   n3 = (child0, child1, parent, -) as int bits; child < 0 is leaf slot ~c
+// ---------------------------------------------------------------------------
+
+struct RayPre {
+  float3 o;
+  float3 inv;   // 1/d with zero components replaced by +-1e-30 (box tests only)
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
+  RayPre r;
+  r.o = o;
+  float dx = fabsf(d.x) < 1e-30f ? copysignf(1e-30f, d.x) : d.x;
+  float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
+  float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
+  r.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
+  // watertight shear constants (Woop, Benthin, Wald 2013)
+  float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+  int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  if (comp(d, kz) < 0.0f) { int t = kx; kx = ky; ky = t; }
+  r.kx = kx; r.ky = ky; r.kz = kz;
+  float dkz = comp(d, kz);
+  r.Sx = __fdiv_rn(comp(d, kx), dkz);
+  r.Sy = __fdiv_rn(comp(d, ky), dkz);
+  r.Sz = __fdiv_rn(1.0f, dkz);
+  return r;
+}
+
+// Conservative slab test: entry/exit over [0, tcap]; the (1 + 1e-5) widening
+// keeps every triangle whose FP32 watertight test could report a hit.
+__device__ __forceinline__ bool slab(const RayPre& r, float lox, float hix, float loy, float hiy,
+                                     float loz, float hiz, float tcap, float& tn_out) {
+  float t0x = __fmul_rn(__fsub_rn(lox, r.o.x), r.inv.x), t1x = __fmul_rn(__fsub_rn(hix, r.o.x), r.inv.x);
+  float t0y = __fmul_rn(__fsub_rn(loy, r.o.y), r.inv.y), t1y = __fmul_rn(__fsub_rn(hiy, r.o.y), r.inv.y);
+  float t0z = __fmul_rn(__fsub_rn(loz, r.o.z), r.inv.z), t1z = __fmul_rn(__fsub_rn(hiz, r.o.z), r.inv.z);
+  float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+  float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tcap));
+  tn_out = tn;
+  return tn <= __fmul_rn(tf, 1.00001f) + 1e-30f;
+}
+
+// Watertight ray/triangle test in FP32. Returns true and the ray parameter t
+// when the ray passes through the triangle (no back-face culling).
+__device__ __forceinline__ bool tri_hit(const RayPre& r, float3 v0, float3 v1, float3 v2, float& t) {
+  float3 A = sub3(v0, r.o), B = sub3(v1, r.o), C = sub3(v2, r.o);
+  float Akx = comp(A, r.kx), Aky = comp(A, r.ky), Akz = comp(A, r.kz);
+  float Bkx = comp(B, r.kx), Bky = comp(B, r.ky), Bkz = comp(B, r.kz);
+  float Ckx = comp(C, r.kx), Cky = comp(C, r.ky), Ckz = comp(C, r.kz);
+  float Ax = __fmaf_rn(-r.Sx, Akz, Akx), Ay = __fmaf_rn(-r.Sy, Akz, Aky);
+  float Bx = __fmaf_rn(-r.Sx, Bkz, Bkx), By = __fmaf_rn(-r.Sy, Bkz, Bky);
+  float Cx = __fmaf_rn(-r.Sx, Ckz, Ckx), Cy = __fmaf_rn(-r.Sy, Ckz, Cky);
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.0f || V == 0.0f || W == 0.0f) {  // exact edge: decide in double
+    double U2 = (double)Cx * (double)By - (double)Cy * (double)Bx;
+    double V2 = (double)Ax * (double)Cy - (double)Ay * (double)Cx;
+    double W2 = (double)Bx * (double)Ay - (double)By * (double)Ax;
+    U = (float)U2; V = (float)V2; W = (float)W2;
+    if (U == 0.0f && U2 != 0.0) U = U2 > 0 ? 2e-38f : -2e-38f;
+    if (V == 0.0f && V2 != 0.0) V = V2 > 0 ? 2e-38f : -2e-38f;
+    if (W == 0.0f && W2 != 0.0) W = W2 > 0 ? 2e-38f : -2e-38f;
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+  float det = __fadd_rn(__fadd_rn(U, V), W);
+  if (det == 0.0f) return false;
+  float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+  float T = __fmaf_rn(W, Cz, __fmaf_rn(V, Bz, __fmul_rn(U, Az)));
+  t = __fdiv_rn(T, det);
+  return true;
+}
+
+__device__ __forceinline__ void load_tri(const float4* __restrict__ tris, int slot, float3& v0,
+                                         float3& v1, float3& v2, int& id) {
+  float4 a = __ldg(&tris[3 * slot]), b = __ldg(&tris[3 * slot + 1]), c = __ldg(&tris[3 * slot + 2]);
+  v0 = f3(a.x, a.y, a.z);
+  v1 = f3(b.x, b.y, b.z);
+  v2 = f3(c.x, c.y, c.z);
+  id = __float_as_int(a.w);
+}
+
+struct Bvh {
+  const float4* __restrict__ nodes;
+  const float4* __restrict__ tris;
+  int root0, root1;
+  int max_visits;  // nodes + leaves of both trees: a valid traversal never exceeds it
+};
+
+// Closest hit over both trees, t > tmin, excluding triangle id `excl`; ties in
+// t go to the lowest triangle id, so the result does not depend on the tree
+// shape or the traversal order. Returns the leaf slot or -1.
+__device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, float tmin, int excl,
+                                           float& t_best, int& id_best, unsigned& overflow) {
+  int stack[kStack];
+  int sp = 0;
+  t_best = __int_as_float(0x7f800000);
+  id_best = 0x7fffffff;
+  int slot_best = -1;
+  if (bvh.root1 != kEmpty) stack[sp++] = bvh.root1;
+  int cur = bvh.root0;
+  for (int visits = 0;; ++visits) {
+    if (visits > bvh.max_visits) {  // malformed tree: stop and report
+      overflow = 1u;
+      break;
+    }
+    if (cur == kEmpty) {
+      if (sp == 0) break;
+      cur = stack[--sp];
+      continue;
+    }
+    if (cur >= 0) {
+      const float4* n = bvh.nodes + 4 * (size_t)cur;
+      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+      float tn0, tn1;
+      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, t_best, tn0);
+      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, t_best, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        int nearc = tn0 <= tn1 ? c0 : c1, farc = tn0 <= tn1 ? c1 : c0;
+        if (sp < kStack) stack[sp++] = farc;
+        else overflow = 1u;
+        cur = nearc;
+      } else if (h0) {
+        cur = c0;
+      } else if (h1) {
+        cur = c1;
+      } else {
+        cur = kEmpty;
+      }
+    } else {
+      int slot = ~cur;
+      float3 v0, v1, v2;
+      int id;
+      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      float t;
+      if (id != excl && tri_hit(r, v0, v1, v2, t) && t > tmin) {
+        if (t < t_best || (t == t_best && id < id_best)) {
+          t_best = t;
+          id_best = id;
+          slot_best = slot;
+        }
+      }
+      cur = kEmpty;
+    }
+  }
+  return slot_best;
+}
+
+// Any hit with t in (t0, t1), excluding ids ex0 and ex1 (occlusion test).
+__device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t0, float t1,
+                                        int ex0, int ex1, unsigned& overflow) {
+  int stack[kStack];
+  int sp = 0;
+  if (bvh.root1 != kEmpty) stack[sp++] = bvh.root1;
+  int cur = bvh.root0;
+  for (int visits = 0;; ++visits) {
+    if (visits > bvh.max_visits) {
+      overflow = 1u;
+      break;
+    }
+    if (cur == kEmpty) {
+      if (sp == 0) break;
+      cur = stack[--sp];
+      continue;
+    }
+    if (cur >= 0) {
+      const float4* n = bvh.nodes + 4 * (size_t)cur;
+      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+      float tn0, tn1;
+      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, t1, tn0);
+      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, t1, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        if (sp < kStack) stack[sp++] = c1;
+        else overflow = 1u;
+        cur = c0;
+      } else if (h0) {
+        cur = c0;
+      } else if (h1) {
+        cur = c1;
+      } else {
+        cur = kEmpty;
+      }
+    } else {
+      float3 v0, v1, v2;
+      int id;
+      load_tri(bvh.tris, ~cur, v0, v1, v2, id);
+      float t;
+      if (id != ex0 && id != ex1 && tri_hit(r, v0, v1, v2, t) && t > t0 && t < t1) return true;
+      cur = kEmpty;
+    }
+  }
+  return false;
+}
+
+// Reception-sphere capture of one segment (o, d unit, unfolded start length D,
+// length tend) by receiver R: closest approach s in [0, tend], captured iff
+// |R - (o + s d)| <= alpha_eff (D + s).
+__device__ __forceinline__ bool captured(float3 o, float3 d, float D, float tend, float alpha_eff,
+                                         float3 R) {
+  float3 w = sub3(R, o);
+  float s = dot3(w, d);
+  s = fminf(fmaxf(s, 0.0f), tend);
+  float3 q = f3(__fmaf_rn(-s, d.x, w.x), __fmaf_rn(-s, d.y, w.y), __fmaf_rn(-s, d.z, w.z));
+  float dist2 = dot3(q, q);
+  float rho = __fmul_rn(alpha_eff, __fadd_rn(D, s));
+  return dist2 <= __fmul_rn(rho, rho);
+}
+
+// Does the segment o + t d, t in [0, tend], meet the box (conservatively)?
+__device__ __forceinline__ bool seg_box(const RayPre& r, float tend, const float* b) {
+  float tn;
+  return slab(r, b[0], b[3], b[1], b[4], b[2], b[5], tend, tn);
+}
+
+// 64-bit path key: (rx, depth, triangle ids) mixed with the SplitMix64 finaliser.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Total order on float bits usable with atomicMin/atomicMax on unsigned.
+__device__ __forceinline__ unsigned f2o(float f) {
+  unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float o2f(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+#else
+  unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  float f;
+  memcpy(&f, &v, 4);
+  return f;
+#endif
+}
+
+}  // namespace dcem

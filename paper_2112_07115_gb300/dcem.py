@@ -1,0 +1,349 @@
+"""ctypes binding of libdcem (include/dcem.h): argument marshalling only.
+
+Every step of a frame runs in the library's CUDA kernels; this module only
+converts numpy arrays / torch tensors to pointers and sizes. Module-level
+functions carry the C names; ``Scene`` is a small convenience wrapper.
+If the library has not been built the import of a function fails loudly:
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdcem.so")
+
+MAX_REFL = 10
+OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_NONFINITE, ERR_STACK, ERR_HASH, ERR_STATE, ERR_NOMEM = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+MODE_FULL, MODE_COHERENT = 0, 1
+PTR_HOST, PTR_DEVICE = 0, 1
+PATH_POL_DEGENERATE = 1
+
+EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
+            "dcem_scene_update_transforms", "dcem_trace_frame", "dcem_scene_reset_cache",
+            "dcem_scene_set_stream", "dcem_scene_destroy", "dcem_status_string", "dcem_scene_info",
+            "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
+            "dcem_scene_get_candidates"]
+
+
+class Material(C.Structure):
+    _fields_ = [("eps_r", C.c_float), ("sigma", C.c_float), ("pec", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("freq_hz", C.c_double), ("tx_power_w", C.c_double), ("max_refl", C.c_int32),
+                ("mode", C.c_int32), ("rx_radius_scale", C.c_float), ("t_min", C.c_float),
+                ("escape_len", C.c_float), ("eps_occ", C.c_float), ("pol", C.c_float * 3),
+                ("timing", C.c_int32)]
+
+
+class Path(C.Structure):
+    _fields_ = [("rx", C.c_int32), ("depth", C.c_int32), ("tri", C.c_int32 * MAX_REFL),
+                ("flags", C.c_uint32), ("ray", C.c_int32), ("key", C.c_uint64),
+                ("len_m", C.c_double), ("delay_s", C.c_double), ("amp_re", C.c_double),
+                ("amp_im", C.c_double), ("pts", C.c_float * (3 * MAX_REFL))]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("segments_traced", C.c_int64),
+                ("segments_reused", C.c_int64), ("rays_retraced", C.c_int64),
+                ("candidates", C.c_int64), ("candidates_reused", C.c_int64),
+                ("unique_candidates", C.c_int64), ("paths_valid", C.c_int64),
+                ("objects_moved", C.c_int64), ("rx_moved", C.c_int64),
+                ("stack_overflow", C.c_int32), ("coherent", C.c_int32),
+                ("ms_stage", C.c_float * 8)]
+
+
+class Result(C.Structure):
+    _fields_ = [("ptr_kind", C.c_int32), ("max_paths", C.c_int32), ("field", C.c_void_p),
+                ("p_coh_dbm", C.c_void_p), ("p_inc_dbm", C.c_void_p), ("paths", C.c_void_p),
+                ("n_paths", C.c_int32), ("stats", Stats)]
+
+
+PATH_DTYPE = np.dtype([("rx", np.int32), ("depth", np.int32), ("tri", np.int32, (MAX_REFL,)),
+                       ("flags", np.uint32), ("ray", np.int32), ("key", np.uint64),
+                       ("len_m", np.float64), ("delay_s", np.float64), ("amp_re", np.float64),
+                       ("amp_im", np.float64), ("pts", np.float32, (MAX_REFL, 3))])
+assert PATH_DTYPE.itemsize == C.sizeof(Path)
+
+STAGES = ["prep", "mark", "trace", "dedupe", "validate", "reduce", "copy_out", "total"]
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdcem.so is not built ({LIB_PATH}); run "
+                               "paper_2112_07115_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        P = C.POINTER
+        L.dcem_params_default.argtypes = [P(Params)]
+        L.dcem_params_default.restype = None
+        L.dcem_scene_create.argtypes = [vp, i32, vp, vp, i32, vp, i32, vp, P(vp)]
+        L.dcem_scene_set_rays.argtypes = [vp, vp, i32]
+        L.dcem_scene_update_transforms.argtypes = [vp, vp, i32]
+        L.dcem_trace_frame.argtypes = [vp, vp, vp, i32, i32, P(Params), P(Result)]
+        L.dcem_scene_reset_cache.argtypes = [vp]
+        L.dcem_scene_set_stream.argtypes = [vp, vp]
+        L.dcem_scene_destroy.argtypes = [vp]
+        L.dcem_scene_destroy.restype = None
+        L.dcem_status_string.argtypes = [C.c_int]
+        L.dcem_status_string.restype = C.c_char_p
+        L.dcem_scene_info.argtypes = [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]
+        L.dcem_scene_get_world_tris.argtypes = [vp, vp]
+        L.dcem_scene_get_bvh.argtypes = [vp, vp, vp, vp]
+        L.dcem_scene_get_ray_log.argtypes = [vp, vp, vp, vp]
+        L.dcem_scene_get_candidates.argtypes = [vp, vp, i64, P(i64)]
+        for name in EXPORTED:
+            if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class DcemError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def status_string(status: int) -> str:
+    return lib().dcem_status_string(int(status)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise DcemError(rc, where)
+
+
+# --------------------------------------------------------------------------
+# pointer marshalling
+# --------------------------------------------------------------------------
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+def _ptr(x, dtype):
+    """(pointer, kind, keepalive) of a numpy array (host) or torch tensor."""
+    if x is None:
+        return None, PTR_HOST, None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), (PTR_DEVICE if x.is_cuda else PTR_HOST), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, PTR_HOST, a
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().dcem_params_default(C.byref(p))
+    for k, v in kw.items():
+        if k == "pol":
+            for i in range(3):
+                p.pol[i] = float(v[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------------------
+# C names
+# --------------------------------------------------------------------------
+def dcem_scene_create(tris, tri_mat, materials, tri_obj=None, nobj=0, stream=None) -> int:
+    """Returns an opaque handle (int). materials: (M,3) rows (eps_r, sigma, pec)."""
+    tris = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+    tri_mat = np.ascontiguousarray(tri_mat, np.int32)
+    mats = np.asarray(materials, np.float64).reshape(-1, 3)
+    marr = (Material * max(len(mats), 1))()
+    for i, (e, s, p) in enumerate(mats):
+        marr[i].eps_r, marr[i].sigma, marr[i].pec = float(e), float(s), int(p)
+    to = None if tri_obj is None else np.ascontiguousarray(tri_obj, np.int32)
+    h = C.c_void_p()
+    rc = lib().dcem_scene_create(tris.ctypes.data if tris.size else None, tris.shape[0],
+                                 tri_mat.ctypes.data if tri_mat.size else None, marr, len(mats),
+                                 to.ctypes.data if to is not None and to.size else None, int(nobj),
+                                 stream, C.byref(h))
+    _check(rc, "dcem_scene_create")
+    return h.value
+
+
+def dcem_scene_set_rays(h, dirs):
+    d = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+    _check(lib().dcem_scene_set_rays(h, d.ctypes.data if d.size else None, d.shape[0]),
+           "dcem_scene_set_rays")
+
+
+def dcem_scene_update_transforms(h, xf):
+    p, kind, keep = _ptr(xf, np.float32)
+    _check(lib().dcem_scene_update_transforms(h, p, kind), "dcem_scene_update_transforms")
+
+
+def dcem_trace_frame(h, tx, rx, params: Params, result: Result) -> int:
+    """Raw call; returns the status (the caller owns `result`'s arrays)."""
+    txa = np.ascontiguousarray(tx, np.float32).reshape(3)
+    rp, kind, keep = _ptr(rx, np.float32)
+    nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+    return lib().dcem_trace_frame(h, txa.ctypes.data, rp, nrx, kind, C.byref(params),
+                                  C.byref(result))
+
+
+def dcem_scene_reset_cache(h):
+    _check(lib().dcem_scene_reset_cache(h), "dcem_scene_reset_cache")
+
+
+def dcem_scene_set_stream(h, stream):
+    _check(lib().dcem_scene_set_stream(h, stream), "dcem_scene_set_stream")
+
+
+def dcem_scene_destroy(h):
+    lib().dcem_scene_destroy(h)
+
+
+def dcem_scene_info(h) -> dict:
+    v = [C.c_int32() for _ in range(5)]
+    _check(lib().dcem_scene_info(h, *[C.byref(x) for x in v]), "dcem_scene_info")
+    return dict(zip(["ntri", "nobj", "n_rays", "static_nodes", "dynamic_nodes"], [x.value for x in v]))
+
+
+def dcem_scene_get_world_tris(h, ntri) -> np.ndarray:
+    out = np.empty((ntri, 3, 3), np.float32)
+    _check(lib().dcem_scene_get_world_tris(h, out.ctypes.data if ntri else None),
+           "dcem_scene_get_world_tris")
+    return out
+
+
+def dcem_scene_get_bvh(h):
+    info = dcem_scene_info(h)
+    nn = info["static_nodes"] + info["dynamic_nodes"]
+    child = np.empty((max(nn, 1), 2), np.int32)
+    bounds = np.empty((max(nn, 1), 2, 6), np.float32)
+    roots = np.empty(2, np.int32)
+    _check(lib().dcem_scene_get_bvh(h, child.ctypes.data, bounds.ctypes.data, roots.ctypes.data),
+           "dcem_scene_get_bvh")
+    return child[:nn], bounds[:nn], roots, info
+
+
+def dcem_scene_get_ray_log(h, n_rays, max_refl):
+    W = max_refl + 1
+    ids = np.empty((n_rays, W), np.int32)
+    t = np.empty((n_rays, W), np.float32)
+    ns = np.empty(n_rays, np.int32)
+    if n_rays:
+        _check(lib().dcem_scene_get_ray_log(h, ids.ctypes.data, t.ctypes.data, ns.ctypes.data),
+               "dcem_scene_get_ray_log")
+    return ids, t, ns
+
+
+def dcem_scene_get_candidates(h) -> np.ndarray:
+    n = C.c_int64(0)
+    rc = lib().dcem_scene_get_candidates(h, None, 0, C.byref(n))
+    if rc not in (OK, ERR_CAPACITY):
+        _check(rc, "dcem_scene_get_candidates")
+    out = np.empty((max(n.value, 1), 3), np.int32)
+    if n.value:
+        _check(lib().dcem_scene_get_candidates(h, out.ctypes.data, n.value, C.byref(n)),
+               "dcem_scene_get_candidates")
+    return out[:n.value]
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper
+# --------------------------------------------------------------------------
+@dataclass
+class Frame:
+    status: int
+    field: np.ndarray        # complex128 (nrx,)
+    p_coh_dbm: np.ndarray
+    p_inc_dbm: np.ndarray
+    paths: np.ndarray        # PATH_DTYPE
+    stats: dict
+
+
+def stats_dict(s: Stats) -> dict:
+    d = {k: getattr(s, k) for k, _ in Stats._fields_ if k != "ms_stage"}
+    d["ms_stage"] = dict(zip(STAGES, list(s.ms_stage)))
+    return d
+
+
+class Scene:
+    """A scene on the current CUDA device (see include/dcem.h)."""
+
+    def __init__(self, tris, tri_mat, materials, tri_obj=None, nobj=0, stream=None):
+        self.ntri = int(np.asarray(tris).reshape(-1, 9).shape[0])
+        self.nobj = int(nobj)
+        self.h = dcem_scene_create(tris, tri_mat, materials, tri_obj, nobj, stream)
+        self.n_rays = 0
+        self.max_refl = 3
+
+    @classmethod
+    def from_scene(cls, sc, stream=None):
+        return cls(sc.tris, sc.tri_mat, sc.materials, sc.tri_obj, sc.nobj, stream)
+
+    def set_rays(self, dirs):
+        dcem_scene_set_rays(self.h, dirs)
+        self.n_rays = int(np.asarray(dirs).reshape(-1, 3).shape[0])
+
+    def update_transforms(self, xf):
+        dcem_scene_update_transforms(self.h, xf)
+
+    def trace(self, tx, rx, params: Params | None = None, max_paths: int | None = None,
+              raise_on_error: bool = True) -> Frame:
+        params = params or default_params()
+        self.max_refl = int(params.max_refl)
+        nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+        if max_paths is None:
+            max_paths = max(1024, 256 * nrx)
+        field = np.empty((max(nrx, 1), 2), np.float64)
+        pc = np.empty(max(nrx, 1), np.float64)
+        pi = np.empty(max(nrx, 1), np.float64)
+        paths = np.empty(max_paths, PATH_DTYPE)
+        res = Result()
+        res.ptr_kind = PTR_HOST
+        res.max_paths = max_paths
+        res.field, res.p_coh_dbm, res.p_inc_dbm = field.ctypes.data, pc.ctypes.data, pi.ctypes.data
+        res.paths = paths.ctypes.data
+        rc = dcem_trace_frame(self.h, tx, rx, params, res)
+        if rc != OK and raise_on_error:
+            raise DcemError(rc, "dcem_trace_frame")
+        n = min(res.n_paths, max_paths)
+        return Frame(rc, field[:nrx, 0] + 1j * field[:nrx, 1], pc[:nrx], pi[:nrx], paths[:n].copy(),
+                     stats_dict(res.stats))
+
+    def reset_cache(self):
+        dcem_scene_reset_cache(self.h)
+
+    def world_tris(self):
+        return dcem_scene_get_world_tris(self.h, self.ntri)
+
+    def bvh(self):
+        return dcem_scene_get_bvh(self.h)
+
+    def ray_log(self):
+        return dcem_scene_get_ray_log(self.h, self.n_rays, self.max_refl)
+
+    def candidates(self):
+        return dcem_scene_get_candidates(self.h)
+
+    def info(self):
+        return dcem_scene_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            dcem_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
