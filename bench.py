@@ -1,0 +1,479 @@
+#!/usr/bin/env python
+"""Benchmark of the dynamic coherence-based EM ray tracer on one GB300.
+
+Workload: highway V2I -- 2 km six-lane road with concrete barriers
+(about 4.0k triangles), 200 moving vehicles with one receiver on each roof,
+one roadside transmitter, 1M Fibonacci-sphere rays, 4 reflections, 28 GHz,
+frames at 10 Hz. One step = one frame of the whole hot path (transform and
+refit, coherence marking, shooting and bouncing, capture, dedupe,
+image-method validation, field, per-receiver reduction) in COHERENT mode.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0. `value` is coherent frames/s with inputs
+resident in HBM (device pointers through the C ABI); `e2e` is the same
+through the C ABI with host buffers (copies inside the timed region). The
+full-retrace rate, ray-segments/s, per-stage times, the roofline of the
+dominant kernel, the received-power error against the FP64 oracle, and the
+oracle's own rate on the host cores are reported alongside.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ray-segments/s & frames/s, coherent vs full retrace; Rx power err (dB) vs FP64"
+WORKLOAD = "highway V2I: 2 km 6-lane road + barriers, 200 vehicles, 200 roof Rx, 1M rays, 4 reflections, 28 GHz, 10 Hz frames"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rays", type=int, default=1_000_000)
+    ap.add_argument("--freq", type=float, default=28e9)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, n_frames):
+    from paper_2112_07115_gb300 import scenes
+    sc = scenes.highway(seed=0, n_frames=n_frames, n_rays=args.rays, max_refl=4, freq_hz=args.freq)
+    return sc, scenes.fibonacci_sphere(sc.n_rays)
+
+
+def config(args, sc, extra=None):
+    c = {"workload": WORKLOAD, "triangles": sc.ntri, "vehicles": sc.nobj, "receivers": sc.nrx,
+         "rays": sc.n_rays, "max_reflections": sc.max_refl, "freq_hz": sc.freq_hz,
+         "mode": "coherent", "l2": "flushed before every timed step (256 MiB write)",
+         "parallelism": f"replicas x{args.gpus}"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.lines, self.proc = [], None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def src_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2112_07115_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(kernel)
+    if not e or e.get("src_sha") != src_sha():
+        return None
+    return e
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args):
+    import ctypes as C
+    import torch
+    from paper_2112_07115_gb300 import build as B
+    from paper_2112_07115_gb300 import dcem
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    K, W = args.steps, args.warmup
+    sc, rays = workload(args, n_frames=W + K + 2)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    xf_d = torch.from_numpy(sc.xf).to(dev)
+    rx_d = torch.from_numpy(sc.rx).to(dev)
+    tx = sc.tx
+    nrx = sc.nrx
+    max_paths = 1 << 17
+    field_d = torch.empty((nrx, 2), dtype=torch.float64, device=dev)
+    pc_d = torch.empty(nrx, dtype=torch.float64, device=dev)
+    pi_d = torch.empty(nrx, dtype=torch.float64, device=dev)
+    paths_d = torch.empty(max_paths * C.sizeof(dcem.Path), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def new_result():
+        r = dcem.Result()
+        r.ptr_kind = dcem.PTR_DEVICE
+        r.max_paths = max_paths
+        r.field, r.p_coh_dbm, r.p_inc_dbm = field_d.data_ptr(), pc_d.data_ptr(), pi_d.data_ptr()
+        r.paths = paths_d.data_ptr()
+        return r
+
+    def run(mode, frames, timed):
+        s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+        s.set_rays(rays)
+        prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=1)
+        res = new_result()
+        stats, ms = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i, f in enumerate(frames):
+            is_t = i >= W and timed
+            if is_t:
+                flush.zero_()
+            e0.record(stream)
+            dcem.dcem_scene_update_transforms(s.h, xf_d[f])
+            rc = dcem.dcem_trace_frame(s.h, tx, rx_d[f], prm, res)
+            e1.record(stream)
+            e1.synchronize()
+            if rc != dcem.OK:
+                raise dcem.DcemError(rc, f"frame {f}")
+            if is_t:
+                ms.append(e0.elapsed_time(e1))
+                stats.append(dcem.stats_dict(res.stats))
+        return s, ms, stats
+
+    frames = list(range(1, W + K + 1))
+    # coherent (the headline)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    s_coh, ms_coh, st_coh = run(dcem.MODE_COHERENT, frames, True)
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    # full retrace of the same frames
+    s_full, ms_full, st_full = run(dcem.MODE_FULL, frames, True)
+    t_coh = sum(ms_coh) / 1e3
+    t_full = sum(ms_full) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_coh, t_full], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_coh, t_full = float(t[0]), float(t[1])
+        dist.barrier()
+    fps_coh = world * K / t_coh
+    fps_full = world * K / t_full
+    seg_full = world * sum(x["segments_traced"] for x in st_full) / t_full
+    seg_coh_traced = world * sum(x["segments_traced"] for x in st_coh) / t_coh
+    seg_coh_repr = world * sum(x["segments_traced"] + x["segments_reused"] for x in st_coh) / t_coh
+
+    # stage times and roofline of the dominant kernel (coherent frames)
+    stage_names = dcem.STAGES
+    mean_stage = {n: float(np.mean([x["ms_stage"][n] for x in st_coh])) for n in stage_names}
+    mean_stage_full = {n: float(np.mean([x["ms_stage"][n] for x in st_full])) for n in stage_names}
+    dom = max(["mark", "trace", "dedupe", "validate", "reduce"], key=lambda n: mean_stage[n])
+    R = sc.n_rays
+    peak, peak_kind = measured_peaks()
+
+    def bytes_trace(x):
+        q = x["rays_retraced"]
+        return (q * (32 + 4) + x["segments_traced"] * 36 + x["node_visits"] * 64 + x["tri_tests"] * 48)
+
+    def bytes_mark(x):
+        examined = x["segments_reused"] + x["rays_retraced"]
+        return R * 8 + examined * 32 + x["rays_retraced"] * 4
+
+    kern = {"trace": ("k_trace", bytes_trace), "mark": ("k_mark", bytes_mark)}
+    roof = None
+    if dom in kern:
+        kname, fb = kern[dom]
+        b = float(np.mean([fb(x) for x in st_coh]))
+        ach = b / (mean_stage[dom] * 1e-3) / 1e9
+        tr = ncu_traffic(kname)
+        roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": int(b),
+                "traffic": (tr or {}).get("dram_bytes_per_launch"),
+                "traffic_note": (tr or {}).get("note", "no ncu capture on the current source")}
+    # full-retrace traversal roofline (context)
+    bf = float(np.mean([bytes_trace(x) for x in st_full]))
+    roof_full_trace = {"kernel": "k_trace", "achieved": round(bf / (mean_stage_full["trace"] * 1e-3) / 1e9, 1),
+                       "unit": "GB/s", "frac": None}
+    roof_full_trace["frac"] = round(roof_full_trace["achieved"] / peak, 4)
+    seg_mean = float(np.mean([x["segments_traced"] for x in st_full]))
+    nodes_per_seg = float(np.mean([x["node_visits"] for x in st_full])) / max(seg_mean, 1)
+    tris_per_seg = float(np.mean([x["tri_tests"] for x in st_full])) / max(seg_mean, 1)
+
+    # received power error vs the FP64 oracle on the same path keys (last frame)
+    err = None
+    if rank == 0:
+        err = power_error_vs_oracle(sc, s_coh, frames[-1], max_paths, paths_d, pc_d, pi_d, res_n=st_coh[-1])
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, sc, rays, stream, W, K, world, dev)
+    base = None
+    if rank == 0 and world == 1 and not args.no_baseline:
+        base = cpu_baseline(sc, rays, frames[W])
+    launches = int(np.mean([x["kernel_launches"] for x in st_coh]))
+    s_coh.close()
+    s_full.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(fps_coh, 2), "unit": "frames/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": round(1e3 * t_coh / K, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry / f64 field",
+            "data": "synthetic (seeded highway generator)", "impl": "ours",
+            "config": config(args, sc),
+            "coherent": {"frames_per_s": round(fps_coh, 2), "ms_per_frame": round(1e3 * t_coh / K, 4),
+                         "ray_segments_traced_per_s": round(seg_coh_traced, 0),
+                         "ray_segments_represented_per_s": round(seg_coh_repr, 0),
+                         "rays_retraced_frac": round(float(np.mean([x["rays_retraced"] for x in st_coh])) / R, 4),
+                         "segments_reused_frac": round(float(np.mean(
+                             [x["segments_reused"] / max(1, x["segments_reused"] + x["segments_traced"])
+                              for x in st_coh])), 4),
+                         "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
+                         "frame_ms_p50_max": [round(float(np.median(ms_coh)), 4), round(float(max(ms_coh)), 4)],
+                         "nodes_per_segment": round(float(np.sum([x["node_visits"] for x in st_coh])) /
+                                                    max(1.0, float(np.sum([x["segments_traced"] for x in st_coh]))), 2),
+                         "max_segment_nodes": int(max(x["max_segment_nodes"] for x in st_coh)),
+                         "bvh_rebuilds": int(sum(x["bvh_rebuilt"] for x in st_coh))},
+            "full": {"frames_per_s": round(fps_full, 2), "ms_per_frame": round(1e3 * t_full / K, 4),
+                     "ray_segments_per_s": round(seg_full, 0), "segments_per_frame": int(seg_mean),
+                     "nodes_per_segment": round(nodes_per_seg, 2), "tris_per_segment": round(tris_per_seg, 2),
+                     "max_segment_nodes": int(max(x["max_segment_nodes"] for x in st_full)),
+                     "stage_ms": {k: round(v, 4) for k, v in mean_stage_full.items()},
+                     "frame_ms_p50_max": [round(float(np.median(ms_full)), 4), round(float(max(ms_full)), 4)],
+                     "trace_roofline": roof_full_trace},
+            "coherent_speedup": round(fps_coh / fps_full, 3),
+            "paths_per_frame": int(np.mean([x["paths_valid"] for x in st_coh])),
+            "rx_power_err_db": err,
+            "roofline": roof,
+            "e2e": e2e,
+            "cpu_baseline": base,
+            "clocks": clocks,
+            "gpu_launches": launches * K,
+            "gpu_launches_per_step": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def power_error_vs_oracle(sc, s, f, max_paths, paths_d, pc_d, pi_d, res_n):
+    """Validate the GPU's distinct path keys with the FP64 oracle and compare
+    the per-receiver power (same path set, FP64 vs the GPU)."""
+    from oracle import oracle as O
+    from paper_2112_07115_gb300 import dcem
+    n = min(int(res_n["paths_valid"]), max_paths)
+    raw = paths_d[: n * dcem.PATH_DTYPE.itemsize].cpu().numpy().view(dcem.PATH_DTYPE)
+    N = sc.max_refl
+    keys = np.full((n, 2 + N), -1, np.int32)
+    keys[:, 0] = raw["rx"]
+    keys[:, 1] = raw["depth"]
+    keys[:, 2:] = raw["tri"][:, :N]
+    order = np.lexsort(keys.T[::-1])
+    keys = keys[order]
+    wt = O.transform(sc.tris, sc.tri_obj, sc.xf[f])
+    prm = O.OracleParams(freq_hz=sc.freq_hz, n_rays=sc.n_rays, max_refl=N)
+    ref = O.validate(wt, sc.tri_mat, sc.materials, sc.tx, sc.rx[f], keys, prm)
+    _, pc, pi = O.reduce(keys, ref, sc.nrx, prm.tx_power_w)
+    gc, gi = pc_d.cpu().numpy(), pi_d.cpu().numpy()
+    fin = np.isfinite(pc) & np.isfinite(gc)
+    return {"frame": int(f), "paths": int(n), "oracle_invalid": int((ref["valid"] == 0).sum()),
+            "max_abs_p_coh": float(np.max(np.abs(pc[fin] - gc[fin]))) if fin.any() else 0.0,
+            "max_abs_p_inc": float(np.max(np.abs(pi[fin] - gi[fin]))) if fin.any() else 0.0,
+            "max_len_err_m": float(np.max(np.abs(ref["len_m"][ref["valid"] == 1] -
+                                                 raw["len_m"][order][ref["valid"] == 1]))) if n else 0.0,
+            "against": "FP64 oracle validation of the same path keys"}
+
+
+def run_e2e(args, sc, rays, stream, W, K, world, dev):
+    """Same frames through the C ABI with host buffers: per step the
+    transforms and receivers are copied host->device and the per-receiver
+    results and paths device->host inside the timed region."""
+    import torch
+    from paper_2112_07115_gb300 import dcem
+    s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+    s.set_rays(rays)
+    prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=dcem.MODE_COHERENT)
+    xf_h = torch.from_numpy(sc.xf).pin_memory()
+    rx_h = torch.from_numpy(sc.rx).pin_memory()
+    nrx = sc.nrx
+    max_paths = 1 << 17
+    field = torch.empty((nrx, 2), dtype=torch.float64).pin_memory()
+    pc = torch.empty(nrx, dtype=torch.float64).pin_memory()
+    pi = torch.empty(nrx, dtype=torch.float64).pin_memory()
+    paths = torch.empty(max_paths * dcem.PATH_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    res = dcem.Result()
+    res.ptr_kind = dcem.PTR_HOST
+    res.max_paths = max_paths
+    res.field, res.p_coh_dbm, res.p_inc_dbm, res.paths = (field.data_ptr(), pc.data_ptr(), pi.data_ptr(),
+                                                          paths.data_ptr())
+    h2d = d2h = 0
+    t = 0.0
+    for i, f in enumerate(range(1, W + K + 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dcem.dcem_scene_update_transforms(s.h, xf_h[f])
+        rc = dcem.dcem_trace_frame(s.h, sc.tx, rx_h[f], prm, res)
+        t1 = time.perf_counter()
+        if rc != dcem.OK:
+            raise dcem.DcemError(rc, "e2e")
+        if i >= W:
+            t += t1 - t0
+            h2d += sc.nobj * 48 + nrx * 12
+            d2h += nrx * 32 + res.n_paths * dcem.PATH_DTYPE.itemsize + 2 * 96
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt[0])
+    return {"value": round(world * K / t, 2), "unit": "frames/s", "h2d_bytes_per_step": int(h2d / K),
+            "d2h_bytes_per_step": int(d2h / K),
+            "note": "C-ABI calls with pinned host transforms/receivers and host outputs; wall clock"}
+
+
+def cpu_baseline(sc, rays, f, frac=8):
+    """The FP64 oracle on the host cores, on a bounded sample of one frame:
+    every `frac`-th ray traced and its distinct keys validated, scaled by frac."""
+    from oracle import oracle as O
+    prm = O.OracleParams(freq_hz=sc.freq_hz, n_rays=sc.n_rays, max_refl=sc.max_refl)
+    wt = O.transform(sc.tris, sc.tri_obj, sc.xf[f])
+    sub = rays[::frac]
+    t0 = time.perf_counter()
+    tr = O.trace(wt, sc.tri_mat, sc.materials, sc.tx, sub, sc.rx[f], prm)
+    keys = O.unique_keys(O.candidate_keys(tr["cands"], tr["hit_id"], prm.max_refl))
+    O.validate(wt, sc.tri_mat, sc.materials, sc.tx, sc.rx[f], keys, prm)
+    dt = time.perf_counter() - t0
+    t_frame = dt * frac
+    segs = int(tr["nseg"].sum()) * frac
+    return {"value": round(1.0 / t_frame, 5), "unit": "frames/s", "cores": os.cpu_count(),
+            "kind": "oracle", "ray_segments_per_s": round(segs / t_frame, 0),
+            "sample": f"every {frac}th ray of highway frame {f} ({len(sub)} rays) traced + its keys validated, "
+                      f"{dt:.1f} s, scaled x{frac}"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    K, W = args.steps, args.warmup
+    sc, rays = workload(args, n_frames=W + K + 2)
+    frac = 32
+    prm = O.OracleParams(freq_hz=sc.freq_hz, n_rays=sc.n_rays, max_refl=sc.max_refl)
+    times, segs = [], []
+    for i, f in enumerate(range(1, W + K + 1)):
+        sub = rays[(f % frac)::frac]
+        t0 = time.perf_counter()
+        wt = O.transform(sc.tris, sc.tri_obj, sc.xf[f])
+        tr = O.trace(wt, sc.tri_mat, sc.materials, sc.tx, sub, sc.rx[f], prm)
+        keys = O.unique_keys(O.candidate_keys(tr["cands"], tr["hit_id"], prm.max_refl))
+        O.validate(wt, sc.tri_mat, sc.materials, sc.tx, sc.rx[f], keys, prm)
+        dt = time.perf_counter() - t0
+        if i >= W:
+            times.append(dt * frac)
+            segs.append(int(tr["nseg"].sum()) * frac)
+    t = sum(times)
+    v = K / t
+    line = {"metric": METRIC, "value": round(v, 5), "unit": "frames/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": round(1e3 * t / K, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+            "data": "synthetic (seeded highway generator)", "config": config(args, sc, {"mode": "full retrace"}),
+            "ray_segments_per_s": round(sum(segs) / t, 0),
+            "cpu_baseline": {"value": round(v, 5), "unit": "frames/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"each step traces 1/{frac} of the rays of one frame and validates "
+                                       f"its keys; time scaled x{frac}"},
+            "e2e": {"value": round(v, 5), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

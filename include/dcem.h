@@ -119,10 +119,21 @@ typedef struct {
   int64_t paths_valid;         /* validated paths                                */
   int64_t objects_moved;       /* rigid objects whose transform changed          */
   int64_t rx_moved;            /* receivers whose position changed               */
+  int64_t node_visits;         /* BVH internal nodes visited by closest-hit
+                                  traversals (64 B each)                         */
+  int64_t tri_tests;           /* triangles tested by closest-hit traversals
+                                  (48 B each)                                    */
   int32_t stack_overflow;      /* traversals that overflowed the stack           */
   int32_t coherent;            /* 1 if the frame reused the cache                */
+  int32_t kernel_launches;     /* kernels launched by this call and by the
+                                  transform updates since the previous frame    */
+  int32_t bvh_rebuilt;         /* 1 if the moving-object tree was rebuilt since
+                                  the previous frame                             */
   float ms_stage[8];           /* if params.timing: prep, mark, trace, dedupe,
                                   validate, reduce, copy-out, total              */
+  float bvh_cost_ratio;        /* surface-area cost of the moving-object tree
+                                  over its cost right after the last rebuild     */
+  int32_t max_segment_nodes;   /* most BVH nodes visited by one traversal        */
 } dcem_stats;
 
 typedef struct {
@@ -184,6 +195,16 @@ int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kin
  * DCEM_ERR_STACK, DCEM_ERR_HASH, DCEM_ERR_CUDA. */
 int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nrx,
                      int32_t rx_ptr_kind, const dcem_params* params, dcem_result* out);
+
+/* Quality-driven rebuild of the moving-object hierarchy (Sec. III "Efficient
+ * BVH updating": update every frame, rebuild only when the measured
+ * degradation warrants it). After every refit the library measures the
+ * tree's surface-area cost (sum of node surface areas over the root's); when
+ * it exceeds `ratio` times the cost right after the last rebuild, the next
+ * dcem_scene_update_transforms rebuilds the tree (LBVH over the current
+ * positions) instead of refitting it. ratio <= 0: refit only. Default 1.25.
+ * Results never depend on the tree shape. Errors: DCEM_ERR_ARG. */
+int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
 
 /* Drops the coherence cache: the next COHERENT frame is a full retrace. */
 int dcem_scene_reset_cache(dcem_scene* s);

@@ -89,6 +89,43 @@ __global__ void k_place_dyn(const float* __restrict__ v9, const float4* __restri
   }
 }
 
+__device__ __forceinline__ unsigned spread16(unsigned v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+// Direction-coherence key of each ray: 2D Morton code of its octahedral map.
+__global__ void k_ray_keys(const float4* __restrict__ d, int n, unsigned* keys, unsigned* idx) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float4 v = d[i];
+    float l1 = fabsf(v.x) + fabsf(v.y) + fabsf(v.z);
+    float x = v.x / l1, y = v.y / l1;
+    if (v.z < 0.0f) {
+      float fx = (1.0f - fabsf(y)) * (x >= 0.0f ? 1.0f : -1.0f);
+      float fy = (1.0f - fabsf(x)) * (y >= 0.0f ? 1.0f : -1.0f);
+      x = fx;
+      y = fy;
+    }
+    unsigned qu = (unsigned)fminf(fmaxf((x + 1.0f) * 32767.5f, 0.0f), 65535.0f);
+    unsigned qv = (unsigned)fminf(fmaxf((y + 1.0f) * 32767.5f, 0.0f), 65535.0f);
+    keys[i] = (spread16(qu) << 1) | spread16(qv);
+    idx[i] = (unsigned)i;
+  }
+}
+
+__global__ void k_gather_rays(const float4* __restrict__ src, const unsigned* __restrict__ idx, int n,
+                              float4* dst, int* perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned j = idx[i];
+    dst[i] = src[j];
+    perm[i] = (int)j;
+  }
+}
+
 }  // namespace
 
 struct dcem_scene {
@@ -120,13 +157,18 @@ struct dcem_scene {
   BuildScratch scr;
   int root_h[2] = {kEmpty, kEmpty};
   bool dyn_on_world = false;
+  float rebuild_ratio = 1.25f;   // rebuild the moving-object tree above this cost ratio
+  float sah_build = 0.0f, sah_now = 0.0f;
+  bool rebuilt_since_frame = false;
   DevCounters* ctr = nullptr;
   DevCounters* uctr = nullptr;  // errors raised by per-frame updates
   DevCounters* ctr_h = nullptr; // pinned: [0] frame counters, [1] update counters
   // rays and segment log
   bool rays_set = false;
   int R = 0;
-  float4* rays = nullptr;
+  float4* rays = nullptr;        // sorted by direction: slot order
+  int* ray_perm = nullptr;       // slot -> caller's ray index
+  std::vector<int> ray_perm_h;
   int logW = 0;
   float4* log_o = nullptr;
   float4* log_d = nullptr;
@@ -146,6 +188,8 @@ struct dcem_scene {
   int* uniq = nullptr;
   unsigned ucap = 0;
   PathRec* prec = nullptr;
+  double* vpts = nullptr;
+  int* vstate = nullptr;
   dcem_path* pout = nullptr;
   // receivers
   int nrx_cap = 0;
@@ -158,6 +202,15 @@ struct dcem_scene {
   unsigned* bucket_cnt = nullptr;
   int bucket_cap = 1024;
   double* rxout = nullptr;
+  // per-frame trees over the receivers and over the moved-object boxes
+  float* rx_prim = nullptr;
+  float4* rxt_nodes = nullptr;
+  int *rxt_parent = nullptr, *rxt_perm = nullptr, *rxt_arrive = nullptr, *rxt_root = nullptr;
+  float* rxt_root_box = nullptr;
+  float4* mvt_nodes = nullptr;
+  int *mvt_parent = nullptr, *mvt_perm = nullptr, *mvt_arrive = nullptr, *mvt_root = nullptr;
+  float* mvt_root_box = nullptr;
+  int mv_cap = 0;
   // coherence cache
   bool cache_valid = false;
   dcem_params cparams;
@@ -165,14 +218,14 @@ struct dcem_scene {
   int cnrx = -1;
   unsigned last_ncand = 0;
   cudaEvent_t ev[9] = {};
-  bool events = false;
+  int launches = 0;  // kernels launched since the last completed frame
 };
 
 namespace {
 
 void scene_free(dcem_scene* s) {
   if (!s) return;
-  if (s->st || true) cudaStreamSynchronize(s->st);
+  cudaStreamSynchronize(s->st);
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
@@ -180,11 +233,15 @@ void scene_free(dcem_scene* s) {
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
   dfree(s->scr.v1); dfree(s->scr.hist); dfree(s->scr.keys); dfree(s->ctr); dfree(s->uctr);
   if (s->ctr_h) cudaFreeHost(s->ctr_h);
-  dfree(s->rays); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->nseg); dfree(s->restart);
+  dfree(s->rays); dfree(s->ray_perm); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->nseg); dfree(s->restart);
   dfree(s->queue); dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->prev_ncand); dfree(s->hkey);
   dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
+  dfree(s->vpts); dfree(s->vstate);
   dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list); dfree(s->bucket);
   dfree(s->bucket_cnt); dfree(s->rxout);
+  dfree(s->rx_prim); dfree(s->rxt_nodes); dfree(s->rxt_parent); dfree(s->rxt_perm); dfree(s->rxt_arrive);
+  dfree(s->rxt_root); dfree(s->rxt_root_box); dfree(s->mvt_nodes); dfree(s->mvt_parent); dfree(s->mvt_perm);
+  dfree(s->mvt_arrive); dfree(s->mvt_root); dfree(s->mvt_root_box);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
   delete s;
@@ -202,10 +259,46 @@ int root_code(int n, int node_base, int leaf_base) {
   return n >= 2 ? node_base : (n == 1 ? ~leaf_base : kEmpty);
 }
 
+bool dyn_fused(const dcem_scene* s) {
+  return s->nd <= kSmemRefit + 1 && dyn_update_smem(s->nd, s->nobj) <= 200 * 1024;
+}
+
+// One-CTA update of the moving-object tree (see DynUpdateArgs).
+int dyn_update(dcem_scene* s, bool rebuild) {
+  if (s->nd == 0) return DCEM_OK;
+  DynUpdateArgs d;
+  d.objv_src = s->objv_src;
+  d.objv = s->objv;
+  d.sel_d = s->sel_d;
+  d.tri_mat = s->tri_mat_d;
+  d.xf = s->xf_cur;
+  d.prim = s->prim;
+  d.nd = s->nd;
+  d.nobj = s->nobj;
+  d.node_base = s->nint_s;
+  d.leaf_base = s->ns;
+  d.rebuild = rebuild ? 1 : 0;
+  d.tris = s->tris;
+  d.nodes = s->nodes;
+  d.leaf_parent = s->leaf_parent;
+  d.perm = s->perm;
+  d.slot_of_id = s->slot_of_id;
+  d.obj_box = s->obj_box_cur;
+  d.root_box = s->root_box + 6;
+  d.root = s->roots + 1;
+  d.uctr = s->uctr;
+  CK(launch_dyn_update(d, s->st));
+  s->launches += 1;
+  if (rebuild) s->rebuilt_since_frame = true;
+  return DCEM_OK;
+}
+
 // (Re)builds the moving-object tree over the objects' current world positions.
 int rebuild_dynamic(dcem_scene* s) {
   if (s->nd == 0) return DCEM_OK;
+  if (dyn_fused(s)) return dyn_update(s, true);
   int bs = 256, g = (s->nd + bs - 1) / bs;
+  s->launches += 3 + (s->nd <= kSmallBuild ? 1 : 22);
   k_xform_prims<<<g, bs, 0, s->st>>>(s->objv_src, s->xf_cur, s->nd, s->v9d);
   launch_tri_boxes(s->v9d, nullptr, s->nd, s->prim, s->st);
   CK(build_tree(s->prim, s->nd, s->nint_s, s->ns, s->nodes, s->leaf_parent, s->perm, s->arrive, s->roots + 1,
@@ -254,10 +347,12 @@ int ensure_paths(dcem_scene* s, unsigned cand_cap, unsigned ucap) {
     s->cache_valid = false;  // previous captures are gone
   }
   if (ucap > s->ucap) {
-    dfree(s->uniq); dfree(s->prec); dfree(s->pout);
+    dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->vpts); dfree(s->vstate);
     CK(dalloc(&s->uniq, ucap));
     CK(dalloc(&s->prec, ucap));
     CK(dalloc(&s->pout, ucap));
+    CK(dalloc(&s->vpts, (size_t)ucap * 3 * (kMaxRefl + 2)));
+    CK(dalloc(&s->vstate, ucap));
     s->ucap = ucap;
   }
   return DCEM_OK;
@@ -277,7 +372,13 @@ int ensure_rx(dcem_scene* s, int nrx, int bucket_cap) {
   if (bucket_cap > s->bucket_cap) s->bucket_cap = bucket_cap;
   CK(dalloc(&s->bucket, (size_t)cap * s->bucket_cap));
   CK(dalloc(&s->bucket_cnt, cap));
-  CK(dalloc(&s->rxout, 4 * (size_t)cap));
+  CK(dalloc(&s->rxout, 4 * (size_t)cap));  // staging: field (2 cap), P_coh (cap), P_inc (cap)
+  dfree(s->rx_prim); dfree(s->rxt_nodes); dfree(s->rxt_parent); dfree(s->rxt_perm); dfree(s->rxt_arrive);
+  CK(dalloc(&s->rx_prim, 6 * (size_t)cap));
+  CK(dalloc(&s->rxt_nodes, 4 * (size_t)cap));
+  CK(dalloc(&s->rxt_parent, cap));
+  CK(dalloc(&s->rxt_perm, cap));
+  CK(dalloc(&s->rxt_arrive, cap));
   s->nrx_cap = cap;
   s->cache_valid = false;
   return DCEM_OK;
@@ -405,6 +506,15 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->obj_box_cur, 6 * (size_t)nobj));
   CKF(dalloc(&s->obj_box_traced, 6 * (size_t)nobj));
   CKF(dalloc(&s->moved_boxes, 12 * (size_t)nobj));
+  s->mv_cap = std::min(2 * nobj, kSmallBuild);
+  CKF(dalloc(&s->mvt_nodes, 4 * (size_t)s->mv_cap));
+  CKF(dalloc(&s->mvt_parent, s->mv_cap));
+  CKF(dalloc(&s->mvt_perm, s->mv_cap));
+  CKF(dalloc(&s->mvt_arrive, s->mv_cap));
+  CKF(dalloc(&s->mvt_root, 1));
+  CKF(dalloc(&s->mvt_root_box, 6));
+  CKF(dalloc(&s->rxt_root, 1));
+  CKF(dalloc(&s->rxt_root_box, 6));
   CKF(dalloc(&s->ctr, 1));
   CKF(dalloc(&s->uctr, 1));
   CKF(dalloc(&s->prev_ncand, 1));
@@ -451,9 +561,11 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(cudaMemsetAsync(s->uctr, 0, sizeof(DevCounters), st));
   CKF(cudaMemsetAsync(s->prev_ncand, 0, sizeof(unsigned), st));
   if (nobj) {
-    CKF(cudaMemsetAsync(s->obj_box_cur, 0xff, sizeof(unsigned) * 3 * nobj, st));
-    CKF(cudaMemsetAsync(s->obj_box_cur + 3 * nobj, 0, sizeof(unsigned) * 3 * nobj, st));
-    if (s->nd) {
+    if (!(s->nd && dyn_fused(s))) {  // the fused update already wrote the object boxes
+      CKF(cudaMemsetAsync(s->obj_box_cur, 0xff, sizeof(unsigned) * 3 * nobj, st));
+      CKF(cudaMemsetAsync(s->obj_box_cur + 3 * nobj, 0, sizeof(unsigned) * 3 * nobj, st));
+    }
+    if (s->nd && !dyn_fused(s)) {
       CKF(cudaMemsetAsync(s->arrive, 0, sizeof(int) * (s->nint_d > 0 ? s->nint_d : 1), st));
       launch_transform_refit(s->objv, s->xf_cur, s->nd, nobj, s->nint_s, s->ns, s->tris, s->nodes, s->leaf_parent,
                              s->arrive, s->root_box + 6, s->obj_box_cur, s->uctr, st);
@@ -479,17 +591,47 @@ int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays) {
     if (!(x * x + y * y + z * z > 0.0f)) return DCEM_ERR_ARG;
   }
   CK(cudaStreamSynchronize(s->st));
-  dfree(s->rays); dfree(s->nseg); dfree(s->restart); dfree(s->queue);
+  dfree(s->rays); dfree(s->ray_perm); dfree(s->nseg); dfree(s->restart); dfree(s->queue);
   dfree(s->log_o); dfree(s->log_d); dfree(s->log_id);
   s->logW = 0;
   s->R = n_rays;
+  s->rays_set = false;
   CK(dalloc(&s->rays, n_rays));
+  CK(dalloc(&s->ray_perm, n_rays));
   CK(dalloc(&s->nseg, n_rays));
   CK(dalloc(&s->restart, n_rays));
   CK(dalloc(&s->queue, n_rays));
-  std::vector<float4> h(n_rays > 0 ? n_rays : 1);
-  for (int i = 0; i < n_rays; ++i) h[i] = make_float4(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], 0.0f);
-  if (n_rays) CK(cudaMemcpy(s->rays, h.data(), sizeof(float4) * n_rays, cudaMemcpyHostToDevice));
+  s->ray_perm_h.assign(n_rays, 0);
+  if (n_rays) {
+    // upload, then reorder the rays by direction so that a warp's rays are
+    // close in angle (the caller's order is kept in ray_perm)
+    std::vector<float4> h(n_rays);
+    for (int i = 0; i < n_rays; ++i) h[i] = make_float4(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], 0.0f);
+    float4* src = nullptr;
+    unsigned *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr;
+    int nb = (n_rays + 1023) / 1024;
+    cudaError_t e = dalloc(&src, n_rays);
+    if (!e) e = dalloc(&k0, n_rays);
+    if (!e) e = dalloc(&v0, n_rays);
+    if (!e) e = dalloc(&k1, n_rays);
+    if (!e) e = dalloc(&v1, n_rays);
+    if (!e) e = dalloc(&hist, (size_t)256 * nb);
+    if (!e) e = cudaMemcpyAsync(src, h.data(), sizeof(float4) * n_rays, cudaMemcpyHostToDevice, s->st);
+    if (!e) {
+      int g = std::min((n_rays + 255) / 256, 4096);
+      k_ray_keys<<<g, 256, 0, s->st>>>(src, n_rays, k0, v0);
+      e = sort_pairs_u32(k0, v0, k1, v1, hist, n_rays, 32, s->st);
+      if (!e) {
+        k_gather_rays<<<g, 256, 0, s->st>>>(src, v0, n_rays, s->rays, s->ray_perm);
+        e = cudaGetLastError();
+      }
+    }
+    if (!e) e = cudaMemcpyAsync(s->ray_perm_h.data(), s->ray_perm, sizeof(int) * n_rays, cudaMemcpyDeviceToHost,
+                                s->st);
+    if (!e) e = cudaStreamSynchronize(s->st);
+    dfree(src); dfree(k0); dfree(v0); dfree(k1); dfree(v1); dfree(hist);
+    CK(e);
+  }
   s->rays_set = true;
   s->cache_valid = false;
   return DCEM_OK;
@@ -504,6 +646,17 @@ int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kin
   cudaStream_t st = s->st;
   CK(cudaMemcpyAsync(s->xf_cur, xf, sizeof(float) * 12 * s->nobj,
                      ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  if (dyn_fused(s)) {
+    // Sec. III: refit every frame; rebuild when the measured quality of the
+    // refit tree has degraded (surface-area cost ratio above the threshold)
+    bool rebuild = !s->dyn_on_world ||
+                   (s->rebuild_ratio > 0.0f && s->sah_build > 0.0f && s->sah_now > s->rebuild_ratio * s->sah_build);
+    int rc = dyn_update(s, rebuild);
+    if (rc != DCEM_OK) return rc;
+    s->dyn_on_world = true;
+    if (rebuild) s->sah_now = 0.0f;  // until the next measurement
+    return DCEM_OK;
+  }
   if (!s->dyn_on_world) {
     int rc = rebuild_dynamic(s);
     if (rc != DCEM_OK) return rc;
@@ -516,7 +669,14 @@ int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kin
     launch_transform_refit(s->objv, s->xf_cur, s->nd, s->nobj, s->nint_s, s->ns, s->tris, s->nodes,
                            s->leaf_parent, s->arrive, s->root_box + 6, s->obj_box_cur, s->uctr, st);
     CK(cudaGetLastError());
+    s->launches += 1;
   }
+  return DCEM_OK;
+}
+
+int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio) {
+  if (!s || !std::isfinite(ratio)) return DCEM_ERR_ARG;
+  s->rebuild_ratio = ratio;
   return DCEM_OK;
 }
 
@@ -535,15 +695,16 @@ int dcem_scene_set_stream(dcem_scene* s, void* stream) {
 
 void dcem_scene_destroy(dcem_scene* s) { scene_free(s); }
 
-static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent) {
+static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent,
+                      const dcem_result* out) {
   cudaStream_t st = s->st;
   int N = p->max_refl;
   int nxt = s->cur ^ 1;
   bool tm = p->timing != 0;
   if (tm) CK(cudaEventRecord(s->ev[0], st));
   CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
-  if (nrx) CK(cudaMemsetAsync(s->bucket_cnt, 0, sizeof(unsigned) * nrx, st));
-  CK(launch_rx_pack(s->rx3, nrx, s->rx_cur, s->rx_traced, coherent ? 1 : 0, s->rx_moved, s->moved_list, s->ctr, st));
+  // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce
+  s->launches += 1 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0);
 
   TraceArgs a;
   a.bvh.nodes = s->nodes;
@@ -571,14 +732,49 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.cand = s->cand[nxt];
   a.cand_cap = s->cand_cap;
   a.ctr = s->ctr;
+  a.rxt.nodes = s->rxt_nodes;
+  a.rxt.perm = s->rxt_perm;
+  a.rxt.root = s->rxt_root;
+  a.rxt.root_box = s->rxt_root_box;
+  a.rxt.max_visits = 2 * nrx + 8;
+  FramePrepArgs fp;
+  fp.rx3 = s->rx3;
+  fp.nrx = nrx;
+  fp.rx_cur = s->rx_cur;
+  fp.rx_traced = s->rx_traced;
+  fp.have_prev = coherent ? 1 : 0;
+  fp.rx_moved = s->rx_moved;
+  fp.moved_list = s->moved_list;
+  fp.rx_prim = s->rx_prim;
+  fp.bucket_cnt = s->bucket_cnt;
+  fp.coherent = coherent ? 1 : 0;
+  fp.nobj = s->nobj;
+  fp.xf_cur = s->xf_cur;
+  fp.xf_traced = s->xf_traced;
+  fp.obj_box_cur = s->obj_box_cur;
+  fp.obj_box_traced = s->obj_box_traced;
+  fp.moved_boxes = s->moved_boxes;
+  fp.ctr = s->ctr;
+  fp.trx.prim = s->rx_prim;
+  fp.trx.n = nrx;
+  fp.trx.nodes = s->rxt_nodes;
+  fp.trx.leaf_parent = s->rxt_parent;
+  fp.trx.perm = s->rxt_perm;
+  fp.trx.arrive = s->rxt_arrive;
+  fp.trx.root = s->rxt_root;
+  fp.trx.root_box = s->rxt_root_box;
+  fp.tmv.prim = s->moved_boxes;
+  fp.tmv.cap = s->mv_cap;
+  fp.tmv.nodes = s->mvt_nodes;
+  fp.tmv.leaf_parent = s->mvt_parent;
+  fp.tmv.perm = s->mvt_perm;
+  fp.tmv.arrive = s->mvt_arrive;
+  fp.tmv.root = s->mvt_root;
+  fp.tmv.root_box = s->mvt_root_box;
+  CK(launch_frame_prep(fp, st));
+  if (tm) CK(cudaEventRecord(s->ev[1], st));
   if (coherent) {
     CoherentArgs c;
-    c.nobj = s->nobj;
-    c.xf_cur = s->xf_cur;
-    c.xf_traced = s->xf_traced;
-    c.obj_box_cur = s->obj_box_cur;
-    c.obj_box_traced = s->obj_box_traced;
-    c.moved_boxes = s->moved_boxes;
     c.moved_list = s->moved_list;
     c.rx_moved = s->rx_moved;
     c.restart = s->restart;
@@ -586,21 +782,18 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
     c.prev_cand = s->cand[s->cur];
     c.prev_ncand = s->prev_ncand;
     c.prev_cap = s->cand_cap;
-    c.smem_boxes = 2 * s->nobj < kMovedSmem ? 2 * s->nobj : kMovedSmem;
-    c.smem_rx = nrx < kRxSmem ? nrx : kRxSmem;
-    CK(launch_coherent_prep(c, st));
-    if (tm) CK(cudaEventRecord(s->ev[1], st));
+    c.mvt.nodes = s->mvt_nodes;
+    c.mvt.perm = s->mvt_perm;
+    c.mvt.root = s->mvt_root;
+    c.mvt.root_box = s->mvt_root_box;
+    c.mvt.max_visits = 2 * s->mv_cap + 8;
+    c.mv_cap = s->mv_cap;
     CK(launch_mark(a, c, grid_cap_of(s, 8), st));
     CK(launch_carry(a, c, st));
-    if (tm) CK(cudaEventRecord(s->ev[2], st));
     a.queue = s->queue;
-  } else {
-    if (tm) {
-      CK(cudaEventRecord(s->ev[1], st));
-      CK(cudaEventRecord(s->ev[2], st));
-    }
   }
-  if (s->R > 0) CK(launch_trace(a, grid_cap_of(s, 16), st));
+  if (tm) CK(cudaEventRecord(s->ev[2], st));
+  if (s->R > 0) CK(launch_trace(a, s->sms, st));
   if (tm) CK(cudaEventRecord(s->ev[3], st));
 
   PathArgs q;
@@ -615,12 +808,26 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   q.uniq = s->uniq;
   q.ucap = s->ucap;
   q.prec = s->prec;
+  q.ray_perm = s->ray_perm;
+  q.vpts = s->vpts;
+  q.vstate = s->vstate;
+  q.N = N;
   q.bucket = s->bucket;
   q.bucket_cnt = s->bucket_cnt;
   q.bucket_cap = s->bucket_cap;
-  q.pout = s->pout;
-  q.pout_cap = s->ucap;
-  q.rxout = s->rxout;
+  if (out->ptr_kind == DCEM_PTR_DEVICE) {  // results go straight to the caller's buffers
+    q.pout = out->paths;
+    q.pout_cap = out->paths ? (unsigned)out->max_paths : 0u;
+    q.out_field = out->field;
+    q.out_pc = out->p_coh_dbm;
+    q.out_pi = out->p_inc_dbm;
+  } else {
+    q.pout = s->pout;
+    q.pout_cap = s->ucap;
+    q.out_field = s->rxout;
+    q.out_pc = s->rxout + 2 * (size_t)s->nrx_cap;
+    q.out_pi = s->rxout + 3 * (size_t)s->nrx_cap;
+  }
   q.tris = s->tris;
   q.slot_of_id = s->slot_of_id;
   q.mats = s->mats;
@@ -658,7 +865,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
                      const dcem_params* p, dcem_result* out) {
   if (!s || !tx || !p || !out) return DCEM_ERR_ARG;
   if (nrx < 0 || (nrx > 0 && !rx)) return DCEM_ERR_ARG;
-  if (nrx >= (1 << 27)) return DCEM_ERR_ARG;
+  if (nrx > kSmallBuild) return DCEM_ERR_ARG;
   if (rx_ptr_kind != DCEM_PTR_HOST && rx_ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->ptr_kind != DCEM_PTR_HOST && out->ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->max_paths < 0 || (out->max_paths > 0 && !out->paths)) return DCEM_ERR_ARG;
@@ -694,7 +901,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
                   s->logW == p->max_refl + 1;
   DevCounters* c = nullptr;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    rc = trace_once(s, tx, nrx, p, coherent);
+    rc = trace_once(s, tx, nrx, p, coherent, out);
     if (rc != DCEM_OK) {
       s->cache_valid = false;
       return rc;
@@ -738,8 +945,18 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   S.paths_valid = c[0].n_valid;
   S.objects_moved = coherent ? (int64_t)c[0].objects_moved : (int64_t)s->nobj;
   S.rx_moved = c[0].rx_moved;
+  S.node_visits = (int64_t)c[0].node_visits;
+  S.max_segment_nodes = (int32_t)c[0].max_seg_nodes;
+  S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;
+  S.kernel_launches = s->launches;
+  s->launches = 0;
+  if (c[1].sah_build > 0.0f) s->sah_build = c[1].sah_build;
+  if (c[1].sah_refit > 0.0f) s->sah_now = c[1].sah_refit;
+  S.bvh_rebuilt = s->rebuilt_since_frame ? 1 : 0;
+  s->rebuilt_since_frame = false;
+  S.bvh_cost_ratio = s->sah_build > 0.0f ? s->sah_now / s->sah_build : 0.0f;
   s->last_ncand = std::min(c[0].n_cand, s->cand_cap);
   if (err & ERR_HASH_COLLISION) {
     s->cache_valid = false;
@@ -753,15 +970,18 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   }
   // copy out
   bool tm = p->timing != 0;
-  cudaMemcpyKind k = out->ptr_kind == DCEM_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (nrx) {
-    if (out->field) CK(cudaMemcpy2DAsync(out->field, 16, s->rxout, 32, 16, nrx, k, st));
-    if (out->p_coh_dbm) CK(cudaMemcpy2DAsync(out->p_coh_dbm, 8, s->rxout + 2, 32, 8, nrx, k, st));
-    if (out->p_inc_dbm) CK(cudaMemcpy2DAsync(out->p_inc_dbm, 8, s->rxout + 3, 32, 8, nrx, k, st));
-  }
   int nvalid = (int)c[0].n_valid;
-  int ncopy = std::min(nvalid, out->max_paths);
-  if (ncopy > 0) CK(cudaMemcpyAsync(out->paths, s->pout, sizeof(dcem_path) * ncopy, k, st));
+  if (out->ptr_kind == DCEM_PTR_HOST) {
+    cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+    size_t cap = (size_t)s->nrx_cap;
+    if (nrx) {
+      if (out->field) CK(cudaMemcpyAsync(out->field, s->rxout, sizeof(double) * 2 * nrx, k, st));
+      if (out->p_coh_dbm) CK(cudaMemcpyAsync(out->p_coh_dbm, s->rxout + 2 * cap, sizeof(double) * nrx, k, st));
+      if (out->p_inc_dbm) CK(cudaMemcpyAsync(out->p_inc_dbm, s->rxout + 3 * cap, sizeof(double) * nrx, k, st));
+    }
+    int ncopy = std::min(nvalid, out->max_paths);
+    if (ncopy > 0 && out->paths) CK(cudaMemcpyAsync(out->paths, s->pout, sizeof(dcem_path) * ncopy, k, st));
+  }
   if (tm) CK(cudaEventRecord(s->ev[7], st));
   CK(cudaStreamSynchronize(st));
   if (tm) {
@@ -856,12 +1076,13 @@ int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t
     CK(cudaMemcpy(ids.data(), s->log_id, sizeof(int) * (size_t)W * R, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(ld.data(), s->log_d, sizeof(float4) * (size_t)W * R, cudaMemcpyDeviceToHost));
   }
-  for (int i = 0; i < R; ++i) {
-    if (nseg) nseg[i] = ns[i];
+  for (int i = 0; i < R; ++i) {  // slot i holds the caller's ray ray_perm[i]
+    size_t o = (size_t)s->ray_perm_h[i];
+    if (nseg) nseg[o] = ns[i];
     for (int b = 0; b < W; ++b) {
       bool live = b < ns[i];
-      if (hit_id) hit_id[(size_t)i * W + b] = live ? ids[(size_t)b * R + i] : -2;
-      if (hit_t) hit_t[(size_t)i * W + b] = live ? ld[(size_t)b * R + i].w : NAN;
+      if (hit_id) hit_id[o * W + b] = live ? ids[(size_t)b * R + i] : -2;
+      if (hit_t) hit_t[o * W + b] = live ? ld[(size_t)b * R + i].w : NAN;
     }
   }
   return DCEM_OK;
@@ -876,7 +1097,7 @@ int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t*
   CK(cudaMemcpy(c.data(), s->cand[s->cur], sizeof(Cand) * c.size(), cudaMemcpyDeviceToHost));
   int64_t m = std::min<int64_t>(cap, (int64_t)c.size());
   for (int64_t i = 0; i < m; ++i) {
-    out[3 * i] = c[i].ray;
+    out[3 * i] = s->ray_perm_h[c[i].ray];
     out[3 * i + 1] = cand_seg(c[i]);
     out[3 * i + 2] = cand_rx(c[i]);
   }

@@ -132,11 +132,19 @@ __device__ __forceinline__ void refit_up(float4* nodes, int* arrive, int node_ba
 // ---------------------------------------------------------------------------
 // one-CTA builder: n <= kSmallBuild primitives given as boxes (lo.xyz, hi.xyz)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_build_small(const float* __restrict__ prim, int n,
-                                                      int node_base, int leaf_base, float4* nodes,
-                                                      int* leaf_parent, int* perm, int* arrive,
-                                                      int* root_out, float* root_box) {
-  extern __shared__ unsigned long long keys[];
+__device__ __forceinline__ float box_area(const float* b) {
+  float ex = b[3] - b[0], ey = b[4] - b[1], ez = b[5] - b[2];
+  return 2.0f * (ex * ey + ey * ez + ez * ex);
+}
+
+// Topology of the tree over n primitive boxes: Morton codes of the centroids,
+// bitonic sort of (code, index) in shared memory, Karras nodes. Called by all
+// threads of one CTA; `keys` holds the next power of two >= n 64-bit keys.
+// Leaves the leaf order in perm, child codes and parents in the global
+// nodes, and the root code; for n == 1 also the root box.
+__device__ void sort_karras_dev(const float* __restrict__ prim, int n, int node_base, int leaf_base,
+                                float4* nodes, int* leaf_parent, int* perm, int* root_out, float* root_box,
+                                unsigned long long* keys) {
   __shared__ float red[6][32];
   __shared__ float bnd[6];
   int tid = threadIdx.x, nt = blockDim.x;
@@ -144,7 +152,6 @@ __global__ void __launch_bounds__(1024) k_build_small(const float* __restrict__ 
     if (tid == 0) root_out[0] = kEmpty;
     return;
   }
-  // centroid bounds
   float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
   for (int i = tid; i < n; i += nt) {
     const float* b = prim + 6 * (size_t)i;
@@ -183,7 +190,6 @@ __global__ void __launch_bounds__(1024) k_build_small(const float* __restrict__ 
     }
   }
   __syncthreads();
-  // bitonic sort (keys unique: code, index)
   for (int k = 2; k <= np2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < np2; i += nt) {
@@ -204,20 +210,152 @@ __global__ void __launch_bounds__(1024) k_build_small(const float* __restrict__ 
       leaf_parent[leaf_base] = -1;
       for (int k = 0; k < 6; ++k) root_box[k] = prim[k];
     }
+    __syncthreads();
     return;
   }
-  for (int i = tid; i < n - 1; i += nt) {
-    reinterpret_cast<int*>(nodes + 4 * (size_t)(node_base + i) + 3)[2] = -1;
-    arrive[i] = 0;
-  }
+  for (int i = tid; i < n - 1; i += nt) reinterpret_cast<int*>(nodes + 4 * (size_t)(node_base + i) + 3)[2] = -1;
   __syncthreads();
   for (int i = tid; i < n - 1; i += nt) karras_node(keys, n, i, node_base, leaf_base, nodes, leaf_parent);
-  __syncthreads();
   if (tid == 0) root_out[0] = node_base;
-  // in-CTA refit
+  __syncthreads();
+}
+
+// Walk from leaf slot `slot` (box b) to the root through shared-memory child
+// boxes `sbox` (12 floats per node) and arrival counters `sarr`; the second
+// arrival at a node forms its box. Adds each formed node's surface area to
+// *sah (when not null). Topology comes from the global nodes.
+__device__ __forceinline__ void smem_walk_up(const float4* nodes, int node_base, int slot, int p, float* b,
+                                             float* sbox, int* sarr, float* root_box, float* sah) {
+  int code = ~slot;
+  for (int depth = 0; depth < 128 && p >= 0; ++depth) {
+    const int* n3 = reinterpret_cast<const int*>(nodes + 4 * (size_t)p + 3);
+    int li = p - node_base;
+    int side = n3[0] == code ? 0 : 1;
+    volatile float* mine = sbox + 12 * (size_t)li + 6 * side;
+    for (int k = 0; k < 6; ++k) mine[k] = b[k];
+    __threadfence_block();
+    if (atomicAdd(&sarr[li], 1) == 0) return;
+    __threadfence_block();
+    volatile float* both = sbox + 12 * (size_t)li;
+    for (int k = 0; k < 3; ++k) {
+      b[k] = fminf(both[k], both[6 + k]);
+      b[k + 3] = fmaxf(both[k + 3], both[9 + k]);
+    }
+    if (sah) atomicAdd(sah, box_area(b));
+    code = p;
+    p = n3[2];
+    if (p < 0)
+      for (int k = 0; k < 6; ++k) root_box[k] = b[k];
+  }
+}
+
+// Called by all threads of one CTA.
+__device__ void build_small_dev(const float* __restrict__ prim, int n, int node_base, int leaf_base,
+                                float4* nodes, int* leaf_parent, int* perm, int* arrive, int* root_out,
+                                float* root_box, unsigned long long* keys, float* sbox) {
+  int tid = threadIdx.x, nt = blockDim.x;
+  sort_karras_dev(prim, n, node_base, leaf_base, nodes, leaf_parent, perm, root_out, root_box, keys);
+  if (n <= 1) return;
+  if (sbox && n - 1 <= kSmemRefit) {
+    int* sarr = reinterpret_cast<int*>(sbox + 12 * (size_t)(n - 1));
+    for (int i = tid; i < n - 1; i += nt) sarr[i] = 0;
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      const float* pb = prim + 6 * (size_t)perm[j];
+      float b[6] = {pb[0], pb[1], pb[2], pb[3], pb[4], pb[5]};
+      smem_walk_up(nodes, node_base, leaf_base + j, leaf_parent[leaf_base + j], b, sbox, sarr, root_box, nullptr);
+    }
+    __syncthreads();
+    for (int i = tid; i < n - 1; i += nt) {
+      put_child_box(nodes, node_base + i, 0, sbox + 12 * (size_t)i);
+      put_child_box(nodes, node_base + i, 1, sbox + 12 * (size_t)i + 6);
+    }
+    return;
+  }
+  // in-CTA refit through global memory
+  for (int i = tid; i < n - 1; i += nt) arrive[i] = 0;
+  __syncthreads();
   for (int j = tid; j < n; j += nt) {
     const float* b = prim + 6 * (size_t)perm[j];
     refit_up(nodes, arrive, node_base, leaf_parent[leaf_base + j], ~(leaf_base + j), b, root_box);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_build_small(const float* __restrict__ prim, int n,
+                                                      int node_base, int leaf_base, float4* nodes,
+                                                      int* leaf_parent, int* perm, int* arrive,
+                                                      int* root_out, float* root_box) {
+  extern __shared__ unsigned long long keys[];
+  build_small_dev(prim, n, node_base, leaf_base, nodes, leaf_parent, perm, arrive, root_out, root_box, keys,
+                  nullptr);
+}
+
+// Per-frame preparation (see FramePrepArgs). Shared memory: np2 keys, then,
+// when the larger tree has at most kSmemRefit internal nodes, 12 floats + 1
+// int per internal node for the shared-memory refit.
+__global__ void __launch_bounds__(1024) k_frame_prep(FramePrepArgs a, int np2, int smem_refit) {
+  extern __shared__ unsigned long long keys[];
+  float* sbox = smem_refit ? reinterpret_cast<float*>(keys + np2) : nullptr;
+  int tid = threadIdx.x, nt = blockDim.x;
+  if (blockIdx.x == 0) {
+    for (int r = tid; r < a.nrx; r += nt) {
+      float x = a.rx3[3 * r], y = a.rx3[3 * r + 1], z = a.rx3[3 * r + 2];
+      if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(&a.ctr->err, ERR_NONFINITE);
+      a.rx_cur[r] = make_float4(x, y, z, 0.0f);
+      float* pb = a.rx_prim + 6 * (size_t)r;
+      pb[0] = pb[3] = x;
+      pb[1] = pb[4] = y;
+      pb[2] = pb[5] = z;
+      bool mv = true;
+      if (a.have_prev) {
+        float4 q = a.rx_traced[r];
+        mv = __float_as_uint(q.x) != __float_as_uint(x) || __float_as_uint(q.y) != __float_as_uint(y) ||
+             __float_as_uint(q.z) != __float_as_uint(z);
+      }
+      a.rx_moved[r] = mv ? 1 : 0;
+      if (mv) a.moved_list[atomicAdd(&a.ctr->rx_moved, 1u)] = r;
+      a.bucket_cnt[r] = 0u;
+    }
+    __syncthreads();
+    const SmallTreeArgs& t = a.trx;
+    build_small_dev(t.prim, t.n, 0, 0, t.nodes, t.leaf_parent, t.perm, t.arrive, t.root, t.root_box, keys,
+                    sbox);
+  } else {
+    if (a.coherent) {
+      for (int ob = tid; ob < a.nobj; ob += nt) {
+        bool moved = false;
+        for (int k = 0; k < 12; ++k)
+          moved = moved || (__float_as_uint(a.xf_cur[12 * ob + k]) != __float_as_uint(a.xf_traced[12 * ob + k]));
+        if (!moved) continue;
+        atomicAdd(&a.ctr->objects_moved, 1u);
+        const unsigned* boxes[2] = {a.obj_box_traced, a.obj_box_cur};
+        float bx[2][6];
+        bool ok[2];
+        for (int q = 0; q < 2; ++q) {
+          ok[q] = true;
+          for (int k = 0; k < 3; ++k) {
+            float lo = o2f(boxes[q][3 * (size_t)ob + k]);
+            float hi = o2f(boxes[q][3 * (size_t)(a.nobj + ob) + k]);
+            ok[q] = ok[q] && (lo <= hi);  // false for an object without triangles
+            float m = 1e-3f + 1e-5f * fmaxf(fabsf(lo), fabsf(hi));
+            bx[q][k] = lo - m;
+            bx[q][k + 3] = hi + m;
+          }
+        }
+        unsigned nq = (ok[0] ? 1u : 0u) + (ok[1] ? 1u : 0u);
+        if (!nq) continue;
+        unsigned at = atomicAdd(&a.ctr->n_moved_boxes, nq);
+        for (int q = 0; q < 2; ++q) {
+          if (!ok[q]) continue;
+          float* out = a.moved_boxes + 6 * (size_t)at++;
+          for (int k = 0; k < 6; ++k) out[k] = bx[q][k];
+        }
+      }
+    }
+    __syncthreads();
+    const SmallTreeArgs& t = a.tmv;
+    int n = a.coherent ? (int)min(a.ctr->n_moved_boxes, (unsigned)t.cap) : 0;
+    build_small_dev(t.prim, n, 0, 0, t.nodes, t.leaf_parent, t.perm, t.arrive, t.root, t.root_box, keys, sbox);
   }
 }
 
@@ -451,6 +589,127 @@ __global__ void k_transform_refit(const float4* __restrict__ objv, const float* 
 }
 
 // ---------------------------------------------------------------------------
+// per frame, moving objects of up to kSmemRefit + 1 triangles: one CTA
+// transforms, (re)builds when asked, refits in shared memory and measures
+// the tree's surface-area cost
+// ---------------------------------------------------------------------------
+// Shared-memory layout (n = nd leaves, m = n - 1 nodes, np2 = next power of
+// two >= n): keys[np2] (rebuild sort) | node boxes float[12 m] | arrivals
+// int[m] | topology int[3 m] (child 0, child 1, parent) | object boxes
+// unsigned[6 nobj].
+__global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
+  extern __shared__ unsigned long long keys[];
+  int tid = threadIdx.x, nt = blockDim.x;
+  int n = a.nd, m = n > 1 ? n - 1 : 1;
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  float* sbox = reinterpret_cast<float*>(keys + np2);
+  int* sarr = reinterpret_cast<int*>(sbox + 12 * (size_t)m);
+  int* stop = sarr + m;
+  unsigned* sobj = reinterpret_cast<unsigned*>(stop + 3 * (size_t)m);
+  __shared__ float sah_part[32];
+  __shared__ unsigned bad;
+  if (tid == 0) bad = 0u;
+  float sah = 0.0f;  // this thread's share of the node surface areas
+  for (int k = tid; k < 6 * a.nobj; k += nt) sobj[k] = k < 3 * a.nobj ? 0xffffffffu : 0u;
+  if (a.rebuild) {
+    // world boxes of the primitives (primitive order), then a fresh topology
+    for (int i = tid; i < n; i += nt) {
+      const float4* q = a.objv_src + 3 * (size_t)i;
+      const float* mx = a.xf + 12 * (size_t)__float_as_int(q[0].w);
+      float3 w0 = xform(mx, f3(q[0].x, q[0].y, q[0].z)), w1 = xform(mx, f3(q[1].x, q[1].y, q[1].z)),
+             w2 = xform(mx, f3(q[2].x, q[2].y, q[2].z));
+      tri_box(w0, w1, w2, a.prim + 6 * (size_t)i);
+    }
+    __syncthreads();
+    sort_karras_dev(a.prim, n, a.node_base, a.leaf_base, a.nodes, a.leaf_parent, a.perm, a.root, a.root_box, keys);
+    for (int j = tid; j < n; j += nt) {
+      int i = a.perm[j];
+      int gid = a.sel_d[i];
+      int slot = a.leaf_base + j;
+      for (int k = 0; k < 3; ++k) a.objv[3 * (size_t)j + k] = a.objv_src[3 * (size_t)i + k];
+      a.tris[3 * (size_t)slot].w = __int_as_float(gid);
+      a.tris[3 * (size_t)slot + 1].w = __int_as_float(a.tri_mat[gid]);
+      a.slot_of_id[gid] = slot;
+    }
+  }
+  // topology to shared memory (node-local indices; leaves stay as ~slot)
+  for (int i = tid; i < n - 1; i += nt) {
+    const int* n3 = reinterpret_cast<const int*>(a.nodes + 4 * (size_t)(a.node_base + i) + 3);
+    stop[3 * i] = n3[0];
+    stop[3 * i + 1] = n3[1];
+    stop[3 * i + 2] = n3[2];
+    sarr[i] = 0;
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += nt) {
+    const float4* q = a.objv + 3 * (size_t)j;
+    int ob = __float_as_int(q[0].w);
+    const float* mx = a.xf + 12 * (size_t)ob;
+    float3 w0 = xform(mx, f3(q[0].x, q[0].y, q[0].z)), w1 = xform(mx, f3(q[1].x, q[1].y, q[1].z)),
+           w2 = xform(mx, f3(q[2].x, q[2].y, q[2].z));
+    int slot = a.leaf_base + j;
+    float4* t = a.tris + 3 * (size_t)slot;
+    t[0].x = w0.x; t[0].y = w0.y; t[0].z = w0.z;
+    t[1].x = w1.x; t[1].y = w1.y; t[1].z = w1.z;
+    t[2] = make_float4(w2.x, w2.y, w2.z, 0.0f);
+    float b[6];
+    tri_box(w0, w1, w2, b);
+    bool fin = true;
+    for (int k = 0; k < 6; ++k) fin = fin && isfinite(b[k]);
+    if (!fin) bad = 1u;
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&sobj[3 * ob + k], f2o(b[k]));
+      atomicMax(&sobj[3 * (a.nobj + ob) + k], f2o(b[k + 3]));
+    }
+    if (n == 1) {
+      for (int k = 0; k < 6; ++k) a.root_box[k] = b[k];
+      continue;
+    }
+    // walk up through shared memory
+    int code = ~slot;
+    int p = a.leaf_parent[slot];
+    for (int depth = 0; depth < 128 && p >= 0; ++depth) {
+      int li = p - a.node_base;
+      int side = stop[3 * li] == code ? 0 : 1;
+      volatile float* mine = sbox + 12 * (size_t)li + 6 * side;
+      for (int k = 0; k < 6; ++k) mine[k] = b[k];
+      __threadfence_block();
+      if (atomicAdd(&sarr[li], 1) == 0) break;
+      __threadfence_block();
+      volatile float* both = sbox + 12 * (size_t)li;
+      for (int k = 0; k < 3; ++k) {
+        b[k] = fminf(both[k], both[6 + k]);
+        b[k + 3] = fmaxf(both[k + 3], both[9 + k]);
+      }
+      sah += box_area(b);
+      code = p;
+      p = stop[3 * li + 2];
+      if (p < 0)
+        for (int k = 0; k < 6; ++k) a.root_box[k] = b[k];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n - 1; i += nt) {
+    put_child_box(a.nodes, a.node_base + i, 0, sbox + 12 * (size_t)i);
+    put_child_box(a.nodes, a.node_base + i, 1, sbox + 12 * (size_t)i + 6);
+  }
+  for (int k = tid; k < 6 * a.nobj; k += nt) a.obj_box[k] = sobj[k];
+  for (int off = 16; off > 0; off >>= 1) sah += __shfl_down_sync(0xffffffffu, sah, off);
+  if ((tid & 31) == 0) sah_part[tid >> 5] = sah;
+  __syncthreads();
+  if (tid == 0) {
+    float tot = 0.0f;
+    for (int w = 0; w < (nt + 31) / 32; ++w) tot += sah_part[w];
+    if (bad) atomicOr(&a.uctr->err, ERR_NONFINITE);
+    float ra = box_area(a.root_box);
+    float cost = ra > 0.0f ? tot / ra : 0.0f;
+    a.uctr->sah_refit = cost;
+    if (a.rebuild) a.uctr->sah_build = cost;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static inline int nblk(long n, int bs, int cap = 4096) {
@@ -505,6 +764,47 @@ cudaError_t build_tree(const float* d_prim, int n, int node_base, int leaf_base,
   return cudaGetLastError();
 }
 
+cudaError_t launch_frame_prep(const FramePrepArgs& a, cudaStream_t st) {
+  int nmax = a.nrx > a.tmv.cap ? a.nrx : a.tmv.cap;
+  int np2 = 1;
+  while (np2 < nmax) np2 <<= 1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_frame_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kSmallBuild * sizeof(unsigned long long)));
+    attr = true;
+  }
+  size_t smem = (size_t)np2 * sizeof(unsigned long long);
+  int smem_refit = nmax - 1 <= kSmemRefit ? 1 : 0;
+  if (smem_refit) smem += (size_t)(nmax > 1 ? nmax - 1 : 1) * (12 * sizeof(float) + sizeof(int));
+  k_frame_prep<<<2, 1024, smem, st>>>(a, np2, smem_refit);
+  return cudaGetLastError();
+}
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys; the result is left in k0/v0 (k1/v1, hist are scratch).
+cudaError_t sort_pairs_u32(unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1, unsigned* hist, int n,
+                           int bits, cudaStream_t st) {
+  int nb = (n + kRadixItems - 1) / kRadixItems;
+  unsigned *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+  int passes = (bits + 7) / 8;
+  for (int pass = 0; pass < passes; ++pass) {
+    int shift = 8 * pass;
+    k_radix_hist<<<nb, 256, 0, st>>>(ki, n, shift, hist, nb);
+    k_scan_excl<<<1, 1024, 0, st>>>(hist, 256 * nb);
+    k_radix_scatter<<<nb, 256, 0, st>>>(ki, vi, n, shift, hist, nb, ko, vo);
+    unsigned* t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  if (ki != k0) {
+    cudaError_t e = cudaMemcpyAsync(k0, ki, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(v0, vi, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
 void launch_tri_boxes(const float* d_v9, const int* d_sel, int n, float* d_prim, cudaStream_t st) {
   if (n > 0) k_tri_boxes<<<nblk(n, 256), 256, 0, st>>>(d_v9, d_sel, n, d_prim);
 }
@@ -515,6 +815,27 @@ void launch_place_tris(const float* d_v9, const int* d_sel, const int* d_perm, c
   if (n > 0)
     k_place_tris<<<nblk(n, 256), 256, 0, st>>>(d_v9, d_sel, d_perm, d_tri_mat, d_tri_obj, n, leaf_base,
                                                d_tris, d_objv, d_slot_of_id);
+}
+
+size_t dyn_update_smem(int nd, int nobj) {
+  int np2 = 1;
+  while (np2 < nd) np2 <<= 1;
+  size_t m = (size_t)(nd > 1 ? nd - 1 : 1);
+  return (size_t)np2 * sizeof(unsigned long long) + m * (12 * sizeof(float) + 4 * sizeof(int)) +
+         (size_t)6 * nobj * sizeof(unsigned);
+}
+
+cudaError_t launch_dyn_update(const DynUpdateArgs& a, cudaStream_t st) {
+  if (a.nd <= 0) return cudaSuccess;
+  size_t smem = dyn_update_smem(a.nd, a.nobj);
+  static size_t attr = 0;
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_dyn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  k_dyn_update<<<1, 1024, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 void launch_transform_refit(const float4* d_objv, const float* d_xf, int n, int nobj, int node_base, int leaf_base,

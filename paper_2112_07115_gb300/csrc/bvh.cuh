@@ -21,6 +21,57 @@ cudaError_t build_tree(const float* d_prim, int n, int node_base, int leaf_base,
                        int* d_leaf_parent, int* d_perm, int* d_arrive, int* d_root, float* d_root_box,
                        BuildScratch& scr, cudaStream_t st);
 
+// A small per-frame tree (receivers, moved-object boxes) built by one CTA:
+// n primitives (or min(*n_dev, cap) when n_dev is set), nodes [0, n-1),
+// leaves [0, n) with leaf j holding primitive perm[j].
+struct SmallTreeArgs {
+  const float* prim = nullptr;
+  int n = 0;
+  const unsigned* n_dev = nullptr;
+  int cap = 0;
+  float4* nodes = nullptr;
+  int* leaf_parent = nullptr;
+  int* perm = nullptr;
+  int* arrive = nullptr;
+  int* root = nullptr;
+  float* root_box = nullptr;
+};
+
+// Per-frame preparation in one launch of two CTAs.
+//   CTA 0: receivers -> float4 + point boxes, finiteness check, moved flags
+//          and list (bitwise against the cached frame when have_prev), zero
+//          the per-receiver path counters, then build the receiver tree.
+//   CTA 1: (coherent frames) objects whose transform changed -> their old and
+//          new world boxes (widened by 1 mm + 1e-5 relative), then build the
+//          tree over those boxes.
+struct FramePrepArgs {
+  const float* rx3 = nullptr;
+  int nrx = 0;
+  float4* rx_cur = nullptr;
+  const float4* rx_traced = nullptr;
+  int have_prev = 0;
+  unsigned char* rx_moved = nullptr;
+  int* moved_list = nullptr;
+  float* rx_prim = nullptr;
+  unsigned* bucket_cnt = nullptr;
+  int coherent = 0;
+  int nobj = 0;
+  const float* xf_cur = nullptr;
+  const float* xf_traced = nullptr;
+  const unsigned* obj_box_cur = nullptr;
+  const unsigned* obj_box_traced = nullptr;
+  float* moved_boxes = nullptr;
+  DevCounters* ctr = nullptr;
+  SmallTreeArgs trx, tmv;
+};
+
+cudaError_t launch_frame_prep(const FramePrepArgs& a, cudaStream_t st);
+
+// Stable radix sort of n (key, value) pairs by the low `bits` key bits; the
+// sorted pairs end in k0/v0 (k1, v1: n scratch each; hist: 256*ceil(n/1024)).
+cudaError_t sort_pairs_u32(unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1, unsigned* hist, int n,
+                           int bits, cudaStream_t st);
+
 // Boxes of triangles v9[sel[i]] (9 floats each).
 void launch_tri_boxes(const float* d_v9, const int* d_sel, int n, float* d_prim, cudaStream_t st);
 
@@ -29,6 +80,33 @@ void launch_tri_boxes(const float* d_v9, const int* d_sel, int n, float* d_prim,
 void launch_place_tris(const float* d_v9, const int* d_sel, const int* d_perm, const int* d_tri_mat,
                        const int* d_tri_obj, int n, int leaf_base, float4* d_tris, float4* d_objv,
                        int* d_slot_of_id, cudaStream_t st);
+
+// Per frame, for at most kSmemRefit + 1 moving triangles, in one CTA: world
+// vertices (fmaf transform), per-object world boxes, an optional rebuild of
+// the tree over the current positions (rebuild != 0), the bottom-up refit in
+// shared memory, and the tree's surface-area cost (sum of node areas over
+// the root area) in uctr->sah_refit (and sah_build after a rebuild).
+struct DynUpdateArgs {
+  const float4* objv_src = nullptr;  // primitive order, object space, object id in v0.w
+  float4* objv = nullptr;            // leaf order
+  const int* sel_d = nullptr;        // primitive -> triangle id
+  const int* tri_mat = nullptr;      // triangle id -> material
+  const float* xf = nullptr;         // nobj x 12
+  float* prim = nullptr;             // scratch: nd x 6 boxes (rebuild)
+  int nd = 0, nobj = 0, node_base = 0, leaf_base = 0, rebuild = 0;
+  float4* tris = nullptr;
+  float4* nodes = nullptr;
+  int* leaf_parent = nullptr;
+  int* perm = nullptr;
+  int* slot_of_id = nullptr;
+  unsigned* obj_box = nullptr;       // lo [0, 3 nobj), hi [3 nobj, 6 nobj) as ordered ints
+  float* root_box = nullptr;
+  int* root = nullptr;
+  DevCounters* uctr = nullptr;
+};
+cudaError_t launch_dyn_update(const DynUpdateArgs& a, cudaStream_t st);
+// Shared memory the one-CTA update needs (must stay within 227 KB).
+size_t dyn_update_smem(int nd, int nobj);
 
 // Per frame: world vertices of the moving triangles, per-object boxes and the
 // bottom-up refit of their tree (d_arrive zeroed by the caller).

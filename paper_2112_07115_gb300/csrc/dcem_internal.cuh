@@ -16,8 +16,7 @@ constexpr int kMaxRefl = DCEM_MAX_REFL;
 constexpr int kStack = 72;              // traversal stack entries (LBVH depth <= 64 per tree)
 constexpr int kEmpty = (int)0x80000000; // empty tree / no node
 constexpr int kSmallBuild = 16384;      // largest tree built by the one-CTA builder
-constexpr int kRxSmem = 4096;           // receivers staged in shared memory per CTA
-constexpr int kMovedSmem = 4096;        // moved-object boxes staged in shared memory
+constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
 
 // device error bits (DevCounters::err)
 enum : unsigned {
@@ -44,7 +43,13 @@ struct DevCounters {
   unsigned int objects_moved;
   unsigned int rx_moved;
   unsigned int n_moved_boxes;
-  unsigned int pad[4];
+  unsigned int work_trace;         // dynamic work counters of the persistent kernels
+  unsigned int work_capture;
+  float sah_refit;                 // moving-object tree cost after the last refit
+  float sah_build;                 // ... right after its last rebuild
+  unsigned int max_seg_nodes;      // most nodes visited by one closest-hit traversal
+  unsigned long long node_visits;  // internal nodes visited by closest-hit traversals
+  unsigned long long tri_tests;    // triangles tested by closest-hit traversals
 };
 
 // Candidate = one reception-sphere capture: ray index and (rx << 4 | segment).
@@ -187,7 +192,8 @@ struct Bvh {
 // t go to the lowest triangle id, so the result does not depend on the tree
 // shape or the traversal order. Returns the leaf slot or -1.
 __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, float tmin, int excl,
-                                           float& t_best, int& id_best, unsigned& overflow) {
+                                           float& t_best, int& id_best, unsigned& overflow,
+                                           unsigned& n_nodes, unsigned& n_tris) {
   int stack[kStack];
   int sp = 0;
   t_best = __int_as_float(0x7f800000);
@@ -206,6 +212,7 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
       continue;
     }
     if (cur >= 0) {
+      ++n_nodes;
       const float4* n = bvh.nodes + 4 * (size_t)cur;
       float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
       float tn0, tn1;
@@ -226,6 +233,7 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
       }
     } else {
       int slot = ~cur;
+      ++n_tris;
       float3 v0, v1, v2;
       int id;
       load_tri(bvh.tris, slot, v0, v1, v2, id);
@@ -304,10 +312,117 @@ __device__ __forceinline__ bool captured(float3 o, float3 d, float D, float tend
   return dist2 <= __fmul_rn(rho, rho);
 }
 
+// ---------------------------------------------------------------------------
+// small per-frame trees: receivers (points) and moved-object boxes
+// ---------------------------------------------------------------------------
+struct SmallBvh {
+  const float4* __restrict__ nodes;  // same node layout as the scene trees
+  const int* __restrict__ perm;      // leaf j -> receiver / box index
+  const int* root;                   // device: root code (kEmpty, leaf ~j, or node)
+  const float* root_box;             // device: box of a single-leaf tree
+  int max_visits;
+};
+
+// Slab test returning the clipped parameter interval [tn, tf] within [0, tcap].
+__device__ __forceinline__ bool slab_io(const RayPre& r, float lox, float hix, float loy, float hiy,
+                                        float loz, float hiz, float tcap, float& tn, float& tf) {
+  float t0x = __fmul_rn(__fsub_rn(lox, r.o.x), r.inv.x), t1x = __fmul_rn(__fsub_rn(hix, r.o.x), r.inv.x);
+  float t0y = __fmul_rn(__fsub_rn(loy, r.o.y), r.inv.y), t1y = __fmul_rn(__fsub_rn(hiy, r.o.y), r.inv.y);
+  float t0z = __fmul_rn(__fsub_rn(loz, r.o.z), r.inv.z), t1z = __fmul_rn(__fsub_rn(hiz, r.o.z), r.inv.z);
+  tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+  tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tcap));
+  return tn <= __fmul_rn(tf, 1.00001f) + 1e-30f;
+}
+
+// Conservative filter for the capture cone of a segment against a box of
+// receivers: false only if no point of the box can pass `captured`. A point
+// captured at parameter s lies within rho(s) = alpha (D + s) of the segment,
+// so the segment meets the box grown by rho(tend); within that clipped
+// interval [tn, tf] the radius is at most rho(tf), so the segment also meets
+// the box grown by rho(tf). Margins (0.1% and 1 cm) exceed FP32 rounding.
+__device__ __forceinline__ bool cone_box(const RayPre& r, float D, float tend, float alpha, float lox,
+                                         float hix, float loy, float hiy, float loz, float hiz) {
+  float a = alpha * 1.001f;
+  float g = a * (D + tend) + 0.01f;
+  float tn, tf;
+  if (!slab_io(r, lox - g, hix + g, loy - g, hiy + g, loz - g, hiz + g, tend, tn, tf)) return false;
+  g = a * (D + fminf(tf * 1.00001f, tend)) + 0.01f;
+  return slab_io(r, lox - g, hix + g, loy - g, hiy + g, loz - g, hiz + g, tend, tn, tf);
+}
+
+// Every receiver whose reception sphere captures the segment (r.o, d, D,
+// tend) is passed to emit(rx index). Returns false on a malformed tree or a
+// stack overflow.
+template <class Emit>
+__device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __restrict__ rx,
+                                             const RayPre& r, float3 d, float D, float tend, float alpha,
+                                             Emit&& emit) {
+  int root = *t.root;
+  if (root == kEmpty) return true;
+  int stack[64];
+  int sp = 0;
+  int cur = root;
+  for (int visits = 0; visits <= t.max_visits; ++visits) {
+    if (cur < 0) {
+      int ri = __ldg(&t.perm[~cur]);
+      float4 v = __ldg(&rx[ri]);
+      if (captured(r.o, d, D, tend, alpha, f3(v.x, v.y, v.z))) emit(ri);
+    } else {
+      const float4* n = t.nodes + 4 * (size_t)cur;
+      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      bool m0 = cone_box(r, D, tend, alpha, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
+      bool m1 = cone_box(r, D, tend, alpha, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
+      if (m1) {
+        if (sp >= 64) return false;
+        stack[sp++] = c1;
+      }
+      if (m0) {
+        if (sp >= 64) return false;
+        stack[sp++] = c0;
+      }
+    }
+    if (sp == 0) return true;
+    cur = stack[--sp];
+  }
+  return false;
+}
+
 // Does the segment o + t d, t in [0, tend], meet the box (conservatively)?
 __device__ __forceinline__ bool seg_box(const RayPre& r, float tend, const float* b) {
   float tn;
   return slab(r, b[0], b[3], b[1], b[4], b[2], b[5], tend, tn);
+}
+
+// Does the segment meet any box of the tree? On a malformed tree or a stack
+// overflow the answer is conservatively true.
+__device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r, float tend) {
+  int root = *t.root;
+  if (root == kEmpty) return false;
+  if (root < 0) return seg_box(r, tend, t.root_box);
+  int stack[64];
+  int sp = 0;
+  int cur = root;
+  for (int visits = 0; visits <= t.max_visits; ++visits) {
+    const float4* n = t.nodes + 4 * (size_t)cur;
+    float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+    int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+    float tn;
+    bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tend, tn);
+    bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tend, tn);
+    if ((h0 && c0 < 0) || (h1 && c1 < 0)) return true;
+    if (h1) {
+      if (sp >= 64) return true;
+      stack[sp++] = c1;
+    }
+    if (h0) {
+      if (sp >= 64) return true;
+      stack[sp++] = c0;
+    }
+    if (sp == 0) return false;
+    cur = stack[--sp];
+  }
+  return true;
 }
 
 // 64-bit path key: (rx, depth, triangle ids) mixed with the SplitMix64 finaliser.

@@ -99,38 +99,60 @@ __device__ __forceinline__ d3 dx(d3 a, d3 b) {
 __device__ __forceinline__ double dn(d3 a) { return sqrt(dd(a, a)); }
 __device__ __forceinline__ d3 du(d3 a) { return a * (1.0 / dn(a)); }
 
-struct cx {
-  double re, im;
+// FP32 complex arithmetic for the reflection coefficients and polarisation
+struct cf {
+  float re, im;
 };
-__device__ __forceinline__ cx C(double r, double i = 0.0) { return cx{r, i}; }
-__device__ __forceinline__ cx operator+(cx a, cx b) { return C(a.re + b.re, a.im + b.im); }
-__device__ __forceinline__ cx operator-(cx a, cx b) { return C(a.re - b.re, a.im - b.im); }
-__device__ __forceinline__ cx operator*(cx a, cx b) {
-  return C(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
-}
-__device__ __forceinline__ cx operator*(cx a, double s) { return C(a.re * s, a.im * s); }
-__device__ __forceinline__ cx cdiv(cx a, cx b) {
-  // Smith's algorithm
-  if (fabs(b.re) >= fabs(b.im)) {
-    double r = b.im / b.re, den = b.re + b.im * r;
-    return C((a.re + a.im * r) / den, (a.im - a.re * r) / den);
+__device__ __forceinline__ cf F(float r, float i = 0.0f) { return cf{r, i}; }
+__device__ __forceinline__ cf operator+(cf a, cf b) { return F(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cf operator-(cf a, cf b) { return F(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cf operator*(cf a, cf b) { return F(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+__device__ __forceinline__ cf operator*(cf a, float s) { return F(a.re * s, a.im * s); }
+__device__ __forceinline__ cf fdiv(cf a, cf b) {  // Smith's algorithm
+  if (fabsf(b.re) >= fabsf(b.im)) {
+    float r = b.im / b.re, den = b.re + b.im * r;
+    return F((a.re + a.im * r) / den, (a.im - a.re * r) / den);
   }
-  double r = b.re / b.im, den = b.re * r + b.im;
-  return C((a.re * r + a.im) / den, (a.im * r - a.re) / den);
+  float r = b.re / b.im, den = b.re * r + b.im;
+  return F((a.re * r + a.im) / den, (a.im * r - a.re) / den);
 }
-// principal square root
-__device__ __forceinline__ cx csqrt_p(cx z) {
-  double m = hypot(z.re, z.im);
-  if (m == 0.0) return C(0.0, 0.0);
-  double a = sqrt(0.5 * (m + fabs(z.re)));
-  if (z.re >= 0.0) return C(a, z.im / (2.0 * a));
-  return C(fabs(z.im) / (2.0 * a), copysign(a, z.im));
+__device__ __forceinline__ cf fsqrt_p(cf z) {  // principal square root
+  float m = hypotf(z.re, z.im);
+  if (m == 0.0f) return F(0.0f, 0.0f);
+  float a = sqrtf(0.5f * (m + fabsf(z.re)));
+  if (z.re >= 0.0f) return F(a, z.im / (2.0f * a));
+  return F(fabsf(z.im) / (2.0f * a), copysignf(a, z.im));
 }
-
-struct cv3 {
-  cx x, y, z;
+struct cf3 {
+  cf x, y, z;
 };
-__device__ __forceinline__ cx cdot(cv3 e, d3 v) { return e.x * v.x + e.y * v.y + e.z * v.z; }
+__device__ __forceinline__ cf fdot(cf3 e, float3 v) { return e.x * v.x + e.y * v.y + e.z * v.z; }
+__device__ __forceinline__ float3 funit(float3 v) {
+  float n = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+  return f3(v.x / n, v.y / n, v.z / n);
+}
+__device__ __forceinline__ float3 fcross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float fdot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 fdir(d3 a, d3 b) {  // unit vector a -> b from FP64 points
+  d3 v = b - a;
+  return funit(f3((float)v.x, (float)v.y, (float)v.z));
+}
+// Polarisation of an isotropic antenna along unit d: u - (u.d) d, normalised.
+__device__ __forceinline__ float3 fpol(float3 u, float3 d, unsigned& flags) {
+  float ud = fdot3(u, d);
+  float3 p = f3(u.x - ud * d.x, u.y - ud * d.y, u.z - ud * d.z);
+  float n = sqrtf(fdot3(p, p));
+  if (n < 1e-6f) {
+    flags |= DCEM_PATH_POL_DEGENERATE;
+    float3 ax = fabsf(d.x) < 0.9f ? f3(1, 0, 0) : f3(0, 1, 0);
+    float ad = fdot3(ax, d);
+    p = f3(ax.x - ad * d.x, ax.y - ad * d.y, ax.z - ad * d.z);
+    n = sqrtf(fdot3(p, p));
+  }
+  return f3(p.x / n, p.y / n, p.z / n);
+}
 
 __device__ __forceinline__ void load_tri_d(const PathArgs& a, int id, d3& v0, d3& v1, d3& v2, int& mat) {
   int slot = a.slot_of_id[id];
@@ -142,26 +164,23 @@ __device__ __forceinline__ void load_tri_d(const PathArgs& a, int id, d3& v0, d3
   mat = __float_as_int(q.w);
 }
 
-// Polarisation of an isotropic antenna along d: u - (u.d) d, normalised.
-__device__ __forceinline__ d3 pol_of(d3 u, d3 d, unsigned& flags) {
-  d3 p = u - d * dd(u, d);
-  double n = dn(p);
-  if (n < 1e-9) {
-    flags |= DCEM_PATH_POL_DEGENERATE;
-    d3 ax = fabs(d.x) < 0.9 ? mk3(1, 0, 0) : mk3(0, 1, 0);
-    p = ax - d * dd(ax, d);
-    n = dn(p);
-  }
-  return p * (1.0 / n);
-}
+// ---------------------------------------------------------------------------
+// validation + field in three kernels:
+//   k_val_geom   one thread per distinct key: image sources, back-trace,
+//                reflection points inside their triangles (FP64)
+//   k_val_occ    one thread per (key, sub-segment): FP32 any-hit occlusion
+//   k_val_field  one thread per distinct key: length, Fresnel, polarisation,
+//                complex amplitude (FP64); valid paths go to their receiver
+// ---------------------------------------------------------------------------
+// Distinct keys are few (thousands): thread t of block b takes keys
+// b + gridDim * t, so that every SM gets a share.
+__device__ __forceinline__ unsigned spread_index(unsigned i) { return blockIdx.x + gridDim.x * i; }
 
-// ---------------------------------------------------------------------------
-// validation + field, one thread per distinct candidate
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_validate(PathArgs a) {
+__global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
   unsigned nu = min(a.ctr->n_unique, a.ucap);
-  unsigned ovf = 0;
-  for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
+  for (unsigned t = threadIdx.x;; t += blockDim.x) {
+    unsigned u = spread_index(t);
+    if (u >= nu) break;
     int ci = a.uniq[u];
     Cand c = a.cand[ci];
     int slot = a.cand_slot[ci];
@@ -176,6 +195,7 @@ __global__ void __launch_bounds__(128) k_validate(PathArgs a) {
     rec.ray = c.ray;
     rec.flags = 0;
     rec.valid = 0;
+    rec.pad = 0;
     rec.len = 0.0;
     rec.amp_re = rec.amp_im = 0.0;
     int ids[kMaxRefl];
@@ -185,22 +205,20 @@ __global__ void __launch_bounds__(128) k_validate(PathArgs a) {
       rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
     }
     float4 rxv = a.rx[rxi];
-    d3 X[kMaxRefl + 2], V0[kMaxRefl], Nn[kMaxRefl];
-    int mats[kMaxRefl];
+    d3 X[kMaxRefl + 2], V0[kMaxRefl], V1[kMaxRefl], V2[kMaxRefl], Nn[kMaxRefl];
     d3 tx = mk3(a.tx.x, a.tx.y, a.tx.z), rx = mk3(rxv.x, rxv.y, rxv.z);
     // step 3: image sources I_1..I_k
     d3 img[kMaxRefl + 1];
     img[0] = tx;
     bool ok = true;
     for (int j = 0; j < k && ok; ++j) {
-      d3 v0, v1, v2;
-      load_tri_d(a, ids[j], v0, v1, v2, mats[j]);
-      d3 n = dx(v1 - v0, v2 - v0);
+      int m;
+      load_tri_d(a, ids[j], V0[j], V1[j], V2[j], m);
+      d3 n = dx(V1[j] - V0[j], V2[j] - V0[j]);
       double nn = dd(n, n);
       if (!(nn > 0.0)) { ok = false; break; }
-      V0[j] = v0;
       Nn[j] = n;
-      img[j + 1] = img[j] - n * (2.0 * dd(img[j] - v0, n) / nn);
+      img[j + 1] = img[j] - n * (2.0 * dd(img[j] - V0[j], n) / nn);
     }
     // step 4: back-trace from the receiver, reflection points in their triangles
     X[0] = tx;
@@ -212,9 +230,7 @@ __global__ void __launch_bounds__(128) k_validate(PathArgs a) {
       double s = dd(V0[j - 1] - X[j + 1], Nn[j - 1]) / den;
       if (!(s > 0.0 && s < 1.0)) { ok = false; break; }
       X[j] = X[j + 1] + dir * s;
-      d3 v0, v1, v2;
-      int m;
-      load_tri_d(a, ids[j - 1], v0, v1, v2, m);
+      d3 v0 = V0[j - 1], v1 = V1[j - 1], v2 = V2[j - 1];
       d3 n = Nn[j - 1];
       if (dd(dx(v1 - v0, X[j] - v0), n) < 0.0 || dd(dx(v2 - v1, X[j] - v1), n) < 0.0 ||
           dd(dx(v0 - v2, X[j] - v2), n) < 0.0)
@@ -225,78 +241,122 @@ __global__ void __launch_bounds__(128) k_validate(PathArgs a) {
       for (int j = 0; j <= k; ++j) L += dn(X[j + 1] - X[j]);
       if (!(L > 0.0)) ok = false;
     }
-    // sub-segment occlusion in FP32 over (eps, 1 - eps)
-    for (int j = 0; j <= k && ok; ++j) {
-      d3 dv = X[j + 1] - X[j];
-      float3 o = f3((float)X[j].x, (float)X[j].y, (float)X[j].z);
-      float3 dvf = f3((float)dv.x, (float)dv.y, (float)dv.z);
-      RayPre rp = ray_pre(o, dvf);
-      int ex0 = j >= 1 ? ids[j - 1] : -1, ex1 = j < k ? ids[j] : -1;
-      if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf)) ok = false;
-    }
+    d3* xs = reinterpret_cast<d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
     if (ok) {
-      // step 6: field with vector polarisation
-      unsigned fl = 0;
-      d3 upol = mk3(a.pol.x, a.pol.y, a.pol.z);
-      d3 e0 = pol_of(upol, du(X[1] - X[0]), fl);
-      cv3 E = {C(e0.x), C(e0.y), C(e0.z)};
-      for (int j = 1; j <= k; ++j) {
-        d3 din = du(X[j] - X[j - 1]), dout = du(X[j + 1] - X[j]);
-        d3 nh = du(Nn[j - 1]);
-        double ct = fabs(dd(din, nh));
-        d3 sv = dx(din, nh);
-        double sn = dn(sv);
-        if (sn < 1e-12) {
-          d3 ax = fabs(nh.x) < 0.9 ? mk3(1, 0, 0) : mk3(0, 1, 0);
-          sv = du(dx(nh, ax));
-        } else {
-          sv = sv * (1.0 / sn);
-        }
-        d3 pin = dx(sv, din), pout = dx(sv, dout);
-        const float4 mt = a.mats[mats[j - 1]];
-        cx gte, gtm;
-        if (mt.z != 0.0f) {
-          gte = C(-1.0);
-          gtm = C(1.0);
-        } else {
-          cx ec = C((double)mt.x, -(double)mt.y / (2.0 * M_PI * a.freq * 8.8541878128e-12));
-          cx root = csqrt_p(ec - C(1.0 - ct * ct));
-          gte = cdiv(C(ct) - root, C(ct) + root);
-          gtm = cdiv(ec * ct - root, ec * ct + root);
-        }
-        cx es = cdot(E, sv), ep = cdot(E, pin);
-        cx ts = gte * es, tp = gtm * ep;
-        E.x = ts * sv.x + tp * pout.x;
-        E.y = ts * sv.y + tp * pout.y;
-        E.z = ts * sv.z + tp * pout.z;
-      }
-      d3 drx = du(X[k + 1] - X[k]);
-      d3 prx = pol_of(upol, drx * -1.0, fl);
-      double lam = 299792458.0 / a.freq;
-      double kw = 2.0 * M_PI * a.freq / 299792458.0;
-      double sn, cs;
-      sincos(kw * L, &sn, &cs);
-      cx amp = cdot(E, prx) * C(cs, -sn) * (lam / (4.0 * M_PI) / L);
-      rec.valid = 1;
-      rec.flags = fl;
+      for (int j = 0; j <= k + 1; ++j) xs[j] = X[j];
       rec.len = L;
-      rec.amp_re = amp.re;
-      rec.amp_im = amp.im;
-      for (int j = 0; j < k; ++j) {
-        rec.pts[j][0] = (float)X[j + 1].x;
-        rec.pts[j][1] = (float)X[j + 1].y;
-        rec.pts[j][2] = (float)X[j + 1].z;
-      }
-      unsigned pos = atomicAdd(&a.bucket_cnt[rxi], 1u);
-      if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)rxi * a.bucket_cap + pos] = (int)u;
-      else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
-      atomicAdd(&a.ctr->n_valid, 1u);
     }
+    a.vstate[u] = ok ? 1 : 0;   // 1 = geometry valid, occlusion pending
     a.prec[u] = rec;
+  }
+}
+
+__global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
+  unsigned nu = min(a.ctr->n_unique, a.ucap);
+  unsigned W = (unsigned)a.N + 1u;
+  unsigned total = nu * W;
+  unsigned ovf = 0;
+  for (unsigned t = threadIdx.x;; t += blockDim.x) {
+    unsigned q = spread_index(t);
+    if (q >= total) break;
+    unsigned u = q / W;
+    int j = (int)(q - u * W);
+    if (a.vstate[u] != 1) continue;
+    int ci = a.uniq[u];
+    Cand c = a.cand[ci];
+    int k = cand_seg(c);
+    if (j > k) continue;
+    const d3* xs = reinterpret_cast<const d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
+    d3 p0 = xs[j], p1 = xs[j + 1];
+    d3 dv = p1 - p0;
+    float3 o = f3((float)p0.x, (float)p0.y, (float)p0.z);
+    float3 dvf = f3((float)dv.x, (float)dv.y, (float)dv.z);
+    RayPre rp = ray_pre(o, dvf);
+    int ex0 = j >= 1 ? a.log_id[(size_t)(j - 1) * a.R + c.ray] : -1;
+    int ex1 = j < k ? a.log_id[(size_t)j * a.R + c.ray] : -1;
+    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf)) a.vstate[u] = 2;  // occluded
   }
   if (ovf) {
     atomicAdd(&a.ctr->stack_overflow, 1u);
     atomicOr(&a.ctr->err, ERR_STACK);
+  }
+}
+
+// Field of a valid path. Length L and the phase k L are FP64 (the phase is
+// reduced modulo 2 pi in FP64 before an FP32 sincos); directions, Fresnel
+// coefficients and polarisation are FP32 (relative amplitude error ~1e-6).
+__global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
+  unsigned nu = min(a.ctr->n_unique, a.ucap);
+  for (unsigned t = threadIdx.x;; t += blockDim.x) {
+    unsigned u = spread_index(t);
+    if (u >= nu) break;
+    if (a.vstate[u] != 1) continue;
+    PathRec& rec = a.prec[u];
+    int k = rec.depth;
+    const d3* X = reinterpret_cast<const d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
+    double L = rec.len;
+    unsigned fl = 0;
+    float3 upol = a.pol;
+    float3 din = fdir(X[0], X[1]);
+    float3 e0 = fpol(upol, din, fl);
+    cf3 E = {F(e0.x), F(e0.y), F(e0.z)};
+    float wfac = (float)(-1.0 / (2.0 * M_PI * a.freq * 8.8541878128e-12));
+    for (int j = 1; j <= k; ++j) {
+      int slot = a.slot_of_id[rec.tri[j - 1]];
+      const float4* tp = a.tris + 3 * (size_t)slot;
+      float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+      float3 nh = funit(fcross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z)));
+      float3 dout = fdir(X[j], X[j + 1]);
+      float ct = fabsf(fdot3(din, nh));
+      float3 sv = fcross(din, nh);
+      float sn = sqrtf(fdot3(sv, sv));
+      if (sn < 1e-6f) {
+        float3 ax = fabsf(nh.x) < 0.9f ? f3(1, 0, 0) : f3(0, 1, 0);
+        sv = funit(fcross(nh, ax));
+      } else {
+        sv = f3(sv.x / sn, sv.y / sn, sv.z / sn);
+      }
+      float3 pin = fcross(sv, din), pout = fcross(sv, dout);
+      const float4 mt = a.mats[__float_as_int(p1.w)];
+      cf gte, gtm;
+      if (mt.z != 0.0f) {
+        gte = F(-1.0f);
+        gtm = F(1.0f);
+      } else {
+        cf ec = F(mt.x, mt.y * wfac);
+        cf root = fsqrt_p(ec - F(1.0f - ct * ct));
+        gte = fdiv(F(ct) - root, F(ct) + root);
+        gtm = fdiv(ec * ct - root, ec * ct + root);
+      }
+      cf es = fdot(E, sv), ep = fdot(E, pin);
+      cf ts = gte * es, tpp = gtm * ep;
+      E.x = ts * sv.x + tpp * pout.x;
+      E.y = ts * sv.y + tpp * pout.y;
+      E.z = ts * sv.z + tpp * pout.z;
+      din = dout;
+    }
+    float3 prx = fpol(upol, f3(-din.x, -din.y, -din.z), fl);
+    double lam = 299792458.0 / a.freq;
+    double ph = fmod(2.0 * M_PI * a.freq / 299792458.0 * L, 2.0 * M_PI);
+    float sn, cs;
+    sincosf((float)ph, &sn, &cs);
+    cf proj = fdot(E, prx);
+    double g = lam / (4.0 * M_PI) / L;
+    double re = (double)(proj.re * cs + proj.im * sn), im = (double)(proj.im * cs - proj.re * sn);
+    rec.valid = 1;
+    rec.flags = fl;
+    rec.amp_re = re * g;
+    rec.amp_im = im * g;
+    for (int j = 0; j < k; ++j) {
+      rec.pts[j][0] = (float)X[j + 1].x;
+      rec.pts[j][1] = (float)X[j + 1].y;
+      rec.pts[j][2] = (float)X[j + 1].z;
+    }
+    int rxi = rec.rx;
+    unsigned pos = atomicAdd(&a.bucket_cnt[rxi], 1u);
+    if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)rxi * a.bucket_cap + pos] = (int)u;
+    else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+    atomicAdd(&a.ctr->n_valid, 1u);
   }
 }
 
@@ -369,7 +429,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
         q.pts[j][2] = p.pts[j][2];
       }
       q.flags = p.flags;
-      q.ray = p.ray;
+      q.ray = a.ray_perm[p.ray];
       q.key = p.key;
       q.len_m = p.len;
       q.delay_s = p.len / 299792458.0;
@@ -389,11 +449,12 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
   }
   if (tid == 0) {
     double fr = red[0][0], fi = red[1][0], pinc = red[2][0];
-    double* o = a.rxout + 4 * (size_t)r;
-    o[0] = fr;
-    o[1] = fi;
-    o[2] = 10.0 * log10(a.tx_power * (fr * fr + fi * fi)) + 30.0;
-    o[3] = 10.0 * log10(a.tx_power * pinc) + 30.0;
+    if (a.out_field) {
+      a.out_field[2 * (size_t)r] = fr;
+      a.out_field[2 * (size_t)r + 1] = fi;
+    }
+    if (a.out_pc) a.out_pc[r] = 10.0 * log10(a.tx_power * (fr * fr + fi * fi)) + 30.0;
+    if (a.out_pi) a.out_pi[r] = 10.0 * log10(a.tx_power * pinc) + 30.0;
   }
 }
 
@@ -407,7 +468,9 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st) {
-  k_validate<<<grid, 128, 0, st>>>(a);
+  k_val_geom<<<grid, 64, 0, st>>>(a);
+  k_val_occ<<<grid, 64, 0, st>>>(a);
+  k_val_field<<<grid, 64, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -17,12 +17,18 @@ struct PathArgs {
   int* uniq;                      // representative candidate per distinct key
   unsigned ucap;
   PathRec* prec;                  // per distinct key
+  const int* ray_perm;            // ray slot -> caller's ray index
+  double* vpts;                   // per distinct key: (kMaxRefl + 2) FP64 path points
+  int* vstate;                    // per distinct key: 0 invalid, 1 valid so far, 2 occluded
+  int N;                          // reflections (sub-segments per path <= N + 1)
   int* bucket;                    // nrx x bucket_cap distinct-key indices of valid paths
   unsigned* bucket_cnt;           // nrx
   int bucket_cap;                 // power of two
-  dcem_path* pout;                // ordered output (rx, key)
+  dcem_path* pout;                // ordered output (rx, key): caller's device buffer or staging
   unsigned pout_cap;
-  double* rxout;                  // nrx x 4: field re, im, P_coh dBm, P_inc dBm
+  double* out_field;              // nrx x 2 (re, im), or null
+  double* out_pc;                 // nrx P_coh dBm, or null
+  double* out_pi;                 // nrx P_inc dBm, or null
   const float4* tris;             // leaf-ordered triangles
   const int* slot_of_id;
   const float4* mats;             // eps_r, sigma, pec

@@ -28,7 +28,7 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_update_transforms", "dcem_trace_frame", "dcem_scene_reset_cache",
             "dcem_scene_set_stream", "dcem_scene_destroy", "dcem_status_string", "dcem_scene_info",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
-            "dcem_scene_get_candidates"]
+            "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold"]
 
 
 class Material(C.Structure):
@@ -55,8 +55,11 @@ class Stats(C.Structure):
                 ("candidates", C.c_int64), ("candidates_reused", C.c_int64),
                 ("unique_candidates", C.c_int64), ("paths_valid", C.c_int64),
                 ("objects_moved", C.c_int64), ("rx_moved", C.c_int64),
+                ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
                 ("stack_overflow", C.c_int32), ("coherent", C.c_int32),
-                ("ms_stage", C.c_float * 8)]
+                ("kernel_launches", C.c_int32), ("bvh_rebuilt", C.c_int32),
+                ("ms_stage", C.c_float * 8), ("bvh_cost_ratio", C.c_float),
+                ("max_segment_nodes", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -103,6 +106,7 @@ def lib():
         L.dcem_scene_get_bvh.argtypes = [vp, vp, vp, vp]
         L.dcem_scene_get_ray_log.argtypes = [vp, vp, vp, vp]
         L.dcem_scene_get_candidates.argtypes = [vp, vp, i64, P(i64)]
+        L.dcem_scene_set_rebuild_threshold.argtypes = [vp, C.c_float]
         for name in EXPORTED:
             if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string"):
                 getattr(L, name).restype = C.c_int
@@ -195,6 +199,10 @@ def dcem_trace_frame(h, tx, rx, params: Params, result: Result) -> int:
     nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
     return lib().dcem_trace_frame(h, txa.ctypes.data, rp, nrx, kind, C.byref(params),
                                   C.byref(result))
+
+
+def dcem_scene_set_rebuild_threshold(h, ratio: float):
+    _check(lib().dcem_scene_set_rebuild_threshold(h, float(ratio)), "dcem_scene_set_rebuild_threshold")
 
 
 def dcem_scene_reset_cache(h):
@@ -321,6 +329,9 @@ class Scene:
 
     def reset_cache(self):
         dcem_scene_reset_cache(self.h)
+
+    def set_rebuild_threshold(self, ratio: float):
+        dcem_scene_set_rebuild_threshold(self.h, ratio)
 
     def world_tris(self):
         return dcem_scene_get_world_tris(self.h, self.ntri)

@@ -50,7 +50,7 @@ def compare_candidates(gpu_cands, ref_tr):
     return g, r
 
 
-def compare_paths(frame, ref, max_refl, len_tol=1e-6, amp_rtol=1e-6):
+def compare_paths(frame, ref, max_refl, len_tol=1e-6, amp_rtol=1e-4):
     """GPU valid paths vs the oracle's validated keys. Keys discovered by an
     unflagged ray and not flagged in validation must agree in validity, and
     valid ones in length and amplitude. Returns a dict of findings."""
