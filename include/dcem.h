@@ -247,6 +247,41 @@ int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t
  * triples are written (DCEM_ERR_CAPACITY if cap < count). */
 int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t* n);
 
+/* ---- received power without device allocation ---- */
+
+/* Per-receiver sum of given path records, with no device allocation. The
+ * paper has no counterpart of this call. It is for callers that cannot
+ * allocate device memory when they need the result: a host framework that
+ * owns the whole device memory pool, or a real-time loop that must not call
+ * cudaMalloc after start-up (an allocation can synchronise the device and
+ * stall the loop). The caller passes the inputs and outputs; the scratch
+ * lives in one fixed device array of the library (about 310 KB per device,
+ * reserved while the library is loaded).
+ *   paths      device, n_paths records (e.g. the paths dcem_trace_frame
+ *              wrote to a device result); order does not matter
+ *   nrx        receivers; every paths[i].rx must lie in [0, nrx)
+ *   tx_power_w transmit power (> 0)
+ *   field      device, nrx x 2 (re, im) of sum a, or NULL
+ *   p_coh_dbm  device, nrx values of P_t |sum a|^2 in dBm, or NULL
+ *   p_inc_dbm  device, nrx values of P_t sum |a|^2 in dBm, or NULL
+ *   stream     cudaStream_t of the work (NULL = legacy default stream)
+ * The sums use the same order as dcem_trace_frame (paths of a receiver
+ * sorted by key), so the results equal those of the frame for the same
+ * records bit for bit.
+ * Limits: n_paths <= 65536, nrx <= 4096, at most 4096 paths per receiver;
+ * beyond them the call returns DCEM_ERR_CAPACITY without touching the GPU
+ * (the per-receiver limit is checked on the device).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call on a device shares the one scratch
+ * array and clears what it needs at its start: calls whose work overlaps on
+ * the GPU (for instance on two streams) race, so order them. The call
+ * synchronises `stream` before returning, to report device-side errors.
+ * Errors: DCEM_ERR_ARG (null or negative arguments, a receiver index out of
+ * range), DCEM_ERR_CAPACITY, DCEM_ERR_CUDA. */
+int dcem_reduce_paths_noalloc(const dcem_path* paths, int32_t n_paths, int32_t nrx, double tx_power_w,
+                              double* field, double* p_coh_dbm, double* p_inc_dbm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

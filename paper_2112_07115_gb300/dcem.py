@@ -28,7 +28,8 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_update_transforms", "dcem_trace_frame", "dcem_scene_reset_cache",
             "dcem_scene_set_stream", "dcem_scene_destroy", "dcem_status_string", "dcem_scene_info",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
-            "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold"]
+            "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
+            "dcem_reduce_paths_noalloc"]
 
 
 class Material(C.Structure):
@@ -107,6 +108,7 @@ def lib():
         L.dcem_scene_get_ray_log.argtypes = [vp, vp, vp, vp]
         L.dcem_scene_get_candidates.argtypes = [vp, vp, i64, P(i64)]
         L.dcem_scene_set_rebuild_threshold.argtypes = [vp, C.c_float]
+        L.dcem_reduce_paths_noalloc.argtypes = [vp, i32, i32, C.c_double, vp, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string"):
                 getattr(L, name).restype = C.c_int
@@ -203,6 +205,14 @@ def dcem_trace_frame(h, tx, rx, params: Params, result: Result) -> int:
 
 def dcem_scene_set_rebuild_threshold(h, ratio: float):
     _check(lib().dcem_scene_set_rebuild_threshold(h, float(ratio)), "dcem_scene_set_rebuild_threshold")
+
+
+def dcem_reduce_paths_noalloc(paths_ptr, n_paths, nrx, tx_power_w, field_ptr, p_coh_ptr, p_inc_ptr,
+                              stream=None) -> int:
+    """Per-receiver sums of device path records without device allocation
+    (device pointers as ints); returns the status."""
+    return lib().dcem_reduce_paths_noalloc(paths_ptr, int(n_paths), int(nrx), float(tx_power_w), field_ptr,
+                                           p_coh_ptr, p_inc_ptr, stream)
 
 
 def dcem_scene_reset_cache(h):
