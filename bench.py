@@ -155,6 +155,18 @@ def ncu_traffic(kernel: str):
     return e
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of per-rank timings over the process group (the
+    values themselves when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 # ---------------------------------------------------------------- ours
 def run_ours(args):
     import ctypes as C
@@ -228,11 +240,9 @@ def run_ours(args):
     s_full, ms_full, st_full = run(dcem.MODE_FULL, frames, True)
     t_coh = sum(ms_coh) / 1e3
     t_full = sum(ms_full) / 1e3
+    t_coh, t_full = max_over_ranks([t_coh, t_full], dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([t_coh, t_full], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_coh, t_full = float(t[0]), float(t[1])
         dist.barrier()
     fps_coh = world * K / t_coh
     fps_full = world * K / t_full
@@ -399,11 +409,7 @@ def run_e2e(args, sc, rays, stream, W, K, world, dev):
             h2d += sc.nobj * 48 + nrx * 12
             d2h += nrx * 32 + res.n_paths * dcem.PATH_DTYPE.itemsize + 2 * 96
     s.close()
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt[0])
+    t = max_over_ranks([t], dev)[0]
     return {"value": round(world * K / t, 2), "unit": "frames/s", "h2d_bytes_per_step": int(h2d / K),
             "d2h_bytes_per_step": int(d2h / K),
             "note": "C-ABI calls with pinned host transforms/receivers and host outputs; wall clock"}
