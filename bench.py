@@ -254,7 +254,7 @@ def run_ours(args):
     stage_names = dcem.STAGES
     mean_stage = {n: float(np.mean([x["ms_stage"][n] for x in st_coh])) for n in stage_names}
     mean_stage_full = {n: float(np.mean([x["ms_stage"][n] for x in st_full])) for n in stage_names}
-    dom = max(["mark", "trace", "dedupe", "validate", "reduce"], key=lambda n: mean_stage[n])
+    dom = max(["mark", "trace", "capture", "dedupe", "validate", "reduce"], key=lambda n: mean_stage[n])
     R = sc.n_rays
     peak, peak_kind = measured_peaks()
 
@@ -266,7 +266,13 @@ def run_ours(args):
         examined = x["segments_reused"] + x["rays_retraced"]
         return R * 8 + examined * 32 + x["rays_retraced"] * 4
 
-    kern = {"trace": ("k_trace", bytes_trace), "mark": ("k_mark", bytes_mark)}
+    def bytes_capture(x):
+        # log entry (origin, D, direction, t) and segment count per tested
+        # segment, 8 B per emitted candidate
+        return x["segments_traced"] * 36 + (x["candidates"] - x["candidates_reused"]) * 8
+
+    tname = "k_trace_q" if st_coh[-1]["trace_kernel"] == 1 else "k_trace"
+    kern = {"trace": (tname, bytes_trace), "mark": ("k_mark", bytes_mark), "capture": ("k_capture", bytes_capture)}
     roof = None
     if dom in kern:
         kname, fb = kern[dom]
@@ -280,7 +286,7 @@ def run_ours(args):
                 "traffic_note": (tr or {}).get("note", "no ncu capture on the current source")}
     # full-retrace traversal roofline (context)
     bf = float(np.mean([bytes_trace(x) for x in st_full]))
-    roof_full_trace = {"kernel": "k_trace", "achieved": round(bf / (mean_stage_full["trace"] * 1e-3) / 1e9, 1),
+    roof_full_trace = {"kernel": tname, "achieved": round(bf / (mean_stage_full["trace"] * 1e-3) / 1e9, 1),
                        "unit": "GB/s", "frac": None}
     roof_full_trace["frac"] = round(roof_full_trace["achieved"] / peak, 4)
     seg_mean = float(np.mean([x["segments_traced"] for x in st_full]))

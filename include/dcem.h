@@ -129,11 +129,15 @@ typedef struct {
                                   transform updates since the previous frame    */
   int32_t bvh_rebuilt;         /* 1 if the moving-object tree was rebuilt since
                                   the previous frame                             */
-  float ms_stage[8];           /* if params.timing: prep, mark, trace, dedupe,
-                                  validate, reduce, copy-out, total              */
+  float ms_stage[10];          /* if params.timing: prep, mark, trace, capture,
+                                  dedupe, validate, reduce, copy-out, total,
+                                  (unused)                                       */
   float bvh_cost_ratio;        /* surface-area cost of the moving-object tree
                                   over its cost right after the last rebuild     */
   int32_t max_segment_nodes;   /* most BVH nodes visited by one traversal        */
+  int32_t trace_kernel;        /* closest-hit kernel of this frame: 0 = nodes
+                                  read from global memory, 1 = compact node
+                                  copy in shared memory                          */
 } dcem_stats;
 
 typedef struct {

@@ -142,6 +142,8 @@ struct dcem_scene {
   int* tri_mat_d = nullptr;
   float* v9d = nullptr;         // world vertices of moving primitives (rebuilds)
   float4* nodes = nullptr;
+  uint4* qnodes = nullptr;       // compact node copy for shared-memory traversal
+  float* qframe = nullptr;
   int* leaf_parent = nullptr;
   int* arrive = nullptr;
   int* roots = nullptr;
@@ -217,8 +219,9 @@ struct dcem_scene {
   float ctx[3] = {0, 0, 0};
   int cnrx = -1;
   unsigned last_ncand = 0;
-  cudaEvent_t ev[9] = {};
+  cudaEvent_t ev[10] = {};
   int launches = 0;  // kernels launched since the last completed frame
+  int last_use_q = 0;  // closest-hit kernel of the last frame (1: shared-memory node copy)
 };
 
 namespace {
@@ -227,7 +230,7 @@ void scene_free(dcem_scene* s) {
   if (!s) return;
   cudaStreamSynchronize(s->st);
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
-  dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->leaf_parent); dfree(s->arrive);
+  dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
   dfree(s->xf_cur); dfree(s->xf_traced); dfree(s->obj_box_cur); dfree(s->obj_box_traced);
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
@@ -494,6 +497,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->tri_mat_d, ntri));
   CKF(dalloc(&s->v9d, 9 * (size_t)s->nd));
   CKF(dalloc(&s->nodes, 4 * (size_t)(s->nint_s + s->nint_d)));
+  CKF(dalloc(&s->qnodes, 2 * (size_t)(s->nint_s + s->nint_d)));
+  CKF(dalloc(&s->qframe, 6));
   CKF(dalloc(&s->leaf_parent, ntri));
   CKF(dalloc(&s->arrive, nmax));
   CKF(dalloc(&s->roots, 2));
@@ -704,7 +709,8 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   if (tm) CK(cudaEventRecord(s->ev[0], st));
   CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce
-  s->launches += 1 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0);
+  s->launches += 1 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) +
+                 ((s->nint_s + s->nint_d) > 0 && 220L * 1024 - (long)(s->nint_s + s->nint_d) * 32 >= 12L * 4096 ? 1 : 0);
 
   TraceArgs a;
   a.bvh.nodes = s->nodes;
@@ -737,6 +743,22 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.rxt.root = s->rxt_root;
   a.rxt.root_box = s->rxt_root_box;
   a.rxt.max_visits = 2 * nrx + 8;
+  a.qnodes = s->qnodes;
+  a.qframe = s->qframe;
+  a.n_nodes = s->nint_s + s->nint_d;
+  // the compact copy of both trees and 1024 threads' stacks fit in shared
+  // memory: traverse it there
+  {
+    long avail = 220L * 1024 - (long)a.n_nodes * 32;
+    a.stack_cap = (int)std::min<long>(kStackTrace, avail > 0 ? avail / (1024 * (long)sizeof(int)) : 0);
+    a.use_q = (a.n_nodes > 0 && a.stack_cap >= 12) ? 1 : 0;
+    s->last_use_q = a.use_q;
+  }
+  if (a.use_q) {
+    launch_quantize(s->nodes, a.n_nodes, s->root_box, s->root_h[0] != kEmpty, s->root_h[1] != kEmpty, s->qnodes,
+                    s->qframe, st);
+    CK(cudaGetLastError());
+  }
   FramePrepArgs fp;
   fp.rx3 = s->rx3;
   fp.nrx = nrx;
@@ -795,6 +817,8 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   if (tm) CK(cudaEventRecord(s->ev[2], st));
   if (s->R > 0) CK(launch_trace(a, s->sms, st));
   if (tm) CK(cudaEventRecord(s->ev[3], st));
+  if (s->R > 0) CK(launch_capture(a, s->sms, st));
+  if (tm) CK(cudaEventRecord(s->ev[4], st));
 
   PathArgs q;
   q.R = s->R;
@@ -840,11 +864,11 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
   CK(launch_dedupe(q, grid_cap_of(s, 4), st));
-  if (tm) CK(cudaEventRecord(s->ev[4], st));
-  CK(launch_validate(q, grid_cap_of(s, 4), st));
   if (tm) CK(cudaEventRecord(s->ev[5], st));
-  CK(launch_reduce(q, nrx, st));
+  CK(launch_validate(q, grid_cap_of(s, 4), st));
   if (tm) CK(cudaEventRecord(s->ev[6], st));
+  CK(launch_reduce(q, nrx, st));
+  if (tm) CK(cudaEventRecord(s->ev[7], st));
   // state the next frame compares against
   CK(cudaMemcpyAsync(s->prev_ncand, &s->ctr->n_cand, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
   if (nrx) CK(cudaMemcpyAsync(s->rx_traced, s->rx_cur, sizeof(float4) * nrx, cudaMemcpyDeviceToDevice, st));
@@ -947,6 +971,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   S.rx_moved = c[0].rx_moved;
   S.node_visits = (int64_t)c[0].node_visits;
   S.max_segment_nodes = (int32_t)c[0].max_seg_nodes;
+  S.trace_kernel = s->last_use_q;
   S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;
@@ -982,11 +1007,11 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
     int ncopy = std::min(nvalid, out->max_paths);
     if (ncopy > 0 && out->paths) CK(cudaMemcpyAsync(out->paths, s->pout, sizeof(dcem_path) * ncopy, k, st));
   }
-  if (tm) CK(cudaEventRecord(s->ev[7], st));
+  if (tm) CK(cudaEventRecord(s->ev[8], st));
   CK(cudaStreamSynchronize(st));
   if (tm) {
-    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&S.ms_stage[i], s->ev[i], s->ev[i + 1]);
-    cudaEventElapsedTime(&S.ms_stage[7], s->ev[0], s->ev[7]);
+    for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&S.ms_stage[i], s->ev[i], s->ev[i + 1]);
+    cudaEventElapsedTime(&S.ms_stage[8], s->ev[0], s->ev[8]);
   }
   out->n_paths = nvalid;
   s->cache_valid = true;

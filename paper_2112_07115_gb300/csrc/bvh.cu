@@ -710,6 +710,62 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// compact copy of both trees for shared-memory traversal (QFrame layout in
+// dcem_internal.cuh). The frame is the union of the two root boxes padded by
+// 1 m + 0.1%; every child box is rounded outward by one 16-bit step.
+// ---------------------------------------------------------------------------
+// Codes are rounded outward by two steps: the FP32 quotient (v - o) / s is
+// within a small fraction of a step of the exact one, so the decoded box
+// still contains the exact box by more than a step.
+__device__ __forceinline__ unsigned qenc_lo(float v, float o, float s) {
+  if (!isfinite(v)) return 0u;
+  float d = floorf((v - o) / s) - 2.0f;
+  if (!(d >= 1.0f)) return 0u;
+  return d > 65534.0f ? 65534u : (unsigned)d;
+}
+__device__ __forceinline__ unsigned qenc_hi(float v, float o, float s) {
+  if (!isfinite(v)) return 65535u;
+  float d = ceilf((v - o) / s) + 2.0f;
+  if (!(d <= 65534.0f)) return 65535u;
+  return d < 1.0f ? 1u : (unsigned)d;
+}
+
+__global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float* __restrict__ root_box,
+                           int has0, int has1, uint4* qn, float* qframe) {
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  for (int t = 0; t < 2; ++t) {
+    if (!(t == 0 ? has0 : has1)) continue;
+    for (int k = 0; k < 3; ++k) {
+      float a = root_box[6 * t + k], b = root_box[6 * t + 3 + k];
+      if (isfinite(a)) lo[k] = fminf(lo[k], a);
+      if (isfinite(b)) hi[k] = fmaxf(hi[k], b);
+    }
+  }
+  float o[3], sc[3];
+  for (int k = 0; k < 3; ++k) {
+    if (!(hi[k] >= lo[k])) { lo[k] = 0.0f; hi[k] = 0.0f; }
+    float pad = 1.0f + 1e-3f * (hi[k] - lo[k]);
+    o[k] = lo[k] - pad;
+    sc[k] = fmaxf((hi[k] + pad - o[k]) / 65000.0f, 1e-6f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) { qframe[k] = o[k]; qframe[3 + k] = sc[k]; }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    float4 n0 = nodes[4 * (size_t)i], n1 = nodes[4 * (size_t)i + 1], n2 = nodes[4 * (size_t)i + 2],
+           n3 = nodes[4 * (size_t)i + 3];
+    // child 0: lo (n0.x, n0.z, n2.x), hi (n0.y, n0.w, n2.y); child 1 likewise
+    unsigned c[12] = {qenc_lo(n0.x, o[0], sc[0]), qenc_lo(n0.z, o[1], sc[1]), qenc_lo(n2.x, o[2], sc[2]),
+                      qenc_hi(n0.y, o[0], sc[0]), qenc_hi(n0.w, o[1], sc[1]), qenc_hi(n2.y, o[2], sc[2]),
+                      qenc_lo(n1.x, o[0], sc[0]), qenc_lo(n1.z, o[1], sc[1]), qenc_lo(n2.z, o[2], sc[2]),
+                      qenc_hi(n1.y, o[0], sc[0]), qenc_hi(n1.w, o[1], sc[1]), qenc_hi(n2.w, o[2], sc[2])};
+    qn[2 * (size_t)i] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16),
+                                   c[6] | (c[7] << 16));
+    qn[2 * (size_t)i + 1] = make_uint4(c[8] | (c[9] << 16), c[10] | (c[11] << 16), __float_as_uint(n3.x),
+                                       __float_as_uint(n3.y));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static inline int nblk(long n, int bs, int cap = 4096) {
@@ -815,6 +871,14 @@ void launch_place_tris(const float* d_v9, const int* d_sel, const int* d_perm, c
   if (n > 0)
     k_place_tris<<<nblk(n, 256), 256, 0, st>>>(d_v9, d_sel, d_perm, d_tri_mat, d_tri_obj, n, leaf_base,
                                                d_tris, d_objv, d_slot_of_id);
+}
+
+void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int has0, int has1, uint4* d_qn,
+                     float* d_qframe, cudaStream_t st) {
+  int g = (nn + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 1024) g = 1024;
+  k_quantize<<<g, 256, 0, st>>>(d_nodes, nn, d_root_box, has0, has1, d_qn, d_qframe);
 }
 
 size_t dyn_update_smem(int nd, int nobj) {

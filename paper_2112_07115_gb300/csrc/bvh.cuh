@@ -108,6 +108,11 @@ cudaError_t launch_dyn_update(const DynUpdateArgs& a, cudaStream_t st);
 // Shared memory the one-CTA update needs (must stay within 227 KB).
 size_t dyn_update_smem(int nd, int nobj);
 
+// Compact copy of the nn nodes of both trees (2 uint4 per node) and its
+// frame (origin.xyz, step.xyz), from the current node boxes and root boxes.
+void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int has0, int has1, uint4* d_qn,
+                     float* d_qframe, cudaStream_t st);
+
 // Per frame: world vertices of the moving triangles, per-object boxes and the
 // bottom-up refit of their tree (d_arrive zeroed by the caller).
 void launch_transform_refit(const float4* d_objv, const float* d_xf, int n, int nobj, int node_base,

@@ -13,7 +13,8 @@
 namespace dcem {
 
 constexpr int kMaxRefl = DCEM_MAX_REFL;
-constexpr int kStack = 72;              // traversal stack entries (LBVH depth <= 64 per tree)
+constexpr int kStackTrace = 24;         // shared-memory stack entries per thread (scene traversal)
+constexpr int kStackSmall = 16;         // ... (per-frame receiver / moved-box trees)
 constexpr int kEmpty = (int)0x80000000; // empty tree / no node
 constexpr int kSmallBuild = 16384;      // largest tree built by the one-CTA builder
 constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
@@ -99,6 +100,41 @@ __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (
 //   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   n3 = (child0, child1, parent, -) as int bits; child < 0 is leaf slot ~c
 // ---------------------------------------------------------------------------
+
+// Traversal stack: the first `cap` entries of each thread live in shared
+// memory (entry k of thread t at s[k * blockDim.x + t]: consecutive threads,
+// consecutive banks), deeper entries in a small local-memory spill area that
+// only deep traversals touch. Local-memory stacks of 1024 threads per SM do
+// not fit the L1 cache and turn every push and pop into an L2 access.
+constexpr int kSpill = 48;
+struct TStack {
+  int* s;
+  int stride;
+  int cap;
+  int sp;
+  int spill[kSpill];
+  __device__ __forceinline__ void reset() { sp = 0; }
+  __device__ __forceinline__ bool empty() const { return sp == 0; }
+  __device__ __forceinline__ bool push(int v) {
+    if (sp < cap) s[sp * stride] = v;
+    else if (sp - cap < kSpill) spill[sp - cap] = v;
+    else return false;
+    ++sp;
+    return true;
+  }
+  __device__ __forceinline__ int pop() {
+    --sp;
+    return sp < cap ? s[sp * stride] : spill[sp - cap];
+  }
+};
+
+// This thread's stack over `cap` shared entries per thread at `smem`.
+__device__ __forceinline__ void bind_stack(TStack& t, int* smem, int cap) {
+  t.s = smem + threadIdx.x;
+  t.stride = blockDim.x;
+  t.cap = cap;
+  t.sp = 0;
+}
 
 struct RayPre {
   float3 o;
@@ -193,13 +229,12 @@ struct Bvh {
 // shape or the traversal order. Returns the leaf slot or -1.
 __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, float tmin, int excl,
                                            float& t_best, int& id_best, unsigned& overflow,
-                                           unsigned& n_nodes, unsigned& n_tris) {
-  int stack[kStack];
-  int sp = 0;
+                                           unsigned& n_nodes, unsigned& n_tris, TStack& st) {
+  st.reset();
   t_best = __int_as_float(0x7f800000);
   id_best = 0x7fffffff;
   int slot_best = -1;
-  if (bvh.root1 != kEmpty) stack[sp++] = bvh.root1;
+  if (bvh.root1 != kEmpty) st.push(bvh.root1);
   int cur = bvh.root0;
   for (int visits = 0;; ++visits) {
     if (visits > bvh.max_visits) {  // malformed tree: stop and report
@@ -207,8 +242,8 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
       break;
     }
     if (cur == kEmpty) {
-      if (sp == 0) break;
-      cur = stack[--sp];
+      if (st.empty()) break;
+      cur = st.pop();
       continue;
     }
     if (cur >= 0) {
@@ -221,8 +256,88 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
         int nearc = tn0 <= tn1 ? c0 : c1, farc = tn0 <= tn1 ? c1 : c0;
-        if (sp < kStack) stack[sp++] = farc;
-        else overflow = 1u;
+        if (!st.push(farc)) overflow = 1u;
+        cur = nearc;
+      } else if (h0) {
+        cur = c0;
+      } else if (h1) {
+        cur = c1;
+      } else {
+        cur = kEmpty;
+      }
+    } else {
+      int slot = ~cur;
+      ++n_tris;
+      float3 v0, v1, v2;
+      int id;
+      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      float t;
+      if (id != excl && tri_hit(r, v0, v1, v2, t) && t > tmin) {
+        if (t < t_best || (t == t_best && id < id_best)) {
+          t_best = t;
+          id_best = id;
+          slot_best = slot;
+        }
+      }
+      cur = kEmpty;
+    }
+  }
+  return slot_best;
+}
+
+// ---------------------------------------------------------------------------
+// compact nodes for shared memory: child boxes as 16-bit codes in a per-frame
+// scene frame (origin O, step S per axis), rounded outward by one step, so a
+// decoded box always contains the exact one; code 0 (lo) and 65535 (hi) mean
+// unbounded. 32 bytes per node:
+//   q[0..5] = child 0 (lo.xyz, hi.xyz), q[6..11] = child 1, then child codes.
+// ---------------------------------------------------------------------------
+struct QFrame {
+  float ox, oy, oz, sx, sy, sz;
+};
+
+__device__ __forceinline__ float qlo(unsigned q, float o, float s) {
+  return q == 0u ? __int_as_float(0xff800000) : __fmaf_rn((float)q, s, o);
+}
+__device__ __forceinline__ float qhi(unsigned q, float o, float s) {
+  return q == 65535u ? __int_as_float(0x7f800000) : __fmaf_rn((float)q, s, o);
+}
+
+// Closest hit as closest_hit(), with the nodes read from a compact copy
+// (shared memory). Same triangle test and tie rule, so the same result.
+__device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, const Bvh& bvh, const RayPre& r,
+                                             float tmin, int excl, float& t_best, int& id_best, unsigned& overflow,
+                                             unsigned& n_nodes, unsigned& n_tris, TStack& st) {
+  st.reset();
+  t_best = __int_as_float(0x7f800000);
+  id_best = 0x7fffffff;
+  int slot_best = -1;
+  if (bvh.root1 != kEmpty) st.push(bvh.root1);
+  int cur = bvh.root0;
+  for (int visits = 0;; ++visits) {
+    if (visits > bvh.max_visits) {
+      overflow = 1u;
+      break;
+    }
+    if (cur == kEmpty) {
+      if (st.empty()) break;
+      cur = st.pop();
+      continue;
+    }
+    if (cur >= 0) {
+      ++n_nodes;
+      uint4 a = qn[2 * cur], b = qn[2 * cur + 1];
+      float tn0, tn1;
+      bool h0 = slab(r, qlo(a.x & 0xffffu, f.ox, f.sx), qhi(a.y >> 16, f.ox, f.sx), qlo(a.x >> 16, f.oy, f.sy),
+                     qhi(a.z & 0xffffu, f.oy, f.sy), qlo(a.y & 0xffffu, f.oz, f.sz), qhi(a.z >> 16, f.oz, f.sz),
+                     t_best, tn0);
+      bool h1 = slab(r, qlo(a.w & 0xffffu, f.ox, f.sx), qhi(b.x >> 16, f.ox, f.sx), qlo(a.w >> 16, f.oy, f.sy),
+                     qhi(b.y & 0xffffu, f.oy, f.sy), qlo(b.x & 0xffffu, f.oz, f.sz), qhi(b.y >> 16, f.oz, f.sz),
+                     t_best, tn1);
+      int c0 = (int)b.z, c1 = (int)b.w;
+      if (h0 && h1) {
+        int nearc = tn0 <= tn1 ? c0 : c1, farc = tn0 <= tn1 ? c1 : c0;
+        if (!st.push(farc)) overflow = 1u;
         cur = nearc;
       } else if (h0) {
         cur = c0;
@@ -253,10 +368,9 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
 
 // Any hit with t in (t0, t1), excluding ids ex0 and ex1 (occlusion test).
 __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t0, float t1,
-                                        int ex0, int ex1, unsigned& overflow) {
-  int stack[kStack];
-  int sp = 0;
-  if (bvh.root1 != kEmpty) stack[sp++] = bvh.root1;
+                                        int ex0, int ex1, unsigned& overflow, TStack& st) {
+  st.reset();
+  if (bvh.root1 != kEmpty) st.push(bvh.root1);
   int cur = bvh.root0;
   for (int visits = 0;; ++visits) {
     if (visits > bvh.max_visits) {
@@ -264,8 +378,8 @@ __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t
       break;
     }
     if (cur == kEmpty) {
-      if (sp == 0) break;
-      cur = stack[--sp];
+      if (st.empty()) break;
+      cur = st.pop();
       continue;
     }
     if (cur >= 0) {
@@ -276,8 +390,7 @@ __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t
       bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, t1, tn1);
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       if (h0 && h1) {
-        if (sp < kStack) stack[sp++] = c1;
-        else overflow = 1u;
+        if (!st.push(c1)) overflow = 1u;
         cur = c0;
       } else if (h0) {
         cur = c0;
@@ -356,11 +469,10 @@ __device__ __forceinline__ bool cone_box(const RayPre& r, float D, float tend, f
 template <class Emit>
 __device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __restrict__ rx,
                                              const RayPre& r, float3 d, float D, float tend, float alpha,
-                                             Emit&& emit) {
+                                             TStack& st, Emit&& emit) {
   int root = *t.root;
   if (root == kEmpty) return true;
-  int stack[64];
-  int sp = 0;
+  st.reset();
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
     if (cur < 0) {
@@ -373,17 +485,11 @@ __device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       bool m0 = cone_box(r, D, tend, alpha, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
       bool m1 = cone_box(r, D, tend, alpha, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
-      if (m1) {
-        if (sp >= 64) return false;
-        stack[sp++] = c1;
-      }
-      if (m0) {
-        if (sp >= 64) return false;
-        stack[sp++] = c0;
-      }
+      if (m1 && !st.push(c1)) return false;
+      if (m0 && !st.push(c0)) return false;
     }
-    if (sp == 0) return true;
-    cur = stack[--sp];
+    if (st.empty()) return true;
+    cur = st.pop();
   }
   return false;
 }
@@ -396,12 +502,11 @@ __device__ __forceinline__ bool seg_box(const RayPre& r, float tend, const float
 
 // Does the segment meet any box of the tree? On a malformed tree or a stack
 // overflow the answer is conservatively true.
-__device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r, float tend) {
+__device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r, float tend, TStack& st) {
   int root = *t.root;
   if (root == kEmpty) return false;
   if (root < 0) return seg_box(r, tend, t.root_box);
-  int stack[64];
-  int sp = 0;
+  st.reset();
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
     const float4* n = t.nodes + 4 * (size_t)cur;
@@ -411,16 +516,10 @@ __device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r
     bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tend, tn);
     bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, tend, tn);
     if ((h0 && c0 < 0) || (h1 && c1 < 0)) return true;
-    if (h1) {
-      if (sp >= 64) return true;
-      stack[sp++] = c1;
-    }
-    if (h0) {
-      if (sp >= 64) return true;
-      stack[sp++] = c0;
-    }
-    if (sp == 0) return false;
-    cur = stack[--sp];
+    if (h1 && !st.push(c1)) return true;
+    if (h0 && !st.push(c0)) return true;
+    if (st.empty()) return false;
+    cur = st.pop();
   }
   return true;
 }

@@ -252,6 +252,9 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
 }
 
 __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackTrace);
   unsigned nu = min(a.ctr->n_unique, a.ucap);
   unsigned W = (unsigned)a.N + 1u;
   unsigned total = nu * W;
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
     RayPre rp = ray_pre(o, dvf);
     int ex0 = j >= 1 ? a.log_id[(size_t)(j - 1) * a.R + c.ray] : -1;
     int ex1 = j < k ? a.log_id[(size_t)j * a.R + c.ray] : -1;
-    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf)) a.vstate[u] = 2;  // occluded
+    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st)) a.vstate[u] = 2;  // occluded
   }
   if (ovf) {
     atomicAdd(&a.ctr->stack_overflow, 1u);
@@ -469,7 +472,7 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
 
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st) {
   k_val_geom<<<grid, 64, 0, st>>>(a);
-  k_val_occ<<<grid, 64, 0, st>>>(a);
+  k_val_occ<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a);
   k_val_field<<<grid, 64, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -39,7 +39,8 @@ __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
 // the expensive grazing rays from piling up on a few SMs). Per ray, segment
 // b from its restart point (0 in a full frame) to N: closest hit, segment
 // log, specular reflection. Captures are tested by k_capture.
-__global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
+template <bool kQ>
+__device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st) {
   const int R = a.R;
   const int nq = a.queue ? (int)min(*a.nq_dev, (unsigned)R) : R;
   unsigned long long segs = 0, nodes = 0, tris = 0;
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
         float t;
         int id;
         unsigned nn = 0, nt = 0;
-        int slot = closest_hit(a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt);
+        int slot = kQ ? closest_hit_q(qn, qf, a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st)
+                      : closest_hit(a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st);
         ++segs;
         nodes += nn;
         tris += nt;
@@ -118,12 +120,41 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackTrace);
+  QFrame f{};
+  trace_rays<false>(a, nullptr, f, st);
+}
+
+// Same traversal with the compact node copy staged in shared memory (one
+// 1024-thread CTA per SM, the whole copy loaded once per CTA).
+__global__ void __launch_bounds__(1024, 1) k_trace_q(TraceArgs a) {
+  extern __shared__ uint4 sq[];
+  TStack st;
+  bind_stack(st, reinterpret_cast<int*>(sq + 2 * a.n_nodes), a.stack_cap);
+  for (int i = threadIdx.x; i < 2 * a.n_nodes; i += blockDim.x) sq[i] = a.qnodes[i];
+  QFrame f;
+  f.ox = a.qframe[0];
+  f.oy = a.qframe[1];
+  f.oz = a.qframe[2];
+  f.sx = a.qframe[3];
+  f.sy = a.qframe[4];
+  f.sz = a.qframe[5];
+  __syncthreads();
+  trace_rays<true>(a, sq, f, st);
+}
+
 // Reception-sphere captures of traced segments, one work item per (ray,
 // segment), segment-major so that a warp reads consecutive log entries.
 // Full frame: every segment of every ray. Coherent frame: the segments of
 // the retraced rays from their restart point on (reused segments were tested
 // against the moved receivers in k_mark).
 __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackSmall);
   const SmallBvh& rxt = a.rxt;
   const float4* rx = a.rx;
   const int R = a.R;
@@ -150,7 +181,7 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
         float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
         float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
         rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-        if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, [&](int r) { emit_cand(a, ray, b, r); }))
+        if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) { emit_cand(a, ray, b, r); }))
           ovf = 1u;
       }
     }
@@ -169,6 +200,9 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
 // restart point; earlier segments are reused and re-tested against the
 // receivers that moved.
 __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackSmall);
   const SmallBvh& rxt = a.rxt;
   const float4* rx = a.rx;
   const SmallBvh& mvt = c.mvt;
@@ -191,13 +225,13 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
       float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
       float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
       rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-      if (seg_hits_tree(mvt, rp, t)) {
+      if (seg_hits_tree(mvt, rp, t, st)) {
         bstar = b;
         break;
       }
       if (any_rx) {
         float tend = isinf(t) ? a.escape : t;
-        if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, [&](int r) {
+        if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) {
               if (c.rx_moved[r]) emit_cand(a, ray, b, r);
             }))
           ovf = 1u;
@@ -246,26 +280,41 @@ static int grid_for(long n, int bs, int max_blocks) {
 }
 
 // Persistent launches: as many 256-thread blocks as fit on the GPU at once.
-static int resident_blocks(const void* fn, int sms) {
+static int resident_blocks(const void* fn, int sms, size_t smem) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess || nb < 1) nb = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, smem) != cudaSuccess || nb < 1) nb = 1;
   return nb * sms;
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
-  static int g_trace = 0, g_cap = 0;
-  if (!g_trace) {
-    g_trace = resident_blocks((const void*)k_trace, sms);
-    g_cap = resident_blocks((const void*)k_capture, sms);
-  }
+  static int g_trace = 0;
+  if (!g_trace) g_trace = resident_blocks((const void*)k_trace, sms, 256 * kStackTrace * sizeof(int));
   long n = a.R;
-  k_trace<<<grid_for(n, 256, g_trace), 256, 0, st>>>(a);
-  k_capture<<<grid_for(n * (a.N + 1), 256, g_cap), 256, 0, st>>>(a);
+  if (a.use_q) {
+    size_t smem = (size_t)a.n_nodes * 2 * sizeof(uint4) + (size_t)1024 * a.stack_cap * sizeof(int);
+    static size_t attr = 0;
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_trace_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
+    k_trace_q<<<grid_for(n, 1024, sms), 1024, smem, st>>>(a);
+  } else {
+    k_trace<<<grid_for(n, 256, g_trace), 256, 256 * kStackTrace * sizeof(int), st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st) {
+  static int g_cap = 0;
+  if (!g_cap) g_cap = resident_blocks((const void*)k_capture, sms, 256 * kStackSmall * sizeof(int));
+  long n = a.R;
+  k_capture<<<grid_for(n * (a.N + 1), 256, g_cap), 256, 256 * kStackSmall * sizeof(int), st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st) {
-  k_mark<<<grid_for(a.R, 256, grid_cap), 256, 0, st>>>(a, c);
+  k_mark<<<grid_for(a.R, 256, grid_cap), 256, 256 * kStackSmall * sizeof(int), st>>>(a, c);
   return cudaGetLastError();
 }
 

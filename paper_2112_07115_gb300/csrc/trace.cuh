@@ -14,6 +14,11 @@ struct TraceArgs {
   const float4* rx;        // nrx receivers (xyz)
   int nrx;
   SmallBvh rxt;            // per-frame tree over the receivers
+  const uint4* qnodes;     // compact node copy (2 uint4 per node) and its frame
+  const float* qframe;
+  int n_nodes;             // internal nodes of both trees
+  int use_q;               // 1: traverse the compact copy from shared memory
+  int stack_cap;           // shared-memory stack entries per thread with use_q
   float4* log_o;           // (N+1) x R: origin, unfolded length D
   float4* log_d;           // (N+1) x R: direction, hit t (+inf escaped)
   int* log_id;             // (N+1) x R: hit triangle id or -1
@@ -42,6 +47,7 @@ struct CoherentArgs {
 // Persistent traversal of every ray (or of the retrace queue) followed by
 // the capture pass over the traced segments. `sms`: multiprocessor count.
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st);
+cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st);
 cudaError_t launch_carry(const TraceArgs& a, const CoherentArgs& c, cudaStream_t st);
 

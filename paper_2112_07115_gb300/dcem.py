@@ -59,8 +59,8 @@ class Stats(C.Structure):
                 ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
                 ("stack_overflow", C.c_int32), ("coherent", C.c_int32),
                 ("kernel_launches", C.c_int32), ("bvh_rebuilt", C.c_int32),
-                ("ms_stage", C.c_float * 8), ("bvh_cost_ratio", C.c_float),
-                ("max_segment_nodes", C.c_int32)]
+                ("ms_stage", C.c_float * 10), ("bvh_cost_ratio", C.c_float),
+                ("max_segment_nodes", C.c_int32), ("trace_kernel", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -75,7 +75,7 @@ PATH_DTYPE = np.dtype([("rx", np.int32), ("depth", np.int32), ("tri", np.int32, 
                        ("amp_im", np.float64), ("pts", np.float32, (MAX_REFL, 3))])
 assert PATH_DTYPE.itemsize == C.sizeof(Path)
 
-STAGES = ["prep", "mark", "trace", "dedupe", "validate", "reduce", "copy_out", "total"]
+STAGES = ["prep", "mark", "trace", "capture", "dedupe", "validate", "reduce", "copy_out", "total"]
 
 _lib = None
 

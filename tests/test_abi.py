@@ -106,3 +106,37 @@ def test_valid_create_without_gpu_reports_cuda_error(L):
         pytest.skip("this machine has a GPU")
     rc, h = _create(L, np.zeros((1, 9), np.float32), [0], [(5.31, 0.0326, 0)])
     assert rc == L.ERR_CUDA and not h.value
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and field offsets of the header's structs, as a C compiler lays
+    them out (gcc, the header alone)."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dcem.h"', "int main(void) {"]
+    for cname, fields in structs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for ln in out.splitlines():
+        a, b, c = ln.split()
+        got[(a, b)] = int(c)
+    return got
+
+
+def test_ctypes_layout_matches_header(L, tmp_path):
+    pairs = [("dcem_material", L.Material), ("dcem_params", L.Params), ("dcem_path", L.Path),
+             ("dcem_stats", L.Stats), ("dcem_result", L.Result)]
+    structs = [(c, [f for f, _ in py._fields_]) for c, py in pairs]
+    got = _c_layout(tmp_path, structs)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
