@@ -710,7 +710,7 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce
   s->launches += 1 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) +
-                 ((s->nint_s + s->nint_d) > 0 && 220L * 1024 - (long)(s->nint_s + s->nint_d) * 32 >= 12L * 4096 ? 1 : 0);
+                 (trace_q_stack_cap(s->nint_s + s->nint_d) > 0 ? 1 : 0);
 
   TraceArgs a;
   a.bvh.nodes = s->nodes;
@@ -746,12 +746,11 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.qnodes = s->qnodes;
   a.qframe = s->qframe;
   a.n_nodes = s->nint_s + s->nint_d;
-  // the compact copy of both trees and 1024 threads' stacks fit in shared
+  // the compact copy of both trees and the CTA's stacks fit in shared
   // memory: traverse it there
   {
-    long avail = 220L * 1024 - (long)a.n_nodes * 32;
-    a.stack_cap = (int)std::min<long>(kStackTrace, avail > 0 ? avail / (1024 * (long)sizeof(int)) : 0);
-    a.use_q = (a.n_nodes > 0 && a.stack_cap >= 12) ? 1 : 0;
+    a.stack_cap = trace_q_stack_cap(a.n_nodes);
+    a.use_q = a.stack_cap > 0 ? 1 : 0;
     s->last_use_q = a.use_q;
   }
   if (a.use_q) {

@@ -714,22 +714,26 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
 // dcem_internal.cuh). The frame is the union of the two root boxes padded by
 // 1 m + 0.1%; every child box is rounded outward by one 16-bit step.
 // ---------------------------------------------------------------------------
-// Codes are rounded outward by two steps: the FP32 quotient (v - o) / s is
-// within a small fraction of a step of the exact one, so the decoded box
-// still contains the exact box by more than a step.
+// Codes are rounded outward by three steps: the FP32 quotient (v - o) / s is
+// within a small fraction of a step of the exact one, so the code box
+// contains the exact box with more than two steps to spare on every side.
 __device__ __forceinline__ unsigned qenc_lo(float v, float o, float s) {
   if (!isfinite(v)) return 0u;
-  float d = floorf((v - o) / s) - 2.0f;
-  if (!(d >= 1.0f)) return 0u;
-  return d > 65534.0f ? 65534u : (unsigned)d;
+  float d = floorf((v - o) / s) - 3.0f;
+  if (!(d >= 0.0f)) return 0u;
+  return d > 65535.0f ? 65535u : (unsigned)d;
 }
 __device__ __forceinline__ unsigned qenc_hi(float v, float o, float s) {
   if (!isfinite(v)) return 65535u;
-  float d = ceilf((v - o) / s) + 2.0f;
-  if (!(d <= 65534.0f)) return 65535u;
-  return d < 1.0f ? 1u : (unsigned)d;
+  float d = ceilf((v - o) / s) + 3.0f;
+  if (!(d <= 65535.0f)) return 65535u;
+  return d < 0.0f ? 0u : (unsigned)d;
 }
 
+// Compact copy of both trees (layout and grid in dcem_internal.cuh): the
+// grid pads the union of the root boxes by 1 m + 1e-3 of its largest extent
+// on every side, so every box lies well inside it, with 65000 steps across
+// each padded axis.
 __global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float* __restrict__ root_box,
                            int has0, int has1, uint4* qn, float* qframe) {
   float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
@@ -741,12 +745,16 @@ __global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float
       if (isfinite(b)) hi[k] = fmaxf(hi[k], b);
     }
   }
-  float o[3], sc[3];
+  float ext = 0.0f;
   for (int k = 0; k < 3; ++k) {
     if (!(hi[k] >= lo[k])) { lo[k] = 0.0f; hi[k] = 0.0f; }
-    float pad = 1.0f + 1e-3f * (hi[k] - lo[k]);
+    ext = fmaxf(ext, hi[k] - lo[k]);
+  }
+  float pad = 1.0f + 1e-3f * ext;
+  float o[3], sc[3];
+  for (int k = 0; k < 3; ++k) {
     o[k] = lo[k] - pad;
-    sc[k] = fmaxf((hi[k] + pad - o[k]) / 65000.0f, 1e-6f);
+    sc[k] = fmaxf((hi[k] - lo[k] + 2.0f * pad) / 65000.0f, 1e-6f);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (int k = 0; k < 3; ++k) { qframe[k] = o[k]; qframe[3 + k] = sc[k]; }
@@ -754,14 +762,14 @@ __global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float
     float4 n0 = nodes[4 * (size_t)i], n1 = nodes[4 * (size_t)i + 1], n2 = nodes[4 * (size_t)i + 2],
            n3 = nodes[4 * (size_t)i + 3];
     // child 0: lo (n0.x, n0.z, n2.x), hi (n0.y, n0.w, n2.y); child 1 likewise
-    unsigned c[12] = {qenc_lo(n0.x, o[0], sc[0]), qenc_lo(n0.z, o[1], sc[1]), qenc_lo(n2.x, o[2], sc[2]),
-                      qenc_hi(n0.y, o[0], sc[0]), qenc_hi(n0.w, o[1], sc[1]), qenc_hi(n2.y, o[2], sc[2]),
-                      qenc_lo(n1.x, o[0], sc[0]), qenc_lo(n1.z, o[1], sc[1]), qenc_lo(n2.z, o[2], sc[2]),
-                      qenc_hi(n1.y, o[0], sc[0]), qenc_hi(n1.w, o[1], sc[1]), qenc_hi(n2.w, o[2], sc[2])};
-    qn[2 * (size_t)i] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16),
-                                   c[6] | (c[7] << 16));
-    qn[2 * (size_t)i + 1] = make_uint4(c[8] | (c[9] << 16), c[10] | (c[11] << 16), __float_as_uint(n3.x),
-                                       __float_as_uint(n3.y));
+    unsigned w[6] = {qenc_lo(n0.x, o[0], sc[0]) | (qenc_hi(n0.y, o[0], sc[0]) << 16),
+                     qenc_lo(n0.z, o[1], sc[1]) | (qenc_hi(n0.w, o[1], sc[1]) << 16),
+                     qenc_lo(n2.x, o[2], sc[2]) | (qenc_hi(n2.y, o[2], sc[2]) << 16),
+                     qenc_lo(n1.x, o[0], sc[0]) | (qenc_hi(n1.y, o[0], sc[0]) << 16),
+                     qenc_lo(n1.z, o[1], sc[1]) | (qenc_hi(n1.w, o[1], sc[1]) << 16),
+                     qenc_lo(n2.z, o[2], sc[2]) | (qenc_hi(n2.w, o[2], sc[2]) << 16)};
+    qn[2 * (size_t)i] = make_uint4(w[0], w[1], w[2], w[3]);
+    qn[2 * (size_t)i + 1] = make_uint4(w[4], w[5], __float_as_uint(n3.x), __float_as_uint(n3.y));
   }
 }
 

@@ -286,54 +286,115 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
 }
 
 // ---------------------------------------------------------------------------
-// compact nodes for shared memory: child boxes as 16-bit codes in a per-frame
-// scene frame (origin O, step S per axis), rounded outward by one step, so a
-// decoded box always contains the exact one; code 0 (lo) and 65535 (hi) mean
-// unbounded. 32 bytes per node:
-//   q[0..5] = child 0 (lo.xyz, hi.xyz), q[6..11] = child 1, then child codes.
+// compact nodes for shared memory: child boxes as 16-bit codes on a per-frame
+// grid (origin O, step S_k on axis k) that contains both trees, rounded
+// outward by three steps, so a code box always contains the exact box. 32
+// bytes per node: words 0-2 = child 0 axes x, y, z, words 3-5 = child 1
+// axes, words 6-7 = child ids; each axis word holds the lo code in its low
+// half and the hi code in its high half.
+//
+// The slab test runs in grid units: with F = 2^23 + code (the float whose
+// bits are 0x4B00'code', built by one byte permute) the plane parameter is
+// t = F * (S_k/d_k) + ((O_k - o_k)/d_k - 2^23 S_k/d_k), one FMA per plane.
+// For ray origins within 4e6 steps of O on every axis the rounding of the
+// two per-ray terms moves a plane by less than 1.3 steps (half a step from
+// the 2^23 offset, 0.75 from (O - o)/d, the rest relative), which the
+// 3-step margin covers; farther origins take the full-precision traversal
+// instead. The per-axis sign of d picks the near and far code, so no
+// per-axis min/max is needed.
 // ---------------------------------------------------------------------------
 struct QFrame {
   float ox, oy, oz, sx, sy, sz;
 };
 
-__device__ __forceinline__ float qlo(unsigned q, float o, float s) {
-  return q == 0u ? __int_as_float(0xff800000) : __fmaf_rn((float)q, s, o);
-}
-__device__ __forceinline__ float qhi(unsigned q, float o, float s) {
-  return q == 65535u ? __int_as_float(0x7f800000) : __fmaf_rn((float)q, s, o);
+struct QRay {
+  float ix, iy, iz;        // S_k / d_k per axis
+  float kx, ky, kz;        // (O_k - o_k) / d_k - 2^23 S_k / d_k per axis
+  unsigned nx, ny, nz;     // byte-permute selector of the near code per axis
+};
+
+__device__ __forceinline__ bool qray_make(const QFrame& f, const RayPre& r, QRay& q) {
+  float ex = __fsub_rn(f.ox, r.o.x), ey = __fsub_rn(f.oy, r.o.y), ez = __fsub_rn(f.oz, r.o.z);
+  if (!(fabsf(ex) <= __fmul_rn(4.0e6f, f.sx) && fabsf(ey) <= __fmul_rn(4.0e6f, f.sy) &&
+        fabsf(ez) <= __fmul_rn(4.0e6f, f.sz)))
+    return false;
+  q.ix = __fmul_rn(f.sx, r.inv.x);
+  q.iy = __fmul_rn(f.sy, r.inv.y);
+  q.iz = __fmul_rn(f.sz, r.inv.z);
+  q.kx = __fmaf_rn(-8388608.0f, q.ix, __fmul_rn(ex, r.inv.x));
+  q.ky = __fmaf_rn(-8388608.0f, q.iy, __fmul_rn(ey, r.inv.y));
+  q.kz = __fmaf_rn(-8388608.0f, q.iz, __fmul_rn(ez, r.inv.z));
+  q.nx = r.inv.x >= 0.0f ? 0x5410u : 0x5432u;
+  q.ny = r.inv.y >= 0.0f ? 0x5410u : 0x5432u;
+  q.nz = r.inv.z >= 0.0f ? 0x5410u : 0x5432u;
+  return true;
 }
 
-// Closest hit as closest_hit(), with the nodes read from a compact copy
+// 2^23 + the near (sel) or far (sel ^ 0x22) code of an axis word
+__device__ __forceinline__ float qcode(unsigned w, unsigned sel) {
+  return __uint_as_float(__byte_perm(w, 0x4B00u, sel));
+}
+
+__device__ __forceinline__ bool qslab(const QRay& q, unsigned wx, unsigned wy, unsigned wz, float tcap,
+                                      float& tn_out) {
+  float tnx = __fmaf_rn(qcode(wx, q.nx), q.ix, q.kx), tfx = __fmaf_rn(qcode(wx, q.nx ^ 0x22u), q.ix, q.kx);
+  float tny = __fmaf_rn(qcode(wy, q.ny), q.iy, q.ky), tfy = __fmaf_rn(qcode(wy, q.ny ^ 0x22u), q.iy, q.ky);
+  float tnz = __fmaf_rn(qcode(wz, q.nz), q.iz, q.kz), tfz = __fmaf_rn(qcode(wz, q.nz ^ 0x22u), q.iz, q.kz);
+  float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
+  float tf = fminf(fminf(tfx, tfy), fminf(tfz, tcap));
+  tn_out = tn;
+  return tn <= __fmul_rn(tf, 1.00001f) + 1e-30f;
+}
+
+// Ray origins far outside the grid: full-precision nodes, out of line so
+// that the common path keeps its registers.
+static __device__ __noinline__ int closest_hit_far(const Bvh bvh, const RayPre r, float tmin, int excl, float* t_best,
+                                            int* id_best, unsigned* overflow, unsigned* n_nodes, unsigned* n_tris,
+                                            int* sbase, int stride, int cap) {
+  TStack st;
+  st.s = sbase;
+  st.stride = stride;
+  st.cap = cap;
+  st.sp = 0;
+  float t;
+  int id;
+  unsigned ovf = 0, nn = 0, nt = 0;
+  int slot = closest_hit(bvh, r, tmin, excl, t, id, ovf, nn, nt, st);
+  *t_best = t;
+  *id_best = id;
+  *overflow |= ovf;
+  *n_nodes += nn;
+  *n_tris += nt;
+  return slot;
+}
+
+// Closest hit as closest_hit(), with the nodes read from the compact copy
 // (shared memory). Same triangle test and tie rule, so the same result.
 __device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, const Bvh& bvh, const RayPre& r,
                                              float tmin, int excl, float& t_best, int& id_best, unsigned& overflow,
                                              unsigned& n_nodes, unsigned& n_tris, TStack& st) {
+  QRay q;
+  if (!qray_make(f, r, q))
+    return closest_hit_far(bvh, r, tmin, excl, &t_best, &id_best, &overflow, &n_nodes, &n_tris, st.s, st.stride,
+                           st.cap);
   st.reset();
   t_best = __int_as_float(0x7f800000);
   id_best = 0x7fffffff;
   int slot_best = -1;
   if (bvh.root1 != kEmpty) st.push(bvh.root1);
   int cur = bvh.root0;
-  for (int visits = 0;; ++visits) {
+  if (cur == kEmpty) cur = st.empty() ? kEmpty : st.pop();
+  for (int visits = 0; cur != kEmpty; ++visits) {
     if (visits > bvh.max_visits) {
       overflow = 1u;
       break;
-    }
-    if (cur == kEmpty) {
-      if (st.empty()) break;
-      cur = st.pop();
-      continue;
     }
     if (cur >= 0) {
       ++n_nodes;
       uint4 a = qn[2 * cur], b = qn[2 * cur + 1];
       float tn0, tn1;
-      bool h0 = slab(r, qlo(a.x & 0xffffu, f.ox, f.sx), qhi(a.y >> 16, f.ox, f.sx), qlo(a.x >> 16, f.oy, f.sy),
-                     qhi(a.z & 0xffffu, f.oy, f.sy), qlo(a.y & 0xffffu, f.oz, f.sz), qhi(a.z >> 16, f.oz, f.sz),
-                     t_best, tn0);
-      bool h1 = slab(r, qlo(a.w & 0xffffu, f.ox, f.sx), qhi(b.x >> 16, f.ox, f.sx), qlo(a.w >> 16, f.oy, f.sy),
-                     qhi(b.y & 0xffffu, f.oy, f.sy), qlo(b.x & 0xffffu, f.oz, f.sz), qhi(b.y >> 16, f.oz, f.sz),
-                     t_best, tn1);
+      bool h0 = qslab(q, a.x, a.y, a.z, t_best, tn0);
+      bool h1 = qslab(q, a.w, b.x, b.y, t_best, tn1);
       int c0 = (int)b.z, c1 = (int)b.w;
       if (h0 && h1) {
         int nearc = tn0 <= tn1 ? c0 : c1, farc = tn0 <= tn1 ? c1 : c0;
@@ -344,7 +405,7 @@ __device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, c
       } else if (h1) {
         cur = c1;
       } else {
-        cur = kEmpty;
+        cur = st.empty() ? kEmpty : st.pop();
       }
     } else {
       int slot = ~cur;
@@ -360,7 +421,7 @@ __device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, c
           slot_best = slot;
         }
       }
-      cur = kEmpty;
+      cur = st.empty() ? kEmpty : st.pop();
     }
   }
   return slot_best;

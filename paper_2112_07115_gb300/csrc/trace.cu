@@ -34,57 +34,77 @@ __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
   return __shfl_sync(0xffffffffu, base, 0);
 }
 
-// Persistent traversal: each warp takes 32 rays at a time (rays are sorted by
-// direction, so a warp's rays travel together, and the dynamic fetch keeps
-// the expensive grazing rays from piling up on a few SMs). Per ray, segment
-// b from its restart point (0 in a full frame) to N: closest hit, segment
-// log, specular reflection. Captures are tested by k_capture.
+// Persistent traversal with a per-lane ray fetch: every lane traces one
+// segment of its own ray per step, and a lane whose ray has ended takes the
+// next ray of the queue at once (one atomic per warp for all such lanes), so
+// a warp never waits for its longest ray. Rays are sorted by direction, so
+// consecutive fetches travel together. A queue smaller than the resident
+// lanes is spread over every warp (at most `width` lanes of each take rays)
+// so that short retrace queues use all SMs. Per segment b from the ray's
+// restart point (0 in a full frame) to N: closest hit, segment log, specular
+// reflection. Captures are tested by k_capture.
 template <bool kQ>
 __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st) {
   const int R = a.R;
   const int nq = a.queue ? (int)min(*a.nq_dev, (unsigned)R) : R;
-  unsigned long long segs = 0, nodes = 0, tris = 0;
-  unsigned ovf = 0, maxn = 0;
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int width = min(32, max(1, (nq + warps - 1) / warps));
+  unsigned segs = 0, nodes = 0, tris = 0, ovf = 0, maxn = 0;
+  int ray = lane < width ? -1 : -2;  // -1: takes a ray next, -2: finished
+  int b = 0, last = -1;
+  float3 o = f3(0.0f, 0.0f, 0.0f), d = o;
+  float D = 0.0f;
   for (;;) {
-    int base = fetch_warp(&a.ctr->work_trace, 32u);
-    if (base >= nq) break;
-    int q = base + (threadIdx.x & 31);
-    if (q < nq) {
-      int ray = a.queue ? a.queue[q] : q;
-      int b0 = a.queue ? a.restart[ray] : 0;
-      float3 o, d;
-      float D;
-      int last;
-      if (b0 == 0) {
-        float4 rd = __ldg(&a.rays[ray]);
-        o = a.tx;
-        d = f3(rd.x, rd.y, rd.z);
-        D = 0.0f;
-        last = -1;
-      } else {
-        float4 lo = a.log_o[(size_t)b0 * R + ray], ld = a.log_d[(size_t)b0 * R + ray];
-        o = f3(lo.x, lo.y, lo.z);
-        D = lo.w;
-        d = f3(ld.x, ld.y, ld.z);
-        last = a.log_id[(size_t)(b0 - 1) * R + ray];
+    unsigned need = __ballot_sync(0xffffffffu, ray == -1);
+    if (need) {
+      int leader = __ffs(need) - 1;
+      int base = 0;
+      if (lane == leader) base = (int)atomicAdd(&a.ctr->work_trace, (unsigned)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (ray == -1) {
+        int q = base + __popc(need & ((1u << lane) - 1u));
+        if (q < nq) {
+          ray = a.queue ? a.queue[q] : q;
+          b = a.queue ? a.restart[ray] : 0;
+          if (b == 0) {
+            float4 rd = __ldg(&a.rays[ray]);
+            o = a.tx;
+            d = f3(rd.x, rd.y, rd.z);
+            D = 0.0f;
+            last = -1;
+          } else {
+            float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
+            o = f3(lo.x, lo.y, lo.z);
+            D = lo.w;
+            d = f3(ld.x, ld.y, ld.z);
+            last = a.log_id[(size_t)(b - 1) * R + ray];
+          }
+        } else {
+          ray = -2;
+        }
       }
-      int b = b0;
-      for (; b <= a.N; ++b) {
-        RayPre rp = ray_pre(o, d);
-        float t;
-        int id;
-        unsigned nn = 0, nt = 0;
-        int slot = kQ ? closest_hit_q(qn, qf, a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st)
-                      : closest_hit(a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st);
-        ++segs;
-        nodes += nn;
-        tris += nt;
-        maxn = max(maxn, nn);
-        bool hit = slot >= 0;
-        a.log_o[(size_t)b * R + ray] = make_float4(o.x, o.y, o.z, D);
-        a.log_d[(size_t)b * R + ray] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
-        a.log_id[(size_t)b * R + ray] = hit ? id : -1;
-        if (!hit) break;
+    }
+    if (__all_sync(0xffffffffu, ray == -2)) break;
+    if (ray >= 0) {
+      RayPre rp = ray_pre(o, d);
+      float t;
+      int id;
+      unsigned nn = 0, nt = 0;
+      int slot = kQ ? closest_hit_q(qn, qf, a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st)
+                    : closest_hit(a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st);
+      ++segs;
+      nodes += nn;
+      tris += nt;
+      maxn = max(maxn, nn);
+      bool hit = slot >= 0;
+      a.log_o[(size_t)b * R + ray] = make_float4(o.x, o.y, o.z, D);
+      a.log_d[(size_t)b * R + ray] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
+      a.log_id[(size_t)b * R + ray] = hit ? id : -1;
+      if (!hit || b == a.N) {
+        a.nseg[ray] = b + 1;
+        ray = -1;
+      } else {
         // specular reflection: d' = d - 2 (d.n)/(n.n) n, renormalised
         float3 v0, v1, v2;
         int tid;
@@ -97,21 +117,21 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
         d = f3(__fmul_rn(dr.x, inv), __fmul_rn(dr.y, inv), __fmul_rn(dr.z, inv));
         D = __fadd_rn(D, t);
         last = id;
+        ++b;
       }
-      a.nseg[ray] = (b > a.N ? a.N : b) + 1;
     }
-    __syncwarp();
   }
+  unsigned long long wsegs = segs, wnodes = nodes, wtris = tris;
   for (int off = 16; off > 0; off >>= 1) {
-    segs += __shfl_down_sync(0xffffffffu, segs, off);
-    nodes += __shfl_down_sync(0xffffffffu, nodes, off);
-    tris += __shfl_down_sync(0xffffffffu, tris, off);
+    wsegs += __shfl_down_sync(0xffffffffu, wsegs, off);
+    wnodes += __shfl_down_sync(0xffffffffu, wnodes, off);
+    wtris += __shfl_down_sync(0xffffffffu, wtris, off);
+    maxn = max(maxn, __shfl_down_sync(0xffffffffu, maxn, off));
   }
-  for (int off = 16; off > 0; off >>= 1) maxn = max(maxn, __shfl_down_sync(0xffffffffu, maxn, off));
-  if ((threadIdx.x & 31) == 0 && segs) {
-    atomicAdd(&a.ctr->segments_traced, segs);
-    atomicAdd(&a.ctr->node_visits, nodes);
-    atomicAdd(&a.ctr->tri_tests, tris);
+  if (lane == 0 && wsegs) {
+    atomicAdd(&a.ctr->segments_traced, wsegs);
+    atomicAdd(&a.ctr->node_visits, wnodes);
+    atomicAdd(&a.ctr->tri_tests, wtris);
     atomicMax(&a.ctr->max_seg_nodes, maxn);
   }
   if (ovf) {
@@ -129,8 +149,8 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
 }
 
 // Same traversal with the compact node copy staged in shared memory (one
-// 1024-thread CTA per SM, the whole copy loaded once per CTA).
-__global__ void __launch_bounds__(1024, 1) k_trace_q(TraceArgs a) {
+// CTA of kTraceQThreads threads per SM, the whole copy loaded once per CTA).
+__global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   extern __shared__ uint4 sq[];
   TStack st;
   bind_stack(st, reinterpret_cast<int*>(sq + 2 * a.n_nodes), a.stack_cap);
@@ -286,19 +306,25 @@ static int resident_blocks(const void* fn, int sms, size_t smem) {
   return nb * sms;
 }
 
+int trace_q_stack_cap(int n_nodes) {
+  long avail = kTraceQSmem - (long)n_nodes * 2 * (long)sizeof(uint4);
+  int cap = avail > 0 ? (int)std::min<long>(kStackTrace, avail / (kTraceQThreads * (long)sizeof(int))) : 0;
+  return (n_nodes > 0 && cap >= 12) ? cap : 0;
+}
+
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
   static int g_trace = 0;
   if (!g_trace) g_trace = resident_blocks((const void*)k_trace, sms, 256 * kStackTrace * sizeof(int));
   long n = a.R;
   if (a.use_q) {
-    size_t smem = (size_t)a.n_nodes * 2 * sizeof(uint4) + (size_t)1024 * a.stack_cap * sizeof(int);
+    size_t smem = (size_t)a.n_nodes * 2 * sizeof(uint4) + (size_t)kTraceQThreads * a.stack_cap * sizeof(int);
     static size_t attr = 0;
     if (smem > attr) {
       cudaError_t e = cudaFuncSetAttribute(k_trace_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       attr = smem;
     }
-    k_trace_q<<<grid_for(n, 1024, sms), 1024, smem, st>>>(a);
+    k_trace_q<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
   } else {
     k_trace<<<grid_for(n, 256, g_trace), 256, 256 * kStackTrace * sizeof(int), st>>>(a);
   }

@@ -46,6 +46,13 @@ struct CoherentArgs {
 
 // Persistent traversal of every ray (or of the retrace queue) followed by
 // the capture pass over the traced segments. `sms`: multiprocessor count.
+// Closest-hit kernel with the compact node copy in shared memory: threads
+// per CTA (one CTA per SM) and the shared memory it may use.
+constexpr int kTraceQThreads = 768;
+constexpr long kTraceQSmem = 220L * 1024;
+// Shared-memory stack entries per thread for a compact copy of n_nodes
+// nodes, or 0 if copy and stacks do not fit (then nodes come from global).
+int trace_q_stack_cap(int n_nodes);
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st);
