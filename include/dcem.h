@@ -172,8 +172,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat,
                       int32_t nobj, void* stream, dcem_scene** out);
 
 /* Sets the sampled sphere of ray directions (Sec. III step 1): host, n*3
- * floats of unit vectors, uploaded once and reused every frame. n may be 0.
- * Invalidates the coherence cache. */
+ * floats of unit vectors, uploaded once and reused every frame. n may be 0
+ * and at most 2^27 (DCEM_ERR_ARG above). Invalidates the coherence cache. */
 int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays);
 
 /* Per-frame update (Sec. III "Efficient BVH updating"): xf holds nobj

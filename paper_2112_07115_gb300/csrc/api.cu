@@ -175,6 +175,7 @@ struct dcem_scene {
   float4* log_o = nullptr;
   float4* log_d = nullptr;
   int* log_id = nullptr;
+  unsigned* capitems = nullptr;  // segments traced this frame: ray << 4 | segment
   int* nseg = nullptr;
   int* restart = nullptr;
   int* queue = nullptr;
@@ -236,7 +237,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
   dfree(s->scr.v1); dfree(s->scr.hist); dfree(s->scr.keys); dfree(s->ctr); dfree(s->uctr);
   if (s->ctr_h) cudaFreeHost(s->ctr_h);
-  dfree(s->rays); dfree(s->ray_perm); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->nseg); dfree(s->restart);
+  dfree(s->rays); dfree(s->ray_perm); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems); dfree(s->nseg); dfree(s->restart);
   dfree(s->queue); dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->prev_ncand); dfree(s->hkey);
   dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
   dfree(s->vpts); dfree(s->vstate);
@@ -324,11 +325,12 @@ int alloc_build_scratch(dcem_scene* s, int n) {
 
 int ensure_log(dcem_scene* s, int W) {
   if (s->logW >= W && s->log_o) return DCEM_OK;
-  dfree(s->log_o); dfree(s->log_d); dfree(s->log_id);
+  dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems);
   size_t n = (size_t)W * (size_t)(s->R > 0 ? s->R : 1);
   CK(dalloc(&s->log_o, n));
   CK(dalloc(&s->log_d, n));
   CK(dalloc(&s->log_id, n));
+  CK(dalloc(&s->capitems, n));
   s->logW = W;
   s->cache_valid = false;
   return DCEM_OK;
@@ -589,7 +591,7 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
 }
 
 int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays) {
-  if (!s || n_rays < 0 || (n_rays > 0 && !dirs)) return DCEM_ERR_ARG;
+  if (!s || n_rays < 0 || n_rays > (1 << 27) || (n_rays > 0 && !dirs)) return DCEM_ERR_ARG;
   if (n_rays > 0 && !finite_arr(dirs, 3 * (size_t)n_rays)) return DCEM_ERR_NONFINITE;
   for (int i = 0; i < n_rays; ++i) {
     float x = dirs[3 * i], y = dirs[3 * i + 1], z = dirs[3 * i + 2];
@@ -597,7 +599,7 @@ int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays) {
   }
   CK(cudaStreamSynchronize(s->st));
   dfree(s->rays); dfree(s->ray_perm); dfree(s->nseg); dfree(s->restart); dfree(s->queue);
-  dfree(s->log_o); dfree(s->log_d); dfree(s->log_id);
+  dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems);
   s->logW = 0;
   s->R = n_rays;
   s->rays_set = false;
@@ -730,6 +732,7 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.log_o = s->log_o;
   a.log_d = s->log_d;
   a.log_id = s->log_id;
+  a.capitems = s->capitems;
   a.nseg = s->nseg;
   a.queue = nullptr;
   a.queue_w = s->queue;
@@ -879,6 +882,8 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   CK(cudaMemcpyAsync(s->ctr_h, s->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(s->ctr_h + 1, s->uctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
   CK(cudaMemsetAsync(s->uctr, 0, sizeof(DevCounters), st));
+  // with device outputs nothing follows on the stream: the frame ends here
+  if (tm && out->ptr_kind == DCEM_PTR_DEVICE) CK(cudaEventRecord(s->ev[8], st));
   CK(cudaStreamSynchronize(st));
   s->cur = nxt;
   return DCEM_OK;
@@ -1006,8 +1011,10 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
     int ncopy = std::min(nvalid, out->max_paths);
     if (ncopy > 0 && out->paths) CK(cudaMemcpyAsync(out->paths, s->pout, sizeof(dcem_path) * ncopy, k, st));
   }
-  if (tm) CK(cudaEventRecord(s->ev[8], st));
-  CK(cudaStreamSynchronize(st));
+  if (out->ptr_kind == DCEM_PTR_HOST) {
+    if (tm) CK(cudaEventRecord(s->ev[8], st));
+    CK(cudaStreamSynchronize(st));
+  }
   if (tm) {
     for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&S.ms_stage[i], s->ev[i], s->ev[i + 1]);
     cudaEventElapsedTime(&S.ms_stage[8], s->ev[0], s->ev[8]);

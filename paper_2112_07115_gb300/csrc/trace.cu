@@ -86,6 +86,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       }
     }
     if (__all_sync(0xffffffffu, ray == -2)) break;
+    unsigned item = 0xffffffffu;  // segment traced in this step, for the capture list
     if (ray >= 0) {
       RayPre rp = ray_pre(o, d);
       float t;
@@ -101,6 +102,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       a.log_o[(size_t)b * R + ray] = make_float4(o.x, o.y, o.z, D);
       a.log_d[(size_t)b * R + ray] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
       a.log_id[(size_t)b * R + ray] = hit ? id : -1;
+      item = ((unsigned)ray << 4) | (unsigned)b;
       if (!hit || b == a.N) {
         a.nseg[ray] = b + 1;
         ray = -1;
@@ -119,6 +121,14 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
         last = id;
         ++b;
       }
+    }
+    unsigned logged = __ballot_sync(0xffffffffu, item != 0xffffffffu);
+    if (logged) {
+      int leader = __ffs(logged) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&a.ctr->n_capitems, (unsigned)__popc(logged));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (item != 0xffffffffu) a.capitems[base + __popc(logged & ((1u << lane) - 1u))] = item;
     }
   }
   unsigned long long wsegs = segs, wnodes = nodes, wtris = tris;
@@ -166,11 +176,10 @@ __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   trace_rays<true>(a, sq, f, st);
 }
 
-// Reception-sphere captures of traced segments, one work item per (ray,
-// segment), segment-major so that a warp reads consecutive log entries.
-// Full frame: every segment of every ray. Coherent frame: the segments of
-// the retraced rays from their restart point on (reused segments were tested
-// against the moved receivers in k_mark).
+// Reception-sphere captures of the segments traced this frame (the list the
+// closest-hit kernel appends to, in tracing order, so a warp reads segments
+// of neighbouring rays). In a coherent frame reused segments were tested
+// against the moved receivers in k_mark.
 __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
   extern __shared__ int sstk[];
   TStack st;
@@ -178,32 +187,27 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
   const SmallBvh& rxt = a.rxt;
   const float4* rx = a.rx;
   const int R = a.R;
-  const int nq = a.queue ? (int)min(*a.nq_dev, (unsigned)R) : R;
-  const unsigned total = (unsigned)nq * (unsigned)(a.N + 1);
+  const unsigned total = min(a.ctr->n_capitems, (unsigned)R * (unsigned)(a.N + 1));
   unsigned ovf = 0;
   for (;;) {
     int base = fetch_warp(&a.ctr->work_capture, 32u);
     if ((unsigned)base >= total) break;
     unsigned q = (unsigned)base + (threadIdx.x & 31);
     if (q < total) {
-      int b = (int)(q / (unsigned)nq);
-      int i = (int)(q - (unsigned)b * (unsigned)nq);
-      int ray = a.queue ? a.queue[i] : i;
-      int b0 = a.queue ? a.restart[ray] : 0;
-      if (b >= b0 && b < a.nseg[ray]) {
-        float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
-        float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
-        float D = lo.w, t = ld.w;
-        float tend = isinf(t) ? a.escape : t;
-        RayPre rp;
-        rp.o = o;
-        float dx = fabsf(d.x) < 1e-30f ? copysignf(1e-30f, d.x) : d.x;
-        float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
-        float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
-        rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-        if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) { emit_cand(a, ray, b, r); }))
-          ovf = 1u;
-      }
+      unsigned it = a.capitems[q];
+      int ray = (int)(it >> 4), b = (int)(it & 15u);
+      float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
+      float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
+      float D = lo.w, t = ld.w;
+      float tend = isinf(t) ? a.escape : t;
+      RayPre rp;
+      rp.o = o;
+      float dx = fabsf(d.x) < 1e-30f ? copysignf(1e-30f, d.x) : d.x;
+      float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
+      float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
+      rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
+      if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) { emit_cand(a, ray, b, r); }))
+        ovf = 1u;
     }
     __syncwarp();
   }
@@ -216,9 +220,9 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
 // ---------------------------------------------------------------------------
 // coherent frame: marking and carry-over
 // ---------------------------------------------------------------------------
-// One thread per ray: the first logged segment that meets a moved box is the
-// restart point; earlier segments are reused and re-tested against the
-// receivers that moved.
+// One thread per ray (warps take 32 rays at a time): the first logged
+// segment that meets a moved box is the restart point; earlier segments are
+// reused and re-tested against the receivers that moved.
 __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
   extern __shared__ int sstk[];
   TStack st;
@@ -232,7 +236,11 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
   const int R = a.R;
   unsigned long long reused = 0;
   unsigned ovf = 0;
-  for (int ray = blockIdx.x * blockDim.x + threadIdx.x; ray < R; ray += gridDim.x * blockDim.x) {
+  for (;;) {
+    int base = fetch_warp(&c.ctr->work_mark, 32u);
+    if (base >= R) break;
+    int ray = base + (threadIdx.x & 31);
+    if (ray >= R) continue;
     int ns = a.nseg[ray];
     int bstar = all ? 0 : ns;
     for (int b = 0; b < bstar; ++b) {
@@ -264,6 +272,7 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
       a.queue_w[at] = ray;
     }
   }
+  __syncwarp();
   for (int off = 16; off > 0; off >>= 1) reused += __shfl_down_sync(0xffffffffu, reused, off);
   if ((threadIdx.x & 31) == 0 && reused) atomicAdd(&c.ctr->segments_reused, reused);
   if (ovf) {

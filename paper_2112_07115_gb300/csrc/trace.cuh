@@ -22,6 +22,7 @@ struct TraceArgs {
   float4* log_o;           // (N+1) x R: origin, unfolded length D
   float4* log_d;           // (N+1) x R: direction, hit t (+inf escaped)
   int* log_id;             // (N+1) x R: hit triangle id or -1
+  unsigned* capitems;      // (N+1) x R capacity: traced segments, ray << 4 | segment
   int* nseg;               // R
   const int* queue;        // retrace queue (null: all rays from segment 0)
   int* queue_w;            // retrace queue written by the marking kernel
