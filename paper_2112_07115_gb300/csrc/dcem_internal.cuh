@@ -539,12 +539,12 @@ __device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
     if (cur < 0) {
-      int ri = __ldg(&t.perm[~cur]);
-      float4 v = __ldg(&rx[ri]);
+      int ri = t.perm[~cur];
+      float4 v = rx[ri];
       if (captured(r.o, d, D, tend, alpha, f3(v.x, v.y, v.z))) emit(ri);
     } else {
       const float4* n = t.nodes + 4 * (size_t)cur;
-      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+      float4 n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       bool m0 = cone_box(r, D, tend, alpha, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
       bool m1 = cone_box(r, D, tend, alpha, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
@@ -573,7 +573,7 @@ __device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
     const float4* n = t.nodes + 4 * (size_t)cur;
-    float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+    float4 n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
     float tn;
     bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, tend, tn);
@@ -585,6 +585,31 @@ __device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r
     cur = st.pop();
   }
   return true;
+}
+
+// Copies a per-frame small tree (nn internal nodes, nperm leaves) to shared
+// memory at dst (16-byte aligned) and points t at the copy; returns the end
+// of the copy (16-byte aligned). All threads of the block call it; the
+// caller synchronises before use.
+__device__ __forceinline__ char* stage_tree(const SmallBvh& g, int nn, int nperm, char* dst, SmallBvh& t) {
+  float4* sn = reinterpret_cast<float4*>(dst);
+  for (int i = threadIdx.x; i < 4 * nn; i += blockDim.x) sn[i] = g.nodes[i];
+  int* sp = reinterpret_cast<int*>(sn + 4 * nn);
+  for (int i = threadIdx.x; i < nperm; i += blockDim.x) sp[i] = g.perm[i];
+  int* sr = sp + ((nperm + 3) & ~3);  // root code, then the root box
+  if (threadIdx.x == 0) sr[0] = *g.root;
+  if (threadIdx.x < 6) reinterpret_cast<float*>(sr + 1)[threadIdx.x] = g.root_box[threadIdx.x];
+  t = g;
+  t.nodes = sn;
+  t.perm = sp;
+  t.root = sr;
+  t.root_box = reinterpret_cast<const float*>(sr + 1);
+  return reinterpret_cast<char*>(sr + 8);
+}
+
+// Shared-memory bytes stage_tree needs.
+__host__ __device__ __forceinline__ size_t stage_bytes(int nn, int nperm) {
+  return (size_t)nn * 64 + (size_t)((nperm + 3) & ~3) * 4 + 32;
 }
 
 // 64-bit path key: (rx, depth, triangle ids) mixed with the SplitMix64 finaliser.

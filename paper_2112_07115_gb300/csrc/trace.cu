@@ -180,12 +180,25 @@ __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
 // closest-hit kernel appends to, in tracing order, so a warp reads segments
 // of neighbouring rays). In a coherent frame reused segments were tested
 // against the moved receivers in k_mark.
+// Receivers and their tree copied to shared memory after the stacks (kS).
+__device__ __forceinline__ char* stage_receivers(const TraceArgs& a, char* p, const float4*& rx, SmallBvh& rxt) {
+  float4* srx = reinterpret_cast<float4*>(p);
+  for (int i = threadIdx.x; i < a.nrx; i += blockDim.x) srx[i] = a.rx[i];
+  rx = srx;
+  return stage_tree(a.rxt, max(a.nrx - 1, 0), a.nrx, reinterpret_cast<char*>(srx + a.nrx), rxt);
+}
+
+template <bool kS>
 __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
-  extern __shared__ int sstk[];
+  extern __shared__ __align__(16) int sstk[];
   TStack st;
   bind_stack(st, sstk, kStackSmall);
-  const SmallBvh& rxt = a.rxt;
+  SmallBvh rxt = a.rxt;
   const float4* rx = a.rx;
+  if (kS) {
+    stage_receivers(a, reinterpret_cast<char*>(sstk + blockDim.x * kStackSmall), rx, rxt);
+    __syncthreads();
+  }
   const int R = a.R;
   const unsigned total = min(a.ctr->n_capitems, (unsigned)R * (unsigned)(a.N + 1));
   unsigned ovf = 0;
@@ -223,15 +236,22 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
 // One thread per ray (warps take 32 rays at a time): the first logged
 // segment that meets a moved box is the restart point; earlier segments are
 // reused and re-tested against the receivers that moved.
+template <bool kS>
 __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
-  extern __shared__ int sstk[];
+  extern __shared__ __align__(16) int sstk[];
   TStack st;
   bind_stack(st, sstk, kStackSmall);
-  const SmallBvh& rxt = a.rxt;
+  SmallBvh rxt = a.rxt;
   const float4* rx = a.rx;
-  const SmallBvh& mvt = c.mvt;
+  SmallBvh mvt = c.mvt;
   // more moved boxes than the per-frame tree holds: retrace everything
-  bool all = c.ctr->n_moved_boxes > (unsigned)c.mv_cap;
+  const unsigned nmb = c.ctr->n_moved_boxes;
+  bool all = nmb > (unsigned)c.mv_cap;
+  if (kS) {
+    char* p = stage_receivers(a, reinterpret_cast<char*>(sstk + blockDim.x * kStackSmall), rx, rxt);
+    stage_tree(c.mvt, all ? 0 : max((int)nmb - 1, 0), 0, p, mvt);
+    __syncthreads();
+  }
   bool any_rx = c.ctr->rx_moved > 0;
   const int R = a.R;
   unsigned long long reused = 0;
@@ -340,16 +360,39 @@ cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Shared memory of the capture and marking kernels: stacks, plus the
+// receivers, their tree and (marking) the moved-box tree when these fit.
+static size_t rx_stage_bytes(int nrx) { return (size_t)nrx * 16 + stage_bytes(nrx > 1 ? nrx - 1 : 0, nrx); }
+constexpr size_t kStageLimit = 96 * 1024;
+
+static cudaError_t allow_smem(const void* fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st) {
-  static int g_cap = 0;
-  if (!g_cap) g_cap = resident_blocks((const void*)k_capture, sms, 256 * kStackSmall * sizeof(int));
-  long n = a.R;
-  k_capture<<<grid_for(n * (a.N + 1), 256, g_cap), 256, 256 * kStackSmall * sizeof(int), st>>>(a);
+  size_t base = 256 * kStackSmall * sizeof(int);
+  size_t staged = base + rx_stage_bytes(a.nrx);
+  bool kS = a.nrx <= 1024 && staged <= kStageLimit;
+  const void* fn = kS ? (const void*)k_capture<true> : (const void*)k_capture<false>;
+  size_t smem = kS ? staged : base;
+  cudaError_t e = allow_smem(fn, smem);
+  if (e != cudaSuccess) return e;
+  int blocks = grid_for((long)a.R * (a.N + 1), 256, resident_blocks(fn, sms, smem));
+  if (kS) k_capture<true><<<blocks, 256, smem, st>>>(a);
+  else k_capture<false><<<blocks, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st) {
-  k_mark<<<grid_for(a.R, 256, grid_cap), 256, 256 * kStackSmall * sizeof(int), st>>>(a, c);
+  size_t base = 256 * kStackSmall * sizeof(int);
+  size_t staged = base + rx_stage_bytes(a.nrx) + stage_bytes(c.mv_cap > 1 ? c.mv_cap - 1 : 0, 0);
+  bool kS = a.nrx <= 1024 && staged <= kStageLimit;
+  size_t smem = kS ? staged : base;
+  cudaError_t e = allow_smem(kS ? (const void*)k_mark<true> : (const void*)k_mark<false>, smem);
+  if (e != cudaSuccess) return e;
+  if (kS) k_mark<true><<<grid_for(a.R, 256, grid_cap), 256, smem, st>>>(a, c);
+  else k_mark<false><<<grid_for(a.R, 256, grid_cap), 256, smem, st>>>(a, c);
   return cudaGetLastError();
 }
 
