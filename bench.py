@@ -41,8 +41,8 @@ WORKLOAD = "highway V2I: 2 km 6-lane road + barriers, 200 vehicles, 200 roof Rx,
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--freq", type=float, default=28e9)
@@ -84,7 +84,7 @@ class Clocks:
         self.lines, self.proc = [], None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(device)], stdout=subprocess.PIPE,
+                                          "-lms", "50", "-i", str(device)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -234,10 +234,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = Clocks(local)
     s_coh, ms_coh, st_coh = run(dcem.MODE_COHERENT, frames, True)
-    clocks = clk.stop()
     torch.cuda.synchronize()
     # full retrace of the same frames
     s_full, ms_full, st_full = run(dcem.MODE_FULL, frames, True)
+    clocks = clk.stop()
     t_coh = sum(ms_coh) / 1e3
     t_full = sum(ms_full) / 1e3
     t_coh, t_full = max_over_ranks([t_coh, t_full], dev)
