@@ -47,6 +47,35 @@ unsigned pow2_at_least(unsigned long long v) {
   return (unsigned)p;
 }
 
+// End of a frame in one launch: the state the next frame compares against
+// (receiver positions, transforms, object boxes, capture count) and both
+// counter blocks written straight to mapped host memory; the update
+// counters are cleared for the next update.
+__global__ void k_frame_end(const float4* __restrict__ rx_cur, float4* rx_traced, int nrx,
+                            const float* __restrict__ xf_cur, float* xf_traced,
+                            const unsigned* __restrict__ box_cur, unsigned* box_traced, int nobj,
+                            const DevCounters* __restrict__ ctr, DevCounters* uctr, unsigned* prev_ncand,
+                            DevCounters* host) {
+  int i0 = blockIdx.x * blockDim.x + threadIdx.x, step = gridDim.x * blockDim.x;
+  for (int i = i0; i < nrx; i += step) rx_traced[i] = rx_cur[i];
+  for (int i = i0; i < 12 * nobj; i += step) xf_traced[i] = xf_cur[i];
+  for (int i = i0; i < 6 * nobj; i += step) box_traced[i] = box_cur[i];
+  if (blockIdx.x == 0) {
+    constexpr int W = sizeof(DevCounters) / sizeof(unsigned);
+    const unsigned* a = reinterpret_cast<const unsigned*>(ctr);
+    unsigned* b = reinterpret_cast<unsigned*>(uctr);
+    unsigned* ha = reinterpret_cast<unsigned*>(host);
+    unsigned* hb = reinterpret_cast<unsigned*>(host + 1);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+      ha[k] = a[k];
+      hb[k] = b[k];
+    }
+    if (threadIdx.x == 0) *prev_ncand = ctr->n_cand;
+    __syncthreads();
+    for (int k = threadIdx.x; k < W; k += blockDim.x) b[k] = 0u;
+  }
+}
+
 __global__ void k_objv_src(const float* __restrict__ v9, const int* __restrict__ sel,
                            const int* __restrict__ tri_obj, int n, float4* objv_src) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -145,6 +174,8 @@ struct dcem_scene {
   uint4* qnodes = nullptr;       // compact node copy for shared-memory traversal
   float* qframe = nullptr;
   int* leaf_parent = nullptr;
+  int* dsched = nullptr;  // moving-object tree: nodes by height, and the height bounds
+  int* dlvl = nullptr;
   int* arrive = nullptr;
   int* roots = nullptr;
   float* root_box = nullptr;
@@ -164,7 +195,8 @@ struct dcem_scene {
   bool rebuilt_since_frame = false;
   DevCounters* ctr = nullptr;
   DevCounters* uctr = nullptr;  // errors raised by per-frame updates
-  DevCounters* ctr_h = nullptr; // pinned: [0] frame counters, [1] update counters
+  DevCounters* ctr_h = nullptr; // pinned, mapped: [0] frame counters, [1] update counters
+  DevCounters* ctr_hd = nullptr; // device address of ctr_h
   // rays and segment log
   bool rays_set = false;
   int R = 0;
@@ -232,6 +264,7 @@ void scene_free(dcem_scene* s) {
   cudaStreamSynchronize(s->st);
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe); dfree(s->leaf_parent); dfree(s->arrive);
+  dfree(s->dsched); dfree(s->dlvl);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
   dfree(s->xf_cur); dfree(s->xf_traced); dfree(s->obj_box_cur); dfree(s->obj_box_traced);
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
@@ -290,6 +323,8 @@ int dyn_update(dcem_scene* s, bool rebuild) {
   d.obj_box = s->obj_box_cur;
   d.root_box = s->root_box + 6;
   d.root = s->roots + 1;
+  d.sched = s->dsched;
+  d.lvl = s->dlvl;
   d.uctr = s->uctr;
   CK(launch_dyn_update(d, s->st));
   s->launches += 1;
@@ -502,6 +537,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->qnodes, 2 * (size_t)(s->nint_s + s->nint_d)));
   CKF(dalloc(&s->qframe, 6));
   CKF(dalloc(&s->leaf_parent, ntri));
+  CKF(dalloc(&s->dsched, ntri > 1 ? ntri : 1));
+  CKF(dalloc(&s->dlvl, kDynLevels + 2));
   CKF(dalloc(&s->arrive, nmax));
   CKF(dalloc(&s->roots, 2));
   CKF(dalloc(&s->root_box, 12));
@@ -525,7 +562,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->ctr, 1));
   CKF(dalloc(&s->uctr, 1));
   CKF(dalloc(&s->prev_ncand, 1));
-  CKF(cudaMallocHost((void**)&s->ctr_h, 2 * sizeof(DevCounters)));
+  CKF(cudaHostAlloc((void**)&s->ctr_h, 2 * sizeof(DevCounters), cudaHostAllocMapped));
+  CKF(cudaHostGetDevicePointer((void**)&s->ctr_hd, s->ctr_h, 0));
   if ((rc = alloc_build_scratch(s, nmax)) != DCEM_OK) return fail2(rc);
   CKF(dalloc(&v9, 9 * (size_t)ntri));
   CKF(dalloc(&tri_obj_d, ntri));
@@ -676,7 +714,6 @@ int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kin
     launch_transform_refit(s->objv, s->xf_cur, s->nd, s->nobj, s->nint_s, s->ns, s->tris, s->nodes,
                            s->leaf_parent, s->arrive, s->root_box + 6, s->obj_box_cur, s->uctr, st);
     CK(cudaGetLastError());
-    s->launches += 1;
   }
   return DCEM_OK;
 }
@@ -710,8 +747,8 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   bool tm = p->timing != 0;
   if (tm) CK(cudaEventRecord(s->ev[0], st));
   CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
-  // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce
-  s->launches += 1 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) +
+  // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
+  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) +
                  (trace_q_stack_cap(s->nint_s + s->nint_d) > 0 ? 1 : 0);
 
   TraceArgs a;
@@ -735,6 +772,7 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.capitems = s->capitems;
   a.nseg = s->nseg;
   a.queue = nullptr;
+  a.rx_moved = nullptr;
   a.queue_w = s->queue;
   a.restart = s->restart;
   a.nq_dev = &s->ctr->n_retrace;
@@ -815,6 +853,7 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
     CK(launch_mark(a, c, grid_cap_of(s, 8), st));
     CK(launch_carry(a, c, st));
     a.queue = s->queue;
+    a.rx_moved = s->rx_moved;
   }
   if (tm) CK(cudaEventRecord(s->ev[2], st));
   if (s->R > 0) CK(launch_trace(a, s->sms, st));
@@ -871,17 +910,14 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   if (tm) CK(cudaEventRecord(s->ev[6], st));
   CK(launch_reduce(q, nrx, st));
   if (tm) CK(cudaEventRecord(s->ev[7], st));
-  // state the next frame compares against
-  CK(cudaMemcpyAsync(s->prev_ncand, &s->ctr->n_cand, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
-  if (nrx) CK(cudaMemcpyAsync(s->rx_traced, s->rx_cur, sizeof(float4) * nrx, cudaMemcpyDeviceToDevice, st));
-  if (s->nobj) {
-    CK(cudaMemcpyAsync(s->xf_traced, s->xf_cur, sizeof(float) * 12 * s->nobj, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(s->obj_box_traced, s->obj_box_cur, sizeof(unsigned) * 6 * s->nobj,
-                       cudaMemcpyDeviceToDevice, st));
+  // state the next frame compares against, and the counters to the host
+  {
+    int n = std::max(nrx, 12 * s->nobj);
+    int g = std::max(1, std::min(64, (n + 255) / 256));
+    k_frame_end<<<g, 256, 0, st>>>(s->rx_cur, s->rx_traced, nrx, s->xf_cur, s->xf_traced, s->obj_box_cur,
+                                   s->obj_box_traced, s->nobj, s->ctr, s->uctr, s->prev_ncand, s->ctr_hd);
+    CK(cudaGetLastError());
   }
-  CK(cudaMemcpyAsync(s->ctr_h, s->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(s->ctr_h + 1, s->uctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemsetAsync(s->uctr, 0, sizeof(DevCounters), st));
   // with device outputs nothing follows on the stream: the frame ends here
   if (tm && out->ptr_kind == DCEM_PTR_DEVICE) CK(cudaEventRecord(s->ev[8], st));
   CK(cudaStreamSynchronize(st));

@@ -590,27 +590,39 @@ __global__ void k_transform_refit(const float4* __restrict__ objv, const float* 
 
 // ---------------------------------------------------------------------------
 // per frame, moving objects of up to kSmemRefit + 1 triangles: one CTA
-// transforms, (re)builds when asked, refits in shared memory and measures
-// the tree's surface-area cost
+// transforms, (re)builds when asked, refits level by level in shared memory
+// and measures the tree's surface-area cost
 // ---------------------------------------------------------------------------
+// After each (re)build the internal nodes are ordered by height (1 + the
+// larger child height, leaves 0), in node order within a height, and that
+// schedule is kept in global memory. A refit then needs no atomics: leaf
+// boxes first, then one height at a time with a barrier in between, every
+// node of a height formed from its children's boxes by one thread. The
+// surface-area sum runs in schedule order, so it is the same in every run.
+//
 // Shared-memory layout (n = nd leaves, m = n - 1 nodes, np2 = next power of
-// two >= n): keys[np2] (rebuild sort) | node boxes float[12 m] | arrivals
-// int[m] | topology int[3 m] (child 0, child 1, parent) | object boxes
-// unsigned[6 nobj].
+// two >= n): keys[np2] (rebuild sort; node heights afterwards) | leaf boxes
+// float[6 n] | node boxes float[6 m] | children int[2 m] | schedule int[m] |
+// level bounds int[kMaxLevels + 2] (lvl[h]..lvl[h + 1] = height h + 1) |
+// object boxes unsigned[6 nobj].
+constexpr int kMaxLevels = kDynLevels;
+
 __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
   extern __shared__ unsigned long long keys[];
   int tid = threadIdx.x, nt = blockDim.x;
   int n = a.nd, m = n > 1 ? n - 1 : 1;
   int np2 = 1;
   while (np2 < n) np2 <<= 1;
-  float* sbox = reinterpret_cast<float*>(keys + np2);
-  int* sarr = reinterpret_cast<int*>(sbox + 12 * (size_t)m);
-  int* stop = sarr + m;
-  unsigned* sobj = reinterpret_cast<unsigned*>(stop + 3 * (size_t)m);
+  float* lbox = reinterpret_cast<float*>(keys + np2);
+  float* nbox = lbox + 6 * (size_t)n;
+  int* kids = reinterpret_cast<int*>(nbox + 6 * (size_t)m);
+  int* sched = kids + 2 * (size_t)m;
+  int* lvl = sched + m;
+  unsigned* sobj = reinterpret_cast<unsigned*>(lvl + kMaxLevels + 2);
   __shared__ float sah_part[32];
   __shared__ unsigned bad;
+  __shared__ int nlvl, left;
   if (tid == 0) bad = 0u;
-  float sah = 0.0f;  // this thread's share of the node surface areas
   for (int k = tid; k < 6 * a.nobj; k += nt) sobj[k] = k < 3 * a.nobj ? 0xffffffffu : 0u;
   if (a.rebuild) {
     // world boxes of the primitives (primitive order), then a fresh topology
@@ -633,15 +645,82 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
       a.slot_of_id[gid] = slot;
     }
   }
-  // topology to shared memory (node-local indices; leaves stay as ~slot)
-  for (int i = tid; i < n - 1; i += nt) {
-    const int* n3 = reinterpret_cast<const int*>(a.nodes + 4 * (size_t)(a.node_base + i) + 3);
-    stop[3 * i] = n3[0];
-    stop[3 * i + 1] = n3[1];
-    stop[3 * i + 2] = n3[2];
-    sarr[i] = 0;
-  }
+  // children of every node (global codes: >= 0 node, < 0 leaf ~slot)
+  if (n > 1)
+    for (int i = tid; i < m; i += nt) {
+      const int* n3 = reinterpret_cast<const int*>(a.nodes + 4 * (size_t)(a.node_base + i) + 3);
+      kids[2 * i] = n3[0];
+      kids[2 * i + 1] = n3[1];
+    }
   __syncthreads();
+  if (a.rebuild && n > 1) {
+    // node heights by repeated passes (at most the tree height, <= 63 for
+    // 64-bit Karras keys), then the schedule
+    volatile int* hgt = reinterpret_cast<volatile int*>(keys);
+    for (int i = tid; i < m; i += nt) hgt[i] = -1;
+    if (tid == 0) left = m;
+    __syncthreads();
+    for (int pass = 0; pass < kMaxLevels && left > 0; ++pass) {
+      for (int i = tid; i < m; i += nt) {
+        if (hgt[i] >= 0) continue;
+        int c0 = kids[2 * i], c1 = kids[2 * i + 1];
+        int h0 = c0 < 0 ? 0 : hgt[c0 - a.node_base], h1 = c1 < 0 ? 0 : hgt[c1 - a.node_base];
+        if (h0 >= 0 && h1 >= 0) {
+          hgt[i] = 1 + max(h0, h1);
+          atomicSub(&left, 1);
+        }
+      }
+      __syncthreads();
+    }
+    if (left > 0) {  // deeper than kMaxLevels: a malformed tree
+      if (tid == 0) atomicOr(&a.uctr->err, ERR_STACK);
+      return;
+    }
+    // level starts: heights 1.. in increasing order
+    for (int h = tid; h < kMaxLevels + 2; h += nt) lvl[h] = 0;
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) atomicAdd(&lvl[hgt[i]], 1);  // lvl[h] = count of height h
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0, top = 0;
+      for (int h = 1; h <= kMaxLevels; ++h) {
+        int c = lvl[h];
+        lvl[h] = run;  // start of height h (levels indexed from 1)
+        run += c;
+        if (c) top = h;
+      }
+      lvl[kMaxLevels + 1] = run;
+      nlvl = top;
+    }
+    __syncthreads();
+    // stable scatter by height (warp 0, 32 nodes at a time)
+    if (tid < 32) {
+      for (int c = 0; c < m; c += 32) {
+        int i = c + tid;
+        int h = i < m ? hgt[i] : 0;
+        unsigned peers = __match_any_sync(0xffffffffu, h);
+        int rank = __popc(peers & ((1u << tid) - 1u));
+        if (i < m) sched[lvl[h] + rank] = i;
+        __syncwarp();
+        if (i < m && rank == 0) lvl[h] += __popc(peers);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // lvl[h] (h >= 1) now holds the end of height h, which is where height
+    // h + 1 starts; lvl[0] = 0 is where height 1 starts
+    if (tid == 0) lvl[0] = 0;
+    __syncthreads();
+    for (int k = tid; k < m; k += nt) a.sched[k] = sched[k];
+    for (int h = tid; h <= nlvl; h += nt) a.lvl[h] = lvl[h];
+    if (tid == 0) a.lvl[kMaxLevels + 1] = nlvl;
+  } else if (n > 1) {
+    for (int k = tid; k < m; k += nt) sched[k] = a.sched[k];
+    if (tid == 0) nlvl = a.lvl[kMaxLevels + 1];
+    __syncthreads();
+    for (int h = tid; h <= nlvl; h += nt) lvl[h] = a.lvl[h];
+  }
+  // world triangles, leaf boxes, object boxes
   for (int j = tid; j < n; j += nt) {
     const float4* q = a.objv + 3 * (size_t)j;
     int ob = __float_as_int(q[0].w);
@@ -653,7 +732,7 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
     t[0].x = w0.x; t[0].y = w0.y; t[0].z = w0.z;
     t[1].x = w1.x; t[1].y = w1.y; t[1].z = w1.z;
     t[2] = make_float4(w2.x, w2.y, w2.z, 0.0f);
-    float b[6];
+    float* b = lbox + 6 * (size_t)j;
     tri_box(w0, w1, w2, b);
     bool fin = true;
     for (int k = 0; k < 6; ++k) fin = fin && isfinite(b[k]);
@@ -662,37 +741,30 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
       atomicMin(&sobj[3 * ob + k], f2o(b[k]));
       atomicMax(&sobj[3 * (a.nobj + ob) + k], f2o(b[k + 3]));
     }
-    if (n == 1) {
-      for (int k = 0; k < 6; ++k) a.root_box[k] = b[k];
-      continue;
-    }
-    // walk up through shared memory
-    int code = ~slot;
-    int p = a.leaf_parent[slot];
-    for (int depth = 0; depth < 128 && p >= 0; ++depth) {
-      int li = p - a.node_base;
-      int side = stop[3 * li] == code ? 0 : 1;
-      volatile float* mine = sbox + 12 * (size_t)li + 6 * side;
-      for (int k = 0; k < 6; ++k) mine[k] = b[k];
-      __threadfence_block();
-      if (atomicAdd(&sarr[li], 1) == 0) break;
-      __threadfence_block();
-      volatile float* both = sbox + 12 * (size_t)li;
-      for (int k = 0; k < 3; ++k) {
-        b[k] = fminf(both[k], both[6 + k]);
-        b[k + 3] = fmaxf(both[k + 3], both[9 + k]);
-      }
-      sah += box_area(b);
-      code = p;
-      p = stop[3 * li + 2];
-      if (p < 0)
-        for (int k = 0; k < 6; ++k) a.root_box[k] = b[k];
-    }
   }
   __syncthreads();
-  for (int i = tid; i < n - 1; i += nt) {
-    put_child_box(a.nodes, a.node_base + i, 0, sbox + 12 * (size_t)i);
-    put_child_box(a.nodes, a.node_base + i, 1, sbox + 12 * (size_t)i + 6);
+  float sah = 0.0f;  // this thread's share of the node surface areas
+  if (n == 1) {
+    if (tid < 6) a.root_box[tid] = lbox[tid];
+  } else {
+    for (int h = 0; h < nlvl; ++h) {
+      for (int k = lvl[h] + tid; k < lvl[h + 1]; k += nt) {
+        int i = sched[k];
+        int c0 = kids[2 * i], c1 = kids[2 * i + 1];
+        const float* b0 = c0 < 0 ? lbox + 6 * (size_t)(~c0 - a.leaf_base) : nbox + 6 * (size_t)(c0 - a.node_base);
+        const float* b1 = c1 < 0 ? lbox + 6 * (size_t)(~c1 - a.leaf_base) : nbox + 6 * (size_t)(c1 - a.node_base);
+        put_child_box(a.nodes, a.node_base + i, 0, b0);
+        put_child_box(a.nodes, a.node_base + i, 1, b1);
+        float* u = nbox + 6 * (size_t)i;
+        for (int q = 0; q < 3; ++q) {
+          u[q] = fminf(b0[q], b1[q]);
+          u[q + 3] = fmaxf(b0[q + 3], b1[q + 3]);
+        }
+        sah += box_area(u);
+      }
+      __syncthreads();
+    }
+    if (tid < 6) a.root_box[tid] = nbox[tid];  // the Karras root is node 0
   }
   for (int k = tid; k < 6 * a.nobj; k += nt) a.obj_box[k] = sobj[k];
   for (int off = 16; off > 0; off >>= 1) sah += __shfl_down_sync(0xffffffffu, sah, off);
@@ -710,9 +782,7 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// compact copy of both trees for shared-memory traversal (QFrame layout in
-// dcem_internal.cuh). The frame is the union of the two root boxes padded by
-// 1 m + 0.1%; every child box is rounded outward by one 16-bit step.
+// compact copy of both trees for shared-memory traversal
 // ---------------------------------------------------------------------------
 // Codes are rounded outward by three steps: the FP32 quotient (v - o) / s is
 // within a small fraction of a step of the exact one, so the code box
@@ -892,9 +962,9 @@ void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int
 size_t dyn_update_smem(int nd, int nobj) {
   int np2 = 1;
   while (np2 < nd) np2 <<= 1;
-  size_t m = (size_t)(nd > 1 ? nd - 1 : 1);
-  return (size_t)np2 * sizeof(unsigned long long) + m * (12 * sizeof(float) + 4 * sizeof(int)) +
-         (size_t)6 * nobj * sizeof(unsigned);
+  size_t n = (size_t)(nd > 0 ? nd : 1), m = (size_t)(nd > 1 ? nd - 1 : 1);
+  return (size_t)np2 * sizeof(unsigned long long) + n * 6 * sizeof(float) + m * 6 * sizeof(float) +
+         m * 3 * sizeof(int) + (size_t)(kMaxLevels + 2) * sizeof(int) + (size_t)6 * nobj * sizeof(unsigned);
 }
 
 cudaError_t launch_dyn_update(const DynUpdateArgs& a, cudaStream_t st) {

@@ -102,8 +102,12 @@ struct DynUpdateArgs {
   unsigned* obj_box = nullptr;       // lo [0, 3 nobj), hi [3 nobj, 6 nobj) as ordered ints
   float* root_box = nullptr;
   int* root = nullptr;
+  int* sched = nullptr;              // nd - 1 node indices by height (kept between rebuilds)
+  int* lvl = nullptr;                // kDynLevels + 2: starts of each height, then their count
   DevCounters* uctr = nullptr;
 };
+constexpr int kDynLevels = 128;      // heights the scheduled refit handles (Karras trees over
+                                     // 64-bit keys have at most 63)
 cudaError_t launch_dyn_update(const DynUpdateArgs& a, cudaStream_t st);
 // Shared memory the one-CTA update needs (must stay within 227 KB).
 size_t dyn_update_smem(int nd, int nobj);

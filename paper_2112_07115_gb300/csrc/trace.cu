@@ -176,10 +176,11 @@ __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   trace_rays<true>(a, sq, f, st);
 }
 
-// Reception-sphere captures of the segments traced this frame (the list the
-// closest-hit kernel appends to, in tracing order, so a warp reads segments
-// of neighbouring rays). In a coherent frame reused segments were tested
-// against the moved receivers in k_mark.
+// Reception-sphere captures of the segments in the frame's capture list: the
+// segments traced this frame (appended by the closest-hit kernel in tracing
+// order, so a warp reads segments of neighbouring rays) and, in a coherent
+// frame, the reused segments (appended by k_mark), which only the receivers
+// that moved need to test.
 // Receivers and their tree copied to shared memory after the stacks (kS).
 __device__ __forceinline__ char* stage_receivers(const TraceArgs& a, char* p, const float4*& rx, SmallBvh& rxt) {
   float4* srx = reinterpret_cast<float4*>(p);
@@ -208,7 +209,8 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
     unsigned q = (unsigned)base + (threadIdx.x & 31);
     if (q < total) {
       unsigned it = a.capitems[q];
-      int ray = (int)(it >> 4), b = (int)(it & 15u);
+      bool reused = (it & 0x80000000u) != 0u;
+      int ray = (int)((it & 0x7fffffffu) >> 4), b = (int)(it & 15u);
       float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
       float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
       float D = lo.w, t = ld.w;
@@ -219,7 +221,9 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
       float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
       float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
       rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-      if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) { emit_cand(a, ray, b, r); }))
+      if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) {
+            if (!reused || a.rx_moved[r]) emit_cand(a, ray, b, r);
+          }))
         ovf = 1u;
     }
     __syncwarp();
@@ -235,70 +239,66 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
 // ---------------------------------------------------------------------------
 // One thread per ray (warps take 32 rays at a time): the first logged
 // segment that meets a moved box is the restart point; earlier segments are
-// reused and re-tested against the receivers that moved.
+// reused and, when receivers moved, appended to the capture list (flagged
+// reused). The warp walks segment index b in step so that the appends stay
+// one atomic per warp.
 template <bool kS>
 __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
   extern __shared__ __align__(16) int sstk[];
   TStack st;
   bind_stack(st, sstk, kStackSmall);
-  SmallBvh rxt = a.rxt;
-  const float4* rx = a.rx;
   SmallBvh mvt = c.mvt;
   // more moved boxes than the per-frame tree holds: retrace everything
   const unsigned nmb = c.ctr->n_moved_boxes;
-  bool all = nmb > (unsigned)c.mv_cap;
+  const bool all = nmb > (unsigned)c.mv_cap;
   if (kS) {
-    char* p = stage_receivers(a, reinterpret_cast<char*>(sstk + blockDim.x * kStackSmall), rx, rxt);
-    stage_tree(c.mvt, all ? 0 : max((int)nmb - 1, 0), 0, p, mvt);
+    stage_tree(c.mvt, all ? 0 : max((int)nmb - 1, 0), 0, reinterpret_cast<char*>(sstk + blockDim.x * kStackSmall),
+               mvt);
     __syncthreads();
   }
-  bool any_rx = c.ctr->rx_moved > 0;
+  const bool any_rx = c.ctr->rx_moved > 0;
   const int R = a.R;
+  const int lane = threadIdx.x & 31;
   unsigned long long reused = 0;
-  unsigned ovf = 0;
   for (;;) {
     int base = fetch_warp(&c.ctr->work_mark, 32u);
     if (base >= R) break;
-    int ray = base + (threadIdx.x & 31);
-    if (ray >= R) continue;
-    int ns = a.nseg[ray];
+    int ray = base + lane;
+    int ns = ray < R ? a.nseg[ray] : 0;
     int bstar = all ? 0 : ns;
-    for (int b = 0; b < bstar; ++b) {
-      float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
-      float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
-      float D = lo.w, t = ld.w;
-      RayPre rp;
-      rp.o = o;
-      float dx = fabsf(d.x) < 1e-30f ? copysignf(1e-30f, d.x) : d.x;
-      float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
-      float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
-      rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-      if (seg_hits_tree(mvt, rp, t, st)) {
-        bstar = b;
-        break;
+    for (int b = 0; b <= a.N; ++b) {
+      unsigned item = 0xffffffffu;
+      if (b < bstar) {
+        float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
+        RayPre rp;
+        rp.o = f3(lo.x, lo.y, lo.z);
+        float dx = fabsf(ld.x) < 1e-30f ? copysignf(1e-30f, ld.x) : ld.x;
+        float dy = fabsf(ld.y) < 1e-30f ? copysignf(1e-30f, ld.y) : ld.y;
+        float dz = fabsf(ld.z) < 1e-30f ? copysignf(1e-30f, ld.z) : ld.z;
+        rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
+        if (seg_hits_tree(mvt, rp, ld.w, st)) bstar = b;
+        else if (any_rx) item = 0x80000000u | ((unsigned)ray << 4) | (unsigned)b;
       }
-      if (any_rx) {
-        float tend = isinf(t) ? a.escape : t;
-        if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) {
-              if (c.rx_moved[r]) emit_cand(a, ray, b, r);
-            }))
-          ovf = 1u;
+      unsigned want = __ballot_sync(0xffffffffu, item != 0xffffffffu);
+      if (want) {
+        int leader = __ffs(want) - 1;
+        unsigned at = 0;
+        if (lane == leader) at = atomicAdd(&c.ctr->n_capitems, (unsigned)__popc(want));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (item != 0xffffffffu) a.capitems[at + __popc(want & ((1u << lane) - 1u))] = item;
       }
     }
-    c.restart[ray] = bstar;
-    reused += (unsigned long long)bstar;
-    if (bstar < ns) {
-      unsigned at = atomicAdd(&c.ctr->n_retrace, 1u);
-      a.queue_w[at] = ray;
+    if (ray < R) {
+      c.restart[ray] = bstar;
+      reused += (unsigned long long)bstar;
+      if (bstar < ns) {
+        unsigned at = atomicAdd(&c.ctr->n_retrace, 1u);
+        a.queue_w[at] = ray;
+      }
     }
   }
-  __syncwarp();
   for (int off = 16; off > 0; off >>= 1) reused += __shfl_down_sync(0xffffffffu, reused, off);
-  if ((threadIdx.x & 31) == 0 && reused) atomicAdd(&c.ctr->segments_reused, reused);
-  if (ovf) {
-    atomicAdd(&c.ctr->stack_overflow, 1u);
-    atomicOr(&c.ctr->err, ERR_STACK);
-  }
+  if (lane == 0 && reused) atomicAdd(&c.ctr->segments_reused, reused);
 }
 
 // Previous frame's captures by receivers that did not move, from segments
@@ -386,8 +386,8 @@ cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st) {
 
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st) {
   size_t base = 256 * kStackSmall * sizeof(int);
-  size_t staged = base + rx_stage_bytes(a.nrx) + stage_bytes(c.mv_cap > 1 ? c.mv_cap - 1 : 0, 0);
-  bool kS = a.nrx <= 1024 && staged <= kStageLimit;
+  size_t staged = base + stage_bytes(c.mv_cap > 1 ? c.mv_cap - 1 : 0, 0);
+  bool kS = staged <= kStageLimit;
   size_t smem = kS ? staged : base;
   cudaError_t e = allow_smem(kS ? (const void*)k_mark<true> : (const void*)k_mark<false>, smem);
   if (e != cudaSuccess) return e;

@@ -22,7 +22,9 @@ struct TraceArgs {
   float4* log_o;           // (N+1) x R: origin, unfolded length D
   float4* log_d;           // (N+1) x R: direction, hit t (+inf escaped)
   int* log_id;             // (N+1) x R: hit triangle id or -1
-  unsigned* capitems;      // (N+1) x R capacity: traced segments, ray << 4 | segment
+  unsigned* capitems;      // (N+1) x R capacity: segments to capture-test, ray << 4 | segment,
+                           // bit 31 set: reused segment, test only the moved receivers
+  const unsigned char* rx_moved;  // coherent frame: nrx flags (null in a full frame)
   int* nseg;               // R
   const int* queue;        // retrace queue (null: all rays from segment 0)
   int* queue_w;            // retrace queue written by the marking kernel
