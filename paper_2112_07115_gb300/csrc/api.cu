@@ -76,14 +76,17 @@ __global__ void k_frame_end(const float4* __restrict__ rx_cur, float4* rx_traced
   }
 }
 
+// Object-space vertices of the moving triangles: (v0, object), (v1, triangle
+// id), (v2, material); the last two are the .w of the world triangle record.
 __global__ void k_objv_src(const float* __restrict__ v9, const int* __restrict__ sel,
-                           const int* __restrict__ tri_obj, int n, float4* objv_src) {
+                           const int* __restrict__ tri_obj, const int* __restrict__ tri_mat, int n,
+                           float4* objv_src) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int gid = sel[i];
     const float* v = v9 + 9 * (size_t)gid;
     objv_src[3 * (size_t)i] = make_float4(v[0], v[1], v[2], __int_as_float(tri_obj[gid]));
-    objv_src[3 * (size_t)i + 1] = make_float4(v[3], v[4], v[5], 0.0f);
-    objv_src[3 * (size_t)i + 2] = make_float4(v[6], v[7], v[8], 0.0f);
+    objv_src[3 * (size_t)i + 1] = make_float4(v[3], v[4], v[5], __int_as_float(gid));
+    objv_src[3 * (size_t)i + 2] = make_float4(v[6], v[7], v[8], __int_as_float(tri_mat[gid]));
   }
 }
 
@@ -591,7 +594,7 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   // moving objects: identity transforms until the first update
   if (s->nd) {
     int g = (s->nd + 255) / 256;
-    k_objv_src<<<g, 256, 0, st>>>(v9, s->sel_d, tri_obj_d, s->nd, s->objv_src);
+    k_objv_src<<<g, 256, 0, st>>>(v9, s->sel_d, tri_obj_d, s->tri_mat_d, s->nd, s->objv_src);
     CKF(cudaGetLastError());
   }
   if (nobj) {

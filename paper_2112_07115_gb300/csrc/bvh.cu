@@ -543,8 +543,8 @@ __global__ void k_place_tris(const float* __restrict__ v9, const int* __restrict
       float4* q = objv + 3 * (size_t)j;
       int ob = tri_obj[gid];
       q[0] = make_float4(v[0], v[1], v[2], __int_as_float(ob));
-      q[1] = make_float4(v[3], v[4], v[5], 0.0f);
-      q[2] = make_float4(v[6], v[7], v[8], 0.0f);
+      q[1] = make_float4(v[3], v[4], v[5], __int_as_float(gid));
+      q[2] = make_float4(v[6], v[7], v[8], __int_as_float(tri_mat[gid]));
     }
     slot_of_id[gid] = slot;
   }
@@ -645,13 +645,19 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
       a.slot_of_id[gid] = slot;
     }
   }
-  // children of every node (global codes: >= 0 node, < 0 leaf ~slot)
-  if (n > 1)
+  // children of every node (global codes: >= 0 node, < 0 leaf ~slot); on a
+  // refit also the kept schedule, in the same round of loads
+  if (n > 1) {
     for (int i = tid; i < m; i += nt) {
-      const int* n3 = reinterpret_cast<const int*>(a.nodes + 4 * (size_t)(a.node_base + i) + 3);
-      kids[2 * i] = n3[0];
-      kids[2 * i + 1] = n3[1];
+      int2 c = *reinterpret_cast<const int2*>(a.nodes + 4 * (size_t)(a.node_base + i) + 3);
+      kids[2 * i] = c.x;
+      kids[2 * i + 1] = c.y;
     }
+    if (!a.rebuild) {
+      for (int k = tid; k < m; k += nt) sched[k] = a.sched[k];
+      for (int h = tid; h < kMaxLevels + 2; h += nt) lvl[h] = a.lvl[h];
+    }
+  }
   __syncthreads();
   if (a.rebuild && n > 1) {
     // node heights by repeated passes (at most the tree height, <= 63 for
@@ -715,22 +721,22 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
     for (int h = tid; h <= nlvl; h += nt) a.lvl[h] = lvl[h];
     if (tid == 0) a.lvl[kMaxLevels + 1] = nlvl;
   } else if (n > 1) {
-    for (int k = tid; k < m; k += nt) sched[k] = a.sched[k];
-    if (tid == 0) nlvl = a.lvl[kMaxLevels + 1];
-    __syncthreads();
-    for (int h = tid; h <= nlvl; h += nt) lvl[h] = a.lvl[h];
+    if (tid == 0) nlvl = lvl[kMaxLevels + 1];
   }
-  // world triangles, leaf boxes, object boxes
+  // world triangles (whole 16-byte records), leaf boxes, object boxes
   for (int j = tid; j < n; j += nt) {
     const float4* q = a.objv + 3 * (size_t)j;
-    int ob = __float_as_int(q[0].w);
-    const float* mx = a.xf + 12 * (size_t)ob;
-    float3 w0 = xform(mx, f3(q[0].x, q[0].y, q[0].z)), w1 = xform(mx, f3(q[1].x, q[1].y, q[1].z)),
-           w2 = xform(mx, f3(q[2].x, q[2].y, q[2].z));
+    float4 q0 = q[0], q1 = q[1], q2 = q[2];
+    int ob = __float_as_int(q0.w);
+    const float4* mx4 = reinterpret_cast<const float4*>(a.xf + 12 * (size_t)ob);
+    float4 r0 = mx4[0], r1 = mx4[1], r2 = mx4[2];
+    float mx[12] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w};
+    float3 w0 = xform(mx, f3(q0.x, q0.y, q0.z)), w1 = xform(mx, f3(q1.x, q1.y, q1.z)),
+           w2 = xform(mx, f3(q2.x, q2.y, q2.z));
     int slot = a.leaf_base + j;
     float4* t = a.tris + 3 * (size_t)slot;
-    t[0].x = w0.x; t[0].y = w0.y; t[0].z = w0.z;
-    t[1].x = w1.x; t[1].y = w1.y; t[1].z = w1.z;
+    t[0] = make_float4(w0.x, w0.y, w0.z, q1.w);
+    t[1] = make_float4(w1.x, w1.y, w1.z, q2.w);
     t[2] = make_float4(w2.x, w2.y, w2.z, 0.0f);
     float* b = lbox + 6 * (size_t)j;
     tri_box(w0, w1, w2, b);
@@ -753,8 +759,6 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
         int c0 = kids[2 * i], c1 = kids[2 * i + 1];
         const float* b0 = c0 < 0 ? lbox + 6 * (size_t)(~c0 - a.leaf_base) : nbox + 6 * (size_t)(c0 - a.node_base);
         const float* b1 = c1 < 0 ? lbox + 6 * (size_t)(~c1 - a.leaf_base) : nbox + 6 * (size_t)(c1 - a.node_base);
-        put_child_box(a.nodes, a.node_base + i, 0, b0);
-        put_child_box(a.nodes, a.node_base + i, 1, b1);
         float* u = nbox + 6 * (size_t)i;
         for (int q = 0; q < 3; ++q) {
           u[q] = fminf(b0[q], b1[q]);
@@ -765,6 +769,16 @@ __global__ void __launch_bounds__(1024) k_dyn_update(DynUpdateArgs a) {
       __syncthreads();
     }
     if (tid < 6) a.root_box[tid] = nbox[tid];  // the Karras root is node 0
+    // child boxes into the node records, three 16-byte stores per node
+    for (int i = tid; i < m; i += nt) {
+      int c0 = kids[2 * i], c1 = kids[2 * i + 1];
+      const float* b0 = c0 < 0 ? lbox + 6 * (size_t)(~c0 - a.leaf_base) : nbox + 6 * (size_t)(c0 - a.node_base);
+      const float* b1 = c1 < 0 ? lbox + 6 * (size_t)(~c1 - a.leaf_base) : nbox + 6 * (size_t)(c1 - a.node_base);
+      float4* nd = a.nodes + 4 * (size_t)(a.node_base + i);
+      nd[0] = make_float4(b0[0], b0[3], b0[1], b0[4]);
+      nd[1] = make_float4(b1[0], b1[3], b1[1], b1[4]);
+      nd[2] = make_float4(b0[2], b0[5], b1[2], b1[5]);
+    }
   }
   for (int k = tid; k < 6 * a.nobj; k += nt) a.obj_box[k] = sobj[k];
   for (int off = 16; off > 0; off >>= 1) sah += __shfl_down_sync(0xffffffffu, sah, off);
