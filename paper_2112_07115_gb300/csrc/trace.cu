@@ -291,10 +291,16 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     if (ray < R) {
       c.restart[ray] = bstar;
       reused += (unsigned long long)bstar;
-      if (bstar < ns) {
-        unsigned at = atomicAdd(&c.ctr->n_retrace, 1u);
-        a.queue_w[at] = ray;
-      }
+    }
+    // retrace queue: one atomic per warp, the warp's rays kept in direction order
+    bool rq = ray < R && bstar < ns;
+    unsigned want = __ballot_sync(0xffffffffu, rq);
+    if (want) {
+      int leader = __ffs(want) - 1;
+      unsigned at = 0;
+      if (lane == leader) at = atomicAdd(&c.ctr->n_retrace, (unsigned)__popc(want));
+      at = __shfl_sync(0xffffffffu, at, leader);
+      if (rq) a.queue_w[at + __popc(want & ((1u << lane) - 1u))] = ray;
     }
   }
   for (int off = 16; off > 0; off >>= 1) reused += __shfl_down_sync(0xffffffffu, reused, off);
