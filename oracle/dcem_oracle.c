@@ -100,21 +100,11 @@ typedef struct {
 typedef struct {
   int ntri;
   otri* t;
-  const float* mats;  /* nmat x 3: eps_r, sigma, pec */
+  double* mats;  /* nmat x 3: eps_r, sigma, pec (owned copy) */
   int nmat;
 } oscene;
 
-static int scene_load(oscene* s, const float* tris, const int32_t* tri_mat, int ntri,
-                      const float* mats, int nmat) {
-  s->ntri = ntri;
-  s->mats = mats;
-  s->nmat = nmat;
-  s->t = (otri*)calloc((size_t)(ntri > 0 ? ntri : 1), sizeof(otri));
-  if (!s->t) return -1;
-  for (int i = 0; i < ntri; ++i) {
-    otri* T = &s->t[i];
-    for (int k = 0; k < 3; ++k)
-      T->v[k] = mk(tris[9 * i + 3 * k], tris[9 * i + 3 * k + 1], tris[9 * i + 3 * k + 2]);
+static void tri_setup(otri* T) {
     T->e[0] = sub(T->v[1], T->v[0]);
     T->e[1] = sub(T->v[2], T->v[1]);
     T->e[2] = sub(T->v[0], T->v[2]);
@@ -122,12 +112,35 @@ static int scene_load(oscene* s, const float* tris, const int32_t* tri_mat, int 
     T->n = cross(sub(T->v[1], T->v[0]), sub(T->v[2], T->v[0]));
     double nn = norm(T->n);
     T->nh = nn > 0 ? scl(T->n, 1.0 / nn) : mk(0, 0, 0);
+}
+
+/* Exactly one of tris / tris_d (vertices) and of mats / mats_d is given. */
+static int scene_load_any(oscene* s, const float* tris, const double* tris_d, const int32_t* tri_mat,
+                          int ntri, const float* mats, const double* mats_d, int nmat) {
+  s->ntri = ntri;
+  s->nmat = nmat;
+  s->t = (otri*)calloc((size_t)(ntri > 0 ? ntri : 1), sizeof(otri));
+  s->mats = (double*)calloc((size_t)(nmat > 0 ? 3 * nmat : 3), sizeof(double));
+  if (!s->t || !s->mats) return -1;
+  for (int i = 0; i < 3 * nmat; ++i) s->mats[i] = mats_d ? mats_d[i] : (double)mats[i];
+  for (int i = 0; i < ntri; ++i) {
+    otri* T = &s->t[i];
+    for (int k = 0; k < 3; ++k)
+      T->v[k] = tris_d ? mk(tris_d[9 * i + 3 * k], tris_d[9 * i + 3 * k + 1], tris_d[9 * i + 3 * k + 2])
+                       : mk(tris[9 * i + 3 * k], tris[9 * i + 3 * k + 1], tris[9 * i + 3 * k + 2]);
+    tri_setup(T);
     T->mat = tri_mat ? tri_mat[i] : 0;
   }
   return 0;
 }
 
-static void scene_free(oscene* s) { free(s->t); }
+/* FP32 world triangles and materials widened to FP64 */
+static int scene_load(oscene* s, const float* tris, const int32_t* tri_mat, int ntri,
+                      const float* mats, int nmat) {
+  return scene_load_any(s, tris, NULL, tri_mat, ntri, mats, NULL, nmat);
+}
+
+static void scene_free(oscene* s) { free(s->t); free(s->mats); }
 
 static int default_threads(int req) {
   if (req > 0) return req;
@@ -181,15 +194,15 @@ static void fresnel64(double eps_r, double sigma, int pec, double freq, double c
   *g_tm = (ec * cos_t - root) / (ec * cos_t + root);
 }
 
-/* material row (eps_r, sigma, pec) as stored in FP32 */
-static void fresnel(const float* mat, double freq, double cos_t, double complex* g_te,
+/* material row (eps_r, sigma, pec) */
+static void fresnel(const double* mat, double freq, double cos_t, double complex* g_te,
                     double complex* g_tm) {
-  fresnel64((double)mat[0], (double)mat[1], mat[2] != 0.0f, freq, cos_t, g_te, g_tm);
+  fresnel64(mat[0], mat[1], mat[2] != 0.0, freq, cos_t, g_te, g_tm);
 }
 
 void or_fresnel(double eps_r, double sigma, int32_t pec, double freq, double cos_t,
                 double* out4) {
-  float m[3] = {(float)eps_r, (float)sigma, (float)pec};
+  double m[3] = {(double)(float)eps_r, (double)(float)sigma, (double)pec};
   double complex te, tm;
   fresnel(m, freq, cos_t, &te, &tm);
   out4[0] = creal(te); out4[1] = cimag(te);
@@ -536,8 +549,11 @@ static v3 pol_dir(v3 u, v3 d, uint32_t* fl) {
   return scl(p, 1.0 / n);
 }
 
+/* Sec. III steps 3, 4 and 6 for one candidate: image sources, back-trace,
+ * reflection points inside their triangles, (if check_occ) unoccluded
+ * sub-segments, then the path length and complex amplitude. */
 static void validate_one(const oscene* S, const or_params* P, v3 tx, v3 rx, int k,
-                         const int32_t* ids, opath* out) {
+                         const int32_t* ids, opath* out, int check_occ) {
   memset(out, 0, sizeof(*out));
   uint32_t fl = 0;
   for (int j = 0; j < k; ++j)
@@ -581,7 +597,7 @@ static void validate_one(const oscene* S, const or_params* P, v3 tx, v3 rx, int 
   double L = 0;
   for (int j = 0; j <= k; ++j) L += norm(sub(X[j + 1], X[j]));
   if (!(L > 0)) { out->valid = 0; out->flags = fl; return; }
-  for (int j = 0; j <= k; ++j) {
+  for (int j = 0; check_occ && j <= k; ++j) {
     int ex0 = j >= 1 ? ids[j - 1] : -1;
     int ex1 = j + 1 <= k ? ids[j] : -1;
     if (occluded(S, X[j], X[j + 1], ex0, ex1, P, scale + L, &fl)) ok = 0;
@@ -658,7 +674,7 @@ static void* val_worker(void* p) {
       const int32_t* kk = &J->keys[(size_t)i * J->stride];
       int r = kk[0], depth = kk[1];
       v3 R = mk(J->rx[3 * r], J->rx[3 * r + 1], J->rx[3 * r + 2]);
-      validate_one(J->S, J->P, J->tx, R, depth, kk + 2, &J->out[i]);
+      validate_one(J->S, J->P, J->tx, R, depth, kk + 2, &J->out[i], 1);
     }
   }
   return NULL;
@@ -681,6 +697,28 @@ int or_validate(const float* tris, const int32_t* tri_mat, int32_t ntri, const f
   for (int k = 0; k < nt; ++k) pthread_create(&th[k], NULL, val_worker, &J);
   for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
   free(th);
+  scene_free(&S);
+  return 0;
+}
+
+/* Path amplitude of fixed triangle sequences (keys as in or_validate) with
+ * FP64 vertices (ntri x 9), materials (nmat x 3), Tx and receivers: the same
+ * steps without the occlusion test, for derivatives of the field by central
+ * differences over a fixed path topology. */
+int or_path_amp_d(const double* tris, const int32_t* tri_mat, int32_t ntri, const double* mats,
+                  int32_t nmat, const double* tx, const double* rx, int32_t nrx, const int32_t* keys,
+                  int64_t nkeys, const or_params* P, opath* out) {
+  if (P->max_refl < 0 || P->max_refl > OR_MAX_REFL) return -1;
+  oscene S;
+  if (scene_load_any(&S, NULL, tris, tri_mat, ntri, NULL, mats, nmat)) return -2;
+  int stride = 2 + P->max_refl;
+  for (int64_t i = 0; i < nkeys; ++i) {
+    const int32_t* kk = &keys[(size_t)i * stride];
+    int r = kk[0];
+    if (r < 0 || r >= nrx) { memset(&out[i], 0, sizeof(opath)); continue; }
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    validate_one(&S, P, mk(tx[0], tx[1], tx[2]), R, kk[1], kk + 2, &out[i], 0);
+  }
   scene_free(&S);
   return 0;
 }
@@ -712,7 +750,7 @@ int64_t or_exhaustive(const float* tris, const int32_t* tri_mat, int32_t ntri, c
         for (int j = 1; j < k; ++j)
           if (ids[j] == ids[j - 1]) { okseq = 0; break; }
         if (okseq) {
-          validate_one(&S, P, mk(tx[0], tx[1], tx[2]), R, k, ids, &tmp);
+          validate_one(&S, P, mk(tx[0], tx[1], tx[2]), R, k, ids, &tmp, 1);
           if (tmp.valid) {
             if (nvalid < cap) {
               int32_t* kk = &keys_out[(size_t)nvalid * stride];

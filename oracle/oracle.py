@@ -17,6 +17,11 @@ Pipeline of one frame (arXiv 2112.07115, Sec. III):
                  occlusion; length, delay, Fresnel TE/TM, complex amplitude
   reduce      -> received power per receiver: coherent P_t |sum a|^2 and
                  incoherent P_t sum |a|^2 in dBm, summed in sorted key order.
+  gradient    -> derivatives of the per-receiver field over a fixed path
+                 topology with respect to each material's (eps_r, sigma) and
+                 each rigid object's (x, y) translation, by FP64 central
+                 differences of the same amplitude computation (without the
+                 occlusion test, since the paths are given).
 """
 from __future__ import annotations
 
@@ -86,6 +91,9 @@ def lib():
         _lib.or_exhaustive.argtypes = [f32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                        P(_Params), i32, C.c_void_p, C.c_int64]
         _lib.or_exhaustive.restype = C.c_int64
+        _lib.or_path_amp_d.argtypes = [f64, i32, C.c_int32, f64, C.c_int32, f64, f64, C.c_int32,
+                                       i32, C.c_int64, P(_Params), C.c_void_p]
+        _lib.or_path_amp_d.restype = C.c_int
         _lib.or_fresnel.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double, f64]
         _lib.or_fresnel64.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double, f64]
         _lib.or_free.argtypes = [C.c_void_p]
@@ -272,6 +280,95 @@ def reduce(keys: np.ndarray, paths: np.ndarray, nrx: int, tx_power_w: float):
         field[r] += a
         inc[r] += abs(a) ** 2
     return field, dbm(tx_power_w * np.abs(field) ** 2), dbm(tx_power_w * inc)
+
+
+def path_amp_d(tris, tri_mat, materials, tx, rx, keys, prm: OracleParams) -> np.ndarray:
+    """Steps 3, 4 and 6 for fixed triangle sequences with FP64 vertices,
+    materials, Tx and receivers, without the occlusion test (the topology is
+    given): PATH_DTYPE records whose ``valid`` is the geometric validity."""
+    wt = np.ascontiguousarray(tris, np.float64).reshape(-1, 9)
+    mats = np.ascontiguousarray(materials, np.float64).reshape(-1, 3)
+    rx = np.ascontiguousarray(rx, np.float64).reshape(-1, 3)
+    keys = _i32(keys).reshape(-1, 2 + prm.max_refl)
+    out = np.zeros(keys.shape[0], PATH_DTYPE)
+    prm_c = prm.c()
+    rc = lib().or_path_amp_d(_p(wt, C.c_double), _p(_i32(tri_mat), C.c_int32), wt.shape[0],
+                             _p(mats, C.c_double), mats.shape[0],
+                             _p(np.ascontiguousarray(tx, np.float64), C.c_double), _p(rx, C.c_double),
+                             rx.shape[0], _p(keys, C.c_int32), keys.shape[0], C.byref(prm_c),
+                             out.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        raise RuntimeError(f"or_path_amp_d failed: {rc}")
+    return out
+
+
+def field_of(keys, paths, nrx) -> np.ndarray:
+    """Per-receiver sum of the amplitudes of the rows marked valid, in key order."""
+    e = np.zeros(nrx, np.complex128)
+    for i in range(keys.shape[0]):
+        if paths["valid"][i]:
+            e[int(keys[i, 0])] += complex(paths["amp_re"][i], paths["amp_im"][i])
+    return e
+
+
+def field_gradient(world_tris, tri_mat, tri_obj, materials, tx, rx, keys, prm: OracleParams,
+                   nobj: int, h_pos: float = 1e-6, h_mat: float = 1e-6):
+    """Derivatives of the per-receiver field E = sum a over a fixed set of
+    paths (``keys``) by central differences in FP64, with respect to
+    theta = (eps_r, sigma) of every material, then (x, y) translations of
+    every rigid object (all its triangles moved together), in that order.
+
+    Returns (E, dE, ok): E (nrx,) complex at theta, dE (nrx, 2 nmat + 2 nobj)
+    complex, ok (nkeys,) -- the keys whose geometric validity is the same at
+    theta and at every perturbed point (only those enter E and dE)."""
+    wt = np.ascontiguousarray(world_tris, np.float64).reshape(-1, 3, 3)
+    mats = np.ascontiguousarray(materials, np.float64).reshape(-1, 3)
+    tri_obj = np.asarray(tri_obj)
+    rx = np.ascontiguousarray(rx, np.float64).reshape(-1, 3)
+    nrx, nmat = rx.shape[0], mats.shape[0]
+    base = path_amp_d(wt, tri_mat, mats, tx, rx, keys, prm)
+    ok = base["valid"] != 0
+    evals = []
+    for m in range(nmat):
+        for c in range(2):
+            h = h_mat * max(1.0, abs(mats[m, c]))
+            mp, mm = mats.copy(), mats.copy()
+            mp[m, c] += h
+            mm[m, c] -= h
+            evals.append((h, (wt, mp), (wt, mm)))
+    for o in range(nobj):
+        sel = tri_obj == o
+        for c in range(2):
+            tp, tm = wt.copy(), wt.copy()
+            tp[sel, :, c] += h_pos
+            tm[sel, :, c] -= h_pos
+            evals.append((h_pos, (tp, mats), (tm, mats)))
+    res = []
+    for h, (tp, mp), (tm, mm) in evals:
+        pp = path_amp_d(tp, tri_mat, mp, tx, rx, keys, prm)
+        pm = path_amp_d(tm, tri_mat, mm, tx, rx, keys, prm)
+        ok &= (pp["valid"] != 0) & (pm["valid"] != 0)
+        res.append((h, pp, pm))
+    sel = base.copy()
+    sel["valid"] = ok
+    e = field_of(keys, sel, nrx)
+    de = np.zeros((nrx, len(res)), np.complex128)
+    for i, (h, pp, pm) in enumerate(res):
+        pp = pp.copy()
+        pm = pm.copy()
+        pp["valid"] = ok
+        pm["valid"] = ok
+        de[:, i] = (field_of(keys, pp, nrx) - field_of(keys, pm, nrx)) / (2.0 * h)
+    return e, de, ok
+
+
+def pcoh_dbm_gradient(e, de, tx_power_w):
+    """d P_coh[dBm] / d theta from E and dE: P = P_t |E|^2, so dP = 2 P_t
+    Re(conj(E) dE) and d(dBm) = 10 / ln 10 * dP / P."""
+    p = tx_power_w * np.abs(e) ** 2
+    dp = 2.0 * tx_power_w * np.real(np.conj(e)[:, None] * de)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return (10.0 / np.log(10.0)) * dp / p[:, None]
 
 
 @dataclass
