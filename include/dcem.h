@@ -253,6 +253,42 @@ int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t*
 
 /* ---- received power without device allocation ---- */
 
+/* Number of parameters dcem_path_gradients differentiates by:
+ * 2 * (materials) + 2 * (rigid objects). */
+int dcem_scene_gradient_size(const dcem_scene* s, int32_t* n_params);
+
+/* Derivatives of the received field over a fixed set of paths (a frame's
+ * path topology) with respect to every material's relative permittivity
+ * eps_r and conductivity sigma and every rigid object's translation in x and
+ * y. The amplitude of each path is recomputed from the scene's current world
+ * triangles as in Sec. III steps 3, 4 and 6 -- image sources, back-trace,
+ * Fresnel reflection with vector polarisation, the amplitude of Eq. 1 with
+ * the spreading of Eq. 3 -- in FP64 with forward-mode derivatives, without
+ * the occlusion test (the paths are given). Translating an object moves all
+ * its triangles; a material enters through eps_c = eps_r - j sigma/(w eps0).
+ *   tx          host, 3 floats
+ *   rx          nrx x 3 floats (host or device per rx_ptr_kind)
+ *   paths       n_paths records (host or device per ptr_kind) grouped by
+ *               receiver in non-decreasing rx order, as dcem_trace_frame
+ *               writes them; rx, depth and tri[0..depth) are read
+ *   params      freq_hz, tx_power_w, pol, max_refl (>= every path's depth)
+ *   field       nrx x 2 (re, im) of sum a over the paths, or NULL
+ *   dfield      nrx x n_params x 2 (re, im) of d(sum a)/d theta, theta in
+ *               the order eps_r(0), sigma(0), eps_r(1), sigma(1), ...,
+ *               x(0), y(0), x(1), y(1), ... (materials, then objects)
+ *   dpcoh_dbm   nrx x n_params of d P_coh[dBm] / d theta, or NULL
+ *               (0 for a receiver without paths)
+ * The outputs are host or device per ptr_kind, caller-owned. Perfect
+ * conductors have no material derivative. Sums run in path order, so
+ * repeated calls give identical results. The call synchronises the scene
+ * stream. Errors: DCEM_ERR_ARG (null or out-of-range arguments, paths not
+ * grouped by receiver, a depth above max_refl, a triangle id out of range, a
+ * triangle sequence without reflection geometry), DCEM_ERR_NONFINITE,
+ * DCEM_ERR_CUDA. */
+int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                        const dcem_path* paths, int32_t n_paths, const dcem_params* params, int32_t ptr_kind,
+                        double* field, double* dfield, double* dpcoh_dbm);
+
 /* Per-receiver sum of given path records, with no device allocation. The
  * paper has no counterpart of this call. It is for callers that cannot
  * allocate device memory when they need the result: a host framework that

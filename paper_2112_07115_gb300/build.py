@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdcem.so")
-SOURCES = ["api.cu", "bvh.cu", "trace.cu", "paths.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "bvh.cu", "trace.cu", "paths.cu", "grad.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", f"-I{INCLUDE}", "--expt-relaxed-constexpr"]

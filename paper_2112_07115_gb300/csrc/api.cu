@@ -9,6 +9,7 @@
 
 #include "bvh.cuh"
 #include "paths.cuh"
+#include "grad.cuh"
 #include "trace.cuh"
 
 using namespace dcem;
@@ -177,6 +178,15 @@ struct dcem_scene {
   uint4* qnodes = nullptr;       // compact node copy for shared-memory traversal
   float* qframe = nullptr;
   int* leaf_parent = nullptr;
+  int* tri_obj_d = nullptr;  // triangle id -> rigid object (-1 static)
+  double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
+  int* g_param = nullptr;      // staged outputs and the error flag (dcem_path_gradients)
+  double* g_out = nullptr;
+  unsigned* g_err = nullptr;
+  size_t g_items_cap = 0, g_out_cap = 0;
+  dcem_path* g_paths = nullptr;
+  float4* g_rx = nullptr;
+  size_t g_paths_cap = 0, g_rx_cap = 0;
   int* dsched = nullptr;  // moving-object tree: nodes by height, and the height bounds
   int* dlvl = nullptr;
   int* arrive = nullptr;
@@ -267,7 +277,9 @@ void scene_free(dcem_scene* s) {
   cudaStreamSynchronize(s->st);
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe); dfree(s->leaf_parent); dfree(s->arrive);
-  dfree(s->dsched); dfree(s->dlvl);
+  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d);
+  dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
+  dfree(s->g_rx);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
   dfree(s->xf_cur); dfree(s->xf_traced); dfree(s->obj_box_cur); dfree(s->obj_box_traced);
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
@@ -516,9 +528,9 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   int nmax = s->ns > s->nd ? s->ns : s->nd;
 
   float* v9 = nullptr;
-  int *tri_obj_d = nullptr, *sel_s_d = nullptr;
+  int* sel_s_d = nullptr;
   auto fail2 = [&](int code) {
-    dfree(v9); dfree(tri_obj_d); dfree(sel_s_d);
+    dfree(v9); dfree(sel_s_d);
     return fail(code);
   };
 #define CKF(x)                                  \
@@ -569,7 +581,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(cudaHostGetDevicePointer((void**)&s->ctr_hd, s->ctr_h, 0));
   if ((rc = alloc_build_scratch(s, nmax)) != DCEM_OK) return fail2(rc);
   CKF(dalloc(&v9, 9 * (size_t)ntri));
-  CKF(dalloc(&tri_obj_d, ntri));
+  CKF(dalloc(&s->tri_obj_d, ntri));
+  int* tri_obj_d = s->tri_obj_d;
   CKF(dalloc(&sel_s_d, s->ns));
   cudaStream_t st = s->st;
   if (ntri > 0) {
@@ -625,7 +638,7 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   s->root_h[1] = root_code(s->nd, s->nint_s, s->ns);
   CKF(cudaStreamSynchronize(st));
   for (auto& ev : s->ev) CKF(cudaEventCreate(&ev));
-  dfree(v9); dfree(tri_obj_d); dfree(sel_s_d);
+  dfree(v9); dfree(sel_s_d);
 #undef CKF
   *out = s;
   return DCEM_OK;
@@ -1066,6 +1079,118 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   if (err & ERR_STACK) return DCEM_ERR_STACK;
   if (nvalid > out->max_paths && out->paths) return DCEM_ERR_CAPACITY;
   return DCEM_OK;
+}
+
+int dcem_scene_gradient_size(const dcem_scene* s, int32_t* n_params) {
+  if (!s || !n_params) return DCEM_ERR_ARG;
+  *n_params = grad_nparam(s->nmat, s->nobj);
+  return DCEM_OK;
+}
+
+int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                        const dcem_path* paths, int32_t n_paths, const dcem_params* p, int32_t ptr_kind,
+                        double* field, double* dfield, double* dpcoh_dbm) {
+  if (!s || !tx || !p) return DCEM_ERR_ARG;
+  if (nrx < 0 || nrx > kSmallBuild || (nrx > 0 && (!rx || !dfield)) || n_paths < 0 || (n_paths > 0 && !paths))
+    return DCEM_ERR_ARG;
+  if (rx_ptr_kind != DCEM_PTR_HOST && rx_ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
+  if (ptr_kind != DCEM_PTR_HOST && ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
+  if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
+  if (!(p->freq_hz > 0) || !std::isfinite(p->freq_hz) || !(p->tx_power_w > 0) || !std::isfinite(p->tx_power_w))
+    return DCEM_ERR_ARG;
+  if (!finite_arr(p->pol, 3) || !(p->pol[0] * p->pol[0] + p->pol[1] * p->pol[1] + p->pol[2] * p->pol[2] > 0))
+    return DCEM_ERR_ARG;
+  if (!finite_arr(tx, 3)) return DCEM_ERR_NONFINITE;
+  if (rx_ptr_kind == DCEM_PTR_HOST && nrx > 0 && !finite_arr(rx, 3 * (size_t)nrx)) return DCEM_ERR_NONFINITE;
+  if (nrx == 0) return DCEM_OK;
+  cudaStream_t st = s->st;
+  const int np = grad_nparam(s->nmat, s->nobj);
+  const int W = 1 + 4 * p->max_refl;
+  // device copies of the inputs given on the host, scratch, staged outputs
+  if ((size_t)nrx > s->g_rx_cap) {
+    dfree(s->g_rx);
+    CK(dalloc(&s->g_rx, (size_t)nrx));
+    s->g_rx_cap = (size_t)nrx;
+  }
+  if (rx_ptr_kind == DCEM_PTR_HOST) {
+    std::vector<float4> h((size_t)nrx);
+    for (int i = 0; i < nrx; ++i) h[i] = make_float4(rx[3 * i], rx[3 * i + 1], rx[3 * i + 2], 0.0f);
+    CK(cudaMemcpyAsync(s->g_rx, h.data(), sizeof(float4) * nrx, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // h goes out of scope
+  } else {
+    CK(launch_pack_rx(rx, nrx, s->g_rx, st));
+  }
+  const dcem_path* pd = paths;
+  if (ptr_kind == DCEM_PTR_HOST && n_paths > 0) {
+    if ((size_t)n_paths > s->g_paths_cap) {
+      dfree(s->g_paths);
+      CK(dalloc(&s->g_paths, (size_t)n_paths));
+      s->g_paths_cap = (size_t)n_paths;
+    }
+    CK(cudaMemcpyAsync(s->g_paths, paths, sizeof(dcem_path) * n_paths, cudaMemcpyHostToDevice, st));
+    pd = s->g_paths;
+  }
+  size_t nitems = (size_t)n_paths * W;
+  if (nitems > s->g_items_cap) {
+    dfree(s->g_items);
+    dfree(s->g_param);
+    CK(dalloc(&s->g_items, nitems));
+    CK(dalloc(&s->g_param, nitems));
+    s->g_items_cap = nitems;
+  }
+  size_t nout = ptr_kind == DCEM_PTR_HOST ? (size_t)nrx * (2 + 3 * (size_t)np) : 0;
+  if (nout > s->g_out_cap) {
+    dfree(s->g_out);
+    CK(dalloc(&s->g_out, nout));
+    s->g_out_cap = nout;
+  }
+  if (!s->g_err) CK(dalloc(&s->g_err, 1));
+  CK(cudaMemsetAsync(s->g_err, 0, sizeof(unsigned), st));
+  GradArgs g;
+  g.paths = pd;
+  g.n_paths = n_paths;
+  g.W = W;
+  g.max_refl = p->max_refl;
+  g.tris = s->tris;
+  g.slot_of_id = s->slot_of_id;
+  g.tri_mat = s->tri_mat_d;
+  g.tri_obj = s->tri_obj_d;
+  g.ntri = s->ntri;
+  g.mats = s->mats;
+  g.nmat = s->nmat;
+  g.nobj = s->nobj;
+  g.rx = s->g_rx;
+  g.nrx = nrx;
+  for (int k = 0; k < 3; ++k) {
+    g.tx[k] = tx[k];
+    g.pol[k] = p->pol[k];
+  }
+  g.freq = p->freq_hz;
+  g.tx_power = p->tx_power_w;
+  g.items = s->g_items;
+  g.param = s->g_param;
+  g.err = s->g_err;
+  if (ptr_kind == DCEM_PTR_DEVICE) {
+    g.field = field;
+    g.dfield = dfield;
+    g.dpcoh = dpcoh_dbm;
+  } else {
+    g.field = s->g_out;
+    g.dfield = s->g_out + 2 * (size_t)nrx;
+    g.dpcoh = s->g_out + 2 * (size_t)nrx + 2 * (size_t)nrx * np;
+  }
+  CK(launch_gradients(g, st));
+  s->launches += (n_paths > 0 ? 1 : 0) + 1 + (rx_ptr_kind == DCEM_PTR_DEVICE ? 1 : 0);
+  unsigned err = 0;
+  CK(cudaMemcpyAsync(&err, s->g_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  if (ptr_kind == DCEM_PTR_HOST) {
+    cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+    if (field) CK(cudaMemcpyAsync(field, g.field, sizeof(double) * 2 * nrx, k, st));
+    CK(cudaMemcpyAsync(dfield, g.dfield, sizeof(double) * 2 * (size_t)nrx * np, k, st));
+    if (dpcoh_dbm) CK(cudaMemcpyAsync(dpcoh_dbm, g.dpcoh, sizeof(double) * (size_t)nrx * np, k, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return err ? DCEM_ERR_ARG : DCEM_OK;
 }
 
 int dcem_scene_info(const dcem_scene* s, int32_t* ntri, int32_t* nobj, int32_t* n_rays, int32_t* static_nodes,

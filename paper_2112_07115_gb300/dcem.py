@@ -29,7 +29,7 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_set_stream", "dcem_scene_destroy", "dcem_status_string", "dcem_scene_info",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
             "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
-            "dcem_reduce_paths_noalloc"]
+            "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients"]
 
 
 class Material(C.Structure):
@@ -109,6 +109,8 @@ def lib():
         L.dcem_scene_get_candidates.argtypes = [vp, vp, i64, P(i64)]
         L.dcem_scene_set_rebuild_threshold.argtypes = [vp, C.c_float]
         L.dcem_reduce_paths_noalloc.argtypes = [vp, i32, i32, C.c_double, vp, vp, vp, vp]
+        L.dcem_scene_gradient_size.argtypes = [vp, P(i32)]
+        L.dcem_path_gradients.argtypes = [vp, vp, vp, i32, i32, vp, i32, P(Params), i32, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string"):
                 getattr(L, name).restype = C.c_int
@@ -213,6 +215,29 @@ def dcem_reduce_paths_noalloc(paths_ptr, n_paths, nrx, tx_power_w, field_ptr, p_
     (device pointers as ints); returns the status."""
     return lib().dcem_reduce_paths_noalloc(paths_ptr, int(n_paths), int(nrx), float(tx_power_w), field_ptr,
                                            p_coh_ptr, p_inc_ptr, stream)
+
+
+def dcem_scene_gradient_size(h) -> int:
+    n = C.c_int32(0)
+    _check(lib().dcem_scene_gradient_size(h, C.byref(n)), "dcem_scene_gradient_size")
+    return int(n.value)
+
+
+def dcem_path_gradients(h, tx, rx, paths, params: Params, ptr_kind: int, field_ptr, dfield_ptr,
+                        dpcoh_ptr, n_paths: int | None = None) -> int:
+    """Raw call; returns the status. ``rx`` is an array or tensor (its kind
+    decides rx_ptr_kind); ``paths`` and the outputs are host or device
+    pointers as ints per ``ptr_kind`` (or a PATH_DTYPE array for host paths)."""
+    txa = np.ascontiguousarray(tx, np.float32).reshape(3)
+    rp, rkind, keep = _ptr(rx, np.float32)
+    nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+    if isinstance(paths, np.ndarray):
+        n_paths = paths.shape[0] if n_paths is None else n_paths
+        pp = paths.ctypes.data if n_paths else None
+    else:
+        pp = paths
+    return lib().dcem_path_gradients(h, txa.ctypes.data, rp, nrx, rkind, pp, int(n_paths or 0),
+                                     C.byref(params), ptr_kind, field_ptr, dfield_ptr, dpcoh_ptr)
 
 
 def dcem_scene_reset_cache(h):
@@ -336,6 +361,25 @@ class Scene:
         n = min(res.n_paths, max_paths)
         return Frame(rc, field[:nrx, 0] + 1j * field[:nrx, 1], pc[:nrx], pi[:nrx], paths[:n].copy(),
                      stats_dict(res.stats))
+
+    def gradients(self, tx, rx, paths: np.ndarray, params: Params | None = None):
+        """Field E (nrx,) complex, dE/dtheta (nrx, n_params) complex and
+        d P_coh[dBm]/dtheta (nrx, n_params) for host PATH_DTYPE records;
+        theta = eps_r, sigma per material, then x, y per object."""
+        params = params or default_params()
+        nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+        npar = dcem_scene_gradient_size(self.h)
+        field = np.zeros((max(nrx, 1), 2), np.float64)
+        dfield = np.zeros((max(nrx, 1), max(npar, 1), 2), np.float64)
+        dp = np.zeros((max(nrx, 1), max(npar, 1)), np.float64)
+        paths = np.ascontiguousarray(paths, PATH_DTYPE)
+        rc = dcem_path_gradients(self.h, tx, rx, paths, params, PTR_HOST, field.ctypes.data,
+                                 dfield.ctypes.data, dp.ctypes.data)
+        if rc != OK:
+            raise DcemError(rc, "dcem_path_gradients")
+        e = field[:nrx, 0] + 1j * field[:nrx, 1]
+        de = dfield[:nrx, :npar, 0] + 1j * dfield[:nrx, :npar, 1]
+        return e, de, dp[:nrx, :npar]
 
     def reset_cache(self):
         dcem_scene_reset_cache(self.h)

@@ -97,6 +97,9 @@ def test_null_scene_calls(L):
     assert lib.dcem_scene_update_transforms(None, None, 0) == L.ERR_ARG
     assert lib.dcem_scene_reset_cache(None) == L.ERR_ARG
     assert lib.dcem_scene_info(None, None, None, None, None, None) == L.ERR_ARG
+    n = C.c_int32(0)
+    assert lib.dcem_scene_gradient_size(None, C.byref(n)) == L.ERR_ARG
+    assert lib.dcem_path_gradients(None, tx, None, 0, 0, None, 0, C.byref(p), 0, None, None, None) == L.ERR_ARG
     lib.dcem_scene_destroy(None)  # no-op
 
 
