@@ -266,10 +266,21 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     int ray = base + lane;
     int ns = ray < R ? a.nseg[ray] : 0;
     int bstar = all ? 0 : ns;
-    for (int b = 0; b <= a.N; ++b) {
+    // the first kPre logged segments of the warp's rays are loaded together
+    // (one memory latency instead of one per segment)
+    constexpr int kPre = 5;
+    float4 plo[kPre], pld[kPre];
+#pragma unroll
+    for (int b = 0; b < kPre; ++b) {
+      plo[b] = pld[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b < bstar) {
+        plo[b] = a.log_o[(size_t)b * R + ray];
+        pld[b] = a.log_d[(size_t)b * R + ray];
+      }
+    }
+    auto step = [&](int b, float4 lo, float4 ld) {
       unsigned item = 0xffffffffu;
       if (b < bstar) {
-        float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
         RayPre rp;
         rp.o = f3(lo.x, lo.y, lo.z);
         float dx = fabsf(ld.x) < 1e-30f ? copysignf(1e-30f, ld.x) : ld.x;
@@ -287,6 +298,16 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
         at = __shfl_sync(0xffffffffu, at, leader);
         if (item != 0xffffffffu) a.capitems[at + __popc(want & ((1u << lane) - 1u))] = item;
       }
+    };
+#pragma unroll
+    for (int b = 0; b < kPre; ++b) step(b, plo[b], pld[b]);
+    for (int b = kPre; b <= a.N; ++b) {
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), ld = lo;
+      if (b < bstar) {
+        lo = a.log_o[(size_t)b * R + ray];
+        ld = a.log_d[(size_t)b * R + ray];
+      }
+      step(b, lo, ld);
     }
     if (ray < R) {
       c.restart[ray] = bstar;
