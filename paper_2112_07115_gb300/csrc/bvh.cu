@@ -190,8 +190,29 @@ __device__ void sort_karras_dev(const float* __restrict__ prim, int n, int node_
     }
   }
   __syncthreads();
-  for (int k = 2; k <= np2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
+  // Bitonic sort of the np2 keys. Compare-exchanges at distance j < 32 stay
+  // within a 32-key chunk and run in registers with warp shuffles (no block
+  // barrier); only distances >= 32 go through shared memory.
+  const int lane = tid & 31, nw = nt >> 5;
+  const int nchunk = (np2 + 31) >> 5;
+  auto in_warp = [&](int kmin, int kmax, int jmax) {
+    for (int c = tid >> 5; c < nchunk; c += nw) {
+      int i = (c << 5) + lane;
+      unsigned long long x = i < np2 ? keys[i] : ~0ull;  // padding sorts last
+      for (int k = kmin; k <= kmax; k <<= 1) {
+        for (int j = min(k >> 1, jmax); j > 0; j >>= 1) {
+          unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+          bool up = (i & k) == 0, low = (lane & j) == 0;
+          x = (low == up) ? (x < y ? x : y) : (x < y ? y : x);
+        }
+      }
+      if (i < np2) keys[i] = x;
+    }
+    __syncthreads();
+  };
+  in_warp(2, 32, 16);  // stages k = 2..32: every 32-key chunk sorted, directions alternating
+  for (int k = 64; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j >= 32; j >>= 1) {
       for (int i = tid; i < np2; i += nt) {
         int ixj = i ^ j;
         if (ixj > i) {
@@ -202,6 +223,7 @@ __device__ void sort_karras_dev(const float* __restrict__ prim, int n, int node_
       }
       __syncthreads();
     }
+    in_warp(k, k, 16);  // the rest of stage k: distances 16..1
   }
   for (int i = tid; i < n; i += nt) perm[i] = (int)(keys[i] & 0xffffffffu);
   if (n == 1) {
