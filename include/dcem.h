@@ -90,7 +90,9 @@ typedef struct {
   float eps_occ;          /* occlusion ignores the first/last eps of a sub-
                              segment (relative); default 1e-4                    */
   float pol[3];           /* antenna polarisation reference u; default (0,0,1)  */
-  int32_t timing;         /* 1: record per-stage device times in the stats       */
+  int32_t timing;         /* 1: record per-stage device times in the stats;
+                             2: only the closest-hit kernel's (ms_stage[2]),
+                             with two event records instead of nine         */
 } dcem_params;
 
 /* One valid propagation path (Sec. III step 6). */
@@ -129,7 +131,7 @@ typedef struct {
                                   transform updates since the previous frame    */
   int32_t bvh_rebuilt;         /* 1 if the moving-object tree was rebuilt since
                                   the previous frame                             */
-  float ms_stage[10];          /* if params.timing: prep, mark, trace, capture,
+  float ms_stage[10];          /* if params.timing == 1: prep, mark, trace, capture,
                                   dedupe, validate, reduce, copy-out, total,
                                   (unused)                                       */
   float bvh_cost_ratio;        /* surface-area cost of the moving-object tree

@@ -760,7 +760,8 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   cudaStream_t st = s->st;
   int N = p->max_refl;
   int nxt = s->cur ^ 1;
-  bool tm = p->timing != 0;
+  bool tm = p->timing == 1;                     // every stage
+  bool tk = p->timing == 1 || p->timing == 2;   // the closest-hit kernel
   if (tm) CK(cudaEventRecord(s->ev[0], st));
   CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
@@ -871,9 +872,9 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
     a.queue = s->queue;
     a.rx_moved = s->rx_moved;
   }
-  if (tm) CK(cudaEventRecord(s->ev[2], st));
+  if (tk) CK(cudaEventRecord(s->ev[2], st));
   if (s->R > 0) CK(launch_trace(a, s->sms, st));
-  if (tm) CK(cudaEventRecord(s->ev[3], st));
+  if (tk) CK(cudaEventRecord(s->ev[3], st));
   if (s->R > 0) CK(launch_capture(a, s->sms, st));
   if (tm) CK(cudaEventRecord(s->ev[4], st));
 
@@ -951,6 +952,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   if (out->max_paths < 0 || (out->max_paths > 0 && !out->paths)) return DCEM_ERR_ARG;
   if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
   if (p->mode != DCEM_MODE_FULL && p->mode != DCEM_MODE_COHERENT) return DCEM_ERR_ARG;
+  if (p->timing < 0 || p->timing > 2) return DCEM_ERR_ARG;
   if (!(p->freq_hz > 0) || !std::isfinite(p->freq_hz) || !(p->tx_power_w > 0) || !std::isfinite(p->tx_power_w))
     return DCEM_ERR_ARG;
   if (!(p->rx_radius_scale > 0) || !std::isfinite(p->rx_radius_scale) || !(p->t_min >= 0) ||
@@ -1050,7 +1052,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
     return DCEM_ERR_NONFINITE;
   }
   // copy out
-  bool tm = p->timing != 0;
+  bool tm = p->timing == 1;
   int nvalid = (int)c[0].n_valid;
   if (out->ptr_kind == DCEM_PTR_HOST) {
     cudaMemcpyKind k = cudaMemcpyDeviceToHost;
@@ -1070,6 +1072,9 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   if (tm) {
     for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&S.ms_stage[i], s->ev[i], s->ev[i + 1]);
     cudaEventElapsedTime(&S.ms_stage[8], s->ev[0], s->ev[8]);
+  } else if (p->timing == 2 && s->R > 0) {
+    for (int i = 0; i < 10; ++i) S.ms_stage[i] = 0.0f;
+    cudaEventElapsedTime(&S.ms_stage[2], s->ev[2], s->ev[3]);
   }
   out->n_paths = nvalid;
   s->cache_valid = true;
