@@ -239,3 +239,36 @@ def test_highway_reduced_both_bands(cuda, freq):
     assert out["checked"] > 0 and not out["missing"] and not out["extra"] and not out["amp"]
     assert np.all(P.power_close(fr.p_coh_dbm, ref.p_coh_dbm))
     s.close()
+
+
+@pytest.mark.parametrize("tx", [(600.0, 300.0, 300.0), (5e4, 300.0, 2.5e4)])
+def test_far_transmitter(cuda, tx):
+    """Rays aimed at the street from outside it. From (600, 300, 300) every
+    segment stays within the compact node copy's reach; from 50 km away
+    (far beyond 4e6 grid steps of the 200 m street: about 12 km across, 1 km
+    vertically) first segments take the full-precision nodes and later ones,
+    starting in the street, the compact copy. Hit ids equal the oracle's on
+    every unflagged ray."""
+    torch = cuda
+    sc = scenes.toy_street(n_rays=20_000, max_refl=3)
+    f = 3
+    sc.tx = np.array(tx, np.float32)
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([7, int(tx[0])])))
+    aim = rng.uniform([-100.0, -100.0, 0.0], [100.0, 100.0, 15.0], size=(20_000, 3))
+    d = aim - sc.tx.astype(np.float64)
+    rays = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    rx = sc.rx[f][:1]
+    s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(rays)
+    s.update_transforms(sc.xf[f])
+    fr = s.trace(sc.tx, rx, P.gpu_params(sc), max_paths=1 << 16)
+    ids, t, ns = s.ray_log()
+    s.close()
+    wt = O.transform(sc.tris, sc.tri_obj, sc.xf[f])
+    ref = O.trace(wt, sc.tri_mat, sc.materials, sc.tx, rays, rx, P.oracle_params(sc, n_rays=20_000))
+    n, nflag, bad = P.compare_hits(ids, ns, ref)
+    assert len(bad) == 0, (len(bad), bad[:5])
+    assert n > 15_000
+    # most aimed rays hit the street
+    assert (ns > 1).mean() > 0.5
+    assert fr.status == dcem.OK
