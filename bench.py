@@ -313,6 +313,32 @@ def run_ours(args):
     # field derivatives over the last frame's paths (device in, device out)
     grads = grad_timing(s_coh, sc, rx_d[frames[-1]], paths_d, int(st_coh[-1]["paths_valid"]), stream, dev)
 
+    # validation arithmetic: FP64 and double-float, full frames with every
+    # stage timed, each checked against the oracle on its last frame
+    precs = {}
+    if rank == 0:
+        sub = frames[-min(len(frames), 60):]
+        for name, prec in (("f64", dcem.PREC_F64), ("df32", dcem.PREC_DF32)):
+            sp = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+            sp.set_rays(rays)
+            prm_p = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=dcem.MODE_FULL,
+                                        timing=1, prec=prec)
+            res_p = new_result()
+            vms, last = [], None
+            for f in sub:
+                dcem.dcem_scene_update_transforms(sp.h, xf_d[f])
+                rc = dcem.dcem_trace_frame(sp.h, tx, rx_d[f], prm_p, res_p)
+                if rc != dcem.OK:
+                    raise dcem.DcemError(rc, f"frame {f} ({name})")
+                last = dcem.stats_dict(res_p.stats)
+                vms.append(last["ms_stage"]["validate"])
+            torch.cuda.synchronize()
+            e_p = power_error_vs_oracle(sc, sp, sub[-1], max_paths, paths_d, pc_d, pi_d, res_n=last)
+            precs[name] = {"validate_ms": round(float(np.mean(vms[1:] or vms)), 4),
+                           "max_abs_p_coh_db": e_p["max_abs_p_coh"], "max_abs_p_inc_db": e_p["max_abs_p_inc"],
+                           "max_len_err_m": e_p["max_len_err_m"], "paths": e_p["paths"]}
+            sp.close()
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sc, rays, stream, W, K, world, dev)
@@ -346,6 +372,7 @@ def run_ours(args):
                          "max_segment_nodes": int(max(x["max_segment_nodes"] for x in st_coh)),
                          "bvh_rebuilds": int(sum(x["bvh_rebuilt"] for x in st_coh))},
             "gradients": grads,
+            "validation_precision": precs,
             "full": {"frames_per_s": round(fps_full, 2), "ms_per_frame": round(1e3 * t_full / K, 4),
                      "ray_segments_per_s": round(seg_full, 0), "segments_per_frame": int(seg_mean),
                      "nodes_per_segment": round(nodes_per_seg, 2), "tris_per_segment": round(tris_per_seg, 2),

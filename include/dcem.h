@@ -62,6 +62,10 @@ typedef enum {
 } dcem_status;
 
 typedef enum { DCEM_MODE_FULL = 0, DCEM_MODE_COHERENT = 1 } dcem_mode;
+/* Arithmetic of the validation geometry (image sources, back-trace,
+ * reflection points, path length) and of the phase: FP64, or double-float
+ * (pairs of FP32 values, about 44 significant bits) on the FP32 pipe. */
+typedef enum { DCEM_PREC_F64 = 0, DCEM_PREC_DF32 = 1 } dcem_prec;
 typedef enum { DCEM_PTR_HOST = 0, DCEM_PTR_DEVICE = 1 } dcem_ptr_kind;
 
 /* Path flag bits (dcem_path.flags). */
@@ -93,6 +97,7 @@ typedef struct {
   int32_t timing;         /* 1: record per-stage device times in the stats;
                              2: only the closest-hit kernel's (ms_stage[2]),
                              with two event records instead of nine         */
+  int32_t prec;           /* DCEM_PREC_F64 (default) or DCEM_PREC_DF32       */
 } dcem_params;
 
 /* One valid propagation path (Sec. III step 6). */

@@ -468,6 +468,7 @@ void dcem_params_default(dcem_params* p) {
   p->pol[1] = 0.0f;
   p->pol[2] = 1.0f;
   p->timing = 0;
+  p->prec = DCEM_PREC_F64;
 }
 
 const char* dcem_status_string(int st) {
@@ -918,6 +919,7 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   q.tx = a.tx;
   q.pol = make_float3(p->pol[0], p->pol[1], p->pol[2]);
   q.eps_occ = p->eps_occ;
+  q.prec_df = p->prec == DCEM_PREC_DF32 ? 1 : 0;
   q.freq = p->freq_hz;
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
@@ -953,6 +955,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
   if (p->mode != DCEM_MODE_FULL && p->mode != DCEM_MODE_COHERENT) return DCEM_ERR_ARG;
   if (p->timing < 0 || p->timing > 2) return DCEM_ERR_ARG;
+  if (p->prec != DCEM_PREC_F64 && p->prec != DCEM_PREC_DF32) return DCEM_ERR_ARG;
   if (!(p->freq_hz > 0) || !std::isfinite(p->freq_hz) || !(p->tx_power_w > 0) || !std::isfinite(p->tx_power_w))
     return DCEM_ERR_ARG;
   if (!(p->rx_radius_scale > 0) || !std::isfinite(p->rx_radius_scale) || !(p->t_min >= 0) ||

@@ -99,6 +99,80 @@ __device__ __forceinline__ d3 dx(d3 a, d3 b) {
 __device__ __forceinline__ double dn(d3 a) { return sqrt(dd(a, a)); }
 __device__ __forceinline__ d3 du(d3 a) { return a * (1.0 / dn(a)); }
 
+// Double-float numbers (hi + lo, two FP32 values, about 44 significant
+// bits): the validation geometry in this precision runs on the FP32 pipe.
+// Sums and products are formed with the error-free transformations
+// (Knuth's two-sum, the FMA two-product); quotients and square roots add
+// correction steps from the remainder.
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+  df s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  df r = quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return quick_two_sum(r.hi, __fadd_rn(r.lo, t.lo));
+}
+__device__ __forceinline__ df operator-(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df operator/(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = a - b * df{q1, 0.0f};
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  r = r - b * df{q2, 0.0f};
+  float q3 = __fdiv_rn(r.hi, b.hi);
+  return quick_two_sum(q1, q2) + df{q3, 0.0f};
+}
+__device__ __forceinline__ double root(double a) { return ::sqrt(a); }
+__device__ __forceinline__ df root(df a) {
+  if (!(a.hi > 0.0f)) return df{0.0f, 0.0f};
+  float s = __fsqrt_rn(a.hi);
+  float p = __fmul_rn(s, s), pe = __fmaf_rn(s, s, -p);
+  float e = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo), __fmul_rn(2.0f, s));
+  return quick_two_sum(s, e);
+}
+
+// Scalars of the validation geometry: FP64 (default) or double-float.
+template <class T> __device__ __forceinline__ T sc_of(float v);
+template <> __device__ __forceinline__ double sc_of<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ df sc_of<df>(float v) { return df{v, 0.0f}; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(df v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ bool pos(double v) { return v > 0.0; }
+__device__ __forceinline__ bool pos(df v) { return v.hi > 0.0f || (v.hi == 0.0f && v.lo > 0.0f); }
+__device__ __forceinline__ bool neg(double v) { return v < 0.0; }
+__device__ __forceinline__ bool neg(df v) { return v.hi < 0.0f || (v.hi == 0.0f && v.lo < 0.0f); }
+__device__ __forceinline__ bool zero(double v) { return v == 0.0; }
+__device__ __forceinline__ bool zero(df v) { return v.hi == 0.0f && v.lo == 0.0f; }
+
+template <class T>
+struct v3 {
+  T x, y, z;
+};
+template <class T> __device__ __forceinline__ v3<T> operator+(v3<T> a, v3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T> __device__ __forceinline__ v3<T> operator-(v3<T> a, v3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> __device__ __forceinline__ v3<T> scale(v3<T> a, T s) { return {a.x * s, a.y * s, a.z * s}; }
+template <class T> __device__ __forceinline__ T vdot(v3<T> a, v3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> __device__ __forceinline__ v3<T> vcross(v3<T> a, v3<T> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class T> __device__ __forceinline__ v3<T> vof(float x, float y, float z) {
+  return {sc_of<T>(x), sc_of<T>(y), sc_of<T>(z)};
+}
+
 // FP32 complex arithmetic for the reflection coefficients and polarisation
 struct cf {
   float re, im;
@@ -154,15 +228,6 @@ __device__ __forceinline__ float3 fpol(float3 u, float3 d, unsigned& flags) {
   return f3(p.x / n, p.y / n, p.z / n);
 }
 
-__device__ __forceinline__ void load_tri_d(const PathArgs& a, int id, d3& v0, d3& v1, d3& v2, int& mat) {
-  int slot = a.slot_of_id[id];
-  const float4* t = a.tris + 3 * (size_t)slot;
-  float4 p = t[0], q = t[1], r = t[2];
-  v0 = mk3(p.x, p.y, p.z);
-  v1 = mk3(q.x, q.y, q.z);
-  v2 = mk3(r.x, r.y, r.z);
-  mat = __float_as_int(q.w);
-}
 
 // ---------------------------------------------------------------------------
 // validation + field in three kernels:
@@ -176,6 +241,9 @@ __device__ __forceinline__ void load_tri_d(const PathArgs& a, int id, d3& v0, d3
 // b + gridDim * t, so that every SM gets a share.
 __device__ __forceinline__ unsigned spread_index(unsigned i) { return blockIdx.x + gridDim.x * i; }
 
+// T = double (FP64) or df (double-float) for every step of the geometry;
+// path points and length are stored in FP64 either way.
+template <class T>
 __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
   unsigned nu = min(a.ctr->n_unique, a.ucap);
   for (unsigned t = threadIdx.x;; t += blockDim.x) {
@@ -205,46 +273,52 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
       rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
     }
     float4 rxv = a.rx[rxi];
-    d3 X[kMaxRefl + 2], V0[kMaxRefl], V1[kMaxRefl], V2[kMaxRefl], Nn[kMaxRefl];
-    d3 tx = mk3(a.tx.x, a.tx.y, a.tx.z), rx = mk3(rxv.x, rxv.y, rxv.z);
+    v3<T> X[kMaxRefl + 2], V0[kMaxRefl], V1[kMaxRefl], V2[kMaxRefl], Nn[kMaxRefl];
+    v3<T> tx = vof<T>(a.tx.x, a.tx.y, a.tx.z), rx = vof<T>(rxv.x, rxv.y, rxv.z);
     // step 3: image sources I_1..I_k
-    d3 img[kMaxRefl + 1];
+    v3<T> img[kMaxRefl + 1];
     img[0] = tx;
     bool ok = true;
+    const T two = sc_of<T>(2.0f), one = sc_of<T>(1.0f);
     for (int j = 0; j < k && ok; ++j) {
-      int m;
-      load_tri_d(a, ids[j], V0[j], V1[j], V2[j], m);
-      d3 n = dx(V1[j] - V0[j], V2[j] - V0[j]);
-      double nn = dd(n, n);
-      if (!(nn > 0.0)) { ok = false; break; }
+      const float4* tp = a.tris + 3 * (size_t)a.slot_of_id[ids[j]];
+      float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+      V0[j] = vof<T>(p0.x, p0.y, p0.z);
+      V1[j] = vof<T>(p1.x, p1.y, p1.z);
+      V2[j] = vof<T>(p2.x, p2.y, p2.z);
+      v3<T> n = vcross(V1[j] - V0[j], V2[j] - V0[j]);
+      T nn = vdot(n, n);
+      if (!pos(nn)) { ok = false; break; }
       Nn[j] = n;
-      img[j + 1] = img[j] - n * (2.0 * dd(img[j] - V0[j], n) / nn);
+      img[j + 1] = img[j] - scale(n, two * vdot(img[j] - V0[j], n) / nn);
     }
     // step 4: back-trace from the receiver, reflection points in their triangles
     X[0] = tx;
     X[k + 1] = rx;
     for (int j = k; j >= 1 && ok; --j) {
-      d3 dir = img[j] - X[j + 1];
-      double den = dd(dir, Nn[j - 1]);
-      if (den == 0.0) { ok = false; break; }
-      double s = dd(V0[j - 1] - X[j + 1], Nn[j - 1]) / den;
-      if (!(s > 0.0 && s < 1.0)) { ok = false; break; }
-      X[j] = X[j + 1] + dir * s;
-      d3 v0 = V0[j - 1], v1 = V1[j - 1], v2 = V2[j - 1];
-      d3 n = Nn[j - 1];
-      if (dd(dx(v1 - v0, X[j] - v0), n) < 0.0 || dd(dx(v2 - v1, X[j] - v1), n) < 0.0 ||
-          dd(dx(v0 - v2, X[j] - v2), n) < 0.0)
+      v3<T> dir = img[j] - X[j + 1];
+      T den = vdot(dir, Nn[j - 1]);
+      if (zero(den)) { ok = false; break; }
+      T sp = vdot(V0[j - 1] - X[j + 1], Nn[j - 1]) / den;
+      if (!(pos(sp) && neg(sp - one))) { ok = false; break; }
+      X[j] = X[j + 1] + scale(dir, sp);
+      v3<T> v0 = V0[j - 1], v1 = V1[j - 1], v2 = V2[j - 1], n = Nn[j - 1];
+      if (neg(vdot(vcross(v1 - v0, X[j] - v0), n)) || neg(vdot(vcross(v2 - v1, X[j] - v1), n)) ||
+          neg(vdot(vcross(v0 - v2, X[j] - v2), n)))
         ok = false;
     }
-    double L = 0.0;
+    T L = sc_of<T>(0.0f);
     if (ok) {
-      for (int j = 0; j <= k; ++j) L += dn(X[j + 1] - X[j]);
-      if (!(L > 0.0)) ok = false;
+      for (int j = 0; j <= k; ++j) {
+        v3<T> e = X[j + 1] - X[j];
+        L = L + root(vdot(e, e));
+      }
+      if (!pos(L)) ok = false;
     }
     d3* xs = reinterpret_cast<d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
     if (ok) {
-      for (int j = 0; j <= k + 1; ++j) xs[j] = X[j];
-      rec.len = L;
+      for (int j = 0; j <= k + 1; ++j) xs[j] = mk3(to_d(X[j].x), to_d(X[j].y), to_d(X[j].z));
+      rec.len = to_d(L);
     }
     a.vstate[u] = ok ? 1 : 0;   // 1 = geometry valid, occlusion pending
     a.prec[u] = rec;
@@ -340,7 +414,12 @@ __global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
     }
     float3 prx = fpol(upol, f3(-din.x, -din.y, -din.z), fl);
     double lam = 299792458.0 / a.freq;
-    double ph = fmod(2.0 * M_PI * a.freq / 299792458.0 * L, 2.0 * M_PI);
+    // phase k L reduced modulo 2 pi: subtract the nearest multiple of 2 pi,
+    // the product n * 2 pi taken exactly by an FMA against a two-part 2 pi
+    double kl = 2.0 * M_PI * a.freq / 299792458.0 * L;
+    double nq = rint(kl * (0.5 / M_PI));
+    double ph = fma(-nq, 6.283185307179586, kl);
+    ph = fma(-nq, 2.4492935982947064e-16, ph);
     float sn, cs;
     sincosf((float)ph, &sn, &cs);
     cf proj = fdot(E, prx);
@@ -471,7 +550,8 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st) {
-  k_val_geom<<<grid, 64, 0, st>>>(a);
+  if (a.prec_df) k_val_geom<df><<<grid, 64, 0, st>>>(a);
+  else k_val_geom<double><<<grid, 64, 0, st>>>(a);
   k_val_occ<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a);
   k_val_field<<<grid, 64, 0, st>>>(a);
   return cudaGetLastError();

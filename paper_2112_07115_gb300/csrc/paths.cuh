@@ -37,6 +37,7 @@ struct PathArgs {
   float3 tx;
   float3 pol;
   float eps_occ;
+  int prec_df;                    // 1: validation geometry in double-float, 0: FP64
   double freq, tx_power;
   DevCounters* ctr;
 };

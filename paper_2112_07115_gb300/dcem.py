@@ -21,6 +21,7 @@ MAX_REFL = 10
 OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_NONFINITE, ERR_STACK, ERR_HASH, ERR_STATE, ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 MODE_FULL, MODE_COHERENT = 0, 1
+PREC_F64, PREC_DF32 = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 PATH_POL_DEGENERATE = 1
 
@@ -40,7 +41,7 @@ class Params(C.Structure):
     _fields_ = [("freq_hz", C.c_double), ("tx_power_w", C.c_double), ("max_refl", C.c_int32),
                 ("mode", C.c_int32), ("rx_radius_scale", C.c_float), ("t_min", C.c_float),
                 ("escape_len", C.c_float), ("eps_occ", C.c_float), ("pol", C.c_float * 3),
-                ("timing", C.c_int32)]
+                ("timing", C.c_int32), ("prec", C.c_int32)]
 
 
 class Path(C.Structure):

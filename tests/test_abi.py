@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(L):
 
 def test_struct_sizes_match_header(L):
     assert C.sizeof(L.Path) == 216
-    assert C.sizeof(L.Params) == 56
+    assert C.sizeof(L.Params) == 64
     assert L.PATH_DTYPE.itemsize == 216
 
 

@@ -102,11 +102,12 @@ def test_bvh_structure_and_refit_bounds(cuda, which):
 
 # ------------------------------------------------------------------ frames
 
-def _frame_vs_oracle(torch, sc, frames, n_rays=None, mode=dcem.MODE_FULL, check_paths=True):
+def _frame_vs_oracle(torch, sc, frames, n_rays=None, mode=dcem.MODE_FULL, check_paths=True,
+                     prec=dcem.PREC_F64):
     n_rays = n_rays or sc.n_rays
     rays = scenes.fibonacci_sphere(n_rays)
     s = make_scene(torch, sc, rays)
-    prm = P.gpu_params(sc, mode=mode)
+    prm = P.gpu_params(sc, mode=mode, prec=prec)
     oprm = P.oracle_params(sc, n_rays=n_rays)
     report = []
     for f in frames:
@@ -144,6 +145,43 @@ def test_toy_street_more_rays_and_reflections(cuda):
 def test_highway_reduced_vs_oracle(cuda):
     sc = scenes.highway(n_frames=4, n_vehicles=40, length=400.0, n_rays=100_000, max_refl=4)
     _frame_vs_oracle(cuda, sc, range(4))
+
+
+@pytest.mark.parametrize("which", ["toy", "highway"])
+def test_double_float_validation_vs_oracle(cuda, which):
+    """Validation geometry and phase in double-float (DCEM_PREC_DF32): the
+    same path set, lengths within 1e-6 m, amplitudes within 1e-4 and power
+    within 0.01 dB of the FP64 oracle."""
+    if which == "toy":
+        sc = scenes.toy_street()
+        frames = range(sc.nframes)
+    else:
+        sc = scenes.highway(n_frames=3, n_vehicles=40, length=400.0, n_rays=100_000, max_refl=4)
+        frames = range(3)
+    _frame_vs_oracle(cuda, sc, frames, prec=dcem.PREC_DF32)
+
+
+def test_double_float_matches_fp64_paths(cuda):
+    """Both precisions give the same path records up to ~1e-10 in length and
+    amplitude (the double-float geometry carries about 44 bits)."""
+    sc = scenes.highway(n_frames=2, n_vehicles=60, length=600.0, n_rays=200_000, max_refl=4)
+    rays = scenes.fibonacci_sphere(sc.n_rays)
+    out = []
+    for prec in (dcem.PREC_F64, dcem.PREC_DF32):
+        s = make_scene(cuda, sc, rays)
+        s.update_transforms(sc.xf[1])
+        out.append(s.trace(sc.tx, sc.rx[1], P.gpu_params(sc, prec=prec)))
+        s.close()
+    a, b = out
+    assert a.paths.shape == b.paths.shape and a.paths.shape[0] > 20
+    assert np.array_equal(a.paths["key"], b.paths["key"])
+    assert np.abs(a.paths["len_m"] - b.paths["len_m"]).max() < 1e-6
+    amp_a = a.paths["amp_re"] + 1j * a.paths["amp_im"]
+    amp_b = b.paths["amp_re"] + 1j * b.paths["amp_im"]
+    assert np.abs(amp_a - amp_b).max() <= 1e-6 * np.abs(amp_a).max()
+    fin = np.isfinite(a.p_coh_dbm)
+    assert np.array_equal(fin, np.isfinite(b.p_coh_dbm))
+    assert np.abs(a.p_coh_dbm[fin] - b.p_coh_dbm[fin]).max() < 1e-4
 
 
 @pytest.mark.parametrize("seed", range(4))
