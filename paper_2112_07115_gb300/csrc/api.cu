@@ -175,8 +175,12 @@ struct dcem_scene {
   int* tri_mat_d = nullptr;
   float* v9d = nullptr;         // world vertices of moving primitives (rebuilds)
   float4* nodes = nullptr;
-  uint4* qnodes = nullptr;       // compact node copy for shared-memory traversal
+  uint4* qnodes = nullptr;       // 4-wide compact node copy for shared-memory traversal
   float* qframe = nullptr;
+  int4* q4_kid = nullptr;        // 4-wide mapping of the binary trees: children, box sources,
+  int4* q4_src = nullptr;        // node count and roots (rebuilt with the topology)
+  int* q4_count = nullptr;
+  int* q4_roots = nullptr;
   int* leaf_parent = nullptr;
   int* tri_obj_d = nullptr;  // triangle id -> rigid object (-1 static)
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
@@ -276,7 +280,8 @@ void scene_free(dcem_scene* s) {
   if (!s) return;
   cudaStreamSynchronize(s->st);
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
-  dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe); dfree(s->leaf_parent); dfree(s->arrive);
+  dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
+  dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx);
@@ -315,6 +320,15 @@ bool dyn_fused(const dcem_scene* s) {
   return s->nd <= kSmemRefit + 1 && dyn_update_smem(s->nd, s->nobj) <= 200 * 1024;
 }
 
+// The 4-wide mapping of both trees, after any change of topology.
+int remap4(dcem_scene* s) {
+  if (!s->qnodes) return DCEM_OK;
+  CK(launch_bvh4_map(s->nodes, s->nint_s + s->nint_d, s->roots, s->q4_kid, s->q4_src, s->q4_count, s->q4_roots,
+                     s->st));
+  s->launches += 1;
+  return DCEM_OK;
+}
+
 // One-CTA update of the moving-object tree (see DynUpdateArgs).
 int dyn_update(dcem_scene* s, bool rebuild) {
   if (s->nd == 0) return DCEM_OK;
@@ -343,7 +357,10 @@ int dyn_update(dcem_scene* s, bool rebuild) {
   d.uctr = s->uctr;
   CK(launch_dyn_update(d, s->st));
   s->launches += 1;
-  if (rebuild) s->rebuilt_since_frame = true;
+  if (rebuild) {
+    s->rebuilt_since_frame = true;
+    return remap4(s);
+  }
   return DCEM_OK;
 }
 
@@ -360,7 +377,7 @@ int rebuild_dynamic(dcem_scene* s) {
   k_place_dyn<<<g, bs, 0, s->st>>>(s->v9d, s->objv_src, s->perm, s->sel_d, s->tri_mat_d, s->nd, s->ns, s->tris,
                                    s->objv, s->slot_of_id);
   CK(cudaGetLastError());
-  return DCEM_OK;
+  return remap4(s);
 }
 
 int alloc_build_scratch(dcem_scene* s, int n) {
@@ -550,7 +567,16 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->tri_mat_d, ntri));
   CKF(dalloc(&s->v9d, 9 * (size_t)s->nd));
   CKF(dalloc(&s->nodes, 4 * (size_t)(s->nint_s + s->nint_d)));
-  CKF(dalloc(&s->qnodes, 2 * (size_t)(s->nint_s + s->nint_d)));
+  {
+    int nn = s->nint_s + s->nint_d;
+    if (trace_q_stack_cap(nn) > 0) {  // the 4-wide copy fits in shared memory
+      CKF(dalloc(&s->qnodes, 4 * (size_t)bvh4_bound(nn)));
+      CKF(dalloc(&s->q4_kid, nn));
+      CKF(dalloc(&s->q4_src, nn));
+      CKF(dalloc(&s->q4_count, 1));
+      CKF(dalloc(&s->q4_roots, 2));
+    }
+  }
   CKF(dalloc(&s->qframe, 6));
   CKF(dalloc(&s->leaf_parent, ntri));
   CKF(dalloc(&s->dsched, ntri > 1 ? ntri : 1));
@@ -637,6 +663,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   }
   s->root_h[0] = root_code(s->ns, 0, 0);
   s->root_h[1] = root_code(s->nd, s->nint_s, s->ns);
+  CKF(cudaStreamSynchronize(st));
+  if ((rc = remap4(s)) != DCEM_OK) return fail2(rc);
   CKF(cudaStreamSynchronize(st));
   for (auto& ev : s->ev) CKF(cudaEventCreate(&ev));
   dfree(v9); dfree(sel_s_d);
@@ -805,16 +833,19 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.qnodes = s->qnodes;
   a.qframe = s->qframe;
   a.n_nodes = s->nint_s + s->nint_d;
+  a.q4_count = s->q4_count;
+  a.q4_roots = s->q4_roots;
+  a.q4_bound = bvh4_bound(a.n_nodes);
   // the compact copy of both trees and the CTA's stacks fit in shared
   // memory: traverse it there
   {
     a.stack_cap = trace_q_stack_cap(a.n_nodes);
-    a.use_q = a.stack_cap > 0 ? 1 : 0;
+    a.use_q = (a.stack_cap > 0 && s->qnodes) ? 1 : 0;
     s->last_use_q = a.use_q;
   }
   if (a.use_q) {
-    launch_quantize(s->nodes, a.n_nodes, s->root_box, s->root_h[0] != kEmpty, s->root_h[1] != kEmpty, s->qnodes,
-                    s->qframe, st);
+    launch_quantize4(s->nodes, a.q4_bound, s->q4_count, s->q4_kid, s->q4_src, s->root_box, s->root_h[0] != kEmpty,
+                     s->root_h[1] != kEmpty, s->qnodes, s->qframe, st);
     CK(cudaGetLastError());
   }
   FramePrepArgs fp;

@@ -880,6 +880,152 @@ __global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float
 }
 
 // ---------------------------------------------------------------------------
+// 4-wide compact copy of both trees (layout in dcem_internal.cuh)
+// ---------------------------------------------------------------------------
+// One CTA maps the binary trees (nn internal nodes, roots roots[0..1]) to
+// 4-wide nodes: every internal node at even depth becomes a 4-wide node whose
+// children are its own children, an internal child replaced by that child's
+// two children. For each child slot it records the child (4-wide index,
+// leaf ~slot, or kEmpty) and where its box lives in the binary records
+// (record << 1 | side). Shared memory: depth[nn], index[nn].
+__global__ void __launch_bounds__(1024) k_bvh4_map(const float4* __restrict__ nodes, int nn,
+                                                   const int* __restrict__ roots, int4* kid4, int4* src4,
+                                                   int* n4_out, int* roots4_out) {
+  extern __shared__ int sm4[];
+  int* depth = sm4;
+  int* idx = sm4 + nn;
+  __shared__ int changed, total;
+  int tid = threadIdx.x, nt = blockDim.x;
+  auto kid = [&](int n, int side) {
+    return reinterpret_cast<const int*>(nodes + 4 * (size_t)n + 3)[side];
+  };
+  for (int i = tid; i < nn; i += nt) depth[i] = -1;
+  __syncthreads();
+  if (tid < 2) {
+    int r = roots[tid];
+    if (r >= 0 && r < nn) depth[r] = 0;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 256; ++pass) {
+    if (tid == 0) changed = 0;
+    __syncthreads();
+    for (int i = tid; i < nn; i += nt) {
+      int di = depth[i];
+      if (di < 0) continue;
+      for (int side = 0; side < 2; ++side) {
+        int c = kid(i, side);
+        if (c >= 0 && c < nn && depth[c] < 0) {
+          depth[c] = di + 1;
+          changed = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (!changed) break;
+    __syncthreads();
+  }
+  // exclusive prefix count of even-depth nodes (one warp per 32 nodes, then
+  // a serial pass over the warp sums)
+  for (int i = tid; i < nn; i += nt) idx[i] = (depth[i] >= 0 && (depth[i] & 1) == 0) ? 1 : 0;
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < nn; ++i) {
+      int f = idx[i];
+      idx[i] = run;
+      run += f;
+    }
+    total = run;
+  }
+  __syncthreads();
+  for (int i = tid; i < nn; i += nt) {
+    if (!(depth[i] >= 0 && (depth[i] & 1) == 0)) continue;
+    int k[4] = {kEmpty, kEmpty, kEmpty, kEmpty}, sr[4] = {0, 0, 0, 0};
+    int m = 0;
+    for (int side = 0; side < 2; ++side) {
+      int c = kid(i, side);
+      if (c >= 0) {  // internal child: its two children become slots
+        for (int s2 = 0; s2 < 2; ++s2) {
+          int g = kid(c, s2);
+          k[m] = g >= 0 ? idx[g] : g;
+          sr[m] = (c << 1) | s2;
+          ++m;
+        }
+      } else {
+        k[m] = c;
+        sr[m] = (i << 1) | side;
+        ++m;
+      }
+    }
+    kid4[idx[i]] = make_int4(k[0], k[1], k[2], k[3]);
+    src4[idx[i]] = make_int4(sr[0], sr[1], sr[2], sr[3]);
+  }
+  if (tid < 2) {
+    int r = roots[tid];
+    roots4_out[tid] = (r >= 0 && r < nn) ? idx[r] : r;
+  }
+  if (tid == 0) *n4_out = total;
+}
+
+__device__ __forceinline__ unsigned qword(float lo, float hi, float o, float s) {
+  return qenc_lo(lo, o, s) | (qenc_hi(hi, o, s) << 16);
+}
+
+// Per frame: the 4-wide compact nodes from the current binary child boxes,
+// on the grid of k_quantize (written to qframe by the first thread).
+__global__ void k_quantize4(const float4* __restrict__ nodes, const int* __restrict__ n4p,
+                            const int4* __restrict__ kid4, const int4* __restrict__ src4,
+                            const float* __restrict__ root_box, int has0, int has1, uint4* q4, float* qframe) {
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  for (int t = 0; t < 2; ++t) {
+    if (!(t == 0 ? has0 : has1)) continue;
+    for (int k = 0; k < 3; ++k) {
+      float a = root_box[6 * t + k], b = root_box[6 * t + 3 + k];
+      if (isfinite(a)) lo[k] = fminf(lo[k], a);
+      if (isfinite(b)) hi[k] = fmaxf(hi[k], b);
+    }
+  }
+  float ext = 0.0f;
+  for (int k = 0; k < 3; ++k) {
+    if (!(hi[k] >= lo[k])) { lo[k] = 0.0f; hi[k] = 0.0f; }
+    ext = fmaxf(ext, hi[k] - lo[k]);
+  }
+  float pad = 1.0f + 1e-3f * ext;
+  float o[3], sc[3];
+  for (int k = 0; k < 3; ++k) {
+    o[k] = lo[k] - pad;
+    sc[k] = fmaxf((hi[k] - lo[k] + 2.0f * pad) / 65000.0f, 1e-6f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) { qframe[k] = o[k]; qframe[3 + k] = sc[k]; }
+  const int n4 = *n4p;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    int4 kd = kid4[i], sr = src4[i];
+    int kk[4] = {kd.x, kd.y, kd.z, kd.w}, ss[4] = {sr.x, sr.y, sr.z, sr.w};
+    unsigned w[12];
+    for (int j = 0; j < 4; ++j) {
+      if (kk[j] == kEmpty) {  // an inverted box: no ray meets it
+        w[3 * j] = w[3 * j + 1] = w[3 * j + 2] = 0x0000FFFFu;
+        continue;
+      }
+      const float4* n = nodes + 4 * (size_t)(ss[j] >> 1);
+      float4 n0 = n[0], n1 = n[1], n2 = n[2];
+      bool s1 = (ss[j] & 1) != 0;
+      float4 xy = s1 ? n1 : n0;
+      float zl = s1 ? n2.z : n2.x, zh = s1 ? n2.w : n2.y;
+      w[3 * j] = qword(xy.x, xy.y, o[0], sc[0]);
+      w[3 * j + 1] = qword(xy.z, xy.w, o[1], sc[1]);
+      w[3 * j + 2] = qword(zl, zh, o[2], sc[2]);
+    }
+    uint4* d = q4 + 4 * (size_t)i;
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    d[2] = make_uint4(w[8], w[9], w[10], w[11]);
+    d[3] = make_uint4((unsigned)kk[0], (unsigned)kk[1], (unsigned)kk[2], (unsigned)kk[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static inline int nblk(long n, int bs, int cap = 4096) {
@@ -993,6 +1139,26 @@ void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int
   if (g < 1) g = 1;
   if (g > 1024) g = 1024;
   k_quantize<<<g, 256, 0, st>>>(d_nodes, nn, d_root_box, has0, has1, d_qn, d_qframe);
+}
+
+
+cudaError_t launch_bvh4_map(const float4* d_nodes, int nn, const int* d_roots, int4* d_kid4, int4* d_src4,
+                            int* d_n4, int* d_roots4, cudaStream_t st) {
+  size_t smem = 2 * (size_t)(nn > 0 ? nn : 1) * sizeof(int);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bvh4_map, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_bvh4_map<<<1, 1024, smem, st>>>(d_nodes, nn, d_roots, d_kid4, d_src4, d_n4, d_roots4);
+  return cudaGetLastError();
+}
+
+void launch_quantize4(const float4* d_nodes, int n4_bound, const int* d_n4, const int4* d_kid4, const int4* d_src4,
+                      const float* d_root_box, int has0, int has1, uint4* d_q4, float* d_qframe, cudaStream_t st) {
+  int g = (n4_bound + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 1024) g = 1024;
+  k_quantize4<<<g, 256, 0, st>>>(d_nodes, d_n4, d_kid4, d_src4, d_root_box, has0, has1, d_q4, d_qframe);
 }
 
 size_t dyn_update_smem(int nd, int nobj) {

@@ -117,6 +117,16 @@ size_t dyn_update_smem(int nd, int nobj);
 void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int has0, int has1, uint4* d_qn,
                      float* d_qframe, cudaStream_t st);
 
+// 4-wide compact copy: map the binary trees (nn internal nodes, 2 root codes)
+// to 4-wide nodes once per topology (one CTA, nn <= 8192), then encode the
+// child boxes every frame. n4 and the 4-wide roots stay on the device.
+cudaError_t launch_bvh4_map(const float4* d_nodes, int nn, const int* d_roots, int4* d_kid4, int4* d_src4,
+                            int* d_n4, int* d_roots4, cudaStream_t st);
+void launch_quantize4(const float4* d_nodes, int n4_bound, const int* d_n4, const int4* d_kid4, const int4* d_src4,
+                      const float* d_root_box, int has0, int has1, uint4* d_q4, float* d_qframe, cudaStream_t st);
+// At most (2 + 2 nn) / 3 internal nodes of two trees lie at even depth.
+inline int bvh4_bound(int nn) { return (2 + 2 * nn) / 3; }
+
 // Per frame: world vertices of the moving triangles, per-object boxes and the
 // bottom-up refit of their tree (d_arrive zeroed by the caller).
 void launch_transform_refit(const float4* d_objv, const float* d_xf, int n, int nobj, int node_base,

@@ -429,6 +429,84 @@ __device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, c
   return slot_best;
 }
 
+// 4-wide compact nodes (shared memory), 64 bytes each: words 0-11 = the axis
+// words of children 0-3 (x, y, z per child, as in the 2-wide copy), words
+// 12-15 = the child codes (4-wide node index, leaf ~slot, or kEmpty with an
+// inverted box that no ray meets).
+__device__ __forceinline__ void cswap(float& da, int& ca, float& db, int& cb) {
+  bool sw = db < da;
+  float t = sw ? db : da;
+  db = sw ? da : db;
+  da = t;
+  int c = sw ? cb : ca;
+  cb = sw ? ca : cb;
+  ca = c;
+}
+
+// Closest hit as closest_hit(), over the 4-wide compact copy: per step the
+// four child boxes are tested, the hit ones ordered by entry distance, the
+// nearest visited next and the others pushed. Node visits count box pairs
+// (a 4-wide step = 2), the unit of the 2-wide traversals.
+__device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, const Bvh& bvh, int root0,
+                                              int root1, const RayPre& r, float tmin, int excl, float& t_best,
+                                              int& id_best, unsigned& overflow, unsigned& n_nodes,
+                                              unsigned& n_tris, TStack& st) {
+  QRay q;
+  if (!qray_make(f, r, q))
+    return closest_hit_far(bvh, r, tmin, excl, &t_best, &id_best, &overflow, &n_nodes, &n_tris, st.s, st.stride,
+                           st.cap);
+  const float inf = __int_as_float(0x7f800000);
+  st.reset();
+  t_best = inf;
+  id_best = 0x7fffffff;
+  int slot_best = -1;
+  if (root1 != kEmpty) st.push(root1);
+  int cur = root0;
+  if (cur == kEmpty) cur = st.empty() ? kEmpty : st.pop();
+  for (int visits = 0; cur != kEmpty; ++visits) {
+    if (visits > bvh.max_visits) {
+      overflow = 1u;
+      break;
+    }
+    if (cur >= 0) {
+      n_nodes += 2;
+      const uint4* nd = qn + 4 * cur;
+      uint4 A = nd[0], B = nd[1], C = nd[2], K = nd[3];
+      float t0, t1, t2, t3;
+      float d0 = qslab(q, A.x, A.y, A.z, t_best, t0) ? t0 : inf;
+      float d1 = qslab(q, A.w, B.x, B.y, t_best, t1) ? t1 : inf;
+      float d2 = qslab(q, B.z, B.w, C.x, t_best, t2) ? t2 : inf;
+      float d3 = qslab(q, C.y, C.z, C.w, t_best, t3) ? t3 : inf;
+      int c0 = (int)K.x, c1 = (int)K.y, c2 = (int)K.z, c3 = (int)K.w;
+      cswap(d0, c0, d1, c1);
+      cswap(d2, c2, d3, c3);
+      cswap(d0, c0, d2, c2);
+      cswap(d1, c1, d3, c3);
+      cswap(d1, c1, d2, c2);
+      if (d3 < inf && !st.push(c3)) overflow = 1u;
+      if (d2 < inf && !st.push(c2)) overflow = 1u;
+      if (d1 < inf && !st.push(c1)) overflow = 1u;
+      cur = d0 < inf ? c0 : (st.empty() ? kEmpty : st.pop());
+    } else {
+      int slot = ~cur;
+      ++n_tris;
+      float3 v0, v1, v2;
+      int id;
+      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      float t;
+      if (id != excl && tri_hit(r, v0, v1, v2, t) && t > tmin) {
+        if (t < t_best || (t == t_best && id < id_best)) {
+          t_best = t;
+          id_best = id;
+          slot_best = slot;
+        }
+      }
+      cur = st.empty() ? kEmpty : st.pop();
+    }
+  }
+  return slot_best;
+}
+
 // Any hit with t in (t0, t1), excluding ids ex0 and ex1 (occlusion test).
 __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t0, float t1,
                                         int ex0, int ex1, unsigned& overflow, TStack& st) {

@@ -16,6 +16,8 @@
 // same device code in both modes, so the result equals a full retrace.
 #include "trace.cuh"
 
+#include "bvh.cuh"
+
 namespace dcem {
 
 // ---------------------------------------------------------------------------
@@ -44,7 +46,8 @@ __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
 // restart point (0 in a full frame) to N: closest hit, segment log, specular
 // reflection. Captures are tested by k_capture.
 template <bool kQ>
-__device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st) {
+__device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st,
+                                           int qr0, int qr1) {
   const int R = a.R;
   const int nq = a.queue ? (int)min(*a.nq_dev, (unsigned)R) : R;
   const int lane = threadIdx.x & 31;
@@ -92,7 +95,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       float t;
       int id;
       unsigned nn = 0, nt = 0;
-      int slot = kQ ? closest_hit_q(qn, qf, a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st)
+      int slot = kQ ? closest_hit_q4(qn, qf, a.bvh, qr0, qr1, rp, a.tmin, last, t, id, ovf, nn, nt, st)
                     : closest_hit(a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st);
       ++segs;
       nodes += nn;
@@ -155,16 +158,18 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
   TStack st;
   bind_stack(st, sstk, kStackTrace);
   QFrame f{};
-  trace_rays<false>(a, nullptr, f, st);
+  trace_rays<false>(a, nullptr, f, st, kEmpty, kEmpty);
 }
 
-// Same traversal with the compact node copy staged in shared memory (one
-// CTA of kTraceQThreads threads per SM, the whole copy loaded once per CTA).
+// Same traversal over the 4-wide compact node copy staged in shared memory
+// (one CTA of kTraceQThreads threads per SM, the copy loaded once per CTA).
 __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   extern __shared__ uint4 sq[];
   TStack st;
-  bind_stack(st, reinterpret_cast<int*>(sq + 2 * a.n_nodes), a.stack_cap);
-  for (int i = threadIdx.x; i < 2 * a.n_nodes; i += blockDim.x) sq[i] = a.qnodes[i];
+  bind_stack(st, reinterpret_cast<int*>(sq + 4 * a.q4_bound), a.stack_cap);
+  const int n4 = min(*a.q4_count, a.q4_bound);
+  for (int i = threadIdx.x; i < 4 * n4; i += blockDim.x) sq[i] = a.qnodes[i];
+  const int qr0 = a.q4_roots[0], qr1 = a.q4_roots[1];
   QFrame f;
   f.ox = a.qframe[0];
   f.oy = a.qframe[1];
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   f.sy = a.qframe[4];
   f.sz = a.qframe[5];
   __syncthreads();
-  trace_rays<true>(a, sq, f, st);
+  trace_rays<true>(a, sq, f, st, qr0, qr1);
 }
 
 // Reception-sphere captures of the segments in the frame's capture list: the
@@ -363,7 +368,7 @@ static int resident_blocks(const void* fn, int sms, size_t smem) {
 }
 
 int trace_q_stack_cap(int n_nodes) {
-  long avail = kTraceQSmem - (long)n_nodes * 2 * (long)sizeof(uint4);
+  long avail = kTraceQSmem - (long)bvh4_bound(n_nodes) * 4 * (long)sizeof(uint4);
   int cap = avail > 0 ? (int)std::min<long>(kStackTrace, avail / (kTraceQThreads * (long)sizeof(int))) : 0;
   return (n_nodes > 0 && cap >= 12) ? cap : 0;
 }
@@ -373,7 +378,7 @@ cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
   if (!g_trace) g_trace = resident_blocks((const void*)k_trace, sms, 256 * kStackTrace * sizeof(int));
   long n = a.R;
   if (a.use_q) {
-    size_t smem = (size_t)a.n_nodes * 2 * sizeof(uint4) + (size_t)kTraceQThreads * a.stack_cap * sizeof(int);
+    size_t smem = (size_t)a.q4_bound * 4 * sizeof(uint4) + (size_t)kTraceQThreads * a.stack_cap * sizeof(int);
     static size_t attr = 0;
     if (smem > attr) {
       cudaError_t e = cudaFuncSetAttribute(k_trace_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

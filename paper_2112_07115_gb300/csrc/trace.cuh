@@ -14,9 +14,12 @@ struct TraceArgs {
   const float4* rx;        // nrx receivers (xyz)
   int nrx;
   SmallBvh rxt;            // per-frame tree over the receivers
-  const uint4* qnodes;     // compact node copy (2 uint4 per node) and its frame
+  const uint4* qnodes;     // 4-wide compact node copy (4 uint4 per node) and its frame
   const float* qframe;
-  int n_nodes;             // internal nodes of both trees
+  int n_nodes;             // internal nodes of both trees (2-wide)
+  const int* q4_count;     // 4-wide nodes (device), at most q4_bound
+  const int* q4_roots;     // roots of both trees in the 4-wide copy (device)
+  int q4_bound;
   int use_q;               // 1: traverse the compact copy from shared memory
   int stack_cap;           // shared-memory stack entries per thread with use_q
   float4* log_o;           // (N+1) x R: origin, unfolded length D
