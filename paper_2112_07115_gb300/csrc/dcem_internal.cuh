@@ -613,6 +613,19 @@ __device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __
                                              TStack& st, Emit&& emit) {
   int root = *t.root;
   if (root == kEmpty) return true;
+  // Every receiver lies in the root box, so a capture at s puts the segment
+  // within rho(s) <= rho(te) of that box: clip the culling length te to the
+  // exit of the box grown by the largest radius, twice (the second time
+  // with the radius at the first exit). The exact test keeps tend.
+  float te = tend;
+  {
+    const float* rb = t.root_box;
+    for (int it = 0; it < 2; ++it) {
+      float g = alpha * 1.001f * (D + te) + 0.01f, tn, tf;
+      if (!slab_io(r, rb[0] - g, rb[3] + g, rb[1] - g, rb[4] + g, rb[2] - g, rb[5] + g, te, tn, tf)) return true;
+      te = fminf(te, tf * 1.00001f + 1e-6f);
+    }
+  }
   st.reset();
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
@@ -624,8 +637,8 @@ __device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __
       const float4* n = t.nodes + 4 * (size_t)cur;
       float4 n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-      bool m0 = cone_box(r, D, tend, alpha, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
-      bool m1 = cone_box(r, D, tend, alpha, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
+      bool m0 = cone_box(r, D, te, alpha, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
+      bool m1 = cone_box(r, D, te, alpha, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w);
       if (m1 && !st.push(c1)) return false;
       if (m0 && !st.push(c0)) return false;
     }
