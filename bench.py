@@ -203,11 +203,12 @@ def run_ours(args):
         r.paths = paths_d.data_ptr()
         return r
 
-    def run(mode, frames, timed, timing):
+    def run(mode, frames, timed, timing, graphs=True):
         # timing 2: only the closest-hit kernel is bracketed by events (the
         # timed loops); timing 1: every stage (the instrumented pass)
         s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
         s.set_rays(rays)
+        s.set_graph_replay(graphs)
         prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=timing)
         res = new_result()
         stats, ms = [], []
@@ -239,6 +240,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     # full retrace of the same frames
     s_full, ms_full, st_full = run(dcem.MODE_FULL, frames, True, 2)
+    torch.cuda.synchronize()
+    # the coherent frames again, every operation launched on its own
+    s_dir, ms_dir, _ = run(dcem.MODE_COHERENT, frames, True, 2, graphs=False)
+    s_dir.close()
     clocks = clk.stop()
     # instrumented pass over the same frames (not timed): per-stage breakdown
     si, _, ist_coh = run(dcem.MODE_COHERENT, frames, True, 1)
@@ -247,7 +252,8 @@ def run_ours(args):
     si.close()
     t_coh = sum(ms_coh) / 1e3
     t_full = sum(ms_full) / 1e3
-    t_coh, t_full = max_over_ranks([t_coh, t_full], dev)
+    t_dir = sum(ms_dir) / 1e3
+    t_coh, t_full, t_dir = max_over_ranks([t_coh, t_full, t_dir], dev)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -380,6 +386,10 @@ def run_ours(args):
                      "stage_ms": {k: round(v, 4) for k, v in mean_stage_full.items()},
                      "frame_ms_p50_max": [round(float(np.median(ms_full)), 4), round(float(max(ms_full)), 4)],
                      "trace_roofline": roof_full_trace},
+            "graph_replay": {"frames_replayed_frac": round(float(np.mean([x["graph_replayed"] for x in st_coh])), 4),
+                             "direct_launch_frames_per_s": round(world * K / t_dir, 2),
+                             "note": "coherent frames launched as one replayed CUDA graph each (value) vs "
+                                     "operation by operation (direct)"},
             "coherent_speedup": round(fps_coh / fps_full, 3),
             "paths_per_frame": int(np.mean([x["paths_valid"] for x in st_coh])),
             "rx_power_err_db": err,

@@ -145,6 +145,8 @@ typedef struct {
   int32_t trace_kernel;        /* closest-hit kernel of this frame: 0 = nodes
                                   read from global memory, 1 = compact node
                                   copy in shared memory                          */
+  int32_t graph_replayed;      /* 1 if the frame's device work was launched as
+                                  one replayed CUDA graph                        */
 } dcem_stats;
 
 typedef struct {
@@ -216,6 +218,17 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
  * positions) instead of refitting it. ratio <= 0: refit only. Default 1.25.
  * Results never depend on the tree shape. Errors: DCEM_ERR_ARG. */
 int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
+
+/* Graph replay of dcem_trace_frame's device work (default on = 1). The work
+ * a frame enqueues (about 16 kernels, memsets and events) is fixed by its
+ * arguments: the scene's buffers, tx, nrx, params, the output pointers and
+ * the coherence state. When a call's arguments equal those of the call two
+ * frames earlier (the candidate buffers alternate), the work captured from
+ * that call is launched as one CUDA graph instead of operation by operation.
+ * Results are identical either way; stats.graph_replayed tells which ran.
+ * on = 0 launches every frame operation by operation. Errors: DCEM_ERR_ARG
+ * (on not 0 or 1). */
+int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on);
 
 /* Drops the coherence cache: the next COHERENT frame is a full retrace. */
 int dcem_scene_reset_cache(dcem_scene* s);

@@ -161,6 +161,38 @@ __global__ void k_gather_rays(const float4* __restrict__ src, const unsigned* __
 
 }  // namespace
 
+// Everything one frame enqueues is fixed by this plan: the kernels' argument
+// blocks, the launch shapes they imply and the switches below. Two frames with
+// byte-equal plans enqueue the same work, so a plan seen before replays the
+// CUDA graph captured from it (one launch) instead of ~16 stream operations.
+// The struct is zero-filled before it is set, so its padding compares equal.
+struct FramePlan {
+  int32_t coherent, tm, tk, use_q, nrx, R, has0, has1, q4_bound, nobj, ptr_dev;
+  TraceArgs a;
+  FramePrepArgs fp;
+  CoherentArgs c;
+  PathArgs q;
+  // quantisation and end-of-frame arguments (scene buffers)
+  const float4* nodes;
+  int* q4_count;
+  int4* q4_kid;
+  int4* q4_src;
+  float* root_box;
+  uint4* qnodes;
+  float* qframe;
+  float4 *rx_cur, *rx_traced;
+  float *xf_cur, *xf_traced;
+  unsigned *obj_box_cur, *obj_box_traced, *prev_ncand;
+  DevCounters *ctr, *uctr, *ctr_hd;
+  cudaEvent_t ev[10];
+};
+
+struct FrameGraph {
+  FramePlan key;
+  bool have_key = false;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct dcem_scene {
   int device = 0;
   int sms = 1;
@@ -272,6 +304,12 @@ struct dcem_scene {
   cudaEvent_t ev[10] = {};
   int launches = 0;  // kernels launched since the last completed frame
   int last_use_q = 0;  // closest-hit kernel of the last frame (1: shared-memory node copy)
+  // graph replay of the frame's device work (see FramePlan)
+  FramePlan plan;
+  FrameGraph fgraph[2];
+  cudaStream_t cap_st = nullptr;
+  bool use_graphs = true;
+  int graph_replayed = 0;
 };
 
 namespace {
@@ -301,6 +339,9 @@ void scene_free(dcem_scene* s) {
   dfree(s->mvt_arrive); dfree(s->mvt_root); dfree(s->mvt_root_box);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& g : s->fgraph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (s->cap_st) cudaStreamDestroy(s->cap_st);
   delete s;
 }
 
@@ -309,8 +350,6 @@ bool finite_arr(const float* p, size_t n) {
     if (!std::isfinite(p[i])) return false;
   return true;
 }
-
-int grid_cap_of(const dcem_scene* s, int per_sm) { return s->sms * per_sm; }
 
 int root_code(int n, int node_base, int leaf_base) {
   return n >= 2 ? node_base : (n == 1 ? ~leaf_base : kEmpty);
@@ -769,6 +808,12 @@ int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio) {
   return DCEM_OK;
 }
 
+int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on) {
+  if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
+  s->use_graphs = on != 0;
+  return DCEM_OK;
+}
+
 int dcem_scene_reset_cache(dcem_scene* s) {
   if (!s) return DCEM_ERR_ARG;
   s->cache_valid = false;
@@ -784,20 +829,22 @@ int dcem_scene_set_stream(dcem_scene* s, void* stream) {
 
 void dcem_scene_destroy(dcem_scene* s) { scene_free(s); }
 
-static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent,
-                      const dcem_result* out) {
-  cudaStream_t st = s->st;
+static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent,
+                      const dcem_result* out, FramePlan& P) {
+  std::memset(&P, 0, sizeof(P));
   int N = p->max_refl;
   int nxt = s->cur ^ 1;
-  bool tm = p->timing == 1;                     // every stage
-  bool tk = p->timing == 1 || p->timing == 2;   // the closest-hit kernel
-  if (tm) CK(cudaEventRecord(s->ev[0], st));
-  CK(cudaMemsetAsync(s->ctr, 0, sizeof(DevCounters), st));
-  // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
-  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) +
-                 (trace_q_stack_cap(s->nint_s + s->nint_d) > 0 ? 1 : 0);
+  P.coherent = coherent ? 1 : 0;
+  P.tm = p->timing == 1;                       // every stage
+  P.tk = p->timing == 1 || p->timing == 2;     // the closest-hit kernel
+  P.nrx = nrx;
+  P.R = s->R;
+  P.nobj = s->nobj;
+  P.has0 = s->root_h[0] != kEmpty;
+  P.has1 = s->root_h[1] != kEmpty;
+  P.ptr_dev = out->ptr_kind == DCEM_PTR_DEVICE;
 
-  TraceArgs a;
+  TraceArgs& a = P.a;
   a.bvh.nodes = s->nodes;
   a.bvh.tris = s->tris;
   a.bvh.root0 = s->root_h[0];
@@ -838,17 +885,12 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.q4_bound = bvh4_bound(a.n_nodes);
   // the compact copy of both trees and the CTA's stacks fit in shared
   // memory: traverse it there
-  {
-    a.stack_cap = trace_q_stack_cap(a.n_nodes);
-    a.use_q = (a.stack_cap > 0 && s->qnodes) ? 1 : 0;
-    s->last_use_q = a.use_q;
-  }
-  if (a.use_q) {
-    launch_quantize4(s->nodes, a.q4_bound, s->q4_count, s->q4_kid, s->q4_src, s->root_box, s->root_h[0] != kEmpty,
-                     s->root_h[1] != kEmpty, s->qnodes, s->qframe, st);
-    CK(cudaGetLastError());
-  }
-  FramePrepArgs fp;
+  a.stack_cap = trace_q_stack_cap(a.n_nodes);
+  a.use_q = (a.stack_cap > 0 && s->qnodes) ? 1 : 0;
+  P.use_q = a.use_q;
+  P.q4_bound = a.q4_bound;
+
+  FramePrepArgs& fp = P.fp;
   fp.rx3 = s->rx3;
   fp.nrx = nrx;
   fp.rx_cur = s->rx_cur;
@@ -882,10 +924,9 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   fp.tmv.arrive = s->mvt_arrive;
   fp.tmv.root = s->mvt_root;
   fp.tmv.root_box = s->mvt_root_box;
-  CK(launch_frame_prep(fp, st));
-  if (tm) CK(cudaEventRecord(s->ev[1], st));
+
   if (coherent) {
-    CoherentArgs c;
+    CoherentArgs& c = P.c;
     c.moved_list = s->moved_list;
     c.rx_moved = s->rx_moved;
     c.restart = s->restart;
@@ -899,18 +940,9 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
     c.mvt.root_box = s->mvt_root_box;
     c.mvt.max_visits = 2 * s->mv_cap + 8;
     c.mv_cap = s->mv_cap;
-    CK(launch_mark(a, c, grid_cap_of(s, 8), st));
-    CK(launch_carry(a, c, st));
-    a.queue = s->queue;
-    a.rx_moved = s->rx_moved;
   }
-  if (tk) CK(cudaEventRecord(s->ev[2], st));
-  if (s->R > 0) CK(launch_trace(a, s->sms, st));
-  if (tk) CK(cudaEventRecord(s->ev[3], st));
-  if (s->R > 0) CK(launch_capture(a, s->sms, st));
-  if (tm) CK(cudaEventRecord(s->ev[4], st));
 
-  PathArgs q;
+  PathArgs& q = P.q;
   q.R = s->R;
   q.log_id = s->log_id;
   q.cand = s->cand[nxt];
@@ -954,24 +986,132 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
   q.freq = p->freq_hz;
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
-  CK(launch_dedupe(q, grid_cap_of(s, 4), st));
-  if (tm) CK(cudaEventRecord(s->ev[5], st));
-  CK(launch_validate(q, grid_cap_of(s, 4), st));
-  if (tm) CK(cudaEventRecord(s->ev[6], st));
-  CK(launch_reduce(q, nrx, st));
-  if (tm) CK(cudaEventRecord(s->ev[7], st));
+
+  P.nodes = s->nodes;
+  P.q4_count = s->q4_count;
+  P.q4_kid = s->q4_kid;
+  P.q4_src = s->q4_src;
+  P.root_box = s->root_box;
+  P.qnodes = s->qnodes;
+  P.qframe = s->qframe;
+  P.rx_cur = s->rx_cur;
+  P.rx_traced = s->rx_traced;
+  P.xf_cur = s->xf_cur;
+  P.xf_traced = s->xf_traced;
+  P.obj_box_cur = s->obj_box_cur;
+  P.obj_box_traced = s->obj_box_traced;
+  P.prev_ncand = s->prev_ncand;
+  P.ctr = s->ctr;
+  P.uctr = s->uctr;
+  P.ctr_hd = s->ctr_hd;
+  for (int i = 0; i < 10; ++i) P.ev[i] = s->ev[i];
+}
+
+// Event record on a stream, or an event-record node when the stream is being
+// captured (so that the replayed graph records the event too).
+static cudaError_t rec(cudaEvent_t e, cudaStream_t st, bool cap) {
+  return cap ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+}
+
+// The frame's device work, in stream order; no host synchronisation.
+static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap) {
+  bool tm = P.tm, tk = P.tk;
+  if (tm) CK(rec(P.ev[0], st, cap));
+  CK(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
+  if (P.use_q) {
+    launch_quantize4(P.nodes, P.q4_bound, P.q4_count, P.q4_kid, P.q4_src, P.root_box, P.has0, P.has1, P.qnodes,
+                     P.qframe, st);
+    CK(cudaGetLastError());
+  }
+  CK(launch_frame_prep(P.fp, st));
+  if (tm) CK(rec(P.ev[1], st, cap));
+  TraceArgs a = P.a;
+  if (P.coherent) {
+    CK(launch_mark(a, P.c, sms * 8, st));
+    CK(launch_carry(a, P.c, st));
+    a.queue = P.a.queue_w;
+    a.rx_moved = P.c.rx_moved;
+  }
+  if (tk) CK(rec(P.ev[2], st, cap));
+  if (P.R > 0) CK(launch_trace(a, sms, st));
+  if (tk) CK(rec(P.ev[3], st, cap));
+  if (P.R > 0) CK(launch_capture(a, sms, st));
+  if (tm) CK(rec(P.ev[4], st, cap));
+  CK(launch_dedupe(P.q, sms * 4, st));
+  if (tm) CK(rec(P.ev[5], st, cap));
+  CK(launch_validate(P.q, sms * 4, st));
+  if (tm) CK(rec(P.ev[6], st, cap));
+  CK(launch_reduce(P.q, P.nrx, st));
+  if (tm) CK(rec(P.ev[7], st, cap));
   // state the next frame compares against, and the counters to the host
   {
-    int n = std::max(nrx, 12 * s->nobj);
+    int n = std::max(P.nrx, 12 * P.nobj);
     int g = std::max(1, std::min(64, (n + 255) / 256));
-    k_frame_end<<<g, 256, 0, st>>>(s->rx_cur, s->rx_traced, nrx, s->xf_cur, s->xf_traced, s->obj_box_cur,
-                                   s->obj_box_traced, s->nobj, s->ctr, s->uctr, s->prev_ncand, s->ctr_hd);
+    k_frame_end<<<g, 256, 0, st>>>(P.rx_cur, P.rx_traced, P.nrx, P.xf_cur, P.xf_traced, P.obj_box_cur,
+                                   P.obj_box_traced, P.nobj, P.ctr, P.uctr, P.prev_ncand, P.ctr_hd);
     CK(cudaGetLastError());
   }
   // with device outputs nothing follows on the stream: the frame ends here
-  if (tm && out->ptr_kind == DCEM_PTR_DEVICE) CK(cudaEventRecord(s->ev[8], st));
+  if (tm && P.ptr_dev) CK(rec(P.ev[8], st, cap));
+  return DCEM_OK;
+}
+// Captures the frame's work from its plan into a graph on the scene's
+// capture stream (nothing runs while capturing) and instantiates it.
+static int capture_frame(dcem_scene* s, const FramePlan& P, cudaGraphExec_t* exec) {
+  if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_frame(P, s->sms, s->cap_st, true);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
+  if (rc == DCEM_OK && e != cudaSuccess) rc = status_of(e);
+  if (rc == DCEM_OK) {
+    e = cudaGraphInstantiate(exec, g, 0);
+    if (e != cudaSuccess) {
+      *exec = nullptr;
+      rc = status_of(e);
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return rc;
+}
+
+static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent,
+                      const dcem_result* out) {
+  cudaStream_t st = s->st;
+  FramePlan& P = s->plan;
+  make_plan(s, tx, nrx, p, coherent, out, P);
+  s->last_use_q = P.use_q;
+  // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
+  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) + (P.use_q ? 1 : 0);
+  // Plans alternate with the candidate buffers' parity: one cached graph per
+  // parity. A plan is captured the second time it is seen in a row (the
+  // first run also sets every kernel's launch attributes), then replayed.
+  s->graph_replayed = 0;
+  FrameGraph& G = s->fgraph[s->cur];
+  bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
+  if (!same) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.key = P;
+    G.have_key = true;
+  }
+  if (s->use_graphs && same && !G.exec) {
+    int rc = capture_frame(s, P, &G.exec);
+    if (rc != DCEM_OK) {
+      G.have_key = false;
+      return rc;
+    }
+  }
+  if (s->use_graphs && same && G.exec) {
+    CK(cudaGraphLaunch(G.exec, st));
+    s->graph_replayed = 1;
+  } else {
+    int rc = enqueue_frame(P, s->sms, st, false);
+    if (rc != DCEM_OK) return rc;
+  }
   CK(cudaStreamSynchronize(st));
-  s->cur = nxt;
+  s->cur ^= 1;
   return DCEM_OK;
 }
 
@@ -1064,6 +1204,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   S.node_visits = (int64_t)c[0].node_visits;
   S.max_segment_nodes = (int32_t)c[0].max_seg_nodes;
   S.trace_kernel = s->last_use_q;
+  S.graph_replayed = s->graph_replayed;
   S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;

@@ -30,7 +30,8 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_set_stream", "dcem_scene_destroy", "dcem_status_string", "dcem_scene_info",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
             "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
-            "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients"]
+            "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients",
+            "dcem_scene_set_graph_replay"]
 
 
 class Material(C.Structure):
@@ -61,7 +62,8 @@ class Stats(C.Structure):
                 ("stack_overflow", C.c_int32), ("coherent", C.c_int32),
                 ("kernel_launches", C.c_int32), ("bvh_rebuilt", C.c_int32),
                 ("ms_stage", C.c_float * 10), ("bvh_cost_ratio", C.c_float),
-                ("max_segment_nodes", C.c_int32), ("trace_kernel", C.c_int32)]
+                ("max_segment_nodes", C.c_int32), ("trace_kernel", C.c_int32),
+                ("graph_replayed", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -109,6 +111,7 @@ def lib():
         L.dcem_scene_get_ray_log.argtypes = [vp, vp, vp, vp]
         L.dcem_scene_get_candidates.argtypes = [vp, vp, i64, P(i64)]
         L.dcem_scene_set_rebuild_threshold.argtypes = [vp, C.c_float]
+        L.dcem_scene_set_graph_replay.argtypes = [vp, i32]
         L.dcem_reduce_paths_noalloc.argtypes = [vp, i32, i32, C.c_double, vp, vp, vp, vp]
         L.dcem_scene_gradient_size.argtypes = [vp, P(i32)]
         L.dcem_path_gradients.argtypes = [vp, vp, vp, i32, i32, vp, i32, P(Params), i32, vp, vp, vp]
@@ -208,6 +211,10 @@ def dcem_trace_frame(h, tx, rx, params: Params, result: Result) -> int:
 
 def dcem_scene_set_rebuild_threshold(h, ratio: float):
     _check(lib().dcem_scene_set_rebuild_threshold(h, float(ratio)), "dcem_scene_set_rebuild_threshold")
+
+
+def dcem_scene_set_graph_replay(h, on: bool):
+    _check(lib().dcem_scene_set_graph_replay(h, int(bool(on))), "dcem_scene_set_graph_replay")
 
 
 def dcem_reduce_paths_noalloc(paths_ptr, n_paths, nrx, tx_power_w, field_ptr, p_coh_ptr, p_inc_ptr,
@@ -387,6 +394,9 @@ class Scene:
 
     def set_rebuild_threshold(self, ratio: float):
         dcem_scene_set_rebuild_threshold(self.h, ratio)
+
+    def set_graph_replay(self, on: bool):
+        dcem_scene_set_graph_replay(self.h, on)
 
     def world_tris(self):
         return dcem_scene_get_world_tris(self.h, self.ntri)

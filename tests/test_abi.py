@@ -96,6 +96,7 @@ def test_null_scene_calls(L):
     assert lib.dcem_scene_set_rays(None, None, 0) == L.ERR_ARG
     assert lib.dcem_scene_update_transforms(None, None, 0) == L.ERR_ARG
     assert lib.dcem_scene_reset_cache(None) == L.ERR_ARG
+    assert lib.dcem_scene_set_graph_replay(None, 1) == L.ERR_ARG
     assert lib.dcem_scene_info(None, None, None, None, None, None) == L.ERR_ARG
     n = C.c_int32(0)
     assert lib.dcem_scene_gradient_size(None, C.byref(n)) == L.ERR_ARG
