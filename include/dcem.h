@@ -106,7 +106,13 @@ typedef struct {
   int32_t depth;                    /* number of reflections k                  */
   int32_t tri[DCEM_MAX_REFL];       /* reflecting triangle ids, Tx side first   */
   uint32_t flags;                   /* DCEM_PATH_* bits                         */
-  int32_t ray;                      /* a ray that discovered the path           */
+  int32_t ray;                      /* a ray that discovered the path (index
+                                       into the caller's directions; with
+                                       several ray sets, into their
+                                       concatenation)                           */
+  int32_t tx;                       /* transmitter (ray set); 0 from
+                                       dcem_trace_frame                         */
+  int32_t reserved;                 /* 0                                        */
   uint64_t key;                     /* 64-bit hash of (rx, depth, tri[0..k))    */
   double len_m;                     /* unfolded path length L                   */
   double delay_s;                   /* L / c                                    */
@@ -152,10 +158,12 @@ typedef struct {
 typedef struct {
   int32_t ptr_kind;     /* DCEM_PTR_HOST / DCEM_PTR_DEVICE for the arrays below */
   int32_t max_paths;    /* capacity of `paths`                                  */
-  double* field;        /* nrx x 2 (re, im) of sum a, or NULL                   */
-  double* p_coh_dbm;    /* nrx: P_t |sum a|^2 in dBm (-inf without paths)      */
-  double* p_inc_dbm;    /* nrx: P_t sum |a|^2 in dBm                           */
-  dcem_path* paths;     /* max_paths records ordered by (rx, key), or NULL     */
+  double* field;        /* links x 2 (re, im) of sum a, or NULL; links = nrx
+                           (dcem_trace_frame) or ntx * nrx (dcem_trace_links,
+                           link t * nrx + r)                                    */
+  double* p_coh_dbm;    /* links: P_t |sum a|^2 in dBm (-inf without paths)    */
+  double* p_inc_dbm;    /* links: P_t sum |a|^2 in dBm                         */
+  dcem_path* paths;     /* max_paths records ordered by (link, key), or NULL   */
   int32_t n_paths;      /* out: number of valid paths (may exceed max_paths:
                            then DCEM_ERR_CAPACITY and the first max_paths are
                            written)                                             */
@@ -185,6 +193,16 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat,
  * and at most 2^27 (DCEM_ERR_ARG above). Invalidates the coherence cache. */
 int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays);
 
+/* Ray sets of several transmitters (Sec. III step 1 for each of them), for
+ * dcem_trace_links: host; dirs holds the sets' unit directions one after the
+ * other (n_rays[0] + ... + n_rays[ntx-1] rows of 3 floats), and set t is the
+ * sampled sphere of transmitter t. Each set keeps its own angular spacing
+ * alpha_t = sqrt(4 pi / n_rays[t]) for its reception spheres, so budgets may
+ * differ. 1 <= ntx <= 4096, every n_rays[t] >= 1, total <= 2^27
+ * (DCEM_ERR_ARG otherwise). dcem_scene_set_rays(s, d, n) is one set of n.
+ * Invalidates the coherence cache. */
+int dcem_scene_set_ray_sets(dcem_scene* s, const float* dirs, const int32_t* n_rays, int32_t ntx);
+
 /* Per-frame update (Sec. III "Efficient BVH updating"): xf holds nobj
  * row-major 3x4 transforms (host or device per ptr_kind). World vertices are
  * recomputed as fmaf(R0,x, fmaf(R1,y, fmaf(R2,z,t))) per row and the moving
@@ -203,10 +221,28 @@ int dcem_scene_update_transforms(dcem_scene* s, const float* xf, int32_t ptr_kin
  * COHERENT mode falls back to a full retrace (stats.coherent = 0) when the
  * ray set, tx, nrx or the parameters changed since the cached frame. Results
  * equal a full retrace bit for bit. Synchronises the scene stream.
- * Errors: DCEM_ERR_ARG, DCEM_ERR_STATE (no rays set), DCEM_ERR_NONFINITE,
+ * Errors: DCEM_ERR_ARG, DCEM_ERR_STATE (no rays set, or more than one ray
+ * set), DCEM_ERR_NONFINITE,
  * DCEM_ERR_CAPACITY (out->n_paths holds the required count),
  * DCEM_ERR_STACK, DCEM_ERR_HASH, DCEM_ERR_CUDA. */
 int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nrx,
+                     int32_t rx_ptr_kind, const dcem_params* params, dcem_result* out);
+
+/* One frame of ntx transmitters against the same receivers, every
+ * transmitter's ray set traced, captured, deduplicated, validated and summed
+ * in the same kernel launches (as dcem_trace_frame per transmitter, at once):
+ *   tx       host, ntx x 3 floats; ntx equals the scene's number of ray sets
+ *   rx       nrx*3 floats (host or device per rx_ptr_kind), shared by all
+ *   params   host (tx_power_w applies to every transmitter)
+ *   out      per link l = t * nrx + r: field[l], p_coh_dbm[l], p_inc_dbm[l];
+ *            path records carry tx and rx and are ordered by (link, key)
+ * Transmitter t's paths and power equal those of dcem_trace_frame with tx[t]
+ * and set t alone as the scene's rays. ntx * nrx <= 2^24. COHERENT mode
+ * reuses the cache when no transmitter, parameter or nrx changed.
+ * dcem_trace_frame is this call with ntx = 1 (and requires one ray set).
+ * Errors: as dcem_trace_frame; DCEM_ERR_STATE if ntx differs from the
+ * scene's ray-set count. */
+int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
                      int32_t rx_ptr_kind, const dcem_params* params, dcem_result* out);
 
 /* Quality-driven rebuild of the moving-object hierarchy (Sec. III "Efficient
@@ -219,12 +255,14 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
  * Results never depend on the tree shape. Errors: DCEM_ERR_ARG. */
 int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
 
-/* Graph replay of dcem_trace_frame's device work (default on = 1). The work
- * a frame enqueues (about 16 kernels, memsets and events) is fixed by its
- * arguments: the scene's buffers, tx, nrx, params, the output pointers and
- * the coherence state. When a call's arguments equal those of the call two
- * frames earlier (the candidate buffers alternate), the work captured from
- * that call is launched as one CUDA graph instead of operation by operation.
+/* Graph replay of dcem_trace_frame's and dcem_trace_links' device work
+ * (default on = 1). The work a frame enqueues (about 16 kernels, memsets,
+ * copies and events) is fixed by the scene's buffers, nrx, the traversal and
+ * field parameters, the output pointers and whether the frame is coherent;
+ * transmitter positions and capture radii are copied in as data. When these
+ * equal those of the call two frames earlier (the candidate buffers
+ * alternate), the work captured from that call is launched as one CUDA graph
+ * instead of operation by operation.
  * Results are identical either way; stats.graph_replayed tells which ran.
  * on = 0 launches every frame operation by operation. Errors: DCEM_ERR_ARG
  * (on not 0 or 1). */
@@ -290,7 +328,8 @@ int dcem_scene_gradient_size(const dcem_scene* s, int32_t* n_params);
  *   rx          nrx x 3 floats (host or device per rx_ptr_kind)
  *   paths       n_paths records (host or device per ptr_kind) grouped by
  *               receiver in non-decreasing rx order, as dcem_trace_frame
- *               writes them; rx, depth and tri[0..depth) are read
+ *               writes them; rx, depth and tri[0..depth) are read (the
+ *               paths of the one transmitter tx: their tx field is not read)
  *   params      freq_hz, tx_power_w, pol, max_refl (>= every path's depth)
  *   field       nrx x 2 (re, im) of sum a over the paths, or NULL
  *   dfield      nrx x n_params x 2 (re, im) of d(sum a)/d theta, theta in
@@ -319,7 +358,8 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
  * reserved while the library is loaded).
  *   paths      device, n_paths records (e.g. the paths dcem_trace_frame
  *              wrote to a device result); order does not matter
- *   nrx        receivers; every paths[i].rx must lie in [0, nrx)
+ *   nrx        receivers; every paths[i].rx must lie in [0, nrx) (the
+ *              records of one transmitter: paths[i].tx is not read)
  *   tx_power_w transmit power (> 0)
  *   field      device, nrx x 2 (re, im) of sum a, or NULL
  *   p_coh_dbm  device, nrx values of P_t |sum a|^2 in dBm, or NULL

@@ -150,6 +150,13 @@ __global__ void k_ray_keys(const float4* __restrict__ d, int n, unsigned* keys, 
   }
 }
 
+// Sort key of the second pass: the set of the ray at each sorted position.
+__global__ void k_set_keys(const float4* __restrict__ src, const unsigned* __restrict__ idx, int n,
+                           unsigned* keys) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    keys[i] = __float_as_uint(src[idx[i]].w);
+}
+
 __global__ void k_gather_rays(const float4* __restrict__ src, const unsigned* __restrict__ idx, int n,
                               float4* dst, int* perm) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -167,7 +174,7 @@ __global__ void k_gather_rays(const float4* __restrict__ src, const unsigned* __
 // CUDA graph captured from it (one launch) instead of ~16 stream operations.
 // The struct is zero-filled before it is set, so its padding compares equal.
 struct FramePlan {
-  int32_t coherent, tm, tk, use_q, nrx, R, has0, has1, q4_bound, nobj, ptr_dev;
+  int32_t coherent, tm, tk, use_q, nrx, R, has0, has1, q4_bound, nobj, ptr_dev, nsets, nlinks;
   TraceArgs a;
   FramePrepArgs fp;
   CoherentArgs c;
@@ -184,6 +191,9 @@ struct FramePlan {
   float *xf_cur, *xf_traced;
   unsigned *obj_box_cur, *obj_box_traced, *prev_ncand;
   DevCounters *ctr, *uctr, *ctr_hd;
+  float4* txs;           // transmitters (device), copied from the pinned txs_h
+  const float4* txs_h;
+  unsigned* bucket_cnt;  // cleared by a memset when there are more links than receivers
   cudaEvent_t ev[10];
 };
 
@@ -252,6 +262,10 @@ struct dcem_scene {
   float4* rays = nullptr;        // sorted by direction: slot order
   int* ray_perm = nullptr;       // slot -> caller's ray index
   std::vector<int> ray_perm_h;
+  int nsets = 0;                 // ray sets (transmitters); rays[].w holds the set
+  std::vector<int> set_rays_h;   // rays per set
+  float4* txs = nullptr;         // per set: transmitter xyz and capture spacing (device)
+  float4* txs_h = nullptr;       // the same, pinned host staging copied in every frame
   int logW = 0;
   float4* log_o = nullptr;
   float4* log_d = nullptr;
@@ -285,6 +299,8 @@ struct dcem_scene {
   int* bucket = nullptr;
   unsigned* bucket_cnt = nullptr;
   int bucket_cap = 1024;
+  int nlink_cap = 0;             // links (transmitter-receiver pairs) the arrays below hold
+  unsigned* link_off = nullptr;  // per link output offset (many links)
   double* rxout = nullptr;
   // per-frame trees over the receivers and over the moved-object boxes
   float* rx_prim = nullptr;
@@ -298,7 +314,7 @@ struct dcem_scene {
   // coherence cache
   bool cache_valid = false;
   dcem_params cparams;
-  float ctx[3] = {0, 0, 0};
+  std::vector<float> ctx;        // transmitters of the cached frame
   int cnrx = -1;
   unsigned last_ncand = 0;
   cudaEvent_t ev[10] = {};
@@ -333,7 +349,8 @@ void scene_free(dcem_scene* s) {
   dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
   dfree(s->vpts); dfree(s->vstate);
   dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list); dfree(s->bucket);
-  dfree(s->bucket_cnt); dfree(s->rxout);
+  dfree(s->bucket_cnt); dfree(s->rxout); dfree(s->link_off); dfree(s->txs);
+  if (s->txs_h) cudaFreeHost(s->txs_h);
   dfree(s->rx_prim); dfree(s->rxt_nodes); dfree(s->rxt_parent); dfree(s->rxt_perm); dfree(s->rxt_arrive);
   dfree(s->rxt_root); dfree(s->rxt_root_box); dfree(s->mvt_nodes); dfree(s->mvt_parent); dfree(s->mvt_perm);
   dfree(s->mvt_arrive); dfree(s->mvt_root); dfree(s->mvt_root_box);
@@ -469,29 +486,42 @@ int ensure_paths(dcem_scene* s, unsigned cand_cap, unsigned ucap) {
   return DCEM_OK;
 }
 
-int ensure_rx(dcem_scene* s, int nrx, int bucket_cap) {
-  if (nrx <= s->nrx_cap && bucket_cap <= s->bucket_cap && s->rx3) return DCEM_OK;
-  int cap = nrx > s->nrx_cap ? nrx : s->nrx_cap;
-  if (cap < 1) cap = 1;
-  dfree(s->rx3); dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list);
-  dfree(s->bucket); dfree(s->bucket_cnt); dfree(s->rxout);
-  CK(dalloc(&s->rx3, 3 * (size_t)cap));
-  CK(dalloc(&s->rx_cur, cap));
-  CK(dalloc(&s->rx_traced, cap));
-  CK(dalloc(&s->rx_moved, cap));
-  CK(dalloc(&s->moved_list, cap));
-  if (bucket_cap > s->bucket_cap) s->bucket_cap = bucket_cap;
-  CK(dalloc(&s->bucket, (size_t)cap * s->bucket_cap));
-  CK(dalloc(&s->bucket_cnt, cap));
-  CK(dalloc(&s->rxout, 4 * (size_t)cap));  // staging: field (2 cap), P_coh (cap), P_inc (cap)
-  dfree(s->rx_prim); dfree(s->rxt_nodes); dfree(s->rxt_parent); dfree(s->rxt_perm); dfree(s->rxt_arrive);
-  CK(dalloc(&s->rx_prim, 6 * (size_t)cap));
-  CK(dalloc(&s->rxt_nodes, 4 * (size_t)cap));
-  CK(dalloc(&s->rxt_parent, cap));
-  CK(dalloc(&s->rxt_perm, cap));
-  CK(dalloc(&s->rxt_arrive, cap));
-  s->nrx_cap = cap;
-  s->cache_valid = false;
+// Receiver arrays for nrx receivers, and link arrays (buckets of valid
+// paths, staged outputs, output offsets) for nlinks transmitter-receiver
+// pairs with bucket_cap paths each.
+int ensure_rx(dcem_scene* s, int nrx, int nlinks, int bucket_cap) {
+  if (nrx > s->nrx_cap || !s->rx3) {
+    int cap = std::max(1, std::max(nrx, s->nrx_cap));
+    dfree(s->rx3); dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list);
+    CK(dalloc(&s->rx3, 3 * (size_t)cap));
+    CK(dalloc(&s->rx_cur, cap));
+    CK(dalloc(&s->rx_traced, cap));
+    CK(dalloc(&s->rx_moved, cap));
+    CK(dalloc(&s->moved_list, cap));
+    dfree(s->rx_prim); dfree(s->rxt_nodes); dfree(s->rxt_parent); dfree(s->rxt_perm); dfree(s->rxt_arrive);
+    CK(dalloc(&s->rx_prim, 6 * (size_t)cap));
+    CK(dalloc(&s->rxt_nodes, 4 * (size_t)cap));
+    CK(dalloc(&s->rxt_parent, cap));
+    CK(dalloc(&s->rxt_perm, cap));
+    CK(dalloc(&s->rxt_arrive, cap));
+    s->nrx_cap = cap;
+    s->cache_valid = false;
+  }
+  if (nlinks > s->nlink_cap || bucket_cap > s->bucket_cap || !s->bucket) {
+    int cap = std::max(1, std::max(nlinks, s->nlink_cap));
+    bool first = !s->bucket;
+    // many links start with smaller buckets (grown on overflow)
+    if (first)
+      while (bucket_cap > 64 && (size_t)cap * bucket_cap > ((size_t)1 << 26)) bucket_cap >>= 1;
+    dfree(s->bucket); dfree(s->bucket_cnt); dfree(s->rxout); dfree(s->link_off);
+    s->bucket_cap = first ? bucket_cap : std::max(bucket_cap, s->bucket_cap);
+    CK(dalloc(&s->bucket, (size_t)cap * s->bucket_cap));
+    CK(dalloc(&s->bucket_cnt, cap));
+    CK(dalloc(&s->rxout, 4 * (size_t)cap));  // staging: field (2 cap), P_coh (cap), P_inc (cap)
+    CK(dalloc(&s->link_off, cap));
+    s->nlink_cap = cap;
+    s->cache_valid = false;
+  }
   return DCEM_OK;
 }
 
@@ -500,8 +530,10 @@ bool same_traversal(const dcem_params& a, const dcem_params& b) {
          a.escape_len == b.escape_len;
 }
 
-float alpha_eff_of(const dcem_scene* s, const dcem_params* p) {
-  double alpha = std::sqrt(4.0 * M_PI / (double)(s->R > 0 ? s->R : 1));
+// Reception-sphere spacing of a set of n rays (Sec. III step 1: angular
+// spacing alpha = sqrt(4 pi / n)), times the radius scale, over sqrt(3).
+float alpha_eff_of(int n, const dcem_params* p) {
+  double alpha = std::sqrt(4.0 * M_PI / (double)(n > 0 ? n : 1));
   return (float)((double)p->rx_radius_scale * alpha / std::sqrt(3.0));
 }
 
@@ -713,50 +745,80 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
 }
 
 int dcem_scene_set_rays(dcem_scene* s, const float* dirs, int32_t n_rays) {
-  if (!s || n_rays < 0 || n_rays > (1 << 27) || (n_rays > 0 && !dirs)) return DCEM_ERR_ARG;
-  if (n_rays > 0 && !finite_arr(dirs, 3 * (size_t)n_rays)) return DCEM_ERR_NONFINITE;
-  for (int i = 0; i < n_rays; ++i) {
+  if (!s || n_rays < 0) return DCEM_ERR_ARG;
+  return dcem_scene_set_ray_sets(s, dirs, &n_rays, 1);
+}
+
+int dcem_scene_set_ray_sets(dcem_scene* s, const float* dirs, const int32_t* n_rays, int32_t ntx) {
+  if (!s || !n_rays || ntx < 1 || ntx > kMaxRaySets) return DCEM_ERR_ARG;
+  long long total = 0;
+  for (int t = 0; t < ntx; ++t) {
+    // one set may be empty only when it is the only one (dcem_scene_set_rays(s, _, 0))
+    if (n_rays[t] < (ntx > 1 ? 1 : 0)) return DCEM_ERR_ARG;
+    total += n_rays[t];
+  }
+  if (total > (1 << 27) || (total > 0 && !dirs)) return DCEM_ERR_ARG;
+  const int n = (int)total;
+  if (n > 0 && !finite_arr(dirs, 3 * (size_t)n)) return DCEM_ERR_NONFINITE;
+  for (int i = 0; i < n; ++i) {
     float x = dirs[3 * i], y = dirs[3 * i + 1], z = dirs[3 * i + 2];
     if (!(x * x + y * y + z * z > 0.0f)) return DCEM_ERR_ARG;
   }
   CK(cudaStreamSynchronize(s->st));
   dfree(s->rays); dfree(s->ray_perm); dfree(s->nseg); dfree(s->restart); dfree(s->queue);
   dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems);
+  dfree(s->txs);
+  if (s->txs_h) cudaFreeHost(s->txs_h);
+  s->txs_h = nullptr;
   s->logW = 0;
-  s->R = n_rays;
+  s->R = n;
   s->rays_set = false;
-  CK(dalloc(&s->rays, n_rays));
-  CK(dalloc(&s->ray_perm, n_rays));
-  CK(dalloc(&s->nseg, n_rays));
-  CK(dalloc(&s->restart, n_rays));
-  CK(dalloc(&s->queue, n_rays));
-  s->ray_perm_h.assign(n_rays, 0);
-  if (n_rays) {
-    // upload, then reorder the rays by direction so that a warp's rays are
+  s->nsets = ntx;
+  s->set_rays_h.assign(n_rays, n_rays + ntx);
+  CK(dalloc(&s->txs, ntx));
+  CK(cudaHostAlloc((void**)&s->txs_h, sizeof(float4) * ntx, cudaHostAllocDefault));
+  CK(dalloc(&s->rays, n));
+  CK(dalloc(&s->ray_perm, n));
+  CK(dalloc(&s->nseg, n));
+  CK(dalloc(&s->restart, n));
+  CK(dalloc(&s->queue, n));
+  s->ray_perm_h.assign(n, 0);
+  if (n) {
+    // upload (.w = the ray's set), then order the rays by set and, within a
+    // set, by direction, so that a warp's rays share a transmitter and are
     // close in angle (the caller's order is kept in ray_perm)
-    std::vector<float4> h(n_rays);
-    for (int i = 0; i < n_rays; ++i) h[i] = make_float4(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], 0.0f);
+    std::vector<float4> h(n);
+    for (int t = 0, i = 0; t < ntx; ++t)
+      for (int k = 0; k < n_rays[t]; ++k, ++i) {
+        float sid;
+        std::memcpy(&sid, &t, sizeof(int));
+        h[i] = make_float4(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], sid);
+      }
     float4* src = nullptr;
     unsigned *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr;
-    int nb = (n_rays + 1023) / 1024;
-    cudaError_t e = dalloc(&src, n_rays);
-    if (!e) e = dalloc(&k0, n_rays);
-    if (!e) e = dalloc(&v0, n_rays);
-    if (!e) e = dalloc(&k1, n_rays);
-    if (!e) e = dalloc(&v1, n_rays);
+    int nb = (n + 1023) / 1024;
+    cudaError_t e = dalloc(&src, n);
+    if (!e) e = dalloc(&k0, n);
+    if (!e) e = dalloc(&v0, n);
+    if (!e) e = dalloc(&k1, n);
+    if (!e) e = dalloc(&v1, n);
     if (!e) e = dalloc(&hist, (size_t)256 * nb);
-    if (!e) e = cudaMemcpyAsync(src, h.data(), sizeof(float4) * n_rays, cudaMemcpyHostToDevice, s->st);
+    if (!e) e = cudaMemcpyAsync(src, h.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st);
     if (!e) {
-      int g = std::min((n_rays + 255) / 256, 4096);
-      k_ray_keys<<<g, 256, 0, s->st>>>(src, n_rays, k0, v0);
-      e = sort_pairs_u32(k0, v0, k1, v1, hist, n_rays, 32, s->st);
+      int g = std::min((n + 255) / 256, 4096);
+      k_ray_keys<<<g, 256, 0, s->st>>>(src, n, k0, v0);
+      e = sort_pairs_u32(k0, v0, k1, v1, hist, n, 32, s->st);
+      if (!e && ntx > 1) {
+        // stable second pass by set
+        k_set_keys<<<g, 256, 0, s->st>>>(src, v0, n, k0);
+        e = sort_pairs_u32(k0, v0, k1, v1, hist, n, ntx > 256 ? 16 : 8, s->st);
+      }
       if (!e) {
-        k_gather_rays<<<g, 256, 0, s->st>>>(src, v0, n_rays, s->rays, s->ray_perm);
+        k_gather_rays<<<g, 256, 0, s->st>>>(src, v0, n, s->rays, s->ray_perm);
         e = cudaGetLastError();
       }
     }
-    if (!e) e = cudaMemcpyAsync(s->ray_perm_h.data(), s->ray_perm, sizeof(int) * n_rays, cudaMemcpyDeviceToHost,
-                                s->st);
+    if (!e) e = cudaMemcpyAsync(s->ray_perm_h.data(), s->ray_perm, sizeof(int) * n, cudaMemcpyDeviceToHost, s->st);
     if (!e) e = cudaStreamSynchronize(s->st);
     dfree(src); dfree(k0); dfree(v0); dfree(k1); dfree(v1); dfree(hist);
     CK(e);
@@ -829,8 +891,8 @@ int dcem_scene_set_stream(dcem_scene* s, void* stream) {
 
 void dcem_scene_destroy(dcem_scene* s) { scene_free(s); }
 
-static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent,
-                      const dcem_result* out, FramePlan& P) {
+static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coherent, const dcem_result* out,
+                      FramePlan& P) {
   std::memset(&P, 0, sizeof(P));
   int N = p->max_refl;
   int nxt = s->cur ^ 1;
@@ -843,6 +905,8 @@ static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params
   P.has0 = s->root_h[0] != kEmpty;
   P.has1 = s->root_h[1] != kEmpty;
   P.ptr_dev = out->ptr_kind == DCEM_PTR_DEVICE;
+  P.nsets = s->nsets;
+  P.nlinks = s->nsets * nrx;
 
   TraceArgs& a = P.a;
   a.bvh.nodes = s->nodes;
@@ -851,12 +915,12 @@ static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params
   a.bvh.root1 = s->root_h[1];
   a.bvh.max_visits = 2 * (s->nint_s + s->nint_d + s->ntri) + 8;
   a.rays = s->rays;
-  a.tx = make_float3(tx[0], tx[1], tx[2]);
+  a.txs = s->txs;
+  a.nsets = s->nsets;
   a.R = s->R;
   a.N = N;
   a.tmin = p->t_min;
   a.escape = p->escape_len;
-  a.alpha_eff = alpha_eff_of(s, p);
   a.rx = s->rx_cur;
   a.nrx = nrx;
   a.log_o = s->log_o;
@@ -961,6 +1025,7 @@ static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params
   q.bucket = s->bucket;
   q.bucket_cnt = s->bucket_cnt;
   q.bucket_cap = s->bucket_cap;
+  q.link_off = P.nlinks > kScanLinks ? s->link_off : nullptr;
   if (out->ptr_kind == DCEM_PTR_DEVICE) {  // results go straight to the caller's buffers
     q.pout = out->paths;
     q.pout_cap = out->paths ? (unsigned)out->max_paths : 0u;
@@ -971,15 +1036,16 @@ static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params
     q.pout = s->pout;
     q.pout_cap = s->ucap;
     q.out_field = s->rxout;
-    q.out_pc = s->rxout + 2 * (size_t)s->nrx_cap;
-    q.out_pi = s->rxout + 3 * (size_t)s->nrx_cap;
+    q.out_pc = s->rxout + 2 * (size_t)s->nlink_cap;
+    q.out_pi = s->rxout + 3 * (size_t)s->nlink_cap;
   }
   q.tris = s->tris;
   q.slot_of_id = s->slot_of_id;
   q.mats = s->mats;
   q.bvh = a.bvh;
   q.rx = s->rx_cur;
-  q.tx = a.tx;
+  q.nrx = nrx;
+  q.txs = s->txs;
   q.pol = make_float3(p->pol[0], p->pol[1], p->pol[2]);
   q.eps_occ = p->eps_occ;
   q.prec_df = p->prec == DCEM_PREC_DF32 ? 1 : 0;
@@ -1004,6 +1070,9 @@ static void make_plan(dcem_scene* s, const float* tx, int nrx, const dcem_params
   P.ctr = s->ctr;
   P.uctr = s->uctr;
   P.ctr_hd = s->ctr_hd;
+  P.txs = s->txs;
+  P.txs_h = s->txs_h;
+  P.bucket_cnt = s->bucket_cnt;
   for (int i = 0; i < 10; ++i) P.ev[i] = s->ev[i];
 }
 
@@ -1018,6 +1087,10 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   bool tm = P.tm, tk = P.tk;
   if (tm) CK(rec(P.ev[0], st, cap));
   CK(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
+  // transmitters and their capture spacing, from the pinned staging the
+  // host filled for this frame
+  CK(cudaMemcpyAsync(P.txs, P.txs_h, sizeof(float4) * P.nsets, cudaMemcpyHostToDevice, st));
+  if (P.nlinks > P.nrx) CK(cudaMemsetAsync(P.bucket_cnt, 0, sizeof(unsigned) * P.nlinks, st));
   if (P.use_q) {
     launch_quantize4(P.nodes, P.q4_bound, P.q4_count, P.q4_kid, P.q4_src, P.root_box, P.has0, P.has1, P.qnodes,
                      P.qframe, st);
@@ -1041,7 +1114,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   if (tm) CK(rec(P.ev[5], st, cap));
   CK(launch_validate(P.q, sms * 4, st));
   if (tm) CK(rec(P.ev[6], st, cap));
-  CK(launch_reduce(P.q, P.nrx, st));
+  CK(launch_reduce(P.q, P.nlinks, st));
   if (tm) CK(rec(P.ev[7], st, cap));
   // state the next frame compares against, and the counters to the host
   {
@@ -1076,14 +1149,14 @@ static int capture_frame(dcem_scene* s, const FramePlan& P, cudaGraphExec_t* exe
   return rc;
 }
 
-static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params* p, bool coherent,
-                      const dcem_result* out) {
+static int trace_once(dcem_scene* s, int nrx, const dcem_params* p, bool coherent, const dcem_result* out) {
   cudaStream_t st = s->st;
   FramePlan& P = s->plan;
-  make_plan(s, tx, nrx, p, coherent, out, P);
+  make_plan(s, nrx, p, coherent, out, P);
   s->last_use_q = P.use_q;
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
-  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) + (P.use_q ? 1 : 0);
+  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) + (P.use_q ? 1 : 0) +
+                 (P.q.link_off ? 1 : 0);
   // Plans alternate with the candidate buffers' parity: one cached graph per
   // parity. A plan is captured the second time it is seen in a row (the
   // first run also sets every kernel's launch attributes), then replayed.
@@ -1117,9 +1190,15 @@ static int trace_once(dcem_scene* s, const float* tx, int nrx, const dcem_params
 
 int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
                      const dcem_params* p, dcem_result* out) {
-  if (!s || !tx || !p || !out) return DCEM_ERR_ARG;
+  if (s && s->rays_set && s->nsets != 1) return DCEM_ERR_STATE;
+  return dcem_trace_links(s, tx, 1, rx, nrx, rx_ptr_kind, p, out);
+}
+
+int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
+                     int32_t rx_ptr_kind, const dcem_params* p, dcem_result* out) {
+  if (!s || !tx || !p || !out || ntx < 1) return DCEM_ERR_ARG;
   if (nrx < 0 || (nrx > 0 && !rx)) return DCEM_ERR_ARG;
-  if (nrx > kSmallBuild) return DCEM_ERR_ARG;
+  if (nrx > kSmallBuild || (long long)ntx * nrx > kMaxLinks) return DCEM_ERR_ARG;
   if (rx_ptr_kind != DCEM_PTR_HOST && rx_ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->ptr_kind != DCEM_PTR_HOST && out->ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->max_paths < 0 || (out->max_paths > 0 && !out->paths)) return DCEM_ERR_ARG;
@@ -1135,9 +1214,9 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
     return DCEM_ERR_ARG;
   if (!finite_arr(p->pol, 3) || !(p->pol[0] * p->pol[0] + p->pol[1] * p->pol[1] + p->pol[2] * p->pol[2] > 0))
     return DCEM_ERR_ARG;
-  if (!finite_arr(tx, 3)) return DCEM_ERR_NONFINITE;
+  if (!finite_arr(tx, 3 * (size_t)ntx)) return DCEM_ERR_NONFINITE;
   if (rx_ptr_kind == DCEM_PTR_HOST && nrx > 0 && !finite_arr(rx, 3 * (size_t)nrx)) return DCEM_ERR_NONFINITE;
-  if (!s->rays_set) return DCEM_ERR_STATE;
+  if (!s->rays_set || ntx != s->nsets) return DCEM_ERR_STATE;
   std::memset(&out->stats, 0, sizeof(out->stats));
   out->n_paths = 0;
 
@@ -1146,18 +1225,22 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   unsigned want_c = s->cand_cap ? s->cand_cap : (unsigned)std::max(65536, s->R / 8);
   unsigned want_u = s->ucap ? s->ucap : std::min(want_c, 1u << 18);
   if ((rc = ensure_paths(s, want_c, want_u)) != DCEM_OK) return rc;
-  if ((rc = ensure_rx(s, nrx, s->bucket_cap)) != DCEM_OK) return rc;
+  const int nlinks = ntx * nrx;
+  if ((rc = ensure_rx(s, nrx, nlinks, s->bucket_cap)) != DCEM_OK) return rc;
   cudaStream_t st = s->st;
+  for (int t = 0; t < ntx; ++t)
+    s->txs_h[t] = make_float4(tx[3 * t], tx[3 * t + 1], tx[3 * t + 2], alpha_eff_of(s->set_rays_h[t], p));
   if (nrx)
     CK(cudaMemcpyAsync(s->rx3, rx, sizeof(float) * 3 * nrx,
                        rx_ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
 
   bool coherent = p->mode == DCEM_MODE_COHERENT && s->cache_valid && same_traversal(*p, s->cparams) &&
-                  nrx == s->cnrx && std::memcmp(tx, s->ctx, sizeof(s->ctx)) == 0 &&
+                  nrx == s->cnrx && s->ctx.size() == 3 * (size_t)ntx &&
+                  std::memcmp(tx, s->ctx.data(), sizeof(float) * 3 * ntx) == 0 &&
                   s->logW == p->max_refl + 1;
   DevCounters* c = nullptr;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    rc = trace_once(s, tx, nrx, p, coherent, out);
+    rc = trace_once(s, nrx, p, coherent, out);
     if (rc != DCEM_OK) {
       s->cache_valid = false;
       return rc;
@@ -1181,7 +1264,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
         s->cache_valid = false;
         return DCEM_ERR_CAPACITY;
       }
-      if ((rc = ensure_rx(s, nrx, nb)) != DCEM_OK) return rc;
+      if ((rc = ensure_rx(s, nrx, nlinks, nb)) != DCEM_OK) return rc;
       CK(cudaMemcpyAsync(s->rx3, rx, sizeof(float) * 3 * nrx,
                          rx_ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
     }
@@ -1231,11 +1314,13 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   int nvalid = (int)c[0].n_valid;
   if (out->ptr_kind == DCEM_PTR_HOST) {
     cudaMemcpyKind k = cudaMemcpyDeviceToHost;
-    size_t cap = (size_t)s->nrx_cap;
-    if (nrx) {
-      if (out->field) CK(cudaMemcpyAsync(out->field, s->rxout, sizeof(double) * 2 * nrx, k, st));
-      if (out->p_coh_dbm) CK(cudaMemcpyAsync(out->p_coh_dbm, s->rxout + 2 * cap, sizeof(double) * nrx, k, st));
-      if (out->p_inc_dbm) CK(cudaMemcpyAsync(out->p_inc_dbm, s->rxout + 3 * cap, sizeof(double) * nrx, k, st));
+    size_t cap = (size_t)s->nlink_cap;
+    if (nlinks) {
+      if (out->field) CK(cudaMemcpyAsync(out->field, s->rxout, sizeof(double) * 2 * nlinks, k, st));
+      if (out->p_coh_dbm)
+        CK(cudaMemcpyAsync(out->p_coh_dbm, s->rxout + 2 * cap, sizeof(double) * nlinks, k, st));
+      if (out->p_inc_dbm)
+        CK(cudaMemcpyAsync(out->p_inc_dbm, s->rxout + 3 * cap, sizeof(double) * nlinks, k, st));
     }
     int ncopy = std::min(nvalid, out->max_paths);
     if (ncopy > 0 && out->paths) CK(cudaMemcpyAsync(out->paths, s->pout, sizeof(dcem_path) * ncopy, k, st));
@@ -1254,7 +1339,7 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   out->n_paths = nvalid;
   s->cache_valid = true;
   s->cparams = *p;
-  std::memcpy(s->ctx, tx, sizeof(s->ctx));
+  s->ctx.assign(tx, tx + 3 * ntx);
   s->cnrx = nrx;
   if (err & ERR_STACK) return DCEM_ERR_STACK;
   if (nvalid > out->max_paths && out->paths) return DCEM_ERR_CAPACITY;

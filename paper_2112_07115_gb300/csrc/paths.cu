@@ -1,9 +1,10 @@
 // paths.cu -- duplicate-path removal, image-method validation, field, and
-// the per-receiver reduction.
+// the per-link reduction (a link is a transmitter-receiver pair: t * nrx + r;
+// with one transmitter, the receiver index).
 //
 // Sec. III "Backward ray tracing":
 //   step 2  a table of visited propagation paths per reflection depth: every
-//           capture is keyed by (receiver, depth, triangle sequence); a
+//           capture is keyed by (link, depth, triangle sequence); a
 //           device hash table keeps one representative per distinct key
 //           (the capture of the lowest ray index), and every other capture
 //           is checked against it key by key (a 64-bit collision between
@@ -17,8 +18,8 @@
 //           of the ray field (Eq. 1) with the free-space spreading of Eq. 3
 //           (exponent 2) and one Fresnel TE/TM reflection per bounce, with
 //           vector polarisation (FP64).
-// The per-receiver sums of amplitudes are formed in a fixed order (paths
-// sorted by key), so the received power is reproducible bit for bit.
+// The per-link sums of amplitudes are formed in a fixed order (paths sorted
+// by key), so the received power is reproducible bit for bit.
 #include "paths.cuh"
 
 namespace dcem {
@@ -26,14 +27,20 @@ namespace dcem {
 // ---------------------------------------------------------------------------
 // keys
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long path_key(const PathArgs& a, Cand c) {
-  int rx = cand_rx(c), k = cand_seg(c);
+// 64-bit hash of (rx, depth, triangle sequence of `ray`'s first k segments).
+__device__ __forceinline__ unsigned long long path_key_of(const PathArgs& a, int ray, int rx, int k) {
   unsigned long long h = mix64(0x9e3779b97f4a7c15ull + (unsigned long long)(unsigned)rx);
   h = mix64(h + 0x100000001b3ull * (unsigned long long)(k + 1));
   for (int j = 0; j < k; ++j)
-    h = mix64(h + ((unsigned long long)(unsigned)a.log_id[(size_t)j * a.R + c.ray] |
+    h = mix64(h + ((unsigned long long)(unsigned)a.log_id[(size_t)j * a.R + ray] |
                    ((unsigned long long)(j + 1) << 40)));
   return h ? h : 1ull;
+}
+
+// Hash-table key of a capture: its link (transmitter * nrx + receiver),
+// depth and sequence, so that transmitters never share an entry.
+__device__ __forceinline__ unsigned long long path_key(const PathArgs& a, Cand c) {
+  return path_key_of(a, c.ray, cand_rx(c), cand_seg(c));
 }
 
 __device__ __forceinline__ bool same_key(const PathArgs& a, Cand x, Cand y) {
@@ -235,7 +242,8 @@ __device__ __forceinline__ float3 fpol(float3 u, float3 d, unsigned& flags) {
 //                reflection points inside their triangles (FP64)
 //   k_val_occ    one thread per (key, sub-segment): FP32 any-hit occlusion
 //   k_val_field  one thread per distinct key: length, Fresnel, polarisation,
-//                complex amplitude (FP64); valid paths go to their receiver
+//                complex amplitude (FP64); valid paths go to their link's
+//                bucket
 // ---------------------------------------------------------------------------
 // Distinct keys are few (thousands): thread t of block b takes keys
 // b + gridDim * t, so that every SM gets a share.
@@ -258,6 +266,10 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
     a.hkey[slot] = 0ull;
     a.hrep[slot] = ~0ull;
     int k = cand_seg(c), rxi = cand_rx(c);
+    // the record's key (the output order within a link) leaves the
+    // transmitter out: (receiver, depth, sequence), as a single-transmitter
+    // frame has it
+    if (rxi >= a.nrx) rec.key = path_key_of(a, c.ray, rxi % a.nrx, k);
     rec.rx = rxi;
     rec.depth = k;
     rec.ray = c.ray;
@@ -272,9 +284,10 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
       rec.tri[j] = ids[j];
       rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
     }
-    float4 rxv = a.rx[rxi];
+    // link -> transmitter and receiver
+    float4 rxv = a.rx[rxi % a.nrx], txv = a.txs[rxi / a.nrx];
     v3<T> X[kMaxRefl + 2], V0[kMaxRefl], V1[kMaxRefl], V2[kMaxRefl], Nn[kMaxRefl];
-    v3<T> tx = vof<T>(a.tx.x, a.tx.y, a.tx.z), rx = vof<T>(rxv.x, rxv.y, rxv.z);
+    v3<T> tx = vof<T>(txv.x, txv.y, txv.z), rx = vof<T>(rxv.x, rxv.y, rxv.z);
     // step 3: image sources I_1..I_k
     v3<T> img[kMaxRefl + 1];
     img[0] = tx;
@@ -443,9 +456,35 @@ __global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// per receiver: sort paths by key, sum in that order, write them out
+// per link: sort paths by key, sum in that order, write them out
 // ---------------------------------------------------------------------------
 constexpr int kReduceThreads = 256;
+
+// Exclusive scan of the links' valid-path counts (one CTA: each thread sums
+// a contiguous run of links, the run totals are scanned in shared memory,
+// then each thread writes its run's offsets).
+__global__ void __launch_bounds__(1024) k_link_scan(const unsigned* __restrict__ cnt, int n, unsigned cap,
+                                                    unsigned* __restrict__ off) {
+  __shared__ unsigned part[1024];
+  int tid = threadIdx.x;
+  int per = (n + 1023) / 1024;
+  int lo = min(n, tid * per), hi = min(n, lo + per);
+  unsigned sum = 0;
+  for (int i = lo; i < hi; ++i) sum += min(cnt[i], cap);
+  part[tid] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    unsigned v = tid >= o ? part[tid - o] : 0u;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  unsigned base = tid ? part[tid - 1] : 0u;
+  for (int i = lo; i < hi; ++i) {
+    off[i] = base;
+    base += min(cnt[i], cap);
+  }
+}
 
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
   extern __shared__ unsigned long long skey[];   // bucket_cap keys, then bucket_cap ints
@@ -454,13 +493,16 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
   __shared__ unsigned soff;
   int r = blockIdx.x, tid = threadIdx.x;
   int cnt = (int)min(a.bucket_cnt[r], (unsigned)a.bucket_cap);
-  // output offset: valid paths of all lower receivers
-  unsigned part = 0;
-  for (int q = tid; q < r; q += kReduceThreads) part += min(a.bucket_cnt[q], (unsigned)a.bucket_cap);
-  for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-  if (tid == 0) soff = 0;
+  // output offset: valid paths of all lower links (scanned beforehand when
+  // there are many links)
+  if (tid == 0) soff = a.link_off ? a.link_off[r] : 0u;
   __syncthreads();
-  if ((tid & 31) == 0) atomicAdd(&soff, part);
+  if (!a.link_off) {
+    unsigned part = 0;
+    for (int q = tid; q < r; q += kReduceThreads) part += min(a.bucket_cnt[q], (unsigned)a.bucket_cap);
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((tid & 31) == 0) atomicAdd(&soff, part);
+  }
   int np2 = 1;
   while (np2 < cnt) np2 <<= 1;
   for (int i = tid; i < np2; i += kReduceThreads) {
@@ -502,7 +544,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
     unsigned o = off + (unsigned)i;
     if (o < a.pout_cap) {
       dcem_path q;
-      q.rx = p.rx;
+      q.rx = p.rx % a.nrx;
+      q.tx = p.rx / a.nrx;
+      q.reserved = 0;
       q.depth = p.depth;
       for (int j = 0; j < kMaxRefl; ++j) {
         q.tri[j] = p.tri[j];
@@ -557,15 +601,16 @@ cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const PathArgs& a, int nrx, cudaStream_t st) {
-  if (nrx <= 0) return cudaSuccess;
+cudaError_t launch_reduce(const PathArgs& a, int nlinks, cudaStream_t st) {
+  if (nlinks <= 0) return cudaSuccess;
+  if (a.link_off) k_link_scan<<<1, 1024, 0, st>>>(a.bucket_cnt, nlinks, (unsigned)a.bucket_cap, a.link_off);
   size_t smem = (size_t)a.bucket_cap * (sizeof(unsigned long long) + sizeof(int));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr = true;
   }
-  k_reduce<<<nrx, kReduceThreads, smem, st>>>(a);
+  k_reduce<<<nlinks, kReduceThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

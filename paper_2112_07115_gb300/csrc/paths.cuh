@@ -21,20 +21,22 @@ struct PathArgs {
   double* vpts;                   // per distinct key: (kMaxRefl + 2) FP64 path points
   int* vstate;                    // per distinct key: 0 invalid, 1 valid so far, 2 occluded
   int N;                          // reflections (sub-segments per path <= N + 1)
-  int* bucket;                    // nrx x bucket_cap distinct-key indices of valid paths
-  unsigned* bucket_cnt;           // nrx
+  int* bucket;                    // links x bucket_cap distinct-key indices of valid paths
+  unsigned* bucket_cnt;           // links (link = transmitter * nrx + receiver)
   int bucket_cap;                 // power of two
-  dcem_path* pout;                // ordered output (rx, key): caller's device buffer or staging
+  unsigned* link_off;             // links: output offset of each link's paths (many links), or null
+  dcem_path* pout;                // ordered output (link, key): caller's device buffer or staging
   unsigned pout_cap;
-  double* out_field;              // nrx x 2 (re, im), or null
-  double* out_pc;                 // nrx P_coh dBm, or null
-  double* out_pi;                 // nrx P_inc dBm, or null
+  double* out_field;              // links x 2 (re, im), or null
+  double* out_pc;                 // links P_coh dBm, or null
+  double* out_pi;                 // links P_inc dBm, or null
   const float4* tris;             // leaf-ordered triangles
   const int* slot_of_id;
   const float4* mats;             // eps_r, sigma, pec
   Bvh bvh;
-  const float4* rx;
-  float3 tx;
+  const float4* rx;               // nrx receivers
+  int nrx;
+  const float4* txs;              // per transmitter: position (xyz)
   float3 pol;
   float eps_occ;
   int prec_df;                    // 1: validation geometry in double-float, 0: FP64
@@ -44,6 +46,9 @@ struct PathArgs {
 
 cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_reduce(const PathArgs& a, int nrx, cudaStream_t st);
+// Per-link sums and ordered output; links above kScanLinks take their output
+// offsets from a scan (a.link_off) instead of summing the lower links' counts.
+constexpr int kScanLinks = 4096;
+cudaError_t launch_reduce(const PathArgs& a, int nlinks, cudaStream_t st);
 
 }  // namespace dcem

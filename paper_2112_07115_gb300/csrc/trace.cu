@@ -72,7 +72,8 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
           b = a.queue ? a.restart[ray] : 0;
           if (b == 0) {
             float4 rd = __ldg(&a.rays[ray]);
-            o = a.tx;
+            float4 t4 = __ldg(&a.txs[__float_as_int(rd.w)]);
+            o = f3(t4.x, t4.y, t4.z);
             d = f3(rd.x, rd.y, rd.z);
             D = 0.0f;
             last = -1;
@@ -220,14 +221,19 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
       float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
       float D = lo.w, t = ld.w;
       float tend = isinf(t) ? a.escape : t;
+      // the ray's set: its capture spacing, and the link of its captures
+      int set = a.nsets > 1 ? __float_as_int(__ldg(reinterpret_cast<const float*>(a.rays) + 4 * (size_t)ray + 3))
+                            : 0;
+      float alpha = __ldg(&a.txs[set].w);
+      int link0 = set * a.nrx;
       RayPre rp;
       rp.o = o;
       float dx = fabsf(d.x) < 1e-30f ? copysignf(1e-30f, d.x) : d.x;
       float dy = fabsf(d.y) < 1e-30f ? copysignf(1e-30f, d.y) : d.y;
       float dz = fabsf(d.z) < 1e-30f ? copysignf(1e-30f, d.z) : d.z;
       rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-      if (!capture_tree(rxt, rx, rp, d, D, tend, a.alpha_eff, st, [&](int r) {
-            if (!reused || a.rx_moved[r]) emit_cand(a, ray, b, r);
+      if (!capture_tree(rxt, rx, rp, d, D, tend, alpha, st, [&](int r) {
+            if (!reused || a.rx_moved[r]) emit_cand(a, ray, b, link0 + r);
           }))
         ovf = 1u;
     }
@@ -340,9 +346,10 @@ __global__ void k_carry(TraceArgs a, CoherentArgs c) {
   unsigned kept = 0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     Cand x = c.prev_cand[i];
-    int r = cand_rx(x), s = cand_seg(x);
+    int l = cand_rx(x), s = cand_seg(x);
+    int r = a.nsets > 1 ? l % a.nrx : l;   // link -> receiver
     if (s < c.restart[x.ray] && !c.rx_moved[r]) {
-      emit_cand(a, x.ray, s, r);
+      emit_cand(a, x.ray, s, l);
       ++kept;
     }
   }

@@ -7,11 +7,13 @@ namespace dcem {
 
 struct TraceArgs {
   Bvh bvh;
-  const float4* rays;      // R unit directions (xyz)
-  float3 tx;
+  const float4* rays;      // R unit directions (xyz), .w = the ray's set (int bits)
+  const float4* txs;       // per ray set: transmitter position (xyz) and the
+                           // effective capture spacing alpha_t / sqrt(3) (w)
+  int nsets;
   int R, N;                // rays, reflections
-  float tmin, escape, alpha_eff;
-  const float4* rx;        // nrx receivers (xyz)
+  float tmin, escape;
+  const float4* rx;        // nrx receivers (xyz); a capture's link is set * nrx + r
   int nrx;
   SmallBvh rxt;            // per-frame tree over the receivers
   const uint4* qnodes;     // 4-wide compact node copy (4 uint4 per node) and its frame

@@ -31,7 +31,7 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
             "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
             "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients",
-            "dcem_scene_set_graph_replay"]
+            "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links"]
 
 
 class Material(C.Structure):
@@ -47,8 +47,8 @@ class Params(C.Structure):
 
 class Path(C.Structure):
     _fields_ = [("rx", C.c_int32), ("depth", C.c_int32), ("tri", C.c_int32 * MAX_REFL),
-                ("flags", C.c_uint32), ("ray", C.c_int32), ("key", C.c_uint64),
-                ("len_m", C.c_double), ("delay_s", C.c_double), ("amp_re", C.c_double),
+                ("flags", C.c_uint32), ("ray", C.c_int32), ("tx", C.c_int32),
+                ("reserved", C.c_int32), ("key", C.c_uint64), ("len_m", C.c_double), ("delay_s", C.c_double), ("amp_re", C.c_double),
                 ("amp_im", C.c_double), ("pts", C.c_float * (3 * MAX_REFL))]
 
 
@@ -73,7 +73,8 @@ class Result(C.Structure):
 
 
 PATH_DTYPE = np.dtype([("rx", np.int32), ("depth", np.int32), ("tri", np.int32, (MAX_REFL,)),
-                       ("flags", np.uint32), ("ray", np.int32), ("key", np.uint64),
+                       ("flags", np.uint32), ("ray", np.int32), ("tx", np.int32),
+                       ("reserved", np.int32), ("key", np.uint64),
                        ("len_m", np.float64), ("delay_s", np.float64), ("amp_re", np.float64),
                        ("amp_im", np.float64), ("pts", np.float32, (MAX_REFL, 3))])
 assert PATH_DTYPE.itemsize == C.sizeof(Path)
@@ -99,6 +100,8 @@ def lib():
         L.dcem_scene_set_rays.argtypes = [vp, vp, i32]
         L.dcem_scene_update_transforms.argtypes = [vp, vp, i32]
         L.dcem_trace_frame.argtypes = [vp, vp, vp, i32, i32, P(Params), P(Result)]
+        L.dcem_scene_set_ray_sets.argtypes = [vp, vp, vp, i32]
+        L.dcem_trace_links.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), P(Result)]
         L.dcem_scene_reset_cache.argtypes = [vp]
         L.dcem_scene_set_stream.argtypes = [vp, vp]
         L.dcem_scene_destroy.argtypes = [vp]
@@ -193,6 +196,24 @@ def dcem_scene_set_rays(h, dirs):
     d = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
     _check(lib().dcem_scene_set_rays(h, d.ctypes.data if d.size else None, d.shape[0]),
            "dcem_scene_set_rays")
+
+
+def dcem_scene_set_ray_sets(h, sets):
+    """One ray set per transmitter: `sets` is a list of (n_t, 3) direction arrays."""
+    d = [np.ascontiguousarray(x, np.float32).reshape(-1, 3) for x in sets]
+    n = np.array([x.shape[0] for x in d], np.int32)
+    cat = np.ascontiguousarray(np.concatenate(d) if d else np.zeros((0, 3), np.float32))
+    _check(lib().dcem_scene_set_ray_sets(h, cat.ctypes.data if cat.size else None, n.ctypes.data, len(d)),
+           "dcem_scene_set_ray_sets")
+
+
+def dcem_trace_links(h, tx, rx, params: Params, result: Result) -> int:
+    """Raw call for ntx transmitters (tx: (ntx, 3)); returns the status."""
+    txa = np.ascontiguousarray(tx, np.float32).reshape(-1, 3)
+    rp, kind, keep = _ptr(rx, np.float32)
+    nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+    return lib().dcem_trace_links(h, txa.ctypes.data, txa.shape[0], rp, nrx, kind, C.byref(params),
+                                  C.byref(result))
 
 
 def dcem_scene_update_transforms(h, xf):
@@ -343,6 +364,39 @@ class Scene:
     def set_rays(self, dirs):
         dcem_scene_set_rays(self.h, dirs)
         self.n_rays = int(np.asarray(dirs).reshape(-1, 3).shape[0])
+
+    def set_ray_sets(self, sets):
+        """Ray sets of several transmitters (for trace_links)."""
+        dcem_scene_set_ray_sets(self.h, sets)
+        self.set_sizes = [int(np.asarray(x).reshape(-1, 3).shape[0]) for x in sets]
+        self.n_rays = sum(self.set_sizes)
+
+    def trace_links(self, tx, rx, params: Params | None = None, max_paths: int | None = None,
+                    raise_on_error: bool = True) -> Frame:
+        """One frame of every transmitter (tx: (ntx, 3)) against the receivers:
+        field and powers have shape (ntx, nrx); path records carry tx and rx."""
+        params = params or default_params()
+        self.max_refl = int(params.max_refl)
+        ntx = np.asarray(tx).reshape(-1, 3).shape[0]
+        nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+        nl = ntx * nrx
+        if max_paths is None:
+            max_paths = max(1024, 256 * nl)
+        field = np.empty((max(nl, 1), 2), np.float64)
+        pc = np.empty(max(nl, 1), np.float64)
+        pi = np.empty(max(nl, 1), np.float64)
+        paths = np.empty(max_paths, PATH_DTYPE)
+        res = Result()
+        res.ptr_kind = PTR_HOST
+        res.max_paths = max_paths
+        res.field, res.p_coh_dbm, res.p_inc_dbm = field.ctypes.data, pc.ctypes.data, pi.ctypes.data
+        res.paths = paths.ctypes.data
+        rc = dcem_trace_links(self.h, tx, rx, params, res)
+        if rc != OK and raise_on_error:
+            raise DcemError(rc, "dcem_trace_links")
+        n = min(res.n_paths, max_paths)
+        return Frame(rc, (field[:nl, 0] + 1j * field[:nl, 1]).reshape(ntx, nrx), pc[:nl].reshape(ntx, nrx),
+                     pi[:nl].reshape(ntx, nrx), paths[:n].copy(), stats_dict(res.stats))
 
     def update_transforms(self, xf):
         dcem_scene_update_transforms(self.h, xf)

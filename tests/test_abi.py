@@ -40,9 +40,9 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_struct_sizes_match_header(L):
-    assert C.sizeof(L.Path) == 216
+    assert C.sizeof(L.Path) == 224
     assert C.sizeof(L.Params) == 64
-    assert L.PATH_DTYPE.itemsize == 216
+    assert L.PATH_DTYPE.itemsize == 224
 
 
 def test_status_strings(L):
@@ -97,6 +97,9 @@ def test_null_scene_calls(L):
     assert lib.dcem_scene_update_transforms(None, None, 0) == L.ERR_ARG
     assert lib.dcem_scene_reset_cache(None) == L.ERR_ARG
     assert lib.dcem_scene_set_graph_replay(None, 1) == L.ERR_ARG
+    n = (C.c_int32 * 1)(4)
+    assert lib.dcem_scene_set_ray_sets(None, None, n, 1) == L.ERR_ARG
+    assert lib.dcem_trace_links(None, tx, 1, None, 0, 0, C.byref(p), C.byref(r)) == L.ERR_ARG
     assert lib.dcem_scene_info(None, None, None, None, None, None) == L.ERR_ARG
     n = C.c_int32(0)
     assert lib.dcem_scene_gradient_size(None, C.byref(n)) == L.ERR_ARG
