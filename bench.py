@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--freq", type=float, default=28e9)
     ap.add_argument("--no-baseline", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-transmitter workload")
+    ap.add_argument("--batched-frames", type=int, default=8)
     return ap.parse_args()
 
 
@@ -345,6 +347,10 @@ def run_ours(args):
                            "max_len_err_m": e_p["max_len_err_m"], "paths": e_p["paths"]}
             sp.close()
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, stream, dev, world, flush)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sc, rays, stream, W, K, world, dev)
@@ -379,6 +385,7 @@ def run_ours(args):
                          "bvh_rebuilds": int(sum(x["bvh_rebuilt"] for x in st_coh))},
             "gradients": grads,
             "validation_precision": precs,
+            "batched": batched,
             "full": {"frames_per_s": round(fps_full, 2), "ms_per_frame": round(1e3 * t_full / K, 4),
                      "ray_segments_per_s": round(seg_full, 0), "segments_per_frame": int(seg_mean),
                      "nodes_per_segment": round(nodes_per_seg, 2), "tris_per_segment": round(tris_per_seg, 2),
@@ -404,6 +411,76 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batched(args, stream, dev, world, flush, warmup=2):
+    """The batched multi-transmitter workload: an urban grid (10 x 10 blocks,
+    ~51k static and 10k moving triangles, 1000 vehicles), 64 roadside
+    transmitters with log-uniform budgets of 64k-2M rays (~31M rays in all),
+    4096 receivers (262,144 links), 5 reflections, every transmitter traced in
+    the same launches per frame (dcem_trace_links). Full and coherent frames,
+    L2 flushed before each, timed with CUDA events; max over ranks."""
+    import ctypes as C
+    import torch
+    from paper_2112_07115_gb300 import dcem, scenes
+    K = args.batched_frames
+    sc = scenes.urban_grid(seed=0, n_frames=warmup + K + 1)
+    txs, budgets = sc.meta["tx"], sc.meta["budgets"]
+    sets = [scenes.fibonacci_sphere(n) for n in budgets]
+    nl = len(budgets) * sc.nrx
+    xf_d = torch.from_numpy(sc.xf).to(dev)
+    rx_d = torch.from_numpy(sc.rx).to(dev)
+    max_paths = 1 << 22
+    field_d = torch.empty((nl, 2), dtype=torch.float64, device=dev)
+    pc_d = torch.empty(nl, dtype=torch.float64, device=dev)
+    pi_d = torch.empty(nl, dtype=torch.float64, device=dev)
+    paths_d = torch.empty(max_paths * C.sizeof(dcem.Path), dtype=torch.uint8, device=dev)
+    out = {"workload": "urban grid 10x10 blocks (100 m pitch, 20 m streets), %d triangles (%d moving), "
+                       "%d vehicles, %d Tx with %d-%d rays each (%d rays), %d Rx, %d links, %d reflections, "
+                       "28 GHz" % (sc.ntri, int((sc.tri_obj >= 0).sum()), sc.nobj, len(budgets), min(budgets),
+                                   max(budgets), sum(budgets), sc.nrx, nl, sc.max_refl)}
+    for name, mode in (("full", dcem.MODE_FULL), ("coherent", dcem.MODE_COHERENT)):
+        s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+        s.set_ray_sets(sets)
+        prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=2)
+        res = dcem.Result()
+        res.ptr_kind = dcem.PTR_DEVICE
+        res.max_paths = max_paths
+        res.field, res.p_coh_dbm, res.p_inc_dbm = field_d.data_ptr(), pc_d.data_ptr(), pi_d.data_ptr()
+        res.paths = paths_d.data_ptr()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, st = [], []
+        for i in range(warmup + K):
+            f = i + 1
+            flush.zero_()
+            e0.record(stream)
+            dcem.dcem_scene_update_transforms(s.h, xf_d[f])
+            rc = dcem.dcem_trace_links(s.h, txs, rx_d[f], prm, res)
+            e1.record(stream)
+            e1.synchronize()
+            if rc != dcem.OK:
+                raise dcem.DcemError(rc, f"batched frame {f}")
+            if i >= warmup:
+                ms.append(e0.elapsed_time(e1))
+                st.append(dcem.stats_dict(res.stats))
+        s.close()
+        t = max_over_ranks([sum(ms) / 1e3], dev)[0]
+        segs = float(np.mean([x["segments_traced"] for x in st]))
+        trace_ms = float(np.mean([x["ms_stage"]["trace"] for x in st]))
+        out[name] = {"frames_per_s": round(world * K / t, 3), "ms_per_frame": round(1e3 * t / K, 3),
+                     "rays_per_s": round(world * K * sum(budgets) / t, 0),
+                     "segments_traced_per_frame": int(segs),
+                     "ray_segments_traced_per_s": round(world * K * segs / t, 0),
+                     "links_per_s": round(world * K * nl / t, 0),
+                     "paths_per_frame": int(np.mean([x["paths_valid"] for x in st])),
+                     "unique_candidates_per_frame": int(np.mean([x["unique_candidates"] for x in st])),
+                     "closest_hit_ms": round(trace_ms, 3),
+                     "closest_hit_kernel": "k_trace_q" if st[-1]["trace_kernel"] == 1 else "k_trace",
+                     "nodes_per_segment": round(float(np.mean([x["node_visits"] for x in st])) / max(segs, 1.0), 2),
+                     "segments_reused_frac": round(float(np.mean(
+                         [x["segments_reused"] / max(1, x["segments_reused"] + x["segments_traced"]) for x in st])), 4),
+                     "graph_replayed_frac": round(float(np.mean([x["graph_replayed"] for x in st])), 3)}
+    return out
 
 
 def grad_timing(s, sc, rx_f, paths_d, n_paths, stream, dev, reps=20):

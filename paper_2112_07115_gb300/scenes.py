@@ -13,6 +13,10 @@ Workloads:
   * ``highway``     -- 2 km six-lane road with concrete barriers, 200 vehicles
     of three box classes with lane changes, one roadside Tx, one Rx per
     vehicle roof, 1M rays, 4 reflections, 100 frames at 10 Hz.
+  * ``urban_grid``  -- Manhattan grid of blocks with extruded-polygon
+    buildings (four static material classes), moving vehicles on four-lane
+    streets, many roadside Tx with uneven ray budgets, four roof Rx per
+    vehicle plus static roadside Rx (the batched multi-transmitter workload).
   * small closed-form scenes (ground plane, parallel plates, random triangles).
 
 The paper (Sec. III) uses an .obj town model and measurement campaigns that
@@ -320,6 +324,146 @@ def highway(seed: int = 0, n_frames: int = 100, n_vehicles: int = 200,
                  xf.astype(np.float32), np.array([length / 2, 20.0, 8.0], np.float32),
                  rx.astype(np.float32), freq_hz=freq_hz, n_rays=n_rays, max_refl=max_refl,
                  meta={"seed": seed, "dt": dt, "classes": cls.tolist()})
+
+
+# ----------------------------------------------------------------------------
+# urban grid (batched transmitters)
+# ----------------------------------------------------------------------------
+
+# Static material classes of the urban grid, rows of ``urban_materials``:
+# concrete (the configs' value), brick, glass, ground; vehicles are metal.
+# Brick/glass/ground are ITU-R P.2040-style constants chosen for the build.
+URBAN_CONCRETE, URBAN_BRICK, URBAN_GLASS, URBAN_GROUND, URBAN_METAL = range(5)
+
+
+def urban_materials() -> np.ndarray:
+    return np.array([[5.31, 0.0326, 0.0],    # concrete
+                     [3.75, 0.038, 0.0],     # brick
+                     [6.27, 0.0043, 0.0],    # glass
+                     [15.0, 0.035, 0.0],     # ground
+                     [1.0, 0.0, 1.0]],       # metal (vehicles)
+                    dtype=np.float32)
+
+
+def _extruded_polygon(cx, cy, rmax, n, h, rng):
+    """Walls (2 triangles per edge) and a roof fan of a star-shaped polygon of
+    n vertices around (cx, cy), radii in [0.55, 1] rmax, extruded to height h."""
+    ang = np.sort(rng.uniform(0.0, 2.0 * np.pi, size=n))
+    rad = rng.uniform(0.55, 1.0, size=n) * rmax
+    px, py = cx + rad * np.cos(ang), cy + rad * np.sin(ang)
+    out = []
+    for k in range(n):
+        a, b = k, (k + 1) % n
+        out += _quad((px[a], py[a], 0.0), (px[b], py[b], 0.0), (px[b], py[b], h), (px[a], py[a], h))
+        out.append([(cx, cy, h), (px[a], py[a], h), (px[b], py[b], h)])
+    return out
+
+
+def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: float = 20.0,
+               parcels: int = 4, n_vehicles: int = 1000, n_tx: int = 64,
+               budgets: tuple = (65_536, 2_097_152), n_static_rx: int = 96, n_frames: int = 200,
+               max_refl: int = 5, freq_hz: float = 28e9) -> Scene:
+    """Manhattan grid: ``blocks`` x ``blocks`` blocks at ``pitch`` m with
+    ``street`` m streets (street centre lines at x = i * pitch and
+    y = j * pitch, i, j = 0..blocks). Each block holds ``parcels`` x
+    ``parcels`` buildings: star-shaped polygons of 6-14 vertices extruded to
+    U[10, 60] m, each of concrete, brick or glass. Ground of 25 m tiles.
+    Vehicles (car/van/truck boxes as on the highway, metal) drive on four
+    lanes per street (two each way, 2.5 m and 7.5 m from the centre line) at
+    a per-lane speed U[5, 15] m/s with equal spacing and wrap-around, so they
+    never overlap. Receivers: the four roof corners of every vehicle (0.2 m
+    in, 0.1 m above the roof), then ``n_static_rx`` roadside receivers at
+    2 m. Transmitters: ``n_tx`` roadside units at random street corners,
+    6-10 m high, with ray budgets log-uniform in ``budgets`` (returned in
+    ``meta["tx"]`` and ``meta["budgets"]``; ``tx`` is the first one).
+    Frames at 10 Hz.
+    """
+    ss = np.random.SeedSequence([seed, 3])
+    r_bld, r_veh, r_tx = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
+    size = blocks * pitch
+    static, smat = [], []
+    tile = 25.0
+    nt = int(round((size + street) / tile))
+    for i in range(nt):
+        for j in range(nt):
+            x0, y0 = -street / 2 + i * tile, -street / 2 + j * tile
+            static += _quad((x0, y0, 0.0), (x0 + tile, y0, 0.0), (x0 + tile, y0 + tile, 0.0), (x0, y0 + tile, 0.0))
+            smat += [URBAN_GROUND] * 2
+    lot = pitch - street
+    cell = lot / parcels
+    for bi in range(blocks):
+        for bj in range(blocks):
+            for pi in range(parcels):
+                for pj in range(parcels):
+                    cx = bi * pitch + street / 2 + (pi + 0.5) * cell
+                    cy = bj * pitch + street / 2 + (pj + 0.5) * cell
+                    n = int(r_bld.integers(6, 15))
+                    h = float(r_bld.uniform(10.0, 60.0))
+                    m = int(r_bld.integers(0, 3))
+                    b = _extruded_polygon(cx, cy, 0.45 * cell, n, h, r_bld)
+                    static += b
+                    smat += [m] * len(b)
+    # vehicles: lanes along x (streets y = j * pitch) and along y (x = i * pitch)
+    lanes = []
+    for axis in (0, 1):
+        for k in range(blocks + 1):
+            for off, sgn in ((-7.5, -1.0), (-2.5, -1.0), (2.5, 1.0), (7.5, 1.0)):
+                lanes.append((axis, k * pitch + off, sgn))
+    lane_of = r_veh.integers(0, len(lanes), size=n_vehicles)
+    u = r_veh.uniform(size=n_vehicles)
+    cls = np.where(u < 0.7, 0, np.where(u < 0.9, 1, 2))
+    names = ["car", "van", "truck"]
+    dims = np.array([VEH_CLASSES[names[c]] for c in cls])
+    s0 = np.zeros(n_vehicles)
+    speed = np.zeros(n_vehicles)
+    span = size + street
+    for ln in range(len(lanes)):
+        idx = np.nonzero(lane_of == ln)[0]
+        if len(idx) == 0:
+            continue
+        gap = span / len(idx)
+        if gap < 25.0:
+            raise ValueError("too many vehicles for the lanes")
+        phase = r_veh.uniform(0.0, gap)
+        s0[idx] = phase + gap * np.arange(len(idx)) + r_veh.uniform(-0.2, 0.2, size=len(idx)) * (gap - 20.0)
+        speed[idx] = r_veh.uniform(5.0, 15.0)
+    meshes = [box_tris(*dims[k]) for k in range(n_vehicles)]
+    tris, tobj, tmat = _assemble(static, smat, meshes, [URBAN_METAL] * n_vehicles)
+    dt = 0.1
+    xf = np.zeros((n_frames, n_vehicles, 12), np.float64)
+    nrx = 4 * n_vehicles + n_static_rx
+    rx = np.zeros((n_frames, nrx, 3), np.float64)
+    corners = np.array([[1, 1], [1, -1], [-1, 1], [-1, -1]], np.float64)
+    for f in range(n_frames):
+        for k in range(n_vehicles):
+            axis, c, sgn = lanes[lane_of[k]]
+            along = (s0[k] + sgn * speed[k] * dt * f) % span - street / 2
+            if axis == 0:
+                x, y, yaw = along, c, (0.0 if sgn > 0 else np.pi)
+            else:
+                x, y, yaw = c, along, (np.pi / 2 if sgn > 0 else -np.pi / 2)
+            xf[f, k] = _xf_row(yaw, x, y, 0.0)
+            cy_, sy_ = np.cos(yaw), np.sin(yaw)
+            lx, ly, lz = dims[k, 0] / 2 - 0.2, dims[k, 1] / 2 - 0.2, dims[k, 2] + 0.1
+            for q, (a, b) in enumerate(corners):
+                px, py = a * lx, b * ly
+                rx[f, 4 * k + q] = (x + cy_ * px - sy_ * py, y + sy_ * px + cy_ * py, lz)
+    # static roadside receivers and the transmitters, at street corners
+    def corner_points(n, rng, hlo, hhi):
+        ii = rng.integers(0, blocks + 1, size=n)
+        jj = rng.integers(0, blocks + 1, size=n)
+        sx = rng.choice([-1.0, 1.0], size=n)
+        sy = rng.choice([-1.0, 1.0], size=n)
+        return np.stack([ii * pitch + sx * (street / 2 - 1.0), jj * pitch + sy * (street / 2 - 1.0),
+                         rng.uniform(hlo, hhi, size=n)], 1)
+    rx[:, 4 * n_vehicles:] = corner_points(n_static_rx, r_tx, 2.0, 2.0)[None]
+    txs = corner_points(n_tx, r_tx, 6.0, 10.0).astype(np.float32)
+    lo, hi = np.log(budgets[0]), np.log(budgets[1])
+    bud = np.exp(r_tx.uniform(lo, hi, size=n_tx)).astype(np.int64)
+    return Scene("urban_grid", tris, tobj, tmat, urban_materials(), n_vehicles,
+                 xf.astype(np.float32), txs[0].copy(), rx.astype(np.float32), freq_hz=freq_hz,
+                 n_rays=int(bud[0]), max_refl=max_refl,
+                 meta={"seed": seed, "dt": dt, "tx": txs, "budgets": bud.tolist(), "classes": cls.tolist()})
 
 
 # ----------------------------------------------------------------------------

@@ -188,3 +188,38 @@ def test_links_errors(cuda):
     # three identical transmitters with identical sets: identical links
     assert np.array_equal(r.p_coh_dbm[0], r.p_coh_dbm[1]) and np.array_equal(r.p_coh_dbm[0], r.p_coh_dbm[2])
     s.close()
+
+
+def test_urban_grid_reduced_links(cuda):
+    """The batched workload's scene family, reduced to 2 x 2 blocks, 12
+    vehicles and 3 transmitters with uneven budgets, 5 reflections: each
+    transmitter bit for bit as its own frame, and against the oracle."""
+    sc = scenes.urban_grid(blocks=2, parcels=2, n_vehicles=12, n_tx=3, budgets=(4_000, 24_000),
+                           n_static_rx=4, n_frames=3, max_refl=5)
+    txs = sc.meta["tx"]
+    sizes = sc.meta["budgets"]
+    st = _compare_links_vs_single(cuda, sc, txs, sizes, range(3), mode=dcem.MODE_COHERENT)
+    assert st[-1]["paths_valid"] > 0
+    sets = [scenes.fibonacci_sphere(n) for n in sizes]
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    a = _scene(cuda, sc)
+    a.set_ray_sets(sets)
+    f = 2
+    a.update_transforms(sc.xf[f])
+    fl = a.trace_links(txs, sc.rx[f], P.gpu_params(sc))
+    ids, tt, ns = a.ray_log()
+    checked = 0
+    for t in range(len(sizes)):
+        sct = copy.copy(sc)
+        sct.tx = txs[t]
+        ref = O.frame(sct, f, sets[t], P.oracle_params(sc, n_rays=sizes[t]))
+        sl = slice(offs[t], offs[t] + sizes[t])
+        _, _, bad = P.compare_hits(ids[sl], ns[sl], ref.tr)
+        assert len(bad) == 0, (t, bad[:5])
+        got = copy.copy(fl)
+        got.paths = _per_tx(fl, t, sc.nrx, offs[t])
+        res = P.compare_paths(got, ref, sc.max_refl)
+        checked += res["checked"]
+        assert not res["missing"] and not res["extra"] and not res["len"] and not res["amp"], t
+    assert checked > 0
+    a.close()
