@@ -291,7 +291,7 @@ def run_ours(args):
         # segment, 8 B per emitted candidate
         return x["segments_traced"] * 36 + (x["candidates"] - x["candidates_reused"]) * 8
 
-    tname = "k_trace_q" if st_coh[-1]["trace_kernel"] == 1 else "k_trace"
+    tname = ["k_trace", "k_trace_q", "k_trace_qg"][st_coh[-1]["trace_kernel"]]
     kern = {"trace": (tname, bytes_trace), "mark": ("k_mark", bytes_mark), "capture": ("k_capture", bytes_capture)}
     roof = None
     if dom in kern:
@@ -439,9 +439,19 @@ def run_batched(args, stream, dev, world, flush, warmup=2):
                        "%d vehicles, %d Tx with %d-%d rays each (%d rays), %d Rx, %d links, %d reflections, "
                        "28 GHz" % (sc.ntri, int((sc.tri_obj >= 0).sum()), sc.nobj, len(budgets), min(budgets),
                                    max(budgets), sum(budgets), sc.nrx, nl, sc.max_refl)}
+    # closest-hit configuration: the autotuner on the first frame (untimed)
+    s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+    s.set_ray_sets(sets)
+    s.update_transforms(sc.xf[1])
+    tune = s.autotune(txs, sc.rx[1], dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz), reps=1)
+    s.close()
+    out["closest_hit_config"] = {"kernel": ["binary nodes, global", "4-wide copy, shared memory",
+                                            "4-wide copy, global"][tune[0]],
+                                 "block": tune[1], "stack": tune[2], "chosen_by": "dcem_scene_autotune"}
     for name, mode in (("full", dcem.MODE_FULL), ("coherent", dcem.MODE_COHERENT)):
         s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
         s.set_ray_sets(sets)
+        s.set_trace_config(tune[0], tune[1] if tune[0] != 1 else 256, tune[2] if tune[0] != 1 else 24)
         prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=2)
         res = dcem.Result()
         res.ptr_kind = dcem.PTR_DEVICE
@@ -475,7 +485,7 @@ def run_batched(args, stream, dev, world, flush, warmup=2):
                      "paths_per_frame": int(np.mean([x["paths_valid"] for x in st])),
                      "unique_candidates_per_frame": int(np.mean([x["unique_candidates"] for x in st])),
                      "closest_hit_ms": round(trace_ms, 3),
-                     "closest_hit_kernel": "k_trace_q" if st[-1]["trace_kernel"] == 1 else "k_trace",
+                     "closest_hit_kernel": ["k_trace", "k_trace_q", "k_trace_qg"][st[-1]["trace_kernel"]],
                      "nodes_per_segment": round(float(np.mean([x["node_visits"] for x in st])) / max(segs, 1.0), 2),
                      "segments_reused_frac": round(float(np.mean(
                          [x["segments_reused"] / max(1, x["segments_reused"] + x["segments_traced"]) for x in st])), 4),

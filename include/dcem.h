@@ -148,9 +148,10 @@ typedef struct {
   float bvh_cost_ratio;        /* surface-area cost of the moving-object tree
                                   over its cost right after the last rebuild     */
   int32_t max_segment_nodes;   /* most BVH nodes visited by one traversal        */
-  int32_t trace_kernel;        /* closest-hit kernel of this frame: 0 = nodes
-                                  read from global memory, 1 = compact node
-                                  copy in shared memory                          */
+  int32_t trace_kernel;        /* closest-hit kernel of this frame: 0 = binary
+                                  nodes read from global memory, 1 = 4-wide
+                                  compact copy in shared memory, 2 = 4-wide
+                                  compact copy read from global memory        */
   int32_t graph_replayed;      /* 1 if the frame's device work was launched as
                                   one replayed CUDA graph                        */
 } dcem_stats;
@@ -254,6 +255,34 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
  * positions) instead of refitting it. ratio <= 0: refit only. Default 1.25.
  * Results never depend on the tree shape. Errors: DCEM_ERR_ARG. */
 int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
+
+/* Closest-hit kernel configuration. Results never depend on it (closest hit
+ * and lowest-id ties are decided by the triangle test alone):
+ *   kernel  -1 automatic (default: 1 when the compact copy and the stacks fit
+ *           in shared memory, else 2), 0 binary nodes read from global
+ *           memory, 1 the 4-wide compact copy staged in shared memory (768
+ *           threads per CTA, one CTA per SM), 2 the 4-wide compact copy read
+ *           from global memory
+ *   block   threads per CTA of kernels 0 and 2: 64, 128 or 256 (default 256)
+ *   stack   shared-memory stack entries per thread of kernels 0 and 2, 8..32
+ *           (default 24; deeper traversals continue in a 48-entry local
+ *           extension)
+ * Errors: DCEM_ERR_ARG (out of range, or kernel 1 or 2 where the scene has no
+ * compact copy that fits). */
+int dcem_scene_set_trace_config(dcem_scene* s, int32_t kernel, int32_t block, int32_t stack);
+
+/* Autotuner of the closest-hit kernel: traces the given frame (as
+ * dcem_trace_links, FULL mode, params otherwise as given) `reps` times
+ * (1..16) under each candidate configuration: kernel 1 if it fits, then
+ * kernels 2 and 0 with 128 or 256 threads and 16, 24 or 32 stack entries.
+ * It times the closest-hit kernel with CUDA events, keeps the fastest
+ * (minimum over reps) as the scene's configuration, and returns it in
+ * kernel, block and stack (any may be NULL). The scene's transforms should
+ * be those of a representative frame. Drops the coherence cache.
+ * Errors: as dcem_trace_links (the configuration is then left unchanged). */
+int dcem_scene_autotune(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
+                        int32_t rx_ptr_kind, const dcem_params* params, int32_t reps, int32_t* kernel,
+                        int32_t* block, int32_t* stack);
 
 /* Graph replay of dcem_trace_frame's and dcem_trace_links' device work
  * (default on = 1). The work a frame enqueues (about 16 kernels, memsets,

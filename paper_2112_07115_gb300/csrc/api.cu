@@ -223,6 +223,7 @@ struct dcem_scene {
   int4* q4_src = nullptr;        // node count and roots (rebuilt with the topology)
   int* q4_count = nullptr;
   int* q4_roots = nullptr;
+  int* q4_scr = nullptr;         // scratch of the 4-wide mapping of large trees
   int* leaf_parent = nullptr;
   int* tri_obj_d = nullptr;  // triangle id -> rigid object (-1 static)
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
@@ -319,7 +320,9 @@ struct dcem_scene {
   unsigned last_ncand = 0;
   cudaEvent_t ev[10] = {};
   int launches = 0;  // kernels launched since the last completed frame
-  int last_use_q = 0;  // closest-hit kernel of the last frame (1: shared-memory node copy)
+  int last_use_q = 0;  // closest-hit kernel of the last frame (TraceArgs::use_q)
+  // closest-hit configuration (dcem_scene_set_trace_config / dcem_scene_autotune)
+  int tc_kernel = -1, tc_block = 256, tc_stack = kStackTrace;
   // graph replay of the frame's device work (see FramePlan)
   FramePlan plan;
   FrameGraph fgraph[2];
@@ -335,7 +338,7 @@ void scene_free(dcem_scene* s) {
   cudaStreamSynchronize(s->st);
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
-  dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->leaf_parent); dfree(s->arrive);
+  dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx);
@@ -380,7 +383,7 @@ bool dyn_fused(const dcem_scene* s) {
 int remap4(dcem_scene* s) {
   if (!s->qnodes) return DCEM_OK;
   CK(launch_bvh4_map(s->nodes, s->nint_s + s->nint_d, s->roots, s->q4_kid, s->q4_src, s->q4_count, s->q4_roots,
-                     s->st));
+                     s->q4_scr, s->st));
   s->launches += 1;
   return DCEM_OK;
 }
@@ -639,13 +642,16 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->v9d, 9 * (size_t)s->nd));
   CKF(dalloc(&s->nodes, 4 * (size_t)(s->nint_s + s->nint_d)));
   {
+    // the 4-wide compact copy: traversed from shared memory when it fits
+    // there, else from global memory
     int nn = s->nint_s + s->nint_d;
-    if (trace_q_stack_cap(nn) > 0) {  // the 4-wide copy fits in shared memory
+    if (nn > 0) {
       CKF(dalloc(&s->qnodes, 4 * (size_t)bvh4_bound(nn)));
       CKF(dalloc(&s->q4_kid, nn));
       CKF(dalloc(&s->q4_src, nn));
       CKF(dalloc(&s->q4_count, 1));
       CKF(dalloc(&s->q4_roots, 2));
+      if (bvh4_map_smem(nn) == 0) CKF(dalloc(&s->q4_scr, 2 * (size_t)nn));
     }
   }
   CKF(dalloc(&s->qframe, 6));
@@ -870,6 +876,72 @@ int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio) {
   return DCEM_OK;
 }
 
+int dcem_scene_set_trace_config(dcem_scene* s, int32_t kernel, int32_t block, int32_t stack) {
+  if (!s || kernel < -1 || kernel > 2) return DCEM_ERR_ARG;
+  bool okb = false;
+  for (int b : kTraceBlocks) okb = okb || b == block;
+  if (!okb || stack < kTraceStackMin || stack > kTraceStackMax) return DCEM_ERR_ARG;
+  if (kernel == 1 && (!s->qnodes || trace_q_stack_cap(s->nint_s + s->nint_d) == 0)) return DCEM_ERR_ARG;
+  if (kernel == 2 && !s->qnodes) return DCEM_ERR_ARG;
+  s->tc_kernel = kernel;
+  s->tc_block = block;
+  s->tc_stack = stack;
+  return DCEM_OK;
+}
+
+int dcem_scene_autotune(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
+                        int32_t rx_ptr_kind, const dcem_params* params, int32_t reps, int32_t* kernel,
+                        int32_t* block, int32_t* stack) {
+  if (!s || !params || reps < 1 || reps > 16) return DCEM_ERR_ARG;
+  dcem_params p = *params;
+  p.mode = DCEM_MODE_FULL;
+  p.timing = 2;
+  dcem_result r;
+  std::memset(&r, 0, sizeof(r));
+  r.ptr_kind = DCEM_PTR_HOST;
+  struct Cfg {
+    int k, b, st;
+  };
+  std::vector<Cfg> cands;
+  if (s->qnodes && trace_q_stack_cap(s->nint_s + s->nint_d) > 0) cands.push_back({1, s->tc_block, s->tc_stack});
+  for (int k : {2, 0}) {
+    if (k == 2 && !s->qnodes) continue;
+    for (int b : {128, 256})
+      for (int sd : {16, 24, 32}) cands.push_back({k, b, sd});
+  }
+  const int ok = s->tc_kernel, ob = s->tc_block, os = s->tc_stack;
+  float best = INFINITY;
+  Cfg pick{ok, ob, os};
+  for (const Cfg& c : cands) {
+    s->tc_kernel = c.k;
+    s->tc_block = c.b;
+    s->tc_stack = c.st;
+    float t = INFINITY;
+    for (int i = 0; i < reps; ++i) {
+      int rc = dcem_trace_links(s, tx, ntx, rx, nrx, rx_ptr_kind, &p, &r);
+      if (rc != DCEM_OK) {
+        s->tc_kernel = ok;
+        s->tc_block = ob;
+        s->tc_stack = os;
+        return rc;
+      }
+      t = std::min(t, r.stats.ms_stage[2]);
+    }
+    if (t < best) {
+      best = t;
+      pick = c;
+    }
+  }
+  s->tc_kernel = pick.k;
+  s->tc_block = pick.b;
+  s->tc_stack = pick.st;
+  s->cache_valid = false;
+  if (kernel) *kernel = pick.k;
+  if (block) *block = pick.k == 1 ? kTraceQThreads : pick.b;
+  if (stack) *stack = pick.k == 1 ? trace_q_stack_cap(s->nint_s + s->nint_d) : pick.st;
+  return DCEM_OK;
+}
+
 int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on) {
   if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
   s->use_graphs = on != 0;
@@ -947,10 +1019,17 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   a.q4_count = s->q4_count;
   a.q4_roots = s->q4_roots;
   a.q4_bound = bvh4_bound(a.n_nodes);
-  // the compact copy of both trees and the CTA's stacks fit in shared
-  // memory: traverse it there
-  a.stack_cap = trace_q_stack_cap(a.n_nodes);
-  a.use_q = (a.stack_cap > 0 && s->qnodes) ? 1 : 0;
+  // closest-hit kernel: the configured one, or automatically the compact
+  // copy from shared memory when it and the CTA's stacks fit there (1), else
+  // from global memory (2); binary nodes (0) when there is no compact copy
+  {
+    int qcap = trace_q_stack_cap(a.n_nodes);
+    int k = s->tc_kernel;
+    if (k < 0 || (k == 1 && qcap == 0) || (k > 0 && !s->qnodes)) k = !s->qnodes ? 0 : (qcap > 0 ? 1 : 2);
+    a.use_q = k;
+    a.stack_cap = k == 1 ? qcap : s->tc_stack;
+    a.block = k == 1 ? kTraceQThreads : s->tc_block;
+  }
   P.use_q = a.use_q;
   P.q4_bound = a.q4_bound;
 

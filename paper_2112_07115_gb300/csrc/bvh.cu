@@ -887,14 +887,16 @@ __global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float
 // children are its own children, an internal child replaced by that child's
 // two children. For each child slot it records the child (4-wide index,
 // leaf ~slot, or kEmpty) and where its box lives in the binary records
-// (record << 1 | side). Shared memory: depth[nn], index[nn].
+// (record << 1 | side). Scratch depth[nn], index[nn]: shared memory, or the
+// global array `gscr` (2 nn ints) when that does not fit.
 __global__ void __launch_bounds__(1024) k_bvh4_map(const float4* __restrict__ nodes, int nn,
                                                    const int* __restrict__ roots, int4* kid4, int4* src4,
-                                                   int* n4_out, int* roots4_out) {
+                                                   int* n4_out, int* roots4_out, int* gscr) {
   extern __shared__ int sm4[];
-  int* depth = sm4;
-  int* idx = sm4 + nn;
-  __shared__ int changed, total;
+  int* depth = gscr ? gscr : sm4;
+  int* idx = depth + nn;
+  __shared__ int changed, total, carry;
+  __shared__ int wsum[32];
   int tid = threadIdx.x, nt = blockDim.x;
   auto kid = [&](int n, int side) {
     return reinterpret_cast<const int*>(nodes + 4 * (size_t)n + 3)[side];
@@ -924,19 +926,37 @@ __global__ void __launch_bounds__(1024) k_bvh4_map(const float4* __restrict__ no
     if (!changed) break;
     __syncthreads();
   }
-  // exclusive prefix count of even-depth nodes (one warp per 32 nodes, then
-  // a serial pass over the warp sums)
-  for (int i = tid; i < nn; i += nt) idx[i] = (depth[i] >= 0 && (depth[i] & 1) == 0) ? 1 : 0;
+  // exclusive prefix count of even-depth nodes, one tile of nt nodes at a
+  // time: warp scans, a scan of the warp sums, and the running carry
+  if (tid == 0) carry = 0;
   __syncthreads();
-  if (tid == 0) {
-    int run = 0;
-    for (int i = 0; i < nn; ++i) {
-      int f = idx[i];
-      idx[i] = run;
-      run += f;
+  const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  for (int base = 0; base < nn; base += nt) {
+    int i = base + tid;
+    int f = (i < nn && depth[i] >= 0 && (depth[i] & 1) == 0) ? 1 : 0;
+    int v = f;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
     }
-    total = run;
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int x = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    int excl = carry + (w > 0 ? wsum[w - 1] : 0) + v - f;
+    if (i < nn) idx[i] = excl;
+    __syncthreads();
+    if (tid == nt - 1) carry = excl + f;
+    __syncthreads();
   }
+  if (tid == 0) total = carry;
   __syncthreads();
   for (int i = tid; i < nn; i += nt) {
     if (!(depth[i] >= 0 && (depth[i] & 1) == 0)) continue;
@@ -1143,13 +1163,15 @@ void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int
 
 
 cudaError_t launch_bvh4_map(const float4* d_nodes, int nn, const int* d_roots, int4* d_kid4, int4* d_src4,
-                            int* d_n4, int* d_roots4, cudaStream_t st) {
-  size_t smem = 2 * (size_t)(nn > 0 ? nn : 1) * sizeof(int);
+                            int* d_n4, int* d_roots4, int* d_scratch, cudaStream_t st) {
+  size_t smem = bvh4_map_smem(nn);
+  if (smem == 0 && !d_scratch) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_bvh4_map, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_bvh4_map<<<1, 1024, smem, st>>>(d_nodes, nn, d_roots, d_kid4, d_src4, d_n4, d_roots4);
+  k_bvh4_map<<<1, 1024, smem, st>>>(d_nodes, nn, d_roots, d_kid4, d_src4, d_n4, d_roots4,
+                                    smem ? nullptr : d_scratch);
   return cudaGetLastError();
 }
 

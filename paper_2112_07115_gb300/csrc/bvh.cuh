@@ -120,8 +120,14 @@ void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int
 // 4-wide compact copy: map the binary trees (nn internal nodes, 2 root codes)
 // to 4-wide nodes once per topology (one CTA, nn <= 8192), then encode the
 // child boxes every frame. n4 and the 4-wide roots stay on the device.
+// Shared memory of the 4-wide mapping of nn binary internal nodes, or 0 when
+// it needs the global scratch (2 nn ints) instead.
+inline size_t bvh4_map_smem(int nn) {
+  size_t b = 2 * (size_t)(nn > 0 ? nn : 1) * sizeof(int);
+  return b <= 200 * 1024 ? b : 0;
+}
 cudaError_t launch_bvh4_map(const float4* d_nodes, int nn, const int* d_roots, int4* d_kid4, int4* d_src4,
-                            int* d_n4, int* d_roots4, cudaStream_t st);
+                            int* d_n4, int* d_roots4, int* d_scratch, cudaStream_t st);
 void launch_quantize4(const float4* d_nodes, int n4_bound, const int* d_n4, const int4* d_kid4, const int4* d_src4,
                       const float* d_root_box, int has0, int has1, uint4* d_q4, float* d_qframe, cudaStream_t st);
 // At most (2 + 2 nn) / 3 internal nodes of two trees lie at even depth.

@@ -448,7 +448,9 @@ __device__ __forceinline__ void cswap(float& da, int& ca, float& db, int& cb) {
 // Closest hit as closest_hit(), over the 4-wide compact copy: per step the
 // four child boxes are tested, the hit ones ordered by entry distance, the
 // nearest visited next and the others pushed. Node visits count box pairs
-// (a 4-wide step = 2), the unit of the 2-wide traversals.
+// (a 4-wide step = 2), the unit of the 2-wide traversals. kG: the copy is
+// read from global memory (read-only path) instead of shared memory.
+template <bool kG = false>
 __device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, const Bvh& bvh, int root0,
                                               int root1, const RayPre& r, float tmin, int excl, float& t_best,
                                               int& id_best, unsigned& overflow, unsigned& n_nodes,
@@ -472,8 +474,19 @@ __device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, 
     }
     if (cur >= 0) {
       n_nodes += 2;
-      const uint4* nd = qn + 4 * cur;
-      uint4 A = nd[0], B = nd[1], C = nd[2], K = nd[3];
+      const uint4* nd = qn + 4 * (size_t)cur;
+      uint4 A, B, C, K;
+      if (kG) {
+        A = __ldg(nd);
+        B = __ldg(nd + 1);
+        C = __ldg(nd + 2);
+        K = __ldg(nd + 3);
+      } else {
+        A = nd[0];
+        B = nd[1];
+        C = nd[2];
+        K = nd[3];
+      }
       float t0, t1, t2, t3;
       float d0 = qslab(q, A.x, A.y, A.z, t_best, t0) ? t0 : inf;
       float d1 = qslab(q, A.w, B.x, B.y, t_best, t1) ? t1 : inf;

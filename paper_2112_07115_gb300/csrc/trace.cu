@@ -45,7 +45,7 @@ __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
 // so that short retrace queues use all SMs. Per segment b from the ray's
 // restart point (0 in a full frame) to N: closest hit, segment log, specular
 // reflection. Captures are tested by k_capture.
-template <bool kQ>
+template <bool kQ, bool kG = false>
 __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st,
                                            int qr0, int qr1) {
   const int R = a.R;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       float t;
       int id;
       unsigned nn = 0, nt = 0;
-      int slot = kQ ? closest_hit_q4(qn, qf, a.bvh, qr0, qr1, rp, a.tmin, last, t, id, ovf, nn, nt, st)
+      int slot = kQ ? closest_hit_q4<kG>(qn, qf, a.bvh, qr0, qr1, rp, a.tmin, last, t, id, ovf, nn, nt, st)
                     : closest_hit(a.bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st);
       ++segs;
       nodes += nn;
@@ -157,7 +157,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
 __global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
   extern __shared__ int sstk[];
   TStack st;
-  bind_stack(st, sstk, kStackTrace);
+  bind_stack(st, sstk, a.stack_cap);
   QFrame f{};
   trace_rays<false>(a, nullptr, f, st, kEmpty, kEmpty);
 }
@@ -180,6 +180,23 @@ __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   f.sz = a.qframe[5];
   __syncthreads();
   trace_rays<true>(a, sq, f, st, qr0, qr1);
+}
+
+// The 4-wide compact copy read from global memory (L2), for scenes whose copy
+// does not fit in shared memory; stacks in shared memory.
+__global__ void __launch_bounds__(256, 3) k_trace_qg(TraceArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, a.stack_cap);
+  const int qr0 = a.q4_roots[0], qr1 = a.q4_roots[1];
+  QFrame f;
+  f.ox = a.qframe[0];
+  f.oy = a.qframe[1];
+  f.oz = a.qframe[2];
+  f.sx = a.qframe[3];
+  f.sy = a.qframe[4];
+  f.sz = a.qframe[5];
+  trace_rays<true, true>(a, a.qnodes, f, st, qr0, qr1);
 }
 
 // Reception-sphere captures of the segments in the frame's capture list: the
@@ -368,9 +385,9 @@ static int grid_for(long n, int bs, int max_blocks) {
 }
 
 // Persistent launches: as many 256-thread blocks as fit on the GPU at once.
-static int resident_blocks(const void* fn, int sms, size_t smem) {
+static int resident_blocks(const void* fn, int sms, size_t smem, int block = 256) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, smem) != cudaSuccess || nb < 1) nb = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess || nb < 1) nb = 1;
   return nb * sms;
 }
 
@@ -381,10 +398,21 @@ int trace_q_stack_cap(int n_nodes) {
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
-  static int g_trace = 0;
-  if (!g_trace) g_trace = resident_blocks((const void*)k_trace, sms, 256 * kStackTrace * sizeof(int));
   long n = a.R;
-  if (a.use_q) {
+  if (a.use_q != 1) {
+    // kernels 0 and 2: a.block threads, a.stack_cap shared stack entries per
+    // thread; resident CTAs per SM looked up once per configuration
+    static int key[3] = {-1, -1, -1}, resident[3] = {0, 0, 0};
+    const void* fn = a.use_q == 2 ? (const void*)k_trace_qg : (const void*)k_trace;
+    size_t smem = (size_t)a.block * a.stack_cap * sizeof(int);
+    int k = a.block * 64 + a.stack_cap;
+    if (key[a.use_q] != k) {
+      resident[a.use_q] = resident_blocks(fn, sms, smem, a.block);
+      key[a.use_q] = k;
+    }
+    if (a.use_q == 2) k_trace_qg<<<grid_for(n, a.block, resident[2]), a.block, smem, st>>>(a);
+    else k_trace<<<grid_for(n, a.block, resident[0]), a.block, smem, st>>>(a);
+  } else {
     size_t smem = (size_t)a.q4_bound * 4 * sizeof(uint4) + (size_t)kTraceQThreads * a.stack_cap * sizeof(int);
     static size_t attr = 0;
     if (smem > attr) {
@@ -393,8 +421,6 @@ cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
       attr = smem;
     }
     k_trace_q<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
-  } else {
-    k_trace<<<grid_for(n, 256, g_trace), 256, 256 * kStackTrace * sizeof(int), st>>>(a);
   }
   return cudaGetLastError();
 }

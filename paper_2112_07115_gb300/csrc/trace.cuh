@@ -22,8 +22,10 @@ struct TraceArgs {
   const int* q4_count;     // 4-wide nodes (device), at most q4_bound
   const int* q4_roots;     // roots of both trees in the 4-wide copy (device)
   int q4_bound;
-  int use_q;               // 1: traverse the compact copy from shared memory
-  int stack_cap;           // shared-memory stack entries per thread with use_q
+  int use_q;               // closest-hit kernel: 0 binary nodes (k_trace), 1 the 4-wide compact
+                           // copy from shared memory (k_trace_q), 2 from global memory (k_trace_qg)
+  int stack_cap;           // shared-memory stack entries per thread
+  int block;               // threads per CTA of kernels 0 and 2 (kernel 1: kTraceQThreads)
   float4* log_o;           // (N+1) x R: origin, unfolded length D
   float4* log_d;           // (N+1) x R: direction, hit t (+inf escaped)
   int* log_id;             // (N+1) x R: hit triangle id or -1
@@ -61,6 +63,10 @@ constexpr long kTraceQSmem = 220L * 1024;
 // Shared-memory stack entries per thread for a compact copy of n_nodes
 // nodes, or 0 if copy and stacks do not fit (then nodes come from global).
 int trace_q_stack_cap(int n_nodes);
+// Closest-hit configurations of kernels 0 and 2: threads per CTA and shared
+// stack entries per thread.
+constexpr int kTraceBlocks[] = {64, 128, 256};
+constexpr int kTraceStackMin = 8, kTraceStackMax = 32;
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st);

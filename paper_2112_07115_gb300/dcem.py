@@ -31,7 +31,8 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
             "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
             "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients",
-            "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links"]
+            "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
+            "dcem_scene_set_trace_config", "dcem_scene_autotune"]
 
 
 class Material(C.Structure):
@@ -102,6 +103,8 @@ def lib():
         L.dcem_trace_frame.argtypes = [vp, vp, vp, i32, i32, P(Params), P(Result)]
         L.dcem_scene_set_ray_sets.argtypes = [vp, vp, vp, i32]
         L.dcem_trace_links.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), P(Result)]
+        L.dcem_scene_set_trace_config.argtypes = [vp, i32, i32, i32]
+        L.dcem_scene_autotune.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), i32, P(i32), P(i32), P(i32)]
         L.dcem_scene_reset_cache.argtypes = [vp]
         L.dcem_scene_set_stream.argtypes = [vp, vp]
         L.dcem_scene_destroy.argtypes = [vp]
@@ -214,6 +217,23 @@ def dcem_trace_links(h, tx, rx, params: Params, result: Result) -> int:
     nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
     return lib().dcem_trace_links(h, txa.ctypes.data, txa.shape[0], rp, nrx, kind, C.byref(params),
                                   C.byref(result))
+
+
+def dcem_scene_set_trace_config(h, kernel: int, block: int = 256, stack: int = 24):
+    _check(lib().dcem_scene_set_trace_config(h, int(kernel), int(block), int(stack)),
+           "dcem_scene_set_trace_config")
+
+
+def dcem_scene_autotune(h, tx, rx, params: Params, reps: int = 2):
+    """Times the closest-hit kernel under each configuration on this frame
+    and keeps the fastest; returns (kernel, block, stack)."""
+    txa = np.ascontiguousarray(tx, np.float32).reshape(-1, 3)
+    rp, kind, keep = _ptr(rx, np.float32)
+    nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+    k, b, s = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    _check(lib().dcem_scene_autotune(h, txa.ctypes.data, txa.shape[0], rp, nrx, kind, C.byref(params), int(reps),
+                                     C.byref(k), C.byref(b), C.byref(s)), "dcem_scene_autotune")
+    return k.value, b.value, s.value
 
 
 def dcem_scene_update_transforms(h, xf):
@@ -451,6 +471,12 @@ class Scene:
 
     def set_graph_replay(self, on: bool):
         dcem_scene_set_graph_replay(self.h, on)
+
+    def set_trace_config(self, kernel: int, block: int = 256, stack: int = 24):
+        dcem_scene_set_trace_config(self.h, kernel, block, stack)
+
+    def autotune(self, tx, rx, params: Params | None = None, reps: int = 2):
+        return dcem_scene_autotune(self.h, tx, rx, params or default_params(), reps)
 
     def world_tris(self):
         return dcem_scene_get_world_tris(self.h, self.ntri)
