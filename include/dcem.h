@@ -61,7 +61,14 @@ typedef enum {
   DCEM_ERR_NOMEM = -8      /* device allocation failed                           */
 } dcem_status;
 
-typedef enum { DCEM_MODE_FULL = 0, DCEM_MODE_COHERENT = 1 } dcem_mode;
+/* FULL: every ray traced every frame. COHERENT: segments reused across
+ * frames (the result equals FULL bit for bit). STICKY: COHERENT plus the
+ * paper's path-cache retention (Sec. III "Propagation path caching": cached
+ * paths are kept and updated until removed): every valid path of the
+ * previous frame is re-validated against the current geometry and kept if
+ * still valid, even when no ray of this frame captured it (flag
+ * DCEM_PATH_STICKY, count stats.paths_sticky); a superset of FULL. */
+typedef enum { DCEM_MODE_FULL = 0, DCEM_MODE_COHERENT = 1, DCEM_MODE_STICKY = 2 } dcem_mode;
 /* Arithmetic of the validation geometry (image sources, back-trace,
  * reflection points, path length) and of the phase: FP64, or double-float
  * (pairs of FP32 values, about 44 significant bits) on the FP32 pipe. */
@@ -70,6 +77,8 @@ typedef enum { DCEM_PTR_HOST = 0, DCEM_PTR_DEVICE = 1 } dcem_ptr_kind;
 
 /* Path flag bits (dcem_path.flags). */
 #define DCEM_PATH_POL_DEGENERATE 1u /* polarisation reference parallel to a path end */
+#define DCEM_PATH_STICKY 2u         /* DCEM_MODE_STICKY: kept from the previous frame
+                                       (re-validated), no ray captured it this frame */
 
 typedef struct dcem_scene dcem_scene;
 
@@ -86,7 +95,7 @@ typedef struct {
   double freq_hz;         /* carrier frequency; default 28e9                     */
   double tx_power_w;      /* transmit power; default 5 W (Sec. III, outdoor)     */
   int32_t max_refl;       /* N: reflections per ray, 0..DCEM_MAX_REFL; default 3 */
-  int32_t mode;           /* DCEM_MODE_FULL or DCEM_MODE_COHERENT                */
+  int32_t mode;           /* DCEM_MODE_FULL, _COHERENT or _STICKY                */
   float rx_radius_scale;  /* capture radius = scale * alpha * (D+s) / sqrt(3),
                              alpha = sqrt(4 pi / n_rays); default 1.35           */
   float t_min;            /* self-hit offset after a reflection [m]; 1e-4        */
@@ -154,6 +163,8 @@ typedef struct {
                                   compact copy read from global memory        */
   int32_t graph_replayed;      /* 1 if the frame's device work was launched as
                                   one replayed CUDA graph                        */
+  int32_t paths_sticky;        /* DCEM_MODE_STICKY: valid paths that only the
+                                  path cache kept (no ray captured them)         */
 } dcem_stats;
 
 typedef struct {

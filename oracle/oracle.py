@@ -17,6 +17,10 @@ Pipeline of one frame (arXiv 2112.07115, Sec. III):
                  occlusion; length, delay, Fresnel TE/TM, complex amplitude
   reduce      -> received power per receiver: coherent P_t |sum a|^2 and
                  incoherent P_t sum |a|^2 in dBm, summed in sorted key order.
+  sticky      -> the path cache's literal retention (Sec. III "Propagation
+                 path caching", cached paths kept and updated until removed):
+                 a frame's keys are the ones its rays capture plus every key
+                 valid in the previous frame, all validated anew.
   gradient    -> derivatives of the per-receiver field over a fixed path
                  topology with respect to each material's (eps_r, sigma) and
                  each rigid object's (x, y) translation, by FP64 central
@@ -392,3 +396,28 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
     paths = validate(wt, scene.tri_mat, scene.materials, scene.tx, rx, keys, prm)
     fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)
     return FrameResult(wt, tr, keys, paths, fld, pc, pi)
+
+
+def sticky_frames(scene, frames, rays: np.ndarray, prm: OracleParams):
+    """Frames in the path cache's retention mode (Sec. III "Propagation path
+    caching": a cached path is kept and updated until it is removed). Frame
+    i's keys: the distinct keys its rays capture, plus (from the second frame
+    on) every key that was valid in frame i-1; all of them are validated with
+    frame i's geometry, so a kept path stays while it is valid and is removed
+    when it is not. Returns per frame a FrameResult over that key set, with
+    ``extra["kept_only"]``: the valid keys that no ray of the frame captured."""
+    out = []
+    prev = None
+    for f in frames:
+        fr = frame(scene, f, rays, prm)
+        keys = fr.keys
+        if prev is not None and prev.shape[0]:
+            keys = unique_keys(np.concatenate([fr.keys, prev]))
+        paths = validate(fr.world_tris, scene.tri_mat, scene.materials, scene.tx, scene.rx[f], keys, prm)
+        fld, pc, pi = reduce(keys, paths, scene.rx[f].shape[0], prm.tx_power_w)
+        disc = {tuple(k) for k in fr.keys.tolist()}
+        valid = keys[paths["valid"] != 0]
+        kept = np.array([k for k in valid.tolist() if tuple(k) not in disc], np.int32).reshape(-1, keys.shape[1])
+        out.append(FrameResult(fr.world_tris, fr.tr, keys, paths, fld, pc, pi, {"kept_only": kept}))
+        prev = valid
+    return out

@@ -174,7 +174,7 @@ __global__ void k_gather_rays(const float4* __restrict__ src, const unsigned* __
 // CUDA graph captured from it (one launch) instead of ~16 stream operations.
 // The struct is zero-filled before it is set, so its padding compares equal.
 struct FramePlan {
-  int32_t coherent, tm, tk, use_q, nrx, R, has0, has1, q4_bound, nobj, ptr_dev, nsets, nlinks;
+  int32_t coherent, tm, tk, use_q, nrx, R, has0, has1, q4_bound, nobj, ptr_dev, nsets, nlinks, sticky;
   TraceArgs a;
   FramePrepArgs fp;
   CoherentArgs c;
@@ -194,6 +194,7 @@ struct FramePlan {
   float4* txs;           // transmitters (device), copied from the pinned txs_h
   const float4* txs_h;
   unsigned* bucket_cnt;  // cleared by a memset when there are more links than receivers
+  unsigned* sticky_n_next;  // sticky mode: this frame's kept-path count (persistent)
   cudaEvent_t ev[10];
 };
 
@@ -290,6 +291,8 @@ struct dcem_scene {
   double* vpts = nullptr;
   int* vstate = nullptr;
   dcem_path* pout = nullptr;
+  StickyKey* sticky[2] = {nullptr, nullptr};  // sticky mode: kept paths (by parity)
+  unsigned* sticky_n = nullptr;               // their counts (device, by parity)
   // receivers
   int nrx_cap = 0;
   float* rx3 = nullptr;
@@ -350,7 +353,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->rays); dfree(s->ray_perm); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems); dfree(s->nseg); dfree(s->restart);
   dfree(s->queue); dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->prev_ncand); dfree(s->hkey);
   dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
-  dfree(s->vpts); dfree(s->vstate);
+  dfree(s->vpts); dfree(s->vstate); dfree(s->sticky[0]); dfree(s->sticky[1]); dfree(s->sticky_n);
   dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list); dfree(s->bucket);
   dfree(s->bucket_cnt); dfree(s->rxout); dfree(s->link_off); dfree(s->txs);
   if (s->txs_h) cudaFreeHost(s->txs_h);
@@ -484,6 +487,12 @@ int ensure_paths(dcem_scene* s, unsigned cand_cap, unsigned ucap) {
     CK(dalloc(&s->pout, ucap));
     CK(dalloc(&s->vpts, (size_t)ucap * 3 * (kMaxRefl + 2)));
     CK(dalloc(&s->vstate, ucap));
+    // sticky mode: kept paths of the previous frame and of this one
+    dfree(s->sticky[0]); dfree(s->sticky[1]);
+    CK(dalloc(&s->sticky[0], ucap));
+    CK(dalloc(&s->sticky[1], ucap));
+    if (!s->sticky_n) CK(dalloc(&s->sticky_n, 2));
+    CK(cudaMemsetAsync(s->sticky_n, 0, 2 * sizeof(unsigned), s->st));
     s->ucap = ucap;
   }
   return DCEM_OK;
@@ -1131,6 +1140,14 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.freq = p->freq_hz;
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
+  // sticky mode: the previous frame's kept paths (when the cache is valid),
+  // and this frame's
+  P.sticky = p->mode == DCEM_MODE_STICKY;
+  q.sticky_prev = P.sticky && coherent && s->cparams.mode == DCEM_MODE_STICKY ? s->sticky[s->cur] : nullptr;
+  q.sticky_prev_n = s->sticky_n ? s->sticky_n + s->cur : nullptr;
+  q.sticky_cap = s->ucap;
+  q.sticky_next = P.sticky ? s->sticky[nxt] : nullptr;
+  P.sticky_n_next = s->sticky_n ? s->sticky_n + nxt : nullptr;
 
   P.nodes = s->nodes;
   P.q4_count = s->q4_count;
@@ -1190,6 +1207,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   if (P.R > 0) CK(launch_capture(a, sms, st));
   if (tm) CK(rec(P.ev[4], st, cap));
   CK(launch_dedupe(P.q, sms * 4, st));
+  if (P.q.sticky_prev) CK(launch_sticky_probe(P.q, sms * 4, st));
   if (tm) CK(rec(P.ev[5], st, cap));
   CK(launch_validate(P.q, sms * 4, st));
   if (tm) CK(rec(P.ev[6], st, cap));
@@ -1203,6 +1221,8 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
                                    P.obj_box_traced, P.nobj, P.ctr, P.uctr, P.prev_ncand, P.ctr_hd);
     CK(cudaGetLastError());
   }
+  if (P.sticky)  // the kept-path count, for the next frame
+    CK(cudaMemcpyAsync(P.sticky_n_next, &P.ctr->n_sticky_next, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
   // with device outputs nothing follows on the stream: the frame ends here
   if (tm && P.ptr_dev) CK(rec(P.ev[8], st, cap));
   return DCEM_OK;
@@ -1235,7 +1255,7 @@ static int trace_once(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->last_use_q = P.use_q;
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) + (P.use_q ? 1 : 0) +
-                 (P.q.link_off ? 1 : 0);
+                 (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0);
   // Plans alternate with the candidate buffers' parity: one cached graph per
   // parity. A plan is captured the second time it is seen in a row (the
   // first run also sets every kernel's launch attributes), then replayed.
@@ -1282,7 +1302,8 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
   if (out->ptr_kind != DCEM_PTR_HOST && out->ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->max_paths < 0 || (out->max_paths > 0 && !out->paths)) return DCEM_ERR_ARG;
   if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
-  if (p->mode != DCEM_MODE_FULL && p->mode != DCEM_MODE_COHERENT) return DCEM_ERR_ARG;
+  if (p->mode != DCEM_MODE_FULL && p->mode != DCEM_MODE_COHERENT && p->mode != DCEM_MODE_STICKY)
+    return DCEM_ERR_ARG;
   if (p->timing < 0 || p->timing > 2) return DCEM_ERR_ARG;
   if (p->prec != DCEM_PREC_F64 && p->prec != DCEM_PREC_DF32) return DCEM_ERR_ARG;
   if (!(p->freq_hz > 0) || !std::isfinite(p->freq_hz) || !(p->tx_power_w > 0) || !std::isfinite(p->tx_power_w))
@@ -1313,7 +1334,7 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
     CK(cudaMemcpyAsync(s->rx3, rx, sizeof(float) * 3 * nrx,
                        rx_ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
 
-  bool coherent = p->mode == DCEM_MODE_COHERENT && s->cache_valid && same_traversal(*p, s->cparams) &&
+  bool coherent = p->mode != DCEM_MODE_FULL && s->cache_valid && same_traversal(*p, s->cparams) &&
                   nrx == s->cnrx && s->ctx.size() == 3 * (size_t)ntx &&
                   std::memcmp(tx, s->ctx.data(), sizeof(float) * 3 * ntx) == 0 &&
                   s->logW == p->max_refl + 1;
@@ -1367,6 +1388,7 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
   S.max_segment_nodes = (int32_t)c[0].max_seg_nodes;
   S.trace_kernel = s->last_use_q;
   S.graph_replayed = s->graph_replayed;
+  S.paths_sticky = (int32_t)c[0].n_sticky_valid;
   S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;

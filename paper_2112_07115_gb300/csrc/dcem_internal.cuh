@@ -55,6 +55,15 @@ struct DevCounters {
   unsigned int max_seg_nodes;      // most nodes visited by one closest-hit traversal
   unsigned long long node_visits;  // internal nodes visited by closest-hit traversals
   unsigned long long tri_tests;    // triangles tested by closest-hit traversals
+  unsigned int n_sticky_valid;     // sticky mode: valid paths that only the cache kept
+  unsigned int n_sticky_next;      // sticky mode: valid paths kept for the next frame
+};
+
+// Sticky mode: a valid path kept for the next frame (link, depth, sequence).
+struct StickyKey {
+  int link;
+  int depth;
+  int tri[kMaxRefl];
 };
 
 // Candidate = one reception-sphere capture: ray index and (rx << 4 | segment).

@@ -27,14 +27,19 @@ namespace dcem {
 // ---------------------------------------------------------------------------
 // keys
 // ---------------------------------------------------------------------------
-// 64-bit hash of (rx, depth, triangle sequence of `ray`'s first k segments).
-__device__ __forceinline__ unsigned long long path_key_of(const PathArgs& a, int ray, int rx, int k) {
+// 64-bit hash of (rx, depth, triangle sequence id_at(0..k-1)).
+template <class F>
+__device__ __forceinline__ unsigned long long seq_key(int rx, int k, F id_at) {
   unsigned long long h = mix64(0x9e3779b97f4a7c15ull + (unsigned long long)(unsigned)rx);
   h = mix64(h + 0x100000001b3ull * (unsigned long long)(k + 1));
   for (int j = 0; j < k; ++j)
-    h = mix64(h + ((unsigned long long)(unsigned)a.log_id[(size_t)j * a.R + ray] |
-                   ((unsigned long long)(j + 1) << 40)));
+    h = mix64(h + ((unsigned long long)(unsigned)id_at(j) | ((unsigned long long)(j + 1) << 40)));
   return h ? h : 1ull;
+}
+
+// ... of `ray`'s first k logged segments.
+__device__ __forceinline__ unsigned long long path_key_of(const PathArgs& a, int ray, int rx, int k) {
+  return seq_key(rx, k, [&](int j) { return a.log_id[(size_t)j * a.R + ray]; });
 }
 
 // Hash-table key of a capture: its link (transmitter * nrx + receiver),
@@ -86,6 +91,38 @@ __global__ void k_dedupe_unique(PathArgs a) {
     } else if (!same_key(a, a.cand[i], a.cand[rep])) {
       atomicOr(&a.ctr->err, ERR_HASH_COLLISION);
     }
+  }
+}
+
+// Sticky mode (Sec. III "Propagation path caching", paths kept until they are
+// removed): each of the previous frame's valid paths is looked up in this
+// frame's table; one that no capture has joins the distinct keys as entry ~i.
+__global__ void k_sticky_probe(PathArgs a) {
+  unsigned n = min(*a.sticky_prev_n, a.sticky_cap);
+  unsigned mask = a.hcap - 1u;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const StickyKey& sk = a.sticky_prev[i];
+    unsigned long long h = seq_key(sk.link, sk.depth, [&](int j) { return sk.tri[j]; });
+    unsigned slot = (unsigned)(h & mask);
+    bool found = false;
+    for (unsigned p = 0; p < a.hcap; ++p) {
+      unsigned long long kk = a.hkey[slot];
+      if (kk == 0ull) break;
+      if (kk == h) {
+        // the same key must be the same path: compare with the representative
+        Cand c = a.cand[(unsigned)(a.hrep[slot] & 0xffffffffull)];
+        bool same = cand_rx(c) == sk.link && cand_seg(c) == sk.depth;
+        for (int j = 0; same && j < sk.depth; ++j) same = a.log_id[(size_t)j * a.R + c.ray] == sk.tri[j];
+        if (!same) atomicOr(&a.ctr->err, ERR_HASH_COLLISION);
+        found = true;
+        break;
+      }
+      slot = (slot + 1u) & mask;
+    }
+    if (found) continue;
+    unsigned u = atomicAdd(&a.ctr->n_unique, 1u);
+    if (u < a.ucap) a.uniq[u] = ~(int)i;
+    else atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
   }
 }
 
@@ -258,29 +295,43 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
     unsigned u = spread_index(t);
     if (u >= nu) break;
     int ci = a.uniq[u];
-    Cand c = a.cand[ci];
-    int slot = a.cand_slot[ci];
     PathRec rec;
-    rec.key = a.hkey[slot];
-    // this slot is no longer needed: leave the table empty for the next frame
-    a.hkey[slot] = 0ull;
-    a.hrep[slot] = ~0ull;
-    int k = cand_seg(c), rxi = cand_rx(c);
-    // the record's key (the output order within a link) leaves the
-    // transmitter out: (receiver, depth, sequence), as a single-transmitter
-    // frame has it
-    if (rxi >= a.nrx) rec.key = path_key_of(a, c.ray, rxi % a.nrx, k);
+    int k, rxi, ray;
+    int ids[kMaxRefl];
+    unsigned fl0 = 0u;
+    if (ci >= 0) {
+      Cand c = a.cand[ci];
+      int slot = a.cand_slot[ci];
+      rec.key = a.hkey[slot];
+      // this slot is no longer needed: leave the table empty for the next frame
+      a.hkey[slot] = 0ull;
+      a.hrep[slot] = ~0ull;
+      k = cand_seg(c);
+      rxi = cand_rx(c);
+      ray = c.ray;
+      // the record's key (the output order within a link) leaves the
+      // transmitter out: (receiver, depth, sequence), as a single-transmitter
+      // frame has it
+      if (rxi >= a.nrx) rec.key = path_key_of(a, ray, rxi % a.nrx, k);
+      for (int j = 0; j < kMaxRefl; ++j) ids[j] = j < k ? a.log_id[(size_t)j * a.R + ray] : -1;
+    } else {  // sticky mode: a kept path that no capture of this frame has
+      const StickyKey& sk = a.sticky_prev[~ci];
+      k = sk.depth;
+      rxi = sk.link;
+      ray = -1;
+      for (int j = 0; j < kMaxRefl; ++j) ids[j] = j < k ? sk.tri[j] : -1;
+      rec.key = seq_key(rxi % a.nrx, k, [&](int j) { return ids[j]; });
+      fl0 = DCEM_PATH_STICKY;
+    }
     rec.rx = rxi;
     rec.depth = k;
-    rec.ray = c.ray;
-    rec.flags = 0;
+    rec.ray = ray;
+    rec.flags = fl0;
     rec.valid = 0;
     rec.pad = 0;
     rec.len = 0.0;
     rec.amp_re = rec.amp_im = 0.0;
-    int ids[kMaxRefl];
     for (int j = 0; j < kMaxRefl; ++j) {
-      ids[j] = j < k ? a.log_id[(size_t)j * a.R + c.ray] : -1;
       rec.tri[j] = ids[j];
       rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
     }
@@ -352,9 +403,8 @@ __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
     unsigned u = q / W;
     int j = (int)(q - u * W);
     if (a.vstate[u] != 1) continue;
-    int ci = a.uniq[u];
-    Cand c = a.cand[ci];
-    int k = cand_seg(c);
+    const PathRec& rec = a.prec[u];
+    int k = rec.depth;
     if (j > k) continue;
     const d3* xs = reinterpret_cast<const d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
     d3 p0 = xs[j], p1 = xs[j + 1];
@@ -362,8 +412,8 @@ __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
     float3 o = f3((float)p0.x, (float)p0.y, (float)p0.z);
     float3 dvf = f3((float)dv.x, (float)dv.y, (float)dv.z);
     RayPre rp = ray_pre(o, dvf);
-    int ex0 = j >= 1 ? a.log_id[(size_t)(j - 1) * a.R + c.ray] : -1;
-    int ex1 = j < k ? a.log_id[(size_t)j * a.R + c.ray] : -1;
+    int ex0 = j >= 1 ? rec.tri[j - 1] : -1;
+    int ex1 = j < k ? rec.tri[j] : -1;
     if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st)) a.vstate[u] = 2;  // occluded
   }
   if (ovf) {
@@ -439,7 +489,7 @@ __global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
     double g = lam / (4.0 * M_PI) / L;
     double re = (double)(proj.re * cs + proj.im * sn), im = (double)(proj.im * cs - proj.re * sn);
     rec.valid = 1;
-    rec.flags = fl;
+    rec.flags |= fl;
     rec.amp_re = re * g;
     rec.amp_im = im * g;
     for (int j = 0; j < k; ++j) {
@@ -452,6 +502,17 @@ __global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
     if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)rxi * a.bucket_cap + pos] = (int)u;
     else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
     atomicAdd(&a.ctr->n_valid, 1u);
+    if (a.sticky_next) {  // kept for the next frame
+      if (rec.flags & DCEM_PATH_STICKY) atomicAdd(&a.ctr->n_sticky_valid, 1u);
+      unsigned q = atomicAdd(&a.ctr->n_sticky_next, 1u);
+      if (q < a.sticky_cap) {
+        StickyKey sk;
+        sk.link = rxi;
+        sk.depth = k;
+        for (int j = 0; j < kMaxRefl; ++j) sk.tri[j] = rec.tri[j];
+        a.sticky_next[q] = sk;
+      }
+    }
   }
 }
 
@@ -555,7 +616,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
         q.pts[j][2] = p.pts[j][2];
       }
       q.flags = p.flags;
-      q.ray = a.ray_perm[p.ray];
+      q.ray = p.ray >= 0 ? a.ray_perm[p.ray] : -1;
       q.key = p.key;
       q.len_m = p.len;
       q.delay_s = p.len / 299792458.0;
@@ -590,6 +651,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
 cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
   k_dedupe_insert<<<grid, 256, 0, st>>>(a);
   k_dedupe_unique<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sticky_probe(const PathArgs& a, int grid, cudaStream_t st) {
+  k_sticky_probe<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

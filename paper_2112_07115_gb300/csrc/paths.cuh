@@ -42,9 +42,19 @@ struct PathArgs {
   int prec_df;                    // 1: validation geometry in double-float, 0: FP64
   double freq, tx_power;
   DevCounters* ctr;
+  // sticky mode (null otherwise): the previous frame's valid paths, to be
+  // re-validated when no capture of this frame has their key, and the
+  // buffer that keeps this frame's valid paths for the next one
+  const StickyKey* sticky_prev;
+  const unsigned* sticky_prev_n;
+  unsigned sticky_cap;
+  StickyKey* sticky_next;
 };
 
 cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st);
+// Sticky mode: the previous frame's valid paths whose key no capture of this
+// frame has join the distinct keys (validated like them).
+cudaError_t launch_sticky_probe(const PathArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st);
 // Per-link sums and ordered output; links above kScanLinks take their output
 // offsets from a scan (a.link_off) instead of summing the lower links' counts.

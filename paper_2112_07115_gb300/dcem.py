@@ -20,10 +20,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdcem.so")
 MAX_REFL = 10
 OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_NONFINITE, ERR_STACK, ERR_HASH, ERR_STATE, ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
-MODE_FULL, MODE_COHERENT = 0, 1
+MODE_FULL, MODE_COHERENT, MODE_STICKY = 0, 1, 2
 PREC_F64, PREC_DF32 = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 PATH_POL_DEGENERATE = 1
+PATH_STICKY = 2
 
 EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_update_transforms", "dcem_trace_frame", "dcem_scene_reset_cache",
@@ -64,7 +65,7 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int32), ("bvh_rebuilt", C.c_int32),
                 ("ms_stage", C.c_float * 10), ("bvh_cost_ratio", C.c_float),
                 ("max_segment_nodes", C.c_int32), ("trace_kernel", C.c_int32),
-                ("graph_replayed", C.c_int32)]
+                ("graph_replayed", C.c_int32), ("paths_sticky", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -11,7 +11,8 @@ PATH_FLAGS = O.PATH_FLAGS
 
 
 def oracle_params(sc, n_rays=None, **kw):
-    return O.OracleParams(freq_hz=sc.freq_hz, n_rays=n_rays or sc.n_rays, max_refl=sc.max_refl, **kw)
+    kw.setdefault("max_refl", sc.max_refl)
+    return O.OracleParams(freq_hz=sc.freq_hz, n_rays=n_rays or sc.n_rays, **kw)
 
 
 def gpu_params(sc, **kw):

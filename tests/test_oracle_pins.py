@@ -389,3 +389,37 @@ def test_transform_exact_cases(oracle_mod):
     out = O.transform(tris, np.array([0]), rot)
     want = np.stack([10 - tris[0, :, 1], -20 + tris[0, :, 0], 3 + tris[0, :, 2]], axis=1)
     assert np.array_equal(out[0], want.astype(np.float32))
+
+
+# ---------------------------------------------------------------- path cache
+
+def test_sticky_retention_keeps_true_paths(oracle_mod):
+    """The path cache's retention mode (Sec. III "Propagation path caching"):
+    with few rays, discovery misses paths from frame to frame, and retention
+    keeps paths found earlier. Every path a frame reports (captured or kept)
+    is a true path of that frame's geometry: it is in the exhaustive
+    enumeration of all sequences, with the same length and amplitude. Kept
+    paths were valid in the previous frame, and each frame's set contains the
+    plain frame's valid set."""
+    O = oracle_mod
+    s = scenes.toy_street()
+    n = 200
+    prm = O.OracleParams(max_refl=2, n_rays=n)
+    rays = scenes.fibonacci_sphere(n)
+    res = O.sticky_frames(s, range(10), rays, prm)
+    kept_total = 0
+    prev_valid = set()
+    for f, r in enumerate(res):
+        ek, ep = O.exhaustive(r.world_tris, s.tri_mat, s.materials, s.tx, s.rx[f], prm)
+        ex = {tuple(k): p for k, p in zip(ek.tolist(), ep)}
+        valid = {tuple(k): p for k, p in zip(r.keys.tolist(), r.paths) if p["valid"]}
+        assert set(valid) <= set(ex)
+        for k, p in valid.items():
+            assert abs(p["len_m"] - ex[k]["len_m"]) <= 1e-9 and abs(p["amp_re"] - ex[k]["amp_re"]) <= 1e-12
+        plain = O.frame(s, f, rays, prm)
+        assert {tuple(k) for k, p in zip(plain.keys.tolist(), plain.paths) if p["valid"]} <= set(valid)
+        kept = {tuple(k) for k in r.extra["kept_only"].tolist()}
+        assert kept <= prev_valid and kept <= set(valid)
+        kept_total += len(kept)
+        prev_valid = set(valid)
+    assert kept_total > 0
