@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-transmitter workload")
     ap.add_argument("--batched-frames", type=int, default=8)
+    ap.add_argument("--no-multi-scene", action="store_true", help="skip the multi-scene batch workload")
     return ap.parse_args()
 
 
@@ -350,6 +351,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, stream, dev, world, flush)
+    multi = None
+    if not args.no_multi_scene:
+        multi = run_multi_scene(args, stream, dev, world, flush)
 
     e2e = None
     if not args.no_e2e:
@@ -386,6 +390,7 @@ def run_ours(args):
             "gradients": grads,
             "validation_precision": precs,
             "batched": batched,
+            "multi_scene": multi,
             "full": {"frames_per_s": round(fps_full, 2), "ms_per_frame": round(1e3 * t_full / K, 4),
                      "ray_segments_per_s": round(seg_full, 0), "segments_per_frame": int(seg_mean),
                      "nodes_per_segment": round(nodes_per_seg, 2), "tris_per_segment": round(tris_per_seg, 2),
@@ -491,6 +496,96 @@ def run_batched(args, stream, dev, world, flush, warmup=2):
                          [x["segments_reused"] / max(1, x["segments_reused"] + x["segments_traced"]) for x in st])), 4),
                      "graph_replayed_frac": round(float(np.mean([x["graph_replayed"] for x in st])), 3)}
     return out
+
+
+def run_multi_scene(args, stream, dev, world, flush, warmup=2):
+    """The multi-scene batch: 32 independent urban grids (1k-200k triangles,
+    10-2000 vehicles, 1-16 transmitters each with 16k-512k rays; 1.2M
+    triangles, 296 transmitters, 43.5M rays, 367k links in all), 4
+    reflections, refit and traced together (dcem_batch_update_transforms +
+    dcem_batch_trace: one graph launch per frame once the plans repeat),
+    device outputs, L2 flushed before each frame. Also the same frames with
+    the scenes traced one after another (dcem_trace_links each) for the
+    concurrency gain."""
+    import ctypes as C
+    import torch
+    from paper_2112_07115_gb300 import dcem, scenes
+    K = args.batched_frames
+    nf = warmup + K + 1
+    scs = scenes.scene_batch(seed=0, n_frames=2 * nf + 1)
+    objs, res, keep = [], [], []
+    for sc in scs:
+        s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+        s.set_ray_sets([scenes.fibonacci_sphere(n) for n in sc.meta["budgets"]])
+        objs.append(s)
+        nl = len(sc.meta["budgets"]) * sc.nrx
+        mp = max(1024, 8 * nl)
+        bufs = (torch.empty((nl, 2), dtype=torch.float64, device=dev), torch.empty(nl, dtype=torch.float64, device=dev),
+                torch.empty(nl, dtype=torch.float64, device=dev),
+                torch.empty(mp * C.sizeof(dcem.Path), dtype=torch.uint8, device=dev))
+        keep.append(bufs)
+        r = dcem.Result()
+        r.ptr_kind = dcem.PTR_DEVICE
+        r.max_paths = mp
+        r.field, r.p_coh_dbm, r.p_inc_dbm, r.paths = [x.data_ptr() for x in bufs]
+        res.append(r)
+    xf_d = [torch.from_numpy(sc.xf).to(dev) if sc.nobj else None for sc in scs]
+    rx_d = [torch.from_numpy(sc.rx).to(dev) for sc in scs]
+    txs = [sc.meta["tx"] for sc in scs]
+    prm = dcem.default_params(max_refl=4, freq_hz=28e9, mode=dcem.MODE_FULL)
+    b = dcem.Batch(objs, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, st = [], []
+    for i in range(warmup + K):
+        f = i + 1
+        flush.zero_()
+        e0.record(stream)
+        b.update_transforms([x[f] if x is not None else None for x in xf_d])
+        rc, failed = b.trace_raw(txs, [x[f] for x in rx_d], prm, res)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != dcem.OK:
+            raise dcem.DcemError(rc, f"multi-scene frame {f} (scene {failed})")
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+            st.append([dcem.stats_dict(r.stats) for r in res])
+    b.close()
+    # the same scenes, one after another
+    ms_seq = []
+    for i in range(warmup + K):
+        f = nf + i + 1
+        flush.zero_()
+        e0.record(stream)
+        for k, s in enumerate(objs):
+            if xf_d[k] is not None:
+                dcem.dcem_scene_update_transforms(s.h, xf_d[k][f])
+            rc = dcem.dcem_trace_links(s.h, txs[k], rx_d[k][f], prm, res[k])
+            if rc != dcem.OK:
+                raise dcem.DcemError(rc, f"multi-scene sequential frame {f} (scene {k})")
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            ms_seq.append(e0.elapsed_time(e1))
+    for s in objs:
+        s.close()
+    t = max_over_ranks([sum(ms) / 1e3], dev)[0]
+    t_seq = max_over_ranks([sum(ms_seq) / 1e3], dev)[0]
+    rays = sum(sum(sc.meta["budgets"]) for sc in scs)
+    links = sum(len(sc.meta["budgets"]) * sc.nrx for sc in scs)
+    segs = float(np.mean([sum(x["segments_traced"] for x in fr) for fr in st]))
+    return {"workload": "%d independent urban grids: %d-%d triangles (%d in all), %d-%d vehicles (%d), %d "
+                        "transmitters with %d-%d rays (%d rays), %d links, 4 reflections, 28 GHz, full frames"
+                        % (len(scs), min(x.ntri for x in scs), max(x.ntri for x in scs), sum(x.ntri for x in scs),
+                           min(x.nobj for x in scs), max(x.nobj for x in scs), sum(x.nobj for x in scs),
+                           sum(len(x.meta["budgets"]) for x in scs), min(min(x.meta["budgets"]) for x in scs),
+                           max(max(x.meta["budgets"]) for x in scs), rays, links),
+            "frames_per_s": round(world * K / t, 3), "ms_per_frame": round(1e3 * t / K, 3),
+            "rays_per_s": round(world * K * rays / t, 0),
+            "ray_segments_traced_per_s": round(world * K * segs / t, 0),
+            "paths_per_frame": int(np.mean([sum(x["paths_valid"] for x in fr) for fr in st])),
+            "graph_replayed_frac": round(float(np.mean([min(x["graph_replayed"] for x in fr) for fr in st])), 3),
+            "one_after_another": {"frames_per_s": round(world * K / t_seq, 3),
+                                  "ms_per_frame": round(1e3 * t_seq / K, 3)}}
 
 
 def grad_timing(s, sc, rx_f, paths_d, n_paths, stream, dev, reps=20):

@@ -320,6 +320,39 @@ void dcem_scene_destroy(dcem_scene* s);
 /* Static string for a status code. */
 const char* dcem_status_string(int status);
 
+/* ---- several scenes per frame ---- */
+
+/* A batch of n distinct scenes traced together. Each frame's device work of
+ * all scenes is one CUDA graph launch: every scene's captured frame graph
+ * (see dcem_scene_set_graph_replay) is a parallel child, so independent
+ * scenes run concurrently. The scenes stay owned by the caller, must
+ * outlive the batch, and are moved to `stream` (dcem_scene_set_stream).
+ * Errors: DCEM_ERR_ARG (null, n < 1, n > 1024, a scene listed twice),
+ * DCEM_ERR_CUDA. */
+typedef struct dcem_batch dcem_batch;
+int dcem_batch_create(dcem_scene* const* scenes, int32_t n, void* stream, dcem_batch** out);
+
+/* Per-frame update of every scene, as dcem_scene_update_transforms(scene i,
+ * xf[i], ptr_kind) (xf[i] may be NULL for a scene without moving objects).
+ * The scenes' updates run concurrently on streams forked from the batch
+ * stream and joined back to it. Host transforms are checked before any work
+ * is enqueued. Errors: as dcem_scene_update_transforms. */
+int dcem_batch_update_transforms(dcem_batch* b, const float* const* xf, int32_t ptr_kind);
+
+/* One frame of every scene: scene i as dcem_trace_links(scene i, tx[i],
+ * ntx[i], rx[i], nrx[i], rx_ptr_kind, params, &out[i]), with bit-identical
+ * results. When every scene's frame plan repeats and params->timing == 0,
+ * the frame is one graph launch (stats.graph_replayed = 1 in every result);
+ * otherwise the scenes' frames are launched one after another. Synchronises
+ * the batch stream. Errors: the first failing scene's status, its index in
+ * *failed (if not NULL; -1 when all succeed). */
+int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, const float* const* rx,
+                     const int32_t* nrx, int32_t rx_ptr_kind, const dcem_params* params, dcem_result* out,
+                     int32_t* failed);
+
+/* Frees the batch (not its scenes). NULL is a no-op. */
+void dcem_batch_destroy(dcem_batch* b);
+
 /* ---- introspection (tests and tools; synchronise the scene stream) ---- */
 
 /* Counts of the scene: ntri, nobj, n_rays, internal nodes of the static and

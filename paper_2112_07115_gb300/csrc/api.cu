@@ -201,7 +201,15 @@ struct FramePlan {
 struct FrameGraph {
   FramePlan key;
   bool have_key = false;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;     // the captured frame (also a child of batch graphs)
+  cudaGraphExec_t exec = nullptr;  // its instantiation for single-scene replay
+  unsigned long long gen = 0;      // capture number (identifies the graph in batch graphs)
+  void drop() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
 };
 
 struct dcem_scene {
@@ -362,8 +370,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->mvt_arrive); dfree(s->mvt_root); dfree(s->mvt_root_box);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
-  for (auto& g : s->fgraph)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& g : s->fgraph) g.drop();
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   delete s;
 }
@@ -1229,7 +1236,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
 }
 // Captures the frame's work from its plan into a graph on the scene's
 // capture stream (nothing runs while capturing) and instantiates it.
-static int capture_frame(dcem_scene* s, const FramePlan& P, cudaGraphExec_t* exec) {
+static int capture_frame(dcem_scene* s, const FramePlan& P, FrameGraph& G) {
   if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
   CK(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
   int rc = enqueue_frame(P, s->sms, s->cap_st, true);
@@ -1237,49 +1244,65 @@ static int capture_frame(dcem_scene* s, const FramePlan& P, cudaGraphExec_t* exe
   cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
   if (rc == DCEM_OK && e != cudaSuccess) rc = status_of(e);
   if (rc == DCEM_OK) {
-    e = cudaGraphInstantiate(exec, g, 0);
+    e = cudaGraphInstantiate(&G.exec, g, 0);
     if (e != cudaSuccess) {
-      *exec = nullptr;
+      G.exec = nullptr;
       rc = status_of(e);
     }
   }
-  if (g) cudaGraphDestroy(g);
+  if (rc == DCEM_OK) {
+    static unsigned long long captures = 0;
+    G.graph = g;
+    G.gen = ++captures;
+  } else if (g) {
+    cudaGraphDestroy(g);
+  }
   cudaGetLastError();
   return rc;
 }
 
-static int trace_once(dcem_scene* s, int nrx, const dcem_params* p, bool coherent, const dcem_result* out) {
-  cudaStream_t st = s->st;
+// The frame's plan, and its captured graph when the plan repeats. Plans
+// alternate with the candidate buffers' parity: one cached graph per parity.
+// A plan is captured the second time it is seen in a row (the first run also
+// sets every kernel's launch attributes), then replayed. Returns whether the
+// graph is ready (G.exec and G.graph).
+static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coherent, const dcem_result* out,
+                      bool* ready) {
   FramePlan& P = s->plan;
   make_plan(s, nrx, p, coherent, out, P);
   s->last_use_q = P.use_q;
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) + (P.use_q ? 1 : 0) +
                  (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0);
-  // Plans alternate with the candidate buffers' parity: one cached graph per
-  // parity. A plan is captured the second time it is seen in a row (the
-  // first run also sets every kernel's launch attributes), then replayed.
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
   if (!same) {
-    if (G.exec) cudaGraphExecDestroy(G.exec);
-    G.exec = nullptr;
+    G.drop();
     G.key = P;
     G.have_key = true;
   }
   if (s->use_graphs && same && !G.exec) {
-    int rc = capture_frame(s, P, &G.exec);
+    int rc = capture_frame(s, P, G);
     if (rc != DCEM_OK) {
       G.have_key = false;
       return rc;
     }
   }
-  if (s->use_graphs && same && G.exec) {
-    CK(cudaGraphLaunch(G.exec, st));
+  *ready = s->use_graphs && same && G.exec != nullptr;
+  return DCEM_OK;
+}
+
+static int trace_once(dcem_scene* s, int nrx, const dcem_params* p, bool coherent, const dcem_result* out) {
+  cudaStream_t st = s->st;
+  bool ready = false;
+  int rc = plan_frame(s, nrx, p, coherent, out, &ready);
+  if (rc != DCEM_OK) return rc;
+  if (ready) {
+    CK(cudaGraphLaunch(s->fgraph[s->cur].exec, st));
     s->graph_replayed = 1;
   } else {
-    int rc = enqueue_frame(P, s->sms, st, false);
+    rc = enqueue_frame(s->plan, s->sms, st, false);
     if (rc != DCEM_OK) return rc;
   }
   CK(cudaStreamSynchronize(st));
@@ -1293,8 +1316,11 @@ int dcem_trace_frame(dcem_scene* s, const float* tx, const float* rx, int32_t nr
   return dcem_trace_links(s, tx, 1, rx, nrx, rx_ptr_kind, p, out);
 }
 
-int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
-                     int32_t rx_ptr_kind, const dcem_params* p, dcem_result* out) {
+// Checks a frame's arguments, sizes the buffers and stages its inputs (the
+// receivers' copy on the scene stream, the transmitters in pinned memory);
+// decides whether the frame may reuse the cache.
+static int frame_begin(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
+                       int32_t rx_ptr_kind, const dcem_params* p, dcem_result* out, bool* coherent) {
   if (!s || !tx || !p || !out || ntx < 1) return DCEM_ERR_ARG;
   if (nrx < 0 || (nrx > 0 && !rx)) return DCEM_ERR_ARG;
   if (nrx > kSmallBuild || (long long)ntx * nrx > kMaxLinks) return DCEM_ERR_ARG;
@@ -1334,16 +1360,28 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
     CK(cudaMemcpyAsync(s->rx3, rx, sizeof(float) * 3 * nrx,
                        rx_ptr_kind == DCEM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
 
-  bool coherent = p->mode != DCEM_MODE_FULL && s->cache_valid && same_traversal(*p, s->cparams) &&
+  *coherent = p->mode != DCEM_MODE_FULL && s->cache_valid && same_traversal(*p, s->cparams) &&
                   nrx == s->cnrx && s->ctx.size() == 3 * (size_t)ntx &&
                   std::memcmp(tx, s->ctx.data(), sizeof(float) * 3 * ntx) == 0 &&
                   s->logW == p->max_refl + 1;
+  return DCEM_OK;
+}
+
+// After the frame's first trace: regrowth and retrace on an internal
+// capacity overflow, the statistics, the copy-out and the cache state.
+static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
+                        int32_t rx_ptr_kind, const dcem_params* p, dcem_result* out, bool coherent, bool traced) {
+  int rc = DCEM_OK;
+  cudaStream_t st = s->st;
+  const int nlinks = ntx * nrx;
   DevCounters* c = nullptr;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    rc = trace_once(s, nrx, p, coherent, out);
-    if (rc != DCEM_OK) {
-      s->cache_valid = false;
-      return rc;
+    if (!(traced && attempt == 0)) {
+      rc = trace_once(s, nrx, p, coherent, out);
+      if (rc != DCEM_OK) {
+        s->cache_valid = false;
+        return rc;
+      }
     }
     c = s->ctr_h;
     unsigned err = c[0].err | c[1].err;
@@ -1446,6 +1484,198 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
   if (nvalid > out->max_paths && out->paths) return DCEM_ERR_CAPACITY;
   return DCEM_OK;
 }
+
+int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* rx, int32_t nrx,
+                     int32_t rx_ptr_kind, const dcem_params* p, dcem_result* out) {
+  bool coherent = false;
+  int rc = frame_begin(s, tx, ntx, rx, nrx, rx_ptr_kind, p, out, &coherent);
+  if (rc != DCEM_OK) return rc;
+  return frame_finish(s, tx, ntx, rx, nrx, rx_ptr_kind, p, out, coherent, false);
+}
+
+// ---------------------------------------------------------------------------
+// several scenes per frame
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct dcem_batch {
+  std::vector<dcem_scene*> sc;
+  cudaStream_t st = nullptr;
+  std::vector<cudaStream_t> fork;  // streams of the concurrent per-scene updates
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork_ev = nullptr;
+  // batch graphs: one child per scene (its captured frame), keyed by the
+  // children's capture numbers; two kept (the candidate parities alternate)
+  struct Parent {
+    std::vector<unsigned long long> kids;
+    cudaGraphExec_t exec = nullptr;
+  } parent[2];
+  int victim = 0;
+};
+
+namespace {
+
+void batch_free(dcem_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  for (auto& p : b->parent)
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+  for (auto f : b->fork) cudaStreamDestroy(f);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  delete b;
+}
+
+// The batch graph over the scenes' current frame graphs: reused when the
+// same captures are its children, else built (and the older one replaced).
+int batch_graph(dcem_batch* b, cudaGraphExec_t* exec) {
+  std::vector<unsigned long long> kids;
+  for (dcem_scene* s : b->sc) kids.push_back(s->fgraph[s->cur].gen);
+  for (auto& p : b->parent)
+    if (p.exec && p.kids == kids) {
+      *exec = p.exec;
+      return DCEM_OK;
+    }
+  auto& p = b->parent[b->victim];
+  b->victim ^= 1;
+  if (p.exec) cudaGraphExecDestroy(p.exec);
+  p.exec = nullptr;
+  p.kids.clear();
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaSuccess;
+  for (dcem_scene* s : b->sc) {
+    cudaGraphNode_t node;
+    e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, s->fgraph[s->cur].graph);
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p.exec = nullptr;
+    return status_of(e);
+  }
+  p.kids = kids;
+  *exec = p.exec;
+  return DCEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dcem_batch_create(dcem_scene* const* scenes, int32_t n, void* stream, dcem_batch** out) {
+  if (!scenes || !out || n < 1 || n > kMaxBatch) return DCEM_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!scenes[i]) return DCEM_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (scenes[j] == scenes[i]) return DCEM_ERR_ARG;
+  }
+  dcem_batch* b = new dcem_batch;
+  b->st = (cudaStream_t)stream;
+  b->sc.assign(scenes, scenes + n);
+  int nf = std::min(n, 8);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int k = 0; k < nf && e == cudaSuccess; ++k) {
+    cudaStream_t f;
+    cudaEvent_t j;
+    e = cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->fork.push_back(f);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->join.push_back(j);
+  }
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    int rc = dcem_scene_set_stream(scenes[i], stream);
+    if (rc != DCEM_OK) e = cudaErrorUnknown;
+  }
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return status_of(e);
+  }
+  *out = b;
+  return DCEM_OK;
+}
+
+int dcem_batch_update_transforms(dcem_batch* b, const float* const* xf, int32_t ptr_kind) {
+  if (!b || !xf) return DCEM_ERR_ARG;
+  if (ptr_kind != DCEM_PTR_HOST && ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
+  // host transforms are checked before any work is enqueued
+  for (size_t i = 0; i < b->sc.size(); ++i) {
+    dcem_scene* s = b->sc[i];
+    if (s->nobj > 0 && !xf[i]) return DCEM_ERR_ARG;
+    if (s->nobj > 0 && ptr_kind == DCEM_PTR_HOST && !finite_arr(xf[i], 12 * (size_t)s->nobj))
+      return DCEM_ERR_NONFINITE;
+  }
+  const int nf = (int)b->fork.size();
+  CK(cudaEventRecord(b->fork_ev, b->st));
+  for (int k = 0; k < nf; ++k) CK(cudaStreamWaitEvent(b->fork[k], b->fork_ev, 0));
+  int rc = DCEM_OK;
+  for (size_t i = 0; i < b->sc.size() && rc == DCEM_OK; ++i) {
+    dcem_scene* s = b->sc[i];
+    if (s->nobj == 0) continue;
+    s->st = b->fork[i % nf];
+    rc = dcem_scene_update_transforms(s, xf[i], ptr_kind);
+    s->st = b->st;
+  }
+  for (int k = 0; k < nf; ++k) {
+    CK(cudaEventRecord(b->join[k], b->fork[k]));
+    CK(cudaStreamWaitEvent(b->st, b->join[k], 0));
+  }
+  return rc;
+}
+
+int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, const float* const* rx,
+                     const int32_t* nrx, int32_t rx_ptr_kind, const dcem_params* p, dcem_result* out,
+                     int32_t* failed) {
+  if (failed) *failed = -1;
+  if (!b || !tx || !ntx || !rx || !nrx || !p || !out) return DCEM_ERR_ARG;
+  const int n = (int)b->sc.size();
+  std::vector<char> coh(n, 0);
+  auto fail = [&](int i, int rc) {
+    if (failed) *failed = i;
+    return rc;
+  };
+  for (int i = 0; i < n; ++i) {
+    bool c = false;
+    int rc = frame_begin(b->sc[i], tx[i], ntx[i], rx[i], nrx[i], rx_ptr_kind, p, &out[i], &c);
+    if (rc != DCEM_OK) return fail(i, rc);
+    coh[i] = c;
+  }
+  // every scene's frame graph ready (and no event timing): one launch
+  bool all = p->timing == 0;
+  for (int i = 0; i < n; ++i) {
+    bool ready = false;
+    int rc = plan_frame(b->sc[i], nrx[i], p, coh[i] != 0, &out[i], &ready);
+    if (rc != DCEM_OK) return fail(i, rc);
+    all = all && ready;
+  }
+  if (all) {
+    cudaGraphExec_t exec = nullptr;
+    int rc = batch_graph(b, &exec);
+    if (rc != DCEM_OK) return fail(0, rc);
+    CK(cudaGraphLaunch(exec, b->st));
+    for (dcem_scene* s : b->sc) s->graph_replayed = 1;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      int rc = enqueue_frame(b->sc[i]->plan, b->sc[i]->sms, b->st, false);
+      if (rc != DCEM_OK) return fail(i, rc);
+    }
+  }
+  CK(cudaStreamSynchronize(b->st));
+  for (dcem_scene* s : b->sc) s->cur ^= 1;
+  int first = DCEM_OK;
+  for (int i = 0; i < n; ++i) {
+    int rc = frame_finish(b->sc[i], tx[i], ntx[i], rx[i], nrx[i], rx_ptr_kind, p, &out[i], coh[i] != 0, true);
+    if (rc != DCEM_OK && first == DCEM_OK) {
+      first = rc;
+      if (failed) *failed = i;
+    }
+  }
+  return first;
+}
+
+void dcem_batch_destroy(dcem_batch* b) { batch_free(b); }
 
 int dcem_scene_gradient_size(const dcem_scene* s, int32_t* n_params) {
   if (!s || !n_params) return DCEM_ERR_ARG;

@@ -19,6 +19,7 @@ constexpr int kEmpty = (int)0x80000000; // empty tree / no node
 constexpr int kSmallBuild = 16384;      // largest tree built by the one-CTA builder
 constexpr int kMaxRaySets = 4096;       // transmitters (ray sets) per scene
 constexpr int kMaxLinks = 1 << 24;      // transmitter-receiver pairs per frame
+constexpr int kMaxBatch = 1024;         // scenes per batch
 constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
 
 // device error bits (DevCounters::err)

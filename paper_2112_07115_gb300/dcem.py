@@ -33,7 +33,8 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
             "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients",
             "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
-            "dcem_scene_set_trace_config", "dcem_scene_autotune"]
+            "dcem_scene_set_trace_config", "dcem_scene_autotune", "dcem_batch_create",
+            "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy"]
 
 
 class Material(C.Structure):
@@ -105,6 +106,11 @@ def lib():
         L.dcem_scene_set_ray_sets.argtypes = [vp, vp, vp, i32]
         L.dcem_trace_links.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), P(Result)]
         L.dcem_scene_set_trace_config.argtypes = [vp, i32, i32, i32]
+        L.dcem_batch_create.argtypes = [vp, i32, vp, P(vp)]
+        L.dcem_batch_update_transforms.argtypes = [vp, vp, i32]
+        L.dcem_batch_trace.argtypes = [vp, vp, vp, vp, vp, i32, P(Params), vp, P(i32)]
+        L.dcem_batch_destroy.argtypes = [vp]
+        L.dcem_batch_destroy.restype = None
         L.dcem_scene_autotune.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), i32, P(i32), P(i32), P(i32)]
         L.dcem_scene_reset_cache.argtypes = [vp]
         L.dcem_scene_set_stream.argtypes = [vp, vp]
@@ -123,7 +129,8 @@ def lib():
         L.dcem_scene_gradient_size.argtypes = [vp, P(i32)]
         L.dcem_path_gradients.argtypes = [vp, vp, vp, i32, i32, vp, i32, P(Params), i32, vp, vp, vp]
         for name in EXPORTED:
-            if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string"):
+            if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string",
+                            "dcem_batch_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -497,6 +504,95 @@ class Scene:
     def close(self):
         if getattr(self, "h", None):
             dcem_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several scenes traced together, one graph launch per frame (see
+    dcem_batch_create in include/dcem.h). The scenes stay owned by the caller."""
+
+    def __init__(self, scenes, stream=None):
+        self.scenes = list(scenes)
+        arr = (C.c_void_p * len(self.scenes))(*[x.h for x in self.scenes])
+        h = C.c_void_p()
+        _check(lib().dcem_batch_create(arr, len(self.scenes), stream, C.byref(h)), "dcem_batch_create")
+        self.h = h
+
+    def update_transforms(self, xfs):
+        """xfs: one (nobj, 12) array per scene (None for static scenes), all host or all device."""
+        keep, ptrs, kind = [], [], PTR_HOST
+        for x in xfs:
+            p, k, kp = _ptr(x, np.float32)
+            keep.append(kp)
+            ptrs.append(p)
+            if x is not None:
+                kind = k
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        _check(lib().dcem_batch_update_transforms(self.h, arr, kind), "dcem_batch_update_transforms")
+
+    def trace_raw(self, txs, rxs, params: Params, results):
+        """txs: per scene an (ntx, 3) array; rxs: per scene receivers (all host or
+        all device); results: per scene a Result. Returns (status, failed index)."""
+        n = len(self.scenes)
+        keep = []
+        txa = [np.ascontiguousarray(t, np.float32).reshape(-1, 3) for t in txs]
+        ntx = np.array([t.shape[0] for t in txa], np.int32)
+        tptr = (C.c_void_p * n)(*[t.ctypes.data for t in txa])
+        rptr, kind, nrx = [], PTR_HOST, []
+        for r in rxs:
+            p, k, kp = _ptr(r, np.float32)
+            keep.append(kp)
+            rptr.append(p)
+            kind = k
+            nrx.append((r.numel() if hasattr(r, "numel") else np.asarray(r).size) // 3)
+        nrx = np.array(nrx, np.int32)
+        rarr = (C.c_void_p * n)(*rptr)
+        res = (Result * n)(*results)
+        failed = C.c_int32(-1)
+        rc = lib().dcem_batch_trace(self.h, tptr, ntx.ctypes.data, rarr, nrx.ctypes.data, kind, C.byref(params),
+                                    res, C.byref(failed))
+        for i in range(n):
+            results[i] = res[i]
+        return rc, failed.value
+
+    def trace(self, txs, rxs, params: Params | None = None, max_paths: int | None = None):
+        """One frame of every scene with host outputs: a list of Frame."""
+        params = params or default_params()
+        bufs, results = [], []
+        for t, r in zip(txs, rxs):
+            ntx = np.asarray(t).reshape(-1, 3).shape[0]
+            nrx = (r.numel() if hasattr(r, "numel") else np.asarray(r).size) // 3
+            nl = ntx * nrx
+            mp = max_paths or max(1024, 256 * nl)
+            b = (np.empty((max(nl, 1), 2)), np.empty(max(nl, 1)), np.empty(max(nl, 1)), np.empty(mp, PATH_DTYPE),
+                 ntx, nrx)
+            res = Result()
+            res.ptr_kind = PTR_HOST
+            res.max_paths = mp
+            res.field, res.p_coh_dbm, res.p_inc_dbm = b[0].ctypes.data, b[1].ctypes.data, b[2].ctypes.data
+            res.paths = b[3].ctypes.data
+            bufs.append(b)
+            results.append(res)
+        rc, failed = self.trace_raw(txs, rxs, params, results)
+        if rc != OK:
+            raise DcemError(rc, f"dcem_batch_trace (scene {failed})")
+        out = []
+        for (field, pc, pi, paths, ntx, nrx), res in zip(bufs, results):
+            nl = ntx * nrx
+            n = min(res.n_paths, paths.shape[0])
+            out.append(Frame(rc, (field[:nl, 0] + 1j * field[:nl, 1]).reshape(ntx, nrx), pc[:nl].reshape(ntx, nrx),
+                             pi[:nl].reshape(ntx, nrx), paths[:n].copy(), stats_dict(res.stats)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dcem_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

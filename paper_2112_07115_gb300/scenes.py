@@ -17,6 +17,8 @@ Workloads:
     buildings (four static material classes), moving vehicles on four-lane
     streets, many roadside Tx with uneven ray budgets, four roof Rx per
     vehicle plus static roadside Rx (the batched multi-transmitter workload).
+  * ``scene_batch`` -- independent urban grids of very different sizes (1k-200k
+    triangles, 10-2000 vehicles, 1-16 Tx with uneven budgets) traced together.
   * small closed-form scenes (ground plane, parallel plates, random triangles).
 
 The paper (Sec. III) uses an .obj town model and measurement campaigns that
@@ -464,6 +466,35 @@ def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: fl
                  xf.astype(np.float32), txs[0].copy(), rx.astype(np.float32), freq_hz=freq_hz,
                  n_rays=int(bud[0]), max_refl=max_refl,
                  meta={"seed": seed, "dt": dt, "tx": txs, "budgets": bud.tolist(), "classes": cls.tolist()})
+
+
+def scene_batch(seed: int = 0, n: int = 32, tris: tuple = (1_000, 200_000), vehicles: tuple = (10, 2000),
+                tx_per_scene: tuple = (1, 16), budgets: tuple = (16_384, 524_288), n_frames: int = 10,
+                max_refl: int = 4, freq_hz: float = 28e9):
+    """``n`` independent urban-grid scenes for a multi-scene batch: triangle
+    targets log-uniform in ``tris`` (blocks and buildings per block chosen to
+    approach them), vehicles log-uniform in ``vehicles`` (capped at 30% of the
+    lanes' room), 1-16 roadside transmitters each with ray budgets
+    log-uniform in ``budgets``. Returns a list of Scene (``meta["tx"]``,
+    ``meta["budgets"]`` as in ``urban_grid``)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 4])))
+    out = []
+    for i in range(n):
+        target = float(np.exp(rng.uniform(np.log(tris[0]), np.log(tris[1]))))
+        best = None
+        for b in range(2, 15):
+            for p in range(1, 9):
+                est = 30.0 * b * b * p * p + 2.0 * ((100.0 * b + 20.0) / 25.0) ** 2
+                err = abs(np.log(est / target))
+                if best is None or err < best[0]:
+                    best = (err, b, p)
+        _, b, p = best
+        room = int(0.3 * 8 * (b + 1) * (100.0 * b + 20.0) / 25.0)
+        nv = int(min(room, np.exp(rng.uniform(np.log(vehicles[0]), np.log(vehicles[1])))))
+        ntx = int(rng.integers(tx_per_scene[0], tx_per_scene[1] + 1))
+        out.append(urban_grid(seed=1000 * seed + i, blocks=b, parcels=p, n_vehicles=nv, n_tx=ntx, budgets=budgets,
+                              n_static_rx=8, n_frames=n_frames, max_refl=max_refl, freq_hz=freq_hz))
+    return out
 
 
 # ----------------------------------------------------------------------------
