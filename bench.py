@@ -126,11 +126,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def src_sha() -> str:
+# The sources a kernel is compiled from: its translation unit and the
+# headers it includes (a traffic figure is stale once one of them changed).
+KERNEL_SOURCES = {
+    "k_trace_q": ["paper_2112_07115_gb300/csrc/trace.cu", "paper_2112_07115_gb300/csrc/trace.cuh",
+                  "paper_2112_07115_gb300/csrc/bvh.cuh", "paper_2112_07115_gb300/csrc/dcem_internal.cuh",
+                  "include/dcem.h"],
+}
+
+
+def src_sha(kernel: str) -> str:
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2112_07115_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
+    for f in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
@@ -153,7 +161,7 @@ def ncu_traffic(kernel: str):
     with open(p) as fh:
         d = json.load(fh)
     e = d.get(kernel)
-    if not e or e.get("src_sha") != src_sha():
+    if not e or kernel not in KERNEL_SOURCES or e.get("src_sha") != src_sha(kernel):
         return None
     return e
 
