@@ -22,6 +22,14 @@
  *                  (ray field of Eq. 1 with the free-space loss of Eq. 3).
  *   or_exhaustive  every triangle sequence of length <= N validated by the
  *                  image method (no sampling): the complete valid path set.
+ *   or_trace_tree  steps 1-2 with transmission (Sec. III "Reflected and
+ *                  transmitted rays"; Table II penetration losses): at a hit
+ *                  on a transmitting material the ray both reflects and
+ *                  continues straight through (a child ray), up to N
+ *                  reflections and T transmissions per path; or_validate
+ *                  takes such sequences (transmission marked by OR_TRANS in
+ *                  the triangle id) and scales the field by the material's
+ *                  penetration loss at each transmission.
  *   or_fresnel     Fresnel reflection coefficients.
  *
  * Everything after the FP32 inputs is FP64. Decisions that FP32 arithmetic
@@ -42,6 +50,7 @@
 #include <unistd.h>
 
 #define OR_MAX_REFL 10
+#define OR_TRANS 0x40000000  /* interaction id flag: transmission through the triangle */
 
 /* ray / path flag bits */
 #define ORF_NEAR_EDGE 1u     /* a triangle's in/out decision is within the margin */
@@ -83,7 +92,13 @@ typedef struct {
   double pol[3];           /* antenna polarisation reference vector u          */
   int32_t max_refl;        /* N reflections                                    */
   int32_t nthreads;        /* 0 = all cores                                     */
+  const double* trans_db;  /* per material penetration loss [dB]; < 0 opaque;
+                              NULL: every material opaque                       */
+  int32_t max_trans;       /* T transmissions per path (N + T <= OR_MAX_REFL)   */
+  int32_t pad_;
 } or_params;
+
+
 
 /* ------------------------------------------------------------------------ */
 /* scene: FP32 world triangles widened to FP64                               */
@@ -103,6 +118,10 @@ typedef struct {
   double* mats;  /* nmat x 3: eps_r, sigma, pec (owned copy) */
   int nmat;
 } oscene;
+
+static int transmits(const oscene* S, const or_params* P, int mat) {
+  return P->trans_db && P->max_trans > 0 && mat >= 0 && mat < S->nmat && P->trans_db[mat] >= 0.0;
+}
 
 static void tri_setup(otri* T) {
     T->e[0] = sub(T->v[1], T->v[0]);
@@ -465,6 +484,255 @@ int or_trace(const float* tris, const int32_t* tri_mat, int32_t ntri, const floa
   return J.err ? -3 : 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* or_trace_tree: steps 1-2 with transmission                                */
+/* ------------------------------------------------------------------------ */
+/* A ray instance: the primary ray of a sampled direction, or a child that
+ * continues straight through a transmitting triangle its parent hit. Its
+ * interaction ids (hit[0..nseg-1]; OR_TRANS marks a transmission) include
+ * the parent's prefix, so any capture's key is hit[0..seg-1]. */
+#define OR_MAX_SEG (OR_MAX_REFL + 1)
+typedef struct {
+  int32_t root;         /* sampled direction (primary ray index)          */
+  int32_t start;        /* first segment this instance traces              */
+  int32_t nseg;
+  uint32_t flags;       /* own and inherited flag bits                     */
+  int32_t hit[OR_MAX_SEG];
+  double t[OR_MAX_SEG];
+} oinst;
+
+typedef struct {
+  oinst* v;
+  long n, cap;
+} ivec;
+
+static int ipush(ivec* v, const oinst* x) {
+  if (v->n == v->cap) {
+    long nc = v->cap ? 2 * v->cap : 256;
+    oinst* p = (oinst*)realloc(v->v, (size_t)nc * sizeof(oinst));
+    if (!p) return -1;
+    v->v = p; v->cap = nc;
+  }
+  v->v[v->n++] = *x;
+  return 0;
+}
+
+/* one pending instance: state at the start of segment b */
+typedef struct {
+  oinst in;
+  v3 o, d;
+  double D;
+  int b, nr, nt, last;
+} opend;
+
+typedef struct {
+  const oscene* S;
+  const or_params* P;
+  v3 tx;
+  const float* rays;
+  int nrays;
+  const float* rx;
+  int nrx;
+  oinst* prim;        /* nrays primary instances */
+  ivec* kids;         /* per thread: children, in (root, spawn) order */
+  cvec* cv;           /* per thread: captures; ray = instance code (see below) */
+  atomic_long next;
+  int err;
+} tree_job;
+
+typedef struct { tree_job* J; int tid; } tree_arg;
+
+/* capture code of an instance: primary i -> i; the c-th child of this thread
+ * -> -(1 + c) (mapped to global ids after the merge) */
+static void trace_tree_one(tree_job* J, int tid, int i, xinfo* xs) {
+  const oscene* S = J->S;
+  const or_params* P = J->P;
+  const int N = P->max_refl, T = P->max_trans;
+  const double ae = P->rx_radius_scale * P->alpha / sqrt(3.0);
+  /* pending instances (depth first): at most N+T+1 spawns per instance on
+   * each of at most T+1 levels */
+  opend stack[128];
+  int sp = 0;
+  opend* q = &stack[sp++];
+  memset(q, 0, sizeof(*q));
+  q->in.root = i;
+  q->o = J->tx;
+  q->d = unit(mk(J->rays[3 * i], J->rays[3 * i + 1], J->rays[3 * i + 2]));
+  q->last = -1;
+  int first = 1;
+  while (sp > 0) {
+    opend cur = stack[--sp];
+    int code;
+    if (first) {
+      code = i;
+    } else {
+      code = -(int)(1 + J->kids[tid].n);
+    }
+    oinst in = cur.in;
+    in.start = cur.b;
+    v3 o = cur.o, d = cur.d;
+    double D = cur.D;
+    int b = cur.b, nr = cur.nr, nt = cur.nt, last = cur.last;
+    uint32_t fl = in.flags;
+    for (;;) {
+      double t, ct;
+      int id = closest_hit(S, o, d, D, last, P, xs, &t, &ct, &fl);
+      double tend = id >= 0 ? t : P->escape_len;
+      double base = P->edge_eps * (maxabs(o) + D);
+      double dtb = id >= 0 ? (base + P->edge_eps * t) / fmax(ct, 1e-6) : 0.0;
+      for (int r = 0; r < J->nrx; ++r) {
+        v3 R = mk(J->rx[3 * r], J->rx[3 * r + 1], J->rx[3 * r + 2]);
+        v3 w = sub(R, o);
+        double s = dot(w, d);
+        int clamped = 0;
+        if (s < 0) s = 0;
+        if (s > tend) { s = tend; clamped = 1; }
+        double dist = norm(sub(w, scl(d, s)));
+        double rho = ae * (D + s);
+        double m = (base + P->edge_eps * s) * (1.0 + ae) + (clamped ? dtb * (1.0 + ae) : 0.0);
+        if (fabs(dist - rho) <= m) fl |= ORF_NEAR_SPHERE;
+        if (dist <= rho && cpush(&J->cv[tid], code, b, r)) J->err = 1;
+      }
+      in.hit[b] = id;
+      in.t[b] = id >= 0 ? t : INFINITY;
+      in.nseg = b + 1;
+      if (id < 0) break;
+      const otri* Tr = &S->t[id];
+      v3 p = add(o, scl(d, t));
+      /* transmission: a child continues straight through */
+      if (nt < T && b + 1 <= N + T && transmits(S, P, Tr->mat)) {
+        if (sp >= 128) { J->err = 1; break; }
+        opend* c = &stack[sp++];
+        c->in = in;
+        c->in.hit[b] = id | OR_TRANS;
+        c->in.flags = fl;
+        c->o = p;
+        c->d = d;
+        c->D = D + t;
+        c->b = b + 1;
+        c->nr = nr;
+        c->nt = nt + 1;
+        c->last = id;
+      }
+      if (nr >= N) break;
+      /* specular reflection: d' = d - 2 (d.n^) n^ */
+      d = unit(sub(d, scl(Tr->nh, 2.0 * dot(d, Tr->nh))));
+      o = p;
+      D += t;
+      last = id;
+      ++nr;
+      ++b;
+    }
+    for (int k = in.nseg; k < OR_MAX_SEG; ++k) { in.hit[k] = -2; in.t[k] = NAN; }
+    in.flags = fl;
+    if (first) {
+      J->prim[i] = in;
+      first = 0;
+    } else if (ipush(&J->kids[tid], &in)) {
+      J->err = 1;
+    }
+    /* children of this instance inherit its flags at spawn (set above) */
+  }
+}
+
+static void* trace_tree_worker(void* p) {
+  tree_arg* a = (tree_arg*)p;
+  tree_job* J = a->J;
+  xinfo* xs = (xinfo*)malloc(sizeof(xinfo) * (size_t)(J->S->ntri > 0 ? J->S->ntri : 1));
+  if (!xs) { J->err = 1; return NULL; }
+  for (;;) {
+    long s = atomic_fetch_add(&J->next, 16);
+    if (s >= J->nrays) break;
+    long e = s + 16 < J->nrays ? s + 16 : J->nrays;
+    for (long i = s; i < e; ++i) trace_tree_one(J, a->tid, (int)i, xs);
+  }
+  free(xs);
+  return NULL;
+}
+
+static int inst_cmp(const void* a, const void* b) {
+  const long* x = (const long*)a;
+  const long* y = (const long*)b;
+  return x[0] < y[0] ? -1 : (x[0] > y[0] ? 1 : (x[1] < y[1] ? -1 : (x[1] > y[1] ? 1 : 0)));
+}
+
+/* Steps 1-2 with transmission. Instances: the nrays primaries (index = ray)
+ * then the children ordered by (root ray, spawn order). Outputs (malloc'd,
+ * free with or_free): inst (n_inst records), cands (3 ints per capture:
+ * instance, segment, receiver; sorted). */
+int or_trace_tree(const float* tris, const int32_t* tri_mat, int32_t ntri, const float* mats,
+                  int32_t nmat, const float* tx, const float* rays, int32_t nrays, const float* rx,
+                  int32_t nrx, const or_params* P, oinst** inst_out, int64_t* ninst_out,
+                  int32_t** cand_out, int64_t* ncand_out) {
+  if (P->max_refl < 0 || P->max_trans < 0 || P->max_refl + P->max_trans > OR_MAX_REFL) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  tree_job J;
+  memset(&J, 0, sizeof(J));
+  J.S = &S; J.P = P; J.tx = mk(tx[0], tx[1], tx[2]);
+  J.rays = rays; J.nrays = nrays; J.rx = rx; J.nrx = nrx;
+  J.prim = (oinst*)calloc((size_t)(nrays > 0 ? nrays : 1), sizeof(oinst));
+  atomic_init(&J.next, 0);
+  int nt = default_threads(P->nthreads);
+  J.kids = (ivec*)calloc((size_t)nt, sizeof(ivec));
+  J.cv = (cvec*)calloc((size_t)nt, sizeof(cvec));
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+  tree_arg* args = (tree_arg*)malloc(sizeof(tree_arg) * (size_t)nt);
+  for (int k = 0; k < nt; ++k) {
+    args[k].J = &J; args[k].tid = k;
+    pthread_create(&th[k], NULL, trace_tree_worker, &args[k]);
+  }
+  for (int k = 0; k < nt; ++k) pthread_join(th[k], NULL);
+  /* order the children by (root, spawn order): sort (root, thread, index) */
+  long nk = 0;
+  for (int k = 0; k < nt; ++k) nk += J.kids[k].n;
+  long* ord = (long*)malloc(sizeof(long) * 3 * (size_t)(nk > 0 ? nk : 1));
+  long pos = 0;
+  for (int k = 0; k < nt; ++k)
+    for (long c = 0; c < J.kids[k].n; ++c) {
+      ord[3 * pos] = J.kids[k].v[c].root;
+      ord[3 * pos + 1] = c;  /* spawn order within the thread (rays of a thread are processed in order) */
+      ord[3 * pos + 2] = k;
+      ++pos;
+    }
+  qsort(ord, (size_t)nk, 3 * sizeof(long), inst_cmp);
+  /* global id of each thread's child c */
+  long** gid = (long**)calloc((size_t)nt, sizeof(long*));
+  for (int k = 0; k < nt; ++k) gid[k] = (long*)malloc(sizeof(long) * (size_t)(J.kids[k].n > 0 ? J.kids[k].n : 1));
+  oinst* inst = (oinst*)malloc(sizeof(oinst) * (size_t)(nrays + nk > 0 ? nrays + nk : 1));
+  if (nrays) memcpy(inst, J.prim, sizeof(oinst) * (size_t)nrays);
+  for (long r = 0; r < nk; ++r) {
+    int k = (int)ord[3 * r + 2];
+    long c = ord[3 * r + 1];
+    gid[k][c] = nrays + r;
+    inst[nrays + r] = J.kids[k].v[c];
+  }
+  long tot = 0;
+  for (int k = 0; k < nt; ++k) tot += J.cv[k].n;
+  ocand* all = (ocand*)malloc(sizeof(ocand) * (size_t)(tot > 0 ? tot : 1));
+  pos = 0;
+  for (int k = 0; k < nt; ++k) {
+    for (long c = 0; c < J.cv[k].n; ++c) {
+      ocand x = J.cv[k].c[c];
+      if (x.ray < 0) x.ray = (int32_t)gid[k][-x.ray - 1];
+      all[pos++] = x;
+    }
+    free(J.cv[k].c);
+    free(J.kids[k].v);
+    free(gid[k]);
+  }
+  qsort(all, (size_t)tot, sizeof(ocand), cand_cmp);
+  *inst_out = inst;
+  *ninst_out = nrays + nk;
+  *cand_out = (int32_t*)all;
+  *ncand_out = tot;
+  free(ord); free(gid); free(J.kids); free(J.cv); free(th); free(args); free(J.prim);
+  scene_free(&S);
+  return J.err ? -3 : 0;
+}
+
+int32_t or_inst_size(void) { return (int32_t)sizeof(oinst); }
+
 void or_free(void* p) { free(p); }
 
 /* ------------------------------------------------------------------------ */
@@ -556,40 +824,77 @@ static void validate_one(const oscene* S, const or_params* P, v3 tx, v3 rx, int 
                          const int32_t* ids, opath* out, int check_occ) {
   memset(out, 0, sizeof(*out));
   uint32_t fl = 0;
-  for (int j = 0; j < k; ++j)
-    if (ids[j] < 0 || ids[j] >= S->ntri) { out->valid = 0; return; }
-  /* image sources I_1..I_k of the transmitter in the planes of tri_1..tri_k */
+  /* interactions: reflections, and transmissions (OR_TRANS) straight through
+   * a transmitting triangle */
+  int tid[OR_MAX_REFL], isT[OR_MAX_REFL], rj[OR_MAX_REFL], m = 0;
+  for (int j = 0; j < k; ++j) {
+    if (ids[j] < 0) { out->valid = 0; return; }
+    isT[j] = (ids[j] & OR_TRANS) != 0;
+    tid[j] = ids[j] & ~OR_TRANS;
+    if (tid[j] >= S->ntri) { out->valid = 0; return; }
+    if (isT[j] && !transmits(S, P, S->t[tid[j]].mat)) { out->valid = 0; return; }
+    if (!isT[j]) rj[m++] = j;
+  }
+  /* image sources I_1..I_m of the transmitter in the planes of the
+   * reflecting triangles (transmissions do not turn the path) */
   v3 img[OR_MAX_REFL + 1];
   img[0] = tx;
-  for (int j = 1; j <= k; ++j) {
-    const otri* T = &S->t[ids[j - 1]];
+  for (int q = 1; q <= m; ++q) {
+    const otri* T = &S->t[tid[rj[q - 1]]];
     double nn = dot(T->n, T->n);
     if (!(nn > 0)) { out->valid = 0; return; }
-    double h = dot(sub(img[j - 1], T->v[0]), T->n) / nn;
-    img[j] = sub(img[j - 1], scl(T->n, 2.0 * h));
+    double h = dot(sub(img[q - 1], T->v[0]), T->n) / nn;
+    img[q] = sub(img[q - 1], scl(T->n, 2.0 * h));
   }
-  /* back-trace from the receiver: X_{k+1} = Rx, P_j on plane j toward I_j */
-  v3 X[OR_MAX_REFL + 2];
-  X[k + 1] = rx;
-  X[0] = tx;
+  /* back-trace from the receiver: XR_{m+1} = Rx, reflection point q on its
+   * plane toward I_q */
+  v3 XR[OR_MAX_REFL + 2];
+  XR[m + 1] = rx;
+  XR[0] = tx;
   double scale = fmax(maxabs(tx), maxabs(rx));
-  for (int j = k; j >= 1; --j) {
-    const otri* T = &S->t[ids[j - 1]];
-    v3 dir = sub(img[j], X[j + 1]);
+  double ve = P->val_eps;
+  for (int q = m; q >= 1; --q) {
+    const otri* T = &S->t[tid[rj[q - 1]]];
+    v3 dir = sub(img[q], XR[q + 1]);
     double den = dot(dir, T->n);
     if (den == 0) { out->valid = 0; out->flags = fl; return; }
-    double s = dot(sub(T->v[0], X[j + 1]), T->n) / den;
-    double ve = P->val_eps;
-    if (fabs(s) <= ve || fabs(s - 1.0) <= ve) fl |= ORF_VAL_PARAM;
-    if (!(s > 0 && s < 1)) { out->valid = 0; out->flags = fl; return; }
-    X[j] = add(X[j + 1], scl(dir, s));
-    scale = fmax(scale, maxabs(X[j]));
+    double sv = dot(sub(T->v[0], XR[q + 1]), T->n) / den;
+    if (fabs(sv) <= ve || fabs(sv - 1.0) <= ve) fl |= ORF_VAL_PARAM;
+    if (!(sv > 0 && sv < 1)) { out->valid = 0; out->flags = fl; return; }
+    XR[q] = add(XR[q + 1], scl(dir, sv));
+    scale = fmax(scale, maxabs(XR[q]));
+  }
+  /* the interaction points in order: a transmission crosses its triangle's
+   * plane on the straight piece between the surrounding reflection points,
+   * after the previous interaction of that piece */
+  v3 X[OR_MAX_REFL + 2];
+  X[0] = tx;
+  X[k + 1] = rx;
+  {
+    int q = 0;
+    double s_prev = 0.0;
+    for (int j = 0; j < k; ++j) {
+      if (!isT[j]) {
+        X[j + 1] = XR[++q];
+        s_prev = 0.0;
+        continue;
+      }
+      const otri* T = &S->t[tid[j]];
+      v3 A = XR[q], B = XR[q + 1], dir = sub(B, A);
+      double den = dot(dir, T->n);
+      if (den == 0) { out->valid = 0; out->flags = fl; return; }
+      double sv = dot(sub(T->v[0], A), T->n) / den;
+      if (fabs(sv - s_prev) <= ve || fabs(sv - 1.0) <= ve) fl |= ORF_VAL_PARAM;
+      if (!(sv > s_prev && sv < 1)) { out->valid = 0; out->flags = fl; return; }
+      X[j + 1] = add(A, scl(dir, sv));
+      s_prev = sv;
+    }
   }
   int ok = 1;
   for (int j = 1; j <= k; ++j) {
-    const otri* T = &S->t[ids[j - 1]];
-    double m = edge_margin(T, X[j]);
-    if (m <= P->val_eps * (scale + 1.0)) fl |= ORF_VAL_EDGE;
+    const otri* T = &S->t[tid[j - 1]];
+    double mg = edge_margin(T, X[j]);
+    if (mg <= P->val_eps * (scale + 1.0)) fl |= ORF_VAL_EDGE;
     if (!point_in_tri(T, X[j])) ok = 0;
   }
   if (!ok) { out->valid = 0; out->flags = fl; return; }
@@ -598,8 +903,8 @@ static void validate_one(const oscene* S, const or_params* P, v3 tx, v3 rx, int 
   for (int j = 0; j <= k; ++j) L += norm(sub(X[j + 1], X[j]));
   if (!(L > 0)) { out->valid = 0; out->flags = fl; return; }
   for (int j = 0; check_occ && j <= k; ++j) {
-    int ex0 = j >= 1 ? ids[j - 1] : -1;
-    int ex1 = j + 1 <= k ? ids[j] : -1;
+    int ex0 = j >= 1 ? tid[j - 1] : -1;
+    int ex1 = j + 1 <= k ? tid[j] : -1;
     if (occluded(S, X[j], X[j + 1], ex0, ex1, P, scale + L, &fl)) ok = 0;
   }
   out->flags = fl;
@@ -617,7 +922,12 @@ static void validate_one(const oscene* S, const or_params* P, v3 tx, v3 rx, int 
   v3 e0 = pol_dir(u, d0, &fl);
   c3 E = {e0.x, e0.y, e0.z};
   for (int j = 1; j <= k; ++j) {
-    const otri* T = &S->t[ids[j - 1]];
+    const otri* T = &S->t[tid[j - 1]];
+    if (isT[j - 1]) {  /* penetration loss (power dB): field times 10^(-L/20) */
+      double g = pow(10.0, -P->trans_db[T->mat] / 20.0);
+      E.x *= g; E.y *= g; E.z *= g;
+      continue;
+    }
     v3 din = unit(sub(X[j], X[j - 1]));
     v3 dout = unit(sub(X[j + 1], X[j]));
     v3 nh = T->nh;
@@ -680,17 +990,18 @@ static void* val_worker(void* p) {
   return NULL;
 }
 
-/* keys: ncand rows of (2 + max_refl) int32: rx index, depth k, tri ids (k used). */
+/* keys: ncand rows of (2 + max_refl + max_trans) int32: rx index, depth k
+ * (interactions), tri ids (k used; OR_TRANS marks a transmission). */
 int or_validate(const float* tris, const int32_t* tri_mat, int32_t ntri, const float* mats,
                 int32_t nmat, const float* tx, const float* rx, int32_t nrx,
                 const int32_t* keys, int64_t ncand, const or_params* P, opath* out) {
   (void)nrx;
-  if (P->max_refl < 0 || P->max_refl > OR_MAX_REFL) return -1;
+  if (P->max_refl < 0 || P->max_trans < 0 || P->max_refl + P->max_trans > OR_MAX_REFL) return -1;
   oscene S;
   if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
   val_job J;
   J.S = &S; J.P = P; J.tx = mk(tx[0], tx[1], tx[2]); J.rx = rx; J.keys = keys;
-  J.stride = 2 + P->max_refl; J.ncand = ncand; J.out = out;
+  J.stride = 2 + P->max_refl + P->max_trans; J.ncand = ncand; J.out = out;
   atomic_init(&J.next, 0);
   int nt = default_threads(P->nthreads);
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
@@ -733,29 +1044,37 @@ int32_t or_path_size(void) { return (int32_t)sizeof(opath); }
 int64_t or_exhaustive(const float* tris, const int32_t* tri_mat, int32_t ntri, const float* mats,
                       int32_t nmat, const float* tx, const float* rx, int32_t nrx,
                       const or_params* P, int32_t* keys_out, opath* paths_out, int64_t cap) {
-  if (P->max_refl < 0 || P->max_refl > OR_MAX_REFL) return -1;
+  if (P->max_refl < 0 || P->max_trans < 0 || P->max_refl + P->max_trans > OR_MAX_REFL) return -1;
   oscene S;
   if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
-  int N = P->max_refl, stride = 2 + N;
+  const int N = P->max_refl, T = P->trans_db ? P->max_trans : 0, W = N + T, stride = 2 + W;
+  /* each interaction: a triangle and (with transmission) reflect or transmit */
+  const int ch = T > 0 ? 2 * ntri : ntri;
   int64_t nvalid = 0;
-  int32_t ids[OR_MAX_REFL];
+  int32_t ids[OR_MAX_REFL], c[OR_MAX_REFL];
   opath tmp;
   for (int r = 0; r < nrx; ++r) {
     v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
-    for (int k = 0; k <= N; ++k) {
+    for (int k = 0; k <= W; ++k) {
       if (k > 0 && ntri == 0) break;
-      for (int j = 0; j < k; ++j) ids[j] = 0;
+      for (int j = 0; j < k; ++j) c[j] = 0;
       for (;;) {
-        int okseq = 1;
-        for (int j = 1; j < k; ++j)
-          if (ids[j] == ids[j - 1]) { okseq = 0; break; }
+        int okseq = 1, nr = 0, ntr = 0;
+        for (int j = 0; j < k; ++j) {
+          int tri = T > 0 ? c[j] >> 1 : c[j], tr = T > 0 ? (c[j] & 1) : 0;
+          ids[j] = tr ? (tri | OR_TRANS) : tri;
+          if (tr) ++ntr; else ++nr;
+          if (tr && !transmits(&S, P, S.t[tri].mat)) okseq = 0;
+          if (j > 0 && (ids[j] & ~OR_TRANS) == (ids[j - 1] & ~OR_TRANS)) okseq = 0;
+        }
+        if (nr > N || ntr > T) okseq = 0;
         if (okseq) {
           validate_one(&S, P, mk(tx[0], tx[1], tx[2]), R, k, ids, &tmp, 1);
           if (tmp.valid) {
             if (nvalid < cap) {
               int32_t* kk = &keys_out[(size_t)nvalid * stride];
               kk[0] = r; kk[1] = k;
-              for (int j = 0; j < N; ++j) kk[2 + j] = j < k ? ids[j] : -1;
+              for (int j = 0; j < W; ++j) kk[2 + j] = j < k ? ids[j] : -1;
               paths_out[nvalid] = tmp;
             }
             nvalid++;
@@ -764,8 +1083,8 @@ int64_t or_exhaustive(const float* tris, const int32_t* tri_mat, int32_t ntri, c
         /* next sequence (odometer) */
         int j = k - 1;
         while (j >= 0) {
-          if (++ids[j] < ntri) break;
-          ids[j] = 0;
+          if (++c[j] < ch) break;
+          c[j] = 0;
           --j;
         }
         if (j < 0) break;

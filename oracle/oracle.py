@@ -67,7 +67,14 @@ class _Params(C.Structure):
                 ("rx_radius_scale", C.c_double), ("t_min", C.c_double),
                 ("escape_len", C.c_double), ("eps_occ", C.c_double), ("edge_eps", C.c_double),
                 ("val_eps", C.c_double), ("pol", C.c_double * 3), ("max_refl", C.c_int32),
-                ("nthreads", C.c_int32)]
+                ("nthreads", C.c_int32), ("trans_db", C.c_void_p), ("max_trans", C.c_int32),
+                ("pad_", C.c_int32)]
+
+
+TRANS = 0x40000000   # interaction id flag: transmission through the triangle
+MAX_SEG = MAX_REFL + 1
+INST_DTYPE = np.dtype([("root", np.int32), ("start", np.int32), ("nseg", np.int32), ("flags", np.uint32),
+                       ("hit", np.int32, (MAX_SEG,)), ("t", np.float64, (MAX_SEG,))], align=True)
 
 
 PATH_DTYPE = np.dtype([("valid", np.int32), ("flags", np.uint32), ("len_m", np.float64),
@@ -103,6 +110,12 @@ def lib():
         _lib.or_free.argtypes = [C.c_void_p]
         _lib.or_path_size.restype = C.c_int32
         assert _lib.or_path_size() == PATH_DTYPE.itemsize, "path record layout mismatch"
+        _lib.or_trace_tree.argtypes = [f32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32, f32,
+                                       C.c_int32, P(_Params), P(C.c_void_p), P(C.c_int64),
+                                       P(P(C.c_int32)), P(C.c_int64)]
+        _lib.or_trace_tree.restype = C.c_int
+        _lib.or_inst_size.restype = C.c_int32
+        assert _lib.or_inst_size() == INST_DTYPE.itemsize, "instance record layout mismatch"
     return _lib
 
 
@@ -123,6 +136,17 @@ class OracleParams:
     val_eps: float = 1e-9
     pol: tuple = (0.0, 0.0, 1.0)
     nthreads: int = 0
+    max_trans: int = 0          # transmissions per path (Table II penetration)
+    trans_db: tuple = ()        # per material penetration loss [dB], < 0 opaque
+
+    @property
+    def width(self) -> int:
+        """Most interactions of a path (reflections + transmissions): key width."""
+        return self.max_refl + (self.max_trans if self.transmission else 0)
+
+    @property
+    def transmission(self) -> bool:
+        return self.max_trans > 0 and any(x >= 0 for x in self.trans_db)
 
     def c(self) -> _Params:
         p = _Params()
@@ -139,6 +163,13 @@ class OracleParams:
             p.pol[i] = self.pol[i]
         p.max_refl = self.max_refl
         p.nthreads = self.nthreads
+        if self.transmission:
+            self._trans = np.ascontiguousarray(self.trans_db, np.float64)
+            p.trans_db = self._trans.ctypes.data
+            p.max_trans = self.max_trans
+        else:
+            p.trans_db = None
+            p.max_trans = 0
         return p
 
 
@@ -170,7 +201,10 @@ def transform(tris: np.ndarray, tri_obj: np.ndarray, xf: np.ndarray) -> np.ndarr
 def trace(world_tris, tri_mat, materials, tx, rays, rx, prm: OracleParams, seg_od=False):
     """Step 1-2 over every ray. Returns a dict with per-ray hit ids per segment
     (-1 escaped, -2 not reached), hit distances, segment counts, flag bits and
-    the captures (ray, segment, receiver), sorted."""
+    the captures (ray, segment, receiver), sorted. With transmission the rows
+    are ray instances (the primaries, then their children, see trace_tree)."""
+    if prm.transmission:
+        return trace_tree(world_tris, tri_mat, materials, tx, rays, rx, prm)
     wt = _f32(world_tris).reshape(-1, 9)
     mats = _f32(materials).reshape(-1, 3)
     rays = _f32(rays).reshape(-1, 3)
@@ -201,6 +235,39 @@ def trace(world_tris, tri_mat, materials, tx, rays, rx, prm: OracleParams, seg_o
     return out
 
 
+def trace_tree(world_tris, tri_mat, materials, tx, rays, rx, prm: OracleParams):
+    """Steps 1-2 with transmission (Sec. III "Reflected and transmitted
+    rays"): a ray hitting a transmitting material both reflects and spawns a
+    child continuing straight through, up to max_refl reflections and
+    max_trans transmissions per path. Rows: the n primary instances (row i =
+    ray i) then the children by (root ray, spawn order); hit ids carry TRANS
+    on transmissions and include each child's inherited prefix. Adds "root"
+    (sampled direction of each row) and "start" (first segment it traced)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rays = _f32(rays).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    n, W = rays.shape[0], prm.width + 1
+    iptr, ni = C.c_void_p(), C.c_int64(0)
+    cptr, ncand = C.POINTER(C.c_int32)(), C.c_int64(0)
+    prm_c = prm.c()
+    rc = lib().or_trace_tree(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), wt.shape[0],
+                             _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                             _p(rays, C.c_float), n, _p(rx, C.c_float), rx.shape[0], C.byref(prm_c),
+                             C.byref(iptr), C.byref(ni), C.byref(cptr), C.byref(ncand))
+    k, m = int(ni.value), int(ncand.value)
+    buf = (C.c_char * (max(k, 1) * INST_DTYPE.itemsize)).from_address(iptr.value)
+    inst = np.frombuffer(bytes(buf), INST_DTYPE, count=k).copy() if k else np.zeros(0, INST_DTYPE)
+    cands = np.ctypeslib.as_array(cptr, shape=(max(m, 1) * 3,))[:m * 3].reshape(m, 3).copy()
+    lib().or_free(iptr)
+    lib().or_free(C.cast(cptr, C.c_void_p))
+    if rc != 0:
+        raise RuntimeError(f"or_trace_tree failed: {rc}")
+    return {"hit_id": inst["hit"][:, :W].copy(), "hit_t": inst["t"][:, :W].copy(), "nseg": inst["nseg"].copy(),
+            "flags": inst["flags"].copy(), "cands": cands, "root": inst["root"].copy(),
+            "start": inst["start"].copy()}
+
+
 def candidate_keys(cands: np.ndarray, hit_id: np.ndarray, max_refl: int) -> np.ndarray:
     """Key rows (rx, depth, tri ids of bounces 1..depth, -1 padding) of each capture."""
     m = cands.shape[0]
@@ -225,7 +292,7 @@ def validate(world_tris, tri_mat, materials, tx, rx, keys, prm: OracleParams) ->
     wt = _f32(world_tris).reshape(-1, 9)
     mats = _f32(materials).reshape(-1, 3)
     rx = _f32(rx).reshape(-1, 3)
-    keys = _i32(keys).reshape(-1, 2 + prm.max_refl)
+    keys = _i32(keys).reshape(-1, 2 + prm.width)
     out = np.zeros(keys.shape[0], PATH_DTYPE)
     prm_c = prm.c()
     rc = lib().or_validate(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), wt.shape[0],
@@ -242,7 +309,7 @@ def exhaustive(world_tris, tri_mat, materials, tx, rx, prm: OracleParams, cap=1 
     wt = _f32(world_tris).reshape(-1, 9)
     mats = _f32(materials).reshape(-1, 3)
     rx = _f32(rx).reshape(-1, 3)
-    stride = 2 + prm.max_refl
+    stride = 2 + prm.width
     keys = np.zeros((cap, stride), np.int32)
     paths = np.zeros(cap, PATH_DTYPE)
     prm_c = prm.c()
@@ -392,7 +459,7 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
     wt = transform(scene.tris, scene.tri_obj, scene.xf[f] if scene.nobj else np.zeros((0, 12)))
     rx = scene.rx[f]
     tr = trace(wt, scene.tri_mat, scene.materials, scene.tx, rays, rx, prm, seg_od=seg_od)
-    keys = unique_keys(candidate_keys(tr["cands"], tr["hit_id"], prm.max_refl))
+    keys = unique_keys(candidate_keys(tr["cands"], tr["hit_id"], prm.width))
     paths = validate(wt, scene.tri_mat, scene.materials, scene.tx, rx, keys, prm)
     fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)
     return FrameResult(wt, tr, keys, paths, fld, pc, pi)

@@ -667,7 +667,7 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
       CKF(dalloc(&s->q4_src, nn));
       CKF(dalloc(&s->q4_count, 1));
       CKF(dalloc(&s->q4_roots, 2));
-      if (bvh4_map_smem(nn) == 0) CKF(dalloc(&s->q4_scr, 2 * (size_t)nn));
+      if (bvh4_map_smem(nn) == 0) CKF(dalloc(&s->q4_scr, 3 * (size_t)nn));
     }
   }
   CKF(dalloc(&s->qframe, 6));

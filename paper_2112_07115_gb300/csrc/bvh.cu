@@ -887,45 +887,42 @@ __global__ void k_quantize(const float4* __restrict__ nodes, int nn, const float
 // children are its own children, an internal child replaced by that child's
 // two children. For each child slot it records the child (4-wide index,
 // leaf ~slot, or kEmpty) and where its box lives in the binary records
-// (record << 1 | side). Scratch depth[nn], index[nn]: shared memory, or the
-// global array `gscr` (2 nn ints) when that does not fit.
+// (record << 1 | side). Scratch parent[nn], depth[nn], index[nn]: shared
+// memory, or the global array `gscr` (3 nn ints) when that does not fit.
 __global__ void __launch_bounds__(1024) k_bvh4_map(const float4* __restrict__ nodes, int nn,
                                                    const int* __restrict__ roots, int4* kid4, int4* src4,
                                                    int* n4_out, int* roots4_out, int* gscr) {
   extern __shared__ int sm4[];
-  int* depth = gscr ? gscr : sm4;
+  int* par = gscr ? gscr : sm4;
+  int* depth = par + nn;
   int* idx = depth + nn;
-  __shared__ int changed, total, carry;
+  __shared__ int total, carry;
   __shared__ int wsum[32];
   int tid = threadIdx.x, nt = blockDim.x;
   auto kid = [&](int n, int side) {
     return reinterpret_cast<const int*>(nodes + 4 * (size_t)n + 3)[side];
   };
-  for (int i = tid; i < nn; i += nt) depth[i] = -1;
+  // parents from the child codes, then each node's depth by walking up to
+  // its root (no level-by-level passes); a node that does not reach one of
+  // the two roots gets no 4-wide node
+  for (int i = tid; i < nn; i += nt) par[i] = -1;
   __syncthreads();
-  if (tid < 2) {
-    int r = roots[tid];
-    if (r >= 0 && r < nn) depth[r] = 0;
-  }
-  __syncthreads();
-  for (int pass = 0; pass < 256; ++pass) {
-    if (tid == 0) changed = 0;
-    __syncthreads();
-    for (int i = tid; i < nn; i += nt) {
-      int di = depth[i];
-      if (di < 0) continue;
-      for (int side = 0; side < 2; ++side) {
-        int c = kid(i, side);
-        if (c >= 0 && c < nn && depth[c] < 0) {
-          depth[c] = di + 1;
-          changed = 1;
-        }
-      }
+  for (int i = tid; i < nn; i += nt)
+    for (int side = 0; side < 2; ++side) {
+      int c = kid(i, side);
+      if (c >= 0 && c < nn) par[c] = i;
     }
-    __syncthreads();
-    if (!changed) break;
-    __syncthreads();
+  __syncthreads();
+  const int r0 = roots[0], r1 = roots[1];
+  for (int i = tid; i < nn; i += nt) {
+    int d = 0, top = i;
+    while (par[top] >= 0 && d < 4096) {
+      top = par[top];
+      ++d;
+    }
+    depth[i] = (par[top] < 0 && (top == r0 || top == r1)) ? d : -1;
   }
+  __syncthreads();
   // exclusive prefix count of even-depth nodes, one tile of nt nodes at a
   // time: warp scans, a scan of the warp sums, and the running carry
   if (tid == 0) carry = 0;

@@ -121,9 +121,9 @@ void launch_quantize(const float4* d_nodes, int nn, const float* d_root_box, int
 // to 4-wide nodes once per topology (one CTA, nn <= 8192), then encode the
 // child boxes every frame. n4 and the 4-wide roots stay on the device.
 // Shared memory of the 4-wide mapping of nn binary internal nodes, or 0 when
-// it needs the global scratch (2 nn ints) instead.
+// it needs the global scratch (3 nn ints) instead.
 inline size_t bvh4_map_smem(int nn) {
-  size_t b = 2 * (size_t)(nn > 0 ? nn : 1) * sizeof(int);
+  size_t b = 3 * (size_t)(nn > 0 ? nn : 1) * sizeof(int);
   return b <= 200 * 1024 ? b : 0;
 }
 cudaError_t launch_bvh4_map(const float4* d_nodes, int nn, const int* d_roots, int4* d_kid4, int4* d_src4,

@@ -423,3 +423,112 @@ def test_sticky_retention_keeps_true_paths(oracle_mod):
         kept_total += len(kept)
         prev_valid = set(valid)
     assert kept_total > 0
+
+
+# ---------------------------------------------------------------- transmission
+
+def _walls(xs, tx=(0.0, 3.0, 7.0), rx=(100.0, 3.0, 7.0)):
+    """Square walls (100 m x 100 m, two triangles each) in the planes x = xs[k],
+    wall k of material k; the Tx-Rx line crosses them off their diagonals."""
+    tris, mats = [], []
+    for k, x in enumerate(xs):
+        tris += scenes._quad((x, -50.0, -50.0), (x, 50.0, -50.0), (x, 50.0, 50.0), (x, -50.0, 50.0))
+        mats += [k, k]
+    materials = np.array([[5.31, 0.0326, 0.0]] * len(xs), np.float32)
+    return scenes._static_scene("walls", tris, mats, tx, rx, materials=materials)
+
+
+def _table2():
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as fh:
+        rows = json.load(fh)["table2_materials"]["rows"]
+    return {r["material"]: r for r in rows}
+
+
+def _los_amp(freq, L, loss_db=0.0):
+    lam = C0 / freq
+    k = 2 * np.pi * freq / C0
+    return lam / (4 * np.pi * L) * np.exp(-1j * k * L) * 10.0 ** (-loss_db / 20.0)
+
+
+def test_transmission_table2_wall_friis_minus_loss(oracle_mod):
+    """Table II's indoor wall (20 dB) between Tx and Rx: the only path is the
+    direct one through the wall, a = Friis amplitude x 10^(-20/20); the
+    sampled sphere (the paper's 2000 rays) finds exactly that path."""
+    O = oracle_mod
+    loss = _table2()["wall (indoor)"]["penetration_loss_db"]
+    s = _walls([50.0])
+    prm = O.OracleParams(freq_hz=30e9, n_rays=2000, max_refl=2, max_trans=2, trans_db=(loss,))
+    ek, ep = O.exhaustive(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    assert ek.shape[0] == 1 and ek[0, 1] == 1 and (ek[0, 2] & O.TRANS)
+    a = complex(ep[0]["amp_re"], ep[0]["amp_im"])
+    assert abs(ep[0]["len_m"] - 100.0) <= 1e-12
+    assert abs(a - _los_amp(30e9, 100.0, loss)) <= 1e-12 * abs(a)
+    res = O.frame(s, 0, scenes.fibonacci_sphere(2000), prm)
+    assert {tuple(k) for k, p in zip(res.keys.tolist(), res.paths) if p["valid"]} == {tuple(ek[0])}
+    # received power: Friis minus the penetration loss
+    friis = 10 * np.log10(prm.tx_power_w * (C0 / 30e9 / (4 * np.pi * 100.0)) ** 2) + 30
+    assert abs(res.p_coh_dbm[0] - (friis - loss)) <= 1e-9
+
+
+def test_transmission_losses_add_and_limits(oracle_mod):
+    """Wall (20 dB) then glass (5 dB): one path through both at Friis - 25 dB;
+    with one transmission allowed, or with the glass opaque, no path."""
+    O = oracle_mod
+    t2 = _table2()
+    lw, lg = t2["wall (indoor)"]["penetration_loss_db"], t2["glass (indoor)"]["penetration_loss_db"]
+    s = _walls([30.0, 60.0])
+    wt = s.tris.reshape(-1, 9)
+    prm = O.OracleParams(freq_hz=30e9, max_refl=1, max_trans=2, trans_db=(lw, lg))
+    ek, ep = O.exhaustive(wt, s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    assert ek.shape[0] == 1 and ek[0, 1] == 2 and (ek[0, 2] & O.TRANS) and (ek[0, 3] & O.TRANS)
+    # the first crossing is the 30 m wall (triangles 0/1), then the glass (2/3)
+    assert (ek[0, 2] & ~O.TRANS) in (0, 1) and (ek[0, 3] & ~O.TRANS) in (2, 3)
+    a = complex(ep[0]["amp_re"], ep[0]["amp_im"])
+    assert abs(a - _los_amp(30e9, 100.0, lw + lg)) <= 1e-12 * abs(a)
+    p1 = O.OracleParams(freq_hz=30e9, max_refl=1, max_trans=1, trans_db=(lw, lg))
+    assert O.exhaustive(wt, s.tri_mat, s.materials, s.tx, s.rx[0], p1)[0].shape[0] == 0
+    p2 = O.OracleParams(freq_hz=30e9, max_refl=1, max_trans=2, trans_db=(lw, -1.0))
+    assert O.exhaustive(wt, s.tri_mat, s.materials, s.tx, s.rx[0], p2)[0].shape[0] == 0
+    # the same key with the glass reversed in order is not a path
+    bad = ek.copy()
+    bad[0, 2], bad[0, 3] = ek[0, 3], ek[0, 2]
+    assert not O.validate(wt, s.tri_mat, s.materials, s.tx, s.rx[0], bad, prm)["valid"][0]
+
+
+def test_transmission_zero_loss_is_free_space(oracle_mod):
+    """A 0 dB wall changes nothing but the path's interaction list: the
+    amplitude equals the free-space line of sight."""
+    O = oracle_mod
+    s = _walls([40.0])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=1, max_trans=1, trans_db=(0.0,))
+    ek, ep = O.exhaustive(s.tris.reshape(-1, 9), s.tri_mat, s.materials, s.tx, s.rx[0], prm)
+    f = scenes.free_space(tx=tuple(s.tx), rx=tuple(map(tuple, s.rx[0])))
+    fk, fp = O.exhaustive(np.zeros((0, 9), np.float32), f.tri_mat, f.materials, f.tx, f.rx[0],
+                          O.OracleParams(freq_hz=28e9, max_refl=1))
+    assert ek.shape[0] == 1 and fk.shape[0] == 1
+    a, b = complex(ep[0]["amp_re"], ep[0]["amp_im"]), complex(fp[0]["amp_re"], fp[0]["amp_im"])
+    assert abs(a - b) <= 1e-13 * abs(b)
+
+
+@pytest.mark.parametrize("seed", [0, 2, 5])
+def test_transmission_sbr_subset_of_exhaustive(oracle_mod, seed):
+    """With transmitting materials (ground 10 dB, the rest 3 dB), every path
+    the ray tree finds is a valid exhaustive path, and with many rays the two
+    sets coincide."""
+    O = oracle_mod
+    s = scenes.random_tiny(seed, ntri=6, nobj=1, nrx=2)
+    mats = np.vstack([s.materials, s.materials[:1]])
+    tm = s.tri_mat.copy()
+    tm[2:] = mats.shape[0] - 1
+    s.materials, s.tri_mat = mats, tm
+    tdb = (10.0,) + (-1.0,) * (mats.shape[0] - 2) + (3.0,)
+    for n_rays in (3000, 200_000):
+        prm = O.OracleParams(max_refl=1, max_trans=1, n_rays=n_rays, trans_db=tdb)
+        res = O.frame(s, 1, scenes.fibonacci_sphere(n_rays), prm)
+        ek, _ = O.exhaustive(res.world_tris, s.tri_mat, s.materials, s.tx, s.rx[1], prm)
+        ex = {tuple(k) for k in ek.tolist()}
+        sbr = {tuple(k) for k, p in zip(res.keys.tolist(), res.paths) if p["valid"]}
+        assert sbr <= ex
+        assert any(any(v >= 0 and (v & O.TRANS) for v in k[2:]) for k in ex)
+        if n_rays > 100_000:
+            assert sbr == ex
