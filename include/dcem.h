@@ -79,6 +79,9 @@ typedef enum { DCEM_PTR_HOST = 0, DCEM_PTR_DEVICE = 1 } dcem_ptr_kind;
 #define DCEM_PATH_POL_DEGENERATE 1u /* polarisation reference parallel to a path end */
 #define DCEM_PATH_STICKY 2u         /* DCEM_MODE_STICKY: kept from the previous frame
                                        (re-validated), no ray captured it this frame */
+/* dcem_path.tri[j] flag: interaction j is a transmission through the
+ * triangle (straight through, penetration loss), not a reflection. */
+#define DCEM_TRI_TRANSMIT 0x40000000
 
 typedef struct dcem_scene dcem_scene;
 
@@ -165,6 +168,7 @@ typedef struct {
                                   one replayed CUDA graph                        */
   int32_t paths_sticky;        /* DCEM_MODE_STICKY: valid paths that only the
                                   path cache kept (no ray captured them)         */
+  int32_t child_rays;          /* transmission: child rays spawned this frame   */
 } dcem_stats;
 
 typedef struct {
@@ -266,6 +270,19 @@ int dcem_trace_links(dcem_scene* s, const float* tx, int32_t ntx, const float* r
  * positions) instead of refitting it. ratio <= 0: refit only. Default 1.25.
  * Results never depend on the tree shape. Errors: DCEM_ERR_ARG. */
 int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
+
+/* Transmission (Sec. III "Reflected and transmitted rays"; Table II
+ * penetration losses). loss_db[m] >= 0 makes material m transmitting: a ray
+ * hitting it both reflects and continues straight through (thin slab, no
+ * refraction), and a path's field is scaled by 10^(-loss/20) at each such
+ * transmission; loss_db[m] < 0: opaque (the default). max_trans: most
+ * transmissions per path (0 = off); max_refl + max_trans <= DCEM_MAX_REFL
+ * at trace time. A transmission appears in dcem_path.tri as the id with
+ * DCEM_TRI_TRANSMIT set; depth counts reflections and transmissions. While
+ * max_trans > 0 every frame is a full trace (COHERENT and STICKY frames are
+ * traced in full). host loss_db, nmat entries (the scene's material count).
+ * Errors: DCEM_ERR_ARG, DCEM_ERR_NONFINITE. */
+int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nmat, int32_t max_trans);
 
 /* Closest-hit kernel configuration. Results never depend on it (closest hit
  * and lowest-id ties are decided by the triangle test alone):
@@ -372,8 +389,9 @@ int dcem_scene_get_world_tris(dcem_scene* s, float* out);
  *           leaf code as in `child`, or INT32_MIN when the tree is empty) */
 int dcem_scene_get_bvh(dcem_scene* s, int32_t* child, float* bounds, int32_t* roots);
 
-/* Per-ray log of the last traced frame: hit_id n_rays*(max_refl+1) int32
- * (triangle id, -1 escaped, -2 not reached), hit_t same shape (FP32 ray
+/* Per-ray log of the last traced frame: hit_id n_rays*(max_refl+max_trans+1)
+ * int32 (triangle id, -1 escaped, -2 not reached; with transmission, the
+ * primary rays, which reflect at every hit), hit_t same shape (FP32 ray
  * parameter; +inf when escaped), nseg n_rays. Any pointer may be NULL. */
 int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t* nseg);
 

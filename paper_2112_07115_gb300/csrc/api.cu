@@ -276,7 +276,13 @@ struct dcem_scene {
   std::vector<int> set_rays_h;   // rays per set
   float4* txs = nullptr;         // per set: transmitter xyz and capture spacing (device)
   float4* txs_h = nullptr;       // the same, pinned host staging copied in every frame
-  int logW = 0;
+  int logW = 0;                  // segments per slot in the log
+  int LS = 0;                    // log stride: R + child_cap
+  int max_trans = 0;             // transmission: per path (0 = off)
+  int child_cap = 0;             // child-ray slots after the R primaries
+  int* inst = nullptr;           // per child slot: reflections | transmissions << 4 | set << 8
+  int* inst_root = nullptr;      // per child slot: its primary ray's slot
+  std::vector<float4> mats_h;    // host copy of the material table
   float4* log_o = nullptr;
   float4* log_d = nullptr;
   int* log_id = nullptr;
@@ -358,6 +364,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
   dfree(s->scr.v1); dfree(s->scr.hist); dfree(s->scr.keys); dfree(s->ctr); dfree(s->uctr);
   if (s->ctr_h) cudaFreeHost(s->ctr_h);
+  dfree(s->inst); dfree(s->inst_root);
   dfree(s->rays); dfree(s->ray_perm); dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems); dfree(s->nseg); dfree(s->restart);
   dfree(s->queue); dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->prev_ncand); dfree(s->hkey);
   dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
@@ -459,15 +466,28 @@ int alloc_build_scratch(dcem_scene* s, int n) {
   return DCEM_OK;
 }
 
-int ensure_log(dcem_scene* s, int W) {
-  if (s->logW >= W && s->log_o) return DCEM_OK;
+// The segment log for W segments per slot over the R primary rays and
+// child_cap transmission children (their restart points, segment counts and
+// instance words too).
+int ensure_log(dcem_scene* s, int W, int child_cap) {
+  if (s->logW >= W && s->log_o && s->child_cap == child_cap) return DCEM_OK;
+  const int LS = s->R + child_cap;
   dfree(s->log_o); dfree(s->log_d); dfree(s->log_id); dfree(s->capitems);
-  size_t n = (size_t)W * (size_t)(s->R > 0 ? s->R : 1);
+  size_t n = (size_t)W * (size_t)(LS > 0 ? LS : 1);
   CK(dalloc(&s->log_o, n));
   CK(dalloc(&s->log_d, n));
   CK(dalloc(&s->log_id, n));
   CK(dalloc(&s->capitems, n));
+  if (child_cap != s->child_cap) {
+    dfree(s->nseg); dfree(s->restart); dfree(s->inst); dfree(s->inst_root);
+    CK(dalloc(&s->nseg, LS > 0 ? LS : 1));
+    CK(dalloc(&s->restart, LS > 0 ? LS : 1));
+    if (child_cap) CK(dalloc(&s->inst, child_cap));
+    if (child_cap) CK(dalloc(&s->inst_root, child_cap));
+  }
   s->logW = W;
+  s->child_cap = child_cap;
+  s->LS = LS;
   s->cache_valid = false;
   return DCEM_OK;
 }
@@ -716,7 +736,9 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   if (s->ns) CKF(cudaMemcpyAsync(sel_s_d, sel_s.data(), sizeof(int) * s->ns, cudaMemcpyHostToDevice, st));
   if (s->nd) CKF(cudaMemcpyAsync(s->sel_d, sel_d.data(), sizeof(int) * s->nd, cudaMemcpyHostToDevice, st));
   std::vector<float4> mh(nmat > 0 ? nmat : 1);
-  for (int m = 0; m < nmat; ++m) mh[m] = make_float4(mats[m].eps_r, mats[m].sigma, mats[m].pec ? 1.0f : 0.0f, 0.0f);
+  // .w: penetration loss [dB] of a transmitting material, < 0 opaque (default)
+  for (int m = 0; m < nmat; ++m) mh[m] = make_float4(mats[m].eps_r, mats[m].sigma, mats[m].pec ? 1.0f : 0.0f, -1.0f);
+  s->mats_h = mh;
   if (nmat) CKF(cudaMemcpyAsync(s->mats, mh.data(), sizeof(float4) * nmat, cudaMemcpyHostToDevice, st));
   // static tree (built once)
   launch_tri_boxes(v9, sel_s_d, s->ns, s->prim, st);
@@ -794,6 +816,10 @@ int dcem_scene_set_ray_sets(dcem_scene* s, const float* dirs, const int32_t* n_r
   s->txs_h = nullptr;
   s->logW = 0;
   s->R = n;
+  s->LS = n;
+  s->child_cap = 0;
+  dfree(s->inst);
+  dfree(s->inst_root);
   s->rays_set = false;
   s->nsets = ntx;
   s->set_rays_h.assign(n_rays, n_rays + ntx);
@@ -958,6 +984,19 @@ int dcem_scene_autotune(dcem_scene* s, const float* tx, int32_t ntx, const float
   return DCEM_OK;
 }
 
+int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nmat, int32_t max_trans) {
+  if (!s || max_trans < 0 || max_trans > DCEM_MAX_REFL) return DCEM_ERR_ARG;
+  if (nmat != s->nmat || (nmat > 0 && !loss_db)) return DCEM_ERR_ARG;
+  for (int m = 0; m < nmat; ++m)
+    if (!std::isfinite(loss_db[m])) return DCEM_ERR_NONFINITE;
+  CK(cudaStreamSynchronize(s->st));
+  for (int m = 0; m < nmat; ++m) s->mats_h[m].w = loss_db[m] >= 0.0f ? loss_db[m] : -1.0f;
+  if (nmat) CK(cudaMemcpy(s->mats, s->mats_h.data(), sizeof(float4) * nmat, cudaMemcpyHostToDevice));
+  s->max_trans = max_trans;
+  s->cache_valid = false;
+  return DCEM_OK;
+}
+
 int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on) {
   if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
   s->use_graphs = on != 0;
@@ -1006,6 +1045,13 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   a.txs = s->txs;
   a.nsets = s->nsets;
   a.R = s->R;
+  a.LS = s->LS;
+  a.mats = s->mats;
+  a.max_trans = s->max_trans;
+  a.pass = 0;
+  a.child_cap = s->child_cap;
+  a.inst = s->inst;
+  a.inst_root = s->inst_root;
   a.N = N;
   a.tmin = p->t_min;
   a.escape = p->escape_len;
@@ -1102,7 +1148,10 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   }
 
   PathArgs& q = P.q;
-  q.R = s->R;
+  q.R = s->LS;
+  q.max_trans = s->max_trans;
+  q.R0 = s->R;
+  q.inst_root = s->inst_root;
   q.log_id = s->log_id;
   q.cand = s->cand[nxt];
   q.cand_cap = s->cand_cap;
@@ -1210,6 +1259,12 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   }
   if (tk) CK(rec(P.ev[2], st, cap));
   if (P.R > 0) CK(launch_trace(a, sms, st));
+  // transmission: pass p traces the children pass p - 1 spawned
+  for (int p = 1; P.R > 0 && p <= a.max_trans; ++p) {
+    TraceArgs ap = a;
+    ap.pass = p;
+    CK(launch_trace(ap, sms, st));
+  }
   if (tk) CK(rec(P.ev[3], st, cap));
   if (P.R > 0) CK(launch_capture(a, sms, st));
   if (tm) CK(rec(P.ev[4], st, cap));
@@ -1272,8 +1327,8 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   make_plan(s, nrx, p, coherent, out, P);
   s->last_use_q = P.use_q;
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
-  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 : 0) + 5 + (nrx > 0 ? 1 : 0) + (P.use_q ? 1 : 0) +
-                 (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0);
+  s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
+                 (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -1327,7 +1382,7 @@ static int frame_begin(dcem_scene* s, const float* tx, int32_t ntx, const float*
   if (rx_ptr_kind != DCEM_PTR_HOST && rx_ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->ptr_kind != DCEM_PTR_HOST && out->ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (out->max_paths < 0 || (out->max_paths > 0 && !out->paths)) return DCEM_ERR_ARG;
-  if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
+  if (p->max_refl < 0 || p->max_refl + s->max_trans > DCEM_MAX_REFL) return DCEM_ERR_ARG;
   if (p->mode != DCEM_MODE_FULL && p->mode != DCEM_MODE_COHERENT && p->mode != DCEM_MODE_STICKY)
     return DCEM_ERR_ARG;
   if (p->timing < 0 || p->timing > 2) return DCEM_ERR_ARG;
@@ -1347,7 +1402,11 @@ static int frame_begin(dcem_scene* s, const float* tx, int32_t ntx, const float*
   out->n_paths = 0;
 
   int rc;
-  if ((rc = ensure_log(s, p->max_refl + 1)) != DCEM_OK) return rc;
+  // transmission: W segments per slot and child slots after the primaries
+  const int W = p->max_refl + s->max_trans + 1;
+  const int cc = s->max_trans > 0 ? std::max(s->child_cap, std::max(s->R, 1024)) : 0;
+  if ((long long)s->R + cc > (1ll << 27)) return DCEM_ERR_CAPACITY;
+  if ((rc = ensure_log(s, W, cc)) != DCEM_OK) return rc;
   unsigned want_c = s->cand_cap ? s->cand_cap : (unsigned)std::max(65536, s->R / 8);
   unsigned want_u = s->ucap ? s->ucap : std::min(want_c, 1u << 18);
   if ((rc = ensure_paths(s, want_c, want_u)) != DCEM_OK) return rc;
@@ -1363,7 +1422,7 @@ static int frame_begin(dcem_scene* s, const float* tx, int32_t ntx, const float*
   *coherent = p->mode != DCEM_MODE_FULL && s->cache_valid && same_traversal(*p, s->cparams) &&
                   nrx == s->cnrx && s->ctx.size() == 3 * (size_t)ntx &&
                   std::memcmp(tx, s->ctx.data(), sizeof(float) * 3 * ntx) == 0 &&
-                  s->logW == p->max_refl + 1;
+                  s->logW == p->max_refl + 1 && s->max_trans == 0;
   return DCEM_OK;
 }
 
@@ -1385,7 +1444,8 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
     }
     c = s->ctr_h;
     unsigned err = c[0].err | c[1].err;
-    unsigned grow = err & (ERR_CAND_OVERFLOW | ERR_UNIQUE_OVERFLOW | ERR_HASH_FULL | ERR_BUCKET_OVERFLOW);
+    unsigned grow = err & (ERR_CAND_OVERFLOW | ERR_UNIQUE_OVERFLOW | ERR_HASH_FULL | ERR_BUCKET_OVERFLOW |
+                           ERR_SPAWN_OVERFLOW);
     if (!grow) break;
     // internal capacity exceeded: grow and retrace the frame from scratch
     CK(cudaStreamSynchronize(st));
@@ -1396,6 +1456,13 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
     if ((rc = ensure_paths(s, nc, nu)) != DCEM_OK) return rc;
     CK(cudaMemsetAsync(s->hkey, 0, sizeof(unsigned long long) * s->hcap, st));
     CK(cudaMemsetAsync(s->hrep, 0xff, sizeof(unsigned long long) * s->hcap, st));
+    if (err & ERR_SPAWN_OVERFLOW) {  // more transmission children than slots
+      unsigned long long sp = 0;
+      for (int k = 0; k <= kMaxRefl; ++k) sp += c[0].n_spawn[k];
+      long long cc = std::max<long long>(2ll * s->child_cap, (long long)(sp * 5 / 4) + 1024);
+      if ((long long)s->R + cc > (1ll << 27)) return DCEM_ERR_CAPACITY;
+      if ((rc = ensure_log(s, s->logW, (int)cc)) != DCEM_OK) return rc;
+    }
     if (err & ERR_BUCKET_OVERFLOW) {
       int nb = s->bucket_cap * 2;
       if (nb > 8192) {
@@ -1427,6 +1494,11 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
   S.trace_kernel = s->last_use_q;
   S.graph_replayed = s->graph_replayed;
   S.paths_sticky = (int32_t)c[0].n_sticky_valid;
+  {
+    unsigned long long sp = 0;
+    for (int k = 0; k <= kMaxRefl; ++k) sp += c[0].n_spawn[k];
+    S.child_rays = (int32_t)std::min<unsigned long long>(sp, 0x7fffffffull);
+  }
   S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;
@@ -1858,22 +1930,23 @@ int dcem_scene_get_bvh(dcem_scene* s, int32_t* child, float* bounds, int32_t* ro
 int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t* nseg) {
   if (!s) return DCEM_ERR_ARG;
   if (!s->rays_set || s->logW == 0) return DCEM_ERR_STATE;
-  int R = s->R, W = s->cparams.max_refl + 1;
+  // the last frame's segments per ray (the log may hold more rows)
+  int R = s->R, W = std::min(s->logW, s->cparams.max_refl + s->max_trans + 1), LS = s->LS;
   CK(cudaStreamSynchronize(s->st));
-  std::vector<int> ns(R > 0 ? R : 1), ids((size_t)W * (R > 0 ? R : 1));
-  std::vector<float4> ld((size_t)W * (R > 0 ? R : 1));
+  std::vector<int> ns(R > 0 ? R : 1), ids((size_t)W * (LS > 0 ? LS : 1));
+  std::vector<float4> ld((size_t)W * (LS > 0 ? LS : 1));
   if (R) {
     CK(cudaMemcpy(ns.data(), s->nseg, sizeof(int) * R, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(ids.data(), s->log_id, sizeof(int) * (size_t)W * R, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(ld.data(), s->log_d, sizeof(float4) * (size_t)W * R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ids.data(), s->log_id, sizeof(int) * (size_t)W * LS, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ld.data(), s->log_d, sizeof(float4) * (size_t)W * LS, cudaMemcpyDeviceToHost));
   }
   for (int i = 0; i < R; ++i) {  // slot i holds the caller's ray ray_perm[i]
     size_t o = (size_t)s->ray_perm_h[i];
     if (nseg) nseg[o] = ns[i];
     for (int b = 0; b < W; ++b) {
       bool live = b < ns[i];
-      if (hit_id) hit_id[o * W + b] = live ? ids[(size_t)b * R + i] : -2;
-      if (hit_t) hit_t[o * W + b] = live ? ld[(size_t)b * R + i].w : NAN;
+      if (hit_id) hit_id[o * W + b] = live ? ids[(size_t)b * LS + i] : -2;
+      if (hit_t) hit_t[o * W + b] = live ? ld[(size_t)b * LS + i].w : NAN;
     }
   }
   return DCEM_OK;

@@ -20,6 +20,7 @@ constexpr int kSmallBuild = 16384;      // largest tree built by the one-CTA bui
 constexpr int kMaxRaySets = 4096;       // transmitters (ray sets) per scene
 constexpr int kMaxLinks = 1 << 24;      // transmitter-receiver pairs per frame
 constexpr int kMaxBatch = 1024;         // scenes per batch
+constexpr int kTransBit = 0x40000000;   // interaction id flag: transmission (DCEM_TRI_TRANSMIT)
 constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
 
 // device error bits (DevCounters::err)
@@ -32,6 +33,7 @@ enum : unsigned {
   ERR_STACK = 32u,
   ERR_HASH_FULL = 64u,
   ERR_QUEUE_OVERFLOW = 128u,
+  ERR_SPAWN_OVERFLOW = 256u,       // transmission: more child rays than slots
 };
 
 struct DevCounters {
@@ -58,6 +60,8 @@ struct DevCounters {
   unsigned long long tri_tests;    // triangles tested by closest-hit traversals
   unsigned int n_sticky_valid;     // sticky mode: valid paths that only the cache kept
   unsigned int n_sticky_next;      // sticky mode: valid paths kept for the next frame
+  unsigned int n_spawn[kMaxRefl + 1];    // transmission: child rays spawned by trace pass p
+  unsigned int work_pass[kMaxRefl + 1];  // ... work counters of passes p >= 1
 };
 
 // Sticky mode: a valid path kept for the next frame (link, depth, sequence).

@@ -74,7 +74,10 @@ __global__ void k_dedupe_insert(PathArgs a) {
       continue;
     }
     a.cand_slot[i] = (int)slot;
-    atomicMin(&a.hrep[slot], ((unsigned long long)(unsigned)c.ray << 32) | i);
+    // representative: the capture of the lowest primary ray (a transmission
+    // child counts as its primary; one primary reaches a key at most once)
+    int root = c.ray < a.R0 ? c.ray : a.inst_root[c.ray - a.R0];
+    atomicMin(&a.hrep[slot], ((unsigned long long)(unsigned)root << 32) | i);
   }
 }
 
@@ -314,6 +317,7 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
       // frame has it
       if (rxi >= a.nrx) rec.key = path_key_of(a, ray, rxi % a.nrx, k);
       for (int j = 0; j < kMaxRefl; ++j) ids[j] = j < k ? a.log_id[(size_t)j * a.R + ray] : -1;
+      if (ray >= a.R0) ray = a.inst_root[ray - a.R0];  // reported as its primary ray
     } else {  // sticky mode: a kept path that no capture of this frame has
       const StickyKey& sk = a.sticky_prev[~ci];
       k = sk.depth;
@@ -339,37 +343,72 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
     float4 rxv = a.rx[rxi % a.nrx], txv = a.txs[rxi / a.nrx];
     v3<T> X[kMaxRefl + 2], V0[kMaxRefl], V1[kMaxRefl], V2[kMaxRefl], Nn[kMaxRefl];
     v3<T> tx = vof<T>(txv.x, txv.y, txv.z), rx = vof<T>(rxv.x, rxv.y, rxv.z);
-    // step 3: image sources I_1..I_k
-    v3<T> img[kMaxRefl + 1];
-    img[0] = tx;
-    bool ok = true;
     const T two = sc_of<T>(2.0f), one = sc_of<T>(1.0f);
+    bool ok = true;
+    // interactions: reflections, and transmissions (kTransBit) straight
+    // through a transmitting triangle; rj lists the reflections
+    int rj[kMaxRefl], m = 0;
+    bool isT[kMaxRefl];
     for (int j = 0; j < k && ok; ++j) {
-      const float4* tp = a.tris + 3 * (size_t)a.slot_of_id[ids[j]];
+      isT[j] = (ids[j] & kTransBit) != 0;
+      const float4* tp = a.tris + 3 * (size_t)a.slot_of_id[ids[j] & ~kTransBit];
       float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+      if (isT[j] && !(a.mats[__float_as_int(p1.w)].w >= 0.0f)) ok = false;
       V0[j] = vof<T>(p0.x, p0.y, p0.z);
       V1[j] = vof<T>(p1.x, p1.y, p1.z);
       V2[j] = vof<T>(p2.x, p2.y, p2.z);
       v3<T> n = vcross(V1[j] - V0[j], V2[j] - V0[j]);
-      T nn = vdot(n, n);
-      if (!pos(nn)) { ok = false; break; }
+      if (!pos(vdot(n, n))) ok = false;
       Nn[j] = n;
-      img[j + 1] = img[j] - scale(n, two * vdot(img[j] - V0[j], n) / nn);
+      if (!isT[j]) rj[m++] = j;
     }
-    // step 4: back-trace from the receiver, reflection points in their triangles
+    // step 3: image sources I_1..I_m in the planes of the reflecting triangles
+    v3<T> img[kMaxRefl + 1];
+    img[0] = tx;
+    for (int q = 0; q < m && ok; ++q) {
+      int j = rj[q];
+      T nn = vdot(Nn[j], Nn[j]);
+      img[q + 1] = img[q] - scale(Nn[j], two * vdot(img[q] - V0[j], Nn[j]) / nn);
+    }
+    // step 4: back-trace from the receiver; XR = reflection points
+    v3<T> XR[kMaxRefl + 2];
+    XR[0] = tx;
+    XR[m + 1] = rx;
+    for (int q = m; q >= 1 && ok; --q) {
+      int j = rj[q - 1];
+      v3<T> dir = img[q] - XR[q + 1];
+      T den = vdot(dir, Nn[j]);
+      if (zero(den)) { ok = false; break; }
+      T sp = vdot(V0[j] - XR[q + 1], Nn[j]) / den;
+      if (!(pos(sp) && neg(sp - one))) { ok = false; break; }
+      XR[q] = XR[q + 1] + scale(dir, sp);
+    }
+    // the interaction points in order: a transmission crosses its plane on
+    // the straight piece between the surrounding reflection points, after
+    // the previous interaction of that piece; every point inside its triangle
     X[0] = tx;
     X[k + 1] = rx;
-    for (int j = k; j >= 1 && ok; --j) {
-      v3<T> dir = img[j] - X[j + 1];
-      T den = vdot(dir, Nn[j - 1]);
-      if (zero(den)) { ok = false; break; }
-      T sp = vdot(V0[j - 1] - X[j + 1], Nn[j - 1]) / den;
-      if (!(pos(sp) && neg(sp - one))) { ok = false; break; }
-      X[j] = X[j + 1] + scale(dir, sp);
-      v3<T> v0 = V0[j - 1], v1 = V1[j - 1], v2 = V2[j - 1], n = Nn[j - 1];
-      if (neg(vdot(vcross(v1 - v0, X[j] - v0), n)) || neg(vdot(vcross(v2 - v1, X[j] - v1), n)) ||
-          neg(vdot(vcross(v0 - v2, X[j] - v2), n)))
-        ok = false;
+    {
+      int q = 0;
+      T s_prev = sc_of<T>(0.0f);
+      for (int j = 0; j < k && ok; ++j) {
+        if (!isT[j]) {
+          X[j + 1] = XR[++q];
+          s_prev = sc_of<T>(0.0f);
+        } else {
+          v3<T> A = XR[q], dir = XR[q + 1] - XR[q];
+          T den = vdot(dir, Nn[j]);
+          if (zero(den)) { ok = false; break; }
+          T sp = vdot(V0[j] - A, Nn[j]) / den;
+          if (!(pos(sp - s_prev) && neg(sp - one))) { ok = false; break; }
+          X[j + 1] = A + scale(dir, sp);
+          s_prev = sp;
+        }
+        v3<T> v0 = V0[j], v1 = V1[j], v2 = V2[j], n = Nn[j], x = X[j + 1];
+        if (neg(vdot(vcross(v1 - v0, x - v0), n)) || neg(vdot(vcross(v2 - v1, x - v1), n)) ||
+            neg(vdot(vcross(v0 - v2, x - v2), n)))
+          ok = false;
+      }
     }
     T L = sc_of<T>(0.0f);
     if (ok) {
@@ -394,7 +433,7 @@ __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
   TStack st;
   bind_stack(st, sstk, kStackTrace);
   unsigned nu = min(a.ctr->n_unique, a.ucap);
-  unsigned W = (unsigned)a.N + 1u;
+  unsigned W = (unsigned)(a.N + a.max_trans) + 1u;
   unsigned total = nu * W;
   unsigned ovf = 0;
   for (unsigned t = threadIdx.x;; t += blockDim.x) {
@@ -412,8 +451,8 @@ __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
     float3 o = f3((float)p0.x, (float)p0.y, (float)p0.z);
     float3 dvf = f3((float)dv.x, (float)dv.y, (float)dv.z);
     RayPre rp = ray_pre(o, dvf);
-    int ex0 = j >= 1 ? rec.tri[j - 1] : -1;
-    int ex1 = j < k ? rec.tri[j] : -1;
+    int ex0 = j >= 1 ? rec.tri[j - 1] & ~kTransBit : -1;
+    int ex1 = j < k ? rec.tri[j] & ~kTransBit : -1;
     if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st)) a.vstate[u] = 2;  // occluded
   }
   if (ovf) {
@@ -442,9 +481,16 @@ __global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
     cf3 E = {F(e0.x), F(e0.y), F(e0.z)};
     float wfac = (float)(-1.0 / (2.0 * M_PI * a.freq * 8.8541878128e-12));
     for (int j = 1; j <= k; ++j) {
-      int slot = a.slot_of_id[rec.tri[j - 1]];
+      int slot = a.slot_of_id[rec.tri[j - 1] & ~kTransBit];
       const float4* tp = a.tris + 3 * (size_t)slot;
       float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+      if (rec.tri[j - 1] & kTransBit) {  // penetration loss L dB: field times 10^(-L/20)
+        float g = (float)pow(10.0, -(double)a.mats[__float_as_int(p1.w)].w / 20.0);
+        E.x = E.x * g;
+        E.y = E.y * g;
+        E.z = E.z * g;
+        continue;
+      }
       float3 nh = funit(fcross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z)));
       float3 dout = fdir(X[j], X[j + 1]);
       float ct = fabsf(fdot3(din, nh));

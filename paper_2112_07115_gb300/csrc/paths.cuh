@@ -6,7 +6,7 @@
 namespace dcem {
 
 struct PathArgs {
-  int R;                          // rays (log stride)
+  int R;                          // segment-log stride (rays, plus child slots with transmission)
   const int* log_id;              // (N+1) x R hit ids
   const Cand* cand;
   unsigned cand_cap;
@@ -20,7 +20,10 @@ struct PathArgs {
   const int* ray_perm;            // ray slot -> caller's ray index
   double* vpts;                   // per distinct key: (kMaxRefl + 2) FP64 path points
   int* vstate;                    // per distinct key: 0 invalid, 1 valid so far, 2 occluded
-  int N;                          // reflections (sub-segments per path <= N + 1)
+  int N;                          // reflections (sub-segments per path <= N + max_trans + 1)
+  int max_trans;                  // transmissions per path (ids with kTransBit)
+  int R0;                         // primary rays; slots from R0 on are transmission children
+  const int* inst_root;           // per child slot: its primary ray's slot
   int* bucket;                    // links x bucket_cap distinct-key indices of valid paths
   unsigned* bucket_cnt;           // links (link = transmitter * nrx + receiver)
   int bucket_cap;                 // power of two

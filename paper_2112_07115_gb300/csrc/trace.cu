@@ -45,17 +45,41 @@ __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
 // so that short retrace queues use all SMs. Per segment b from the ray's
 // restart point (0 in a full frame) to N: closest hit, segment log, specular
 // reflection. Captures are tested by k_capture.
-template <bool kQ, bool kG = false>
+//
+// kT (transmission): a hit on a transmitting material also spawns a child
+// that continues straight through (Sec. III "Reflected and transmitted
+// rays"); the child's slot gets the parent's interaction prefix, the
+// transmission (id | kTransBit) and its start state, and the next pass
+// traces it. Pass p > 0 takes the children of pass p - 1 as its work.
+template <bool kQ, bool kG = false, bool kT = false>
 __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st,
                                            int qr0, int qr1) {
-  const int R = a.R;
-  const int nq = a.queue ? (int)min(*a.nq_dev, (unsigned)R) : R;
+  const int R = a.R, LS = a.LS;
+  int nq, slot0 = 0, spawn_base = R;
+  unsigned* work = &a.ctr->work_trace;
+  if (kT) {
+    // children of earlier passes occupy the slots from R on, pass by pass
+    for (int p = 0; p < a.pass; ++p) {
+      int n = (int)a.ctr->n_spawn[p];
+      if (p == a.pass - 1) slot0 = spawn_base;
+      spawn_base += n;
+    }
+    if (a.pass > 0) {
+      nq = min((int)a.ctr->n_spawn[a.pass - 1], max(0, R + a.child_cap - slot0));
+      work = &a.ctr->work_pass[a.pass];
+    } else {
+      nq = R;
+    }
+  } else {
+    nq = a.queue ? (int)min(*a.nq_dev, (unsigned)R) : R;
+  }
   const int lane = threadIdx.x & 31;
   const int warps = (int)((gridDim.x * blockDim.x) >> 5);
   const int width = min(32, max(1, (nq + warps - 1) / warps));
   unsigned segs = 0, nodes = 0, tris = 0, ovf = 0, maxn = 0;
   int ray = lane < width ? -1 : -2;  // -1: takes a ray next, -2: finished
   int b = 0, last = -1;
+  int nr = 0, ntr = 0, set = 0;     // transmission: reflections, transmissions, ray set
   float3 o = f3(0.0f, 0.0f, 0.0f), d = o;
   float D = 0.0f;
   for (;;) {
@@ -63,26 +87,38 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
     if (need) {
       int leader = __ffs(need) - 1;
       int base = 0;
-      if (lane == leader) base = (int)atomicAdd(&a.ctr->work_trace, (unsigned)__popc(need));
+      if (lane == leader) base = (int)atomicAdd(work, (unsigned)__popc(need));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (ray == -1) {
         int q = base + __popc(need & ((1u << lane) - 1u));
         if (q < nq) {
-          ray = a.queue ? a.queue[q] : q;
-          b = a.queue ? a.restart[ray] : 0;
+          if (kT && a.pass > 0) {
+            ray = slot0 + q;
+            b = a.restart[ray];
+            int inf = a.inst[ray - R];
+            nr = inf & 15;
+            ntr = (inf >> 4) & 15;
+            set = inf >> 8;
+          } else {
+            ray = a.queue ? a.queue[q] : q;
+            b = a.queue ? a.restart[ray] : 0;
+            nr = b;
+            ntr = 0;
+          }
           if (b == 0) {
             float4 rd = __ldg(&a.rays[ray]);
-            float4 t4 = __ldg(&a.txs[__float_as_int(rd.w)]);
+            set = __float_as_int(rd.w);
+            float4 t4 = __ldg(&a.txs[set]);
             o = f3(t4.x, t4.y, t4.z);
             d = f3(rd.x, rd.y, rd.z);
             D = 0.0f;
             last = -1;
           } else {
-            float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
+            float4 lo = a.log_o[(size_t)b * LS + ray], ld = a.log_d[(size_t)b * LS + ray];
             o = f3(lo.x, lo.y, lo.z);
             D = lo.w;
             d = f3(ld.x, ld.y, ld.z);
-            last = a.log_id[(size_t)(b - 1) * R + ray];
+            last = a.log_id[(size_t)(b - 1) * LS + ray] & ~kTransBit;
           }
         } else {
           ray = -2;
@@ -103,11 +139,31 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       tris += nt;
       maxn = max(maxn, nn);
       bool hit = slot >= 0;
-      a.log_o[(size_t)b * R + ray] = make_float4(o.x, o.y, o.z, D);
-      a.log_d[(size_t)b * R + ray] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
-      a.log_id[(size_t)b * R + ray] = hit ? id : -1;
+      a.log_o[(size_t)b * LS + ray] = make_float4(o.x, o.y, o.z, D);
+      a.log_d[(size_t)b * LS + ray] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
+      a.log_id[(size_t)b * LS + ray] = hit ? id : -1;
       item = ((unsigned)ray << 4) | (unsigned)b;
-      if (!hit || b == a.N) {
+      if (kT && hit && ntr < a.max_trans) {
+        // transmitting material: a child continues straight through
+        int m = __float_as_int(__ldg(&a.bvh.tris[3 * slot + 1]).w);
+        if (__ldg(&a.mats[m]).w >= 0.0f) {
+          unsigned c = atomicAdd(&a.ctr->n_spawn[a.pass], 1u);
+          int cs = spawn_base + (int)c;
+          if (cs < R + a.child_cap) {
+            for (int j = 0; j < b; ++j) a.log_id[(size_t)j * LS + cs] = a.log_id[(size_t)j * LS + ray];
+            a.log_id[(size_t)b * LS + cs] = id | kTransBit;
+            float3 p = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
+            a.log_o[(size_t)(b + 1) * LS + cs] = make_float4(p.x, p.y, p.z, __fadd_rn(D, t));
+            a.log_d[(size_t)(b + 1) * LS + cs] = make_float4(d.x, d.y, d.z, 0.0f);
+            a.restart[cs] = b + 1;
+            a.inst[cs - R] = nr | ((ntr + 1) << 4) | (set << 8);
+            a.inst_root[cs - R] = ray < R ? ray : a.inst_root[ray - R];
+          } else {
+            atomicOr(&a.ctr->err, ERR_SPAWN_OVERFLOW);
+          }
+        }
+      }
+      if (!hit || (kT ? nr >= a.N : b == a.N)) {
         a.nseg[ray] = b + 1;
         ray = -1;
       } else {
@@ -124,6 +180,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
         D = __fadd_rn(D, t);
         last = id;
         ++b;
+        if (kT) ++nr;
       }
     }
     unsigned logged = __ballot_sync(0xffffffffu, item != 0xffffffffu);
@@ -162,9 +219,19 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs a) {
   trace_rays<false>(a, nullptr, f, st, kEmpty, kEmpty);
 }
 
+// The same with transmission (child rays, one launch per pass).
+__global__ void __launch_bounds__(256) k_trace_t(TraceArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, a.stack_cap);
+  QFrame f{};
+  trace_rays<false, false, true>(a, nullptr, f, st, kEmpty, kEmpty);
+}
+
 // Same traversal over the 4-wide compact node copy staged in shared memory
 // (one CTA of kTraceQThreads threads per SM, the copy loaded once per CTA).
-__global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
+template <bool kT>
+__device__ __forceinline__ void trace_q_body(const TraceArgs& a) {
   extern __shared__ uint4 sq[];
   TStack st;
   bind_stack(st, reinterpret_cast<int*>(sq + 4 * a.q4_bound), a.stack_cap);
@@ -179,8 +246,11 @@ __global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) {
   f.sy = a.qframe[4];
   f.sz = a.qframe[5];
   __syncthreads();
-  trace_rays<true>(a, sq, f, st, qr0, qr1);
+  trace_rays<true, false, kT>(a, sq, f, st, qr0, qr1);
 }
+
+__global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_q(TraceArgs a) { trace_q_body<false>(a); }
+__global__ void __launch_bounds__(kTraceQThreads, 1) k_trace_qt(TraceArgs a) { trace_q_body<true>(a); }
 
 // The 4-wide compact copy read from global memory (L2), for scenes whose copy
 // does not fit in shared memory; stacks in shared memory.
@@ -223,8 +293,8 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
     stage_receivers(a, reinterpret_cast<char*>(sstk + blockDim.x * kStackSmall), rx, rxt);
     __syncthreads();
   }
-  const int R = a.R;
-  const unsigned total = min(a.ctr->n_capitems, (unsigned)R * (unsigned)(a.N + 1));
+  const int R = a.R, LS = a.LS;
+  const unsigned total = min(a.ctr->n_capitems, (unsigned)LS * (unsigned)(a.N + a.max_trans + 1));
   unsigned ovf = 0;
   for (;;) {
     int base = fetch_warp(&a.ctr->work_capture, 32u);
@@ -234,13 +304,15 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
       unsigned it = a.capitems[q];
       bool reused = (it & 0x80000000u) != 0u;
       int ray = (int)((it & 0x7fffffffu) >> 4), b = (int)(it & 15u);
-      float4 lo = a.log_o[(size_t)b * R + ray], ld = a.log_d[(size_t)b * R + ray];
+      float4 lo = a.log_o[(size_t)b * LS + ray], ld = a.log_d[(size_t)b * LS + ray];
       float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
       float D = lo.w, t = ld.w;
       float tend = isinf(t) ? a.escape : t;
       // the ray's set: its capture spacing, and the link of its captures
-      int set = a.nsets > 1 ? __float_as_int(__ldg(reinterpret_cast<const float*>(a.rays) + 4 * (size_t)ray + 3))
-                            : 0;
+      // (a transmission child: its parent's)
+      int set = ray >= R ? (a.inst[ray - R] >> 8)
+                         : a.nsets > 1 ? __float_as_int(__ldg(reinterpret_cast<const float*>(a.rays) + 4 * (size_t)ray + 3))
+                                       : 0;
       float alpha = __ldg(&a.txs[set].w);
       int link0 = set * a.nrx;
       RayPre rp;
@@ -285,7 +357,7 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     __syncthreads();
   }
   const bool any_rx = c.ctr->rx_moved > 0;
-  const int R = a.R;
+  const int R = a.R, LS = a.LS;
   const int lane = threadIdx.x & 31;
   unsigned long long reused = 0;
   for (;;) {
@@ -302,8 +374,8 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     for (int b = 0; b < kPre; ++b) {
       plo[b] = pld[b] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (b < bstar) {
-        plo[b] = a.log_o[(size_t)b * R + ray];
-        pld[b] = a.log_d[(size_t)b * R + ray];
+        plo[b] = a.log_o[(size_t)b * LS + ray];
+        pld[b] = a.log_d[(size_t)b * LS + ray];
       }
     }
     auto step = [&](int b, float4 lo, float4 ld) {
@@ -332,8 +404,8 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     for (int b = kPre; b <= a.N; ++b) {
       float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), ld = lo;
       if (b < bstar) {
-        lo = a.log_o[(size_t)b * R + ray];
-        ld = a.log_d[(size_t)b * R + ray];
+        lo = a.log_o[(size_t)b * LS + ray];
+        ld = a.log_d[(size_t)b * LS + ray];
       }
       step(b, lo, ld);
     }
@@ -399,28 +471,34 @@ int trace_q_stack_cap(int n_nodes) {
 
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
   long n = a.R;
+  const bool tr = a.max_trans > 0;
   if (a.use_q != 1) {
     // kernels 0 and 2: a.block threads, a.stack_cap shared stack entries per
-    // thread; resident CTAs per SM looked up once per configuration
-    static int key[3] = {-1, -1, -1}, resident[3] = {0, 0, 0};
-    const void* fn = a.use_q == 2 ? (const void*)k_trace_qg : (const void*)k_trace;
+    // thread; resident CTAs per SM looked up once per configuration.
+    // Transmission uses the binary-node kernel with child rays (slot 3).
+    static int key[4] = {-1, -1, -1, -1}, resident[4] = {0, 0, 0, 0};
+    const int v = tr ? 3 : a.use_q;
+    const void* fn = v == 3 ? (const void*)k_trace_t : v == 2 ? (const void*)k_trace_qg : (const void*)k_trace;
     size_t smem = (size_t)a.block * a.stack_cap * sizeof(int);
     int k = a.block * 64 + a.stack_cap;
-    if (key[a.use_q] != k) {
-      resident[a.use_q] = resident_blocks(fn, sms, smem, a.block);
-      key[a.use_q] = k;
+    if (key[v] != k) {
+      resident[v] = resident_blocks(fn, sms, smem, a.block);
+      key[v] = k;
     }
-    if (a.use_q == 2) k_trace_qg<<<grid_for(n, a.block, resident[2]), a.block, smem, st>>>(a);
+    if (v == 3) k_trace_t<<<grid_for(n, a.block, resident[3]), a.block, smem, st>>>(a);
+    else if (v == 2) k_trace_qg<<<grid_for(n, a.block, resident[2]), a.block, smem, st>>>(a);
     else k_trace<<<grid_for(n, a.block, resident[0]), a.block, smem, st>>>(a);
   } else {
     size_t smem = (size_t)a.q4_bound * 4 * sizeof(uint4) + (size_t)kTraceQThreads * a.stack_cap * sizeof(int);
-    static size_t attr = 0;
-    if (smem > attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_trace_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static size_t attr[2] = {0, 0};
+    const void* fn = tr ? (const void*)k_trace_qt : (const void*)k_trace_q;
+    if (smem > attr[tr]) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      attr = smem;
+      attr[tr] = smem;
     }
-    k_trace_q<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
+    if (tr) k_trace_qt<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
+    else k_trace_q<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -443,7 +521,7 @@ cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st) {
   size_t smem = kS ? staged : base;
   cudaError_t e = allow_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  int blocks = grid_for((long)a.R * (a.N + 1), 256, resident_blocks(fn, sms, smem));
+  int blocks = grid_for((long)a.LS * (a.N + a.max_trans + 1), 256, resident_blocks(fn, sms, smem));
   if (kS) k_capture<true><<<blocks, 256, smem, st>>>(a);
   else k_capture<false><<<blocks, 256, smem, st>>>(a);
   return cudaGetLastError();

@@ -12,6 +12,16 @@ struct TraceArgs {
                            // effective capture spacing alpha_t / sqrt(3) (w)
   int nsets;
   int R, N;                // rays, reflections
+  int LS;                  // segment-log stride: R, plus the child slots with transmission
+  // transmission (Sec. III "Reflected and transmitted rays"): a hit on a
+  // material with mats[m].w >= 0 also spawns a child ray straight through
+  // it, up to max_trans per path; child slots R .. R + child_cap - 1 carry
+  // inst = reflections | transmissions << 4 | ray set << 8. Pass p traces
+  // the children pass p - 1 spawned.
+  const float4* mats;
+  int max_trans, pass, child_cap;
+  int* inst;
+  int* inst_root;          // per child slot: its primary ray's slot
   float tmin, escape;
   const float4* rx;        // nrx receivers (xyz); a capture's link is set * nrx + r
   int nrx;
@@ -35,7 +45,7 @@ struct TraceArgs {
   int* nseg;               // R
   const int* queue;        // retrace queue (null: all rays from segment 0)
   int* queue_w;            // retrace queue written by the marking kernel
-  const int* restart;      // R: first segment to retrace
+  int* restart;            // R + child slots: first segment to (re)trace
   const unsigned* nq_dev;  // queue length (device)
   Cand* cand;
   unsigned cand_cap;

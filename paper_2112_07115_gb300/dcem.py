@@ -25,6 +25,7 @@ PREC_F64, PREC_DF32 = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 PATH_POL_DEGENERATE = 1
 PATH_STICKY = 2
+TRI_TRANSMIT = 0x40000000
 
 EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_update_transforms", "dcem_trace_frame", "dcem_scene_reset_cache",
@@ -34,7 +35,8 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients",
             "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
             "dcem_scene_set_trace_config", "dcem_scene_autotune", "dcem_batch_create",
-            "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy"]
+            "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy",
+            "dcem_scene_set_transmission"]
 
 
 class Material(C.Structure):
@@ -66,7 +68,7 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int32), ("bvh_rebuilt", C.c_int32),
                 ("ms_stage", C.c_float * 10), ("bvh_cost_ratio", C.c_float),
                 ("max_segment_nodes", C.c_int32), ("trace_kernel", C.c_int32),
-                ("graph_replayed", C.c_int32), ("paths_sticky", C.c_int32)]
+                ("graph_replayed", C.c_int32), ("paths_sticky", C.c_int32), ("child_rays", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -106,6 +108,7 @@ def lib():
         L.dcem_scene_set_ray_sets.argtypes = [vp, vp, vp, i32]
         L.dcem_trace_links.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), P(Result)]
         L.dcem_scene_set_trace_config.argtypes = [vp, i32, i32, i32]
+        L.dcem_scene_set_transmission.argtypes = [vp, vp, i32, i32]
         L.dcem_batch_create.argtypes = [vp, i32, vp, P(vp)]
         L.dcem_batch_update_transforms.argtypes = [vp, vp, i32]
         L.dcem_batch_trace.argtypes = [vp, vp, vp, vp, vp, i32, P(Params), vp, P(i32)]
@@ -225,6 +228,12 @@ def dcem_trace_links(h, tx, rx, params: Params, result: Result) -> int:
     nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
     return lib().dcem_trace_links(h, txa.ctypes.data, txa.shape[0], rp, nrx, kind, C.byref(params),
                                   C.byref(result))
+
+
+def dcem_scene_set_transmission(h, loss_db, max_trans: int):
+    a = np.ascontiguousarray(loss_db, np.float32).reshape(-1)
+    _check(lib().dcem_scene_set_transmission(h, a.ctypes.data if a.size else None, a.size, int(max_trans)),
+           "dcem_scene_set_transmission")
 
 
 def dcem_scene_set_trace_config(h, kernel: int, block: int = 256, stack: int = 24):
@@ -480,6 +489,11 @@ class Scene:
     def set_graph_replay(self, on: bool):
         dcem_scene_set_graph_replay(self.h, on)
 
+    def set_transmission(self, loss_db, max_trans: int):
+        """Per-material penetration loss [dB] (< 0 opaque) and transmissions per path."""
+        dcem_scene_set_transmission(self.h, loss_db, max_trans)
+        self.max_trans = int(max_trans)
+
     def set_trace_config(self, kernel: int, block: int = 256, stack: int = 24):
         dcem_scene_set_trace_config(self.h, kernel, block, stack)
 
@@ -493,7 +507,8 @@ class Scene:
         return dcem_scene_get_bvh(self.h)
 
     def ray_log(self):
-        return dcem_scene_get_ray_log(self.h, self.n_rays, self.max_refl)
+        """Primary rays' hit ids, distances (max_refl + max_trans + 1 segments) and segment counts."""
+        return dcem_scene_get_ray_log(self.h, self.n_rays, self.max_refl + getattr(self, "max_trans", 0))
 
     def candidates(self):
         return dcem_scene_get_candidates(self.h)

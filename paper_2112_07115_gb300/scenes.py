@@ -19,6 +19,8 @@ Workloads:
     vehicle plus static roadside Rx (the batched multi-transmitter workload).
   * ``scene_batch`` -- independent urban grids of very different sizes (1k-200k
     triangles, 10-2000 vehicles, 1-16 Tx with uneven budgets) traced together.
+  * ``office``      -- an indoor floor of rooms with Table II walls (20 dB) and
+    glass windows (5 dB), moving metal carts, Tx at 2 m, 30 GHz (transmission).
   * small closed-form scenes (ground plane, parallel plates, random triangles).
 
 The paper (Sec. III) uses an .obj town model and measurement campaigns that
@@ -495,6 +497,106 @@ def scene_batch(seed: int = 0, n: int = 32, tris: tuple = (1_000, 200_000), vehi
         out.append(urban_grid(seed=1000 * seed + i, blocks=b, parcels=p, n_vehicles=nv, n_tx=ntx, budgets=budgets,
                               n_static_rx=8, n_frames=n_frames, max_refl=max_refl, freq_hz=freq_hz))
     return out
+
+
+# ----------------------------------------------------------------------------
+# indoor office (transmission)
+# ----------------------------------------------------------------------------
+
+# Office materials: rows of ``office_materials``; penetration losses (Table
+# II: indoor wall 20 dB, glass 5 dB) in ``meta["trans_db"]``.
+OFFICE_SLAB, OFFICE_WALL, OFFICE_GLASS, OFFICE_METAL = range(4)
+
+
+def office_materials() -> np.ndarray:
+    return np.array([[5.31, 0.0326, 0.0],    # floor and ceiling slabs (opaque)
+                     [5.31, 0.0326, 0.0],    # indoor walls (Table II: 20 dB)
+                     [6.27, 0.0043, 0.0],    # glass (Table II: 5 dB)
+                     [1.0, 0.0, 1.0]],       # metal carts
+                    dtype=np.float32)
+
+
+def office(seed: int = 0, rooms_x: int = 4, rooms_y: int = 3, room=(6.0, 5.0), height: float = 3.0,
+           n_carts: int = 4, rx_per_room: int = 4, n_frames: int = 10, n_rays: int = 1_000_000,
+           max_refl: int = 2, max_trans: int = 2, freq_hz: float = 30e9) -> Scene:
+    """An office floor of rooms_x x rooms_y rooms (room[0] x room[1] m, 3 m
+    high): floor and ceiling slabs, interior walls (Table II indoor wall,
+    20 dB), exterior walls with a 2 m glass window per room side (Table II
+    glass, 5 dB), and ``n_carts`` metal carts (1.2 x 0.6 x 1 m) moving across
+    the floor at 1 m/s. Tx at 2 m in the first room (the paper's indoor
+    set-up: 2 m, 30 GHz, 0.5 W), ``rx_per_room`` receivers at 1.5 m in every
+    room. ``meta["trans_db"]`` holds the per-material penetration losses
+    (-1 = opaque) and ``meta["max_trans"]`` the transmissions per path."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 5])))
+    W, H = rooms_x * room[0], rooms_y * room[1]
+    static, smat = [], []
+    for i in range(rooms_x):
+        for j in range(rooms_y):
+            x0, y0 = i * room[0], j * room[1]
+            x1, y1 = x0 + room[0], y0 + room[1]
+            static += _quad((x0, y0, 0.0), (x1, y0, 0.0), (x1, y1, 0.0), (x0, y1, 0.0))
+            static += _quad((x0, y0, height), (x0, y1, height), (x1, y1, height), (x1, y0, height))
+            smat += [OFFICE_SLAB] * 4
+
+    def wall_x(x, ya, yb, window):
+        # a wall in the plane x between y = ya and yb; a window pane in the middle
+        out, mats = [], []
+        if window:
+            ym = 0.5 * (ya + yb)
+            for a, b in ((ya, ym - 1.0), (ym + 1.0, yb)):
+                out += _quad((x, a, 0.0), (x, b, 0.0), (x, b, height), (x, a, height))
+                mats += [OFFICE_WALL] * 2
+            out += _quad((x, ym - 1.0, 0.0), (x, ym + 1.0, 0.0), (x, ym + 1.0, 1.0), (x, ym - 1.0, 1.0))
+            out += _quad((x, ym - 1.0, 2.5), (x, ym + 1.0, 2.5), (x, ym + 1.0, height), (x, ym - 1.0, height))
+            mats += [OFFICE_WALL] * 4
+            out += _quad((x, ym - 1.0, 1.0), (x, ym + 1.0, 1.0), (x, ym + 1.0, 2.5), (x, ym - 1.0, 2.5))
+            mats += [OFFICE_GLASS] * 2
+        else:
+            out += _quad((x, ya, 0.0), (x, yb, 0.0), (x, yb, height), (x, ya, height))
+            mats += [OFFICE_WALL] * 2
+        return out, mats
+
+    def swap_xy(tris):
+        return [[(p[1], p[0], p[2]) for p in t] for t in tris]
+
+    for i in range(rooms_x + 1):
+        for j in range(rooms_y):
+            t, m = wall_x(i * room[0], j * room[1], (j + 1) * room[1], i in (0, rooms_x))
+            static += t
+            smat += m
+    for j in range(rooms_y + 1):
+        for i in range(rooms_x):
+            t, m = wall_x(j * room[1], i * room[0], (i + 1) * room[0], j in (0, rooms_y))
+            static += swap_xy(t)
+            smat += m
+    meshes = [box_tris(1.2, 0.6, 1.0) for _ in range(n_carts)]
+    tris, tobj, tmat = _assemble(static, smat, meshes, [OFFICE_METAL] * n_carts)
+    # carts: straight lines across the floor, reflected at the outer walls
+    pos = np.stack([rng.uniform(1.0, W - 1.0, n_carts), rng.uniform(1.0, H - 1.0, n_carts)], 1)
+    ang = rng.uniform(0.0, 2.0 * np.pi, n_carts)
+    vel = np.stack([np.cos(ang), np.sin(ang)], 1)
+    dt = 0.1
+    xf = np.zeros((n_frames, n_carts, 12), np.float64)
+    for f in range(n_frames):
+        for k in range(n_carts):
+            xf[f, k] = _xf_row(float(np.arctan2(vel[k, 1], vel[k, 0])), pos[k, 0], pos[k, 1], 0.0)
+        pos += vel * dt
+        for ax, lim in ((0, W), (1, H)):
+            out = (pos[:, ax] < 0.8) | (pos[:, ax] > lim - 0.8)
+            vel[out, ax] *= -1.0
+    rxs = []
+    g = int(np.ceil(np.sqrt(rx_per_room)))
+    for i in range(rooms_x):
+        for j in range(rooms_y):
+            for q in range(rx_per_room):
+                u, v = (q % g + 0.5) / g, (q // g + 0.5) / g
+                rxs.append((i * room[0] + u * room[0], j * room[1] + v * room[1], 1.5))
+    rx = np.repeat(np.asarray(rxs, np.float64)[None], n_frames, axis=0)
+    tx = np.array([0.5 * room[0] + 0.3, 0.5 * room[1] + 0.2, 2.0], np.float32)
+    trans = [-1.0, 20.0, 5.0, -1.0]
+    return Scene("office", tris, tobj, tmat, office_materials(), n_carts, xf.astype(np.float32), tx,
+                 rx.astype(np.float32), freq_hz=freq_hz, n_rays=n_rays, max_refl=max_refl,
+                 meta={"seed": seed, "trans_db": trans, "max_trans": max_trans, "tx_power_w": 0.5})
 
 
 # ----------------------------------------------------------------------------

@@ -54,7 +54,8 @@ def compare_candidates(gpu_cands, ref_tr):
 def compare_paths(frame, ref, max_refl, len_tol=1e-6, amp_rtol=1e-4):
     """GPU valid paths vs the oracle's validated keys. Keys discovered by an
     unflagged ray and not flagged in validation must agree in validity, and
-    valid ones in length and amplitude. Returns a dict of findings."""
+    valid ones in length and amplitude. Returns a dict of findings.
+    max_refl: the key width (reflections plus transmissions per path)."""
     flagged = (ref.tr["flags"] & RAY_FLAGS) != 0
     ckeys = O.candidate_keys(ref.tr["cands"], ref.tr["hit_id"], max_refl)
     clean = {tuple(k) for k, c in zip(ckeys.tolist(), ref.tr["cands"].tolist()) if not flagged[c[0]]}
