@@ -31,6 +31,18 @@
  *                  the triangle id) and scales the field by the material's
  *                  penetration loss at each transmission.
  *   or_fresnel     Fresnel reflection coefficients.
+ *   or_diffract    step 5, first order: edge diffraction paths Tx -> Q -> Rx
+ *                  over the wedges of the static geometry (edges shared by
+ *                  two non-coplanar triangles), Q on the edge by Keller's law,
+ *                  kept when the receiver lies in the source's shadow region
+ *                  behind the wedge and both legs are unoccluded; field by the
+ *                  uniform theory of diffraction (UTD): R. G. Kouyoumjian and
+ *                  P. H. Pathak, "A uniform geometrical theory of diffraction
+ *                  for an edge in a perfectly conducting surface", Proc. IEEE
+ *                  62(11), 1974, with R. J. Luebbers' finite-conductivity
+ *                  reflection factors (IEEE Trans. Antennas Propag. 32(1),
+ *                  1984). The transition function is evaluated from its
+ *                  integral definition by quadrature along a rotated contour.
  *
  * Everything after the FP32 inputs is FP64. Decisions that FP32 arithmetic
  * could take differently (a ray passing within a margin of a triangle edge,
@@ -51,6 +63,7 @@
 
 #define OR_MAX_REFL 10
 #define OR_TRANS 0x40000000  /* interaction id flag: transmission through the triangle */
+#define OR_DIFF 0x20000000   /* interaction id flag: diffraction at edge `id` */
 
 /* ray / path flag bits */
 #define ORF_NEAR_EDGE 1u     /* a triangle's in/out decision is within the margin */
@@ -1032,6 +1045,278 @@ int or_path_amp_d(const double* tris, const int32_t* tri_mat, int32_t ntri, cons
   }
   scene_free(&S);
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* or_diffract: first-order edge diffraction (step 5) with the UTD            */
+/* ------------------------------------------------------------------------ */
+/* UTD transition function F(x) = 2j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt
+ * (x >= 0). The integral, with t = a + e^{-j pi/4} v, becomes
+ * e^{-j pi/4} e^{-j a^2} int_0^inf exp(-2 a e^{j pi/4} v - v^2) dv: a smooth,
+ * decaying integrand, integrated by the composite Simpson rule. */
+static double complex transition_fn(double x) {
+  if (!(x > 0)) return 0.0;
+  double a = sqrt(x);
+  double complex c = 2.0 * a * cexp(I * M_PI / 4.0);
+  double vmax = fmin(9.0, 60.0 / (creal(c) + 1e-300));
+  double h = fmin(2e-4, 0.005 / (1.0 + cabs(c)));
+  long n = (long)ceil(vmax / h);
+  if (n % 2) ++n;
+  h = vmax / (double)n;
+  double complex sum = 0.0;
+  for (long i = 0; i <= n; ++i) {
+    double v = i * h;
+    double complex f = cexp(-c * v - v * v);
+    double w = (i == 0 || i == n) ? 1.0 : ((i % 2) ? 4.0 : 2.0);
+    sum += w * f;
+  }
+  double complex G = cexp(-I * M_PI / 4.0) * cexp(-I * x) * (sum * h / 3.0);
+  return 2.0 * I * a * cexp(I * x) * G;
+}
+
+void or_transition(double x, double* out2) {
+  double complex f = transition_fn(x);
+  out2[0] = creal(f);
+  out2[1] = cimag(f);
+}
+
+/* one cot((pi + s beta)/(2n)) F(k L a^s(beta)) term; a^s(beta) = 2 cos^2((2 n pi N - beta)/2)
+ * with N the integer closest to a solution of 2 pi n N - beta = s pi */
+static double complex utd_term(double n, double beta, double s, double kL, uint32_t* fl) {
+  double N = round((beta + s * M_PI) / (2.0 * M_PI * n));
+  double c = cos((2.0 * n * M_PI * N - beta) / 2.0);
+  double arg = (M_PI + s * beta) / (2.0 * n);
+  double sn = sin(arg);
+  if (fabs(sn) < 1e-9) { if (fl) *fl |= ORF_VAL_PARAM; return 0.0; }  /* on a shadow boundary */
+  return cos(arg) / sn * transition_fn(kL * 2.0 * c * c);
+}
+
+/* Wedge diffraction coefficient: n = exterior angle / pi; phi, phip the
+ * receiver and source angles from face 0 through the exterior; beta0 the
+ * angle between the incident ray and the edge; L the distance parameter;
+ * R0, Rn the reflection factors of faces 0 and n (-1 soft / +1 hard for a
+ * perfect conductor, the faces' Fresnel coefficients after Luebbers). */
+static double complex utd_coeff(double n, double phi, double phip, double beta0, double L, double k,
+                                double complex R0, double complex Rn, uint32_t* fl) {
+  double complex pre = -cexp(-I * M_PI / 4.0) / (2.0 * n * sqrt(2.0 * M_PI * k) * sin(beta0));
+  double bm = phi - phip, bp = phi + phip, kL = k * L;
+  return pre * (utd_term(n, bm, +1.0, kL, fl) + utd_term(n, bm, -1.0, kL, fl) +
+                R0 * utd_term(n, bp, -1.0, kL, fl) + Rn * utd_term(n, bp, +1.0, kL, fl));
+}
+
+void or_utd(double n, double phi, double phip, double beta0, double L, double k, const double* r0,
+            const double* rn, double* out2) {
+  double complex d = utd_coeff(n, phi, phip, beta0, L, k, r0[0] + I * r0[1], rn[0] + I * rn[1], NULL);
+  out2[0] = creal(d);
+  out2[1] = cimag(d);
+}
+
+/* Wedges of the static geometry: edges shared by exactly two static
+ * triangles (identical vertex coordinates) whose planes differ. Edge list in
+ * (lower triangle id, higher triangle id) order; face 0 is the lower id. */
+typedef struct {
+  int ta, tb;       /* faces 0 and n                                   */
+  v3 p0, e;         /* edge start and unit direction                   */
+  double len;
+  v3 t0, y0;        /* in the plane normal to e: face 0's direction and
+                       the exterior's positive angular direction        */
+  double n;         /* exterior angle / pi                             */
+} owedge;
+
+static int vkey_cmp(const float* a, const float* b) {
+  for (int k = 0; k < 3; ++k) if (a[k] != b[k]) return a[k] < b[k] ? -1 : 1;
+  return 0;
+}
+
+typedef struct { float a[3], b[3]; int tri; } oedge_rec;
+
+static int oedge_cmp(const void* x, const void* y) {
+  const oedge_rec* p = (const oedge_rec*)x;
+  const oedge_rec* q = (const oedge_rec*)y;
+  int c = vkey_cmp(p->a, q->a);
+  if (c) return c;
+  c = vkey_cmp(p->b, q->b);
+  if (c) return c;
+  return p->tri < q->tri ? -1 : (p->tri > q->tri);
+}
+
+static int wedge_cmp(const void* x, const void* y) {
+  const owedge* p = (const owedge*)x;
+  const owedge* q = (const owedge*)y;
+  if (p->ta != q->ta) return p->ta < q->ta ? -1 : 1;
+  return p->tb < q->tb ? -1 : (p->tb > q->tb);
+}
+
+static long find_wedges(const float* tris, const int32_t* tri_obj, int ntri, owedge** out) {
+  oedge_rec* r = (oedge_rec*)malloc(sizeof(oedge_rec) * (size_t)(3 * ntri + 1));
+  long m = 0;
+  for (int i = 0; i < ntri; ++i) {
+    if (tri_obj && tri_obj[i] >= 0) continue;
+    for (int k = 0; k < 3; ++k) {
+      const float* a = &tris[9 * i + 3 * k];
+      const float* b = &tris[9 * i + 3 * ((k + 1) % 3)];
+      oedge_rec* e = &r[m++];
+      if (vkey_cmp(a, b) <= 0) { memcpy(e->a, a, 12); memcpy(e->b, b, 12); }
+      else { memcpy(e->a, b, 12); memcpy(e->b, a, 12); }
+      e->tri = i;
+    }
+  }
+  qsort(r, (size_t)m, sizeof(oedge_rec), oedge_cmp);
+  owedge* w = (owedge*)malloc(sizeof(owedge) * (size_t)(m + 1));
+  long nw = 0;
+  for (long i = 0; i < m;) {
+    long j = i + 1;
+    while (j < m && !vkey_cmp(r[j].a, r[i].a) && !vkey_cmp(r[j].b, r[i].b)) ++j;
+    if (j - i == 2) {
+      int ta = r[i].tri < r[i + 1].tri ? r[i].tri : r[i + 1].tri;
+      int tb = r[i].tri < r[i + 1].tri ? r[i + 1].tri : r[i].tri;
+      v3 p0 = mk(r[i].a[0], r[i].a[1], r[i].a[2]), p1 = mk(r[i].b[0], r[i].b[1], r[i].b[2]);
+      v3 e = sub(p1, p0);
+      double len = norm(e);
+      if (len > 0) {
+        e = scl(e, 1.0 / len);
+        /* third vertices of the two faces, projected normal to the edge */
+        v3 third[2];
+        int tt[2] = {ta, tb};
+        for (int q = 0; q < 2; ++q) {
+          third[q] = p0;
+          for (int k = 0; k < 3; ++k) {
+            const float* v = &tris[9 * tt[q] + 3 * k];
+            v3 vv = mk(v[0], v[1], v[2]);
+            if (vkey_cmp(v, r[i].a) && vkey_cmp(v, r[i].b)) third[q] = vv;
+          }
+        }
+        v3 da = sub(third[0], p0), db = sub(third[1], p0);
+        da = sub(da, scl(e, dot(da, e)));
+        db = sub(db, scl(e, dot(db, e)));
+        double la = norm(da), lb = norm(db);
+        if (la > 0 && lb > 0) {
+          v3 t0 = scl(da, 1.0 / la), tB = scl(db, 1.0 / lb);
+          v3 y0 = cross(e, t0);
+          /* the interior (face n side) is at a positive angle alpha from face 0
+           * about +y0; the exterior angles run the other way */
+          double alpha = atan2(dot(tB, y0), dot(tB, t0));
+          if (alpha < 0) { y0 = scl(y0, -1.0); alpha = -alpha; }
+          y0 = scl(y0, -1.0);  /* exterior direction */
+          if (fabs(alpha - M_PI) > 1e-6 && alpha > 1e-9) {
+            owedge* W = &w[nw++];
+            W->ta = ta; W->tb = tb; W->p0 = p0; W->e = e; W->len = len;
+            W->t0 = t0; W->y0 = y0; W->n = 2.0 - alpha / M_PI;
+          }
+        }
+      }
+    }
+    i = j;
+  }
+  free(r);
+  qsort(w, (size_t)nw, sizeof(owedge), wedge_cmp);
+  *out = w;
+  return nw;
+}
+
+/* angle of point X about the wedge (from face 0 through the exterior) */
+static double wedge_angle(const owedge* W, v3 X) {
+  v3 d = sub(X, W->p0);
+  d = sub(d, scl(W->e, dot(d, W->e)));
+  double a = atan2(dot(d, W->y0), dot(d, W->t0));
+  if (a < 0) a += 2.0 * M_PI;
+  return a;
+}
+
+int32_t or_count_wedges(const float* tris, const int32_t* tri_obj, int32_t ntri) {
+  owedge* w = NULL;
+  long n = find_wedges(tris, tri_obj, ntri, &w);
+  free(w);
+  return (int32_t)n;
+}
+
+/* First-order diffraction paths for every (receiver, wedge); writes the
+ * valid ones (keys: rx, 1, wedge | OR_DIFF; -1 padded to 2 + width) and
+ * returns their count (may exceed cap). */
+int64_t or_diffract(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                    const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                    const or_params* P, int32_t width, int32_t* keys_out, opath* paths_out, int64_t cap) {
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  int64_t nvalid = 0;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (long w = 0; w < nw; ++w) {
+      const owedge* E = &W[w];
+      uint32_t fl = 0;
+      /* Keller's law: Q where the unfolded path crosses the edge line */
+      v3 dt = sub(T, E->p0), dr = sub(R, E->p0);
+      double zt = dot(dt, E->e), zr = dot(dr, E->e);
+      double rt = norm(sub(dt, scl(E->e, zt))), rr = norm(sub(dr, scl(E->e, zr)));
+      if (!(rt > 0 && rr > 0)) continue;
+      double zq = zt + (zr - zt) * rt / (rt + rr);
+      double uq = zq / E->len;
+      if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+      if (!(uq > 0 && uq < 1)) continue;
+      v3 Q = add(E->p0, scl(E->e, zq));
+      double phip = wedge_angle(E, T), phi = wedge_angle(E, R), nn = E->n;
+      double ang_eps = 1e-9;
+      if (phip > nn * M_PI || phi > nn * M_PI) continue;        /* inside the wedge */
+      /* the paper's step 5: the source lies in the shadow region seen from
+       * the receiver, i.e. the receiver is beyond the incident shadow boundary */
+      if (fabs(fabs(phi - phip) - M_PI) <= ang_eps) fl |= ORF_VAL_PARAM;
+      if (!(fabs(phi - phip) > M_PI)) continue;
+      double scale = fmax(maxabs(T), maxabs(R));
+      if (occluded(&S, T, Q, E->ta, E->tb, P, scale, &fl)) continue;
+      if (occluded(&S, Q, R, E->ta, E->tb, P, scale, &fl)) continue;
+      /* UTD field */
+      double sp = norm(sub(Q, T)), s = norm(sub(R, Q));
+      v3 ip = scl(sub(Q, T), 1.0 / sp), dd = scl(sub(R, Q), 1.0 / s);
+      double cb = dot(ip, E->e);
+      double beta0 = acos(fmax(-1.0, fmin(1.0, cb)));
+      double L = s * sp * sin(beta0) * sin(beta0) / (s + sp);
+      v3 php = cross(E->e, ip), ph = cross(E->e, dd);
+      php = scl(php, -1.0 / norm(php));
+      ph = scl(ph, 1.0 / norm(ph));
+      v3 bp = cross(ip, php), bd = cross(dd, ph);
+      /* Luebbers: faces' reflection coefficients at the grazing angles
+       * phi' (face 0) and n pi - phi (face n) */
+      int ma = S.t[E->ta].mat, mb = S.t[E->tb].mat;
+      if (ma < 0 || ma >= S.nmat) ma = 0;
+      if (mb < 0 || mb >= S.nmat) mb = 0;
+      double complex r0s, r0h, rns, rnh;
+      fresnel(&S.mats[3 * ma], P->freq_hz, fabs(sin(phip)), &r0s, &r0h);
+      fresnel(&S.mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - phi)), &rns, &rnh);
+      double complex Ds = utd_coeff(nn, phi, phip, beta0, L, k, r0s, rns, &fl);
+      double complex Dh = utd_coeff(nn, phi, phip, beta0, L, k, r0h, rnh, &fl);
+      v3 e0 = pol_dir(u, ip, &fl);
+      double complex Ei = cexp(-I * k * sp) / sp;
+      double complex Eb = Ei * dot(e0, bp), Ep = Ei * dot(e0, php);
+      double complex A = csqrt(sp / (s * (s + sp))) * cexp(-I * k * s);
+      /* E_d = (-Ds E_beta' beta0^ - Dh E_phi' phi^) A e^{-jks} */
+      v3 prx = pol_dir(u, scl(dd, -1.0), &fl);
+      double complex proj = (-Ds * Eb) * dot(bd, prx) + (-Dh * Ep) * dot(ph, prx);
+      double complex a = (lam / (4.0 * M_PI)) * proj * A;
+      if (nvalid < cap) {
+        int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+        kk[0] = r; kk[1] = 1; kk[2] = (int32_t)w | OR_DIFF;
+        for (int j = 1; j < width; ++j) kk[2 + j] = -1;
+        opath* o = &paths_out[nvalid];
+        memset(o, 0, sizeof(*o));
+        o->valid = 1;
+        o->flags = fl;
+        o->len_m = sp + s;
+        o->delay_s = (sp + s) / C0;
+        o->amp_re = creal(a);
+        o->amp_im = cimag(a);
+        o->pts[0][0] = Q.x; o->pts[0][1] = Q.y; o->pts[0][2] = Q.z;
+      }
+      nvalid++;
+    }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
 }
 
 int32_t or_path_size(void) { return (int32_t)sizeof(opath); }

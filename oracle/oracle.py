@@ -17,6 +17,8 @@ Pipeline of one frame (arXiv 2112.07115, Sec. III):
                  occlusion; length, delay, Fresnel TE/TM, complex amplitude
   reduce      -> received power per receiver: coherent P_t |sum a|^2 and
                  incoherent P_t sum |a|^2 in dBm, summed in sorted key order.
+  diffract    -> step 5, first order: edge diffraction paths with the UTD
+                 coefficient (Kouyoumjian & Pathak 1974; Luebbers 1984).
   sticky      -> the path cache's literal retention (Sec. III "Propagation
                  path caching", cached paths kept and updated until removed):
                  a frame's keys are the ones its rays capture plus every key
@@ -72,6 +74,7 @@ class _Params(C.Structure):
 
 
 TRANS = 0x40000000   # interaction id flag: transmission through the triangle
+DIFF = 0x20000000    # interaction id flag: diffraction at the wedge of that index
 MAX_SEG = MAX_REFL + 1
 INST_DTYPE = np.dtype([("root", np.int32), ("start", np.int32), ("nseg", np.int32), ("flags", np.uint32),
                        ("hit", np.int32, (MAX_SEG,)), ("t", np.float64, (MAX_SEG,))], align=True)
@@ -116,6 +119,15 @@ def lib():
         _lib.or_trace_tree.restype = C.c_int
         _lib.or_inst_size.restype = C.c_int32
         assert _lib.or_inst_size() == INST_DTYPE.itemsize, "instance record layout mismatch"
+        _lib.or_transition.argtypes = [C.c_double, f64]
+        _lib.or_transition.restype = None
+        _lib.or_utd.argtypes = [C.c_double] * 6 + [f64, f64, f64]
+        _lib.or_utd.restype = None
+        _lib.or_count_wedges.argtypes = [f32, i32, C.c_int32]
+        _lib.or_count_wedges.restype = C.c_int32
+        _lib.or_diffract.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                     P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
+        _lib.or_diffract.restype = C.c_int64
     return _lib
 
 
@@ -138,6 +150,7 @@ class OracleParams:
     nthreads: int = 0
     max_trans: int = 0          # transmissions per path (Table II penetration)
     trans_db: tuple = ()        # per material penetration loss [dB], < 0 opaque
+    diffraction: bool = False   # first-order edge diffraction paths (UTD)
 
     @property
     def width(self) -> int:
@@ -455,14 +468,67 @@ class FrameResult:
 
 
 def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> FrameResult:
-    """The whole oracle pipeline for frame ``f`` of a ``scenes.Scene``."""
+    """The whole oracle pipeline for frame ``f`` of a ``scenes.Scene``
+    (with prm.diffraction, the first-order diffraction paths join the
+    validated keys before the reduction)."""
     wt = transform(scene.tris, scene.tri_obj, scene.xf[f] if scene.nobj else np.zeros((0, 12)))
     rx = scene.rx[f]
     tr = trace(wt, scene.tri_mat, scene.materials, scene.tx, rays, rx, prm, seg_od=seg_od)
     keys = unique_keys(candidate_keys(tr["cands"], tr["hit_id"], prm.width))
     paths = validate(wt, scene.tri_mat, scene.materials, scene.tx, rx, keys, prm)
+    if prm.diffraction:
+        dk, dp = diffract(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm)
+        keys = np.concatenate([keys, dk])
+        paths = np.concatenate([paths, dp])
+        order = np.lexsort(keys.T[::-1])
+        keys, paths = keys[order], paths[order]
     fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)
     return FrameResult(wt, tr, keys, paths, fld, pc, pi)
+
+
+def transition(x: float) -> complex:
+    """UTD transition function F(x) (Kouyoumjian & Pathak 1974)."""
+    out = np.zeros(2)
+    lib().or_transition(float(x), _p(out, C.c_double))
+    return complex(out[0], out[1])
+
+
+def utd_coefficient(n, phi, phip, beta0, L, k, r0, rn) -> complex:
+    """Wedge diffraction coefficient with face reflection factors r0, rn
+    (-1 soft / +1 hard for a perfect conductor; Luebbers' Fresnel factors)."""
+    out = np.zeros(2)
+    a = np.array([complex(r0).real, complex(r0).imag])
+    b = np.array([complex(rn).real, complex(rn).imag])
+    lib().or_utd(float(n), float(phi), float(phip), float(beta0), float(L), float(k),
+                 _p(a, C.c_double), _p(b, C.c_double), _p(out, C.c_double))
+    return complex(out[0], out[1])
+
+
+def count_wedges(world_tris, tri_obj) -> int:
+    wt = _f32(world_tris).reshape(-1, 9)
+    return int(lib().or_count_wedges(_p(wt, C.c_float), _p(_i32(tri_obj), C.c_int32), wt.shape[0]))
+
+
+def diffract(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleParams, cap=1 << 20):
+    """Step 5, first order: every (receiver, wedge) diffraction path that is
+    valid (Keller point on the edge, receiver in the source's shadow region,
+    both legs unoccluded), with its UTD field. Keys (rx, 1, wedge | DIFF)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    width = prm.width
+    keys = np.zeros((cap, 2 + width), np.int32)
+    paths = np.zeros(cap, PATH_DTYPE)
+    prm_c = prm.c()
+    n = lib().or_diffract(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), _p(_i32(tri_obj), C.c_int32),
+                          wt.shape[0], _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                          _p(rx, C.c_float), rx.shape[0], C.byref(prm_c), width, _p(keys, C.c_int32),
+                          paths.ctypes.data_as(C.c_void_p), cap)
+    if n < 0:
+        raise RuntimeError(f"or_diffract failed: {n}")
+    if n > cap:
+        raise RuntimeError(f"or_diffract: {n} paths exceed capacity {cap}")
+    return keys[:n].copy(), paths[:n].copy()
 
 
 def sticky_frames(scene, frames, rays: np.ndarray, prm: OracleParams):

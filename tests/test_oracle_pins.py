@@ -532,3 +532,119 @@ def test_transmission_sbr_subset_of_exhaustive(oracle_mod, seed):
         assert any(any(v >= 0 and (v & O.TRANS) for v in k[2:]) for k in ex)
         if n_rays > 100_000:
             assert sbr == ex
+
+
+# ---------------------------------------------------------------- diffraction
+
+def test_utd_transition_function_vs_fresnel_integrals(oracle_mod):
+    """F(x) = 2j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt (Kouyoumjian &
+    Pathak 1974) against the Fresnel integrals of scipy: the tail integral is
+    sqrt(pi/2) [(1/2 - C(z)) - j (1/2 - S(z))], z = sqrt(2x/pi)."""
+    sp = pytest.importorskip("scipy.special")
+    O = oracle_mod
+    for x in (1e-6, 1e-3, 0.3, 1.0, 3.0, 10.0, 100.0, 1e4):
+        z = np.sqrt(2.0 * x / np.pi)
+        S, Cf = sp.fresnel(z)
+        ref = 2j * np.sqrt(x) * np.exp(1j * x) * np.sqrt(np.pi / 2) * ((0.5 - Cf) - 1j * (0.5 - S))
+        assert abs(O.transition(x) - ref) <= 1e-10 * abs(ref), x
+
+
+@pytest.mark.parametrize("phi,phip", [(2.0, 0.5), (4.5, 1.0), (5.5, 0.3), (3.0, 2.5)])
+def test_utd_half_plane_reduces_to_keller(oracle_mod, phi, phip):
+    """Far from the shadow boundaries (F -> 1) the UTD coefficient of a
+    perfectly conducting half plane (n = 2) is Keller's:
+    -e^{-j pi/4} / (2 sqrt(2 pi k) sin b0) [sec((phi-phi')/2) -/+ sec((phi+phi')/2)]."""
+    O = oracle_mod
+    k = 2 * np.pi * 28e9 / C0
+    for b0 in (np.pi / 2, 1.1):
+        for sgn, R in ((-1.0, -1.0), (1.0, 1.0)):
+            D = O.utd_coefficient(2.0, phi, phip, b0, 1e10, k, R, R)
+            ref = -np.exp(-1j * np.pi / 4) / (2 * np.sqrt(2 * np.pi * k) * np.sin(b0)) * (
+                1 / np.cos((phi - phip) / 2) + sgn / np.cos((phi + phip) / 2))
+            assert abs(D - ref) <= 1e-8 * abs(ref)
+
+
+def test_utd_total_field_continuous_at_shadow_boundary(oracle_mod):
+    """Plane wave on a conducting half plane: the geometric-optics field
+    switches off at the incident shadow boundary phi = phi' + pi, and the
+    diffracted field makes up the jump, so the total field is continuous."""
+    O = oracle_mod
+    k = 2 * np.pi * 28e9 / C0
+    phip, s = 0.7, 2.0
+
+    def total(phi):
+        go = np.exp(1j * k * s * np.cos(phi - phip)) if phi - phip < np.pi else 0.0
+        d = O.utd_coefficient(2.0, phi, phip, np.pi / 2, s, k, -1.0, -1.0)
+        return go + d * np.exp(-1j * k * s) / np.sqrt(s)
+
+    for delta, tol in ((1e-5, 1e-3), (1e-7, 1e-5)):
+        a, b = total(np.pi + phip - delta), total(np.pi + phip + delta)
+        assert abs(a - b) <= tol
+        # each part alone jumps by about half the incident field
+        assert abs(O.utd_coefficient(2.0, np.pi + phip + delta, phip, np.pi / 2, s, k, -1.0, -1.0) -
+                   O.utd_coefficient(2.0, np.pi + phip - delta, phip, np.pi / 2, s, k, -1.0, -1.0)) > 0.5
+
+
+def _corner(rx=(-20.0, 30.0, 2.0)):
+    """A building corner: walls y = 0 (x in [0, 50]) and x = 0 (y in [0, 50])
+    meeting at the vertical edge x = y = 0; Tx at (30, -20, 2)."""
+    tris = scenes._quad((0.0, 0.0, -50.0), (50.0, 0.0, -50.0), (50.0, 0.0, 50.0), (0.0, 0.0, 50.0))
+    tris += scenes._quad((0.0, 0.0, -50.0), (0.0, 50.0, -50.0), (0.0, 50.0, 50.0), (0.0, 0.0, 50.0))
+    return scenes._static_scene("corner", tris, [0, 0, 0, 0], (30.0, -20.0, 2.0), (rx,))
+
+
+def test_diffraction_path_around_a_corner(oracle_mod):
+    """Tx and Rx on the two sides of a concrete building corner (no line of
+    sight, no reflection path): one diffraction path at Q = (0, 0, 2) (Keller:
+    equal angles with the edge), whose field, assembled here from the
+    geometry and the UTD coefficient (vertical polarisation along a vertical
+    edge: the soft coefficient with Luebbers' TE factors), is the oracle's."""
+    O = oracle_mod
+    sc = _corner()
+    wt = sc.tris.reshape(-1, 9)
+    assert O.count_wedges(wt, sc.tri_obj) == 1
+    prm = O.OracleParams(freq_hz=28e9, max_refl=2, diffraction=True)
+    ek, _ = O.exhaustive(wt, sc.tri_mat, sc.materials, sc.tx, sc.rx[0], prm)
+    assert ek.shape[0] == 0
+    dk, dp = O.diffract(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)
+    assert dk.shape[0] == 1 and dk[0, 1] == 1 and (dk[0, 2] & O.DIFF)
+    assert np.allclose(dp[0]["pts"][0], [0.0, 0.0, 2.0], atol=1e-12)
+    sp_, s_ = np.hypot(30.0, 20.0), np.hypot(20.0, 30.0)
+    assert abs(dp[0]["len_m"] - (sp_ + s_)) <= 1e-9
+    k = 2 * np.pi * 28e9 / C0
+    n = 1.5
+    # angles from one face through the exterior (the result does not depend
+    # on which face is face 0: both are concrete)
+    phip = np.arctan2(20.0, 30.0)
+    phi = 2 * np.pi - np.arctan2(30.0, -20.0)
+    L = s_ * sp_ / (s_ + sp_)
+    er, sg = float(np.float32(5.31)), float(np.float32(0.0326))   # the scene's FP32 material
+    g0, _ = O.fresnel(er, sg, 0, 28e9, abs(np.sin(phip)), exact=True)
+    gn, _ = O.fresnel(er, sg, 0, 28e9, abs(np.sin(n * np.pi - phi)), exact=True)
+    Ds = O.utd_coefficient(n, phi, phip, np.pi / 2, L, k, g0, gn)
+    lam = C0 / 28e9
+    a = lam / (4 * np.pi) * Ds * np.exp(-1j * k * (sp_ + s_)) / sp_ * np.sqrt(sp_ / (s_ * (s_ + sp_)))
+    got = complex(dp[0]["amp_re"], dp[0]["amp_im"])
+    assert abs(got - a) <= 1e-9 * abs(a)
+    # a receiver in sight of the transmitter: no diffraction path (the
+    # paper's step 5 keeps sources in the receiver's shadow region)
+    lit = _corner(rx=(-20.0, -30.0, 2.0))
+    assert O.diffract(wt, lit.tri_mat, lit.tri_obj, lit.materials, lit.tx, lit.rx[0], prm)[0].shape[0] == 0
+
+
+def test_toy_street_wedges_and_diffraction_frame(oracle_mod):
+    """The toy street's two buildings have four vertical corner wedges each;
+    with receivers behind the buildings (seen from the Tx), a diffraction
+    frame adds diffraction paths to the reflection paths and sums them."""
+    O = oracle_mod
+    sc = scenes.toy_street()
+    behind = np.array([[-30.0, 45.0, 1.5], [30.0, -45.0, 1.5], [-45.0, 30.0, 1.5], [12.0, 12.0, 1.5]], np.float32)
+    sc.rx = np.repeat(behind[None], sc.nframes, axis=0)
+    wt = O.transform(sc.tris, sc.tri_obj, sc.xf[0])
+    assert O.count_wedges(wt, sc.tri_obj) == 8
+    prm = O.OracleParams(max_refl=2, n_rays=10_000, diffraction=True)
+    r = O.frame(sc, 0, scenes.fibonacci_sphere(10_000), prm)
+    d = (r.keys[:, 2] >= 0) & ((r.keys[:, 2] & O.DIFF) != 0)
+    assert d.any() and r.paths["valid"][d].all()
+    plain = O.frame(sc, 0, scenes.fibonacci_sphere(10_000), O.OracleParams(max_refl=2, n_rays=10_000))
+    assert set(map(tuple, plain.keys.tolist())) == set(map(tuple, r.keys[~d].tolist()))
