@@ -82,6 +82,9 @@ typedef enum { DCEM_PTR_HOST = 0, DCEM_PTR_DEVICE = 1 } dcem_ptr_kind;
 /* dcem_path.tri[j] flag: interaction j is a transmission through the
  * triangle (straight through, penetration loss), not a reflection. */
 #define DCEM_TRI_TRANSMIT 0x40000000
+/* dcem_path.tri[0] flag of a diffraction path: the rest is the wedge index
+ * (see dcem_scene_set_diffraction). */
+#define DCEM_TRI_DIFFRACT 0x20000000
 
 typedef struct dcem_scene dcem_scene;
 
@@ -283,6 +286,22 @@ int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
  * traced in full). host loss_db, nmat entries (the scene's material count).
  * Errors: DCEM_ERR_ARG, DCEM_ERR_NONFINITE. */
 int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nmat, int32_t max_trans);
+
+/* First-order edge diffraction (Sec. III step 5; uniform theory of
+ * diffraction after Kouyoumjian & Pathak, Proc. IEEE 1974, with Luebbers'
+ * finite-conductivity face factors, IEEE Trans. AP 1984). on = 1 finds the
+ * wedges of the static geometry once: edges whose two vertices (identical
+ * coordinates) belong to exactly two static triangles with different planes,
+ * numbered in the order of their faces' (lower, higher) triangle ids. Every
+ * frame then adds, for each (link, wedge), the path Tx -> Q -> Rx with Q on
+ * the edge by Keller's law, kept when the receiver lies beyond the incident
+ * shadow boundary (the paper keeps sources in the receiver's shadow region)
+ * and both legs are unoccluded, with its UTD field. Record: depth 1,
+ * tri[0] = wedge | DCEM_TRI_DIFFRACT, pts[0] = Q, ray = -1. Moving objects'
+ * edges are not wedges. on = 0 turns it off. *n_wedges (may be NULL): the
+ * wedge count. Cost: one thread per (link, wedge) per frame. Errors:
+ * DCEM_ERR_ARG, DCEM_ERR_CUDA. */
+int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
 
 /* Closest-hit kernel configuration. Results never depend on it (closest hit
  * and lowest-id ties are decided by the triangle test alone):

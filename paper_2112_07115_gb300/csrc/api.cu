@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <array>
 #include <vector>
 
 #include "bvh.cuh"
@@ -235,6 +236,11 @@ struct dcem_scene {
   int* q4_scr = nullptr;         // scratch of the 4-wide mapping of large trees
   int* leaf_parent = nullptr;
   int* tri_obj_d = nullptr;  // triangle id -> rigid object (-1 static)
+  std::vector<float> tris_h;   // input vertices (static ones are world space) and objects,
+  std::vector<int> tri_obj_h;  // kept for the wedge search of edge diffraction
+  Wedge* wedges = nullptr;     // first-order diffraction: wedges of the static geometry
+  int nw = 0;
+  bool diffraction = false;
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
   int* g_param = nullptr;      // staged outputs and the error flag (dcem_path_gradients)
   double* g_out = nullptr;
@@ -356,7 +362,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
-  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d);
+  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
@@ -564,6 +570,99 @@ int ensure_rx(dcem_scene* s, int nrx, int nlinks, int bucket_cap) {
   return DCEM_OK;
 }
 
+// Wedges of the static geometry for first-order diffraction: edges whose
+// two end vertices (bit-identical coordinates) belong to exactly two static
+// triangles whose planes differ. Face 0 is the lower triangle id; the list
+// is ordered by (face 0, face n); the edge starts at its lexicographically
+// lower vertex.
+std::vector<Wedge> find_wedges(const std::vector<float>& tris, const std::vector<int>& tri_obj) {
+  struct Rec {
+    std::array<float, 3> a, b;
+    int tri;
+  };
+  auto lessv = [](const std::array<float, 3>& x, const std::array<float, 3>& y) { return x < y; };
+  const int ntri = (int)tri_obj.size();
+  std::vector<Rec> r;
+  r.reserve(3 * (size_t)ntri);
+  for (int i = 0; i < ntri; ++i) {
+    if (tri_obj[i] >= 0) continue;
+    for (int k = 0; k < 3; ++k) {
+      const float* p = &tris[9 * (size_t)i + 3 * k];
+      const float* q = &tris[9 * (size_t)i + 3 * ((k + 1) % 3)];
+      std::array<float, 3> va = {p[0], p[1], p[2]}, vb = {q[0], q[1], q[2]};
+      if (lessv(vb, va)) std::swap(va, vb);
+      r.push_back(Rec{va, vb, i});
+    }
+  }
+  std::sort(r.begin(), r.end(), [](const Rec& x, const Rec& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    return x.tri < y.tri;
+  });
+  std::vector<Wedge> out;
+  for (size_t i = 0; i < r.size();) {
+    size_t j = i + 1;
+    while (j < r.size() && r[j].a == r[i].a && r[j].b == r[i].b) ++j;
+    if (j - i == 2) {
+      int ta = std::min(r[i].tri, r[i + 1].tri), tb = std::max(r[i].tri, r[i + 1].tri);
+      double p0[3] = {r[i].a[0], r[i].a[1], r[i].a[2]};
+      double e[3] = {r[i].b[0] - p0[0], r[i].b[1] - p0[1], r[i].b[2] - p0[2]};
+      double len = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      if (len > 0.0) {
+        for (double& c : e) c /= len;
+        // directions of the two faces normal to the edge (through their third vertices)
+        double t[2][3];
+        bool ok = true;
+        const int tt[2] = {ta, tb};
+        for (int q = 0; q < 2; ++q) {
+          double v[3] = {p0[0], p0[1], p0[2]};
+          for (int k = 0; k < 3; ++k) {
+            const float* x = &tris[9 * (size_t)tt[q] + 3 * k];
+            std::array<float, 3> vx = {x[0], x[1], x[2]};
+            if (vx != r[i].a && vx != r[i].b) v[0] = x[0], v[1] = x[1], v[2] = x[2];
+          }
+          double d[3] = {v[0] - p0[0], v[1] - p0[1], v[2] - p0[2]};
+          double de = d[0] * e[0] + d[1] * e[1] + d[2] * e[2];
+          for (int c = 0; c < 3; ++c) d[c] -= de * e[c];
+          double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          if (!(l > 0.0)) ok = false;
+          for (int c = 0; c < 3; ++c) t[q][c] = ok ? d[c] / l : 0.0;
+        }
+        if (ok) {
+          double y0[3] = {e[1] * t[0][2] - e[2] * t[0][1], e[2] * t[0][0] - e[0] * t[0][2],
+                          e[0] * t[0][1] - e[1] * t[0][0]};
+          double alpha = std::atan2(t[1][0] * y0[0] + t[1][1] * y0[1] + t[1][2] * y0[2],
+                                    t[1][0] * t[0][0] + t[1][1] * t[0][1] + t[1][2] * t[0][2]);
+          if (alpha < 0.0) {
+            for (double& c : y0) c = -c;
+            alpha = -alpha;
+          }
+          for (double& c : y0) c = -c;  // the exterior runs away from face n
+          if (std::fabs(alpha - M_PI) > 1e-6 && alpha > 1e-9) {
+            Wedge w;
+            for (int c = 0; c < 3; ++c) {
+              w.p0[c] = p0[c];
+              w.e[c] = e[c];
+              w.t0[c] = t[0][c];
+              w.y0[c] = y0[c];
+            }
+            w.len = len;
+            w.n = 2.0 - alpha / M_PI;
+            w.ta = ta;
+            w.tb = tb;
+            out.push_back(w);
+          }
+        }
+      }
+    }
+    i = j;
+  }
+  std::sort(out.begin(), out.end(), [](const Wedge& x, const Wedge& y) {
+    return x.ta != y.ta ? x.ta < y.ta : x.tb < y.tb;
+  });
+  return out;
+}
+
 bool same_traversal(const dcem_params& a, const dcem_params& b) {
   return a.max_refl == b.max_refl && a.rx_radius_scale == b.rx_radius_scale && a.t_min == b.t_min &&
          a.escape_len == b.escape_len;
@@ -723,6 +822,9 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&v9, 9 * (size_t)ntri));
   CKF(dalloc(&s->tri_obj_d, ntri));
   int* tri_obj_d = s->tri_obj_d;
+  s->tris_h.assign(tris, tris + 9 * (size_t)ntri);
+  s->tri_obj_h.assign(ntri, -1);
+  if (tri_obj) std::memcpy(s->tri_obj_h.data(), tri_obj, sizeof(int) * ntri);
   CKF(dalloc(&sel_s_d, s->ns));
   cudaStream_t st = s->st;
   if (ntri > 0) {
@@ -997,6 +1099,21 @@ int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nma
   return DCEM_OK;
 }
 
+int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
+  if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
+  if (on && !s->wedges) {
+    std::vector<Wedge> w = find_wedges(s->tris_h, s->tri_obj_h);
+    s->nw = (int)w.size();
+    if (s->nw) {
+      CK(dalloc(&s->wedges, s->nw));
+      CK(cudaMemcpy(s->wedges, w.data(), sizeof(Wedge) * w.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  s->diffraction = on != 0;
+  if (n_wedges) *n_wedges = s->nw;
+  return DCEM_OK;
+}
+
 int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on) {
   if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
   s->use_graphs = on != 0;
@@ -1196,6 +1313,8 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.freq = p->freq_hz;
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
+  q.wedges = s->diffraction && s->nw > 0 ? s->wedges : nullptr;
+  q.nw = s->nw;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
   P.sticky = p->mode == DCEM_MODE_STICKY;
@@ -1272,6 +1391,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   if (P.q.sticky_prev) CK(launch_sticky_probe(P.q, sms * 4, st));
   if (tm) CK(rec(P.ev[5], st, cap));
   CK(launch_validate(P.q, sms * 4, st));
+  if (P.q.wedges) CK(launch_diffract(P.q, P.nlinks, sms * 8, st));
   if (tm) CK(rec(P.ev[6], st, cap));
   CK(launch_reduce(P.q, P.nlinks, st));
   if (tm) CK(rec(P.ev[7], st, cap));
@@ -1328,7 +1448,8 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->last_use_q = P.use_q;
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
-                 (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0);
+                 (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
+                 (P.q.wedges && P.nlinks > 0 ? 1 : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;

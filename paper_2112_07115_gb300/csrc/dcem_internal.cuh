@@ -21,6 +21,17 @@ constexpr int kMaxRaySets = 4096;       // transmitters (ray sets) per scene
 constexpr int kMaxLinks = 1 << 24;      // transmitter-receiver pairs per frame
 constexpr int kMaxBatch = 1024;         // scenes per batch
 constexpr int kTransBit = 0x40000000;   // interaction id flag: transmission (DCEM_TRI_TRANSMIT)
+constexpr int kDiffBit = 0x20000000;    // interaction id flag: diffraction at wedge id (DCEM_TRI_DIFFRACT)
+
+// A wedge of the static geometry (edge shared by two non-coplanar
+// triangles), for first-order diffraction: edge start p0 and unit direction
+// e, length, face 0's direction t0 and the exterior's angular direction y0
+// in the plane normal to e, n = exterior angle / pi, the two faces.
+struct Wedge {
+  double p0[3], e[3], t0[3], y0[3];
+  double len, n;
+  int ta, tb;
+};
 constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
 
 // device error bits (DevCounters::err)

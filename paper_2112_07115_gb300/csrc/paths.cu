@@ -563,6 +563,235 @@ __global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// first-order edge diffraction (Sec. III step 5) with the UTD
+// ---------------------------------------------------------------------------
+// Complex FP64 arithmetic for the diffraction coefficient.
+struct zd {
+  double re, im;
+};
+__device__ __forceinline__ zd Z(double r, double i = 0.0) { return zd{r, i}; }
+__device__ __forceinline__ zd operator+(zd a, zd b) { return Z(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ zd operator-(zd a, zd b) { return Z(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ zd operator*(zd a, zd b) { return Z(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+__device__ __forceinline__ zd operator*(zd a, double s) { return Z(a.re * s, a.im * s); }
+__device__ __forceinline__ zd zdiv(zd a, zd b) {
+  double d = b.re * b.re + b.im * b.im;
+  return Z((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+__device__ __forceinline__ zd zexp(zd a) {
+  double m = exp(a.re), sn, cs;
+  sincos(a.im, &sn, &cs);
+  return Z(m * cs, m * sn);
+}
+__device__ __forceinline__ zd zsqrt(zd a) {  // principal branch
+  double r = hypot(a.re, a.im);
+  double x = sqrt(0.5 * (r + fabs(a.re)));
+  if (x == 0.0) return Z(0.0, 0.0);
+  double y = a.im / (2.0 * x);
+  return a.re >= 0.0 ? Z(x, y) : Z(fabs(y), a.im >= 0.0 ? x : -x);
+}
+
+// erfc(z) for Re z > 0: the Maclaurin series of erf (Abramowitz & Stegun
+// 7.1.5) for |z| < 3, else the continued fraction of A&S 7.1.14.
+__device__ zd erfc_z(zd z) {
+  const double rsqpi = 0.56418958354775628695;  // 1/sqrt(pi)
+  double az = hypot(z.re, z.im);
+  if (az < 3.0) {
+    zd z2 = z * z, term = z, sum = z;
+    for (int n = 1; n < 200; ++n) {
+      term = term * z2 * (-1.0 / n);
+      zd t = term * (1.0 / (2 * n + 1));
+      sum = sum + t;
+      if (hypot(t.re, t.im) < 1e-17 * hypot(sum.re, sum.im)) break;
+    }
+    return Z(1.0) - sum * (2.0 * rsqpi);
+  }
+  // erfc z = e^{-z^2}/sqrt(pi) * 1/(z + (1/2)/(z + 1/(z + (3/2)/(z + ...))))
+  zd f = z;
+  for (int k = 60; k >= 1; --k) f = z + zdiv(Z(0.5 * k), f);
+  zd ez = zexp(Z(-(z.re * z.re - z.im * z.im), -2.0 * z.re * z.im));
+  return zdiv(ez * rsqpi, f);
+}
+
+// UTD transition function F(x) = 2j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt,
+// the tail integral being (sqrt(pi)/2) e^{-j pi/4} erfc(e^{j pi/4} sqrt x).
+__device__ zd transition_fn(double x) {
+  if (!(x > 0.0)) return Z(0.0);
+  double a = sqrt(x);
+  const double h = 0.70710678118654752440;
+  zd G = Z(h, -h) * erfc_z(Z(h * a, h * a)) * 0.88622692545275801365;  // sqrt(pi)/2
+  double sn, cs;
+  sincos(x, &sn, &cs);
+  return Z(0.0, 2.0 * a) * Z(cs, sn) * G;
+}
+
+__device__ zd utd_term(double n, double beta, double s, double kL, unsigned& fl) {
+  double N = rint((beta + s * M_PI) / (2.0 * M_PI * n));
+  double c = cos((2.0 * n * M_PI * N - beta) / 2.0);
+  double arg = (M_PI + s * beta) / (2.0 * n);
+  double sn = sin(arg);
+  if (fabs(sn) < 1e-9) return Z(0.0);
+  return transition_fn(kL * 2.0 * c * c) * (cos(arg) / sn);
+}
+
+// Kouyoumjian-Pathak wedge coefficient with face reflection factors r0, rn.
+__device__ zd utd_coeff(double n, double phi, double phip, double beta0, double L, double k, zd r0, zd rn,
+                        unsigned& fl) {
+  const double h = 0.70710678118654752440;
+  zd pre = Z(-h, h) * (1.0 / (2.0 * n * sqrt(2.0 * M_PI * k) * sin(beta0)));  // -e^{-j pi/4} / (...)
+  double bm = phi - phip, bp = phi + phip, kL = k * L;
+  return pre * (utd_term(n, bm, 1.0, kL, fl) + utd_term(n, bm, -1.0, kL, fl) + r0 * utd_term(n, bp, -1.0, kL, fl) +
+                rn * utd_term(n, bp, 1.0, kL, fl));
+}
+
+// Fresnel TE / TM coefficients in FP64 (eps_c = eps_r - j sigma/(w eps0)).
+__device__ void fresnel_d(float4 mt, double freq, double ct, zd& te, zd& tm) {
+  if (mt.z != 0.0f) {
+    te = Z(-1.0);
+    tm = Z(1.0);
+    return;
+  }
+  zd ec = Z((double)mt.x, -(double)mt.y / (2.0 * M_PI * freq * 8.8541878128e-12));
+  zd root = zsqrt(ec - Z(1.0 - ct * ct));
+  te = zdiv(Z(ct) - root, Z(ct) + root);
+  tm = zdiv(ec * ct - root, ec * ct + root);
+}
+
+struct d3w {
+  double x, y, z;
+};
+__device__ __forceinline__ d3w D3(double x, double y, double z) { return d3w{x, y, z}; }
+__device__ __forceinline__ d3w operator-(d3w a, d3w b) { return D3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ d3w operator+(d3w a, d3w b) { return D3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ d3w operator*(d3w a, double s) { return D3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ double dotw(d3w a, d3w b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3w crossw(d3w a, d3w b) {
+  return D3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ d3w unitw(d3w a) { return a * (1.0 / sqrt(dotw(a, a))); }
+__device__ __forceinline__ d3w polw(d3w u, d3w d, unsigned& fl) {
+  d3w p = u - d * dotw(u, d);
+  double n = sqrt(dotw(p, p));
+  if (n < 1e-9) {
+    fl |= DCEM_PATH_POL_DEGENERATE;
+    d3w a = fabs(d.x) < 0.9 ? D3(1, 0, 0) : D3(0, 1, 0);
+    p = a - d * dotw(a, d);
+    n = sqrt(dotw(p, p));
+  }
+  return p * (1.0 / n);
+}
+
+// Angle of X about the wedge, from face 0 through the exterior.
+__device__ __forceinline__ double wedge_angle(const Wedge& W, d3w X) {
+  d3w e = D3(W.e[0], W.e[1], W.e[2]);
+  d3w d = X - D3(W.p0[0], W.p0[1], W.p0[2]);
+  d = d - e * dotw(d, e);
+  double a = atan2(dotw(d, D3(W.y0[0], W.y0[1], W.y0[2])), dotw(d, D3(W.t0[0], W.t0[1], W.t0[2])));
+  return a < 0.0 ? a + 2.0 * M_PI : a;
+}
+
+// FP32 any-hit of the open segment a -> b, the two wedge faces excluded.
+__device__ __forceinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, unsigned& ovf,
+                                             TStack& st) {
+  d3w dv = q - p;
+  RayPre rp = ray_pre(f3((float)p.x, (float)p.y, (float)p.z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+  return any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st);
+}
+
+// One thread per (link, wedge): the Keller point on the edge (unfolding the
+// path about the edge line), the paper's shadow rule (the receiver beyond the
+// incident shadow boundary), both legs unoccluded, then the UTD field; a
+// valid path joins its link's bucket like a validated path.
+__global__ void __launch_bounds__(64) k_diffract(PathArgs a, int nlinks) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackTrace);
+  const long total = (long)nlinks * a.nw;
+  const double k = 2.0 * M_PI * a.freq / 299792458.0, lam = 299792458.0 / a.freq;
+  unsigned ovf = 0;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
+    const Wedge W = a.wedges[w];
+    float4 rxv = a.rx[link % a.nrx], txv = a.txs[link / a.nrx];
+    d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
+    d3w e = D3(W.e[0], W.e[1], W.e[2]), p0 = D3(W.p0[0], W.p0[1], W.p0[2]);
+    d3w dt = T - p0, dr = R - p0;
+    double zt = dotw(dt, e), zr = dotw(dr, e);
+    d3w pt = dt - e * zt, pr = dr - e * zr;
+    double rt = sqrt(dotw(pt, pt)), rr = sqrt(dotw(pr, pr));
+    if (!(rt > 0.0 && rr > 0.0)) continue;
+    double zq = zt + (zr - zt) * rt / (rt + rr);
+    double uq = zq / W.len;
+    if (!(uq > 0.0 && uq < 1.0)) continue;
+    d3w Q = p0 + e * zq;
+    double phip = wedge_angle(W, T), phi = wedge_angle(W, R), n = W.n;
+    if (phip > n * M_PI || phi > n * M_PI) continue;
+    if (!(fabs(phi - phip) > M_PI)) continue;
+    if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, R, W.ta, W.tb, ovf, st)) continue;
+    unsigned fl = 0;
+    d3w qt = Q - T, rq = R - Q;
+    double sp = sqrt(dotw(qt, qt)), s = sqrt(dotw(rq, rq));
+    d3w ip = qt * (1.0 / sp), dd = rq * (1.0 / s);
+    double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
+    double sb = sin(beta0);
+    double L = s * sp * sb * sb / (s + sp);
+    d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
+    d3w bp = crossw(ip, php), bd = crossw(dd, ph);
+    // Luebbers: the faces' Fresnel factors at the grazing angles phi' and n pi - phi
+    const float4 ma = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.ta] + 1].w)];
+    const float4 mb = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.tb] + 1].w)];
+    zd r0s, r0h, rns, rnh;
+    fresnel_d(ma, a.freq, fabs(sin(phip)), r0s, r0h);
+    fresnel_d(mb, a.freq, fabs(sin(n * M_PI - phi)), rns, rnh);
+    zd Ds = utd_coeff(n, phi, phip, beta0, L, k, r0s, rns, fl);
+    zd Dh = utd_coeff(n, phi, phip, beta0, L, k, r0h, rnh, fl);
+    d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
+    d3w e0 = polw(u, ip, fl), prx = polw(u, dd * -1.0, fl);
+    double sn, cs;
+    sincos(-k * sp, &sn, &cs);
+    zd Ei = Z(cs / sp, sn / sp);
+    zd Eb = Ei * dotw(e0, bp), Ep = Ei * dotw(e0, php);
+    sincos(-k * s, &sn, &cs);
+    zd A = Z(cs, sn) * sqrt(sp / (s * (s + sp)));
+    zd proj = (Ds * Eb) * (-dotw(bd, prx)) + (Dh * Ep) * (-dotw(ph, prx));
+    zd amp = proj * A * (lam / (4.0 * M_PI));
+    unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
+    if (uu >= a.ucap) {
+      atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
+      continue;
+    }
+    PathRec rec;
+    int id = w | kDiffBit;
+    rec.key = seq_key(link % a.nrx, 1, [&](int) { return id; });
+    rec.rx = link;
+    rec.depth = 1;
+    rec.ray = -1;
+    rec.flags = fl;
+    rec.valid = 1;
+    rec.pad = 0;
+    rec.len = sp + s;
+    rec.amp_re = amp.re;
+    rec.amp_im = amp.im;
+    for (int j = 0; j < kMaxRefl; ++j) {
+      rec.tri[j] = j == 0 ? id : -1;
+      rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
+    }
+    rec.pts[0][0] = (float)Q.x;
+    rec.pts[0][1] = (float)Q.y;
+    rec.pts[0][2] = (float)Q.z;
+    a.prec[uu] = rec;
+    unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
+    if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
+    else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+    atomicAdd(&a.ctr->n_valid, 1u);
+  }
+  if (ovf) {
+    atomicAdd(&a.ctr->stack_overflow, 1u);
+    atomicOr(&a.ctr->err, ERR_STACK);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // per link: sort paths by key, sum in that order, write them out
 // ---------------------------------------------------------------------------
 constexpr int kReduceThreads = 256;
@@ -697,6 +926,12 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
 cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
   k_dedupe_insert<<<grid, 256, 0, st>>>(a);
   k_dedupe_unique<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diffract(const PathArgs& a, int nlinks, int grid, cudaStream_t st) {
+  if (!a.wedges || a.nw <= 0 || nlinks <= 0) return cudaSuccess;
+  k_diffract<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a, nlinks);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,9 @@ struct PathArgs {
   // sticky mode (null otherwise): the previous frame's valid paths, to be
   // re-validated when no capture of this frame has their key, and the
   // buffer that keeps this frame's valid paths for the next one
+  // first-order edge diffraction (null: off)
+  const Wedge* wedges;
+  int nw;
   const StickyKey* sticky_prev;
   const unsigned* sticky_prev_n;
   unsigned sticky_cap;
@@ -59,6 +62,8 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st);
 // frame has join the distinct keys (validated like them).
 cudaError_t launch_sticky_probe(const PathArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st);
+// First-order edge diffraction paths of every (link, wedge) (after validation).
+cudaError_t launch_diffract(const PathArgs& a, int nlinks, int grid, cudaStream_t st);
 // Per-link sums and ordered output; links above kScanLinks take their output
 // offsets from a scan (a.link_off) instead of summing the lower links' counts.
 constexpr int kScanLinks = 4096;

@@ -26,6 +26,7 @@ PTR_HOST, PTR_DEVICE = 0, 1
 PATH_POL_DEGENERATE = 1
 PATH_STICKY = 2
 TRI_TRANSMIT = 0x40000000
+TRI_DIFFRACT = 0x20000000
 
 EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_update_transforms", "dcem_trace_frame", "dcem_scene_reset_cache",
@@ -36,7 +37,7 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
             "dcem_scene_set_trace_config", "dcem_scene_autotune", "dcem_batch_create",
             "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy",
-            "dcem_scene_set_transmission"]
+            "dcem_scene_set_transmission", "dcem_scene_set_diffraction"]
 
 
 class Material(C.Structure):
@@ -109,6 +110,7 @@ def lib():
         L.dcem_trace_links.argtypes = [vp, vp, i32, vp, i32, i32, P(Params), P(Result)]
         L.dcem_scene_set_trace_config.argtypes = [vp, i32, i32, i32]
         L.dcem_scene_set_transmission.argtypes = [vp, vp, i32, i32]
+        L.dcem_scene_set_diffraction.argtypes = [vp, i32, P(i32)]
         L.dcem_batch_create.argtypes = [vp, i32, vp, P(vp)]
         L.dcem_batch_update_transforms.argtypes = [vp, vp, i32]
         L.dcem_batch_trace.argtypes = [vp, vp, vp, vp, vp, i32, P(Params), vp, P(i32)]
@@ -234,6 +236,12 @@ def dcem_scene_set_transmission(h, loss_db, max_trans: int):
     a = np.ascontiguousarray(loss_db, np.float32).reshape(-1)
     _check(lib().dcem_scene_set_transmission(h, a.ctypes.data if a.size else None, a.size, int(max_trans)),
            "dcem_scene_set_transmission")
+
+
+def dcem_scene_set_diffraction(h, on: bool) -> int:
+    n = C.c_int32(0)
+    _check(lib().dcem_scene_set_diffraction(h, int(bool(on)), C.byref(n)), "dcem_scene_set_diffraction")
+    return n.value
 
 
 def dcem_scene_set_trace_config(h, kernel: int, block: int = 256, stack: int = 24):
@@ -493,6 +501,10 @@ class Scene:
         """Per-material penetration loss [dB] (< 0 opaque) and transmissions per path."""
         dcem_scene_set_transmission(self.h, loss_db, max_trans)
         self.max_trans = int(max_trans)
+
+    def set_diffraction(self, on: bool = True) -> int:
+        """First-order edge diffraction paths (UTD); returns the wedge count."""
+        return dcem_scene_set_diffraction(self.h, on)
 
     def set_trace_config(self, kernel: int, block: int = 256, stack: int = 24):
         dcem_scene_set_trace_config(self.h, kernel, block, stack)

@@ -103,6 +103,7 @@ def test_null_scene_calls(L):
     assert lib.dcem_batch_trace(None, None, None, None, None, 0, C.byref(p), None, None) == L.ERR_ARG
     lib.dcem_batch_destroy(None)
     assert lib.dcem_scene_set_transmission(None, None, 0, 1) == L.ERR_ARG
+    assert lib.dcem_scene_set_diffraction(None, 1, None) == L.ERR_ARG
     assert lib.dcem_scene_autotune(None, tx, 1, None, 0, 0, C.byref(p), 1, None, None, None) == L.ERR_ARG
     n = (C.c_int32 * 1)(4)
     assert lib.dcem_scene_set_ray_sets(None, None, n, 1) == L.ERR_ARG
