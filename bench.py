@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--batched-frames", type=int, default=8)
     ap.add_argument("--no-multi-scene", action="store_true", help="skip the multi-scene batch workload")
     ap.add_argument("--no-transmission", action="store_true", help="skip the indoor transmission workload")
+    ap.add_argument("--no-diffraction", action="store_true", help="skip the diffraction measurement")
     return ap.parse_args()
 
 
@@ -366,6 +367,9 @@ def run_ours(args):
     trans = None
     if not args.no_transmission:
         trans = run_transmission(args, stream, dev, world, flush, rank)
+    diff = None
+    if not args.no_diffraction:
+        diff = run_diffraction(args, sc, rays, stream, dev, world, flush)
 
     e2e = None
     if not args.no_e2e:
@@ -404,6 +408,7 @@ def run_ours(args):
             "batched": batched,
             "multi_scene": multi,
             "transmission": trans,
+            "diffraction": diff,
             "full": {"frames_per_s": round(fps_full, 2), "ms_per_frame": round(1e3 * t_full / K, 4),
                      "ray_segments_per_s": round(seg_full, 0), "segments_per_frame": int(seg_mean),
                      "nodes_per_segment": round(nodes_per_seg, 2), "tris_per_segment": round(tris_per_seg, 2),
@@ -682,6 +687,62 @@ def run_transmission(args, stream, dev, world, flush, rank, warmup=3):
             "oracle_invalid": int((ref["valid"] == 0).sum()),
             "max_abs_p_coh": float(np.max(np.abs(pc[fin] - gc[fin]))) if fin.any() else 0.0,
             "max_abs_p_inc": float(np.max(np.abs(pi[fin] - gi[fin]))) if fin.any() else 0.0}
+    return out
+
+
+def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
+    """First-order edge diffraction on the headline highway frames (coherent
+    mode, every frame adds the diffraction paths of every (receiver, wedge)
+    pair): frames/s with and without it, the wedge count and the
+    diffraction paths per frame."""
+    import ctypes as C
+    import torch
+    from paper_2112_07115_gb300 import dcem
+    K = args.batched_frames * 4
+    xf_d = torch.from_numpy(sc.xf).to(dev)
+    rx_d = torch.from_numpy(sc.rx).to(dev)
+    nrx, max_paths = sc.nrx, 1 << 17
+    bufs = [torch.empty((nrx, 2), dtype=torch.float64, device=dev), torch.empty(nrx, dtype=torch.float64, device=dev),
+            torch.empty(nrx, dtype=torch.float64, device=dev),
+            torch.empty(max_paths * C.sizeof(dcem.Path), dtype=torch.uint8, device=dev)]
+    out = {}
+    for on in (True, False):
+        s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+        s.set_rays(rays)
+        nw = s.set_diffraction(on)
+        prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=dcem.MODE_COHERENT)
+        res = dcem.Result()
+        res.ptr_kind = dcem.PTR_DEVICE
+        res.max_paths = max_paths
+        res.field, res.p_coh_dbm, res.p_inc_dbm, res.paths = [x.data_ptr() for x in bufs]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, nd = [], []
+        for i in range(warmup + K):
+            f = i + 1
+            flush.zero_()
+            e0.record(stream)
+            dcem.dcem_scene_update_transforms(s.h, xf_d[f])
+            rc = dcem.dcem_trace_frame(s.h, sc.tx, rx_d[f], prm, res)
+            e1.record(stream)
+            e1.synchronize()
+            if rc != dcem.OK:
+                raise dcem.DcemError(rc, f"diffraction frame {f}")
+            if i >= warmup:
+                ms.append(e0.elapsed_time(e1))
+                if on:
+                    n = min(res.n_paths, max_paths)
+                    p = bufs[3][: n * C.sizeof(dcem.Path)].cpu().numpy().view(dcem.PATH_DTYPE)
+                    nd.append(int(np.sum((p["tri"][:, 0] & dcem.TRI_DIFFRACT) != 0)))
+        s.close()
+        t = max_over_ranks([sum(ms) / 1e3], dev)[0]
+        if on:
+            out.update({"wedges": nw, "frames_per_s": round(world * K / t, 2), "ms_per_frame": round(1e3 * t / K, 4),
+                        "diffraction_paths_per_frame": round(float(np.mean(nd)), 1),
+                        "receiver_wedge_pairs_per_frame": nw * nrx})
+        else:
+            out["without_diffraction_frames_per_s"] = round(world * K / t, 2)
+    out["workload"] = ("highway frames (coherent), first-order UTD diffraction at the barrier wedges for all 200 "
+                       "receivers")
     return out
 
 
