@@ -500,7 +500,13 @@ def run_batched(args, stream, dev, world, flush, warmup=2):
         t = max_over_ranks([sum(ms) / 1e3], dev)[0]
         segs = float(np.mean([x["segments_traced"] for x in st]))
         trace_ms = float(np.mean([x["ms_stage"]["trace"] for x in st]))
+        tb = float(np.mean([x["rays_retraced"] * 36 + x["segments_traced"] * 36 + x["node_visits"] * 64 +
+                            x["tri_tests"] * 48 for x in st]))
+        peak, _ = measured_peaks()
         out[name] = {"frames_per_s": round(world * K / t, 3), "ms_per_frame": round(1e3 * t / K, 3),
+                     "trace_roofline": {"achieved": round(tb / (trace_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                                        "frac": round(tb / (trace_ms * 1e-3) / 1e9 / peak, 4),
+                                        "note": "algorithmic bytes of the closest-hit kernel (nodes from L2)"},
                      "rays_per_s": round(world * K * sum(budgets) / t, 0),
                      "segments_traced_per_frame": int(segs),
                      "ray_segments_traced_per_s": round(world * K * segs / t, 0),
@@ -606,6 +612,19 @@ def run_multi_scene(args, stream, dev, world, flush, warmup=2):
                                   "ms_per_frame": round(1e3 * t_seq / K, 3)}}
 
 
+def _trace_roof(st):
+    """Closest-hit roofline of timed frames (stats with timing=2): the
+    survey's algorithmic bytes (36 B per ray and per segment, 64 B per node
+    pair, 48 B per triangle test) over the kernel time, of the measured HBM
+    copy bandwidth."""
+    peak, _ = measured_peaks()
+    b = float(np.mean([(x["n_rays"] + x["child_rays"]) * 36 + x["segments_traced"] * 36 + x["node_visits"] * 64 +
+                       x["tri_tests"] * 48 for x in st]))
+    ms = float(np.mean([x["ms_stage"]["trace"] for x in st]))
+    ach = b / (ms * 1e-3) / 1e9
+    return {"achieved": round(ach, 1), "unit": "GB/s", "frac": round(ach / peak, 4)}
+
+
 def run_transmission(args, stream, dev, world, flush, rank, warmup=3):
     """Transmission (Table II penetration losses): the indoor office (12
     rooms, 262 triangles, indoor walls 20 dB, glass 5 dB, 4 moving metal
@@ -662,6 +681,7 @@ def run_transmission(args, stream, dev, world, flush, rank, warmup=3):
            "segments_traced_per_frame": int(segs),
            "ray_segments_traced_per_s": round(world * K * segs / t, 0),
            "closest_hit_ms_all_passes": round(float(np.mean([x["ms_stage"]["trace"] for x in st])), 4),
+           "trace_roofline": _trace_roof(st),
            "paths_per_frame": int(np.mean([x["paths_valid"] for x in st]))}
     if rank == 0:
         # the last frame's paths re-validated by the FP64 oracle

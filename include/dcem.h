@@ -290,15 +290,16 @@ int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nma
 /* First-order edge diffraction (Sec. III step 5; uniform theory of
  * diffraction after Kouyoumjian & Pathak, Proc. IEEE 1974, with Luebbers'
  * finite-conductivity face factors, IEEE Trans. AP 1984). on = 1 finds the
- * wedges of the static geometry once: edges whose two vertices (identical
- * coordinates) belong to exactly two static triangles with different planes,
- * numbered in the order of their faces' (lower, higher) triangle ids. Every
+ * wedges once: edges whose two vertices (identical input coordinates) belong
+ * to exactly two triangles of the same rigid object (or both static) with
+ * different planes, numbered in the order of their faces' (lower, higher)
+ * triangle ids; moving objects' wedges follow their objects. Every
  * frame then adds, for each (link, wedge), the path Tx -> Q -> Rx with Q on
  * the edge by Keller's law, kept when the receiver lies beyond the incident
  * shadow boundary (the paper keeps sources in the receiver's shadow region)
  * and both legs are unoccluded, with its UTD field. Record: depth 1,
- * tri[0] = wedge | DCEM_TRI_DIFFRACT, pts[0] = Q, ray = -1. Moving objects'
- * edges are not wedges. on = 0 turns it off. *n_wedges (may be NULL): the
+ * tri[0] = wedge | DCEM_TRI_DIFFRACT, pts[0] = Q, ray = -1. on = 0 turns it
+ * off. *n_wedges (may be NULL): the
  * wedge count. Cost: one thread per (link, wedge) per frame. Errors:
  * DCEM_ERR_ARG, DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
@@ -415,8 +416,9 @@ int dcem_scene_get_bvh(dcem_scene* s, int32_t* child, float* bounds, int32_t* ro
 int dcem_scene_get_ray_log(dcem_scene* s, int32_t* hit_id, float* hit_t, int32_t* nseg);
 
 /* Reception-sphere captures of the last traced frame as (ray, segment, rx)
- * int32 triples in unspecified order. *n receives the count; at most cap
- * triples are written (DCEM_ERR_CAPACITY if cap < count). */
+ * int32 triples in unspecified order (rx: the link t * nrx + r with several
+ * transmitters; ray: a transmission child's primary ray). *n receives the
+ * count; at most cap triples are written (DCEM_ERR_CAPACITY if cap < count). */
 int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t* n);
 
 /* ---- received power without device allocation ---- */
@@ -452,8 +454,9 @@ int dcem_scene_gradient_size(const dcem_scene* s, int32_t* n_params);
  * repeated calls give identical results. The call synchronises the scene
  * stream. Errors: DCEM_ERR_ARG (null or out-of-range arguments, paths not
  * grouped by receiver, a depth above max_refl, a triangle id out of range, a
- * triangle sequence without reflection geometry), DCEM_ERR_NONFINITE,
- * DCEM_ERR_CUDA. */
+ * triangle sequence without reflection geometry; transmission and
+ * diffraction records are not differentiated and are argument errors),
+ * DCEM_ERR_NONFINITE, DCEM_ERR_CUDA. */
 int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
                         const dcem_path* paths, int32_t n_paths, const dcem_params* params, int32_t ptr_kind,
                         double* field, double* dfield, double* dpcoh_dbm);

@@ -32,8 +32,9 @@
  *                  penetration loss at each transmission.
  *   or_fresnel     Fresnel reflection coefficients.
  *   or_diffract    step 5, first order: edge diffraction paths Tx -> Q -> Rx
- *                  over the wedges of the static geometry (edges shared by
- *                  two non-coplanar triangles), Q on the edge by Keller's law,
+ *                  over the wedges of the scene (edges shared by two
+ *                  non-coplanar triangles of one rigid object or both
+ *                  static), Q on the edge by Keller's law,
  *                  kept when the receiver lies in the source's shadow region
  *                  behind the wedge and both legs are unoccluded; field by the
  *                  uniform theory of diffraction (UTD): R. G. Kouyoumjian and
@@ -1111,9 +1112,10 @@ void or_utd(double n, double phi, double phip, double beta0, double L, double k,
   out2[1] = cimag(d);
 }
 
-/* Wedges of the static geometry: edges shared by exactly two static
- * triangles (identical vertex coordinates) whose planes differ. Edge list in
- * (lower triangle id, higher triangle id) order; face 0 is the lower id. */
+/* Wedges: edges shared by exactly two triangles of the same rigid object
+ * (or both static) with identical world vertex coordinates, whose planes
+ * differ. Edge list in (lower triangle id, higher triangle id) order; face 0
+ * is the lower id. */
 typedef struct {
   int ta, tb;       /* faces 0 and n                                   */
   v3 p0, e;         /* edge start and unit direction                   */
@@ -1128,11 +1130,12 @@ static int vkey_cmp(const float* a, const float* b) {
   return 0;
 }
 
-typedef struct { float a[3], b[3]; int tri; } oedge_rec;
+typedef struct { float a[3], b[3]; int tri, obj; } oedge_rec;
 
 static int oedge_cmp(const void* x, const void* y) {
   const oedge_rec* p = (const oedge_rec*)x;
   const oedge_rec* q = (const oedge_rec*)y;
+  if (p->obj != q->obj) return p->obj < q->obj ? -1 : 1;
   int c = vkey_cmp(p->a, q->a);
   if (c) return c;
   c = vkey_cmp(p->b, q->b);
@@ -1151,7 +1154,6 @@ static long find_wedges(const float* tris, const int32_t* tri_obj, int ntri, owe
   oedge_rec* r = (oedge_rec*)malloc(sizeof(oedge_rec) * (size_t)(3 * ntri + 1));
   long m = 0;
   for (int i = 0; i < ntri; ++i) {
-    if (tri_obj && tri_obj[i] >= 0) continue;
     for (int k = 0; k < 3; ++k) {
       const float* a = &tris[9 * i + 3 * k];
       const float* b = &tris[9 * i + 3 * ((k + 1) % 3)];
@@ -1159,6 +1161,7 @@ static long find_wedges(const float* tris, const int32_t* tri_obj, int ntri, owe
       if (vkey_cmp(a, b) <= 0) { memcpy(e->a, a, 12); memcpy(e->b, b, 12); }
       else { memcpy(e->a, b, 12); memcpy(e->b, a, 12); }
       e->tri = i;
+      e->obj = tri_obj ? tri_obj[i] : -1;
     }
   }
   qsort(r, (size_t)m, sizeof(oedge_rec), oedge_cmp);
@@ -1166,7 +1169,7 @@ static long find_wedges(const float* tris, const int32_t* tri_obj, int ntri, owe
   long nw = 0;
   for (long i = 0; i < m;) {
     long j = i + 1;
-    while (j < m && !vkey_cmp(r[j].a, r[i].a) && !vkey_cmp(r[j].b, r[i].b)) ++j;
+    while (j < m && r[j].obj == r[i].obj && !vkey_cmp(r[j].a, r[i].a) && !vkey_cmp(r[j].b, r[i].b)) ++j;
     if (j - i == 2) {
       int ta = r[i].tri < r[i + 1].tri ? r[i].tri : r[i + 1].tri;
       int tb = r[i].tri < r[i + 1].tri ? r[i + 1].tri : r[i].tri;

@@ -238,7 +238,8 @@ struct dcem_scene {
   int* tri_obj_d = nullptr;  // triangle id -> rigid object (-1 static)
   std::vector<float> tris_h;   // input vertices (static ones are world space) and objects,
   std::vector<int> tri_obj_h;  // kept for the wedge search of edge diffraction
-  Wedge* wedges = nullptr;     // first-order diffraction: wedges of the static geometry
+  Wedge* wedges = nullptr;     // first-order diffraction: wedge geometry (per frame)
+  WedgeTopo* wtopo = nullptr;  // ... and topology
   int nw = 0;
   bool diffraction = false;
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
@@ -362,7 +363,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
-  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges);
+  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
@@ -570,94 +571,73 @@ int ensure_rx(dcem_scene* s, int nrx, int nlinks, int bucket_cap) {
   return DCEM_OK;
 }
 
-// Wedges of the static geometry for first-order diffraction: edges whose
-// two end vertices (bit-identical coordinates) belong to exactly two static
-// triangles whose planes differ. Face 0 is the lower triangle id; the list
-// is ordered by (face 0, face n); the edge starts at its lexicographically
-// lower vertex.
-std::vector<Wedge> find_wedges(const std::vector<float>& tris, const std::vector<int>& tri_obj) {
+// Wedges for first-order diffraction: edges whose two end vertices
+// (bit-identical input coordinates: world space for static triangles, object
+// space for moving ones, which a rigid transform maps alike) belong to
+// exactly two triangles of the same rigid object (or both static) whose
+// planes differ. Face 0 is the lower triangle id; the list is ordered by
+// (face 0, face n). The geometry follows the objects every frame
+// (k_wedge_geom); here only the topology is kept.
+std::vector<WedgeTopo> find_wedges(const std::vector<float>& tris, const std::vector<int>& tri_obj) {
   struct Rec {
+    int obj;
     std::array<float, 3> a, b;
-    int tri;
+    int tri, k0, k1;
   };
-  auto lessv = [](const std::array<float, 3>& x, const std::array<float, 3>& y) { return x < y; };
   const int ntri = (int)tri_obj.size();
   std::vector<Rec> r;
   r.reserve(3 * (size_t)ntri);
-  for (int i = 0; i < ntri; ++i) {
-    if (tri_obj[i] >= 0) continue;
+  for (int i = 0; i < ntri; ++i)
     for (int k = 0; k < 3; ++k) {
       const float* p = &tris[9 * (size_t)i + 3 * k];
       const float* q = &tris[9 * (size_t)i + 3 * ((k + 1) % 3)];
       std::array<float, 3> va = {p[0], p[1], p[2]}, vb = {q[0], q[1], q[2]};
-      if (lessv(vb, va)) std::swap(va, vb);
-      r.push_back(Rec{va, vb, i});
+      int k0 = k, k1 = (k + 1) % 3;
+      if (vb < va) {
+        std::swap(va, vb);
+        std::swap(k0, k1);
+      }
+      r.push_back(Rec{tri_obj[i], va, vb, i, k0, k1});
     }
-  }
   std::sort(r.begin(), r.end(), [](const Rec& x, const Rec& y) {
+    if (x.obj != y.obj) return x.obj < y.obj;
     if (x.a != y.a) return x.a < y.a;
     if (x.b != y.b) return x.b < y.b;
     return x.tri < y.tri;
   });
-  std::vector<Wedge> out;
+  std::vector<WedgeTopo> out;
   for (size_t i = 0; i < r.size();) {
     size_t j = i + 1;
-    while (j < r.size() && r[j].a == r[i].a && r[j].b == r[i].b) ++j;
+    while (j < r.size() && r[j].obj == r[i].obj && r[j].a == r[i].a && r[j].b == r[i].b) ++j;
     if (j - i == 2) {
-      int ta = std::min(r[i].tri, r[i + 1].tri), tb = std::max(r[i].tri, r[i + 1].tri);
-      double p0[3] = {r[i].a[0], r[i].a[1], r[i].a[2]};
-      double e[3] = {r[i].b[0] - p0[0], r[i].b[1] - p0[1], r[i].b[2] - p0[2]};
+      const Rec& A = r[i].tri < r[i + 1].tri ? r[i] : r[i + 1];
+      const Rec& B = r[i].tri < r[i + 1].tri ? r[i + 1] : r[i];
+      // the third vertex of each face: the one off the edge
+      int kat = 3 - A.k0 - A.k1, kbt = 3 - B.k0 - B.k1;
+      double p0[3] = {A.a[0], A.a[1], A.a[2]};
+      double e[3] = {A.b[0] - p0[0], A.b[1] - p0[1], A.b[2] - p0[2]};
       double len = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-      if (len > 0.0) {
-        for (double& c : e) c /= len;
-        // directions of the two faces normal to the edge (through their third vertices)
-        double t[2][3];
-        bool ok = true;
-        const int tt[2] = {ta, tb};
-        for (int q = 0; q < 2; ++q) {
-          double v[3] = {p0[0], p0[1], p0[2]};
-          for (int k = 0; k < 3; ++k) {
-            const float* x = &tris[9 * (size_t)tt[q] + 3 * k];
-            std::array<float, 3> vx = {x[0], x[1], x[2]};
-            if (vx != r[i].a && vx != r[i].b) v[0] = x[0], v[1] = x[1], v[2] = x[2];
-          }
-          double d[3] = {v[0] - p0[0], v[1] - p0[1], v[2] - p0[2]};
-          double de = d[0] * e[0] + d[1] * e[1] + d[2] * e[2];
-          for (int c = 0; c < 3; ++c) d[c] -= de * e[c];
-          double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-          if (!(l > 0.0)) ok = false;
-          for (int c = 0; c < 3; ++c) t[q][c] = ok ? d[c] / l : 0.0;
-        }
-        if (ok) {
-          double y0[3] = {e[1] * t[0][2] - e[2] * t[0][1], e[2] * t[0][0] - e[0] * t[0][2],
-                          e[0] * t[0][1] - e[1] * t[0][0]};
-          double alpha = std::atan2(t[1][0] * y0[0] + t[1][1] * y0[1] + t[1][2] * y0[2],
-                                    t[1][0] * t[0][0] + t[1][1] * t[0][1] + t[1][2] * t[0][2]);
-          if (alpha < 0.0) {
-            for (double& c : y0) c = -c;
-            alpha = -alpha;
-          }
-          for (double& c : y0) c = -c;  // the exterior runs away from face n
-          if (std::fabs(alpha - M_PI) > 1e-6 && alpha > 1e-9) {
-            Wedge w;
-            for (int c = 0; c < 3; ++c) {
-              w.p0[c] = p0[c];
-              w.e[c] = e[c];
-              w.t0[c] = t[0][c];
-              w.y0[c] = y0[c];
-            }
-            w.len = len;
-            w.n = 2.0 - alpha / M_PI;
-            w.ta = ta;
-            w.tb = tb;
-            out.push_back(w);
-          }
-        }
+      double t[2][3];
+      bool ok = len > 0.0;
+      const int tt[2] = {A.tri, B.tri}, kk[2] = {kat, kbt};
+      for (int q = 0; q < 2 && ok; ++q) {
+        const float* x = &tris[9 * (size_t)tt[q] + 3 * kk[q]];
+        double d[3] = {x[0] - p0[0], x[1] - p0[1], x[2] - p0[2]};
+        double de = (d[0] * e[0] + d[1] * e[1] + d[2] * e[2]) / (len * len);
+        for (int c = 0; c < 3; ++c) d[c] -= de * e[c];
+        double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!(l > 0.0)) ok = false;
+        for (int c = 0; c < 3; ++c) t[q][c] = ok ? d[c] / l : 0.0;
+      }
+      if (ok) {
+        double cosa = t[0][0] * t[1][0] + t[0][1] * t[1][1] + t[0][2] * t[1][2];
+        double alpha = std::acos(std::max(-1.0, std::min(1.0, cosa)));
+        if (std::fabs(alpha - M_PI) > 1e-6 && alpha > 1e-9) out.push_back(WedgeTopo{A.tri, B.tri, A.k0, A.k1, kat, kbt});
       }
     }
     i = j;
   }
-  std::sort(out.begin(), out.end(), [](const Wedge& x, const Wedge& y) {
+  std::sort(out.begin(), out.end(), [](const WedgeTopo& x, const WedgeTopo& y) {
     return x.ta != y.ta ? x.ta < y.ta : x.tb < y.tb;
   });
   return out;
@@ -1101,12 +1081,13 @@ int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nma
 
 int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
   if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
-  if (on && !s->wedges) {
-    std::vector<Wedge> w = find_wedges(s->tris_h, s->tri_obj_h);
+  if (on && !s->wtopo) {
+    std::vector<WedgeTopo> w = find_wedges(s->tris_h, s->tri_obj_h);
     s->nw = (int)w.size();
     if (s->nw) {
+      CK(dalloc(&s->wtopo, s->nw));
       CK(dalloc(&s->wedges, s->nw));
-      CK(cudaMemcpy(s->wedges, w.data(), sizeof(Wedge) * w.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(s->wtopo, w.data(), sizeof(WedgeTopo) * w.size(), cudaMemcpyHostToDevice));
     }
   }
   s->diffraction = on != 0;
@@ -1314,6 +1295,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
   q.wedges = s->diffraction && s->nw > 0 ? s->wedges : nullptr;
+  q.wtopo = s->wtopo;
   q.nw = s->nw;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
@@ -1449,7 +1431,7 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
-                 (P.q.wedges && P.nlinks > 0 ? 1 : 0);
+                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -2080,9 +2062,17 @@ int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t*
   std::vector<Cand> c(s->last_ncand);
   CK(cudaStreamSynchronize(s->st));
   CK(cudaMemcpy(c.data(), s->cand[s->cur], sizeof(Cand) * c.size(), cudaMemcpyDeviceToHost));
+  // a transmission child's capture is reported with its primary ray
+  std::vector<int> root;
+  if (s->child_cap > 0 && s->inst_root) {
+    root.resize(s->child_cap);
+    CK(cudaMemcpy(root.data(), s->inst_root, sizeof(int) * root.size(), cudaMemcpyDeviceToHost));
+  }
   int64_t m = std::min<int64_t>(cap, (int64_t)c.size());
   for (int64_t i = 0; i < m; ++i) {
-    out[3 * i] = s->ray_perm_h[c[i].ray];
+    int r = c[i].ray;
+    if (r >= s->R) r = r - s->R < (int)root.size() ? root[r - s->R] : -1;
+    out[3 * i] = r >= 0 && r < s->R ? s->ray_perm_h[r] : -1;
     out[3 * i + 1] = cand_seg(c[i]);
     out[3 * i + 2] = cand_rx(c[i]);
   }

@@ -32,6 +32,13 @@ struct Wedge {
   double len, n;
   int ta, tb;
 };
+
+// Wedge topology (fixed for a rigid object): faces ta < tb, the local
+// indices of the edge's vertices in ta and of the faces' third vertices.
+struct WedgeTopo {
+  int ta, tb;
+  int ka0, ka1, kat, kbt;
+};
 constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
 
 // device error bits (DevCounters::err)

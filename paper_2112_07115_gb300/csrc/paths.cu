@@ -698,6 +698,55 @@ __device__ __forceinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, in
   return any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st);
 }
 
+// Wedge geometry from the current world triangles (moving objects' wedges
+// follow their objects): the edge from its lexicographically lower vertex,
+// the faces' directions normal to it, and n = exterior angle / pi.
+__device__ __forceinline__ bool vless(float4 a, float4 b) {
+  if (a.x != b.x) return a.x < b.x;
+  if (a.y != b.y) return a.y < b.y;
+  return a.z < b.z;
+}
+
+__global__ void k_wedge_geom(const float4* __restrict__ tris, const int* __restrict__ slot_of_id,
+                             const WedgeTopo* __restrict__ topo, int nw, Wedge* out) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+    WedgeTopo t = topo[w];
+    const float4* A = tris + 3 * (size_t)slot_of_id[t.ta];
+    const float4* B = tris + 3 * (size_t)slot_of_id[t.tb];
+    float4 va = A[t.ka0], vb = A[t.ka1], vt = A[t.kat], vu = B[t.kbt];
+    if (vless(vb, va)) {
+      float4 x = va;
+      va = vb;
+      vb = x;
+    }
+    Wedge W;
+    d3w p0 = D3(va.x, va.y, va.z), e = D3((double)vb.x - va.x, (double)vb.y - va.y, (double)vb.z - va.z);
+    double len = sqrt(dotw(e, e));
+    e = e * (1.0 / len);
+    d3w da = D3((double)vt.x - va.x, (double)vt.y - va.y, (double)vt.z - va.z);
+    d3w db = D3((double)vu.x - va.x, (double)vu.y - va.y, (double)vu.z - va.z);
+    da = da - e * dotw(da, e);
+    db = db - e * dotw(db, e);
+    d3w t0 = da * (1.0 / sqrt(dotw(da, da))), tB = db * (1.0 / sqrt(dotw(db, db)));
+    d3w y0 = crossw(e, t0);
+    double alpha = atan2(dotw(tB, y0), dotw(tB, t0));
+    if (alpha < 0.0) {
+      y0 = y0 * -1.0;
+      alpha = -alpha;
+    }
+    y0 = y0 * -1.0;  // the exterior runs away from face n
+    W.p0[0] = p0.x; W.p0[1] = p0.y; W.p0[2] = p0.z;
+    W.e[0] = e.x; W.e[1] = e.y; W.e[2] = e.z;
+    W.t0[0] = t0.x; W.t0[1] = t0.y; W.t0[2] = t0.z;
+    W.y0[0] = y0.x; W.y0[1] = y0.y; W.y0[2] = y0.z;
+    W.len = len;
+    W.n = 2.0 - alpha / M_PI;
+    W.ta = t.ta;
+    W.tb = t.tb;
+    out[w] = W;
+  }
+}
+
 // One thread per (link, wedge): the Keller point on the edge (unfolding the
 // path about the edge line), the paper's shadow rule (the receiver beyond the
 // incident shadow boundary), both legs unoccluded, then the UTD field; a
@@ -930,8 +979,9 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_diffract(const PathArgs& a, int nlinks, int grid, cudaStream_t st) {
-  if (!a.wedges || a.nw <= 0 || nlinks <= 0) return cudaSuccess;
-  k_diffract<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a, nlinks);
+  if (!a.wedges || a.nw <= 0) return cudaSuccess;
+  k_wedge_geom<<<(a.nw + 255) / 256, 256, 0, st>>>(a.tris, a.slot_of_id, a.wtopo, a.nw, a.wedges);
+  if (nlinks > 0) k_diffract<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a, nlinks);
   return cudaGetLastError();
 }
 

@@ -49,7 +49,8 @@ struct PathArgs {
   // re-validated when no capture of this frame has their key, and the
   // buffer that keeps this frame's valid paths for the next one
   // first-order edge diffraction (null: off)
-  const Wedge* wedges;
+  Wedge* wedges;                  // geometry, rebuilt every frame from the world triangles
+  const WedgeTopo* wtopo;
   int nw;
   const StickyKey* sticky_prev;
   const unsigned* sticky_prev_n;

@@ -128,3 +128,11 @@ def test_diffraction_off_and_links(cuda):
         assert np.array_equal(fl.p_coh_dbm[t], single.p_coh_dbm)
     for s in (a, b, sl):
         s.close()
+
+
+def test_highway_vehicle_wedges(cuda):
+    """Wedges of the moving vehicle boxes follow their objects frame by
+    frame (with the barrier wedges): same paths and fields as the oracle,
+    which finds the wedges anew from each frame's world triangles."""
+    sc = scenes.highway(n_frames=4, n_vehicles=60, length=600.0)
+    _check(cuda, sc, 50_000, 2, range(4), mode=dcem.MODE_COHERENT, min_diff=4)

@@ -192,3 +192,24 @@ def test_kernels_graphs_links_identical(cuda):
     sl.close()
     s2.close()
     ref.close()
+
+
+def test_introspection_and_gradients_with_children(cuda):
+    """Captures of child rays are reported with their primary ray; the field
+    derivatives refuse transmission records (not differentiated)."""
+    torch = cuda
+    sc = scenes.office(n_frames=2)
+    rays = scenes.fibonacci_sphere(20_000)
+    s = _scene(torch, sc, rays, sc.meta["trans_db"], 2)
+    prm = dcem.default_params(max_refl=2, freq_hz=30e9, tx_power_w=0.5)
+    s.update_transforms(sc.xf[0])
+    fr = s.trace(sc.tx, sc.rx[0], prm)
+    assert fr.stats["child_rays"] > 0
+    c = s.candidates()
+    assert c.shape[0] == fr.stats["candidates"]
+    assert np.all((c[:, 0] >= 0) & (c[:, 0] < rays.shape[0]))
+    tp = fr.paths[np.any((fr.paths["tri"] >= 0) & ((fr.paths["tri"] & dcem.TRI_TRANSMIT) != 0), axis=1)]
+    assert tp.shape[0] > 0
+    with pytest.raises(dcem.DcemError):
+        s.gradients(sc.tx, sc.rx[0], tp[:1], dcem.default_params(max_refl=4, freq_hz=30e9))
+    s.close()

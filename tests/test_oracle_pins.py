@@ -633,7 +633,8 @@ def test_diffraction_path_around_a_corner(oracle_mod):
 
 
 def test_toy_street_wedges_and_diffraction_frame(oracle_mod):
-    """The toy street's two buildings have four vertical corner wedges each;
+    """The toy street's two buildings have four vertical corner wedges each
+    and its four vehicle boxes eight each (four roof edges, four vertical);
     with receivers behind the buildings (seen from the Tx), a diffraction
     frame adds diffraction paths to the reflection paths and sums them."""
     O = oracle_mod
@@ -641,7 +642,9 @@ def test_toy_street_wedges_and_diffraction_frame(oracle_mod):
     behind = np.array([[-30.0, 45.0, 1.5], [30.0, -45.0, 1.5], [-45.0, 30.0, 1.5], [12.0, 12.0, 1.5]], np.float32)
     sc.rx = np.repeat(behind[None], sc.nframes, axis=0)
     wt = O.transform(sc.tris, sc.tri_obj, sc.xf[0])
-    assert O.count_wedges(wt, sc.tri_obj) == 8
+    assert O.count_wedges(wt, sc.tri_obj) == 8 + 4 * 8
+    static = sc.tri_obj < 0
+    assert O.count_wedges(wt[static], sc.tri_obj[static]) == 8
     prm = O.OracleParams(max_refl=2, n_rays=10_000, diffraction=True)
     r = O.frame(sc, 0, scenes.fibonacci_sphere(10_000), prm)
     d = (r.keys[:, 2] >= 0) & ((r.keys[:, 2] & O.DIFF) != 0)
