@@ -197,6 +197,8 @@ struct FramePlan {
   unsigned* bucket_cnt;  // cleared by a memset when there are more links than receivers
   unsigned* sticky_n_next;  // sticky mode: this frame's kept-path count (persistent)
   cudaEvent_t ev[10];
+  cudaStream_t side;     // second branch of the frame (compact copy, end-of-frame state)
+  cudaEvent_t br[4];     // its fork and join events
 };
 
 struct FrameGraph {
@@ -343,6 +345,8 @@ struct dcem_scene {
   int cnrx = -1;
   unsigned last_ncand = 0;
   cudaEvent_t ev[10] = {};
+  cudaStream_t side = nullptr;   // the frame's second branch (see enqueue_frame)
+  cudaEvent_t br[4] = {};
   int launches = 0;  // kernels launched since the last completed frame
   int last_use_q = 0;  // closest-hit kernel of the last frame (TraceArgs::use_q)
   // closest-hit configuration (dcem_scene_set_trace_config / dcem_scene_autotune)
@@ -386,6 +390,9 @@ void scene_free(dcem_scene* s) {
     if (e) cudaEventDestroy(e);
   for (auto& g : s->fgraph) g.drop();
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
+  if (s->side) cudaStreamDestroy(s->side);
+  for (auto& e : s->br)
+    if (e) cudaEventDestroy(e);
   delete s;
 }
 
@@ -864,6 +871,8 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   if ((rc = remap4(s)) != DCEM_OK) return fail2(rc);
   CKF(cudaStreamSynchronize(st));
   for (auto& ev : s->ev) CKF(cudaEventCreate(&ev));
+  CKF(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+  for (auto& e : s->br) CKF(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   dfree(v9); dfree(sel_s_d);
 #undef CKF
   *out = s;
@@ -1327,6 +1336,8 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   P.txs_h = s->txs_h;
   P.bucket_cnt = s->bucket_cnt;
   for (int i = 0; i < 10; ++i) P.ev[i] = s->ev[i];
+  P.side = s->side;
+  for (int i = 0; i < 4; ++i) P.br[i] = s->br[i];
 }
 
 // Event record on a stream, or an event-record node when the stream is being
@@ -1344,10 +1355,15 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   // host filled for this frame
   CK(cudaMemcpyAsync(P.txs, P.txs_h, sizeof(float4) * P.nsets, cudaMemcpyHostToDevice, st));
   if (P.nlinks > P.nrx) CK(cudaMemsetAsync(P.bucket_cnt, 0, sizeof(unsigned) * P.nlinks, st));
+  // second branch: the compact node copy, concurrent with the frame
+  // preparation and the marking pass (joined before the closest hit)
   if (P.use_q) {
+    CK(cudaEventRecord(P.br[0], st));
+    CK(cudaStreamWaitEvent(P.side, P.br[0], 0));
     launch_quantize4(P.nodes, P.q4_bound, P.q4_count, P.q4_kid, P.q4_src, P.root_box, P.has0, P.has1, P.qnodes,
-                     P.qframe, st);
+                     P.qframe, P.side);
     CK(cudaGetLastError());
+    CK(cudaEventRecord(P.br[1], P.side));
   }
   CK(launch_frame_prep(P.fp, st));
   if (tm) CK(rec(P.ev[1], st, cap));
@@ -1358,6 +1374,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
     a.queue = P.a.queue_w;
     a.rx_moved = P.c.rx_moved;
   }
+  if (P.use_q) CK(cudaStreamWaitEvent(st, P.br[1], 0));
   if (tk) CK(rec(P.ev[2], st, cap));
   if (P.R > 0) CK(launch_trace(a, sms, st));
   // transmission: pass p traces the children pass p - 1 spawned
@@ -1375,18 +1392,25 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   CK(launch_validate(P.q, sms * 4, st));
   if (P.q.wedges) CK(launch_diffract(P.q, P.nlinks, sms * 8, st));
   if (tm) CK(rec(P.ev[6], st, cap));
-  CK(launch_reduce(P.q, P.nlinks, st));
-  if (tm) CK(rec(P.ev[7], st, cap));
-  // state the next frame compares against, and the counters to the host
+  // every counter is final here: the state the next frame compares against
+  // and the counters to the host go on the second branch, concurrent with
+  // the reduction
+  CK(cudaEventRecord(P.br[2], st));
+  CK(cudaStreamWaitEvent(P.side, P.br[2], 0));
   {
     int n = std::max(P.nrx, 12 * P.nobj);
     int g = std::max(1, std::min(64, (n + 255) / 256));
-    k_frame_end<<<g, 256, 0, st>>>(P.rx_cur, P.rx_traced, P.nrx, P.xf_cur, P.xf_traced, P.obj_box_cur,
-                                   P.obj_box_traced, P.nobj, P.ctr, P.uctr, P.prev_ncand, P.ctr_hd);
+    k_frame_end<<<g, 256, 0, P.side>>>(P.rx_cur, P.rx_traced, P.nrx, P.xf_cur, P.xf_traced, P.obj_box_cur,
+                                       P.obj_box_traced, P.nobj, P.ctr, P.uctr, P.prev_ncand, P.ctr_hd);
     CK(cudaGetLastError());
   }
   if (P.sticky)  // the kept-path count, for the next frame
-    CK(cudaMemcpyAsync(P.sticky_n_next, &P.ctr->n_sticky_next, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(P.sticky_n_next, &P.ctr->n_sticky_next, sizeof(unsigned), cudaMemcpyDeviceToDevice,
+                       P.side));
+  CK(cudaEventRecord(P.br[3], P.side));
+  CK(launch_reduce(P.q, P.nlinks, st));
+  if (tm) CK(rec(P.ev[7], st, cap));
+  CK(cudaStreamWaitEvent(st, P.br[3], 0));
   // with device outputs nothing follows on the stream: the frame ends here
   if (tm && P.ptr_dev) CK(rec(P.ev[8], st, cap));
   return DCEM_OK;
