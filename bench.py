@@ -614,9 +614,9 @@ def run_multi_scene(args, stream, dev, world, flush, warmup=2):
 
 def _trace_roof(st):
     """Closest-hit roofline of timed frames (stats with timing=2): the
-    survey's algorithmic bytes (36 B per ray and per segment, 64 B per node
-    pair, 48 B per triangle test) over the kernel time, of the measured HBM
-    copy bandwidth."""
+    algorithmic bytes (36 B per ray and per segment, 64 B per node pair,
+    48 B per triangle test) over the kernel time, of the measured HBM copy
+    bandwidth."""
     peak, _ = measured_peaks()
     b = float(np.mean([(x["n_rays"] + x["child_rays"]) * 36 + x["segments_traced"] * 36 + x["node_visits"] * 64 +
                        x["tri_tests"] * 48 for x in st]))
