@@ -1369,7 +1369,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   if (tm) CK(rec(P.ev[1], st, cap));
   TraceArgs a = P.a;
   if (P.coherent) {
-    CK(launch_mark(a, P.c, sms * 8, st));
+    CK(launch_mark(a, P.c, sms, st));
     CK(launch_carry(a, P.c, st));
     a.queue = P.a.queue_w;
     a.rx_moved = P.c.rx_moved;

@@ -69,7 +69,6 @@ struct DevCounters {
   unsigned int n_moved_boxes;
   unsigned int work_trace;         // dynamic work counters of the persistent kernels
   unsigned int work_capture;
-  unsigned int work_mark;
   unsigned int n_capitems;         // segments traced this frame (capture work list)
   float sah_refit;                 // moving-object tree cost after the last refit
   float sah_build;                 // ... right after its last rebuild

@@ -337,11 +337,17 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
 // ---------------------------------------------------------------------------
 // coherent frame: marking and carry-over
 // ---------------------------------------------------------------------------
-// One thread per ray (warps take 32 rays at a time): the first logged
-// segment that meets a moved box is the restart point; earlier segments are
-// reused and, when receivers moved, appended to the capture list (flagged
-// reused). The warp walks segment index b in step so that the appends stay
-// one atomic per warp.
+// Restart points: for every ray the first logged segment that meets a moved
+// box; earlier segments are reused and, when receivers moved, appended to the
+// capture list (flagged reused), and rays with a restart point go to the
+// retrace queue. One thread per ray; each warp takes a static stride of
+// 32-ray batches (a work counter measured slower: its round trip and the
+// order in which it hands out batches cost more than the balance gains). The
+// kernel is bound by memory round trips, so each batch makes few of them:
+// segment 0 (every ray has one) comes with the segment count, and the
+// batch's appends to the capture list and to the queue take one atomic each,
+// issued together. The appended segments are ordered by segment index within
+// the batch, so that consecutive capture threads read neighbouring rays.
 template <bool kS>
 __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
   extern __shared__ __align__(16) int sstk[];
@@ -357,71 +363,73 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     __syncthreads();
   }
   const bool any_rx = c.ctr->rx_moved > 0;
-  const int R = a.R, LS = a.LS;
+  const int R = a.R, LS = a.LS, N = a.N;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   unsigned long long reused = 0;
-  for (;;) {
-    int base = fetch_warp(&c.ctr->work_mark, 32u);
-    if (base >= R) break;
-    int ray = base + lane;
-    int ns = ray < R ? a.nseg[ray] : 0;
-    int bstar = all ? 0 : ns;
-    // the first kPre logged segments of the warp's rays are loaded together
-    // (one memory latency instead of one per segment)
-    constexpr int kPre = 5;
+  constexpr int kPre = 5;  // segments held in registers (later ones are loaded when tested)
+  const long nwarps = (long)((gridDim.x * blockDim.x) >> 5);
+  for (long b0 = (long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; b0 < R; b0 += 32 * nwarps) {
+    const int base = (int)b0;
+    const int ray = base + lane;
+    const bool in = ray < R;
     float4 plo[kPre], pld[kPre];
 #pragma unroll
-    for (int b = 0; b < kPre; ++b) {
-      plo[b] = pld[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (b < bstar) {
+    for (int b = 0; b < kPre; ++b) plo[b] = pld[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int ns = 0;
+    if (in) {
+      ns = a.nseg[ray];
+      plo[0] = a.log_o[ray];
+      pld[0] = a.log_d[ray];
+    }
+    const int lim = all ? 0 : ns;
+#pragma unroll
+    for (int b = 1; b < kPre; ++b) {
+      if (b < lim) {
         plo[b] = a.log_o[(size_t)b * LS + ray];
         pld[b] = a.log_d[(size_t)b * LS + ray];
       }
     }
-    auto step = [&](int b, float4 lo, float4 ld) {
-      unsigned item = 0xffffffffu;
-      if (b < bstar) {
-        RayPre rp;
-        rp.o = f3(lo.x, lo.y, lo.z);
-        float dx = fabsf(ld.x) < 1e-30f ? copysignf(1e-30f, ld.x) : ld.x;
-        float dy = fabsf(ld.y) < 1e-30f ? copysignf(1e-30f, ld.y) : ld.y;
-        float dz = fabsf(ld.z) < 1e-30f ? copysignf(1e-30f, ld.z) : ld.z;
-        rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
-        if (seg_hits_tree(mvt, rp, ld.w, st)) bstar = b;
-        else if (any_rx) item = 0x80000000u | ((unsigned)ray << 4) | (unsigned)b;
-      }
-      unsigned want = __ballot_sync(0xffffffffu, item != 0xffffffffu);
-      if (want) {
-        int leader = __ffs(want) - 1;
-        unsigned at = 0;
-        if (lane == leader) at = atomicAdd(&c.ctr->n_capitems, (unsigned)__popc(want));
-        at = __shfl_sync(0xffffffffu, at, leader);
-        if (item != 0xffffffffu) a.capitems[at + __popc(want & ((1u << lane) - 1u))] = item;
-      }
+    // restart point: the first segment that meets a moved box (ns if none)
+    int bstar = lim;
+    auto test = [&](int b, float4 lo, float4 ld) {
+      RayPre rp;
+      rp.o = f3(lo.x, lo.y, lo.z);
+      float dx = fabsf(ld.x) < 1e-30f ? copysignf(1e-30f, ld.x) : ld.x;
+      float dy = fabsf(ld.y) < 1e-30f ? copysignf(1e-30f, ld.y) : ld.y;
+      float dz = fabsf(ld.z) < 1e-30f ? copysignf(1e-30f, ld.z) : ld.z;
+      rp.inv = f3(__fdiv_rn(1.0f, dx), __fdiv_rn(1.0f, dy), __fdiv_rn(1.0f, dz));
+      if (seg_hits_tree(mvt, rp, ld.w, st)) bstar = b;
     };
 #pragma unroll
-    for (int b = 0; b < kPre; ++b) step(b, plo[b], pld[b]);
-    for (int b = kPre; b <= a.N; ++b) {
-      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), ld = lo;
-      if (b < bstar) {
-        lo = a.log_o[(size_t)b * LS + ray];
-        ld = a.log_d[(size_t)b * LS + ray];
-      }
-      step(b, lo, ld);
+    for (int b = 0; b < kPre; ++b)
+      if (b < bstar) test(b, plo[b], pld[b]);
+    for (int b = kPre; b < bstar; ++b) test(b, a.log_o[(size_t)b * LS + ray], a.log_d[(size_t)b * LS + ray]);
+    // the batch's reused segments (when receivers moved) and retraced rays
+    const int nitem = any_rx ? bstar : 0;
+    unsigned tot = (unsigned)nitem;
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    const bool rq = in && bstar < ns;
+    const unsigned qmask = __ballot_sync(0xffffffffu, rq);
+    unsigned at = 0, aq = 0;
+    if (lane == 0) {
+      if (tot) at = atomicAdd(&c.ctr->n_capitems, tot);
+      if (qmask) aq = atomicAdd(&c.ctr->n_retrace, (unsigned)__popc(qmask));
     }
-    if (ray < R) {
+    at = __shfl_sync(0xffffffffu, at, 0);
+    aq = __shfl_sync(0xffffffffu, aq, 0);
+    if (tot) {
+      for (int b = 0; b <= N; ++b) {
+        unsigned m = __ballot_sync(0xffffffffu, b < nitem);
+        if (!m) break;
+        if (b < nitem) a.capitems[at + __popc(m & lt)] = 0x80000000u | ((unsigned)ray << 4) | (unsigned)b;
+        at += (unsigned)__popc(m);
+      }
+    }
+    if (rq) a.queue_w[aq + __popc(qmask & lt)] = ray;
+    if (in) {
       c.restart[ray] = bstar;
       reused += (unsigned long long)bstar;
-    }
-    // retrace queue: one atomic per warp, the warp's rays kept in direction order
-    bool rq = ray < R && bstar < ns;
-    unsigned want = __ballot_sync(0xffffffffu, rq);
-    if (want) {
-      int leader = __ffs(want) - 1;
-      unsigned at = 0;
-      if (lane == leader) at = atomicAdd(&c.ctr->n_retrace, (unsigned)__popc(want));
-      at = __shfl_sync(0xffffffffu, at, leader);
-      if (rq) a.queue_w[at + __popc(want & ((1u << lane) - 1u))] = ray;
     }
   }
   for (int off = 16; off > 0; off >>= 1) reused += __shfl_down_sync(0xffffffffu, reused, off);
@@ -527,15 +535,24 @@ cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st) {
+cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int sms, cudaStream_t st) {
   size_t base = 256 * kStackSmall * sizeof(int);
   size_t staged = base + stage_bytes(c.mv_cap > 1 ? c.mv_cap - 1 : 0, 0);
   bool kS = staged <= kStageLimit;
   size_t smem = kS ? staged : base;
   cudaError_t e = allow_smem(kS ? (const void*)k_mark<true> : (const void*)k_mark<false>, smem);
   if (e != cudaSuccess) return e;
-  if (kS) k_mark<true><<<grid_for(a.R, 256, grid_cap), 256, smem, st>>>(a, c);
-  else k_mark<false><<<grid_for(a.R, 256, grid_cap), 256, smem, st>>>(a, c);
+  // one wave of resident blocks (each stages the moved-box tree once)
+  static size_t key = 0;
+  static int resident = 0;
+  const void* fn = kS ? (const void*)k_mark<true> : (const void*)k_mark<false>;
+  if (key != smem + kS) {
+    resident = resident_blocks(fn, sms, smem);
+    key = smem + kS;
+  }
+  int blocks = grid_for(a.R, 256, resident);
+  if (kS) k_mark<true><<<blocks, 256, smem, st>>>(a, c);
+  else k_mark<false><<<blocks, 256, smem, st>>>(a, c);
   return cudaGetLastError();
 }
 

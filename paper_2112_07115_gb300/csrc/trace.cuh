@@ -79,7 +79,7 @@ constexpr int kTraceBlocks[] = {64, 128, 256};
 constexpr int kTraceStackMin = 8, kTraceStackMax = 32;
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st);
-cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int grid_cap, cudaStream_t st);
+cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int sms, cudaStream_t st);
 cudaError_t launch_carry(const TraceArgs& a, const CoherentArgs& c, cudaStream_t st);
 
 }  // namespace dcem
