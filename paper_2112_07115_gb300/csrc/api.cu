@@ -782,6 +782,12 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->dlvl, kDynLevels + 2));
   CKF(dalloc(&s->arrive, nmax));
   CKF(dalloc(&s->roots, 2));
+  {
+    // both trees empty until built: a scene without moving triangles never
+    // builds the second, and the 4-wide mapping reads both roots
+    const int empty[2] = {kEmpty, kEmpty};
+    CKF(cudaMemcpy(s->roots, empty, sizeof(empty), cudaMemcpyHostToDevice));
+  }
   CKF(dalloc(&s->root_box, 12));
   CKF(dalloc(&s->perm, nmax));
   CKF(dalloc(&s->prim, 6 * (size_t)nmax));

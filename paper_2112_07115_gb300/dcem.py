@@ -627,3 +627,49 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def path_power(scene: Scene, theta, tx, rx, paths: np.ndarray, params: Params | None = None):
+    """Received power P_coh [dBm] per receiver over a fixed path topology, as
+    a differentiable function of theta for torch autograd.
+
+    theta (a torch tensor of dcem_scene_gradient_size values) stands for the
+    scene's current parameters in the order of dcem_path_gradients: eps_r and
+    sigma of every material, then the x and y translation of every rigid
+    object. The function is evaluated at the scene's state (theta's values are
+    not read; pass the current ones), holding the topology `paths` fixed, as
+    Sec. III steps 3, 4 and 6 define the field of a path (Eq. 1, Eq. 3). The
+    power comes from dcem_reduce_paths_noalloc and the Jacobian d P_coh[dBm] /
+    d theta from dcem_path_gradients (FP64 forward-mode derivatives in the
+    library's kernels); the backward pass contracts the incoming gradient with
+    that Jacobian. Receivers without paths have P = -inf and zero gradient.
+    The result lives on theta's device (a CUDA device: the power kernel runs
+    there on the current stream)."""
+    import torch
+
+    class _PathPower(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th):
+            prm = params or default_params()
+            npar = dcem_scene_gradient_size(scene.h)
+            if th.numel() != npar:
+                raise DcemError(ERR_ARG, f"path_power: theta has {th.numel()} values, the scene {npar}")
+            nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+            _, _, dp = scene.gradients(tx, rx, paths, prm)
+            recs = np.ascontiguousarray(paths, PATH_DTYPE)
+            dev = th.device
+            pd = torch.from_numpy(recs.view(np.uint8).copy()).to(dev)
+            pc = torch.empty(max(nrx, 1), dtype=torch.float64, device=dev)
+            rc = dcem_reduce_paths_noalloc(pd.data_ptr(), recs.shape[0], nrx, prm.tx_power_w, None,
+                                           pc.data_ptr(), None, torch.cuda.current_stream(dev).cuda_stream)
+            if rc != OK:
+                raise DcemError(rc, "dcem_reduce_paths_noalloc")
+            ctx.save_for_backward(torch.from_numpy(dp).to(dev))
+            return pc[:nrx]
+
+        @staticmethod
+        def backward(ctx, g):
+            (jac,) = ctx.saved_tensors
+            return (g.to(jac.dtype) @ jac).to(theta.dtype).reshape(theta.shape)
+
+    return _PathPower.apply(theta)

@@ -155,3 +155,39 @@ def test_gradients_errors(cuda):
                                       dfl.ctypes.data, None)
         assert rc == dcem.ERR_ARG, bad
     s.close()
+
+
+def test_path_power_autograd(cuda):
+    """The received power as a torch autograd function of the scene's
+    parameters: forward equals the frame's P_coh, and a weighted loss's
+    gradient equals the Jacobian of dcem_path_gradients contracted with the
+    weights."""
+    torch = cuda
+    sc = scenes.toy_street()
+    f = 8
+    s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(scenes.fibonacci_sphere(10_000))
+    s.update_transforms(sc.xf[f])
+    prm = dcem.default_params(max_refl=3, freq_hz=28e9)
+    fr = s.trace(sc.tx, sc.rx[f], prm)
+    assert fr.paths.shape[0] > 0
+    # theta: eps_r, sigma per material, then the x, y translation per object
+    xf = sc.xf[f].reshape(sc.nobj, 12)
+    th0 = np.concatenate([sc.materials[:, :2].astype(np.float64).ravel(),
+                          np.stack([xf[:, 3], xf[:, 7]], 1).astype(np.float64).ravel()])
+    theta = torch.tensor(th0, dtype=torch.float64, device="cuda", requires_grad=True)
+    p = dcem.path_power(s, theta, sc.tx, sc.rx[f], fr.paths, prm)
+    pc = p.detach().cpu().numpy()
+    fin = np.isfinite(fr.p_coh_dbm)
+    assert np.array_equal(np.isfinite(pc), fin) and fin.any()
+    assert np.abs(pc[fin] - fr.p_coh_dbm[fin]).max() <= 1e-9
+    w = torch.from_numpy(np.random.default_rng(3).normal(size=sc.nrx)).cuda()
+    m = torch.from_numpy(fin).cuda()
+    loss = (w * torch.where(m, p, torch.zeros_like(p))).sum()
+    loss.backward()
+    _, _, dp = s.gradients(sc.tx, sc.rx[f], fr.paths, prm)
+    want = (w.cpu().numpy()[fin, None] * dp[fin]).sum(0)
+    got = theta.grad.cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+    assert np.abs(want).max() > 0
+    s.close()
