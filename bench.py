@@ -738,7 +738,7 @@ def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ms, nd = [], []
         for i in range(warmup + K):
-            f = i + 1
+            f = 1 + i % (sc.nframes - 1)  # short runs have fewer frames than this loop
             flush.zero_()
             e0.record(stream)
             dcem.dcem_scene_update_transforms(s.h, xf_d[f])

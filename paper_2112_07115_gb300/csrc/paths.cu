@@ -592,7 +592,9 @@ __device__ __forceinline__ zd zsqrt(zd a) {  // principal branch
 }
 
 // erfc(z) for Re z > 0: the Maclaurin series of erf (Abramowitz & Stegun
-// 7.1.5) for |z| < 3, else the continued fraction of A&S 7.1.14.
+// 7.1.5) for |z| < 3, else the continued fraction of A&S 7.1.14, truncated
+// after 40, 30 or 20 terms for |z| from 3, 3.5 or 4.5 on (relative error
+// below 2e-15 against a Faddeeva-function reference).
 __device__ zd erfc_z(zd z) {
   const double rsqpi = 0.56418958354775628695;  // 1/sqrt(pi)
   double az = hypot(z.re, z.im);
@@ -602,21 +604,39 @@ __device__ zd erfc_z(zd z) {
       term = term * z2 * (-1.0 / n);
       zd t = term * (1.0 / (2 * n + 1));
       sum = sum + t;
-      if (hypot(t.re, t.im) < 1e-17 * hypot(sum.re, sum.im)) break;
+      if (fabs(t.re) + fabs(t.im) < 1e-17 * (fabs(sum.re) + fabs(sum.im))) break;
     }
     return Z(1.0) - sum * (2.0 * rsqpi);
   }
   // erfc z = e^{-z^2}/sqrt(pi) * 1/(z + (1/2)/(z + 1/(z + (3/2)/(z + ...))))
   zd f = z;
-  for (int k = 60; k >= 1; --k) f = z + zdiv(Z(0.5 * k), f);
+  for (int k = az < 3.5 ? 40 : az < 4.5 ? 30 : 20; k >= 1; --k) f = z + zdiv(Z(0.5 * k), f);
   zd ez = zexp(Z(-(z.re * z.re - z.im * z.im), -2.0 * z.re * z.im));
   return zdiv(ez * rsqpi, f);
 }
 
 // UTD transition function F(x) = 2j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt,
 // the tail integral being (sqrt(pi)/2) e^{-j pi/4} erfc(e^{j pi/4} sqrt x).
+// For x >= 30 its large-argument expansion (repeated integration by parts of
+// the tail integral, as Kouyoumjian & Pathak give it): F(x) = sum_m t_m with
+// t_0 = 1, t_m = t_{m-1} j (2m - 1) / (2x), i.e. 1 + j/(2x) - 3/(4x^2) - ...;
+// its terms shrink while 2m - 1 < 2x, and the sum stops there or at 1e-17;
+// the error is below 1e-13 for x >= 30. Away from shadow and reflection
+// boundaries x = 2kL cos^2(.) is in the thousands, so this is the usual case.
 __device__ zd transition_fn(double x) {
   if (!(x > 0.0)) return Z(0.0);
+  if (x >= 30.0) {
+    const double r = 1.0 / (2.0 * x);
+    zd t = Z(1.0), sum = Z(1.0);
+    for (int m = 1; m <= 40; ++m) {
+      double c = (2.0 * m - 1.0) * r;
+      if (c >= 1.0) break;  // the terms grow from here on
+      t = Z(-t.im * c, t.re * c);  // times j (2m - 1) / (2x)
+      sum = sum + t;
+      if (fabs(t.re) + fabs(t.im) < 1e-17 * (fabs(sum.re) + fabs(sum.im))) break;
+    }
+    return sum;
+  }
   double a = sqrt(x);
   const double h = 0.70710678118654752440;
   zd G = Z(h, -h) * erfc_z(Z(h * a, h * a)) * 0.88622692545275801365;  // sqrt(pi)/2
@@ -690,6 +710,48 @@ __device__ __forceinline__ double wedge_angle(const Wedge& W, d3w X) {
   return a < 0.0 ? a + 2.0 * M_PI : a;
 }
 
+// FP32 pre-test of a (transmitter, receiver, wedge) triple: false only when
+// the FP64 test below rejects the triple too, so that most triples (far from
+// the Keller cone of a short vehicle edge, or on the lit side) cost no FP64
+// work. Rejections keep margins above the FP32 rounding of the geometry: the
+// Keller point off the edge by more than 5 cm (plus 1e-5 of the distances),
+// an angle beyond the wedge or the shadow-boundary rule missed by more than
+// ten times the angle's rounding bound (at least 1e-3 rad). Angles near the
+// 0 / 2 pi cut, or of points near the edge line, reject nothing.
+__device__ __forceinline__ float wedge_angle32(float3 d, float3 t0, float3 y0, float r, float dist, bool& sure,
+                                               float& tol) {
+  float a = atan2f(fdot3(d, y0), fdot3(d, t0));
+  if (a < 0.0f) a += 6.2831853f;
+  float err = 4e-6f * (dist + 1.0f) / r + 1e-5f;  // rounding of the in-plane direction, radians
+  tol = fmaxf(1e-3f, 10.0f * err);
+  sure = r > 0.0f && err < 1e-3f && a > tol && a < 6.2831853f - tol;
+  return a;
+}
+
+__device__ __forceinline__ bool diffract_candidate(const Wedge& W, float4 txv, float4 rxv) {
+  float3 e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
+  float3 p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+  float3 dt = f3(txv.x - p0.x, txv.y - p0.y, txv.z - p0.z), dr = f3(rxv.x - p0.x, rxv.y - p0.y, rxv.z - p0.z);
+  float zt = fdot3(dt, e), zr = fdot3(dr, e);
+  float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
+  float3 pr = f3(dr.x - e.x * zr, dr.y - e.y * zr, dr.z - e.z * zr);
+  float rt = sqrtf(fdot3(pt, pt)), rr = sqrtf(fdot3(pr, pr));
+  float lt = sqrtf(fdot3(dt, dt)), lr = sqrtf(fdot3(dr, dr));
+  if (!(rt > 1e-3f && rr > 1e-3f)) return true;
+  float zq = zt + (zr - zt) * rt / (rt + rr);
+  float mz = 0.05f + 1e-5f * (lt + lr);
+  if (zq < -mz || zq > (float)W.len + mz) return false;
+  float3 t0 = f3((float)W.t0[0], (float)W.t0[1], (float)W.t0[2]);
+  float3 y0 = f3((float)W.y0[0], (float)W.y0[1], (float)W.y0[2]);
+  bool st, sr;
+  float tt, tr;
+  float phip = wedge_angle32(pt, t0, y0, rt, lt, st, tt), phi = wedge_angle32(pr, t0, y0, rr, lr, sr, tr);
+  float npi = (float)(W.n * M_PI);
+  if ((st && phip > npi + tt) || (sr && phi > npi + tr)) return false;
+  if (st && sr && fabsf(phi - phip) < 3.14159265f - (tt + tr)) return false;
+  return true;
+}
+
 // FP32 any-hit of the open segment a -> b, the two wedge faces excluded.
 __device__ __forceinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, unsigned& ovf,
                                              TStack& st) {
@@ -751,88 +813,124 @@ __global__ void k_wedge_geom(const float4* __restrict__ tris, const int* __restr
 // path about the edge line), the paper's shadow rule (the receiver beyond the
 // incident shadow boundary), both legs unoccluded, then the UTD field; a
 // valid path joins its link's bucket like a validated path.
+// One (link, wedge) pair that passed the FP32 pre-test: the exact FP64
+// test, the legs' occlusion, the UTD field and the path record.
+__device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, double k, double lam, unsigned& ovf,
+                                              TStack& st) {
+  int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
+  const Wedge W = a.wedges[w];
+  float4 rxv = a.rx[link % a.nrx], txv = a.txs[link / a.nrx];
+  d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
+  d3w e = D3(W.e[0], W.e[1], W.e[2]), p0 = D3(W.p0[0], W.p0[1], W.p0[2]);
+  d3w dt = T - p0, dr = R - p0;
+  double zt = dotw(dt, e), zr = dotw(dr, e);
+  d3w pt = dt - e * zt, pr = dr - e * zr;
+  double rt = sqrt(dotw(pt, pt)), rr = sqrt(dotw(pr, pr));
+  if (!(rt > 0.0 && rr > 0.0)) return;
+  double zq = zt + (zr - zt) * rt / (rt + rr);
+  double uq = zq / W.len;
+  if (!(uq > 0.0 && uq < 1.0)) return;
+  d3w Q = p0 + e * zq;
+  double phip = wedge_angle(W, T), phi = wedge_angle(W, R), n = W.n;
+  if (phip > n * M_PI || phi > n * M_PI) return;
+  if (!(fabs(phi - phip) > M_PI)) return;
+  if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, R, W.ta, W.tb, ovf, st)) return;
+  unsigned fl = 0;
+  d3w qt = Q - T, rq = R - Q;
+  double sp = sqrt(dotw(qt, qt)), s = sqrt(dotw(rq, rq));
+  d3w ip = qt * (1.0 / sp), dd = rq * (1.0 / s);
+  double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
+  double sb = sin(beta0);
+  double L = s * sp * sb * sb / (s + sp);
+  d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
+  d3w bp = crossw(ip, php), bd = crossw(dd, ph);
+  // Luebbers: the faces' Fresnel factors at the grazing angles phi' and n pi - phi
+  const float4 ma = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.ta] + 1].w)];
+  const float4 mb = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.tb] + 1].w)];
+  zd r0s, r0h, rns, rnh;
+  fresnel_d(ma, a.freq, fabs(sin(phip)), r0s, r0h);
+  fresnel_d(mb, a.freq, fabs(sin(n * M_PI - phi)), rns, rnh);
+  zd Ds = utd_coeff(n, phi, phip, beta0, L, k, r0s, rns, fl);
+  zd Dh = utd_coeff(n, phi, phip, beta0, L, k, r0h, rnh, fl);
+  d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
+  d3w e0 = polw(u, ip, fl), prx = polw(u, dd * -1.0, fl);
+  double sn, cs;
+  sincos(-k * sp, &sn, &cs);
+  zd Ei = Z(cs / sp, sn / sp);
+  zd Eb = Ei * dotw(e0, bp), Ep = Ei * dotw(e0, php);
+  sincos(-k * s, &sn, &cs);
+  zd A = Z(cs, sn) * sqrt(sp / (s * (s + sp)));
+  zd proj = (Ds * Eb) * (-dotw(bd, prx)) + (Dh * Ep) * (-dotw(ph, prx));
+  zd amp = proj * A * (lam / (4.0 * M_PI));
+  unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
+  if (uu >= a.ucap) {
+    atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
+    return;
+  }
+  PathRec rec;
+  int id = w | kDiffBit;
+  rec.key = seq_key(link % a.nrx, 1, [&](int) { return id; });
+  rec.rx = link;
+  rec.depth = 1;
+  rec.ray = -1;
+  rec.flags = fl;
+  rec.valid = 1;
+  rec.pad = 0;
+  rec.len = sp + s;
+  rec.amp_re = amp.re;
+  rec.amp_im = amp.im;
+  for (int j = 0; j < kMaxRefl; ++j) {
+    rec.tri[j] = j == 0 ? id : -1;
+    rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
+  }
+  rec.pts[0][0] = (float)Q.x;
+  rec.pts[0][1] = (float)Q.y;
+  rec.pts[0][2] = (float)Q.z;
+  a.prec[uu] = rec;
+  unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
+  if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
+  else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+  atomicAdd(&a.ctr->n_valid, 1u);
+}
+
+// Every (link, wedge) pair: the FP32 pre-test rejects most of them; the
+// survivors gather in shared memory and take the FP64 work in batches of a
+// whole block, so that the narrow FP64 pipe runs full warps (survivors are
+// sparse and cluster in index, and one at a time they left most lanes idle
+// and most SMs without work). Blocks take chunks of 64 pairs in a grid
+// stride, which spreads clusters of survivors over the blocks.
 __global__ void __launch_bounds__(64) k_diffract(PathArgs a, int nlinks) {
   extern __shared__ int sstk[];
+  __shared__ long sq[128];
+  __shared__ int nsq;
   TStack st;
   bind_stack(st, sstk, kStackTrace);
   const long total = (long)nlinks * a.nw;
+  const long nchunks = (total + 63) / 64;
   const double k = 2.0 * M_PI * a.freq / 299792458.0, lam = 299792458.0 / a.freq;
+  const int tid = threadIdx.x;
   unsigned ovf = 0;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
-    const Wedge W = a.wedges[w];
-    float4 rxv = a.rx[link % a.nrx], txv = a.txs[link / a.nrx];
-    d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
-    d3w e = D3(W.e[0], W.e[1], W.e[2]), p0 = D3(W.p0[0], W.p0[1], W.p0[2]);
-    d3w dt = T - p0, dr = R - p0;
-    double zt = dotw(dt, e), zr = dotw(dr, e);
-    d3w pt = dt - e * zt, pr = dr - e * zr;
-    double rt = sqrt(dotw(pt, pt)), rr = sqrt(dotw(pr, pr));
-    if (!(rt > 0.0 && rr > 0.0)) continue;
-    double zq = zt + (zr - zt) * rt / (rt + rr);
-    double uq = zq / W.len;
-    if (!(uq > 0.0 && uq < 1.0)) continue;
-    d3w Q = p0 + e * zq;
-    double phip = wedge_angle(W, T), phi = wedge_angle(W, R), n = W.n;
-    if (phip > n * M_PI || phi > n * M_PI) continue;
-    if (!(fabs(phi - phip) > M_PI)) continue;
-    if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, R, W.ta, W.tb, ovf, st)) continue;
-    unsigned fl = 0;
-    d3w qt = Q - T, rq = R - Q;
-    double sp = sqrt(dotw(qt, qt)), s = sqrt(dotw(rq, rq));
-    d3w ip = qt * (1.0 / sp), dd = rq * (1.0 / s);
-    double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
-    double sb = sin(beta0);
-    double L = s * sp * sb * sb / (s + sp);
-    d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
-    d3w bp = crossw(ip, php), bd = crossw(dd, ph);
-    // Luebbers: the faces' Fresnel factors at the grazing angles phi' and n pi - phi
-    const float4 ma = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.ta] + 1].w)];
-    const float4 mb = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.tb] + 1].w)];
-    zd r0s, r0h, rns, rnh;
-    fresnel_d(ma, a.freq, fabs(sin(phip)), r0s, r0h);
-    fresnel_d(mb, a.freq, fabs(sin(n * M_PI - phi)), rns, rnh);
-    zd Ds = utd_coeff(n, phi, phip, beta0, L, k, r0s, rns, fl);
-    zd Dh = utd_coeff(n, phi, phip, beta0, L, k, r0h, rnh, fl);
-    d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
-    d3w e0 = polw(u, ip, fl), prx = polw(u, dd * -1.0, fl);
-    double sn, cs;
-    sincos(-k * sp, &sn, &cs);
-    zd Ei = Z(cs / sp, sn / sp);
-    zd Eb = Ei * dotw(e0, bp), Ep = Ei * dotw(e0, php);
-    sincos(-k * s, &sn, &cs);
-    zd A = Z(cs, sn) * sqrt(sp / (s * (s + sp)));
-    zd proj = (Ds * Eb) * (-dotw(bd, prx)) + (Dh * Ep) * (-dotw(ph, prx));
-    zd amp = proj * A * (lam / (4.0 * M_PI));
-    unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
-    if (uu >= a.ucap) {
-      atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
-      continue;
+  if (tid == 0) nsq = 0;
+  __syncthreads();
+  for (long c = blockIdx.x;; c += gridDim.x) {
+    const bool more = c < nchunks;  // the same in the whole block
+    if (more) {
+      long idx = c * 64 + tid;
+      if (idx < total) {
+        int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
+        if (diffract_candidate(a.wedges[w], a.txs[link / a.nrx], a.rx[link % a.nrx])) sq[atomicAdd(&nsq, 1)] = idx;
+      }
     }
-    PathRec rec;
-    int id = w | kDiffBit;
-    rec.key = seq_key(link % a.nrx, 1, [&](int) { return id; });
-    rec.rx = link;
-    rec.depth = 1;
-    rec.ray = -1;
-    rec.flags = fl;
-    rec.valid = 1;
-    rec.pad = 0;
-    rec.len = sp + s;
-    rec.amp_re = amp.re;
-    rec.amp_im = amp.im;
-    for (int j = 0; j < kMaxRefl; ++j) {
-      rec.tri[j] = j == 0 ? id : -1;
-      rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
+    __syncthreads();
+    const int n = nsq;  // at most 63 left over + 64 new
+    if (!more && n == 0) break;
+    if (n >= 64 || !more) {
+      const int m = min(n, 64);
+      if (tid < m) diffract_pair(a, sq[n - m + tid], k, lam, ovf, st);
+      __syncthreads();
+      if (tid == 0) nsq = n - m;
+      __syncthreads();
     }
-    rec.pts[0][0] = (float)Q.x;
-    rec.pts[0][1] = (float)Q.y;
-    rec.pts[0][2] = (float)Q.z;
-    a.prec[uu] = rec;
-    unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
-    if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
-    else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
-    atomicAdd(&a.ctr->n_valid, 1u);
   }
   if (ovf) {
     atomicAdd(&a.ctr->stack_overflow, 1u);
