@@ -761,8 +761,8 @@ def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
                         "receiver_wedge_pairs_per_frame": nw * nrx})
         else:
             out["without_diffraction_frames_per_s"] = round(world * K / t, 2)
-    out["workload"] = ("highway frames (coherent), first-order UTD diffraction at the barrier wedges for all 200 "
-                       "receivers")
+    out["workload"] = ("highway frames (coherent), first-order UTD diffraction at every wedge (barrier tops and "
+                       "vehicle edges) for all 200 receivers")
     return out
 
 
