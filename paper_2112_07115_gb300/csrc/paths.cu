@@ -594,7 +594,8 @@ __device__ __forceinline__ zd zsqrt(zd a) {  // principal branch
 // erfc(z) for Re z > 0: the Maclaurin series of erf (Abramowitz & Stegun
 // 7.1.5) for |z| < 3, else the continued fraction of A&S 7.1.14, truncated
 // after 40, 30 or 20 terms for |z| from 3, 3.5 or 4.5 on (relative error
-// below 2e-15 against a Faddeeva-function reference).
+// below 3e-15 against a Faddeeva-function reference). Only |z| < 5.5 comes
+// here: transition_fn takes its large-argument series from x = 30 on.
 __device__ zd erfc_z(zd z) {
   const double rsqpi = 0.56418958354775628695;  // 1/sqrt(pi)
   double az = hypot(z.re, z.im);
@@ -608,11 +609,21 @@ __device__ zd erfc_z(zd z) {
     }
     return Z(1.0) - sum * (2.0 * rsqpi);
   }
-  // erfc z = e^{-z^2}/sqrt(pi) * 1/(z + (1/2)/(z + 1/(z + (3/2)/(z + ...))))
-  zd f = z;
-  for (int k = az < 3.5 ? 40 : az < 4.5 ? 30 : 20; k >= 1; --k) f = z + zdiv(Z(0.5 * k), f);
+  // erfc z = e^{-z^2}/sqrt(pi) * 1/(z + (1/2)/(z + 1/(z + (3/2)/(z + ...)))),
+  // the truncated fraction evaluated forward as A_n / B_n (A_k = z A_{k-1} +
+  // (k/2) A_{k-2}, B likewise) with one division at the end; for |z| < 5.5
+  // and 40 terms |A|, |B| stay below 1e40
+  zd A0 = Z(1.0), A1 = z, B0 = Z(0.0), B1 = Z(1.0);
+  const int nt = az < 3.5 ? 40 : az < 4.5 ? 30 : 20;
+  for (int k = 1; k <= nt; ++k) {
+    zd A2 = z * A1 + A0 * (0.5 * k), B2 = z * B1 + B0 * (0.5 * k);
+    A0 = A1;
+    A1 = A2;
+    B0 = B1;
+    B1 = B2;
+  }
   zd ez = zexp(Z(-(z.re * z.re - z.im * z.im), -2.0 * z.re * z.im));
-  return zdiv(ez * rsqpi, f);
+  return zdiv(ez * rsqpi * B1, A1);
 }
 
 // UTD transition function F(x) = 2j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt,
@@ -654,14 +665,26 @@ __device__ zd utd_term(double n, double beta, double s, double kL, unsigned& fl)
   return transition_fn(kL * 2.0 * c * c) * (cos(arg) / sn);
 }
 
-// Kouyoumjian-Pathak wedge coefficient with face reflection factors r0, rn.
-__device__ zd utd_coeff(double n, double phi, double phip, double beta0, double L, double k, zd r0, zd rn,
-                        unsigned& fl) {
+// Kouyoumjian-Pathak wedge coefficient D = pre (t1 + t2 + r0 t3 + rn t4)
+// with face reflection factors r0, rn. The prefactor and the four terms do
+// not depend on r0 and rn, so the soft and hard coefficients share them
+// (utd_parts once, utd_coeff per polarisation).
+struct UtdParts {
+  zd pre, t[4];
+};
+__device__ UtdParts utd_parts(double n, double phi, double phip, double beta0, double L, double k, unsigned& fl) {
   const double h = 0.70710678118654752440;
-  zd pre = Z(-h, h) * (1.0 / (2.0 * n * sqrt(2.0 * M_PI * k) * sin(beta0)));  // -e^{-j pi/4} / (...)
+  UtdParts u;
+  u.pre = Z(-h, h) * (1.0 / (2.0 * n * sqrt(2.0 * M_PI * k) * sin(beta0)));  // -e^{-j pi/4} / (...)
   double bm = phi - phip, bp = phi + phip, kL = k * L;
-  return pre * (utd_term(n, bm, 1.0, kL, fl) + utd_term(n, bm, -1.0, kL, fl) + r0 * utd_term(n, bp, -1.0, kL, fl) +
-                rn * utd_term(n, bp, 1.0, kL, fl));
+  u.t[0] = utd_term(n, bm, 1.0, kL, fl);
+  u.t[1] = utd_term(n, bm, -1.0, kL, fl);
+  u.t[2] = utd_term(n, bp, -1.0, kL, fl);
+  u.t[3] = utd_term(n, bp, 1.0, kL, fl);
+  return u;
+}
+__device__ zd utd_coeff(const UtdParts& u, zd r0, zd rn) {
+  return u.pre * (u.t[0] + u.t[1] + r0 * u.t[2] + rn * u.t[3]);
 }
 
 // Fresnel TE / TM coefficients in FP64 (eps_c = eps_r - j sigma/(w eps0)).
@@ -850,8 +873,9 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   zd r0s, r0h, rns, rnh;
   fresnel_d(ma, a.freq, fabs(sin(phip)), r0s, r0h);
   fresnel_d(mb, a.freq, fabs(sin(n * M_PI - phi)), rns, rnh);
-  zd Ds = utd_coeff(n, phi, phip, beta0, L, k, r0s, rns, fl);
-  zd Dh = utd_coeff(n, phi, phip, beta0, L, k, r0h, rnh, fl);
+  const UtdParts up = utd_parts(n, phi, phip, beta0, L, k, fl);
+  zd Ds = utd_coeff(up, r0s, rns);
+  zd Dh = utd_coeff(up, r0h, rnh);
   d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
   d3w e0 = polw(u, ip, fl), prx = polw(u, dd * -1.0, fl);
   double sn, cs;
