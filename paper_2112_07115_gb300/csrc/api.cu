@@ -244,6 +244,8 @@ struct dcem_scene {
   WedgeTopo* wtopo = nullptr;  // ... and topology
   int nw = 0;
   bool diffraction = false;
+  unsigned long long* dsurv = nullptr;  // diffraction: pre-test survivor list
+  unsigned dsurv_cap = 0;
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
   int* g_param = nullptr;      // staged outputs and the error flag (dcem_path_gradients)
   double* g_out = nullptr;
@@ -367,7 +369,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
-  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo);
+  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo); dfree(s->dsurv);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
@@ -1105,6 +1107,10 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
       CK(cudaMemcpy(s->wtopo, w.data(), sizeof(WedgeTopo) * w.size(), cudaMemcpyHostToDevice));
     }
   }
+  if (on && s->nw && !s->dsurv) {
+    CK(dalloc(&s->dsurv, (size_t)65536));
+    s->dsurv_cap = 65536;
+  }
   s->diffraction = on != 0;
   if (n_wedges) *n_wedges = s->nw;
   return DCEM_OK;
@@ -1312,6 +1318,8 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.wedges = s->diffraction && s->nw > 0 ? s->wedges : nullptr;
   q.wtopo = s->wtopo;
   q.nw = s->nw;
+  q.dsurv = s->dsurv;
+  q.dsurv_cap = s->dsurv_cap;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
   P.sticky = p->mode == DCEM_MODE_STICKY;
@@ -1396,7 +1404,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   if (P.q.sticky_prev) CK(launch_sticky_probe(P.q, sms * 4, st));
   if (tm) CK(rec(P.ev[5], st, cap));
   CK(launch_validate(P.q, sms * 4, st));
-  if (P.q.wedges) CK(launch_diffract(P.q, P.nlinks, sms * 8, st));
+  if (P.q.wedges) CK(launch_diffract(P.q, P.nlinks, sms, st));
   if (tm) CK(rec(P.ev[6], st, cap));
   // every counter is final here: the state the next frame compares against
   // and the counters to the host go on the second branch, concurrent with
@@ -1578,7 +1586,7 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
     c = s->ctr_h;
     unsigned err = c[0].err | c[1].err;
     unsigned grow = err & (ERR_CAND_OVERFLOW | ERR_UNIQUE_OVERFLOW | ERR_HASH_FULL | ERR_BUCKET_OVERFLOW |
-                           ERR_SPAWN_OVERFLOW);
+                           ERR_SPAWN_OVERFLOW | ERR_DIFF_OVERFLOW);
     if (!grow) break;
     // internal capacity exceeded: grow and retrace the frame from scratch
     CK(cudaStreamSynchronize(st));
@@ -1595,6 +1603,14 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
       long long cc = std::max<long long>(2ll * s->child_cap, (long long)(sp * 5 / 4) + 1024);
       if ((long long)s->R + cc > (1ll << 27)) return DCEM_ERR_CAPACITY;
       if ((rc = ensure_log(s, s->logW, (int)cc)) != DCEM_OK) return rc;
+    }
+    if (err & ERR_DIFF_OVERFLOW) {  // more diffraction pre-test survivors than list slots
+      unsigned long long want = std::max<unsigned long long>(2ull * s->dsurv_cap,
+                                                             (unsigned long long)c[0].n_dsurv * 5 / 4 + 1024);
+      if (want > 0x7fffffffull) return DCEM_ERR_CAPACITY;
+      dfree(s->dsurv);
+      CK(dalloc(&s->dsurv, (size_t)want));
+      s->dsurv_cap = (unsigned)want;
     }
     if (err & ERR_BUCKET_OVERFLOW) {
       int nb = s->bucket_cap * 2;

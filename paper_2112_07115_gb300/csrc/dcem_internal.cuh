@@ -52,6 +52,7 @@ enum : unsigned {
   ERR_HASH_FULL = 64u,
   ERR_QUEUE_OVERFLOW = 128u,
   ERR_SPAWN_OVERFLOW = 256u,       // transmission: more child rays than slots
+  ERR_DIFF_OVERFLOW = 512u,        // diffraction: more pre-test survivors than list slots
 };
 
 struct DevCounters {
@@ -79,6 +80,7 @@ struct DevCounters {
   unsigned int n_sticky_next;      // sticky mode: valid paths kept for the next frame
   unsigned int n_spawn[kMaxRefl + 1];    // transmission: child rays spawned by trace pass p
   unsigned int work_pass[kMaxRefl + 1];  // ... work counters of passes p >= 1
+  unsigned int n_dsurv;            // diffraction: (link, wedge) pairs past the FP32 pre-test
 };
 
 // Sticky mode: a valid path kept for the next frame (link, depth, sequence).

@@ -22,6 +22,8 @@
 // by key), so the received power is reproducible bit for bit.
 #include "paths.cuh"
 
+#include <algorithm>
+
 namespace dcem {
 
 // ---------------------------------------------------------------------------
@@ -917,45 +919,45 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   atomicAdd(&a.ctr->n_valid, 1u);
 }
 
-// Every (link, wedge) pair: the FP32 pre-test rejects most of them; the
-// survivors gather in shared memory and take the FP64 work in batches of a
-// whole block, so that the narrow FP64 pipe runs full warps (survivors are
-// sparse and cluster in index, and one at a time they left most lanes idle
-// and most SMs without work). Blocks take chunks of 64 pairs in a grid
-// stride, which spreads clusters of survivors over the blocks.
-__global__ void __launch_bounds__(64) k_diffract(PathArgs a, int nlinks) {
-  extern __shared__ int sstk[];
-  __shared__ long sq[128];
-  __shared__ int nsq;
-  TStack st;
-  bind_stack(st, sstk, kStackTrace);
+// Pass 1 over every (link, wedge) pair: the FP32 pre-test rejects most of
+// them; the survivors' indices go to a list (one atomic per warp).
+__global__ void __launch_bounds__(256) k_diffract_pre(PathArgs a, int nlinks) {
   const long total = (long)nlinks * a.nw;
-  const long nchunks = (total + 63) / 64;
-  const double k = 2.0 * M_PI * a.freq / 299792458.0, lam = 299792458.0 / a.freq;
-  const int tid = threadIdx.x;
-  unsigned ovf = 0;
-  if (tid == 0) nsq = 0;
-  __syncthreads();
-  for (long c = blockIdx.x;; c += gridDim.x) {
-    const bool more = c < nchunks;  // the same in the whole block
-    if (more) {
-      long idx = c * 64 + tid;
-      if (idx < total) {
-        int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
-        if (diffract_candidate(a.wedges[w], a.txs[link / a.nrx], a.rx[link % a.nrx])) sq[atomicAdd(&nsq, 1)] = idx;
-      }
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long idx = base + lane;
+    bool keep = false;
+    if (idx < total) {
+      int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
+      keep = diffract_candidate(a.wedges[w], a.txs[link / a.nrx], a.rx[link % a.nrx]);
     }
-    __syncthreads();
-    const int n = nsq;  // at most 63 left over + 64 new
-    if (!more && n == 0) break;
-    if (n >= 64 || !more) {
-      const int m = min(n, 64);
-      if (tid < m) diffract_pair(a, sq[n - m + tid], k, lam, ovf, st);
-      __syncthreads();
-      if (tid == 0) nsq = n - m;
-      __syncthreads();
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & ((1u << lane) - 1u));
+    if (keep) {
+      if (at < a.dsurv_cap) a.dsurv[at] = (unsigned long long)idx;
+      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
     }
   }
+}
+
+// Pass 2 over the survivors: the exact FP64 test, the occlusion legs and the
+// UTD field. The SM's FP64 pipe is narrow and a warp instruction costs it the
+// same whatever the number of active lanes, so the survivors are dealt one
+// warp per SM (survivor i to block i mod grid): every SM gets an equal share,
+// packed into one warp, instead of a few SMs taking whole batches.
+__global__ void __launch_bounds__(32) k_diffract(PathArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackTrace);
+  const unsigned n = min(a.ctr->n_dsurv, a.dsurv_cap);
+  const double k = 2.0 * M_PI * a.freq / 299792458.0, lam = 299792458.0 / a.freq;
+  unsigned ovf = 0;
+  for (unsigned i = blockIdx.x + gridDim.x * threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    diffract_pair(a, (long)a.dsurv[i], k, lam, ovf, st);
   if (ovf) {
     atomicAdd(&a.ctr->stack_overflow, 1u);
     atomicOr(&a.ctr->err, ERR_STACK);
@@ -1100,10 +1102,15 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_diffract(const PathArgs& a, int nlinks, int grid, cudaStream_t st) {
+cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t st) {
   if (!a.wedges || a.nw <= 0) return cudaSuccess;
   k_wedge_geom<<<(a.nw + 255) / 256, 256, 0, st>>>(a.tris, a.slot_of_id, a.wtopo, a.nw, a.wedges);
-  if (nlinks > 0) k_diffract<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a, nlinks);
+  if (nlinks > 0) {
+    long total = (long)nlinks * a.nw;
+    long g = std::min<long>((total + 255) / 256, 8L * sms);
+    k_diffract_pre<<<(int)std::max<long>(g, 1), 256, 0, st>>>(a, nlinks);
+    k_diffract<<<sms, 32, 32 * kStackTrace * sizeof(int), st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ struct PathArgs {
   Wedge* wedges;                  // geometry, rebuilt every frame from the world triangles
   const WedgeTopo* wtopo;
   int nw;
+  unsigned long long* dsurv;      // (link, wedge) pair indices past the FP32 pre-test
+  unsigned dsurv_cap;
   const StickyKey* sticky_prev;
   const unsigned* sticky_prev_n;
   unsigned sticky_cap;
@@ -64,7 +66,7 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_sticky_probe(const PathArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st);
 // First-order edge diffraction paths of every (link, wedge) (after validation).
-cudaError_t launch_diffract(const PathArgs& a, int nlinks, int grid, cudaStream_t st);
+cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t st);
 // Per-link sums and ordered output; links above kScanLinks take their output
 // offsets from a scan (a.link_off) instead of summing the lower links' counts.
 constexpr int kScanLinks = 4096;
