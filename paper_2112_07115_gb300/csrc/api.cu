@@ -1107,9 +1107,9 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
       CK(cudaMemcpy(s->wtopo, w.data(), sizeof(WedgeTopo) * w.size(), cudaMemcpyHostToDevice));
     }
   }
-  if (on && s->nw && !s->dsurv) {
-    CK(dalloc(&s->dsurv, (size_t)65536));
-    s->dsurv_cap = 65536;
+  if (on && s->nw && !s->dsurv) {  // grown (and the frame traced again) when a frame needs more
+    CK(dalloc(&s->dsurv, (size_t)1024));
+    s->dsurv_cap = 1024;
   }
   s->diffraction = on != 0;
   if (n_wedges) *n_wedges = s->nw;

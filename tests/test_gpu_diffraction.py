@@ -136,3 +136,45 @@ def test_highway_vehicle_wedges(cuda):
     which finds the wedges anew from each frame's world triangles."""
     sc = scenes.highway(n_frames=4, n_vehicles=60, length=600.0)
     _check(cuda, sc, 50_000, 2, range(4), mode=dcem.MODE_COHERENT, min_diff=4)
+
+
+def test_many_receivers_grow_the_survivor_list(cuda):
+    """A street grid of 4096 receivers against every wedge of a reduced urban
+    grid: more pairs pass the FP32 pre-test than the survivor list's initial
+    1024 slots (there are more diffraction paths than that, and each comes
+    from a survivor), so the frame grows the list and is traced again. Its
+    diffraction paths must equal, record for record, those of the same frame
+    traced in eight batches of 512 receivers."""
+    torch = cuda
+    sc = scenes.urban_grid(blocks=2, parcels=2, n_vehicles=12, n_tx=1, budgets=(20_000, 20_000), n_static_rx=4,
+                           n_frames=2, max_refl=2)
+    lo, hi = sc.tris.reshape(-1, 3).min(axis=0), sc.tris.reshape(-1, 3).max(axis=0)
+    g = np.stack(np.meshgrid(np.linspace(lo[0] + 1, hi[0] - 1, 64), np.linspace(lo[1] + 1, hi[1] - 1, 64),
+                             indexing="ij"), -1).reshape(-1, 2)
+    rx = np.concatenate([g, np.full((g.shape[0], 1), 1.5)], 1).astype(np.float32)
+    tx = sc.meta["tx"][0]
+    s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(scenes.fibonacci_sphere(20_000))
+    s.set_diffraction(True)
+    prm = dcem.default_params(max_refl=2, freq_hz=28e9)
+    s.update_transforms(sc.xf[1])
+    whole = s.trace(tx, rx, prm, max_paths=1 << 20)
+    dw = whole.paths[(whole.paths["tri"][:, 0] & dcem.TRI_DIFFRACT) != 0]
+    assert dw.shape[0] > 1024
+    parts = []
+    for k in range(8):
+        sl = slice(512 * k, 512 * (k + 1))
+        fr = s.trace(tx, rx[sl], prm, max_paths=1 << 18)
+        p = fr.paths[(fr.paths["tri"][:, 0] & dcem.TRI_DIFFRACT) != 0].copy()
+        p["rx"] += 512 * k
+        parts.append(p)
+    db = np.concatenate(parts)
+    # a first-order diffraction path is its (receiver, wedge); the record key
+    # hashes the receiver's index within its call, so it is not compared
+    wa, wb = dw["tri"][:, 0], db["tri"][:, 0]
+    assert sorted(zip(dw["rx"].tolist(), wa.tolist())) == sorted(zip(db["rx"].tolist(), wb.tolist()))
+    oa = np.lexsort((wa, dw["rx"]))
+    ob = np.lexsort((wb, db["rx"]))
+    for f in ("len_m", "amp_re", "amp_im"):
+        assert np.array_equal(dw[f][oa], db[f][ob]), f
+    s.close()
