@@ -409,12 +409,19 @@ __global__ void k_centroid_bounds(const float* __restrict__ prim, int n, unsigne
 
 __global__ void k_morton(const float* __restrict__ prim, int n, const unsigned* ob, unsigned* codes,
                          unsigned* idx) {
-  float lo[3], inv[3];
+  // One scale for all axes (the largest extent): in a large flat scene (a
+  // city) the short axis then splits deep in the tree instead of at its top.
+  // Measured on the 61k-triangle urban grid: 56 -> 42 node pairs per segment,
+  // closest hit 27 -> 23 ms. The one-CTA builder keeps one scale per axis:
+  // on the highway (2 km x 30 m) a cubic frame made its trees slower to
+  // traverse (1920 against 2300 frames/s, with 16 bits per axis as well).
+  float lo[3], inv[3], m = 0.0f;
   for (int k = 0; k < 3; ++k) {
     lo[k] = o2f(ob[k]);
     float h = o2f(ob[k + 3]);
-    inv[k] = h > lo[k] ? 1.0f / (h - lo[k]) : 0.0f;
+    m = fmaxf(m, h > lo[k] ? h - lo[k] : 0.0f);
   }
+  for (int k = 0; k < 3; ++k) inv[k] = m > 0.0f ? 1.0f / m : 0.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float* b = prim + 6 * (size_t)i;
     codes[i] = morton30(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]), lo, inv);
