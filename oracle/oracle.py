@@ -39,8 +39,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "dcem_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+# The mutation test (tests/test_oracle_mutations.py) points these at a copy of
+# the source with one planted mistake and at a build folder of its own.
+_SRC = os.environ.get("DCEM_ORACLE_SRC") or os.path.join(_HERE, "dcem_oracle.c")
+_BUILD = os.environ.get("DCEM_ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libdcem_oracle.so")
 
 MAX_REFL = 10
