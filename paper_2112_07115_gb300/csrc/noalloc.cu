@@ -7,8 +7,10 @@
 // cudaMalloc after start-up (cudaMalloc can synchronise the device and stall
 // the loop). dcem_reduce_paths_noalloc serves them: the caller passes device
 // buffers for the inputs and outputs, and the only scratch the kernels need
-// lives in one file-scope device array of fixed size, reserved when the
-// library is loaded.
+// lives in one file-scope device array of fixed size. The CUDA runtime may
+// load this file's kernels and reserve that array lazily, at the first use
+// on a device; a set-up call (n_paths = 0, nrx = 0) made once per device at
+// start-up does that work, so that later calls allocate nothing.
 #include <mutex>
 
 #include "dcem_internal.cuh"
@@ -32,9 +34,9 @@ struct NaScratch {
   int order[kNaMaxPaths];      // path indices grouped by receiver
 };
 
-// The scratch of every call on a device (about 310 KB per device, held while
-// the library is loaded). Host code reaches it only through the address
-// returned by cudaGetSymbolAddress.
+// The scratch of every call on a device (about 310 KB per device, held from
+// the first use on that device until the process exits). Host code reaches it
+// only through the address returned by cudaGetSymbolAddress.
 static __device__ __align__(256) NaScratch g_na_scratch;
 
 __global__ void k_na_clear(NaScratch* s, int nrx) {
@@ -89,9 +91,13 @@ __global__ void k_na_scatter(NaScratch* s, const dcem_path* __restrict__ p, int 
   }
 }
 
-// One CTA per receiver: its paths sorted by key, then the same fixed-order
-// sums as the frame reduction (thread t takes sorted positions t, t+256, ...,
-// then a fixed binary tree), so the results match dcem_trace_frame's.
+// One CTA per receiver: its paths sorted by key, records with equal keys (the
+// same sequence from two transmitters) by record index, then the same
+// fixed-order sums as the frame reduction (thread t takes sorted positions t,
+// t+256, ..., then a fixed binary tree). The order, and so every bit of the
+// sums, depends only on the records, not on the order in which the scatter's
+// atomics placed them; for one transmitter's records (distinct keys) it is
+// the frame's order, so the results match dcem_trace_frame's.
 __global__ void __launch_bounds__(kNaThreads) k_na_reduce(NaScratch* s, const dcem_path* __restrict__ p, int nrx,
                                                           double tx_power, double* field, double* pc,
                                                           double* pi) {
@@ -121,8 +127,11 @@ __global__ void __launch_bounds__(kNaThreads) k_na_reduce(NaScratch* s, const dc
         int ixj = i ^ j;
         if (ixj > i) {
           unsigned long long x = skey[i], y = skey[ixj];
+          int xi = sidx[i], yi = sidx[ixj];
+          // (key, record index); padding (~0, -1) sorts last
+          bool gt = x != y ? x > y : (unsigned)xi > (unsigned)yi;
           bool up = (i & k) == 0;
-          if ((x > y) == up) {
+          if (gt == up) {
             skey[i] = y;
             skey[ixj] = x;
             int t = sidx[i];
@@ -180,7 +189,7 @@ extern "C" int dcem_reduce_paths_noalloc(const dcem_path* paths, int32_t n_paths
   if (n_paths < 0 || nrx < 0 || (n_paths > 0 && !paths)) return DCEM_ERR_ARG;
   if (!(tx_power_w > 0.0)) return DCEM_ERR_ARG;
   if (n_paths > kNaMaxPaths || nrx > kNaMaxRx) return DCEM_ERR_CAPACITY;
-  if (nrx == 0) return DCEM_OK;
+  if (nrx == 0 && n_paths > 0) return DCEM_ERR_ARG;  // no receiver can hold them
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_status(e);
@@ -199,10 +208,20 @@ extern "C" int dcem_reduce_paths_noalloc(const dcem_path* paths, int32_t n_paths
       size_t smem = (size_t)kNaMaxPerRx * (sizeof(unsigned long long) + sizeof(int));
       e = cudaFuncSetAttribute(k_na_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return na_status(e);
+      // the other kernels too, so that a lazily loading runtime loads them
+      // all now rather than at a later call
+      cudaFuncAttributes fa;
+      const void* fns[] = {(const void*)k_na_clear, (const void*)k_na_count, (const void*)k_na_scan,
+                           (const void*)k_na_scatter};
+      for (const void* fn : fns) {
+        e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return na_status(e);
+      }
       g_na_attr[dev] = true;
     }
     s = g_na_addr[dev];
   }
+  if (nrx == 0) return DCEM_OK;  // the set-up call
   cudaStream_t st = (cudaStream_t)stream;
   int g = (nrx + 255) / 256;
   k_na_clear<<<g, 256, 0, st>>>(s, nrx);
