@@ -172,6 +172,8 @@ typedef struct {
   int32_t paths_sticky;        /* DCEM_MODE_STICKY: valid paths that only the
                                   path cache kept (no ray captured them)         */
   int32_t child_rays;          /* transmission: child rays spawned this frame   */
+  int32_t keys_reused;         /* coherent: distinct keys whose validation was
+                                  copied from the previous frame               */
 } dcem_stats;
 
 typedef struct {
@@ -468,7 +470,7 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
  * cudaMalloc after start-up (an allocation can synchronise the device and
  * stall the loop). The caller passes the inputs and outputs; the scratch
  * lives in one fixed device array of the library (about 310 KB per device,
- * reserved while the library is loaded).
+ * held from the first call on that device until the process exits).
  *   paths      device, n_paths records (e.g. the paths dcem_trace_frame
  *              wrote to a device result); order does not matter
  *   nrx        receivers; every paths[i].rx must lie in [0, nrx) (the
@@ -479,19 +481,27 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
  *   p_inc_dbm  device, nrx values of P_t sum |a|^2 in dBm, or NULL
  *   stream     cudaStream_t of the work (NULL = legacy default stream)
  * The sums use the same order as dcem_trace_frame (paths of a receiver
- * sorted by key), so the results equal those of the frame for the same
- * records bit for bit.
+ * sorted by key; records with equal keys, e.g. one sequence from two
+ * transmitters, by their index in `paths`), so the results equal those of
+ * the frame for the same records bit for bit and never depend on the
+ * scheduling of the device work.
  * Limits: n_paths <= 65536, nrx <= 4096, at most 4096 paths per receiver;
  * beyond them the call returns DCEM_ERR_CAPACITY without touching the GPU
  * (the per-receiver limit is checked on the device).
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call on a device shares the one scratch
- * array and clears what it needs at its start: calls whose work overlaps on
- * the GPU (for instance on two streams) race, so order them. The call
- * synchronises `stream` before returning, to report device-side errors.
- * Errors: DCEM_ERR_ARG (null or negative arguments, a receiver index out of
- * range), DCEM_ERR_CAPACITY, DCEM_ERR_CUDA. */
+ * Set-up: the first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) and the kernels' attributes with that device
+ * current. A CUDA runtime that loads modules lazily (the default) loads this
+ * call's kernels and reserves the scratch array at that moment, which may
+ * allocate device memory; so make one set-up call per device at start-up,
+ * before any stream capture: n_paths = 0 and nrx = 0 (paths may be NULL)
+ * does the set-up and nothing else. Calls after it allocate nothing.
+ * Every call on a device shares the one scratch array and clears what it
+ * needs at its start: calls whose work overlaps on the GPU (for instance on
+ * two streams) race, so order them. The call synchronises `stream` before
+ * returning, to report device-side errors.
+ * Errors: DCEM_ERR_ARG (null or negative arguments, records but no
+ * receivers, a receiver index out of range), DCEM_ERR_CAPACITY,
+ * DCEM_ERR_CUDA. */
 int dcem_reduce_paths_noalloc(const dcem_path* paths, int32_t n_paths, int32_t nrx, double tx_power_w,
                               double* field, double* p_coh_dbm, double* p_inc_dbm, void* stream);
 

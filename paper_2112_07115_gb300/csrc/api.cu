@@ -312,9 +312,18 @@ struct dcem_scene {
   int* cand_slot = nullptr;
   int* uniq = nullptr;
   unsigned ucap = 0;
-  PathRec* prec = nullptr;
-  double* vpts = nullptr;
+  PathRec* prec = nullptr;      // per distinct key (two buffers by frame parity: this
+  double* vpts = nullptr;       // frame's and the previous frame's, for validation reuse)
   int* vstate = nullptr;
+  PathRec* prec_b = nullptr;
+  double* vpts_b = nullptr;
+  int* vstate_b = nullptr;
+  unsigned long long* ckey = nullptr;      // per distinct key: its link key
+  unsigned long long* vc_key[2] = {nullptr, nullptr};  // link key -> record index tables,
+  unsigned* vc_u[2] = {nullptr, nullptr};              // one per parity
+  unsigned vc_cap = 0;
+  bool vc_valid = false;        // the previous frame built its table (parity s->cur)
+  unsigned char* obj_moved = nullptr;  // per rigid object: transform changed this frame
   dcem_path* pout = nullptr;
   StickyKey* sticky[2] = {nullptr, nullptr};  // sticky mode: kept paths (by parity)
   unsigned* sticky_n = nullptr;               // their counts (device, by parity)
@@ -382,6 +391,8 @@ void scene_free(dcem_scene* s) {
   dfree(s->queue); dfree(s->cand[0]); dfree(s->cand[1]); dfree(s->prev_ncand); dfree(s->hkey);
   dfree(s->hrep); dfree(s->cand_slot); dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->rx3);
   dfree(s->vpts); dfree(s->vstate); dfree(s->sticky[0]); dfree(s->sticky[1]); dfree(s->sticky_n);
+  dfree(s->prec_b); dfree(s->vpts_b); dfree(s->vstate_b); dfree(s->ckey); dfree(s->vc_key[0]);
+  dfree(s->vc_key[1]); dfree(s->vc_u[0]); dfree(s->vc_u[1]); dfree(s->obj_moved);
   dfree(s->rx_cur); dfree(s->rx_traced); dfree(s->rx_moved); dfree(s->moved_list); dfree(s->bucket);
   dfree(s->bucket_cnt); dfree(s->rxout); dfree(s->link_off); dfree(s->txs);
   if (s->txs_h) cudaFreeHost(s->txs_h);
@@ -525,11 +536,23 @@ int ensure_paths(dcem_scene* s, unsigned cand_cap, unsigned ucap) {
   }
   if (ucap > s->ucap) {
     dfree(s->uniq); dfree(s->prec); dfree(s->pout); dfree(s->vpts); dfree(s->vstate);
+    dfree(s->prec_b); dfree(s->vpts_b); dfree(s->vstate_b); dfree(s->ckey);
+    dfree(s->vc_key[0]); dfree(s->vc_key[1]); dfree(s->vc_u[0]); dfree(s->vc_u[1]);
     CK(dalloc(&s->uniq, ucap));
     CK(dalloc(&s->prec, ucap));
     CK(dalloc(&s->pout, ucap));
     CK(dalloc(&s->vpts, (size_t)ucap * 3 * (kMaxRefl + 2)));
     CK(dalloc(&s->vstate, ucap));
+    CK(dalloc(&s->prec_b, ucap));
+    CK(dalloc(&s->vpts_b, (size_t)ucap * 3 * (kMaxRefl + 2)));
+    CK(dalloc(&s->vstate_b, ucap));
+    CK(dalloc(&s->ckey, ucap));
+    s->vc_cap = pow2_at_least(2ull * ucap);
+    for (int b = 0; b < 2; ++b) {
+      CK(dalloc(&s->vc_key[b], s->vc_cap));
+      CK(dalloc(&s->vc_u[b], s->vc_cap));
+    }
+    s->vc_valid = false;  // the previous frame's records are gone
     // sticky mode: kept paths of the previous frame and of this one
     dfree(s->sticky[0]); dfree(s->sticky[1]);
     CK(dalloc(&s->sticky[0], ucap));
@@ -799,6 +822,7 @@ int dcem_scene_create(const float* tris, int32_t ntri, const int32_t* tri_mat, c
   CKF(dalloc(&s->obj_box_cur, 6 * (size_t)nobj));
   CKF(dalloc(&s->obj_box_traced, 6 * (size_t)nobj));
   CKF(dalloc(&s->moved_boxes, 12 * (size_t)nobj));
+  CKF(dalloc(&s->obj_moved, (size_t)std::max(nobj, 1)));
   s->mv_cap = std::min(2 * nobj, kSmallBuild);
   CKF(dalloc(&s->mvt_nodes, 4 * (size_t)s->mv_cap));
   CKF(dalloc(&s->mvt_parent, s->mv_cap));
@@ -1231,6 +1255,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   fp.obj_box_cur = s->obj_box_cur;
   fp.obj_box_traced = s->obj_box_traced;
   fp.moved_boxes = s->moved_boxes;
+  fp.obj_moved = s->obj_moved;
   fp.ctr = s->ctr;
   fp.trx.prim = s->rx_prim;
   fp.trx.n = nrx;
@@ -1280,10 +1305,39 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.cand_slot = s->cand_slot;
   q.uniq = s->uniq;
   q.ucap = s->ucap;
-  q.prec = s->prec;
+  // this frame's records: buffer nxt (a = the frame's parity); the previous
+  // frame's: buffer cur
+  PathRec* precs[2] = {s->prec, s->prec_b};
+  double* vptss[2] = {s->vpts, s->vpts_b};
+  int* vstates[2] = {s->vstate, s->vstate_b};
+  q.prec = precs[nxt];
   q.ray_perm = s->ray_perm;
-  q.vpts = s->vpts;
-  q.vstate = s->vstate;
+  q.vpts = vptss[nxt];
+  q.vstate = vstates[nxt];
+  // validation reuse: exact coherent mode (not sticky), same validation
+  // parameters as the previous frame, whose table and records are intact
+  const bool vc_on = p->mode == DCEM_MODE_COHERENT && s->max_trans == 0;
+  q.reuse = (coherent && vc_on && s->vc_valid && p->freq_hz == s->cparams.freq_hz &&
+             std::memcmp(p->pol, s->cparams.pol, sizeof(p->pol)) == 0 && p->eps_occ == s->cparams.eps_occ &&
+             p->prec == s->cparams.prec) ? 1 : 0;
+  q.vc_prev_key = s->vc_key[s->cur];
+  q.vc_prev_u = s->vc_u[s->cur];
+  q.prev_prec = precs[s->cur];
+  q.prev_vpts = vptss[s->cur];
+  q.prev_vstate = vstates[s->cur];
+  q.vc_cap = s->vc_cap;
+  q.vc_next_key = vc_on ? s->vc_key[nxt] : nullptr;
+  q.vc_next_u = s->vc_u[nxt];
+  q.ckey = vc_on ? s->ckey : nullptr;
+  q.rx_moved = s->rx_moved;
+  q.obj_moved = s->obj_moved;
+  q.tri_obj = s->tri_obj_d;
+  q.mvt.nodes = s->mvt_nodes;
+  q.mvt.perm = s->mvt_perm;
+  q.mvt.root = s->mvt_root;
+  q.mvt.root_box = s->mvt_root_box;
+  q.mvt.max_visits = 2 * s->mv_cap + 8;
+  q.mv_cap = (unsigned)s->mv_cap;
   q.N = N;
   q.bucket = s->bucket;
   q.bucket_cnt = s->bucket_cnt;
@@ -1379,6 +1433,8 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
     CK(cudaGetLastError());
     CK(cudaEventRecord(P.br[1], P.side));
   }
+  if (P.q.vc_next_key)  // the key table this frame builds for the next one
+    CK(cudaMemsetAsync(P.q.vc_next_key, 0, sizeof(unsigned long long) * P.q.vc_cap, st));
   CK(launch_frame_prep(P.fp, st));
   if (tm) CK(rec(P.ev[1], st, cap));
   TraceArgs a = P.a;
@@ -1404,6 +1460,7 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   if (P.q.sticky_prev) CK(launch_sticky_probe(P.q, sms * 4, st));
   if (tm) CK(rec(P.ev[5], st, cap));
   CK(launch_validate(P.q, sms * 4, st));
+  if (P.q.vc_next_key) CK(launch_vcache_build(P.q, sms * 4, st));
   if (P.q.wedges) CK(launch_diffract(P.q, P.nlinks, sms, st));
   if (tm) CK(rec(P.ev[6], st, cap));
   // every counter is final here: the state the next frame compares against
@@ -1468,6 +1525,7 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->last_use_q = P.use_q;
   // kernels of this frame: prep, [mark, carry], trace, capture, dedupe x2, validate x3, reduce, end
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
+                 (P.q.vc_next_key ? 1 : 0) +
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
                  (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0);
   s->graph_replayed = 0;
@@ -1648,6 +1706,7 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
     for (int k = 0; k <= kMaxRefl; ++k) sp += c[0].n_spawn[k];
     S.child_rays = (int32_t)std::min<unsigned long long>(sp, 0x7fffffffull);
   }
+  S.keys_reused = (int32_t)c[0].n_val_reused;
   S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;
@@ -1698,6 +1757,7 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
   }
   out->n_paths = nvalid;
   s->cache_valid = true;
+  s->vc_valid = p->mode == DCEM_MODE_COHERENT && s->max_trans == 0;  // this frame built its key table
   s->cparams = *p;
   s->ctx.assign(tx, tx + 3 * ntx);
   s->cnrx = nrx;

@@ -348,6 +348,7 @@ __global__ void __launch_bounds__(1024) k_frame_prep(FramePrepArgs a, int np2, i
         bool moved = false;
         for (int k = 0; k < 12; ++k)
           moved = moved || (__float_as_uint(a.xf_cur[12 * ob + k]) != __float_as_uint(a.xf_traced[12 * ob + k]));
+        if (a.obj_moved) a.obj_moved[ob] = moved ? 1 : 0;
         if (!moved) continue;
         atomicAdd(&a.ctr->objects_moved, 1u);
         const unsigned* boxes[2] = {a.obj_box_traced, a.obj_box_cur};

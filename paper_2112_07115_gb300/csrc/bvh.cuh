@@ -61,6 +61,7 @@ struct FramePrepArgs {
   const unsigned* obj_box_cur = nullptr;
   const unsigned* obj_box_traced = nullptr;
   float* moved_boxes = nullptr;
+  unsigned char* obj_moved = nullptr;  // nobj flags: transform changed (coherent frames)
   DevCounters* ctr = nullptr;
   SmallTreeArgs trx, tmv;
 };

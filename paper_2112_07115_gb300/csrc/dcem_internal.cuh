@@ -81,6 +81,7 @@ struct DevCounters {
   unsigned int n_spawn[kMaxRefl + 1];    // transmission: child rays spawned by trace pass p
   unsigned int work_pass[kMaxRefl + 1];  // ... work counters of passes p >= 1
   unsigned int n_dsurv;            // diffraction: (link, wedge) pairs past the FP32 pre-test
+  unsigned int n_val_reused;       // coherent frames: distinct keys whose validation was reused
 };
 
 // Sticky mode: a valid path kept for the next frame (link, depth, sequence).

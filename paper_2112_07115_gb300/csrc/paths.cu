@@ -222,61 +222,53 @@ template <class T> __device__ __forceinline__ v3<T> vof(float x, float y, float 
   return {sc_of<T>(x), sc_of<T>(y), sc_of<T>(z)};
 }
 
-// FP32 complex arithmetic for the reflection coefficients and polarisation
-struct cf {
-  float re, im;
+// Complex FP64 arithmetic: reflection coefficients, polarisation and the
+// diffraction coefficient.
+struct zd {
+  double re, im;
 };
-__device__ __forceinline__ cf F(float r, float i = 0.0f) { return cf{r, i}; }
-__device__ __forceinline__ cf operator+(cf a, cf b) { return F(a.re + b.re, a.im + b.im); }
-__device__ __forceinline__ cf operator-(cf a, cf b) { return F(a.re - b.re, a.im - b.im); }
-__device__ __forceinline__ cf operator*(cf a, cf b) { return F(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
-__device__ __forceinline__ cf operator*(cf a, float s) { return F(a.re * s, a.im * s); }
-__device__ __forceinline__ cf fdiv(cf a, cf b) {  // Smith's algorithm
-  if (fabsf(b.re) >= fabsf(b.im)) {
-    float r = b.im / b.re, den = b.re + b.im * r;
-    return F((a.re + a.im * r) / den, (a.im - a.re * r) / den);
-  }
-  float r = b.re / b.im, den = b.re * r + b.im;
-  return F((a.re * r + a.im) / den, (a.im * r - a.re) / den);
+__device__ __forceinline__ zd Z(double r, double i = 0.0) { return zd{r, i}; }
+__device__ __forceinline__ zd operator+(zd a, zd b) { return Z(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ zd operator-(zd a, zd b) { return Z(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ zd operator*(zd a, zd b) { return Z(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+__device__ __forceinline__ zd operator*(zd a, double s) { return Z(a.re * s, a.im * s); }
+__device__ __forceinline__ zd zdiv(zd a, zd b) {
+  double d = b.re * b.re + b.im * b.im;
+  return Z((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
 }
-__device__ __forceinline__ cf fsqrt_p(cf z) {  // principal square root
-  float m = hypotf(z.re, z.im);
-  if (m == 0.0f) return F(0.0f, 0.0f);
-  float a = sqrtf(0.5f * (m + fabsf(z.re)));
-  if (z.re >= 0.0f) return F(a, z.im / (2.0f * a));
-  return F(fabsf(z.im) / (2.0f * a), copysignf(a, z.im));
+__device__ __forceinline__ zd zexp(zd a) {
+  double m = exp(a.re), sn, cs;
+  sincos(a.im, &sn, &cs);
+  return Z(m * cs, m * sn);
 }
-struct cf3 {
-  cf x, y, z;
-};
-__device__ __forceinline__ cf fdot(cf3 e, float3 v) { return e.x * v.x + e.y * v.y + e.z * v.z; }
-__device__ __forceinline__ float3 funit(float3 v) {
-  float n = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-  return f3(v.x / n, v.y / n, v.z / n);
-}
-__device__ __forceinline__ float3 fcross(float3 a, float3 b) {
-  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float fdot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 fdir(d3 a, d3 b) {  // unit vector a -> b from FP64 points
-  d3 v = b - a;
-  return funit(f3((float)v.x, (float)v.y, (float)v.z));
-}
-// Polarisation of an isotropic antenna along unit d: u - (u.d) d, normalised.
-__device__ __forceinline__ float3 fpol(float3 u, float3 d, unsigned& flags) {
-  float ud = fdot3(u, d);
-  float3 p = f3(u.x - ud * d.x, u.y - ud * d.y, u.z - ud * d.z);
-  float n = sqrtf(fdot3(p, p));
-  if (n < 1e-6f) {
-    flags |= DCEM_PATH_POL_DEGENERATE;
-    float3 ax = fabsf(d.x) < 0.9f ? f3(1, 0, 0) : f3(0, 1, 0);
-    float ad = fdot3(ax, d);
-    p = f3(ax.x - ad * d.x, ax.y - ad * d.y, ax.z - ad * d.z);
-    n = sqrtf(fdot3(p, p));
-  }
-  return f3(p.x / n, p.y / n, p.z / n);
+__device__ __forceinline__ zd zsqrt(zd a) {  // principal branch
+  double r = hypot(a.re, a.im);
+  double x = sqrt(0.5 * (r + fabs(a.re)));
+  if (x == 0.0) return Z(0.0, 0.0);
+  double y = a.im / (2.0 * x);
+  return a.re >= 0.0 ? Z(x, y) : Z(fabs(y), a.im >= 0.0 ? x : -x);
 }
 
+__device__ __forceinline__ float fdot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+struct z3 {
+  zd x, y, z;
+};
+__device__ __forceinline__ zd zdot(z3 e, d3 v) { return e.x * v.x + e.y * v.y + e.z * v.z; }
+__device__ __forceinline__ d3 dir_of(d3 a, d3 b) { return du(b - a); }  // unit vector a -> b
+// Polarisation of an isotropic antenna along unit d: u - (u.d) d, normalised
+// (a fixed axis instead when u is along d; the path is then flagged).
+__device__ __forceinline__ d3 pol_of(d3 u, d3 d, unsigned& flags) {
+  d3 p = u - d * dd(u, d);
+  double n = dn(p);
+  if (n < 1e-9) {
+    flags |= DCEM_PATH_POL_DEGENERATE;
+    d3 ax = fabs(d.x) < 0.9 ? mk3(1, 0, 0) : mk3(0, 1, 0);
+    p = ax - d * dd(ax, d);
+    n = dn(p);
+  }
+  return p * (1.0 / n);
+}
 
 // ---------------------------------------------------------------------------
 // validation + field in three kernels:
@@ -291,11 +283,52 @@ __device__ __forceinline__ float3 fpol(float3 u, float3 d, unsigned& flags) {
 // b + gridDim * t, so that every SM gets a share.
 __device__ __forceinline__ unsigned spread_index(unsigned i) { return blockIdx.x + gridDim.x * i; }
 
+// Validation reuse (Sec. III "Propagation path caching": the cached paths
+// are re-checked each frame; here a check is skipped when its result cannot
+// have changed). The previous frame's record of the same link key is copied
+// bit for bit when the receiver did not move (a coherent frame has the same
+// transmitter and parameters), no triangle of the sequence belongs to an
+// object that moved (so the image geometry is the same), and, for a record
+// whose geometry was valid, no sub-segment meets a moved object's old or new
+// box (so its occlusion test is the same).
+__device__ __forceinline__ int vc_find(const PathArgs& a, unsigned long long key) {
+  const unsigned mask = a.vc_cap - 1u;
+  unsigned slot = (unsigned)(key & mask);
+  for (unsigned p = 0; p < a.vc_cap; ++p) {
+    unsigned long long k = a.vc_prev_key[slot];
+    if (k == 0ull) return -1;
+    if (k == key) return (int)a.vc_prev_u[slot];
+    slot = (slot + 1u) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ bool vc_reusable(const PathArgs& a, int pu, int rxi, int k, const int* ids, TStack& st) {
+  if (a.rx_moved[rxi % a.nrx]) return false;
+  for (int j = 0; j < k; ++j) {
+    int o = a.tri_obj[ids[j] & ~(kTransBit | kDiffBit)];
+    if (o >= 0 && a.obj_moved[o]) return false;
+  }
+  if (a.prev_vstate[pu] == 0) return true;  // invalid geometry: depends on nothing else
+  const d3* xs = reinterpret_cast<const d3*>(a.prev_vpts) + (size_t)pu * (kMaxRefl + 2);
+  for (int j = 0; j <= k; ++j) {
+    d3 p0 = xs[j], p1 = xs[j + 1];
+    d3 dv = p1 - p0;
+    RayPre rp = ray_pre(f3((float)p0.x, (float)p0.y, (float)p0.z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+    if (seg_hits_tree(a.mvt, rp, 1.0f, st)) return false;
+  }
+  return true;
+}
+
 // T = double (FP64) or df (double-float) for every step of the geometry;
 // path points and length are stored in FP64 either way.
 template <class T>
 __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackSmall);
   unsigned nu = min(a.ctr->n_unique, a.ucap);
+  const bool reuse = a.reuse && a.ctr->n_moved_boxes <= a.mv_cap;
   for (unsigned t = threadIdx.x;; t += blockDim.x) {
     unsigned u = spread_index(t);
     if (u >= nu) break;
@@ -304,10 +337,12 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
     int k, rxi, ray;
     int ids[kMaxRefl];
     unsigned fl0 = 0u;
+    unsigned long long lkey = 0ull;  // the link key (0: a sticky record)
     if (ci >= 0) {
       Cand c = a.cand[ci];
       int slot = a.cand_slot[ci];
       rec.key = a.hkey[slot];
+      lkey = rec.key;
       // this slot is no longer needed: leave the table empty for the next frame
       a.hkey[slot] = 0ull;
       a.hrep[slot] = ~0ull;
@@ -328,6 +363,31 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
       for (int j = 0; j < kMaxRefl; ++j) ids[j] = j < k ? sk.tri[j] : -1;
       rec.key = seq_key(rxi % a.nrx, k, [&](int j) { return ids[j]; });
       fl0 = DCEM_PATH_STICKY;
+    }
+    if (a.ckey) a.ckey[u] = lkey;
+    if (reuse && lkey) {
+      int pu = vc_find(a, lkey);
+      if (pu >= 0 && vc_reusable(a, pu, rxi, k, ids, st)) {
+        PathRec pr = a.prev_prec[pu];
+        pr.ray = ray;  // this frame's representative
+        const int ps = a.prev_vstate[pu];
+        const bool valid = ps == 1 || ps == 3;
+        if (ps != 0) {
+          const d3* src = reinterpret_cast<const d3*>(a.prev_vpts) + (size_t)pu * (kMaxRefl + 2);
+          d3* dst = reinterpret_cast<d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
+          for (int j = 0; j <= k + 1; ++j) dst[j] = src[j];
+        }
+        a.prec[u] = pr;
+        a.vstate[u] = valid ? 3 : ps;  // 3: valid, reused (occlusion and field skip it)
+        if (valid) {
+          unsigned pos = atomicAdd(&a.bucket_cnt[rxi], 1u);
+          if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)rxi * a.bucket_cap + pos] = (int)u;
+          else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+          atomicAdd(&a.ctr->n_valid, 1u);
+        }
+        atomicAdd(&a.ctr->n_val_reused, 1u);
+        continue;
+      }
     }
     rec.rx = rxi;
     rec.depth = k;
@@ -463,136 +523,165 @@ __global__ void __launch_bounds__(64) k_val_occ(PathArgs a) {
   }
 }
 
-// Field of a valid path. Length L and the phase k L are FP64 (the phase is
-// reduced modulo 2 pi in FP64 before an FP32 sincos); directions, Fresnel
-// coefficients and polarisation are FP32 (relative amplitude error ~1e-6).
-__global__ void __launch_bounds__(64) k_val_field(PathArgs a) {
-  unsigned nu = min(a.ctr->n_unique, a.ucap);
-  for (unsigned t = threadIdx.x;; t += blockDim.x) {
-    unsigned u = spread_index(t);
+// Field of a valid path, in FP64 throughout (Sec. III step 6, Eq. 1): the
+// directions of the sub-segments, the polarisation basis of each bounce, the
+// Fresnel coefficients and the phase k L (reduced modulo 2 pi in FP64 before
+// the sincos). FP64 runs at a small fraction of the FP32 rate on this GPU, so
+// a key is taken by a group of kFieldLanes lanes: each lane forms the
+// coefficients of its own bounces (they depend only on the path points), and
+// the group's first lane then carries the field through them in order.
+constexpr int kFieldLanes = 8;
+constexpr int kFieldThreads = 64;
+struct BounceCoef {
+  double sv[3], pin[3], pout[3];  // polarisation basis: s, p before and after the bounce
+  double te_re, te_im, tm_re, tm_im;  // Gamma_TE, Gamma_TM (a transmission: te_re = field factor)
+  int trans;
+  int pad;
+};
+struct FieldEnds {
+  double e0[3], prx[3];  // Tx and Rx polarisation along the first and last sub-segment
+  double sn, cs;          // sin, cos of the reduced phase
+  unsigned fl0, fl1;
+};
+
+__global__ void __launch_bounds__(kFieldThreads) k_val_field(PathArgs a) {
+  constexpr int kGroups = kFieldThreads / kFieldLanes;
+  __shared__ BounceCoef scoef[kGroups][kMaxRefl];
+  __shared__ FieldEnds sends[kGroups];
+  const unsigned nu = min(a.ctr->n_unique, a.ucap);
+  const int grp = threadIdx.x / kFieldLanes, gl = threadIdx.x % kFieldLanes;
+  const unsigned gmask = ((1u << kFieldLanes) - 1u) << ((threadIdx.x & 31) & ~(kFieldLanes - 1));
+  const d3 upol = mk3(a.pol.x, a.pol.y, a.pol.z);
+  const double wfac = -1.0 / (2.0 * M_PI * a.freq * 8.8541878128e-12);
+  BounceCoef* C = scoef[grp];
+  FieldEnds& ends = sends[grp];
+  for (unsigned it = 0;; ++it) {
+    unsigned u = blockIdx.x + gridDim.x * (grp + kGroups * it);
     if (u >= nu) break;
     if (a.vstate[u] != 1) continue;
     PathRec& rec = a.prec[u];
-    int k = rec.depth;
+    const int k = rec.depth;
     const d3* X = reinterpret_cast<const d3*>(a.vpts) + (size_t)u * (kMaxRefl + 2);
-    double L = rec.len;
-    unsigned fl = 0;
-    float3 upol = a.pol;
-    float3 din = fdir(X[0], X[1]);
-    float3 e0 = fpol(upol, din, fl);
-    cf3 E = {F(e0.x), F(e0.y), F(e0.z)};
-    float wfac = (float)(-1.0 / (2.0 * M_PI * a.freq * 8.8541878128e-12));
-    for (int j = 1; j <= k; ++j) {
-      int slot = a.slot_of_id[rec.tri[j - 1] & ~kTransBit];
-      const float4* tp = a.tris + 3 * (size_t)slot;
+    const double L = rec.len;
+    // bounce j (1..k): incoming X[j-1] -> X[j], outgoing X[j] -> X[j+1]
+    for (int j = 1 + gl; j <= k; j += kFieldLanes) {
+      BounceCoef& c = C[j - 1];
+      const int id = rec.tri[j - 1];
+      const float4* tp = a.tris + 3 * (size_t)a.slot_of_id[id & ~kTransBit];
       float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
-      if (rec.tri[j - 1] & kTransBit) {  // penetration loss L dB: field times 10^(-L/20)
-        float g = (float)pow(10.0, -(double)a.mats[__float_as_int(p1.w)].w / 20.0);
-        E.x = E.x * g;
-        E.y = E.y * g;
-        E.z = E.z * g;
+      const float4 mt = a.mats[__float_as_int(p1.w)];
+      if (id & kTransBit) {  // penetration loss L dB: field times 10^(-L/20)
+        c.trans = 1;
+        c.te_re = pow(10.0, -(double)mt.w / 20.0);
         continue;
       }
-      float3 nh = funit(fcross(f3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), f3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z)));
-      float3 dout = fdir(X[j], X[j + 1]);
-      float ct = fabsf(fdot3(din, nh));
-      float3 sv = fcross(din, nh);
-      float sn = sqrtf(fdot3(sv, sv));
-      if (sn < 1e-6f) {
-        float3 ax = fabsf(nh.x) < 0.9f ? f3(1, 0, 0) : f3(0, 1, 0);
-        sv = funit(fcross(nh, ax));
+      c.trans = 0;
+      d3 din = dir_of(X[j - 1], X[j]), dout = dir_of(X[j], X[j + 1]);
+      d3 q0 = mk3(p0.x, p0.y, p0.z);
+      d3 nh = du(dx(mk3(p1.x, p1.y, p1.z) - q0, mk3(p2.x, p2.y, p2.z) - q0));
+      double ct = fabs(dd(din, nh));
+      d3 sv = dx(din, nh);
+      double sn = dn(sv);
+      if (sn < 1e-12) {  // normal incidence: any unit vector perpendicular to n
+        d3 ax = fabs(nh.x) < 0.9 ? mk3(1, 0, 0) : mk3(0, 1, 0);
+        sv = du(dx(nh, ax));
       } else {
-        sv = f3(sv.x / sn, sv.y / sn, sv.z / sn);
+        sv = sv * (1.0 / sn);
       }
-      float3 pin = fcross(sv, din), pout = fcross(sv, dout);
-      const float4 mt = a.mats[__float_as_int(p1.w)];
-      cf gte, gtm;
+      d3 pin = dx(sv, din), pout = dx(sv, dout);
+      zd gte, gtm;
       if (mt.z != 0.0f) {
-        gte = F(-1.0f);
-        gtm = F(1.0f);
+        gte = Z(-1.0);
+        gtm = Z(1.0);
       } else {
-        cf ec = F(mt.x, mt.y * wfac);
-        cf root = fsqrt_p(ec - F(1.0f - ct * ct));
-        gte = fdiv(F(ct) - root, F(ct) + root);
-        gtm = fdiv(ec * ct - root, ec * ct + root);
+        zd ec = Z((double)mt.x, (double)mt.y * wfac);
+        zd root = zsqrt(ec - Z(1.0 - ct * ct));
+        gte = zdiv(Z(ct) - root, Z(ct) + root);
+        gtm = zdiv(ec * ct - root, ec * ct + root);
       }
-      cf es = fdot(E, sv), ep = fdot(E, pin);
-      cf ts = gte * es, tpp = gtm * ep;
-      E.x = ts * sv.x + tpp * pout.x;
-      E.y = ts * sv.y + tpp * pout.y;
-      E.z = ts * sv.z + tpp * pout.z;
-      din = dout;
+      c.sv[0] = sv.x; c.sv[1] = sv.y; c.sv[2] = sv.z;
+      c.pin[0] = pin.x; c.pin[1] = pin.y; c.pin[2] = pin.z;
+      c.pout[0] = pout.x; c.pout[1] = pout.y; c.pout[2] = pout.z;
+      c.te_re = gte.re; c.te_im = gte.im;
+      c.tm_re = gtm.re; c.tm_im = gtm.im;
     }
-    float3 prx = fpol(upol, f3(-din.x, -din.y, -din.z), fl);
-    double lam = 299792458.0 / a.freq;
-    // phase k L reduced modulo 2 pi: subtract the nearest multiple of 2 pi,
-    // the product n * 2 pi taken exactly by an FMA against a two-part 2 pi
-    double kl = 2.0 * M_PI * a.freq / 299792458.0 * L;
-    double nq = rint(kl * (0.5 / M_PI));
-    double ph = fma(-nq, 6.283185307179586, kl);
-    ph = fma(-nq, 2.4492935982947064e-16, ph);
-    float sn, cs;
-    sincosf((float)ph, &sn, &cs);
-    cf proj = fdot(E, prx);
-    double g = lam / (4.0 * M_PI) / L;
-    double re = (double)(proj.re * cs + proj.im * sn), im = (double)(proj.im * cs - proj.re * sn);
-    rec.valid = 1;
-    rec.flags |= fl;
-    rec.amp_re = re * g;
-    rec.amp_im = im * g;
-    for (int j = 0; j < k; ++j) {
-      rec.pts[j][0] = (float)X[j + 1].x;
-      rec.pts[j][1] = (float)X[j + 1].y;
-      rec.pts[j][2] = (float)X[j + 1].z;
+    // the ends, on lanes that hold no bounce of a path of up to 5 bounces
+    if (gl == kFieldLanes - 1) {
+      unsigned f = 0;
+      d3 e0 = pol_of(upol, dir_of(X[0], X[1]), f);
+      ends.e0[0] = e0.x; ends.e0[1] = e0.y; ends.e0[2] = e0.z;
+      ends.fl0 = f;
+    } else if (gl == kFieldLanes - 2) {
+      unsigned f = 0;
+      d3 prx = pol_of(upol, dir_of(X[k + 1], X[k]), f);
+      ends.prx[0] = prx.x; ends.prx[1] = prx.y; ends.prx[2] = prx.z;
+      ends.fl1 = f;
+    } else if (gl == kFieldLanes - 3) {
+      // phase k L reduced modulo 2 pi: subtract the nearest multiple of 2 pi,
+      // the product n * 2 pi taken exactly by an FMA against a two-part 2 pi
+      double kl = 2.0 * M_PI * a.freq / 299792458.0 * L;
+      double nq = rint(kl * (0.5 / M_PI));
+      double ph = fma(-nq, 6.283185307179586, kl);
+      ph = fma(-nq, 2.4492935982947064e-16, ph);
+      sincos(ph, &ends.sn, &ends.cs);
     }
-    int rxi = rec.rx;
-    unsigned pos = atomicAdd(&a.bucket_cnt[rxi], 1u);
-    if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)rxi * a.bucket_cap + pos] = (int)u;
-    else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
-    atomicAdd(&a.ctr->n_valid, 1u);
-    if (a.sticky_next) {  // kept for the next frame
-      if (rec.flags & DCEM_PATH_STICKY) atomicAdd(&a.ctr->n_sticky_valid, 1u);
-      unsigned q = atomicAdd(&a.ctr->n_sticky_next, 1u);
-      if (q < a.sticky_cap) {
-        StickyKey sk;
-        sk.link = rxi;
-        sk.depth = k;
-        for (int j = 0; j < kMaxRefl; ++j) sk.tri[j] = rec.tri[j];
-        a.sticky_next[q] = sk;
+    __syncwarp(gmask);
+    if (gl == 0) {
+      z3 E = {Z(ends.e0[0]), Z(ends.e0[1]), Z(ends.e0[2])};
+      for (int j = 0; j < k; ++j) {
+        const BounceCoef& c = C[j];
+        if (c.trans) {
+          E.x = E.x * c.te_re;
+          E.y = E.y * c.te_re;
+          E.z = E.z * c.te_re;
+          continue;
+        }
+        const d3 sv = mk3(c.sv[0], c.sv[1], c.sv[2]), pin = mk3(c.pin[0], c.pin[1], c.pin[2]),
+                 pout = mk3(c.pout[0], c.pout[1], c.pout[2]);
+        zd ts = Z(c.te_re, c.te_im) * zdot(E, sv), tpp = Z(c.tm_re, c.tm_im) * zdot(E, pin);
+        E.x = ts * sv.x + tpp * pout.x;
+        E.y = ts * sv.y + tpp * pout.y;
+        E.z = ts * sv.z + tpp * pout.z;
+      }
+      const unsigned fl = ends.fl0 | ends.fl1;
+      const double sn = ends.sn, cs = ends.cs;
+      zd proj = zdot(E, mk3(ends.prx[0], ends.prx[1], ends.prx[2]));
+      double lam = 299792458.0 / a.freq;
+      double g = lam / (4.0 * M_PI) / L;
+      double re = proj.re * cs + proj.im * sn, im = proj.im * cs - proj.re * sn;
+      rec.valid = 1;
+      rec.flags |= fl;
+      rec.amp_re = re * g;
+      rec.amp_im = im * g;
+      for (int j = 0; j < k; ++j) {
+        rec.pts[j][0] = (float)X[j + 1].x;
+        rec.pts[j][1] = (float)X[j + 1].y;
+        rec.pts[j][2] = (float)X[j + 1].z;
+      }
+      int rxi = rec.rx;
+      unsigned pos = atomicAdd(&a.bucket_cnt[rxi], 1u);
+      if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)rxi * a.bucket_cap + pos] = (int)u;
+      else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+      atomicAdd(&a.ctr->n_valid, 1u);
+      if (a.sticky_next) {  // kept for the next frame
+        if (rec.flags & DCEM_PATH_STICKY) atomicAdd(&a.ctr->n_sticky_valid, 1u);
+        unsigned q = atomicAdd(&a.ctr->n_sticky_next, 1u);
+        if (q < a.sticky_cap) {
+          StickyKey sk;
+          sk.link = rxi;
+          sk.depth = k;
+          for (int j = 0; j < kMaxRefl; ++j) sk.tri[j] = rec.tri[j];
+          a.sticky_next[q] = sk;
+        }
       }
     }
+    __syncwarp(gmask);  // the group's shared records are free again
   }
 }
 
 // ---------------------------------------------------------------------------
 // first-order edge diffraction (Sec. III step 5) with the UTD
 // ---------------------------------------------------------------------------
-// Complex FP64 arithmetic for the diffraction coefficient.
-struct zd {
-  double re, im;
-};
-__device__ __forceinline__ zd Z(double r, double i = 0.0) { return zd{r, i}; }
-__device__ __forceinline__ zd operator+(zd a, zd b) { return Z(a.re + b.re, a.im + b.im); }
-__device__ __forceinline__ zd operator-(zd a, zd b) { return Z(a.re - b.re, a.im - b.im); }
-__device__ __forceinline__ zd operator*(zd a, zd b) { return Z(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
-__device__ __forceinline__ zd operator*(zd a, double s) { return Z(a.re * s, a.im * s); }
-__device__ __forceinline__ zd zdiv(zd a, zd b) {
-  double d = b.re * b.re + b.im * b.im;
-  return Z((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
-}
-__device__ __forceinline__ zd zexp(zd a) {
-  double m = exp(a.re), sn, cs;
-  sincos(a.im, &sn, &cs);
-  return Z(m * cs, m * sn);
-}
-__device__ __forceinline__ zd zsqrt(zd a) {  // principal branch
-  double r = hypot(a.re, a.im);
-  double x = sqrt(0.5 * (r + fabs(a.re)));
-  if (x == 0.0) return Z(0.0, 0.0);
-  double y = a.im / (2.0 * x);
-  return a.re >= 0.0 ? Z(x, y) : Z(fabs(y), a.im >= 0.0 ? x : -x);
-}
-
 // erfc(z) for Re z > 0: the Maclaurin series of erf (Abramowitz & Stegun
 // 7.1.5) for |z| < 3, else the continued fraction of A&S 7.1.14, truncated
 // after 40, 30 or 20 terms for |z| from 3, 3.5 or 4.5 on (relative error
@@ -1120,10 +1209,35 @@ cudaError_t launch_sticky_probe(const PathArgs& a, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st) {
-  if (a.prec_df) k_val_geom<df><<<grid, 64, 0, st>>>(a);
-  else k_val_geom<double><<<grid, 64, 0, st>>>(a);
+  const size_t gsm = 64 * kStackSmall * sizeof(int);
+  if (a.prec_df) k_val_geom<df><<<grid, 64, gsm, st>>>(a);
+  else k_val_geom<double><<<grid, 64, gsm, st>>>(a);
   k_val_occ<<<grid, 64, 64 * kStackTrace * sizeof(int), st>>>(a);
-  k_val_field<<<grid, 64, 0, st>>>(a);
+  k_val_field<<<grid, kFieldThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// The next frame's table: link key -> record index of each distinct key.
+__global__ void k_vcache_build(PathArgs a) {
+  unsigned nu = min(a.ctr->n_unique, a.ucap);
+  const unsigned mask = a.vc_cap - 1u;
+  for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
+    unsigned long long key = a.ckey[u];
+    if (!key) continue;
+    unsigned slot = (unsigned)(key & mask);
+    for (unsigned p = 0; p < a.vc_cap; ++p) {
+      unsigned long long prev = atomicCAS(&a.vc_next_key[slot], 0ull, key);
+      if (prev == 0ull || prev == key) {
+        a.vc_next_u[slot] = u;
+        break;
+      }
+      slot = (slot + 1u) & mask;
+    }
+  }
+}
+
+cudaError_t launch_vcache_build(const PathArgs& a, int grid, cudaStream_t st) {
+  k_vcache_build<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

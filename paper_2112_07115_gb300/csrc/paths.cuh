@@ -54,6 +54,24 @@ struct PathArgs {
   int nw;
   unsigned long long* dsurv;      // (link, wedge) pair indices past the FP32 pre-test
   unsigned dsurv_cap;
+  // validation reuse (coherent frames; Sec. III "Propagation path caching"):
+  // the previous frame's records of its distinct keys, found through a hash
+  // table of their link keys, are copied when nothing they depend on moved
+  int reuse;                      // 1: look the keys up in the previous frame's table
+  const unsigned long long* vc_prev_key;  // previous table: link key (0 = empty) and record index
+  const unsigned* vc_prev_u;
+  const PathRec* prev_prec;       // the previous frame's records, points and states
+  const double* prev_vpts;
+  const int* prev_vstate;
+  unsigned vc_cap;                // slots of each table (power of two)
+  unsigned long long* vc_next_key;  // this frame's table (built after validation), or null
+  unsigned* vc_next_u;
+  unsigned long long* ckey;       // per distinct key of this frame: its link key
+  const unsigned char* rx_moved;  // receivers whose position changed
+  const unsigned char* obj_moved; // rigid objects whose transform changed
+  const int* tri_obj;             // triangle id -> rigid object (-1 static)
+  SmallBvh mvt;                   // the moved objects' old and new boxes
+  unsigned mv_cap;                // boxes the tree holds (more moved boxes: no reuse)
   const StickyKey* sticky_prev;
   const unsigned* sticky_prev_n;
   unsigned sticky_cap;
@@ -65,6 +83,9 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st);
 // frame has join the distinct keys (validated like them).
 cudaError_t launch_sticky_probe(const PathArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_validate(const PathArgs& a, int grid, cudaStream_t st);
+// The table of this frame's distinct keys for the next frame's validation
+// reuse (after validation, before diffraction adds its records).
+cudaError_t launch_vcache_build(const PathArgs& a, int grid, cudaStream_t st);
 // First-order edge diffraction paths of every (link, wedge) (after validation).
 cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t st);
 // Per-link sums and ordered output; links above kScanLinks take their output

@@ -3,7 +3,7 @@
 Bit-exact: world vertices (fmaf transform), refit bounds (min/max), hit
 triangle ids per segment and captures of rays the oracle does not flag as
 within the FP32 margin of an edge, tie, self-hit offset or sphere boundary.
-Within tolerance: path lengths (1e-6 m), amplitudes (1e-4 relative), and
+Within tolerance: path lengths (1e-6 m), amplitudes (1e-6 relative), and
 per-receiver power (0.01 dB). Coherent frames must equal full retraces bit
 for bit.
 """
@@ -150,7 +150,7 @@ def test_highway_reduced_vs_oracle(cuda):
 @pytest.mark.parametrize("which", ["toy", "highway"])
 def test_double_float_validation_vs_oracle(cuda, which):
     """Validation geometry and phase in double-float (DCEM_PREC_DF32): the
-    same path set, lengths within 1e-6 m, amplitudes within 1e-4 and power
+    same path set, lengths within 1e-6 m, amplitudes within 1e-6 and power
     within 0.01 dB of the FP64 oracle."""
     if which == "toy":
         sc = scenes.toy_street()
