@@ -463,6 +463,40 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
                         const dcem_path* paths, int32_t n_paths, const dcem_params* params, int32_t ptr_kind,
                         double* field, double* dfield, double* dpcoh_dbm);
 
+/* The field derivatives of dcem_path_gradients from a hand-written
+ * reverse-mode (adjoint) kernel, evaluated at the parameters theta, and the
+ * gradient of a loss of the received powers: the field of Sec. III step 6
+ * (Eq. 1 with the spreading of Eq. 3) over the fixed paths, differentiated by
+ * one backward sweep per path. The kernel keeps only the path's vertices from
+ * its forward sweep (FP64 image sources and back-trace) and recomputes each
+ * bounce's directions, polarisation basis, Fresnel coefficients and incident
+ * field from them during the backward sweep; an object's translation reaches
+ * the vertices through the tangent of the image geometry. The cost per path
+ * does not grow with the number of parameters.
+ *   theta       n_params values, or NULL for the scene's current values:
+ *               eps_r, sigma of every material, then the x, y translation of
+ *               every rigid object (absolute: an object's triangles are
+ *               shifted by theta's translation minus the translation of its
+ *               current transform)
+ *   pcoh_bar    nrx values d loss / d P_coh[dBm] (a receiver without paths
+ *               contributes nothing), or NULL; needed for theta_bar
+ *   field       nrx x 2 (re, im) of sum a at theta, or NULL
+ *   pcoh_dbm    nrx values P_t |sum a|^2 in dBm at theta (-inf without
+ *               paths), or NULL
+ *   dfield      nrx x n_params x 2 of d(sum a)/d theta, or NULL
+ *   dpcoh_dbm   nrx x n_params of d P_coh[dBm] / d theta, or NULL
+ *   theta_bar   n_params values sum_r pcoh_bar[r] d P_coh[r] / d theta
+ *               (receivers in order), or NULL
+ * theta, pcoh_bar and every output are host or device per ptr_kind and
+ * caller-owned; tx, rx, paths, params as in dcem_path_gradients. With theta
+ * NULL both calls give the same derivatives up to rounding. Errors: those of
+ * dcem_path_gradients, DCEM_ERR_ARG for theta_bar without pcoh_bar,
+ * DCEM_ERR_NONFINITE for a non-finite host theta. */
+int dcem_path_adjoint(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                      const dcem_path* paths, int32_t n_paths, const dcem_params* params,
+                      const double* theta, const double* pcoh_bar, int32_t ptr_kind, double* field,
+                      double* pcoh_dbm, double* dfield, double* dpcoh_dbm, double* theta_bar);
+
 /* Per-receiver sum of given path records, with no device allocation. The
  * paper has no counterpart of this call. It is for callers that cannot
  * allocate device memory when they need the result: a host framework that

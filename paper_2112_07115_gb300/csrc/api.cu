@@ -252,6 +252,8 @@ struct dcem_scene {
   unsigned* g_err = nullptr;
   size_t g_items_cap = 0, g_out_cap = 0;
   dcem_path* g_paths = nullptr;
+  double* g_theta = nullptr;   // adjoint: theta staged from the host
+  size_t g_theta_cap = 0;
   float4* g_rx = nullptr;
   size_t g_paths_cap = 0, g_rx_cap = 0;
   int* dsched = nullptr;  // moving-object tree: nodes by height, and the height bounds
@@ -380,7 +382,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo); dfree(s->dsurv);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
-  dfree(s->g_rx);
+  dfree(s->g_rx); dfree(s->g_theta);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
   dfree(s->xf_cur); dfree(s->xf_traced); dfree(s->obj_box_cur); dfree(s->obj_box_traced);
   dfree(s->moved_boxes); dfree(s->scr.bounds); dfree(s->scr.k0); dfree(s->scr.v0); dfree(s->scr.k1);
@@ -1964,12 +1966,20 @@ int dcem_scene_gradient_size(const dcem_scene* s, int32_t* n_params) {
   return DCEM_OK;
 }
 
-int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
-                        const dcem_path* paths, int32_t n_paths, const dcem_params* p, int32_t ptr_kind,
-                        double* field, double* dfield, double* dpcoh_dbm) {
+}  // extern "C"
+
+// Field derivatives over a fixed path topology: forward mode (one thread per
+// (path, parameter)) at the scene's parameters, or the adjoint kernel (one
+// thread per path) at theta (null: the scene's parameters).
+static int path_derivs(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                       const dcem_path* paths, int32_t n_paths, const dcem_params* p, const double* theta,
+                       const double* pcoh_bar, int32_t ptr_kind, double* field, double* pcoh_dbm, double* dfield,
+                       double* dpcoh_dbm, double* theta_bar, bool adjoint) {
   if (!s || !tx || !p) return DCEM_ERR_ARG;
-  if (nrx < 0 || nrx > kSmallBuild || (nrx > 0 && (!rx || !dfield)) || n_paths < 0 || (n_paths > 0 && !paths))
+  if (nrx < 0 || nrx > kSmallBuild || (nrx > 0 && !rx) || n_paths < 0 || (n_paths > 0 && !paths))
     return DCEM_ERR_ARG;
+  if (!adjoint && nrx > 0 && !dfield) return DCEM_ERR_ARG;
+  if (theta_bar && !pcoh_bar) return DCEM_ERR_ARG;
   if (rx_ptr_kind != DCEM_PTR_HOST && rx_ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (ptr_kind != DCEM_PTR_HOST && ptr_kind != DCEM_PTR_DEVICE) return DCEM_ERR_ARG;
   if (p->max_refl < 0 || p->max_refl > DCEM_MAX_REFL) return DCEM_ERR_ARG;
@@ -1979,9 +1989,20 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
     return DCEM_ERR_ARG;
   if (!finite_arr(tx, 3)) return DCEM_ERR_NONFINITE;
   if (rx_ptr_kind == DCEM_PTR_HOST && nrx > 0 && !finite_arr(rx, 3 * (size_t)nrx)) return DCEM_ERR_NONFINITE;
-  if (nrx == 0) return DCEM_OK;
-  cudaStream_t st = s->st;
   const int np = grad_nparam(s->nmat, s->nobj);
+  if (theta && ptr_kind == DCEM_PTR_HOST) {
+    for (int i = 0; i < np; ++i)
+      if (!std::isfinite(theta[i])) return DCEM_ERR_NONFINITE;
+  }
+  cudaStream_t st = s->st;
+  if (nrx == 0) {  // no receiver: nothing depends on theta
+    if (theta_bar && np > 0) {
+      if (ptr_kind == DCEM_PTR_HOST) std::fill(theta_bar, theta_bar + np, 0.0);
+      else CK(cudaMemsetAsync(theta_bar, 0, sizeof(double) * np, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    return DCEM_OK;
+  }
   const int W = 1 + 4 * p->max_refl;
   // device copies of the inputs given on the host, scratch, staged outputs
   if ((size_t)nrx > s->g_rx_cap) {
@@ -2015,15 +2036,33 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
     CK(dalloc(&s->g_param, nitems));
     s->g_items_cap = nitems;
   }
-  size_t nout = ptr_kind == DCEM_PTR_HOST ? (size_t)nrx * (2 + 3 * (size_t)np) : 0;
+  // staging: field 2 nrx, P_coh nrx, dfield 2 nrx np, dpcoh nrx np, theta_bar np,
+  // pcoh_bar nrx, theta np
+  const size_t o_pc = 2 * (size_t)nrx, o_df = o_pc + nrx, o_dp = o_df + 2 * (size_t)nrx * np,
+               o_tb = o_dp + (size_t)nrx * np, o_pb = o_tb + np, o_th = o_pb + nrx, nout = o_th + np;
   if (nout > s->g_out_cap) {
     dfree(s->g_out);
     CK(dalloc(&s->g_out, nout));
     s->g_out_cap = nout;
   }
+  double* G = s->g_out;
   if (!s->g_err) CK(dalloc(&s->g_err, 1));
   CK(cudaMemsetAsync(s->g_err, 0, sizeof(unsigned), st));
+  const bool dev = ptr_kind == DCEM_PTR_DEVICE;
+  const double* theta_d = theta;
+  const double* pbar_d = pcoh_bar;
+  if (!dev && theta) {
+    CK(cudaMemcpyAsync(G + o_th, theta, sizeof(double) * np, cudaMemcpyHostToDevice, st));
+    theta_d = G + o_th;
+  }
+  if (!dev && pcoh_bar) {
+    CK(cudaMemcpyAsync(G + o_pb, pcoh_bar, sizeof(double) * nrx, cudaMemcpyHostToDevice, st));
+    pbar_d = G + o_pb;
+  }
   GradArgs g;
+  g.theta = theta_d;
+  g.xf = s->xf_cur;
+  g.pcoh_bar = pbar_d;
   g.paths = pd;
   g.n_paths = n_paths;
   g.W = W;
@@ -2047,27 +2086,42 @@ int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t
   g.items = s->g_items;
   g.param = s->g_param;
   g.err = s->g_err;
-  if (ptr_kind == DCEM_PTR_DEVICE) {
-    g.field = field;
-    g.dfield = dfield;
-    g.dpcoh = dpcoh_dbm;
-  } else {
-    g.field = s->g_out;
-    g.dfield = s->g_out + 2 * (size_t)nrx;
-    g.dpcoh = s->g_out + 2 * (size_t)nrx + 2 * (size_t)nrx * np;
-  }
-  CK(launch_gradients(g, st));
-  s->launches += (n_paths > 0 ? 1 : 0) + 1 + (rx_ptr_kind == DCEM_PTR_DEVICE ? 1 : 0);
+  g.field = dev && field ? field : G;
+  g.pcoh = dev && pcoh_dbm ? pcoh_dbm : G + o_pc;
+  g.dfield = dev && dfield ? dfield : G + o_df;
+  g.dpcoh = dev && dpcoh_dbm ? dpcoh_dbm : G + o_dp;
+  g.theta_bar = theta_bar ? (dev ? theta_bar : G + o_tb) : nullptr;
+  CK(adjoint ? launch_adjoint(g, st) : launch_gradients(g, st));
+  s->launches += (n_paths > 0 ? 1 : 0) + 1 + (rx_ptr_kind == DCEM_PTR_DEVICE ? 1 : 0) + (g.theta_bar ? 1 : 0);
   unsigned err = 0;
   CK(cudaMemcpyAsync(&err, s->g_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  if (ptr_kind == DCEM_PTR_HOST) {
+  if (!dev) {
     cudaMemcpyKind k = cudaMemcpyDeviceToHost;
     if (field) CK(cudaMemcpyAsync(field, g.field, sizeof(double) * 2 * nrx, k, st));
-    CK(cudaMemcpyAsync(dfield, g.dfield, sizeof(double) * 2 * (size_t)nrx * np, k, st));
+    if (pcoh_dbm) CK(cudaMemcpyAsync(pcoh_dbm, g.pcoh, sizeof(double) * nrx, k, st));
+    if (dfield) CK(cudaMemcpyAsync(dfield, g.dfield, sizeof(double) * 2 * (size_t)nrx * np, k, st));
     if (dpcoh_dbm) CK(cudaMemcpyAsync(dpcoh_dbm, g.dpcoh, sizeof(double) * (size_t)nrx * np, k, st));
+    if (theta_bar) CK(cudaMemcpyAsync(theta_bar, g.theta_bar, sizeof(double) * np, k, st));
   }
   CK(cudaStreamSynchronize(st));
   return err ? DCEM_ERR_ARG : DCEM_OK;
+}
+
+extern "C" {
+
+int dcem_path_gradients(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                        const dcem_path* paths, int32_t n_paths, const dcem_params* p, int32_t ptr_kind,
+                        double* field, double* dfield, double* dpcoh_dbm) {
+  return path_derivs(s, tx, rx, nrx, rx_ptr_kind, paths, n_paths, p, nullptr, nullptr, ptr_kind, field, nullptr,
+                     dfield, dpcoh_dbm, nullptr, false);
+}
+
+int dcem_path_adjoint(dcem_scene* s, const float* tx, const float* rx, int32_t nrx, int32_t rx_ptr_kind,
+                      const dcem_path* paths, int32_t n_paths, const dcem_params* p, const double* theta,
+                      const double* pcoh_bar, int32_t ptr_kind, double* field, double* pcoh_dbm, double* dfield,
+                      double* dpcoh_dbm, double* theta_bar) {
+  return path_derivs(s, tx, rx, nrx, rx_ptr_kind, paths, n_paths, p, theta, pcoh_bar, ptr_kind, field, pcoh_dbm,
+                     dfield, dpcoh_dbm, theta_bar, true);
 }
 
 int dcem_scene_info(const dcem_scene* s, int32_t* ntri, int32_t* nobj, int32_t* n_rays, int32_t* static_nodes,

@@ -28,11 +28,21 @@ struct GradArgs {
   double* field;            // nrx x 2
   double* dfield;           // nrx x nparam x 2
   double* dpcoh;            // nrx x nparam, d P_coh[dBm] / d theta
+  // adjoint kernel only: the parameters to evaluate at (null: the scene's),
+  // eps_r, sigma per material, then x, y translation per object, and the
+  // objects' current transforms (the translations theta is measured against)
+  const double* theta;
+  const float* xf;          // nobj x 12, row-major [R | t]
+  double* pcoh;             // nrx P_coh [dBm] at theta, or null
+  const double* pcoh_bar;   // nrx upstream d loss / d P_coh[dBm], or null
+  double* theta_bar;        // nparam: sum over receivers of pcoh_bar * d P_coh / d theta
 };
 
 inline int grad_nparam(int nmat, int nobj) { return 2 * nmat + 2 * nobj; }
 
 cudaError_t launch_gradients(const GradArgs& a, cudaStream_t st);
+// The same outputs from the reverse-mode (adjoint) kernel, one thread per path.
+cudaError_t launch_adjoint(const GradArgs& a, cudaStream_t st);
 // nrx receivers as 3 floats each (device) -> float4
 cudaError_t launch_pack_rx(const float* rx3, int n, float4* out, cudaStream_t st);
 

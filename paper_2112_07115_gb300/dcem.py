@@ -33,7 +33,7 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_set_stream", "dcem_scene_destroy", "dcem_status_string", "dcem_scene_info",
             "dcem_scene_get_world_tris", "dcem_scene_get_bvh", "dcem_scene_get_ray_log",
             "dcem_scene_get_candidates", "dcem_scene_set_rebuild_threshold",
-            "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients",
+            "dcem_reduce_paths_noalloc", "dcem_scene_gradient_size", "dcem_path_gradients", "dcem_path_adjoint",
             "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
             "dcem_scene_set_trace_config", "dcem_scene_autotune", "dcem_batch_create",
             "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy",
@@ -133,6 +133,7 @@ def lib():
         L.dcem_scene_set_graph_replay.argtypes = [vp, i32]
         L.dcem_reduce_paths_noalloc.argtypes = [vp, i32, i32, C.c_double, vp, vp, vp, vp]
         L.dcem_scene_gradient_size.argtypes = [vp, P(i32)]
+        L.dcem_path_adjoint.argtypes = [vp, vp, vp, i32, i32, vp, i32, P(Params), vp, vp, i32, vp, vp, vp, vp, vp]
         L.dcem_path_gradients.argtypes = [vp, vp, vp, i32, i32, vp, i32, P(Params), i32, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("dcem_params_default", "dcem_scene_destroy", "dcem_status_string",
@@ -315,6 +316,25 @@ def dcem_path_gradients(h, tx, rx, paths, params: Params, ptr_kind: int, field_p
                                      C.byref(params), ptr_kind, field_ptr, dfield_ptr, dpcoh_ptr)
 
 
+def dcem_path_adjoint(h, tx, rx, paths, params: Params, ptr_kind: int, theta_ptr=None, pcoh_bar_ptr=None,
+                      field_ptr=None, pcoh_ptr=None, dfield_ptr=None, dpcoh_ptr=None, theta_bar_ptr=None,
+                      n_paths: int | None = None) -> int:
+    """Raw call of the adjoint; returns the status. ``rx`` as in
+    dcem_path_gradients; ``paths``, theta, pcoh_bar and the outputs are host
+    or device pointers as ints per ``ptr_kind`` (None = NULL)."""
+    txa = np.ascontiguousarray(tx, np.float32).reshape(3)
+    rp, rkind, keep = _ptr(rx, np.float32)
+    nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+    if isinstance(paths, np.ndarray):
+        n_paths = paths.shape[0] if n_paths is None else n_paths
+        pp = paths.ctypes.data if n_paths else None
+    else:
+        pp = paths
+    return lib().dcem_path_adjoint(h, txa.ctypes.data, rp, nrx, rkind, pp, int(n_paths or 0), C.byref(params),
+                                   theta_ptr, pcoh_bar_ptr, ptr_kind, field_ptr, pcoh_ptr, dfield_ptr, dpcoh_ptr,
+                                   theta_bar_ptr)
+
+
 def dcem_scene_reset_cache(h):
     _check(lib().dcem_scene_reset_cache(h), "dcem_scene_reset_cache")
 
@@ -399,6 +419,7 @@ class Scene:
     def __init__(self, tris, tri_mat, materials, tri_obj=None, nobj=0, stream=None):
         self.ntri = int(np.asarray(tris).reshape(-1, 9).shape[0])
         self.nobj = int(nobj)
+        self.materials = np.asarray(materials, np.float32).reshape(-1, 3).copy()
         self.h = dcem_scene_create(tris, tri_mat, materials, tri_obj, nobj, stream)
         self.n_rays = 0
         self.max_refl = 3
@@ -488,6 +509,42 @@ class Scene:
         e = field[:nrx, 0] + 1j * field[:nrx, 1]
         de = dfield[:nrx, :npar, 0] + 1j * dfield[:nrx, :npar, 1]
         return e, de, dp[:nrx, :npar]
+
+    def adjoint(self, tx, rx, paths: np.ndarray, params: Params | None = None, theta=None, pcoh_bar=None):
+        """The adjoint kernel on host PATH_DTYPE records at theta (None: the
+        scene's parameters): field E (nrx,) complex, P_coh [dBm] (nrx,),
+        dE/dtheta (nrx, n_params) complex, d P_coh/dtheta (nrx, n_params) and,
+        with pcoh_bar (nrx,), the vector-Jacobian product (n_params,)."""
+        params = params or default_params()
+        nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+        npar = dcem_scene_gradient_size(self.h)
+        field = np.zeros((max(nrx, 1), 2), np.float64)
+        pc = np.zeros(max(nrx, 1), np.float64)
+        dfield = np.zeros((max(nrx, 1), max(npar, 1), 2), np.float64)
+        dp = np.zeros((max(nrx, 1), max(npar, 1)), np.float64)
+        tb = np.zeros(max(npar, 1), np.float64)
+        paths = np.ascontiguousarray(paths, PATH_DTYPE)
+        th = None if theta is None else np.ascontiguousarray(theta, np.float64)
+        pb = None if pcoh_bar is None else np.ascontiguousarray(pcoh_bar, np.float64)
+        rc = dcem_path_adjoint(self.h, tx, rx, paths, params, PTR_HOST,
+                               None if th is None else th.ctypes.data, None if pb is None else pb.ctypes.data,
+                               field.ctypes.data, pc.ctypes.data, dfield.ctypes.data, dp.ctypes.data,
+                               None if pb is None else tb.ctypes.data)
+        if rc != OK:
+            raise DcemError(rc, "dcem_path_adjoint")
+        e = field[:nrx, 0] + 1j * field[:nrx, 1]
+        de = dfield[:nrx, :npar, 0] + 1j * dfield[:nrx, :npar, 1]
+        return e, pc[:nrx], de, dp[:nrx, :npar], (tb[:npar] if pb is not None else None)
+
+    def theta(self, xf=None) -> np.ndarray:
+        """The scene's parameters in the order of the derivatives: eps_r,
+        sigma of every material, then the x, y translation of every object
+        (from ``xf``, nobj x 12, the transforms last given)."""
+        m = self.materials[:, :2].astype(np.float64).ravel()
+        if self.nobj == 0:
+            return m
+        x = np.asarray(xf, np.float32).reshape(self.nobj, 12)
+        return np.concatenate([m, np.stack([x[:, 3], x[:, 7]], 1).astype(np.float64).ravel()])
 
     def reset_cache(self):
         dcem_scene_reset_cache(self.h)
@@ -634,43 +691,58 @@ def path_power(scene: Scene, theta, tx, rx, paths: np.ndarray, params: Params | 
     """Received power P_coh [dBm] per receiver over a fixed path topology, as
     a differentiable function of theta for torch autograd.
 
-    theta (a torch tensor of dcem_scene_gradient_size values) stands for the
-    scene's current parameters in the order of dcem_path_gradients: eps_r and
-    sigma of every material, then the x and y translation of every rigid
-    object. The function is evaluated at the scene's state (theta's values are
-    not read; pass the current ones), holding the topology `paths` fixed, as
-    Sec. III steps 3, 4 and 6 define the field of a path (Eq. 1, Eq. 3). The
-    power comes from dcem_reduce_paths_noalloc and the Jacobian d P_coh[dBm] /
-    d theta from dcem_path_gradients (FP64 forward-mode derivatives in the
-    library's kernels); the backward pass contracts the incoming gradient with
-    that Jacobian. Receivers without paths have P = -inf and zero gradient.
-    The result lives on theta's device (a CUDA device: the power kernel runs
-    there on the current stream)."""
+    theta (a CUDA torch tensor of dcem_scene_gradient_size values, FP64) holds
+    the parameters in the order of the derivatives: eps_r and sigma of every
+    material, then the x and y translation of every rigid object (absolute;
+    Scene.theta(xf) gives the scene's current values). The forward pass is the
+    field of the paths' triangle sequences (Sec. III steps 3, 4 and 6, Eq. 1,
+    Eq. 3) evaluated at theta by the library's adjoint kernel: materials
+    replaced by theta's values and each object's triangles shifted by theta's
+    translation minus its current one; the topology `paths` stays fixed and
+    the scene is not modified. The backward pass runs the adjoint kernel again
+    with the incoming gradient and returns the vector-Jacobian product it
+    computes. Receivers without paths have P = -inf and no gradient. The work
+    runs on theta's device, on that device's current stream."""
     import torch
+
+    prm = params or default_params()
+    nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
+    recs = np.ascontiguousarray(paths, PATH_DTYPE)
 
     class _PathPower(torch.autograd.Function):
         @staticmethod
         def forward(ctx, th):
-            prm = params or default_params()
             npar = dcem_scene_gradient_size(scene.h)
             if th.numel() != npar:
                 raise DcemError(ERR_ARG, f"path_power: theta has {th.numel()} values, the scene {npar}")
-            nrx = (rx.numel() if hasattr(rx, "numel") else np.asarray(rx).size) // 3
-            _, _, dp = scene.gradients(tx, rx, paths, prm)
-            recs = np.ascontiguousarray(paths, PATH_DTYPE)
             dev = th.device
-            pd = torch.from_numpy(recs.view(np.uint8).copy()).to(dev)
-            pc = torch.empty(max(nrx, 1), dtype=torch.float64, device=dev)
-            rc = dcem_reduce_paths_noalloc(pd.data_ptr(), recs.shape[0], nrx, prm.tx_power_w, None,
-                                           pc.data_ptr(), None, torch.cuda.current_stream(dev).cuda_stream)
-            if rc != OK:
-                raise DcemError(rc, "dcem_reduce_paths_noalloc")
-            ctx.save_for_backward(torch.from_numpy(dp).to(dev))
+            with torch.cuda.device(dev):
+                thd = th.detach().to(torch.float64).contiguous()
+                pd = torch.from_numpy(recs.view(np.uint8).copy()).to(dev)
+                pc = torch.empty(max(nrx, 1), dtype=torch.float64, device=dev)
+                # theta comes from torch's stream; the library's call ends with
+                # a synchronisation of the scene's stream
+                torch.cuda.current_stream(dev).synchronize()
+                rc = dcem_path_adjoint(scene.h, tx, rx, pd.data_ptr(), prm, PTR_DEVICE, thd.data_ptr(), None,
+                                       None, pc.data_ptr(), n_paths=recs.shape[0])
+                if rc != OK:
+                    raise DcemError(rc, "dcem_path_adjoint")
+            ctx.save_for_backward(thd, pd)
             return pc[:nrx]
 
         @staticmethod
         def backward(ctx, g):
-            (jac,) = ctx.saved_tensors
-            return (g.to(jac.dtype) @ jac).to(theta.dtype).reshape(theta.shape)
+            thd, pd = ctx.saved_tensors
+            dev = thd.device
+            with torch.cuda.device(dev):
+                gb = torch.zeros(max(nrx, 1), dtype=torch.float64, device=dev)
+                gb[:nrx] = g.to(torch.float64)
+                tb = torch.empty(thd.numel(), dtype=torch.float64, device=dev)
+                torch.cuda.current_stream(dev).synchronize()
+                rc = dcem_path_adjoint(scene.h, tx, rx, pd.data_ptr(), prm, PTR_DEVICE, thd.data_ptr(),
+                                       gb.data_ptr(), theta_bar_ptr=tb.data_ptr(), n_paths=recs.shape[0])
+                if rc != OK:
+                    raise DcemError(rc, "dcem_path_adjoint")
+            return tb.to(theta.dtype).reshape(theta.shape)
 
     return _PathPower.apply(theta)

@@ -349,6 +349,23 @@ def urban_materials() -> np.ndarray:
                     dtype=np.float32)
 
 
+def urban_grad_materials() -> np.ndarray:
+    """Eight (eps_r, sigma) classes for the differentiable urban workload:
+    seven building materials and the ground, then metal for the vehicles.
+    Concrete is the configs' value; the others are this build's choice of
+    ITU-R P.2040-style constants."""
+    return np.array([[5.31, 0.0326, 0.0],    # concrete
+                     [3.75, 0.038, 0.0],     # brick
+                     [6.27, 0.0043, 0.0],    # glass
+                     [2.73, 0.0085, 0.0],    # plasterboard
+                     [1.99, 0.0047, 0.0],    # wood
+                     [7.51, 0.030, 0.0],     # limestone
+                     [7.07, 0.0055, 0.0],    # marble
+                     [15.0, 0.035, 0.0],     # ground
+                     [1.0, 0.0, 1.0]],       # metal (vehicles)
+                    dtype=np.float32)
+
+
 def _extruded_polygon(cx, cy, rmax, n, h, rng):
     """Walls (2 triangles per edge) and a roof fan of a star-shaped polygon of
     n vertices around (cx, cy), radii in [0.55, 1] rmax, extruded to height h."""
@@ -366,7 +383,7 @@ def _extruded_polygon(cx, cy, rmax, n, h, rng):
 def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: float = 20.0,
                parcels: int = 4, n_vehicles: int = 1000, n_tx: int = 64,
                budgets: tuple = (65_536, 2_097_152), n_static_rx: int = 96, n_frames: int = 200,
-               max_refl: int = 5, freq_hz: float = 28e9) -> Scene:
+               max_refl: int = 5, freq_hz: float = 28e9, building_classes: int = 3) -> Scene:
     """Manhattan grid: ``blocks`` x ``blocks`` blocks at ``pitch`` m with
     ``street`` m streets (street centre lines at x = i * pitch and
     y = j * pitch, i, j = 0..blocks). Each block holds ``parcels`` x
@@ -380,8 +397,15 @@ def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: fl
     2 m. Transmitters: ``n_tx`` roadside units at random street corners,
     6-10 m high, with ray budgets log-uniform in ``budgets`` (returned in
     ``meta["tx"]`` and ``meta["budgets"]``; ``tx`` is the first one).
-    Frames at 10 Hz.
+    Frames at 10 Hz. building_classes 7 takes the eight-class table of
+    urban_grad_materials (seven building classes, then ground and metal).
     """
+    if building_classes == 3:
+        mats, m_ground, m_metal = urban_materials(), URBAN_GROUND, URBAN_METAL
+    elif building_classes == 7:
+        mats, m_ground, m_metal = urban_grad_materials(), 7, 8
+    else:
+        raise ValueError("building_classes is 3 or 7")
     ss = np.random.SeedSequence([seed, 3])
     r_bld, r_veh, r_tx = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
     size = blocks * pitch
@@ -392,7 +416,7 @@ def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: fl
         for j in range(nt):
             x0, y0 = -street / 2 + i * tile, -street / 2 + j * tile
             static += _quad((x0, y0, 0.0), (x0 + tile, y0, 0.0), (x0 + tile, y0 + tile, 0.0), (x0, y0 + tile, 0.0))
-            smat += [URBAN_GROUND] * 2
+            smat += [m_ground] * 2
     lot = pitch - street
     cell = lot / parcels
     for bi in range(blocks):
@@ -403,7 +427,7 @@ def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: fl
                     cy = bj * pitch + street / 2 + (pj + 0.5) * cell
                     n = int(r_bld.integers(6, 15))
                     h = float(r_bld.uniform(10.0, 60.0))
-                    m = int(r_bld.integers(0, 3))
+                    m = int(r_bld.integers(0, building_classes))
                     b = _extruded_polygon(cx, cy, 0.45 * cell, n, h, r_bld)
                     static += b
                     smat += [m] * len(b)
@@ -432,7 +456,7 @@ def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: fl
         s0[idx] = phase + gap * np.arange(len(idx)) + r_veh.uniform(-0.2, 0.2, size=len(idx)) * (gap - 20.0)
         speed[idx] = r_veh.uniform(5.0, 15.0)
     meshes = [box_tris(*dims[k]) for k in range(n_vehicles)]
-    tris, tobj, tmat = _assemble(static, smat, meshes, [URBAN_METAL] * n_vehicles)
+    tris, tobj, tmat = _assemble(static, smat, meshes, [m_metal] * n_vehicles)
     dt = 0.1
     xf = np.zeros((n_frames, n_vehicles, 12), np.float64)
     nrx = 4 * n_vehicles + n_static_rx
@@ -464,10 +488,26 @@ def urban_grid(seed: int = 0, blocks: int = 10, pitch: float = 100.0, street: fl
     txs = corner_points(n_tx, r_tx, 6.0, 10.0).astype(np.float32)
     lo, hi = np.log(budgets[0]), np.log(budgets[1])
     bud = np.exp(r_tx.uniform(lo, hi, size=n_tx)).astype(np.int64)
-    return Scene("urban_grid", tris, tobj, tmat, urban_materials(), n_vehicles,
+    return Scene("urban_grid", tris, tobj, tmat, mats, n_vehicles,
                  xf.astype(np.float32), txs[0].copy(), rx.astype(np.float32), freq_hz=freq_hz,
                  n_rays=int(bud[0]), max_refl=max_refl,
                  meta={"seed": seed, "dt": dt, "tx": txs, "budgets": bud.tolist(), "classes": cls.tolist()})
+
+
+def urban_gradient(seed: int = 0, blocks: int = 10, parcels: int = 4, n_vehicles: int = 1000, n_rx: int = 256,
+                   n_rays: int = 1_000_000, max_refl: int = 4, n_frames: int = 3, freq_hz: float = 28e9) -> Scene:
+    """The differentiable-tracing workload: the urban grid with eight
+    (eps_r, sigma) classes (urban_grad_materials), its moving metal vehicles,
+    one roadside transmitter with ``n_rays`` rays, and ``n_rx`` static
+    roadside receivers at 2 m (the grid's static receivers; the roof
+    receivers are dropped)."""
+    sc = urban_grid(seed=seed, blocks=blocks, parcels=parcels, n_vehicles=n_vehicles, n_tx=1,
+                    budgets=(n_rays, n_rays), n_static_rx=n_rx, n_frames=n_frames, max_refl=max_refl,
+                    freq_hz=freq_hz, building_classes=7)
+    sc.rx = np.ascontiguousarray(sc.rx[:, 4 * n_vehicles:])
+    sc.n_rays = n_rays
+    sc.name = "urban_gradient"
+    return sc
 
 
 def scene_batch(seed: int = 0, n: int = 32, tris: tuple = (1_000, 200_000), vehicles: tuple = (10, 2000),
