@@ -58,7 +58,9 @@ typedef enum {
   DCEM_ERR_STACK = -5,     /* BVH traversal stack overflow (counted, not trapped) */
   DCEM_ERR_HASH = -6,      /* 64-bit path-key collision between distinct keys    */
   DCEM_ERR_STATE = -7,     /* call out of order (e.g. trace before set_rays)     */
-  DCEM_ERR_NOMEM = -8      /* device allocation failed                           */
+  DCEM_ERR_NOMEM = -8,     /* device allocation failed                           */
+  DCEM_ERR_CHECK = -9      /* bounds-checked build only: an index was out of range
+                              (replaced, not used; see the library's build) */
 } dcem_status;
 
 /* FULL: every ray traced every frame. COHERENT: segments reused across

@@ -411,6 +411,18 @@ void scene_free(dcem_scene* s) {
   delete s;
 }
 
+// Bounds-checked build: failures of every translation unit since the last
+// call (0 in the normal build).
+unsigned checks_take_all() {
+  unsigned n = 0, line = 0;
+  n += checks_take_api(&line);
+  n += checks_take_bvh(&line);
+  n += checks_take_trace(&line);
+  n += checks_take_paths(&line);
+  n += checks_take_grad(&line);
+  return n;
+}
+
 bool finite_arr(const float* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(p[i])) return false;
@@ -722,6 +734,7 @@ const char* dcem_status_string(int st) {
     case DCEM_ERR_HASH: return "path-key hash collision";
     case DCEM_ERR_STATE: return "call out of order";
     case DCEM_ERR_NOMEM: return "device allocation failed";
+    case DCEM_ERR_CHECK: return "bounds check failed (bounds-checked build)";
     default: return "unknown status";
   }
 }
@@ -1186,6 +1199,8 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   a.bvh.root0 = s->root_h[0];
   a.bvh.root1 = s->root_h[1];
   a.bvh.max_visits = 2 * (s->nint_s + s->nint_d + s->ntri) + 8;
+  a.bvh.nnodes = s->nint_s + s->nint_d;
+  a.bvh.ntris = s->ntri;
   a.rays = s->rays;
   a.txs = s->txs;
   a.nsets = s->nsets;
@@ -1220,6 +1235,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   a.rxt.root = s->rxt_root;
   a.rxt.root_box = s->rxt_root_box;
   a.rxt.max_visits = 2 * nrx + 8;
+  a.rxt.cap = s->nrx_cap;
   a.qnodes = s->qnodes;
   a.qframe = s->qframe;
   a.n_nodes = s->nint_s + s->nint_d;
@@ -1290,6 +1306,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
     c.mvt.root = s->mvt_root;
     c.mvt.root_box = s->mvt_root_box;
     c.mvt.max_visits = 2 * s->mv_cap + 8;
+    c.mvt.cap = s->mv_cap;
     c.mv_cap = s->mv_cap;
   }
 
@@ -1339,6 +1356,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.mvt.root = s->mvt_root;
   q.mvt.root_box = s->mvt_root_box;
   q.mvt.max_visits = 2 * s->mv_cap + 8;
+  q.mvt.cap = s->mv_cap;
   q.mv_cap = (unsigned)s->mv_cap;
   q.N = N;
   q.bucket = s->bucket;
@@ -1757,6 +1775,10 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
     for (int i = 0; i < 10; ++i) S.ms_stage[i] = 0.0f;
     cudaEventElapsedTime(&S.ms_stage[2], s->ev[2], s->ev[3]);
   }
+  if (checks_take_all()) {  // bounds-checked build: an index was out of range
+    s->cache_valid = false;
+    return DCEM_ERR_CHECK;
+  }
   out->n_paths = nvalid;
   s->cache_valid = true;
   s->vc_valid = p->mode == DCEM_MODE_COHERENT && s->max_trans == 0;  // this frame built its key table
@@ -2104,6 +2126,7 @@ static int path_derivs(dcem_scene* s, const float* tx, const float* rx, int32_t 
     if (theta_bar) CK(cudaMemcpyAsync(theta_bar, g.theta_bar, sizeof(double) * np, k, st));
   }
   CK(cudaStreamSynchronize(st));
+  if (checks_take_all()) return DCEM_ERR_CHECK;
   return err ? DCEM_ERR_ARG : DCEM_OK;
 }
 
@@ -2240,3 +2263,7 @@ int dcem_scene_get_candidates(dcem_scene* s, int32_t* out, int64_t cap, int64_t*
 }
 
 }  // extern "C"
+
+namespace dcem {
+DCEM_CHECKS_TAKER(checks_take_api)
+}  // namespace dcem

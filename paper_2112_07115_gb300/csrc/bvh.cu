@@ -1217,4 +1217,6 @@ void launch_transform_refit(const float4* d_objv, const float* d_xf, int n, int 
                                                     d_leaf_parent, d_arrive, d_root_box, d_obj_box, d_ctr);
 }
 
+DCEM_CHECKS_TAKER(checks_take_bvh)
+
 }  // namespace dcem

@@ -41,6 +41,47 @@ struct WedgeTopo {
 };
 constexpr int kSmemRefit = 2047;        // per-frame trees up to this many nodes refit in shared memory
 
+// Bounds-checked build (compiled with DCEM_CHECKS): an index marked with
+// DCEM_IDX(i, n) is checked against [0, n) before use. One out of range adds
+// to this translation unit's check word, keeps the first failing source line,
+// and is replaced by 0 (an index every checked array holds), so the access
+// stays in bounds and nothing traps. The host reads and clears the words of
+// every translation unit after each frame (checks_take_*) and reports
+// DCEM_ERR_CHECK. Without DCEM_CHECKS the macro is the index itself.
+#ifdef DCEM_CHECKS
+static __device__ unsigned g_check_word[2];  // failures, first failing line
+template <class T>
+__device__ __forceinline__ T check_index(T i, long long n, int line) {
+  if ((long long)i >= 0 && (long long)i < n) return i;
+  atomicAdd(&g_check_word[0], 1u);
+  atomicCAS(&g_check_word[1], 0u, (unsigned)line);
+  return T(0);
+}
+#define DCEM_IDX(i, n) ::dcem::check_index((i), (long long)(n), __LINE__)
+#define DCEM_CHECKS_TAKER(name)                                                   \
+  unsigned name(unsigned* line) {                                                 \
+    unsigned w[2] = {0u, 0u}, z[2] = {0u, 0u};                                    \
+    if (cudaMemcpyFromSymbol(w, g_check_word, sizeof(w)) != cudaSuccess) return ~0u; \
+    if (w[0] && cudaMemcpyToSymbol(g_check_word, z, sizeof(z)) != cudaSuccess) return ~0u; \
+    if (line) *line = w[1];                                                       \
+    return w[0];                                                                  \
+  }
+#else
+#define DCEM_IDX(i, n) (i)
+#define DCEM_CHECKS_TAKER(name)          \
+  unsigned name(unsigned* line) {        \
+    if (line) *line = 0u;                \
+    return 0u;                           \
+  }
+#endif
+// Failures counted by the bounds-checked build in each translation unit since
+// the last call (0 in the normal build); *line: the first failing line.
+unsigned checks_take_api(unsigned* line);
+unsigned checks_take_bvh(unsigned* line);
+unsigned checks_take_trace(unsigned* line);
+unsigned checks_take_paths(unsigned* line);
+unsigned checks_take_grad(unsigned* line);
+
 // device error bits (DevCounters::err)
 enum : unsigned {
   ERR_CAND_OVERFLOW = 1u,
@@ -161,7 +202,7 @@ struct TStack {
     return true;
   }
   __device__ __forceinline__ int pop() {
-    --sp;
+    sp = DCEM_IDX(sp - 1, cap + kSpill);
     return sp < cap ? s[sp * stride] : spill[sp - cap];
   }
 };
@@ -276,6 +317,7 @@ struct Bvh {
   const float4* __restrict__ tris;
   int root0, root1;
   int max_visits;  // nodes + leaves of both trees: a valid traversal never exceeds it
+  int nnodes, ntris;  // internal nodes of both trees, triangle (leaf) slots
 };
 
 // Closest hit over both trees, t > tmin, excluding triangle id `excl`; ties in
@@ -302,7 +344,7 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
     }
     if (cur >= 0) {
       ++n_nodes;
-      const float4* n = bvh.nodes + 4 * (size_t)cur;
+      const float4* n = bvh.nodes + 4 * (size_t)DCEM_IDX(cur, bvh.nnodes);
       float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
       float tn0, tn1;
       bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, t_best, tn0);
@@ -324,7 +366,7 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
       ++n_tris;
       float3 v0, v1, v2;
       int id;
-      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      load_tri(bvh.tris, DCEM_IDX(slot, bvh.ntris), v0, v1, v2, id);
       float t;
       if (id != excl && tri_hit(r, v0, v1, v2, t) && t > tmin) {
         if (t < t_best || (t == t_best && id < id_best)) {
@@ -359,6 +401,7 @@ __device__ __forceinline__ int closest_hit(const Bvh& bvh, const RayPre& r, floa
 // ---------------------------------------------------------------------------
 struct QFrame {
   float ox, oy, oz, sx, sy, sz;
+  int n4;  // 4-wide nodes in the copy (index checks)
 };
 
 struct QRay {
@@ -445,7 +488,8 @@ __device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, c
     }
     if (cur >= 0) {
       ++n_nodes;
-      uint4 a = qn[2 * cur], b = qn[2 * cur + 1];
+      const int ci = DCEM_IDX(cur, bvh.nnodes);
+      uint4 a = qn[2 * ci], b = qn[2 * ci + 1];
       float tn0, tn1;
       bool h0 = qslab(q, a.x, a.y, a.z, t_best, tn0);
       bool h1 = qslab(q, a.w, b.x, b.y, t_best, tn1);
@@ -466,7 +510,7 @@ __device__ __forceinline__ int closest_hit_q(const uint4* qn, const QFrame& f, c
       ++n_tris;
       float3 v0, v1, v2;
       int id;
-      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      load_tri(bvh.tris, DCEM_IDX(slot, bvh.ntris), v0, v1, v2, id);
       float t;
       if (id != excl && tri_hit(r, v0, v1, v2, t) && t > tmin) {
         if (t < t_best || (t == t_best && id < id_best)) {
@@ -524,7 +568,7 @@ __device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, 
     }
     if (cur >= 0) {
       n_nodes += 2;
-      const uint4* nd = qn + 4 * (size_t)cur;
+      const uint4* nd = qn + 4 * (size_t)DCEM_IDX(cur, f.n4);
       uint4 A, B, C, K;
       if (kG) {
         A = __ldg(nd);
@@ -557,7 +601,7 @@ __device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, 
       ++n_tris;
       float3 v0, v1, v2;
       int id;
-      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      load_tri(bvh.tris, DCEM_IDX(slot, bvh.ntris), v0, v1, v2, id);
       float t;
       if (id != excl && tri_hit(r, v0, v1, v2, t) && t > tmin) {
         if (t < t_best || (t == t_best && id < id_best)) {
@@ -589,7 +633,7 @@ __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t
       continue;
     }
     if (cur >= 0) {
-      const float4* n = bvh.nodes + 4 * (size_t)cur;
+      const float4* n = bvh.nodes + 4 * (size_t)DCEM_IDX(cur, bvh.nnodes);
       float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
       float tn0, tn1;
       bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, t1, tn0);
@@ -608,7 +652,7 @@ __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t
     } else {
       float3 v0, v1, v2;
       int id;
-      load_tri(bvh.tris, ~cur, v0, v1, v2, id);
+      load_tri(bvh.tris, DCEM_IDX(~cur, bvh.ntris), v0, v1, v2, id);
       float t;
       if (id != ex0 && id != ex1 && tri_hit(r, v0, v1, v2, t) && t > t0 && t < t1) return true;
       cur = kEmpty;
@@ -640,6 +684,7 @@ struct SmallBvh {
   const int* root;                   // device: root code (kEmpty, leaf ~j, or node)
   const float* root_box;             // device: box of a single-leaf tree
   int max_visits;
+  int cap;                           // leaves the tree's arrays hold (nodes: cap - 1)
 };
 
 // Slab test returning the clipped parameter interval [tn, tf] within [0, tcap].
@@ -695,11 +740,11 @@ __device__ __forceinline__ bool capture_tree(const SmallBvh& t, const float4* __
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
     if (cur < 0) {
-      int ri = t.perm[~cur];
-      float4 v = rx[ri];
+      int ri = t.perm[DCEM_IDX(~cur, t.cap)];
+      float4 v = rx[DCEM_IDX(ri, t.cap)];
       if (captured(r.o, d, D, tend, alpha, f3(v.x, v.y, v.z))) emit(ri);
     } else {
-      const float4* n = t.nodes + 4 * (size_t)cur;
+      const float4* n = t.nodes + 4 * (size_t)DCEM_IDX(cur, t.cap - 1);
       float4 n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
       int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
       bool m0 = cone_box(r, D, te, alpha, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y);
@@ -728,7 +773,7 @@ __device__ __forceinline__ bool seg_hits_tree(const SmallBvh& t, const RayPre& r
   st.reset();
   int cur = root;
   for (int visits = 0; visits <= t.max_visits; ++visits) {
-    const float4* n = t.nodes + 4 * (size_t)cur;
+    const float4* n = t.nodes + 4 * (size_t)DCEM_IDX(cur, t.cap - 1);
     float4 n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
     float tn;
@@ -756,6 +801,7 @@ __device__ __forceinline__ char* stage_tree(const SmallBvh& g, int nn, int nperm
   if (threadIdx.x == 0) sr[0] = *g.root;
   if (threadIdx.x < 6) reinterpret_cast<float*>(sr + 1)[threadIdx.x] = g.root_box[threadIdx.x];
   t = g;
+  t.cap = nn + 1;
   t.nodes = sn;
   t.perm = sp;
   t.root = sr;

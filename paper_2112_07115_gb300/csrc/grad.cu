@@ -680,4 +680,6 @@ cudaError_t launch_gradients(const GradArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+DCEM_CHECKS_TAKER(checks_take_grad)
+
 }  // namespace dcem

@@ -39,9 +39,14 @@ __device__ __forceinline__ unsigned long long seq_key(int rx, int k, F id_at) {
   return h ? h : 1ull;
 }
 
+// Hit id of segment j of slot `ray` in the log ((N + T + 1) x R).
+__device__ __forceinline__ int log_id_at(const PathArgs& a, int j, int ray) {
+  return a.log_id[(size_t)DCEM_IDX(j, a.N + a.max_trans + 1) * a.R + DCEM_IDX(ray, a.R)];
+}
+
 // ... of `ray`'s first k logged segments.
 __device__ __forceinline__ unsigned long long path_key_of(const PathArgs& a, int ray, int rx, int k) {
-  return seq_key(rx, k, [&](int j) { return a.log_id[(size_t)j * a.R + ray]; });
+  return seq_key(rx, k, [&](int j) { return log_id_at(a, j, ray); });
 }
 
 // Hash-table key of a capture: its link (transmitter * nrx + receiver),
@@ -53,7 +58,7 @@ __device__ __forceinline__ unsigned long long path_key(const PathArgs& a, Cand c
 __device__ __forceinline__ bool same_key(const PathArgs& a, Cand x, Cand y) {
   if (cand_rx(x) != cand_rx(y) || cand_seg(x) != cand_seg(y)) return false;
   for (int j = 0; j < cand_seg(x); ++j)
-    if (a.log_id[(size_t)j * a.R + x.ray] != a.log_id[(size_t)j * a.R + y.ray]) return false;
+    if (log_id_at(a, j, x.ray) != log_id_at(a, j, y.ray)) return false;
   return true;
 }
 
@@ -78,7 +83,7 @@ __global__ void k_dedupe_insert(PathArgs a) {
     a.cand_slot[i] = (int)slot;
     // representative: the capture of the lowest primary ray (a transmission
     // child counts as its primary; one primary reaches a key at most once)
-    int root = c.ray < a.R0 ? c.ray : a.inst_root[c.ray - a.R0];
+    int root = c.ray < a.R0 ? c.ray : a.inst_root[DCEM_IDX(c.ray - a.R0, a.R - a.R0)];
     atomicMin(&a.hrep[slot], ((unsigned long long)(unsigned)root << 32) | i);
   }
 }
@@ -93,7 +98,7 @@ __global__ void k_dedupe_unique(PathArgs a) {
       unsigned u = atomicAdd(&a.ctr->n_unique, 1u);
       if (u < a.ucap) a.uniq[u] = (int)i;
       else atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
-    } else if (!same_key(a, a.cand[i], a.cand[rep])) {
+    } else if (!same_key(a, a.cand[i], a.cand[DCEM_IDX(rep, a.cand_cap)])) {
       atomicOr(&a.ctr->err, ERR_HASH_COLLISION);
     }
   }
@@ -115,9 +120,9 @@ __global__ void k_sticky_probe(PathArgs a) {
       if (kk == 0ull) break;
       if (kk == h) {
         // the same key must be the same path: compare with the representative
-        Cand c = a.cand[(unsigned)(a.hrep[slot] & 0xffffffffull)];
+        Cand c = a.cand[DCEM_IDX((unsigned)(a.hrep[slot] & 0xffffffffull), a.cand_cap)];
         bool same = cand_rx(c) == sk.link && cand_seg(c) == sk.depth;
-        for (int j = 0; same && j < sk.depth; ++j) same = a.log_id[(size_t)j * a.R + c.ray] == sk.tri[j];
+        for (int j = 0; same && j < sk.depth; ++j) same = log_id_at(a, j, c.ray) == sk.tri[j];
         if (!same) atomicOr(&a.ctr->err, ERR_HASH_COLLISION);
         found = true;
         break;
@@ -339,8 +344,8 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
     unsigned fl0 = 0u;
     unsigned long long lkey = 0ull;  // the link key (0: a sticky record)
     if (ci >= 0) {
-      Cand c = a.cand[ci];
-      int slot = a.cand_slot[ci];
+      Cand c = a.cand[DCEM_IDX(ci, a.cand_cap)];
+      int slot = DCEM_IDX(a.cand_slot[DCEM_IDX(ci, a.cand_cap)], a.hcap);
       rec.key = a.hkey[slot];
       lkey = rec.key;
       // this slot is no longer needed: leave the table empty for the next frame
@@ -353,8 +358,8 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
       // transmitter out: (receiver, depth, sequence), as a single-transmitter
       // frame has it
       if (rxi >= a.nrx) rec.key = path_key_of(a, ray, rxi % a.nrx, k);
-      for (int j = 0; j < kMaxRefl; ++j) ids[j] = j < k ? a.log_id[(size_t)j * a.R + ray] : -1;
-      if (ray >= a.R0) ray = a.inst_root[ray - a.R0];  // reported as its primary ray
+      for (int j = 0; j < kMaxRefl; ++j) ids[j] = j < k ? log_id_at(a, j, ray) : -1;
+      if (ray >= a.R0) ray = a.inst_root[DCEM_IDX(ray - a.R0, a.R - a.R0)];  // reported as its primary ray
     } else {  // sticky mode: a kept path that no capture of this frame has
       const StickyKey& sk = a.sticky_prev[~ci];
       k = sk.depth;
@@ -413,7 +418,8 @@ __global__ void __launch_bounds__(64) k_val_geom(PathArgs a) {
     bool isT[kMaxRefl];
     for (int j = 0; j < k && ok; ++j) {
       isT[j] = (ids[j] & kTransBit) != 0;
-      const float4* tp = a.tris + 3 * (size_t)a.slot_of_id[ids[j] & ~kTransBit];
+      const float4* tp = a.tris + 3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(ids[j] & ~kTransBit, a.bvh.ntris)],
+                                                        a.bvh.ntris);
       float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
       if (isT[j] && !(a.mats[__float_as_int(p1.w)].w >= 0.0f)) ok = false;
       V0[j] = vof<T>(p0.x, p0.y, p0.z);
@@ -567,7 +573,8 @@ __global__ void __launch_bounds__(kFieldThreads) k_val_field(PathArgs a) {
     for (int j = 1 + gl; j <= k; j += kFieldLanes) {
       BounceCoef& c = C[j - 1];
       const int id = rec.tri[j - 1];
-      const float4* tp = a.tris + 3 * (size_t)a.slot_of_id[id & ~kTransBit];
+      const float4* tp = a.tris + 3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(id & ~kTransBit, a.bvh.ntris)],
+                                                        a.bvh.ntris);
       float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
       const float4 mt = a.mats[__float_as_int(p1.w)];
       if (id & kTransBit) {  // penetration loss L dB: field times 10^(-L/20)
@@ -959,8 +966,10 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
   d3w bp = crossw(ip, php), bd = crossw(dd, ph);
   // Luebbers: the faces' Fresnel factors at the grazing angles phi' and n pi - phi
-  const float4 ma = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.ta] + 1].w)];
-  const float4 mb = a.mats[__float_as_int(a.tris[3 * (size_t)a.slot_of_id[W.tb] + 1].w)];
+  const float4 ma =
+      a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.ta, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+  const float4 mb =
+      a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.tb, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
   zd r0s, r0h, rns, rnh;
   fresnel_d(ma, a.freq, fabs(sin(phip)), r0s, r0h);
   fresnel_d(mb, a.freq, fabs(sin(n * M_PI - phi)), rns, rnh);
@@ -1105,7 +1114,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(PathArgs a) {
   while (np2 < cnt) np2 <<= 1;
   for (int i = tid; i < np2; i += kReduceThreads) {
     if (i < cnt) {
-      int u = a.bucket[(size_t)r * a.bucket_cap + i];
+      int u = DCEM_IDX(a.bucket[(size_t)r * a.bucket_cap + i], a.ucap);
       skey[i] = a.prec[u].key;
       sidx[i] = u;
     } else {
@@ -1253,5 +1262,7 @@ cudaError_t launch_reduce(const PathArgs& a, int nlinks, cudaStream_t st) {
   k_reduce<<<nlinks, kReduceThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
+
+DCEM_CHECKS_TAKER(checks_take_paths)
 
 }  // namespace dcem

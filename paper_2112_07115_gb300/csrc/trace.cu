@@ -29,6 +29,15 @@ __device__ __forceinline__ void emit_cand(const TraceArgs& a, int ray, int seg, 
   else atomicOr(&a.ctr->err, ERR_CAND_OVERFLOW);
 }
 
+// Index of segment b of slot `ray` in the log arrays ((N + T + 1) x LS).
+__device__ __forceinline__ size_t log_at(const TraceArgs& a, int b, int ray) {
+  return (size_t)DCEM_IDX(b, a.N + a.max_trans + 1) * a.LS + DCEM_IDX(ray, a.LS);
+}
+// Capacity of the capture work list.
+__device__ __forceinline__ long long capitems_cap(const TraceArgs& a) {
+  return (long long)(a.N + a.max_trans + 1) * a.LS;
+}
+
 // Warp-wide dynamic work fetch: lane 0 takes the next `n` items.
 __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
   int base = 0;
@@ -94,31 +103,31 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
         if (q < nq) {
           if (kT && a.pass > 0) {
             ray = slot0 + q;
-            b = a.restart[ray];
-            int inf = a.inst[ray - R];
+            b = a.restart[DCEM_IDX(ray, LS)];
+            int inf = a.inst[DCEM_IDX(ray - R, a.child_cap)];
             nr = inf & 15;
             ntr = (inf >> 4) & 15;
             set = inf >> 8;
           } else {
-            ray = a.queue ? a.queue[q] : q;
-            b = a.queue ? a.restart[ray] : 0;
+            ray = a.queue ? a.queue[DCEM_IDX(q, R)] : q;
+            b = a.queue ? a.restart[DCEM_IDX(ray, R)] : 0;
             nr = b;
             ntr = 0;
           }
           if (b == 0) {
-            float4 rd = __ldg(&a.rays[ray]);
+            float4 rd = __ldg(&a.rays[DCEM_IDX(ray, R)]);
             set = __float_as_int(rd.w);
-            float4 t4 = __ldg(&a.txs[set]);
+            float4 t4 = __ldg(&a.txs[DCEM_IDX(set, a.nsets)]);
             o = f3(t4.x, t4.y, t4.z);
             d = f3(rd.x, rd.y, rd.z);
             D = 0.0f;
             last = -1;
           } else {
-            float4 lo = a.log_o[(size_t)b * LS + ray], ld = a.log_d[(size_t)b * LS + ray];
+            float4 lo = a.log_o[log_at(a, b, ray)], ld = a.log_d[log_at(a, b, ray)];
             o = f3(lo.x, lo.y, lo.z);
             D = lo.w;
             d = f3(ld.x, ld.y, ld.z);
-            last = a.log_id[(size_t)(b - 1) * LS + ray] & ~kTransBit;
+            last = a.log_id[log_at(a, b - 1, ray)] & ~kTransBit;
           }
         } else {
           ray = -2;
@@ -139,38 +148,38 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       tris += nt;
       maxn = max(maxn, nn);
       bool hit = slot >= 0;
-      a.log_o[(size_t)b * LS + ray] = make_float4(o.x, o.y, o.z, D);
-      a.log_d[(size_t)b * LS + ray] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
-      a.log_id[(size_t)b * LS + ray] = hit ? id : -1;
+      a.log_o[log_at(a, b, ray)] = make_float4(o.x, o.y, o.z, D);
+      a.log_d[log_at(a, b, ray)] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
+      a.log_id[log_at(a, b, ray)] = hit ? id : -1;
       item = ((unsigned)ray << 4) | (unsigned)b;
       if (kT && hit && ntr < a.max_trans) {
         // transmitting material: a child continues straight through
-        int m = __float_as_int(__ldg(&a.bvh.tris[3 * slot + 1]).w);
+        int m = __float_as_int(__ldg(&a.bvh.tris[3 * DCEM_IDX(slot, a.bvh.ntris) + 1]).w);
         if (__ldg(&a.mats[m]).w >= 0.0f) {
           unsigned c = atomicAdd(&a.ctr->n_spawn[a.pass], 1u);
           int cs = spawn_base + (int)c;
           if (cs < R + a.child_cap) {
-            for (int j = 0; j < b; ++j) a.log_id[(size_t)j * LS + cs] = a.log_id[(size_t)j * LS + ray];
-            a.log_id[(size_t)b * LS + cs] = id | kTransBit;
+            for (int j = 0; j < b; ++j) a.log_id[log_at(a, j, cs)] = a.log_id[log_at(a, j, ray)];
+            a.log_id[log_at(a, b, cs)] = id | kTransBit;
             float3 p = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
-            a.log_o[(size_t)(b + 1) * LS + cs] = make_float4(p.x, p.y, p.z, __fadd_rn(D, t));
-            a.log_d[(size_t)(b + 1) * LS + cs] = make_float4(d.x, d.y, d.z, 0.0f);
+            a.log_o[log_at(a, b + 1, cs)] = make_float4(p.x, p.y, p.z, __fadd_rn(D, t));
+            a.log_d[log_at(a, b + 1, cs)] = make_float4(d.x, d.y, d.z, 0.0f);
             a.restart[cs] = b + 1;
-            a.inst[cs - R] = nr | ((ntr + 1) << 4) | (set << 8);
-            a.inst_root[cs - R] = ray < R ? ray : a.inst_root[ray - R];
+            a.inst[DCEM_IDX(cs - R, a.child_cap)] = nr | ((ntr + 1) << 4) | (set << 8);
+            a.inst_root[DCEM_IDX(cs - R, a.child_cap)] = ray < R ? ray : a.inst_root[DCEM_IDX(ray - R, a.child_cap)];
           } else {
             atomicOr(&a.ctr->err, ERR_SPAWN_OVERFLOW);
           }
         }
       }
       if (!hit || (kT ? nr >= a.N : b == a.N)) {
-        a.nseg[ray] = b + 1;
+        a.nseg[DCEM_IDX(ray, LS)] = b + 1;
         ray = -1;
       } else {
         // specular reflection: d' = d - 2 (d.n)/(n.n) n, renormalised
         float3 v0, v1, v2;
         int tid;
-        load_tri(a.bvh.tris, slot, v0, v1, v2, tid);
+        load_tri(a.bvh.tris, DCEM_IDX(slot, a.bvh.ntris), v0, v1, v2, tid);
         float3 n = cross3(sub3(v1, v0), sub3(v2, v0));
         float k = __fdiv_rn(__fmul_rn(2.0f, dot3(d, n)), dot3(n, n));
         float3 dr = f3(__fmaf_rn(-k, n.x, d.x), __fmaf_rn(-k, n.y, d.y), __fmaf_rn(-k, n.z, d.z));
@@ -189,7 +198,7 @@ __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, 
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(&a.ctr->n_capitems, (unsigned)__popc(logged));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (item != 0xffffffffu) a.capitems[base + __popc(logged & ((1u << lane) - 1u))] = item;
+      if (item != 0xffffffffu) a.capitems[DCEM_IDX(base + __popc(logged & ((1u << lane) - 1u)), capitems_cap(a))] = item;
     }
   }
   unsigned long long wsegs = segs, wnodes = nodes, wtris = tris;
@@ -245,6 +254,7 @@ __device__ __forceinline__ void trace_q_body(const TraceArgs& a) {
   f.sx = a.qframe[3];
   f.sy = a.qframe[4];
   f.sz = a.qframe[5];
+  f.n4 = n4;
   __syncthreads();
   trace_rays<true, false, kT>(a, sq, f, st, qr0, qr1);
 }
@@ -266,6 +276,7 @@ __global__ void __launch_bounds__(256, 3) k_trace_qg(TraceArgs a) {
   f.sx = a.qframe[3];
   f.sy = a.qframe[4];
   f.sz = a.qframe[5];
+  f.n4 = min(*a.q4_count, a.q4_bound);
   trace_rays<true, true>(a, a.qnodes, f, st, qr0, qr1);
 }
 
@@ -304,16 +315,16 @@ __global__ void __launch_bounds__(256) k_capture(TraceArgs a) {
       unsigned it = a.capitems[q];
       bool reused = (it & 0x80000000u) != 0u;
       int ray = (int)((it & 0x7fffffffu) >> 4), b = (int)(it & 15u);
-      float4 lo = a.log_o[(size_t)b * LS + ray], ld = a.log_d[(size_t)b * LS + ray];
+      float4 lo = a.log_o[log_at(a, b, ray)], ld = a.log_d[log_at(a, b, ray)];
       float3 o = f3(lo.x, lo.y, lo.z), d = f3(ld.x, ld.y, ld.z);
       float D = lo.w, t = ld.w;
       float tend = isinf(t) ? a.escape : t;
       // the ray's set: its capture spacing, and the link of its captures
       // (a transmission child: its parent's)
-      int set = ray >= R ? (a.inst[ray - R] >> 8)
+      int set = ray >= R ? (a.inst[DCEM_IDX(ray - R, a.child_cap)] >> 8)
                          : a.nsets > 1 ? __float_as_int(__ldg(reinterpret_cast<const float*>(a.rays) + 4 * (size_t)ray + 3))
                                        : 0;
-      float alpha = __ldg(&a.txs[set].w);
+      float alpha = __ldg(&a.txs[DCEM_IDX(set, a.nsets)].w);
       int link0 = set * a.nrx;
       RayPre rp;
       rp.o = o;
@@ -379,15 +390,15 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     int ns = 0;
     if (in) {
       ns = a.nseg[ray];
-      plo[0] = a.log_o[ray];
-      pld[0] = a.log_d[ray];
+      plo[0] = a.log_o[log_at(a, 0, ray)];
+      pld[0] = a.log_d[log_at(a, 0, ray)];
     }
     const int lim = all ? 0 : ns;
 #pragma unroll
     for (int b = 1; b < kPre; ++b) {
       if (b < lim) {
-        plo[b] = a.log_o[(size_t)b * LS + ray];
-        pld[b] = a.log_d[(size_t)b * LS + ray];
+        plo[b] = a.log_o[log_at(a, b, ray)];
+        pld[b] = a.log_d[log_at(a, b, ray)];
       }
     }
     // restart point: the first segment that meets a moved box (ns if none)
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
 #pragma unroll
     for (int b = 0; b < kPre; ++b)
       if (b < bstar) test(b, plo[b], pld[b]);
-    for (int b = kPre; b < bstar; ++b) test(b, a.log_o[(size_t)b * LS + ray], a.log_d[(size_t)b * LS + ray]);
+    for (int b = kPre; b < bstar; ++b) test(b, a.log_o[log_at(a, b, ray)], a.log_d[log_at(a, b, ray)]);
     // the batch's reused segments (when receivers moved) and retraced rays
     const int nitem = any_rx ? bstar : 0;
     unsigned tot = (unsigned)nitem;
@@ -422,11 +433,12 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
       for (int b = 0; b <= N; ++b) {
         unsigned m = __ballot_sync(0xffffffffu, b < nitem);
         if (!m) break;
-        if (b < nitem) a.capitems[at + __popc(m & lt)] = 0x80000000u | ((unsigned)ray << 4) | (unsigned)b;
+        if (b < nitem)
+          a.capitems[DCEM_IDX(at + __popc(m & lt), capitems_cap(a))] = 0x80000000u | ((unsigned)ray << 4) | (unsigned)b;
         at += (unsigned)__popc(m);
       }
     }
-    if (rq) a.queue_w[aq + __popc(qmask & lt)] = ray;
+    if (rq) a.queue_w[DCEM_IDX(aq + __popc(qmask & lt), R)] = ray;
     if (in) {
       c.restart[ray] = bstar;
       reused += (unsigned long long)bstar;
@@ -445,7 +457,7 @@ __global__ void k_carry(TraceArgs a, CoherentArgs c) {
     Cand x = c.prev_cand[i];
     int l = cand_rx(x), s = cand_seg(x);
     int r = a.nsets > 1 ? l % a.nrx : l;   // link -> receiver
-    if (s < c.restart[x.ray] && !c.rx_moved[r]) {
+    if (s < c.restart[DCEM_IDX(x.ray, a.R)] && !c.rx_moved[DCEM_IDX(r, a.nrx)]) {
       emit_cand(a, x.ray, s, l);
       ++kept;
     }
@@ -560,5 +572,7 @@ cudaError_t launch_carry(const TraceArgs& a, const CoherentArgs& c, cudaStream_t
   k_carry<<<grid_for(c.prev_cap, 256, 1024), 256, 0, st>>>(a, c);
   return cudaGetLastError();
 }
+
+DCEM_CHECKS_TAKER(checks_take_trace)
 
 }  // namespace dcem

@@ -15,11 +15,14 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libdcem.so")
+# DCEM_LIB_VARIANT=checks selects the bounds-checked build (build.build(checks=True))
+_VARIANT = os.environ.get("DCEM_LIB_VARIANT", "")
+LIB_PATH = (os.path.join(_HERE, "_build_checks", "libdcem_checks.so") if _VARIANT == "checks"
+            else os.path.join(_HERE, "_build", "libdcem.so"))
 
 MAX_REFL = 10
-OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_NONFINITE, ERR_STACK, ERR_HASH, ERR_STATE, ERR_NOMEM = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_NONFINITE, ERR_STACK, ERR_HASH, ERR_STATE, ERR_NOMEM, ERR_CHECK = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 MODE_FULL, MODE_COHERENT, MODE_STICKY = 0, 1, 2
 PREC_F64, PREC_DF32 = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
