@@ -168,7 +168,9 @@ typedef struct {
   int32_t trace_kernel;        /* closest-hit kernel of this frame: 0 = binary
                                   nodes read from global memory, 1 = 4-wide
                                   compact copy in shared memory, 2 = 4-wide
-                                  compact copy read from global memory        */
+                                  compact copy read from global memory, 3 =
+                                  one launch for every scene of a batch
+                                  (binary nodes from global memory)           */
   int32_t graph_replayed;      /* 1 if the frame's device work was launched as
                                   one replayed CUDA graph                        */
   int32_t paths_sticky;        /* DCEM_MODE_STICKY: valid paths that only the
@@ -363,11 +365,14 @@ const char* dcem_status_string(int status);
 
 /* ---- several scenes per frame ---- */
 
-/* A batch of n distinct scenes traced together. Each frame's device work of
- * all scenes is one CUDA graph launch: every scene's captured frame graph
- * (see dcem_scene_set_graph_replay) is a parallel child, so independent
- * scenes run concurrently. The scenes stay owned by the caller, must
- * outlive the batch, and are moved to `stream` (dcem_scene_set_stream).
+/* A batch of n distinct scenes traced together. In a frame, every scene's
+ * rays (its retrace queue in a coherent frame) are traced by one persistent
+ * closest-hit launch that takes chunks of 32 rays of any scene from a shared
+ * counter; each scene's preparation before it and its capture, dedupe,
+ * validation and reduction after it run concurrently on forked streams, and
+ * the whole frame is one CUDA graph once the scenes' plans repeat. The scenes
+ * stay owned by the caller, must outlive the batch, and are moved to
+ * `stream` (dcem_scene_set_stream).
  * Errors: DCEM_ERR_ARG (null, n < 1, n > 1024, a scene listed twice),
  * DCEM_ERR_CUDA. */
 typedef struct dcem_batch dcem_batch;
@@ -382,9 +387,11 @@ int dcem_batch_update_transforms(dcem_batch* b, const float* const* xf, int32_t 
 
 /* One frame of every scene: scene i as dcem_trace_links(scene i, tx[i],
  * ntx[i], rx[i], nrx[i], rx_ptr_kind, params, &out[i]), with bit-identical
- * results. When every scene's frame plan repeats and params->timing == 0,
- * the frame is one graph launch (stats.graph_replayed = 1 in every result);
- * otherwise the scenes' frames are launched one after another. Synchronises
+ * results. With params->timing == 0 and no scene with transmission, the
+ * scenes' rays share one closest-hit launch (stats.trace_kernel = 3), and
+ * from the second time the scenes' plans repeat the frame is one graph
+ * launch (stats.graph_replayed = 1 in every result); with timing or
+ * transmission the scenes' frames are launched one after another. Synchronises
  * the batch stream. Errors: the first failing scene's status, its index in
  * *failed (if not NULL; -1 when all succeed). */
 int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, const float* const* rx,

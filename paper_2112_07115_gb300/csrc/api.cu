@@ -1434,9 +1434,21 @@ static cudaError_t rec(cudaEvent_t e, cudaStream_t st, bool cap) {
   return cap ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
 }
 
-// The frame's device work, in stream order; no host synchronisation.
-static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap) {
-  bool tm = P.tm, tk = P.tk;
+// The frame's trace arguments: in a coherent frame the retrace queue the
+// marking pass writes and the moved-receiver flags.
+static TraceArgs frame_trace_args(const FramePlan& P) {
+  TraceArgs a = P.a;
+  if (P.coherent) {
+    a.queue = P.a.queue_w;
+    a.rx_moved = P.c.rx_moved;
+  }
+  return a;
+}
+
+// The frame's device work before the closest hit, in stream order (timing
+// events only with `timed`).
+static int enqueue_pre(const FramePlan& P, int sms, cudaStream_t st, bool cap, bool timed) {
+  bool tm = P.tm && timed;
   if (tm) CK(rec(P.ev[0], st, cap));
   CK(cudaMemsetAsync(P.ctr, 0, sizeof(DevCounters), st));
   // transmitters and their capture spacing, from the pinned staging the
@@ -1457,14 +1469,18 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
     CK(cudaMemsetAsync(P.q.vc_next_key, 0, sizeof(unsigned long long) * P.q.vc_cap, st));
   CK(launch_frame_prep(P.fp, st));
   if (tm) CK(rec(P.ev[1], st, cap));
-  TraceArgs a = P.a;
   if (P.coherent) {
-    CK(launch_mark(a, P.c, sms, st));
-    CK(launch_carry(a, P.c, st));
-    a.queue = P.a.queue_w;
-    a.rx_moved = P.c.rx_moved;
+    CK(launch_mark(P.a, P.c, sms, st));
+    CK(launch_carry(P.a, P.c, st));
   }
   if (P.use_q) CK(cudaStreamWaitEvent(st, P.br[1], 0));
+  return DCEM_OK;
+}
+
+// The closest-hit pass (and, with transmission, its passes over the children).
+static int enqueue_trace(const FramePlan& P, int sms, cudaStream_t st, bool cap, bool timed) {
+  bool tk = P.tk && timed;
+  TraceArgs a = frame_trace_args(P);
   if (tk) CK(rec(P.ev[2], st, cap));
   if (P.R > 0) CK(launch_trace(a, sms, st));
   // transmission: pass p traces the children pass p - 1 spawned
@@ -1474,6 +1490,14 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
     CK(launch_trace(ap, sms, st));
   }
   if (tk) CK(rec(P.ev[3], st, cap));
+  return DCEM_OK;
+}
+
+// The frame's device work after the closest hit: capture, dedupe,
+// validation, reduction and the state the next frame compares against.
+static int enqueue_post(const FramePlan& P, int sms, cudaStream_t st, bool cap, bool timed) {
+  bool tm = P.tm && timed;
+  TraceArgs a = frame_trace_args(P);
   if (P.R > 0) CK(launch_capture(a, sms, st));
   if (tm) CK(rec(P.ev[4], st, cap));
   CK(launch_dedupe(P.q, sms * 4, st));
@@ -1505,6 +1529,14 @@ static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap)
   // with device outputs nothing follows on the stream: the frame ends here
   if (tm && P.ptr_dev) CK(rec(P.ev[8], st, cap));
   return DCEM_OK;
+}
+
+// The frame's device work, in stream order; no host synchronisation.
+static int enqueue_frame(const FramePlan& P, int sms, cudaStream_t st, bool cap) {
+  int rc = enqueue_pre(P, sms, st, cap, true);
+  if (rc == DCEM_OK) rc = enqueue_trace(P, sms, st, cap, true);
+  if (rc == DCEM_OK) rc = enqueue_post(P, sms, st, cap, true);
+  return rc;
 }
 // Captures the frame's work from its plan into a graph on the scene's
 // capture stream (nothing runs while capturing) and instantiates it.
@@ -1816,6 +1848,20 @@ struct dcem_batch {
     cudaGraphExec_t exec = nullptr;
   } parent[2];
   int victim = 0;
+  // one closest-hit launch for every scene (frames without timing or
+  // transmission): the scenes' trace arguments staged in pinned memory and
+  // copied in by the frame, the launch's chunk counter, and the captured
+  // frames keyed by the scenes' plans (captured the second time a key is seen)
+  TraceArgs* h_tab = nullptr;
+  TraceArgs* d_tab = nullptr;
+  unsigned* d_chunk = nullptr;
+  cudaStream_t cap_st = nullptr;
+  struct One {
+    std::vector<FramePlan> keys;
+    cudaGraphExec_t exec = nullptr;
+  } one[2];
+  std::vector<FramePlan> pending[2];  // by the frames' parity (the candidate buffers alternate)
+  int one_victim = 0;
 };
 
 namespace {
@@ -1825,6 +1871,12 @@ void batch_free(dcem_batch* b) {
   if (b->st) cudaStreamSynchronize(b->st);
   for (auto& p : b->parent)
     if (p.exec) cudaGraphExecDestroy(p.exec);
+  for (auto& o : b->one)
+    if (o.exec) cudaGraphExecDestroy(o.exec);
+  if (b->h_tab) cudaFreeHost(b->h_tab);
+  dfree(b->d_tab);
+  dfree(b->d_chunk);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
   for (auto f : b->fork) cudaStreamDestroy(f);
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
@@ -1865,6 +1917,90 @@ int batch_graph(dcem_batch* b, cudaGraphExec_t* exec) {
   return DCEM_OK;
 }
 
+// Every scene's frame with one closest-hit launch between the scenes'
+// preparation and their capture, dedupe, validation and reduction; the
+// scenes' own stages run on the fork streams in turn. Stream order only.
+int batch_enqueue(dcem_batch* b, cudaStream_t st, bool cap) {
+  const int n = (int)b->sc.size(), nf = (int)b->fork.size();
+  CK(cudaEventRecord(b->fork_ev, st));
+  for (int k = 0; k < nf; ++k) CK(cudaStreamWaitEvent(b->fork[k], b->fork_ev, 0));
+  for (int i = 0; i < n; ++i) {
+    int rc = enqueue_pre(b->sc[i]->plan, b->sc[i]->sms, b->fork[i % nf], cap, false);
+    if (rc != DCEM_OK) return rc;
+  }
+  for (int k = 0; k < nf; ++k) {
+    CK(cudaEventRecord(b->join[k], b->fork[k]));
+    CK(cudaStreamWaitEvent(st, b->join[k], 0));
+  }
+  CK(cudaMemcpyAsync(b->d_tab, b->h_tab, sizeof(TraceArgs) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(b->d_chunk, 0, sizeof(unsigned), st));
+  CK(launch_trace_batch(b->d_tab, n, b->d_chunk, b->sc[0]->sms, st));
+  CK(cudaEventRecord(b->fork_ev, st));
+  for (int k = 0; k < nf; ++k) CK(cudaStreamWaitEvent(b->fork[k], b->fork_ev, 0));
+  for (int i = 0; i < n; ++i) {
+    int rc = enqueue_post(b->sc[i]->plan, b->sc[i]->sms, b->fork[i % nf], cap, false);
+    if (rc != DCEM_OK) return rc;
+  }
+  for (int k = 0; k < nf; ++k) {
+    CK(cudaEventRecord(b->join[k], b->fork[k]));
+    CK(cudaStreamWaitEvent(st, b->join[k], 0));
+  }
+  return DCEM_OK;
+}
+
+bool same_plans(const std::vector<FramePlan>& a, const std::vector<FramePlan>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i)
+    if (std::memcmp(&a[i], &b[i], sizeof(FramePlan)) != 0) return false;
+  return true;
+}
+
+// The one-launch frame of the batch: replays its captured graph when the
+// scenes' plans were captured before, captures it the second time the plans
+// are seen in a row, else runs it directly (which also sets every kernel's
+// launch attributes).
+int batch_one_launch(dcem_batch* b, bool* replayed) {
+  *replayed = false;
+  std::vector<FramePlan> keys;
+  for (dcem_scene* s : b->sc) keys.push_back(s->plan);
+  for (auto& o : b->one)
+    if (o.exec && same_plans(o.keys, keys)) {
+      CK(cudaGraphLaunch(o.exec, b->st));
+      *replayed = true;
+      return DCEM_OK;
+    }
+  std::vector<FramePlan>& pend = b->pending[b->sc[0]->cur];
+  if (!same_plans(pend, keys)) {
+    pend = keys;
+    return batch_enqueue(b, b->st, false);
+  }
+  if (!b->cap_st) CK(cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking));
+  auto& o = b->one[b->one_victim];
+  b->one_victim ^= 1;
+  if (o.exec) cudaGraphExecDestroy(o.exec);
+  o.exec = nullptr;
+  o.keys.clear();
+  CK(cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal));
+  int rc = batch_enqueue(b, b->cap_st, true);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap_st, &g);
+  if (rc == DCEM_OK && e != cudaSuccess) rc = status_of(e);
+  if (rc == DCEM_OK) {
+    e = cudaGraphInstantiate(&o.exec, g, 0);
+    if (e != cudaSuccess) {
+      o.exec = nullptr;
+      rc = status_of(e);
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (rc != DCEM_OK) return rc;
+  o.keys = keys;
+  CK(cudaGraphLaunch(o.exec, b->st));
+  *replayed = true;
+  return DCEM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1894,6 +2030,9 @@ int dcem_batch_create(dcem_scene* const* scenes, int32_t n, void* stream, dcem_b
     int rc = dcem_scene_set_stream(scenes[i], stream);
     if (rc != DCEM_OK) e = cudaErrorUnknown;
   }
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_tab, sizeof(TraceArgs) * n);
+  if (e == cudaSuccess) e = dalloc(&b->d_tab, (size_t)n);
+  if (e == cudaSuccess) e = dalloc(&b->d_chunk, (size_t)1);
   if (e != cudaSuccess) {
     batch_free(b);
     return status_of(e);
@@ -1946,6 +2085,42 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
     int rc = frame_begin(b->sc[i], tx[i], ntx[i], rx[i], nrx[i], rx_ptr_kind, p, &out[i], &c);
     if (rc != DCEM_OK) return fail(i, rc);
     coh[i] = c;
+  }
+  // frames without timing and transmission: one closest-hit launch for
+  // every scene's rays
+  bool one = p->timing == 0;
+  for (int i = 0; i < n; ++i) one = one && b->sc[i]->max_trans == 0;
+  if (one) {
+    for (int i = 0; i < n; ++i) {
+      dcem_scene* s = b->sc[i];
+      make_plan(s, nrx[i], p, coh[i] != 0, &out[i], s->plan);
+      FramePlan& P = s->plan;
+      P.use_q = 0;  // the batch launch reads the binary nodes from L2: no compact copy
+      P.a.use_q = 0;
+      s->last_use_q = 3;  // every scene's rays in one launch
+      s->launches += 2 + (coh[i] ? 2 : 0) + (s->R > 0 ? 1 : 0) + 5 + (nrx[i] > 0 ? 1 : 0) +
+                     (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
+                     (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) + (i == 0 ? 1 : 0);
+      s->graph_replayed = 0;
+      b->h_tab[i] = frame_trace_args(P);
+    }
+    bool replayed = false;
+    int rc = batch_one_launch(b, &replayed);
+    if (rc != DCEM_OK) return fail(0, rc);
+    CK(cudaStreamSynchronize(b->st));
+    for (dcem_scene* s : b->sc) {
+      s->cur ^= 1;
+      s->graph_replayed = replayed ? 1 : 0;
+    }
+    int first = DCEM_OK;
+    for (int i = 0; i < n; ++i) {
+      int rc2 = frame_finish(b->sc[i], tx[i], ntx[i], rx[i], nrx[i], rx_ptr_kind, p, &out[i], coh[i] != 0, true);
+      if (rc2 != DCEM_OK && first == DCEM_OK) {
+        first = rc2;
+        if (failed) *failed = i;
+      }
+    }
+    return first;
   }
   // every scene's frame graph ready (and no event timing): one launch
   bool all = p->timing == 0;

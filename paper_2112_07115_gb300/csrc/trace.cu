@@ -237,6 +237,131 @@ __global__ void __launch_bounds__(256) k_trace_t(TraceArgs a) {
   trace_rays<false, false, true>(a, nullptr, f, st, kEmpty, kEmpty);
 }
 
+// ---------------------------------------------------------------------------
+// several scenes in one launch
+// ---------------------------------------------------------------------------
+// Every scene's rays (its retrace queue in a coherent frame) in one
+// persistent launch: the scenes' work is cut into chunks of 32 rays of one
+// scene, a warp takes the next chunk from a counter shared by all scenes and
+// traces its rays over that scene's binary trees (nodes from L2), with the
+// same per-segment steps as trace_rays. A chunk's scene is found by a binary
+// search over the chunk counts' prefix, formed by every CTA at its start.
+__global__ void __launch_bounds__(256) k_trace_batch(const TraceArgs* __restrict__ tab, int n, unsigned* chunk_ctr) {
+  extern __shared__ int sstk[];
+  __shared__ unsigned pre[kMaxBatch + 1];  // pre[s]: chunks of the scenes before s
+  TStack st;
+  bind_stack(st, sstk, kStackTrace);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const TraceArgs& t = tab[i];
+    unsigned nq = t.queue ? min(*t.nq_dev, (unsigned)t.R) : (unsigned)t.R;
+    pre[i + 1] = (nq + 31u) >> 5;
+  }
+  if (threadIdx.x == 0) pre[0] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i <= n; ++i) pre[i] += pre[i - 1];
+  __syncthreads();
+  const unsigned total = pre[n];
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned c = 0;
+    if (lane == 0) c = atomicAdd(chunk_ctr, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= total) break;
+    int lo = 0, hi = n;  // the scene s with pre[s] <= c < pre[s + 1]
+    while (hi - lo > 1) {
+      int m = (lo + hi) >> 1;
+      if (pre[m] <= c) lo = m; else hi = m;
+    }
+    const TraceArgs& a = tab[lo];
+    const Bvh bvh = a.bvh;
+    const int R = a.R, LS = a.LS, N = a.N;
+    const unsigned nq = a.queue ? min(*a.nq_dev, (unsigned)R) : (unsigned)R;
+    const unsigned q = ((c - pre[lo]) << 5) + (unsigned)lane;
+    int ray = -1, b = 0, last = -1;
+    float3 o = f3(0.0f, 0.0f, 0.0f), d = o;
+    float D = 0.0f;
+    if (q < nq) {
+      ray = a.queue ? a.queue[DCEM_IDX((int)q, R)] : (int)q;
+      b = a.queue ? a.restart[DCEM_IDX(ray, R)] : 0;
+      if (b == 0) {
+        float4 rd = __ldg(&a.rays[DCEM_IDX(ray, R)]);
+        float4 t4 = __ldg(&a.txs[DCEM_IDX(__float_as_int(rd.w), a.nsets)]);
+        o = f3(t4.x, t4.y, t4.z);
+        d = f3(rd.x, rd.y, rd.z);
+      } else {
+        float4 lo4 = a.log_o[log_at(a, b, ray)], ld = a.log_d[log_at(a, b, ray)];
+        o = f3(lo4.x, lo4.y, lo4.z);
+        D = lo4.w;
+        d = f3(ld.x, ld.y, ld.z);
+        last = a.log_id[log_at(a, b - 1, ray)];
+      }
+    }
+    unsigned segs = 0, nodes = 0, tris = 0, ovf = 0, maxn = 0;
+    while (__any_sync(0xffffffffu, ray >= 0)) {
+      unsigned item = 0xffffffffu;
+      if (ray >= 0) {
+        RayPre rp = ray_pre(o, d);
+        float t;
+        int id;
+        unsigned nn = 0, nt = 0;
+        const int slot = closest_hit(bvh, rp, a.tmin, last, t, id, ovf, nn, nt, st);
+        ++segs;
+        nodes += nn;
+        tris += nt;
+        maxn = max(maxn, nn);
+        const bool hit = slot >= 0;
+        a.log_o[log_at(a, b, ray)] = make_float4(o.x, o.y, o.z, D);
+        a.log_d[log_at(a, b, ray)] = make_float4(d.x, d.y, d.z, hit ? t : __int_as_float(0x7f800000));
+        a.log_id[log_at(a, b, ray)] = hit ? id : -1;
+        item = ((unsigned)ray << 4) | (unsigned)b;
+        if (!hit || b == N) {
+          a.nseg[DCEM_IDX(ray, LS)] = b + 1;
+          ray = -1;
+        } else {
+          // specular reflection: d' = d - 2 (d.n)/(n.n) n, renormalised (as trace_rays)
+          float3 v0, v1, v2;
+          int tid;
+          load_tri(bvh.tris, DCEM_IDX(slot, bvh.ntris), v0, v1, v2, tid);
+          float3 nrm = cross3(sub3(v1, v0), sub3(v2, v0));
+          float k = __fdiv_rn(__fmul_rn(2.0f, dot3(d, nrm)), dot3(nrm, nrm));
+          float3 dr = f3(__fmaf_rn(-k, nrm.x, d.x), __fmaf_rn(-k, nrm.y, d.y), __fmaf_rn(-k, nrm.z, d.z));
+          float inv = __fdiv_rn(1.0f, __fsqrt_rn(dot3(dr, dr)));
+          o = f3(__fmaf_rn(t, d.x, o.x), __fmaf_rn(t, d.y, o.y), __fmaf_rn(t, d.z, o.z));
+          d = f3(__fmul_rn(dr.x, inv), __fmul_rn(dr.y, inv), __fmul_rn(dr.z, inv));
+          D = __fadd_rn(D, t);
+          last = id;
+          ++b;
+        }
+      }
+      const unsigned logged = __ballot_sync(0xffffffffu, item != 0xffffffffu);
+      if (logged) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&a.ctr->n_capitems, (unsigned)__popc(logged));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (item != 0xffffffffu) a.capitems[DCEM_IDX(base + __popc(logged & ((1u << lane) - 1u)), capitems_cap(a))] = item;
+      }
+    }
+    unsigned long long wsegs = segs, wnodes = nodes, wtris = tris;
+    for (int off = 16; off > 0; off >>= 1) {
+      wsegs += __shfl_down_sync(0xffffffffu, wsegs, off);
+      wnodes += __shfl_down_sync(0xffffffffu, wnodes, off);
+      wtris += __shfl_down_sync(0xffffffffu, wtris, off);
+      maxn = max(maxn, __shfl_down_sync(0xffffffffu, maxn, off));
+    }
+    if (lane == 0 && wsegs) {
+      atomicAdd(&a.ctr->segments_traced, wsegs);
+      atomicAdd(&a.ctr->node_visits, wnodes);
+      atomicAdd(&a.ctr->tri_tests, wtris);
+      atomicMax(&a.ctr->max_seg_nodes, maxn);
+    }
+    if (__any_sync(0xffffffffu, ovf != 0u) && lane == 0) {
+      atomicAdd(&a.ctr->stack_overflow, 1u);
+      atomicOr(&a.ctr->err, ERR_STACK);
+    }
+  }
+}
+
 // Same traversal over the 4-wide compact node copy staged in shared memory
 // (one CTA of kTraceQThreads threads per SM, the copy loaded once per CTA).
 template <bool kT>
@@ -520,6 +645,14 @@ cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st) {
     if (tr) k_trace_qt<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
     else k_trace_q<<<grid_for(n, kTraceQThreads, sms), kTraceQThreads, smem, st>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_batch(const TraceArgs* d_tab, int n, unsigned* chunk_ctr, int sms, cudaStream_t st) {
+  static int resident = 0;
+  size_t smem = 256 * (size_t)kStackTrace * sizeof(int);
+  if (!resident) resident = resident_blocks((const void*)k_trace_batch, sms, smem);
+  k_trace_batch<<<resident, 256, smem, st>>>(d_tab, n, chunk_ctr);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,9 @@ constexpr int kTraceBlocks[] = {64, 128, 256};
 constexpr int kTraceStackMin = 8, kTraceStackMax = 32;
 cudaError_t launch_trace(const TraceArgs& a, int sms, cudaStream_t st);
 cudaError_t launch_capture(const TraceArgs& a, int sms, cudaStream_t st);
+// The closest-hit pass of n scenes in one launch (d_tab: their arguments on the
+// device; chunk_ctr zeroed before). No transmission.
+cudaError_t launch_trace_batch(const TraceArgs* d_tab, int n, unsigned* chunk_ctr, int sms, cudaStream_t st);
 cudaError_t launch_mark(const TraceArgs& a, const CoherentArgs& c, int sms, cudaStream_t st);
 cudaError_t launch_carry(const TraceArgs& a, const CoherentArgs& c, cudaStream_t st);
 
