@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-diffraction", action="store_true", help="skip the diffraction measurement")
     ap.add_argument("--no-toy", action="store_true", help="skip the toy-street workload")
     ap.add_argument("--no-band", action="store_true", help="skip the highway at 5.9 GHz")
+    ap.add_argument("--no-roadside", action="store_true", help="skip the highway with static roadside receivers")
     ap.add_argument("--no-gradient", action="store_true", help="skip the differentiable urban workload")
     return ap.parse_args()
 
@@ -423,6 +424,9 @@ def run_ours(args):
     band = None
     if not args.no_band:
         band = run_band(args, stream, dev, world, flush, rank)
+    roadside = None
+    if not args.no_roadside:
+        roadside = run_roadside(args, stream, dev, world, flush, rank)
     gradw = None
     if not args.no_gradient:
         gradw = run_gradient(args, stream, dev, world, flush, rank)
@@ -463,6 +467,7 @@ def run_ours(args):
             "validation_precision": precs,
             "toy_street": toy,
             "highway_5p9ghz": band,
+            "highway_roadside_rx": roadside,
             "differentiable_urban": gradw,
             "batched": batched,
             "multi_scene": multi,
@@ -628,6 +633,48 @@ def run_band(args, stream, dev, world, flush, rank, freq=5.9e9, warmup=5):
             out["rx_power_err_db"] = power_error_vs_oracle(sc, s, frames[-1], max_paths, bufs[3], bufs[1], bufs[2],
                                                            res_n=st[-1])
         s.close()
+    out["coherent_speedup"] = round(out["coherent"]["frames_per_s"] / out["full"]["frames_per_s"], 3)
+    return out
+
+
+def run_roadside(args, stream, dev, world, flush, rank, warmup=5):
+    """The headline highway with its 200 receivers as static roadside units
+    (2.5 m high, 2 m beyond the outer barriers) instead of on the vehicles'
+    roofs: the same moving traffic, so the coherent frame re-tests no reused
+    segment against moved receivers and copies the validation of keys that
+    no moved object touches. Coherent and full frames (L2 flushed before
+    each), the stage times of an instrumented pass of both, and the last
+    frame's paths re-validated by the FP64 oracle."""
+    import torch
+    from paper_2112_07115_gb300 import dcem, scenes
+    K = min(args.steps, 100)
+    sc = scenes.highway(seed=0, n_frames=warmup + K + 2, n_rays=args.rays, max_refl=4, freq_hz=args.freq,
+                        roadside_rx=200)
+    rays = scenes.fibonacci_sphere(sc.n_rays)
+    frames = list(range(1, warmup + K + 1))
+    xf_d = torch.from_numpy(sc.xf).to(dev)
+    rx_d = torch.from_numpy(sc.rx).to(dev)
+    max_paths = 1 << 17
+    res, bufs = _device_result(sc.nrx, max_paths, dev)
+    out = {"workload": "highway V2I as the headline (1M rays, 4 reflections, 200 moving vehicles), 200 static "
+                       "roadside receivers instead of roof receivers"}
+    for name, mode in (("full", dcem.MODE_FULL), ("coherent", dcem.MODE_COHERENT)):
+        s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+        s.set_rays(rays)
+        prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=2)
+        ms, st = _frames_timed(s, sc, frames, prm, stream, flush, xf_d, rx_d, res, warmup)
+        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev)
+        if name == "coherent" and rank == 0:
+            out["rx_power_err_db"] = power_error_vs_oracle(sc, s, frames[-1], max_paths, bufs[3], bufs[1], bufs[2],
+                                                           res_n=st[-1])
+        s.close()
+        # instrumented pass (events around every stage; not timed)
+        s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
+        s.set_rays(rays)
+        prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=1)
+        _, sti = _frames_timed(s, sc, frames[:warmup + 10], prm, stream, flush, xf_d, rx_d, res, warmup)
+        s.close()
+        out[name]["stage_ms"] = {n: round(float(np.mean([x["ms_stage"][n] for x in sti])), 4) for n in dcem.STAGES}
     out["coherent_speedup"] = round(out["coherent"]["frames_per_s"] / out["full"]["frames_per_s"], 3)
     return out
 

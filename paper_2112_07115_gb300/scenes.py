@@ -222,13 +222,15 @@ VEH_CLASSES = {  # length, width, height
 
 def highway(seed: int = 0, n_frames: int = 100, n_vehicles: int = 200,
             n_rays: int = 1_000_000, max_refl: int = 4, freq_hz: float = 28e9,
-            length: float = HW_LENGTH) -> Scene:
+            length: float = HW_LENGTH, roadside_rx: int = 0) -> Scene:
     """Highway V2I: straight 6-lane road (30 m wide, 20 m tessellation), three
     2 m x 0.5 m concrete barriers (road edges and median), ``n_vehicles``
     vehicles (70% car, 20% van, 10% truck, 10 tris each) at U[20,35] m/s with
     Poisson(0.05/s) lane changes along a 3 s cosine profile, a 10 m gap rule,
     and wrap-around at the road ends. Tx at (L/2, 20, 8); one Rx 0.1 m above
-    each vehicle roof. Frames at 10 Hz.
+    each vehicle roof. Frames at 10 Hz. With ``roadside_rx`` > 0 the
+    receivers are that many static roadside units instead, 2.5 m high and 2 m
+    beyond the outer barriers, evenly spaced along both road edges.
     """
     ss = np.random.SeedSequence([seed, 2])
     r_layout, r_speed, r_lc = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
@@ -324,6 +326,14 @@ def highway(seed: int = 0, n_frames: int = 100, n_vehicles: int = 200,
             lc_from[k] = cur
             lc_to[k] = nb[r_lc.integers(0, len(nb))]
             lc_t[k] = 0.0
+    if roadside_rx > 0:
+        half = (roadside_rx + 1) // 2
+        yo = max(abs(b) for b in HW_BARRIER_Y) + 2.0
+        pts = []
+        for side, cnt in ((1.0, half), (-1.0, roadside_rx - half)):
+            xs = (np.arange(cnt) + 0.5) * (length / cnt)
+            pts += [(xx, side * yo, 2.5) for xx in xs]
+        rx = np.broadcast_to(np.asarray(pts, np.float64), (n_frames, roadside_rx, 3)).copy()
     return Scene("highway", tris, tobj, tmat, default_materials(), n_vehicles,
                  xf.astype(np.float32), np.array([length / 2, 20.0, 8.0], np.float32),
                  rx.astype(np.float32), freq_hz=freq_hz, n_rays=n_rays, max_refl=max_refl,
