@@ -787,8 +787,18 @@ static int point_in_tri(const otri* T, v3 p) {
 
 /* Occlusion of the open sub-segment a->b by any triangle except ex0/ex1.
  * Parameter range (eps_occ, 1-eps_occ). Returns 1 if occluded. */
+static int occluded3(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, const or_params* P,
+                     double scale, uint32_t* fl);
+
 static int occluded(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_params* P,
                     double scale, uint32_t* fl) {
+  return occluded3(S, a, b, ex0, ex1, ex1, P, scale, fl);
+}
+
+/* Is the open segment a-b (its first and last eps_occ trimmed) blocked by a
+ * triangle other than ex0, ex1, ex2? Flags decisions within the FP32 margin. */
+static int occluded3(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, const or_params* P,
+                     double scale, uint32_t* fl) {
   v3 dv = sub(b, a);
   double len = norm(dv);
   if (!(len > 0)) return 0;
@@ -796,7 +806,7 @@ static int occluded(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_para
   double base = P->edge_eps * scale;
   int occ = 0;
   for (int j = 0; j < S->ntri; ++j) {
-    if (j == ex0 || j == ex1) continue;
+    if (j == ex0 || j == ex1 || j == ex2) continue;
     xinfo x;
     ray_tri(&S->t[j], a, d, base, P->edge_eps, &x);
     if (isnan(x.t)) continue;
@@ -1315,6 +1325,176 @@ int64_t or_diffract(const float* tris, const int32_t* tri_mat, const int32_t* tr
         o->pts[0][0] = Q.x; o->pts[0][1] = Q.y; o->pts[0][2] = Q.z;
       }
       nvalid++;
+    }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
+/* Sec. III steps 3-5 combined: one reflection on a static triangle j before
+ * or after a first-order diffraction at wedge w. By image theory the path
+ * Tx -> P -> Q -> Rx (reflection first) is the diffraction of the
+ * transmitter's image T' in j's plane, and Tx -> Q -> P -> Rx (reflection
+ * last) the diffraction toward the receiver's image R'; Q follows Keller's
+ * law for that pair, P is where the unfolded leg crosses the plane. The path
+ * is kept when Q lies inside the edge, P inside j, the receiver (or its
+ * image) beyond the incident shadow boundary of the source (or its image),
+ * and the three legs unoccluded. Field: the UTD coefficient (as or_diffract)
+ * with the image's distances (spreading and phase over the unfolded length)
+ * and the Fresnel reflection at P in the bounce basis of validate_one.
+ * Keys: rx, 2, then j, w | OR_DIFF (reflection first) or w | OR_DIFF, j;
+ * -1 padded to 2 + width. Returns the number of valid paths (may exceed
+ * cap). */
+int64_t or_diffract_refl(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                         const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                         const or_params* P, int32_t width, int32_t* keys_out, opath* paths_out, int64_t cap) {
+  if (width < 2) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  int64_t nvalid = 0;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (long w = 0; w < nw; ++w) {
+      const owedge* E = &W[w];
+      for (int j = 0; j < ntri; ++j) {
+        if ((tri_obj && tri_obj[j] >= 0) || j == E->ta || j == E->tb) continue;
+        const otri* Tj = &S.t[j];
+        double cpl = dot(Tj->nh, Tj->v[0]);
+        for (int first = 1; first >= 0; --first) {  /* 1: reflection before the wedge */
+          uint32_t fl = 0;
+          v3 src = T, obs = R;
+          if (first) src = sub(T, scl(Tj->nh, 2.0 * (dot(Tj->nh, T) - cpl)));
+          else obs = sub(R, scl(Tj->nh, 2.0 * (dot(Tj->nh, R) - cpl)));
+          /* Keller's law for (src, obs) */
+          v3 dt = sub(src, E->p0), dr = sub(obs, E->p0);
+          double zt = dot(dt, E->e), zr = dot(dr, E->e);
+          double rt = norm(sub(dt, scl(E->e, zt))), rr = norm(sub(dr, scl(E->e, zr)));
+          if (!(rt > 0 && rr > 0)) continue;
+          double zq = zt + (zr - zt) * rt / (rt + rr);
+          double uq = zq / E->len;
+          if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+          if (!(uq > 0 && uq < 1)) continue;
+          v3 Q = add(E->p0, scl(E->e, zq));
+          double phip = wedge_angle(E, src), phi = wedge_angle(E, obs), nn = E->n;
+          if (phip > nn * M_PI || phi > nn * M_PI) continue;
+          if (fabs(fabs(phi - phip) - M_PI) <= 1e-9) fl |= ORF_VAL_PARAM;
+          if (!(fabs(phi - phip) > M_PI)) continue;
+          /* the reflection point on the unfolded leg src -> Q or Q -> obs */
+          v3 a0 = first ? src : Q, a1 = first ? Q : obs;
+          double den = dot(Tj->nh, sub(a1, a0));
+          if (den == 0.0) continue;
+          double sp_ = (cpl - dot(Tj->nh, a0)) / den;
+          if (fabs(sp_) <= P->val_eps || fabs(sp_ - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+          if (!(sp_ > 0 && sp_ < 1)) continue;
+          v3 Pp = add(a0, scl(sub(a1, a0), sp_));
+          double scale = fmax(maxabs(T), maxabs(R));
+          if (edge_margin(Tj, Pp) <= P->val_eps * (scale + 1.0)) fl |= ORF_VAL_EDGE;
+          if (!point_in_tri(Tj, Pp)) continue;
+          /* the three legs */
+          if (first) {
+            if (occluded3(&S, T, Pp, j, j, j, P, scale, &fl)) continue;
+            if (occluded3(&S, Pp, Q, j, E->ta, E->tb, P, scale, &fl)) continue;
+            if (occluded3(&S, Q, R, E->ta, E->tb, E->tb, P, scale, &fl)) continue;
+          } else {
+            if (occluded3(&S, T, Q, E->ta, E->tb, E->tb, P, scale, &fl)) continue;
+            if (occluded3(&S, Q, Pp, j, E->ta, E->tb, P, scale, &fl)) continue;
+            if (occluded3(&S, Pp, R, j, j, j, P, scale, &fl)) continue;
+          }
+          /* UTD with the image's geometry */
+          double sp = norm(sub(Q, src)), sd = norm(sub(obs, Q));
+          v3 ip = scl(sub(Q, src), 1.0 / sp), dd = scl(sub(obs, Q), 1.0 / sd);
+          double beta0 = acos(fmax(-1.0, fmin(1.0, dot(ip, E->e))));
+          double Ld = sd * sp * sin(beta0) * sin(beta0) / (sd + sp);
+          v3 php = cross(E->e, ip), ph = cross(E->e, dd);
+          php = scl(php, -1.0 / norm(php));
+          ph = scl(ph, 1.0 / norm(ph));
+          v3 bp = cross(ip, php), bd = cross(dd, ph);
+          int ma = S.t[E->ta].mat, mb = S.t[E->tb].mat;
+          if (ma < 0 || ma >= S.nmat) ma = 0;
+          if (mb < 0 || mb >= S.nmat) mb = 0;
+          double complex r0s, r0h, rns, rnh;
+          fresnel(&S.mats[3 * ma], P->freq_hz, fabs(sin(phip)), &r0s, &r0h);
+          fresnel(&S.mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - phi)), &rns, &rnh);
+          double complex Ds = utd_coeff(nn, phi, phip, beta0, Ld, k, r0s, rns, &fl);
+          double complex Dh = utd_coeff(nn, phi, phip, beta0, Ld, k, r0h, rnh, &fl);
+          /* the reflection at P: incoming and outgoing directions, bounce basis */
+          v3 din = first ? unit(sub(Pp, T)) : dd;
+          v3 dout = first ? ip : unit(sub(R, Pp));
+          v3 nh = Tj->nh;
+          double ct = fabs(dot(din, nh));
+          v3 sv = cross(din, nh);
+          double sn = norm(sv);
+          if (sn < 1e-12) {
+            v3 ax = fabs(nh.x) < 0.9 ? mk(1, 0, 0) : mk(0, 1, 0);
+            sv = unit(cross(nh, ax));
+          } else {
+            sv = scl(sv, 1.0 / sn);
+          }
+          v3 pin = cross(sv, din), pout = cross(sv, dout);
+          int mj = Tj->mat;
+          if (mj < 0 || mj >= S.nmat) mj = 0;
+          double complex gte, gtm;
+          fresnel(&S.mats[3 * mj], P->freq_hz, ct, &gte, &gtm);
+          double complex A = csqrt(sp / (sd * (sd + sp))) * cexp(-I * k * sd);
+          double complex a;
+          if (first) {
+            /* Tx field along T -> P, reflected at P, arrives at Q from T' */
+            v3 e0 = pol_dir(u, din, &fl);
+            double complex es = dot(e0, sv), ep = dot(e0, pin);
+            c3 E1;
+            E1.x = gte * es * sv.x + gtm * ep * pout.x;
+            E1.y = gte * es * sv.y + gtm * ep * pout.y;
+            E1.z = gte * es * sv.z + gtm * ep * pout.z;
+            double complex Ei = cexp(-I * k * sp) / sp;
+            double complex Eb = Ei * cdot(E1, bp), Ep = Ei * cdot(E1, php);
+            v3 prx = pol_dir(u, scl(dd, -1.0), &fl);
+            double complex proj = (-Ds * Eb) * dot(bd, prx) + (-Dh * Ep) * dot(ph, prx);
+            a = (lam / (4.0 * M_PI)) * proj * A;
+          } else {
+            /* diffracted field toward R', reflected at P */
+            v3 e0 = pol_dir(u, ip, &fl);
+            double complex Ei = cexp(-I * k * sp) / sp;
+            double complex Eb = Ei * dot(e0, bp), Ep = Ei * dot(e0, php);
+            c3 Ed;
+            Ed.x = (-Ds * Eb) * bd.x + (-Dh * Ep) * ph.x;
+            Ed.y = (-Ds * Eb) * bd.y + (-Dh * Ep) * ph.y;
+            Ed.z = (-Ds * Eb) * bd.z + (-Dh * Ep) * ph.z;
+            double complex es = cdot(Ed, sv), ep = cdot(Ed, pin);
+            c3 E2;
+            E2.x = gte * es * sv.x + gtm * ep * pout.x;
+            E2.y = gte * es * sv.y + gtm * ep * pout.y;
+            E2.z = gte * es * sv.z + gtm * ep * pout.z;
+            v3 prx = pol_dir(u, scl(dout, -1.0), &fl);
+            a = (lam / (4.0 * M_PI)) * cdot(E2, prx) * A;
+          }
+          if (nvalid < cap) {
+            int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+            kk[0] = r;
+            kk[1] = 2;
+            kk[2] = first ? j : ((int32_t)w | OR_DIFF);
+            kk[3] = first ? ((int32_t)w | OR_DIFF) : j;
+            for (int q = 2; q < width; ++q) kk[2 + q] = -1;
+            opath* o = &paths_out[nvalid];
+            memset(o, 0, sizeof(*o));
+            o->valid = 1;
+            o->flags = fl;
+            o->len_m = sp + sd;
+            o->delay_s = (sp + sd) / C0;
+            o->amp_re = creal(a);
+            o->amp_im = cimag(a);
+            v3 p1 = first ? Pp : Q, p2 = first ? Q : Pp;
+            o->pts[0][0] = p1.x; o->pts[0][1] = p1.y; o->pts[0][2] = p1.z;
+            o->pts[1][0] = p2.x; o->pts[1][1] = p2.y; o->pts[1][2] = p2.z;
+          }
+          nvalid++;
+        }
+      }
     }
   }
   free(W);

@@ -58,6 +58,12 @@ MUTANTS = [
      "d = unit(sub(d, scl(T->nh, dot(d, T->nh))));"),
     # delay
     ("delay_light_speed", "out->delay_s = L / C0;", "out->delay_s = L / 3.0e8;"),
+    # image of the transmitter for a reflection before a diffraction
+    ("diffraction_image_half", "if (first) src = sub(T, scl(Tj->nh, 2.0 * (dot(Tj->nh, T) - cpl)));",
+     "if (first) src = sub(T, scl(Tj->nh, 1.0 * (dot(Tj->nh, T) - cpl)));"),
+    # the reflection after a diffraction uses the bounce basis of the outgoing leg
+    ("diffraction_reflection_basis", "v3 pin = cross(sv, din), pout = cross(sv, dout);\n          int mj",
+     "v3 pin = cross(sv, dout), pout = cross(sv, din);\n          int mj"),
 ]
 
 

@@ -651,3 +651,80 @@ def test_toy_street_wedges_and_diffraction_frame(oracle_mod):
     assert d.any() and r.paths["valid"][d].all()
     plain = O.frame(sc, 0, scenes.fibonacci_sphere(10_000), O.OracleParams(max_refl=2, n_rays=10_000))
     assert set(map(tuple, plain.keys.tolist())) == set(map(tuple, r.keys[~d].tolist()))
+
+
+def _ground_and_building(ground_mat, building_mat, tx, rx, with_ground=True):
+    """A 20 x 20 x 15 m box building centred at the origin on a ground plane
+    z = 0 (two triangles, 400 m square), or the building alone."""
+    tris = scenes._quad((-200.0, -200.0, 0.0), (200.0, -200.0, 0.0), (200.0, 200.0, 0.0), (-200.0, 200.0, 0.0)) \
+        if with_ground else []
+    mats = [ground_mat] * len(tris)
+    b = scenes.box_tris(20.0, 20.0, 15.0)
+    tris += b
+    mats += [building_mat] * len(b)
+    return scenes._static_scene("ground_building", tris, mats, tx, (rx,))
+
+
+def _paths_by_point(keys, paths, slot):
+    """{rounded diffraction point: (amplitude, length)} of combined paths,
+    the diffraction point at pts[slot]."""
+    out = {}
+    for k, p in zip(keys, paths):
+        q = tuple(np.round(p["pts"][slot], 6))
+        out[q] = (complex(p["amp_re"], p["amp_im"]), float(p["len_m"]))
+    return out
+
+
+@pytest.mark.parametrize("building_mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+@pytest.mark.parametrize("tx,rx", [((-40.0, -12.0, 2.0), (35.0, 22.0, 10.0)),    # reflection first
+                                   ((-40.0, -12.0, 6.0), (35.0, 22.0, 2.0))])    # reflection last
+def test_reflection_then_diffraction_is_the_image_source_diffracted(oracle_mod, building_mat, tx, rx):
+    """Image theory over a perfectly conducting ground, vertical polarisation:
+    the ground reflection before a wedge (Tx -> P -> Q -> Rx) equals the
+    first-order diffraction of the transmitter's image (no ground), and the
+    reflection after it (Tx -> Q -> P -> Rx) the diffraction toward the
+    receiver's image -- same diffraction points, lengths and amplitudes (the
+    PEC reflection of a vertically polarised field is the image's field)."""
+    O = oracle_mod
+    a = _ground_and_building(scenes.MAT_METAL, building_mat, tx, rx)
+    prm = O.OracleParams(freq_hz=28e9, max_refl=2)
+    wa = a.tris.reshape(-1, 9)
+    keys, paths = O.diffract_refl(wa, a.tri_mat, a.tri_obj, a.materials, a.tx, a.rx[0], prm)
+    first = (keys[:, 3] >= 0) & ((keys[:, 3] & O.DIFF) != 0)          # reflection, then wedge
+    last = (keys[:, 2] >= 0) & ((keys[:, 2] & O.DIFF) != 0)           # wedge, then reflection
+    ground = lambda col: keys[:, col] < 2                             # the ground's two triangles
+    rd = first & ground(2)
+    dr = last & ground(3)
+    assert rd.sum() + dr.sum() >= 2
+    for sel, src, obs, slot in ((rd, (tx[0], tx[1], -tx[2]), rx, 1), (dr, tx, (rx[0], rx[1], -rx[2]), 0)):
+        b = _ground_and_building(scenes.MAT_METAL, building_mat, src, obs, with_ground=False)
+        bk, bp = O.diffract(b.tris.reshape(-1, 9), b.tri_mat, b.tri_obj, b.materials, b.tx, b.rx[0], prm)
+        # the image's diffraction points on the real edges (above the ground)
+        want = {q: v for q, v in _paths_by_point(bk, bp, 0).items() if q[2] > 0.0}
+        got = _paths_by_point(keys[sel], paths[sel], slot)
+        assert set(got) == set(want)
+        for q, (amp, length) in got.items():
+            wa_, wl = want[q]
+            assert abs(length - wl) <= 1e-9 * wl
+            assert abs(amp - wa_) <= 1e-9 * abs(wa_)
+
+
+def test_reflection_diffraction_reciprocity(oracle_mod):
+    """Perfect conductors everywhere (reciprocal face factors): swapping Tx and
+    Rx turns each reflection-then-wedge path into the wedge-then-reflection
+    path with the same triangle, wedge, length and amplitude."""
+    O = oracle_mod
+    tx, rx = (-40.0, -12.0, 6.0), (35.0, 22.0, 2.0)
+    prm = O.OracleParams(freq_hz=28e9, max_refl=2)
+    out = []
+    for t, r in ((tx, rx), (rx, tx)):
+        sc = _ground_and_building(scenes.MAT_METAL, scenes.MAT_METAL, t, r)
+        k, p = O.diffract_refl(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)
+        out.append({tuple(kk[2:4].tolist()): (complex(pp["amp_re"], pp["amp_im"]), float(pp["len_m"]))
+                    for kk, pp in zip(k, p)})
+    fwd, back = out
+    assert len(fwd) >= 2 and len(fwd) == len(back)
+    for (i0, i1), (amp, length) in fwd.items():
+        amp2, len2 = back[(i1, i0)]
+        assert abs(length - len2) <= 1e-9 * length
+        assert abs(amp - amp2) <= 1e-9 * abs(amp)
