@@ -1091,10 +1091,11 @@ def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
             torch.empty(nrx, dtype=torch.float64, device=dev),
             torch.empty(max_paths * C.sizeof(dcem.Path), dtype=torch.uint8, device=dev)]
     out = {}
-    for on in (True, False):
+    for on in ("refl", True, False):
         s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
         s.set_rays(rays)
-        nw = s.set_diffraction(on)
+        nw = s.set_diffraction(bool(on))
+        nrp = s.set_diffraction_reflections(True) if on == "refl" else 0
         prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=dcem.MODE_COHERENT)
         res = dcem.Result()
         res.ptr_kind = dcem.PTR_DEVICE
@@ -1117,12 +1118,20 @@ def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
                 if on:
                     n = min(res.n_paths, max_paths)
                     p = bufs[3][: n * C.sizeof(dcem.Path)].cpu().numpy().view(dcem.PATH_DTYPE)
-                    nd.append(int(np.sum((p["tri"][:, 0] & dcem.TRI_DIFFRACT) != 0)))
+                    first = (p["depth"] == 1) & ((p["tri"][:, 0] & dcem.TRI_DIFFRACT) != 0)
+                    comb = (p["depth"] == 2) & ((((p["tri"][:, 0] | p["tri"][:, 1]) & dcem.TRI_DIFFRACT)) != 0)
+                    nd.append((int(first.sum()), int(comb.sum())))
         s.close()
         t = max_over_ranks([sum(ms) / 1e3], dev)[0]
-        if on:
+        if on == "refl":
+            out["with_one_reflection"] = {
+                "reflector_planes": nrp, "frames_per_s": round(world * K / t, 2), "ms_per_frame": round(1e3 * t / K, 4),
+                "combined_paths_per_frame": round(float(np.mean([x[1] for x in nd])), 1),
+                "candidates_per_frame": nw * nrx * nrp * 2,
+                "note": "first-order diffraction plus one reflection on a static plane before or after it"}
+        elif on:
             out.update({"wedges": nw, "frames_per_s": round(world * K / t, 2), "ms_per_frame": round(1e3 * t / K, 4),
-                        "diffraction_paths_per_frame": round(float(np.mean(nd)), 1),
+                        "diffraction_paths_per_frame": round(float(np.mean([x[0] for x in nd])), 1),
                         "receiver_wedge_pairs_per_frame": nw * nrx})
         else:
             out["without_diffraction_frames_per_s"] = round(world * K / t, 2)

@@ -310,6 +310,26 @@ int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nma
  * DCEM_ERR_ARG, DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
 
+/* With diffraction on: one reflection before or after the diffraction (Sec.
+ * III steps 3-5 combined). on = 1 groups the static triangles into
+ * reflector planes once (triangles whose unit normals and offsets agree to
+ * 1e-7 and 1e-4 m; normals oriented so that their first nonzero component is
+ * positive). Every frame then adds, for each (link, wedge, reflector plane),
+ * the path Tx -> P -> Q -> Rx, the diffraction of the transmitter's image in
+ * the plane, and the path Tx -> Q -> P -> Rx, the diffraction toward the
+ * receiver's image (image theory), with Q on the edge by Keller's law for
+ * that image, the receiver (or its image) beyond the incident shadow boundary
+ * of the transmitter (or its image), P inside a triangle of the plane (the
+ * image is then taken in that triangle's own plane) and the three legs
+ * unoccluded; field: the UTD coefficient with the image's distances and the
+ * Fresnel reflection at P. Record: depth 2, tri = {P's triangle id,
+ * wedge | DCEM_TRI_DIFFRACT} or {wedge | DCEM_TRI_DIFFRACT, triangle id},
+ * pts = the two points in path order, ray = -1. on = 0 turns it off.
+ * *n_planes (may be NULL): the reflector-plane count. Cost: one pre-test
+ * thread per (link, wedge, plane, order) per frame. Errors: DCEM_ERR_ARG,
+ * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
+int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes);
+
 /* Closest-hit kernel configuration. Results never depend on it (closest hit
  * and lowest-id ties are decided by the triangle test alone):
  *   kernel  -1 automatic (default: 1 when the compact copy and the stacks fit

@@ -245,6 +245,10 @@ struct dcem_scene {
   int nw = 0;
   bool diffraction = false;
   unsigned long long* dsurv = nullptr;  // diffraction: pre-test survivor list
+  RPlane* rplanes = nullptr;   // diffraction combined with a reflection: reflector planes
+  int* rmembers = nullptr;     // ... and their triangle ids
+  int nrp = 0;
+  bool diff_refl = false;
   unsigned dsurv_cap = 0;
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
   int* g_param = nullptr;      // staged outputs and the error flag (dcem_path_gradients)
@@ -381,6 +385,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo); dfree(s->dsurv);
+  dfree(s->rplanes); dfree(s->rmembers);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx); dfree(s->g_theta);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
@@ -687,6 +692,73 @@ std::vector<WedgeTopo> find_wedges(const std::vector<float>& tris, const std::ve
     return x.ta != y.ta ? x.ta < y.ta : x.tb < y.tb;
   });
   return out;
+}
+
+// Reflector planes: the static triangles grouped by plane (unit normal
+// oriented with its first nonzero component positive, offset c = n . v0),
+// planes equal when the normals agree to 1e-7 and the offsets to 1e-4 m.
+void group_planes(const std::vector<float>& tris, const std::vector<int>& tri_obj, std::vector<RPlane>& planes,
+                  std::vector<int>& members) {
+  struct Item {
+    double n[3], c;
+    int id;
+  };
+  std::vector<Item> it;
+  const int ntri = (int)tri_obj.size();
+  for (int i = 0; i < ntri; ++i) {
+    if (tri_obj[i] >= 0) continue;
+    const float* v = &tris[9 * (size_t)i];
+    double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+    double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(len > 0.0)) continue;
+    for (double& x : n) x /= len;
+    double sg = n[0] != 0.0 ? n[0] : (n[1] != 0.0 ? n[1] : n[2]);
+    if (sg < 0.0)
+      for (double& x : n) x = -x;
+    Item q;
+    for (int k = 0; k < 3; ++k) q.n[k] = n[k];
+    q.c = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+    q.id = i;
+    it.push_back(q);
+  }
+  auto key = [](const Item& q, int k) {
+    return k < 3 ? std::llround(q.n[k] * 1e7) : std::llround(q.c * 1e4);
+  };
+  std::sort(it.begin(), it.end(), [&](const Item& a, const Item& b) {
+    for (int k = 0; k < 4; ++k) {
+      long long x = key(a, k), y = key(b, k);
+      if (x != y) return x < y;
+    }
+    return a.id < b.id;
+  });
+  for (size_t i = 0; i < it.size();) {
+    size_t j = i + 1;
+    while (j < it.size() && key(it[j], 0) == key(it[i], 0) && key(it[j], 1) == key(it[i], 1) &&
+           key(it[j], 2) == key(it[i], 2) && key(it[j], 3) == key(it[i], 3))
+      ++j;
+    RPlane p;
+    for (int k = 0; k < 3; ++k) p.n[k] = it[i].n[k];
+    p.c = it[i].c;
+    p.first = (int)members.size();
+    p.count = (int)(j - i);
+    for (int k = 0; k < 3; ++k) {
+      p.box[k] = 3.4e38f;
+      p.box[k + 3] = -3.4e38f;
+    }
+    for (size_t q = i; q < j; ++q) {
+      members.push_back(it[q].id);
+      const float* v = &tris[9 * (size_t)it[q].id];
+      for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 3; ++k) {
+          p.box[k] = std::min(p.box[k], v[3 * c + k]);
+          p.box[k + 3] = std::max(p.box[k + 3], v[3 * c + k]);
+        }
+    }
+    planes.push_back(p);
+    i = j;
+  }
 }
 
 bool same_traversal(const dcem_params& a, const dcem_params& b) {
@@ -1155,6 +1227,26 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
   return DCEM_OK;
 }
 
+int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes) {
+  if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
+  if (on && !s->diffraction) return DCEM_ERR_STATE;
+  if (on && !s->rplanes) {
+    std::vector<RPlane> planes;
+    std::vector<int> members;
+    group_planes(s->tris_h, s->tri_obj_h, planes, members);
+    s->nrp = (int)planes.size();
+    if (s->nrp) {
+      CK(dalloc(&s->rplanes, planes.size()));
+      CK(dalloc(&s->rmembers, members.size()));
+      CK(cudaMemcpy(s->rplanes, planes.data(), sizeof(RPlane) * planes.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(s->rmembers, members.data(), sizeof(int) * members.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  s->diff_refl = on != 0;
+  if (n_planes) *n_planes = s->nrp;
+  return DCEM_OK;
+}
+
 int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on) {
   if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
   s->use_graphs = on != 0;
@@ -1394,6 +1486,10 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.nw = s->nw;
   q.dsurv = s->dsurv;
   q.dsurv_cap = s->dsurv_cap;
+  const bool dr = q.wedges && s->diff_refl && s->nrp > 0;
+  q.rplanes = dr ? s->rplanes : nullptr;
+  q.rmembers = dr ? s->rmembers : nullptr;
+  q.nrp = dr ? s->nrp : 0;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
   P.sticky = p->mode == DCEM_MODE_STICKY;
@@ -1579,7 +1675,7 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
                  (P.q.vc_next_key ? 1 : 0) +
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
-                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0);
+                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) + (P.q.rplanes && P.nlinks > 0 ? 1 : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -2100,7 +2196,8 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
       s->last_use_q = 3;  // every scene's rays in one launch
       s->launches += 2 + (coh[i] ? 2 : 0) + (s->R > 0 ? 1 : 0) + 5 + (nrx[i] > 0 ? 1 : 0) +
                      (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
-                     (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) + (i == 0 ? 1 : 0);
+                     (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
+                     (P.q.rplanes && P.nlinks > 0 ? 1 : 0) + (i == 0 ? 1 : 0);
       s->graph_replayed = 0;
       b->h_tab[i] = frame_trace_args(P);
     }

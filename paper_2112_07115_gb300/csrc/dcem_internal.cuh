@@ -33,6 +33,15 @@ struct Wedge {
   int ta, tb;
 };
 
+// A reflector plane for diffraction combined with a reflection: a maximal
+// group of coplanar static triangles (unit normal n, offset c = n . x), the
+// box of its triangles and their ids (members[first .. first + count)).
+struct RPlane {
+  double n[3], c;
+  float box[6];
+  int first, count;
+};
+
 // Wedge topology (fixed for a rigid object): faces ta < tb, the local
 // indices of the edge's vertices in ta and of the faces' third vertices.
 struct WedgeTopo {
@@ -616,9 +625,9 @@ __device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, 
   return slot_best;
 }
 
-// Any hit with t in (t0, t1), excluding ids ex0 and ex1 (occlusion test).
+// Any hit with t in (t0, t1), excluding ids ex0, ex1 and ex2 (occlusion test).
 __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t0, float t1,
-                                        int ex0, int ex1, unsigned& overflow, TStack& st) {
+                                        int ex0, int ex1, unsigned& overflow, TStack& st, int ex2 = -1) {
   st.reset();
   if (bvh.root1 != kEmpty) st.push(bvh.root1);
   int cur = bvh.root0;
@@ -654,7 +663,7 @@ __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t
       int id;
       load_tri(bvh.tris, DCEM_IDX(~cur, bvh.ntris), v0, v1, v2, id);
       float t;
-      if (id != ex0 && id != ex1 && tri_hit(r, v0, v1, v2, t) && t > t0 && t < t1) return true;
+      if (id != ex0 && id != ex1 && id != ex2 && tri_hit(r, v0, v1, v2, t) && t > t0 && t < t1) return true;
       cur = kEmpty;
     }
   }

@@ -873,12 +873,13 @@ __device__ __forceinline__ bool diffract_candidate(const Wedge& W, float4 txv, f
   return true;
 }
 
-// FP32 any-hit of the open segment a -> b, the two wedge faces excluded.
+// FP32 any-hit of the open segment a -> b, the wedge faces (and a reflecting
+// triangle) excluded.
 __device__ __forceinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, unsigned& ovf,
-                                             TStack& st) {
+                                             TStack& st, int ex2 = -1) {
   d3w dv = q - p;
   RayPre rp = ray_pre(f3((float)p.x, (float)p.y, (float)p.z), f3((float)dv.x, (float)dv.y, (float)dv.z));
-  return any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st);
+  return any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex0, ex1, ovf, st, ex2);
 }
 
 // Wedge geometry from the current world triangles (moving objects' wedges
@@ -1017,6 +1018,280 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   atomicAdd(&a.ctr->n_valid, 1u);
 }
 
+// ---------------------------------------------------------------------------
+// one reflection before or after a diffraction (Sec. III steps 3-5)
+// ---------------------------------------------------------------------------
+// By image theory a reflection on plane (n, c) before the wedge is the
+// diffraction of the transmitter's image, a reflection after it the
+// diffraction toward the receiver's image; the reflection point is where the
+// unfolded leg (image -> Q, or Q -> image) crosses the plane. Candidates are
+// (link, wedge, reflector plane, order); survivors of the FP32 pre-test carry
+// bit 63 in the survivor list: ((link * nw + wedge) * nrp + plane) * 2 + first.
+constexpr unsigned long long kReflTag = 1ull << 63;
+
+__device__ __forceinline__ float3 mirror32(float3 x, float3 n, float c) {
+  float h = 2.0f * (fdot3(n, x) - c);
+  return f3(x.x - h * n.x, x.y - h * n.y, x.z - h * n.z);
+}
+
+// FP32 pre-test: false only when the FP64 test rejects the candidate too
+// (Keller point and angles as diffract_candidate with the image; the
+// reflection point off the plane's box by more than 5 cm + 1e-4 of the
+// distances, or off the unfolded leg).
+__device__ __forceinline__ bool diffract_refl_candidate(const Wedge& W, const RPlane& P, float4 txv, float4 rxv,
+                                                        bool first) {
+  const float3 n = f3((float)P.n[0], (float)P.n[1], (float)P.n[2]);
+  const float c = (float)P.c;
+  float3 T = f3(txv.x, txv.y, txv.z), R = f3(rxv.x, rxv.y, rxv.z);
+  float3 S = first ? mirror32(T, n, c) : T, O = first ? R : mirror32(R, n, c);
+  if (!diffract_candidate(W, make_float4(S.x, S.y, S.z, 0.0f), make_float4(O.x, O.y, O.z, 0.0f))) return false;
+  float3 e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
+  float3 p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+  float3 dt = f3(S.x - p0.x, S.y - p0.y, S.z - p0.z), dr = f3(O.x - p0.x, O.y - p0.y, O.z - p0.z);
+  float zt = fdot3(dt, e), zr = fdot3(dr, e);
+  float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
+  float3 pr = f3(dr.x - e.x * zr, dr.y - e.y * zr, dr.z - e.z * zr);
+  float rt = sqrtf(fdot3(pt, pt)), rr = sqrtf(fdot3(pr, pr));
+  if (!(rt > 1e-3f && rr > 1e-3f)) return true;
+  float zq = zt + (zr - zt) * rt / (rt + rr);
+  float3 Q = f3(p0.x + e.x * zq, p0.y + e.y * zq, p0.z + e.z * zq);
+  float3 a0 = first ? S : Q, a1 = first ? Q : O;
+  float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
+  float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
+  if (!(fabsf(den) > 1e-6f * len)) return true;
+  float t = (c - fdot3(n, a0)) / den;
+  float mt = (0.05f + 1e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
+  if (t < -mt || t > 1.0f + mt) return false;
+  float3 X = f3(a0.x + t * dv.x, a0.y + t * dv.y, a0.z + t * dv.z);
+  float mb = 0.05f + 1e-4f * (len + sqrtf(fdot3(X, X)));
+  if (X.x < P.box[0] - mb || X.y < P.box[1] - mb || X.z < P.box[2] - mb || X.x > P.box[3] + mb ||
+      X.y > P.box[4] + mb || X.z > P.box[5] + mb)
+    return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_diffract_refl_pre(PathArgs a, int nlinks) {
+  const long total = (long)nlinks * a.nw * a.nrp * 2;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long idx = base + lane;
+    bool keep = false;
+    if (idx < total) {
+      long r = idx >> 1;
+      int p = (int)(r % a.nrp);
+      r /= a.nrp;
+      int w = (int)(r % a.nw), link = (int)(r / a.nw);
+      keep = diffract_refl_candidate(a.wedges[w], a.rplanes[p], a.txs[link / a.nrx], a.rx[link % a.nrx],
+                                     (idx & 1) != 0);
+    }
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & ((1u << lane) - 1u));
+    if (keep) {
+      if (at < a.dsurv_cap) a.dsurv[at] = kReflTag | (unsigned long long)idx;
+      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+    }
+  }
+}
+
+// Image, Keller point and reflection point for plane (n, c): false when the
+// Keller point leaves the edge, an angle falls inside the wedge, the shadow
+// rule fails or the reflection point leaves the unfolded leg.
+struct ReflGeom {
+  d3w S, O, Q, P;  // source (or image), observer (or image), diffraction and reflection points
+  double phip, phi;
+};
+__device__ __forceinline__ bool refl_geometry(const Wedge& W, d3w n, double c, d3w T, d3w R, bool first,
+                                              ReflGeom& g) {
+  g.S = first ? T - n * (2.0 * (dotw(n, T) - c)) : T;
+  g.O = first ? R : R - n * (2.0 * (dotw(n, R) - c));
+  d3w e = D3(W.e[0], W.e[1], W.e[2]), p0 = D3(W.p0[0], W.p0[1], W.p0[2]);
+  d3w dt = g.S - p0, dr = g.O - p0;
+  double zt = dotw(dt, e), zr = dotw(dr, e);
+  d3w pt = dt - e * zt, pr = dr - e * zr;
+  double rt = sqrt(dotw(pt, pt)), rr = sqrt(dotw(pr, pr));
+  if (!(rt > 0.0 && rr > 0.0)) return false;
+  double zq = zt + (zr - zt) * rt / (rt + rr);
+  double uq = zq / W.len;
+  if (!(uq > 0.0 && uq < 1.0)) return false;
+  g.Q = p0 + e * zq;
+  g.phip = wedge_angle(W, g.S);
+  g.phi = wedge_angle(W, g.O);
+  if (g.phip > W.n * M_PI || g.phi > W.n * M_PI) return false;
+  if (!(fabs(g.phi - g.phip) > M_PI)) return false;
+  d3w a0 = first ? g.S : g.Q, a1 = first ? g.Q : g.O;
+  double den = dotw(n, a1 - a0);
+  if (den == 0.0) return false;
+  double t = (c - dotw(n, a0)) / den;
+  if (!(t > 0.0 && t < 1.0)) return false;
+  g.P = a0 + (a1 - a0) * t;
+  return true;
+}
+
+// Triangle slot geometry: vertices and the (unnormalised) normal.
+__device__ __forceinline__ void tri64(const PathArgs& a, int id, d3w& v0, d3w& v1, d3w& v2, float4& mat) {
+  const float4* tp = a.tris + 3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(id, a.bvh.ntris)], a.bvh.ntris);
+  float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+  v0 = D3(p0.x, p0.y, p0.z);
+  v1 = D3(p1.x, p1.y, p1.z);
+  v2 = D3(p2.x, p2.y, p2.z);
+  mat = a.mats[__float_as_int(p1.w)];
+}
+
+__device__ __forceinline__ bool inside_tri64(d3w v0, d3w v1, d3w v2, d3w x) {
+  d3w n = crossw(v1 - v0, v2 - v0);
+  return !(dotw(crossw(v1 - v0, x - v0), n) < 0.0 || dotw(crossw(v2 - v1, x - v1), n) < 0.0 ||
+           dotw(crossw(v0 - v2, x - v2), n) < 0.0);
+}
+
+struct zv3 {
+  zd x, y, z;
+};
+__device__ __forceinline__ zd zvdot(zv3 E, d3w v) { return E.x * v.x + E.y * v.y + E.z * v.z; }
+
+// One survivor: exact geometry on the plane, the member triangle holding the
+// reflection point, the geometry again on that triangle's own plane, the
+// three legs, then the UTD field with the Fresnel reflection at P (bounce
+// basis as in k_val_field) and the path record (depth 2).
+__device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned long long code, double k,
+                                                   double lam, unsigned& ovf, TStack& st) {
+  const bool first = (code & 1ull) != 0;
+  code >>= 1;
+  const int p = (int)(code % (unsigned long long)a.nrp);
+  code /= (unsigned long long)a.nrp;
+  const int w = (int)(code % (unsigned long long)a.nw), link = (int)(code / (unsigned long long)a.nw);
+  const Wedge W = a.wedges[w];
+  const RPlane Pl = a.rplanes[p];
+  float4 rxv = a.rx[link % a.nrx], txv = a.txs[link / a.nrx];
+  d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
+  ReflGeom g;
+  if (!refl_geometry(W, D3(Pl.n[0], Pl.n[1], Pl.n[2]), Pl.c, T, R, first, g)) return;
+  int j = -1;
+  d3w v0, v1, v2;
+  float4 mj;
+  for (int q = 0; q < Pl.count && j < 0; ++q) {
+    int id = a.rmembers[Pl.first + q];
+    if (id == W.ta || id == W.tb) continue;
+    tri64(a, id, v0, v1, v2, mj);
+    if (inside_tri64(v0, v1, v2, g.P)) j = id;
+  }
+  if (j < 0) return;
+  // the member's own plane
+  d3w nj = unitw(crossw(v1 - v0, v2 - v0));
+  if (!refl_geometry(W, nj, dotw(nj, v0), T, R, first, g)) return;
+  if (!inside_tri64(v0, v1, v2, g.P)) return;
+  const d3w Q = g.Q, Pp = g.P;
+  if (first) {
+    if (leg_occluded(a, T, Pp, j, j, ovf, st) || leg_occluded(a, Pp, Q, j, W.ta, ovf, st, W.tb) ||
+        leg_occluded(a, Q, R, W.ta, W.tb, ovf, st))
+      return;
+  } else {
+    if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, Pp, j, W.ta, ovf, st, W.tb) ||
+        leg_occluded(a, Pp, R, j, j, ovf, st))
+      return;
+  }
+  unsigned fl = 0;
+  const double n = W.n, phip = g.phip, phi = g.phi;
+  d3w e = D3(W.e[0], W.e[1], W.e[2]);
+  d3w qs = Q - g.S, oq = g.O - Q;
+  double sp = sqrt(dotw(qs, qs)), s = sqrt(dotw(oq, oq));
+  d3w ip = qs * (1.0 / sp), dd = oq * (1.0 / s);
+  double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
+  double sb = sin(beta0);
+  double L = s * sp * sb * sb / (s + sp);
+  d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
+  d3w bp = crossw(ip, php), bd = crossw(dd, ph);
+  float4 ma, mb;
+  {
+    d3w x0, x1, x2;
+    tri64(a, W.ta, x0, x1, x2, ma);
+    tri64(a, W.tb, x0, x1, x2, mb);
+  }
+  zd r0s, r0h, rns, rnh;
+  fresnel_d(ma, a.freq, fabs(sin(phip)), r0s, r0h);
+  fresnel_d(mb, a.freq, fabs(sin(n * M_PI - phi)), rns, rnh);
+  const UtdParts up = utd_parts(n, phi, phip, beta0, L, k, fl);
+  zd Ds = utd_coeff(up, r0s, rns);
+  zd Dh = utd_coeff(up, r0h, rnh);
+  // the reflection at P: directions and bounce basis
+  d3w din = first ? unitw(Pp - T) : dd;
+  d3w dout = first ? ip : unitw(R - Pp);
+  double ct = fabs(dotw(din, nj));
+  d3w sv = crossw(din, nj);
+  double sn_ = sqrt(dotw(sv, sv));
+  if (sn_ < 1e-12) {
+    d3w ax = fabs(nj.x) < 0.9 ? D3(1, 0, 0) : D3(0, 1, 0);
+    sv = unitw(crossw(nj, ax));
+  } else {
+    sv = sv * (1.0 / sn_);
+  }
+  d3w pin = crossw(sv, din), pout = crossw(sv, dout);
+  zd gte, gtm;
+  fresnel_d(mj, a.freq, ct, gte, gtm);
+  d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
+  double sn, cs;
+  sincos(-k * sp, &sn, &cs);
+  zd Ei = Z(cs / sp, sn / sp);
+  sincos(-k * s, &sn, &cs);
+  zd A = Z(cs, sn) * sqrt(sp / (s * (s + sp)));
+  zd proj;
+  if (first) {
+    d3w e0 = polw(u, din, fl);
+    zd es = Z(dotw(e0, sv)), ep = Z(dotw(e0, pin));
+    zd ts = gte * es, tp = gtm * ep;
+    zv3 E1 = {ts * sv.x + tp * pout.x, ts * sv.y + tp * pout.y, ts * sv.z + tp * pout.z};
+    zd Eb = Ei * zvdot(E1, bp), Ep = Ei * zvdot(E1, php);
+    d3w prx = polw(u, dd * -1.0, fl);
+    proj = (Ds * Eb) * (-dotw(bd, prx)) + (Dh * Ep) * (-dotw(ph, prx));
+  } else {
+    d3w e0 = polw(u, ip, fl);
+    zd Eb = Ei * dotw(e0, bp), Ep = Ei * dotw(e0, php);
+    zd cb = (Ds * Eb) * -1.0, cp = (Dh * Ep) * -1.0;
+    zv3 Ed = {cb * bd.x + cp * ph.x, cb * bd.y + cp * ph.y, cb * bd.z + cp * ph.z};
+    zd ts = gte * zvdot(Ed, sv), tp = gtm * zvdot(Ed, pin);
+    zv3 E2 = {ts * sv.x + tp * pout.x, ts * sv.y + tp * pout.y, ts * sv.z + tp * pout.z};
+    d3w prx = polw(u, dout * -1.0, fl);
+    proj = zvdot(E2, prx);
+  }
+  zd amp = proj * A * (lam / (4.0 * M_PI));
+  unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
+  if (uu >= a.ucap) {
+    atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
+    return;
+  }
+  PathRec rec;
+  const int id0 = first ? j : (w | kDiffBit), id1 = first ? (w | kDiffBit) : j;
+  rec.key = seq_key(link % a.nrx, 2, [&](int q) { return q == 0 ? id0 : id1; });
+  rec.rx = link;
+  rec.depth = 2;
+  rec.ray = -1;
+  rec.flags = fl;
+  rec.valid = 1;
+  rec.pad = 0;
+  rec.len = sp + s;
+  rec.amp_re = amp.re;
+  rec.amp_im = amp.im;
+  for (int q = 0; q < kMaxRefl; ++q) {
+    rec.tri[q] = q == 0 ? id0 : q == 1 ? id1 : -1;
+    rec.pts[q][0] = rec.pts[q][1] = rec.pts[q][2] = 0.0f;
+  }
+  const d3w x0 = first ? Pp : Q, x1 = first ? Q : Pp;
+  rec.pts[0][0] = (float)x0.x;
+  rec.pts[0][1] = (float)x0.y;
+  rec.pts[0][2] = (float)x0.z;
+  rec.pts[1][0] = (float)x1.x;
+  rec.pts[1][1] = (float)x1.y;
+  rec.pts[1][2] = (float)x1.z;
+  a.prec[uu] = rec;
+  unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
+  if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
+  else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+  atomicAdd(&a.ctr->n_valid, 1u);
+}
+
 // Pass 1 over every (link, wedge) pair: the FP32 pre-test rejects most of
 // them; the survivors' indices go to a list (one atomic per warp).
 __global__ void __launch_bounds__(256) k_diffract_pre(PathArgs a, int nlinks) {
@@ -1054,8 +1329,11 @@ __global__ void __launch_bounds__(32) k_diffract(PathArgs a) {
   const unsigned n = min(a.ctr->n_dsurv, a.dsurv_cap);
   const double k = 2.0 * M_PI * a.freq / 299792458.0, lam = 299792458.0 / a.freq;
   unsigned ovf = 0;
-  for (unsigned i = blockIdx.x + gridDim.x * threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    diffract_pair(a, (long)a.dsurv[i], k, lam, ovf, st);
+  for (unsigned i = blockIdx.x + gridDim.x * threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long c = a.dsurv[i];
+    if (c & kReflTag) diffract_refl_pair(a, c & ~kReflTag, k, lam, ovf, st);
+    else diffract_pair(a, (long)c, k, lam, ovf, st);
+  }
   if (ovf) {
     atomicAdd(&a.ctr->stack_overflow, 1u);
     atomicOr(&a.ctr->err, ERR_STACK);
@@ -1207,6 +1485,11 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
     long total = (long)nlinks * a.nw;
     long g = std::min<long>((total + 255) / 256, 8L * sms);
     k_diffract_pre<<<(int)std::max<long>(g, 1), 256, 0, st>>>(a, nlinks);
+    if (a.rplanes && a.nrp > 0) {
+      long tr = (long)nlinks * a.nw * a.nrp * 2;
+      long gr = std::min<long>((tr + 255) / 256, 8L * sms);
+      k_diffract_refl_pre<<<(int)std::max<long>(gr, 1), 256, 0, st>>>(a, nlinks);
+    }
     k_diffract<<<sms, 32, 32 * kStackTrace * sizeof(int), st>>>(a);
   }
   return cudaGetLastError();

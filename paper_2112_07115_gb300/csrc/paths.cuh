@@ -54,6 +54,11 @@ struct PathArgs {
   int nw;
   unsigned long long* dsurv;      // (link, wedge) pair indices past the FP32 pre-test
   unsigned dsurv_cap;
+  // one reflection before or after a diffraction (null: off): reflector
+  // planes and their member triangle ids
+  const RPlane* rplanes;
+  const int* rmembers;
+  int nrp;
   // validation reuse (coherent frames; Sec. III "Propagation path caching"):
   // the previous frame's records of its distinct keys, found through a hash
   // table of their link keys, are copied when nothing they depend on moved

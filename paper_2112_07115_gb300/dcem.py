@@ -40,7 +40,7 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
             "dcem_scene_set_trace_config", "dcem_scene_autotune", "dcem_batch_create",
             "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy",
-            "dcem_scene_set_transmission", "dcem_scene_set_diffraction"]
+            "dcem_scene_set_transmission", "dcem_scene_set_diffraction", "dcem_scene_set_diffraction_reflections"]
 
 
 class Material(C.Structure):
@@ -115,6 +115,7 @@ def lib():
         L.dcem_scene_set_trace_config.argtypes = [vp, i32, i32, i32]
         L.dcem_scene_set_transmission.argtypes = [vp, vp, i32, i32]
         L.dcem_scene_set_diffraction.argtypes = [vp, i32, P(i32)]
+        L.dcem_scene_set_diffraction_reflections.argtypes = [vp, i32, P(i32)]
         L.dcem_batch_create.argtypes = [vp, i32, vp, P(vp)]
         L.dcem_batch_update_transforms.argtypes = [vp, vp, i32]
         L.dcem_batch_trace.argtypes = [vp, vp, vp, vp, vp, i32, P(Params), vp, P(i32)]
@@ -566,6 +567,14 @@ class Scene:
     def set_diffraction(self, on: bool = True) -> int:
         """First-order edge diffraction paths (UTD); returns the wedge count."""
         return dcem_scene_set_diffraction(self.h, on)
+
+    def set_diffraction_reflections(self, on: bool = True) -> int:
+        """With diffraction on: one reflection on a static reflector plane
+        before or after the diffraction; returns the reflector-plane count."""
+        n = C.c_int32(0)
+        _check(lib().dcem_scene_set_diffraction_reflections(self.h, int(bool(on)), C.byref(n)),
+               "dcem_scene_set_diffraction_reflections")
+        return int(n.value)
 
     def set_trace_config(self, kernel: int, block: int = 256, stack: int = 24):
         dcem_scene_set_trace_config(self.h, kernel, block, stack)
