@@ -555,13 +555,14 @@ int dcem_path_adjoint(dcem_scene* s, const float* tx, const float* rx, int32_t n
  * address (cudaGetSymbolAddress) and the kernels' attributes with that device
  * current. A CUDA runtime that loads modules lazily (the default) loads this
  * call's kernels and reserves the scratch array at that moment, which may
- * allocate device memory; so make one set-up call per device at start-up,
- * before any stream capture: n_paths = 0 and nrx = 0 (paths may be NULL)
- * does the set-up and nothing else. Calls after it allocate nothing.
+ * allocate device memory; so make one set-up call per device at start-up:
+ * n_paths = 0 and nrx = 0 (paths may be NULL) does the set-up and nothing
+ * else. Calls after it allocate nothing.
  * Every call on a device shares the one scratch array and clears what it
  * needs at its start: calls whose work overlaps on the GPU (for instance on
  * two streams) race, so order them. The call synchronises `stream` before
- * returning, to report device-side errors.
+ * returning, to report device-side errors, so it cannot be recorded into a
+ * CUDA graph (no call of it may run while `stream` is capturing).
  * Errors: DCEM_ERR_ARG (null or negative arguments, records but no
  * receivers, a receiver index out of range), DCEM_ERR_CAPACITY,
  * DCEM_ERR_CUDA. */
