@@ -787,8 +787,13 @@ static int point_in_tri(const otri* T, v3 p) {
 
 /* Occlusion of the open sub-segment a->b by any triangle except ex0/ex1.
  * Parameter range (eps_occ, 1-eps_occ). Returns 1 if occluded. */
-static int occluded3(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, const or_params* P,
+static int occluded4(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, int ex3, const or_params* P,
                      double scale, uint32_t* fl);
+
+static int occluded3(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, const or_params* P,
+                     double scale, uint32_t* fl) {
+  return occluded4(S, a, b, ex0, ex1, ex2, ex2, P, scale, fl);
+}
 
 static int occluded(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_params* P,
                     double scale, uint32_t* fl) {
@@ -796,8 +801,8 @@ static int occluded(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_para
 }
 
 /* Is the open segment a-b (its first and last eps_occ trimmed) blocked by a
- * triangle other than ex0, ex1, ex2? Flags decisions within the FP32 margin. */
-static int occluded3(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, const or_params* P,
+ * triangle other than ex0 .. ex3? Flags decisions within the FP32 margin. */
+static int occluded4(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, int ex3, const or_params* P,
                      double scale, uint32_t* fl) {
   v3 dv = sub(b, a);
   double len = norm(dv);
@@ -806,7 +811,7 @@ static int occluded3(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, con
   double base = P->edge_eps * scale;
   int occ = 0;
   for (int j = 0; j < S->ntri; ++j) {
-    if (j == ex0 || j == ex1 || j == ex2) continue;
+    if (j == ex0 || j == ex1 || j == ex2 || j == ex3) continue;
     xinfo x;
     ray_tri(&S->t[j], a, d, base, P->edge_eps, &x);
     if (isnan(x.t)) continue;
@@ -1496,6 +1501,283 @@ int64_t or_diffract_refl(const float* tris, const int32_t* tri_mat, const int32_
         }
       }
     }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diffraction of order 2 and 3 (Sec. III step 5; the paper's bound is 3)    */
+/* ------------------------------------------------------------------------ */
+#define OR_GRAZE 1e-6  /* a leg between two wedges closer than this to a face (rad) grazes it */
+
+/* Unfolded length of T -> Q_1 .. Q_m -> R with Q_i = p0_i + t_i e_i. */
+static double chain_length(const owedge* const* E, int m, v3 T, v3 R, const double* t) {
+  v3 prev = T;
+  double L = 0.0;
+  for (int i = 0; i < m; ++i) {
+    v3 q = add(E[i]->p0, scl(E[i]->e, t[i]));
+    L += norm(sub(q, prev));
+    prev = q;
+  }
+  return L + norm(sub(R, prev));
+}
+
+/* Solves the m x m system H x = b (m <= 3) by Gaussian elimination with
+ * partial pivoting; 0 when H is singular. */
+static int solve_small(int m, double H[3][3], double* b, double* x) {
+  double A[3][4];
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[i][j] = H[i][j];
+    A[i][m] = b[i];
+  }
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r) if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (!(fabs(A[piv][c]) > 1e-300)) return 0;
+    if (piv != c) for (int j = 0; j <= m; ++j) { double tmp = A[c][j]; A[c][j] = A[piv][j]; A[piv][j] = tmp; }
+    for (int r = c + 1; r < m; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int j = c; j <= m; ++j) A[r][j] -= f * A[c][j];
+    }
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double v = A[i][m];
+    for (int j = i + 1; j < m; ++j) v -= A[i][j] * x[j];
+    x[i] = v / A[i][i];
+  }
+  return 1;
+}
+
+/* Keller points of a chain of m wedges: the edge parameters t that make the
+ * unfolded length stationary, i.e. at every edge the incident and the
+ * diffracted leg make the same angle with the edge (Keller's law). The
+ * length is a convex function of t (a sum of distances between points
+ * moving linearly with t), so its stationary point is its minimum; it is
+ * found by Newton's method from the edges' midpoints, halving a step that
+ * does not shorten the chain. Returns 1 when converged (gradient, the cosine
+ * mismatch summed over the edge, below 1e-12). */
+static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
+  for (int i = 0; i < m; ++i) t[i] = 0.5 * E[i]->len;
+  double Lc = chain_length(E, m, T, R, t);
+  for (int it = 0; it < 200; ++it) {
+    v3 X[OR_MAX_REFL + 2];
+    X[0] = T;
+    for (int i = 0; i < m; ++i) X[i + 1] = add(E[i]->p0, scl(E[i]->e, t[i]));
+    X[m + 1] = R;
+    double g[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int j = 0; j <= m; ++j) {  /* leg j: X[j] -> X[j+1]; moves with t[j-1] and t[j] */
+      v3 d = sub(X[j + 1], X[j]);
+      double l = norm(d);
+      if (!(l > 0)) return 0;
+      v3 u = scl(d, 1.0 / l);
+      int a = j - 1, b = j;
+      double ca = a >= 0 ? dot(E[a]->e, u) : 0.0, cb = b < m ? dot(E[b]->e, u) : 0.0;
+      if (b < m) { g[b] += cb; H[b][b] += (1.0 - cb * cb) / l; }
+      if (a >= 0) { g[a] -= ca; H[a][a] += (1.0 - ca * ca) / l; }
+      if (a >= 0 && b < m) {
+        double h = -(dot(E[a]->e, E[b]->e) - ca * cb) / l;
+        H[a][b] += h;
+        H[b][a] += h;
+      }
+    }
+    double gmax = 0.0;
+    for (int i = 0; i < m; ++i) gmax = fmax(gmax, fabs(g[i]));
+    if (gmax < 1e-12) return 1;
+    double mg[3] = {-g[0], -g[1], -g[2]}, dx[3];
+    if (!solve_small(m, H, mg, dx)) return 0;
+    double step = 1.0, tn[3];
+    for (int k = 0; k < 60; ++k) {
+      for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
+      double Ln = chain_length(E, m, T, R, tn);
+      if (Ln <= Lc) { Lc = Ln; break; }
+      step *= 0.5;
+    }
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) { dmax = fmax(dmax, fabs(tn[i] - t[i])); t[i] = tn[i]; }
+    if (dmax == 0.0) return gmax < 1e-9;
+  }
+  return 0;
+}
+
+/* Paths Tx -> Q_1 -> ... -> Q_m -> Rx over m pairwise distinct wedges
+ * (m = 2 or 3), consecutive wedges sharing no face. Each Q_i is a Keller
+ * point (keller_points) strictly inside its edge; at every wedge the
+ * previous point (Tx or Q_{i-1}) and the next point (Q_{i+1} or Rx) lie in
+ * the exterior and the next point lies beyond the incident shadow boundary
+ * of the previous one (or_diffract's rule, edge by edge); a leg between two
+ * wedges makes an angle above OR_GRAZE with the faces of both (it does not
+ * run along a face, as between two edges of one planar face); every leg is
+ * unoccluded (the faces of the wedges at its ends excluded). Field: at each
+ * wedge the UTD coefficient of or_diffract (Luebbers' face factors) acts on
+ * the field the previous leg brings, in the edge-fixed bases of that wedge.
+ * The spreading follows Kouyoumjian & Pathak (1974) for a straight edge:
+ * the wave leaving wedge i has one caustic on the edge (radius of curvature
+ * s along phi^) and the other at rho_e behind it (radius rho_e + s along
+ * beta^), rho_e being the incident wavefront's radius of curvature in the
+ * plane of the edge (Euler's formula on the principal radii rho_1, rho_2
+ * along the edge's projection; rho_e = s' for the spherical wave of the
+ * transmitter); the spreading factor is sqrt(rho_e / (s (rho_e + s))) and
+ * the distance parameter L = s (rho_e + s) rho_1 rho_2 sin^2 beta_0 /
+ * (rho_e (rho_1 + s) (rho_2 + s)), which is s s' sin^2 beta_0 / (s + s') for
+ * the spherical wave. Keys: rx, m, w_1 | OR_DIFF, .., w_m | OR_DIFF, -1
+ * padded to 2 + width (width >= m). Returns the number of valid paths (may
+ * exceed cap). */
+int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                          const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                          const or_params* P, int32_t order, int32_t width, int32_t* keys_out,
+                          opath* paths_out, int64_t cap) {
+  if (order < 2 || order > 3 || width < order) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  const int m = order;
+  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
+  const double ang_eps = 1e-9;
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  int64_t nvalid = 0;
+  long w[3] = {0, 0, 0};
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (w[0] = 0; w[0] < nw; ++w[0])
+      for (w[1] = 0; w[1] < nw; ++w[1])
+        for (w[2] = 0; w[2] < (m == 3 ? nw : 1); ++w[2]) {
+          /* pairwise distinct; consecutive wedges share no face */
+          int ok = w[0] != w[1] && (m < 3 || (w[2] != w[0] && w[2] != w[1]));
+          for (int i = 0; ok && i + 1 < m; ++i) {
+            const owedge *A = &W[w[i]], *B = &W[w[i + 1]];
+            if (A->ta == B->ta || A->ta == B->tb || A->tb == B->ta || A->tb == B->tb) ok = 0;
+          }
+          if (!ok) continue;
+          const owedge* E[3] = {&W[w[0]], &W[w[1]], m == 3 ? &W[w[2]] : NULL};
+          /* the transmitter outside the first wedge, the receiver outside the
+           * last (the angles about an edge do not depend on the Keller points;
+           * the same tests are repeated below with the others) */
+          if (wedge_angle(E[0], T) > E[0]->n * M_PI || wedge_angle(E[m - 1], R) > E[m - 1]->n * M_PI) continue;
+          uint32_t fl = 0;
+          double t[3];
+          if (!keller_points(E, m, T, R, t)) continue;
+          v3 X[5];
+          X[0] = T;
+          for (int i = 0; i < m; ++i) X[i + 1] = add(E[i]->p0, scl(E[i]->e, t[i]));
+          X[m + 1] = R;
+          for (int i = 0; ok && i < m; ++i) {
+            double uq = t[i] / E[i]->len;
+            if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+            if (!(uq > 0 && uq < 1)) ok = 0;
+          }
+          double ell[4];
+          for (int j = 0; ok && j <= m; ++j) {
+            ell[j] = norm(sub(X[j + 1], X[j]));
+            if (!(ell[j] > 1e-9)) ok = 0;
+          }
+          if (!ok) continue;
+          /* exterior and shadow rule at every wedge; a leg between two wedges
+           * may not run along a face of either (grazing: within 1e-6 rad) */
+          double phip[3], phi[3];
+          for (int i = 0; ok && i < m; ++i) {
+            phip[i] = wedge_angle(E[i], X[i]);
+            phi[i] = wedge_angle(E[i], X[i + 2]);
+            double nn = E[i]->n;
+            if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) ok = 0;
+            else {
+              if (fabs(fabs(phi[i] - phip[i]) - M_PI) <= ang_eps) fl |= ORF_VAL_PARAM;
+              if (!(fabs(phi[i] - phip[i]) > M_PI)) ok = 0;
+            }
+            for (int q = 0; ok && q < 2; ++q) {
+              if (q == 0 ? i == 0 : i == m - 1) continue;  /* the transmitter's and receiver's legs */
+              double a = q == 0 ? phip[i] : phi[i];
+              double g = fmin(a, nn * M_PI - a);
+              if (fabs(g - OR_GRAZE) <= ang_eps) fl |= ORF_VAL_PARAM;
+              if (!(g > OR_GRAZE)) ok = 0;
+            }
+          }
+          if (!ok) continue;
+          double scale = fmax(maxabs(T), maxabs(R));
+          for (int j = 0; ok && j <= m; ++j) {
+            int e0 = j >= 1 ? E[j - 1]->ta : -1, e1 = j >= 1 ? E[j - 1]->tb : -1;
+            int e2 = j < m ? E[j]->ta : -1, e3 = j < m ? E[j]->tb : -1;
+            if (occluded4(&S, X[j], X[j + 1], e0, e1, e2, e3, P, scale, &fl)) ok = 0;
+          }
+          if (!ok) continue;
+          /* field: transmitter's spherical wave, then wedge by wedge */
+          v3 ip = scl(sub(X[1], X[0]), 1.0 / ell[0]);
+          v3 e0 = pol_dir(u, ip, &fl);
+          double complex Ei = cexp(-I * k * ell[0]) / ell[0];
+          c3 Ev = {Ei * e0.x, Ei * e0.y, Ei * e0.z};
+          double rho1 = ell[0], rho2 = ell[0];
+          v3 dir1 = mk(0, 0, 0), dir2 = mk(0, 0, 0);
+          v3 dd = ip;
+          for (int i = 0; i < m; ++i) {
+            const owedge* Ew = E[i];
+            double s = ell[i + 1];
+            dd = scl(sub(X[i + 2], X[i + 1]), 1.0 / s);
+            double cb = dot(ip, Ew->e);
+            double beta0 = acos(fmax(-1.0, fmin(1.0, cb)));
+            double sb = sin(beta0);
+            v3 php = cross(Ew->e, ip), ph = cross(Ew->e, dd);
+            php = scl(php, -1.0 / norm(php));
+            ph = scl(ph, 1.0 / norm(ph));
+            v3 bp = cross(ip, php), bd = cross(dd, ph);
+            /* incident radius of curvature in the plane of the edge */
+            double rhoe;
+            if (i == 0) rhoe = ell[0];
+            else {
+              double c1 = dot(bp, dir1), c2 = dot(bp, dir2);
+              rhoe = 1.0 / (c1 * c1 / rho1 + c2 * c2 / rho2);
+            }
+            double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
+            int ma = S.t[Ew->ta].mat, mb = S.t[Ew->tb].mat;
+            if (ma < 0 || ma >= S.nmat) ma = 0;
+            if (mb < 0 || mb >= S.nmat) mb = 0;
+            double nn = Ew->n;
+            double complex r0s, r0h, rns, rnh;
+            fresnel(&S.mats[3 * ma], P->freq_hz, fabs(sin(phip[i])), &r0s, &r0h);
+            fresnel(&S.mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - phi[i])), &rns, &rnh);
+            double complex Ds = utd_coeff(nn, phi[i], phip[i], beta0, L, k, r0s, rns, &fl);
+            double complex Dh = utd_coeff(nn, phi[i], phip[i], beta0, L, k, r0h, rnh, &fl);
+            double complex Eb = cdot(Ev, bp), Ep = cdot(Ev, php);
+            double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);
+            double complex cb_ = -Ds * Eb * A, cp_ = -Dh * Ep * A;
+            Ev.x = cb_ * bd.x + cp_ * ph.x;
+            Ev.y = cb_ * bd.y + cp_ * ph.y;
+            Ev.z = cb_ * bd.z + cp_ * ph.z;
+            /* the wave behind the edge: caustic on the edge (along phi^),
+             * the other at rho_e behind it (along beta^) */
+            rho1 = s;
+            dir1 = ph;
+            rho2 = rhoe + s;
+            dir2 = bd;
+            ip = dd;
+          }
+          v3 prx = pol_dir(u, scl(dd, -1.0), &fl);
+          double complex a = (lam / (4.0 * M_PI)) * cdot(Ev, prx);
+          double Ltot = 0.0;
+          for (int j = 0; j <= m; ++j) Ltot += ell[j];
+          if (nvalid < cap) {
+            int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+            kk[0] = r;
+            kk[1] = m;
+            for (int j = 0; j < width; ++j) kk[2 + j] = j < m ? ((int32_t)w[j] | OR_DIFF) : -1;
+            opath* o = &paths_out[nvalid];
+            memset(o, 0, sizeof(*o));
+            o->valid = 1;
+            o->flags = fl;
+            o->len_m = Ltot;
+            o->delay_s = Ltot / C0;
+            o->amp_re = creal(a);
+            o->amp_im = cimag(a);
+            for (int i = 0; i < m; ++i) {
+              o->pts[i][0] = X[i + 1].x;
+              o->pts[i][1] = X[i + 1].y;
+              o->pts[i][2] = X[i + 1].z;
+            }
+          }
+          nvalid++;
+        }
   }
   free(W);
   scene_free(&S);

@@ -133,6 +133,9 @@ def lib():
         _lib.or_diffract_refl.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                           P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
         _lib.or_diffract_refl.restype = C.c_int64
+        _lib.or_diffract_multi.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                           P(_Params), C.c_int32, C.c_int32, i32, C.c_void_p, C.c_int64]
+        _lib.or_diffract_multi.restype = C.c_int64
     return _lib
 
 
@@ -156,6 +159,7 @@ class OracleParams:
     max_trans: int = 0          # transmissions per path (Table II penetration)
     trans_db: tuple = ()        # per material penetration loss [dB], < 0 opaque
     diffraction: bool = False   # first-order edge diffraction paths (UTD)
+    diffraction_order: int = 1  # with diffraction: paths over up to this many wedges (1-3)
 
     @property
     def width(self) -> int:
@@ -485,6 +489,10 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
         dk, dp = diffract(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm)
         keys = np.concatenate([keys, dk])
         paths = np.concatenate([paths, dp])
+        for m in range(2, prm.diffraction_order + 1):
+            mk_, mp_ = diffract_multi(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm, m)
+            keys = np.concatenate([keys, mk_])
+            paths = np.concatenate([paths, mp_])
         order = np.lexsort(keys.T[::-1])
         keys, paths = keys[order], paths[order]
     fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)
@@ -533,6 +541,31 @@ def diffract(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleParams,
         raise RuntimeError(f"or_diffract failed: {n}")
     if n > cap:
         raise RuntimeError(f"or_diffract: {n} paths exceed capacity {cap}")
+    return keys[:n].copy(), paths[:n].copy()
+
+
+def diffract_multi(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleParams, order: int,
+                   cap=1 << 20):
+    """Step 5, orders 2 and 3: paths over ``order`` distinct wedges (Keller
+    points by minimising the unfolded length, the shadow rule at every wedge,
+    every leg unoccluded) with the chained UTD field and the astigmatic
+    spreading of edge-diffracted waves. Keys (rx, order, w1 | DIFF, ..),
+    -1 padded to 2 + max(prm.width, order)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    width = max(prm.width, order)
+    keys = np.zeros((cap, 2 + width), np.int32)
+    paths = np.zeros(cap, PATH_DTYPE)
+    prm_c = prm.c()
+    n = lib().or_diffract_multi(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), _p(_i32(tri_obj), C.c_int32),
+                                wt.shape[0], _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                                _p(rx, C.c_float), rx.shape[0], C.byref(prm_c), int(order), width,
+                                _p(keys, C.c_int32), paths.ctypes.data_as(C.c_void_p), cap)
+    if n < 0:
+        raise RuntimeError(f"or_diffract_multi failed: {n}")
+    if n > cap:
+        raise RuntimeError(f"or_diffract_multi: {n} paths exceed capacity {cap}")
     return keys[:n].copy(), paths[:n].copy()
 
 

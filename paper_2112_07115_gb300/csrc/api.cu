@@ -504,10 +504,9 @@ int rebuild_dynamic(dcem_scene* s) {
 
 int alloc_build_scratch(dcem_scene* s, int n) {
   if (n <= kSmallBuild) return DCEM_OK;
-  int nb = (n + 1023) / 1024;
   CK(dalloc(&s->scr.bounds, 6));
   CK(dalloc(&s->scr.k0, n)); CK(dalloc(&s->scr.v0, n)); CK(dalloc(&s->scr.k1, n)); CK(dalloc(&s->scr.v1, n));
-  CK(dalloc(&s->scr.hist, (size_t)256 * nb));
+  CK(dalloc(&s->scr.hist, radix_hist_size(n)));
   CK(dalloc(&s->scr.keys, n));
   return DCEM_OK;
 }
@@ -1054,13 +1053,12 @@ int dcem_scene_set_ray_sets(dcem_scene* s, const float* dirs, const int32_t* n_r
       }
     float4* src = nullptr;
     unsigned *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr;
-    int nb = (n + 1023) / 1024;
     cudaError_t e = dalloc(&src, n);
     if (!e) e = dalloc(&k0, n);
     if (!e) e = dalloc(&v0, n);
     if (!e) e = dalloc(&k1, n);
     if (!e) e = dalloc(&v1, n);
-    if (!e) e = dalloc(&hist, (size_t)256 * nb);
+    if (!e) e = dalloc(&hist, radix_hist_size(n));
     if (!e) e = cudaMemcpyAsync(src, h.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st);
     if (!e) {
       int g = std::min((n + 255) / 256, 4096);

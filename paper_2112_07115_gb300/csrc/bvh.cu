@@ -446,27 +446,67 @@ __global__ void __launch_bounds__(256) k_radix_hist(const unsigned* __restrict__
   hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of m counts in one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) k_scan_excl(unsigned* a, int m) {
-  __shared__ unsigned part[1024];
-  int per = (m + 1023) / 1024;
-  int s = threadIdx.x * per, e = min(s + per, m);
-  unsigned acc = 0;
-  for (int i = s; i < e; ++i) acc += a[i];
-  part[threadIdx.x] = acc;
+// Exclusive scan of m counts in tiles of 4096 (1024 threads, 4 consecutive
+// counts each): each tile is scanned in place and, with `sums`, its total is
+// written to sums[tile]; k_scan_add then adds the scanned tile totals.
+constexpr int kScanTile = 4096;
+__global__ void __launch_bounds__(1024) k_scan_tile(unsigned* a, int m, unsigned* sums) {
+  __shared__ unsigned wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long base = (long)blockIdx.x * kScanTile + 4 * tid;
+  unsigned v[4], t = 0;
+  for (int j = 0; j < 4; ++j) {
+    v[j] = base + j < m ? a[base + j] : 0u;
+    t += v[j];
+  }
+  unsigned inc = t;  // inclusive scan of the thread totals within the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) wsum[w] = inc;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (w == 0) {
+    unsigned x = wsum[lane], y = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned u = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += u;
+    }
+    wsum[lane] = y - x;  // exclusive over the warps
+    if (lane == 31 && sums) sums[blockIdx.x] = y;
   }
-  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (int i = s; i < e; ++i) {
-    unsigned v = a[i];
-    a[i] = run;
-    run += v;
+  __syncthreads();
+  unsigned run = wsum[w] + inc - t;
+  for (int j = 0; j < 4; ++j) {
+    if (base + j < m) a[base + j] = run;
+    run += v[j];
   }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(unsigned* a, int m, const unsigned* sums) {
+  const unsigned add = sums[blockIdx.x];
+  const long base = (long)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  for (int j = 0; j < 4; ++j)
+    if (base + j < m) a[base + j] += add;
+}
+
+// In-place exclusive scan of a[0, m); `scratch` holds scan_scratch_size(m)
+// counts for the tile totals of every level.
+static void scan_excl(unsigned* a, int m, unsigned* scratch, cudaStream_t st) {
+  int tiles = (m + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    k_scan_tile<<<1, 1024, 0, st>>>(a, m, nullptr);
+    return;
+  }
+  k_scan_tile<<<tiles, 1024, 0, st>>>(a, m, scratch);
+  scan_excl(scratch, tiles, scratch + tiles, st);
+  k_scan_add<<<tiles, 1024, 0, st>>>(a, m, scratch);
+}
+
+size_t scan_scratch_size(size_t m) {
+  size_t n = 0;
+  for (size_t t = (m + kScanTile - 1) / kScanTile; t > 1; t = (t + kScanTile - 1) / kScanTile) n += t;
+  return n + 1;
 }
 
 __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned* __restrict__ kin,
@@ -1090,7 +1130,7 @@ cudaError_t build_tree(const float* d_prim, int n, int node_base, int leaf_base,
   for (int pass = 0; pass < 4; ++pass) {
     int shift = 8 * pass;
     k_radix_hist<<<nb, 256, 0, st>>>(ki, n, shift, scr.hist, nb);
-    k_scan_excl<<<1, 1024, 0, st>>>(scr.hist, 256 * nb);
+    scan_excl(scr.hist, 256 * nb, scr.hist + (size_t)256 * nb, st);
     k_radix_scatter<<<nb, 256, 0, st>>>(ki, vi, n, shift, scr.hist, nb, ko, vo);
     unsigned* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
@@ -1132,7 +1172,7 @@ cudaError_t sort_pairs_u32(unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v
   for (int pass = 0; pass < passes; ++pass) {
     int shift = 8 * pass;
     k_radix_hist<<<nb, 256, 0, st>>>(ki, n, shift, hist, nb);
-    k_scan_excl<<<1, 1024, 0, st>>>(hist, 256 * nb);
+    scan_excl(hist, 256 * nb, hist + (size_t)256 * nb, st);
     k_radix_scatter<<<nb, 256, 0, st>>>(ki, vi, n, shift, hist, nb, ko, vo);
     unsigned* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;

@@ -9,7 +9,7 @@ namespace dcem {
 struct BuildScratch {
   unsigned* bounds = nullptr;           // 6
   unsigned *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr;  // n each
-  unsigned* hist = nullptr;             // 256 * ceil(n / 1024)
+  unsigned* hist = nullptr;             // radix_hist_size(n)
   unsigned long long* keys = nullptr;   // n
 };
 
@@ -68,8 +68,17 @@ struct FramePrepArgs {
 
 cudaError_t launch_frame_prep(const FramePrepArgs& a, cudaStream_t st);
 
+// Counts of scratch the scan of m histogram entries needs beyond them.
+size_t scan_scratch_size(size_t m);
+// Counts in the radix sort's histogram buffer for n pairs: the histogram and
+// its scan scratch.
+inline size_t radix_hist_size(int n) {
+  size_t m = (size_t)256 * ((n + 1023) / 1024);
+  return m + scan_scratch_size(m);
+}
+
 // Stable radix sort of n (key, value) pairs by the low `bits` key bits; the
-// sorted pairs end in k0/v0 (k1, v1: n scratch each; hist: 256*ceil(n/1024)).
+// sorted pairs end in k0/v0 (k1, v1: n scratch each; hist: radix_hist_size(n)).
 cudaError_t sort_pairs_u32(unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1, unsigned* hist, int n,
                            int bits, cudaStream_t st);
 

@@ -728,3 +728,168 @@ def test_reflection_diffraction_reciprocity(oracle_mod):
         amp2, len2 = back[(i1, i0)]
         assert abs(length - len2) <= 1e-9 * length
         assert abs(amp - amp2) <= 1e-9 * abs(amp)
+
+
+# ---------------------------------------------------------------------------
+# diffraction of order 2 and 3 (Sec. III step 5, bound 3)
+# ---------------------------------------------------------------------------
+def _slab(x0, x1, y0, y1, h=10.0):
+    """A thin vertical wall (four side faces, no top: only its vertical edges are wedges)."""
+    return scenes.box_tris(x1 - x0, y1 - y0, h, center=((x0 + x1) / 2, (y0 + y1) / 2, 0.0),
+                           faces=("xm", "xp", "ym", "yp"))
+
+
+def _prism(theta, r_tip=20.0, r_base=8.0, half=2.0, h=10.0):
+    """A thin vertical triangular prism pointing radially outward at angle theta: its tip is a
+    sharp vertical wedge (interior angle about 19 degrees)."""
+    c, s = np.cos(theta), np.sin(theta)
+    tip = np.array([r_tip * c, r_tip * s])
+    t = np.array([-s, c])
+    b1, b2 = np.array([r_base * c, r_base * s]) + half * t, np.array([r_base * c, r_base * s]) - half * t
+    out = []
+    for a, b in ((tip, b1), (b1, b2), (b2, tip)):
+        out += scenes._quad((a[0], a[1], 0.0), (b[0], b[1], 0.0), (b[0], b[1], h), (a[0], a[1], h))
+    return out
+
+
+def _composition_check(O, sc, m, prm):
+    """The one path of order m of a scene whose wedges are parallel vertical edges, with Tx, Rx
+    and so every Keller point at one height. For parallel edges the astigmatic spreading of
+    successive edge-diffracted waves reduces to a closed form: the wave behind edge i has
+    caustics on edge i and at the unfolded distance back to the source, which gives
+    a_m = (lam/4pi) D_1 .. D_m e^{-jkS} / sqrt(s_0 s_1 .. s_m S) (S the unfolded length), with
+    edge i's distance parameter s_{i-1} s_i / (s_{i-1} + s_i) -- the one of a first-order
+    diffraction from Q_{i-1} toward Q_{i+1}. So a_m equals the product of the m first-order
+    amplitudes (Q_{i-1} -> wedge i -> Q_{i+1}, each computed by or_diffract on its own) times
+    (4pi/lam)^(m-1) e^{jk(s_1 + .. + s_{m-1})} sqrt(s_1 .. s_{m-1} (s_0+s_1) .. (s_{m-1}+s_m) / S).
+    The first-order calls also find the same Keller points (Keller's law at each edge). The
+    Keller points are exact in FP32 (their x, y are vertices, z the common height), so the
+    first-order calls see exactly the same geometry."""
+    k, lam = 2.0 * np.pi * prm.freq_hz / C0, C0 / prm.freq_hz
+    wt = sc.tris.reshape(-1, 9)
+    keys, paths = O.diffract_multi(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm, m)
+    assert len(keys) == 1, keys
+    p = paths[0]
+    Q = [p["pts"][i].astype(np.float64) for i in range(m)]
+    T, R = sc.tx.astype(np.float64), sc.rx[0][0].astype(np.float64)
+    for q in Q:
+        assert q[2] == T[2] == R[2]
+    X = [T] + Q + [R]
+    s = [float(np.linalg.norm(X[i + 1] - X[i])) for i in range(m + 1)]
+    S = sum(s)
+    assert abs(p["len_m"] - S) <= 1e-12 * S
+    ws = [int(x) & ~O.DIFF for x in keys[0][2:2 + m]]
+    prod = 1.0 + 0.0j
+    for i in range(m):
+        kk, pp = O.diffract(wt, sc.tri_mat, sc.tri_obj, sc.materials, X[i].astype(np.float32),
+                            X[i + 2].astype(np.float32)[None], prm)
+        j = [q for q, key in enumerate(kk) if (key[2] & ~O.DIFF) == ws[i]]
+        assert len(j) == 1
+        assert np.max(np.abs(pp["pts"][j[0]][0] - Q[i])) <= 1e-9
+        prod *= complex(pp["amp_re"][j[0]], pp["amp_im"][j[0]])
+    inner = np.prod(s[1:m]) * np.prod([s[i] + s[i + 1] for i in range(m)])
+    want = prod * (4.0 * np.pi / lam) ** (m - 1) * np.exp(1j * k * sum(s[1:m])) * np.sqrt(inner / S)
+    got = complex(p["amp_re"], p["amp_im"])
+    assert abs(got - want) <= 1e-9 * abs(want), (got, want)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_double_diffraction_composes_from_first_order(oracle_mod, mat):
+    """Two thin walls, one reaching south from y = 0 and one north from y = 5: no direct or
+    first-order path, one double diffraction around the walls' ends. The edges of one wall's end
+    face are not a path (the leg would run along that face)."""
+    O = oracle_mod
+    tris = _slab(0.0, 0.5, -50.0, 0.0) + _slab(10.0, 10.5, 5.0, 55.0)
+    sc = scenes._static_scene("walls", tris, [mat] * len(tris), (-10.0, -20.0, 2.0), [(20.0, 20.0, 2.0)])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    k1, _ = O.diffract(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)
+    assert len(k1) == 0
+    _composition_check(O, sc, 2, prm)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_triple_diffraction_composes_from_first_order(oracle_mod, mat):
+    """Three thin prisms at 60, 0 and -60 degrees: the path wraps around their tips, each tip
+    hiding the point after the next one."""
+    O = oracle_mod
+    tris = []
+    for a in np.deg2rad([60.0, 0.0, -60.0]):
+        tris += _prism(a)
+    at = lambda deg: (22.0 * np.cos(np.deg2rad(deg)), 22.0 * np.sin(np.deg2rad(deg)), 2.0)
+    sc = scenes._static_scene("prisms", tris, [mat] * len(tris), at(120.0), [at(-120.0)])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    wt = sc.tris.reshape(-1, 9)
+    for m in (1, 2):
+        fn = (lambda: O.diffract(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)) if m == 1 else \
+            (lambda: O.diffract_multi(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm, m))
+        assert len(fn()[0]) == 0
+    _composition_check(O, sc, 3, prm)
+
+
+def _crossed_edges():
+    """Three boxes: an order-2 path over a horizontal roof edge (box 0, x = 2.25, z = 4, along y)
+    and then a vertical corner (box 1, x = 7.25, y = 2.75)."""
+    boxes = [(4.5, 6.0, 4.0, 4.5, -12.5), (4.5, 8.5, 7.5, 5.0, 7.0), (7.0, 4.5, 9.5, -11.5, -7.0)]
+    tris = []
+    for lx, ly, lz, cx, cy in boxes:
+        tris += scenes.box_tris(lx, ly, lz, center=(cx, cy, 0.0))
+    return tris, (-4.0, -31.0, 2.5), (12.0, 19.5, 6.0)
+
+
+def _crossed_path(O, tris, tx, rx, freq):
+    sc = scenes._static_scene("boxes", tris, [scenes.MAT_METAL] * len(tris), tx, [rx])
+    prm = O.OracleParams(freq_hz=freq, max_refl=3)
+    keys, paths = O.diffract_multi(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx,
+                                   sc.rx[0], prm, 2)
+    sel = [i for i, p in enumerate(paths) if abs(p["pts"][0][2] - 4.0) < 1e-9 and abs(p["pts"][1][0] - 7.25) < 1e-9
+           and abs(p["pts"][1][1] - 2.75) < 1e-9]
+    assert len(sel) == 1
+    return keys[sel[0]], paths[sel[0]]
+
+
+def test_multi_diffraction_keller_law_and_minimum(oracle_mod):
+    """Non-parallel edges: at each Keller point the incident and the diffracted leg make the same
+    angle with the edge, the points lie on their edges, and moving either along its edge
+    lengthens the path (the unfolded length is convex, its stationary point its minimum)."""
+    O = oracle_mod
+    tris, tx, rx = _crossed_edges()
+    _, p = _crossed_path(O, tris, tx, rx, 28e9)
+    T, R = np.array(tx, np.float64), np.array(rx, np.float64)
+    Q1, Q2 = p["pts"][0].astype(np.float64), p["pts"][1].astype(np.float64)
+    e1, e2 = np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    assert abs(Q1[0] - 2.25) < 1e-12 and -15.5 < Q1[1] < -9.5
+    assert 0.0 < Q2[2] < 7.5
+    u = lambda v: v / np.linalg.norm(v)
+    assert abs(u(Q1 - T) @ e1 - u(Q2 - Q1) @ e1) < 1e-10
+    assert abs(u(Q2 - Q1) @ e2 - u(R - Q2) @ e2) < 1e-10
+    length = lambda a, b: np.linalg.norm(a - T) + np.linalg.norm(b - a) + np.linalg.norm(R - b)
+    L0 = length(Q1, Q2)
+    assert abs(L0 - p["len_m"]) < 1e-9
+    for d1 in (-1e-3, 0.0, 1e-3):
+        for d2 in (-1e-3, 0.0, 1e-3):
+            if d1 or d2:
+                assert length(Q1 + d1 * e1, Q2 + d2 * e2) > L0
+
+
+def test_multi_diffraction_reciprocal_at_high_frequency(oracle_mod):
+    """Perfect conductors, non-parallel edges: swapping Tx and Rx gives the same path; the
+    amplitudes differ only through the transition functions' arguments (the distance parameters
+    of an astigmatic wave are not symmetric), an O(1/(kL)) effect, while the spreading of the
+    astigmatic chain is reciprocal. So the relative difference falls as 1/f and is below 1e-4 at
+    280 THz; a wrong caustic or principal direction would leave an O(1) mismatch."""
+    O = oracle_mod
+    tris, tx, rx = _crossed_edges()
+    diffs = []
+    for f in (2.8e12, 28e12, 280e12):
+        ka, pa = _crossed_path(O, tris, tx, rx, f)
+        sc = scenes._static_scene("boxes", tris, [scenes.MAT_METAL] * len(tris), rx, [tx])
+        prm = O.OracleParams(freq_hz=f, max_refl=3)
+        kb, pb = O.diffract_multi(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx,
+                                  sc.rx[0], prm, 2)
+        j = [i for i, k in enumerate(kb) if k[2] == ka[3] and k[3] == ka[2]]
+        assert len(j) == 1
+        assert abs(pb["len_m"][j[0]] - pa["len_m"]) <= 1e-12 * pa["len_m"]
+        a, b = complex(pa["amp_re"], pa["amp_im"]), complex(pb["amp_re"][j[0]], pb["amp_im"][j[0]])
+        diffs.append(abs(a - b) / abs(a))
+    assert diffs[2] < 1e-4
+    assert 5.0 < diffs[0] / diffs[1] < 20.0 and 5.0 < diffs[1] / diffs[2] < 20.0
