@@ -330,6 +330,28 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
  * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes);
 
+/* With diffraction on: paths over up to max_order wedges (1, 2 or 3; Sec.
+ * III step 5, whose bound is 3 diffractions). For m = 2, 3 every frame adds,
+ * for each link and each sequence of m pairwise distinct wedges whose
+ * consecutive members share no triangle, the path Tx -> Q_1 -> .. -> Q_m ->
+ * Rx whose points make the unfolded length stationary (Keller's law at every
+ * edge: the minimum of that convex length), kept when every Q_i lies inside
+ * its edge, at every wedge the previous and the next point lie in the
+ * exterior and the next point beyond the incident shadow boundary of the
+ * previous one, no leg between two wedges runs within 1e-6 rad of a face of
+ * either, and every leg is unoccluded (the faces of the wedges at its ends
+ * excluded). Field: the UTD coefficient of each wedge applied to the field
+ * the previous leg brings, with the astigmatic spreading of an
+ * edge-diffracted wave (Kouyoumjian & Pathak 1974, straight edge: a caustic
+ * on the edge and one at the arriving wavefront's radius of curvature along
+ * the edge). Record: depth m, tri[i] = wedge_i | DCEM_TRI_DIFFRACT, pts[i]
+ * = Q_i, ray = -1. Cost per frame: one pre-test thread per (transmitter,
+ * wedge pair), for m = 3 per (pair, wedge), then per (sequence, receiver);
+ * the wedge-pair relation takes nw * nw bits of device memory for m = 3.
+ * max_order = 1 turns the higher orders off. Errors: DCEM_ERR_ARG,
+ * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
+int dcem_scene_set_diffraction_order(dcem_scene* s, int32_t max_order);
+
 /* Closest-hit kernel configuration. Results never depend on it (closest hit
  * and lowest-id ties are decided by the triangle test alone):
  *   kernel  -1 automatic (default: 1 when the compact copy and the stacks fit

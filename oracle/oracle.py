@@ -489,6 +489,8 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
         dk, dp = diffract(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm)
         keys = np.concatenate([keys, dk])
         paths = np.concatenate([paths, dp])
+        if prm.diffraction_order > prm.width:
+            raise ValueError("diffraction_order exceeds the key width (max_refl + max_trans)")
         for m in range(2, prm.diffraction_order + 1):
             mk_, mp_ = diffract_multi(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm, m)
             keys = np.concatenate([keys, mk_])

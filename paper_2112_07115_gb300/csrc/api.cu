@@ -250,6 +250,11 @@ struct dcem_scene {
   int nrp = 0;
   bool diff_refl = false;
   unsigned dsurv_cap = 0;
+  int diff_order = 1;          // diffraction: most wedges on one path (1-3)
+  int4* dseq2 = nullptr;       // ... the frame's wedge pairs and triples, the pair relation
+  int4* dseq3 = nullptr;
+  unsigned dseq2_cap = 0, dseq3_cap = 0;
+  unsigned* drel = nullptr;
   double2* g_items = nullptr;  // field derivatives: per-item results, their parameter,
   int* g_param = nullptr;      // staged outputs and the error flag (dcem_path_gradients)
   double* g_out = nullptr;
@@ -386,6 +391,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo); dfree(s->dsurv);
   dfree(s->rplanes); dfree(s->rmembers);
+  dfree(s->dseq2); dfree(s->dseq3); dfree(s->drel);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx); dfree(s->g_theta);
   dfree(s->roots); dfree(s->root_box); dfree(s->perm); dfree(s->prim); dfree(s->mats);
@@ -1245,6 +1251,23 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
   return DCEM_OK;
 }
 
+int dcem_scene_set_diffraction_order(dcem_scene* s, int32_t max_order) {
+  if (!s || max_order < 1 || max_order > 3) return DCEM_ERR_ARG;
+  if (max_order > 1 && !s->diffraction) return DCEM_ERR_STATE;
+  if (max_order >= 2 && !s->dseq2 && s->nw > 1) {  // lists grown (and the frame traced again) on demand
+    CK(dalloc(&s->dseq2, (size_t)4096));
+    s->dseq2_cap = 4096;
+  }
+  if (max_order >= 3 && !s->dseq3 && s->nw > 2) {
+    CK(dalloc(&s->dseq3, (size_t)4096));
+    s->dseq3_cap = 4096;
+    CK(dalloc(&s->drel, ((size_t)s->nw * s->nw + 31) / 32));
+  }
+  CK(cudaStreamSynchronize(s->st));
+  s->diff_order = max_order;
+  return DCEM_OK;
+}
+
 int dcem_scene_set_graph_replay(dcem_scene* s, int32_t on) {
   if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
   s->use_graphs = on != 0;
@@ -1486,6 +1509,13 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.dsurv_cap = s->dsurv_cap;
   const bool dr = q.wedges && s->diff_refl && s->nrp > 0;
   q.rplanes = dr ? s->rplanes : nullptr;
+  const int dord = q.wedges && s->nw > 1 ? std::min(s->diff_order, s->nw > 2 ? 3 : 2) : 1;
+  q.diff_order = dord;
+  q.dseq2 = dord >= 2 ? s->dseq2 : nullptr;
+  q.dseq2_cap = dord >= 2 ? s->dseq2_cap : 0;
+  q.dseq3 = dord >= 3 ? s->dseq3 : nullptr;
+  q.dseq3_cap = dord >= 3 ? s->dseq3_cap : 0;
+  q.drel = dord >= 3 ? s->drel : nullptr;
   q.rmembers = dr ? s->rmembers : nullptr;
   q.nrp = dr ? s->nrp : 0;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
@@ -1673,7 +1703,8 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
                  (P.q.vc_next_key ? 1 : 0) +
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
-                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) + (P.q.rplanes && P.nlinks > 0 ? 1 : 0);
+                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) + (P.q.rplanes && P.nlinks > 0 ? 1 : 0) +
+                 (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -1808,13 +1839,19 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
       if ((long long)s->R + cc > (1ll << 27)) return DCEM_ERR_CAPACITY;
       if ((rc = ensure_log(s, s->logW, (int)cc)) != DCEM_OK) return rc;
     }
-    if (err & ERR_DIFF_OVERFLOW) {  // more diffraction pre-test survivors than list slots
-      unsigned long long want = std::max<unsigned long long>(2ull * s->dsurv_cap,
-                                                             (unsigned long long)c[0].n_dsurv * 5 / 4 + 1024);
-      if (want > 0x7fffffffull) return DCEM_ERR_CAPACITY;
-      dfree(s->dsurv);
-      CK(dalloc(&s->dsurv, (size_t)want));
-      s->dsurv_cap = (unsigned)want;
+    if (err & ERR_DIFF_OVERFLOW) {  // more diffraction pre-test survivors (or wedge pairs, triples) than slots
+      auto grow = [&](unsigned n, unsigned& cap, auto*& buf) -> int {
+        if (n <= cap) return DCEM_OK;
+        unsigned long long want = std::max<unsigned long long>(2ull * cap, (unsigned long long)n * 5 / 4 + 1024);
+        if (want > 0x7fffffffull) return DCEM_ERR_CAPACITY;
+        dfree(buf);
+        CK(dalloc(&buf, (size_t)want));
+        cap = (unsigned)want;
+        return DCEM_OK;
+      };
+      if ((rc = grow(c[0].n_dsurv, s->dsurv_cap, s->dsurv)) != DCEM_OK) return rc;
+      if (s->dseq2 && (rc = grow(c[0].n_dpair, s->dseq2_cap, s->dseq2)) != DCEM_OK) return rc;
+      if (s->dseq3 && (rc = grow(c[0].n_dtrip, s->dseq3_cap, s->dseq3)) != DCEM_OK) return rc;
     }
     if (err & ERR_BUCKET_OVERFLOW) {
       int nb = s->bucket_cap * 2;
@@ -2195,7 +2232,8 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
       s->launches += 2 + (coh[i] ? 2 : 0) + (s->R > 0 ? 1 : 0) + 5 + (nrx[i] > 0 ? 1 : 0) +
                      (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
                      (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
-                     (P.q.rplanes && P.nlinks > 0 ? 1 : 0) + (i == 0 ? 1 : 0);
+                     (P.q.rplanes && P.nlinks > 0 ? 1 : 0) +
+                     (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order : 0) + (i == 0 ? 1 : 0);
       s->graph_replayed = 0;
       b->h_tab[i] = frame_trace_args(P);
     }

@@ -132,6 +132,8 @@ struct DevCounters {
   unsigned int work_pass[kMaxRefl + 1];  // ... work counters of passes p >= 1
   unsigned int n_dsurv;            // diffraction: (link, wedge) pairs past the FP32 pre-test
   unsigned int n_val_reused;       // coherent frames: distinct keys whose validation was reused
+  unsigned int n_dpair;            // diffraction of order >= 2: wedge pairs past the pre-test
+  unsigned int n_dtrip;            // ... triples
 };
 
 // Sticky mode: a valid path kept for the next frame (link, depth, sequence).
@@ -625,9 +627,10 @@ __device__ __forceinline__ int closest_hit_q4(const uint4* qn, const QFrame& f, 
   return slot_best;
 }
 
-// Any hit with t in (t0, t1), excluding ids ex0, ex1 and ex2 (occlusion test).
+// Any hit with t in (t0, t1), excluding ids ex0 .. ex3 (occlusion test).
 __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t0, float t1,
-                                        int ex0, int ex1, unsigned& overflow, TStack& st, int ex2 = -1) {
+                                        int ex0, int ex1, unsigned& overflow, TStack& st, int ex2 = -1,
+                                        int ex3 = -1) {
   st.reset();
   if (bvh.root1 != kEmpty) st.push(bvh.root1);
   int cur = bvh.root0;
@@ -663,7 +666,8 @@ __device__ __forceinline__ bool any_hit(const Bvh& bvh, const RayPre& r, float t
       int id;
       load_tri(bvh.tris, DCEM_IDX(~cur, bvh.ntris), v0, v1, v2, id);
       float t;
-      if (id != ex0 && id != ex1 && id != ex2 && tri_hit(r, v0, v1, v2, t) && t > t0 && t < t1) return true;
+      if (id != ex0 && id != ex1 && id != ex2 && id != ex3 && tri_hit(r, v0, v1, v2, t) && t > t0 && t < t1)
+        return true;
       cur = kEmpty;
     }
   }

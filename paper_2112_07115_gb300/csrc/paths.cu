@@ -1292,6 +1292,479 @@ __device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned l
   atomicAdd(&a.ctr->n_valid, 1u);
 }
 
+// ---------------------------------------------------------------------------
+// diffraction of order 2 and 3 (Sec. III step 5; the paper's bound is 3)
+// ---------------------------------------------------------------------------
+// Paths Tx -> Q_1 -> .. -> Q_m -> Rx over m pairwise distinct wedges,
+// consecutive ones sharing no face. Per frame: the ordered wedge pairs that
+// can start a path from a transmitter (k_diff_pairs), for m = 3 the triples
+// built from them (k_diff_triples), then every (sequence, receiver) through
+// an FP32 pre-test at the last wedge (k_diff_multi_pre). The pre-tests only
+// reject what the FP64 test rejects too (margins above FP32 rounding); the
+// survivors go to the diffraction survivor list with their order in the top
+// bits: 01 order 2, 11 order 3 (10 is a reflection pair, 00 first order).
+constexpr unsigned long long kKindShift = 62;
+constexpr unsigned long long kMulti2 = 1ull << kKindShift, kMulti3 = 3ull << kKindShift;
+constexpr double kGraze = 1e-6;  // a leg between two wedges this close to a face (rad) grazes it
+
+struct WedgeF {  // a wedge's frame in FP32 for the pre-tests
+  float3 p0, e, t0, y0;
+  float len, npi;
+};
+__device__ __forceinline__ WedgeF wedge_f(const Wedge& W) {
+  WedgeF f;
+  f.p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+  f.e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
+  f.t0 = f3((float)W.t0[0], (float)W.t0[1], (float)W.t0[2]);
+  f.y0 = f3((float)W.y0[0], (float)W.y0[1], (float)W.y0[2]);
+  f.len = (float)W.len;
+  f.npi = (float)(W.n * M_PI);
+  return f;
+}
+// X in the wedge's normal plane: (along t0, along y0), its distance from the
+// edge line and from the wedge's start.
+__device__ __forceinline__ float2 wedge_plane(const WedgeF& W, float3 X, float& r, float& dist) {
+  float3 d = f3(X.x - W.p0.x, X.y - W.p0.y, X.z - W.p0.z);
+  float z = fdot3(d, W.e);
+  float3 q = f3(d.x - W.e.x * z, d.y - W.e.y * z, d.z - W.e.z * z);
+  r = sqrtf(fdot3(q, q));
+  dist = sqrtf(fdot3(d, d));
+  return make_float2(fdot3(q, W.t0), fdot3(q, W.y0));
+}
+// The edge's end points.
+__device__ __forceinline__ void edge_ends(const WedgeF& W, float3& A, float3& B) {
+  A = W.p0;
+  B = f3(W.p0.x + W.e.x * W.len, W.p0.y + W.e.y * W.len, W.p0.z + W.e.z * W.len);
+}
+// Could some point of segment A-B lie strictly inside the angular sector
+// (lo, hi) about wedge W (angles from face 0 through the exterior, hi - lo
+// below pi)? The sector is the intersection of two half-spaces bounded by
+// planes through the edge line, so the test clips the segment's parameter
+// range against both; each plane is moved outward by `m` (metres) and the
+// sector widened by `ta` (radians) first, so the answer is "no" only when
+// the exact sector misses the segment by more than the margins.
+__device__ __forceinline__ bool sector_meets(const WedgeF& W, float lo, float hi, float ta, float m, float3 A,
+                                             float3 B) {
+  lo -= ta;
+  hi += ta;
+  if (hi - lo >= 3.14f) return true;
+  float ra, rb, da, db;
+  float2 pa = wedge_plane(W, A, ra, da), pb = wedge_plane(W, B, rb, db);
+  float u0 = 0.0f, u1 = 1.0f;
+  for (int q = 0; q < 2; ++q) {
+    float ang = q == 0 ? lo : hi, sg = q == 0 ? 1.0f : -1.0f;
+    float c = cosf(ang), s = sinf(ang);
+    // signed distance beyond the plane at angle `ang` toward the sector's inside
+    float fa = sg * (c * pa.y - s * pa.x) + m, fb = sg * (c * pb.y - s * pb.x) + m;
+    if (fa < 0.0f && fb < 0.0f) return false;
+    if (fa < 0.0f) u0 = fmaxf(u0, fa / (fa - fb));
+    else if (fb < 0.0f) u1 = fminf(u1, fa / (fa - fb));
+  }
+  return u0 <= u1 + 1e-3f;
+}
+// Margins of the pre-tests: angles by ten times their rounding bound (at
+// least 1e-3 rad), positions by 5 cm plus 1e-5 of the coordinates' size.
+__device__ __forceinline__ float pre_margin_m(float3 X) {
+  return 0.05f + 1e-5f * (fabsf(X.x) + fabsf(X.y) + fabsf(X.z));
+}
+// Is X certainly inside wedge W (beyond its exterior [0, n pi])?
+__device__ __forceinline__ bool surely_inside(const WedgeF& W, float3 X) {
+  float r, dist;
+  float2 p = wedge_plane(W, X, r, dist);
+  bool sure;
+  float tol;
+  float a = wedge_angle32(f3(p.x * W.t0.x + p.y * W.y0.x, p.x * W.t0.y + p.y * W.y0.y, p.x * W.t0.z + p.y * W.y0.z),
+                          W.t0, W.y0, r, dist, sure, tol);
+  return sure && r > pre_margin_m(X) && a > W.npi + tol;
+}
+// Could some point of edge B's segment be in wedge A's exterior [0, n pi]?
+__device__ __forceinline__ bool edge_sees(const WedgeF& A, const WedgeF& B, float m) {
+  float3 P, Q;
+  edge_ends(B, P, Q);
+  // n >= 1: the interior (n pi, 2 pi) is a convex sector, so the segment is
+  // inside it only when both ends are; n < 1: the exterior is the convex one
+  if (A.npi >= 3.14159265f) return !(surely_inside(A, P) && surely_inside(A, Q));
+  return sector_meets(A, 0.0f, A.npi, 1e-3f, m, P, Q);
+}
+// Could a point of segment P-Q be beyond the incident shadow boundary of a
+// source X at wedge W (|phi - phi'| > pi, phi <= n pi)? The rule is
+// symmetric in the two points, so this also tests a receiver X against the
+// previous edge.
+__device__ __forceinline__ bool shadow_meets(const WedgeF& W, float3 X, float3 P, float3 Q) {
+  float r, dist;
+  float2 p = wedge_plane(W, X, r, dist);
+  float m = fmaxf(pre_margin_m(X), fmaxf(pre_margin_m(P), pre_margin_m(Q)));
+  if (!(r > m)) return true;
+  bool sure;
+  float tol;
+  float a = wedge_angle32(f3(p.x * W.t0.x + p.y * W.y0.x, p.x * W.t0.y + p.y * W.y0.y, p.x * W.t0.z + p.y * W.y0.z),
+                          W.t0, W.y0, r, dist, sure, tol);
+  if (!sure) return true;
+  if (a > W.npi + tol) return false;  // X inside the wedge
+  const float pi = 3.14159265f;
+  if (fabsf(a - pi) <= tol) return true;
+  float lo = a < pi ? a + pi : 0.0f, hi = a < pi ? W.npi : a - pi;
+  if (hi < lo - tol) return false;
+  return sector_meets(W, lo, hi, tol, m, P, Q);
+}
+
+// Ordered pairs (w1, w2) per transmitter that can start a path of order
+// >= 2: distinct, no shared face, each edge partly in the other's exterior,
+// the transmitter outside w1, and some point of edge 2 beyond the incident
+// shadow boundary of the transmitter at w1. With order 3, the relation
+// (the first three conditions) also goes to a bit matrix for the triples.
+__global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int ntx) {
+  const long nw = a.nw, total = (long)ntx * nw * nw;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long idx = base + lane;
+    bool keep = false;
+    int t = 0, w1 = 0, w2 = 0;
+    if (idx < total) {
+      t = (int)(idx / (nw * nw));
+      long r = idx - (long)t * nw * nw;
+      w1 = (int)(r / nw);
+      w2 = (int)(r - (long)w1 * nw);
+      const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
+      bool rel = w1 != w2 && A.ta != B.ta && A.ta != B.tb && A.tb != B.ta && A.tb != B.tb;
+      if (rel) {
+        WedgeF fa = wedge_f(A), fb = wedge_f(B);
+        float3 pa, qa;
+        edge_ends(fa, pa, qa);
+        float m = fmaxf(pre_margin_m(pa), pre_margin_m(qa));
+        rel = edge_sees(fa, fb, m) && edge_sees(fb, fa, m);
+        if (rel && t == 0 && a.drel) {
+          size_t bit = (size_t)w1 * nw + w2;
+          atomicOr(&a.drel[bit >> 5], 1u << (bit & 31));
+        }
+        if (rel) {
+          float4 tv = a.txs[t];
+          float3 T = f3(tv.x, tv.y, tv.z), P, Q;
+          edge_ends(fb, P, Q);
+          keep = !surely_inside(fa, T) && shadow_meets(fa, T, P, Q);
+        }
+      }
+    }
+    unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (!mk) continue;
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(&a.ctr->n_dpair, (unsigned)__popc(mk));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+    if (keep) {
+      if (at < a.dseq2_cap) a.dseq2[at] = make_int4(t, w1, w2, -1);
+      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+    }
+  }
+}
+
+// Triples (w1, w2, w3) from the pairs: (w2, w3) in the relation, w3 not w1.
+__global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
+  const long nw = a.nw;
+  const long np = (long)min(a.ctr->n_dpair, a.dseq2_cap), total = np * nw;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long idx = base + lane;
+    bool keep = false;
+    int4 pr = make_int4(0, 0, 0, -1);
+    int w3 = 0;
+    if (idx < total) {
+      long p = idx / nw;
+      w3 = (int)(idx - p * nw);
+      pr = a.dseq2[p];
+      size_t bit = (size_t)pr.z * nw + w3;
+      keep = w3 != pr.y && ((a.drel[bit >> 5] >> (bit & 31)) & 1u);
+    }
+    unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (!mk) continue;
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(&a.ctr->n_dtrip, (unsigned)__popc(mk));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+    if (keep) {
+      if (at < a.dseq3_cap) a.dseq3[at] = make_int4(pr.x, pr.y, pr.z, w3);
+      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+    }
+  }
+}
+
+// Every (sequence, receiver): the receiver outside the last wedge and some
+// point of the previous edge beyond its shadow boundary at the last wedge.
+__global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
+  const long n2 = a.diff_order >= 2 ? (long)min(a.ctr->n_dpair, a.dseq2_cap) : 0;
+  const long n3 = a.diff_order >= 3 ? (long)min(a.ctr->n_dtrip, a.dseq3_cap) : 0;
+  const long total = (n2 + n3) * a.nrx;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+    long idx = base + lane;
+    bool keep = false;
+    unsigned long long code = 0;
+    if (idx < total) {
+      long e = idx / a.nrx;
+      int r = (int)(idx - e * a.nrx);
+      bool three = e >= n2;
+      long ei = three ? e - n2 : e;
+      int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
+      int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
+      WedgeF fl = wedge_f(a.wedges[wl]), fp = wedge_f(a.wedges[wp]);
+      float4 rv = a.rx[r];
+      float3 R = f3(rv.x, rv.y, rv.z), P, Q;
+      edge_ends(fp, P, Q);
+      keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+      code = ((unsigned long long)ei * a.nrx + r) | (three ? kMulti3 : kMulti2);
+    }
+    unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (!mk) continue;
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+    if (keep) {
+      if (at < a.dsurv_cap) a.dsurv[at] = code;
+      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+    }
+  }
+}
+
+// Unfolded length of the chain with edge parameters t.
+__device__ __forceinline__ double chain_len(const Wedge* const* E, int m, d3w T, d3w R, const double* t) {
+  d3w prev = T;
+  double L = 0.0;
+  for (int i = 0; i < m; ++i) {
+    d3w q = D3(E[i]->p0[0], E[i]->p0[1], E[i]->p0[2]) + D3(E[i]->e[0], E[i]->e[1], E[i]->e[2]) * t[i];
+    d3w d = q - prev;
+    L += sqrt(dotw(d, d));
+    prev = q;
+  }
+  d3w d = R - prev;
+  return L + sqrt(dotw(d, d));
+}
+
+// Keller points: the stationary point (the minimum: the length is convex in
+// t) of the unfolded length over the edge parameters, by Newton's method
+// from the edges' midpoints, a step that does not shorten the chain halved;
+// converged when every edge's cosine mismatch is below 1e-12.
+__device__ bool keller_chain(const Wedge* const* E, int m, d3w T, d3w R, double* t) {
+  for (int i = 0; i < m; ++i) t[i] = 0.5 * E[i]->len;
+  double Lc = chain_len(E, m, T, R, t);
+  for (int it = 0; it < 200; ++it) {
+    d3w X[5];
+    X[0] = T;
+    for (int i = 0; i < m; ++i)
+      X[i + 1] = D3(E[i]->p0[0], E[i]->p0[1], E[i]->p0[2]) + D3(E[i]->e[0], E[i]->e[1], E[i]->e[2]) * t[i];
+    X[m + 1] = R;
+    double g[3] = {0.0, 0.0, 0.0}, H[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int j = 0; j <= m; ++j) {
+      d3w d = X[j + 1] - X[j];
+      double l = sqrt(dotw(d, d));
+      if (!(l > 0.0)) return false;
+      d3w u = d * (1.0 / l);
+      int ia = j - 1, ib = j;
+      d3w ea = ia >= 0 ? D3(E[ia]->e[0], E[ia]->e[1], E[ia]->e[2]) : D3(0, 0, 0);
+      d3w eb = ib < m ? D3(E[ib]->e[0], E[ib]->e[1], E[ib]->e[2]) : D3(0, 0, 0);
+      double ca = dotw(ea, u), cb = dotw(eb, u);
+      if (ib < m) {
+        g[ib] += cb;
+        H[ib][ib] += (1.0 - cb * cb) / l;
+      }
+      if (ia >= 0) {
+        g[ia] -= ca;
+        H[ia][ia] += (1.0 - ca * ca) / l;
+      }
+      if (ia >= 0 && ib < m) {
+        double h = -(dotw(ea, eb) - ca * cb) / l;
+        H[ia][ib] += h;
+        H[ib][ia] += h;
+      }
+    }
+    double gmax = 0.0;
+    for (int i = 0; i < m; ++i) gmax = fmax(gmax, fabs(g[i]));
+    if (gmax < 1e-12) return true;
+    // H dx = -g by elimination with partial pivoting
+    double A[3][4], dx[3];
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) A[i][j] = H[i][j];
+      A[i][m] = -g[i];
+    }
+    for (int c = 0; c < m; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+      if (!(fabs(A[piv][c]) > 1e-300)) return false;
+      if (piv != c)
+        for (int j = 0; j <= m; ++j) {
+          double x = A[c][j];
+          A[c][j] = A[piv][j];
+          A[piv][j] = x;
+        }
+      for (int r = c + 1; r < m; ++r) {
+        double f = A[r][c] / A[c][c];
+        for (int j = c; j <= m; ++j) A[r][j] -= f * A[c][j];
+      }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double v = A[i][m];
+      for (int j = i + 1; j < m; ++j) v -= A[i][j] * dx[j];
+      dx[i] = v / A[i][i];
+    }
+    double step = 1.0, tn[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < 60; ++q) {
+      for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
+      double Ln = chain_len(E, m, T, R, tn);
+      if (Ln <= Lc) {
+        Lc = Ln;
+        break;
+      }
+      step *= 0.5;
+    }
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) {
+      dmax = fmax(dmax, fabs(tn[i] - t[i]));
+      t[i] = tn[i];
+    }
+    if (dmax == 0.0) return gmax < 1e-9;
+  }
+  return false;
+}
+
+// One (sequence, receiver) survivor of order m: the Keller points, the
+// wedge rules, the legs (FP32 any-hit, the faces of the wedges at each end
+// excluded), then the UTD chain: at each wedge the coefficient acts on the
+// arriving field in the wedge's edge-fixed bases; the wave behind it has a
+// caustic on the edge (radius s along phi^) and one rho_e behind it (radius
+// rho_e + s along beta^), rho_e the arriving wavefront's radius of curvature
+// along the edge's projection (Euler's formula; the transmitter's distance
+// for its spherical wave); spreading sqrt(rho_e / (s (rho_e + s))) and
+// distance parameter L = s (rho_e + s) rho_1 rho_2 sin^2 beta_0 /
+// (rho_e (rho_1 + s) (rho_2 + s)) (Kouyoumjian & Pathak 1974, straight edge).
+__device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long long code, double k, double lam,
+                                            unsigned& ovf, TStack& st) {
+  const bool three = (code >> kKindShift) == 3ull;
+  const int m = three ? 3 : 2;
+  const unsigned long long c = code & ((1ull << kKindShift) - 1ull);
+  const long ei = (long)(c / a.nrx);
+  const int r = (int)(c - (unsigned long long)ei * a.nrx);
+  const int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
+  const int w[3] = {sq.y, sq.z, sq.w};
+  const int link = sq.x * a.nrx + r;
+  const Wedge* E[3] = {&a.wedges[w[0]], &a.wedges[w[1]], three ? &a.wedges[w[2]] : &a.wedges[w[1]]};
+  float4 rxv = a.rx[r], txv = a.txs[sq.x];
+  const d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
+  if (wedge_angle(*E[0], T) > E[0]->n * M_PI || wedge_angle(*E[m - 1], R) > E[m - 1]->n * M_PI) return;
+  double t[3];
+  if (!keller_chain(E, m, T, R, t)) return;
+  d3w X[5];
+  X[0] = T;
+  for (int i = 0; i < m; ++i) {
+    double uq = t[i] / E[i]->len;
+    if (!(uq > 0.0 && uq < 1.0)) return;
+    X[i + 1] = D3(E[i]->p0[0], E[i]->p0[1], E[i]->p0[2]) + D3(E[i]->e[0], E[i]->e[1], E[i]->e[2]) * t[i];
+  }
+  X[m + 1] = R;
+  double ell[4];
+  for (int j = 0; j <= m; ++j) {
+    d3w d = X[j + 1] - X[j];
+    ell[j] = sqrt(dotw(d, d));
+    if (!(ell[j] > 1e-9)) return;
+  }
+  double phip[3], phi[3];
+  for (int i = 0; i < m; ++i) {
+    phip[i] = wedge_angle(*E[i], X[i]);
+    phi[i] = wedge_angle(*E[i], X[i + 2]);
+    const double nn = E[i]->n;
+    if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) return;
+    if (!(fabs(phi[i] - phip[i]) > M_PI)) return;
+    if (i > 0 && !(fmin(phip[i], nn * M_PI - phip[i]) > kGraze)) return;
+    if (i < m - 1 && !(fmin(phi[i], nn * M_PI - phi[i]) > kGraze)) return;
+  }
+  for (int j = 0; j <= m; ++j) {
+    int e0 = j >= 1 ? E[j - 1]->ta : -1, e1 = j >= 1 ? E[j - 1]->tb : -1;
+    int e2 = j < m ? E[j]->ta : -1, e3 = j < m ? E[j]->tb : -1;
+    d3w dv = X[j + 1] - X[j];
+    RayPre rp = ray_pre(f3((float)X[j].x, (float)X[j].y, (float)X[j].z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, e0, e1, ovf, st, e2, e3)) return;
+  }
+  unsigned fl = 0;
+  const d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
+  d3w ip = (X[1] - X[0]) * (1.0 / ell[0]);
+  d3w e0 = polw(u, ip, fl);
+  double sn, cs;
+  sincos(-k * ell[0], &sn, &cs);
+  zd Ei = Z(cs / ell[0], sn / ell[0]);
+  zv3 Ev = {Ei * e0.x, Ei * e0.y, Ei * e0.z};
+  double rho1 = ell[0], rho2 = ell[0];
+  d3w dir1 = D3(0, 0, 0), dir2 = D3(0, 0, 0), dd = ip;
+  for (int i = 0; i < m; ++i) {
+    const Wedge& W = *E[i];
+    const double s = ell[i + 1], nn = W.n;
+    const d3w e = D3(W.e[0], W.e[1], W.e[2]);
+    dd = (X[i + 2] - X[i + 1]) * (1.0 / s);
+    double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
+    double sb = sin(beta0);
+    d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
+    d3w bp = crossw(ip, php), bd = crossw(dd, ph);
+    double rhoe;
+    if (i == 0) rhoe = ell[0];
+    else {
+      double c1 = dotw(bp, dir1), c2 = dotw(bp, dir2);
+      rhoe = 1.0 / (c1 * c1 / rho1 + c2 * c2 / rho2);
+    }
+    double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
+    const float4 ma =
+        a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.ta, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+    const float4 mb =
+        a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.tb, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+    zd r0s, r0h, rns, rnh;
+    fresnel_d(ma, a.freq, fabs(sin(phip[i])), r0s, r0h);
+    fresnel_d(mb, a.freq, fabs(sin(nn * M_PI - phi[i])), rns, rnh);
+    const UtdParts up = utd_parts(nn, phi[i], phip[i], beta0, L, k, fl);
+    zd Ds = utd_coeff(up, r0s, rns), Dh = utd_coeff(up, r0h, rnh);
+    sincos(-k * s, &sn, &cs);
+    zd A = Z(cs, sn) * sqrt(rhoe / (s * (rhoe + s)));
+    zd cb = Ds * zvdot(Ev, bp) * A * -1.0, cp = Dh * zvdot(Ev, php) * A * -1.0;
+    Ev = zv3{cb * bd.x + cp * ph.x, cb * bd.y + cp * ph.y, cb * bd.z + cp * ph.z};
+    rho1 = s;
+    dir1 = ph;
+    rho2 = rhoe + s;
+    dir2 = bd;
+    ip = dd;
+  }
+  d3w prx = polw(u, dd * -1.0, fl);
+  zd amp = zvdot(Ev, prx) * (lam / (4.0 * M_PI));
+  double Ltot = 0.0;
+  for (int j = 0; j <= m; ++j) Ltot += ell[j];
+  unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
+  if (uu >= a.ucap) {
+    atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
+    return;
+  }
+  PathRec rec;
+  rec.key = seq_key(r, m, [&](int q) { return w[q] | kDiffBit; });
+  rec.rx = link;
+  rec.depth = m;
+  rec.ray = -1;
+  rec.flags = fl;
+  rec.valid = 1;
+  rec.pad = 0;
+  rec.len = Ltot;
+  rec.amp_re = amp.re;
+  rec.amp_im = amp.im;
+  for (int q = 0; q < kMaxRefl; ++q) {
+    rec.tri[q] = q < m ? (w[q] | kDiffBit) : -1;
+    rec.pts[q][0] = rec.pts[q][1] = rec.pts[q][2] = 0.0f;
+  }
+  for (int q = 0; q < m; ++q) {
+    rec.pts[q][0] = (float)X[q + 1].x;
+    rec.pts[q][1] = (float)X[q + 1].y;
+    rec.pts[q][2] = (float)X[q + 1].z;
+  }
+  a.prec[uu] = rec;
+  unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
+  if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
+  else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+  atomicAdd(&a.ctr->n_valid, 1u);
+}
+
 // Pass 1 over every (link, wedge) pair: the FP32 pre-test rejects most of
 // them; the survivors' indices go to a list (one atomic per warp).
 __global__ void __launch_bounds__(256) k_diffract_pre(PathArgs a, int nlinks) {
@@ -1331,7 +1804,9 @@ __global__ void __launch_bounds__(32) k_diffract(PathArgs a) {
   unsigned ovf = 0;
   for (unsigned i = blockIdx.x + gridDim.x * threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned long long c = a.dsurv[i];
-    if (c & kReflTag) diffract_refl_pair(a, c & ~kReflTag, k, lam, ovf, st);
+    const unsigned kind = (unsigned)(c >> kKindShift);
+    if (kind == 2u) diffract_refl_pair(a, c & ~kReflTag, k, lam, ovf, st);
+    else if (kind != 0u) diffract_multi(a, c, k, lam, ovf, st);
     else diffract_pair(a, (long)c, k, lam, ovf, st);
   }
   if (ovf) {
@@ -1489,6 +1964,14 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
       long tr = (long)nlinks * a.nw * a.nrp * 2;
       long gr = std::min<long>((tr + 255) / 256, 8L * sms);
       k_diffract_refl_pre<<<(int)std::max<long>(gr, 1), 256, 0, st>>>(a, nlinks);
+    }
+    if (a.diff_order >= 2 && a.nw > 1) {
+      int ntx = nlinks / a.nrx;
+      long tp = (long)ntx * a.nw * a.nw;
+      if (a.drel) cudaMemsetAsync(a.drel, 0, sizeof(unsigned) * (((size_t)a.nw * a.nw + 31) / 32), st);
+      k_diff_pairs<<<(int)std::max<long>(std::min<long>((tp + 255) / 256, 8L * sms), 1), 256, 0, st>>>(a, ntx);
+      if (a.diff_order >= 3) k_diff_triples<<<8 * sms, 256, 0, st>>>(a);
+      k_diff_multi_pre<<<8 * sms, 256, 0, st>>>(a);
     }
     k_diffract<<<sms, 32, 32 * kStackTrace * sizeof(int), st>>>(a);
   }

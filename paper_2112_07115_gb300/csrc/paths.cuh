@@ -59,6 +59,15 @@ struct PathArgs {
   const RPlane* rplanes;
   const int* rmembers;
   int nrp;
+  // diffraction of order 2 and 3 (diff_order <= 1: off): the wedge pairs
+  // (t, w1, w2, -1) and triples (t, w1, w2, w3) of the frame, and the pair
+  // relation as a bit matrix (nw x nw bits; order 3 only)
+  int diff_order;
+  int4* dseq2;
+  unsigned dseq2_cap;
+  int4* dseq3;
+  unsigned dseq3_cap;
+  unsigned* drel;
   // validation reuse (coherent frames; Sec. III "Propagation path caching"):
   // the previous frame's records of its distinct keys, found through a hash
   // table of their link keys, are copied when nothing they depend on moved

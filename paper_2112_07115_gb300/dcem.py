@@ -40,7 +40,8 @@ EXPORTED = ["dcem_params_default", "dcem_scene_create", "dcem_scene_set_rays",
             "dcem_scene_set_graph_replay", "dcem_scene_set_ray_sets", "dcem_trace_links",
             "dcem_scene_set_trace_config", "dcem_scene_autotune", "dcem_batch_create",
             "dcem_batch_update_transforms", "dcem_batch_trace", "dcem_batch_destroy",
-            "dcem_scene_set_transmission", "dcem_scene_set_diffraction", "dcem_scene_set_diffraction_reflections"]
+            "dcem_scene_set_transmission", "dcem_scene_set_diffraction", "dcem_scene_set_diffraction_reflections",
+            "dcem_scene_set_diffraction_order"]
 
 
 class Material(C.Structure):
@@ -116,6 +117,7 @@ def lib():
         L.dcem_scene_set_transmission.argtypes = [vp, vp, i32, i32]
         L.dcem_scene_set_diffraction.argtypes = [vp, i32, P(i32)]
         L.dcem_scene_set_diffraction_reflections.argtypes = [vp, i32, P(i32)]
+        L.dcem_scene_set_diffraction_order.argtypes = [vp, i32]
         L.dcem_batch_create.argtypes = [vp, i32, vp, P(vp)]
         L.dcem_batch_update_transforms.argtypes = [vp, vp, i32]
         L.dcem_batch_trace.argtypes = [vp, vp, vp, vp, vp, i32, P(Params), vp, P(i32)]
@@ -575,6 +577,10 @@ class Scene:
         _check(lib().dcem_scene_set_diffraction_reflections(self.h, int(bool(on)), C.byref(n)),
                "dcem_scene_set_diffraction_reflections")
         return int(n.value)
+
+    def set_diffraction_order(self, max_order: int):
+        """With diffraction on: paths over up to max_order (1-3) wedges."""
+        _check(lib().dcem_scene_set_diffraction_order(self.h, int(max_order)), "dcem_scene_set_diffraction_order")
 
     def set_trace_config(self, kernel: int, block: int = 256, stack: int = 24):
         dcem_scene_set_trace_config(self.h, kernel, block, stack)

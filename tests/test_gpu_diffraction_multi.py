@@ -1,0 +1,168 @@
+"""Diffraction of order 2 and 3 on the GPU (dcem_scene_set_diffraction_order)
+against the oracle's or_diffract_multi: the same wedge sequences, the same
+Keller points, lengths and fields (within 1e-6), and the frame's received
+power with every mechanism summed. Decisions the oracle flags as within the
+FP margins (a Keller point at an edge's end, the shadow or grazing rule at its
+threshold, an occlusion near a leg's end) may differ."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2112_07115_gb300 import dcem, scenes
+from tests import parity as P
+from tests.test_oracle_pins import _prism, _slab
+
+pytestmark = pytest.mark.gpu
+
+FLAGS = O.VAL_PARAM | O.VAL_EDGE | O.OCC_NEAR
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2112_07115_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def _of_order(paths, m):
+    t = paths["tri"]
+    sel = paths["depth"] == m
+    for i in range(m):
+        sel &= (t[:, i] & dcem.TRI_DIFFRACT) != 0
+    return sel
+
+
+def _check(torch, sc, n_rays, max_refl, frames, order, mode=dcem.MODE_FULL, min_paths=(1, 0)):
+    """Frames of `sc` with diffraction up to `order` wedges: per order the GPU's
+    paths against the oracle's, then the received power of the whole frame."""
+    rays = scenes.fibonacci_sphere(n_rays)
+    s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(rays)
+    s.set_diffraction(True)
+    s.set_diffraction_order(order)
+    prm = P.gpu_params(sc, max_refl=max_refl, mode=mode)
+    oprm = P.oracle_params(sc, n_rays=n_rays, max_refl=max_refl, diffraction=True, diffraction_order=order)
+    totals = [0, 0]
+    for f in frames:
+        if sc.nobj:
+            s.update_transforms(sc.xf[f])
+        fr = s.trace(sc.tx, sc.rx[f], prm)
+        wt = O.transform(sc.tris, sc.tri_obj, sc.xf[f] if sc.nobj else np.zeros((0, 12)))
+        for m in range(2, order + 1):
+            ck, cp = O.diffract_multi(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[f], oprm, m)
+            ref = {tuple(k): p for k, p in zip(ck.tolist(), cp)}
+            g = fr.paths[_of_order(fr.paths, m)]
+            gk = {tuple(k): p for k, p in zip(P.path_keys(g, oprm.width), g)}
+            flagged = {k for k, p in ref.items() if p["flags"] & FLAGS}
+            diff = set(gk) ^ set(ref)
+            assert diff <= flagged, (f, m, sorted(diff - flagged)[:4])
+            for k in set(gk) & set(ref):
+                a, b = gk[k], ref[k]
+                assert abs(a["len_m"] - b["len_m"]) <= 1e-6, (f, k)
+                za, zb = complex(a["amp_re"], a["amp_im"]), complex(b["amp_re"], b["amp_im"])
+                assert abs(za - zb) <= 1e-6 * abs(zb), (f, k, za, zb)
+                assert np.allclose(a["pts"][:m], b["pts"][:m], atol=1e-4)
+                assert a["ray"] == -1
+            totals[m - 2] += len(gk)
+        # the whole frame: reflections and diffraction of every order
+        r = O.frame(sc, f, rays, oprm)
+        fin = np.isfinite(r.p_coh_dbm) & np.isfinite(fr.p_coh_dbm)
+        assert np.array_equal(np.isfinite(r.p_coh_dbm), np.isfinite(fr.p_coh_dbm))
+        assert np.all(np.abs(r.p_coh_dbm[fin] - fr.p_coh_dbm[fin]) <= 0.01), f
+    s.close()
+    assert totals[0] >= min_paths[0] and totals[1] >= min_paths[1], totals
+    return totals
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_two_walls(cuda, mat):
+    """The double diffraction around two thin walls' ends (the oracle's
+    composition pin), with extra receivers around them."""
+    tris = _slab(0.0, 0.5, -50.0, 0.0) + _slab(10.0, 10.5, 5.0, 55.0)
+    rx = [(20.0, 20.0, 2.0), (25.0, 10.0, 1.5), (15.0, 30.0, 4.0), (-5.0, 20.0, 2.0)]
+    sc = scenes._static_scene("walls", tris, [mat] * len(tris), (-10.0, -20.0, 2.0), rx)
+    _check(cuda, sc, 20_000, 3, [0], 3, min_paths=(2, 0))
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_three_prisms(cuda, mat):
+    """The triple diffraction around three prism tips, and receivers beside it."""
+    tris = []
+    for a in np.deg2rad([60.0, 0.0, -60.0]):
+        tris += _prism(a)
+    at = lambda deg, r=22.0, z=2.0: (r * np.cos(np.deg2rad(deg)), r * np.sin(np.deg2rad(deg)), z)
+    rx = [at(-120.0), at(-110.0, 25.0, 3.0), at(-130.0, 21.0, 1.0), at(-100.0, 30.0, 5.0)]
+    sc = scenes._static_scene("prisms", tris, [mat] * len(tris), at(120.0), rx)
+    _check(cuda, sc, 20_000, 3, [0], 3, min_paths=(0, 1))
+
+
+def _boxes(seed, n_boxes=6, nrx=20, n_moving=0, n_frames=1):
+    """Random boxes (vertical corners and roof edges in every orientation
+    pair), materials metal or concrete, a random Tx and receivers; the first
+    n_moving boxes are rigid objects translating by 0.4 m per frame."""
+    rng = np.random.default_rng(seed)
+    meshes = []
+    for _ in range(n_boxes):
+        lx, ly, lz = rng.uniform(3, 10), rng.uniform(3, 10), rng.uniform(3, 12)
+        meshes.append(scenes.box_tris(lx, ly, lz, center=(rng.uniform(-20, 20), rng.uniform(-20, 20), 0.0)))
+    mat_of = [scenes.MAT_METAL if rng.uniform() < 0.5 else scenes.MAT_CONCRETE for _ in range(n_boxes)]
+    tx = (rng.uniform(-40, 40), rng.uniform(-40, 40), rng.uniform(1, 6))
+    rx = np.array([(rng.uniform(-40, 40), rng.uniform(-40, 40), rng.uniform(1, 6)) for _ in range(nrx)], np.float32)
+    static = [t for mesh in meshes[n_moving:] for t in mesh]
+    smat = [m for mesh, m in zip(meshes[n_moving:], mat_of[n_moving:]) for _ in mesh]
+    tris, tobj, tmat = scenes._assemble(static, smat, meshes[:n_moving], mat_of[:n_moving])
+    xf = np.zeros((n_frames, n_moving, 12), np.float32)
+    for f in range(n_frames):
+        for o in range(n_moving):
+            xf[f, o] = scenes._xf_row(0.0, 0.4 * f, 0.2 * f * (o + 1), 0.0)
+    return scenes.Scene("boxes", tris, tobj, tmat, scenes.default_materials(), n_moving, xf,
+                        np.asarray(tx, np.float32), np.repeat(rx[None], n_frames, axis=0), n_rays=20_000, max_refl=3)
+
+
+@pytest.mark.parametrize("seed,least", [(1, (10, 0)), (6, (5, 4)), (10, (8, 16)), (14, (3, 12))])
+def test_random_boxes(cuda, seed, least):
+    """Six random boxes, 20 receivers: many paths of orders 2 and 3."""
+    _check(cuda, _boxes(seed), 20_000, 3, [0], 3, min_paths=least)
+
+
+@pytest.mark.parametrize("mode", [dcem.MODE_FULL, dcem.MODE_COHERENT])
+def test_moving_boxes(cuda, mode):
+    """Two of the boxes move (their wedges follow them), frames 0-2 in full
+    and coherent frames."""
+    _check(cuda, _boxes(6, n_moving=2, n_frames=3), 20_000, 3, range(3), 3, mode=mode, min_paths=(20, 8))
+
+
+def test_order_needs_diffraction_and_range(cuda):
+    sc = scenes.toy_street()
+    s = dcem.Scene.from_scene(sc)
+    with pytest.raises(dcem.DcemError):
+        s.set_diffraction_order(2)
+    s.set_diffraction(True)
+    for bad in (0, 4):
+        with pytest.raises(dcem.DcemError):
+            s.set_diffraction_order(bad)
+    s.set_diffraction_order(3)
+    s.set_diffraction_order(1)
+    s.close()
+
+
+def test_order_one_is_unchanged(cuda):
+    """max_order 1 after 3 gives the first-order frame bit for bit."""
+    sc = scenes.toy_street()
+    rays = scenes.fibonacci_sphere(10_000)
+    out = []
+    for orders in ((1,), (3, 1)):
+        s = dcem.Scene.from_scene(sc, stream=cuda.cuda.current_stream().cuda_stream)
+        s.set_rays(rays)
+        s.set_diffraction(True)
+        for o in orders:
+            s.set_diffraction_order(o)
+        s.update_transforms(sc.xf[1])
+        fr = s.trace(sc.tx, sc.rx[1], P.gpu_params(sc, max_refl=3))
+        out.append((fr.paths.tobytes(), fr.p_coh_dbm.tobytes()))
+        s.close()
+    assert out[0] == out[1]
