@@ -178,6 +178,11 @@ typedef struct {
   int32_t child_rays;          /* transmission: child rays spawned this frame   */
   int32_t keys_reused;         /* coherent: distinct keys whose validation was
                                   copied from the previous frame               */
+  int32_t diff_candidates;     /* diffraction: candidates past the FP32 pre-tests
+                                  (all orders), given the exact FP64 test      */
+  int32_t diff_pairs;          /* diffraction of order >= 2: wedge pairs that can
+                                  start a path (all transmitters)              */
+  int32_t diff_triples;        /* diffraction of order 3: wedge triples          */
 } dcem_stats;
 
 typedef struct {
@@ -333,9 +338,10 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
 /* With diffraction on: paths over up to max_order wedges (1, 2 or 3; Sec.
  * III step 5, whose bound is 3 diffractions). For m = 2, 3 every frame adds,
  * for each link and each sequence of m pairwise distinct wedges whose
- * consecutive members share no triangle, the path Tx -> Q_1 -> .. -> Q_m ->
- * Rx whose points make the unfolded length stationary (Keller's law at every
- * edge: the minimum of that convex length), kept when every Q_i lies inside
+ * consecutive members share no vertex and do not lie on one line, the path
+ * Tx -> Q_1 -> .. -> Q_m -> Rx whose points make the unfolded length
+ * stationary (Keller's law at every edge: the minimum of that convex
+ * length), kept when every Q_i lies inside
  * its edge, at every wedge the previous and the next point lie in the
  * exterior and the next point beyond the incident shadow boundary of the
  * previous one, no leg between two wedges runs within 1e-6 rad of a face of

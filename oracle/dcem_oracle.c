@@ -1134,9 +1134,11 @@ void or_utd(double n, double phi, double phip, double beta0, double L, double k,
 typedef struct {
   int ta, tb;       /* faces 0 and n                                   */
   v3 p0, e;         /* edge start and unit direction                   */
+  v3 p1;            /* edge end (the input vertex)                     */
   double len;
   v3 t0, y0;        /* in the plane normal to e: face 0's direction and
                        the exterior's positive angular direction        */
+  v3 tB;            /* ... and face n's direction                      */
   double n;         /* exterior angle / pi                             */
 } owedge;
 
@@ -1218,8 +1220,8 @@ static long find_wedges(const float* tris, const int32_t* tri_obj, int ntri, owe
           y0 = scl(y0, -1.0);  /* exterior direction */
           if (fabs(alpha - M_PI) > 1e-6 && alpha > 1e-9) {
             owedge* W = &w[nw++];
-            W->ta = ta; W->tb = tb; W->p0 = p0; W->e = e; W->len = len;
-            W->t0 = t0; W->y0 = y0; W->n = 2.0 - alpha / M_PI;
+            W->ta = ta; W->tb = tb; W->p0 = p0; W->p1 = p1; W->e = e; W->len = len;
+            W->t0 = t0; W->y0 = y0; W->tB = tB; W->n = 2.0 - alpha / M_PI;
           }
         }
       }
@@ -1511,6 +1513,44 @@ int64_t or_diffract_refl(const float* tris, const int32_t* tri_mat, const int32_
 /* Diffraction of order 2 and 3 (Sec. III step 5; the paper's bound is 3)    */
 /* ------------------------------------------------------------------------ */
 #define OR_GRAZE 1e-6  /* a leg between two wedges closer than this to a face (rad) grazes it */
+#define OR_LEG_MIN 1e-6  /* shortest leg of a diffraction chain while its Keller points are sought [m] */
+
+/* Do two edges share an end vertex (identical input coordinates)? Consecutive
+ * wedges of a chain may not (which includes sharing a face): the length's
+ * minimum then tends to the common corner (a vertex, not an edge, would
+ * diffract), or the leg between them runs along a face they bound. */
+static int share_vertex(const owedge* A, const owedge* B) {
+  const v3* a[2] = {&A->p0, &A->p1};
+  const v3* b[2] = {&B->p0, &B->p1};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (a[i]->x == b[j]->x && a[i]->y == b[j]->y && a[i]->z == b[j]->z) return 1;
+  return 0;
+}
+
+/* Do two edges lie on one line (directions parallel to 1e-9, the second's
+ * start within 1e-9 m (relative to the coordinates' size) of the first's
+ * line)? Consecutive wedges of a chain may not: the leg between them would
+ * run along both edges, and the unfolded length has its minimum where that
+ * leg vanishes (no Keller points). */
+static int collinear_edges(const owedge* A, const owedge* B) {
+  if (norm(cross(A->e, B->e)) > 1e-9) return 0;
+  v3 d = sub(B->p0, A->p0);
+  return norm(cross(d, A->e)) <= 1e-9 * (1.0 + maxabs(A->p0) + maxabs(B->p0));
+}
+
+/* Does edge B lie in the plane of a face of wedge A (both its ends within
+ * 1e-9 m, relative to the coordinates' size, of the plane)? Then so does the
+ * leg between them, and at A its direction is that face's (grazing), or the
+ * face's extension beyond the edge, where no source in A's exterior has its
+ * shadow boundary crossed: no chain passes. */
+static int in_face_plane(const owedge* A, const owedge* B) {
+  double tol = 1e-9 * (1.0 + maxabs(A->p0) + maxabs(B->p0));
+  v3 f[2] = {cross(A->e, A->t0), cross(A->e, A->tB)};
+  for (int q = 0; q < 2; ++q)
+    if (fabs(dot(f[q], sub(B->p0, A->p0))) <= tol && fabs(dot(f[q], sub(B->p1, A->p0))) <= tol) return 1;
+  return 0;
+}
 
 /* Unfolded length of T -> Q_1 .. Q_m -> R with Q_i = p0_i + t_i e_i. */
 static double chain_length(const owedge* const* E, int m, v3 T, v3 R, const double* t) {
@@ -1555,13 +1595,17 @@ static int solve_small(int m, double H[3][3], double* b, double* x) {
  * diffracted leg make the same angle with the edge (Keller's law). The
  * length is a convex function of t (a sum of distances between points
  * moving linearly with t), so its stationary point is its minimum; it is
- * found by Newton's method from the edges' midpoints, halving a step that
- * does not shorten the chain. Returns 1 when converged (gradient, the cosine
- * mismatch summed over the edge, below 1e-12). */
+ * found by Newton's method from the edges' midpoints (at most 50 steps),
+ * halving a step that does not shorten the chain (at most 40 times) until
+ * the cosine mismatch is below 1e-8, full steps after that.
+ * Returns 1 when converged (every edge's cosine mismatch below 1e-12); 0
+ * when not, or when a leg shrinks below OR_LEG_MIN: the minimum is then at
+ * a kink of the length (two consecutive edge lines meet), where Keller's
+ * law has no solution. */
 static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
   for (int i = 0; i < m; ++i) t[i] = 0.5 * E[i]->len;
   double Lc = chain_length(E, m, T, R, t);
-  for (int it = 0; it < 200; ++it) {
+  for (int it = 0; it < 50; ++it) {
     v3 X[OR_MAX_REFL + 2];
     X[0] = T;
     for (int i = 0; i < m; ++i) X[i + 1] = add(E[i]->p0, scl(E[i]->e, t[i]));
@@ -1570,7 +1614,7 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
     for (int j = 0; j <= m; ++j) {  /* leg j: X[j] -> X[j+1]; moves with t[j-1] and t[j] */
       v3 d = sub(X[j + 1], X[j]);
       double l = norm(d);
-      if (!(l > 0)) return 0;
+      if (!(l > OR_LEG_MIN)) return 0;
       v3 u = scl(d, 1.0 / l);
       int a = j - 1, b = j;
       double ca = a >= 0 ? dot(E[a]->e, u) : 0.0, cb = b < m ? dot(E[b]->e, u) : 0.0;
@@ -1588,10 +1632,12 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
     double mg[3] = {-g[0], -g[1], -g[2]}, dx[3];
     if (!solve_small(m, H, mg, dx)) return 0;
     double step = 1.0, tn[3];
-    for (int k = 0; k < 60; ++k) {
+    for (int k = 0; k < 40; ++k) {
       for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
       double Ln = chain_length(E, m, T, R, tn);
-      if (Ln <= Lc) { Lc = Ln; break; }
+      /* near the minimum (mismatch below 1e-8) the full Newton step is taken:
+       * the length it saves is below the length's own rounding there */
+      if (Ln <= Lc || gmax < 1e-8) { Lc = Ln; break; }
       step *= 0.5;
     }
     double dmax = 0.0;
@@ -1602,7 +1648,9 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
 }
 
 /* Paths Tx -> Q_1 -> ... -> Q_m -> Rx over m pairwise distinct wedges
- * (m = 2 or 3), consecutive wedges sharing no face. Each Q_i is a Keller
+ * (m = 2 or 3), consecutive wedges sharing no vertex (share_vertex), not on
+ * one line (collinear_edges), neither edge in a face plane of the other
+ * (in_face_plane). Each Q_i is a Keller
  * point (keller_points) strictly inside its edge; at every wedge the
  * previous point (Tx or Q_{i-1}) and the next point (Q_{i+1} or Rx) lie in
  * the exterior and the next point lies beyond the incident shadow boundary
@@ -1645,11 +1693,11 @@ int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32
     for (w[0] = 0; w[0] < nw; ++w[0])
       for (w[1] = 0; w[1] < nw; ++w[1])
         for (w[2] = 0; w[2] < (m == 3 ? nw : 1); ++w[2]) {
-          /* pairwise distinct; consecutive wedges share no face */
+          /* pairwise distinct; consecutive wedges share no vertex, are not on one line */
           int ok = w[0] != w[1] && (m < 3 || (w[2] != w[0] && w[2] != w[1]));
           for (int i = 0; ok && i + 1 < m; ++i) {
             const owedge *A = &W[w[i]], *B = &W[w[i + 1]];
-            if (A->ta == B->ta || A->ta == B->tb || A->tb == B->ta || A->tb == B->tb) ok = 0;
+            if (share_vertex(A, B) || collinear_edges(A, B) || in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;
           }
           if (!ok) continue;
           const owedge* E[3] = {&W[w[0]], &W[w[1]], m == 3 ? &W[w[2]] : NULL};

@@ -1890,6 +1890,9 @@ static int frame_finish(dcem_scene* s, const float* tx, int32_t ntx, const float
     S.child_rays = (int32_t)std::min<unsigned long long>(sp, 0x7fffffffull);
   }
   S.keys_reused = (int32_t)c[0].n_val_reused;
+  S.diff_candidates = (int32_t)std::min(c[0].n_dsurv, 0x7fffffffu);
+  S.diff_pairs = (int32_t)std::min(c[0].n_dpair, 0x7fffffffu);
+  S.diff_triples = (int32_t)std::min(c[0].n_dtrip, 0x7fffffffu);
   S.tri_tests = (int64_t)c[0].tri_tests;
   S.stack_overflow = (int32_t)c[0].stack_overflow;
   S.coherent = coherent ? 1 : 0;

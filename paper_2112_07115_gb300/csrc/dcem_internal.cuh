@@ -29,6 +29,8 @@ constexpr int kDiffBit = 0x20000000;    // interaction id flag: diffraction at w
 // in the plane normal to e, n = exterior angle / pi, the two faces.
 struct Wedge {
   double p0[3], e[3], t0[3], y0[3];
+  double p1[3];  // the edge's end vertex (p0 its start)
+  double tB[3];  // face n's direction normal to the edge (t0: face 0's)
   double len, n;
   int ta, tb;
 };

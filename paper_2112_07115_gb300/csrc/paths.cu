@@ -920,8 +920,10 @@ __global__ void k_wedge_geom(const float4* __restrict__ tris, const int* __restr
     }
     y0 = y0 * -1.0;  // the exterior runs away from face n
     W.p0[0] = p0.x; W.p0[1] = p0.y; W.p0[2] = p0.z;
+    W.p1[0] = vb.x; W.p1[1] = vb.y; W.p1[2] = vb.z;
     W.e[0] = e.x; W.e[1] = e.y; W.e[2] = e.z;
     W.t0[0] = t0.x; W.t0[1] = t0.y; W.t0[2] = t0.z;
+    W.tB[0] = tB.x; W.tB[1] = tB.y; W.tB[2] = tB.z;
     W.y0[0] = y0.x; W.y0[1] = y0.y; W.y0[2] = y0.z;
     W.len = len;
     W.n = 2.0 - alpha / M_PI;
@@ -1296,11 +1298,13 @@ __device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned l
 // diffraction of order 2 and 3 (Sec. III step 5; the paper's bound is 3)
 // ---------------------------------------------------------------------------
 // Paths Tx -> Q_1 -> .. -> Q_m -> Rx over m pairwise distinct wedges,
-// consecutive ones sharing no face. Per frame: the ordered wedge pairs that
-// can start a path from a transmitter (k_diff_pairs), for m = 3 the triples
-// built from them (k_diff_triples), then every (sequence, receiver) through
-// an FP32 pre-test at the last wedge (k_diff_multi_pre). The pre-tests only
-// reject what the FP64 test rejects too (margins above FP32 rounding); the
+// consecutive ones sharing no vertex, not on one line, neither edge in a
+// face plane of the other. Per frame: the
+// ordered wedge pairs that can start a path from a transmitter
+// (k_diff_pairs), for m = 3 the triples built from them (k_diff_triples),
+// then every (sequence, receiver) through an FP32 pre-test
+// (k_diff_multi_pre). The pre-tests only reject what the FP64 test rejects
+// too (margins above FP32 rounding); the
 // survivors go to the diffraction survivor list with their order in the top
 // bits: 01 order 2, 11 order 3 (10 is a reflection pair, 00 first order).
 constexpr unsigned long long kKindShift = 62;
@@ -1408,8 +1412,53 @@ __device__ __forceinline__ bool shadow_meets(const WedgeF& W, float3 X, float3 P
   return sector_meets(W, lo, hi, tol, m, P, Q);
 }
 
+// Do two edges share an end vertex (identical coordinates)? Consecutive
+// wedges of a chain may not (which includes sharing a face): the length's
+// minimum then tends to the common corner, or the leg between them runs
+// along a face they bound.
+__device__ __forceinline__ bool share_vertex(const Wedge& A, const Wedge& B) {
+  const double* a[2] = {A.p0, A.p1};
+  const double* b[2] = {B.p0, B.p1};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (a[i][0] == b[j][0] && a[i][1] == b[j][1] && a[i][2] == b[j][2]) return true;
+  return false;
+}
+
+// Do two edges lie on one line (directions parallel to 1e-9, the second's
+// start within 1e-9 m, relative to the coordinates' size, of the first's
+// line)? Consecutive wedges of a chain may not: the leg between them would
+// run along both edges (no Keller points: the length's minimum is where it
+// vanishes). Decided in FP64 from the wedges' frames.
+__device__ __forceinline__ bool collinear_edges(const Wedge& A, const Wedge& B) {
+  d3w ea = D3(A.e[0], A.e[1], A.e[2]), eb = D3(B.e[0], B.e[1], B.e[2]);
+  d3w c = crossw(ea, eb);
+  if (sqrt(dotw(c, c)) > 1e-9) return false;
+  d3w pa = D3(A.p0[0], A.p0[1], A.p0[2]), pb = D3(B.p0[0], B.p0[1], B.p0[2]);
+  d3w q = crossw(pb - pa, ea);
+  double sa = fmax(fabs(pa.x), fmax(fabs(pa.y), fabs(pa.z))), sb = fmax(fabs(pb.x), fmax(fabs(pb.y), fabs(pb.z)));
+  return sqrt(dotw(q, q)) <= 1e-9 * (1.0 + sa + sb);
+}
+
+// Does edge B lie in the plane of a face of wedge A (both ends within 1e-9 m,
+// relative to the coordinates' size)? Then so does the leg between them,
+// along that face (grazing) or its extension beyond A's edge, where no source
+// in A's exterior has its shadow boundary crossed: no chain passes.
+__device__ __forceinline__ bool in_face_plane(const Wedge& A, const Wedge& B) {
+  d3w e = D3(A.e[0], A.e[1], A.e[2]), pa = D3(A.p0[0], A.p0[1], A.p0[2]);
+  d3w b0 = D3(B.p0[0], B.p0[1], B.p0[2]) - pa, b1 = D3(B.p1[0], B.p1[1], B.p1[2]) - pa;
+  double sa = fmax(fabs(pa.x), fmax(fabs(pa.y), fabs(pa.z)));
+  double sb = fmax(fabs(B.p0[0]), fmax(fabs(B.p0[1]), fabs(B.p0[2])));
+  double tol = 1e-9 * (1.0 + sa + sb);
+  d3w f[2] = {crossw(e, D3(A.t0[0], A.t0[1], A.t0[2])), crossw(e, D3(A.tB[0], A.tB[1], A.tB[2]))};
+  for (int q = 0; q < 2; ++q)
+    if (fabs(dotw(f[q], b0)) <= tol && fabs(dotw(f[q], b1)) <= tol) return true;
+  return false;
+}
+
 // Ordered pairs (w1, w2) per transmitter that can start a path of order
-// >= 2: distinct, no shared face, each edge partly in the other's exterior,
+// >= 2: distinct, no shared vertex, not on one line, neither edge in a face
+// plane of the other, each edge partly in the other's exterior,
 // the transmitter outside w1, and some point of edge 2 beyond the incident
 // shadow boundary of the transmitter at w1. With order 3, the relation
 // (the first three conditions) also goes to a bit matrix for the triples.
@@ -1427,7 +1476,8 @@ __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int ntx) {
       w1 = (int)(r / nw);
       w2 = (int)(r - (long)w1 * nw);
       const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
-      bool rel = w1 != w2 && A.ta != B.ta && A.ta != B.tb && A.tb != B.ta && A.tb != B.tb;
+      bool rel = w1 != w2 && !share_vertex(A, B) && !collinear_edges(A, B) && !in_face_plane(A, B) &&
+                 !in_face_plane(B, A);
       if (rel) {
         WedgeF fa = wedge_f(A), fb = wedge_f(B);
         float3 pa, qa;
@@ -1488,9 +1538,223 @@ __global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
   }
 }
 
+// FP32 Keller points of a chain (the pre-test's estimate): Newton's method
+// as in keller_chain, in FP32, from the edges' midpoints. Returns true when
+// the cosine mismatch fell below 2e-6 at every edge, or a full Newton step
+// would move no point by more than step_tol (metres).
+__device__ __forceinline__ float3 edge_point(const WedgeF& W, float t) {
+  return f3(W.p0.x + W.e.x * t, W.p0.y + W.e.y * t, W.p0.z + W.e.z * t);
+}
+__device__ __forceinline__ float chain_len32(const WedgeF* W, int m, float3 T, float3 R, const float* t) {
+  float3 prev = T;
+  float L = 0.0f;
+  for (int i = 0; i < m; ++i) {
+    float3 q = edge_point(W[i], t[i]);
+    float3 d = f3(q.x - prev.x, q.y - prev.y, q.z - prev.z);
+    L += sqrtf(fdot3(d, d));
+    prev = q;
+  }
+  float3 d = f3(R.x - prev.x, R.y - prev.y, R.z - prev.z);
+  return L + sqrtf(fdot3(d, d));
+}
+__device__ bool keller32(const WedgeF* W, int m, float3 T, float3 R, float* t, float step_tol) {
+  for (int i = 0; i < m; ++i) t[i] = 0.5f * W[i].len;
+  float Lc = chain_len32(W, m, T, R, t);
+  for (int it = 0; it < 30; ++it) {
+    float3 X[5];
+    X[0] = T;
+    for (int i = 0; i < m; ++i) X[i + 1] = edge_point(W[i], t[i]);
+    X[m + 1] = R;
+    float g[3] = {0.0f, 0.0f, 0.0f}, H[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    for (int j = 0; j <= m; ++j) {
+      float3 d = f3(X[j + 1].x - X[j].x, X[j + 1].y - X[j].y, X[j + 1].z - X[j].z);
+      float l = sqrtf(fdot3(d, d));
+      if (!(l > 0.0f)) return false;
+      float3 u = f3(d.x / l, d.y / l, d.z / l);
+      int ia = j - 1, ib = j;
+      float ca = ia >= 0 ? fdot3(W[ia].e, u) : 0.0f, cb = ib < m ? fdot3(W[ib].e, u) : 0.0f;
+      if (ib < m) {
+        g[ib] += cb;
+        H[ib][ib] += (1.0f - cb * cb) / l;
+      }
+      if (ia >= 0) {
+        g[ia] -= ca;
+        H[ia][ia] += (1.0f - ca * ca) / l;
+      }
+      if (ia >= 0 && ib < m) {
+        float h = -(fdot3(W[ia].e, W[ib].e) - ca * cb) / l;
+        H[ia][ib] += h;
+        H[ib][ia] += h;
+      }
+    }
+    float gmax = 0.0f;
+    for (int i = 0; i < m; ++i) gmax = fmaxf(gmax, fabsf(g[i]));
+    if (gmax < 2e-6f) return true;
+    float A[3][4], dx[3];
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) A[i][j] = H[i][j];
+      A[i][m] = -g[i];
+    }
+    for (int c = 0; c < m; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (fabsf(A[r][c]) > fabsf(A[piv][c])) piv = r;
+      if (!(fabsf(A[piv][c]) > 1e-30f)) return false;
+      if (piv != c)
+        for (int j = 0; j <= m; ++j) {
+          float x = A[c][j];
+          A[c][j] = A[piv][j];
+          A[piv][j] = x;
+        }
+      for (int r = c + 1; r < m; ++r) {
+        float f = A[r][c] / A[c][c];
+        for (int j = c; j <= m; ++j) A[r][j] -= f * A[c][j];
+      }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      float v = A[i][m];
+      for (int j = i + 1; j < m; ++j) v -= A[i][j] * dx[j];
+      dx[i] = v / A[i][i];
+    }
+    float dfull = 0.0f;
+    for (int i = 0; i < m; ++i) dfull = fmaxf(dfull, fabsf(dx[i]));
+    float step = 1.0f, tn[3] = {t[0], t[1], t[2]};
+    bool moved = false;
+    for (int q = 0; q < 30; ++q) {
+      for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
+      float Ln = chain_len32(W, m, T, R, tn);
+      if (Ln <= Lc * (1.0f + 1e-6f)) {
+        Lc = fminf(Lc, Ln);
+        moved = true;
+        break;
+      }
+      step *= 0.5f;
+    }
+    if (!moved) return gmax < 1e-4f;
+    for (int i = 0; i < m; ++i) t[i] = tn[i];
+    // the full Newton step (the quadratic model's distance to the
+    // stationary point) below step_tol: close enough for the margins
+    if (dfull < step_tol) return true;
+  }
+  return false;
+}
+
+// Position margin of the FP32 Keller estimate: 5 cm plus 1e-5 of the
+// coordinates' size (FP32 rounding of the geometry and of the solve).
+__device__ __forceinline__ float chain_margin(float3 T, float3 R) {
+  return 0.05f + 1e-5f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fabsf(R.x) + fabsf(R.y) + fabsf(R.z));
+}
+
+// Is the leg o -> o + dv certainly blocked, whatever its true position within
+// `delta` of this one? Only a triangle (other than ex0 .. ex3) that the leg
+// crosses strictly inside counts: the crossing must lie within the leg's
+// occlusion range (eps_occ, 1 - eps_occ) and at least mu from every edge of
+// the triangle in its plane, mu = delta (1 + 1/|cos|) + FP32 slack, |cos|
+// the leg's angle to the triangle's normal: a leg displaced by delta moves
+// its crossing by at most that much. So the exact leg (FP32 any-hit of the
+// FP64 points) is blocked too, and the chain is rejected either way. An
+// overflow of the stack or of the visit limit answers "not certain".
+__device__ bool leg_surely_blocked(const Bvh& bvh, float3 o, float3 dv, float delta, float eps_occ, int ex0,
+                                   int ex1, int ex2, int ex3, TStack& st) {
+  const float dl = sqrtf(fdot3(dv, dv));
+  if (!(dl > 0.0f)) return false;
+  const float slack = 2e-3f + 1e-6f * (fabsf(o.x) + fabsf(o.y) + fabsf(o.z) + dl);
+  RayPre rp = ray_pre(o, dv);
+  st.reset();
+  if (bvh.root1 != kEmpty && !st.push(bvh.root1)) return false;
+  int cur = bvh.root0;
+  for (int visits = 0;; ++visits) {
+    if (visits > bvh.max_visits) return false;
+    if (cur == kEmpty) {
+      if (st.empty()) break;
+      cur = st.pop();
+      continue;
+    }
+    if (cur >= 0) {
+      const float4* n = bvh.nodes + 4 * (size_t)DCEM_IDX(cur, bvh.nnodes);
+      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+      float tn0, tn1;
+      bool h0 = slab(rp, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, 1.0f, tn0);
+      bool h1 = slab(rp, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, 1.0f, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        if (!st.push(c1)) return false;
+        cur = c0;
+      } else {
+        cur = h0 ? c0 : h1 ? c1 : kEmpty;
+      }
+      continue;
+    }
+    float3 v0, v1, v2;
+    int id;
+    load_tri(bvh.tris, DCEM_IDX(~cur, bvh.ntris), v0, v1, v2, id);
+    cur = kEmpty;
+    if (id == ex0 || id == ex1 || id == ex2 || id == ex3) continue;
+    float3 e01 = f3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z), e12 = f3(v2.x - v1.x, v2.y - v1.y, v2.z - v1.z);
+    float3 e20 = f3(v0.x - v2.x, v0.y - v2.y, v0.z - v2.z);
+    float3 nv = cross3(e01, f3(-e20.x, -e20.y, -e20.z));
+    float nn = sqrtf(fdot3(nv, nv)), dn = fdot3(dv, nv);
+    if (!(fabsf(dn) > 1e-4f * dl * nn)) continue;  // nearly parallel: not certain
+    float u = fdot3(f3(v0.x - o.x, v0.y - o.y, v0.z - o.z), nv) / dn;
+    float mu = delta * (1.0f + dl * nn / fabsf(dn)) + slack;
+    float nu = mu / dl;
+    if (!(u > eps_occ + nu && u < 1.0f - eps_occ - nu)) continue;
+    float3 H = f3(o.x + dv.x * u, o.y + dv.y * u, o.z + dv.z * u);
+    float d0 = fdot3(cross3(e01, f3(H.x - v0.x, H.y - v0.y, H.z - v0.z)), nv) / (sqrtf(fdot3(e01, e01)) * nn);
+    float d1 = fdot3(cross3(e12, f3(H.x - v1.x, H.y - v1.y, H.z - v1.z)), nv) / (sqrtf(fdot3(e12, e12)) * nn);
+    float d2 = fdot3(cross3(e20, f3(H.x - v2.x, H.y - v2.y, H.z - v2.z)), nv) / (sqrtf(fdot3(e20, e20)) * nn);
+    if (fminf(d0, fminf(d1, d2)) > mu) return true;
+  }
+  return false;
+}
+
+// The FP32 estimate of a chain against the FP64 rules, with margins: false
+// only when the exact test rejects the chain too -- a Keller point off its
+// edge by more than the position margin, or at some wedge a point inside the
+// wedge or the shadow rule missed by more than the angle's rounding bound
+// plus the angle the position margin subtends at that point's distance from
+// the edge.
+// *solved: the estimate converged (t then holds it) -- only then can it
+// reject anything.
+__device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float* t, bool* solved) {
+  float mt = chain_margin(T, R);
+  *solved = keller32(W, m, T, R, t, 0.1f * mt);
+  if (!*solved) return true;
+  float3 X[5];
+  X[0] = T;
+  for (int i = 0; i < m; ++i) {
+    if (t[i] < -mt || t[i] > W[i].len + mt) return false;
+    X[i + 1] = edge_point(W[i], t[i]);
+  }
+  X[m + 1] = R;
+  for (int i = 0; i < m; ++i) {
+    float a2[2], tl[2];
+    bool sure[2];
+    for (int q = 0; q < 2; ++q) {
+      float r, dist;
+      float2 p = wedge_plane(W[i], X[i + 2 * q], r, dist);
+      float3 d = f3(p.x * W[i].t0.x + p.y * W[i].y0.x, p.x * W[i].t0.y + p.y * W[i].y0.y,
+                    p.x * W[i].t0.z + p.y * W[i].y0.z);
+      a2[q] = wedge_angle32(d, W[i].t0, W[i].y0, r, dist, sure[q], tl[q]);
+      // points that move with the estimate (the Keller points) carry its margin
+      bool moves = q == 0 ? i > 0 : i < m - 1;
+      if (moves) {
+        if (!(r > 4.0f * mt)) sure[q] = false;
+        else tl[q] += 2.0f * mt / r;
+      }
+    }
+    if ((sure[0] && a2[0] > W[i].npi + tl[0]) || (sure[1] && a2[1] > W[i].npi + tl[1])) return false;
+    if (sure[0] && sure[1] && fabsf(a2[1] - a2[0]) < 3.14159265f - (tl[0] + tl[1])) return false;
+  }
+  return true;
+}
+
 // Every (sequence, receiver): the receiver outside the last wedge and some
 // point of the previous edge beyond its shadow boundary at the last wedge.
 __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
+  extern __shared__ int sstk[];
+  TStack st;
+  bind_stack(st, sstk, kStackTrace);
   const long n2 = a.diff_order >= 2 ? (long)min(a.ctr->n_dpair, a.dseq2_cap) : 0;
   const long n3 = a.diff_order >= 3 ? (long)min(a.ctr->n_dtrip, a.dseq3_cap) : 0;
   const long total = (n2 + n3) * a.nrx;
@@ -1512,6 +1776,34 @@ __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
       float3 R = f3(rv.x, rv.y, rv.z), P, Q;
       edge_ends(fp, P, Q);
       keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+      if (keep) {
+        WedgeF Wc[3];
+        Wc[0] = wedge_f(a.wedges[sq.y]);
+        Wc[1] = three ? fp : fl;  // order 2: (w1, last); order 3: (w1, previous, last)
+        Wc[2] = fl;
+        float4 tv = a.txs[sq.x];
+        const int m = three ? 3 : 2;
+        const float3 T = f3(tv.x, tv.y, tv.z);
+        float t[3];
+        bool solved;
+        keep = chain_possible(Wc, m, T, R, t, &solved);
+        if (keep && solved) {  // a leg certainly blocked rejects the chain
+          const int w[3] = {sq.y, sq.z, sq.w};
+          const float delta = chain_margin(T, R);
+          float3 X[5];
+          X[0] = T;
+          for (int i = 0; i < m; ++i) X[i + 1] = edge_point(Wc[i], t[i]);
+          X[m + 1] = R;
+          for (int j = 0; keep && j <= m; ++j) {
+            const Wedge* A = j >= 1 ? &a.wedges[w[j - 1]] : nullptr;
+            const Wedge* B = j < m ? &a.wedges[w[j]] : nullptr;
+            float3 dv = f3(X[j + 1].x - X[j].x, X[j + 1].y - X[j].y, X[j + 1].z - X[j].z);
+            if (leg_surely_blocked(a.bvh, X[j], dv, delta, a.eps_occ, A ? A->ta : -1, A ? A->tb : -1,
+                                   B ? B->ta : -1, B ? B->tb : -1, st))
+              keep = false;
+          }
+        }
+      }
       code = ((unsigned long long)ei * a.nrx + r) | (three ? kMulti3 : kMulti2);
     }
     unsigned mk = __ballot_sync(0xffffffffu, keep);
@@ -1542,12 +1834,17 @@ __device__ __forceinline__ double chain_len(const Wedge* const* E, int m, d3w T,
 
 // Keller points: the stationary point (the minimum: the length is convex in
 // t) of the unfolded length over the edge parameters, by Newton's method
-// from the edges' midpoints, a step that does not shorten the chain halved;
-// converged when every edge's cosine mismatch is below 1e-12.
+// from the edges' midpoints (at most 50 steps), a step that does not
+// shorten the chain halved (at most 40 times) until the cosine mismatch is
+// below 1e-8, full steps after that; converged when every edge's mismatch is
+// below 1e-12. A leg shorter than kLegMin stops it: the
+// minimum is then at a kink of the length (consecutive edge lines meet),
+// where Keller's law has no solution.
+constexpr double kLegMin = 1e-6;
 __device__ bool keller_chain(const Wedge* const* E, int m, d3w T, d3w R, double* t) {
   for (int i = 0; i < m; ++i) t[i] = 0.5 * E[i]->len;
   double Lc = chain_len(E, m, T, R, t);
-  for (int it = 0; it < 200; ++it) {
+  for (int it = 0; it < 50; ++it) {
     d3w X[5];
     X[0] = T;
     for (int i = 0; i < m; ++i)
@@ -1557,7 +1854,7 @@ __device__ bool keller_chain(const Wedge* const* E, int m, d3w T, d3w R, double*
     for (int j = 0; j <= m; ++j) {
       d3w d = X[j + 1] - X[j];
       double l = sqrt(dotw(d, d));
-      if (!(l > 0.0)) return false;
+      if (!(l > kLegMin)) return false;
       d3w u = d * (1.0 / l);
       int ia = j - 1, ib = j;
       d3w ea = ia >= 0 ? D3(E[ia]->e[0], E[ia]->e[1], E[ia]->e[2]) : D3(0, 0, 0);
@@ -1608,10 +1905,12 @@ __device__ bool keller_chain(const Wedge* const* E, int m, d3w T, d3w R, double*
       dx[i] = v / A[i][i];
     }
     double step = 1.0, tn[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < 60; ++q) {
+    for (int q = 0; q < 40; ++q) {
       for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
       double Ln = chain_len(E, m, T, R, tn);
-      if (Ln <= Lc) {
+      // near the minimum the full step: the length it saves is below the
+      // length's rounding there
+      if (Ln <= Lc || gmax < 1e-8) {
         Lc = Ln;
         break;
       }
@@ -1792,10 +2091,12 @@ __global__ void __launch_bounds__(256) k_diffract_pre(PathArgs a, int nlinks) {
 
 // Pass 2 over the survivors: the exact FP64 test, the occlusion legs and the
 // UTD field. The SM's FP64 pipe is narrow and a warp instruction costs it the
-// same whatever the number of active lanes, so the survivors are dealt one
-// warp per SM (survivor i to block i mod grid): every SM gets an equal share,
-// packed into one warp, instead of a few SMs taking whole batches.
-__global__ void __launch_bounds__(32) k_diffract(PathArgs a) {
+// same whatever the number of active lanes, so survivor i goes to block
+// i mod grid, slot i / grid: every SM gets an equal share, packed into its
+// first warp while there are few survivors and into more warps as they grow
+// (orders 2 and 3 can leave many), instead of a few SMs taking whole batches.
+constexpr int kDiffThreads = 256;
+__global__ void __launch_bounds__(kDiffThreads) k_diffract(PathArgs a) {
   extern __shared__ int sstk[];
   TStack st;
   bind_stack(st, sstk, kStackTrace);
@@ -1971,9 +2272,9 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
       if (a.drel) cudaMemsetAsync(a.drel, 0, sizeof(unsigned) * (((size_t)a.nw * a.nw + 31) / 32), st);
       k_diff_pairs<<<(int)std::max<long>(std::min<long>((tp + 255) / 256, 8L * sms), 1), 256, 0, st>>>(a, ntx);
       if (a.diff_order >= 3) k_diff_triples<<<8 * sms, 256, 0, st>>>(a);
-      k_diff_multi_pre<<<8 * sms, 256, 0, st>>>(a);
+      k_diff_multi_pre<<<8 * sms, 256, 256 * kStackTrace * sizeof(int), st>>>(a);
     }
-    k_diffract<<<sms, 32, 32 * kStackTrace * sizeof(int), st>>>(a);
+    k_diffract<<<sms, kDiffThreads, kDiffThreads * kStackTrace * sizeof(int), st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -74,7 +74,8 @@ class Stats(C.Structure):
                 ("ms_stage", C.c_float * 10), ("bvh_cost_ratio", C.c_float),
                 ("max_segment_nodes", C.c_int32), ("trace_kernel", C.c_int32),
                 ("graph_replayed", C.c_int32), ("paths_sticky", C.c_int32), ("child_rays", C.c_int32),
-                ("keys_reused", C.c_int32)]
+                ("keys_reused", C.c_int32), ("diff_candidates", C.c_int32), ("diff_pairs", C.c_int32),
+                ("diff_triples", C.c_int32)]
 
 
 class Result(C.Structure):
