@@ -344,8 +344,8 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
  * length), kept when every Q_i lies inside
  * its edge, at every wedge the previous and the next point lie in the
  * exterior and the next point beyond the incident shadow boundary of the
- * previous one, no leg between two wedges runs within 1e-6 rad of a face of
- * either, and every leg is unoccluded (the faces of the wedges at its ends
+ * previous one, neither edge of consecutive wedges lies in a face plane of
+ * the other, and every leg is unoccluded (the faces of the wedges at its ends
  * excluded). Field: the UTD coefficient of each wedge applied to the field
  * the previous leg brings, with the astigmatic spreading of an
  * edge-diffracted wave (Kouyoumjian & Pathak 1974, straight edge: a caustic

@@ -1512,7 +1512,6 @@ int64_t or_diffract_refl(const float* tris, const int32_t* tri_mat, const int32_
 /* ------------------------------------------------------------------------ */
 /* Diffraction of order 2 and 3 (Sec. III step 5; the paper's bound is 3)    */
 /* ------------------------------------------------------------------------ */
-#define OR_GRAZE 1e-6  /* a leg between two wedges closer than this to a face (rad) grazes it */
 #define OR_LEG_MIN 1e-6  /* shortest leg of a diffraction chain while its Keller points are sought [m] */
 
 /* Do two edges share an end vertex (identical input coordinates)? Consecutive
@@ -1654,9 +1653,7 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
  * point (keller_points) strictly inside its edge; at every wedge the
  * previous point (Tx or Q_{i-1}) and the next point (Q_{i+1} or Rx) lie in
  * the exterior and the next point lies beyond the incident shadow boundary
- * of the previous one (or_diffract's rule, edge by edge); a leg between two
- * wedges makes an angle above OR_GRAZE with the faces of both (it does not
- * run along a face, as between two edges of one planar face); every leg is
+ * of the previous one (or_diffract's rule, edge by edge); every leg is
  * unoccluded (the faces of the wedges at its ends excluded). Field: at each
  * wedge the UTD coefficient of or_diffract (Luebbers' face factors) acts on
  * the field the previous leg brings, in the edge-fixed bases of that wedge.
@@ -1723,8 +1720,7 @@ int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32
             if (!(ell[j] > 1e-9)) ok = 0;
           }
           if (!ok) continue;
-          /* exterior and shadow rule at every wedge; a leg between two wedges
-           * may not run along a face of either (grazing: within 1e-6 rad) */
+          /* exterior and shadow rule at every wedge */
           double phip[3], phi[3];
           for (int i = 0; ok && i < m; ++i) {
             phip[i] = wedge_angle(E[i], X[i]);
@@ -1734,13 +1730,6 @@ int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32
             else {
               if (fabs(fabs(phi[i] - phip[i]) - M_PI) <= ang_eps) fl |= ORF_VAL_PARAM;
               if (!(fabs(phi[i] - phip[i]) > M_PI)) ok = 0;
-            }
-            for (int q = 0; ok && q < 2; ++q) {
-              if (q == 0 ? i == 0 : i == m - 1) continue;  /* the transmitter's and receiver's legs */
-              double a = q == 0 ? phip[i] : phi[i];
-              double g = fmin(a, nn * M_PI - a);
-              if (fabs(g - OR_GRAZE) <= ang_eps) fl |= ORF_VAL_PARAM;
-              if (!(g > OR_GRAZE)) ok = 0;
             }
           }
           if (!ok) continue;

@@ -1309,7 +1309,6 @@ __device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned l
 // bits: 01 order 2, 11 order 3 (10 is a reflection pair, 00 first order).
 constexpr unsigned long long kKindShift = 62;
 constexpr unsigned long long kMulti2 = 1ull << kKindShift, kMulti3 = 3ull << kKindShift;
-constexpr double kGraze = 1e-6;  // a leg between two wedges this close to a face (rad) grazes it
 
 struct WedgeF {  // a wedge's frame in FP32 for the pre-tests
   float3 p0, e, t0, y0;
@@ -1973,8 +1972,6 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
     const double nn = E[i]->n;
     if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) return;
     if (!(fabs(phi[i] - phip[i]) > M_PI)) return;
-    if (i > 0 && !(fmin(phip[i], nn * M_PI - phip[i]) > kGraze)) return;
-    if (i < m - 1 && !(fmin(phi[i], nn * M_PI - phi[i]) > kGraze)) return;
   }
   for (int j = 0; j <= m; ++j) {
     int e0 = j >= 1 ? E[j - 1]->ta : -1, e1 = j >= 1 ? E[j - 1]->tb : -1;

@@ -2,7 +2,7 @@
 against the oracle's or_diffract_multi: the same wedge sequences, the same
 Keller points, lengths and fields (within 1e-6), and the frame's received
 power with every mechanism summed. Decisions the oracle flags as within the
-FP margins (a Keller point at an edge's end, the shadow or grazing rule at its
+FP margins (a Keller point at an edge's end, the shadow rule at its
 threshold, an occlusion near a leg's end) may differ."""
 import numpy as np
 import pytest

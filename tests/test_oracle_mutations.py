@@ -64,10 +64,10 @@ MUTANTS = [
     # the reflection after a diffraction uses the bounce basis of the outgoing leg
     ("diffraction_reflection_basis", "v3 pin = cross(sv, din), pout = cross(sv, dout);\n          int mj",
      "v3 pin = cross(sv, dout), pout = cross(sv, din);\n          int mj"),
-    # diffraction of order 2 and 3: Keller points, grazing legs, astigmatic spreading
+    # diffraction of order 2 and 3: Keller points, chains in a face plane, astigmatic spreading
     ("keller_gradient_sign", "if (a >= 0) { g[a] -= ca; H[a][a] += (1.0 - ca * ca) / l; }",
      "if (a >= 0) { g[a] += ca; H[a][a] += (1.0 - ca * ca) / l; }"),
-    ("grazing_legs_kept", "if (!(g > OR_GRAZE)) ok = 0;", "if (0) ok = 0;"),
+    ("face_plane_chains_kept", "|| in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;", ") ok = 0;"),
     ("caustic_on_the_edge", "rho1 = s;\n            dir1 = ph;", "rho1 = rhoe + s;\n            dir1 = ph;"),
     ("principal_direction", "dir1 = ph;\n            rho2 = rhoe + s;", "dir1 = bd;\n            rho2 = rhoe + s;"),
     ("spherical_spreading", "double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);",

@@ -796,8 +796,9 @@ def _composition_check(O, sc, m, prm):
 @pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
 def test_double_diffraction_composes_from_first_order(oracle_mod, mat):
     """Two thin walls, one reaching south from y = 0 and one north from y = 5: no direct or
-    first-order path, one double diffraction around the walls' ends. The edges of one wall's end
-    face are not a path (the leg would run along that face)."""
+    first-order path, one double diffraction around the walls' ends. The two edges of one wall's
+    end face are not a chain (each lies in a face plane of the other: the leg would run along
+    that face)."""
     O = oracle_mod
     tris = _slab(0.0, 0.5, -50.0, 0.0) + _slab(10.0, 10.5, 5.0, 55.0)
     sc = scenes._static_scene("walls", tris, [mat] * len(tris), (-10.0, -20.0, 2.0), [(20.0, 20.0, 2.0)])
