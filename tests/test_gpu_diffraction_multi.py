@@ -166,3 +166,71 @@ def test_order_one_is_unchanged(cuda):
         out.append((fr.paths.tobytes(), fr.p_coh_dbm.tobytes()))
         s.close()
     assert out[0] == out[1]
+
+
+def test_links_equal_single_transmitter_frames(cuda):
+    """Two transmitters in one frame (dcem_trace_links): the wedge pairs and
+    triples are formed per transmitter, and each transmitter's links equal its
+    own single-transmitter frame bit for bit (paths of every order, powers)."""
+    torch = cuda
+    sc = _boxes(10)
+    rays = scenes.fibonacci_sphere(20_000)
+    prm = P.gpu_params(sc, max_refl=3)
+    tx2 = sc.tx + np.array([6.0, -9.0, 1.0], np.float32)
+    st = torch.cuda.current_stream().cuda_stream
+    sl = dcem.Scene.from_scene(sc, stream=st)
+    sl.set_ray_sets([rays, rays])
+    sl.set_diffraction(True)
+    sl.set_diffraction_order(3)
+    fl = sl.trace_links(np.stack([sc.tx, tx2]), sc.rx[0], prm)
+    one = dcem.Scene.from_scene(sc, stream=st)
+    one.set_rays(rays)
+    one.set_diffraction(True)
+    one.set_diffraction_order(3)
+    orders = set()
+    for t, tx in enumerate((sc.tx, tx2)):
+        single = one.trace(tx, sc.rx[0], prm)
+        p = fl.paths[fl.paths["tx"] == t].copy()
+        p["tx"] = 0
+        p["ray"] = np.where(p["ray"] >= 0, p["ray"] - t * rays.shape[0], -1)
+        assert p.tobytes() == single.paths.tobytes(), t
+        assert np.array_equal(fl.p_coh_dbm[t], single.p_coh_dbm)
+        for m in (2, 3):
+            if _of_order(single.paths, m).any():
+                orders.add(m)
+    assert orders == {2, 3}
+    sl.close()
+    one.close()
+
+
+@pytest.mark.parametrize("mode", [dcem.MODE_FULL, dcem.MODE_COHERENT])
+def test_batch_equals_single_scenes(cuda, mode):
+    """A batch of scenes with diffraction up to order 3 (one with moving
+    boxes): each scene's frame equals its own frame bit for bit."""
+    torch = cuda
+    st = torch.cuda.current_stream().cuda_stream
+    wl = [_boxes(10, n_frames=3), _boxes(6, n_moving=2, n_frames=3), _boxes(14, n_frames=3)]
+    rays = scenes.fibonacci_sphere(20_000)
+
+    def make(sc):
+        s = dcem.Scene.from_scene(sc, stream=st)
+        s.set_rays(rays)
+        s.set_diffraction(True)
+        s.set_diffraction_order(3)
+        return s
+    batched, alone = [make(sc) for sc in wl], [make(sc) for sc in wl]
+    b = dcem.Batch(batched, stream=st)
+    prm = dcem.default_params(max_refl=3, freq_hz=28e9, mode=mode)
+    for f in range(3):
+        b.update_transforms([sc.xf[f] if sc.nobj else None for sc in wl])
+        got = b.trace([sc.tx[None] for sc in wl], [sc.rx[f] for sc in wl], prm)
+        for sc, s, g in zip(wl, alone, got):
+            if sc.nobj:
+                s.update_transforms(sc.xf[f])
+            ref = s.trace_links(sc.tx[None], sc.rx[f], prm)
+            assert g.paths.tobytes() == ref.paths.tobytes(), (f, sc.nobj)
+            assert np.array_equal(g.p_coh_dbm, ref.p_coh_dbm)
+            assert _of_order(ref.paths, 2).any()
+    b.close()
+    for s in batched + alone:
+        s.close()
