@@ -539,7 +539,11 @@ def _device_result(nrx, max_paths, dev):
     return r, bufs
 
 
-def _mode_summary(ms, st, world, n_rays, dev):
+def _mode_summary(ms, st, world, n_rays, dev, workload=None, mode=None):
+    """Rates of timed frames (ms: CUDA-event times, st: their stats); with
+    `workload` and `mode`, the closest-hit kernel's ncu counters (DRAM and L2
+    bytes, L2 hit rate, warp execution efficiency) when a capture of the
+    current source exists."""
     t = max_over_ranks([sum(ms) / 1e3], dev)[0]
     K = len(ms)
     segs = float(np.mean([x["segments_traced"] for x in st]))
@@ -551,7 +555,10 @@ def _mode_summary(ms, st, world, n_rays, dev):
             "keys_reused_frac": round(float(np.mean([x["keys_reused"] / max(1, x["unique_candidates"])
                                                      for x in st])), 4),
             "closest_hit_ms": round(float(np.mean([x["ms_stage"]["trace"] for x in st])), 4),
-            "paths_per_frame": int(np.mean([x["paths_valid"] for x in st]))}
+            "paths_per_frame": int(np.mean([x["paths_valid"] for x in st])),
+            "closest_hit_measured": (_measured_forms("k_trace_q", workload, mode,
+                                                     float(np.mean([x["ms_stage"]["trace"] for x in st])),
+                                                     measured_peaks()[0]) if workload else None)}
 
 
 def run_toy(args, stream, dev, world, flush, rank, warmup=5):
@@ -579,7 +586,7 @@ def run_toy(args, stream, dev, world, flush, rank, warmup=5):
         prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=2)
         ms, st = _frames_timed(s, sc, frames, prm, stream, flush, xf_d, rx_d, res, warmup)
         s.close()
-        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev)
+        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev, "toy", name)
     out["coherent_speedup"] = round(out["coherent"]["frames_per_s"] / out["full"]["frames_per_s"], 3)
     if rank == 0:
         # every frame in order, coherent, against the oracle
@@ -629,7 +636,8 @@ def run_band(args, stream, dev, world, flush, rank, freq=5.9e9, warmup=5):
         s.set_rays(rays)
         prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=2)
         ms, st = _frames_timed(s, sc, frames, prm, stream, flush, xf_d, rx_d, res, warmup)
-        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev)
+        wl = "highway_5p9ghz" if abs(freq - 5.9e9) < 1e6 else None
+        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev, wl, name)
         if name == "coherent" and rank == 0:
             out["rx_power_err_db"] = power_error_vs_oracle(sc, s, frames[-1], max_paths, bufs[3], bufs[1], bufs[2],
                                                            res_n=st[-1])
@@ -664,7 +672,7 @@ def run_roadside(args, stream, dev, world, flush, rank, warmup=5):
         s.set_rays(rays)
         prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode, timing=2)
         ms, st = _frames_timed(s, sc, frames, prm, stream, flush, xf_d, rx_d, res, warmup)
-        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev)
+        out[name] = _mode_summary(ms, st, world, sc.n_rays, dev, "roadside", name)
         if name == "coherent" and rank == 0:
             out["rx_power_err_db"] = power_error_vs_oracle(sc, s, frames[-1], max_paths, bufs[3], bufs[1], bufs[2],
                                                            res_n=st[-1])
