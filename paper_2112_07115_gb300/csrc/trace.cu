@@ -63,7 +63,8 @@ __device__ __forceinline__ int fetch_warp(unsigned* counter, unsigned n) {
 template <bool kQ, bool kG = false, bool kT = false>
 __device__ __forceinline__ void trace_rays(const TraceArgs& a, const uint4* qn, const QFrame& qf, TStack& st,
                                            int qr0, int qr1) {
-  const int R = a.R, LS = a.LS;
+  const int R = a.R;
+  [[maybe_unused]] const int LS = a.LS;  // bounds of the checked build
   int nq, slot0 = 0, spawn_base = R;
   unsigned* work = &a.ctr->work_trace;
   if (kT) {
@@ -275,7 +276,8 @@ __global__ void __launch_bounds__(256) k_trace_batch(const TraceArgs* __restrict
     }
     const TraceArgs& a = tab[lo];
     const Bvh bvh = a.bvh;
-    const int R = a.R, LS = a.LS, N = a.N;
+    const int R = a.R, N = a.N;
+    [[maybe_unused]] const int LS = a.LS;  // bounds of the checked build
     const unsigned nq = a.queue ? min(*a.nq_dev, (unsigned)R) : (unsigned)R;
     const unsigned q = ((c - pre[lo]) << 5) + (unsigned)lane;
     int ray = -1, b = 0, last = -1;
@@ -499,7 +501,8 @@ __global__ void __launch_bounds__(256) k_mark(TraceArgs a, CoherentArgs c) {
     __syncthreads();
   }
   const bool any_rx = c.ctr->rx_moved > 0;
-  const int R = a.R, LS = a.LS, N = a.N;
+  const int R = a.R, N = a.N;
+  [[maybe_unused]] const int LS = a.LS;  // bounds of the checked build
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long reused = 0;
