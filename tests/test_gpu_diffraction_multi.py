@@ -234,3 +234,44 @@ def test_batch_equals_single_scenes(cuda, mode):
     b.close()
     for s in batched + alone:
         s.close()
+
+
+@pytest.mark.parametrize("seed", [6, 10])
+def test_with_transmission(cuda, seed):
+    """Transmission (concrete boxes 10 dB per pass, up to two passes: through a
+    box) together with diffraction up to order 3: the diffraction paths of each
+    order and the whole frame's power against the oracle (transmitting faces
+    block diffraction legs on both sides)."""
+    torch = cuda
+    sc = _boxes(seed)
+    rays = scenes.fibonacci_sphere(20_000)
+    s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(rays)
+    s.set_transmission([10.0, -1.0], 2)
+    s.set_diffraction(True)
+    s.set_diffraction_order(3)
+    prm = P.gpu_params(sc, max_refl=3)
+    oprm = P.oracle_params(sc, n_rays=20_000, max_refl=3, max_trans=2, trans_db=(10.0, -1.0), diffraction=True,
+                           diffraction_order=3)
+    fr = s.trace(sc.tx, sc.rx[0], prm)
+    ref = O.frame(sc, 0, rays, oprm)
+    wt = sc.tris.reshape(-1, 9)
+    for m in (2, 3):
+        ck, cp = O.diffract_multi(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], oprm, m)
+        g = fr.paths[_of_order(fr.paths, m)]
+        gk = {tuple(k): p for k, p in zip(P.path_keys(g, oprm.width), g)}
+        rk = {tuple(k): p for k, p in zip(ck.tolist(), cp)}
+        flagged = {k for k, p in rk.items() if p["flags"] & FLAGS}
+        assert set(gk) ^ set(rk) <= flagged, m
+        for k in set(gk) & set(rk):
+            za = complex(gk[k]["amp_re"], gk[k]["amp_im"])
+            zb = complex(rk[k]["amp_re"], rk[k]["amp_im"])
+            assert abs(za - zb) <= 1e-6 * abs(zb)
+    res = P.compare_paths(fr, ref, oprm.width)
+    assert not res["missing"] and not res["extra"] and not res["len"] and not res["amp"], res
+    gkeys = P.path_keys(fr.paths, oprm.width)
+    assert any(any(v >= 0 and (v & dcem.TRI_TRANSMIT) for v in k[2:]) for k in gkeys)
+    fin = np.isfinite(ref.p_coh_dbm) & np.isfinite(fr.p_coh_dbm)
+    assert np.array_equal(np.isfinite(ref.p_coh_dbm), np.isfinite(fr.p_coh_dbm))
+    assert np.all(np.abs(ref.p_coh_dbm[fin] - fr.p_coh_dbm[fin]) <= 0.01)
+    s.close()
