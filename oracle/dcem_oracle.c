@@ -1646,29 +1646,237 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
   return 0;
 }
 
+/* The specular reflection of field E at triangle Tj for incoming direction
+ * din and outgoing dout: Fresnel TE / TM of Tj's material in the bounce
+ * basis of validate_one (s = din x n, p_in = s x din, p_out = s x dout). */
+static c3 reflect_field(const oscene* S, const or_params* P, const otri* Tj, v3 din, v3 dout, c3 E) {
+  v3 nh = Tj->nh;
+  double ct = fabs(dot(din, nh));
+  v3 sv = cross(din, nh);
+  double sn = norm(sv);
+  if (sn < 1e-12) {
+    v3 ax = fabs(nh.x) < 0.9 ? mk(1, 0, 0) : mk(0, 1, 0);
+    sv = unit(cross(nh, ax));
+  } else {
+    sv = scl(sv, 1.0 / sn);
+  }
+  v3 pin = cross(sv, din), pout = cross(sv, dout);
+  int mj = Tj->mat;
+  if (mj < 0 || mj >= S->nmat) mj = 0;
+  double complex gte, gtm;
+  fresnel(&S->mats[3 * mj], P->freq_hz, ct, &gte, &gtm);
+  double complex es = cdot(E, sv), ep = cdot(E, pin);
+  c3 out;
+  out.x = gte * es * sv.x + gtm * ep * pout.x;
+  out.y = gte * es * sv.y + gtm * ep * pout.y;
+  out.z = gte * es * sv.z + gtm * ep * pout.z;
+  return out;
+}
+
+static inline c3 mk3c(v3 v) {
+  c3 c = {v.x, v.y, v.z};
+  return c;
+}
+
+/* The chain rules of a wedge sequence w[0..m-1]: pairwise distinct, and
+ * consecutive wedges share no vertex (share_vertex), do not lie on one line
+ * (collinear_edges), and neither edge lies in a face plane of the other
+ * (in_face_plane). */
+static int chain_allowed(const owedge* W, const long* w, int m) {
+  int ok = w[0] != w[1] && (m < 3 || (w[2] != w[0] && w[2] != w[1]));
+  for (int i = 0; ok && i + 1 < m; ++i) {
+    const owedge *A = &W[w[i]], *B = &W[w[i + 1]];
+    if (share_vertex(A, B) || collinear_edges(A, B) || in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;
+  }
+  return ok;
+}
+
+/* One diffraction chain over the wedges E[0..m-1] (m = 1..3) from T to R,
+ * with an optional specular reflection on static triangle j (j < 0: none)
+ * before the first wedge (first = 1) or after the last (first = 0). By
+ * image theory the chain is solved between the source and the observer,
+ * the transmitter's image in j's plane (reflection first) or the receiver's
+ * (reflection last); the reflection point is where the unfolded leg from
+ * the source to Q_1 (or from Q_m to the observer) crosses the plane, and it
+ * must lie inside triangle j. Every rule of or_diffract_multi applies to the
+ * unfolded chain (the angles about an edge are those of the real points:
+ * the real and the image leg lie on one line through Q); the real legs are
+ * unoccluded (triangle j excluded at the reflection point, the wedges' faces
+ * at theirs). Field: at the reflection, the Fresnel coefficients of j's
+ * material in the bounce basis of the real directions (validate_one's); at
+ * the wedges, the UTD chain of or_diffract_multi over the unfolded
+ * distances (a plane mirror keeps the wavefront's radii of curvature).
+ * Returns 1 when the path is valid, with o filled (points in path order). */
+static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R, int j, int first,
+                      const or_params* P, opath* o) {
+  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
+  const double ang_eps = 1e-9;
+  const v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  const otri* Tj = j >= 0 ? &S->t[j] : NULL;
+  const double cpl = Tj ? dot(Tj->nh, Tj->v[0]) : 0.0;
+  uint32_t fl = 0;
+  v3 src = T, obs = R;
+  if (Tj && first) src = sub(T, scl(Tj->nh, 2.0 * (dot(Tj->nh, T) - cpl)));
+  if (Tj && !first) obs = sub(R, scl(Tj->nh, 2.0 * (dot(Tj->nh, R) - cpl)));
+  /* the source outside the first wedge, the observer outside the last (the
+   * angles about an edge do not depend on the Keller points; the same tests
+   * are repeated below with the others) */
+  if (wedge_angle(E[0], src) > E[0]->n * M_PI || wedge_angle(E[m - 1], obs) > E[m - 1]->n * M_PI) return 0;
+  double t[3];
+  if (!keller_points(E, m, src, obs, t)) return 0;
+  v3 X[5];
+  X[0] = src;
+  for (int i = 0; i < m; ++i) X[i + 1] = add(E[i]->p0, scl(E[i]->e, t[i]));
+  X[m + 1] = obs;
+  for (int i = 0; i < m; ++i) {
+    double uq = t[i] / E[i]->len;
+    if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+    if (!(uq > 0 && uq < 1)) return 0;
+  }
+  double ell[4];
+  for (int q = 0; q <= m; ++q) {
+    ell[q] = norm(sub(X[q + 1], X[q]));
+    if (!(ell[q] > 1e-9)) return 0;
+  }
+  /* exterior and shadow rule at every wedge */
+  double phip[3], phi[3];
+  for (int i = 0; i < m; ++i) {
+    phip[i] = wedge_angle(E[i], X[i]);
+    phi[i] = wedge_angle(E[i], X[i + 2]);
+    double nn = E[i]->n;
+    if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) return 0;
+    if (fabs(fabs(phi[i] - phip[i]) - M_PI) <= ang_eps) fl |= ORF_VAL_PARAM;
+    if (!(fabs(phi[i] - phip[i]) > M_PI)) return 0;
+  }
+  double scale = fmax(maxabs(T), maxabs(R));
+  /* the reflection point on the unfolded leg, inside triangle j */
+  v3 Pp = mk(0, 0, 0);
+  if (Tj) {
+    v3 a0 = first ? src : X[m], a1 = first ? X[1] : obs;
+    double den = dot(Tj->nh, sub(a1, a0));
+    if (den == 0.0) return 0;
+    double sp_ = (cpl - dot(Tj->nh, a0)) / den;
+    if (fabs(sp_) <= P->val_eps || fabs(sp_ - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+    if (!(sp_ > 0 && sp_ < 1)) return 0;
+    Pp = add(a0, scl(sub(a1, a0), sp_));
+    if (edge_margin(Tj, Pp) <= P->val_eps * (scale + 1.0)) fl |= ORF_VAL_EDGE;
+    if (!point_in_tri(Tj, Pp)) return 0;
+  }
+  /* the real legs: Y[] the path's points, ex[] two excluded triangles each */
+  v3 Y[6];
+  int ex[6][2], ny = 0;
+  Y[ny] = T; ex[ny][0] = ex[ny][1] = -1; ++ny;
+  if (Tj && first) { Y[ny] = Pp; ex[ny][0] = ex[ny][1] = j; ++ny; }
+  for (int i = 0; i < m; ++i) { Y[ny] = X[i + 1]; ex[ny][0] = E[i]->ta; ex[ny][1] = E[i]->tb; ++ny; }
+  if (Tj && !first) { Y[ny] = Pp; ex[ny][0] = ex[ny][1] = j; ++ny; }
+  Y[ny] = R; ex[ny][0] = ex[ny][1] = -1; ++ny;
+  for (int q = 0; q + 1 < ny; ++q)
+    if (occluded4(S, Y[q], Y[q + 1], ex[q][0], ex[q][1], ex[q + 1][0], ex[q + 1][1], P, scale, &fl)) return 0;
+  /* field: the source's spherical wave (reflected first, if so) */
+  v3 ip = scl(sub(X[1], X[0]), 1.0 / ell[0]);   /* the real direction into Q_1 */
+  double complex Ei = cexp(-I * k * ell[0]) / ell[0];
+  c3 Ev;
+  if (Tj && first) {
+    v3 din = unit(sub(Pp, T));
+    v3 e0 = pol_dir(u, din, &fl);
+    c3 Er = reflect_field(S, P, Tj, din, ip, mk3c(e0));
+    Ev.x = Ei * Er.x; Ev.y = Ei * Er.y; Ev.z = Ei * Er.z;
+  } else {
+    v3 e0 = pol_dir(u, ip, &fl);
+    Ev.x = Ei * e0.x; Ev.y = Ei * e0.y; Ev.z = Ei * e0.z;
+  }
+  double rho1 = ell[0], rho2 = ell[0];
+  v3 dir1 = mk(0, 0, 0), dir2 = mk(0, 0, 0);
+  v3 dd = ip;
+  for (int i = 0; i < m; ++i) {
+    const owedge* Ew = E[i];
+    double s = ell[i + 1];
+    dd = scl(sub(X[i + 2], X[i + 1]), 1.0 / s);
+    double cb = dot(ip, Ew->e);
+    double beta0 = acos(fmax(-1.0, fmin(1.0, cb)));
+    double sb = sin(beta0);
+    v3 php = cross(Ew->e, ip), ph = cross(Ew->e, dd);
+    php = scl(php, -1.0 / norm(php));
+    ph = scl(ph, 1.0 / norm(ph));
+    v3 bp = cross(ip, php), bd = cross(dd, ph);
+    /* incident radius of curvature in the plane of the edge */
+    double rhoe;
+    if (i == 0) rhoe = ell[0];
+    else {
+      double c1 = dot(bp, dir1), c2 = dot(bp, dir2);
+      rhoe = 1.0 / (c1 * c1 / rho1 + c2 * c2 / rho2);
+    }
+    double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
+    int ma = S->t[Ew->ta].mat, mb = S->t[Ew->tb].mat;
+    if (ma < 0 || ma >= S->nmat) ma = 0;
+    if (mb < 0 || mb >= S->nmat) mb = 0;
+    double nn = Ew->n;
+    double complex r0s, r0h, rns, rnh;
+    fresnel(&S->mats[3 * ma], P->freq_hz, fabs(sin(phip[i])), &r0s, &r0h);
+    fresnel(&S->mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - phi[i])), &rns, &rnh);
+    double complex Ds = utd_coeff(nn, phi[i], phip[i], beta0, L, k, r0s, rns, &fl);
+    double complex Dh = utd_coeff(nn, phi[i], phip[i], beta0, L, k, r0h, rnh, &fl);
+    double complex Eb = cdot(Ev, bp), Ep = cdot(Ev, php);
+    double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);
+    double complex cb_ = -Ds * Eb * A, cp_ = -Dh * Ep * A;
+    Ev.x = cb_ * bd.x + cp_ * ph.x;
+    Ev.y = cb_ * bd.y + cp_ * ph.y;
+    Ev.z = cb_ * bd.z + cp_ * ph.z;
+    /* the wave behind the edge: caustic on the edge (along phi^), the other
+     * at rho_e behind it (along beta^) */
+    rho1 = s;
+    dir1 = ph;
+    rho2 = rhoe + s;
+    dir2 = bd;
+    ip = dd;
+  }
+  v3 dlast = dd;
+  if (Tj && !first) {  /* reflected last, toward the real receiver */
+    v3 dout = unit(sub(R, Pp));
+    Ev = reflect_field(S, P, Tj, dd, dout, Ev);
+    dlast = dout;
+  }
+  v3 prx = pol_dir(u, scl(dlast, -1.0), &fl);
+  double complex a = (lam / (4.0 * M_PI)) * cdot(Ev, prx);
+  double Ltot = 0.0;
+  for (int q = 0; q <= m; ++q) Ltot += ell[q];
+  memset(o, 0, sizeof(*o));
+  o->valid = 1;
+  o->flags = fl;
+  o->len_m = Ltot;
+  o->delay_s = Ltot / C0;
+  o->amp_re = creal(a);
+  o->amp_im = cimag(a);
+  for (int q = 1; q + 1 < ny; ++q) {
+    o->pts[q - 1][0] = Y[q].x;
+    o->pts[q - 1][1] = Y[q].y;
+    o->pts[q - 1][2] = Y[q].z;
+  }
+  return 1;
+}
+
 /* Paths Tx -> Q_1 -> ... -> Q_m -> Rx over m pairwise distinct wedges
- * (m = 2 or 3), consecutive wedges sharing no vertex (share_vertex), not on
- * one line (collinear_edges), neither edge in a face plane of the other
- * (in_face_plane). Each Q_i is a Keller
- * point (keller_points) strictly inside its edge; at every wedge the
- * previous point (Tx or Q_{i-1}) and the next point (Q_{i+1} or Rx) lie in
- * the exterior and the next point lies beyond the incident shadow boundary
- * of the previous one (or_diffract's rule, edge by edge); every leg is
- * unoccluded (the faces of the wedges at its ends excluded). Field: at each
- * wedge the UTD coefficient of or_diffract (Luebbers' face factors) acts on
- * the field the previous leg brings, in the edge-fixed bases of that wedge.
- * The spreading follows Kouyoumjian & Pathak (1974) for a straight edge:
- * the wave leaving wedge i has one caustic on the edge (radius of curvature
- * s along phi^) and the other at rho_e behind it (radius rho_e + s along
- * beta^), rho_e being the incident wavefront's radius of curvature in the
- * plane of the edge (Euler's formula on the principal radii rho_1, rho_2
- * along the edge's projection; rho_e = s' for the spherical wave of the
- * transmitter); the spreading factor is sqrt(rho_e / (s (rho_e + s))) and
- * the distance parameter L = s (rho_e + s) rho_1 rho_2 sin^2 beta_0 /
- * (rho_e (rho_1 + s) (rho_2 + s)), which is s s' sin^2 beta_0 / (s + s') for
- * the spherical wave. Keys: rx, m, w_1 | OR_DIFF, .., w_m | OR_DIFF, -1
- * padded to 2 + width (width >= m). Returns the number of valid paths (may
- * exceed cap). */
+ * (m = 2 or 3) allowed by chain_allowed (consecutive wedges sharing no
+ * vertex, not on one line, neither edge in a face plane of the other). Each
+ * Q_i is a Keller point (keller_points) strictly inside its edge; at every
+ * wedge the previous point (Tx or Q_{i-1}) and the next point (Q_{i+1} or
+ * Rx) lie in the exterior and the next point lies beyond the incident
+ * shadow boundary of the previous one (or_diffract's rule, edge by edge);
+ * every leg is unoccluded (the faces of the wedges at its ends excluded).
+ * Field: at each wedge the UTD coefficient of or_diffract (Luebbers' face
+ * factors) acts on the field the previous leg brings, in the edge-fixed
+ * bases of that wedge. The spreading follows Kouyoumjian & Pathak (1974)
+ * for a straight edge: the wave leaving wedge i has one caustic on the edge
+ * (radius of curvature s along phi^) and the other at rho_e behind it
+ * (radius rho_e + s along beta^), rho_e being the incident wavefront's
+ * radius of curvature in the plane of the edge (Euler's formula on the
+ * principal radii rho_1, rho_2 along the edge's projection; rho_e = s' for
+ * the spherical wave of the transmitter); the spreading factor is
+ * sqrt(rho_e / (s (rho_e + s))) and the distance parameter L = s (rho_e +
+ * s) rho_1 rho_2 sin^2 beta_0 / (rho_e (rho_1 + s) (rho_2 + s)), which is
+ * s s' sin^2 beta_0 / (s + s') for the spherical wave (chain_path). Keys:
+ * rx, m, w_1 | OR_DIFF, .., w_m | OR_DIFF, -1 padded to 2 + width (width >=
+ * m). Returns the number of valid paths (may exceed cap). */
 int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
                           const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
                           const or_params* P, int32_t order, int32_t width, int32_t* keys_out,
@@ -1679,141 +1887,84 @@ int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32
   owedge* W = NULL;
   long nw = find_wedges(tris, tri_obj, ntri, &W);
   const int m = order;
-  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
-  const double ang_eps = 1e-9;
   v3 T = mk(tx[0], tx[1], tx[2]);
-  v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
   int64_t nvalid = 0;
   long w[3] = {0, 0, 0};
+  opath tmp;
   for (int r = 0; r < nrx; ++r) {
     v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
     for (w[0] = 0; w[0] < nw; ++w[0])
       for (w[1] = 0; w[1] < nw; ++w[1])
         for (w[2] = 0; w[2] < (m == 3 ? nw : 1); ++w[2]) {
-          /* pairwise distinct; consecutive wedges share no vertex, are not on one line */
-          int ok = w[0] != w[1] && (m < 3 || (w[2] != w[0] && w[2] != w[1]));
-          for (int i = 0; ok && i + 1 < m; ++i) {
-            const owedge *A = &W[w[i]], *B = &W[w[i + 1]];
-            if (share_vertex(A, B) || collinear_edges(A, B) || in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;
-          }
-          if (!ok) continue;
+          if (!chain_allowed(W, w, m)) continue;
           const owedge* E[3] = {&W[w[0]], &W[w[1]], m == 3 ? &W[w[2]] : NULL};
-          /* the transmitter outside the first wedge, the receiver outside the
-           * last (the angles about an edge do not depend on the Keller points;
-           * the same tests are repeated below with the others) */
-          if (wedge_angle(E[0], T) > E[0]->n * M_PI || wedge_angle(E[m - 1], R) > E[m - 1]->n * M_PI) continue;
-          uint32_t fl = 0;
-          double t[3];
-          if (!keller_points(E, m, T, R, t)) continue;
-          v3 X[5];
-          X[0] = T;
-          for (int i = 0; i < m; ++i) X[i + 1] = add(E[i]->p0, scl(E[i]->e, t[i]));
-          X[m + 1] = R;
-          for (int i = 0; ok && i < m; ++i) {
-            double uq = t[i] / E[i]->len;
-            if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
-            if (!(uq > 0 && uq < 1)) ok = 0;
-          }
-          double ell[4];
-          for (int j = 0; ok && j <= m; ++j) {
-            ell[j] = norm(sub(X[j + 1], X[j]));
-            if (!(ell[j] > 1e-9)) ok = 0;
-          }
-          if (!ok) continue;
-          /* exterior and shadow rule at every wedge */
-          double phip[3], phi[3];
-          for (int i = 0; ok && i < m; ++i) {
-            phip[i] = wedge_angle(E[i], X[i]);
-            phi[i] = wedge_angle(E[i], X[i + 2]);
-            double nn = E[i]->n;
-            if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) ok = 0;
-            else {
-              if (fabs(fabs(phi[i] - phip[i]) - M_PI) <= ang_eps) fl |= ORF_VAL_PARAM;
-              if (!(fabs(phi[i] - phip[i]) > M_PI)) ok = 0;
-            }
-          }
-          if (!ok) continue;
-          double scale = fmax(maxabs(T), maxabs(R));
-          for (int j = 0; ok && j <= m; ++j) {
-            int e0 = j >= 1 ? E[j - 1]->ta : -1, e1 = j >= 1 ? E[j - 1]->tb : -1;
-            int e2 = j < m ? E[j]->ta : -1, e3 = j < m ? E[j]->tb : -1;
-            if (occluded4(&S, X[j], X[j + 1], e0, e1, e2, e3, P, scale, &fl)) ok = 0;
-          }
-          if (!ok) continue;
-          /* field: transmitter's spherical wave, then wedge by wedge */
-          v3 ip = scl(sub(X[1], X[0]), 1.0 / ell[0]);
-          v3 e0 = pol_dir(u, ip, &fl);
-          double complex Ei = cexp(-I * k * ell[0]) / ell[0];
-          c3 Ev = {Ei * e0.x, Ei * e0.y, Ei * e0.z};
-          double rho1 = ell[0], rho2 = ell[0];
-          v3 dir1 = mk(0, 0, 0), dir2 = mk(0, 0, 0);
-          v3 dd = ip;
-          for (int i = 0; i < m; ++i) {
-            const owedge* Ew = E[i];
-            double s = ell[i + 1];
-            dd = scl(sub(X[i + 2], X[i + 1]), 1.0 / s);
-            double cb = dot(ip, Ew->e);
-            double beta0 = acos(fmax(-1.0, fmin(1.0, cb)));
-            double sb = sin(beta0);
-            v3 php = cross(Ew->e, ip), ph = cross(Ew->e, dd);
-            php = scl(php, -1.0 / norm(php));
-            ph = scl(ph, 1.0 / norm(ph));
-            v3 bp = cross(ip, php), bd = cross(dd, ph);
-            /* incident radius of curvature in the plane of the edge */
-            double rhoe;
-            if (i == 0) rhoe = ell[0];
-            else {
-              double c1 = dot(bp, dir1), c2 = dot(bp, dir2);
-              rhoe = 1.0 / (c1 * c1 / rho1 + c2 * c2 / rho2);
-            }
-            double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
-            int ma = S.t[Ew->ta].mat, mb = S.t[Ew->tb].mat;
-            if (ma < 0 || ma >= S.nmat) ma = 0;
-            if (mb < 0 || mb >= S.nmat) mb = 0;
-            double nn = Ew->n;
-            double complex r0s, r0h, rns, rnh;
-            fresnel(&S.mats[3 * ma], P->freq_hz, fabs(sin(phip[i])), &r0s, &r0h);
-            fresnel(&S.mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - phi[i])), &rns, &rnh);
-            double complex Ds = utd_coeff(nn, phi[i], phip[i], beta0, L, k, r0s, rns, &fl);
-            double complex Dh = utd_coeff(nn, phi[i], phip[i], beta0, L, k, r0h, rnh, &fl);
-            double complex Eb = cdot(Ev, bp), Ep = cdot(Ev, php);
-            double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);
-            double complex cb_ = -Ds * Eb * A, cp_ = -Dh * Ep * A;
-            Ev.x = cb_ * bd.x + cp_ * ph.x;
-            Ev.y = cb_ * bd.y + cp_ * ph.y;
-            Ev.z = cb_ * bd.z + cp_ * ph.z;
-            /* the wave behind the edge: caustic on the edge (along phi^),
-             * the other at rho_e behind it (along beta^) */
-            rho1 = s;
-            dir1 = ph;
-            rho2 = rhoe + s;
-            dir2 = bd;
-            ip = dd;
-          }
-          v3 prx = pol_dir(u, scl(dd, -1.0), &fl);
-          double complex a = (lam / (4.0 * M_PI)) * cdot(Ev, prx);
-          double Ltot = 0.0;
-          for (int j = 0; j <= m; ++j) Ltot += ell[j];
+          if (!chain_path(&S, E, m, T, R, -1, 0, P, &tmp)) continue;
           if (nvalid < cap) {
             int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
             kk[0] = r;
             kk[1] = m;
-            for (int j = 0; j < width; ++j) kk[2 + j] = j < m ? ((int32_t)w[j] | OR_DIFF) : -1;
-            opath* o = &paths_out[nvalid];
-            memset(o, 0, sizeof(*o));
-            o->valid = 1;
-            o->flags = fl;
-            o->len_m = Ltot;
-            o->delay_s = Ltot / C0;
-            o->amp_re = creal(a);
-            o->amp_im = cimag(a);
-            for (int i = 0; i < m; ++i) {
-              o->pts[i][0] = X[i + 1].x;
-              o->pts[i][1] = X[i + 1].y;
-              o->pts[i][2] = X[i + 1].z;
-            }
+            for (int q = 0; q < width; ++q) kk[2 + q] = q < m ? ((int32_t)w[q] | OR_DIFF) : -1;
+            paths_out[nvalid] = tmp;
           }
           nvalid++;
+        }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
+/* Sec. III steps 3-5 combined: one reflection on a static triangle j before
+ * a chain of m = 2 or 3 wedges or after it (chain_path), the chain allowed
+ * by chain_allowed and j none of its wedges' faces. Keys: rx, m + 1, then
+ * j, w_1 | OR_DIFF, .. (reflection first) or w_1 | OR_DIFF, .., j
+ * (reflection last); -1 padded to 2 + width (width >= m + 1). Returns the
+ * number of valid paths (may exceed cap). */
+int64_t or_diffract_multi_refl(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                               const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                               const or_params* P, int32_t order, int32_t width, int32_t* keys_out,
+                               opath* paths_out, int64_t cap) {
+  if (order < 2 || order > 3 || width < order + 1) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  const int m = order;
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  int64_t nvalid = 0;
+  long w[3] = {0, 0, 0};
+  opath tmp;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (w[0] = 0; w[0] < nw; ++w[0])
+      for (w[1] = 0; w[1] < nw; ++w[1])
+        for (w[2] = 0; w[2] < (m == 3 ? nw : 1); ++w[2]) {
+          if (!chain_allowed(W, w, m)) continue;
+          const owedge* E[3] = {&W[w[0]], &W[w[1]], m == 3 ? &W[w[2]] : NULL};
+          for (int j = 0; j < ntri; ++j) {
+            if (tri_obj && tri_obj[j] >= 0) continue;
+            int face = 0;
+            for (int i = 0; i < m; ++i) face |= j == E[i]->ta || j == E[i]->tb;
+            if (face) continue;
+            for (int first = 1; first >= 0; --first) {
+              if (!chain_path(&S, E, m, T, R, j, first, P, &tmp)) continue;
+              if (nvalid < cap) {
+                int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+                kk[0] = r;
+                kk[1] = m + 1;
+                for (int q = 0; q < width; ++q) {
+                  int v = -1;
+                  if (q <= m) {
+                    if (first) v = q == 0 ? j : ((int32_t)w[q - 1] | OR_DIFF);
+                    else v = q == m ? j : ((int32_t)w[q] | OR_DIFF);
+                  }
+                  kk[2 + q] = v;
+                }
+                paths_out[nvalid] = tmp;
+              }
+              nvalid++;
+            }
+          }
         }
   }
   free(W);

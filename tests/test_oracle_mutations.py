@@ -68,8 +68,11 @@ MUTANTS = [
     ("keller_gradient_sign", "if (a >= 0) { g[a] -= ca; H[a][a] += (1.0 - ca * ca) / l; }",
      "if (a >= 0) { g[a] += ca; H[a][a] += (1.0 - ca * ca) / l; }"),
     ("face_plane_chains_kept", "|| in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;", ") ok = 0;"),
-    ("caustic_on_the_edge", "rho1 = s;\n            dir1 = ph;", "rho1 = rhoe + s;\n            dir1 = ph;"),
-    ("principal_direction", "dir1 = ph;\n            rho2 = rhoe + s;", "dir1 = bd;\n            rho2 = rhoe + s;"),
+    ("caustic_on_the_edge", "rho1 = s;\n    dir1 = ph;", "rho1 = rhoe + s;\n    dir1 = ph;"),
+    ("principal_direction", "dir1 = ph;\n    rho2 = rhoe + s;", "dir1 = bd;\n    rho2 = rhoe + s;"),
+    ("chain_image_half", "if (Tj && first) src = sub(T, scl(Tj->nh, 2.0 * (dot(Tj->nh, T) - cpl)));",
+     "if (Tj && first) src = sub(T, scl(Tj->nh, 1.0 * (dot(Tj->nh, T) - cpl)));"),
+    ("chain_last_reflection_dropped", "Ev = reflect_field(S, P, Tj, dd, dout, Ev);", "(void)0;"),
     ("spherical_spreading", "double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);",
      "double complex A = csqrt(ell[0] / (s * (ell[0] + s))) * cexp(-I * k * s);"),
 ]

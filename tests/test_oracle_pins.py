@@ -894,3 +894,87 @@ def test_multi_diffraction_reciprocal_at_high_frequency(oracle_mod):
         diffs.append(abs(a - b) / abs(a))
     assert diffs[2] < 1e-4
     assert 5.0 < diffs[0] / diffs[1] < 20.0 and 5.0 < diffs[1] / diffs[2] < 20.0
+
+
+# ---------------------------------------------------------------------------
+# one reflection before or after a chain of 2-3 wedges (image theory)
+# ---------------------------------------------------------------------------
+_GROUND = scenes._quad((-200.0, -200.0, 0.0), (200.0, -200.0, 0.0), (200.0, 200.0, 0.0), (-200.0, 200.0, 0.0))
+
+
+def _two_walls():
+    return _slab(0.0, 0.5, -50.0, 0.0) + _slab(10.0, 10.5, 5.0, 55.0)
+
+
+def _prisms():
+    out = []
+    for a in np.deg2rad([60.0, 0.0, -60.0]):
+        out += _prism(a)
+    return out
+
+
+def _at(deg, z):
+    return (22.0 * np.cos(np.deg2rad(deg)), 22.0 * np.sin(np.deg2rad(deg)), z)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+@pytest.mark.parametrize("case", ["walls_first", "walls_last", "prisms_first", "prisms_last"])
+def test_reflection_and_chain_is_the_image_chain(oracle_mod, mat, case):
+    """Over a perfectly conducting ground and for vertical polarisation (the
+    image of the vertically polarised transmitter is a vertically polarised
+    transmitter), a ground reflection before a chain of wedges is the chain
+    from the transmitter's image without the ground, and a reflection after it
+    the chain toward the receiver's image: the same diffraction points,
+    lengths and amplitudes (orders 2 and 3; the two walls and the three prisms
+    of the composition pins, raised so the chain clears the ground)."""
+    O = oracle_mod
+    walls, m = (_two_walls(), 2) if case.startswith("walls") else (_prisms(), 3)
+    first = case.endswith("first")
+    if m == 2:
+        tx, rx = ((-10.0, -20.0, 1.0), (20.0, 20.0, 9.0)) if first else ((-10.0, -20.0, 9.0), (20.0, 20.0, 1.0))
+    else:
+        tx, rx = (_at(120.0, 1.0), _at(-120.0, 9.0)) if first else (_at(120.0, 9.0), _at(-120.0, 1.0))
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    tris = _GROUND + walls
+    sc = scenes._static_scene("ground_walls", tris, [scenes.MAT_METAL] * 2 + [mat] * len(walls), tx, [rx])
+    k, p = O.diffract_multi_refl(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0],
+                                 prm, m)
+    on_ground = [i for i, kk in enumerate(k) if (kk[2] if first else kk[2 + m]) < 2]
+    src = (tx[0], tx[1], -tx[2]) if first else tx
+    obs = rx if first else (rx[0], rx[1], -rx[2])
+    b = scenes._static_scene("walls", walls, [mat] * len(walls), src, [obs])
+    bk, bp = O.diffract_multi(b.tris.reshape(-1, 9), b.tri_mat, b.tri_obj, b.materials, b.tx, b.rx[0], prm, m)
+    assert len(on_ground) == len(bk) == 1
+    i = on_ground[0]
+    wedges = list(k[i][3:3 + m]) if first else list(k[i][2:2 + m])
+    assert wedges == list(bk[0][2:2 + m])
+    q = p["pts"][i][1:1 + m] if first else p["pts"][i][0:m]
+    assert np.max(np.abs(q - bp["pts"][0][:m])) <= 1e-9
+    refl = p["pts"][i][0] if first else p["pts"][i][m]
+    assert abs(refl[2]) <= 1e-9                      # the reflection point on the ground
+    assert abs(p["len_m"][i] - bp["len_m"][0]) <= 1e-9 * bp["len_m"][0]
+    a, b_ = complex(p["amp_re"][i], p["amp_im"][i]), complex(bp["amp_re"][0], bp["amp_im"][0])
+    assert abs(a - b_) <= 1e-9 * abs(b_)
+
+
+def test_reflection_and_chain_reciprocity(oracle_mod):
+    """Perfect conductors, parallel edges: swapping Tx and Rx turns the
+    reflection-first chain into the reflection-last chain over the same wedges
+    in reverse order, with the same length and amplitude."""
+    O = oracle_mod
+    tx, rx = (-10.0, -20.0, 1.0), (20.0, 20.0, 9.0)
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    walls = _two_walls()
+    out = []
+    for t, r in ((tx, rx), (rx, tx)):
+        sc = scenes._static_scene("g", _GROUND + walls, [scenes.MAT_METAL] * (2 + len(walls)), t, [r])
+        k, p = O.diffract_multi_refl(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx,
+                                     sc.rx[0], prm, 2)
+        out.append({tuple(kk[2:5].tolist()): (complex(pp["amp_re"], pp["amp_im"]), float(pp["len_m"]))
+                    for kk, pp in zip(k, p)})
+    fwd, back = out
+    assert len(fwd) >= 1 and len(fwd) == len(back)
+    for (a0, a1, a2), (amp, length) in fwd.items():
+        amp2, len2 = back[(a2, a1, a0)]
+        assert abs(length - len2) <= 1e-9 * length
+        assert abs(amp - amp2) <= 1e-9 * abs(amp)
