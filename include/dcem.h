@@ -331,7 +331,14 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
  * wedge | DCEM_TRI_DIFFRACT} or {wedge | DCEM_TRI_DIFFRACT, triangle id},
  * pts = the two points in path order, ray = -1. on = 0 turns it off.
  * *n_planes (may be NULL): the reflector-plane count. Cost: one pre-test
- * thread per (link, wedge, plane, order) per frame. Errors: DCEM_ERR_ARG,
+ * thread per (link, wedge, plane, order) per frame. With diffraction chains
+ * on (dcem_scene_set_diffraction_order, max_order m >= 2) the reflection also
+ * comes before or after every chain of 2..m wedges: the chain from the
+ * transmitter's image or toward the receiver's image in the plane (Keller
+ * points, wedge rules and spreading over the unfolded chain), the
+ * reflection point inside a triangle of the plane, every real leg
+ * unoccluded, Fresnel at the reflection point; record: depth k + 1 with
+ * tri = {triangle, wedges...} or {wedges..., triangle}. Errors: DCEM_ERR_ARG,
  * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes);
 
@@ -354,8 +361,10 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
  * = Q_i, ray = -1. Cost per frame: one pre-test thread per (transmitter,
  * wedge pair), for m = 3 per (pair, wedge), then per (sequence, receiver);
  * the wedge-pair relation takes nw * nw bits of device memory for m = 3.
- * max_order = 1 turns the higher orders off. Errors: DCEM_ERR_ARG,
- * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
+ * With reflector planes on (dcem_scene_set_diffraction_reflections) every
+ * chain may also have one reflection before or after it. max_order = 1
+ * turns the higher orders off. Errors: DCEM_ERR_ARG, DCEM_ERR_STATE
+ * (diffraction is off), DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction_order(dcem_scene* s, int32_t max_order);
 
 /* Closest-hit kernel configuration. Results never depend on it (closest hit

@@ -1455,14 +1455,78 @@ __device__ __forceinline__ bool in_face_plane(const Wedge& A, const Wedge& B) {
   return false;
 }
 
-// Ordered pairs (w1, w2) per transmitter that can start a path of order
-// >= 2: distinct, no shared vertex, not on one line, neither edge in a face
-// plane of the other, each edge partly in the other's exterior,
+// Source v of a chain (a transmitter, or its image in a reflector plane) and
+// observer rho (a receiver, or its image), in FP32 for the pre-tests.
+__device__ __forceinline__ float3 chain_source32(const PathArgs& a, int v) {
+  if (v < a.dntx) {
+    float4 t = a.txs[v];
+    return f3(t.x, t.y, t.z);
+  }
+  int i = v - a.dntx;
+  float4 t = a.txs[i / a.nrpr];
+  const RPlane& P = a.rplanes[i % a.nrpr];
+  return mirror32(f3(t.x, t.y, t.z), f3((float)P.n[0], (float)P.n[1], (float)P.n[2]), (float)P.c);
+}
+__device__ __forceinline__ float3 chain_observer32(const PathArgs& a, int rho) {
+  if (rho < a.nrx) {
+    float4 r = a.rx[rho];
+    return f3(r.x, r.y, r.z);
+  }
+  int i = rho - a.nrx;
+  float4 r = a.rx[i / a.nrpr];
+  const RPlane& P = a.rplanes[i % a.nrpr];
+  return mirror32(f3(r.x, r.y, r.z), f3((float)P.n[0], (float)P.n[1], (float)P.n[2]), (float)P.c);
+}
+
+// Can a leg from S to some point of segment A-B cross reflector plane Pl
+// inside its box? The legs fill the triangle S, A, B; its section by the
+// plane lies within the box of the crossings of its three sides, so the
+// answer is "no" when S, A and B lie on one side of the plane (by more than
+// the margin m), or when that box, widened by m, misses the plane's box.
+__device__ __forceinline__ bool plane_reachable(const RPlane& Pl, float3 S, float3 A, float3 B, float m) {
+  const float3 n = f3((float)Pl.n[0], (float)Pl.n[1], (float)Pl.n[2]);
+  const float c = (float)Pl.c;
+  const float ds = fdot3(n, S) - c, da = fdot3(n, A) - c, db = fdot3(n, B) - c;
+  if ((ds > m && da > m && db > m) || (ds < -m && da < -m && db < -m)) return false;
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  bool any = false;
+  const float3 P0[3] = {S, S, A}, P1[3] = {A, B, B};
+  const float d0[3] = {ds, ds, da}, d1[3] = {da, db, db};
+  for (int e = 0; e < 3; ++e) {
+    if ((d0[e] > m && d1[e] > m) || (d0[e] < -m && d1[e] < -m)) continue;
+    // the part of this side within m of the plane
+    float den = d0[e] - d1[e];
+    float ta = 0.0f, tb = 1.0f;
+    if (fabsf(den) > 1e-30f) {
+      float t1 = (d0[e] - m) / den, t2 = (d0[e] + m) / den;
+      ta = fmaxf(0.0f, fminf(t1, t2));
+      tb = fminf(1.0f, fmaxf(t1, t2));
+    }
+    if (ta > tb) continue;
+    for (int q = 0; q < 2; ++q) {
+      float t = q ? tb : ta;
+      float x = P0[e].x + t * (P1[e].x - P0[e].x), y = P0[e].y + t * (P1[e].y - P0[e].y),
+            z = P0[e].z + t * (P1[e].z - P0[e].z);
+      lo[0] = fminf(lo[0], x); lo[1] = fminf(lo[1], y); lo[2] = fminf(lo[2], z);
+      hi[0] = fmaxf(hi[0], x); hi[1] = fmaxf(hi[1], y); hi[2] = fmaxf(hi[2], z);
+    }
+    any = true;
+  }
+  if (!any) return false;
+  for (int k = 0; k < 3; ++k)
+    if (hi[k] < Pl.box[k] - m || lo[k] > Pl.box[3 + k] + m) return false;
+  return true;
+}
+
+// Ordered pairs (w1, w2) per source (transmitter or transmitter image) that
+// can start a path of order >= 2: distinct, no shared vertex, not on one
+// line, neither edge in a face plane of the other, each edge partly in the
+// other's exterior,
 // the transmitter outside w1, and some point of edge 2 beyond the incident
 // shadow boundary of the transmitter at w1. With order 3, the relation
 // (the first three conditions) also goes to a bit matrix for the triples.
-__global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int ntx) {
-  const long nw = a.nw, total = (long)ntx * nw * nw;
+__global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int nsrc) {
+  const long nw = a.nw, total = (long)nsrc * nw * nw;
   const int lane = threadIdx.x & 31;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
@@ -1488,10 +1552,15 @@ __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int ntx) {
           atomicOr(&a.drel[bit >> 5], 1u << (bit & 31));
         }
         if (rel) {
-          float4 tv = a.txs[t];
-          float3 T = f3(tv.x, tv.y, tv.z), P, Q;
+          float3 T = chain_source32(a, t), P, Q;
           edge_ends(fb, P, Q);
           keep = !surely_inside(fa, T) && shadow_meets(fa, T, P, Q);
+          if (keep && t >= a.dntx) {  // the image's leg to edge 1 crosses its plane inside the box
+            float3 A1, B1;
+            edge_ends(fa, A1, B1);
+            float mg = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fa.len);
+            keep = plane_reachable(a.rplanes[(t - a.dntx) % a.nrpr], T, A1, B1, mg);
+          }
         }
       }
     }
@@ -1748,15 +1817,22 @@ __device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float
   return true;
 }
 
-// Every (sequence, receiver): the receiver outside the last wedge and some
-// point of the previous edge beyond its shadow boundary at the last wedge.
+// Every (sequence, observer): the observer outside the last wedge and some
+// point of the previous edge beyond its shadow boundary at the last wedge,
+// then the FP32 Keller estimate against the rules, the legs that are real
+// (not those to or from an image) against robust occlusion, and, with a
+// reflection, its point on the unfolded leg inside the plane's box (5 cm +
+// 1e-4 of the distances; as diffract_refl_candidate). Observers: the
+// receivers, and with reflector planes their images (rho = nrx + r * nrpr
+// + p) for sequences from a real transmitter; a chain has one reflection.
 __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
   extern __shared__ int sstk[];
   TStack st;
   bind_stack(st, sstk, kStackTrace);
   const long n2 = a.diff_order >= 2 ? (long)min(a.ctr->n_dpair, a.dseq2_cap) : 0;
   const long n3 = a.diff_order >= 3 ? (long)min(a.ctr->n_dtrip, a.dseq3_cap) : 0;
-  const long total = (n2 + n3) * a.nrx;
+  const long nobs = (long)a.nrx * (1 + a.nrpr);
+  const long total = (n2 + n3) * nobs;
   const int lane = threadIdx.x & 31;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
@@ -1764,46 +1840,73 @@ __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
     bool keep = false;
     unsigned long long code = 0;
     if (idx < total) {
-      long e = idx / a.nrx;
-      int r = (int)(idx - e * a.nrx);
+      long e = idx / nobs;
+      int rho = (int)(idx - e * nobs);
       bool three = e >= n2;
       long ei = three ? e - n2 : e;
       int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
-      int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
-      WedgeF fl = wedge_f(a.wedges[wl]), fp = wedge_f(a.wedges[wp]);
-      float4 rv = a.rx[r];
-      float3 R = f3(rv.x, rv.y, rv.z), P, Q;
-      edge_ends(fp, P, Q);
-      keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
-      if (keep) {
-        WedgeF Wc[3];
-        Wc[0] = wedge_f(a.wedges[sq.y]);
-        Wc[1] = three ? fp : fl;  // order 2: (w1, last); order 3: (w1, previous, last)
-        Wc[2] = fl;
-        float4 tv = a.txs[sq.x];
-        const int m = three ? 3 : 2;
-        const float3 T = f3(tv.x, tv.y, tv.z);
-        float t[3];
-        bool solved;
-        keep = chain_possible(Wc, m, T, R, t, &solved);
-        if (keep && solved) {  // a leg certainly blocked rejects the chain
-          const int w[3] = {sq.y, sq.z, sq.w};
-          const float delta = chain_margin(T, R);
-          float3 X[5];
-          X[0] = T;
-          for (int i = 0; i < m; ++i) X[i + 1] = edge_point(Wc[i], t[i]);
-          X[m + 1] = R;
-          for (int j = 0; keep && j <= m; ++j) {
-            const Wedge* A = j >= 1 ? &a.wedges[w[j - 1]] : nullptr;
-            const Wedge* B = j < m ? &a.wedges[w[j]] : nullptr;
-            float3 dv = f3(X[j + 1].x - X[j].x, X[j + 1].y - X[j].y, X[j + 1].z - X[j].z);
-            if (leg_surely_blocked(a.bvh, X[j], dv, delta, a.eps_occ, A ? A->ta : -1, A ? A->tb : -1,
-                                   B ? B->ta : -1, B ? B->tb : -1, st))
-              keep = false;
+      const bool src_img = sq.x >= a.dntx, obs_img = rho >= a.nrx;
+      if (!(src_img && obs_img)) {
+        int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
+        WedgeF fl = wedge_f(a.wedges[wl]), fp = wedge_f(a.wedges[wp]);
+        float3 R = chain_observer32(a, rho), P, Q;
+        edge_ends(fp, P, Q);
+        keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+        if (keep && obs_img) {  // the leg from the last edge to the image crosses its plane inside the box
+          float3 A1, B1;
+          edge_ends(fl, A1, B1);
+          float mg = 0.1f + 1e-4f * (fabsf(R.x) + fabsf(R.y) + fabsf(R.z) + fl.len);
+          keep = plane_reachable(a.rplanes[(rho - a.nrx) % a.nrpr], R, A1, B1, mg);
+        }
+        if (keep) {
+          WedgeF Wc[3];
+          Wc[0] = wedge_f(a.wedges[sq.y]);
+          Wc[1] = three ? fp : fl;  // order 2: (w1, last); order 3: (w1, previous, last)
+          Wc[2] = fl;
+          const int m = three ? 3 : 2;
+          const float3 T = chain_source32(a, sq.x);
+          float t[3];
+          bool solved;
+          keep = chain_possible(Wc, m, T, R, t, &solved);
+          if (keep && solved) {
+            const int w[3] = {sq.y, sq.z, sq.w};
+            const float delta = chain_margin(T, R);
+            float3 X[5];
+            X[0] = T;
+            for (int i = 0; i < m; ++i) X[i + 1] = edge_point(Wc[i], t[i]);
+            X[m + 1] = R;
+            // a leg certainly blocked rejects the chain (legs to or from an
+            // image are not real: the reflection breaks them)
+            for (int q = 0; keep && q <= m; ++q) {
+              if ((q == 0 && src_img) || (q == m && obs_img)) continue;
+              const Wedge* A = q >= 1 ? &a.wedges[w[q - 1]] : nullptr;
+              const Wedge* B = q < m ? &a.wedges[w[q]] : nullptr;
+              float3 dv = f3(X[q + 1].x - X[q].x, X[q + 1].y - X[q].y, X[q + 1].z - X[q].z);
+              if (leg_surely_blocked(a.bvh, X[q], dv, delta, a.eps_occ, A ? A->ta : -1, A ? A->tb : -1,
+                                     B ? B->ta : -1, B ? B->tb : -1, st))
+                keep = false;
+            }
+            if (keep && (src_img || obs_img)) {  // the reflection point within the plane's box
+              const RPlane& Pl = a.rplanes[src_img ? (sq.x - a.dntx) % a.nrpr : (rho - a.nrx) % a.nrpr];
+              const float3 n = f3((float)Pl.n[0], (float)Pl.n[1], (float)Pl.n[2]);
+              const float3 a0 = src_img ? X[0] : X[m], a1 = src_img ? X[1] : X[m + 1];
+              const float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
+              const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
+              if (fabsf(den) > 1e-6f * len) {
+                float tt = ((float)Pl.c - fdot3(n, a0)) / den;
+                float mt = (0.05f + delta + 1e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
+                if (tt < -mt || tt > 1.0f + mt) keep = false;
+                float3 Xp = f3(a0.x + tt * dv.x, a0.y + tt * dv.y, a0.z + tt * dv.z);
+                float mb = 0.05f + delta + 1e-4f * (len + sqrtf(fdot3(Xp, Xp)));
+                if (Xp.x < Pl.box[0] - mb || Xp.y < Pl.box[1] - mb || Xp.z < Pl.box[2] - mb ||
+                    Xp.x > Pl.box[3] + mb || Xp.y > Pl.box[4] + mb || Xp.z > Pl.box[5] + mb)
+                  keep = false;
+              }
+            }
           }
         }
       }
-      code = ((unsigned long long)ei * a.nrx + r) | (three ? kMulti3 : kMulti2);
+      code = ((unsigned long long)ei * nobs + rho) | (three ? kMulti3 : kMulti2);
     }
     unsigned mk = __ballot_sync(0xffffffffu, keep);
     if (!mk) continue;
@@ -1925,69 +2028,169 @@ __device__ bool keller_chain(const Wedge* const* E, int m, d3w T, d3w R, double*
   return false;
 }
 
-// One (sequence, receiver) survivor of order m: the Keller points, the
-// wedge rules, the legs (FP32 any-hit, the faces of the wedges at each end
-// excluded), then the UTD chain: at each wedge the coefficient acts on the
-// arriving field in the wedge's edge-fixed bases; the wave behind it has a
-// caustic on the edge (radius s along phi^) and one rho_e behind it (radius
-// rho_e + s along beta^), rho_e the arriving wavefront's radius of curvature
-// along the edge's projection (Euler's formula; the transmitter's distance
-// for its spherical wave); spreading sqrt(rho_e / (s (rho_e + s))) and
-// distance parameter L = s (rho_e + s) rho_1 rho_2 sin^2 beta_0 /
-// (rho_e (rho_1 + s) (rho_2 + s)) (Kouyoumjian & Pathak 1974, straight edge).
+// The Keller points of a chain from src to obs and the rules on the
+// unfolded chain: every point inside its edge, every leg longer than 1e-9 m,
+// at every wedge both neighbours in the exterior and the next point beyond
+// the incident shadow boundary of the previous one. X: the chain's points.
+__device__ bool chain_geometry(const Wedge* const* E, int m, d3w src, d3w obs, d3w* X, double* ell,
+                               double* phip, double* phi) {
+  if (wedge_angle(*E[0], src) > E[0]->n * M_PI || wedge_angle(*E[m - 1], obs) > E[m - 1]->n * M_PI) return false;
+  double t[3];
+  if (!keller_chain(E, m, src, obs, t)) return false;
+  X[0] = src;
+  for (int i = 0; i < m; ++i) {
+    double uq = t[i] / E[i]->len;
+    if (!(uq > 0.0 && uq < 1.0)) return false;
+    X[i + 1] = D3(E[i]->p0[0], E[i]->p0[1], E[i]->p0[2]) + D3(E[i]->e[0], E[i]->e[1], E[i]->e[2]) * t[i];
+  }
+  X[m + 1] = obs;
+  for (int q = 0; q <= m; ++q) {
+    d3w d = X[q + 1] - X[q];
+    ell[q] = sqrt(dotw(d, d));
+    if (!(ell[q] > 1e-9)) return false;
+  }
+  for (int i = 0; i < m; ++i) {
+    phip[i] = wedge_angle(*E[i], X[i]);
+    phi[i] = wedge_angle(*E[i], X[i + 2]);
+    const double nn = E[i]->n;
+    if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) return false;
+    if (!(fabs(phi[i] - phip[i]) > M_PI)) return false;
+  }
+  return true;
+}
+
+// The reflection point of the unfolded leg a0 -> a1 on plane (n, c): false
+// when the leg does not cross the plane between its ends.
+__device__ __forceinline__ bool leg_plane(d3w a0, d3w a1, d3w n, double c, d3w& P) {
+  double den = dotw(n, a1 - a0);
+  if (den == 0.0) return false;
+  double t = (c - dotw(n, a0)) / den;
+  if (!(t > 0.0 && t < 1.0)) return false;
+  P = a0 + (a1 - a0) * t;
+  return true;
+}
+
+// The specular reflection of field E at a triangle with unit normal nj and
+// material mj, incoming direction din, outgoing dout: Fresnel TE / TM in the
+// bounce basis of k_val_field (s = din x n, p_in = s x din, p_out = s x dout).
+__device__ zv3 reflect_field_d(const PathArgs& a, d3w nj, float4 mj, d3w din, d3w dout, zv3 E) {
+  double ct = fabs(dotw(din, nj));
+  d3w sv = crossw(din, nj);
+  double sn = sqrt(dotw(sv, sv));
+  if (sn < 1e-12) {
+    d3w ax = fabs(nj.x) < 0.9 ? D3(1, 0, 0) : D3(0, 1, 0);
+    sv = unitw(crossw(nj, ax));
+  } else {
+    sv = sv * (1.0 / sn);
+  }
+  d3w pin = crossw(sv, din), pout = crossw(sv, dout);
+  zd gte, gtm;
+  fresnel_d(mj, a.freq, ct, gte, gtm);
+  zd ts = gte * zvdot(E, sv), tp = gtm * zvdot(E, pin);
+  return zv3{ts * sv.x + tp * pout.x, ts * sv.y + tp * pout.y, ts * sv.z + tp * pout.z};
+}
+
+// One (sequence, observer) survivor of order m: with an image source or
+// observer, the chain is solved on the plane group's image, the member
+// triangle j holding the reflection point is found, and everything is
+// redone with j's own plane (the oracle takes each static triangle as the
+// mirror). Then the Keller points and rules (chain_geometry), the real legs
+// (FP32 any-hit; triangle j excluded at the reflection point, the wedges'
+// faces at theirs), and the UTD chain: at each wedge the coefficient acts on
+// the arriving field in the wedge's edge-fixed bases; the wave behind it has
+// a caustic on the edge (radius s along phi^) and one rho_e behind it
+// (radius rho_e + s along beta^), rho_e the arriving wavefront's radius of
+// curvature along the edge's projection (Euler's formula; the source's
+// distance for its spherical wave); spreading sqrt(rho_e / (s (rho_e + s)))
+// and distance parameter L = s (rho_e + s) rho_1 rho_2 sin^2 beta_0 /
+// (rho_e (rho_1 + s) (rho_2 + s)) (Kouyoumjian & Pathak 1974, straight
+// edge), over the unfolded distances (a plane mirror keeps the wavefront's
+// radii); the reflection applies Fresnel in the real directions.
 __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long long code, double k, double lam,
                                             unsigned& ovf, TStack& st) {
   const bool three = (code >> kKindShift) == 3ull;
   const int m = three ? 3 : 2;
   const unsigned long long c = code & ((1ull << kKindShift) - 1ull);
-  const long ei = (long)(c / a.nrx);
-  const int r = (int)(c - (unsigned long long)ei * a.nrx);
+  const unsigned long long nobs = (unsigned long long)a.nrx * (1 + a.nrpr);
+  const long ei = (long)(c / nobs);
+  const int rho = (int)(c - (unsigned long long)ei * nobs);
   const int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
   const int w[3] = {sq.y, sq.z, sq.w};
-  const int link = sq.x * a.nrx + r;
+  const bool first = sq.x >= a.dntx, last = rho >= a.nrx;  // a reflection before / after the chain
+  if (first && last) return;
+  const int tx = first ? (sq.x - a.dntx) / a.nrpr : sq.x, r = last ? (rho - a.nrx) / a.nrpr : rho;
+  const int pl = first ? (sq.x - a.dntx) % a.nrpr : last ? (rho - a.nrx) % a.nrpr : -1;
+  const int link = tx * a.nrx + r;
   const Wedge* E[3] = {&a.wedges[w[0]], &a.wedges[w[1]], three ? &a.wedges[w[2]] : &a.wedges[w[1]]};
-  float4 rxv = a.rx[r], txv = a.txs[sq.x];
+  float4 rxv = a.rx[r], txv = a.txs[tx];
   const d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
-  if (wedge_angle(*E[0], T) > E[0]->n * M_PI || wedge_angle(*E[m - 1], R) > E[m - 1]->n * M_PI) return;
-  double t[3];
-  if (!keller_chain(E, m, T, R, t)) return;
-  d3w X[5];
-  X[0] = T;
-  for (int i = 0; i < m; ++i) {
-    double uq = t[i] / E[i]->len;
-    if (!(uq > 0.0 && uq < 1.0)) return;
-    X[i + 1] = D3(E[i]->p0[0], E[i]->p0[1], E[i]->p0[2]) + D3(E[i]->e[0], E[i]->e[1], E[i]->e[2]) * t[i];
+  d3w X[5], Pp = D3(0, 0, 0), nj = D3(0, 0, 0);
+  double ell[4], phip[3], phi[3];
+  int j = -1;
+  float4 mj = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (pl < 0) {
+    if (!chain_geometry(E, m, T, R, X, ell, phip, phi)) return;
+  } else {
+    const RPlane Pg = a.rplanes[pl];
+    d3w n = D3(Pg.n[0], Pg.n[1], Pg.n[2]);
+    double cg = Pg.c;
+    for (int pass = 0; pass < 2; ++pass) {
+      d3w src = first ? T - n * (2.0 * (dotw(n, T) - cg)) : T;
+      d3w obs = last ? R - n * (2.0 * (dotw(n, R) - cg)) : R;
+      if (!chain_geometry(E, m, src, obs, X, ell, phip, phi)) return;
+      if (!leg_plane(first ? X[0] : X[m], first ? X[1] : X[m + 1], n, cg, Pp)) return;
+      if (pass == 0) {  // the member triangle holding the point: its own plane next
+        d3w v0, v1, v2;
+        for (int q = 0; q < Pg.count && j < 0; ++q) {
+          int id = a.rmembers[Pg.first + q];
+          bool face = false;
+          for (int i = 0; i < m; ++i) face = face || id == E[i]->ta || id == E[i]->tb;
+          if (face) continue;
+          tri64(a, id, v0, v1, v2, mj);
+          if (inside_tri64(v0, v1, v2, Pp)) j = id;
+        }
+        if (j < 0) return;
+        nj = unitw(crossw(v1 - v0, v2 - v0));
+        n = nj;
+        cg = dotw(nj, v0);
+      } else {
+        d3w v0, v1, v2;
+        tri64(a, j, v0, v1, v2, mj);
+        if (!inside_tri64(v0, v1, v2, Pp)) return;
+      }
+    }
   }
-  X[m + 1] = R;
-  double ell[4];
-  for (int j = 0; j <= m; ++j) {
-    d3w d = X[j + 1] - X[j];
-    ell[j] = sqrt(dotw(d, d));
-    if (!(ell[j] > 1e-9)) return;
-  }
-  double phip[3], phi[3];
-  for (int i = 0; i < m; ++i) {
-    phip[i] = wedge_angle(*E[i], X[i]);
-    phi[i] = wedge_angle(*E[i], X[i + 2]);
-    const double nn = E[i]->n;
-    if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) return;
-    if (!(fabs(phi[i] - phip[i]) > M_PI)) return;
-  }
-  for (int j = 0; j <= m; ++j) {
-    int e0 = j >= 1 ? E[j - 1]->ta : -1, e1 = j >= 1 ? E[j - 1]->tb : -1;
-    int e2 = j < m ? E[j]->ta : -1, e3 = j < m ? E[j]->tb : -1;
-    d3w dv = X[j + 1] - X[j];
-    RayPre rp = ray_pre(f3((float)X[j].x, (float)X[j].y, (float)X[j].z), f3((float)dv.x, (float)dv.y, (float)dv.z));
-    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, e0, e1, ovf, st, e2, e3)) return;
+  // the real legs: Y the path's points, two excluded triangles at each
+  d3w Y[6];
+  int ex[6][2], ny = 0;
+  Y[ny] = T; ex[ny][0] = ex[ny][1] = -1; ++ny;
+  if (first) { Y[ny] = Pp; ex[ny][0] = ex[ny][1] = j; ++ny; }
+  for (int i = 0; i < m; ++i) { Y[ny] = X[i + 1]; ex[ny][0] = E[i]->ta; ex[ny][1] = E[i]->tb; ++ny; }
+  if (last) { Y[ny] = Pp; ex[ny][0] = ex[ny][1] = j; ++ny; }
+  Y[ny] = R; ex[ny][0] = ex[ny][1] = -1; ++ny;
+  for (int q = 0; q + 1 < ny; ++q) {
+    d3w dv = Y[q + 1] - Y[q];
+    RayPre rp = ray_pre(f3((float)Y[q].x, (float)Y[q].y, (float)Y[q].z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex[q][0], ex[q][1], ovf, st, ex[q + 1][0], ex[q + 1][1]))
+      return;
   }
   unsigned fl = 0;
   const d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
-  d3w ip = (X[1] - X[0]) * (1.0 / ell[0]);
-  d3w e0 = polw(u, ip, fl);
+  d3w ip = (X[1] - X[0]) * (1.0 / ell[0]);  // the real direction into Q_1
   double sn, cs;
   sincos(-k * ell[0], &sn, &cs);
   zd Ei = Z(cs / ell[0], sn / ell[0]);
-  zv3 Ev = {Ei * e0.x, Ei * e0.y, Ei * e0.z};
+  zv3 Ev;
+  if (first) {
+    d3w din = unitw(Pp - T);
+    d3w e0 = polw(u, din, fl);
+    zv3 E0 = {Z(e0.x), Z(e0.y), Z(e0.z)};
+    zv3 Er = reflect_field_d(a, nj, mj, din, ip, E0);
+    Ev = zv3{Er.x * Ei, Er.y * Ei, Er.z * Ei};
+  } else {
+    d3w e0 = polw(u, ip, fl);
+    Ev = zv3{Ei * e0.x, Ei * e0.y, Ei * e0.z};
+  }
   double rho1 = ell[0], rho2 = ell[0];
   d3w dir1 = D3(0, 0, 0), dir2 = D3(0, 0, 0), dd = ip;
   for (int i = 0; i < m; ++i) {
@@ -2025,19 +2228,32 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
     dir2 = bd;
     ip = dd;
   }
-  d3w prx = polw(u, dd * -1.0, fl);
+  d3w dlast = dd;
+  if (last) {  // reflected last, toward the real receiver
+    d3w dout = unitw(R - Pp);
+    Ev = reflect_field_d(a, nj, mj, dd, dout, Ev);
+    dlast = dout;
+  }
+  d3w prx = polw(u, dlast * -1.0, fl);
   zd amp = zvdot(Ev, prx) * (lam / (4.0 * M_PI));
   double Ltot = 0.0;
-  for (int j = 0; j <= m; ++j) Ltot += ell[j];
+  for (int q = 0; q <= m; ++q) Ltot += ell[q];
   unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
   if (uu >= a.ucap) {
     atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
     return;
   }
+  const int depth = m + (pl >= 0 ? 1 : 0);
+  int ids[4];
+  for (int q = 0; q < depth; ++q) {
+    if (first) ids[q] = q == 0 ? j : (w[q - 1] | kDiffBit);
+    else if (last) ids[q] = q == m ? j : (w[q] | kDiffBit);
+    else ids[q] = w[q] | kDiffBit;
+  }
   PathRec rec;
-  rec.key = seq_key(r, m, [&](int q) { return w[q] | kDiffBit; });
+  rec.key = seq_key(r, depth, [&](int q) { return ids[q]; });
   rec.rx = link;
-  rec.depth = m;
+  rec.depth = depth;
   rec.ray = -1;
   rec.flags = fl;
   rec.valid = 1;
@@ -2046,13 +2262,13 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
   rec.amp_re = amp.re;
   rec.amp_im = amp.im;
   for (int q = 0; q < kMaxRefl; ++q) {
-    rec.tri[q] = q < m ? (w[q] | kDiffBit) : -1;
+    rec.tri[q] = q < depth ? ids[q] : -1;
     rec.pts[q][0] = rec.pts[q][1] = rec.pts[q][2] = 0.0f;
   }
-  for (int q = 0; q < m; ++q) {
-    rec.pts[q][0] = (float)X[q + 1].x;
-    rec.pts[q][1] = (float)X[q + 1].y;
-    rec.pts[q][2] = (float)X[q + 1].z;
+  for (int q = 1; q + 1 < ny; ++q) {
+    rec.pts[q - 1][0] = (float)Y[q].x;
+    rec.pts[q - 1][1] = (float)Y[q].y;
+    rec.pts[q - 1][2] = (float)Y[q].z;
   }
   a.prec[uu] = rec;
   unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
@@ -2263,15 +2479,18 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
       long gr = std::min<long>((tr + 255) / 256, 8L * sms);
       k_diffract_refl_pre<<<(int)std::max<long>(gr, 1), 256, 0, st>>>(a, nlinks);
     }
+    PathArgs b = a;  // chains: transmitters, and the reflector planes applied to them
+    b.dntx = nlinks / a.nrx;
+    b.nrpr = a.rplanes && a.diff_order >= 2 ? a.nrp : 0;
     if (a.diff_order >= 2 && a.nw > 1) {
-      int ntx = nlinks / a.nrx;
-      long tp = (long)ntx * a.nw * a.nw;
+      int nsrc = b.dntx * (1 + b.nrpr);
+      long tp = (long)nsrc * a.nw * a.nw;
       if (a.drel) cudaMemsetAsync(a.drel, 0, sizeof(unsigned) * (((size_t)a.nw * a.nw + 31) / 32), st);
-      k_diff_pairs<<<(int)std::max<long>(std::min<long>((tp + 255) / 256, 8L * sms), 1), 256, 0, st>>>(a, ntx);
-      if (a.diff_order >= 3) k_diff_triples<<<8 * sms, 256, 0, st>>>(a);
-      k_diff_multi_pre<<<8 * sms, 256, 256 * kStackTrace * sizeof(int), st>>>(a);
+      k_diff_pairs<<<(int)std::max<long>(std::min<long>((tp + 255) / 256, 8L * sms), 1), 256, 0, st>>>(b, nsrc);
+      if (a.diff_order >= 3) k_diff_triples<<<8 * sms, 256, 0, st>>>(b);
+      k_diff_multi_pre<<<8 * sms, 256, 256 * kStackTrace * sizeof(int), st>>>(b);
     }
-    k_diffract<<<sms, kDiffThreads, kDiffThreads * kStackTrace * sizeof(int), st>>>(a);
+    k_diffract<<<sms, kDiffThreads, kDiffThreads * kStackTrace * sizeof(int), st>>>(b);
   }
   return cudaGetLastError();
 }

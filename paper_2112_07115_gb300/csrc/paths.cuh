@@ -60,9 +60,13 @@ struct PathArgs {
   const int* rmembers;
   int nrp;
   // diffraction of order 2 and 3 (diff_order <= 1: off): the wedge pairs
-  // (t, w1, w2, -1) and triples (t, w1, w2, w3) of the frame, and the pair
-  // relation as a bit matrix (nw x nw bits; order 3 only)
+  // (v, w1, w2, -1) and triples (v, w1, w2, w3) of the frame, v a source
+  // (a transmitter, or with reflector planes the image of transmitter t in
+  // plane p: v = dntx + t * nrpr + p), and the pair relation as a bit matrix
+  // (nw x nw bits; order 3 only)
   int diff_order;
+  int dntx;                       // transmitters (set by launch_diffract)
+  int nrpr;                       // reflector planes applied to chains (0: none; set by launch_diffract)
   int4* dseq2;
   unsigned dseq2_cap;
   int4* dseq3;

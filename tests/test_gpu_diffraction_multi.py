@@ -275,3 +275,110 @@ def test_with_transmission(cuda, seed):
     assert np.array_equal(np.isfinite(ref.p_coh_dbm), np.isfinite(fr.p_coh_dbm))
     assert np.all(np.abs(ref.p_coh_dbm[fin] - fr.p_coh_dbm[fin]) <= 0.01)
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# one reflection before or after a chain (dcem_scene_set_diffraction_reflections)
+# ---------------------------------------------------------------------------
+def _refl_chains(paths, m):
+    """Records of m wedges and one reflection (first or last)."""
+    t = paths["tri"]
+    sel = paths["depth"] == m + 1
+    d = np.zeros(len(paths), np.int32)
+    for i in range(m + 1):
+        d += ((t[:, i] >= 0) & ((t[:, i] & dcem.TRI_DIFFRACT) != 0)).astype(np.int32)
+    return sel & (d == m)
+
+
+def _check_refl(torch, sc, frames, order, mode=dcem.MODE_FULL, least=1, refl_orders=None):
+    """GPU chains with one reflection (orders 2..order, or refl_orders) against
+    or_diffract_multi_refl, then the whole frame's power against the oracle's
+    reflections, diffraction of every order and the combined paths."""
+    rays = scenes.fibonacci_sphere(20_000)
+    s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(rays)
+    s.set_diffraction(True)
+    assert s.set_diffraction_reflections(True) >= 1
+    s.set_diffraction_order(order)
+    prm = P.gpu_params(sc, max_refl=4, mode=mode)
+    oprm = P.oracle_params(sc, n_rays=20_000, max_refl=4, diffraction=True, diffraction_order=order)
+    total = 0
+    for f in frames:
+        if sc.nobj:
+            s.update_transforms(sc.xf[f])
+        fr = s.trace(sc.tx, sc.rx[f], prm)
+        wt = O.transform(sc.tris, sc.tri_obj, sc.xf[f] if sc.nobj else np.zeros((0, 12)))
+        extra_k, extra_p = [], []
+        ck1, cp1 = O.diffract_refl(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[f], oprm)
+        extra_k.append(ck1)
+        extra_p.append(cp1)
+        for m in range(2, order + 1):
+            ck, cp = O.diffract_multi_refl(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[f], oprm, m)
+            extra_k.append(ck)
+            extra_p.append(cp)
+            if refl_orders is not None and m not in refl_orders:
+                continue
+            ref = {tuple(k): p for k, p in zip(ck.tolist(), cp)}
+            g = fr.paths[_refl_chains(fr.paths, m)]
+            gk = {tuple(k): p for k, p in zip(P.path_keys(g, oprm.width), g)}
+            flagged = {k for k, p in ref.items() if p["flags"] & FLAGS}
+            assert set(gk) ^ set(ref) <= flagged, (f, m, sorted(set(gk) ^ set(ref))[:4])
+            for k in set(gk) & set(ref):
+                a, b = gk[k], ref[k]
+                assert abs(a["len_m"] - b["len_m"]) <= 1e-6, (f, k)
+                za, zb = complex(a["amp_re"], a["amp_im"]), complex(b["amp_re"], b["amp_im"])
+                assert abs(za - zb) <= 1e-6 * abs(zb), (f, k, za, zb)
+                assert np.allclose(a["pts"][:m + 1], b["pts"][:m + 1], atol=1e-4)
+            total += len(gk)
+        r = O.frame(sc, f, rays, oprm)
+        keys = np.concatenate([r.keys] + extra_k)
+        paths = np.concatenate([r.paths] + extra_p)
+        order_ = np.lexsort(keys.T[::-1])
+        _, pc, _ = O.reduce(keys[order_], paths[order_], sc.nrx, oprm.tx_power_w)
+        fin = np.isfinite(pc) & np.isfinite(fr.p_coh_dbm)
+        assert np.array_equal(np.isfinite(pc), np.isfinite(fr.p_coh_dbm)), f
+        assert np.all(np.abs(pc[fin] - fr.p_coh_dbm[fin]) <= 0.01), f
+    s.close()
+    assert total >= least, total
+    return total
+
+
+def _on_ground(tris, mats, tx, rx, ground_mat):
+    g = scenes._quad((-200.0, -200.0, 0.0), (200.0, -200.0, 0.0), (200.0, 200.0, 0.0), (-200.0, 200.0, 0.0))
+    return scenes._static_scene("ground", g + tris, [ground_mat] * 2 + mats, tx, rx)
+
+
+@pytest.mark.parametrize("ground", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_reflection_and_two_walls(cuda, ground):
+    """The two walls on a ground: the ground reflection before and after
+    their double diffraction (receivers high and low)."""
+    walls = _slab(0.0, 0.5, -50.0, 0.0) + _slab(10.0, 10.5, 5.0, 55.0)
+    rx = [(20.0, 20.0, 9.0), (20.0, 20.0, 1.0), (25.0, 12.0, 6.0), (15.0, 30.0, 2.0)]
+    for tx in ((-10.0, -20.0, 1.0), (-10.0, -20.0, 9.0)):
+        sc = _on_ground(walls, [scenes.MAT_METAL] * len(walls), tx, rx, ground)
+        _check_refl(cuda, sc, [0], 2, least=1)
+
+
+def test_reflection_and_three_prisms(cuda):
+    """The three prisms on a concrete ground: order 3 with the reflection."""
+    pr = []
+    for a in np.deg2rad([60.0, 0.0, -60.0]):
+        pr += _prism(a)
+    at = lambda deg, z, r=22.0: (r * np.cos(np.deg2rad(deg)), r * np.sin(np.deg2rad(deg)), z)
+    rx = [at(-120.0, 9.0), at(-120.0, 1.0), at(-110.0, 5.0, 25.0)]
+    for tx in (at(120.0, 1.0), at(120.0, 9.0)):
+        sc = _on_ground(pr, [scenes.MAT_CONCRETE] * len(pr), tx, rx, scenes.MAT_CONCRETE)
+        _check_refl(cuda, sc, [0], 3, least=1)
+
+
+@pytest.mark.parametrize("mode", [dcem.MODE_FULL, dcem.MODE_COHERENT])
+def test_reflection_and_moving_boxes(cuda, mode):
+    """Random boxes on a ground, two of them moving, order 2 with reflections
+    on the ground and the static boxes' faces, frames 0-2."""
+    sc = _boxes(6, n_moving=2, n_frames=3)
+    g = np.asarray(scenes._quad((-200.0, -200.0, 0.0), (200.0, -200.0, 0.0), (200.0, 200.0, 0.0),
+                                (-200.0, 200.0, 0.0)), np.float32)
+    sc.tris = np.concatenate([g, sc.tris])
+    sc.tri_obj = np.concatenate([np.full(2, -1, np.int32), sc.tri_obj])
+    sc.tri_mat = np.concatenate([np.full(2, scenes.MAT_CONCRETE, np.int32), sc.tri_mat])
+    _check_refl(cuda, sc, range(3), 2, mode=mode, least=3)
