@@ -1152,18 +1152,21 @@ def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
 def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
     """Diffraction of order 1-3 (Sec. III step 5, bound 3): frames/s of the
     city blocks (8 x 8 box buildings, 512 wedges, 64 receivers, 200k rays,
-    3 reflections) with diffraction up to order 1, 2 and 3, the highway frames
-    with order 2, the pre-test candidates and wedge pairs/triples per frame,
-    and order 2 on 8 of the city's receivers against the oracle."""
+    3 reflections) with diffraction up to order 1, 2 and 3, and up to order 2
+    with one reflection before or after each chain (the ground and every
+    building face as reflector planes), the highway frames with order 2, the
+    pre-test candidates and wedge pairs/triples per frame, and order 2 on 8
+    of the city's receivers against the oracle."""
     import torch
     from oracle import oracle as O
     from paper_2112_07115_gb300 import dcem, scenes
     city = scenes.city_blocks()
 
-    def frames(sc, order, n_rays, max_refl, mode):
+    def frames(sc, order, n_rays, max_refl, mode, refl=False):
         s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
         s.set_rays(scenes.fibonacci_sphere(n_rays))
         nw = s.set_diffraction(True)
+        nrp = s.set_diffraction_reflections(True) if refl else 0
         s.set_diffraction_order(order)
         prm = dcem.default_params(max_refl=max_refl, freq_hz=sc.freq_hz, mode=mode)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1185,9 +1188,16 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
               for m in (1, 2, 3)]
         t = max_over_ranks([sum(ms) / 1e3], dev)[0]
         st = fr.stats
-        return {"frames_per_s": round(world * K / t, 2), "ms_per_frame": round(1e3 * t / K, 3), "wedges": nw,
-                "diffraction_paths_by_order": by, "wedge_pairs": st["diff_pairs"],
-                "wedge_triples": st["diff_triples"], "fp64_candidates": st["diff_candidates"]}, fr
+        d = np.zeros(len(p), np.int32)
+        for i in range(4):
+            d += ((p["tri"][:, i] >= 0) & ((p["tri"][:, i] & dcem.TRI_DIFFRACT) != 0)).astype(np.int32)
+        with_refl = [int(((p["depth"] == m + 1) & (d == m)).sum()) for m in (1, 2, 3)]
+        out = {"frames_per_s": round(world * K / t, 2), "ms_per_frame": round(1e3 * t / K, 3), "wedges": nw,
+               "diffraction_paths_by_order": by, "wedge_pairs": st["diff_pairs"],
+               "wedge_triples": st["diff_triples"], "fp64_candidates": st["diff_candidates"]}
+        if refl:
+            out.update({"reflector_planes": nrp, "with_one_reflection_by_order": with_refl})
+        return out, fr
 
     out = {"city_workload": "8 x 8 box buildings (642 triangles, 512 wedges), 1 Tx at 10 m, 64 Rx at 1.5 m, "
                             "200000 rays, 3 reflections, 28 GHz, full frames (static scene)"}
@@ -1197,6 +1207,8 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
         out[f"city_order_{order}"] = r
         if order == 2:
             last = fr
+    r, _ = frames(city, 2, 200_000, 3, dcem.MODE_FULL, refl=True)
+    out["city_order_2_with_reflections"] = r
     r, _ = frames(hw, 2, hw.n_rays, hw.max_refl, dcem.MODE_COHERENT)
     out["highway_order_2"] = r
     # order 2 against the oracle on 8 receivers of the city (the oracle is brute force)
