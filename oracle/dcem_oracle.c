@@ -44,6 +44,14 @@
  *                  reflection factors (IEEE Trans. Antennas Propag. 32(1),
  *                  1984). The transition function is evaluated from its
  *                  integral definition by quadrature along a rotated contour.
+ *   or_diffract_refl, or_diffract_multi, or_diffract_multi_refl,
+ *   or_diffract_refl2
+ *                  step 5 with steps 3-4: one reflection before or after a
+ *                  first-order diffraction, chains of 2-3 wedges (Keller
+ *                  points by minimising the unfolded length), such chains
+ *                  with one reflection before or after them, and two
+ *                  reflections around one diffraction; reflections by image
+ *                  theory on static triangles.
  *
  * Everything after the FP32 inputs is FP64. Decisions that FP32 arithmetic
  * could take differently (a ray passing within a margin of a triangle edge,
@@ -1691,33 +1699,59 @@ static int chain_allowed(const owedge* W, const long* w, int m) {
   return ok;
 }
 
+/* The point where the segment a -> b crosses the plane of triangle Tj
+ * (parameter strictly inside (0, 1), flagged within val_eps of an end), inside
+ * the triangle (flagged within val_eps of its border). Returns 0 when the
+ * segment misses the triangle. */
+static int mirror_point(const otri* Tj, v3 a, v3 b, const or_params* P, double scale, uint32_t* fl, v3* X) {
+  double cpl = dot(Tj->nh, Tj->v[0]);
+  double den = dot(Tj->nh, sub(b, a));
+  if (den == 0.0) return 0;
+  double sp_ = (cpl - dot(Tj->nh, a)) / den;
+  if (fabs(sp_) <= P->val_eps || fabs(sp_ - 1.0) <= P->val_eps) *fl |= ORF_VAL_PARAM;
+  if (!(sp_ > 0 && sp_ < 1)) return 0;
+  *X = add(a, scl(sub(b, a), sp_));
+  if (edge_margin(Tj, *X) <= P->val_eps * (scale + 1.0)) *fl |= ORF_VAL_EDGE;
+  return point_in_tri(Tj, *X);
+}
+
+static v3 mirror_in(const otri* Tj, v3 x) {
+  double cpl = dot(Tj->nh, Tj->v[0]);
+  return sub(x, scl(Tj->nh, 2.0 * (dot(Tj->nh, x) - cpl)));
+}
+
 /* One diffraction chain over the wedges E[0..m-1] (m = 1..3) from T to R,
- * with an optional specular reflection on static triangle j (j < 0: none)
- * before the first wedge (first = 1) or after the last (first = 0). By
- * image theory the chain is solved between the source and the observer,
- * the transmitter's image in j's plane (reflection first) or the receiver's
- * (reflection last); the reflection point is where the unfolded leg from
- * the source to Q_1 (or from Q_m to the observer) crosses the plane, and it
- * must lie inside triangle j. Every rule of or_diffract_multi applies to the
- * unfolded chain (the angles about an edge are those of the real points:
- * the real and the image leg lie on one line through Q); the real legs are
- * unoccluded (triangle j excluded at the reflection point, the wedges' faces
- * at theirs). Field: at the reflection, the Fresnel coefficients of j's
- * material in the bounce basis of the real directions (validate_one's); at
- * the wedges, the UTD chain of or_diffract_multi over the unfolded
- * distances (a plane mirror keeps the wavefront's radii of curvature).
- * Returns 1 when the path is valid, with o filled (points in path order). */
-static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R, int j, int first,
-                      const or_params* P, opath* o) {
+ * with specular reflections on the static triangles jb[0..nb-1] before the
+ * first wedge and ja[0..na-1] after the last (both in path order, nb + na <=
+ * 2). By image theory the chain is solved between the source, the
+ * transmitter's image in the planes of jb[0], jb[1], .. in turn, and the
+ * observer, the receiver's image in the planes of ja[na-1], .., ja[0]. The
+ * reflection points follow by unfolding back: the last one before the chain
+ * is where the leg from the source to Q_1 crosses its plane, the one before
+ * it where the leg from the previous image to that point crosses its plane,
+ * and the same after the chain from Q_m outward; each must lie strictly
+ * inside its leg and inside its triangle. Every rule of or_diffract_multi
+ * applies to the unfolded chain (the angles about an edge are those of the
+ * real points: the real and the unfolded leg lie on one line through Q); the
+ * real legs are unoccluded (the triangle excluded at a reflection point, the
+ * wedge's faces at a diffraction point). Field: the transmitter's wave along
+ * its real first leg, the Fresnel coefficients of each reflection's material
+ * in the bounce basis of the real directions (validate_one's), the UTD chain
+ * of or_diffract_multi over the unfolded distances (a plane mirror keeps the
+ * wavefront's radii of curvature). Returns 1 when the path is valid, with o
+ * filled (points in path order). */
+static int chain_path_r(const oscene* S, const owedge* const* E, int m, v3 T, v3 R, const int* jb, int nb,
+                        const int* ja, int na, const or_params* P, opath* o) {
   const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
   const double ang_eps = 1e-9;
   const v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
-  const otri* Tj = j >= 0 ? &S->t[j] : NULL;
-  const double cpl = Tj ? dot(Tj->nh, Tj->v[0]) : 0.0;
   uint32_t fl = 0;
-  v3 src = T, obs = R;
-  if (Tj && first) src = sub(T, scl(Tj->nh, 2.0 * (dot(Tj->nh, T) - cpl)));
-  if (Tj && !first) obs = sub(R, scl(Tj->nh, 2.0 * (dot(Tj->nh, R) - cpl)));
+  v3 Simg[3], Oimg[3];
+  Simg[0] = T;
+  for (int i = 0; i < nb; ++i) Simg[i + 1] = mirror_in(&S->t[jb[i]], Simg[i]);
+  Oimg[na] = R;
+  for (int i = na - 1; i >= 0; --i) Oimg[i] = mirror_in(&S->t[ja[i]], Oimg[i + 1]);
+  const v3 src = Simg[nb], obs = Oimg[0];
   /* the source outside the first wedge, the observer outside the last (the
    * angles about an edge do not depend on the Keller points; the same tests
    * are repeated below with the others) */
@@ -1749,42 +1783,41 @@ static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R
     if (!(fabs(phi[i] - phip[i]) > M_PI)) return 0;
   }
   double scale = fmax(maxabs(T), maxabs(R));
-  /* the reflection point on the unfolded leg, inside triangle j */
-  v3 Pp = mk(0, 0, 0);
-  if (Tj) {
-    v3 a0 = first ? src : X[m], a1 = first ? X[1] : obs;
-    double den = dot(Tj->nh, sub(a1, a0));
-    if (den == 0.0) return 0;
-    double sp_ = (cpl - dot(Tj->nh, a0)) / den;
-    if (fabs(sp_) <= P->val_eps || fabs(sp_ - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
-    if (!(sp_ > 0 && sp_ < 1)) return 0;
-    Pp = add(a0, scl(sub(a1, a0), sp_));
-    if (edge_margin(Tj, Pp) <= P->val_eps * (scale + 1.0)) fl |= ORF_VAL_EDGE;
-    if (!point_in_tri(Tj, Pp)) return 0;
+  /* the reflection points, unfolded back from the chain's ends */
+  v3 Yb[2], Ya[2];
+  v3 b = X[1];
+  for (int i = nb - 1; i >= 0; --i) {
+    if (!mirror_point(&S->t[jb[i]], Simg[i + 1], b, P, scale, &fl, &Yb[i])) return 0;
+    b = Yb[i];
+  }
+  v3 a0 = X[m];
+  for (int i = 0; i < na; ++i) {
+    if (!mirror_point(&S->t[ja[i]], a0, Oimg[i], P, scale, &fl, &Ya[i])) return 0;
+    a0 = Ya[i];
   }
   /* the real legs: Y[] the path's points, ex[] two excluded triangles each */
-  v3 Y[6];
-  int ex[6][2], ny = 0;
+  v3 Y[8];
+  int ex[8][2], ny = 0;
   Y[ny] = T; ex[ny][0] = ex[ny][1] = -1; ++ny;
-  if (Tj && first) { Y[ny] = Pp; ex[ny][0] = ex[ny][1] = j; ++ny; }
+  for (int i = 0; i < nb; ++i) { Y[ny] = Yb[i]; ex[ny][0] = ex[ny][1] = jb[i]; ++ny; }
   for (int i = 0; i < m; ++i) { Y[ny] = X[i + 1]; ex[ny][0] = E[i]->ta; ex[ny][1] = E[i]->tb; ++ny; }
-  if (Tj && !first) { Y[ny] = Pp; ex[ny][0] = ex[ny][1] = j; ++ny; }
+  for (int i = 0; i < na; ++i) { Y[ny] = Ya[i]; ex[ny][0] = ex[ny][1] = ja[i]; ++ny; }
   Y[ny] = R; ex[ny][0] = ex[ny][1] = -1; ++ny;
   for (int q = 0; q + 1 < ny; ++q)
     if (occluded4(S, Y[q], Y[q + 1], ex[q][0], ex[q][1], ex[q + 1][0], ex[q + 1][1], P, scale, &fl)) return 0;
-  /* field: the source's spherical wave (reflected first, if so) */
+  /* field: the transmitter's wave along its real first leg, reflected at
+   * each point before the chain */
   v3 ip = scl(sub(X[1], X[0]), 1.0 / ell[0]);   /* the real direction into Q_1 */
   double complex Ei = cexp(-I * k * ell[0]) / ell[0];
-  c3 Ev;
-  if (Tj && first) {
-    v3 din = unit(sub(Pp, T));
-    v3 e0 = pol_dir(u, din, &fl);
-    c3 Er = reflect_field(S, P, Tj, din, ip, mk3c(e0));
-    Ev.x = Ei * Er.x; Ev.y = Ei * Er.y; Ev.z = Ei * Er.z;
-  } else {
-    v3 e0 = pol_dir(u, ip, &fl);
-    Ev.x = Ei * e0.x; Ev.y = Ei * e0.y; Ev.z = Ei * e0.z;
+  v3 din = nb ? unit(sub(Y[1], T)) : ip;
+  c3 Er = mk3c(pol_dir(u, din, &fl));
+  for (int i = 0; i < nb; ++i) {
+    v3 dout = i == nb - 1 ? ip : unit(sub(Y[i + 2], Y[i + 1]));
+    Er = reflect_field(S, P, &S->t[jb[i]], din, dout, Er);
+    din = dout;
   }
+  c3 Ev;
+  Ev.x = Ei * Er.x; Ev.y = Ei * Er.y; Ev.z = Ei * Er.z;
   double rho1 = ell[0], rho2 = ell[0];
   v3 dir1 = mk(0, 0, 0), dir2 = mk(0, 0, 0);
   v3 dd = ip;
@@ -1830,10 +1863,12 @@ static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R
     dir2 = bd;
     ip = dd;
   }
+  /* reflected at each point after the chain, toward the real receiver */
   v3 dlast = dd;
-  if (Tj && !first) {  /* reflected last, toward the real receiver */
-    v3 dout = unit(sub(R, Pp));
-    Ev = reflect_field(S, P, Tj, dd, dout, Ev);
+  for (int i = 0; i < na; ++i) {
+    const int at = ny - 1 - na + i;   /* Y[at] is the reflection point on ja[i] */
+    v3 dout = unit(sub(Y[at + 1], Y[at]));
+    Ev = reflect_field(S, P, &S->t[ja[i]], dlast, dout, Ev);
     dlast = dout;
   }
   v3 prx = pol_dir(u, scl(dlast, -1.0), &fl);
@@ -1853,6 +1888,14 @@ static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R
     o->pts[q - 1][2] = Y[q].z;
   }
   return 1;
+}
+
+/* chain_path_r with at most one reflection, on static triangle j (j < 0:
+ * none) before the first wedge (first = 1) or after the last (first = 0). */
+static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R, int j, int first,
+                      const or_params* P, opath* o) {
+  const int nb = j >= 0 && first ? 1 : 0, na = j >= 0 && !first ? 1 : 0;
+  return chain_path_r(S, E, m, T, R, &j, nb, &j, na, P, o);
 }
 
 /* Paths Tx -> Q_1 -> ... -> Q_m -> Rx over m pairwise distinct wedges
@@ -1966,6 +2009,60 @@ int64_t or_diffract_multi_refl(const float* tris, const int32_t* tri_mat, const 
             }
           }
         }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
+/* Sec. III steps 3-5 with the evaluation's mechanism limits (two reflections,
+ * one diffraction): a first-order diffraction at wedge w with two
+ * reflections on static triangles, both before it (j1, j2, w), one on each
+ * side (j1, w, j2) or both after it (w, j1, j2) (chain_path_r with m = 1).
+ * Neither triangle is a face of the wedge; two reflections in a row are on
+ * different triangles (one on each side of the wedge may be on the same
+ * triangle). Keys: rx, 3, then the three ids in path order (the wedge's with
+ * OR_DIFF); -1 padded to 2 + width (width >= 3). Returns the number of
+ * valid paths (may exceed cap). */
+int64_t or_diffract_refl2(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                          const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                          const or_params* P, int32_t width, int32_t* keys_out, opath* paths_out, int64_t cap) {
+  if (width < 3) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  int64_t nvalid = 0;
+  opath tmp;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (long w = 0; w < nw; ++w) {
+      const owedge* E[1] = {&W[w]};
+      for (int j1 = 0; j1 < ntri; ++j1) {
+        if ((tri_obj && tri_obj[j1] >= 0) || j1 == W[w].ta || j1 == W[w].tb) continue;
+        for (int j2 = 0; j2 < ntri; ++j2) {
+          if ((tri_obj && tri_obj[j2] >= 0) || j2 == W[w].ta || j2 == W[w].tb) continue;
+          for (int nb = 2; nb >= 0; --nb) {   /* reflections before the wedge */
+            const int na = 2 - nb;
+            if (nb != 1 && j1 == j2) continue;
+            const int j[2] = {j1, j2};
+            if (!chain_path_r(&S, E, 1, T, R, j, nb, j + nb, na, P, &tmp)) continue;
+            if (nvalid < cap) {
+              int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+              kk[0] = r;
+              kk[1] = 3;
+              kk[2 + nb] = (int32_t)w | OR_DIFF;
+              kk[2 + (nb == 0 ? 1 : 0)] = j1;
+              kk[2 + (nb == 2 ? 1 : 2)] = j2;
+              for (int q = 3; q < width; ++q) kk[2 + q] = -1;
+              paths_out[nvalid] = tmp;
+            }
+            nvalid++;
+          }
+        }
+      }
+    }
   }
   free(W);
   scene_free(&S);

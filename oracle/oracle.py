@@ -139,6 +139,9 @@ def lib():
         _lib.or_diffract_multi_refl.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                                 P(_Params), C.c_int32, C.c_int32, i32, C.c_void_p, C.c_int64]
         _lib.or_diffract_multi_refl.restype = C.c_int64
+        _lib.or_diffract_refl2.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                           P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
+        _lib.or_diffract_refl2.restype = C.c_int64
     return _lib
 
 
@@ -621,6 +624,29 @@ def diffract_refl(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OraclePa
         raise RuntimeError(f"or_diffract_refl failed: {n}")
     if n > cap:
         raise RuntimeError(f"or_diffract_refl: {n} paths exceed capacity {cap}")
+    return keys[:n].copy(), paths[:n].copy()
+
+
+def diffract_refl2(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleParams, cap=1 << 20):
+    """Steps 3-5 combined with two reflections on static triangles around a
+    first-order diffraction: both before the wedge, one on each side, or both
+    after it (image theory over the chain solver). Keys (rx, 3, ids in path
+    order, the wedge's with DIFF), -1 padded to 2 + max(prm.width, 3)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    width = max(prm.width, 3)
+    keys = np.zeros((cap, 2 + width), np.int32)
+    paths = np.zeros(cap, PATH_DTYPE)
+    prm_c = prm.c()
+    n = lib().or_diffract_refl2(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), _p(_i32(tri_obj), C.c_int32),
+                                wt.shape[0], _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                                _p(rx, C.c_float), rx.shape[0], C.byref(prm_c), width, _p(keys, C.c_int32),
+                                paths.ctypes.data_as(C.c_void_p), cap)
+    if n < 0:
+        raise RuntimeError(f"or_diffract_refl2 failed: {n}")
+    if n > cap:
+        raise RuntimeError(f"or_diffract_refl2: {n} paths exceed capacity {cap}")
     return keys[:n].copy(), paths[:n].copy()
 
 

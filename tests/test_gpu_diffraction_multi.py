@@ -382,3 +382,43 @@ def test_reflection_and_moving_boxes(cuda, mode):
     sc.tri_obj = np.concatenate([np.full(2, -1, np.int32), sc.tri_obj])
     sc.tri_mat = np.concatenate([np.full(2, scenes.MAT_CONCRETE, np.int32), sc.tri_mat])
     _check_refl(cuda, sc, range(3), 2, mode=mode, least=3)
+
+
+def test_highway_full_size_sampled(cuda):
+    """The bench's highway at full size (1M rays, 4 reflections, 200 moving
+    receivers, 2400 wedges on the barriers and the moving vehicles), frame 1
+    with diffraction up to order 2, in the launch configuration the bench
+    times: the order-2 paths of four receivers (the three with the most and
+    receiver 0) against the oracle's, which enumerates all 5.8M wedge pairs
+    for each."""
+    torch = cuda
+    hw = scenes.highway(n_frames=3, n_rays=1_000_000, max_refl=4)
+    s = dcem.Scene.from_scene(hw, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(scenes.fibonacci_sphere(hw.n_rays))
+    assert s.set_diffraction(True) == 2400
+    s.set_diffraction_order(2)
+    prm = P.gpu_params(hw, max_refl=4, mode=dcem.MODE_COHERENT)
+    for f in (0, 1):
+        s.update_transforms(hw.xf[f])
+        fr = s.trace(hw.tx, hw.rx[f], prm)
+    assert fr.stats["coherent"] == 1
+    g = fr.paths[_of_order(fr.paths, 2)]
+    counts = np.bincount(g["rx"], minlength=hw.nrx)
+    sample = [0] + [int(r) for r in np.argsort(-counts, kind="stable")[:3]]
+    assert counts[sample[1]] >= 2
+    oprm = P.oracle_params(hw, n_rays=hw.n_rays, max_refl=4)
+    wt = O.transform(hw.tris, hw.tri_obj, hw.xf[1])
+    for r in sample:
+        ck, cp = O.diffract_multi(wt, hw.tri_mat, hw.tri_obj, hw.materials, hw.tx, hw.rx[1][r:r + 1], oprm, 2)
+        ref = {tuple(k[1:]): p for k, p in zip(ck.tolist(), cp)}          # receiver index dropped
+        gr = g[g["rx"] == r]
+        gk = {tuple(k[1:]): p for k, p in zip(P.path_keys(gr, oprm.width), gr)}
+        flagged = {k for k, p in ref.items() if p["flags"] & FLAGS}
+        assert set(gk) ^ set(ref) <= flagged, (r, sorted(set(gk) ^ set(ref))[:4])
+        for k in set(gk) & set(ref):
+            za = complex(gk[k]["amp_re"], gk[k]["amp_im"])
+            zb = complex(ref[k]["amp_re"], ref[k]["amp_im"])
+            assert abs(za - zb) <= 1e-6 * abs(zb), (r, k)
+            assert abs(gk[k]["len_m"] - ref[k]["len_m"]) <= 1e-6
+            assert np.allclose(gk[k]["pts"][:2], ref[k]["pts"][:2], atol=1e-4)
+    s.close()

@@ -70,9 +70,18 @@ MUTANTS = [
     ("face_plane_chains_kept", "|| in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;", ") ok = 0;"),
     ("caustic_on_the_edge", "rho1 = s;\n    dir1 = ph;", "rho1 = rhoe + s;\n    dir1 = ph;"),
     ("principal_direction", "dir1 = ph;\n    rho2 = rhoe + s;", "dir1 = bd;\n    rho2 = rhoe + s;"),
-    ("chain_image_half", "if (Tj && first) src = sub(T, scl(Tj->nh, 2.0 * (dot(Tj->nh, T) - cpl)));",
-     "if (Tj && first) src = sub(T, scl(Tj->nh, 1.0 * (dot(Tj->nh, T) - cpl)));"),
-    ("chain_last_reflection_dropped", "Ev = reflect_field(S, P, Tj, dd, dout, Ev);", "(void)0;"),
+    ("chain_image_half", "return sub(x, scl(Tj->nh, 2.0 * (dot(Tj->nh, x) - cpl)));",
+     "return sub(x, scl(Tj->nh, 1.0 * (dot(Tj->nh, x) - cpl)));"),
+    ("chain_last_reflection_dropped", "Ev = reflect_field(S, P, &S->t[ja[i]], dlast, dout, Ev);", "(void)0;"),
+    # two reflections around a diffraction: the images' order, the unfolding, the field
+    ("refl2_image_order", "Simg[i + 1] = mirror_in(&S->t[jb[i]], Simg[i]);",
+     "Simg[i + 1] = mirror_in(&S->t[jb[nb - 1 - i]], Simg[i]);"),
+    ("refl2_observer_order", "Oimg[i] = mirror_in(&S->t[ja[i]], Oimg[i + 1]);",
+     "Oimg[i] = mirror_in(&S->t[ja[na - 1 - i]], Oimg[i + 1]);"),
+    ("refl2_unfold_from_the_last_image", "if (!mirror_point(&S->t[jb[i]], Simg[i + 1], b, P, scale, &fl, &Yb[i])) return 0;",
+     "if (!mirror_point(&S->t[jb[i]], Simg[nb], b, P, scale, &fl, &Yb[i])) return 0;"),
+    ("refl2_first_reflection_dropped", "Er = reflect_field(S, P, &S->t[jb[i]], din, dout, Er);",
+     "if (i == nb - 1) Er = reflect_field(S, P, &S->t[jb[i]], din, dout, Er);"),
     ("spherical_spreading", "double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);",
      "double complex A = csqrt(ell[0] / (s * (ell[0] + s))) * cexp(-I * k * s);"),
 ]

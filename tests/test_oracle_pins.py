@@ -978,3 +978,147 @@ def test_reflection_and_chain_reciprocity(oracle_mod):
         amp2, len2 = back[(a2, a1, a0)]
         assert abs(length - len2) <= 1e-9 * length
         assert abs(amp - amp2) <= 1e-9 * abs(amp)
+
+
+# ---------------------------------------------------------------------------
+# two reflections around a first-order diffraction
+# ---------------------------------------------------------------------------
+def _vwall(p0, p1, h=20.0):
+    (x0, y0), (x1, y1) = p0, p1
+    return scenes._quad((x0, y0, 0.0), (x1, y1, 0.0), (x1, y1, h), (x0, y0, h))
+
+
+def _walls_and_tip():
+    """Two vertical walls, along y = 25 (triangles 0-1) and along x + y = -20
+    (triangles 2-3): their mirrors do not commute (the planes meet at 45
+    degrees), and points whose coordinates are multiples of 0.5 keep that
+    property. Then the prism pointing along +x, its tip at (20, 0) a sharp
+    vertical wedge (triangles 4-9)."""
+    return _vwall((-10.0, 25.0), (40.0, 25.0)) + _vwall((-45.0, 25.0), (5.0, -25.0)) + _prism(0.0)
+
+
+_T2, _R2 = (14.0, 10.0, 1.5), (14.0, -10.0, 1.0)
+
+
+def _mirror(x, tri):
+    v = np.asarray(tri, np.float64)
+    n = np.cross(v[1] - v[0], v[2] - v[0])
+    n /= np.linalg.norm(n)
+    x = np.asarray(x, np.float64)
+    return x - 2.0 * np.dot(n, x - v[0]) * n
+
+
+def _half(x):
+    r = np.round(2.0 * x) / 2.0
+    assert np.max(np.abs(r - x)) <= 1e-9
+    return r
+
+
+def _refl2(O, tris, mats, tx, rx):
+    sc = scenes._static_scene("r2", tris, mats, tx, [rx])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    return O.diffract_refl2(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_two_reflections_and_diffraction_are_the_image_diffraction(oracle_mod, mat):
+    """Perfectly conducting vertical walls and vertical polarisation: a
+    reflection maps the vertically polarised transmitter (receiver) to a
+    vertically polarised image of opposite sign, so two reflections on the
+    walls around a diffraction, both before it or one on each side, give the
+    first-order diffraction of the prism alone from the transmitter's image
+    (in the walls' planes in path order) toward the receiver's image (in the
+    planes after the wedge, last first): the same diffraction point, length
+    and amplitude. The two walls' mirrors do not commute, so an image built in
+    the wrong order lands elsewhere."""
+    O = oracle_mod
+    tris = _walls_and_tip()
+    mats = [scenes.MAT_METAL] * 4 + [mat] * (len(tris) - 4)
+    k, p = _refl2(O, tris, mats, _T2, _R2)
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    kinds = set()
+    for kk, pp in zip(k, p):
+        ids = kk[2:5].tolist()
+        wi = [i for i, x in enumerate(ids) if x & O.DIFF][0]
+        before, after = ids[:wi], ids[wi + 1:]
+        if any(x >= 4 for x in before + after):
+            continue
+        src = np.asarray(_T2, np.float64)
+        for j in before:
+            src = _mirror(src, tris[j])
+        obs = np.asarray(_R2, np.float64)
+        for j in reversed(after):
+            obs = _mirror(obs, tris[j])
+        # exact in FP32: the images' coordinates are multiples of 0.5
+        src, obs = _half(src), _half(obs)
+        b = scenes._static_scene("tip", _prism(0.0), [mat] * 6, src, [obs])
+        bk, bp = O.diffract(b.tris.reshape(-1, 9), b.tri_mat, b.tri_obj, b.materials, b.tx, b.rx[0], prm)
+        q = pp["pts"][wi]
+        j = [i for i in range(len(bk)) if np.max(np.abs(bp["pts"][i][0] - q)) <= 1e-9]
+        assert len(j) == 1, (ids, len(bk))
+        assert abs(bp["len_m"][j[0]] - pp["len_m"]) <= 1e-12 * pp["len_m"]
+        a, b_ = complex(pp["amp_re"], pp["amp_im"]), complex(bp["amp_re"][j[0]], bp["amp_im"][j[0]])
+        assert abs(a - b_) <= 1e-9 * abs(b_), ids
+        kinds.add(wi)
+    assert kinds == {1, 2}                  # one on each side, and both before
+
+
+def test_two_reflections_and_diffraction_reciprocity(oracle_mod):
+    """Perfect conductors: swapping Tx and Rx turns each path into the one over
+    the same triangles and wedge in reverse order (two reflections before the
+    wedge become two after it), with the same length and amplitude."""
+    O = oracle_mod
+    tris = _walls_and_tip()
+    mats = [scenes.MAT_METAL] * len(tris)
+    out = []
+    for t, r in ((_T2, _R2), (_R2, _T2)):
+        k, p = _refl2(O, tris, mats, t, r)
+        out.append({tuple(kk[2:5].tolist()): (complex(pp["amp_re"], pp["amp_im"]), float(pp["len_m"]))
+                    for kk, pp in zip(k, p)})
+    fwd, back = out
+    assert len(fwd) >= 3 and len(fwd) == len(back)
+    assert {sum(1 for x in key[:[i for i, x in enumerate(key) if x & O.DIFF][0]]) for key in back} >= {0, 1}
+    for key, (amp, length) in fwd.items():
+        amp2, len2 = back[key[::-1]]
+        assert abs(length - len2) <= 1e-9 * length
+        assert abs(amp - amp2) <= 1e-9 * abs(amp)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_two_reflections_and_diffraction_obey_the_laws(oracle_mod, mat):
+    """Every path, the prism's faces among the reflectors too, checked point by
+    point without image theory: a reflection point lies on its triangle (in
+    its plane, inside it) and the outgoing leg is the mirror image of the
+    incoming one; the diffraction point lies on an edge of the prism and the
+    two legs make equal angles with it (Keller's cone); the length is the sum
+    of the legs."""
+    O = oracle_mod
+    tris = _walls_and_tip()
+    mats = [scenes.MAT_METAL] * 4 + [mat] * (len(tris) - 4)
+    tv = np.asarray(tris, np.float64)
+    edges = [(t[a], t[b]) for t in tv[4:] for a, b in ((0, 1), (1, 2), (2, 0))]
+    for tx, rx in ((_T2, _R2), (_R2, _T2)):
+        k, p = _refl2(O, tris, mats, tx, rx)
+        assert len(k) >= 3
+        for kk, pp in zip(k, p):
+            ids = kk[2:5].tolist()
+            X = [np.asarray(tx, np.float64)] + [pp["pts"][i] for i in range(3)] + [np.asarray(rx, np.float64)]
+            legs = [np.linalg.norm(X[i + 1] - X[i]) for i in range(4)]
+            assert abs(sum(legs) - pp["len_m"]) <= 1e-9 * pp["len_m"]
+            for i, tid in enumerate(ids):
+                A, Y, B = X[i], X[i + 1], X[i + 2]
+                din, dout = (Y - A) / legs[i], (B - Y) / legs[i + 1]
+                if tid & O.DIFF:
+                    hit = [(e0, e1) for e0, e1 in edges
+                           if np.linalg.norm(np.cross(e1 - e0, Y - e0)) <= 1e-9 * np.linalg.norm(e1 - e0)]
+                    assert hit, ids
+                    e = (hit[0][1] - hit[0][0]) / np.linalg.norm(hit[0][1] - hit[0][0])
+                    assert abs(np.dot(din, e) - np.dot(dout, e)) <= 1e-9
+                else:
+                    v = tv[tid]
+                    n = np.cross(v[1] - v[0], v[2] - v[0])
+                    n /= np.linalg.norm(n)
+                    assert abs(np.dot(n, Y - v[0])) <= 1e-9
+                    for a in range(3):
+                        assert np.dot(np.cross(v[(a + 1) % 3] - v[a], Y - v[a]), n) >= -1e-9
+                    assert np.max(np.abs(dout - (din - 2.0 * np.dot(din, n) * n))) <= 1e-9
