@@ -1152,9 +1152,11 @@ def run_diffraction(args, sc, rays, stream, dev, world, flush, warmup=3):
 def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
     """Diffraction of order 1-3 (Sec. III step 5, bound 3): frames/s of the
     city blocks (8 x 8 box buildings, 512 wedges, 64 receivers, 200k rays,
-    3 reflections) with diffraction up to order 1, 2 and 3, and up to order 2
+    3 reflections) with diffraction up to order 1, 2 and 3, up to order 2
     with one reflection before or after each chain (the ground and every
-    building face as reflector planes), the highway frames with order 2, the
+    building face as reflector planes), and first order with up to two
+    reflections around it; the highway frames with order 2, and with first
+    order and up to two reflections around it; the
     pre-test candidates and wedge pairs/triples per frame, and order 2 on 8
     of the city's receivers against the oracle."""
     import torch
@@ -1162,11 +1164,11 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
     from paper_2112_07115_gb300 import dcem, scenes
     city = scenes.city_blocks()
 
-    def frames(sc, order, n_rays, max_refl, mode, refl=False):
+    def frames(sc, order, n_rays, max_refl, mode, refl=0):
         s = dcem.Scene.from_scene(sc, stream=stream.cuda_stream)
         s.set_rays(scenes.fibonacci_sphere(n_rays))
         nw = s.set_diffraction(True)
-        nrp = s.set_diffraction_reflections(True) if refl else 0
+        nrp = s.set_diffraction_reflections(refl) if refl else 0
         s.set_diffraction_order(order)
         prm = dcem.default_params(max_refl=max_refl, freq_hz=sc.freq_hz, mode=mode)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1197,6 +1199,12 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
                "wedge_triples": st["diff_triples"], "fp64_candidates": st["diff_candidates"]}
         if refl:
             out.update({"reflector_planes": nrp, "with_one_reflection_by_order": with_refl})
+        if refl >= 2:
+            t3 = p["tri"][:, :3]
+            nd = ((t3 >= 0) & ((t3 & dcem.TRI_DIFFRACT) != 0)).sum(axis=1)
+            sel = (p["depth"] == 3) & (nd == 1)
+            at = [int((sel & ((t3[:, i] & dcem.TRI_DIFFRACT) != 0)).sum()) for i in range(3)]
+            out["with_two_reflections"] = {"both_before": at[2], "one_each_side": at[1], "both_after": at[0]}
         return out, fr
 
     out = {"city_workload": "8 x 8 box buildings (642 triangles, 512 wedges), 1 Tx at 10 m, 64 Rx at 1.5 m, "
@@ -1207,10 +1215,14 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
         out[f"city_order_{order}"] = r
         if order == 2:
             last = fr
-    r, _ = frames(city, 2, 200_000, 3, dcem.MODE_FULL, refl=True)
+    r, _ = frames(city, 2, 200_000, 3, dcem.MODE_FULL, refl=1)
     out["city_order_2_with_reflections"] = r
+    r, _ = frames(city, 1, 200_000, 3, dcem.MODE_FULL, refl=2)
+    out["city_order_1_with_two_reflections"] = r
     r, _ = frames(hw, 2, hw.n_rays, hw.max_refl, dcem.MODE_COHERENT)
     out["highway_order_2"] = r
+    r, _ = frames(hw, 1, hw.n_rays, hw.max_refl, dcem.MODE_COHERENT, refl=2)
+    out["highway_order_1_with_two_reflections"] = r
     # order 2 against the oracle on 8 receivers of the city (the oracle is brute force)
     sub = city.rx[0][:8]
     prm = O.OracleParams(freq_hz=city.freq_hz, max_refl=3)

@@ -338,8 +338,23 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
  * points, wedge rules and spreading over the unfolded chain), the
  * reflection point inside a triangle of the plane, every real leg
  * unoccluded, Fresnel at the reflection point; record: depth k + 1 with
- * tri = {triangle, wedges...} or {wedges..., triangle}. Errors: DCEM_ERR_ARG,
- * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
+ * tri = {triangle, wedges...} or {wedges..., triangle}. on = 2 adds, to
+ * on = 1, two reflections around a first-order diffraction (the paper's
+ * evaluation allows two reflections and one diffraction per path): for each
+ * (link, wedge, ordered pair of reflector planes) the paths Tx -> P1 -> P2 ->
+ * Q -> Rx, Tx -> P1 -> Q -> P2 -> Rx and Tx -> Q -> P1 -> P2 -> Rx (two
+ * reflections in a row on different planes), Q by Keller's law between the
+ * transmitter's image in the planes before the wedge (in path order) and the
+ * receiver's image in those after it (the last first), the reflection points
+ * by unfolding back from Q, each inside a triangle of its plane (the images
+ * are then taken in those triangles' own planes), the rules of first-order
+ * diffraction on the unfolded path, the four legs unoccluded; field: Fresnel
+ * at each reflection in the real directions and the UTD coefficient over the
+ * unfolded distances. Record: depth 3, tri = the two triangle ids and
+ * wedge | DCEM_TRI_DIFFRACT in path order, pts = the three points. Cost: one
+ * warp per (kind, link, plane pair) per frame, its lanes over the wedges.
+ * Errors: DCEM_ERR_ARG (on outside 0..2), DCEM_ERR_STATE (diffraction is
+ * off), DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes);
 
 /* With diffraction on: paths over up to max_order wedges (1, 2 or 3; Sec.

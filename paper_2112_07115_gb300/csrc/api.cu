@@ -248,7 +248,7 @@ struct dcem_scene {
   RPlane* rplanes = nullptr;   // diffraction combined with a reflection: reflector planes
   int* rmembers = nullptr;     // ... and their triangle ids
   int nrp = 0;
-  bool diff_refl = false;
+  int diff_refl = 0;               // reflections around a first-order diffraction (0..2)
   unsigned dsurv_cap = 0;
   int diff_order = 1;          // diffraction: most wedges on one path (1-3)
   int4* dseq2 = nullptr;       // ... the frame's wedge pairs and triples, the pair relation
@@ -1232,7 +1232,7 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
 }
 
 int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes) {
-  if (!s || (on != 0 && on != 1)) return DCEM_ERR_ARG;
+  if (!s || on < 0 || on > 2) return DCEM_ERR_ARG;
   if (on && !s->diffraction) return DCEM_ERR_STATE;
   if (on && !s->rplanes) {
     std::vector<RPlane> planes;
@@ -1246,7 +1246,7 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
       CK(cudaMemcpy(s->rmembers, members.data(), sizeof(int) * members.size(), cudaMemcpyHostToDevice));
     }
   }
-  s->diff_refl = on != 0;
+  s->diff_refl = on;
   if (n_planes) *n_planes = s->nrp;
   return DCEM_OK;
 }
@@ -1518,6 +1518,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.drel = dord >= 3 ? s->drel : nullptr;
   q.rmembers = dr ? s->rmembers : nullptr;
   q.nrp = dr ? s->nrp : 0;
+  q.drefl2 = dr && s->diff_refl >= 2 ? 1 : 0;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
   P.sticky = p->mode == DCEM_MODE_STICKY;
@@ -1703,7 +1704,8 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
                  (P.q.vc_next_key ? 1 : 0) +
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
-                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) + (P.q.rplanes && P.nlinks > 0 ? 1 : 0) +
+                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
+                 (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
                  (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
@@ -2235,7 +2237,7 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
       s->launches += 2 + (coh[i] ? 2 : 0) + (s->R > 0 ? 1 : 0) + 5 + (nrx[i] > 0 ? 1 : 0) +
                      (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
                      (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
-                     (P.q.rplanes && P.nlinks > 0 ? 1 : 0) +
+                     (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
                      (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order : 0) + (i == 0 ? 1 : 0);
       s->graph_replayed = 0;
       b->h_tab[i] = frame_trace_args(P);

@@ -2277,6 +2277,331 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
   atomicAdd(&a.ctr->n_valid, 1u);
 }
 
+// ---------------------------------------------------------------------------
+// two reflections around a first-order diffraction (Sec. III steps 3-5; the
+// paper's evaluation allows two reflections and one diffraction per path)
+// ---------------------------------------------------------------------------
+// Candidates (kind, link, p1, p2, wedge), the reflector planes p1, p2 in path
+// order: kind 0 both before the wedge (Tx -> P1 -> P2 -> Q -> Rx), 1 one on
+// each side (Tx -> P1 -> Q -> P2 -> Rx), 2 both after it (Tx -> Q -> P1 -> P2
+// -> Rx). By image theory the diffraction runs from the transmitter's image
+// in the planes before the wedge (taken in path order) toward the receiver's
+// image in the planes after it (the last one first); the reflection points
+// follow by unfolding back from Q. A block (kind, link, p1, p2) goes to one
+// warp, its lanes take the wedges. Survivors carry 10 in bits 63-62 and 1 in
+// bit 61 over (block * nw + wedge).
+constexpr unsigned long long kRefl2Tag = kReflTag | (1ull << 61);
+constexpr unsigned long long kRefl2Mask = (1ull << 61) - 1ull;
+
+// Can a leg from S (a point's image in plane P1) to some point of P2's box
+// cross P1 inside its box? With every corner of P2's box across the plane
+// from S, the legs' crossings lie within the box of the corner legs'
+// crossings; "no" when every corner lies on S's side (no leg crosses the
+// plane) or when that box, widened by m, misses P1's box.
+__device__ __forceinline__ bool pair_reachable(const RPlane& P1, float3 S, const RPlane& P2, float m) {
+  const float3 n = f3((float)P1.n[0], (float)P1.n[1], (float)P1.n[2]);
+  const float c = (float)P1.c;
+  const float ds = fdot3(n, S) - c;
+  if (fabsf(ds) <= m) return true;
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  int same = 0;
+  for (int q = 0; q < 8; ++q) {
+    const float3 X = f3((q & 1) ? P2.box[3] + m : P2.box[0] - m, (q & 2) ? P2.box[4] + m : P2.box[1] - m,
+                        (q & 4) ? P2.box[5] + m : P2.box[2] - m);
+    const float dx = fdot3(n, X) - c;
+    if (fabsf(dx) <= m) return true;
+    if ((dx > 0.0f) == (ds > 0.0f)) {
+      ++same;
+      continue;
+    }
+    const float t = ds / (ds - dx);
+    const float x = S.x + t * (X.x - S.x), y = S.y + t * (X.y - S.y), z = S.z + t * (X.z - S.z);
+    lo[0] = fminf(lo[0], x); lo[1] = fminf(lo[1], y); lo[2] = fminf(lo[2], z);
+    hi[0] = fmaxf(hi[0], x); hi[1] = fmaxf(hi[1], y); hi[2] = fmaxf(hi[2], z);
+  }
+  if (same == 8) return false;
+  if (same > 0) return true;
+  for (int k = 0; k < 3; ++k)
+    if (hi[k] < P1.box[k] - m || lo[k] > P1.box[3 + k] + m) return false;
+  return true;
+}
+
+// The crossing X of the unfolded leg a0 -> a1 with plane P, within margins
+// (delta + 2e-4 of the distances): 0 when it certainly lies off the leg or
+// off P's box, 1 with X set, 2 when the leg runs nearly parallel to the
+// plane (no conclusion).
+__device__ __forceinline__ int refl_cross32(const RPlane& P, float3 a0, float3 a1, float delta, float3& X) {
+  const float3 n = f3((float)P.n[0], (float)P.n[1], (float)P.n[2]);
+  const float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
+  const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
+  if (!(fabsf(den) > 1e-6f * len)) return 2;
+  const float t = ((float)P.c - fdot3(n, a0)) / den;
+  const float mt = (delta + 2e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
+  if (t < -mt || t > 1.0f + mt) return 0;
+  X = f3(a0.x + t * dv.x, a0.y + t * dv.y, a0.z + t * dv.z);
+  const float mb = delta + 2e-4f * (len + sqrtf(fdot3(X, X)));
+  if (X.x < P.box[0] - mb || X.y < P.box[1] - mb || X.z < P.box[2] - mb || X.x > P.box[3] + mb ||
+      X.y > P.box[4] + mb || X.z > P.box[5] + mb)
+    return 0;
+  return 1;
+}
+
+// FP32 pre-test of one candidate: false only when the FP64 test rejects it
+// too. S, O: the source and observer of the diffraction (images); S1: the
+// transmitter's image in P1 (kind 0), O1: the receiver's image in P2 (kind 2).
+__device__ __forceinline__ bool refl2_candidate(const Wedge& W, const RPlane& P1, const RPlane& P2, int kind,
+                                                float3 S, float3 S1, float3 O, float3 O1) {
+  if (!diffract_candidate(W, make_float4(S.x, S.y, S.z, 0.0f), make_float4(O.x, O.y, O.z, 0.0f))) return false;
+  const float3 e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
+  const float3 p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+  const float3 dt = f3(S.x - p0.x, S.y - p0.y, S.z - p0.z), dr = f3(O.x - p0.x, O.y - p0.y, O.z - p0.z);
+  const float zt = fdot3(dt, e), zr = fdot3(dr, e);
+  const float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
+  const float3 pr = f3(dr.x - e.x * zr, dr.y - e.y * zr, dr.z - e.z * zr);
+  const float rt = sqrtf(fdot3(pt, pt)), rr = sqrtf(fdot3(pr, pr));
+  if (!(rt > 1e-3f && rr > 1e-3f)) return true;
+  const float zq = zt + (zr - zt) * rt / (rt + rr);
+  const float3 Q = f3(p0.x + e.x * zq, p0.y + e.y * zq, p0.z + e.z * zq);
+  const float d = 0.1f;
+  float3 X;
+  if (kind == 0) {
+    const int r = refl_cross32(P2, S, Q, d, X);
+    if (r == 0) return false;
+    if (r == 1 && refl_cross32(P1, S1, X, d, X) == 0) return false;
+  } else if (kind == 1) {
+    if (refl_cross32(P1, S, Q, d, X) == 0) return false;
+    if (refl_cross32(P2, Q, O, d, X) == 0) return false;
+  } else {
+    const int r = refl_cross32(P1, Q, O, d, X);
+    if (r == 0) return false;
+    if (r == 1 && refl_cross32(P2, X, O1, d, X) == 0) return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_diffract_refl2_pre(PathArgs a, int nlinks) {
+  const long nblk = 3L * nlinks * a.nrp * a.nrp;
+  const int lane = threadIdx.x & 31;
+  const long nwarp = (long)gridDim.x * (blockDim.x >> 5);
+  for (long b = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nblk; b += nwarp) {
+    long r = b;
+    const int p2 = (int)(r % a.nrp);
+    r /= a.nrp;
+    const int p1 = (int)(r % a.nrp);
+    r /= a.nrp;
+    const int link = (int)(r % nlinks), kind = (int)(r / nlinks);
+    if (kind != 1 && p1 == p2) continue;  // two reflections in a row on one plane
+    const RPlane &P1 = a.rplanes[p1], &P2 = a.rplanes[p2];
+    const float4 tv = a.txs[link / a.nrx], rv = a.rx[link % a.nrx];
+    const float3 T = f3(tv.x, tv.y, tv.z), R = f3(rv.x, rv.y, rv.z);
+    const float3 n1 = f3((float)P1.n[0], (float)P1.n[1], (float)P1.n[2]);
+    const float3 n2 = f3((float)P2.n[0], (float)P2.n[1], (float)P2.n[2]);
+    const float m = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fabsf(R.x) + fabsf(R.y) + fabsf(R.z));
+    float3 S = T, S1 = T, O = R, O1 = R;
+    if (kind == 0) {
+      S1 = mirror32(T, n1, (float)P1.c);
+      S = mirror32(S1, n2, (float)P2.c);
+      if (!pair_reachable(P1, S1, P2, m)) continue;
+    } else if (kind == 1) {
+      S = S1 = mirror32(T, n1, (float)P1.c);
+      O = O1 = mirror32(R, n2, (float)P2.c);
+    } else {
+      O1 = mirror32(R, n2, (float)P2.c);
+      O = mirror32(O1, n1, (float)P1.c);
+      if (!pair_reachable(P2, O1, P1, m)) continue;
+    }
+    for (int w0 = 0; w0 < a.nw; w0 += 32) {
+      const int w = w0 + lane;
+      const bool keep = w < a.nw && refl2_candidate(a.wedges[w], P1, P2, kind, S, S1, O, O1);
+      const unsigned mk = __ballot_sync(0xffffffffu, keep);
+      if (!mk) continue;
+      unsigned at = 0;
+      if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
+      at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+      if (keep) {
+        if (at < a.dsurv_cap) a.dsurv[at] = kRefl2Tag | ((unsigned long long)b * a.nw + w);
+        else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ d3w mirror_d(d3w x, d3w n, double c) { return x - n * (2.0 * (dotw(n, x) - c)); }
+
+// One survivor of k_diffract_refl2_pre: the images, the Keller point and the
+// wedge rules (chain_geometry with one wedge) and the reflection points on
+// the group planes; the member triangles holding those points; everything
+// again on the members' own planes (the oracle's mirrors are the static
+// triangles); the four real legs (FP32 any-hit; the triangle excluded at a
+// reflection point, the wedge's faces at Q); then the field: the
+// transmitter's wave along its first real leg, Fresnel at each reflection
+// before the wedge in the real directions, the UTD coefficient over the
+// unfolded distances, Fresnel at each reflection after it. Record: depth 3.
+__device__ __noinline__ void diffract_refl2(const PathArgs& a, unsigned long long code, double k, double lam,
+                                            unsigned& ovf, TStack& st) {
+  const int w = (int)(code % (unsigned long long)a.nw);
+  unsigned long long b = code / (unsigned long long)a.nw;
+  const int p2 = (int)(b % (unsigned long long)a.nrp);
+  b /= (unsigned long long)a.nrp;
+  const int p1 = (int)(b % (unsigned long long)a.nrp);
+  b /= (unsigned long long)a.nrp;
+  const unsigned long long nlinks = (unsigned long long)a.dntx * a.nrx;
+  const int link = (int)(b % nlinks), kind = (int)(b / nlinks);
+  const int nb = kind == 0 ? 2 : kind == 1 ? 1 : 0, na = 2 - nb;
+  const Wedge& W = a.wedges[w];
+  const Wedge* E[1] = {&W};
+  const float4 rxv = a.rx[link % a.nrx], txv = a.txs[link / a.nrx];
+  const d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
+  // the planes of the two reflections in path order: the groups', then the members'
+  const int pg[2] = {p1, p2};
+  d3w pn[2];
+  double pc[2];
+  int pj[2] = {-1, -1};
+  float4 pm[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+  for (int i = 0; i < 2; ++i) {
+    const RPlane& G = a.rplanes[pg[i]];
+    pn[i] = D3(G.n[0], G.n[1], G.n[2]);
+    pc[i] = G.c;
+  }
+  d3w X[3], Y[2];
+  double ell[2], phip[1], phi[1];
+  for (int pass = 0; pass < 2; ++pass) {
+    d3w Sim[3], Oim[3];
+    Sim[0] = T;
+    for (int i = 0; i < nb; ++i) Sim[i + 1] = mirror_d(Sim[i], pn[i], pc[i]);
+    Oim[na] = R;
+    for (int i = na - 1; i >= 0; --i) Oim[i] = mirror_d(Oim[i + 1], pn[nb + i], pc[nb + i]);
+    if (!chain_geometry(E, 1, Sim[nb], Oim[0], X, ell, phip, phi)) return;
+    d3w bp = X[1];
+    for (int i = nb - 1; i >= 0; --i) {
+      if (!leg_plane(Sim[i + 1], bp, pn[i], pc[i], Y[i])) return;
+      bp = Y[i];
+    }
+    d3w ap = X[1];
+    for (int i = 0; i < na; ++i) {
+      if (!leg_plane(ap, Oim[i], pn[nb + i], pc[nb + i], Y[nb + i])) return;
+      ap = Y[nb + i];
+    }
+    for (int i = 0; i < 2; ++i) {
+      d3w v0, v1, v2;
+      float4 mj;
+      if (pass == 0) {  // the member triangle holding the point: its own plane next
+        const RPlane& G = a.rplanes[pg[i]];
+        for (int q = 0; q < G.count && pj[i] < 0; ++q) {
+          const int id = a.rmembers[G.first + q];
+          if (id == W.ta || id == W.tb) continue;
+          tri64(a, id, v0, v1, v2, mj);
+          if (inside_tri64(v0, v1, v2, Y[i])) {
+            pj[i] = id;
+            pm[i] = mj;
+            pn[i] = unitw(crossw(v1 - v0, v2 - v0));
+            pc[i] = dotw(pn[i], v0);
+          }
+        }
+        if (pj[i] < 0) return;
+      } else {
+        tri64(a, pj[i], v0, v1, v2, mj);
+        if (!inside_tri64(v0, v1, v2, Y[i])) return;
+      }
+    }
+  }
+  // the real legs: P the path's points, two excluded triangles at each
+  d3w P[5];
+  int ex[5][2], ny = 0;
+  P[ny] = T; ex[ny][0] = ex[ny][1] = -1; ++ny;
+  for (int i = 0; i < nb; ++i) { P[ny] = Y[i]; ex[ny][0] = ex[ny][1] = pj[i]; ++ny; }
+  P[ny] = X[1]; ex[ny][0] = W.ta; ex[ny][1] = W.tb; ++ny;
+  for (int i = 0; i < na; ++i) { P[ny] = Y[nb + i]; ex[ny][0] = ex[ny][1] = pj[nb + i]; ++ny; }
+  P[ny] = R; ex[ny][0] = ex[ny][1] = -1; ++ny;
+  for (int q = 0; q + 1 < ny; ++q) {
+    const d3w dv = P[q + 1] - P[q];
+    RayPre rp = ray_pre(f3((float)P[q].x, (float)P[q].y, (float)P[q].z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex[q][0], ex[q][1], ovf, st, ex[q + 1][0], ex[q + 1][1]))
+      return;
+  }
+  unsigned fl = 0;
+  const d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
+  const d3w ip = (X[1] - X[0]) * (1.0 / ell[0]);  // the real direction into Q
+  double sn, cs;
+  sincos(-k * ell[0], &sn, &cs);
+  const zd Ei = Z(cs / ell[0], sn / ell[0]);
+  d3w din = nb ? unitw(P[1] - T) : ip;
+  const d3w e0 = polw(u, din, fl);
+  zv3 Er = {Z(e0.x), Z(e0.y), Z(e0.z)};
+  for (int i = 0; i < nb; ++i) {
+    const d3w dout = i == nb - 1 ? ip : unitw(P[i + 2] - P[i + 1]);
+    Er = reflect_field_d(a, pn[i], pm[i], din, dout, Er);
+    din = dout;
+  }
+  zv3 Ev = {Er.x * Ei, Er.y * Ei, Er.z * Ei};
+  {  // the wedge: UTD over the unfolded distances, a spherical wave arriving
+    const double s = ell[1], nn = W.n, rhoe = ell[0], rho1 = ell[0], rho2 = ell[0];
+    const d3w e = D3(W.e[0], W.e[1], W.e[2]);
+    const d3w dd = (X[2] - X[1]) * (1.0 / s);
+    const double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
+    const double sb = sin(beta0);
+    const d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
+    const d3w bpv = crossw(ip, php), bd = crossw(dd, ph);
+    const double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
+    const float4 ma =
+        a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.ta, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+    const float4 mb =
+        a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.tb, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+    zd r0s, r0h, rns, rnh;
+    fresnel_d(ma, a.freq, fabs(sin(phip[0])), r0s, r0h);
+    fresnel_d(mb, a.freq, fabs(sin(nn * M_PI - phi[0])), rns, rnh);
+    const UtdParts up = utd_parts(nn, phi[0], phip[0], beta0, L, k, fl);
+    const zd Ds = utd_coeff(up, r0s, rns), Dh = utd_coeff(up, r0h, rnh);
+    sincos(-k * s, &sn, &cs);
+    const zd A = Z(cs, sn) * sqrt(rhoe / (s * (rhoe + s)));
+    const zd cb = Ds * zvdot(Ev, bpv) * A * -1.0, cp = Dh * zvdot(Ev, php) * A * -1.0;
+    Ev = zv3{cb * bd.x + cp * ph.x, cb * bd.y + cp * ph.y, cb * bd.z + cp * ph.z};
+    din = dd;
+  }
+  for (int i = 0; i < na; ++i) {  // reflected after the wedge, toward the real receiver
+    const int at = ny - 1 - na + i;
+    const d3w dout = unitw(P[at + 1] - P[at]);
+    Ev = reflect_field_d(a, pn[nb + i], pm[nb + i], din, dout, Ev);
+    din = dout;
+  }
+  const d3w prx = polw(u, din * -1.0, fl);
+  const zd amp = zvdot(Ev, prx) * (lam / (4.0 * M_PI));
+  unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
+  if (uu >= a.ucap) {
+    atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
+    return;
+  }
+  int ids[3];
+  for (int i = 0; i < nb; ++i) ids[i] = pj[i];
+  ids[nb] = w | kDiffBit;
+  for (int i = 0; i < na; ++i) ids[nb + 1 + i] = pj[nb + i];
+  PathRec rec;
+  rec.key = seq_key(link % a.nrx, 3, [&](int q) { return ids[q]; });
+  rec.rx = link;
+  rec.depth = 3;
+  rec.ray = -1;
+  rec.flags = fl;
+  rec.valid = 1;
+  rec.pad = 0;
+  rec.len = ell[0] + ell[1];
+  rec.amp_re = amp.re;
+  rec.amp_im = amp.im;
+  for (int q = 0; q < kMaxRefl; ++q) {
+    rec.tri[q] = q < 3 ? ids[q] : -1;
+    rec.pts[q][0] = rec.pts[q][1] = rec.pts[q][2] = 0.0f;
+  }
+  for (int q = 1; q + 1 < ny; ++q) {
+    rec.pts[q - 1][0] = (float)P[q].x;
+    rec.pts[q - 1][1] = (float)P[q].y;
+    rec.pts[q - 1][2] = (float)P[q].z;
+  }
+  a.prec[uu] = rec;
+  unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
+  if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
+  else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+  atomicAdd(&a.ctr->n_valid, 1u);
+}
+
 // Pass 1 over every (link, wedge) pair: the FP32 pre-test rejects most of
 // them; the survivors' indices go to a list (one atomic per warp).
 __global__ void __launch_bounds__(256) k_diffract_pre(PathArgs a, int nlinks) {
@@ -2319,7 +2644,8 @@ __global__ void __launch_bounds__(kDiffThreads) k_diffract(PathArgs a) {
   for (unsigned i = blockIdx.x + gridDim.x * threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned long long c = a.dsurv[i];
     const unsigned kind = (unsigned)(c >> kKindShift);
-    if (kind == 2u) diffract_refl_pair(a, c & ~kReflTag, k, lam, ovf, st);
+    if (kind == 2u && ((c >> 61) & 1ull)) diffract_refl2(a, c & kRefl2Mask, k, lam, ovf, st);
+    else if (kind == 2u) diffract_refl_pair(a, c & ~kReflTag, k, lam, ovf, st);
     else if (kind != 0u) diffract_multi(a, c, k, lam, ovf, st);
     else diffract_pair(a, (long)c, k, lam, ovf, st);
   }
@@ -2478,6 +2804,11 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
       long tr = (long)nlinks * a.nw * a.nrp * 2;
       long gr = std::min<long>((tr + 255) / 256, 8L * sms);
       k_diffract_refl_pre<<<(int)std::max<long>(gr, 1), 256, 0, st>>>(a, nlinks);
+      if (a.drefl2) {
+        long nblk = 3L * nlinks * a.nrp * a.nrp;
+        long g2 = std::min<long>((nblk + 7) / 8, 8L * sms);
+        k_diffract_refl2_pre<<<(int)std::max<long>(g2, 1), 256, 0, st>>>(a, nlinks);
+      }
     }
     PathArgs b = a;  // chains: transmitters, and the reflector planes applied to them
     b.dntx = nlinks / a.nrx;

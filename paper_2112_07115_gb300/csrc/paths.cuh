@@ -59,6 +59,7 @@ struct PathArgs {
   const RPlane* rplanes;
   const int* rmembers;
   int nrp;
+  int drefl2;                     // 1: also two reflections around a first-order diffraction
   // diffraction of order 2 and 3 (diff_order <= 1: off): the wedge pairs
   // (v, w1, w2, -1) and triples (v, w1, w2, w3) of the frame, v a source
   // (a transmitter, or with reflector planes the image of transmitter t in

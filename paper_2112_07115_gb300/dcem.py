@@ -571,11 +571,12 @@ class Scene:
         """First-order edge diffraction paths (UTD); returns the wedge count."""
         return dcem_scene_set_diffraction(self.h, on)
 
-    def set_diffraction_reflections(self, on: bool = True) -> int:
-        """With diffraction on: one reflection on a static reflector plane
-        before or after the diffraction; returns the reflector-plane count."""
+    def set_diffraction_reflections(self, on: int = 1) -> int:
+        """With diffraction on: reflections on static reflector planes around
+        the diffraction, up to ``on`` (0-2; True is 1) around a first-order
+        one, one before or after a chain; returns the reflector-plane count."""
         n = C.c_int32(0)
-        _check(lib().dcem_scene_set_diffraction_reflections(self.h, int(bool(on)), C.byref(n)),
+        _check(lib().dcem_scene_set_diffraction_reflections(self.h, int(on), C.byref(n)),
                "dcem_scene_set_diffraction_reflections")
         return int(n.value)
 

@@ -4,8 +4,9 @@ quick checks: python -m paper_2112_07115_gb300.frames --workload toy
 
 Workloads: toy (the toy street, 10k rays, 3 reflections), highway (1M rays,
 4 reflections, 200 roof receivers; --freq selects 28 or 5.9 GHz), roadside
-(the highway with 200 static roadside receivers), city (8 x 8 box buildings,
-diffraction up to --diffraction-order wedges)."""
+(the highway with 200 static roadside receivers), city (8 x 8 box buildings).
+--diffraction-order turns diffraction on (up to that many wedges),
+--diffraction-reflections adds reflections around it."""
 import argparse
 import sys
 
@@ -18,6 +19,8 @@ def main(argv=None):
     ap.add_argument("--freq", type=float, default=28e9)
     ap.add_argument("--rays", type=int, default=0, help="ray count (0: the workload's own)")
     ap.add_argument("--diffraction-order", type=int, default=0, help="0: no diffraction, else 1-3")
+    ap.add_argument("--diffraction-reflections", type=int, default=0,
+                    help="with diffraction: reflections around it (0-2)")
     args = ap.parse_args(argv)
 
     import torch
@@ -40,6 +43,8 @@ def main(argv=None):
     if args.diffraction_order:
         s.set_diffraction(True)
         s.set_diffraction_order(args.diffraction_order)
+        if args.diffraction_reflections:
+            s.set_diffraction_reflections(args.diffraction_reflections)
     mode = dcem.MODE_COHERENT if args.mode == "coherent" else dcem.MODE_FULL
     prm = dcem.default_params(max_refl=sc.max_refl, freq_hz=sc.freq_hz, mode=mode)
     for i in range(args.frames):
