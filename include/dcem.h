@@ -373,9 +373,10 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
  * edge-diffracted wave (Kouyoumjian & Pathak 1974, straight edge: a caustic
  * on the edge and one at the arriving wavefront's radius of curvature along
  * the edge). Record: depth m, tri[i] = wedge_i | DCEM_TRI_DIFFRACT, pts[i]
- * = Q_i, ray = -1. Cost per frame: one pre-test thread per (transmitter,
- * wedge pair), for m = 3 per (pair, wedge), then per (sequence, receiver);
- * the wedge-pair relation takes nw * nw bits of device memory for m = 3.
+ * = Q_i, ray = -1. Cost per frame: the wedge-pair relation once (one thread
+ * per ordered pair, nw * nw bits of device memory), one pre-test thread per
+ * (transmitter, wedge pair), for m = 3 per (pair, wedge), then per
+ * (sequence, receiver).
  * With reflector planes on (dcem_scene_set_diffraction_reflections) every
  * chain may also have one reflection before or after it. max_order = 1
  * turns the higher orders off. Errors: DCEM_ERR_ARG, DCEM_ERR_STATE

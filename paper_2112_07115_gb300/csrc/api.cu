@@ -241,8 +241,12 @@ struct dcem_scene {
   std::vector<float> tris_h;   // input vertices (static ones are world space) and objects,
   std::vector<int> tri_obj_h;  // kept for the wedge search of edge diffraction
   Wedge* wedges = nullptr;     // first-order diffraction: wedge geometry (per frame)
+  WedgeF* wedgesf = nullptr;   // ... the same in FP32
   WedgeTopo* wtopo = nullptr;  // ... and topology
   int nw = 0;
+  int* wperm = nullptr;        // wedge clusters: the wedges in spatial order, 32 per cluster,
+  float* wcbox = nullptr;      // and the clusters' boxes (per frame)
+  int nwc = 0;
   bool diffraction = false;
   unsigned long long* dsurv = nullptr;  // diffraction: pre-test survivor list
   RPlane* rplanes = nullptr;   // diffraction combined with a reflection: reflector planes
@@ -389,7 +393,8 @@ void scene_free(dcem_scene* s) {
   dfree(s->tris); dfree(s->slot_of_id); dfree(s->objv); dfree(s->objv_src); dfree(s->sel_d);
   dfree(s->tri_mat_d); dfree(s->v9d); dfree(s->nodes); dfree(s->qnodes); dfree(s->qframe);
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
-  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wtopo); dfree(s->dsurv);
+  dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wedgesf); dfree(s->wtopo);
+  dfree(s->wperm); dfree(s->wcbox); dfree(s->dsurv);
   dfree(s->rplanes); dfree(s->rmembers);
   dfree(s->dseq2); dfree(s->dseq3); dfree(s->drel);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
@@ -699,6 +704,50 @@ std::vector<WedgeTopo> find_wedges(const std::vector<float>& tris, const std::ve
   return out;
 }
 
+// The wedges in a spatial order for the clusters of the two-reflection
+// pre-test: static wedges by the Morton code (10 bits per axis over their
+// box) of their edges' midpoints, then each moving object's wedges together
+// (their input coordinates are object space), each group by index.
+std::vector<int> wedge_order(const std::vector<float>& tris, const std::vector<int>& tri_obj,
+                             const std::vector<WedgeTopo>& w) {
+  const size_t nw = w.size();
+  std::vector<std::array<double, 3>> mid(nw);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (size_t i = 0; i < nw; ++i) {
+    const float* a = &tris[9 * (size_t)w[i].ta + 3 * w[i].ka0];
+    const float* b = &tris[9 * (size_t)w[i].ta + 3 * w[i].ka1];
+    for (int k = 0; k < 3; ++k) {
+      mid[i][k] = 0.5 * ((double)a[k] + b[k]);
+      if (tri_obj[w[i].ta] < 0) {
+        lo[k] = std::min(lo[k], mid[i][k]);
+        hi[k] = std::max(hi[k], mid[i][k]);
+      }
+    }
+  }
+  auto spread = [](uint64_t x) {  // 10 bits to every third bit
+    uint64_t r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((x >> b) & 1ull) << (3 * b);
+    return r;
+  };
+  std::vector<std::array<uint64_t, 3>> key(nw);
+  for (size_t i = 0; i < nw; ++i) {
+    const int obj = tri_obj[w[i].ta];
+    uint64_t m = 0;
+    if (obj < 0)
+      for (int k = 0; k < 3; ++k) {
+        double ext = hi[k] - lo[k];
+        double u = ext > 0.0 ? (mid[i][k] - lo[k]) / ext : 0.0;
+        uint64_t q = (uint64_t)std::min(1023.0, std::max(0.0, std::floor(u * 1024.0)));
+        m |= spread(q) << k;
+      }
+    key[i] = {obj < 0 ? 0ull : 1ull + (uint64_t)obj, m, (uint64_t)i};
+  }
+  std::vector<int> perm(nw);
+  for (size_t i = 0; i < nw; ++i) perm[i] = (int)i;
+  std::sort(perm.begin(), perm.end(), [&](int x, int y) { return key[x] < key[y]; });
+  return perm;
+}
+
 // Reflector planes: the static triangles grouped by plane (unit normal
 // oriented with its first nonzero component positive, offset c = n . v0),
 // planes equal when the normals agree to 1e-7 and the offsets to 1e-4 m.
@@ -744,8 +793,12 @@ void group_planes(const std::vector<float>& tris, const std::vector<int>& tri_ob
            key(it[j], 2) == key(it[i], 2) && key(it[j], 3) == key(it[i], 3))
       ++j;
     RPlane p;
-    for (int k = 0; k < 3; ++k) p.n[k] = it[i].n[k];
+    for (int k = 0; k < 3; ++k) {
+      p.n[k] = it[i].n[k];
+      p.nf[k] = (float)it[i].n[k];
+    }
     p.c = it[i].c;
+    p.cf = (float)it[i].c;
     p.first = (int)members.size();
     p.count = (int)(j - i);
     for (int k = 0; k < 3; ++k) {
@@ -1217,9 +1270,15 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
     std::vector<WedgeTopo> w = find_wedges(s->tris_h, s->tri_obj_h);
     s->nw = (int)w.size();
     if (s->nw) {
+      std::vector<int> perm = wedge_order(s->tris_h, s->tri_obj_h, w);
+      s->nwc = (s->nw + kWedgeCluster - 1) / kWedgeCluster;
       CK(dalloc(&s->wtopo, s->nw));
       CK(dalloc(&s->wedges, s->nw));
+      CK(dalloc(&s->wedgesf, s->nw));
+      CK(dalloc(&s->wperm, s->nw));
+      CK(dalloc(&s->wcbox, 6 * (size_t)s->nwc));
       CK(cudaMemcpy(s->wtopo, w.data(), sizeof(WedgeTopo) * w.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(s->wperm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
     }
   }
   if (on && s->nw && !s->dsurv) {  // grown (and the frame traced again) when a frame needs more
@@ -1257,11 +1316,11 @@ int dcem_scene_set_diffraction_order(dcem_scene* s, int32_t max_order) {
   if (max_order >= 2 && !s->dseq2 && s->nw > 1) {  // lists grown (and the frame traced again) on demand
     CK(dalloc(&s->dseq2, (size_t)4096));
     s->dseq2_cap = 4096;
+    CK(dalloc(&s->drel, ((size_t)s->nw * s->nw + 31) / 32));
   }
   if (max_order >= 3 && !s->dseq3 && s->nw > 2) {
     CK(dalloc(&s->dseq3, (size_t)4096));
     s->dseq3_cap = 4096;
-    CK(dalloc(&s->drel, ((size_t)s->nw * s->nw + 31) / 32));
   }
   CK(cudaStreamSynchronize(s->st));
   s->diff_order = max_order;
@@ -1503,8 +1562,12 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.tx_power = p->tx_power_w;
   q.ctr = s->ctr;
   q.wedges = s->diffraction && s->nw > 0 ? s->wedges : nullptr;
+  q.wf = s->wedgesf;
   q.wtopo = s->wtopo;
   q.nw = s->nw;
+  q.wperm = s->wperm;
+  q.wcbox = s->wcbox;
+  q.nwc = s->nwc;
   q.dsurv = s->dsurv;
   q.dsurv_cap = s->dsurv_cap;
   const bool dr = q.wedges && s->diff_refl && s->nrp > 0;
@@ -1515,7 +1578,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.dseq2_cap = dord >= 2 ? s->dseq2_cap : 0;
   q.dseq3 = dord >= 3 ? s->dseq3 : nullptr;
   q.dseq3_cap = dord >= 3 ? s->dseq3_cap : 0;
-  q.drel = dord >= 3 ? s->drel : nullptr;
+  q.drel = dord >= 2 ? s->drel : nullptr;
   q.rmembers = dr ? s->rmembers : nullptr;
   q.nrp = dr ? s->nrp : 0;
   q.drefl2 = dr && s->diff_refl >= 2 ? 1 : 0;
@@ -1706,7 +1769,7 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
                  (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
                  (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
-                 (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order : 0);
+                 (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -2238,7 +2301,7 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
                      (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
                      (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
                      (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
-                     (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order : 0) + (i == 0 ? 1 : 0);
+                     (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 : 0) + (i == 0 ? 1 : 0);
       s->graph_replayed = 0;
       b->h_tab[i] = frame_trace_args(P);
     }

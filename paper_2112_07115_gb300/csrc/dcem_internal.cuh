@@ -40,9 +40,19 @@ struct Wedge {
 // box of its triangles and their ids (members[first .. first + count)).
 struct RPlane {
   double n[3], c;
+  float nf[3], cf;  // n and c rounded to FP32 (for the pre-tests)
   float box[6];
   int first, count;
 };
+
+// A wedge's frame rounded to FP32 for the pre-tests (written with the FP64
+// record every frame): start, unit edge direction, face 0's direction and
+// the exterior's, the length and n pi.
+struct WedgeF {
+  float3 p0, e, t0, y0;
+  float len, npi;
+};
+constexpr int kWedgeCluster = 32;  // wedges per cluster (a warp's lanes)
 
 // Wedge topology (fixed for a rigid object): faces ta < tb, the local
 // indices of the edge's vertices in ta and of the faces' third vertices.

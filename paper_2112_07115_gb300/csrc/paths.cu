@@ -849,9 +849,8 @@ __device__ __forceinline__ float wedge_angle32(float3 d, float3 t0, float3 y0, f
   return a;
 }
 
-__device__ __forceinline__ bool diffract_candidate(const Wedge& W, float4 txv, float4 rxv) {
-  float3 e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
-  float3 p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+__device__ __forceinline__ bool diffract_candidate(const WedgeF& W, float4 txv, float4 rxv) {
+  const float3 e = W.e, p0 = W.p0;
   float3 dt = f3(txv.x - p0.x, txv.y - p0.y, txv.z - p0.z), dr = f3(rxv.x - p0.x, rxv.y - p0.y, rxv.z - p0.z);
   float zt = fdot3(dt, e), zr = fdot3(dr, e);
   float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
@@ -861,13 +860,11 @@ __device__ __forceinline__ bool diffract_candidate(const Wedge& W, float4 txv, f
   if (!(rt > 1e-3f && rr > 1e-3f)) return true;
   float zq = zt + (zr - zt) * rt / (rt + rr);
   float mz = 0.05f + 1e-5f * (lt + lr);
-  if (zq < -mz || zq > (float)W.len + mz) return false;
-  float3 t0 = f3((float)W.t0[0], (float)W.t0[1], (float)W.t0[2]);
-  float3 y0 = f3((float)W.y0[0], (float)W.y0[1], (float)W.y0[2]);
+  if (zq < -mz || zq > W.len + mz) return false;
   bool st, sr;
   float tt, tr;
-  float phip = wedge_angle32(pt, t0, y0, rt, lt, st, tt), phi = wedge_angle32(pr, t0, y0, rr, lr, sr, tr);
-  float npi = (float)(W.n * M_PI);
+  float phip = wedge_angle32(pt, W.t0, W.y0, rt, lt, st, tt), phi = wedge_angle32(pr, W.t0, W.y0, rr, lr, sr, tr);
+  const float npi = W.npi;
   if ((st && phip > npi + tt) || (sr && phi > npi + tr)) return false;
   if (st && sr && fabsf(phi - phip) < 3.14159265f - (tt + tr)) return false;
   return true;
@@ -892,7 +889,7 @@ __device__ __forceinline__ bool vless(float4 a, float4 b) {
 }
 
 __global__ void k_wedge_geom(const float4* __restrict__ tris, const int* __restrict__ slot_of_id,
-                             const WedgeTopo* __restrict__ topo, int nw, Wedge* out) {
+                             const WedgeTopo* __restrict__ topo, int nw, Wedge* out, WedgeF* outf) {
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
     WedgeTopo t = topo[w];
     const float4* A = tris + 3 * (size_t)slot_of_id[t.ta];
@@ -930,6 +927,40 @@ __global__ void k_wedge_geom(const float4* __restrict__ tris, const int* __restr
     W.ta = t.ta;
     W.tb = t.tb;
     out[w] = W;
+    WedgeF f;
+    f.p0 = make_float3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+    f.e = make_float3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
+    f.t0 = make_float3((float)W.t0[0], (float)W.t0[1], (float)W.t0[2]);
+    f.y0 = make_float3((float)W.y0[0], (float)W.y0[1], (float)W.y0[2]);
+    f.len = (float)W.len;
+    f.npi = (float)(W.n * M_PI);
+    outf[w] = f;
+  }
+}
+
+// Each cluster's box (one warp per cluster of kWedgeCluster wedges in the
+// order perm): the min and max over its edges' two ends in FP32.
+__global__ void k_wedge_boxes(const WedgeF* __restrict__ wf, const int* __restrict__ perm, int nw, int nwc,
+                              float* __restrict__ box) {
+  const int lane = threadIdx.x & 31;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nwc; c += (gridDim.x * blockDim.x) >> 5) {
+    const int i = c * kWedgeCluster + lane;
+    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+    if (i < nw) {
+      const WedgeF f = wf[perm[i]];
+      const float q[3] = {f.p0.x + f.e.x * f.len, f.p0.y + f.e.y * f.len, f.p0.z + f.e.z * f.len};
+      const float p[3] = {f.p0.x, f.p0.y, f.p0.z};
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(p[k], q[k]);
+        hi[k] = fmaxf(p[k], q[k]);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+        hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+      }
+    if (lane < 6) box[6 * (size_t)c + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
   }
 }
 
@@ -1040,15 +1071,14 @@ __device__ __forceinline__ float3 mirror32(float3 x, float3 n, float c) {
 // (Keller point and angles as diffract_candidate with the image; the
 // reflection point off the plane's box by more than 5 cm + 1e-4 of the
 // distances, or off the unfolded leg).
-__device__ __forceinline__ bool diffract_refl_candidate(const Wedge& W, const RPlane& P, float4 txv, float4 rxv,
+__device__ __forceinline__ bool diffract_refl_candidate(const WedgeF& W, const RPlane& P, float4 txv, float4 rxv,
                                                         bool first) {
-  const float3 n = f3((float)P.n[0], (float)P.n[1], (float)P.n[2]);
-  const float c = (float)P.c;
+  const float3 n = f3(P.nf[0], P.nf[1], P.nf[2]);
+  const float c = P.cf;
   float3 T = f3(txv.x, txv.y, txv.z), R = f3(rxv.x, rxv.y, rxv.z);
   float3 S = first ? mirror32(T, n, c) : T, O = first ? R : mirror32(R, n, c);
   if (!diffract_candidate(W, make_float4(S.x, S.y, S.z, 0.0f), make_float4(O.x, O.y, O.z, 0.0f))) return false;
-  float3 e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
-  float3 p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+  const float3 e = W.e, p0 = W.p0;
   float3 dt = f3(S.x - p0.x, S.y - p0.y, S.z - p0.z), dr = f3(O.x - p0.x, O.y - p0.y, O.z - p0.z);
   float zt = fdot3(dt, e), zr = fdot3(dr, e);
   float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
@@ -1084,7 +1114,7 @@ __global__ void __launch_bounds__(256) k_diffract_refl_pre(PathArgs a, int nlink
       int p = (int)(r % a.nrp);
       r /= a.nrp;
       int w = (int)(r % a.nw), link = (int)(r / a.nw);
-      keep = diffract_refl_candidate(a.wedges[w], a.rplanes[p], a.txs[link / a.nrx], a.rx[link % a.nrx],
+      keep = diffract_refl_candidate(a.wf[w], a.rplanes[p], a.txs[link / a.nrx], a.rx[link % a.nrx],
                                      (idx & 1) != 0);
     }
     unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -1310,10 +1340,6 @@ __device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned l
 constexpr unsigned long long kKindShift = 62;
 constexpr unsigned long long kMulti2 = 1ull << kKindShift, kMulti3 = 3ull << kKindShift;
 
-struct WedgeF {  // a wedge's frame in FP32 for the pre-tests
-  float3 p0, e, t0, y0;
-  float len, npi;
-};
 __device__ __forceinline__ WedgeF wedge_f(const Wedge& W) {
   WedgeF f;
   f.p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
@@ -1465,7 +1491,7 @@ __device__ __forceinline__ float3 chain_source32(const PathArgs& a, int v) {
   int i = v - a.dntx;
   float4 t = a.txs[i / a.nrpr];
   const RPlane& P = a.rplanes[i % a.nrpr];
-  return mirror32(f3(t.x, t.y, t.z), f3((float)P.n[0], (float)P.n[1], (float)P.n[2]), (float)P.c);
+  return mirror32(f3(t.x, t.y, t.z), f3(P.nf[0], P.nf[1], P.nf[2]), P.cf);
 }
 __device__ __forceinline__ float3 chain_observer32(const PathArgs& a, int rho) {
   if (rho < a.nrx) {
@@ -1475,7 +1501,7 @@ __device__ __forceinline__ float3 chain_observer32(const PathArgs& a, int rho) {
   int i = rho - a.nrx;
   float4 r = a.rx[i / a.nrpr];
   const RPlane& P = a.rplanes[i % a.nrpr];
-  return mirror32(f3(r.x, r.y, r.z), f3((float)P.n[0], (float)P.n[1], (float)P.n[2]), (float)P.c);
+  return mirror32(f3(r.x, r.y, r.z), f3(P.nf[0], P.nf[1], P.nf[2]), P.cf);
 }
 
 // Can a leg from S to some point of segment A-B cross reflector plane Pl
@@ -1484,8 +1510,8 @@ __device__ __forceinline__ float3 chain_observer32(const PathArgs& a, int rho) {
 // answer is "no" when S, A and B lie on one side of the plane (by more than
 // the margin m), or when that box, widened by m, misses the plane's box.
 __device__ __forceinline__ bool plane_reachable(const RPlane& Pl, float3 S, float3 A, float3 B, float m) {
-  const float3 n = f3((float)Pl.n[0], (float)Pl.n[1], (float)Pl.n[2]);
-  const float c = (float)Pl.c;
+  const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
+  const float c = Pl.cf;
   const float ds = fdot3(n, S) - c, da = fdot3(n, A) - c, db = fdot3(n, B) - c;
   if ((ds > m && da > m && db > m) || (ds < -m && da < -m && db < -m)) return false;
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
@@ -1518,13 +1544,32 @@ __device__ __forceinline__ bool plane_reachable(const RPlane& Pl, float3 S, floa
   return true;
 }
 
+// The relation of consecutive wedges in a chain, once per frame (moving
+// wedges change it): distinct, no shared vertex, not on one line, neither
+// edge in a face plane of the other, each edge partly in the other's
+// exterior; one bit per ordered pair (w1, w2) in a.drel.
+__global__ void __launch_bounds__(256) k_diff_rel(PathArgs a) {
+  const long nw = a.nw, total = nw * nw;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int w1 = (int)(idx / nw), w2 = (int)(idx - (long)w1 * nw);
+    const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
+    bool rel = w1 != w2 && !share_vertex(A, B) && !collinear_edges(A, B) && !in_face_plane(A, B) &&
+               !in_face_plane(B, A);
+    if (rel) {
+      const WedgeF fa = a.wf[w1], fb = a.wf[w2];
+      float3 pa, qa;
+      edge_ends(fa, pa, qa);
+      const float m = fmaxf(pre_margin_m(pa), pre_margin_m(qa));
+      rel = edge_sees(fa, fb, m) && edge_sees(fb, fa, m);
+    }
+    if (rel) atomicOr(&a.drel[idx >> 5], 1u << (idx & 31));
+  }
+}
+
 // Ordered pairs (w1, w2) per source (transmitter or transmitter image) that
-// can start a path of order >= 2: distinct, no shared vertex, not on one
-// line, neither edge in a face plane of the other, each edge partly in the
-// other's exterior,
-// the transmitter outside w1, and some point of edge 2 beyond the incident
-// shadow boundary of the transmitter at w1. With order 3, the relation
-// (the first three conditions) also goes to a bit matrix for the triples.
+// can start a path of order >= 2: in the relation (k_diff_rel), the
+// transmitter outside w1, and some point of edge 2 beyond the incident
+// shadow boundary of the transmitter at w1.
 __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int nsrc) {
   const long nw = a.nw, total = (long)nsrc * nw * nw;
   const int lane = threadIdx.x & 31;
@@ -1538,29 +1583,16 @@ __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int nsrc) {
       long r = idx - (long)t * nw * nw;
       w1 = (int)(r / nw);
       w2 = (int)(r - (long)w1 * nw);
-      const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
-      bool rel = w1 != w2 && !share_vertex(A, B) && !collinear_edges(A, B) && !in_face_plane(A, B) &&
-                 !in_face_plane(B, A);
-      if (rel) {
-        WedgeF fa = wedge_f(A), fb = wedge_f(B);
-        float3 pa, qa;
-        edge_ends(fa, pa, qa);
-        float m = fmaxf(pre_margin_m(pa), pre_margin_m(qa));
-        rel = edge_sees(fa, fb, m) && edge_sees(fb, fa, m);
-        if (rel && t == 0 && a.drel) {
-          size_t bit = (size_t)w1 * nw + w2;
-          atomicOr(&a.drel[bit >> 5], 1u << (bit & 31));
-        }
-        if (rel) {
-          float3 T = chain_source32(a, t), P, Q;
-          edge_ends(fb, P, Q);
-          keep = !surely_inside(fa, T) && shadow_meets(fa, T, P, Q);
-          if (keep && t >= a.dntx) {  // the image's leg to edge 1 crosses its plane inside the box
-            float3 A1, B1;
-            edge_ends(fa, A1, B1);
-            float mg = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fa.len);
-            keep = plane_reachable(a.rplanes[(t - a.dntx) % a.nrpr], T, A1, B1, mg);
-          }
+      if ((a.drel[r >> 5] >> (r & 31)) & 1u) {
+        const WedgeF fa = a.wf[w1], fb = a.wf[w2];
+        float3 T = chain_source32(a, t), P, Q;
+        edge_ends(fb, P, Q);
+        keep = !surely_inside(fa, T) && shadow_meets(fa, T, P, Q);
+        if (keep && t >= a.dntx) {  // the image's leg to edge 1 crosses its plane inside the box
+          float3 A1, B1;
+          edge_ends(fa, A1, B1);
+          float mg = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fa.len);
+          keep = plane_reachable(a.rplanes[(t - a.dntx) % a.nrpr], T, A1, B1, mg);
         }
       }
     }
@@ -1848,7 +1880,7 @@ __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
       const bool src_img = sq.x >= a.dntx, obs_img = rho >= a.nrx;
       if (!(src_img && obs_img)) {
         int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
-        WedgeF fl = wedge_f(a.wedges[wl]), fp = wedge_f(a.wedges[wp]);
+        const WedgeF fl = a.wf[wl], fp = a.wf[wp];
         float3 R = chain_observer32(a, rho), P, Q;
         edge_ends(fp, P, Q);
         keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
@@ -1860,7 +1892,7 @@ __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
         }
         if (keep) {
           WedgeF Wc[3];
-          Wc[0] = wedge_f(a.wedges[sq.y]);
+          Wc[0] = a.wf[sq.y];
           Wc[1] = three ? fp : fl;  // order 2: (w1, last); order 3: (w1, previous, last)
           Wc[2] = fl;
           const int m = three ? 3 : 2;
@@ -1888,12 +1920,12 @@ __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
             }
             if (keep && (src_img || obs_img)) {  // the reflection point within the plane's box
               const RPlane& Pl = a.rplanes[src_img ? (sq.x - a.dntx) % a.nrpr : (rho - a.nrx) % a.nrpr];
-              const float3 n = f3((float)Pl.n[0], (float)Pl.n[1], (float)Pl.n[2]);
+              const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
               const float3 a0 = src_img ? X[0] : X[m], a1 = src_img ? X[1] : X[m + 1];
               const float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
               const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
               if (fabsf(den) > 1e-6f * len) {
-                float tt = ((float)Pl.c - fdot3(n, a0)) / den;
+                float tt = (Pl.cf - fdot3(n, a0)) / den;
                 float mt = (0.05f + delta + 1e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
                 if (tt < -mt || tt > 1.0f + mt) keep = false;
                 float3 Xp = f3(a0.x + tt * dv.x, a0.y + tt * dv.y, a0.z + tt * dv.z);
@@ -2293,21 +2325,21 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
 constexpr unsigned long long kRefl2Tag = kReflTag | (1ull << 61);
 constexpr unsigned long long kRefl2Mask = (1ull << 61) - 1ull;
 
-// Can a leg from S (a point's image in plane P1) to some point of P2's box
-// cross P1 inside its box? With every corner of P2's box across the plane
-// from S, the legs' crossings lie within the box of the corner legs'
-// crossings; "no" when every corner lies on S's side (no leg crosses the
-// plane) or when that box, widened by m, misses P1's box.
-__device__ __forceinline__ bool pair_reachable(const RPlane& P1, float3 S, const RPlane& P2, float m) {
-  const float3 n = f3((float)P1.n[0], (float)P1.n[1], (float)P1.n[2]);
-  const float c = (float)P1.c;
+// Can a leg from S to some point of `box` cross plane P1 inside P1's box?
+// With every corner of the box across the plane from S, the legs' crossings
+// lie within the box of the corner legs' crossings; "no" when every corner
+// lies on S's side (no leg crosses the plane) or when the crossings' box,
+// widened by m, misses P1's box.
+__device__ __forceinline__ bool box_reachable(const RPlane& P1, float3 S, const float* box, float m) {
+  const float3 n = f3(P1.nf[0], P1.nf[1], P1.nf[2]);
+  const float c = P1.cf;
   const float ds = fdot3(n, S) - c;
   if (fabsf(ds) <= m) return true;
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
   int same = 0;
   for (int q = 0; q < 8; ++q) {
-    const float3 X = f3((q & 1) ? P2.box[3] + m : P2.box[0] - m, (q & 2) ? P2.box[4] + m : P2.box[1] - m,
-                        (q & 4) ? P2.box[5] + m : P2.box[2] - m);
+    const float3 X = f3((q & 1) ? box[3] + m : box[0] - m, (q & 2) ? box[4] + m : box[1] - m,
+                        (q & 4) ? box[5] + m : box[2] - m);
     const float dx = fdot3(n, X) - c;
     if (fabsf(dx) <= m) return true;
     if ((dx > 0.0f) == (ds > 0.0f)) {
@@ -2331,11 +2363,11 @@ __device__ __forceinline__ bool pair_reachable(const RPlane& P1, float3 S, const
 // off P's box, 1 with X set, 2 when the leg runs nearly parallel to the
 // plane (no conclusion).
 __device__ __forceinline__ int refl_cross32(const RPlane& P, float3 a0, float3 a1, float delta, float3& X) {
-  const float3 n = f3((float)P.n[0], (float)P.n[1], (float)P.n[2]);
+  const float3 n = f3(P.nf[0], P.nf[1], P.nf[2]);
   const float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
   const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
   if (!(fabsf(den) > 1e-6f * len)) return 2;
-  const float t = ((float)P.c - fdot3(n, a0)) / den;
+  const float t = (P.cf - fdot3(n, a0)) / den;
   const float mt = (delta + 2e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
   if (t < -mt || t > 1.0f + mt) return 0;
   X = f3(a0.x + t * dv.x, a0.y + t * dv.y, a0.z + t * dv.z);
@@ -2349,11 +2381,10 @@ __device__ __forceinline__ int refl_cross32(const RPlane& P, float3 a0, float3 a
 // FP32 pre-test of one candidate: false only when the FP64 test rejects it
 // too. S, O: the source and observer of the diffraction (images); S1: the
 // transmitter's image in P1 (kind 0), O1: the receiver's image in P2 (kind 2).
-__device__ __forceinline__ bool refl2_candidate(const Wedge& W, const RPlane& P1, const RPlane& P2, int kind,
+__device__ __forceinline__ bool refl2_candidate(const WedgeF& W, const RPlane& P1, const RPlane& P2, int kind,
                                                 float3 S, float3 S1, float3 O, float3 O1) {
   if (!diffract_candidate(W, make_float4(S.x, S.y, S.z, 0.0f), make_float4(O.x, O.y, O.z, 0.0f))) return false;
-  const float3 e = f3((float)W.e[0], (float)W.e[1], (float)W.e[2]);
-  const float3 p0 = f3((float)W.p0[0], (float)W.p0[1], (float)W.p0[2]);
+  const float3 e = W.e, p0 = W.p0;
   const float3 dt = f3(S.x - p0.x, S.y - p0.y, S.z - p0.z), dr = f3(O.x - p0.x, O.y - p0.y, O.z - p0.z);
   const float zt = fdot3(dt, e), zr = fdot3(dr, e);
   const float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
@@ -2394,33 +2425,47 @@ __global__ void __launch_bounds__(256) k_diffract_refl2_pre(PathArgs a, int nlin
     const RPlane &P1 = a.rplanes[p1], &P2 = a.rplanes[p2];
     const float4 tv = a.txs[link / a.nrx], rv = a.rx[link % a.nrx];
     const float3 T = f3(tv.x, tv.y, tv.z), R = f3(rv.x, rv.y, rv.z);
-    const float3 n1 = f3((float)P1.n[0], (float)P1.n[1], (float)P1.n[2]);
-    const float3 n2 = f3((float)P2.n[0], (float)P2.n[1], (float)P2.n[2]);
+    const float3 n1 = f3(P1.nf[0], P1.nf[1], P1.nf[2]);
+    const float3 n2 = f3(P2.nf[0], P2.nf[1], P2.nf[2]);
     const float m = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fabsf(R.x) + fabsf(R.y) + fabsf(R.z));
     float3 S = T, S1 = T, O = R, O1 = R;
     if (kind == 0) {
-      S1 = mirror32(T, n1, (float)P1.c);
-      S = mirror32(S1, n2, (float)P2.c);
-      if (!pair_reachable(P1, S1, P2, m)) continue;
+      S1 = mirror32(T, n1, P1.cf);
+      S = mirror32(S1, n2, P2.cf);
+      if (!box_reachable(P1, S1, P2.box, m)) continue;
     } else if (kind == 1) {
-      S = S1 = mirror32(T, n1, (float)P1.c);
-      O = O1 = mirror32(R, n2, (float)P2.c);
+      S = S1 = mirror32(T, n1, P1.cf);
+      O = O1 = mirror32(R, n2, P2.cf);
     } else {
-      O1 = mirror32(R, n2, (float)P2.c);
-      O = mirror32(O1, n1, (float)P1.c);
-      if (!pair_reachable(P2, O1, P1, m)) continue;
+      O1 = mirror32(R, n2, P2.cf);
+      O = mirror32(O1, n1, P1.cf);
+      if (!box_reachable(P2, O1, P1.box, m)) continue;
     }
-    for (int w0 = 0; w0 < a.nw; w0 += 32) {
-      const int w = w0 + lane;
-      const bool keep = w < a.nw && refl2_candidate(a.wedges[w], P1, P2, kind, S, S1, O, O1);
-      const unsigned mk = __ballot_sync(0xffffffffu, keep);
-      if (!mk) continue;
-      unsigned at = 0;
-      if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
-      at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
-      if (keep) {
-        if (at < a.dsurv_cap) a.dsurv[at] = kRefl2Tag | ((unsigned long long)b * a.nw + w);
-        else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+    // the wedge clusters (lane c tests cluster c0 + c): the unfolded legs to
+    // some point of the cluster's box must cross their planes inside the
+    // planes' boxes; then the lanes take the wedges of each cluster kept
+    for (int c0 = 0; c0 < a.nwc; c0 += 32) {
+      const int c = c0 + lane;
+      bool near = false;
+      if (c < a.nwc) {
+        const float* cb = a.wcbox + 6 * (size_t)c;
+        near = kind == 0 ? box_reachable(P2, S, cb, m)
+               : kind == 1 ? box_reachable(P1, S, cb, m) && box_reachable(P2, O, cb, m)
+                           : box_reachable(P1, O, cb, m);
+      }
+      for (unsigned cm = __ballot_sync(0xffffffffu, near); cm; cm &= cm - 1u) {
+        const int i = (c0 + __ffs(cm) - 1) * kWedgeCluster + lane;
+        const int w = i < a.nw ? a.wperm[i] : -1;
+        const bool keep = w >= 0 && refl2_candidate(a.wf[w], P1, P2, kind, S, S1, O, O1);
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        if (!mk) continue;
+        unsigned at = 0;
+        if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
+        at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+        if (keep) {
+          if (at < a.dsurv_cap) a.dsurv[at] = kRefl2Tag | ((unsigned long long)b * a.nw + w);
+          else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+        }
       }
     }
   }
@@ -2613,7 +2658,7 @@ __global__ void __launch_bounds__(256) k_diffract_pre(PathArgs a, int nlinks) {
     bool keep = false;
     if (idx < total) {
       int link = (int)(idx / a.nw), w = (int)(idx - (long)link * a.nw);
-      keep = diffract_candidate(a.wedges[w], a.txs[link / a.nrx], a.rx[link % a.nrx]);
+      keep = diffract_candidate(a.wf[w], a.txs[link / a.nrx], a.rx[link % a.nrx]);
     }
     unsigned m = __ballot_sync(0xffffffffu, keep);
     if (!m) continue;
@@ -2795,7 +2840,9 @@ cudaError_t launch_dedupe(const PathArgs& a, int grid, cudaStream_t st) {
 
 cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t st) {
   if (!a.wedges || a.nw <= 0) return cudaSuccess;
-  k_wedge_geom<<<(a.nw + 255) / 256, 256, 0, st>>>(a.tris, a.slot_of_id, a.wtopo, a.nw, a.wedges);
+  k_wedge_geom<<<(a.nw + 255) / 256, 256, 0, st>>>(a.tris, a.slot_of_id, a.wtopo, a.nw, a.wedges, a.wf);
+  if (a.drefl2 && a.rplanes && a.nrp > 0)
+    k_wedge_boxes<<<(a.nwc * 32 + 255) / 256, 256, 0, st>>>(a.wf, a.wperm, a.nw, a.nwc, a.wcbox);
   if (nlinks > 0) {
     long total = (long)nlinks * a.nw;
     long g = std::min<long>((total + 255) / 256, 8L * sms);
@@ -2816,7 +2863,8 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
     if (a.diff_order >= 2 && a.nw > 1) {
       int nsrc = b.dntx * (1 + b.nrpr);
       long tp = (long)nsrc * a.nw * a.nw;
-      if (a.drel) cudaMemsetAsync(a.drel, 0, sizeof(unsigned) * (((size_t)a.nw * a.nw + 31) / 32), st);
+      cudaMemsetAsync(a.drel, 0, sizeof(unsigned) * (((size_t)a.nw * a.nw + 31) / 32), st);
+      k_diff_rel<<<(int)std::max<long>(std::min<long>(((long)a.nw * a.nw + 255) / 256, 8L * sms), 1), 256, 0, st>>>(b);
       k_diff_pairs<<<(int)std::max<long>(std::min<long>((tp + 255) / 256, 8L * sms), 1), 256, 0, st>>>(b, nsrc);
       if (a.diff_order >= 3) k_diff_triples<<<8 * sms, 256, 0, st>>>(b);
       k_diff_multi_pre<<<8 * sms, 256, 256 * kStackTrace * sizeof(int), st>>>(b);

@@ -50,8 +50,14 @@ struct PathArgs {
   // buffer that keeps this frame's valid paths for the next one
   // first-order edge diffraction (null: off)
   Wedge* wedges;                  // geometry, rebuilt every frame from the world triangles
+  WedgeF* wf;                     // the same in FP32 (pre-tests)
   const WedgeTopo* wtopo;
   int nw;
+  // wedge clusters: the wedges in a fixed spatial order (wperm), 32 per
+  // cluster, and each cluster's box of its edges (6 floats, every frame)
+  const int* wperm;
+  float* wcbox;
+  int nwc;
   unsigned long long* dsurv;      // (link, wedge) pair indices past the FP32 pre-test
   unsigned dsurv_cap;
   // one reflection before or after a diffraction (null: off): reflector
@@ -64,7 +70,7 @@ struct PathArgs {
   // (v, w1, w2, -1) and triples (v, w1, w2, w3) of the frame, v a source
   // (a transmitter, or with reflector planes the image of transmitter t in
   // plane p: v = dntx + t * nrpr + p), and the pair relation as a bit matrix
-  // (nw x nw bits; order 3 only)
+  // (nw x nw bits)
   int diff_order;
   int dntx;                       // transmitters (set by launch_diffract)
   int nrpr;                       // reflector planes applied to chains (0: none; set by launch_diffract)
