@@ -1173,6 +1173,20 @@ __device__ __forceinline__ void tri64(const PathArgs& a, int id, d3w& v0, d3w& v
   mat = a.mats[__float_as_int(p1.w)];
 }
 
+// Can triangle id hold point x (on its plane group's plane, within 1e-4 m of
+// the triangle's own)? x must lie in the triangle's FP32 box widened by 1 mm +
+// 1e-6 of the coordinates; the FP64 test (inside_tri64) follows for those
+// that do.
+__device__ __forceinline__ bool tri_box_near(const PathArgs& a, int id, d3w x) {
+  const float4* tp = a.tris + 3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(id, a.bvh.ntris)], a.bvh.ntris);
+  const float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+  const float X = (float)x.x, Y = (float)x.y, Zc = (float)x.z;
+  const float m = 1e-3f + 1e-6f * (fabsf(X) + fabsf(Y) + fabsf(Zc));
+  return !(X < fminf(p0.x, fminf(p1.x, p2.x)) - m || X > fmaxf(p0.x, fmaxf(p1.x, p2.x)) + m ||
+           Y < fminf(p0.y, fminf(p1.y, p2.y)) - m || Y > fmaxf(p0.y, fmaxf(p1.y, p2.y)) + m ||
+           Zc < fminf(p0.z, fminf(p1.z, p2.z)) - m || Zc > fmaxf(p0.z, fmaxf(p1.z, p2.z)) + m);
+}
+
 __device__ __forceinline__ bool inside_tri64(d3w v0, d3w v1, d3w v2, d3w x) {
   d3w n = crossw(v1 - v0, v2 - v0);
   return !(dotw(crossw(v1 - v0, x - v0), n) < 0.0 || dotw(crossw(v2 - v1, x - v1), n) < 0.0 ||
@@ -1206,7 +1220,7 @@ __device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned l
   float4 mj;
   for (int q = 0; q < Pl.count && j < 0; ++q) {
     int id = a.rmembers[Pl.first + q];
-    if (id == W.ta || id == W.tb) continue;
+    if (id == W.ta || id == W.tb || !tri_box_near(a, id, g.P)) continue;
     tri64(a, id, v0, v1, v2, mj);
     if (inside_tri64(v0, v1, v2, g.P)) j = id;
   }
@@ -2177,7 +2191,7 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
           int id = a.rmembers[Pg.first + q];
           bool face = false;
           for (int i = 0; i < m; ++i) face = face || id == E[i]->ta || id == E[i]->tb;
-          if (face) continue;
+          if (face || !tri_box_near(a, id, Pp)) continue;
           tri64(a, id, v0, v1, v2, mj);
           if (inside_tri64(v0, v1, v2, Pp)) j = id;
         }
@@ -2534,7 +2548,7 @@ __device__ __noinline__ void diffract_refl2(const PathArgs& a, unsigned long lon
         const RPlane& G = a.rplanes[pg[i]];
         for (int q = 0; q < G.count && pj[i] < 0; ++q) {
           const int id = a.rmembers[G.first + q];
-          if (id == W.ta || id == W.tb) continue;
+          if (id == W.ta || id == W.tb || !tri_box_near(a, id, Y[i])) continue;
           tri64(a, id, v0, v1, v2, mj);
           if (inside_tri64(v0, v1, v2, Y[i])) {
             pj[i] = id;
