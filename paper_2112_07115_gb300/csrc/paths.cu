@@ -1566,15 +1566,17 @@ __global__ void __launch_bounds__(256) k_diff_rel(PathArgs a) {
   const long nw = a.nw, total = nw * nw;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int w1 = (int)(idx / nw), w2 = (int)(idx - (long)w1 * nw);
-    const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
-    bool rel = w1 != w2 && !share_vertex(A, B) && !collinear_edges(A, B) && !in_face_plane(A, B) &&
-               !in_face_plane(B, A);
-    if (rel) {
+    bool rel = w1 != w2;
+    if (rel) {  // the FP32 exterior tests first: they reject most pairs
       const WedgeF fa = a.wf[w1], fb = a.wf[w2];
       float3 pa, qa;
       edge_ends(fa, pa, qa);
       const float m = fmaxf(pre_margin_m(pa), pre_margin_m(qa));
       rel = edge_sees(fa, fb, m) && edge_sees(fb, fa, m);
+    }
+    if (rel) {
+      const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
+      rel = !share_vertex(A, B) && !collinear_edges(A, B) && !in_face_plane(A, B) && !in_face_plane(B, A);
     }
     if (rel) atomicOr(&a.drel[idx >> 5], 1u << (idx & 31));
   }
@@ -1871,98 +1873,150 @@ __device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float
 // 1e-4 of the distances; as diffract_refl_candidate). Observers: the
 // receivers, and with reflector planes their images (rho = nrx + r * nrpr
 // + p) for sequences from a real transmitter; a chain has one reflection.
+// Stage 1 of k_diff_multi_pre for sequence sq and observer rho: the
+// observer outside the last wedge and some point of the previous edge beyond
+// its shadow boundary there; an image observer's leg from the last edge must
+// be able to cross its plane inside the box.
+__device__ __forceinline__ bool multi_stage1(const PathArgs& a, int4 sq, bool three, int rho) {
+  const bool obs_img = rho >= a.nrx;
+  const int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
+  const WedgeF fl = a.wf[wl], fp = a.wf[wp];
+  float3 R = chain_observer32(a, rho), P, Q;
+  edge_ends(fp, P, Q);
+  bool keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+  if (keep && obs_img) {  // the leg from the last edge to the image crosses its plane inside the box
+    float3 A1, B1;
+    edge_ends(fl, A1, B1);
+    float mg = 0.1f + 1e-4f * (fabsf(R.x) + fabsf(R.y) + fabsf(R.z) + fl.len);
+    keep = plane_reachable(a.rplanes[(rho - a.nrx) % a.nrpr], R, A1, B1, mg);
+  }
+  return keep;
+}
+
+// Stage 2 for an index past stage 1: the FP32 Keller estimate against the
+// rules, the real legs against robust occlusion, and with a reflection its
+// point on the unfolded leg inside the plane's box.
+__device__ __forceinline__ bool multi_stage2(const PathArgs& a, long idx, long n2, long nobs, TStack& st) {
+  const long e = idx / nobs;
+  const int rho = (int)(idx - e * nobs);
+  const bool three = e >= n2;
+  const long ei = three ? e - n2 : e;
+  const int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
+  const bool src_img = sq.x >= a.dntx, obs_img = rho >= a.nrx;
+  const int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
+  WedgeF Wc[3];
+  Wc[0] = a.wf[sq.y];
+  Wc[1] = a.wf[three ? wp : wl];  // order 2: (w1, last); order 3: (w1, previous, last)
+  Wc[2] = a.wf[wl];
+  const int m = three ? 3 : 2;
+  const float3 T = chain_source32(a, sq.x), R = chain_observer32(a, rho);
+  float t[3];
+  bool solved;
+  bool keep = chain_possible(Wc, m, T, R, t, &solved);
+  if (keep && solved) {
+    const int w[3] = {sq.y, sq.z, sq.w};
+    const float delta = chain_margin(T, R);
+    float3 X[5];
+    X[0] = T;
+    for (int i = 0; i < m; ++i) X[i + 1] = edge_point(Wc[i], t[i]);
+    X[m + 1] = R;
+    // a leg certainly blocked rejects the chain (legs to or from an
+    // image are not real: the reflection breaks them)
+    for (int q = 0; keep && q <= m; ++q) {
+      if ((q == 0 && src_img) || (q == m && obs_img)) continue;
+      const Wedge* A = q >= 1 ? &a.wedges[w[q - 1]] : nullptr;
+      const Wedge* B = q < m ? &a.wedges[w[q]] : nullptr;
+      float3 dv = f3(X[q + 1].x - X[q].x, X[q + 1].y - X[q].y, X[q + 1].z - X[q].z);
+      if (leg_surely_blocked(a.bvh, X[q], dv, delta, a.eps_occ, A ? A->ta : -1, A ? A->tb : -1,
+                             B ? B->ta : -1, B ? B->tb : -1, st))
+        keep = false;
+    }
+    if (keep && (src_img || obs_img)) {  // the reflection point within the plane's box
+      const RPlane& Pl = a.rplanes[src_img ? (sq.x - a.dntx) % a.nrpr : (rho - a.nrx) % a.nrpr];
+      const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
+      const float3 a0 = src_img ? X[0] : X[m], a1 = src_img ? X[1] : X[m + 1];
+      const float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
+      const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
+      if (fabsf(den) > 1e-6f * len) {
+        float tt = (Pl.cf - fdot3(n, a0)) / den;
+        float mt = (0.05f + delta + 1e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
+        if (tt < -mt || tt > 1.0f + mt) keep = false;
+        float3 Xp = f3(a0.x + tt * dv.x, a0.y + tt * dv.y, a0.z + tt * dv.z);
+        float mb = 0.05f + delta + 1e-4f * (len + sqrtf(fdot3(Xp, Xp)));
+        if (Xp.x < Pl.box[0] - mb || Xp.y < Pl.box[1] - mb || Xp.z < Pl.box[2] - mb ||
+            Xp.x > Pl.box[3] + mb || Xp.y > Pl.box[4] + mb || Xp.z > Pl.box[5] + mb)
+          keep = false;
+      }
+    }
+  }
+  return keep;
+}
+
+// One warp per sequence, its lanes over the observers: every (sequence,
+// observer) through stage 1; the indices (sequence * nobs + observer) that
+// pass wait in a per-warp queue and go through stage 2 (the Newton estimate,
+// the legs) 32 at a time, so that the costly stage runs on full warps.
+// Observers: the receivers, and with reflector planes their images (rho =
+// nrx + r * nrpr + p) for sequences from a real transmitter (a chain has one
+// reflection: a sequence from an image sees the receivers only).
 __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
   extern __shared__ int sstk[];
+  __shared__ long wq[8][64];
   TStack st;
   bind_stack(st, sstk, kStackTrace);
   const long n2 = a.diff_order >= 2 ? (long)min(a.ctr->n_dpair, a.dseq2_cap) : 0;
   const long n3 = a.diff_order >= 3 ? (long)min(a.ctr->n_dtrip, a.dseq3_cap) : 0;
   const long nobs = (long)a.nrx * (1 + a.nrpr);
-  const long total = (n2 + n3) * nobs;
-  const int lane = threadIdx.x & 31;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-    long idx = base + lane;
-    bool keep = false;
-    unsigned long long code = 0;
-    if (idx < total) {
-      long e = idx / nobs;
-      int rho = (int)(idx - e * nobs);
-      bool three = e >= n2;
-      long ei = three ? e - n2 : e;
-      int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
-      const bool src_img = sq.x >= a.dntx, obs_img = rho >= a.nrx;
-      if (!(src_img && obs_img)) {
-        int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
-        const WedgeF fl = a.wf[wl], fp = a.wf[wp];
-        float3 R = chain_observer32(a, rho), P, Q;
-        edge_ends(fp, P, Q);
-        keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
-        if (keep && obs_img) {  // the leg from the last edge to the image crosses its plane inside the box
-          float3 A1, B1;
-          edge_ends(fl, A1, B1);
-          float mg = 0.1f + 1e-4f * (fabsf(R.x) + fabsf(R.y) + fabsf(R.z) + fl.len);
-          keep = plane_reachable(a.rplanes[(rho - a.nrx) % a.nrpr], R, A1, B1, mg);
-        }
-        if (keep) {
-          WedgeF Wc[3];
-          Wc[0] = a.wf[sq.y];
-          Wc[1] = three ? fp : fl;  // order 2: (w1, last); order 3: (w1, previous, last)
-          Wc[2] = fl;
-          const int m = three ? 3 : 2;
-          const float3 T = chain_source32(a, sq.x);
-          float t[3];
-          bool solved;
-          keep = chain_possible(Wc, m, T, R, t, &solved);
-          if (keep && solved) {
-            const int w[3] = {sq.y, sq.z, sq.w};
-            const float delta = chain_margin(T, R);
-            float3 X[5];
-            X[0] = T;
-            for (int i = 0; i < m; ++i) X[i + 1] = edge_point(Wc[i], t[i]);
-            X[m + 1] = R;
-            // a leg certainly blocked rejects the chain (legs to or from an
-            // image are not real: the reflection breaks them)
-            for (int q = 0; keep && q <= m; ++q) {
-              if ((q == 0 && src_img) || (q == m && obs_img)) continue;
-              const Wedge* A = q >= 1 ? &a.wedges[w[q - 1]] : nullptr;
-              const Wedge* B = q < m ? &a.wedges[w[q]] : nullptr;
-              float3 dv = f3(X[q + 1].x - X[q].x, X[q + 1].y - X[q].y, X[q + 1].z - X[q].z);
-              if (leg_surely_blocked(a.bvh, X[q], dv, delta, a.eps_occ, A ? A->ta : -1, A ? A->tb : -1,
-                                     B ? B->ta : -1, B ? B->tb : -1, st))
-                keep = false;
-            }
-            if (keep && (src_img || obs_img)) {  // the reflection point within the plane's box
-              const RPlane& Pl = a.rplanes[src_img ? (sq.x - a.dntx) % a.nrpr : (rho - a.nrx) % a.nrpr];
-              const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
-              const float3 a0 = src_img ? X[0] : X[m], a1 = src_img ? X[1] : X[m + 1];
-              const float3 dv = f3(a1.x - a0.x, a1.y - a0.y, a1.z - a0.z);
-              const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
-              if (fabsf(den) > 1e-6f * len) {
-                float tt = (Pl.cf - fdot3(n, a0)) / den;
-                float mt = (0.05f + delta + 1e-4f * (len + sqrtf(fdot3(a0, a0)))) / len;
-                if (tt < -mt || tt > 1.0f + mt) keep = false;
-                float3 Xp = f3(a0.x + tt * dv.x, a0.y + tt * dv.y, a0.z + tt * dv.z);
-                float mb = 0.05f + delta + 1e-4f * (len + sqrtf(fdot3(Xp, Xp)));
-                if (Xp.x < Pl.box[0] - mb || Xp.y < Pl.box[1] - mb || Xp.z < Pl.box[2] - mb ||
-                    Xp.x > Pl.box[3] + mb || Xp.y > Pl.box[4] + mb || Xp.z > Pl.box[5] + mb)
-                  keep = false;
-              }
-            }
-          }
-        }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // work items: (sequence, run of kObsRun observers), so that the sequences
+  // from a real transmitter, which see every observer, split over warps
+  constexpr long kObsRun = 512;
+  const long nrun = (nobs + kObsRun - 1) / kObsRun, nitem = (n2 + n3) * nrun;
+  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+  long item = (long)blockIdx.x * (blockDim.x >> 5) + wid - nwarps;
+  long e = 0, r0 = 0, r1 = 0;  // the item's sequence and observer range (warp-uniform)
+  int4 sq = make_int4(0, 0, 0, 0);
+  int qn = 0;                  // queued indices of this warp (warp-uniform)
+  for (;;) {
+    while (r0 >= r1) {  // the next item with observers
+      item += nwarps;
+      if (item >= nitem) break;
+      e = item / nrun;
+      sq = e >= n2 ? a.dseq3[e - n2] : a.dseq2[e];
+      const long nob = sq.x >= a.dntx ? a.nrx : nobs;
+      r0 = (item - e * nrun) * kObsRun;
+      r1 = min(r0 + kObsRun, nob);
+    }
+    const bool more = item < nitem;
+    if (more) {
+      const long rho = r0 + lane;
+      const bool pass = rho < r1 && multi_stage1(a, sq, e >= n2, (int)rho);
+      const unsigned mk = __ballot_sync(0xffffffffu, pass);
+      if (pass) wq[wid][qn + __popc(mk & ((1u << lane) - 1u))] = e * nobs + rho;
+      qn += __popc(mk);
+      __syncwarp();
+      r0 += 32;
+    }
+    while (qn >= 32 || (!more && qn > 0)) {
+      const int nn = min(qn, 32);
+      const long idx = lane < nn ? wq[wid][qn - nn + lane] : -1;
+      __syncwarp();
+      qn -= nn;
+      const bool keep = idx >= 0 && multi_stage2(a, idx, n2, nobs, st);
+      const unsigned mk = __ballot_sync(0xffffffffu, keep);
+      if (!mk) continue;
+      unsigned at = 0;
+      if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
+      at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+      if (keep) {
+        const bool three = idx >= n2 * nobs;
+        const unsigned long long code =
+            (unsigned long long)(three ? idx - n2 * nobs : idx) | (three ? kMulti3 : kMulti2);
+        if (at < a.dsurv_cap) a.dsurv[at] = code;
+        else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
       }
-      code = ((unsigned long long)ei * nobs + rho) | (three ? kMulti3 : kMulti2);
     }
-    unsigned mk = __ballot_sync(0xffffffffu, keep);
-    if (!mk) continue;
-    unsigned at = 0;
-    if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
-    at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
-    if (keep) {
-      if (at < a.dsurv_cap) a.dsurv[at] = code;
-      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
-    }
+    if (!more) break;
   }
 }
 
