@@ -2069,6 +2069,49 @@ int64_t or_diffract_refl2(const float* tris, const int32_t* tri_mat, const int32
   return nvalid;
 }
 
+/* One given path of the combined mechanisms, for checking paths found
+ * elsewhere: ids[0..depth-1] in path order, static triangles (reflections)
+ * before and after a run of 1-3 wedge ids marked OR_DIFF, at most two
+ * reflections; evaluated by chain_path_r for transmitter tx and receiver rx.
+ * Returns 1 (valid, o filled), 0 (not a valid path) or -1 (ids not of that
+ * form). */
+int32_t or_diffract_path(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                         const float* mats, int32_t nmat, const float* tx, const float* rx, const int32_t* ids,
+                         int32_t depth, const or_params* P, opath* o) {
+  int jb[2], ja[2], nb = 0, na = 0, m = 0;
+  long wi[3];
+  for (int q = 0; q < depth; ++q) {
+    if (ids[q] & OR_DIFF) {
+      if (na || m == 3) return -1;
+      wi[m++] = ids[q] & ~OR_DIFF;
+    } else if (m == 0) {
+      if (nb == 2) return -1;
+      jb[nb++] = ids[q];
+    } else {
+      if (na == 2) return -1;
+      ja[na++] = ids[q];
+    }
+  }
+  if (m == 0 || nb + na > 2) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  int ok = 1;
+  for (int i = 0; i < m; ++i) ok &= wi[i] >= 0 && wi[i] < nw;
+  for (int i = 0; i < nb; ++i) ok &= jb[i] >= 0 && jb[i] < ntri;
+  for (int i = 0; i < na; ++i) ok &= ja[i] >= 0 && ja[i] < ntri;
+  int r = -1;
+  if (ok) {
+    const owedge* E[3] = {&W[wi[0]], m > 1 ? &W[wi[1]] : NULL, m > 2 ? &W[wi[2]] : NULL};
+    v3 T = mk(tx[0], tx[1], tx[2]), R = mk(rx[0], rx[1], rx[2]);
+    r = chain_path_r(&S, E, m, T, R, jb, nb, ja, na, P, o);
+  }
+  free(W);
+  scene_free(&S);
+  return r;
+}
+
 int32_t or_path_size(void) { return (int32_t)sizeof(opath); }
 
 /* ------------------------------------------------------------------------ */

@@ -142,6 +142,9 @@ def lib():
         _lib.or_diffract_refl2.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                            P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
         _lib.or_diffract_refl2.restype = C.c_int64
+        _lib.or_diffract_path.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, i32, C.c_int32,
+                                          P(_Params), C.c_void_p]
+        _lib.or_diffract_path.restype = C.c_int32
     return _lib
 
 
@@ -648,6 +651,25 @@ def diffract_refl2(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleP
     if n > cap:
         raise RuntimeError(f"or_diffract_refl2: {n} paths exceed capacity {cap}")
     return keys[:n].copy(), paths[:n].copy()
+
+
+def diffract_path(world_tris, tri_mat, tri_obj, materials, tx, rx, ids, prm: OracleParams):
+    """One given path of the combined mechanisms (ids in path order: up to two
+    static-triangle reflections around a run of 1-3 wedge ids marked DIFF),
+    evaluated for one receiver rx. Returns the path record, or None when the
+    path is not valid."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    ids = _i32(ids)
+    out = np.zeros(1, PATH_DTYPE)
+    prm_c = prm.c()
+    r = lib().or_diffract_path(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), _p(_i32(tri_obj), C.c_int32),
+                               wt.shape[0], _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                               _p(_f32(rx).reshape(3), C.c_float), _p(ids, C.c_int32), ids.shape[0],
+                               C.byref(prm_c), out.ctypes.data_as(C.c_void_p))
+    if r < 0:
+        raise ValueError(f"or_diffract_path: ids {ids.tolist()} are not a combined diffraction path ({r})")
+    return out[0] if r == 1 else None
 
 
 def sticky_frames(scene, frames, rays: np.ndarray, prm: OracleParams):

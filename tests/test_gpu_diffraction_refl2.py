@@ -142,3 +142,54 @@ def test_levels_and_errors(cuda):
         with pytest.raises(dcem.DcemError):
             s.set_diffraction_reflections(bad)
     s.close()
+
+
+def test_highway_full_size_sampled(cuda):
+    """The bench's highway at full size (1M rays, 4 reflections, 200 moving
+    receivers, 2400 wedges, the road and barrier faces as 8 reflector
+    planes), frame 1 in coherent frames with diffraction up to order 2 and up
+    to two reflections around it: every path of four receivers (the three
+    with the most two-reflection paths and receiver 0) that has a reflection
+    around one or two wedges, evaluated by the oracle for the same ids
+    (or_diffract_path): valid there too, with the same points, length and
+    field. The oracle's own search over every pair of the 2000 static
+    triangles and every wedge is too slow at this size; the small scenes
+    above check that no path is missing."""
+    torch = cuda
+    hw = scenes.highway(n_frames=3, n_rays=1_000_000, max_refl=4)
+    s = dcem.Scene.from_scene(hw, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_rays(scenes.fibonacci_sphere(hw.n_rays))
+    assert s.set_diffraction(True) == 2400
+    assert s.set_diffraction_reflections(2) == 8
+    s.set_diffraction_order(2)
+    prm = P.gpu_params(hw, max_refl=4, mode=dcem.MODE_COHERENT)
+    for f in (0, 1):
+        s.update_transforms(hw.xf[f])
+        fr = s.trace(hw.tx, hw.rx[f], prm)
+    assert fr.stats["coherent"] == 1
+    p = fr.paths
+    t = p["tri"][:, :4]
+    nd = ((t >= 0) & ((t & dcem.TRI_DIFFRACT) != 0)).sum(axis=1)
+    combined = p[(nd >= 1) & (p["depth"] > nd)]
+    two = _refl2_recs(p)
+    counts = np.bincount(p["rx"][two], minlength=hw.nrx)
+    sample = [0] + [int(r) for r in np.argsort(-counts, kind="stable")[:3]]
+    assert counts[sample[1]] >= 3
+    oprm = P.oracle_params(hw, n_rays=hw.n_rays, max_refl=4)
+    wt = O.transform(hw.tris, hw.tri_obj, hw.xf[1])
+    checked, kinds = 0, set()
+    for rec in combined[np.isin(combined["rx"], sample)]:
+        d = int(rec["depth"])
+        ids = [int(x) for x in rec["tri"][:d]]
+        q = O.diffract_path(wt, hw.tri_mat, hw.tri_obj, hw.materials, hw.tx, hw.rx[1][rec["rx"]], ids, oprm)
+        assert q is not None, ids
+        assert abs(q["len_m"] - rec["len_m"]) <= 1e-6, ids
+        za, zb = complex(rec["amp_re"], rec["amp_im"]), complex(q["amp_re"], q["amp_im"])
+        assert abs(za - zb) <= 1e-6 * abs(zb), ids
+        assert np.allclose(rec["pts"][:d], q["pts"][:d], atol=1e-4), ids
+        kinds.add(tuple(bool(x & dcem.TRI_DIFFRACT) for x in ids))
+        checked += 1
+    s.close()
+    # two reflections (both before, one on each side, both after) and one
+    # reflection around one and two wedges
+    assert checked >= 10 and len(kinds) >= 5, (checked, kinds)

@@ -1122,3 +1122,37 @@ def test_two_reflections_and_diffraction_obey_the_laws(oracle_mod, mat):
                     for a in range(3):
                         assert np.dot(np.cross(v[(a + 1) % 3] - v[a], Y - v[a]), n) >= -1e-9
                     assert np.max(np.abs(dout - (din - 2.0 * np.dot(din, n) * n))) <= 1e-9
+
+
+def test_given_path_equals_the_enumerated_one(oracle_mod):
+    """or_diffract_path evaluates a given combined path (the check of paths
+    found elsewhere): every path the enumerations find, from two reflections
+    around a wedge to one reflection around a chain, comes out identical, and
+    ids that are not such a path are refused."""
+    O = oracle_mod
+    tris = _walls_and_tip()
+    mats = [scenes.MAT_METAL] * 4 + [scenes.MAT_CONCRETE] * (len(tris) - 4)
+    sc = scenes._static_scene("r2", tris, mats, _T2, [_R2])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=4)
+    wt = sc.tris.reshape(-1, 9)
+    found = [O.diffract_refl2(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm),
+             O.diffract_refl(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)]
+    n = 0
+    for exact, (k, p) in zip((True, False), found):
+        for kk, pp in zip(k, p):
+            ids = [int(x) for x in kk[2:2 + kk[1]]]
+            q = O.diffract_path(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0][0], ids, prm)
+            assert q is not None, ids
+            if exact:  # the same computation
+                assert q.tobytes() == pp.tobytes(), ids
+            else:  # or_diffract_refl takes the first-order Keller point in closed form
+                assert abs(q["len_m"] - pp["len_m"]) <= 1e-12 * pp["len_m"]
+                za, zb = complex(q["amp_re"], q["amp_im"]), complex(pp["amp_re"], pp["amp_im"])
+                assert abs(za - zb) <= 1e-9 * abs(zb), ids
+            n += 1
+    assert n >= 5
+    D = O.DIFF
+    with pytest.raises(ValueError):
+        O.diffract_path(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0][0], [0, 2, 3], prm)
+    with pytest.raises(ValueError):
+        O.diffract_path(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0][0], [0, 1 | D, 2, 3], prm)
