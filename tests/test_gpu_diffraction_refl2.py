@@ -193,3 +193,78 @@ def test_highway_full_size_sampled(cuda):
     # two reflections (both before, one on each side, both after) and one
     # reflection around one and two wedges
     assert checked >= 10 and len(kinds) >= 5, (checked, kinds)
+
+
+def test_links_equal_single_transmitter_frames(cuda):
+    """Two transmitters in one frame (dcem_trace_links) with diffraction up to
+    order 2 and up to two reflections around it: each transmitter's links equal
+    its own single-transmitter frame bit for bit (the images of every
+    transmitter are formed per link)."""
+    torch = cuda
+    sc = _ground(_boxes(10))
+    rays = scenes.fibonacci_sphere(20_000)
+    prm = P.gpu_params(sc, max_refl=4)
+    tx2 = sc.tx + np.array([6.0, -9.0, 1.0], np.float32)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def make(sets):
+        s = dcem.Scene.from_scene(sc, stream=st)
+        if sets:
+            s.set_ray_sets([rays, rays])
+        else:
+            s.set_rays(rays)
+        s.set_diffraction(True)
+        s.set_diffraction_reflections(2)
+        s.set_diffraction_order(2)
+        return s
+    sl, one = make(True), make(False)
+    fl = sl.trace_links(np.stack([sc.tx, tx2]), sc.rx[0], prm)
+    n2 = 0
+    for t, tx in enumerate((sc.tx, tx2)):
+        single = one.trace(tx, sc.rx[0], prm)
+        p = fl.paths[fl.paths["tx"] == t].copy()
+        p["tx"] = 0
+        p["ray"] = np.where(p["ray"] >= 0, p["ray"] - t * rays.shape[0], -1)
+        assert p.tobytes() == single.paths.tobytes(), t
+        assert np.array_equal(fl.p_coh_dbm[t], single.p_coh_dbm)
+        n2 += int(_refl2_recs(single.paths).sum())
+    assert n2 >= 5
+    sl.close()
+    one.close()
+
+
+@pytest.mark.parametrize("mode", [dcem.MODE_FULL, dcem.MODE_COHERENT])
+def test_batch_equals_single_scenes(cuda, mode):
+    """A batch of scenes (one with moving boxes) with diffraction up to order
+    2 and up to two reflections around it: each scene's frame equals its own
+    frame bit for bit."""
+    torch = cuda
+    st = torch.cuda.current_stream().cuda_stream
+    wl = [_ground(_boxes(10, n_frames=3)), _ground(_boxes(6, n_moving=2, n_frames=3))]
+    rays = scenes.fibonacci_sphere(20_000)
+
+    def make(sc):
+        s = dcem.Scene.from_scene(sc, stream=st)
+        s.set_rays(rays)
+        s.set_diffraction(True)
+        s.set_diffraction_reflections(2)
+        s.set_diffraction_order(2)
+        return s
+    batched, alone = [make(sc) for sc in wl], [make(sc) for sc in wl]
+    b = dcem.Batch(batched, stream=st)
+    prm = dcem.default_params(max_refl=4, freq_hz=28e9, mode=mode)
+    n2 = 0
+    for f in range(3):
+        b.update_transforms([sc.xf[f] if sc.nobj else None for sc in wl])
+        got = b.trace([sc.tx[None] for sc in wl], [sc.rx[f] for sc in wl], prm)
+        for sc, s, g in zip(wl, alone, got):
+            if sc.nobj:
+                s.update_transforms(sc.xf[f])
+            ref = s.trace_links(sc.tx[None], sc.rx[f], prm)
+            assert g.paths.tobytes() == ref.paths.tobytes(), (f, sc.nobj)
+            assert np.array_equal(g.p_coh_dbm, ref.p_coh_dbm)
+            n2 += int(_refl2_recs(ref.paths).sum())
+    assert n2 >= 10
+    b.close()
+    for s in batched + alone:
+        s.close()
