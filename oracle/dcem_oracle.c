@@ -45,13 +45,14 @@
  *                  1984). The transition function is evaluated from its
  *                  integral definition by quadrature along a rotated contour.
  *   or_diffract_refl, or_diffract_multi, or_diffract_multi_refl,
- *   or_diffract_refl2
+ *   or_diffract_refl2, or_diffract_mid
  *                  step 5 with steps 3-4: one reflection before or after a
  *                  first-order diffraction, chains of 2-3 wedges (Keller
  *                  points by minimising the unfolded length), such chains
- *                  with one reflection before or after them, and two
- *                  reflections around one diffraction; reflections by image
- *                  theory on static triangles.
+ *                  with one reflection before or after them, two reflections
+ *                  around one diffraction, and one reflection between two
+ *                  diffractions; reflections by image theory on static
+ *                  triangles.
  *
  * Everything after the FP32 inputs is FP64. Decisions that FP32 arithmetic
  * could take differently (a ray passing within a margin of a triangle edge,
@@ -2069,18 +2070,216 @@ int64_t or_diffract_refl2(const float* tris, const int32_t* tri_mat, const int32
   return nvalid;
 }
 
+/* A wedge mirrored in the plane of triangle Tj: its points and directions
+ * mirrored (the angle of a mirrored point about the mirrored edge is that of
+ * the point about the edge), its faces and exterior angle kept. */
+static owedge mirror_wedge(const otri* Tj, const owedge* W) {
+  owedge M = *W;
+  M.p0 = mirror_in(Tj, W->p0);
+  M.p1 = mirror_in(Tj, W->p1);
+  v3 n = Tj->nh;
+  M.e = sub(W->e, scl(n, 2.0 * dot(W->e, n)));
+  M.t0 = sub(W->t0, scl(n, 2.0 * dot(W->t0, n)));
+  M.y0 = sub(W->y0, scl(n, 2.0 * dot(W->y0, n)));
+  M.tB = sub(W->tB, scl(n, 2.0 * dot(W->tB, n)));
+  return M;
+}
+
+/* Tx -> Q1 -> P -> Q2 -> Rx: a specular reflection on static triangle j
+ * between two diffractions (wedges A then B). By image theory, mirroring
+ * the part after P in j's plane, it is the chain over A and B's image B'
+ * toward the receiver's image R': the Keller points of that chain
+ * (keller_points), its rules (chain_allowed's, and the exterior and shadow
+ * rule at both wedges), and P where the unfolded leg Q1 -> Q2' crosses the
+ * plane, strictly inside the leg and inside triangle j; Q2 is the mirror of
+ * Q2'. The four real legs are unoccluded (the wedge's faces excluded at Q1
+ * and Q2, j at P). Field: the UTD chain of chain_path_r, with at P the
+ * Fresnel reflection of j's material in the real directions (the bounce
+ * basis of validate_one) and the principal directions of the wavefront
+ * mirrored (a plane mirror keeps its radii of curvature); at B the real
+ * geometry (the direction from P, the angles of P and Rx about B's edge).
+ * Returns 1 when the path is valid, with o filled (points Q1, P, Q2). */
+static int mid_path(const oscene* S, const owedge* A, const owedge* B, int j, v3 T, v3 R, const or_params* P,
+                    opath* o) {
+  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
+  const double ang_eps = 1e-9;
+  const v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  const otri* Tj = &S->t[j];
+  uint32_t fl = 0;
+  const owedge Bm = mirror_wedge(Tj, B);
+  if (share_vertex(A, &Bm) || collinear_edges(A, &Bm) || in_face_plane(A, &Bm) || in_face_plane(&Bm, A)) return 0;
+  const v3 Rm = mirror_in(Tj, R);
+  const owedge* E[2] = {A, &Bm};
+  if (wedge_angle(A, T) > A->n * M_PI || wedge_angle(&Bm, Rm) > Bm.n * M_PI) return 0;
+  double t[2];
+  if (!keller_points(E, 2, T, Rm, t)) return 0;
+  v3 X[4];
+  X[0] = T;
+  for (int i = 0; i < 2; ++i) {
+    double uq = t[i] / E[i]->len;
+    if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+    if (!(uq > 0 && uq < 1)) return 0;
+    X[i + 1] = add(E[i]->p0, scl(E[i]->e, t[i]));
+  }
+  X[3] = Rm;
+  double ell[3];
+  for (int q = 0; q < 3; ++q) {
+    ell[q] = norm(sub(X[q + 1], X[q]));
+    if (!(ell[q] > 1e-9)) return 0;
+  }
+  double phip[2], phi[2];
+  for (int i = 0; i < 2; ++i) {
+    phip[i] = wedge_angle(E[i], X[i]);
+    phi[i] = wedge_angle(E[i], X[i + 2]);
+    double nn = E[i]->n;
+    if (phip[i] > nn * M_PI || phi[i] > nn * M_PI) return 0;
+    if (fabs(fabs(phi[i] - phip[i]) - M_PI) <= ang_eps) fl |= ORF_VAL_PARAM;
+    if (!(fabs(phi[i] - phip[i]) > M_PI)) return 0;
+  }
+  double scale = fmax(maxabs(T), maxabs(R));
+  v3 Pp;
+  if (!mirror_point(Tj, X[1], X[2], P, scale, &fl, &Pp)) return 0;
+  const v3 Q1 = X[1], Q2 = mirror_in(Tj, X[2]);
+  /* the real legs */
+  const v3 Y[5] = {T, Q1, Pp, Q2, R};
+  const int ex[5][2] = {{-1, -1}, {A->ta, A->tb}, {j, j}, {B->ta, B->tb}, {-1, -1}};
+  for (int q = 0; q < 4; ++q)
+    if (occluded4(S, Y[q], Y[q + 1], ex[q][0], ex[q][1], ex[q + 1][0], ex[q + 1][1], P, scale, &fl)) return 0;
+  /* field: the transmitter's wave, UTD at A (spherical incidence) */
+  v3 ip = scl(sub(Q1, T), 1.0 / ell[0]);
+  double complex Ei = cexp(-I * k * ell[0]) / ell[0];
+  c3 Ev;
+  {
+    v3 e0 = pol_dir(u, ip, &fl);
+    Ev.x = Ei * e0.x; Ev.y = Ei * e0.y; Ev.z = Ei * e0.z;
+  }
+  double rho1 = ell[0], rho2 = ell[0];
+  v3 dir1 = mk(0, 0, 0), dir2 = mk(0, 0, 0);
+  const double s1 = ell[1];  /* Q1 to Q2 along the real path (P between) */
+  const v3 din = unit(sub(Pp, Q1)), dout = unit(sub(Q2, Pp));
+  for (int i = 0; i < 2; ++i) {
+    const owedge* Ew = i == 0 ? A : B;
+    const v3 dd = i == 0 ? din : unit(sub(R, Q2));
+    const double s = i == 0 ? s1 : ell[2];
+    if (i == 1) {
+      /* the reflection at P: Fresnel in the real directions, the wavefront's
+       * principal directions mirrored */
+      Ev = reflect_field(S, P, Tj, din, dout, Ev);
+      dir1 = sub(dir1, scl(Tj->nh, 2.0 * dot(dir1, Tj->nh)));
+      dir2 = sub(dir2, scl(Tj->nh, 2.0 * dot(dir2, Tj->nh)));
+      ip = dout;
+    }
+    double cb = dot(ip, Ew->e);
+    double beta0 = acos(fmax(-1.0, fmin(1.0, cb)));
+    double sb = sin(beta0);
+    v3 php = cross(Ew->e, ip), ph = cross(Ew->e, dd);
+    php = scl(php, -1.0 / norm(php));
+    ph = scl(ph, 1.0 / norm(ph));
+    v3 bp = cross(ip, php), bd = cross(dd, ph);
+    double rhoe;
+    if (i == 0) rhoe = ell[0];
+    else {
+      double c1 = dot(bp, dir1), c2 = dot(bp, dir2);
+      rhoe = 1.0 / (c1 * c1 / rho1 + c2 * c2 / rho2);
+    }
+    double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
+    int ma = S->t[Ew->ta].mat, mb = S->t[Ew->tb].mat;
+    if (ma < 0 || ma >= S->nmat) ma = 0;
+    if (mb < 0 || mb >= S->nmat) mb = 0;
+    double nn = Ew->n;
+    /* the angles about the real edge: those about the unfolded one */
+    double pp = phip[i], pf = phi[i];
+    double complex r0s, r0h, rns, rnh;
+    fresnel(&S->mats[3 * ma], P->freq_hz, fabs(sin(pp)), &r0s, &r0h);
+    fresnel(&S->mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - pf)), &rns, &rnh);
+    double complex Ds = utd_coeff(nn, pf, pp, beta0, L, k, r0s, rns, &fl);
+    double complex Dh = utd_coeff(nn, pf, pp, beta0, L, k, r0h, rnh, &fl);
+    double complex Eb = cdot(Ev, bp), Ep = cdot(Ev, php);
+    double complex Amp = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);
+    double complex cb_ = -Ds * Eb * Amp, cp_ = -Dh * Ep * Amp;
+    Ev.x = cb_ * bd.x + cp_ * ph.x;
+    Ev.y = cb_ * bd.y + cp_ * ph.y;
+    Ev.z = cb_ * bd.z + cp_ * ph.z;
+    rho1 = s;
+    dir1 = ph;
+    rho2 = rhoe + s;
+    dir2 = bd;
+    ip = dd;
+  }
+  v3 prx = pol_dir(u, scl(ip, -1.0), &fl);
+  double complex a = (lam / (4.0 * M_PI)) * cdot(Ev, prx);
+  double Ltot = ell[0] + ell[1] + ell[2];
+  memset(o, 0, sizeof(*o));
+  o->valid = 1;
+  o->flags = fl;
+  o->len_m = Ltot;
+  o->delay_s = Ltot / C0;
+  o->amp_re = creal(a);
+  o->amp_im = cimag(a);
+  const v3 pts[3] = {Q1, Pp, Q2};
+  for (int q = 0; q < 3; ++q) {
+    o->pts[q][0] = pts[q].x;
+    o->pts[q][1] = pts[q].y;
+    o->pts[q][2] = pts[q].z;
+  }
+  return 1;
+}
+
+/* Sec. III steps 3-5: a specular reflection on a static triangle j between
+ * two diffractions (mid_path) over distinct wedges A, B, j a face of
+ * neither. Keys: rx, 3, A | OR_DIFF, j, B | OR_DIFF; -1 padded to 2 + width
+ * (width >= 3). Returns the number of valid paths (may exceed cap). */
+int64_t or_diffract_mid(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                        const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                        const or_params* P, int32_t width, int32_t* keys_out, opath* paths_out, int64_t cap) {
+  if (width < 3) return -1;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  int64_t nvalid = 0;
+  opath tmp;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (long a = 0; a < nw; ++a)
+      for (long b = 0; b < nw; ++b) {
+        if (a == b) continue;
+        for (int j = 0; j < ntri; ++j) {
+          if ((tri_obj && tri_obj[j] >= 0) || j == W[a].ta || j == W[a].tb || j == W[b].ta || j == W[b].tb) continue;
+          if (!mid_path(&S, &W[a], &W[b], j, T, R, P, &tmp)) continue;
+          if (nvalid < cap) {
+            int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+            kk[0] = r;
+            kk[1] = 3;
+            kk[2] = (int32_t)a | OR_DIFF;
+            kk[3] = j;
+            kk[4] = (int32_t)b | OR_DIFF;
+            for (int q = 3; q < width; ++q) kk[2 + q] = -1;
+            paths_out[nvalid] = tmp;
+          }
+          nvalid++;
+        }
+      }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
 /* One given path of the combined mechanisms, for checking paths found
  * elsewhere: ids[0..depth-1] in path order, static triangles (reflections)
  * before and after a run of 1-3 wedge ids marked OR_DIFF, at most two
- * reflections; evaluated by chain_path_r for transmitter tx and receiver rx.
- * Returns 1 (valid, o filled), 0 (not a valid path) or -1 (ids not of that
- * form). */
+ * reflections (chain_path_r), or a wedge, a triangle and a wedge (mid_path);
+ * for transmitter tx and receiver rx. Returns 1 (valid, o filled), 0 (not a
+ * valid path) or -1 (ids not of that form). */
 int32_t or_diffract_path(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
                          const float* mats, int32_t nmat, const float* tx, const float* rx, const int32_t* ids,
                          int32_t depth, const or_params* P, opath* o) {
   int jb[2], ja[2], nb = 0, na = 0, m = 0;
   long wi[3];
-  for (int q = 0; q < depth; ++q) {
+  const int mid = depth == 3 && (ids[0] & OR_DIFF) && !(ids[1] & OR_DIFF) && (ids[2] & OR_DIFF);
+  for (int q = 0; q < depth && !mid; ++q) {
     if (ids[q] & OR_DIFF) {
       if (na || m == 3) return -1;
       wi[m++] = ids[q] & ~OR_DIFF;
@@ -2092,12 +2291,26 @@ int32_t or_diffract_path(const float* tris, const int32_t* tri_mat, const int32_
       ja[na++] = ids[q];
     }
   }
+  if (mid) {
+    m = 2;
+    wi[0] = ids[0] & ~OR_DIFF;
+    wi[1] = ids[2] & ~OR_DIFF;
+    ja[0] = ids[1];
+  }
   if (m == 0 || nb + na > 2) return -1;
   oscene S;
   if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
   owedge* W = NULL;
   long nw = find_wedges(tris, tri_obj, ntri, &W);
   int ok = 1;
+  if (mid) {
+    ok = wi[0] >= 0 && wi[0] < nw && wi[1] >= 0 && wi[1] < nw && ja[0] >= 0 && ja[0] < ntri;
+    int r = -1;
+    if (ok) r = mid_path(&S, &W[wi[0]], &W[wi[1]], ja[0], mk(tx[0], tx[1], tx[2]), mk(rx[0], rx[1], rx[2]), P, o);
+    free(W);
+    scene_free(&S);
+    return r;
+  }
   for (int i = 0; i < m; ++i) ok &= wi[i] >= 0 && wi[i] < nw;
   for (int i = 0; i < nb; ++i) ok &= jb[i] >= 0 && jb[i] < ntri;
   for (int i = 0; i < na; ++i) ok &= ja[i] >= 0 && ja[i] < ntri;

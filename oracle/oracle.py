@@ -142,6 +142,9 @@ def lib():
         _lib.or_diffract_refl2.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                            P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
         _lib.or_diffract_refl2.restype = C.c_int64
+        _lib.or_diffract_mid.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                         P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
+        _lib.or_diffract_mid.restype = C.c_int64
         _lib.or_diffract_path.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, i32, C.c_int32,
                                           P(_Params), C.c_void_p]
         _lib.or_diffract_path.restype = C.c_int32
@@ -650,6 +653,29 @@ def diffract_refl2(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleP
         raise RuntimeError(f"or_diffract_refl2 failed: {n}")
     if n > cap:
         raise RuntimeError(f"or_diffract_refl2: {n} paths exceed capacity {cap}")
+    return keys[:n].copy(), paths[:n].copy()
+
+
+def diffract_mid(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleParams, cap=1 << 20):
+    """Steps 3-5 combined: a reflection on a static triangle between two
+    diffractions (image theory: the chain over the first wedge and the second
+    one's image toward the receiver's image). Keys (rx, 3, w1 | DIFF, tri,
+    w2 | DIFF), -1 padded to 2 + max(prm.width, 3)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    width = max(prm.width, 3)
+    keys = np.zeros((cap, 2 + width), np.int32)
+    paths = np.zeros(cap, PATH_DTYPE)
+    prm_c = prm.c()
+    n = lib().or_diffract_mid(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), _p(_i32(tri_obj), C.c_int32),
+                              wt.shape[0], _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                              _p(rx, C.c_float), rx.shape[0], C.byref(prm_c), width, _p(keys, C.c_int32),
+                              paths.ctypes.data_as(C.c_void_p), cap)
+    if n < 0:
+        raise RuntimeError(f"or_diffract_mid failed: {n}")
+    if n > cap:
+        raise RuntimeError(f"or_diffract_mid: {n} paths exceed capacity {cap}")
     return keys[:n].copy(), paths[:n].copy()
 
 

@@ -82,6 +82,11 @@ MUTANTS = [
      "if (!mirror_point(&S->t[jb[i]], Simg[nb], b, P, scale, &fl, &Yb[i])) return 0;"),
     ("refl2_first_reflection_dropped", "Er = reflect_field(S, P, &S->t[jb[i]], din, dout, Er);",
      "if (i == nb - 1) Er = reflect_field(S, P, &S->t[jb[i]], din, dout, Er);"),
+    # a reflection between two diffractions: the receiver's image, the wavefront at the mirror
+    ("mid_receiver_not_mirrored", "const v3 Rm = mirror_in(Tj, R);", "const v3 Rm = R;"),
+    ("mid_reflection_dropped", "Ev = reflect_field(S, P, Tj, din, dout, Ev);", "(void)0;"),
+    ("mid_principal_directions_not_mirrored", "dir1 = sub(dir1, scl(Tj->nh, 2.0 * dot(dir1, Tj->nh)));",
+     "(void)0;"),
     ("spherical_spreading", "double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);",
      "double complex A = csqrt(ell[0] / (s * (ell[0] + s))) * cexp(-I * k * s);"),
 ]

@@ -1151,8 +1151,107 @@ def test_given_path_equals_the_enumerated_one(oracle_mod):
                 assert abs(za - zb) <= 1e-9 * abs(zb), ids
             n += 1
     assert n >= 5
+    # a reflection between two wedges
+    tris2 = _GROUND + _ridge(0.0, 2.0, 10.0) + _ridge(8.0, 2.0, 10.0)
+    sc2 = scenes._static_scene("mid", tris2, [scenes.MAT_CONCRETE] * len(tris2), _TM, [_RM])
+    km, pm = O.diffract_mid(sc2.tris.reshape(-1, 9), sc2.tri_mat, sc2.tri_obj, sc2.materials, sc2.tx, sc2.rx[0],
+                            prm)
+    assert len(km) == 1
+    q = O.diffract_path(sc2.tris.reshape(-1, 9), sc2.tri_mat, sc2.tri_obj, sc2.materials, sc2.tx, sc2.rx[0][0],
+                        [int(x) for x in km[0][2:5]], prm)
+    assert q is not None and q.tobytes() == pm[0].tobytes()
     D = O.DIFF
     with pytest.raises(ValueError):
         O.diffract_path(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0][0], [0, 2, 3], prm)
     with pytest.raises(ValueError):
         O.diffract_path(wt, sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0][0], [0, 1 | D, 2, 3], prm)
+
+
+# ---------------------------------------------------------------------------
+# a reflection between two diffractions
+# ---------------------------------------------------------------------------
+def _ridge(xc, w, h, y0=-20.0, y1=20.0):
+    """A horizontal triangular prism along y on the ground: base from xc - w to
+    xc + w, its ridge (a wedge of about 23 degrees) at height h."""
+    a, b, c = (xc - w, 0.0), (xc, h), (xc + w, 0.0)
+    out = scenes._quad((a[0], y0, a[1]), (b[0], y0, b[1]), (b[0], y1, b[1]), (a[0], y1, a[1]))
+    out += scenes._quad((b[0], y0, b[1]), (c[0], y0, c[1]), (c[0], y1, c[1]), (b[0], y1, b[1]))
+    out += [[(a[0], y0, a[1]), (c[0], y0, c[1]), (b[0], y0, b[1])],
+            [(a[0], y1, a[1]), (b[0], y1, b[1]), (c[0], y1, c[1])]]
+    return out
+
+
+_TM, _RM = (-30.0, -3.0, 1.0), (38.0, 5.0, 1.5)
+
+
+def _mid(O, tris, mats, tx, rx):
+    sc = scenes._static_scene("mid", tris, mats, tx, [rx])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    return O.diffract_mid(sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_reflection_between_wedges_is_the_image_chain(oracle_mod, mat):
+    """Two ridges on a perfectly conducting ground, vertical polarisation: the
+    path over the first ridge, the ground and the second ridge is, by image
+    theory, the order-2 chain over the first ridge and the second ridge's
+    image below the ground (with no ground) toward the receiver's image (a
+    vertically polarised receiver's image is vertically polarised): the same
+    diffraction points (the second mirrored), length and amplitude; the
+    reflection point on the ground between the ridges."""
+    O = oracle_mod
+    r1, r2 = _ridge(0.0, 2.0, 10.0), _ridge(8.0, 2.0, 10.0)
+    tris = _GROUND + r1 + r2
+    k, p = _mid(O, tris, [scenes.MAT_METAL] * 2 + [mat] * (len(tris) - 2), _TM, _RM)
+    assert len(k) == 1 and k[0][3] < 2                     # the reflection on the ground
+    q1, pg, q2 = p["pts"][0][:3]
+    assert abs(pg[2]) <= 1e-12 and 2.0 < pg[0] < 6.0
+    img = r1 + [[(x, y, -z) for (x, y, z) in t] for t in r2]
+    rm = (_RM[0], _RM[1], -_RM[2])
+    b = scenes._static_scene("image", img, [mat] * len(img), _TM, [rm])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=3)
+    bk, bp = O.diffract_multi(b.tris.reshape(-1, 9), b.tri_mat, b.tri_obj, b.materials, b.tx, b.rx[0], prm, 2)
+    q2m = np.array([q2[0], q2[1], -q2[2]])
+    j = [i for i in range(len(bk)) if np.max(np.abs(bp["pts"][i][0] - q1)) <= 1e-9
+         and np.max(np.abs(bp["pts"][i][1] - q2m)) <= 1e-9]
+    assert len(j) == 1
+    assert abs(bp["len_m"][j[0]] - p["len_m"][0]) <= 1e-12 * p["len_m"][0]
+    a, b_ = complex(p["amp_re"][0], p["amp_im"][0]), complex(bp["amp_re"][j[0]], bp["amp_im"][j[0]])
+    assert abs(a - b_) <= 1e-9 * abs(b_)
+
+
+def test_reflection_between_wedges_reciprocity(oracle_mod):
+    """Perfect conductors: swapping Tx and Rx gives the path over the same
+    wedges and triangle in reverse order, with the same length and amplitude."""
+    O = oracle_mod
+    tris = _GROUND + _ridge(0.0, 2.0, 10.0) + _ridge(8.0, 2.0, 10.0)
+    mats = [scenes.MAT_METAL] * len(tris)
+    (kf, pf), (kb, pb) = _mid(O, tris, mats, _TM, _RM), _mid(O, tris, mats, _RM, _TM)
+    assert len(kf) == len(kb) == 1
+    assert list(kf[0][2:5]) == list(kb[0][2:5])[::-1]
+    assert abs(pf["len_m"][0] - pb["len_m"][0]) <= 1e-9 * pf["len_m"][0]
+    a, b = complex(pf["amp_re"][0], pf["amp_im"][0]), complex(pb["amp_re"][0], pb["amp_im"][0])
+    assert abs(a - b) <= 1e-9 * abs(a)
+
+
+@pytest.mark.parametrize("mat", [scenes.MAT_METAL, scenes.MAT_CONCRETE])
+def test_reflection_between_wedges_obeys_the_laws(oracle_mod, mat):
+    """Without image theory, on a concrete ground: the reflection point lies on
+    the ground and the outgoing leg is the mirror image of the incoming one;
+    each diffraction point lies on its ridge and its two legs make equal
+    angles with it; the length is the sum of the four legs."""
+    O = oracle_mod
+    tris = _GROUND + _ridge(0.0, 2.0, 10.0) + _ridge(8.0, 2.0, 10.0)
+    k, p = _mid(O, tris, [scenes.MAT_CONCRETE] * 2 + [mat] * (len(tris) - 2), _TM, _RM)
+    assert len(k) == 1
+    X = [np.asarray(_TM, np.float64)] + [p["pts"][0][i] for i in range(3)] + [np.asarray(_RM, np.float64)]
+    legs = [np.linalg.norm(X[i + 1] - X[i]) for i in range(4)]
+    assert abs(sum(legs) - p["len_m"][0]) <= 1e-9 * p["len_m"][0]
+    e = np.array([0.0, 1.0, 0.0])
+    for i in (1, 3):  # the ridges run along y
+        din, dout = (X[i] - X[i - 1]) / legs[i - 1], (X[i + 1] - X[i]) / legs[i]
+        assert abs(X[i][2] - 10.0) <= 1e-9
+        assert abs(np.dot(din, e) - np.dot(dout, e)) <= 1e-9
+    din, dout = (X[2] - X[1]) / legs[1], (X[3] - X[2]) / legs[2]
+    assert abs(X[2][2]) <= 1e-12
+    assert np.max(np.abs(dout - din * np.array([1.0, 1.0, -1.0]))) <= 1e-9
