@@ -353,8 +353,19 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges);
  * unfolded distances. Record: depth 3, tri = the two triangle ids and
  * wedge | DCEM_TRI_DIFFRACT in path order, pts = the three points. Cost: one
  * warp per (kind, link, plane pair) per frame, its lanes over the wedges.
- * Errors: DCEM_ERR_ARG (on outside 0..2), DCEM_ERR_STATE (diffraction is
- * off), DCEM_ERR_CUDA. */
+ * on = 3 adds, to on = 2 and with diffraction chains on (max_order >= 2), a
+ * reflection between the two wedges of an order-2 chain: Tx -> Q1 -> P ->
+ * Q2 -> Rx, by image theory the chain over the first wedge and the second
+ * one's image in the plane toward the receiver's image (Keller points, the
+ * chain rules, exterior and shadow rules on that chain), P where its middle
+ * leg crosses the plane, inside a triangle of the plane (the images then
+ * taken in that triangle's own plane), the four legs unoccluded; field: the
+ * UTD coefficients and Fresnel at P, the wavefront's principal directions
+ * mirrored there. Record: depth 3, tri = {wedge_1 | DCEM_TRI_DIFFRACT,
+ * triangle id, wedge_2 | DCEM_TRI_DIFFRACT}, pts = Q1, P, Q2. Cost: one warp
+ * per (transmitter, wedge, plane) forming the pairs, then the chains' pre-test
+ * per (pair, receiver). Errors: DCEM_ERR_ARG (on outside 0..3),
+ * DCEM_ERR_STATE (diffraction is off), DCEM_ERR_CUDA. */
 int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes);
 
 /* With diffraction on: paths over up to max_order wedges (1, 2 or 3; Sec.

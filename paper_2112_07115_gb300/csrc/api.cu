@@ -252,7 +252,7 @@ struct dcem_scene {
   RPlane* rplanes = nullptr;   // diffraction combined with a reflection: reflector planes
   int* rmembers = nullptr;     // ... and their triangle ids
   int nrp = 0;
-  int diff_refl = 0;               // reflections around a first-order diffraction (0..2)
+  int diff_refl = 0;               // reflections with diffraction (0..3, see the header)
   unsigned dsurv_cap = 0;
   int diff_order = 1;          // diffraction: most wedges on one path (1-3)
   int4* dseq2 = nullptr;       // ... the frame's wedge pairs and triples, the pair relation
@@ -1291,7 +1291,7 @@ int dcem_scene_set_diffraction(dcem_scene* s, int32_t on, int32_t* n_wedges) {
 }
 
 int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n_planes) {
-  if (!s || on < 0 || on > 2) return DCEM_ERR_ARG;
+  if (!s || on < 0 || on > 3) return DCEM_ERR_ARG;
   if (on && !s->diffraction) return DCEM_ERR_STATE;
   if (on && !s->rplanes) {
     std::vector<RPlane> planes;
@@ -1582,6 +1582,7 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.rmembers = dr ? s->rmembers : nullptr;
   q.nrp = dr ? s->nrp : 0;
   q.drefl2 = dr && s->diff_refl >= 2 ? 1 : 0;
+  q.dmid = dr && s->diff_refl >= 3 && dord >= 2 ? 1 : 0;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
   P.sticky = p->mode == DCEM_MODE_STICKY;
@@ -1769,7 +1770,7 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
                  (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
                  (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
-                 (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 : 0);
+                 (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 + (P.q.dmid ? 1 : 0) : 0);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -2301,7 +2302,7 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
                      (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
                      (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
                      (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
-                     (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 : 0) + (i == 0 ? 1 : 0);
+                     (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 + (P.q.dmid ? 1 : 0) : 0) + (i == 0 ? 1 : 0);
       s->graph_replayed = 0;
       b->h_tab[i] = frame_trace_args(P);
     }

@@ -1624,6 +1624,161 @@ __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int nsrc) {
   }
 }
 
+// A wedge's FP32 frame mirrored in plane (n, c): the point and directions
+// mirrored, the length and exterior angle kept (the angle of a mirrored
+// point about the mirrored edge is that of the point about the edge).
+__device__ __forceinline__ WedgeF wedge_mirror32(const WedgeF& W, float3 n, float c) {
+  auto dir = [&](float3 v) {
+    const float h = 2.0f * fdot3(n, v);
+    return f3(v.x - h * n.x, v.y - h * n.y, v.z - h * n.z);
+  };
+  WedgeF M = W;
+  M.p0 = mirror32(W.p0, n, c);
+  M.e = dir(W.e);
+  M.t0 = dir(W.t0);
+  M.y0 = dir(W.y0);
+  return M;
+}
+
+// A wedge mirrored in plane (n, c) in FP64 (as wedge_mirror32).
+__device__ __forceinline__ Wedge wedge_mirror64(const Wedge& W, d3w n, double c) {
+  auto put = [](double* dst, d3w v) {
+    dst[0] = v.x;
+    dst[1] = v.y;
+    dst[2] = v.z;
+  };
+  auto pt = [&](const double* x) {
+    const d3w v = D3(x[0], x[1], x[2]);
+    return v - n * (2.0 * (dotw(n, v) - c));
+  };
+  auto dir = [&](const double* x) {
+    const d3w v = D3(x[0], x[1], x[2]);
+    return v - n * (2.0 * dotw(n, v));
+  };
+  Wedge M = W;
+  put(M.p0, pt(W.p0));
+  put(M.p1, pt(W.p1));
+  put(M.e, dir(W.e));
+  put(M.t0, dir(W.t0));
+  put(M.y0, dir(W.y0));
+  put(M.tB, dir(W.tB));
+  return M;
+}
+
+// Does the edge of W lie in plane (n, c) up to rounding (both ends within
+// 1e-12 m, relative to the coordinates' size)? A reflection in that plane
+// next to the edge would sit at the diffraction point itself (the oracle
+// flags such a reflection point at its leg's end).
+__device__ __forceinline__ bool edge_in_plane(const Wedge& W, d3w n, double c) {
+  const double tol = 1e-12 * (1.0 + fmax(fabs(W.p0[0]), fmax(fabs(W.p0[1]), fabs(W.p0[2]))));
+  return fabs(dotw(n, D3(W.p0[0], W.p0[1], W.p0[2])) - c) <= tol &&
+         fabs(dotw(n, D3(W.p1[0], W.p1[1], W.p1[2])) - c) <= tol;
+}
+
+// Can a leg from a point of segment A0-A1 to a point of segment B0-B1 cross
+// plane Pl inside its box? Such legs fill the tetrahedron of the four ends,
+// whose section by the plane lies within the box of the crossings of its six
+// edges; "no" when the four ends lie on one side (by more than m) or that
+// box, widened by m, misses the plane's box.
+__device__ __forceinline__ bool section_reachable(const RPlane& Pl, float3 A0, float3 A1, float3 B0, float3 B1,
+                                                  float m) {
+  const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
+  const float3 X[4] = {A0, A1, B0, B1};
+  float d[4];
+  bool pos = false, neg = false;
+  for (int i = 0; i < 4; ++i) {
+    d[i] = fdot3(n, X[i]) - Pl.cf;
+    pos = pos || d[i] > -m;
+    neg = neg || d[i] < m;
+  }
+  if (!pos || !neg) return false;
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  bool any = false;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j) {
+      if ((d[i] > m && d[j] > m) || (d[i] < -m && d[j] < -m)) continue;
+      const float den = d[i] - d[j];
+      float ta = 0.0f, tb = 1.0f;
+      if (fabsf(den) > 1e-30f) {
+        const float t1 = (d[i] - m) / den, t2 = (d[i] + m) / den;
+        ta = fmaxf(0.0f, fminf(t1, t2));
+        tb = fminf(1.0f, fmaxf(t1, t2));
+      }
+      if (ta > tb) continue;
+      for (int q = 0; q < 2; ++q) {
+        const float t = q ? tb : ta;
+        const float x = X[i].x + t * (X[j].x - X[i].x), y = X[i].y + t * (X[j].y - X[i].y),
+                    z = X[i].z + t * (X[j].z - X[i].z);
+        lo[0] = fminf(lo[0], x); lo[1] = fminf(lo[1], y); lo[2] = fminf(lo[2], z);
+        hi[0] = fmaxf(hi[0], x); hi[1] = fmaxf(hi[1], y); hi[2] = fmaxf(hi[2], z);
+      }
+      any = true;
+    }
+  if (!any) return false;
+  for (int k = 0; k < 3; ++k)
+    if (hi[k] < Pl.box[k] - m || lo[k] > Pl.box[3 + k] + m) return false;
+  return true;
+}
+
+// Wedge pairs with a reflection between them (Sec. III steps 3-5): per
+// (transmitter, first wedge, reflector plane), one warp, its lanes over the
+// second wedge. By image theory the path Tx -> Q1 -> P -> Q2 -> Rx is the
+// chain over w1 and w2's image in the plane; the pair is kept when that
+// image and w1 satisfy the pair tests of k_diff_pairs (each partly in the
+// other's exterior, some point of the image beyond the transmitter's shadow
+// boundary at w1, the transmitter outside w1) and some leg between the two
+// edges can cross the plane inside its box. Entries (t, w1, w2, -2 - p) join
+// the pair list (k_diff_triples skips them); the FP64 vertex, line and
+// face-plane rules are the exact stage's.
+__global__ void __launch_bounds__(256) k_diff_mid_pairs(PathArgs a) {
+  const long nblk = (long)a.dntx * a.nw * a.nrp;
+  const int lane = threadIdx.x & 31;
+  const long nwarp = (long)gridDim.x * (blockDim.x >> 5);
+  for (long b = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nblk; b += nwarp) {
+    const int p = (int)(b % a.nrp);
+    const long r = b / a.nrp;
+    const int w1 = (int)(r % a.nw), t = (int)(r / a.nw);
+    const WedgeF fa = a.wf[w1];
+    const float3 T = chain_source32(a, t);
+    if (surely_inside(fa, T)) continue;  // warp-uniform
+    const RPlane& Pl = a.rplanes[p];
+    const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
+    float3 A0, A1;
+    edge_ends(fa, A0, A1);
+    for (int w0 = 0; w0 < a.nw; w0 += 32) {
+      const int w2 = w0 + lane;
+      bool keep = false;
+      if (w2 < a.nw && w2 != w1) {
+        const WedgeF fb = wedge_mirror32(a.wf[w2], n, Pl.cf);
+        float3 B0, B1;
+        edge_ends(fb, B0, B1);
+        const float m = fmaxf(pre_margin_m(A0), pre_margin_m(A1));
+        keep = edge_sees(fa, fb, m) && edge_sees(fb, fa, m) && shadow_meets(fa, T, B0, B1);
+        if (keep) {
+          const float mg = 0.1f + 1e-4f * (fabsf(A0.x) + fabsf(A0.y) + fabsf(A0.z) + fa.len + fb.len);
+          keep = section_reachable(Pl, A0, A1, B0, B1, mg);
+        }
+        if (keep) {  // the exact stage's FP64 rules on the group plane's image
+          const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
+          const d3w n64 = D3(Pl.n[0], Pl.n[1], Pl.n[2]);
+          const Wedge Bm = wedge_mirror64(B, n64, Pl.c);
+          keep = !edge_in_plane(A, n64, Pl.c) && !edge_in_plane(B, n64, Pl.c) && !share_vertex(A, Bm) &&
+                 !collinear_edges(A, Bm) && !in_face_plane(A, Bm) && !in_face_plane(Bm, A);
+        }
+      }
+      const unsigned mk = __ballot_sync(0xffffffffu, keep);
+      if (!mk) continue;
+      unsigned at = 0;
+      if (lane == 0) at = atomicAdd(&a.ctr->n_dpair, (unsigned)__popc(mk));
+      at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+      if (keep) {
+        if (at < a.dseq2_cap) a.dseq2[at] = make_int4(t, w1, w2, -2 - p);
+        else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+      }
+    }
+  }
+}
+
 // Triples (w1, w2, w3) from the pairs: (w2, w3) in the relation, w3 not w1.
 __global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
   const long nw = a.nw;
@@ -1640,7 +1795,7 @@ __global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
       w3 = (int)(idx - p * nw);
       pr = a.dseq2[p];
       size_t bit = (size_t)pr.z * nw + w3;
-      keep = w3 != pr.y && ((a.drel[bit >> 5] >> (bit & 31)) & 1u);
+      keep = pr.w == -1 && w3 != pr.y && ((a.drel[bit >> 5] >> (bit & 31)) & 1u);
     }
     unsigned mk = __ballot_sync(0xffffffffu, keep);
     if (!mk) continue;
@@ -1878,6 +2033,15 @@ __device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float
 // its shadow boundary there; an image observer's leg from the last edge must
 // be able to cross its plane inside the box.
 __device__ __forceinline__ bool multi_stage1(const PathArgs& a, int4 sq, bool three, int rho) {
+  if (!three && sq.w <= -2) {  // a reflection between the wedges: w2 and the receiver mirrored
+    const RPlane& Pl = a.rplanes[-2 - sq.w];
+    const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
+    const WedgeF fl = wedge_mirror32(a.wf[sq.z], n, Pl.cf), fp = a.wf[sq.y];
+    const float3 R = mirror32(chain_observer32(a, rho), n, Pl.cf);
+    float3 P, Q;
+    edge_ends(fp, P, Q);
+    return !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+  }
   const bool obs_img = rho >= a.nrx;
   const int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
   const WedgeF fl = a.wf[wl], fp = a.wf[wp];
@@ -1893,6 +2057,50 @@ __device__ __forceinline__ bool multi_stage1(const PathArgs& a, int4 sq, bool th
   return keep;
 }
 
+// Stage 2 for a pair with a reflection between its wedges: the chain over w1
+// and w2's image toward the receiver's image (FP32 Keller estimate against
+// the rules), the real first and last legs against robust occlusion (the
+// last one mirrored back), and the crossing of the unfolded middle leg with
+// the plane inside its box.
+__device__ __forceinline__ bool mid_stage2(const PathArgs& a, int4 sq, int rho, TStack& st) {
+  const RPlane& Pl = a.rplanes[-2 - sq.w];
+  const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
+  WedgeF Wc[2];
+  Wc[0] = a.wf[sq.y];
+  Wc[1] = wedge_mirror32(a.wf[sq.z], n, Pl.cf);
+  const float3 T = chain_source32(a, sq.x), R = chain_observer32(a, rho), Rm = mirror32(R, n, Pl.cf);
+  float t[2];
+  bool solved;
+  bool keep = chain_possible(Wc, 2, T, Rm, t, &solved);
+  if (!keep || !solved) return keep;
+  const float delta = chain_margin(T, Rm);
+  const float3 Q1 = edge_point(Wc[0], t[0]), Q2m = edge_point(Wc[1], t[1]), Q2 = mirror32(Q2m, n, Pl.cf);
+  const Wedge &A = a.wedges[sq.y], &B = a.wedges[sq.z];
+  float3 dv = f3(Q1.x - T.x, Q1.y - T.y, Q1.z - T.z);
+  if (leg_surely_blocked(a.bvh, T, dv, delta, a.eps_occ, -1, -1, A.ta, A.tb, st)) return false;
+  dv = f3(R.x - Q2.x, R.y - Q2.y, R.z - Q2.z);
+  if (leg_surely_blocked(a.bvh, Q2, dv, delta, a.eps_occ, B.ta, B.tb, -1, -1, st)) return false;
+  dv = f3(Q2m.x - Q1.x, Q2m.y - Q1.y, Q2m.z - Q1.z);
+  const float den = fdot3(n, dv), len = sqrtf(fdot3(dv, dv));
+  if (fabsf(den) > 1e-6f * len) {
+    const float tt = (Pl.cf - fdot3(n, Q1)) / den;
+    const float mt = (0.05f + delta + 1e-4f * (len + sqrtf(fdot3(Q1, Q1)))) / len;
+    if (tt < -mt || tt > 1.0f + mt) return false;
+    const float3 Xp = f3(Q1.x + tt * dv.x, Q1.y + tt * dv.y, Q1.z + tt * dv.z);
+    const float mb = 0.05f + delta + 1e-4f * (len + sqrtf(fdot3(Xp, Xp)));
+    if (Xp.x < Pl.box[0] - mb || Xp.y < Pl.box[1] - mb || Xp.z < Pl.box[2] - mb || Xp.x > Pl.box[3] + mb ||
+        Xp.y > Pl.box[4] + mb || Xp.z > Pl.box[5] + mb)
+      return false;
+    // the two real legs through the reflection point (a crossing near a
+    // leg's end, as the reflector's own at P, does not count)
+    float3 d1 = f3(Xp.x - Q1.x, Xp.y - Q1.y, Xp.z - Q1.z), d2 = f3(Q2.x - Xp.x, Q2.y - Xp.y, Q2.z - Xp.z);
+    if (leg_surely_blocked(a.bvh, Q1, d1, delta, a.eps_occ, A.ta, A.tb, -1, -1, st) ||
+        leg_surely_blocked(a.bvh, Xp, d2, delta, a.eps_occ, -1, -1, B.ta, B.tb, st))
+      return false;
+  }
+  return true;
+}
+
 // Stage 2 for an index past stage 1: the FP32 Keller estimate against the
 // rules, the real legs against robust occlusion, and with a reflection its
 // point on the unfolded leg inside the plane's box.
@@ -1902,6 +2110,7 @@ __device__ __forceinline__ bool multi_stage2(const PathArgs& a, long idx, long n
   const bool three = e >= n2;
   const long ei = three ? e - n2 : e;
   const int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
+  if (!three && sq.w <= -2) return mid_stage2(a, sq, rho, st);
   const bool src_img = sq.x >= a.dntx, obs_img = rho >= a.nrx;
   const int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
   WedgeF Wc[3];
@@ -1983,7 +2192,7 @@ __global__ void __launch_bounds__(256) k_diff_multi_pre(PathArgs a) {
       if (item >= nitem) break;
       e = item / nrun;
       sq = e >= n2 ? a.dseq3[e - n2] : a.dseq2[e];
-      const long nob = sq.x >= a.dntx ? a.nrx : nobs;
+      const long nob = sq.x >= a.dntx || (e < n2 && sq.w <= -2) ? a.nrx : nobs;
       r0 = (item - e * nrun) * kObsRun;
       r1 = min(r0 + kObsRun, nob);
     }
@@ -2206,6 +2415,153 @@ __device__ zv3 reflect_field_d(const PathArgs& a, d3w nj, float4 mj, d3w din, d3
 // (rho_e (rho_1 + s) (rho_2 + s)) (Kouyoumjian & Pathak 1974, straight
 // edge), over the unfolded distances (a plane mirror keeps the wavefront's
 // radii); the reflection applies Fresnel in the real directions.
+// One survivor of a pair with a reflection between its wedges (Sec. III
+// steps 3-5): the FP64 chain over w1 and w2's image in the plane toward the
+// receiver's image (chain_geometry), the vertex, line and face-plane rules
+// on the image, the reflection point where the unfolded middle leg crosses
+// the plane, the member triangle holding it and everything again on that
+// triangle's own plane; the four real legs (FP32 any-hit; the wedges' faces
+// excluded at Q1 and Q2, the triangle at P); then the field: UTD at w1,
+// Fresnel at P in the real directions with the wavefront's principal
+// directions mirrored, UTD at w2 in the real directions (its angles are
+// those about the image). Record: depth 3, {w1 | diffract, triangle,
+// w2 | diffract}.
+__device__ __noinline__ void diffract_mid(const PathArgs& a, int4 sq, int r, double k, double lam, unsigned& ovf,
+                                          TStack& st) {
+  const int w1 = sq.y, w2 = sq.z, tx = sq.x;
+  const int link = tx * a.nrx + r;
+  const Wedge& A = a.wedges[w1];
+  const Wedge& B = a.wedges[w2];
+  const float4 rxv = a.rx[r], txv = a.txs[tx];
+  const d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
+  const RPlane& G = a.rplanes[-2 - sq.w];
+  d3w n = D3(G.n[0], G.n[1], G.n[2]);
+  double c = G.c;
+  auto mir = [&](d3w x) { return x - n * (2.0 * (dotw(n, x) - c)); };
+  int j = -1;
+  float4 mj = make_float4(0.f, 0.f, 0.f, 0.f);
+  d3w X[4], Pp = D3(0, 0, 0);
+  double ell[3], phip[2], phi[2];
+  for (int pass = 0; pass < 2; ++pass) {
+    const Wedge Bm = wedge_mirror64(B, n, c);  // w2's image in the plane
+    if (edge_in_plane(A, n, c) || edge_in_plane(B, n, c)) return;
+    if (share_vertex(A, Bm) || collinear_edges(A, Bm) || in_face_plane(A, Bm) || in_face_plane(Bm, A)) return;
+    const Wedge* E[2] = {&A, &Bm};
+    if (!chain_geometry(E, 2, T, mir(R), X, ell, phip, phi)) return;
+    if (!leg_plane(X[1], X[2], n, c, Pp)) return;
+    d3w v0, v1, v2;
+    if (pass == 0) {  // the member triangle holding P: its own plane next
+      for (int q = 0; q < G.count && j < 0; ++q) {
+        const int id = a.rmembers[G.first + q];
+        if (id == A.ta || id == A.tb || id == B.ta || id == B.tb || !tri_box_near(a, id, Pp)) continue;
+        tri64(a, id, v0, v1, v2, mj);
+        if (inside_tri64(v0, v1, v2, Pp)) j = id;
+      }
+      if (j < 0) return;
+      n = unitw(crossw(v1 - v0, v2 - v0));
+      c = dotw(n, v0);
+    } else {
+      tri64(a, j, v0, v1, v2, mj);
+      if (!inside_tri64(v0, v1, v2, Pp)) return;
+    }
+  }
+  const d3w Q1 = X[1], Q2 = mir(X[2]);
+  // the real legs: two excluded triangles at each point
+  const d3w Y[5] = {T, Q1, Pp, Q2, R};
+  const int ex[5][2] = {{-1, -1}, {A.ta, A.tb}, {j, j}, {B.ta, B.tb}, {-1, -1}};
+  for (int q = 0; q < 4; ++q) {
+    const d3w dv = Y[q + 1] - Y[q];
+    RayPre rp = ray_pre(f3((float)Y[q].x, (float)Y[q].y, (float)Y[q].z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+    if (any_hit(a.bvh, rp, a.eps_occ, 1.0f - a.eps_occ, ex[q][0], ex[q][1], ovf, st, ex[q + 1][0], ex[q + 1][1]))
+      return;
+  }
+  unsigned fl = 0;
+  const d3w u = D3(a.pol.x, a.pol.y, a.pol.z);
+  d3w ip = (Q1 - T) * (1.0 / ell[0]);
+  double sn, cs;
+  sincos(-k * ell[0], &sn, &cs);
+  const zd Ei = Z(cs / ell[0], sn / ell[0]);
+  const d3w e0 = polw(u, ip, fl);
+  zv3 Ev = {Ei * e0.x, Ei * e0.y, Ei * e0.z};
+  double rho1 = ell[0], rho2 = ell[0];
+  d3w dir1 = D3(0, 0, 0), dir2 = D3(0, 0, 0);
+  const d3w din = unitw(Pp - Q1), dout = unitw(Q2 - Pp);
+  for (int i = 0; i < 2; ++i) {
+    const Wedge& W = i == 0 ? A : B;
+    const d3w dd = i == 0 ? din : unitw(R - Q2);
+    const double s = ell[i + 1], nn = W.n;
+    if (i == 1) {  // the reflection at P; the wavefront's principal directions mirrored
+      Ev = reflect_field_d(a, n, mj, din, dout, Ev);
+      dir1 = dir1 - n * (2.0 * dotw(dir1, n));
+      dir2 = dir2 - n * (2.0 * dotw(dir2, n));
+      ip = dout;
+    }
+    const d3w e = D3(W.e[0], W.e[1], W.e[2]);
+    const double beta0 = acos(fmax(-1.0, fmin(1.0, dotw(ip, e))));
+    const double sb = sin(beta0);
+    const d3w php = unitw(crossw(e, ip)) * -1.0, ph = unitw(crossw(e, dd));
+    const d3w bp = crossw(ip, php), bd = crossw(dd, ph);
+    double rhoe;
+    if (i == 0) rhoe = ell[0];
+    else {
+      const double c1 = dotw(bp, dir1), c2 = dotw(bp, dir2);
+      rhoe = 1.0 / (c1 * c1 / rho1 + c2 * c2 / rho2);
+    }
+    const double L = s * (rhoe + s) * rho1 * rho2 * sb * sb / (rhoe * (rho1 + s) * (rho2 + s));
+    const float4 ma =
+        a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.ta, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+    const float4 mb =
+        a.mats[__float_as_int(a.tris[3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(W.tb, a.bvh.ntris)], a.bvh.ntris) + 1].w)];
+    zd r0s, r0h, rns, rnh;
+    fresnel_d(ma, a.freq, fabs(sin(phip[i])), r0s, r0h);
+    fresnel_d(mb, a.freq, fabs(sin(nn * M_PI - phi[i])), rns, rnh);
+    const UtdParts up = utd_parts(nn, phi[i], phip[i], beta0, L, k, fl);
+    const zd Ds = utd_coeff(up, r0s, rns), Dh = utd_coeff(up, r0h, rnh);
+    sincos(-k * s, &sn, &cs);
+    const zd Am = Z(cs, sn) * sqrt(rhoe / (s * (rhoe + s)));
+    const zd cb = Ds * zvdot(Ev, bp) * Am * -1.0, cp = Dh * zvdot(Ev, php) * Am * -1.0;
+    Ev = zv3{cb * bd.x + cp * ph.x, cb * bd.y + cp * ph.y, cb * bd.z + cp * ph.z};
+    rho1 = s;
+    dir1 = ph;
+    rho2 = rhoe + s;
+    dir2 = bd;
+    ip = dd;
+  }
+  const d3w prx = polw(u, ip * -1.0, fl);
+  const zd amp = zvdot(Ev, prx) * (lam / (4.0 * M_PI));
+  unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
+  if (uu >= a.ucap) {
+    atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
+    return;
+  }
+  const int ids[3] = {w1 | kDiffBit, j, w2 | kDiffBit};
+  PathRec rec;
+  rec.key = seq_key(r, 3, [&](int q) { return ids[q]; });
+  rec.rx = link;
+  rec.depth = 3;
+  rec.ray = -1;
+  rec.flags = fl;
+  rec.valid = 1;
+  rec.pad = 0;
+  rec.len = ell[0] + ell[1] + ell[2];
+  rec.amp_re = amp.re;
+  rec.amp_im = amp.im;
+  for (int q = 0; q < kMaxRefl; ++q) {
+    rec.tri[q] = q < 3 ? ids[q] : -1;
+    rec.pts[q][0] = rec.pts[q][1] = rec.pts[q][2] = 0.0f;
+  }
+  for (int q = 0; q < 3; ++q) {
+    rec.pts[q][0] = (float)Y[q + 1].x;
+    rec.pts[q][1] = (float)Y[q + 1].y;
+    rec.pts[q][2] = (float)Y[q + 1].z;
+  }
+  a.prec[uu] = rec;
+  unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
+  if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
+  else atomicOr(&a.ctr->err, ERR_BUCKET_OVERFLOW);
+  atomicAdd(&a.ctr->n_valid, 1u);
+}
+
 __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long long code, double k, double lam,
                                             unsigned& ovf, TStack& st) {
   const bool three = (code >> kKindShift) == 3ull;
@@ -2215,6 +2571,10 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
   const long ei = (long)(c / nobs);
   const int rho = (int)(c - (unsigned long long)ei * nobs);
   const int4 sq = three ? a.dseq3[ei] : a.dseq2[ei];
+  if (!three && sq.w <= -2) {  // a reflection between the two wedges
+    if (rho < a.nrx) diffract_mid(a, sq, rho, k, lam, ovf, st);
+    return;
+  }
   const int w[3] = {sq.y, sq.z, sq.w};
   const bool first = sq.x >= a.dntx, last = rho >= a.nrx;  // a reflection before / after the chain
   if (first && last) return;
@@ -2934,6 +3294,10 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
       cudaMemsetAsync(a.drel, 0, sizeof(unsigned) * (((size_t)a.nw * a.nw + 31) / 32), st);
       k_diff_rel<<<(int)std::max<long>(std::min<long>(((long)a.nw * a.nw + 255) / 256, 8L * sms), 1), 256, 0, st>>>(b);
       k_diff_pairs<<<(int)std::max<long>(std::min<long>((tp + 255) / 256, 8L * sms), 1), 256, 0, st>>>(b, nsrc);
+      if (a.dmid && a.rplanes && a.nrp > 0) {
+        long nblk = (long)b.dntx * a.nw * a.nrp;
+        k_diff_mid_pairs<<<(int)std::max<long>(std::min<long>((nblk + 7) / 8, 8L * sms), 1), 256, 0, st>>>(b);
+      }
       if (a.diff_order >= 3) k_diff_triples<<<8 * sms, 256, 0, st>>>(b);
       k_diff_multi_pre<<<8 * sms, 256, 256 * kStackTrace * sizeof(int), st>>>(b);
     }

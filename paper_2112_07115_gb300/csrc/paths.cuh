@@ -66,8 +66,10 @@ struct PathArgs {
   const int* rmembers;
   int nrp;
   int drefl2;                     // 1: also two reflections around a first-order diffraction
+  int dmid;                       // 1: also a reflection between the two wedges of an order-2 chain
   // diffraction of order 2 and 3 (diff_order <= 1: off): the wedge pairs
-  // (v, w1, w2, -1) and triples (v, w1, w2, w3) of the frame, v a source
+  // (v, w1, w2, -1), the pairs with a reflection on plane p between them
+  // (t, w1, w2, -2 - p) and triples (v, w1, w2, w3) of the frame, v a source
   // (a transmitter, or with reflector planes the image of transmitter t in
   // plane p: v = dntx + t * nrpr + p), and the pair relation as a bit matrix
   // (nw x nw bits)

@@ -574,7 +574,8 @@ class Scene:
     def set_diffraction_reflections(self, on: int = 1) -> int:
         """With diffraction on: reflections on static reflector planes around
         the diffraction, up to ``on`` (0-2; True is 1) around a first-order
-        one, one before or after a chain; returns the reflector-plane count."""
+        one, one before or after a chain; 3 adds one between the two wedges
+        of an order-2 chain. Returns the reflector-plane count."""
         n = C.c_int32(0)
         _check(lib().dcem_scene_set_diffraction_reflections(self.h, int(on), C.byref(n)),
                "dcem_scene_set_diffraction_reflections")

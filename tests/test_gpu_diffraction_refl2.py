@@ -125,7 +125,7 @@ def test_moving_boxes_on_ground(cuda, mode):
 
 def test_levels_and_errors(cuda):
     """on = 1 adds no two-reflection path, on = 2 adds them, on = 0 drops both;
-    outside 0..2 is an argument error."""
+    outside 0..3 is an argument error."""
     torch = cuda
     sc = _ground(_boxes(10))
     s = dcem.Scene.from_scene(sc, stream=torch.cuda.current_stream().cuda_stream)
@@ -138,7 +138,7 @@ def test_levels_and_errors(cuda):
         fr = s.trace(sc.tx, sc.rx[0], prm)
         counts.append(int(_refl2_recs(fr.paths).sum()))
     assert counts[0] == 0 and counts[1] >= 5 and counts[2] == 0
-    for bad in (-1, 3):
+    for bad in (-1, 4):
         with pytest.raises(dcem.DcemError):
             s.set_diffraction_reflections(bad)
     s.close()
@@ -148,9 +148,10 @@ def test_highway_full_size_sampled(cuda):
     """The bench's highway at full size (1M rays, 4 reflections, 200 moving
     receivers, 2400 wedges, the road and barrier faces as 8 reflector
     planes), frame 1 in coherent frames with diffraction up to order 2 and up
-    to two reflections around it: every path of four receivers (the three
-    with the most two-reflection paths and receiver 0) that has a reflection
-    around one or two wedges, evaluated by the oracle for the same ids
+    to two reflections around it or one between two wedges: every path of
+    four receivers (the three with the most two-reflection paths and receiver
+    0) that has a reflection around or between wedges, evaluated by the
+    oracle for the same ids
     (or_diffract_path): valid there too, with the same points, length and
     field. The oracle's own search over every pair of the 2000 static
     triangles and every wedge is too slow at this size; the small scenes
@@ -160,7 +161,7 @@ def test_highway_full_size_sampled(cuda):
     s = dcem.Scene.from_scene(hw, stream=torch.cuda.current_stream().cuda_stream)
     s.set_rays(scenes.fibonacci_sphere(hw.n_rays))
     assert s.set_diffraction(True) == 2400
-    assert s.set_diffraction_reflections(2) == 8
+    assert s.set_diffraction_reflections(3) == 8
     s.set_diffraction_order(2)
     prm = P.gpu_params(hw, max_refl=4, mode=dcem.MODE_COHERENT)
     for f in (0, 1):
@@ -190,8 +191,8 @@ def test_highway_full_size_sampled(cuda):
         kinds.add(tuple(bool(x & dcem.TRI_DIFFRACT) for x in ids))
         checked += 1
     s.close()
-    # two reflections (both before, one on each side, both after) and one
-    # reflection around one and two wedges
+    # two reflections (both before, one on each side, both after), one
+    # reflection around one and two wedges, one between two
     assert checked >= 10 and len(kinds) >= 5, (checked, kinds)
 
 
