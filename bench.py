@@ -1156,7 +1156,9 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
     with one reflection before or after each chain (the ground and every
     building face as reflector planes), and first order with up to two
     reflections around it; the highway frames with order 2, and with first
-    order and up to two reflections around it; the
+    order and up to two reflections around it; both workloads up to order 2
+    with every combination of reflections (around a first-order diffraction,
+    before or after a chain, between its two wedges); the
     pre-test candidates and wedge pairs/triples per frame, and order 2 on 8
     of the city's receivers against the oracle."""
     import torch
@@ -1205,6 +1207,11 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
             sel = (p["depth"] == 3) & (nd == 1)
             at = [int((sel & ((t3[:, i] & dcem.TRI_DIFFRACT) != 0)).sum()) for i in range(3)]
             out["with_two_reflections"] = {"both_before": at[2], "one_each_side": at[1], "both_after": at[0]}
+        if refl >= 3:
+            t3 = p["tri"][:, :3]
+            dd = (t3 >= 0) & ((t3 & dcem.TRI_DIFFRACT) != 0)
+            out["with_a_reflection_between_two_wedges"] = int(((p["depth"] == 3) & dd[:, 0] & ~dd[:, 1] &
+                                                                dd[:, 2]).sum())
         return out, fr
 
     out = {"city_workload": "8 x 8 box buildings (642 triangles, 512 wedges), 1 Tx at 10 m, 64 Rx at 1.5 m, "
@@ -1219,10 +1226,14 @@ def run_diffraction_orders(args, hw, stream, dev, world, flush, warmup=2, K=8):
     out["city_order_2_with_reflections"] = r
     r, _ = frames(city, 1, 200_000, 3, dcem.MODE_FULL, refl=2)
     out["city_order_1_with_two_reflections"] = r
+    r, _ = frames(city, 2, 200_000, 3, dcem.MODE_FULL, refl=3)
+    out["city_order_2_with_reflections_around_and_between"] = r
     r, _ = frames(hw, 2, hw.n_rays, hw.max_refl, dcem.MODE_COHERENT)
     out["highway_order_2"] = r
     r, _ = frames(hw, 1, hw.n_rays, hw.max_refl, dcem.MODE_COHERENT, refl=2)
     out["highway_order_1_with_two_reflections"] = r
+    r, _ = frames(hw, 2, hw.n_rays, hw.max_refl, dcem.MODE_COHERENT, refl=3)
+    out["highway_order_2_with_reflections_around_and_between"] = r
     # order 2 against the oracle on 8 receivers of the city (the oracle is brute force)
     sub = city.rx[0][:8]
     prm = O.OracleParams(freq_hz=city.freq_hz, max_refl=3)
