@@ -132,3 +132,59 @@ def test_level_three_needs_order_two(cuda):
     with pytest.raises(dcem.DcemError):
         s.set_diffraction_reflections(4)
     s.close()
+
+
+def test_links_and_batch_equal_single_frames(cuda):
+    """Two transmitters in one frame, and a batch of two scenes, with every
+    combination of reflections up to order 2: each link (scene) equals its own
+    single frame bit for bit, paths with a reflection between two wedges
+    among them."""
+    torch = cuda
+    st = torch.cuda.current_stream().cuda_stream
+    rays = scenes.fibonacci_sphere(20_000)
+
+    def make(sc, sets=1):
+        s = dcem.Scene.from_scene(sc, stream=st)
+        if sets > 1:
+            s.set_ray_sets([rays] * sets)
+        else:
+            s.set_rays(rays)
+        s.set_diffraction(True)
+        s.set_diffraction_reflections(3)
+        s.set_diffraction_order(2)
+        return s
+    sc = _ground(_boxes(10))
+    prm = P.gpu_params(sc, max_refl=4)
+    tx2 = sc.tx + np.array([6.0, -9.0, 1.0], np.float32)
+    sl, one = make(sc, 2), make(sc)
+    fl = sl.trace_links(np.stack([sc.tx, tx2]), sc.rx[0], prm)
+    n = 0
+    for t, tx in enumerate((sc.tx, tx2)):
+        single = one.trace(tx, sc.rx[0], prm)
+        p = fl.paths[fl.paths["tx"] == t].copy()
+        p["tx"] = 0
+        p["ray"] = np.where(p["ray"] >= 0, p["ray"] - t * rays.shape[0], -1)
+        assert p.tobytes() == single.paths.tobytes(), t
+        assert np.array_equal(fl.p_coh_dbm[t], single.p_coh_dbm)
+        n += int(_mid_recs(single.paths).sum())
+    assert n >= 5
+    for s in (sl, one):
+        s.close()
+    wl = [_ground(_boxes(10, n_frames=2)), _ground(_boxes(6, n_moving=2, n_frames=2))]
+    batched, alone = [make(w) for w in wl], [make(w) for w in wl]
+    b = dcem.Batch(batched, stream=st)
+    prm = dcem.default_params(max_refl=4, freq_hz=28e9, mode=dcem.MODE_COHERENT)
+    n = 0
+    for f in range(2):
+        b.update_transforms([w.xf[f] if w.nobj else None for w in wl])
+        got = b.trace([w.tx[None] for w in wl], [w.rx[f] for w in wl], prm)
+        for w, s, g in zip(wl, alone, got):
+            if w.nobj:
+                s.update_transforms(w.xf[f])
+            ref = s.trace_links(w.tx[None], w.rx[f], prm)
+            assert g.paths.tobytes() == ref.paths.tobytes(), (f, w.nobj)
+            n += int(_mid_recs(ref.paths).sum())
+    assert n >= 10
+    b.close()
+    for s in batched + alone:
+        s.close()
