@@ -2155,6 +2155,16 @@ __device__ __forceinline__ bool multi_stage2(const PathArgs& a, long idx, long n
         if (Xp.x < Pl.box[0] - mb || Xp.y < Pl.box[1] - mb || Xp.z < Pl.box[2] - mb ||
             Xp.x > Pl.box[3] + mb || Xp.y > Pl.box[4] + mb || Xp.z > Pl.box[5] + mb)
           keep = false;
+        if (keep) {  // the two real legs through the reflection point (its own crossing is at their end)
+          const float4 ev = src_img ? a.txs[(sq.x - a.dntx) / a.nrpr] : a.rx[(rho - a.nrx) / a.nrpr];
+          const float3 E = f3(ev.x, ev.y, ev.z);        // the real transmitter or receiver
+          const float3 Qn = src_img ? X[1] : X[m];     // the diffraction point next to the reflection
+          const Wedge& Wn = a.wedges[src_img ? w[0] : w[m - 1]];
+          const float3 d1 = f3(Xp.x - E.x, Xp.y - E.y, Xp.z - E.z), d2 = f3(Qn.x - Xp.x, Qn.y - Xp.y, Qn.z - Xp.z);
+          if (leg_surely_blocked(a.bvh, E, d1, delta, a.eps_occ, -1, -1, -1, -1, st) ||
+              leg_surely_blocked(a.bvh, Xp, d2, delta, a.eps_occ, -1, -1, Wn.ta, Wn.tb, st))
+            keep = false;
+        }
       }
     }
   }
