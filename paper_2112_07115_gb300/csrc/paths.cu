@@ -1374,6 +1374,10 @@ __device__ __forceinline__ float2 wedge_plane(const WedgeF& W, float3 X, float& 
   dist = sqrtf(fdot3(d, d));
   return make_float2(fdot3(q, W.t0), fdot3(q, W.y0));
 }
+// The point at parameter t along the edge.
+__device__ __forceinline__ float3 edge_point(const WedgeF& W, float t) {
+  return f3(W.p0.x + W.e.x * t, W.p0.y + W.e.y * t, W.p0.z + W.e.z * t);
+}
 // The edge's end points.
 __device__ __forceinline__ void edge_ends(const WedgeF& W, float3& A, float3& B) {
   A = W.p0;
@@ -1449,6 +1453,81 @@ __device__ __forceinline__ bool shadow_meets(const WedgeF& W, float3 X, float3 P
   float lo = a < pi ? a + pi : 0.0f, hi = a < pi ? W.npi : a - pi;
   if (hi < lo - tol) return false;
   return sector_meets(W, lo, hi, tol, m, P, Q);
+}
+
+// Keller points from the convexity of the unfolded length. The length of a
+// chain is a sum of distances between affine functions of the edge
+// parameters, so it is convex in them jointly and its derivative along one
+// edge, e.(Q - A)/|Q - A| + e.(Q - B)/|Q - B| for Q's neighbours A and B,
+// does not decrease as Q moves along the edge. When that derivative is
+// positive at the edge's start (less a margin) for every position of the
+// neighbours on their edges, or negative at its end, the minimum -- the
+// Keller points -- has Q, or a neighbour, off its edge, and the exact stage
+// rejects the chain. The tests below bound the derivative's two terms.
+
+// Extremes of e.(Q - Y)/|Q - Y| for Y on wedge S's edge with parameter in
+// [lo, hi], and a lower bound of |Q - Y| there. The directions from Q to the
+// segment's points sweep an arc of a great circle (below pi), along which
+// the cosine is |e_p| cos(angle to e_p), e_p the projection of e onto the
+// arc's plane: the extremes are at the arc's ends, or +-|e_p| where e_p (or
+// -e_p) points into the arc.
+__device__ __forceinline__ void cos_over_edge(float3 e, float3 Q, const WedgeF& S, float lo, float hi, float& cmin,
+                                              float& cmax, float& dmin) {
+  const float3 d0 = f3(Q.x - S.p0.x - S.e.x * lo, Q.y - S.p0.y - S.e.y * lo, Q.z - S.p0.z - S.e.z * lo);
+  const float3 d1 = f3(Q.x - S.p0.x - S.e.x * hi, Q.y - S.p0.y - S.e.y * hi, Q.z - S.p0.z - S.e.z * hi);
+  const float l0 = sqrtf(fdot3(d0, d0)), l1 = sqrtf(fdot3(d1, d1));
+  const float c0 = fdot3(e, d0) / l0, c1 = fdot3(e, d1) / l1;
+  cmin = fminf(c0, c1);
+  cmax = fmaxf(c0, c1);
+  const float3 n = cross3(d0, d1);
+  const float nn = sqrtf(fdot3(n, n));
+  dmin = fminf(fminf(l0, l1), nn / (hi - lo));  // the distance to the segment's line at most
+  if (nn > 1e-3f * l0 * l1) {
+    const float3 u = f3(n.x / nn, n.y / nn, n.z / nn);
+    const float en = fdot3(e, u), pn = sqrtf(fmaxf(0.0f, 1.0f - en * en));
+    const float3 ep = f3(e.x - en * u.x, e.y - en * u.y, e.z - en * u.z);
+    // e_p between the arc's ends (with a tolerance that only widens the range)
+    const float s0 = fdot3(ep, cross3(u, d0)), s1 = fdot3(ep, cross3(d1, u));
+    const float g0 = 1e-3f * l0, g1 = 1e-3f * l1;
+    if (s0 >= -g0 && s1 >= -g1) cmax = fmaxf(cmax, pn);
+    if (s0 <= g0 && s1 <= g1) cmin = fminf(cmin, -pn);
+  } else {  // an arc shorter than 1e-3 rad (or Q on the segment: dmin tells)
+    cmin -= 2e-3f;
+    cmax += 2e-3f;
+  }
+}
+// Could the Keller point on wedge W's edge lie within m of the edge, its
+// neighbours being point F (has_f) or a point of wedge S1's edge, and a
+// point of wedge S2's edge, both edges widened by m? False only when the
+// derivative's bound keeps its sign at both ends by more than its FP32
+// rounding (1e-6 of the coordinates' size over the distance, per term).
+__device__ bool keller_on_edge(const WedgeF& W, bool has_f, float3 F, const WedgeF& S1, const WedgeF& S2, float m) {
+  for (int q = 0; q < 2; ++q) {
+    const float t = q ? W.len + m : -m;
+    const float3 Q = edge_point(W, t);
+    const float sq = fabsf(Q.x) + fabsf(Q.y) + fabsf(Q.z);
+    float lo1, hi1, d1, lo2, hi2, d2, s1;
+    if (has_f) {
+      const float3 d = f3(Q.x - F.x, Q.y - F.y, Q.z - F.z);
+      d1 = sqrtf(fdot3(d, d));
+      lo1 = hi1 = fdot3(W.e, d) / d1;
+      s1 = fabsf(F.x) + fabsf(F.y) + fabsf(F.z);
+    } else {
+      cos_over_edge(W.e, Q, S1, -m, S1.len + m, lo1, hi1, d1);
+      s1 = fabsf(S1.p0.x) + fabsf(S1.p0.y) + fabsf(S1.p0.z) + S1.len;
+    }
+    cos_over_edge(W.e, Q, S2, -m, S2.len + m, lo2, hi2, d2);
+    const float s2 = fabsf(S2.p0.x) + fabsf(S2.p0.y) + fabsf(S2.p0.z) + S2.len;
+    if (!(d1 > 4.0f * m && d2 > 4.0f * m)) return true;
+    const float err = 4e-5f + 2e-6f * ((sq + s1) / d1 + (sq + s2) / d2);
+    if (q == 0 && lo1 + lo2 > err) return false;
+    if (q == 1 && hi1 + hi2 < -err) return false;
+  }
+  return true;
+}
+// The margin of these tests: 5 cm plus 1e-5 of the coordinates' size.
+__device__ __forceinline__ float keller_margin(const WedgeF& W, float3 F) {
+  return 0.05f + 1e-5f * (fabsf(W.p0.x) + fabsf(W.p0.y) + fabsf(W.p0.z) + W.len + fabsf(F.x) + fabsf(F.y) + fabsf(F.z));
 }
 
 // Do two edges share an end vertex (identical coordinates)? Consecutive
@@ -1584,8 +1663,9 @@ __global__ void __launch_bounds__(256) k_diff_rel(PathArgs a) {
 
 // Ordered pairs (w1, w2) per source (transmitter or transmitter image) that
 // can start a path of order >= 2: in the relation (k_diff_rel), the
-// transmitter outside w1, and some point of edge 2 beyond the incident
-// shadow boundary of the transmitter at w1.
+// transmitter outside w1, some point of edge 2 beyond the incident shadow
+// boundary of the transmitter at w1, and a Keller point on w1 possible
+// between the transmitter and edge 2 (keller_on_edge).
 __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int nsrc) {
   const long nw = a.nw, total = (long)nsrc * nw * nw;
   const int lane = threadIdx.x & 31;
@@ -1603,7 +1683,7 @@ __global__ void __launch_bounds__(256) k_diff_pairs(PathArgs a, int nsrc) {
         const WedgeF fa = a.wf[w1], fb = a.wf[w2];
         float3 T = chain_source32(a, t), P, Q;
         edge_ends(fb, P, Q);
-        keep = !surely_inside(fa, T) && shadow_meets(fa, T, P, Q);
+        keep = !surely_inside(fa, T) && shadow_meets(fa, T, P, Q) && keller_on_edge(fa, true, T, fb, fb, keller_margin(fa, T));
         if (keep && t >= a.dntx) {  // the image's leg to edge 1 crosses its plane inside the box
           float3 A1, B1;
           edge_ends(fa, A1, B1);
@@ -1726,8 +1806,9 @@ __device__ __forceinline__ bool section_reachable(const RPlane& Pl, float3 A0, f
 // chain over w1 and w2's image in the plane; the pair is kept when that
 // image and w1 satisfy the pair tests of k_diff_pairs (each partly in the
 // other's exterior, some point of the image beyond the transmitter's shadow
-// boundary at w1, the transmitter outside w1) and some leg between the two
-// edges can cross the plane inside its box. Entries (t, w1, w2, -2 - p) join
+// boundary at w1, the transmitter outside w1, a Keller point on w1
+// possible) and some leg between the two edges can cross the plane inside
+// its box. Entries (t, w1, w2, -2 - p) join
 // the pair list (k_diff_triples skips them); the FP64 vertex, line and
 // face-plane rules are the exact stage's.
 __global__ void __launch_bounds__(256) k_diff_mid_pairs(PathArgs a) {
@@ -1756,7 +1837,7 @@ __global__ void __launch_bounds__(256) k_diff_mid_pairs(PathArgs a) {
         keep = edge_sees(fa, fb, m) && edge_sees(fb, fa, m) && shadow_meets(fa, T, B0, B1);
         if (keep) {
           const float mg = 0.1f + 1e-4f * (fabsf(A0.x) + fabsf(A0.y) + fabsf(A0.z) + fa.len + fb.len);
-          keep = section_reachable(Pl, A0, A1, B0, B1, mg);
+          keep = section_reachable(Pl, A0, A1, B0, B1, mg) && keller_on_edge(fa, true, T, fb, fb, keller_margin(fa, T));
         }
         if (keep) {  // the exact stage's FP64 rules on the group plane's image
           const Wedge &A = a.wedges[w1], &B = a.wedges[w2];
@@ -1779,7 +1860,8 @@ __global__ void __launch_bounds__(256) k_diff_mid_pairs(PathArgs a) {
   }
 }
 
-// Triples (w1, w2, w3) from the pairs: (w2, w3) in the relation, w3 not w1.
+// Triples (w1, w2, w3) from the pairs: (w2, w3) in the relation, w3 not w1,
+// and a Keller point on w2 possible between edges 1 and 3 (keller_on_edge).
 __global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
   const long nw = a.nw;
   const long np = (long)min(a.ctr->n_dpair, a.dseq2_cap), total = np * nw;
@@ -1796,6 +1878,10 @@ __global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
       pr = a.dseq2[p];
       size_t bit = (size_t)pr.z * nw + w3;
       keep = pr.w == -1 && w3 != pr.y && ((a.drel[bit >> 5] >> (bit & 31)) & 1u);
+      if (keep) {  // the Keller point on the middle edge between the other two
+        const WedgeF f2 = a.wf[pr.z];
+        keep = keller_on_edge(f2, false, f2.p0, a.wf[pr.y], a.wf[w3], keller_margin(f2, f2.p0));
+      }
     }
     unsigned mk = __ballot_sync(0xffffffffu, keep);
     if (!mk) continue;
@@ -1813,9 +1899,6 @@ __global__ void __launch_bounds__(256) k_diff_triples(PathArgs a) {
 // as in keller_chain, in FP32, from the edges' midpoints. Returns true when
 // the cosine mismatch fell below 2e-6 at every edge, or a full Newton step
 // would move no point by more than step_tol (metres).
-__device__ __forceinline__ float3 edge_point(const WedgeF& W, float t) {
-  return f3(W.p0.x + W.e.x * t, W.p0.y + W.e.y * t, W.p0.z + W.e.z * t);
-}
 __device__ __forceinline__ float chain_len32(const WedgeF* W, int m, float3 T, float3 R, const float* t) {
   float3 prev = T;
   float L = 0.0f;
@@ -2029,9 +2112,10 @@ __device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float
 // receivers, and with reflector planes their images (rho = nrx + r * nrpr
 // + p) for sequences from a real transmitter; a chain has one reflection.
 // Stage 1 of k_diff_multi_pre for sequence sq and observer rho: the
-// observer outside the last wedge and some point of the previous edge beyond
-// its shadow boundary there; an image observer's leg from the last edge must
-// be able to cross its plane inside the box.
+// observer outside the last wedge, some point of the previous edge beyond
+// its shadow boundary there, and a Keller point on the last edge possible
+// between the previous edge and the observer; an image observer's leg from
+// the last edge must be able to cross its plane inside the box.
 __device__ __forceinline__ bool multi_stage1(const PathArgs& a, int4 sq, bool three, int rho) {
   if (!three && sq.w <= -2) {  // a reflection between the wedges: w2 and the receiver mirrored
     const RPlane& Pl = a.rplanes[-2 - sq.w];
@@ -2040,14 +2124,14 @@ __device__ __forceinline__ bool multi_stage1(const PathArgs& a, int4 sq, bool th
     const float3 R = mirror32(chain_observer32(a, rho), n, Pl.cf);
     float3 P, Q;
     edge_ends(fp, P, Q);
-    return !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+    return !surely_inside(fl, R) && shadow_meets(fl, R, P, Q) && keller_on_edge(fl, true, R, fp, fp, keller_margin(fl, R));
   }
   const bool obs_img = rho >= a.nrx;
   const int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
   const WedgeF fl = a.wf[wl], fp = a.wf[wp];
   float3 R = chain_observer32(a, rho), P, Q;
   edge_ends(fp, P, Q);
-  bool keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q);
+  bool keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q) && keller_on_edge(fl, true, R, fp, fp, keller_margin(fl, R));
   if (keep && obs_img) {  // the leg from the last edge to the image crosses its plane inside the box
     float3 A1, B1;
     edge_ends(fl, A1, B1);

@@ -20,7 +20,7 @@ def main(argv=None):
     ap.add_argument("--rays", type=int, default=0, help="ray count (0: the workload's own)")
     ap.add_argument("--diffraction-order", type=int, default=0, help="0: no diffraction, else 1-3")
     ap.add_argument("--diffraction-reflections", type=int, default=0,
-                    help="with diffraction: reflections around it (0-2)")
+                    help="with diffraction: reflections around it (0-3)")
     args = ap.parse_args(argv)
 
     import torch
