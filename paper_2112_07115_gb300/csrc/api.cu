@@ -250,9 +250,12 @@ struct dcem_scene {
   bool diffraction = false;
   unsigned long long* dsurv = nullptr;  // diffraction: pre-test survivor list
   RPlane* rplanes = nullptr;   // diffraction combined with a reflection: reflector planes
-  int* rmembers = nullptr;     // ... and their triangle ids
+  int* rmembers = nullptr;     // ... their triangle ids and sort keys
+  float* rkeys = nullptr;
   int nrp = 0;
   int diff_refl = 0;               // reflections with diffraction (0..3, see the header)
+  unsigned* rmask = nullptr;   // two reflections: the pre-test's wedge masks, and their words
+  size_t rmask_cap = 0;
   unsigned dsurv_cap = 0;
   int diff_order = 1;          // diffraction: most wedges on one path (1-3)
   int4* dseq2 = nullptr;       // ... the frame's wedge pairs and triples, the pair relation
@@ -395,7 +398,7 @@ void scene_free(dcem_scene* s) {
   dfree(s->q4_kid); dfree(s->q4_src); dfree(s->q4_count); dfree(s->q4_roots); dfree(s->q4_scr); dfree(s->leaf_parent); dfree(s->arrive);
   dfree(s->dsched); dfree(s->dlvl); dfree(s->tri_obj_d); dfree(s->wedges); dfree(s->wedgesf); dfree(s->wtopo);
   dfree(s->wperm); dfree(s->wcbox); dfree(s->dsurv);
-  dfree(s->rplanes); dfree(s->rmembers);
+  dfree(s->rplanes); dfree(s->rmembers); dfree(s->rkeys); dfree(s->rmask);
   dfree(s->dseq2); dfree(s->dseq3); dfree(s->drel);
   dfree(s->g_items); dfree(s->g_param); dfree(s->g_out); dfree(s->g_err); dfree(s->g_paths);
   dfree(s->g_rx); dfree(s->g_theta);
@@ -632,6 +635,20 @@ int ensure_rx(dcem_scene* s, int nrx, int nlinks, int bucket_cap) {
   return DCEM_OK;
 }
 
+// The wedge masks of the two-reflection pre-test (k_refl2_masks): one word
+// per (end point: ntx transmitters and nrx receivers, reflector plane or
+// none, wedge cluster).
+static int ensure_rmask(dcem_scene* s, int ntx, int nrx) {
+  if (!(s->diffraction && s->nw > 0 && s->diff_refl >= 2 && s->nrp > 0)) return DCEM_OK;
+  const size_t need = (size_t)(ntx + nrx) * (size_t)(s->nrp + 1) * (size_t)s->nwc;
+  if (s->rmask && need <= s->rmask_cap) return DCEM_OK;
+  if (need > ((size_t)1 << 31)) return DCEM_ERR_CAPACITY;
+  dfree(s->rmask);
+  CK(dalloc(&s->rmask, std::max<size_t>(need, 1)));
+  s->rmask_cap = std::max<size_t>(need, 1);
+  return DCEM_OK;
+}
+
 // Wedges for first-order diffraction: edges whose two end vertices
 // (bit-identical input coordinates: world space for static triangles, object
 // space for moving ones, which a rigid transform maps alike) belong to
@@ -751,8 +768,11 @@ std::vector<int> wedge_order(const std::vector<float>& tris, const std::vector<i
 // Reflector planes: the static triangles grouped by plane (unit normal
 // oriented with its first nonzero component positive, offset c = n . v0),
 // planes equal when the normals agree to 1e-7 and the offsets to 1e-4 m.
+// Each plane's members are sorted by their lowest coordinate along the
+// longest side of the plane's box (keys: that coordinate), ties by id, so
+// that the member holding a point is found by a binary search.
 void group_planes(const std::vector<float>& tris, const std::vector<int>& tri_obj, std::vector<RPlane>& planes,
-                  std::vector<int>& members) {
+                  std::vector<int>& members, std::vector<float>& keys) {
   struct Item {
     double n[3], c;
     int id;
@@ -806,13 +826,29 @@ void group_planes(const std::vector<float>& tris, const std::vector<int>& tri_ob
       p.box[k + 3] = -3.4e38f;
     }
     for (size_t q = i; q < j; ++q) {
-      members.push_back(it[q].id);
       const float* v = &tris[9 * (size_t)it[q].id];
       for (int c = 0; c < 3; ++c)
         for (int k = 0; k < 3; ++k) {
           p.box[k] = std::min(p.box[k], v[3 * c + k]);
           p.box[k + 3] = std::max(p.box[k + 3], v[3 * c + k]);
         }
+    }
+    p.axis = 0;
+    for (int k = 1; k < 3; ++k)
+      if (p.box[k + 3] - p.box[k] > p.box[p.axis + 3] - p.box[p.axis]) p.axis = k;
+    std::vector<std::pair<float, int>> sm;  // (lowest coordinate along the axis, id)
+    p.ext = 0.0f;
+    for (size_t q = i; q < j; ++q) {
+      const float* v = &tris[9 * (size_t)it[q].id];
+      const float lo = std::min(v[p.axis], std::min(v[3 + p.axis], v[6 + p.axis]));
+      const float hi = std::max(v[p.axis], std::max(v[3 + p.axis], v[6 + p.axis]));
+      p.ext = std::max(p.ext, hi - lo);
+      sm.push_back({lo, it[q].id});
+    }
+    std::sort(sm.begin(), sm.end());
+    for (const auto& e : sm) {
+      members.push_back(e.second);
+      keys.push_back(e.first);
     }
     planes.push_back(p);
     i = j;
@@ -1296,13 +1332,16 @@ int dcem_scene_set_diffraction_reflections(dcem_scene* s, int32_t on, int32_t* n
   if (on && !s->rplanes) {
     std::vector<RPlane> planes;
     std::vector<int> members;
-    group_planes(s->tris_h, s->tri_obj_h, planes, members);
+    std::vector<float> keys;
+    group_planes(s->tris_h, s->tri_obj_h, planes, members, keys);
     s->nrp = (int)planes.size();
     if (s->nrp) {
       CK(dalloc(&s->rplanes, planes.size()));
       CK(dalloc(&s->rmembers, members.size()));
+      CK(dalloc(&s->rkeys, keys.size()));
       CK(cudaMemcpy(s->rplanes, planes.data(), sizeof(RPlane) * planes.size(), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(s->rmembers, members.data(), sizeof(int) * members.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(s->rkeys, keys.data(), sizeof(float) * keys.size(), cudaMemcpyHostToDevice));
     }
   }
   s->diff_refl = on;
@@ -1580,8 +1619,10 @@ static void make_plan(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   q.dseq3_cap = dord >= 3 ? s->dseq3_cap : 0;
   q.drel = dord >= 2 ? s->drel : nullptr;
   q.rmembers = dr ? s->rmembers : nullptr;
+  q.rkeys = dr ? s->rkeys : nullptr;
   q.nrp = dr ? s->nrp : 0;
   q.drefl2 = dr && s->diff_refl >= 2 ? 1 : 0;
+  q.rmask = q.drefl2 ? s->rmask : nullptr;
   q.dmid = dr && s->diff_refl >= 3 && dord >= 2 ? 1 : 0;
   // sticky mode: the previous frame's kept paths (when the cache is valid),
   // and this frame's
@@ -1759,6 +1800,19 @@ static int capture_frame(dcem_scene* s, const FramePlan& P, FrameGraph& G) {
 // A plan is captured the second time it is seen in a row (the first run also
 // sets every kernel's launch attributes), then replayed. Returns whether the
 // graph is ready (G.exec and G.graph).
+// The kernels launch_diffract runs in a frame of plan P.
+static int diffraction_launches(const FramePlan& P) {
+  const PathArgs& q = P.q;
+  if (!q.wedges) return 0;
+  int n = 1 + (q.drefl2 && q.rplanes ? 1 : 0);  // wedge geometry, cluster boxes
+  if (P.nlinks > 0) {
+    n += 2;  // first-order pre-test, exact stage
+    if (q.rplanes) n += 1 + (q.drefl2 ? 2 : 0);  // one reflection; wedge masks, two reflections
+    if (q.diff_order >= 2 && q.nw > 1)  // relation, pairs, [pairs around a plane], [triples], chains
+      n += q.diff_order + 1 + (q.dmid ? 1 : 0);
+  }
+  return n;
+}
 static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coherent, const dcem_result* out,
                       bool* ready) {
   FramePlan& P = s->plan;
@@ -1768,9 +1822,7 @@ static int plan_frame(dcem_scene* s, int nrx, const dcem_params* p, bool coheren
   s->launches += 2 + (coherent ? 2 : 0) + (s->R > 0 ? 2 + P.a.max_trans : 0) + 5 + (nrx > 0 ? 1 : 0) +
                  (P.q.vc_next_key ? 1 : 0) +
                  (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) + (P.q.sticky_prev ? 1 : 0) +
-                 (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
-                 (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
-                 (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 + (P.q.dmid ? 1 : 0) : 0);
+                 diffraction_launches(P);
   s->graph_replayed = 0;
   FrameGraph& G = s->fgraph[s->cur];
   bool same = G.have_key && std::memcmp(&G.key, &P, sizeof(P)) == 0;
@@ -1854,6 +1906,7 @@ static int frame_begin(dcem_scene* s, const float* tx, int32_t ntx, const float*
   if ((rc = ensure_paths(s, want_c, want_u)) != DCEM_OK) return rc;
   const int nlinks = ntx * nrx;
   if ((rc = ensure_rx(s, nrx, nlinks, s->bucket_cap)) != DCEM_OK) return rc;
+  if ((rc = ensure_rmask(s, ntx, nrx)) != DCEM_OK) return rc;
   cudaStream_t st = s->st;
   for (int t = 0; t < ntx; ++t)
     s->txs_h[t] = make_float4(tx[3 * t], tx[3 * t + 1], tx[3 * t + 2], alpha_eff_of(s->set_rays_h[t], p));
@@ -2300,9 +2353,7 @@ int dcem_batch_trace(dcem_batch* b, const float* const* tx, const int32_t* ntx, 
       s->last_use_q = 3;  // every scene's rays in one launch
       s->launches += 2 + (coh[i] ? 2 : 0) + (s->R > 0 ? 1 : 0) + 5 + (nrx[i] > 0 ? 1 : 0) +
                      (P.q.vc_next_key ? 1 : 0) + (P.use_q ? 1 : 0) + (P.q.link_off ? 1 : 0) +
-                     (P.q.sticky_prev ? 1 : 0) + (P.q.wedges ? 1 + (P.nlinks > 0 ? 1 : 0) : 0) +
-                     (P.q.rplanes && P.nlinks > 0 ? 1 + (P.q.drefl2 ? 1 : 0) : 0) +
-                     (P.nlinks > 0 && P.q.diff_order >= 2 ? P.q.diff_order + 1 + (P.q.dmid ? 1 : 0) : 0) + (i == 0 ? 1 : 0);
+                     (P.q.sticky_prev ? 1 : 0) + diffraction_launches(P) + (i == 0 ? 1 : 0);
       s->graph_replayed = 0;
       b->h_tab[i] = frame_trace_args(P);
     }

@@ -42,7 +42,9 @@ struct RPlane {
   double n[3], c;
   float nf[3], cf;  // n and c rounded to FP32 (for the pre-tests)
   float box[6];
-  int first, count;
+  int first, count;  // members first .. first + count - 1, sorted by their lowest coordinate along `axis`
+  int axis;          // the box's longest side
+  float ext;         // the members' largest extent along it
 };
 
 // A wedge's frame rounded to FP32 for the pre-tests (written with the FP64

@@ -1193,6 +1193,48 @@ __device__ __forceinline__ bool inside_tri64(d3w v0, d3w v1, d3w v2, d3w x) {
            dotw(crossw(v0 - v2, x - v2), n) < 0.0);
 }
 
+// The member triangle of plane G holding point x (on G's plane), none of the
+// nex ids in ex: the lowest id among the members whose box holds x
+// (tri_box_near) and that contain it (inside_tri64) -- the one a scan of the
+// members in id order finds first -- with its vertices and material; -1 when
+// there is none. The members are sorted by their lowest coordinate along G's
+// axis, so only those with that coordinate in [u - 2 m - ext, u + 2 m] can
+// pass the box test (u: x's coordinate, m: the test's margin, ext: the
+// members' largest extent along the axis): a binary search, then a scan of
+// that range.
+__device__ int member_at(const PathArgs& a, const RPlane& G, d3w x, const int* ex, int nex, d3w& v0, d3w& v1,
+                         d3w& v2, float4& mat) {
+  const float X = (float)x.x, Y = (float)x.y, Z = (float)x.z;
+  const float m = 1e-3f + 1e-6f * (fabsf(X) + fabsf(Y) + fabsf(Z));
+  const float u = G.axis == 0 ? X : (G.axis == 1 ? Y : Z);
+  const float hi = u + 2.0f * m, lo = u - 2.0f * m - G.ext * (1.0f + 1e-6f);
+  int l = G.first, r = G.first + G.count;  // the first member whose key exceeds hi
+  while (l < r) {
+    const int mid = (l + r) >> 1;
+    if (a.rkeys[mid] <= hi) l = mid + 1;
+    else r = mid;
+  }
+  int best = -1;
+  for (int k = l - 1; k >= G.first && a.rkeys[k] >= lo; --k) {
+    const int id = a.rmembers[k];
+    if (best >= 0 && id > best) continue;
+    bool skip = false;
+    for (int i = 0; i < nex; ++i) skip = skip || id == ex[i];
+    if (skip || !tri_box_near(a, id, x)) continue;
+    d3w w0, w1, w2;
+    float4 mt;
+    tri64(a, id, w0, w1, w2, mt);
+    if (inside_tri64(w0, w1, w2, x)) {
+      best = id;
+      v0 = w0;
+      v1 = w1;
+      v2 = w2;
+      mat = mt;
+    }
+  }
+  return best;
+}
+
 struct zv3 {
   zd x, y, z;
 };
@@ -1215,15 +1257,10 @@ __device__ __forceinline__ void diffract_refl_pair(const PathArgs& a, unsigned l
   d3w T = D3(txv.x, txv.y, txv.z), R = D3(rxv.x, rxv.y, rxv.z);
   ReflGeom g;
   if (!refl_geometry(W, D3(Pl.n[0], Pl.n[1], Pl.n[2]), Pl.c, T, R, first, g)) return;
-  int j = -1;
   d3w v0, v1, v2;
   float4 mj;
-  for (int q = 0; q < Pl.count && j < 0; ++q) {
-    int id = a.rmembers[Pl.first + q];
-    if (id == W.ta || id == W.tb || !tri_box_near(a, id, g.P)) continue;
-    tri64(a, id, v0, v1, v2, mj);
-    if (inside_tri64(v0, v1, v2, g.P)) j = id;
-  }
+  const int exw[2] = {W.ta, W.tb};
+  const int j = member_at(a, Pl, g.P, exw, 2, v0, v1, v2, mj);
   if (j < 0) return;
   // the member's own plane
   d3w nj = unitw(crossw(v1 - v0, v2 - v0));
@@ -2545,12 +2582,8 @@ __device__ __noinline__ void diffract_mid(const PathArgs& a, int4 sq, int r, dou
     if (!leg_plane(X[1], X[2], n, c, Pp)) return;
     d3w v0, v1, v2;
     if (pass == 0) {  // the member triangle holding P: its own plane next
-      for (int q = 0; q < G.count && j < 0; ++q) {
-        const int id = a.rmembers[G.first + q];
-        if (id == A.ta || id == A.tb || id == B.ta || id == B.tb || !tri_box_near(a, id, Pp)) continue;
-        tri64(a, id, v0, v1, v2, mj);
-        if (inside_tri64(v0, v1, v2, Pp)) j = id;
-      }
+      const int exw[4] = {A.ta, A.tb, B.ta, B.tb};
+      j = member_at(a, G, Pp, exw, 4, v0, v1, v2, mj);
       if (j < 0) return;
       n = unitw(crossw(v1 - v0, v2 - v0));
       c = dotw(n, v0);
@@ -2695,14 +2728,12 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
       if (!leg_plane(first ? X[0] : X[m], first ? X[1] : X[m + 1], n, cg, Pp)) return;
       if (pass == 0) {  // the member triangle holding the point: its own plane next
         d3w v0, v1, v2;
-        for (int q = 0; q < Pg.count && j < 0; ++q) {
-          int id = a.rmembers[Pg.first + q];
-          bool face = false;
-          for (int i = 0; i < m; ++i) face = face || id == E[i]->ta || id == E[i]->tb;
-          if (face || !tri_box_near(a, id, Pp)) continue;
-          tri64(a, id, v0, v1, v2, mj);
-          if (inside_tri64(v0, v1, v2, Pp)) j = id;
+        int exw[6];
+        for (int i = 0; i < m; ++i) {
+          exw[2 * i] = E[i]->ta;
+          exw[2 * i + 1] = E[i]->tb;
         }
+        j = member_at(a, Pg, Pp, exw, 2 * m, v0, v1, v2, mj);
         if (j < 0) return;
         nj = unitw(crossw(v1 - v0, v2 - v0));
         n = nj;
@@ -2903,17 +2934,20 @@ __device__ __forceinline__ int refl_cross32(const RPlane& P, float3 a0, float3 a
 // FP32 pre-test of one candidate: false only when the FP64 test rejects it
 // too. S, O: the source and observer of the diffraction (images); S1: the
 // transmitter's image in P1 (kind 0), O1: the receiver's image in P2 (kind 2).
+// The Keller point's place on the edge and the crossings with the planes
+// there come first, the angle rules (diffract_candidate) last.
 __device__ __forceinline__ bool refl2_candidate(const WedgeF& W, const RPlane& P1, const RPlane& P2, int kind,
                                                 float3 S, float3 S1, float3 O, float3 O1) {
-  if (!diffract_candidate(W, make_float4(S.x, S.y, S.z, 0.0f), make_float4(O.x, O.y, O.z, 0.0f))) return false;
   const float3 e = W.e, p0 = W.p0;
   const float3 dt = f3(S.x - p0.x, S.y - p0.y, S.z - p0.z), dr = f3(O.x - p0.x, O.y - p0.y, O.z - p0.z);
   const float zt = fdot3(dt, e), zr = fdot3(dr, e);
   const float3 pt = f3(dt.x - e.x * zt, dt.y - e.y * zt, dt.z - e.z * zt);
   const float3 pr = f3(dr.x - e.x * zr, dr.y - e.y * zr, dr.z - e.z * zr);
   const float rt = sqrtf(fdot3(pt, pt)), rr = sqrtf(fdot3(pr, pr));
-  if (!(rt > 1e-3f && rr > 1e-3f)) return true;
+  if (!(rt > 1e-3f && rr > 1e-3f)) return true;  // as diffract_candidate: no conclusion
   const float zq = zt + (zr - zt) * rt / (rt + rr);
+  const float mz = 0.05f + 1e-5f * (sqrtf(fdot3(dt, dt)) + sqrtf(fdot3(dr, dr)));
+  if (zq < -mz || zq > W.len + mz) return false;  // the Keller point off the edge (as diffract_candidate)
   const float3 Q = f3(p0.x + e.x * zq, p0.y + e.y * zq, p0.z + e.z * zq);
   const float d = 0.1f;
   float3 X;
@@ -2929,68 +2963,202 @@ __device__ __forceinline__ bool refl2_candidate(const WedgeF& W, const RPlane& P
     if (r == 0) return false;
     if (r == 1 && refl_cross32(P2, X, O1, d, X) == 0) return false;
   }
-  return true;
+  return diffract_candidate(W, make_float4(S.x, S.y, S.z, 0.0f), make_float4(O.x, O.y, O.z, 0.0f));
 }
 
-__global__ void __launch_bounds__(256) k_diffract_refl2_pre(PathArgs a, int nlinks) {
-  const long nblk = 3L * nlinks * a.nrp * a.nrp;
+static_assert(kWedgeCluster == 32, "a wedge cluster is one warp's lanes and one mask word");
+
+// Wedge masks of the two-reflection pre-test, per frame. For every end point
+// X (the transmitters, then the receivers) and plane p, bit i of word
+// (X, p, c) is set when the i-th wedge of cluster c could take part in a
+// path with a reflection on p next to X: X's image in p outside the wedge,
+// and some leg from the image to the edge crossing p inside its box
+// (plane_reachable). Plane index nrp stands for no reflection: X itself
+// outside the wedge. A path with one reflection on each side of the wedge
+// needs its wedge in the transmitter's mask for p1 and the receiver's for
+// p2; one with both reflections on one side, in the other end point's mask
+// for no reflection.
+__global__ void __launch_bounds__(256) k_refl2_masks(PathArgs a, int ntx) {
+  const int np1 = a.nrp + 1;
+  const long nitem = (long)(ntx + a.nrx) * np1 * a.nwc;
   const int lane = threadIdx.x & 31;
   const long nwarp = (long)gridDim.x * (blockDim.x >> 5);
-  for (long b = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nblk; b += nwarp) {
+  for (long it = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitem; it += nwarp) {
+    const int c = (int)(it % a.nwc);
+    const long r = it / a.nwc;
+    const int p = (int)(r % np1), x = (int)(r / np1);
+    const float4 xv = x < ntx ? a.txs[x] : a.rx[x - ntx];
+    float3 X = f3(xv.x, xv.y, xv.z);
+    const int i = c * kWedgeCluster + lane;
+    bool bit = false;
+    if (i < a.nw) {
+      const WedgeF W = a.wf[a.wperm[i]];
+      if (p == a.nrp) {
+        bit = !surely_inside(W, X);
+      } else {
+        const RPlane& Pl = a.rplanes[p];
+        X = mirror32(X, f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]), Pl.cf);
+        float3 A, B;
+        edge_ends(W, A, B);
+        const float mg = 0.1f + 1e-4f * (fabsf(X.x) + fabsf(X.y) + fabsf(X.z) + W.len);
+        bit = plane_reachable(Pl, X, A, B, mg) && !surely_inside(W, X);
+      }
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, bit);
+    if (lane == 0) a.rmask[it] = mk;
+  }
+}
+
+// The images of block (kind, link, p1, p2): S, O the diffraction's source
+// and observer, S1 the transmitter's image in P1 (kind 0), O1 the
+// receiver's image in P2 (kind 2); m the block's margin.
+__device__ __forceinline__ void refl2_images(const PathArgs& a, int kind, int link, const RPlane& P1,
+                                             const RPlane& P2, float3& S, float3& S1, float3& O, float3& O1,
+                                             float& m) {
+  const float4 tv = a.txs[link / a.nrx], rv = a.rx[link % a.nrx];
+  const float3 T = f3(tv.x, tv.y, tv.z), R = f3(rv.x, rv.y, rv.z);
+  const float3 n1 = f3(P1.nf[0], P1.nf[1], P1.nf[2]);
+  const float3 n2 = f3(P2.nf[0], P2.nf[1], P2.nf[2]);
+  m = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fabsf(R.x) + fabsf(R.y) + fabsf(R.z));
+  S = S1 = T;
+  O = O1 = R;
+  if (kind == 0) {
+    S1 = mirror32(T, n1, P1.cf);
+    S = mirror32(S1, n2, P2.cf);
+  } else if (kind == 1) {
+    S = S1 = mirror32(T, n1, P1.cf);
+    O = O1 = mirror32(R, n2, P2.cf);
+  } else {
+    O1 = mirror32(R, n2, P2.cf);
+    O = mirror32(O1, n1, P1.cf);
+  }
+}
+
+// Block b's parts: kind, link and the two planes (32-bit division when b fits).
+__device__ __forceinline__ void refl2_block(const PathArgs& a, int nlinks, long b, int& kind, int& link, int& p1,
+                                            int& p2) {
+  if (b < 0x7fffffffL) {
+    unsigned r = (unsigned)b;
+    p2 = (int)(r % (unsigned)a.nrp);
+    r /= (unsigned)a.nrp;
+    p1 = (int)(r % (unsigned)a.nrp);
+    r /= (unsigned)a.nrp;
+    link = (int)(r % (unsigned)nlinks);
+    kind = (int)(r / (unsigned)nlinks);
+  } else {
     long r = b;
-    const int p2 = (int)(r % a.nrp);
+    p2 = (int)(r % a.nrp);
     r /= a.nrp;
-    const int p1 = (int)(r % a.nrp);
+    p1 = (int)(r % a.nrp);
     r /= a.nrp;
-    const int link = (int)(r % nlinks), kind = (int)(r / nlinks);
+    link = (int)(r % nlinks);
+    kind = (int)(r / nlinks);
+  }
+}
+
+// A block's record in a warp's ring: its images, planes, kind and index.
+struct Refl2Blk {
+  float3 S, S1, O, O1;
+  int p1, p2, kind;
+  long b;
+};
+constexpr int kRefl2Queue = 64;  // queue entries and block records per warp
+
+// One warp per block (kind, link, p1, p2). Its wedges: with one reflection
+// on each side, those in both end points' masks (k_refl2_masks); with both
+// on one side, the wedges of the clusters that the unfolded legs can reach
+// through the planes' boxes (lane c tests cluster c), less those the other,
+// real end point lies inside. The candidates wait in a per-warp FIFO queue
+// in shared memory and go through refl2_candidate 32 at a time, so that the
+// test runs on full warps; each entry names its wedge and its block's record
+// in a ring of 64. At most 63 entries wait, each block with an entry adds
+// one, so a record is overwritten only after its entries left the queue.
+__global__ void __launch_bounds__(256, 3) k_diffract_refl2_pre(PathArgs a, int nlinks) {
+  __shared__ Refl2Blk rec[8][kRefl2Queue];
+  __shared__ int qw[8][kRefl2Queue];
+  __shared__ unsigned char qs[8][kRefl2Queue];
+  const long nblk = 3L * nlinks * a.nrp * a.nrp;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long nwarp = (long)gridDim.x * (blockDim.x >> 5);
+  const int np1 = a.nrp + 1, ntx = nlinks / a.nrx;
+  // warp-uniform: queue head and tail (entries head .. tail - 1), next record
+  int head = 0, tail = 0, nrec = 0;
+  // the oldest min(tail - head, 32) entries through the test
+  auto drain = [&]() {
+    const int nn = min(tail - head, 32);
+    bool keep = false;
+    int w = 0;
+    long b = 0;
+    if (lane < nn) {
+      const int e = (head + lane) & (kRefl2Queue - 1);
+      w = qw[wid][e];
+      const Refl2Blk& R = rec[wid][qs[wid][e]];
+      b = R.b;
+      keep = refl2_candidate(a.wf[w], a.rplanes[R.p1], a.rplanes[R.p2], R.kind, R.S, R.S1, R.O, R.O1);
+    }
+    head += nn;
+    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+    if (!mk) return;
+    unsigned at = 0;
+    if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
+    if (keep) {
+      if (at < a.dsurv_cap) a.dsurv[at] = kRefl2Tag | ((unsigned long long)b * a.nw + w);
+      else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+    }
+  };
+  for (long b = (long)blockIdx.x * (blockDim.x >> 5) + wid; b < nblk; b += nwarp) {
+    int kind, link, p1, p2;
+    refl2_block(a, nlinks, b, kind, link, p1, p2);
     if (kind != 1 && p1 == p2) continue;  // two reflections in a row on one plane
     const RPlane &P1 = a.rplanes[p1], &P2 = a.rplanes[p2];
-    const float4 tv = a.txs[link / a.nrx], rv = a.rx[link % a.nrx];
-    const float3 T = f3(tv.x, tv.y, tv.z), R = f3(rv.x, rv.y, rv.z);
-    const float3 n1 = f3(P1.nf[0], P1.nf[1], P1.nf[2]);
-    const float3 n2 = f3(P2.nf[0], P2.nf[1], P2.nf[2]);
-    const float m = 0.1f + 1e-4f * (fabsf(T.x) + fabsf(T.y) + fabsf(T.z) + fabsf(R.x) + fabsf(R.y) + fabsf(R.z));
-    float3 S = T, S1 = T, O = R, O1 = R;
-    if (kind == 0) {
-      S1 = mirror32(T, n1, P1.cf);
-      S = mirror32(S1, n2, P2.cf);
-      if (!box_reachable(P1, S1, P2.box, m)) continue;
-    } else if (kind == 1) {
-      S = S1 = mirror32(T, n1, P1.cf);
-      O = O1 = mirror32(R, n2, P2.cf);
-    } else {
-      O1 = mirror32(R, n2, P2.cf);
-      O = mirror32(O1, n1, P1.cf);
-      if (!box_reachable(P2, O1, P1.box, m)) continue;
-    }
-    // the wedge clusters (lane c tests cluster c0 + c): the unfolded legs to
-    // some point of the cluster's box must cross their planes inside the
-    // planes' boxes; then the lanes take the wedges of each cluster kept
+    float3 S, S1, O, O1;
+    float m;
+    refl2_images(a, kind, link, P1, P2, S, S1, O, O1, m);
+    if (kind == 0 && !box_reachable(P1, S1, P2.box, m)) continue;
+    if (kind == 2 && !box_reachable(P2, O1, P1.box, m)) continue;
+    const int t = link / a.nrx, rr = link % a.nrx;
+    const unsigned* mt = a.rmask + ((long)t * np1 + (kind == 1 ? p1 : a.nrp)) * a.nwc;
+    const unsigned* mr = a.rmask + ((long)(ntx + rr) * np1 + (kind == 1 ? p2 : a.nrp)) * a.nwc;
+    int slot = -1;  // this block's record (written with its first entry)
     for (int c0 = 0; c0 < a.nwc; c0 += 32) {
       const int c = c0 + lane;
-      bool near = false;
+      unsigned word = 0;
       if (c < a.nwc) {
-        const float* cb = a.wcbox + 6 * (size_t)c;
-        near = kind == 0 ? box_reachable(P2, S, cb, m)
-               : kind == 1 ? box_reachable(P1, S, cb, m) && box_reachable(P2, O, cb, m)
-                           : box_reachable(P1, O, cb, m);
-      }
-      for (unsigned cm = __ballot_sync(0xffffffffu, near); cm; cm &= cm - 1u) {
-        const int i = (c0 + __ffs(cm) - 1) * kWedgeCluster + lane;
-        const int w = i < a.nw ? a.wperm[i] : -1;
-        const bool keep = w >= 0 && refl2_candidate(a.wf[w], P1, P2, kind, S, S1, O, O1);
-        const unsigned mk = __ballot_sync(0xffffffffu, keep);
-        if (!mk) continue;
-        unsigned at = 0;
-        if (lane == 0) at = atomicAdd(&a.ctr->n_dsurv, (unsigned)__popc(mk));
-        at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & ((1u << lane) - 1u));
-        if (keep) {
-          if (at < a.dsurv_cap) a.dsurv[at] = kRefl2Tag | ((unsigned long long)b * a.nw + w);
-          else atomicOr(&a.ctr->err, ERR_DIFF_OVERFLOW);
+        if (kind == 1) {
+          word = mt[c] & mr[c];
+        } else {
+          word = kind == 0 ? mr[c] : mt[c];
+          const float* cb = a.wcbox + 6 * (size_t)c;
+          if (word && !(kind == 0 ? box_reachable(P2, S, cb, m) : box_reachable(P1, O, cb, m))) word = 0;
         }
+      }
+      for (unsigned cm = __ballot_sync(0xffffffffu, word != 0); cm; cm &= cm - 1u) {
+        const int src = __ffs(cm) - 1;
+        const unsigned wd = __shfl_sync(0xffffffffu, word, src);
+        if (slot < 0) {
+          slot = nrec++ & (kRefl2Queue - 1);
+          if (lane == 0) {
+            Refl2Blk& R = rec[wid][slot];
+            R.S = S; R.S1 = S1; R.O = O; R.O1 = O1;
+            R.p1 = p1; R.p2 = p2; R.kind = kind; R.b = b;
+          }
+        }
+        const bool bit = (wd >> lane) & 1u;
+        const unsigned bm = __ballot_sync(0xffffffffu, bit);
+        if (bit) {
+          const int e = (tail + __popc(bm & ((1u << lane) - 1u))) & (kRefl2Queue - 1);
+          qw[wid][e] = a.wperm[(c0 + src) * kWedgeCluster + lane];
+          qs[wid][e] = (unsigned char)slot;
+        }
+        tail += __popc(bm);
+        __syncwarp();
+        if (tail - head >= 32) drain();
+        __syncwarp();
       }
     }
   }
+  while (tail > head) drain();
 }
 
 __device__ __forceinline__ d3w mirror_d(d3w x, d3w n, double c) { return x - n * (2.0 * (dotw(n, x) - c)); }
@@ -3054,18 +3222,12 @@ __device__ __noinline__ void diffract_refl2(const PathArgs& a, unsigned long lon
       float4 mj;
       if (pass == 0) {  // the member triangle holding the point: its own plane next
         const RPlane& G = a.rplanes[pg[i]];
-        for (int q = 0; q < G.count && pj[i] < 0; ++q) {
-          const int id = a.rmembers[G.first + q];
-          if (id == W.ta || id == W.tb || !tri_box_near(a, id, Y[i])) continue;
-          tri64(a, id, v0, v1, v2, mj);
-          if (inside_tri64(v0, v1, v2, Y[i])) {
-            pj[i] = id;
-            pm[i] = mj;
-            pn[i] = unitw(crossw(v1 - v0, v2 - v0));
-            pc[i] = dotw(pn[i], v0);
-          }
-        }
+        const int exw[2] = {W.ta, W.tb};
+        pj[i] = member_at(a, G, Y[i], exw, 2, v0, v1, v2, mj);
         if (pj[i] < 0) return;
+        pm[i] = mj;
+        pn[i] = unitw(crossw(v1 - v0, v2 - v0));
+        pc[i] = dotw(pn[i], v0);
       } else {
         tri64(a, pj[i], v0, v1, v2, mj);
         if (!inside_tri64(v0, v1, v2, Y[i])) return;
@@ -3374,6 +3536,9 @@ cudaError_t launch_diffract(const PathArgs& a, int nlinks, int sms, cudaStream_t
       long gr = std::min<long>((tr + 255) / 256, 8L * sms);
       k_diffract_refl_pre<<<(int)std::max<long>(gr, 1), 256, 0, st>>>(a, nlinks);
       if (a.drefl2) {
+        const int ntx = nlinks / a.nrx;
+        long nm = (long)(ntx + a.nrx) * (a.nrp + 1) * a.nwc;
+        k_refl2_masks<<<(int)std::max<long>(std::min<long>((nm + 7) / 8, 8L * sms), 1), 256, 0, st>>>(a, ntx);
         long nblk = 3L * nlinks * a.nrp * a.nrp;
         long g2 = std::min<long>((nblk + 7) / 8, 8L * sms);
         k_diffract_refl2_pre<<<(int)std::max<long>(g2, 1), 256, 0, st>>>(a, nlinks);

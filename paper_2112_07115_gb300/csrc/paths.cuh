@@ -63,9 +63,12 @@ struct PathArgs {
   // one reflection before or after a diffraction (null: off): reflector
   // planes and their member triangle ids
   const RPlane* rplanes;
-  const int* rmembers;
+  const int* rmembers;             // per plane its members, sorted by their lowest coordinate
+  const float* rkeys;              // along the plane's axis, and that coordinate
   int nrp;
   int drefl2;                     // 1: also two reflections around a first-order diffraction
+  unsigned* rmask;                // with drefl2: the wedge masks of k_refl2_masks, one word per
+                                  // (end point: transmitters then receivers, plane or none, cluster)
   int dmid;                       // 1: also a reflection between the two wedges of an order-2 chain
   // diffraction of order 2 and 3 (diff_order <= 1: off): the wedge pairs
   // (v, w1, w2, -1), the pairs with a reflection on plane p between them
