@@ -872,7 +872,7 @@ __device__ __forceinline__ bool diffract_candidate(const WedgeF& W, float4 txv, 
 
 // FP32 any-hit of the open segment a -> b, the wedge faces (and a reflecting
 // triangle) excluded.
-__device__ __forceinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, unsigned& ovf,
+__device__ __noinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, unsigned& ovf,
                                              TStack& st, int ex2 = -1) {
   d3w dv = q - p;
   RayPre rp = ray_pre(f3((float)p.x, (float)p.y, (float)p.z), f3((float)dv.x, (float)dv.y, (float)dv.z));
@@ -2045,7 +2045,7 @@ __device__ __forceinline__ float chain_margin(float3 T, float3 R) {
 // its crossing by at most that much. So the exact leg (FP32 any-hit of the
 // FP64 points) is blocked too, and the chain is rejected either way. An
 // overflow of the stack or of the visit limit answers "not certain".
-__device__ bool leg_surely_blocked(const Bvh& bvh, float3 o, float3 dv, float delta, float eps_occ, int ex0,
+__device__ __noinline__ bool leg_surely_blocked(const Bvh& bvh, float3 o, float3 dv, float delta, float eps_occ, int ex0,
                                    int ex1, int ex2, int ex3, TStack& st) {
   const float dl = sqrtf(fdot3(dv, dv));
   if (!(dl > 0.0f)) return false;
