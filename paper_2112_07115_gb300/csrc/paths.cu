@@ -2107,7 +2107,7 @@ __device__ __noinline__ bool leg_surely_blocked(const Bvh& bvh, float3 o, float3
 // the edge.
 // *solved: the estimate converged (t then holds it) -- only then can it
 // reject anything.
-__device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float* t, bool* solved) {
+__device__ __noinline__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float* t, bool* solved) {
   float mt = chain_margin(T, R);
   *solved = keller32(W, m, T, R, t, 0.1f * mt);
   if (!*solved) return true;
@@ -2154,22 +2154,19 @@ __device__ bool chain_possible(const WedgeF* W, int m, float3 T, float3 R, float
 // between the previous edge and the observer; an image observer's leg from
 // the last edge must be able to cross its plane inside the box.
 __device__ __forceinline__ bool multi_stage1(const PathArgs& a, int4 sq, bool three, int rho) {
-  if (!three && sq.w <= -2) {  // a reflection between the wedges: w2 and the receiver mirrored
+  const bool mid = !three && sq.w <= -2, obs_img = rho >= a.nrx;
+  WedgeF fl = a.wf[three ? sq.w : sq.z];
+  const WedgeF fp = a.wf[three ? sq.z : sq.y];
+  float3 R = chain_observer32(a, rho), P, Q;
+  if (mid) {  // a reflection between the wedges: w2 and the receiver mirrored
     const RPlane& Pl = a.rplanes[-2 - sq.w];
     const float3 n = f3(Pl.nf[0], Pl.nf[1], Pl.nf[2]);
-    const WedgeF fl = wedge_mirror32(a.wf[sq.z], n, Pl.cf), fp = a.wf[sq.y];
-    const float3 R = mirror32(chain_observer32(a, rho), n, Pl.cf);
-    float3 P, Q;
-    edge_ends(fp, P, Q);
-    return !surely_inside(fl, R) && shadow_meets(fl, R, P, Q) && keller_on_edge(fl, true, R, fp, fp, keller_margin(fl, R));
+    fl = wedge_mirror32(fl, n, Pl.cf);
+    R = mirror32(R, n, Pl.cf);
   }
-  const bool obs_img = rho >= a.nrx;
-  const int wl = three ? sq.w : sq.z, wp = three ? sq.z : sq.y;
-  const WedgeF fl = a.wf[wl], fp = a.wf[wp];
-  float3 R = chain_observer32(a, rho), P, Q;
   edge_ends(fp, P, Q);
   bool keep = !surely_inside(fl, R) && shadow_meets(fl, R, P, Q) && keller_on_edge(fl, true, R, fp, fp, keller_margin(fl, R));
-  if (keep && obs_img) {  // the leg from the last edge to the image crosses its plane inside the box
+  if (keep && !mid && obs_img) {  // the leg from the last edge to the image crosses its plane inside the box
     float3 A1, B1;
     edge_ends(fl, A1, B1);
     float mg = 0.1f + 1e-4f * (fabsf(R.x) + fabsf(R.y) + fabsf(R.z) + fl.len);
