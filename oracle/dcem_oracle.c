@@ -1605,7 +1605,8 @@ static int solve_small(int m, double H[3][3], double* b, double* x) {
  * moving linearly with t), so its stationary point is its minimum; it is
  * found by Newton's method from the edges' midpoints (at most 50 steps),
  * halving a step that does not shorten the chain (at most 40 times) until
- * the cosine mismatch is below 1e-8, full steps after that.
+ * the cosine mismatch is below 1e-8 or the Newton decrement below 1e-15 of
+ * the length, full steps after that.
  * Returns 1 when converged (every edge's cosine mismatch below 1e-12); 0
  * when not, or when a leg shrinks below OR_LEG_MIN: the minimum is then at
  * a kink of the length (two consecutive edge lines meet), where Keller's
@@ -1639,13 +1640,19 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
     if (gmax < 1e-12) return 1;
     double mg[3] = {-g[0], -g[1], -g[2]}, dx[3];
     if (!solve_small(m, H, mg, dx)) return 0;
+    /* near the minimum the full Newton step is taken: the length it saves
+     * (the Newton decrement, -g.dx / 2) is below the length's own rounding
+     * there, so comparing lengths cannot judge it -- a mismatch below 1e-8,
+     * or a decrement below 1e-15 of the length (long chains reach that floor
+     * at larger mismatches) */
+    double gdx = 0.0;
+    for (int i = 0; i < m; ++i) gdx += g[i] * dx[i];
+    int at_floor = gmax < 1e-8 || fabs(gdx) <= 2e-15 * Lc;
     double step = 1.0, tn[3];
     for (int k = 0; k < 40; ++k) {
       for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
       double Ln = chain_length(E, m, T, R, tn);
-      /* near the minimum (mismatch below 1e-8) the full Newton step is taken:
-       * the length it saves is below the length's own rounding there */
-      if (Ln <= Lc || gmax < 1e-8) { Lc = Ln; break; }
+      if (Ln <= Lc || at_floor) { Lc = Ln; break; }
       step *= 0.5;
     }
     double dmax = 0.0;

@@ -2375,8 +2375,8 @@ __device__ __forceinline__ double chain_len(const Wedge* const* E, int m, d3w T,
 // t) of the unfolded length over the edge parameters, by Newton's method
 // from the edges' midpoints (at most 50 steps), a step that does not
 // shorten the chain halved (at most 40 times) until the cosine mismatch is
-// below 1e-8, full steps after that; converged when every edge's mismatch is
-// below 1e-12. A leg shorter than kLegMin stops it: the
+// below 1e-8 or the Newton decrement below 1e-15 of the length, full steps
+// after that; converged when every edge's mismatch is below 1e-12. A leg shorter than kLegMin stops it: the
 // minimum is then at a kink of the length (consecutive edge lines meet),
 // where Keller's law has no solution.
 constexpr double kLegMin = 1e-6;
@@ -2443,13 +2443,19 @@ __device__ bool keller_chain(const Wedge* const* E, int m, d3w T, d3w R, double*
       for (int j = i + 1; j < m; ++j) v -= A[i][j] * dx[j];
       dx[i] = v / A[i][i];
     }
+    // near the minimum the full step: the length it saves (the Newton
+    // decrement, -g.dx / 2) is below the length's rounding there, so a
+    // comparison of lengths cannot judge it -- a mismatch below 1e-8, or a
+    // decrement below 1e-15 of the length (long chains reach that floor at
+    // larger mismatches)
+    double gdx = 0.0;
+    for (int i = 0; i < m; ++i) gdx += g[i] * dx[i];
+    const bool floor = gmax < 1e-8 || fabs(gdx) <= 2e-15 * Lc;
     double step = 1.0, tn[3] = {0.0, 0.0, 0.0};
     for (int q = 0; q < 40; ++q) {
       for (int i = 0; i < m; ++i) tn[i] = t[i] + step * dx[i];
       double Ln = chain_len(E, m, T, R, tn);
-      // near the minimum the full step: the length it saves is below the
-      // length's rounding there
-      if (Ln <= Lc || gmax < 1e-8) {
+      if (Ln <= Lc || floor) {
         Lc = Ln;
         break;
       }
