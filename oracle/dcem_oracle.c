@@ -53,6 +53,9 @@
  *                  around one diffraction, and one reflection between two
  *                  diffractions; reflections by image theory on static
  *                  triangles.
+ *   or_keller_points
+ *                  the Keller points of a chain of 1-3 edges between two
+ *                  points (the solver the functions above use), for pins.
  *
  * Everything after the FP32 inputs is FP64. Decisions that FP32 arithmetic
  * could take differently (a ray passing within a margin of a triangle edge,
@@ -1660,6 +1663,26 @@ static int keller_points(const owedge* const* E, int m, v3 T, v3 R, double* t) {
     if (dmax == 0.0) return gmax < 1e-9;
   }
   return 0;
+}
+
+/* Keller points of a chain of m (1..3) edges from T to R, each edge a row
+ * of 7 doubles (start, unit direction, length): keller_points on them.
+ * Returns 1 when it converged, with the edge parameters in t[0 .. m-1]
+ * (test infrastructure: lets pins check the solver alone). */
+int or_keller_points(int32_t m, const double* edges, const double* T, const double* R, double* t) {
+  if (m < 1 || m > 3) return 0;
+  owedge W[3];
+  const owedge* E[3];
+  for (int i = 0; i < m; ++i) {
+    const double* r = edges + 7 * i;
+    memset(&W[i], 0, sizeof W[i]);
+    W[i].p0 = mk(r[0], r[1], r[2]);
+    W[i].e = mk(r[3], r[4], r[5]);
+    W[i].len = r[6];
+    W[i].p1 = add(W[i].p0, scl(W[i].e, W[i].len));
+    E[i] = &W[i];
+  }
+  return keller_points(E, m, mk(T[0], T[1], T[2]), mk(R[0], R[1], R[2]), t);
 }
 
 /* The specular reflection of field E at triangle Tj for incoming direction

@@ -123,6 +123,8 @@ def lib():
         assert _lib.or_inst_size() == INST_DTYPE.itemsize, "instance record layout mismatch"
         _lib.or_transition.argtypes = [C.c_double, f64]
         _lib.or_transition.restype = None
+        _lib.or_keller_points.argtypes = [C.c_int32, f64, f64, f64, f64]
+        _lib.or_keller_points.restype = C.c_int
         _lib.or_utd.argtypes = [C.c_double] * 6 + [f64, f64, f64]
         _lib.or_utd.restype = None
         _lib.or_count_wedges.argtypes = [f32, i32, C.c_int32]
@@ -511,6 +513,20 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
         keys, paths = keys[order], paths[order]
     fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)
     return FrameResult(wt, tr, keys, paths, fld, pc, pi)
+
+
+def keller_points(edges, T, R):
+    """The oracle's Keller points of a chain of 1-3 edges from T to R: edges
+    an (m, 7) array of (start, unit direction, length). Returns (converged,
+    edge parameters t of shape (m,))."""
+    e = np.ascontiguousarray(np.asarray(edges, np.float64).reshape(-1, 7))
+    m = e.shape[0]
+    T = np.ascontiguousarray(np.asarray(T, np.float64))
+    R = np.ascontiguousarray(np.asarray(R, np.float64))
+    t = np.zeros(3, np.float64)
+    ok = lib().or_keller_points(m, _p(e, C.c_double), _p(T, C.c_double), _p(R, C.c_double),
+                                _p(t, C.c_double))
+    return bool(ok), t[:m].copy()
 
 
 def transition(x: float) -> complex:

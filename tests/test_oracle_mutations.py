@@ -16,7 +16,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "dcem_oracle.c")
-PINS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_oracle_grad_pins.py")]
+PINS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_oracle_grad_pins.py"),
+        os.path.join(ROOT, "tests", "test_oracle_keller.py")]
 
 # (name, exact text in the source, replacement). The text of each case must
 # occur in the source; every occurrence is replaced.
@@ -67,6 +68,10 @@ MUTANTS = [
     # diffraction of order 2 and 3: Keller points, chains in a face plane, astigmatic spreading
     ("keller_gradient_sign", "if (a >= 0) { g[a] -= ca; H[a][a] += (1.0 - ca * ca) / l; }",
      "if (a >= 0) { g[a] += ca; H[a][a] += (1.0 - ca * ca) / l; }"),
+    ("keller_stalls_at_the_rounding_floor", "int at_floor = gmax < 1e-8 || fabs(gdx) <= 2e-15 * Lc;",
+     "int at_floor = gmax < 1e-8;"),
+    ("keller_hessian_cross_sign", "double h = -(dot(E[a]->e, E[b]->e) - ca * cb) / l;",
+     "double h = (dot(E[a]->e, E[b]->e) - ca * cb) / l;"),
     ("face_plane_chains_kept", "|| in_face_plane(A, B) || in_face_plane(B, A)) ok = 0;", ") ok = 0;"),
     ("caustic_on_the_edge", "rho1 = s;\n    dir1 = ph;", "rho1 = rhoe + s;\n    dir1 = ph;"),
     ("principal_direction", "dir1 = ph;\n    rho2 = rhoe + s;", "dir1 = bd;\n    rho2 = rhoe + s;"),
