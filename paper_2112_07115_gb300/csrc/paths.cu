@@ -2876,8 +2876,8 @@ __device__ __noinline__ void diffract_multi(const PathArgs& a, unsigned long lon
 // in the planes before the wedge (taken in path order) toward the receiver's
 // image in the planes after it (the last one first); the reflection points
 // follow by unfolding back from Q. A block (kind, link, p1, p2) goes to one
-// warp, its lanes take the wedges. Survivors carry 10 in bits 63-62 and 1 in
-// bit 61 over (block * nw + wedge).
+// warp, which queues the block's candidate wedges (k_diffract_refl2_pre).
+// Survivors carry 10 in bits 63-62 and 1 in bit 61 over (block * nw + wedge).
 constexpr unsigned long long kRefl2Tag = kReflTag | (1ull << 61);
 constexpr unsigned long long kRefl2Mask = (1ull << 61) - 1ull;
 
