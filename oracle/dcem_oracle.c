@@ -53,6 +53,9 @@
  *                  around one diffraction, and one reflection between two
  *                  diffractions; reflections by image theory on static
  *                  triangles.
+ *   or_diffract_trans
+ *                  first-order diffraction whose legs pass straight through
+ *                  penetrable triangles (Table II losses), up to T in all.
  *   or_keller_points
  *                  the Keller points of a chain of 1-3 edges between two
  *                  points (the solver the functions above use), for pins.
@@ -1342,6 +1345,168 @@ int64_t or_diffract(const float* tris, const int32_t* tri_mat, const int32_t* tr
         o->amp_re = creal(a);
         o->amp_im = cimag(a);
         o->pts[0][0] = Q.x; o->pts[0][1] = Q.y; o->pts[0][2] = Q.z;
+      }
+      nvalid++;
+    }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
+/* The triangles (other than ex0, ex1) that cross the open segment a->b (its
+ * first and last eps_occ trimmed), in order along it: their ids in ids[],
+ * at most cap. Returns their count, or -1 when one of them is opaque (no
+ * penetration loss: trans_db NULL or < 0) or there are more than cap.
+ * Decisions within the FP32 margin are flagged as in occluded4. */
+static int leg_crossings(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_params* P, double scale,
+                         uint32_t* fl, int* ids, int cap) {
+  v3 dv = sub(b, a);
+  double len = norm(dv);
+  if (!(len > 0)) return 0;
+  v3 d = scl(dv, 1.0 / len);
+  double base = P->edge_eps * scale;
+  double us[OR_MAX_REFL + 1];
+  int n = 0, bad = 0;
+  for (int j = 0; j < S->ntri; ++j) {
+    if (j == ex0 || j == ex1) continue;
+    xinfo x;
+    ray_tri(&S->t[j], a, d, base, P->edge_eps, &x);
+    if (isnan(x.t)) continue;
+    double u = x.t / len;
+    double du = (base + P->edge_eps * fabs(x.t)) / fmax(x.cos_t, 1e-6) / len;
+    double lo = P->eps_occ, hi = 1.0 - P->eps_occ;
+    if (x.inside || x.flippable) {
+      if (u > lo - du && u < hi + du) {
+        if (x.flippable) *fl |= ORF_OCC_NEAR;
+        if (fabs(u - lo) <= du || fabs(u - hi) <= du) *fl |= ORF_OCC_NEAR;
+      }
+    }
+    if (!(x.inside && u > lo && u < hi)) continue;
+    int m = S->t[j].mat;
+    if (!P->trans_db || m < 0 || m >= S->nmat || P->trans_db[m] < 0) { bad = 1; continue; }
+    if (n >= cap) { bad = 1; continue; }
+    /* insertion in order of the parameter along the leg */
+    int q = n++;
+    while (q > 0 && us[q - 1] > u) { us[q] = us[q - 1]; ids[q] = ids[q - 1]; --q; }
+    us[q] = u;
+    ids[q] = j;
+  }
+  return bad ? -1 : n;
+}
+
+/* Sec. III steps 1-5 combined (the runtime comparisons of Sec. IV allow two
+ * transmissions and one diffraction per path): first-order diffraction
+ * paths Tx -> Q -> Rx whose legs pass straight through penetrable triangles
+ * (Table II losses), at least one and at most max_trans in all. Q, the
+ * rules and the UTD field are or_diffract's; each crossing multiplies the
+ * field by 10^(-L/20), L its material's penetration loss in dB. Keys (rx,
+ * depth, ids): the crossings of the first leg in order from the
+ * transmitter (| OR_TRANS), the wedge (| OR_DIFF), then those of the second
+ * leg in order from Q; -1 padded to 2 + width. Points in path order. Paths
+ * with no crossing are or_diffract's and are not written here. Returns the
+ * count (may exceed cap). */
+int64_t or_diffract_trans(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                          const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                          const or_params* P, int32_t width, int32_t* keys_out, opath* paths_out, int64_t cap) {
+  if (!P->trans_db || P->max_trans < 1) return 0;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
+  const int mt = P->max_trans < OR_MAX_REFL - 1 ? P->max_trans : OR_MAX_REFL - 1;
+  int64_t nvalid = 0;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (long w = 0; w < nw; ++w) {
+      const owedge* E = &W[w];
+      uint32_t fl = 0;
+      v3 dt = sub(T, E->p0), dr = sub(R, E->p0);
+      double zt = dot(dt, E->e), zr = dot(dr, E->e);
+      double rt = norm(sub(dt, scl(E->e, zt))), rr = norm(sub(dr, scl(E->e, zr)));
+      if (!(rt > 0 && rr > 0)) continue;
+      double zq = zt + (zr - zt) * rt / (rt + rr);
+      double uq = zq / E->len;
+      if (fabs(uq) <= P->val_eps || fabs(uq - 1.0) <= P->val_eps) fl |= ORF_VAL_PARAM;
+      if (!(uq > 0 && uq < 1)) continue;
+      v3 Q = add(E->p0, scl(E->e, zq));
+      double phip = wedge_angle(E, T), phi = wedge_angle(E, R), nn = E->n;
+      if (phip > nn * M_PI || phi > nn * M_PI) continue;
+      if (fabs(fabs(phi - phip) - M_PI) <= 1e-9) fl |= ORF_VAL_PARAM;
+      if (!(fabs(phi - phip) > M_PI)) continue;
+      double scale = fmax(maxabs(T), maxabs(R));
+      int c1[OR_MAX_REFL], c2[OR_MAX_REFL];
+      int n1 = leg_crossings(&S, T, Q, E->ta, E->tb, P, scale, &fl, c1, mt);
+      if (n1 < 0) continue;
+      int n2 = leg_crossings(&S, Q, R, E->ta, E->tb, P, scale, &fl, c2, mt);
+      if (n2 < 0 || n1 + n2 < 1 || n1 + n2 > mt) continue;
+      /* UTD field as or_diffract */
+      double sp = norm(sub(Q, T)), s = norm(sub(R, Q));
+      v3 ip = scl(sub(Q, T), 1.0 / sp), dd = scl(sub(R, Q), 1.0 / s);
+      double cb = dot(ip, E->e);
+      double beta0 = acos(fmax(-1.0, fmin(1.0, cb)));
+      double L = s * sp * sin(beta0) * sin(beta0) / (s + sp);
+      v3 php = cross(E->e, ip), ph = cross(E->e, dd);
+      php = scl(php, -1.0 / norm(php));
+      ph = scl(ph, 1.0 / norm(ph));
+      v3 bp = cross(ip, php), bd = cross(dd, ph);
+      int ma = S.t[E->ta].mat, mb = S.t[E->tb].mat;
+      if (ma < 0 || ma >= S.nmat) ma = 0;
+      if (mb < 0 || mb >= S.nmat) mb = 0;
+      double complex r0s, r0h, rns, rnh;
+      fresnel(&S.mats[3 * ma], P->freq_hz, fabs(sin(phip)), &r0s, &r0h);
+      fresnel(&S.mats[3 * mb], P->freq_hz, fabs(sin(nn * M_PI - phi)), &rns, &rnh);
+      double complex Ds = utd_coeff(nn, phi, phip, beta0, L, k, r0s, rns, &fl);
+      double complex Dh = utd_coeff(nn, phi, phip, beta0, L, k, r0h, rnh, &fl);
+      v3 e0 = pol_dir(u, ip, &fl);
+      double complex Ei = cexp(-I * k * sp) / sp;
+      double complex Eb = Ei * dot(e0, bp), Ep = Ei * dot(e0, php);
+      double complex A = csqrt(sp / (s * (s + sp))) * cexp(-I * k * s);
+      v3 prx = pol_dir(u, scl(dd, -1.0), &fl);
+      double complex proj = (-Ds * Eb) * dot(bd, prx) + (-Dh * Ep) * dot(ph, prx);
+      /* the penetration losses of the crossings (power dB: field 10^(-L/20)) */
+      double g = 1.0;
+      for (int i = 0; i < n1; ++i) g *= pow(10.0, -P->trans_db[S.t[c1[i]].mat] / 20.0);
+      for (int i = 0; i < n2; ++i) g *= pow(10.0, -P->trans_db[S.t[c2[i]].mat] / 20.0);
+      double complex a = (lam / (4.0 * M_PI)) * proj * A * g;
+      const int depth = n1 + 1 + n2;
+      if (nvalid < cap && depth <= width) {
+        int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+        kk[0] = r;
+        kk[1] = depth;
+        int q = 0;
+        for (int i = 0; i < n1; ++i) kk[2 + q++] = c1[i] | OR_TRANS;
+        kk[2 + q++] = (int32_t)w | OR_DIFF;
+        for (int i = 0; i < n2; ++i) kk[2 + q++] = c2[i] | OR_TRANS;
+        for (; q < width; ++q) kk[2 + q] = -1;
+        opath* o = &paths_out[nvalid];
+        memset(o, 0, sizeof(*o));
+        o->valid = 1;
+        o->flags = fl;
+        o->len_m = sp + s;
+        o->delay_s = (sp + s) / C0;
+        o->amp_re = creal(a);
+        o->amp_im = cimag(a);
+        /* points in path order: the crossings, Q, the crossings after it */
+        int pq = 0;
+        v3 d1 = sub(Q, T), d2 = sub(R, Q);
+        for (int i = 0; i < n1; ++i, ++pq) {
+          const otri* Tc = &S.t[c1[i]];
+          double tt = dot(sub(Tc->v[0], T), Tc->n) / dot(d1, Tc->n);
+          v3 X = add(T, scl(d1, tt));
+          o->pts[pq][0] = X.x; o->pts[pq][1] = X.y; o->pts[pq][2] = X.z;
+        }
+        o->pts[pq][0] = Q.x; o->pts[pq][1] = Q.y; o->pts[pq][2] = Q.z;
+        ++pq;
+        for (int i = 0; i < n2; ++i, ++pq) {
+          const otri* Tc = &S.t[c2[i]];
+          double tt = dot(sub(Tc->v[0], Q), Tc->n) / dot(d2, Tc->n);
+          v3 X = add(Q, scl(d2, tt));
+          o->pts[pq][0] = X.x; o->pts[pq][1] = X.y; o->pts[pq][2] = X.z;
+        }
       }
       nvalid++;
     }

@@ -17,7 +17,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "dcem_oracle.c")
 PINS = [os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_oracle_grad_pins.py"),
-        os.path.join(ROOT, "tests", "test_oracle_keller.py")]
+        os.path.join(ROOT, "tests", "test_oracle_keller.py"), os.path.join(ROOT, "tests", "test_oracle_diffract_trans.py")]
 
 # (name, exact text in the source, replacement). The text of each case must
 # occur in the source; every occurrence is replaced.
@@ -92,6 +92,12 @@ MUTANTS = [
     ("mid_reflection_dropped", "Ev = reflect_field(S, P, Tj, din, dout, Ev);", "(void)0;"),
     ("mid_principal_directions_not_mirrored", "dir1 = sub(dir1, scl(Tj->nh, 2.0 * dot(dir1, Tj->nh)));",
      "(void)0;"),
+    # transmissions on the legs of a first-order diffraction
+    ("diffract_trans_second_leg_loss_dropped",
+     "for (int i = 0; i < n2; ++i) g *= pow(10.0, -P->trans_db[S.t[c2[i]].mat] / 20.0);", "(void)0;"),
+    ("diffract_trans_crossings_reversed", "while (q > 0 && us[q - 1] > u)", "while (q > 0 && us[q - 1] < u)"),
+    ("diffract_trans_opaque_crossed", "if (!P->trans_db || m < 0 || m >= S->nmat || P->trans_db[m] < 0) { bad = 1; continue; }",
+     "if (!P->trans_db || m < 0 || m >= S->nmat) { bad = 1; continue; }"),
     ("spherical_spreading", "double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);",
      "double complex A = csqrt(ell[0] / (s * (ell[0] + s))) * cexp(-I * k * s);"),
 ]
