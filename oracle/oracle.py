@@ -495,8 +495,10 @@ class FrameResult:
 
 def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> FrameResult:
     """The whole oracle pipeline for frame ``f`` of a ``scenes.Scene``
-    (with prm.diffraction, the first-order diffraction paths join the
-    validated keys before the reduction)."""
+    (with prm.diffraction, the diffraction paths -- first order, chains up to
+    prm.diffraction_order, and with transmission first-order paths whose
+    legs cross penetrable triangles -- join the validated keys before the
+    reduction)."""
     wt = transform(scene.tris, scene.tri_obj, scene.xf[f] if scene.nobj else np.zeros((0, 12)))
     rx = scene.rx[f]
     tr = trace(wt, scene.tri_mat, scene.materials, scene.tx, rays, rx, prm, seg_od=seg_od)
@@ -512,6 +514,12 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
             mk_, mp_ = diffract_multi(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm, m)
             keys = np.concatenate([keys, mk_])
             paths = np.concatenate([paths, mp_])
+        if prm.transmission:  # first-order paths whose legs cross penetrable triangles
+            tk, tp = diffract_trans(wt, scene.tri_mat, scene.tri_obj, scene.materials, scene.tx, rx, prm)
+            if tk.shape[1] != keys.shape[1]:
+                raise ValueError("key widths differ: max_refl must be at least 1 with transmission")
+            keys = np.concatenate([keys, tk])
+            paths = np.concatenate([paths, tp])
         order = np.lexsort(keys.T[::-1])
         keys, paths = keys[order], paths[order]
     fld, pc, pi = reduce(keys, paths, rx.shape[0], prm.tx_power_w)

@@ -870,6 +870,82 @@ __device__ __forceinline__ bool diffract_candidate(const WedgeF& W, float4 txv, 
   return true;
 }
 
+// Triangle slot geometry: vertices and the (unnormalised) normal.
+__device__ __forceinline__ void tri64(const PathArgs& a, int id, d3w& v0, d3w& v1, d3w& v2, float4& mat) {
+  const float4* tp = a.tris + 3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(id, a.bvh.ntris)], a.bvh.ntris);
+  float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
+  v0 = D3(p0.x, p0.y, p0.z);
+  v1 = D3(p1.x, p1.y, p1.z);
+  v2 = D3(p2.x, p2.y, p2.z);
+  mat = a.mats[__float_as_int(p1.w)];
+}
+
+// The triangles (other than ex0, ex1) that the open segment p -> q crosses
+// with parameter in (eps_occ, 1 - eps_occ) (FP32 traversal of the scene, as
+// any_hit), in order along it: their ids in ids[0 .. n-1]. Returns n, or -1
+// when one of them is opaque (a material without penetration loss, loss <
+// 0) or there are more than cap (the transmissions a path has left).
+__device__ __noinline__ int leg_crossings(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, int* ids, int cap,
+                                          unsigned& ovf, TStack& st) {
+  const Bvh& bvh = a.bvh;
+  const d3w dv = q - p;
+  const RayPre r = ray_pre(f3((float)p.x, (float)p.y, (float)p.z), f3((float)dv.x, (float)dv.y, (float)dv.z));
+  const float t0 = a.eps_occ, t1 = 1.0f - a.eps_occ;
+  float ts[kMaxRefl];
+  int n = 0;
+  st.reset();
+  if (bvh.root1 != kEmpty) st.push(bvh.root1);
+  int cur = bvh.root0;
+  for (int visits = 0;; ++visits) {
+    if (visits > bvh.max_visits) {
+      ovf = 1u;
+      break;
+    }
+    if (cur == kEmpty) {
+      if (st.empty()) break;
+      cur = st.pop();
+      continue;
+    }
+    if (cur >= 0) {
+      const float4* nd = bvh.nodes + 4 * (size_t)DCEM_IDX(cur, bvh.nnodes);
+      float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+      float tn0, tn1;
+      bool h0 = slab(r, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, t1, tn0);
+      bool h1 = slab(r, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, t1, tn1);
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        if (!st.push(c1)) ovf = 1u;
+        cur = c0;
+      } else if (h0) {
+        cur = c0;
+      } else if (h1) {
+        cur = c1;
+      } else {
+        cur = kEmpty;
+      }
+    } else {
+      const int slot = DCEM_IDX(~cur, bvh.ntris);
+      float3 v0, v1, v2;
+      int id;
+      load_tri(bvh.tris, slot, v0, v1, v2, id);
+      float t;
+      cur = kEmpty;
+      if (id == ex0 || id == ex1 || !tri_hit(r, v0, v1, v2, t) || !(t > t0 && t < t1)) continue;
+      const float loss = a.mats[__float_as_int(__ldg(&bvh.tris[3 * slot + 1]).w)].w;
+      if (!(loss >= 0.0f) || n >= cap || n >= kMaxRefl) return -1;
+      int k = n++;  // insertion in order along the segment
+      while (k > 0 && ts[k - 1] > t) {
+        ts[k] = ts[k - 1];
+        ids[k] = ids[k - 1];
+        --k;
+      }
+      ts[k] = t;
+      ids[k] = id;
+    }
+  }
+  return n;
+}
+
 // FP32 any-hit of the open segment a -> b, the wedge faces (and a reflecting
 // triangle) excluded.
 __device__ __noinline__ bool leg_occluded(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, unsigned& ovf,
@@ -989,7 +1065,18 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   double phip = wedge_angle(W, T), phi = wedge_angle(W, R), n = W.n;
   if (phip > n * M_PI || phi > n * M_PI) return;
   if (!(fabs(phi - phip) > M_PI)) return;
-  if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, R, W.ta, W.tb, ovf, st)) return;
+  // the legs: unoccluded, or with transmission on, crossing penetrable
+  // triangles only, at most max_trans in all (Table II losses)
+  int c1[kMaxRefl], c2[kMaxRefl], n1 = 0, n2 = 0;
+  if (a.max_trans > 0) {
+    const int mt = min(a.max_trans, kMaxRefl - 1);  // the wedge takes one of the record's slots
+    n1 = leg_crossings(a, T, Q, W.ta, W.tb, c1, mt, ovf, st);
+    if (n1 < 0) return;
+    n2 = leg_crossings(a, Q, R, W.ta, W.tb, c2, mt - n1, ovf, st);
+    if (n2 < 0) return;
+  } else if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, R, W.ta, W.tb, ovf, st)) {
+    return;
+  }
   unsigned fl = 0;
   d3w qt = Q - T, rq = R - Q;
   double sp = sqrt(dotw(qt, qt)), s = sqrt(dotw(rq, rq));
@@ -1019,17 +1106,29 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   sincos(-k * s, &sn, &cs);
   zd A = Z(cs, sn) * sqrt(sp / (s * (s + sp)));
   zd proj = (Ds * Eb) * (-dotw(bd, prx)) + (Dh * Ep) * (-dotw(ph, prx));
-  zd amp = proj * A * (lam / (4.0 * M_PI));
+  // each crossing's penetration loss (power dB): the field times 10^(-L/20)
+  double g = 1.0;
+  for (int i = 0; i < n1 + n2; ++i) {
+    d3w v0, v1, v2;
+    float4 mt;
+    tri64(a, i < n1 ? c1[i] : c2[i - n1], v0, v1, v2, mt);
+    g *= pow(10.0, -(double)mt.w / 20.0);
+  }
+  zd amp = proj * A * (lam / (4.0 * M_PI) * g);
   unsigned uu = atomicAdd(&a.ctr->n_unique, 1u);
   if (uu >= a.ucap) {
     atomicOr(&a.ctr->err, ERR_UNIQUE_OVERFLOW);
     return;
   }
   PathRec rec;
-  int id = w | kDiffBit;
-  rec.key = seq_key(link % a.nrx, 1, [&](int) { return id; });
+  // interactions in path order: the first leg's crossings, the wedge, the second leg's
+  const int depth = n1 + 1 + n2;
+  auto id_at = [&](int q) {
+    return q < n1 ? (c1[q] | kTransBit) : q == n1 ? (w | kDiffBit) : (c2[q - n1 - 1] | kTransBit);
+  };
+  rec.key = seq_key(link % a.nrx, depth, id_at);
   rec.rx = link;
-  rec.depth = 1;
+  rec.depth = depth;
   rec.ray = -1;
   rec.flags = fl;
   rec.valid = 1;
@@ -1038,12 +1137,24 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   rec.amp_re = amp.re;
   rec.amp_im = amp.im;
   for (int j = 0; j < kMaxRefl; ++j) {
-    rec.tri[j] = j == 0 ? id : -1;
+    rec.tri[j] = j < depth ? id_at(j) : -1;
     rec.pts[j][0] = rec.pts[j][1] = rec.pts[j][2] = 0.0f;
   }
-  rec.pts[0][0] = (float)Q.x;
-  rec.pts[0][1] = (float)Q.y;
-  rec.pts[0][2] = (float)Q.z;
+  for (int j = 0; j < depth; ++j) {  // the crossings where the legs meet their triangles' planes, and Q
+    d3w X = Q;
+    if (j != n1) {
+      const bool first = j < n1;
+      const d3w o = first ? T : Q, dl = first ? qt : rq;
+      d3w v0, v1, v2;
+      float4 mt;
+      tri64(a, first ? c1[j] : c2[j - n1 - 1], v0, v1, v2, mt);
+      const d3w nv = crossw(v1 - v0, v2 - v0);
+      X = o + dl * (dotw(v0 - o, nv) / dotw(dl, nv));
+    }
+    rec.pts[j][0] = (float)X.x;
+    rec.pts[j][1] = (float)X.y;
+    rec.pts[j][2] = (float)X.z;
+  }
   a.prec[uu] = rec;
   unsigned pos = atomicAdd(&a.bucket_cnt[link], 1u);
   if (pos < (unsigned)a.bucket_cap) a.bucket[(size_t)link * a.bucket_cap + pos] = (int)uu;
@@ -1163,15 +1274,6 @@ __device__ __forceinline__ bool refl_geometry(const Wedge& W, d3w n, double c, d
   return true;
 }
 
-// Triangle slot geometry: vertices and the (unnormalised) normal.
-__device__ __forceinline__ void tri64(const PathArgs& a, int id, d3w& v0, d3w& v1, d3w& v2, float4& mat) {
-  const float4* tp = a.tris + 3 * (size_t)DCEM_IDX(a.slot_of_id[DCEM_IDX(id, a.bvh.ntris)], a.bvh.ntris);
-  float4 p0 = tp[0], p1 = tp[1], p2 = tp[2];
-  v0 = D3(p0.x, p0.y, p0.z);
-  v1 = D3(p1.x, p1.y, p1.z);
-  v2 = D3(p2.x, p2.y, p2.z);
-  mat = a.mats[__float_as_int(p1.w)];
-}
 
 // Can triangle id hold point x (on its plane group's plane, within 1e-4 m of
 // the triangle's own)? x must lie in the triangle's FP32 box widened by 1 mm +
