@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -141,11 +142,25 @@ _TRACE_SRC = ["paper_2112_07115_gb300/csrc/trace.cu", "paper_2112_07115_gb300/cs
 KERNEL_SOURCES = {"k_trace_q": _TRACE_SRC, "k_trace": _TRACE_SRC, "k_capture": _TRACE_SRC, "k_mark": _TRACE_SRC}
 
 
-def src_sha(kernel: str) -> str:
+_COMMENTS = re.compile(r"//[^\n]*|/\*.*?\*/", re.S)
+
+
+def code_text(text: str) -> str:
+    """C/C++ source without its comments and blank lines (trailing blanks
+    dropped): what the compiler sees, so that a documentation edit leaves a
+    capture current."""
+    code = _COMMENTS.sub("", text)
+    return "\n".join(ln.rstrip() for ln in code.splitlines() if ln.strip())
+
+
+def src_sha(kernel: str, read=None) -> str:
+    """Hash of the code (comments and blank lines dropped) of the sources a
+    kernel is compiled from; `read(path)` gives a file's text (default: the
+    working tree)."""
+    read = read or (lambda f: open(os.path.join(ROOT, f), encoding="utf-8").read())
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(kernel, []):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        h.update(f.encode() + code_text(read(f)).encode())
     return h.hexdigest()[:16]
 
 

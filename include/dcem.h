@@ -292,7 +292,9 @@ int dcem_scene_set_rebuild_threshold(dcem_scene* s, float ratio);
  * transmission; loss_db[m] < 0: opaque (the default). max_trans: most
  * transmissions per path (0 = off); max_refl + max_trans <= DCEM_MAX_REFL
  * at trace time. A transmission appears in dcem_path.tri as the id with
- * DCEM_TRI_TRANSMIT set; depth counts reflections and transmissions. While
+ * DCEM_TRI_TRANSMIT set; depth counts reflections and transmissions. With
+ * first-order diffraction on, its legs may cross transmitting triangles too
+ * (see dcem_scene_set_diffraction). While
  * max_trans > 0 every frame is a full trace (COHERENT and STICKY frames are
  * traced in full). host loss_db, nmat entries (the scene's material count).
  * Errors: DCEM_ERR_ARG, DCEM_ERR_NONFINITE. */
@@ -309,7 +311,13 @@ int dcem_scene_set_transmission(dcem_scene* s, const float* loss_db, int32_t nma
  * the edge by Keller's law, kept when the receiver lies beyond the incident
  * shadow boundary (the paper keeps sources in the receiver's shadow region)
  * and both legs are unoccluded, with its UTD field. Record: depth 1,
- * tri[0] = wedge | DCEM_TRI_DIFFRACT, pts[0] = Q, ray = -1. on = 0 turns it
+ * tri[0] = wedge | DCEM_TRI_DIFFRACT, pts[0] = Q, ray = -1. With transmission
+ * on (dcem_scene_set_transmission, max_trans > 0) a leg may instead cross
+ * transmitting triangles, at most max_trans (and 9) on the two legs
+ * together, the field scaled by 10^(-loss/20) at each; the record then lists
+ * the first leg's crossings in order from the transmitter (id |
+ * DCEM_TRI_TRANSMIT), the wedge, then the second leg's from Q, depth their
+ * count + 1, pts the crossing points and Q in the same order. on = 0 turns it
  * off. *n_wedges (may be NULL): the
  * wedge count. Cost: one thread per (link, wedge) per frame. Errors:
  * DCEM_ERR_ARG, DCEM_ERR_CUDA. */
