@@ -56,6 +56,9 @@
  *   or_diffract_trans
  *                  first-order diffraction whose legs pass straight through
  *                  penetrable triangles (Table II losses), up to T in all.
+ *   or_diffract_multi_trans
+ *                  chains of 2-3 wedges whose legs cross penetrable
+ *                  triangles likewise.
  *   or_keller_points
  *                  the Keller points of a chain of 1-3 edges between two
  *                  points (the solver the functions above use), for pins.
@@ -1354,13 +1357,13 @@ int64_t or_diffract(const float* tris, const int32_t* tri_mat, const int32_t* tr
   return nvalid;
 }
 
-/* The triangles (other than ex0, ex1) that cross the open segment a->b (its
+/* The triangles (other than ex0 .. ex3) that cross the open segment a->b (its
  * first and last eps_occ trimmed), in order along it: their ids in ids[],
  * at most cap. Returns their count, or -1 when one of them is opaque (no
  * penetration loss: trans_db NULL or < 0) or there are more than cap.
  * Decisions within the FP32 margin are flagged as in occluded4. */
-static int leg_crossings(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or_params* P, double scale,
-                         uint32_t* fl, int* ids, int cap) {
+static int leg_crossings(const oscene* S, v3 a, v3 b, int ex0, int ex1, int ex2, int ex3, const or_params* P,
+                         double scale, uint32_t* fl, int* ids, int cap) {
   v3 dv = sub(b, a);
   double len = norm(dv);
   if (!(len > 0)) return 0;
@@ -1369,7 +1372,7 @@ static int leg_crossings(const oscene* S, v3 a, v3 b, int ex0, int ex1, const or
   double us[OR_MAX_REFL + 1];
   int n = 0, bad = 0;
   for (int j = 0; j < S->ntri; ++j) {
-    if (j == ex0 || j == ex1) continue;
+    if (j == ex0 || j == ex1 || j == ex2 || j == ex3) continue;
     xinfo x;
     ray_tri(&S->t[j], a, d, base, P->edge_eps, &x);
     if (isnan(x.t)) continue;
@@ -1439,9 +1442,9 @@ int64_t or_diffract_trans(const float* tris, const int32_t* tri_mat, const int32
       if (!(fabs(phi - phip) > M_PI)) continue;
       double scale = fmax(maxabs(T), maxabs(R));
       int c1[OR_MAX_REFL], c2[OR_MAX_REFL];
-      int n1 = leg_crossings(&S, T, Q, E->ta, E->tb, P, scale, &fl, c1, mt);
+      int n1 = leg_crossings(&S, T, Q, E->ta, E->tb, E->tb, E->tb, P, scale, &fl, c1, mt);
       if (n1 < 0) continue;
-      int n2 = leg_crossings(&S, Q, R, E->ta, E->tb, P, scale, &fl, c2, mt);
+      int n2 = leg_crossings(&S, Q, R, E->ta, E->tb, E->tb, E->tb, P, scale, &fl, c2, mt);
       if (n2 < 0 || n1 + n2 < 1 || n1 + n2 > mt) continue;
       /* UTD field as or_diffract */
       double sp = norm(sub(Q, T)), s = norm(sub(R, Q));
@@ -1936,8 +1939,19 @@ static v3 mirror_in(const otri* Tj, v3 x) {
  * of or_diffract_multi over the unfolded distances (a plane mirror keeps the
  * wavefront's radii of curvature). Returns 1 when the path is valid, with o
  * filled (points in path order). */
+/* Crossings of a path's real legs by transmitting triangles (chain_path_r
+ * with a record: instead of unoccluded legs, legs that cross transmitting
+ * triangles only, at most cap in all): per leg their count, and their ids
+ * in path order. */
+typedef struct {
+  int cap;
+  int total;
+  int n[OR_MAX_REFL + 2];
+  int id[OR_MAX_REFL];
+} ocross;
+
 static int chain_path_r(const oscene* S, const owedge* const* E, int m, v3 T, v3 R, const int* jb, int nb,
-                        const int* ja, int na, const or_params* P, opath* o) {
+                        const int* ja, int na, const or_params* P, opath* o, ocross* cr) {
   const double k = 2.0 * M_PI * P->freq_hz / C0, lam = C0 / P->freq_hz;
   const double ang_eps = 1e-9;
   const v3 u = mk(P->pol[0], P->pol[1], P->pol[2]);
@@ -1999,8 +2013,18 @@ static int chain_path_r(const oscene* S, const owedge* const* E, int m, v3 T, v3
   for (int i = 0; i < m; ++i) { Y[ny] = X[i + 1]; ex[ny][0] = E[i]->ta; ex[ny][1] = E[i]->tb; ++ny; }
   for (int i = 0; i < na; ++i) { Y[ny] = Ya[i]; ex[ny][0] = ex[ny][1] = ja[i]; ++ny; }
   Y[ny] = R; ex[ny][0] = ex[ny][1] = -1; ++ny;
-  for (int q = 0; q + 1 < ny; ++q)
-    if (occluded4(S, Y[q], Y[q + 1], ex[q][0], ex[q][1], ex[q + 1][0], ex[q + 1][1], P, scale, &fl)) return 0;
+  if (cr) cr->total = 0;
+  for (int q = 0; q + 1 < ny; ++q) {
+    if (!cr) {
+      if (occluded4(S, Y[q], Y[q + 1], ex[q][0], ex[q][1], ex[q + 1][0], ex[q + 1][1], P, scale, &fl)) return 0;
+      continue;
+    }
+    int nq = leg_crossings(S, Y[q], Y[q + 1], ex[q][0], ex[q][1], ex[q + 1][0], ex[q + 1][1], P, scale, &fl,
+                           cr->id + cr->total, cr->cap - cr->total);
+    if (nq < 0) return 0;
+    cr->n[q] = nq;
+    cr->total += nq;
+  }
   /* field: the transmitter's wave along its real first leg, reflected at
    * each point before the chain */
   v3 ip = scl(sub(X[1], X[0]), 1.0 / ell[0]);   /* the real direction into Q_1 */
@@ -2069,6 +2093,9 @@ static int chain_path_r(const oscene* S, const owedge* const* E, int m, v3 T, v3
   }
   v3 prx = pol_dir(u, scl(dlast, -1.0), &fl);
   double complex a = (lam / (4.0 * M_PI)) * cdot(Ev, prx);
+  /* the penetration losses of the crossings (power dB: field 10^(-L/20)) */
+  if (cr)
+    for (int i = 0; i < cr->total; ++i) a *= pow(10.0, -P->trans_db[S->t[cr->id[i]].mat] / 20.0);
   double Ltot = 0.0;
   for (int q = 0; q <= m; ++q) Ltot += ell[q];
   memset(o, 0, sizeof(*o));
@@ -2091,7 +2118,7 @@ static int chain_path_r(const oscene* S, const owedge* const* E, int m, v3 T, v3
 static int chain_path(const oscene* S, const owedge* const* E, int m, v3 T, v3 R, int j, int first,
                       const or_params* P, opath* o) {
   const int nb = j >= 0 && first ? 1 : 0, na = j >= 0 && !first ? 1 : 0;
-  return chain_path_r(S, E, m, T, R, &j, nb, &j, na, P, o);
+  return chain_path_r(S, E, m, T, R, &j, nb, &j, na, P, o, NULL);
 }
 
 /* Paths Tx -> Q_1 -> ... -> Q_m -> Rx over m pairwise distinct wedges
@@ -2144,6 +2171,83 @@ int64_t or_diffract_multi(const float* tris, const int32_t* tri_mat, const int32
             kk[1] = m;
             for (int q = 0; q < width; ++q) kk[2 + q] = q < m ? ((int32_t)w[q] | OR_DIFF) : -1;
             paths_out[nvalid] = tmp;
+          }
+          nvalid++;
+        }
+  }
+  free(W);
+  scene_free(&S);
+  return nvalid;
+}
+
+/* Chains of m = 2 or 3 wedges (as or_diffract_multi) whose legs pass
+ * straight through transmitting triangles (Table II losses), at least one
+ * and at most max_trans crossings in all (and at most OR_MAX_REFL - m): the
+ * Keller points, rules and field of the chain, each crossing scaling the
+ * field by 10^(-L/20). Keys: rx, m + crossings, then in path order the
+ * crossings of each leg (| OR_TRANS) and the wedges (| OR_DIFF); -1 padded
+ * to 2 + width. Points in the same order. Chains with no crossing are
+ * or_diffract_multi's and are not written here. Returns the number of
+ * valid paths (may exceed cap). */
+int64_t or_diffract_multi_trans(const float* tris, const int32_t* tri_mat, const int32_t* tri_obj, int32_t ntri,
+                                const float* mats, int32_t nmat, const float* tx, const float* rx, int32_t nrx,
+                                const or_params* P, int32_t order, int32_t width, int32_t* keys_out,
+                                opath* paths_out, int64_t cap) {
+  if (order < 2 || order > 3 || width < order) return -1;
+  if (!P->trans_db || P->max_trans < 1) return 0;
+  oscene S;
+  if (scene_load(&S, tris, tri_mat, ntri, mats, nmat)) return -2;
+  owedge* W = NULL;
+  long nw = find_wedges(tris, tri_obj, ntri, &W);
+  const int m = order, none = -1;
+  v3 T = mk(tx[0], tx[1], tx[2]);
+  int64_t nvalid = 0;
+  long w[3] = {0, 0, 0};
+  opath tmp;
+  ocross cr;
+  for (int r = 0; r < nrx; ++r) {
+    v3 R = mk(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+    for (w[0] = 0; w[0] < nw; ++w[0])
+      for (w[1] = 0; w[1] < nw; ++w[1])
+        for (w[2] = 0; w[2] < (m == 3 ? nw : 1); ++w[2]) {
+          if (!chain_allowed(W, w, m)) continue;
+          const owedge* E[3] = {&W[w[0]], &W[w[1]], m == 3 ? &W[w[2]] : NULL};
+          cr.cap = P->max_trans < OR_MAX_REFL - m ? P->max_trans : OR_MAX_REFL - m;
+          if (!chain_path_r(&S, E, m, T, R, &none, 0, &none, 0, P, &tmp, &cr) || cr.total < 1) continue;
+          const int depth = m + cr.total;
+          if (nvalid < cap && depth <= width) {
+            int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
+            kk[0] = r;
+            kk[1] = depth;
+            /* path order: leg 0's crossings, w_1, leg 1's, .., w_m, leg m's */
+            v3 Pt[OR_MAX_REFL];
+            v3 ends[5];
+            ends[0] = T;
+            for (int i = 0; i < m; ++i) ends[i + 1] = mk(tmp.pts[i][0], tmp.pts[i][1], tmp.pts[i][2]);
+            ends[m + 1] = R;
+            int q = 0, c = 0;
+            for (int leg = 0; leg <= m; ++leg) {
+              v3 a0 = ends[leg], dl = sub(ends[leg + 1], ends[leg]);
+              for (int i = 0; i < cr.n[leg]; ++i, ++c, ++q) {
+                const otri* Tc = &S.t[cr.id[c]];
+                kk[2 + q] = cr.id[c] | OR_TRANS;
+                Pt[q] = add(a0, scl(dl, dot(sub(Tc->v[0], a0), Tc->n) / dot(dl, Tc->n)));
+              }
+              if (leg < m) {
+                kk[2 + q] = (int32_t)w[leg] | OR_DIFF;
+                Pt[q] = ends[leg + 1];
+                ++q;
+              }
+            }
+            for (int j = q; j < width; ++j) kk[2 + j] = -1;
+            opath* o = &paths_out[nvalid];
+            *o = tmp;
+            memset(o->pts, 0, sizeof(o->pts));
+            for (int j = 0; j < depth; ++j) {
+              o->pts[j][0] = Pt[j].x;
+              o->pts[j][1] = Pt[j].y;
+              o->pts[j][2] = Pt[j].z;
+            }
           }
           nvalid++;
         }
@@ -2243,7 +2347,7 @@ int64_t or_diffract_refl2(const float* tris, const int32_t* tri_mat, const int32
             const int na = 2 - nb;
             if (nb != 1 && j1 == j2) continue;
             const int j[2] = {j1, j2};
-            if (!chain_path_r(&S, E, 1, T, R, j, nb, j + nb, na, P, &tmp)) continue;
+            if (!chain_path_r(&S, E, 1, T, R, j, nb, j + nb, na, P, &tmp, NULL)) continue;
             if (nvalid < cap) {
               int32_t* kk = &keys_out[(size_t)nvalid * (2 + width)];
               kk[0] = r;
@@ -2513,7 +2617,7 @@ int32_t or_diffract_path(const float* tris, const int32_t* tri_mat, const int32_
   if (ok) {
     const owedge* E[3] = {&W[wi[0]], m > 1 ? &W[wi[1]] : NULL, m > 2 ? &W[wi[2]] : NULL};
     v3 T = mk(tx[0], tx[1], tx[2]), R = mk(rx[0], rx[1], rx[2]);
-    r = chain_path_r(&S, E, m, T, R, jb, nb, ja, na, P, o);
+    r = chain_path_r(&S, E, m, T, R, jb, nb, ja, na, P, o, NULL);
   }
   free(W);
   scene_free(&S);

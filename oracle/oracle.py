@@ -135,6 +135,9 @@ def lib():
         _lib.or_diffract_trans.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                            P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
         _lib.or_diffract_trans.restype = C.c_int64
+        _lib.or_diffract_multi_trans.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
+                                                 P(_Params), C.c_int32, C.c_int32, i32, C.c_void_p, C.c_int64]
+        _lib.or_diffract_multi_trans.restype = C.c_int64
         _lib.or_diffract_refl.argtypes = [f32, i32, i32, C.c_int32, f32, C.c_int32, f32, f32, C.c_int32,
                                           P(_Params), C.c_int32, i32, C.c_void_p, C.c_int64]
         _lib.or_diffract_refl.restype = C.c_int64
@@ -607,6 +610,31 @@ def diffract_trans(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleP
         raise RuntimeError(f"or_diffract_trans failed: {n}")
     if n > cap:
         raise RuntimeError(f"or_diffract_trans: {n} paths exceed capacity {cap}")
+    return keys[:n].copy(), paths[:n].copy()
+
+
+def diffract_multi_trans(world_tris, tri_mat, tri_obj, materials, tx, rx, prm: OracleParams, order: int,
+                         cap=1 << 20):
+    """Chains of ``order`` wedges (as diffract_multi) whose legs cross
+    penetrable triangles, at least one and at most prm.max_trans in all, the
+    field times 10^(-L/20) per crossing. Keys (rx, depth, then in path order
+    each leg's crossings | TRANS and the wedges | DIFF), -1 padded to 2 +
+    max(prm.width, order + prm.max_trans)."""
+    wt = _f32(world_tris).reshape(-1, 9)
+    mats = _f32(materials).reshape(-1, 3)
+    rx = _f32(rx).reshape(-1, 3)
+    width = max(prm.width, order + prm.max_trans)
+    keys = np.zeros((cap, 2 + width), np.int32)
+    paths = np.zeros(cap, PATH_DTYPE)
+    prm_c = prm.c()
+    n = lib().or_diffract_multi_trans(_p(wt, C.c_float), _p(_i32(tri_mat), C.c_int32), _p(_i32(tri_obj), C.c_int32),
+                                      wt.shape[0], _p(mats, C.c_float), mats.shape[0], _p(_f32(tx), C.c_float),
+                                      _p(rx, C.c_float), rx.shape[0], C.byref(prm_c), int(order), width,
+                                      _p(keys, C.c_int32), paths.ctypes.data_as(C.c_void_p), cap)
+    if n < 0:
+        raise RuntimeError(f"or_diffract_multi_trans failed: {n}")
+    if n > cap:
+        raise RuntimeError(f"or_diffract_multi_trans: {n} paths exceed capacity {cap}")
     return keys[:n].copy(), paths[:n].copy()
 
 

@@ -137,3 +137,51 @@ def test_reversed_direction_and_no_crossing():
     assert abs(_amp(p2[0]) - a2 * 10.0 ** (-(lw + lg) / 20.0)) <= 1e-12 * abs(a2)
     assert abs(p1[0]["len_m"] - p2[0]["len_m"]) <= 1e-12
     assert _run(O.diffract_trans, _scene([(0, 15.0, (10.0, 20.0), 3)]), _prm(2, lw, lg))[0].shape[0] == 0
+
+
+def _ridges(walls):
+    """The two metal ridges of the chain pins (tops along y at x = 0 and
+    x = 8, height 10) with _TM and _RM, plus walls as in _scene spanning y
+    in (-20, 20) and z in (0, 20)."""
+    from tests.test_oracle_pins import _RM, _TM, _ridge
+    tris = _ridge(0.0, 2.0, 10.0) + _ridge(8.0, 2.0, 10.0)
+    mats = [1] * len(tris)
+    for x, m in walls:
+        tris += scenes._quad((x, -20.0, 0.0), (x, 20.0, 0.0), (x, 20.0, 20.0), (x, -20.0, 20.0))
+        mats += [m, m]
+    materials = np.array([[5.31, 0.0326, 0.0], [1.0, 0.0, 1.0], [6.0, 0.0, 0.0], [4.0, 0.0, 0.0]], np.float32)
+    return scenes._static_scene("ridges_walls", tris, mats, _TM, (_RM,), materials=materials)
+
+
+def test_chain_through_walls_before_and_after():
+    """The order-2 chain over the two ridges with glass across its first leg
+    and an indoor wall across its last: the same Keller points and length as
+    without the walls, the amplitude times both losses, the key (glass, w1,
+    w2, wall) in path order; blocked for the plain chain, absent with one
+    transmission allowed or the wall opaque."""
+    lw, lg = _losses()
+    n = len(_ridges([]).tris)
+    base_k, base_p = O.diffract_multi(*_args(_ridges([]), O.OracleParams(freq_hz=28e9, max_refl=2)), 2)
+    assert base_k.shape[0] == 1
+    sc = _ridges([(-15.0, 3), (23.0, 2)])
+    prm = O.OracleParams(freq_hz=28e9, max_refl=2, max_trans=2, trans_db=(-1.0, -1.0, lw, lg))
+    assert O.diffract_multi(*_args(sc, prm), 2)[0].shape[0] == 0
+    k, p = O.diffract_multi_trans(*_args(sc, prm), 2)
+    assert k.shape[0] == 1 and k[0, 1] == 4
+    assert (k[0, 2] & O.TRANS) and (k[0, 2] & ~O.TRANS) in (n, n + 1)
+    assert k[0, 3] == base_k[0, 2] and k[0, 4] == base_k[0, 3]
+    assert (k[0, 5] & O.TRANS) and (k[0, 5] & ~O.TRANS) in (n + 2, n + 3)
+    assert np.allclose(p[0]["pts"][1], base_p[0]["pts"][0], atol=1e-9)
+    assert np.allclose(p[0]["pts"][2], base_p[0]["pts"][1], atol=1e-9)
+    assert abs(p[0]["pts"][0][0] + 15.0) <= 1e-9 and abs(p[0]["pts"][3][0] - 23.0) <= 1e-9
+    assert abs(p[0]["len_m"] - base_p[0]["len_m"]) <= 1e-9
+    a0 = _amp(base_p[0])
+    assert abs(_amp(p[0]) - a0 * 10.0 ** (-(lw + lg) / 20.0)) <= 1e-9 * abs(a0)
+    p1 = O.OracleParams(freq_hz=28e9, max_refl=2, max_trans=1, trans_db=(-1.0, -1.0, lw, lg))
+    assert O.diffract_multi_trans(*_args(sc, p1), 2)[0].shape[0] == 0
+    p2 = O.OracleParams(freq_hz=28e9, max_refl=2, max_trans=2, trans_db=(-1.0, -1.0, -1.0, lg))
+    assert O.diffract_multi_trans(*_args(sc, p2), 2)[0].shape[0] == 0
+
+
+def _args(sc, prm):
+    return (sc.tris.reshape(-1, 9), sc.tri_mat, sc.tri_obj, sc.materials, sc.tx, sc.rx[0], prm)

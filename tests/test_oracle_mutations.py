@@ -98,6 +98,9 @@ MUTANTS = [
     ("diffract_trans_crossings_reversed", "while (q > 0 && us[q - 1] > u)", "while (q > 0 && us[q - 1] < u)"),
     ("diffract_trans_opaque_crossed", "if (!P->trans_db || m < 0 || m >= S->nmat || P->trans_db[m] < 0) { bad = 1; continue; }",
      "if (!P->trans_db || m < 0 || m >= S->nmat) { bad = 1; continue; }"),
+    ("multi_trans_losses_dropped",
+     "for (int i = 0; i < cr->total; ++i) a *= pow(10.0, -P->trans_db[S->t[cr->id[i]].mat] / 20.0);", "(void)0;"),
+    ("multi_trans_limit_ignored", "cr->id + cr->total, cr->cap - cr->total);", "cr->id + cr->total, OR_MAX_REFL - m - cr->total);"),
     ("spherical_spreading", "double complex A = csqrt(rhoe / (s * (rhoe + s))) * cexp(-I * k * s);",
      "double complex A = csqrt(ell[0] / (s * (ell[0] + s))) * cexp(-I * k * s);"),
 ]
