@@ -501,7 +501,8 @@ def frame(scene, f: int, rays: np.ndarray, prm: OracleParams, seg_od=False) -> F
     (with prm.diffraction, the diffraction paths -- first order, chains up to
     prm.diffraction_order, and with transmission first-order paths whose
     legs cross penetrable triangles -- join the validated keys before the
-    reduction)."""
+    reduction; chains through penetrable triangles, diffract_multi_trans,
+    are not part of the frame)."""
     wt = transform(scene.tris, scene.tri_obj, scene.xf[f] if scene.nobj else np.zeros((0, 12)))
     rx = scene.rx[f]
     tr = trace(wt, scene.tri_mat, scene.materials, scene.tx, rays, rx, prm, seg_od=seg_od)

@@ -880,13 +880,13 @@ __device__ __forceinline__ void tri64(const PathArgs& a, int id, d3w& v0, d3w& v
   mat = a.mats[__float_as_int(p1.w)];
 }
 
-// The triangles (other than ex0, ex1) that the open segment p -> q crosses
+// The triangles (other than ex0 .. ex3) that the open segment p -> q crosses
 // with parameter in (eps_occ, 1 - eps_occ) (FP32 traversal of the scene, as
 // any_hit), in order along it: their ids in ids[0 .. n-1]. Returns n, or -1
 // when one of them is opaque (a material without penetration loss, loss <
 // 0) or there are more than cap (the transmissions a path has left).
-__device__ __noinline__ int leg_crossings(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, int* ids, int cap,
-                                          unsigned& ovf, TStack& st) {
+__device__ __noinline__ int leg_crossings(const PathArgs& a, d3w p, d3w q, int ex0, int ex1, int ex2, int ex3,
+                                          int* ids, int cap, unsigned& ovf, TStack& st) {
   const Bvh& bvh = a.bvh;
   const d3w dv = q - p;
   const RayPre r = ray_pre(f3((float)p.x, (float)p.y, (float)p.z), f3((float)dv.x, (float)dv.y, (float)dv.z));
@@ -930,7 +930,8 @@ __device__ __noinline__ int leg_crossings(const PathArgs& a, d3w p, d3w q, int e
       load_tri(bvh.tris, slot, v0, v1, v2, id);
       float t;
       cur = kEmpty;
-      if (id == ex0 || id == ex1 || !tri_hit(r, v0, v1, v2, t) || !(t > t0 && t < t1)) continue;
+      if (id == ex0 || id == ex1 || id == ex2 || id == ex3 || !tri_hit(r, v0, v1, v2, t) || !(t > t0 && t < t1))
+        continue;
       const float loss = a.mats[__float_as_int(__ldg(&bvh.tris[3 * slot + 1]).w)].w;
       if (!(loss >= 0.0f) || n >= cap || n >= kMaxRefl) return -1;
       int k = n++;  // insertion in order along the segment
@@ -1070,9 +1071,9 @@ __device__ __forceinline__ void diffract_pair(const PathArgs& a, long idx, doubl
   int c1[kMaxRefl], c2[kMaxRefl], n1 = 0, n2 = 0;
   if (a.max_trans > 0) {
     const int mt = min(a.max_trans, kMaxRefl - 1);  // the wedge takes one of the record's slots
-    n1 = leg_crossings(a, T, Q, W.ta, W.tb, c1, mt, ovf, st);
+    n1 = leg_crossings(a, T, Q, W.ta, W.tb, W.tb, W.tb, c1, mt, ovf, st);
     if (n1 < 0) return;
-    n2 = leg_crossings(a, Q, R, W.ta, W.tb, c2, mt - n1, ovf, st);
+    n2 = leg_crossings(a, Q, R, W.ta, W.tb, W.tb, W.tb, c2, mt - n1, ovf, st);
     if (n2 < 0) return;
   } else if (leg_occluded(a, T, Q, W.ta, W.tb, ovf, st) || leg_occluded(a, Q, R, W.ta, W.tb, ovf, st)) {
     return;
