@@ -106,4 +106,3 @@ def test_random_penetrable_boxes(cuda, seed):
     from tests.test_gpu_diffraction_multi import _boxes
     sc = _boxes(seed)
     _check(cuda, sc, (10.0, -1.0), 2, max_refl=2, least=1)
-
